@@ -1,0 +1,57 @@
+"""Small synthetic scenes used by the tests (geometry only)."""
+import numpy as np
+
+from paper_2605_24339_b300 import scenes as S
+
+
+def flat_over_big_triangle(nq=2, dx=1e-3, gap=3e-5, dhat=1e-4, rest_gap=1e-3,
+                           kappa=1e5, face_only=True, L=1):
+    """A flat pad (bottom at z=0, normal -z) over one large master triangle
+    facing +z.  The master sits ``rest_gap`` below at t=0 (Y0) and ``gap``
+    below in the returned current configuration xm."""
+    X, tets, bot, top = S.pad_slab(nq, nq, 1, dx, dx, origin=(0.0, 0.0, 0.0))
+    side = nq * dx
+    c = side / 2
+    R = 40 * side
+    Y0 = np.array([[c - R, c - R, -rest_gap], [c + 2 * R, c - R, -rest_gap],
+                   [c - R, c + 2 * R, -rest_gap]])
+    F = np.array([[0, 1, 2]], dtype=np.int32)
+    p = S.default_params(dhat=dhat, kappa=kappa, face_rule_level=L)
+    if face_only:
+        p["kappa_edge"] = 0.0
+        p["kappa_point"] = 0.0
+    p = S._finish_params(p, X, bot)
+    sc = S._single_env(X, tets, bot, top.astype(np.uint8), Y0, F, np.zeros_like(X), p,
+                       "flat", 1)
+    xm = Y0.copy()
+    xm[:, 2] = -gap
+    return sc, X.copy(), xm
+
+
+def small_indent(n_quads=8, subdiv=2, press=0.15e-3, seed=1, L=1, dhat=1e-4):
+    """Reduced tactile_indent scene plus a draped (pressed) pad state."""
+    sc = S.tactile_indent(n_quads=n_quads, side=n_quads * 0.5e-3, nz=2, thick=1e-3,
+                          sphere_subdiv=subdiv, radius=2e-3, seed=seed,
+                          face_rule_level=L, dhat=dhat)
+    x = S.drape_on_master(sc, press, seed=seed + 10)
+    return sc, x
+
+
+def rotation(seed):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def load_golden(name):
+    rows = []
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            rows.append([float(v) for v in line.split()])
+    return np.array(rows)
