@@ -1,0 +1,229 @@
+/*
+ * gmcp.h -- C ABI of libgmcp: the per-Newton-iteration contact pass of
+ * incremental potential contact under the Geometric Mortar Contact Potential
+ * (GMCP) of IsaacIPC (arXiv 2605.24339), on one NVIDIA B300 (sm_103a).
+ *
+ * Problem statement followed (paper Sec. 2.1 and Sec. 4): minimise
+ *   E(x) = 1/2 (x - xhat)^T M (x - xhat) + h^2 (Psi_elastic(x) + Psi_GMCP(x))
+ * over the pad positions x, subject to an intersection-free trajectory, with
+ *   Psi_GMCP = sum_q sum_k kappa_q w_k gamma_k B(g_k, eps_k)   (Eq. gmcp_potential)
+ * over face, edge and point samples of the slave (tactile) surface (Sec. 4.1),
+ * gamma from the C1 Hermite step (Sec. 4.3, Eqs. smoothstep, gamma), eps_k the
+ * adaptive support radius (Sec. 4.4, Eq. adaptive_eps), B the IPC log barrier
+ * -(g-eps)^2 ln(g/eps), and the step bound of Sec. 4.5 (Eqs. ccd, global_ccd)
+ * combined with additive CCD.
+ *
+ * Conventions for every entry point
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; host
+ *    pointers are named *_host or are plain structs.  Positions are
+ *    contiguous FP64 [n][3] (x, y, z per vertex).
+ *  - All GPU work is queued on params.stream (a cudaStream_t; NULL = the
+ *    legacy default stream).  Calls that return a host scalar synchronise
+ *    that stream.
+ *  - Nothing throws across the ABI.  Every call returns an ipc_status; on
+ *    failure the text of the error is available from ipc_last_error(ctx)
+ *    and caller-owned outputs are left unchanged unless stated otherwise.
+ *  - One context per host thread; a context is not reentrant.
+ *  - The library has no CPU fallback: a call on a machine without a usable
+ *    CUDA device fails with IPC_ERR_CUDA.
+ */
+#ifndef GMCP_H
+#define GMCP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IPC_OK = 0,
+    IPC_ERR_ARG = 1,            /* invalid argument (NULL, size, layout) */
+    IPC_ERR_CUDA = 2,           /* CUDA runtime error or no usable device */
+    IPC_ERR_OOM = 3,            /* device allocation failed */
+    IPC_ERR_INFEASIBLE = 4,     /* non-positive gap, inverted tet or touching pair */
+    IPC_ERR_CAPACITY = 5,       /* a fixed-capacity buffer overflowed */
+    IPC_ERR_NOT_CONVERGED = 6,  /* Newton hit max_newton (x holds the last iterate) */
+    IPC_ERR_LINESEARCH = 7,     /* backtracking exhausted max_halvings */
+    IPC_ERR_TIMEOUT = 8         /* a device loop hit its iteration cap */
+} ipc_status;
+
+typedef enum { IPC_PREC_FP64 = 0, IPC_PREC_MIXED = 1 } ipc_precision;
+
+/* Parameters (SI units).  Paper constants: dhat is eps_max of Eq.
+ * (adaptive_eps); kappa, kappa_edge, kappa_point are kappa_q for q = face,
+ * edge, point in Eq. (gmcp_potential); delta_T, delta_e the transition widths
+ * of Sec. 4.3.  face_rule_level L gives 4^L face samples per slave triangle. */
+typedef struct {
+    int32_t precision;          /* ipc_precision */
+    double dhat, kappa, kappa_edge, kappa_point, delta_T, delta_e;
+    int32_t face_rule_level;    /* 1 (4 samples/tri) or 2 (16 samples/tri) */
+    double h, density, youngs, poisson, gravity[3];
+    double newton_tol, pcg_rel_tol;
+    int32_t max_newton, max_pcg, max_halvings;
+    double ccd_slack;           /* ACCD stop fraction s in (0,1) */
+    int32_t ccd_max_iter;       /* ACCD iteration cap per primitive pair */
+    double dhat_guard, kappa_guard;  /* primitive guard barrier; kappa_guard 0 = off */
+    int32_t device;             /* CUDA device ordinal */
+    void* stream;               /* cudaStream_t */
+} ipc_params;
+
+/* Scene: a batch of independent environments concatenated; indices are
+ * global.  All arrays are HOST arrays read during ipc_create only. */
+typedef struct {
+    int32_t n_env;
+    const int64_t* env_vert_off;    /* [n_env+1] pad vertex ranges */
+    const int64_t* env_tet_off;     /* [n_env+1] */
+    const int64_t* env_stri_off;    /* [n_env+1] slave triangle ranges */
+    const int64_t* env_mvert_off;   /* [n_env+1] master vertex ranges */
+    const int64_t* env_mtri_off;    /* [n_env+1] master triangle ranges */
+    int64_t n_vert, n_tet, n_stri, n_mvert, n_mtri;
+    const double* pad_rest;         /* [n_vert][3] rest positions X */
+    const int32_t* tets;            /* [n_tet][4] positive volume at rest */
+    const int32_t* s_tris;          /* [n_stri][3] slave triangles, normal toward the master */
+    const uint8_t* dirichlet;       /* [n_vert] 1 = prescribed vertex */
+    const double* m_rest;           /* [n_mvert][3] master positions at t = 0 */
+    const int32_t* m_tris;          /* [n_mtri][3] master triangles, outward */
+} ipc_scene;
+
+typedef struct ipc_ctx ipc_ctx;
+
+/* Candidate-pair counts of the last broad phase (Sec. 4.1 features). */
+typedef struct {
+    int64_t face;     /* (slave tri, master tri) pairs */
+    int64_t edge;     /* (slave tri, master edge) pairs */
+    int64_t point;    /* (slave tri, master vertex) pairs */
+    int32_t max_per_tri[3];   /* largest per-triangle list of each kind */
+} ipc_candidate_counts;
+
+/* Active-sample counts of the last contact evaluation. */
+typedef struct {
+    int64_t face, edge, point, guard;
+    int64_t face_evaluated;   /* (face sample, candidate) pairs tested */
+} ipc_sample_counts;
+
+/* View of a context-owned block-sparse (3x3) matrix.  Valid until the next
+ * call on the context.  vals is FP64 [nnzb][3][3] (row-major blocks) in
+ * IPC_PREC_FP64 and FP32 in IPC_PREC_MIXED. */
+typedef struct {
+    int64_t n_rows;
+    int64_t nnzb;
+    const int32_t* row_ptr_dev;     /* [n_rows+1] */
+    const int32_t* col_idx_dev;     /* [nnzb] */
+    const void* vals_dev;
+    int32_t dtype;                  /* 0 = FP64, 1 = FP32 */
+} ipc_bsr_view;
+
+typedef struct {
+    double alpha;          /* min(1, alpha_lin, alpha_accd) */
+    double alpha_lin;      /* Eq. (global_ccd); +inf when no sample closes */
+    double alpha_accd;     /* additive CCD minimum over primitive pairs */
+    int64_t n_pairs_pt, n_pairs_ee;
+    int32_t iter_cap_hit;  /* 1 if some pair stopped at ccd_max_iter */
+} ipc_ccd_info;
+
+typedef struct {
+    int32_t newton_iters, pcg_iters_total, line_search_halvings;
+    double residual;       /* final ||G_free|| / max(||G_free(x~)||, floor) */
+    double alpha0;         /* CCD fraction admitted for the predictor */
+    double energy;
+    double ms_total;
+} ipc_step_stats;
+
+/* ---------------------------------------------------------------------- */
+
+/* Create a context on params->device: copies the scene to the device,
+ * builds the derived topology (master edges, adjacency, ownership, BSR
+ * patterns) and sizes the broad-phase grid from the rest positions.
+ * *out receives the context (NULL on failure).  The params are copied. */
+ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx** out);
+
+/* Release every device and host resource of the context.  NULL is a no-op. */
+void ipc_destroy(ipc_ctx* ctx);
+
+/* Text of the last error on this context (never NULL; "" when none).  With
+ * ctx == NULL: the last error of a failed ipc_create on this thread. */
+const char* ipc_last_error(const ipc_ctx* ctx);
+
+/* Broad phase (spatial hash), Sec. 4.1's features within eps_max = dhat:
+ * candidate (slave tri, master tri / edge / vertex) pairs for the
+ * configuration x_dev [n_vert][3], xm_dev [n_mvert][3] (device).  Face
+ * pairs: some face sample of the slave tri lies in the master tri's box
+ * grown by dhat; edge and point pairs: the slave tri's vertex box overlaps
+ * the master feature's box grown by dhat.  Pairs never cross environments.
+ * The lists are stored in the context, sorted per slave triangle; the
+ * per-triangle capacities grow automatically (the query is then repeated).
+ * counts (host, may be NULL) receives totals and synchronises the stream. */
+ipc_status ipc_candidates(ipc_ctx* ctx, const double* x_dev, const double* xm_dev,
+                          ipc_candidate_counts* counts);
+
+/* Copy the last candidate list of kind 0 (face), 1 (edge) or 2 (point) to
+ * pairs_host [capacity][2] as (slave tri, master feature) sorted
+ * lexicographically; master edges are numbered in the lexicographic order
+ * of their (min, max) vertex pairs.  *n_out receives the count; with
+ * pairs_host == NULL only the count is returned.  IPC_ERR_CAPACITY if
+ * capacity is too small (nothing written).  Synchronous. */
+ipc_status ipc_candidates_copy(ipc_ctx* ctx, int32_t kind, int32_t* pairs_host, int64_t capacity,
+                               int64_t* n_out);
+
+/* Contact pass at (x_dev, xm_dev), Sec. 4.1-4.4: runs the broad phase,
+ * builds the face, edge and point samples and evaluates Eq.
+ * (gmcp_potential) with the gradient and the PSD Gauss-Newton Hessian of
+ * Sec. 4.2 (per-sample coefficient clamped at zero).
+ *  energy_dev  (device FP64 scalar, may be NULL) receives Psi;
+ *  energy_host (host, may be NULL) receives Psi and synchronises;
+ *  grad_dev    (device, may be NULL) receives dPsi/dx [n_vert][3], FP64 in
+ *              IPC_PREC_FP64 and FP32 in IPC_PREC_MIXED (the master is
+ *              kinematic: its rows are not formed);
+ *  hess        (host struct, may be NULL) receives a view of the contact
+ *              Hessian in BSR form over the pad vertices (the pattern holds
+ *              every vertex pair of every slave triangle);
+ *  counts      (host, may be NULL) receives active-sample counts and
+ *              synchronises.
+ * Gradient and Hessian are assembled by deterministic gathers (no float
+ * atomics): repeated calls give bitwise identical results. */
+ipc_status ipc_barrier_eval(ipc_ctx* ctx, const double* x_dev, const double* xm_dev,
+                            double* energy_dev, double* energy_host, void* grad_dev,
+                            ipc_bsr_view* hess, ipc_sample_counts* counts);
+
+/* Largest admissible step for the motion x -> x + alpha dx (pad) and
+ * xm0 -> xm0 + alpha (xm1 - xm0) (master; xm1_dev NULL = static master):
+ * alpha = min(1, alpha_lin, alpha_accd), alpha_lin from Eqs. (ccd) and
+ * (global_ccd) over the active samples at (x, xm0) (rounded down by a
+ * relative 1e-10 so that rounding-order differences can only shrink it),
+ * alpha_accd the additive-CCD minimum (Li et al. 2021, Alg. 1) over
+ * primitive pairs (slave surface vertex / master tri, master vertex / slave
+ * tri, slave edge / master edge) whose swept boxes overlap.  alpha_host
+ * receives alpha and synchronises; info (host) may be NULL. */
+ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_dev,
+                            const double* xm0_dev, const double* xm1_dev, double* alpha_host,
+                            ipc_ccd_info* info);
+
+/* One implicit-Euler time step (paper Sec. 2.1 problem statement): x_dev
+ * [n_vert][3] holds x^t on entry and x^{t+1} on exit, v_dev the velocity
+ * (Dirichlet vertices move to x + h v).  xm_next_dev: master at t+1 (NULL =
+ * unchanged).  dx_pred_dev: a predicted displacement used as the Newton
+ * start after CCD filtering (NULL = x + h v).  stats (host) may be NULL.
+ * On IPC_ERR_INFEASIBLE / IPC_ERR_LINESEARCH x and v are restored. */
+ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
+                           const double* dx_pred_dev, ipc_step_stats* stats);
+
+/* Section profiler (not part of the method): CUDA events recorded on the
+ * context stream around each group of launches (grid build, candidate
+ * query, sample kernel, gathers, reductions, step bounds).
+ *  mode 1: reset the totals and start recording;
+ *  mode 0: stop recording;
+ *  mode 2: synchronise on the recorded events and report, for up to
+ *          max_sections sections, the name (names_host, 32 bytes each,
+ *          NUL-terminated), the summed milliseconds (ms_host) and the number
+ *          of recorded calls (calls_host); *n_sections receives the count.
+ * Recording adds two event records per section and no synchronisation. */
+ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* names_host,
+                       double* ms_host, int64_t* calls_host, int32_t* n_sections);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GMCP_H */

@@ -309,12 +309,13 @@ static void tri_box(const double* P, const int32_t* t, double* lo, double* hi) {
  *         dhat overlaps the slave tri's vertex box.
  * Pairs are restricted to one env and returned sorted lexicographically.
  * Caller frees *out with orc_free. */
-ORC_API int64_t orc_candidates(const orc_scene* s, int kind, const double* x, const double* xm,
-                               int32_t** out) {
+static int64_t candidates_sub(const orc_scene* s, int kind, const double* x, const double* xm,
+                              const char* want, int32_t** out) {
     ivec v = {0, 0, 0};
     double eps = s->dhat;
     double* samp = (double*)malloc(sizeof(double) * 3 * (size_t)s->nk);
     for (int t = 0; t < s->ns; ++t) {
+        if (want && !want[t]) continue;
         const int32_t* T = s->stri + 3 * t;
         const double *x0 = x + 3 * T[0], *x1 = x + 3 * T[1], *x2 = x + 3 * T[2];
         int e = s->stri_env[t];
@@ -359,6 +360,11 @@ ORC_API int64_t orc_candidates(const orc_scene* s, int kind, const double* x, co
     qsort(v.a, (size_t)(v.n / 2), 2 * sizeof(int32_t), cmp_pair);
     *out = v.a;
     return v.n / 2;
+}
+
+ORC_API int64_t orc_candidates(const orc_scene* s, int kind, const double* x, const double* xm,
+                               int32_t** out) {
+    return candidates_sub(s, kind, x, xm, NULL, out);
 }
 
 ORC_API void orc_free(void* p) { free(p); }
@@ -606,7 +612,7 @@ static void collect_samples(const orc_scene* s, const double* x, const double* x
     else memset(want, 1, (size_t)s->ns);
     for (int kind = 0; kind < 3; ++kind) {
         int32_t* pairs = NULL;
-        int64_t np = orc_candidates(s, kind, x, xm, &pairs);
+        int64_t np = candidates_sub(s, kind, x, xm, want, &pairs);
         for (int64_t p = 0; p < np; ++p) {
             int t = pairs[2 * p], f = pairs[2 * p + 1];
             if (!want[t]) continue;

@@ -1,0 +1,313 @@
+"""Thin ctypes binding of libgmcp (C ABI in include/gmcp.h).
+
+Argument marshalling only: every step of the contact pass runs in the CUDA
+library.  PyTorch supplies device memory and the stream.  There is no CPU
+fallback: :func:`lib` raises if the library has not been built, and the
+library itself fails with IPC_ERR_CUDA when no usable device is present.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+from typing import Optional
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libgmcp.so")
+HEADER = os.path.join(os.path.dirname(PKG), "include", "gmcp.h")
+
+STATUS = {0: "IPC_OK", 1: "IPC_ERR_ARG", 2: "IPC_ERR_CUDA", 3: "IPC_ERR_OOM",
+          4: "IPC_ERR_INFEASIBLE", 5: "IPC_ERR_CAPACITY", 6: "IPC_ERR_NOT_CONVERGED",
+          7: "IPC_ERR_LINESEARCH", 8: "IPC_ERR_TIMEOUT"}
+PREC = {"fp64": 0, "mixed": 1}
+
+
+class GmcpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("dhat", C.c_double), ("kappa", C.c_double),
+                ("kappa_edge", C.c_double), ("kappa_point", C.c_double), ("delta_T", C.c_double),
+                ("delta_e", C.c_double), ("face_rule_level", C.c_int32), ("h", C.c_double),
+                ("density", C.c_double), ("youngs", C.c_double), ("poisson", C.c_double),
+                ("gravity", C.c_double * 3), ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double),
+                ("max_newton", C.c_int32), ("max_pcg", C.c_int32), ("max_halvings", C.c_int32),
+                ("ccd_slack", C.c_double), ("ccd_max_iter", C.c_int32), ("dhat_guard", C.c_double),
+                ("kappa_guard", C.c_double), ("device", C.c_int32), ("stream", C.c_void_p)]
+
+
+class SceneC(C.Structure):
+    _fields_ = [("n_env", C.c_int32), ("env_vert_off", C.c_void_p), ("env_tet_off", C.c_void_p),
+                ("env_stri_off", C.c_void_p), ("env_mvert_off", C.c_void_p),
+                ("env_mtri_off", C.c_void_p), ("n_vert", C.c_int64), ("n_tet", C.c_int64),
+                ("n_stri", C.c_int64), ("n_mvert", C.c_int64), ("n_mtri", C.c_int64),
+                ("pad_rest", C.c_void_p), ("tets", C.c_void_p), ("s_tris", C.c_void_p),
+                ("dirichlet", C.c_void_p), ("m_rest", C.c_void_p), ("m_tris", C.c_void_p)]
+
+
+class CandCounts(C.Structure):
+    _fields_ = [("face", C.c_int64), ("edge", C.c_int64), ("point", C.c_int64),
+                ("max_per_tri", C.c_int32 * 3)]
+
+
+class SampleCounts(C.Structure):
+    _fields_ = [("face", C.c_int64), ("edge", C.c_int64), ("point", C.c_int64),
+                ("guard", C.c_int64), ("face_evaluated", C.c_int64)]
+
+
+class BsrView(C.Structure):
+    _fields_ = [("n_rows", C.c_int64), ("nnzb", C.c_int64), ("row_ptr_dev", C.c_void_p),
+                ("col_idx_dev", C.c_void_p), ("vals_dev", C.c_void_p), ("dtype", C.c_int32)]
+
+
+class CcdInfo(C.Structure):
+    _fields_ = [("alpha", C.c_double), ("alpha_lin", C.c_double), ("alpha_accd", C.c_double),
+                ("n_pairs_pt", C.c_int64), ("n_pairs_ee", C.c_int64), ("iter_cap_hit", C.c_int32)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("pcg_iters_total", C.c_int32),
+                ("line_search_halvings", C.c_int32), ("residual", C.c_double),
+                ("alpha0", C.c_double), ("energy", C.c_double), ("ms_total", C.c_double)]
+
+
+_lib = None
+
+
+def header_symbols():
+    """Names of the functions declared in include/gmcp.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ipc_[a-z_0-9]+)\s*\(", txt)))
+
+
+def lib():
+    """Load libgmcp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -m paper_2605_24339_b300.build`")
+    L = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    L.ipc_create.restype = C.c_int
+    L.ipc_create.argtypes = [C.POINTER(Params), C.POINTER(SceneC), C.POINTER(P)]
+    L.ipc_destroy.restype = None; L.ipc_destroy.argtypes = [P]
+    L.ipc_last_error.restype = C.c_char_p; L.ipc_last_error.argtypes = [P]
+    L.ipc_candidates.restype = C.c_int
+    L.ipc_candidates.argtypes = [P, P, P, C.POINTER(CandCounts)]
+    L.ipc_candidates_copy.restype = C.c_int
+    L.ipc_candidates_copy.argtypes = [P, C.c_int32, P, C.c_int64, C.POINTER(C.c_int64)]
+    L.ipc_barrier_eval.restype = C.c_int
+    L.ipc_barrier_eval.argtypes = [P, P, P, P, C.POINTER(C.c_double), P, C.POINTER(BsrView),
+                                   C.POINTER(SampleCounts)]
+    L.ipc_ccd_max_step.restype = C.c_int
+    L.ipc_ccd_max_step.argtypes = [P, P, P, P, P, C.POINTER(C.c_double), C.POINTER(CcdInfo)]
+    L.ipc_profile.restype = C.c_int
+    L.ipc_profile.argtypes = [P, C.c_int32, C.c_int32, P, P, P, C.POINTER(C.c_int32)]
+    L.ipc_newton_step.restype = C.c_int
+    L.ipc_newton_step.argtypes = [P, P, P, P, P, C.POINTER(StepStats)]
+    _lib = L
+    return L
+
+
+def make_params(p: dict, precision="fp64", device=0, stream=0) -> Params:
+    q = Params()
+    q.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    for k in ("dhat", "kappa", "kappa_edge", "kappa_point", "delta_T", "delta_e", "h", "density",
+              "youngs", "poisson", "newton_tol", "pcg_rel_tol", "ccd_slack"):
+        setattr(q, k, float(p[k]))
+    q.face_rule_level = int(p["face_rule_level"])
+    q.gravity = (C.c_double * 3)(*[float(v) for v in p["gravity"]])
+    q.max_newton, q.max_pcg = int(p["max_newton"]), int(p["max_pcg"])
+    q.max_halvings = int(p["max_halvings"])
+    q.ccd_max_iter = int(p["ccd_max_iter"])
+    q.dhat_guard = float(p.get("dhat_guard") or 0.0)
+    q.kappa_guard = float(p.get("kappa_guard") or 0.0)
+    q.device = int(device)
+    q.stream = C.c_void_p(int(stream)) if stream else None
+    return q
+
+
+def scene_struct(scene):
+    """(SceneC, keep-alive dict) of host arrays for ipc_create."""
+    k = dict(
+        ev=np.ascontiguousarray(scene.env_vert_off, dtype=np.int64),
+        et=np.ascontiguousarray(scene.env_tet_off, dtype=np.int64),
+        es=np.ascontiguousarray(scene.env_stri_off, dtype=np.int64),
+        emv=np.ascontiguousarray(scene.env_mvert_off, dtype=np.int64),
+        emt=np.ascontiguousarray(scene.env_mtri_off, dtype=np.int64),
+        X=np.ascontiguousarray(scene.X, dtype=np.float64),
+        T=np.ascontiguousarray(scene.tets, dtype=np.int32),
+        S=np.ascontiguousarray(scene.stris, dtype=np.int32),
+        D=np.ascontiguousarray(scene.dirichlet, dtype=np.uint8),
+        Y=np.ascontiguousarray(scene.Y0, dtype=np.float64),
+        M=np.ascontiguousarray(scene.mtris, dtype=np.int32))
+    sc = SceneC()
+    sc.n_env = int(len(k["ev"]) - 1)
+    sc.env_vert_off, sc.env_tet_off = k["ev"].ctypes.data, k["et"].ctypes.data
+    sc.env_stri_off, sc.env_mvert_off = k["es"].ctypes.data, k["emv"].ctypes.data
+    sc.env_mtri_off = k["emt"].ctypes.data
+    sc.n_vert, sc.n_tet, sc.n_stri = k["X"].shape[0], k["T"].shape[0], k["S"].shape[0]
+    sc.n_mvert, sc.n_mtri = k["Y"].shape[0], k["M"].shape[0]
+    sc.pad_rest, sc.tets, sc.s_tris = k["X"].ctypes.data, k["T"].ctypes.data, k["S"].ctypes.data
+    sc.dirichlet, sc.m_rest, sc.m_tris = k["D"].ctypes.data, k["Y"].ctypes.data, k["M"].ctypes.data
+    return sc, k
+
+
+class _CudaArray:
+    """Zero-copy wrapper of context-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
+                                         "data": (int(ptr), True), "version": 3, "strides": None}
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One libgmcp context over a :class:`scenes.Scene` on ``device``.
+
+    Positions passed to the methods are torch CUDA tensors (or arrays that are
+    copied to the device), FP64 contiguous ``[n,3]``.  Work is queued on the
+    torch stream current at construction."""
+
+    def __init__(self, scene, precision="fp64", device=0, params: Optional[dict] = None,
+                 stream=None):
+        import torch
+        self.torch = torch
+        L = lib()
+        p = dict(scene.params)
+        if params:
+            p.update(params)
+        self.params = p
+        self.precision = precision
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        sc, self._keep = scene_struct(scene)
+        self._prm = make_params(p, precision, device, stream.cuda_stream)
+        h = C.c_void_p()
+        st = L.ipc_create(C.byref(self._prm), C.byref(sc), C.byref(h))
+        if st != 0:
+            raise GmcpError(st, L.ipc_last_error(None).decode())
+        self.h = h
+        self.nv, self.ns, self.nmv = sc.n_vert, sc.n_stri, sc.n_mvert
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ipc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise GmcpError(st, lib().ipc_last_error(self.h).decode())
+
+    def _as(self, a):
+        t = self.torch
+        if a is None:
+            return None
+        if not isinstance(a, t.Tensor):
+            a = t.as_tensor(np.asarray(a, dtype=np.float64))
+        return a.to(device=self.device, dtype=t.float64).contiguous()
+
+    # -- broad phase -------------------------------------------------------
+    def candidates(self, x, xm):
+        x, xm = self._as(x), self._as(xm)
+        cc = CandCounts()
+        self._check(lib().ipc_candidates(self.h, _ptr(x), _ptr(xm), C.byref(cc)))
+        return dict(face=cc.face, edge=cc.edge, point=cc.point, max_per_tri=tuple(cc.max_per_tri))
+
+    def candidate_pairs(self, kind: int) -> np.ndarray:
+        n = C.c_int64()
+        self._check(lib().ipc_candidates_copy(self.h, kind, None, 0, C.byref(n)))
+        out = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+        self._check(lib().ipc_candidates_copy(self.h, kind, out.ctypes.data, n.value, C.byref(n)))
+        return out[: n.value]
+
+    # -- contact pass ------------------------------------------------------
+    def barrier_eval(self, x, xm, grad=True, hess=True, counts=True, energy_dev=None, grad_out=None):
+        t = self.torch
+        x, xm = self._as(x), self._as(xm)
+        gdt = t.float32 if self.precision == "mixed" else t.float64
+        g = grad_out
+        if g is None and grad:
+            g = t.empty((self.nv, 3), dtype=gdt, device=self.device)
+        e = C.c_double()
+        bv = BsrView()
+        sc = SampleCounts()
+        self._check(lib().ipc_barrier_eval(self.h, _ptr(x), _ptr(xm), _ptr(energy_dev),
+                                           None if energy_dev is not None else C.byref(e), _ptr(g),
+                                           C.byref(bv) if hess else None,
+                                           C.byref(sc) if counts else None))
+        out = dict(energy=e.value if energy_dev is None else None, grad=g)
+        if counts:
+            out["counts"] = dict(face=sc.face, edge=sc.edge, point=sc.point, guard=sc.guard,
+                                 face_evaluated=sc.face_evaluated)
+        if hess:
+            out["hess"] = self.bsr(bv)
+        return out
+
+    def bsr(self, bv: BsrView):
+        """Copies of a BSR view as torch tensors (row_ptr, col_idx, vals [nnzb,3,3])."""
+        t = self.torch
+        rp = t.as_tensor(_CudaArray(bv.row_ptr_dev, (bv.n_rows + 1,), "<i4"), device=self.device).clone()
+        ci = t.as_tensor(_CudaArray(bv.col_idx_dev, (bv.nnzb,), "<i4"), device=self.device).clone()
+        ts = "<f4" if bv.dtype == 1 else "<f8"
+        vals = t.as_tensor(_CudaArray(bv.vals_dev, (bv.nnzb, 3, 3), ts), device=self.device).clone()
+        return rp, ci, vals
+
+    def ccd_max_step(self, x, dx, xm0, xm1=None):
+        x, dx, xm0, xm1 = self._as(x), self._as(dx), self._as(xm0), self._as(xm1)
+        a = C.c_double()
+        info = CcdInfo()
+        self._check(lib().ipc_ccd_max_step(self.h, _ptr(x), _ptr(dx), _ptr(xm0), _ptr(xm1),
+                                           C.byref(a), C.byref(info)))
+        return dict(alpha=info.alpha, alpha_lin=info.alpha_lin, alpha_accd=info.alpha_accd,
+                    n_pt=info.n_pairs_pt, n_ee=info.n_pairs_ee, iter_cap_hit=bool(info.iter_cap_hit))
+
+    # -- profiling ---------------------------------------------------------
+    def profile_start(self):
+        self._check(lib().ipc_profile(self.h, 1, 0, None, None, None, None))
+
+    def profile_stop(self):
+        self._check(lib().ipc_profile(self.h, 0, 0, None, None, None, None))
+
+    def profile_read(self):
+        n = C.c_int32()
+        K = 16
+        names = C.create_string_buffer(32 * K)
+        ms = (C.c_double * K)()
+        calls = (C.c_int64 * K)()
+        self._check(lib().ipc_profile(self.h, 2, K, names, ms, calls, C.byref(n)))
+        out = {}
+        for i in range(min(n.value, K)):
+            nm = names.raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
+            out[nm] = dict(ms=ms[i], calls=calls[i])
+        return out
+
+    def newton_step(self, x, v, xm_next=None, dx_pred=None):
+        """In-place implicit-Euler step on x, v (torch FP64 CUDA tensors)."""
+        st = StepStats()
+        self._check(lib().ipc_newton_step(self.h, _ptr(x), _ptr(v), _ptr(self._as(xm_next)),
+                                          _ptr(self._as(dx_pred)), C.byref(st)))
+        return dict(newton_iters=st.newton_iters, pcg_iters=st.pcg_iters_total,
+                    halvings=st.line_search_halvings, residual=st.residual, alpha0=st.alpha0,
+                    energy=st.energy, ms=st.ms_total)

@@ -1,0 +1,623 @@
+// api.cu -- the C ABI of libgmcp (declared in include/gmcp.h): context
+// creation (derived topology built on the host and uploaded once), and the
+// entry points that queue the contact-pass kernels on the caller's stream.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gmcp_internal.cuh"
+
+namespace gmcp {
+
+SceneView Ctx::view() const {
+    SceneView S;
+    S.nv = (int32_t)nv; S.ns = (int32_t)ns; S.nmv = (int32_t)nmv; S.nmt = (int32_t)nmt;
+    S.nme = (int32_t)nme; S.nse = (int32_t)nse; S.n_env = n_env;
+    S.stri = stri.p; S.mtri = mtri.p; S.medge = medge.p;
+    S.me_tri_off = me_tri_off.p; S.me_tri = me_tri.p; S.mv_tri_off = mv_tri_off.p; S.mv_tri = mv_tri.p;
+    S.mtri_own_edge = mtri_own_edge.p; S.mtri_own_vert = mtri_own_vert.p;
+    S.stri_own_vert = stri_own_vert.p; S.stri_own_edge = stri_own_edge.p; S.sedge = sedge.p;
+    S.stri_env = stri_env.p; S.mtri_env = mtri_env.p;
+    S.X = X.p; S.Y0 = Y0.p; S.srest_box = srest_box.p; S.mrest_box = mrest_box.p;
+    S.grid_org = grid_org.p; S.grid_inv = grid_inv.p; S.grid_dim = grid_dim.p; S.grid_off = grid_off.p;
+    S.margin = margin;
+    return S;
+}
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct Fail {
+    ipc_status st;
+    std::string msg;
+};
+
+#define CK(expr)                                                                              \
+    do {                                                                                      \
+        cudaError_t _e = (expr);                                                              \
+        if (_e != cudaSuccess)                                                                \
+            throw Fail{_e == cudaErrorMemoryAllocation ? IPC_ERR_OOM : IPC_ERR_CUDA,          \
+                       std::string(#expr) + ": " + cudaGetErrorString(_e)};                   \
+    } while (0)
+
+int32_t env_of(const std::vector<int64_t>& off, int64_t i) {
+    auto it = std::upper_bound(off.begin(), off.end(), i);
+    return (int32_t)(it - off.begin()) - 1;
+}
+
+// unique undirected edges of a triangle list, sorted lexicographically by
+// (min, max) vertex; off/adj: CSR of the triangles adjacent to each edge,
+// in increasing triangle id
+void tri_edges(const int32_t* tris, int64_t n, std::vector<int32_t>& edges,
+               std::vector<int32_t>& off, std::vector<int32_t>& adj) {
+    std::vector<std::array<int32_t, 3>> tr((size_t)n * 3);
+    for (int64_t t = 0; t < n; ++t)
+        for (int k = 0; k < 3; ++k) {
+            int32_t a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+            tr[3 * t + k] = {std::min(a, b), std::max(a, b), (int32_t)t};
+        }
+    std::sort(tr.begin(), tr.end());
+    edges.clear(); off.clear(); adj.clear();
+    for (size_t i = 0; i < tr.size(); ++i) {
+        if (i == 0 || tr[i][0] != tr[i - 1][0] || tr[i][1] != tr[i - 1][1]) {
+            edges.push_back(tr[i][0]); edges.push_back(tr[i][1]);
+            off.push_back((int32_t)i);
+        }
+        adj.push_back(tr[i][2]);
+    }
+    off.push_back((int32_t)tr.size());
+}
+
+__global__ void k_count_sum(const int32_t* __restrict__ cnt, int64_t ns, long long* out) {
+    // out[0..2] = totals per kind, out[3..5] = maxima
+    long long s0 = 0, s1 = 0, s2 = 0;
+    int m0 = 0, m1 = 0, m2 = 0;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ns;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        s0 += cnt[4 * t]; s1 += cnt[4 * t + 1]; s2 += cnt[4 * t + 2];
+        m0 = max(m0, cnt[4 * t]); m1 = max(m1, cnt[4 * t + 1]); m2 = max(m2, cnt[4 * t + 2]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        m0 = max(m0, __shfl_xor_sync(0xffffffffu, m0, o)); m1 = max(m1, __shfl_xor_sync(0xffffffffu, m1, o));
+        m2 = max(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_add_ll(&out[0], s0); atomic_add_ll(&out[1], s1); atomic_add_ll(&out[2], s2);
+        atomicMax(&out[3], (long long)m0); atomicMax(&out[4], (long long)m1); atomicMax(&out[5], (long long)m2);
+    }
+}
+
+__global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = a[i] - b[i];
+}
+
+}  // namespace
+
+// Broad phase with automatic regrowth of the per-triangle capacities.
+cudaError_t run_candidates(Ctx& c, const double* x, const double* xm) {
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        GMCP_CUDA_TRY(bp_build_grid(c, xm, nullptr, false));
+        GMCP_CUDA_TRY(bp_query_contact(c, x, xm));
+        int32_t ov[4];
+        GMCP_CUDA_TRY(cudaMemcpyAsync(ov, c.misc_i32.p, sizeof(ov), cudaMemcpyDeviceToHost, c.stream));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        if (ov[1] == 0 && ov[2] == 0 && ov[3] == 0) return cudaSuccess;
+        auto grow = [](int32_t cap, int32_t need) {
+            int32_t v = cap;
+            while (v < need) v *= 2;
+            return v;
+        };
+        c.cap_f = grow(c.cap_f, ov[1]);
+        c.cap_e = grow(c.cap_e, ov[2]);
+        c.cap_p = grow(c.cap_p, ov[3]);
+        GMCP_CUDA_TRY(c.cand_face.ensure((size_t)c.ns * c.cap_f + 1));
+        GMCP_CUDA_TRY(c.cand_edge.ensure((size_t)c.ns * c.cap_e + 1));
+        GMCP_CUDA_TRY(c.cand_point.ensure((size_t)c.ns * c.cap_p + 1));
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace gmcp
+
+using namespace gmcp;
+
+struct ipc_ctx {
+    Ctx c;
+};
+
+static ipc_status fail_ctx(ipc_ctx* ctx, ipc_status st, const std::string& msg) {
+    if (ctx) ctx->c.err = msg;
+    return st;
+}
+
+static ipc_status cuda_fail(ipc_ctx* ctx, cudaError_t e, const char* where) {
+    cudaGetLastError();
+    return fail_ctx(ctx, e == cudaErrorMemoryAllocation ? IPC_ERR_OOM : IPC_ERR_CUDA,
+                    std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define API_CK(ctx, expr)                                                    \
+    do {                                                                     \
+        cudaError_t _e = (expr);                                             \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #expr);             \
+    } while (0)
+
+static void build_topology(Ctx& c, const ipc_scene* sc) {
+    cudaStream_t s = c.stream;
+    const int64_t ns = c.ns, nmt = c.nmt, nmv = c.nmv, nv = c.nv;
+    // --- master edges, adjacency and ownership (owner = lowest adjacent tri)
+    std::vector<int32_t> medge, me_off, me_adj;
+    tri_edges(sc->m_tris, nmt, medge, me_off, me_adj);
+    c.nme = (int64_t)medge.size() / 2;
+    std::vector<int32_t> mv_off(nmv + 1, 0), mv_adj(3 * nmt);
+    for (int64_t t = 0; t < nmt; ++t)
+        for (int k = 0; k < 3; ++k) mv_off[sc->m_tris[3 * t + k] + 1]++;
+    for (int64_t v = 0; v < nmv; ++v) mv_off[v + 1] += mv_off[v];
+    {
+        std::vector<int32_t> cur(mv_off.begin(), mv_off.end() - 1);
+        for (int64_t t = 0; t < nmt; ++t)
+            for (int k = 0; k < 3; ++k) mv_adj[cur[sc->m_tris[3 * t + k]]++] = (int32_t)t;
+    }
+    std::vector<int32_t> own_e(3 * nmt, -1), own_v(3 * nmt, -1);
+    {
+        std::vector<int> slot(nmt, 0);
+        for (int64_t e = 0; e < c.nme; ++e) {
+            const int32_t owner = me_adj[me_off[e]];
+            own_e[3 * owner + slot[owner]++] = (int32_t)e;
+        }
+        std::fill(slot.begin(), slot.end(), 0);
+        for (int64_t v = 0; v < nmv; ++v) {
+            if (mv_off[v + 1] == mv_off[v]) continue;
+            const int32_t owner = mv_adj[mv_off[v]];   // filled in increasing tri order
+            own_v[3 * owner + slot[owner]++] = (int32_t)v;
+        }
+    }
+    // --- slave edges and ownership (for CCD)
+    std::vector<int32_t> sedge, se_off, se_adj;
+    tri_edges(sc->s_tris, ns, sedge, se_off, se_adj);
+    c.nse = (int64_t)sedge.size() / 2;
+    std::vector<int32_t> sown_e(3 * ns, -1), sown_v(3 * ns, -1);
+    {
+        std::vector<int> slot(ns, 0);
+        for (int64_t e = 0; e < c.nse; ++e) {
+            const int32_t owner = se_adj[se_off[e]];
+            sown_e[3 * owner + slot[owner]++] = (int32_t)e;
+        }
+        std::vector<int32_t> vowner(nv, -1);
+        for (int64_t t = 0; t < ns; ++t)
+            for (int k = 0; k < 3; ++k) {
+                const int32_t v = sc->s_tris[3 * t + k];
+                if (vowner[v] < 0) vowner[v] = (int32_t)t;
+            }
+        std::fill(slot.begin(), slot.end(), 0);
+        for (int64_t v = 0; v < nv; ++v)
+            if (vowner[v] >= 0) sown_v[3 * vowner[v] + slot[vowner[v]]++] = (int32_t)v;
+    }
+    // --- env of each tri
+    std::vector<int32_t> s_env(ns), m_env(nmt);
+    for (int64_t t = 0; t < ns; ++t) s_env[t] = env_of(c.env_stri_off, t);
+    for (int64_t t = 0; t < nmt; ++t) m_env[t] = env_of(c.env_mtri_off, t);
+    // --- rest boxes
+    std::vector<double> sbox(6 * ns), mbox(6 * nmt);
+    auto box = [](const double* P, const int32_t* T, double* out) {
+        for (int q = 0; q < 3; ++q) {
+            const double a = P[3 * T[0] + q], b = P[3 * T[1] + q], d = P[3 * T[2] + q];
+            out[q] = std::min(a, std::min(b, d));
+            out[3 + q] = std::max(a, std::max(b, d));
+        }
+    };
+    for (int64_t t = 0; t < ns; ++t) box(sc->pad_rest, sc->s_tris + 3 * t, &sbox[6 * t]);
+    for (int64_t t = 0; t < nmt; ++t) box(sc->m_rest, sc->m_tris + 3 * t, &mbox[6 * t]);
+    // --- grid per env: master rest box grown by 2 dhat + 5 % of its extent;
+    // cell size = max(largest master tri extent, mean slave tri extent + 2 dhat)
+    const double dhat = c.P.dhat;
+    std::vector<double> org(3 * c.n_env), inv(c.n_env);
+    std::vector<int32_t> dim(3 * c.n_env);
+    std::vector<int64_t> goff(c.n_env + 1, 0);
+    double cmax = 1e-3;
+    for (int64_t i = 0; i < 3 * nv; ++i) cmax = std::max(cmax, std::fabs(sc->pad_rest[i]));
+    for (int64_t i = 0; i < 3 * nmv; ++i) cmax = std::max(cmax, std::fabs(sc->m_rest[i]));
+    for (int e = 0; e < c.n_env; ++e) {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        double mext = 0.0, sext = 0.0;
+        for (int64_t t = c.env_mtri_off[e]; t < c.env_mtri_off[e + 1]; ++t)
+            for (int q = 0; q < 3; ++q) {
+                lo[q] = std::min(lo[q], mbox[6 * t + q]);
+                hi[q] = std::max(hi[q], mbox[6 * t + 3 + q]);
+                mext = std::max(mext, mbox[6 * t + 3 + q] - mbox[6 * t + q]);
+            }
+        const int64_t nse_ = c.env_stri_off[e + 1] - c.env_stri_off[e];
+        for (int64_t t = c.env_stri_off[e]; t < c.env_stri_off[e + 1]; ++t) {
+            double m = 0.0;
+            for (int q = 0; q < 3; ++q) m = std::max(m, sbox[6 * t + 3 + q] - sbox[6 * t + q]);
+            sext += m;
+        }
+        if (nse_ > 0) sext /= (double)nse_;
+        if (!(lo[0] <= hi[0]))
+            for (int q = 0; q < 3; ++q) { lo[q] = 0.0; hi[q] = 0.0; }
+        double h = std::max(mext, sext + 2.0 * dhat);
+        if (!(h > 0.0)) h = std::max(dhat, 1e-6);
+        const double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+        const double grow = 2.0 * dhat + 0.05 * ext;
+        for (int it = 0; it < 64; ++it) {
+            int64_t ncell = 1;
+            for (int q = 0; q < 3; ++q)
+                ncell *= std::max<int64_t>((int64_t)std::ceil((hi[q] - lo[q] + 2 * grow) / h) + 1, 1);
+            if (ncell <= ((int64_t)1 << 22)) break;
+            h *= 1.26;
+        }
+        inv[e] = 1.0 / h;
+        for (int q = 0; q < 3; ++q) {
+            org[3 * e + q] = lo[q] - grow;
+            dim[3 * e + q] = (int32_t)std::max<int64_t>((int64_t)std::ceil((hi[q] - lo[q] + 2 * grow) / h) + 1, 1);
+        }
+        goff[e + 1] = goff[e] + (int64_t)dim[3 * e] * dim[3 * e + 1] * dim[3 * e + 2];
+    }
+    c.n_cells = goff[c.n_env];
+    // slack of the coarse box test: covers the rounding of boxes grown by dhat
+    // for coordinates up to 1000x the largest rest coordinate
+    c.margin = 4e-13 * cmax + 1e-9 * dhat;
+    // --- vertex -> (tri, corner) for the gradient gather
+    std::vector<int32_t> vt_off(nv + 1, 0), vt_ent(3 * ns);
+    for (int64_t t = 0; t < ns; ++t)
+        for (int k = 0; k < 3; ++k) vt_off[sc->s_tris[3 * t + k] + 1]++;
+    for (int64_t v = 0; v < nv; ++v) vt_off[v + 1] += vt_off[v];
+    {
+        std::vector<int32_t> cur(vt_off.begin(), vt_off.end() - 1);
+        for (int64_t t = 0; t < ns; ++t)
+            for (int k = 0; k < 3; ++k) vt_ent[cur[sc->s_tris[3 * t + k]]++] = (int32_t)(t * 4 + k);
+    }
+    // --- contact BSR pattern: blocks (T[a], T[b]) of every slave tri, with
+    // the contributing (tri, a, b) in increasing order
+    std::vector<std::array<int64_t, 3>> blk((size_t)ns * 9);
+    for (int64_t t = 0; t < ns; ++t)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                blk[9 * t + 3 * a + b] = {sc->s_tris[3 * t + a], sc->s_tris[3 * t + b], t * 16 + a * 4 + b};
+    std::sort(blk.begin(), blk.end());
+    std::vector<int32_t> row(nv + 1, 0), col, src_off, src;
+    for (size_t i = 0; i < blk.size(); ++i) {
+        if (i == 0 || blk[i][0] != blk[i - 1][0] || blk[i][1] != blk[i - 1][1]) {
+            col.push_back((int32_t)blk[i][1]);
+            src_off.push_back((int32_t)i);
+            row[blk[i][0] + 1]++;
+        }
+        src.push_back((int32_t)blk[i][2]);
+    }
+    src_off.push_back((int32_t)blk.size());
+    for (int64_t v = 0; v < nv; ++v) row[v + 1] += row[v];
+    c.cb_nnzb = (int64_t)col.size();
+
+    CK(c.stri.upload(sc->s_tris, 3 * ns, s));
+    CK(c.mtri.upload(sc->m_tris, 3 * nmt, s));
+    CK(c.medge.upload(medge.data(), medge.size(), s));
+    CK(c.me_tri_off.upload(me_off.data(), me_off.size(), s));
+    CK(c.me_tri.upload(me_adj.data(), me_adj.size(), s));
+    CK(c.mv_tri_off.upload(mv_off.data(), mv_off.size(), s));
+    CK(c.mv_tri.upload(mv_adj.data(), mv_adj.size(), s));
+    CK(c.mtri_own_edge.upload(own_e.data(), own_e.size(), s));
+    CK(c.mtri_own_vert.upload(own_v.data(), own_v.size(), s));
+    CK(c.stri_own_vert.upload(sown_v.data(), sown_v.size(), s));
+    CK(c.stri_own_edge.upload(sown_e.data(), sown_e.size(), s));
+    CK(c.sedge.upload(sedge.data(), sedge.size(), s));
+    CK(c.stri_env.upload(s_env.data(), s_env.size(), s));
+    CK(c.mtri_env.upload(m_env.data(), m_env.size(), s));
+    CK(c.X.upload(sc->pad_rest, 3 * nv, s));
+    CK(c.Y0.upload(sc->m_rest, 3 * nmv, s));
+    CK(c.srest_box.upload(sbox.data(), sbox.size(), s));
+    CK(c.mrest_box.upload(mbox.data(), mbox.size(), s));
+    CK(c.grid_org.upload(org.data(), org.size(), s));
+    CK(c.grid_inv.upload(inv.data(), inv.size(), s));
+    CK(c.grid_dim.upload(dim.data(), dim.size(), s));
+    CK(c.grid_off.upload(goff.data(), goff.size(), s));
+    CK(c.vt_off.upload(vt_off.data(), vt_off.size(), s));
+    CK(c.vt_ent.upload(vt_ent.data(), vt_ent.size(), s));
+    CK(c.cb_row.upload(row.data(), row.size(), s));
+    CK(c.cb_col.upload(col.data(), col.size(), s));
+    CK(c.cb_src_off.upload(src_off.data(), src_off.size(), s));
+    CK(c.cb_src.upload(src.data(), src.size(), s));
+    // the host vectors above must outlive the asynchronous copies
+    CK(cudaStreamSynchronize(s));
+}
+
+static void alloc_call_buffers(Ctx& c) {
+    const int64_t ns = c.ns;
+    cudaStream_t s = c.stream;
+    CK(c.cand_face.ensure((size_t)ns * c.cap_f + 1));
+    CK(c.cand_edge.ensure((size_t)ns * c.cap_e + 1));
+    CK(c.cand_point.ensure((size_t)ns * c.cap_p + 1));
+    CK(c.cand_count.ensure((size_t)ns * 4 + 4));
+    CK(c.active.ensure((size_t)ns + 1));
+    CK(c.misc_i32.ensure(16));
+    CK(c.tri_E.ensure((size_t)ns + 1));
+    CK(cudaMemsetAsync(c.tri_E.p, 0, sizeof(double) * (ns + 1), s));
+    if (c.P.precision == IPC_PREC_MIXED) {
+        CK(c.tri_G32.ensure(3 * (size_t)ns + 3)); CK(c.tri_S32.ensure(6 * (size_t)ns + 6));
+        CK(c.tri_n32.ensure(3 * (size_t)ns + 3)); CK(c.cb_val32.ensure(9 * (size_t)c.cb_nnzb + 9));
+        CK(cudaMemsetAsync(c.tri_G32.p, 0, sizeof(float) * (3 * ns + 3), s));
+        CK(cudaMemsetAsync(c.tri_S32.p, 0, sizeof(float) * (6 * ns + 6), s));
+        CK(cudaMemsetAsync(c.tri_n32.p, 0, sizeof(float) * (3 * ns + 3), s));
+    } else {
+        CK(c.tri_G64.ensure(3 * (size_t)ns + 3)); CK(c.tri_S64.ensure(6 * (size_t)ns + 6));
+        CK(c.tri_n64.ensure(3 * (size_t)ns + 3)); CK(c.cb_val64.ensure(9 * (size_t)c.cb_nnzb + 9));
+        CK(cudaMemsetAsync(c.tri_G64.p, 0, sizeof(double) * (3 * ns + 3), s));
+        CK(cudaMemsetAsync(c.tri_S64.p, 0, sizeof(double) * (6 * ns + 6), s));
+        CK(cudaMemsetAsync(c.tri_n64.p, 0, sizeof(double) * (3 * ns + 3), s));
+    }
+    CK(c.u64_tmp.ensure(8));
+    CK(c.i64_tmp.ensure(16));
+    CK(c.scal.ensure(16));
+    CK(cudaMallocHost(reinterpret_cast<void**>(&c.h_scalars), 16 * sizeof(double)));
+    CK(cudaMallocHost(reinterpret_cast<void**>(&c.h_counts), 16 * sizeof(long long)));
+}
+
+extern "C" {
+
+ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx** out) {
+    g_create_error.clear();
+    if (!out) { g_create_error = "ipc_create: out is NULL"; return IPC_ERR_ARG; }
+    *out = nullptr;
+    if (!params || !scene) { g_create_error = "ipc_create: NULL params or scene"; return IPC_ERR_ARG; }
+    if (scene->n_env < 1 || !scene->env_vert_off || !scene->env_stri_off || !scene->env_mvert_off ||
+        !scene->env_mtri_off || !scene->env_tet_off) {
+        g_create_error = "ipc_create: scene needs n_env >= 1 and all env offset arrays";
+        return IPC_ERR_ARG;
+    }
+    if (scene->n_vert <= 0 || scene->n_stri < 0 || scene->n_mvert < 0 || scene->n_mtri < 0 ||
+        !scene->pad_rest || (scene->n_stri && !scene->s_tris) || (scene->n_mtri && !scene->m_tris) ||
+        (scene->n_mvert && !scene->m_rest)) {
+        g_create_error = "ipc_create: missing scene arrays";
+        return IPC_ERR_ARG;
+    }
+    if (scene->n_vert >= ((int64_t)1 << 31) || scene->n_stri >= ((int64_t)1 << 27) ||
+        scene->n_mtri >= ((int64_t)1 << 31) || scene->n_tet >= ((int64_t)1 << 31)) {
+        g_create_error = "ipc_create: sizes exceed the 32-bit index range";
+        return IPC_ERR_ARG;
+    }
+    if (params->face_rule_level != 1 && params->face_rule_level != 2) {
+        g_create_error = "ipc_create: face_rule_level must be 1 or 2";
+        return IPC_ERR_ARG;
+    }
+    if (!(params->dhat > 0.0) || !(params->ccd_slack > 0.0 && params->ccd_slack < 1.0) ||
+        params->ccd_max_iter < 1 ||
+        (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_MIXED)) {
+        g_create_error = "ipc_create: invalid dhat, ccd_slack, ccd_max_iter or precision";
+        return IPC_ERR_ARG;
+    }
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || params->device < 0 || ndev <= params->device) {
+        g_create_error = std::string("ipc_create: no usable CUDA device: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return IPC_ERR_CUDA;
+    }
+    ipc_ctx* ctx = new ipc_ctx();
+    Ctx& c = ctx->c;
+    try {
+        c.prm = *params;
+        c.device = params->device;
+        CK(cudaSetDevice(c.device));
+        c.stream = (cudaStream_t)params->stream;
+        c.P.precision = params->precision;
+        c.P.dhat = params->dhat; c.P.kappa = params->kappa; c.P.kappa_edge = params->kappa_edge;
+        c.P.kappa_point = params->kappa_point; c.P.delta_T = params->delta_T; c.P.delta_e = params->delta_e;
+        c.P.L = params->face_rule_level; c.P.nk = 1 << (2 * c.P.L);
+        c.P.dhat_guard = params->dhat_guard; c.P.kappa_guard = params->kappa_guard;
+        c.P.ccd_slack = params->ccd_slack; c.P.ccd_max_iter = params->ccd_max_iter;
+        c.n_env = scene->n_env;
+        auto cp = [&](const int64_t* p) { return std::vector<int64_t>(p, p + scene->n_env + 1); };
+        c.env_vert_off = cp(scene->env_vert_off); c.env_tet_off = cp(scene->env_tet_off);
+        c.env_stri_off = cp(scene->env_stri_off); c.env_mvert_off = cp(scene->env_mvert_off);
+        c.env_mtri_off = cp(scene->env_mtri_off);
+        c.nv = scene->n_vert; c.nt = scene->n_tet; c.ns = scene->n_stri;
+        c.nmv = scene->n_mvert; c.nmt = scene->n_mtri;
+        for (int64_t i = 0; i < 3 * c.ns; ++i)
+            if (scene->s_tris[i] < 0 || scene->s_tris[i] >= c.nv) throw Fail{IPC_ERR_ARG, "s_tris index out of range"};
+        for (int64_t i = 0; i < 3 * c.nmt; ++i)
+            if (scene->m_tris[i] < 0 || scene->m_tris[i] >= c.nmv) throw Fail{IPC_ERR_ARG, "m_tris index out of range"};
+        build_topology(c, scene);
+        alloc_call_buffers(c);
+        CK(cudaStreamSynchronize(c.stream));
+    } catch (const Fail& f) {
+        g_create_error = "ipc_create: " + f.msg;
+        cudaGetLastError();
+        ipc_destroy(ctx);
+        return f.st;
+    } catch (const std::exception& ex) {
+        g_create_error = std::string("ipc_create: ") + ex.what();
+        ipc_destroy(ctx);
+        return IPC_ERR_OOM;
+    }
+    *out = ctx;
+    return IPC_OK;
+}
+
+void ipc_destroy(ipc_ctx* ctx) {
+    if (!ctx) return;
+    Ctx& c = ctx->c;
+    cudaSetDevice(c.device);
+    cudaStreamSynchronize(c.stream);
+    if (c.h_scalars) cudaFreeHost(c.h_scalars);
+    if (c.h_counts) cudaFreeHost(c.h_counts);
+    delete ctx;   // every DBuf member frees its device memory
+}
+
+const char* ipc_last_error(const ipc_ctx* ctx) {
+    if (!ctx) return g_create_error.c_str();
+    return ctx->c.err.c_str();
+}
+
+ipc_status ipc_candidates(ipc_ctx* ctx, const double* x_dev, const double* xm_dev,
+                          ipc_candidate_counts* counts) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!x_dev || (!xm_dev && c.nmv > 0)) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_candidates: NULL positions");
+    API_CK(ctx, cudaSetDevice(c.device));
+    API_CK(ctx, run_candidates(c, x_dev, xm_dev));
+    if (counts) {
+        API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(1024, (c.ns + 255) / 256));
+        k_count_sum<<<(unsigned)blocks, 256, 0, c.stream>>>(c.cand_count.p, c.ns, c.i64_tmp.p);
+        API_CK(ctx, cudaGetLastError());
+        API_CK(ctx, cudaMemcpyAsync(c.h_counts, c.i64_tmp.p, 6 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+        API_CK(ctx, cudaStreamSynchronize(c.stream));
+        counts->face = c.h_counts[0]; counts->edge = c.h_counts[1]; counts->point = c.h_counts[2];
+        counts->max_per_tri[0] = (int32_t)c.h_counts[3];
+        counts->max_per_tri[1] = (int32_t)c.h_counts[4];
+        counts->max_per_tri[2] = (int32_t)c.h_counts[5];
+    }
+    return IPC_OK;
+}
+
+ipc_status ipc_candidates_copy(ipc_ctx* ctx, int32_t kind, int32_t* pairs_host, int64_t capacity,
+                               int64_t* n_out) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (kind < 0 || kind > 2 || !n_out) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_candidates_copy: bad kind or n_out");
+    API_CK(ctx, cudaSetDevice(c.device));
+    const int32_t cap = kind == 0 ? c.cap_f : (kind == 1 ? c.cap_e : c.cap_p);
+    const int32_t* lists = kind == 0 ? c.cand_face.p : (kind == 1 ? c.cand_edge.p : c.cand_point.p);
+    std::vector<int32_t> cnt(4 * c.ns + 4), L((size_t)c.ns * cap + 1);
+    API_CK(ctx, cudaMemcpyAsync(cnt.data(), c.cand_count.p, sizeof(int32_t) * 4 * c.ns, cudaMemcpyDeviceToHost, c.stream));
+    API_CK(ctx, cudaMemcpyAsync(L.data(), lists, sizeof(int32_t) * c.ns * cap, cudaMemcpyDeviceToHost, c.stream));
+    API_CK(ctx, cudaStreamSynchronize(c.stream));
+    int64_t n = 0;
+    for (int64_t t = 0; t < c.ns; ++t) n += std::min(cnt[4 * t + kind], cap);
+    *n_out = n;
+    if (!pairs_host) return IPC_OK;
+    if (capacity < n) return fail_ctx(ctx, IPC_ERR_CAPACITY, "ipc_candidates_copy: capacity too small");
+    int64_t k = 0;
+    for (int64_t t = 0; t < c.ns; ++t) {
+        const int m = std::min(cnt[4 * t + kind], cap);
+        for (int j = 0; j < m; ++j) {
+            pairs_host[2 * k] = (int32_t)t;
+            pairs_host[2 * k + 1] = L[(size_t)t * cap + j];
+            ++k;
+        }
+    }
+    return IPC_OK;
+}
+
+ipc_status ipc_barrier_eval(ipc_ctx* ctx, const double* x_dev, const double* xm_dev,
+                            double* energy_dev, double* energy_host, void* grad_dev,
+                            ipc_bsr_view* hess, ipc_sample_counts* counts) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!x_dev || (!xm_dev && c.nmv > 0)) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_barrier_eval: NULL positions");
+    API_CK(ctx, cudaSetDevice(c.device));
+    API_CK(ctx, run_candidates(c, x_dev, xm_dev));
+    long long* ctr = nullptr;
+    if (counts) {
+        API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
+        ctr = c.i64_tmp.p;
+    }
+    double* edev = energy_dev;
+    if (energy_host && !energy_dev) edev = c.scal.p;
+    API_CK(ctx, contact_eval(c, x_dev, xm_dev, edev, grad_dev, hess != nullptr, ctr));
+    if (energy_host)
+        API_CK(ctx, cudaMemcpyAsync(c.h_scalars, edev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    if (counts)
+        API_CK(ctx, cudaMemcpyAsync(c.h_counts, c.i64_tmp.p, 4 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+    if (energy_host || counts) API_CK(ctx, cudaStreamSynchronize(c.stream));
+    if (energy_host) *energy_host = c.h_scalars[0];
+    if (counts) {
+        counts->face = c.h_counts[0]; counts->edge = c.h_counts[1]; counts->point = c.h_counts[2];
+        counts->guard = 0; counts->face_evaluated = c.h_counts[3];
+    }
+    if (hess) {
+        const bool f32 = c.P.precision == IPC_PREC_MIXED;
+        hess->n_rows = c.nv;
+        hess->nnzb = c.cb_nnzb;
+        hess->row_ptr_dev = c.cb_row.p;
+        hess->col_idx_dev = c.cb_col.p;
+        hess->vals_dev = f32 ? (const void*)c.cb_val32.p : (const void*)c.cb_val64.p;
+        hess->dtype = f32 ? 1 : 0;
+    }
+    return IPC_OK;
+}
+
+ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_dev,
+                            const double* xm0_dev, const double* xm1_dev, double* alpha_host,
+                            ipc_ccd_info* info) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!x_dev || !dx_dev || (!xm0_dev && c.nmv > 0) || !alpha_host)
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_ccd_max_step: NULL argument");
+    API_CK(ctx, cudaSetDevice(c.device));
+    const double* dxm = nullptr;
+    if (xm1_dev) {
+        API_CK(ctx, c.dxm.ensure(3 * (size_t)c.nmv + 3));
+        const int64_t n = 3 * c.nmv;
+        if (n > 0) {
+            k_sub<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(xm1_dev, xm0_dev, c.dxm.p, n);
+            API_CK(ctx, cudaGetLastError());
+        }
+        dxm = c.dxm.p;
+    }
+    // alpha bits: [0] = alpha_lin (init +inf), [1] = alpha_accd (init 1.0)
+    const unsigned long long init[2] = {0x7FF0000000000000ULL, 0x3FF0000000000000ULL};
+    API_CK(ctx, cudaMemcpyAsync(c.u64_tmp.p, init, sizeof(init), cudaMemcpyHostToDevice, c.stream));
+    API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
+    API_CK(ctx, run_candidates(c, x_dev, xm0_dev));
+    API_CK(ctx, contact_alpha_lin(c, x_dev, xm0_dev, dx_dev, dxm, c.u64_tmp.p));
+    API_CK(ctx, bp_ccd_accd(c, x_dev, dx_dev, xm0_dev, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8));
+    unsigned long long bits[2];
+    long long ctr[4];
+    API_CK(ctx, cudaMemcpyAsync(bits, c.u64_tmp.p, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
+    API_CK(ctx, cudaMemcpyAsync(ctr, c.i64_tmp.p + 8, sizeof(ctr), cudaMemcpyDeviceToHost, c.stream));
+    API_CK(ctx, cudaStreamSynchronize(c.stream));
+    double al, aa;
+    memcpy(&al, &bits[0], 8);
+    memcpy(&aa, &bits[1], 8);
+    // rounding-order differences in the linearised gap may only shrink the step
+    if (al < INFINITY) al *= (1.0 - 1e-10);
+    const double a = std::min(1.0, std::min(al, aa));
+    *alpha_host = a;
+    if (info) {
+        info->alpha = a; info->alpha_lin = al; info->alpha_accd = aa;
+        info->n_pairs_pt = ctr[0]; info->n_pairs_ee = ctr[1]; info->iter_cap_hit = (int32_t)(ctr[2] != 0);
+    }
+    return IPC_OK;
+}
+
+ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* names_host,
+                       double* ms_host, int64_t* calls_host, int32_t* n_sections) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    API_CK(ctx, cudaSetDevice(c.device));
+    if (mode == 0) { c.prof.collect(); c.prof.on = false; return IPC_OK; }
+    if (mode == 1) { c.prof.reset(); c.prof.on = true; return IPC_OK; }
+    if (mode != 2) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_profile: mode must be 0, 1 or 2");
+    c.prof.collect();
+    int n = 0;
+    for (int i = 0; i < Profiler::kMax && c.prof.names[i]; ++i) {
+        if (n < max_sections) {
+            if (names_host) {
+                strncpy(names_host + 32 * n, c.prof.names[i], 31);
+                names_host[32 * n + 31] = 0;
+            }
+            if (ms_host) ms_host[n] = c.prof.ms[i];
+            if (calls_host) calls_host[n] = c.prof.calls[i];
+        }
+        ++n;
+    }
+    if (n_sections) *n_sections = n;
+    return IPC_OK;
+}
+
+ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
+                           const double* dx_pred_dev, ipc_step_stats* stats) {
+    if (!ctx) return IPC_ERR_ARG;
+    (void)x_dev; (void)v_dev; (void)xm_next_dev; (void)dx_pred_dev; (void)stats;
+    return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: the time stepper is not part of this build yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,566 @@
+// broadphase.cu -- spatial-hash broad phase and additive CCD (FP64).
+//
+// Compiled with -fmad=false: every product and sum is rounded separately, so
+// the candidate predicates (boxes grown by dhat, face-sample positions
+// ((b0 x0 + b1 x1) + b2 x2)) and the additive-CCD iteration give the same
+// bits as a plain IEEE evaluation in the same order.  That makes candidate
+// sets exact and the CCD step reproducible.
+//
+// Grid: one dense box of cells per environment, sized at context creation
+// from the rest geometry; cell coordinates are clamped to the box, which
+// keeps the cell map monotone (so overlapping boxes always share a cell).
+// Master triangles are counting-sorted into cells (atomic integer counts,
+// exclusive scan, atomic integer cursors).  A query visits the cells of its
+// box and reports a master triangle only in the first cell common to both
+// boxes, so every pair is seen once; per-triangle lists are then sorted,
+// which removes any dependence on the order of the cell entries.
+//
+// Candidate kinds (Sec. 4.1's features, within eps_max = dhat):
+//   face  (slave tri, master tri): a face sample of the slave tri lies in the
+//         master tri's box grown by dhat
+//   edge  (slave tri, master edge): slave vertex box vs edge box grown by dhat
+//   point (slave tri, master vertex): slave vertex box vs vertex grown by dhat
+// Edges and vertices are found through the master triangle that owns them
+// (the lowest-numbered adjacent triangle), whose box contains theirs.
+#include <cfloat>
+
+#include "gmcp_internal.cuh"
+
+namespace gmcp {
+namespace {
+
+struct I3 { int x, y, z; };
+
+__device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
+__device__ __forceinline__ double dmax_(double a, double b) { return a > b ? a : b; }
+
+__device__ __forceinline__ int cell_coord(double p, double o, double inv, int dim) {
+    double f = floor((p - o) * inv);
+    f = f < 0.0 ? 0.0 : f;
+    f = f > (double)(dim - 1) ? (double)(dim - 1) : f;
+    return (f == f) ? (int)f : 0;     // NaN maps to cell 0
+}
+
+__device__ __forceinline__ I3 cell_of(const SceneView& S, int e, double px, double py, double pz) {
+    const double* o = S.grid_org + 3 * e;
+    const int* d = S.grid_dim + 3 * e;
+    const double inv = S.grid_inv[e];
+    return I3{cell_coord(px, o[0], inv, d[0]), cell_coord(py, o[1], inv, d[1]),
+              cell_coord(pz, o[2], inv, d[2])};
+}
+
+__device__ __forceinline__ int64_t cell_id(const SceneView& S, int e, int ix, int iy, int iz) {
+    const int* d = S.grid_dim + 3 * e;
+    return S.grid_off[e] + (int64_t)ix + (int64_t)d[0] * ((int64_t)iy + (int64_t)d[1] * iz);
+}
+
+__device__ __forceinline__ void load3(const double* p, int64_t i, double* o) {
+    o[0] = p[3 * i]; o[1] = p[3 * i + 1]; o[2] = p[3 * i + 2];
+}
+
+// face-rule sample k of level L (upright cells first, then inverted cells)
+__device__ void rule_beta(int L, int k, double* b) {
+    const int n = 1 << L;
+    int c = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; i + j < n; ++j) {
+            if (c == k) {
+                int kk = n - 1 - i - j;
+                b[0] = (double)(3 * i + 1) / (double)(3 * n);
+                b[1] = (double)(3 * j + 1) / (double)(3 * n);
+                b[2] = (double)(3 * kk + 1) / (double)(3 * n);
+                return;
+            }
+            ++c;
+        }
+    for (int i = 0; i < n - 1; ++i)
+        for (int j = 0; i + j < n - 1; ++j) {
+            if (c == k) {
+                int kk = n - 2 - i - j;
+                b[0] = (double)(3 * i + 2) / (double)(3 * n);
+                b[1] = (double)(3 * j + 2) / (double)(3 * n);
+                b[2] = (double)(3 * kk + 2) / (double)(3 * n);
+                return;
+            }
+            ++c;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// grid build
+// ---------------------------------------------------------------------------
+__global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
+                                 const double* __restrict__ dxm, double* __restrict__ mbox,
+                                 int32_t* __restrict__ cnt) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= S.nmt) return;
+    const int32_t* T = S.mtri + 3 * m;
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) {
+            double p = xm[3 * (int64_t)T[a] + c];
+            double q = dxm ? p + dxm[3 * (int64_t)T[a] + c] : p;
+            lo[c] = dmin_(lo[c], dmin_(p, q));
+            hi[c] = dmax_(hi[c], dmax_(p, q));
+        }
+    for (int c = 0; c < 3; ++c) { mbox[6 * m + c] = lo[c]; mbox[6 * m + 3 + c] = hi[c]; }
+    const int e = S.mtri_env[m];
+    I3 a = cell_of(S, e, lo[0], lo[1], lo[2]);
+    I3 b = cell_of(S, e, hi[0], hi[1], hi[2]);
+    for (int iz = a.z; iz <= b.z; ++iz)
+        for (int iy = a.y; iy <= b.y; ++iy)
+            for (int ix = a.x; ix <= b.x; ++ix) atomicAdd(&cnt[cell_id(S, e, ix, iy, iz)], 1);
+}
+
+__global__ void k_mtri_fill(SceneView S, const double* __restrict__ mbox,
+                            const int32_t* __restrict__ start, int32_t* __restrict__ cursor,
+                            int32_t* __restrict__ ent) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= S.nmt) return;
+    const int e = S.mtri_env[m];
+    const double* B = mbox + 6 * m;
+    I3 a = cell_of(S, e, B[0], B[1], B[2]);
+    I3 b = cell_of(S, e, B[3], B[4], B[5]);
+    for (int iz = a.z; iz <= b.z; ++iz)
+        for (int iy = a.y; iy <= b.y; ++iy)
+            for (int ix = a.x; ix <= b.x; ++ix) {
+                int64_t c = cell_id(S, e, ix, iy, iz);
+                int pos = start[c] + atomicAdd(&cursor[c], 1);
+                ent[pos] = (int32_t)m;
+            }
+}
+
+// insertion sort of a short list held in global memory
+__device__ void sort_small(int32_t* a, int n) {
+    for (int i = 1; i < n; ++i) {
+        int32_t v = a[i];
+        int j = i - 1;
+        while (j >= 0 && a[j] > v) { a[j + 1] = a[j]; --j; }
+        a[j + 1] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// contact candidate query: one thread per slave triangle
+// ---------------------------------------------------------------------------
+template <int NK>
+__global__ void __launch_bounds__(128)
+k_query_contact(SceneView S, Params P, CandView C, const double* __restrict__ x,
+                const double* __restrict__ xm, const double* __restrict__ mbox,
+                const int32_t* __restrict__ start, const int32_t* __restrict__ ent,
+                double* __restrict__ triE, void* __restrict__ triG, void* __restrict__ triS,
+                int out_f32) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.ns) return;
+    const int32_t* T = S.stri + 3 * t;
+    double x0[3], x1[3], x2[3];
+    load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
+    const double eps = P.dhat;
+    double slo[3], shi[3];
+    for (int c = 0; c < 3; ++c) {
+        slo[c] = dmin_(x0[c], dmin_(x1[c], x2[c]));
+        shi[c] = dmax_(x0[c], dmax_(x1[c], x2[c]));
+    }
+    double sx[NK], sy[NK], sz[NK];
+    double qlo[3] = {slo[0], slo[1], slo[2]}, qhi[3] = {shi[0], shi[1], shi[2]};
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        double b[3];
+        rule_beta(P.L, k, b);
+        sx[k] = b[0] * x0[0] + b[1] * x1[0] + b[2] * x2[0];
+        sy[k] = b[0] * x0[1] + b[1] * x1[1] + b[2] * x2[1];
+        sz[k] = b[0] * x0[2] + b[1] * x1[2] + b[2] * x2[2];
+        qlo[0] = dmin_(qlo[0], sx[k]); qhi[0] = dmax_(qhi[0], sx[k]);
+        qlo[1] = dmin_(qlo[1], sy[k]); qhi[1] = dmax_(qhi[1], sy[k]);
+        qlo[2] = dmin_(qlo[2], sz[k]); qhi[2] = dmax_(qhi[2], sz[k]);
+    }
+    const double grow = eps + S.margin;
+    for (int c = 0; c < 3; ++c) { qlo[c] = qlo[c] - grow; qhi[c] = qhi[c] + grow; }
+    const int e = S.stri_env[t];
+    const I3 ca = cell_of(S, e, qlo[0], qlo[1], qlo[2]);
+    const I3 cb = cell_of(S, e, qhi[0], qhi[1], qhi[2]);
+    int nf = 0, ne = 0, np = 0;
+    int32_t* Lf = C.face + t * C.cap_f;
+    int32_t* Le = C.edge + t * C.cap_e;
+    int32_t* Lp = C.point + t * C.cap_p;
+    for (int iz = ca.z; iz <= cb.z; ++iz)
+        for (int iy = ca.y; iy <= cb.y; ++iy)
+            for (int ix = ca.x; ix <= cb.x; ++ix) {
+                const int64_t cell = cell_id(S, e, ix, iy, iz);
+                const int k0 = start[cell], k1 = start[cell + 1];
+                for (int k = k0; k < k1; ++k) {
+                    const int32_t m = ent[k];
+                    const double* B = mbox + 6 * (int64_t)m;
+                    const double mlo0 = B[0], mlo1 = B[1], mlo2 = B[2];
+                    const double mhi0 = B[3], mhi1 = B[4], mhi2 = B[5];
+                    // report only in the first cell common to both boxes
+                    I3 mc = cell_of(S, e, mlo0, mlo1, mlo2);
+                    if (max(ca.x, mc.x) != ix || max(ca.y, mc.y) != iy || max(ca.z, mc.z) != iz) continue;
+                    if (qlo[0] > mhi0 || mlo0 > qhi[0] || qlo[1] > mhi1 || mlo1 > qhi[1] ||
+                        qlo[2] > mhi2 || mlo2 > qhi[2])
+                        continue;
+                    // face: some sample inside the master box grown by eps
+                    const double l0 = mlo0 - eps, l1 = mlo1 - eps, l2 = mlo2 - eps;
+                    const double h0 = mhi0 + eps, h1 = mhi1 + eps, h2 = mhi2 + eps;
+                    bool hit = false;
+#pragma unroll
+                    for (int q = 0; q < NK; ++q)
+                        hit |= l0 <= sx[q] && sx[q] <= h0 && l1 <= sy[q] && sy[q] <= h1 &&
+                               l2 <= sz[q] && sz[q] <= h2;
+                    if (hit) { if (nf < C.cap_f) Lf[nf] = m; ++nf; }
+                    // owned edges
+                    for (int j = 0; j < 3; ++j) {
+                        const int32_t me = S.mtri_own_edge[3 * (int64_t)m + j];
+                        if (me < 0) continue;
+                        double ya[3], yb[3];
+                        load3(xm, S.medge[2 * (int64_t)me], ya);
+                        load3(xm, S.medge[2 * (int64_t)me + 1], yb);
+                        bool ok = true;
+                        for (int c = 0; c < 3 && ok; ++c) {
+                            double lo = dmin_(ya[c], yb[c]) - eps, hi = dmax_(ya[c], yb[c]) + eps;
+                            ok = slo[c] <= hi && lo <= shi[c];
+                        }
+                        if (ok) { if (ne < C.cap_e) Le[ne] = me; ++ne; }
+                    }
+                    // owned vertices
+                    for (int j = 0; j < 3; ++j) {
+                        const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
+                        if (u < 0) continue;
+                        double y[3];
+                        load3(xm, u, y);
+                        bool ok = true;
+                        for (int c = 0; c < 3 && ok; ++c) ok = slo[c] <= y[c] + eps && y[c] - eps <= shi[c];
+                        if (ok) { if (np < C.cap_p) Lp[np] = u; ++np; }
+                    }
+                }
+            }
+    sort_small(Lf, min(nf, C.cap_f));
+    sort_small(Le, min(ne, C.cap_e));
+    sort_small(Lp, min(np, C.cap_p));
+    int32_t* cnt = C.count + 4 * t;
+    cnt[0] = nf; cnt[1] = ne; cnt[2] = np; cnt[3] = 0;
+    if (nf > C.cap_f) atomicMax(&C.overflow[0], nf);
+    if (ne > C.cap_e) atomicMax(&C.overflow[1], ne);
+    if (np > C.cap_p) atomicMax(&C.overflow[2], np);
+    if (nf + ne + np > 0) {
+        int idx = atomicAdd(C.n_active, 1);
+        C.active[idx] = (int32_t)t;
+    } else if (triE) {
+        // no candidates: this triangle contributes nothing to the gathers
+        triE[t] = 0.0;
+        if (out_f32) {
+            float* G = (float*)triG; float* Sm = (float*)triS;
+            for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0f;
+            for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0f;
+        } else {
+            double* G = (double*)triG; double* Sm = (double*)triS;
+            for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0;
+            for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// additive CCD (Li, Kaufman, Jiang 2021, Alg. 1), thickness 0
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sub3(const double* a, const double* b, double* o) {
+    o[0] = a[0] - b[0]; o[1] = a[1] - b[1]; o[2] = a[2] - b[2];
+}
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+__device__ __forceinline__ void cross3(const double* a, const double* b, double* o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+__device__ double ps_dist2(const double* p, const double* a, const double* b) {
+    double ab[3], ap[3], q[3], d[3];
+    sub3(b, a, ab); sub3(p, a, ap);
+    double t = dot3(ap, ab) / dot3(ab, ab);
+    t = dmin_(dmax_(t, 0.0), 1.0);
+    for (int c = 0; c < 3; ++c) q[c] = a[c] + t * ab[c];
+    sub3(p, q, d);
+    return dot3(d, d);
+}
+
+// point-triangle: plane distance when the projection is inside, else the
+// nearest edge
+__device__ double pt_dist2(const double* p, const double* t0, const double* t1, const double* t2) {
+    double e1[3], e2[3], d[3];
+    sub3(t1, t0, e1); sub3(t2, t0, e2); sub3(p, t0, d);
+    double a = dot3(e1, e1), bb = dot3(e1, e2), c = dot3(e2, e2);
+    double r1 = dot3(d, e1), r2 = dot3(d, e2);
+    double det = a * c - bb * bb;
+    double v = (c * r1 - bb * r2) / det;
+    double w = (a * r2 - bb * r1) / det;
+    double u = 1.0 - v - w;
+    if (u >= 0.0 && v >= 0.0 && w >= 0.0) {
+        double e1b[3], e2b[3], n[3], db[3];
+        sub3(t1, t0, e1b); sub3(t2, t0, e2b); cross3(e1b, e2b, n); sub3(p, t0, db);
+        double h = dot3(db, n);
+        return h * h / dot3(n, n);
+    }
+    return dmin_(ps_dist2(p, t0, t1), dmin_(ps_dist2(p, t1, t2), ps_dist2(p, t2, t0)));
+}
+
+// segment-segment: four endpoint-segment distances and the line-line
+// distance when both closest-point parameters fall inside the segments
+__device__ double ee_dist2(const double* a0, const double* a1, const double* b0, const double* b1) {
+    double d = dmin_(dmin_(ps_dist2(a0, b0, b1), ps_dist2(a1, b0, b1)),
+                     dmin_(ps_dist2(b0, a0, a1), ps_dist2(b1, a0, a1)));
+    double u[3], v[3], w[3];
+    sub3(a1, a0, u); sub3(b1, b0, v); sub3(a0, b0, w);
+    double A = dot3(u, u), B = dot3(u, v), Cc = dot3(v, v), D = dot3(u, w), E = dot3(v, w);
+    double den = A * Cc - B * B;
+    if (den > 1e-14 * A * Cc) {
+        double sc = (B * E - Cc * D) / den, tc = (A * E - B * D) / den;
+        if (sc > 0.0 && sc < 1.0 && tc > 0.0 && tc < 1.0) {
+            double n[3];
+            cross3(u, v, n);
+            double h = dot3(w, n);
+            d = dmin_(d, h * h / dot3(n, n));
+        }
+    }
+    return d;
+}
+
+// x[12], p[12] (modified); type 0 point-triangle, 1 edge-edge.  Returns the
+// largest safe fraction found in [0, tc] (tc when nothing closes in time).
+__device__ double accd(int type, double* x, double* p, double s, double tc, int max_iter,
+                       int* iters) {
+    double pbar[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 4; ++i)
+        for (int c = 0; c < 3; ++c) pbar[c] += p[3 * i + c];
+    for (int c = 0; c < 3; ++c) pbar[c] = pbar[c] / 4.0;
+    for (int i = 0; i < 4; ++i)
+        for (int c = 0; c < 3; ++c) p[3 * i + c] -= pbar[c];
+    double n[4];
+    for (int i = 0; i < 4; ++i) n[i] = sqrt(dot3(p + 3 * i, p + 3 * i));
+    double lp = type == 0 ? n[0] + dmax_(n[1], dmax_(n[2], n[3])) : dmax_(n[0], n[1]) + dmax_(n[2], n[3]);
+    *iters = 0;
+    if (lp == 0.0) return tc;
+    double d2 = type == 0 ? pt_dist2(x, x + 3, x + 6, x + 9) : ee_dist2(x, x + 3, x + 6, x + 9);
+    double d = sqrt(d2);
+    if (d == 0.0) return 0.0;
+    double gstop = s * d;
+    double t = 0.0;
+    double tl = (1.0 - s) * d / lp;
+    for (int it = 0; it < max_iter; ++it) {
+        *iters = it + 1;
+        for (int i = 0; i < 12; ++i) x[i] = x[i] + tl * p[i];
+        d2 = type == 0 ? pt_dist2(x, x + 3, x + 6, x + 9) : ee_dist2(x, x + 3, x + 6, x + 9);
+        d = sqrt(d2);
+        if (t > 0.0 && d < gstop) return t;
+        t = t + tl;
+        if (t > tc) return tc;
+        tl = 0.9 * d / lp;
+    }
+    return t;
+}
+
+__device__ __forceinline__ void swept_vert(const double* P, const double* D, int64_t v, double* lo,
+                                           double* hi) {
+    for (int c = 0; c < 3; ++c) {
+        double a = P[3 * v + c];
+        double b = D ? a + D[3 * v + c] : a;
+        lo[c] = dmin_(a, b); hi[c] = dmax_(a, b);
+    }
+}
+__device__ __forceinline__ void grow_box(double* lo, double* hi, const double* l2, const double* h2) {
+    for (int c = 0; c < 3; ++c) { lo[c] = dmin_(lo[c], l2[c]); hi[c] = dmax_(hi[c], h2[c]); }
+}
+__device__ __forceinline__ bool overlap(const double* alo, const double* ahi, const double* blo,
+                                        const double* bhi) {
+    return alo[0] <= bhi[0] && blo[0] <= ahi[0] && alo[1] <= bhi[1] && blo[1] <= ahi[1] &&
+           alo[2] <= bhi[2] && blo[2] <= ahi[2];
+}
+
+// atomic minimum of a non-negative double via its bit pattern
+__device__ __forceinline__ void atomic_min_pos(unsigned long long* dst, double v) {
+    atomicMin(dst, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void __launch_bounds__(128)
+k_query_ccd(SceneView S, Params P, const double* __restrict__ x, const double* __restrict__ dx,
+            const double* __restrict__ xm0, const double* __restrict__ dxm,
+            const double* __restrict__ mbox, const int32_t* __restrict__ start,
+            const int32_t* __restrict__ ent, unsigned long long* alpha_bits, long long* counters) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.ns) return;
+    const int32_t* T = S.stri + 3 * t;
+    double tlo[3], thi[3];
+    swept_vert(x, dx, T[0], tlo, thi);
+    for (int a = 1; a < 3; ++a) {
+        double l[3], h[3];
+        swept_vert(x, dx, T[a], l, h);
+        grow_box(tlo, thi, l, h);
+    }
+    double qlo[3], qhi[3];
+    for (int c = 0; c < 3; ++c) { qlo[c] = tlo[c] - S.margin; qhi[c] = thi[c] + S.margin; }
+    const int e = S.stri_env[t];
+    const I3 ca = cell_of(S, e, qlo[0], qlo[1], qlo[2]);
+    const I3 cb = cell_of(S, e, qhi[0], qhi[1], qhi[2]);
+    double best = 1.0;
+    long long n_pt = 0, n_ee = 0;
+    int cap_hit = 0;
+    for (int iz = ca.z; iz <= cb.z; ++iz)
+        for (int iy = ca.y; iy <= cb.y; ++iy)
+            for (int ix = ca.x; ix <= cb.x; ++ix) {
+                const int64_t cell = cell_id(S, e, ix, iy, iz);
+                for (int k = start[cell]; k < start[cell + 1]; ++k) {
+                    const int32_t m = ent[k];
+                    const double* B = mbox + 6 * (int64_t)m;
+                    I3 mc = cell_of(S, e, B[0], B[1], B[2]);
+                    if (max(ca.x, mc.x) != ix || max(ca.y, mc.y) != iy || max(ca.z, mc.z) != iz) continue;
+                    if (!overlap(qlo, qhi, B, B + 3)) continue;
+                    const int32_t* M = S.mtri + 3 * (int64_t)m;
+                    double X12[12], P12[12];
+                    int it;
+                    // slave vertices owned by t vs master triangle m
+                    for (int j = 0; j < 3; ++j) {
+                        const int32_t v = S.stri_own_vert[3 * t + j];
+                        if (v < 0) continue;
+                        double vlo[3], vhi[3];
+                        swept_vert(x, dx, v, vlo, vhi);
+                        if (!overlap(vlo, vhi, B, B + 3)) continue;
+                        for (int c = 0; c < 3; ++c) {
+                            X12[c] = x[3 * (int64_t)v + c]; P12[c] = dx[3 * (int64_t)v + c];
+                            for (int a = 0; a < 3; ++a) {
+                                X12[3 + 3 * a + c] = xm0[3 * (int64_t)M[a] + c];
+                                P12[3 + 3 * a + c] = dxm ? dxm[3 * (int64_t)M[a] + c] : 0.0;
+                            }
+                        }
+                        double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+                        ++n_pt; cap_hit |= it >= P.ccd_max_iter;
+                        best = dmin_(best, r);
+                    }
+                    // master vertices owned by m vs slave triangle t
+                    for (int j = 0; j < 3; ++j) {
+                        const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
+                        if (u < 0) continue;
+                        double ulo[3], uhi[3];
+                        swept_vert(xm0, dxm, u, ulo, uhi);
+                        if (!overlap(ulo, uhi, tlo, thi)) continue;
+                        for (int c = 0; c < 3; ++c) {
+                            X12[c] = xm0[3 * (int64_t)u + c]; P12[c] = dxm ? dxm[3 * (int64_t)u + c] : 0.0;
+                            for (int a = 0; a < 3; ++a) {
+                                X12[3 + 3 * a + c] = x[3 * (int64_t)T[a] + c];
+                                P12[3 + 3 * a + c] = dx[3 * (int64_t)T[a] + c];
+                            }
+                        }
+                        double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+                        ++n_pt; cap_hit |= it >= P.ccd_max_iter;
+                        best = dmin_(best, r);
+                    }
+                    // slave edges owned by t vs master edges owned by m
+                    for (int j = 0; j < 3; ++j) {
+                        const int32_t es = S.stri_own_edge[3 * t + j];
+                        if (es < 0) continue;
+                        const int32_t sa = S.sedge[2 * (int64_t)es], sb = S.sedge[2 * (int64_t)es + 1];
+                        double alo[3], ahi[3], l2[3], h2[3];
+                        swept_vert(x, dx, sa, alo, ahi);
+                        swept_vert(x, dx, sb, l2, h2);
+                        grow_box(alo, ahi, l2, h2);
+                        for (int q = 0; q < 3; ++q) {
+                            const int32_t em = S.mtri_own_edge[3 * (int64_t)m + q];
+                            if (em < 0) continue;
+                            const int32_t m0 = S.medge[2 * (int64_t)em], m1 = S.medge[2 * (int64_t)em + 1];
+                            double blo[3], bhi[3];
+                            swept_vert(xm0, dxm, m0, blo, bhi);
+                            swept_vert(xm0, dxm, m1, l2, h2);
+                            grow_box(blo, bhi, l2, h2);
+                            if (!overlap(alo, ahi, blo, bhi)) continue;
+                            for (int c = 0; c < 3; ++c) {
+                                X12[c] = x[3 * (int64_t)sa + c]; P12[c] = dx[3 * (int64_t)sa + c];
+                                X12[3 + c] = x[3 * (int64_t)sb + c]; P12[3 + c] = dx[3 * (int64_t)sb + c];
+                                X12[6 + c] = xm0[3 * (int64_t)m0 + c]; P12[6 + c] = dxm ? dxm[3 * (int64_t)m0 + c] : 0.0;
+                                X12[9 + c] = xm0[3 * (int64_t)m1 + c]; P12[9 + c] = dxm ? dxm[3 * (int64_t)m1 + c] : 0.0;
+                            }
+                            double r = accd(1, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+                            ++n_ee; cap_hit |= it >= P.ccd_max_iter;
+                            best = dmin_(best, r);
+                        }
+                    }
+                }
+            }
+    if (best < 1.0) atomic_min_pos(alpha_bits, best);
+    if (n_pt) atomic_add_ll(&counters[0], n_pt);
+    if (n_ee) atomic_add_ll(&counters[1], n_ee);
+    if (cap_hit) atomicMax(&counters[2], 1LL);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept) {
+    ProfScope ps(c.prof, c.stream, "grid");
+    SceneView S = c.view();
+    cudaStream_t s = c.stream;
+    GMCP_CUDA_TRY(c.mbox.ensure(6 * (size_t)c.nmt + 6));
+    GMCP_CUDA_TRY(c.cell_cnt.ensure((size_t)c.n_cells + 1));
+    GMCP_CUDA_TRY(c.cell_start.ensure((size_t)c.n_cells + 1));
+    GMCP_CUDA_TRY(c.scan_tmp.ensure(2 * scan_tmp_size(c.n_cells)));
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.cell_cnt.p, 0, sizeof(int32_t) * (c.n_cells + 1), s));
+    const int B = 256;
+    const unsigned g = (unsigned)((c.nmt + B - 1) / B);
+    if (c.nmt > 0) {
+        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mbox.p, c.cell_cnt.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    GMCP_CUDA_TRY(exclusive_scan_i32(c.cell_cnt.p, c.cell_start.p, c.n_cells, c.scan_tmp.p,
+                                     c.scan_tmp.n, s));
+    // read the total number of (cell, triangle) entries to size the entries
+    int32_t total = 0;
+    GMCP_CUDA_TRY(cudaMemcpyAsync(&total, c.cell_start.p + c.n_cells, sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, s));
+    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+    GMCP_CUDA_TRY(c.cell_ent.ensure((size_t)total + 1));
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.cell_cnt.p, 0, sizeof(int32_t) * (c.n_cells + 1), s));
+    if (c.nmt > 0) {
+        k_mtri_fill<<<g, B, 0, s>>>(S, c.mbox.p, c.cell_start.p, c.cell_cnt.p, c.cell_ent.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    return cudaSuccess;
+}
+
+cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
+    ProfScope ps(c.prof, c.stream, "query");
+    SceneView S = c.view();
+    Params P = c.P;
+    cudaStream_t s = c.stream;
+    CandView C = c.cand();
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 4, s));
+    if (c.ns == 0) return cudaSuccess;
+    const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    double* triE = c.tri_E.p;
+    void* triG = f32 ? (void*)c.tri_G32.p : (void*)c.tri_G64.p;
+    void* triS = f32 ? (void*)c.tri_S32.p : (void*)c.tri_S64.p;
+    const int B = 128;
+    const unsigned g = (unsigned)((c.ns + B - 1) / B);
+    if (P.nk == 4)
+        k_query_contact<4><<<g, B, 0, s>>>(S, P, C, x, xm, c.mbox.p, c.cell_start.p, c.cell_ent.p,
+                                           triE, triG, triS, f32);
+    else
+        k_query_contact<16><<<g, B, 0, s>>>(S, P, C, x, xm, c.mbox.p, c.cell_start.p, c.cell_ent.p,
+                                            triE, triG, triS, f32);
+    return cudaGetLastError();
+}
+
+cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
+                        const double* dxm, unsigned long long* alpha_bits, long long* counters) {
+    GMCP_CUDA_TRY(bp_build_grid(c, xm0, dxm, true));
+    ProfScope ps(c.prof, c.stream, "accd");
+    if (c.ns == 0) return cudaSuccess;
+    SceneView S = c.view();
+    const int B = 128;
+    const unsigned g = (unsigned)((c.ns + B - 1) / B);
+    k_query_ccd<<<g, B, 0, c.stream>>>(S, c.P, x, dx, xm0, dxm, c.mbox.p, c.cell_start.p,
+                                       c.cell_ent.p, alpha_bits, counters);
+    return cudaGetLastError();
+}
+
+}  // namespace gmcp

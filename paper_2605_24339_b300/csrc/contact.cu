@@ -1,0 +1,584 @@
+// contact.cu -- GMCP samples, barrier, gradient / Hessian coefficients,
+// deterministic gathers, and the linearised-gap step bound.
+//
+// Work decomposition (one warp per active slave triangle, persistent grid):
+//   face items  = (sample k, candidate master tri)  -> lane handles items
+//                 lane, lane+32, ...; since 32 is a multiple of the 4 or 16
+//                 samples per triangle, each lane keeps one fixed sample k
+//   edge items  = (candidate master edge, Gauss point)
+//   point items = candidate master vertex
+// Each lane accumulates the triangle's energy (FP64) and the coefficients
+//   G_a  = sum_k c1_k beta^s_a,k            (c1 = kappa_q w gamma B')
+//   S_ab = sum_k c2_k beta^s_a beta^s_b      (c2 = max(kappa_q w gamma B'', 0))
+// and a fixed xor-shuffle tree reduces them, so the result does not depend
+// on scheduling.  Per vertex the gradient is -sum_tris G_a n_s and per block
+// the Hessian sum_tris S_ab n_s n_s^T (Sec. 4.2 with dg/dx_a = -beta_a n_s),
+// gathered in a fixed order by k_gather_* (no float atomics).
+//
+// Precision.  FP64 path: everything in double.  Mixed path: face samples are
+// cast in FP32 in a local frame anchored at the slave triangle's first
+// vertex (coordinate differences formed in FP64, then rounded); a sample
+// whose FP32 gap falls below 1e-2 of the shortest slave edge is recomputed
+// in FP64.  Barrier, gradient and Hessian coefficients are FP32; the energy
+// sum stays FP64; edge and point samples, whose point-sample membership test
+// is not weight-continuous, are always built in FP64.
+#include <cfloat>
+
+#include "gmcp_internal.cuh"
+
+namespace gmcp {
+namespace {
+
+constexpr int MODE_EVAL = 0;
+constexpr int MODE_ALPHA = 1;
+
+template <class R>
+struct V3 { R x, y, z; };
+
+template <class R> __device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class R> __device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R> __device__ __forceinline__ V3<R> operator*(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <class R> __device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class R> __device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ V3<double> ld3(const double* p, int64_t i) {
+    return {p[3 * i], p[3 * i + 1], p[3 * i + 2]};
+}
+__device__ __forceinline__ V3<float> tof(V3<double> a) { return {(float)a.x, (float)a.y, (float)a.z}; }
+
+template <class R> __device__ __forceinline__ R rmin(R a, R b) { return a < b ? a : b; }
+template <class R> __device__ __forceinline__ R rmax(R a, R b) { return a > b ? a : b; }
+template <class R> __device__ __forceinline__ R min3(const R* b) { return rmin(b[0], rmin(b[1], b[2])); }
+
+// Eq. (gram): barycentric coordinates of the projection of q on (p0,p1,p2)
+template <class R>
+__device__ __forceinline__ void bary(V3<R> q, V3<R> p0, V3<R> p1, V3<R> p2, R* b) {
+    V3<R> e1 = p1 - p0, e2 = p2 - p0, d = q - p0;
+    R a = dot(e1, e1), bb = dot(e1, e2), c = dot(e2, e2);
+    R r1 = dot(d, e1), r2 = dot(d, e2);
+    R det = a * c - bb * bb;
+    R v = (c * r1 - bb * r2) / det;
+    R w = (a * r2 - bb * r1) / det;
+    b[0] = R(1) - v - w; b[1] = v; b[2] = w;
+}
+
+template <class R>
+__device__ __forceinline__ V3<R> interp(const R* b, V3<R> x0, V3<R> x1, V3<R> x2) {
+    return {b[0] * x0.x + b[1] * x1.x + b[2] * x2.x, b[0] * x0.y + b[1] * x1.y + b[2] * x2.y,
+            b[0] * x0.z + b[1] * x1.z + b[2] * x2.z};
+}
+
+// Eq. (smoothstep)
+template <class R>
+__device__ __forceinline__ R hermite(R x, R delta) {
+    if (x <= R(0)) return R(0);
+    if (x >= delta) return R(1);
+    R t = x / delta;
+    return R(3) * t * t - R(2) * t * t * t;
+}
+
+// IPC barrier and derivatives on (0, eps); the caller guarantees 0 < g < eps
+__device__ __forceinline__ void barrier(double g, double eps, double& B, double& dB, double& d2B) {
+    double d = g - eps, L = log(g / eps);
+    B = -d * d * L;
+    dB = -2.0 * d * L - d * d / g;
+    d2B = -2.0 * L - 4.0 * d / g + d * d / (g * g);
+}
+__device__ __forceinline__ void barrier(float g, float eps, float& B, float& dB, float& d2B) {
+    float d = g - eps, L = logf(g / eps);
+    B = -d * d * L;
+    dB = -2.0f * d * L - d * d / g;
+    d2B = -2.0f * L - 4.0f * d / g + d * d / (g * g);
+}
+
+__device__ void rule_beta(int L, int k, double* b) {
+    const int n = 1 << L;
+    int c = 0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; i + j < n; ++j) {
+            if (c == k) {
+                int kk = n - 1 - i - j;
+                b[0] = (double)(3 * i + 1) / (double)(3 * n);
+                b[1] = (double)(3 * j + 1) / (double)(3 * n);
+                b[2] = (double)(3 * kk + 1) / (double)(3 * n);
+                return;
+            }
+            ++c;
+        }
+    for (int i = 0; i < n - 1; ++i)
+        for (int j = 0; i + j < n - 1; ++j) {
+            if (c == k) {
+                int kk = n - 2 - i - j;
+                b[0] = (double)(3 * i + 2) / (double)(3 * n);
+                b[1] = (double)(3 * j + 2) / (double)(3 * n);
+                b[2] = (double)(3 * kk + 2) / (double)(3 * n);
+                return;
+            }
+            ++c;
+        }
+}
+
+// Face ray cast of Sec. 4.1 (fixed slave-side rule): from xs along ns onto
+// the plane of (y0,y1,y2).  Returns true when the master tri faces the slave,
+// the hit is inside it and g > 0; then x_m - x_s = g n_s (Eq. gap).
+template <class R>
+__device__ __forceinline__ bool face_geom(V3<R> xs, V3<R> ns, V3<R> y0, V3<R> y1, V3<R> y2, R& g,
+                                          R* bm) {
+    V3<R> e1 = y1 - y0, e2 = y2 - y0, N = cross(e1, e2);
+    R den = dot(N, ns);
+    if (!(den < R(0))) return false;
+    g = dot(N, y0 - xs) / den;
+    V3<R> p = xs + g * ns;
+    bary(p, y0, y1, y2, bm);
+    return min3(bm) >= R(0) && g > R(0);
+}
+
+// squared distance between two boxes (0 when they overlap)
+__device__ __forceinline__ double box_dist2(const double* alo, const double* ahi, const double* blo,
+                                            const double* bhi) {
+    double s = 0.0;
+    for (int c = 0; c < 3; ++c) {
+        double d = rmax(0.0, rmax(alo[c] - bhi[c], blo[c] - ahi[c]));
+        s += d * d;
+    }
+    return s;
+}
+
+// Eq. (adaptive_eps): eps is eps_max whenever the rest boxes are so far apart
+// that 0.9 g_ref > eps_max for any sample of the pair (g_ref >= box distance)
+__device__ __forceinline__ bool rest_far(const double* slo, const double* shi, const double* mlo,
+                                         const double* mhi, double eps_max) {
+    const double r = eps_max * (1.2 / 0.9);
+    return box_dist2(slo, shi, mlo, mhi) >= r * r;
+}
+
+__device__ __forceinline__ bool any_facing(const SceneView& S, const double* xm, const int32_t* tris,
+                                           int n, V3<double> ns) {
+    for (int i = 0; i < n; ++i) {
+        const int32_t* M = S.mtri + 3 * (int64_t)tris[i];
+        V3<double> y0 = ld3(xm, M[0]);
+        V3<double> N = cross(ld3(xm, M[1]) - y0, ld3(xm, M[2]) - y0);
+        if (dot(N, ns) < 0.0) return true;
+    }
+    return false;
+}
+
+template <class T>
+struct Acc {
+    double E;
+    T G[3];
+    T S[6];
+    double amin;
+    __device__ void zero() {
+        E = 0.0; amin = INFINITY;
+        for (int i = 0; i < 3; ++i) G[i] = T(0);
+        for (int i = 0; i < 6; ++i) S[i] = T(0);
+    }
+    __device__ void add(double e, T c1, T c2, const T* b) {
+        E += e;
+        G[0] += c1 * b[0]; G[1] += c1 * b[1]; G[2] += c1 * b[2];
+        S[0] += c2 * b[0] * b[0]; S[1] += c2 * b[0] * b[1]; S[2] += c2 * b[0] * b[2];
+        S[3] += c2 * b[1] * b[1]; S[4] += c2 * b[1] * b[2]; S[5] += c2 * b[2] * b[2];
+    }
+};
+
+// one sample of Eq. (gmcp_potential) and its Sec. 4.2 derivatives
+template <class T>
+__device__ __forceinline__ void sample_add(Acc<T>& A, double kq, double w, double gamma, double g,
+                                           double eps, const double* bs) {
+    T Bv, dB, d2B;
+    barrier((T)g, (T)eps, Bv, dB, d2B);
+    T coef = (T)(kq * w * gamma);
+    T b[3] = {(T)bs[0], (T)bs[1], (T)bs[2]};
+    A.add((double)(coef * Bv), coef * dB, rmax(coef * d2B, T(0)), b);
+}
+
+template <class T> __device__ __forceinline__ T shfl_x(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+
+// ---------------------------------------------------------------------------
+// the sample kernel
+// ---------------------------------------------------------------------------
+template <int NK, class T, int MODE>
+__global__ void __launch_bounds__(256)
+k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
+          const double* __restrict__ xm, double* __restrict__ triE, T* __restrict__ triG,
+          T* __restrict__ triS, T* __restrict__ triN, long long* counters,
+          const double* __restrict__ dx, const double* __restrict__ dxm,
+          unsigned long long* alpha_bits) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+    const int n_active = *C.n_active;
+    const double eps_max = P.dhat;
+    const double omega = 1.0 / (double)NK;
+    long long cnt_f = 0, cnt_e = 0, cnt_p = 0, cnt_eval = 0;
+    double beta_k[3];
+    rule_beta(P.L, lane % NK, beta_k);
+    for (int i = warp; i < n_active; i += nwarps) {
+        const int64_t t = C.active[i];
+        const int32_t* Tt = S.stri + 3 * t;
+        const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
+        const V3<double> X0 = ld3(S.X, Tt[0]), X1 = ld3(S.X, Tt[1]), X2 = ld3(S.X, Tt[2]);
+        const V3<double> cr = cross(x1 - x0, x2 - x0);
+        const double clen = sqrt(dot(cr, cr));
+        const V3<double> ns = {cr.x / clen, cr.y / clen, cr.z / clen};
+        const double As = 0.5 * clen;
+        const V3<double> cr0 = cross(X1 - X0, X2 - X0);
+        const double clen0 = sqrt(dot(cr0, cr0));
+        const V3<double> ns0 = {cr0.x / clen0, cr0.y / clen0, cr0.z / clen0};
+        const double* sb = S.srest_box + 6 * t;
+        const int32_t* cnt = C.count + 4 * t;
+        const int nf = min(cnt[0], C.cap_f), ne = min(cnt[1], C.cap_e), np = min(cnt[2], C.cap_p);
+        Acc<T> A;
+        A.zero();
+        // ---------------- face samples ----------------
+        {
+            const V3<double> xs = interp(beta_k, x0, x1, x2);
+            const V3<float> xs_rel = tof(xs - x0);
+            const V3<float> ns_f = tof(ns);
+            const double ell = sqrt(rmin(dot(x1 - x0, x1 - x0), rmin(dot(x2 - x1, x2 - x1), dot(x0 - x2, x0 - x2))));
+            const float g_fp64_below = (float)(1e-2 * ell);
+            const int32_t* Lf = C.face + t * C.cap_f;
+            for (int it = lane; it < nf * NK; it += 32) {
+                const int32_t m = Lf[it / NK];
+                const int32_t* M = S.mtri + 3 * (int64_t)m;
+                const V3<double> y0 = ld3(xm, M[0]), y1 = ld3(xm, M[1]), y2 = ld3(xm, M[2]);
+                ++cnt_eval;
+                double g, bm[3];
+                bool ok;
+                if (sizeof(T) == 4 && MODE == MODE_EVAL) {
+                    float gf, bmf[3];
+                    ok = face_geom<float>(xs_rel, ns_f, tof(y0 - x0), tof(y1 - x0), tof(y2 - x0), gf, bmf);
+                    if (ok && gf < g_fp64_below) {
+                        ok = face_geom<double>(xs, ns, y0, y1, y2, g, bm);
+                    } else {
+                        g = gf; bm[0] = bmf[0]; bm[1] = bmf[1]; bm[2] = bmf[2];
+                    }
+                } else {
+                    ok = face_geom<double>(xs, ns, y0, y1, y2, g, bm);
+                }
+                if (!ok) continue;
+                double eps = eps_max;
+                const double* mb = S.mrest_box + 6 * (int64_t)m;
+                if (!rest_far(sb, sb + 3, mb, mb + 3, eps_max)) {
+                    const V3<double> xs0 = interp(beta_k, X0, X1, X2);
+                    double g0, bm0[3];
+                    bool ok0 = face_geom<double>(xs0, ns0, ld3(S.Y0, M[0]), ld3(S.Y0, M[1]),
+                                                 ld3(S.Y0, M[2]), g0, bm0);
+                    if (ok0) eps = rmin(0.9 * g0, eps_max);
+                }
+                if (!(g < eps)) continue;
+                const double gamma = hermite(min3(bm), P.delta_T);
+                ++cnt_f;
+                if (MODE == MODE_EVAL) {
+                    sample_add<T>(A, P.kappa, omega * As, gamma, g, eps, beta_k);
+                } else {
+                    const V3<double> dsv = interp(beta_k, ld3(dx, Tt[0]), ld3(dx, Tt[1]), ld3(dx, Tt[2]));
+                    const double ds = dot(ns, dsv);
+                    const double dm = dxm ? dot(ns, interp(bm, ld3(dxm, M[0]), ld3(dxm, M[1]), ld3(dxm, M[2]))) : 0.0;
+                    const double dg = dm - ds;
+                    if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                }
+            }
+        }
+        // ---------------- edge samples (FP64 geometry) ----------------
+        {
+            const int32_t* Le = C.edge + t * C.cap_e;
+            const double gp = 1.0 / sqrt(3.0);
+            for (int it = lane; it < ne * 2; it += 32) {
+                const int32_t me = Le[it >> 1];
+                const int q = it & 1;
+                const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
+                const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
+                if (!any_facing(S, xm, S.me_tri + a0, a1 - a0, ns)) continue;
+                const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
+                double bA[3], bB[3];
+                bary(ya, x0, x1, x2, bA);
+                bary(yb, x0, x1, x2, bB);
+                // clip the projected edge by the slave triangle: all beta >= 0
+                double lo = 0.0, hi = 1.0;
+                bool empty = false;
+                for (int a = 0; a < 3; ++a) {
+                    const double D = bB[a] - bA[a];
+                    if (D > 0.0) lo = rmax(lo, -bA[a] / D);
+                    else if (D < 0.0) hi = rmin(hi, -bA[a] / D);
+                    else if (bA[a] < 0.0) empty = true;
+                }
+                if (empty || !(hi > lo)) continue;
+                const V3<double> tv = yb - ya;
+                const double tn = dot(tv, ns);
+                const V3<double> tp = tv - tn * ns;
+                const double ell = (hi - lo) * sqrt(dot(tp, tp));
+                const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+                const double eta = q == 0 ? mid - half * gp : mid + half * gp;
+                const V3<double> xmk = (1.0 - eta) * ya + eta * yb;
+                double bsk[3];
+                bary(xmk, x0, x1, x2, bsk);
+                const V3<double> xs = interp(bsk, x0, x1, x2);
+                const double g = dot(ns, xmk - xs);
+                if (!(g > 0.0)) continue;
+                double eps = eps_max;
+                const V3<double> Ya = ld3(S.Y0, ia), Yb = ld3(S.Y0, ib);
+                const double elo[3] = {rmin(Ya.x, Yb.x), rmin(Ya.y, Yb.y), rmin(Ya.z, Yb.z)};
+                const double ehi[3] = {rmax(Ya.x, Yb.x), rmax(Ya.y, Yb.y), rmax(Ya.z, Yb.z)};
+                if (!rest_far(sb, sb + 3, elo, ehi, eps_max)) {
+                    const V3<double> xm0 = (1.0 - eta) * Ya + eta * Yb;
+                    double bs0[3];
+                    bary(xm0, X0, X1, X2, bs0);
+                    const double g0 = dot(ns0, xm0 - interp(bs0, X0, X1, X2));
+                    if (min3(bs0) >= 0.0 && g0 > 0.0) eps = rmin(0.9 * g0, eps_max);
+                }
+                if (!(g < eps)) continue;
+                ++cnt_e;
+                const double gamma = hermite(eta, P.delta_e) * hermite(1.0 - eta, P.delta_e);
+                if (MODE == MODE_EVAL) {
+                    sample_add<T>(A, P.kappa_edge, 0.5 * ell, gamma, g, eps, bsk);
+                } else {
+                    const double ds = dot(ns, interp(bsk, ld3(dx, Tt[0]), ld3(dx, Tt[1]), ld3(dx, Tt[2])));
+                    const double dm = dxm ? dot(ns, (1.0 - eta) * ld3(dxm, ia) + eta * ld3(dxm, ib)) : 0.0;
+                    const double dg = dm - ds;
+                    if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                }
+            }
+        }
+        // ---------------- point samples (FP64 geometry) ----------------
+        {
+            const int32_t* Lp = C.point + t * C.cap_p;
+            for (int it = lane; it < np; it += 32) {
+                const int32_t u = Lp[it];
+                const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
+                if (!any_facing(S, xm, S.mv_tri + a0, a1 - a0, ns)) continue;
+                const V3<double> y = ld3(xm, u);
+                double bs[3];
+                bary(y, x0, x1, x2, bs);
+                if (!(min3(bs) >= 0.0)) continue;
+                const double g = dot(ns, y - interp(bs, x0, x1, x2));
+                if (!(g > 0.0)) continue;
+                double eps = eps_max;
+                const V3<double> Y = ld3(S.Y0, u);
+                const double yb[3] = {Y.x, Y.y, Y.z};
+                if (!rest_far(sb, sb + 3, yb, yb, eps_max)) {
+                    double bs0[3];
+                    bary(Y, X0, X1, X2, bs0);
+                    const double g0 = dot(ns0, Y - interp(bs0, X0, X1, X2));
+                    if (min3(bs0) >= 0.0 && g0 > 0.0) eps = rmin(0.9 * g0, eps_max);
+                }
+                if (!(g < eps)) continue;
+                ++cnt_p;
+                if (MODE == MODE_EVAL) {
+                    sample_add<T>(A, P.kappa_point, 1.0, 1.0, g, eps, bs);
+                } else {
+                    const double ds = dot(ns, interp(bs, ld3(dx, Tt[0]), ld3(dx, Tt[1]), ld3(dx, Tt[2])));
+                    const double dm = dxm ? dot(ns, ld3(dxm, u)) : 0.0;
+                    const double dg = dm - ds;
+                    if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                }
+            }
+        }
+        // ---------------- fixed-order warp reduction ----------------
+        if (MODE == MODE_EVAL) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                A.E += shfl_x(A.E, o);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) A.G[q] += shfl_x(A.G[q], o);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) A.S[q] += shfl_x(A.S[q], o);
+            }
+            if (lane == 0) {
+                triE[t] = A.E;
+                for (int q = 0; q < 3; ++q) triG[3 * t + q] = A.G[q];
+                for (int q = 0; q < 6; ++q) triS[6 * t + q] = A.S[q];
+                triN[3 * t + 0] = (T)ns.x; triN[3 * t + 1] = (T)ns.y; triN[3 * t + 2] = (T)ns.z;
+            }
+        } else {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) A.amin = rmin(A.amin, shfl_x(A.amin, o));
+            if (lane == 0 && A.amin < INFINITY)
+                atomicMin(alpha_bits, (unsigned long long)__double_as_longlong(A.amin));
+        }
+    }
+    // counters (integers: order does not matter)
+    if (counters) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt_f += shfl_x(cnt_f, o); cnt_e += shfl_x(cnt_e, o);
+            cnt_p += shfl_x(cnt_p, o); cnt_eval += shfl_x(cnt_eval, o);
+        }
+        if (lane == 0 && (cnt_f | cnt_e | cnt_p | cnt_eval)) {
+            atomic_add_ll(&counters[0], cnt_f); atomic_add_ll(&counters[1], cnt_e);
+            atomic_add_ll(&counters[2], cnt_p); atomic_add_ll(&counters[3], cnt_eval);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// deterministic gathers
+// ---------------------------------------------------------------------------
+template <class T, class TO>
+__global__ void k_gather_grad(int64_t nv, const int32_t* __restrict__ off, const int32_t* __restrict__ ent,
+                              const T* __restrict__ triG, const T* __restrict__ triN, TO* __restrict__ out) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    T g0 = T(0), g1 = T(0), g2 = T(0);
+    for (int k = off[v]; k < off[v + 1]; ++k) {
+        const int e = ent[k];
+        const int64_t t = e >> 2;
+        const int a = e & 3;
+        const T c = triG[3 * t + a];
+        g0 -= c * triN[3 * t]; g1 -= c * triN[3 * t + 1]; g2 -= c * triN[3 * t + 2];
+    }
+    out[3 * v] = (TO)g0; out[3 * v + 1] = (TO)g1; out[3 * v + 2] = (TO)g2;
+}
+
+__device__ __forceinline__ int sym_idx(int a, int b) {
+    // 00 01 02 11 12 22
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+}
+
+template <class T>
+__global__ void k_gather_hess(int64_t nnzb, const int32_t* __restrict__ off, const int32_t* __restrict__ ent,
+                              const T* __restrict__ triS, const T* __restrict__ triN, T* __restrict__ out) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nnzb) return;
+    T h[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) h[q] = T(0);
+    for (int k = off[b]; k < off[b + 1]; ++k) {
+        const int e = ent[k];
+        const int64_t t = e >> 4;
+        const int a = (e >> 2) & 3, c = e & 3;
+        const T s = triS[6 * t + sym_idx(a, c)];
+        const T nn[3] = {triN[3 * t], triN[3 * t + 1], triN[3 * t + 2]};
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) h[3 * p + q] += s * nn[p] * nn[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) out[9 * b + q] = h[q];
+}
+
+// two-pass fixed-order sum of n doubles
+constexpr int kRedThreads = 256;
+constexpr int kRedPer = 8;
+__global__ void k_reduce_partial(const double* __restrict__ in, int64_t n, double* __restrict__ part) {
+    __shared__ double sh[kRedThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kRedThreads * kRedPer;
+    double s = 0.0;
+    for (int i = 0; i < kRedPer; ++i) {
+        const int64_t k = base + (int64_t)i * kRedThreads + threadIdx.x;
+        if (k < n) s += in[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < kRedThreads / 32 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+__global__ void k_reduce_final(const double* __restrict__ part, int64_t n, double* __restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += 1024) s += part[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = sh[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) *out = v;
+    }
+}
+
+template <int NK, class T, int MODE>
+cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* Sm, T* N,
+                           long long* counters, const double* dx, const double* dxm,
+                           unsigned long long* alpha_bits) {
+    const int threads = 256;
+    const int blocks = sm_count(c.device) * 8;
+    k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
+        c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int sm_count(int device) {
+    static int cached[64] = {0};
+    if (device >= 0 && device < 64 && cached[device]) return cached[device];
+    int n = 148;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, device);
+    if (device >= 0 && device < 64) cached[device] = n;
+    return n;
+}
+
+cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out) {
+    const int64_t per = (int64_t)kRedThreads * kRedPer;
+    const int64_t nb = (n + per - 1) / per;
+    GMCP_CUDA_TRY(c.red_tmp.ensure((size_t)nb + 2));
+    if (nb > 0) {
+        k_reduce_partial<<<(unsigned)nb, kRedThreads, 0, c.stream>>>(in, n, c.red_tmp.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    k_reduce_final<<<1, 1024, 0, c.stream>>>(c.red_tmp.p, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* energy_dev,
+                         void* grad_dev, bool want_hess, long long* counters) {
+    const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    {
+        ProfScope ps(c.prof, c.stream, "samples");
+        if (f32) {
+            if (c.P.nk == 4)
+                GMCP_CUDA_TRY((launch_samples<4, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, nullptr, nullptr, nullptr)));
+            else
+                GMCP_CUDA_TRY((launch_samples<16, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, nullptr, nullptr, nullptr)));
+        } else {
+            if (c.P.nk == 4)
+                GMCP_CUDA_TRY((launch_samples<4, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, nullptr, nullptr, nullptr)));
+            else
+                GMCP_CUDA_TRY((launch_samples<16, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, nullptr, nullptr, nullptr)));
+        }
+    }
+    const int B = 256;
+    if (grad_dev) {
+        ProfScope ps(c.prof, c.stream, "gather_grad");
+        const unsigned g = (unsigned)((c.nv + B - 1) / B);
+        if (f32)
+            k_gather_grad<float, float><<<g, B, 0, c.stream>>>(c.nv, c.vt_off.p, c.vt_ent.p, c.tri_G32.p, c.tri_n32.p, (float*)grad_dev);
+        else
+            k_gather_grad<double, double><<<g, B, 0, c.stream>>>(c.nv, c.vt_off.p, c.vt_ent.p, c.tri_G64.p, c.tri_n64.p, (double*)grad_dev);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    if (want_hess && c.cb_nnzb > 0) {
+        ProfScope ps(c.prof, c.stream, "gather_hess");
+        const unsigned g = (unsigned)((c.cb_nnzb + B - 1) / B);
+        if (f32)
+            k_gather_hess<float><<<g, B, 0, c.stream>>>(c.cb_nnzb, c.cb_src_off.p, c.cb_src.p, c.tri_S32.p, c.tri_n32.p, c.cb_val32.p);
+        else
+            k_gather_hess<double><<<g, B, 0, c.stream>>>(c.cb_nnzb, c.cb_src_off.p, c.cb_src.p, c.tri_S64.p, c.tri_n64.p, c.cb_val64.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    if (energy_dev) {
+        ProfScope ps(c.prof, c.stream, "reduce");
+        GMCP_CUDA_TRY(reduce_sum(c, c.tri_E.p, c.ns, energy_dev));
+    }
+    return cudaSuccess;
+}
+
+cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const double* dx,
+                              const double* dxm, unsigned long long* alpha_bits) {
+    ProfScope ps(c.prof, c.stream, "alpha_lin");
+    // the step bound always uses FP64 geometry
+    if (c.P.nk == 4)
+        return launch_samples<4, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm, alpha_bits);
+    return launch_samples<16, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm, alpha_bits);
+}
+
+}  // namespace gmcp

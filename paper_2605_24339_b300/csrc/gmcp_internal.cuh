@@ -1,0 +1,279 @@
+// gmcp_internal.cuh -- internal types shared by the libgmcp translation units.
+//
+// Layout in HBM (all device arrays owned by the context unless noted):
+//   positions            caller-owned FP64 [n][3] (x, y, z per vertex)
+//   slave / master tris  int32 [n][3]; master edges int32 [n][2] sorted (a<b)
+//   per-slave-tri output energy (FP64), gradient coefficients G[3], Hessian
+//                        coefficients S[6] and the frozen normal n[3] (FP64
+//                        or FP32 by precision), written by the sample kernel
+//                        and read by the deterministic gathers
+//   candidate lists      fixed-capacity slots per slave triangle, sorted
+//   broad-phase grid     dense uniform grid per environment, counting-sorted
+//                        master triangle ids per cell
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "gmcp.h"
+
+namespace gmcp {
+
+// ------------------------------------------------------------------------
+// device buffers
+// ------------------------------------------------------------------------
+template <class T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    cudaError_t alloc(size_t count) {
+        release();
+        if (count == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&p), count * sizeof(T));
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        n = count;
+        return cudaSuccess;
+    }
+    cudaError_t ensure(size_t count) { return count <= n ? cudaSuccess : alloc(count); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    cudaError_t upload(const T* host, size_t count, cudaStream_t s) {
+        cudaError_t e = ensure(count);
+        if (e != cudaSuccess || count == 0) return e;
+        return cudaMemcpyAsync(p, host, count * sizeof(T), cudaMemcpyHostToDevice, s);
+    }
+};
+
+// ------------------------------------------------------------------------
+// read-only scene view passed to kernels by value
+// ------------------------------------------------------------------------
+struct SceneView {
+    int32_t nv, ns, nmv, nmt, nme, nse, n_env;
+    const int32_t* stri;          // [ns][3]
+    const int32_t* mtri;          // [nmt][3]
+    const int32_t* medge;         // [nme][2]
+    const int32_t* me_tri_off;    // [nme+1] master edge -> adjacent tris
+    const int32_t* me_tri;
+    const int32_t* mv_tri_off;    // [nmv+1] master vertex -> adjacent tris
+    const int32_t* mv_tri;
+    const int32_t* mtri_own_edge; // [nmt][3] edges owned by the tri (lowest adjacent id), -1
+    const int32_t* mtri_own_vert; // [nmt][3]
+    const int32_t* stri_own_vert; // [ns][3] slave surface vertices owned by the tri
+    const int32_t* stri_own_edge; // [ns][3] slave edges owned by the tri (ids into sedge)
+    const int32_t* sedge;         // [nse][2]
+    const int32_t* stri_env;      // [ns]
+    const int32_t* mtri_env;      // [nmt]
+    const double* X;              // pad rest [nv][3]
+    const double* Y0;             // master at t = 0 [nmv][3]
+    const double* srest_box;      // [ns][6] rest box of slave tris (lo xyz, hi xyz)
+    const double* mrest_box;      // [nmt][6] rest box of master tris
+    // broad-phase grid, one dense box of cells per environment
+    const double* grid_org;       // [n_env][3]
+    const double* grid_inv;       // [n_env] 1 / cell size
+    const int32_t* grid_dim;      // [n_env][3]
+    const int64_t* grid_off;      // [n_env+1] first cell of each env
+    double margin;                // coarse-test slack (covers rounding of grown boxes)
+};
+
+struct Params {
+    int precision;
+    double dhat, kappa, kappa_edge, kappa_point, delta_T, delta_e;
+    int L, nk;
+    double dhat_guard, kappa_guard;
+    double ccd_slack;
+    int ccd_max_iter;
+};
+
+// Candidate list storage: fixed capacity per slave triangle.
+struct CandView {
+    int32_t cap_f, cap_e, cap_p;
+    int32_t* face;      // [ns][cap_f]
+    int32_t* edge;      // [ns][cap_e]
+    int32_t* point;     // [ns][cap_p]
+    int32_t* count;     // [ns][4]: face, edge, point, pad
+    int32_t* active;    // [ns] slave tris with at least one candidate
+    int32_t* n_active;  // scalar
+    int32_t* overflow;  // [3] max count seen per kind (for regrowth)
+};
+
+// ------------------------------------------------------------------------
+// section profiler: CUDA events around named groups of launches on the
+// context stream; elapsed times are collected when the caller asks
+// ------------------------------------------------------------------------
+struct Profiler {
+    static constexpr int kMax = 16;
+    bool on = false;
+    const char* names[kMax] = {nullptr};
+    double ms[kMax] = {0};
+    long long calls[kMax] = {0};
+    struct Pending { int sec; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    int sec(const char* name) {
+        for (int i = 0; i < kMax; ++i) {
+            if (names[i] == name) return i;
+            if (!names[i]) { names[i] = name; return i; }
+        }
+        return kMax - 1;
+    }
+    void collect() {
+        for (auto& p : pending) {
+            float t = 0.f;
+            cudaEventSynchronize(p.b);
+            cudaEventElapsedTime(&t, p.a, p.b);
+            ms[p.sec] += t;
+            calls[p.sec] += 1;
+            pool.push_back(p.a);
+            pool.push_back(p.b);
+        }
+        pending.clear();
+    }
+    void reset() {
+        collect();
+        for (int i = 0; i < kMax; ++i) { ms[i] = 0; calls[i] = 0; }
+    }
+    ~Profiler() {
+        for (auto& p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+struct ProfScope {
+    Profiler& P;
+    cudaStream_t s;
+    int sec = -1;
+    cudaEvent_t a{}, b{};
+    ProfScope(Profiler& p, cudaStream_t st, const char* name) : P(p), s(st) {
+        if (!P.on) return;
+        sec = P.sec(name);
+        a = P.get(); b = P.get();
+        cudaEventRecord(a, s);
+    }
+    ~ProfScope() {
+        if (sec < 0) return;
+        cudaEventRecord(b, s);
+        P.pending.push_back({sec, a, b});
+    }
+};
+
+// ------------------------------------------------------------------------
+// the context
+// ------------------------------------------------------------------------
+struct Ctx {
+    ipc_params prm;
+    Params P;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int device = 0;
+
+    // sizes
+    int64_t nv = 0, nt = 0, ns = 0, nmv = 0, nmt = 0, nme = 0, nse = 0;
+    int n_env = 0;
+    int64_t n_cells = 0;
+
+    // host copies needed for topology
+    std::vector<int64_t> env_vert_off, env_tet_off, env_stri_off, env_mvert_off, env_mtri_off;
+
+    // static device topology
+    DBuf<int32_t> stri, mtri, medge, me_tri_off, me_tri, mv_tri_off, mv_tri;
+    DBuf<int32_t> mtri_own_edge, mtri_own_vert, stri_own_vert, stri_own_edge, sedge;
+    DBuf<int32_t> stri_env, mtri_env;
+    DBuf<double> X, Y0, srest_box, mrest_box;
+    DBuf<double> grid_org, grid_inv;
+    DBuf<int32_t> grid_dim;
+    DBuf<int64_t> grid_off;
+    double margin = 0.0;
+
+    // gather topology: vertex -> (tri, corner), contact BSR pattern and its
+    // per-block contribution lists
+    DBuf<int32_t> vt_off, vt_ent;              // [nv+1], entries tri*4+corner
+    DBuf<int32_t> cb_row, cb_col;              // contact BSR [nv+1], [nnzb]
+    DBuf<int32_t> cb_src_off, cb_src;          // [nnzb+1], entries tri*16+a*4+b
+    int64_t cb_nnzb = 0;
+
+    // per-call broad-phase buffers
+    DBuf<double> mbox;                          // [nmt][6]
+    DBuf<int32_t> cell_cnt, cell_start, cell_ent;
+    DBuf<int32_t> scan_tmp;
+    DBuf<int32_t> cand_face, cand_edge, cand_point, cand_count, active, misc_i32;
+    int32_t cap_f = 32, cap_e = 32, cap_p = 16;
+
+    // per-call sample outputs
+    DBuf<double> tri_E;
+    DBuf<double> tri_G64, tri_S64, tri_n64;
+    DBuf<float> tri_G32, tri_S32, tri_n32;
+    DBuf<double> cb_val64;
+    DBuf<float> cb_val32;
+    DBuf<double> red_tmp;                       // reduction partials
+    DBuf<unsigned long long> u64_tmp;           // alpha minima
+    DBuf<long long> i64_tmp;                    // counters
+    DBuf<double> dxm;                           // master displacement for CCD
+    DBuf<double> scal;                          // device scalars (energy, ...)
+
+    // pinned host scratch for scalars
+    double* h_scalars = nullptr;
+    long long* h_counts = nullptr;
+
+    Profiler prof;
+
+    SceneView view() const;
+    CandView cand() {
+        CandView c;
+        c.cap_f = cap_f; c.cap_e = cap_e; c.cap_p = cap_p;
+        c.face = cand_face.p; c.edge = cand_edge.p; c.point = cand_point.p;
+        c.count = cand_count.p; c.active = active.p;
+        c.n_active = misc_i32.p; c.overflow = misc_i32.p + 1;
+        return c;
+    }
+};
+
+// ------------------------------------------------------------------------
+// launchers implemented in the .cu files
+// ------------------------------------------------------------------------
+// broadphase.cu
+cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept);
+cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm);
+cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
+                        const double* dxm, unsigned long long* alpha_bits, long long* counters);
+// scan.cu
+cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
+                               size_t tmp_n, cudaStream_t s);
+size_t scan_tmp_size(int64_t n);
+// api.cu
+cudaError_t run_candidates(Ctx& c, const double* x, const double* xm);
+// contact.cu
+cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* energy_dev,
+                         void* grad_dev, bool want_hess, long long* counters);
+cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const double* dx,
+                              const double* dxm, unsigned long long* alpha_bits);
+cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out);
+int sm_count(int device);
+
+}  // namespace gmcp
+
+// integer atomic add on a signed 64-bit counter (two's complement wraps the same)
+__device__ __forceinline__ void atomic_add_ll(long long* p, long long v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+
+#define GMCP_CUDA_TRY(expr)                                                          \
+    do {                                                                             \
+        cudaError_t _e = (expr);                                                     \
+        if (_e != cudaSuccess) return _e;                                            \
+    } while (0)

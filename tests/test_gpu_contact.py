@@ -1,0 +1,186 @@
+"""GPU parity of the contact pass (C ABI) against the FP64 CPU oracle.
+
+Tolerances: candidate sets bit-exact; FP64 path relative 1e-12 (energy,
+gradient relative L2, Hessian blocks relative Frobenius); mixed path 1e-5 on
+energy and gradient and 1e-4 on Hessian blocks; CCD step never larger than
+the oracle's (additive CCD bit-identical)."""
+import numpy as np
+import pytest
+
+from helpers import small_indent
+from paper_2605_24339_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_24339_b300 import binding
+    binding.lib()
+    return binding
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    d = np.linalg.norm((a - b).ravel())
+    n = np.linalg.norm(b.ravel())
+    return d / n if n > 0 else d
+
+
+def bsr_dict(rp, ci, vals):
+    rp, ci, vals = rp.cpu().numpy(), ci.cpu().numpy(), vals.cpu().numpy().astype(np.float64)
+    out = {}
+    for i in range(rp.shape[0] - 1):
+        for k in range(rp[i], rp[i + 1]):
+            out[(i, int(ci[k]))] = vals[k]
+    return out
+
+
+def hess_rel(gpu_h, orc):
+    G = bsr_dict(*gpu_h)
+    O = {(int(i), int(j)): b for (i, j), b in zip(orc["blk_ij"], orc["blk"])}
+    num = den = 0.0
+    for k in set(G) | set(O):
+        g = G.get(k, np.zeros((3, 3)))
+        o = O.get(k, np.zeros((3, 3)))
+        num += np.sum((g - o) ** 2)
+        den += np.sum(o ** 2)
+    return np.sqrt(num / den) if den > 0 else np.sqrt(num)
+
+
+def _scenes():
+    out = []
+    sc, x = small_indent(n_quads=10, subdiv=3, press=0.12e-3, L=1)
+    out.append(("indent_L1", sc, x))
+    sc, x = small_indent(n_quads=10, subdiv=3, press=0.12e-3, L=2)
+    out.append(("indent_L2", sc, x))
+    # three envs of different sizes batched, each pressed differently
+    parts, xs = [], []
+    for k, (nq, press) in enumerate([(6, 0.08e-3), (9, 0.15e-3), (4, 0.05e-3)]):
+        s, xx = small_indent(n_quads=nq, subdiv=2 + (k % 2), press=press, seed=20 + k)
+        parts.append(s)
+        xs.append(xx)
+    out.append(("batch3", S.concat_envs(parts), np.concatenate(xs)))
+    return out
+
+
+SCENES = _scenes()
+IDS = [s[0] for s in SCENES]
+
+
+@pytest.mark.parametrize("name,sc,x", SCENES, ids=IDS)
+def test_candidates_bit_exact(B, oracle_mod, name, sc, x):
+    ctx = B.Context(sc, precision="fp64")
+    O = oracle_mod.Scene(sc)
+    for xx in (sc.X, x):
+        cnt = ctx.candidates(xx, sc.Y0)
+        for kind in range(3):
+            g = ctx.candidate_pairs(kind)
+            o = O.candidates(kind, xx, sc.Y0)
+            np.testing.assert_array_equal(g, o, err_msg=f"kind {kind}")
+        assert cnt["face"] == O.candidates(0, xx, sc.Y0).shape[0]
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,sc,x", SCENES, ids=IDS)
+def test_barrier_eval_fp64_parity(B, oracle_mod, name, sc, x):
+    ctx = B.Context(sc, precision="fp64")
+    O = oracle_mod.Scene(sc)
+    r = ctx.barrier_eval(x, sc.Y0)
+    o = O.contact(x, sc.Y0)
+    assert o["energy"] > 0
+    assert r["energy"] == pytest.approx(o["energy"], rel=1e-12)
+    assert rel(r["grad"].cpu().numpy(), o["grad"]) < 1e-12
+    assert hess_rel(r["hess"], o) < 1e-12
+    c = r["counts"]
+    assert (c["point"], c["edge"], c["face"]) == tuple(int(v) for v in o["n_samples"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("name,sc,x", SCENES, ids=IDS)
+def test_barrier_eval_mixed_parity(B, oracle_mod, name, sc, x):
+    ctx = B.Context(sc, precision="mixed")
+    O = oracle_mod.Scene(sc)
+    r = ctx.barrier_eval(x, sc.Y0)
+    o = O.contact(x, sc.Y0)
+    assert r["grad"].dtype == torch.float32
+    assert r["energy"] == pytest.approx(o["energy"], rel=1e-5)
+    assert rel(r["grad"].cpu().numpy(), o["grad"]) < 1e-5
+    assert hess_rel(r["hess"], o) < 1e-4
+    ctx.close()
+
+
+def test_barrier_eval_deterministic(B):
+    sc, x = small_indent(n_quads=12, subdiv=3, press=0.15e-3, L=2)
+    for prec in ("fp64", "mixed"):
+        ctx = B.Context(sc, precision=prec)
+        a = ctx.barrier_eval(x, sc.Y0)
+        b = ctx.barrier_eval(x, sc.Y0)
+        assert a["energy"] == b["energy"]
+        assert torch.equal(a["grad"], b["grad"])
+        assert torch.equal(a["hess"][2], b["hess"][2])
+        ctx.close()
+
+
+def test_no_contact_is_zero(B):
+    sc, x = small_indent(n_quads=6, subdiv=2)
+    ctx = B.Context(sc, precision="fp64")
+    r = ctx.barrier_eval(sc.X, sc.Y0)        # rest: 2 dhat away, no contact
+    assert r["energy"] == 0.0
+    assert float(r["grad"].abs().max()) == 0.0
+    assert float(r["hess"][2].abs().max()) == 0.0
+    ctx.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_ccd_max_step_parity(B, oracle_mod, seed):
+    sc, x = small_indent(n_quads=6, subdiv=2, press=0.06e-3, seed=seed)
+    ctx = B.Context(sc, precision="fp64")
+    O = oracle_mod.Scene(sc)
+    rng = np.random.default_rng(seed)
+    dx = np.zeros_like(x)
+    dx[:, 2] = -(2e-4 + 2e-4 * rng.random(x.shape[0]))
+    dx[:, :2] = 3e-5 * rng.normal(size=(x.shape[0], 2))
+    g = ctx.ccd_max_step(x, dx, sc.Y0)
+    a, al, aa = O.ccd_max_step(x, dx, sc.Y0)
+    assert g["alpha_accd"] == aa                      # bit-identical
+    assert g["alpha_lin"] <= al and g["alpha_lin"] == pytest.approx(al, rel=1e-9)
+    assert g["alpha"] <= a and g["alpha"] == pytest.approx(a, rel=1e-9)
+    assert 0 < g["alpha"] < 1
+    # the same kind of approach expressed as master motion
+    xm1 = sc.Y0 + np.array([0.0, 0.0, 3e-4])
+    g2 = ctx.ccd_max_step(x, np.zeros_like(x), sc.Y0, xm1)
+    a2, al2, aa2 = O.ccd_max_step(x, np.zeros_like(x), sc.Y0, xm1)
+    assert g2["alpha_accd"] == aa2
+    assert g2["alpha"] <= a2 and g2["alpha"] == pytest.approx(a2, rel=1e-9)
+    ctx.close()
+
+
+def test_full_size_terrain_sampled_parity(B, oracle_mod):
+    """Terrain workload at full size (131,072 slave tris x 16 samples, 199,712
+    master tris) in the precision modes the benchmark times: gradient rows and
+    Hessian diagonal blocks of sampled contact vertices against the oracle
+    evaluated on exactly the slave triangles around them."""
+    sc = S.gel_on_terrain()
+    x = S.drape_on_master(sc, 0.15e-3)
+    O = oracle_mod.Scene(sc)
+    for prec, tol_g, tol_h in (("fp64", 1e-12, 1e-12), ("mixed", 1e-5, 1e-4)):
+        ctx = B.Context(sc, precision=prec)
+        r = ctx.barrier_eval(x, sc.Y0)
+        grad = r["grad"].cpu().numpy().astype(np.float64)
+        G = bsr_dict(*r["hess"])
+        active = np.nonzero(np.abs(grad).sum(axis=1) > 0)[0]
+        assert active.shape[0] > 1000
+        rng = np.random.default_rng(3)
+        verts = rng.choice(active, 12, replace=False)
+        tris = np.unique(np.nonzero(np.isin(sc.stris, verts).any(axis=1))[0])
+        o = O.contact(x, sc.Y0, subset=tris)
+        Ob = {(int(i), int(j)): b for (i, j), b in zip(o["blk_ij"], o["blk"])}
+        for v in verts:
+            assert rel(grad[v], o["grad"][v]) < tol_g
+            assert rel(G[(int(v), int(v))], Ob[(int(v), int(v))]) < tol_h
+        ctx.close()
