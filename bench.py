@@ -1,0 +1,359 @@
+"""Benchmark of the GMCP contact pass on one B300 (or N independent replicas).
+
+A step is one full contact pass through the C ABI on the gel-on-terrain
+workload (256x256-quad gel pad, 131,072 slave triangles x 16 face samples =
+2,097,152 samples, against a 199,712-triangle Perlin terrain, dhat = 5e-5 m),
+mixed precision (FP32 barrier, FP64 distance anchors and CCD):
+  ipc_barrier_eval  -- broad phase, samples, energy, gradient, BSR Hessian
+  ipc_ccd_max_step  -- linearised-gap bound and additive CCD for a step dx
+The pad state is the terrain pressed 0.15 mm deep (scenes.drape_on_master);
+dx is a seeded downward press of 5 um x U[0.5, 1.5] per vertex plus 1 um
+tangential noise.  Inputs stay resident in HBM; L2 (126 MB) is flushed by
+writing a 256 MB buffer between timed steps, outside the timed region.
+
+metric = contact samples per second, samples per pass = face samples
+(n_slave_tris x 16) + 2 x edge candidates + point candidates.
+
+``--impl reference`` times the FP64 CPU oracle (the correctness reference,
+single-threaded) on a bounded window of the same workload (half-width 2 mm
+around the highest terrain peak) with the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "contact samples/s (barrier E+grad+H+CCD)"
+UNIT = "samples/s"
+WORKLOAD = "gel_on_terrain 256x256 pad (131,072 slave tris x 16 samples) vs 199,712-tri Perlin terrain, pressed 0.15 mm"
+CROP_HALF_WIDTH = 2.0e-3
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def make_workload(seed=11):
+    from paper_2605_24339_b300 import scenes as S
+    sc = S.gel_on_terrain()
+    x = S.drape_on_master(sc, 0.15e-3)
+    rng = np.random.default_rng(seed)
+    dx = np.zeros_like(x)
+    dx[:, 2] = -5e-6 * (0.5 + rng.random(x.shape[0]))
+    dx[:, :2] = 1e-6 * rng.normal(size=(x.shape[0], 2))
+    return sc, x, dx
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl"
+        dist.init_process_group(backend=backend)
+        return rank, world, dist
+    return 0, 1, None
+
+
+def max_over_ranks(v, dist):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def samples_per_pass(ctx, x, xm, nk):
+    c = ctx.candidates(x, xm)
+    return ctx.ns * nk + 2 * c["edge"] + c["point"], c
+
+
+def algorithmic_bytes(ctx, sc, x, cand, precision):
+    """Bytes each section must move at least once (unique inputs, outputs),
+    computed from the candidate lists of the benchmarked state."""
+    face = ctx.candidate_pairs(0)
+    edge = ctx.candidate_pairs(1)
+    point = ctx.candidate_pairs(2)
+    act = np.unique(np.concatenate([face[:, 0], edge[:, 0], point[:, 0]]))
+    sv = np.unique(sc.stris[act])
+    mt = np.unique(face[:, 1])
+    me = np.unique(edge[:, 1])
+    mv = np.unique(np.concatenate([sc.mtris[mt].ravel(), point[:, 1]]))
+    n_pairs = face.shape[0] + edge.shape[0] + point.shape[0]
+    out_per_tri = 8 + (4 if precision == "mixed" else 8) * 12
+    samples = (48 * sv.size + 12 * act.size + 16 * act.size + 4 * n_pairs + 24 * mv.size
+               + 12 * mt.size + 8 * me.size + 48 * mt.size + out_per_tri * act.size)
+    ns = sc.stris.shape[0]
+    nsv = np.unique(sc.stris).size
+    query = 24 * nsv + 12 * ns + 16 * ns + 4 * n_pairs + 48 * sc.mtris.shape[0]
+    gsz = 4 if precision == "mixed" else 8
+    gather_grad = 3 * gsz * sc.X.shape[0] + (gsz * 6) * ns
+    return {"samples": samples, "query": query, "gather_grad": gather_grad,
+            "units": {"active_tris": int(act.size), "pairs": int(n_pairs)}}
+
+
+def run_ours(args):
+    import torch
+    from paper_2605_24339_b300 import binding
+    rank, world, dist = dist_setup(args.gpus)
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    sc, x_np, dx_np = make_workload(seed=11 + rank)
+    nk = 4 ** sc.params["face_rule_level"]
+    stream = torch.cuda.current_stream()
+    ctx = binding.Context(sc, precision=args.precision, device=dev, stream=stream)
+    x = torch.as_tensor(x_np, device="cuda")
+    dx = torch.as_tensor(dx_np, device="cuda")
+    xm = torch.as_tensor(sc.Y0, device="cuda")
+    grad = torch.empty((sc.X.shape[0], 3), device="cuda",
+                       dtype=torch.float32 if args.precision == "mixed" else torch.float64)
+    e_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    units, cand = samples_per_pass(ctx, x, xm, nk)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        ctx.barrier_eval(x, xm, grad=True, hess=True, counts=False, energy_dev=e_dev, grad_out=grad)
+        return ctx.ccd_max_step(x, dx, xm)
+
+    for _ in range(args.warmup):
+        info = step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    ctx.profile_start()
+    barrier(dist)
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0.record(stream)
+        info = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+    torch.cuda.synchronize()
+    barrier(dist)
+    ctx.profile_stop()
+    prof = ctx.profile_read()
+    clk = clocks.stop()
+    total_ms = max_over_ranks(total_ms, dist)
+    ms_step = total_ms / args.steps
+    value = units * args.steps * world / (total_ms / 1e3)
+
+    # end to end: host positions copied in from pinned memory, energy and
+    # alpha read back, every step
+    x_host = torch.as_tensor(x_np).pin_memory()
+    out_host = torch.zeros(2, dtype=torch.float64).pin_memory()
+    x_e2e = torch.empty_like(x)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x_e2e.copy_(x_host, non_blocking=True)
+        ctx.barrier_eval(x_e2e, xm, grad=True, hess=True, counts=False, energy_dev=e_dev, grad_out=grad)
+        info = ctx.ccd_max_step(x_e2e, dx, xm)
+        out_host[:1].copy_(e_dev, non_blocking=False)
+        out_host[1] = info["alpha"]
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e_value = units * args.steps * world / e2e_s
+
+    if rank != 0:
+        return
+    peaks, peak_kind = load_peaks()
+    ab = algorithmic_bytes(ctx, sc, x_np, cand, args.precision)
+    sec_ms = {k: v["ms"] / max(v["calls"], 1) for k, v in prof.items()}
+    # dominant single-kernel section among those with a byte model
+    cand_secs = [s for s in ("samples", "query", "gather_grad") if s in sec_ms]
+    top = max(cand_secs, key=lambda s: sec_ms[s])
+    achieved = ab[top] / (sec_ms[top] / 1e3) / 1e9
+    n_launch_per_step = {"grid": 5, "query": 1, "samples": 1, "gather_grad": 1, "gather_hess": 1,
+                         "reduce": 2, "alpha_lin": 1, "accd": 1}
+    launches = 0
+    for k, v in prof.items():
+        per = n_launch_per_step.get(k, 1)
+        launches += per * v["calls"]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": args.precision, "samples_per_pass": int(units),
+                   "face_samples": int(sc.stris.shape[0] * nk), "edge_candidates": cand["edge"],
+                   "point_candidates": cand["point"], "face_candidates": cand["face"],
+                   "l2": "flushed (256 MB write) between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_np.nbytes),
+                "d2h_bytes_per_step": 16},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peak_kind, "algorithmic_bytes": int(ab[top])},
+        "sections_ms": {k: round(v, 4) for k, v in sec_ms.items()},
+        "alpha": info["alpha"],
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(steps=2)
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(steps=2):
+    """The FP64 oracle, as it stands, on the bounded window of the workload."""
+    from oracle import oracle as O
+    from paper_2605_24339_b300 import scenes as S
+    sc, x, dx = make_workload()
+    top = sc.Y0[np.argmax(sc.Y0[:, 2])]
+    sub, xs = S.crop(sc, x, top[:2], CROP_HALF_WIDTH, 4 * sc.params["dhat"])
+    rng = np.random.default_rng(11)
+    dxs = np.zeros_like(xs)
+    dxs[:, 2] = -5e-6 * (0.5 + rng.random(xs.shape[0]))
+    dxs[:, :2] = 1e-6 * rng.normal(size=(xs.shape[0], 2))
+    Os = O.Scene(sub)
+    nk = 4 ** sc.params["face_rule_level"]
+    cand_e = Os.candidates(1, xs, sub.Y0).shape[0]
+    cand_p = Os.candidates(2, xs, sub.Y0).shape[0]
+    units = sub.stris.shape[0] * nk + 2 * cand_e + cand_p
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        Os.contact(xs, sub.Y0)
+        Os.ccd_max_step(xs, dxs, sub.Y0)
+    dt = time.perf_counter() - t0
+    return {"value": units * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} passes over a {2 * CROP_HALF_WIDTH * 1e3:.0f} mm window "
+                      f"({sub.stris.shape[0]} slave tris, {sub.mtris.shape[0]} master tris, "
+                      f"{units} samples/pass) around the highest terrain peak",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2605_24339_b300 import scenes as S
+    sc, x, dx = make_workload()
+    top = sc.Y0[np.argmax(sc.Y0[:, 2])]
+    sub, xs = S.crop(sc, x, top[:2], CROP_HALF_WIDTH, 4 * sc.params["dhat"])
+    rng = np.random.default_rng(11)
+    dxs = np.zeros_like(xs)
+    dxs[:, 2] = -5e-6 * (0.5 + rng.random(xs.shape[0]))
+    dxs[:, :2] = 1e-6 * rng.normal(size=(xs.shape[0], 2))
+    Os = O.Scene(sub)
+    nk = 4 ** sc.params["face_rule_level"]
+    units = (sub.stris.shape[0] * nk + 2 * Os.candidates(1, xs, sub.Y0).shape[0]
+             + Os.candidates(2, xs, sub.Y0).shape[0])
+    for _ in range(min(args.warmup, 1)):
+        Os.contact(xs, sub.Y0)
+        Os.ccd_max_step(xs, dxs, sub.Y0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        Os.contact(xs, sub.Y0)
+        Os.ccd_max_step(xs, dxs, sub.Y0)
+    dt = time.perf_counter() - t0
+    value = units * args.steps / dt
+    sample = (f"each step one pass over a {2 * CROP_HALF_WIDTH * 1e3:.0f} mm window of the workload "
+              f"({sub.stris.shape[0]} slave tris, {units} samples)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "window": sample}, "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

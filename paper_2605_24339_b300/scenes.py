@@ -521,3 +521,29 @@ def _surface_height(Y, F, P):
     np.maximum.at(out, pid[inside], z[inside])
     out[~np.isfinite(out)] = np.nan
     return out
+
+
+def crop(scene: Scene, x: np.ndarray, center, half_width: float, margin: float):
+    """Contact-only sub-scene of a single-env scene: the slave triangles whose
+    centroid (at x) lies in the xy square ``center +- half_width``, their
+    vertices, and the master triangles whose xy box meets the square grown by
+    ``margin``.  Tets are dropped (the sub-scene serves the contact pass
+    only).  Returns ``(sub_scene, x_sub)``."""
+    cx, cy = center
+    cen = x[scene.stris].mean(axis=1)
+    sel = (np.abs(cen[:, 0] - cx) <= half_width) & (np.abs(cen[:, 1] - cy) <= half_width)
+    S = scene.stris[sel]
+    verts, inv = np.unique(S, return_inverse=True)
+    S2 = inv.reshape(-1, 3).astype(np.int32)
+    tri = scene.Y0[scene.mtris]
+    lo, hi = tri[:, :, :2].min(axis=1), tri[:, :, :2].max(axis=1)
+    w = half_width + margin
+    msel = (hi[:, 0] >= cx - w) & (lo[:, 0] <= cx + w) & (hi[:, 1] >= cy - w) & (lo[:, 1] <= cy + w)
+    M = scene.mtris[msel]
+    mverts, minv = np.unique(M, return_inverse=True)
+    M2 = minv.reshape(-1, 3).astype(np.int32)
+    X2 = scene.X[verts]
+    sub = _single_env(X2, np.zeros((0, 4), dtype=np.int32), S2,
+                      scene.dirichlet[verts], scene.Y0[mverts], M2, scene.v_dirichlet[verts],
+                      dict(scene.params), scene.name + "_crop", scene.n_steps)
+    return sub, x[verts].copy()
