@@ -186,7 +186,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
-        ctx.barrier_eval(x, xm, grad=True, hess=True, counts=False, energy_dev=e_dev, grad_out=grad)
+        ctx.barrier_eval(x, xm, grad=True, hess="view", counts=False, energy_dev=e_dev, grad_out=grad)
         return ctx.ccd_max_step(x, dx, xm)
 
     for _ in range(args.warmup):
@@ -224,7 +224,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         x_e2e.copy_(x_host, non_blocking=True)
-        ctx.barrier_eval(x_e2e, xm, grad=True, hess=True, counts=False, energy_dev=e_dev, grad_out=grad)
+        ctx.barrier_eval(x_e2e, xm, grad=True, hess="view", counts=False, energy_dev=e_dev, grad_out=grad)
         info = ctx.ccd_max_step(x_e2e, dx, xm)
         out_host[:1].copy_(e_dev, non_blocking=False)
         out_host[1] = info["alpha"]

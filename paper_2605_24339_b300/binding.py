@@ -166,7 +166,7 @@ class _CudaArray:
 
     def __init__(self, ptr, shape, typestr):
         self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr,
-                                         "data": (int(ptr), True), "version": 3, "strides": None}
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
 
 
 def _ptr(t):
@@ -261,7 +261,9 @@ class Context:
         if counts:
             out["counts"] = dict(face=sc.face, edge=sc.edge, point=sc.point, guard=sc.guard,
                                  face_evaluated=sc.face_evaluated)
-        if hess:
+        if hess == "view":
+            out["hess"] = bv
+        elif hess:
             out["hess"] = self.bsr(bv)
         return out
 

@@ -16,8 +16,11 @@ LIB = os.path.join(PKG, "libgmcp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 # translation units whose FP64 predicates must round like a plain IEEE
-# evaluation (no fused multiply-add)
-NO_FMA = {"broadphase.cu"}
+# evaluation (no fused multiply-add): candidate boxes, CCD, and the sample
+# geometry whose membership tests (point inside a slave triangle, edge
+# clipping) are not weight-continuous and so must decide exactly as the
+# CPU oracle does on degenerate (coincident) meshes
+NO_FMA = {"broadphase.cu", "contact.cu"}
 SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu"]
 
 

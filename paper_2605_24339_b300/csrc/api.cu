@@ -328,6 +328,33 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
     CK(cudaStreamSynchronize(s));
 }
 
+// Face rule of level L = 1, 2 (4^L samples): centroids of the uniform
+// midpoint subdivision, upright cells (3i+1, 3j+1, 3k+1)/(3n) with
+// i+j+k = n-1 first, then inverted cells (3i+2, 3j+2, 3k+2)/(3n) with
+// i+j+k = n-2; n = 2^L.  Unused slots are zero.
+static void face_rule_table(double* tab /*[2][16][3]*/) {
+    for (int L = 1; L <= 2; ++L) {
+        double* r = tab + 48 * (L - 1);
+        for (int q = 0; q < 48; ++q) r[q] = 0.0;
+        const int n = 1 << L;
+        int c = 0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; i + j < n; ++j, ++c) {
+                const int k = n - 1 - i - j;
+                r[3 * c] = (double)(3 * i + 1) / (double)(3 * n);
+                r[3 * c + 1] = (double)(3 * j + 1) / (double)(3 * n);
+                r[3 * c + 2] = (double)(3 * k + 1) / (double)(3 * n);
+            }
+        for (int i = 0; i < n - 1; ++i)
+            for (int j = 0; i + j < n - 1; ++j, ++c) {
+                const int k = n - 2 - i - j;
+                r[3 * c] = (double)(3 * i + 2) / (double)(3 * n);
+                r[3 * c + 1] = (double)(3 * j + 2) / (double)(3 * n);
+                r[3 * c + 2] = (double)(3 * k + 2) / (double)(3 * n);
+            }
+    }
+}
+
 static void alloc_call_buffers(Ctx& c) {
     const int64_t ns = c.ns;
     cudaStream_t s = c.stream;
@@ -423,6 +450,12 @@ ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx*
             if (scene->s_tris[i] < 0 || scene->s_tris[i] >= c.nv) throw Fail{IPC_ERR_ARG, "s_tris index out of range"};
         for (int64_t i = 0; i < 3 * c.nmt; ++i)
             if (scene->m_tris[i] < 0 || scene->m_tris[i] >= c.nmv) throw Fail{IPC_ERR_ARG, "m_tris index out of range"};
+        {
+            double tab[96];
+            face_rule_table(tab);
+            CK(bp_init_constants(tab));
+            CK(contact_init_constants(tab));
+        }
         build_topology(c, scene);
         alloc_call_buffers(c);
         CK(cudaStreamSynchronize(c.stream));

@@ -58,33 +58,9 @@ __device__ __forceinline__ void load3(const double* p, int64_t i, double* o) {
     o[0] = p[3 * i]; o[1] = p[3 * i + 1]; o[2] = p[3 * i + 2];
 }
 
-// face-rule sample k of level L (upright cells first, then inverted cells)
-__device__ void rule_beta(int L, int k, double* b) {
-    const int n = 1 << L;
-    int c = 0;
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; i + j < n; ++j) {
-            if (c == k) {
-                int kk = n - 1 - i - j;
-                b[0] = (double)(3 * i + 1) / (double)(3 * n);
-                b[1] = (double)(3 * j + 1) / (double)(3 * n);
-                b[2] = (double)(3 * kk + 1) / (double)(3 * n);
-                return;
-            }
-            ++c;
-        }
-    for (int i = 0; i < n - 1; ++i)
-        for (int j = 0; i + j < n - 1; ++j) {
-            if (c == k) {
-                int kk = n - 2 - i - j;
-                b[0] = (double)(3 * i + 2) / (double)(3 * n);
-                b[1] = (double)(3 * j + 2) / (double)(3 * n);
-                b[2] = (double)(3 * kk + 2) / (double)(3 * n);
-                return;
-            }
-            ++c;
-        }
-}
+// face-rule barycentrics per level (index L-1), filled at context creation
+// with the exact quotients (3i+1)/(3n), (3i+2)/(3n) of the fixed rule
+__constant__ double c_rule[2][16][3];
 
 // ---------------------------------------------------------------------------
 // grid build
@@ -161,21 +137,12 @@ k_query_contact(SceneView S, Params P, CandView C, const double* __restrict__ x,
         slo[c] = dmin_(x0[c], dmin_(x1[c], x2[c]));
         shi[c] = dmax_(x0[c], dmax_(x1[c], x2[c]));
     }
-    double sx[NK], sy[NK], sz[NK];
-    double qlo[3] = {slo[0], slo[1], slo[2]}, qhi[3] = {shi[0], shi[1], shi[2]};
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-        double b[3];
-        rule_beta(P.L, k, b);
-        sx[k] = b[0] * x0[0] + b[1] * x1[0] + b[2] * x2[0];
-        sy[k] = b[0] * x0[1] + b[1] * x1[1] + b[2] * x2[1];
-        sz[k] = b[0] * x0[2] + b[1] * x1[2] + b[2] * x2[2];
-        qlo[0] = dmin_(qlo[0], sx[k]); qhi[0] = dmax_(qhi[0], sx[k]);
-        qlo[1] = dmin_(qlo[1], sy[k]); qhi[1] = dmax_(qhi[1], sy[k]);
-        qlo[2] = dmin_(qlo[2], sz[k]); qhi[2] = dmax_(qhi[2], sz[k]);
-    }
+    // the face samples are convex combinations of the vertices, so the vertex
+    // box grown by dhat (plus the rounding margin) bounds every candidate
     const double grow = eps + S.margin;
-    for (int c = 0; c < 3; ++c) { qlo[c] = qlo[c] - grow; qhi[c] = qhi[c] + grow; }
+    double qlo[3], qhi[3];
+    for (int c = 0; c < 3; ++c) { qlo[c] = slo[c] - grow; qhi[c] = shi[c] + grow; }
+    const double (*rule)[3] = c_rule[P.L - 1];
     const int e = S.stri_env[t];
     const I3 ca = cell_of(S, e, qlo[0], qlo[1], qlo[2]);
     const I3 cb = cell_of(S, e, qhi[0], qhi[1], qhi[2]);
@@ -199,14 +166,20 @@ k_query_contact(SceneView S, Params P, CandView C, const double* __restrict__ x,
                     if (qlo[0] > mhi0 || mlo0 > qhi[0] || qlo[1] > mhi1 || mlo1 > qhi[1] ||
                         qlo[2] > mhi2 || mlo2 > qhi[2])
                         continue;
-                    // face: some sample inside the master box grown by eps
+                    // face: some sample ((b0 x0 + b1 x1) + b2 x2) inside the
+                    // master box grown by eps
                     const double l0 = mlo0 - eps, l1 = mlo1 - eps, l2 = mlo2 - eps;
                     const double h0 = mhi0 + eps, h1 = mhi1 + eps, h2 = mhi2 + eps;
                     bool hit = false;
-#pragma unroll
-                    for (int q = 0; q < NK; ++q)
-                        hit |= l0 <= sx[q] && sx[q] <= h0 && l1 <= sy[q] && sy[q] <= h1 &&
-                               l2 <= sz[q] && sz[q] <= h2;
+                    for (int q = 0; q < NK && !hit; ++q) {
+                        const double b0 = rule[q][0], b1 = rule[q][1], b2 = rule[q][2];
+                        const double sxq = b0 * x0[0] + b1 * x1[0] + b2 * x2[0];
+                        if (!(l0 <= sxq && sxq <= h0)) continue;
+                        const double syq = b0 * x0[1] + b1 * x1[1] + b2 * x2[1];
+                        if (!(l1 <= syq && syq <= h1)) continue;
+                        const double szq = b0 * x0[2] + b1 * x1[2] + b2 * x2[2];
+                        hit = l2 <= szq && szq <= h2;
+                    }
                     if (hit) { if (nf < C.cap_f) Lf[nf] = m; ++nf; }
                     // owned edges
                     for (int j = 0; j < 3; ++j) {
@@ -328,7 +301,7 @@ __device__ double ee_dist2(const double* a0, const double* a1, const double* b0,
 
 // x[12], p[12] (modified); type 0 point-triangle, 1 edge-edge.  Returns the
 // largest safe fraction found in [0, tc] (tc when nothing closes in time).
-__device__ double accd(int type, double* x, double* p, double s, double tc, int max_iter,
+__device__ __noinline__ double accd(int type, double* x, double* p, double s, double tc, int max_iter,
                        int* iters) {
     double pbar[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < 4; ++i)
@@ -341,12 +314,36 @@ __device__ double accd(int type, double* x, double* p, double s, double tc, int 
     double lp = type == 0 ? n[0] + dmax_(n[1], dmax_(n[2], n[3])) : dmax_(n[0], n[1]) + dmax_(n[2], n[3]);
     *iters = 0;
     if (lp == 0.0) return tc;
+    // The first advance is tl = (1-s) d / lp and the iteration returns tc as
+    // soon as t = tl exceeds tc, whatever the distance after the advance.  A
+    // lower bound of d (the distance between the two primitives' boxes), with
+    // a relative margin far above rounding, settles that case without the
+    // exact distance; either way the result equals the full iteration's.
+    {
+        double lo0[3], hi0[3], lo1[3], hi1[3];
+        const int na = type == 0 ? 1 : 2;
+        for (int c = 0; c < 3; ++c) {
+            lo0[c] = hi0[c] = x[c];
+            lo1[c] = hi1[c] = x[3 * na + c];
+        }
+        for (int i = 1; i < na; ++i)
+            for (int c = 0; c < 3; ++c) { lo0[c] = dmin_(lo0[c], x[3 * i + c]); hi0[c] = dmax_(hi0[c], x[3 * i + c]); }
+        for (int i = na + 1; i < 4; ++i)
+            for (int c = 0; c < 3; ++c) { lo1[c] = dmin_(lo1[c], x[3 * i + c]); hi1[c] = dmax_(hi1[c], x[3 * i + c]); }
+        double g2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double gap = dmax_(0.0, dmax_(lo0[c] - hi1[c], lo1[c] - hi0[c]));
+            g2 += gap * gap;
+        }
+        if ((1.0 - s) * sqrt(g2) * (1.0 - 1e-9) > tc * lp) { *iters = 1; return tc; }
+    }
     double d2 = type == 0 ? pt_dist2(x, x + 3, x + 6, x + 9) : ee_dist2(x, x + 3, x + 6, x + 9);
     double d = sqrt(d2);
     if (d == 0.0) return 0.0;
     double gstop = s * d;
     double t = 0.0;
     double tl = (1.0 - s) * d / lp;
+    if (tl > tc) { *iters = 1; return tc; }
     for (int it = 0; it < max_iter; ++it) {
         *iters = it + 1;
         for (int i = 0; i < 12; ++i) x[i] = x[i] + tl * p[i];
@@ -496,6 +493,10 @@ k_query_ccd(SceneView S, Params P, const double* __restrict__ x, const double* _
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+cudaError_t bp_init_constants(const double* rule_l1l2) {
+    return cudaMemcpyToSymbol(c_rule, rule_l1l2, sizeof(double) * 2 * 16 * 3);
+}
+
 cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept) {
     ProfScope ps(c.prof, c.stream, "grid");
     SceneView S = c.view();

@@ -15,6 +15,12 @@
 // the Hessian sum_tris S_ab n_s n_s^T (Sec. 4.2 with dg/dx_a = -beta_a n_s),
 // gathered in a fixed order by k_gather_* (no float atomics).
 //
+// Rounding.  This file is compiled without fused multiply-add and its FP64
+// geometry follows the operation order of a plain evaluation of the same
+// formulas, so the sample membership decisions (which are not continuous in
+// the weight for point samples and for edges lying on slave edges) come out
+// identical to a plain IEEE evaluation even on coincident meshes.
+//
 // Precision.  FP64 path: everything in double.  Mixed path: face samples are
 // cast in FP32 in a local frame anchored at the slave triangle's first
 // vertex (coordinate differences formed in FP64, then rounded); a sample
@@ -92,32 +98,8 @@ __device__ __forceinline__ void barrier(float g, float eps, float& B, float& dB,
     d2B = -2.0f * L - 4.0f * d / g + d * d / (g * g);
 }
 
-__device__ void rule_beta(int L, int k, double* b) {
-    const int n = 1 << L;
-    int c = 0;
-    for (int i = 0; i < n; ++i)
-        for (int j = 0; i + j < n; ++j) {
-            if (c == k) {
-                int kk = n - 1 - i - j;
-                b[0] = (double)(3 * i + 1) / (double)(3 * n);
-                b[1] = (double)(3 * j + 1) / (double)(3 * n);
-                b[2] = (double)(3 * kk + 1) / (double)(3 * n);
-                return;
-            }
-            ++c;
-        }
-    for (int i = 0; i < n - 1; ++i)
-        for (int j = 0; i + j < n - 1; ++j) {
-            if (c == k) {
-                int kk = n - 2 - i - j;
-                b[0] = (double)(3 * i + 2) / (double)(3 * n);
-                b[1] = (double)(3 * j + 2) / (double)(3 * n);
-                b[2] = (double)(3 * kk + 2) / (double)(3 * n);
-                return;
-            }
-            ++c;
-        }
-}
+// face-rule barycentrics per level (index L-1), filled at context creation
+__constant__ double c_rule[2][16][3];
 
 // Face ray cast of Sec. 4.1 (fixed slave-side rule): from xs along ns onto
 // the plane of (y0,y1,y2).  Returns true when the master tri faces the slave,
@@ -214,7 +196,7 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
     const double omega = 1.0 / (double)NK;
     long long cnt_f = 0, cnt_e = 0, cnt_p = 0, cnt_eval = 0;
     double beta_k[3];
-    rule_beta(P.L, lane % NK, beta_k);
+    for (int q = 0; q < 3; ++q) beta_k[q] = c_rule[P.L - 1][lane % NK][q];
     for (int i = warp; i < n_active; i += nwarps) {
         const int64_t t = C.active[i];
         const int32_t* Tt = S.stri + 3 * t;
@@ -507,6 +489,10 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
 }
 
 }  // namespace
+
+cudaError_t contact_init_constants(const double* rule_l1l2) {
+    return cudaMemcpyToSymbol(c_rule, rule_l1l2, sizeof(double) * 2 * 16 * 3);
+}
 
 int sm_count(int device) {
     static int cached[64] = {0};

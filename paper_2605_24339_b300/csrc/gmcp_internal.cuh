@@ -247,6 +247,7 @@ struct Ctx {
 // launchers implemented in the .cu files
 // ------------------------------------------------------------------------
 // broadphase.cu
+cudaError_t bp_init_constants(const double* rule_l1l2);
 cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept);
 cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm);
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
@@ -258,6 +259,7 @@ size_t scan_tmp_size(int64_t n);
 // api.cu
 cudaError_t run_candidates(Ctx& c, const double* x, const double* xm);
 // contact.cu
+cudaError_t contact_init_constants(const double* rule_l1l2);
 cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* energy_dev,
                          void* grad_dev, bool want_hess, long long* counters);
 cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const double* dx,
