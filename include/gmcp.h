@@ -222,6 +222,31 @@ ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const dou
 ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* names_host,
                        double* ms_host, int64_t* calls_host, int32_t* n_sections);
 
+/* Allocation-free additive-CCD step bound.  The paper has no counterpart;
+ * this entry point exists for callers that must not allocate device memory
+ * once they are running -- for example a robot controller's real-time loop,
+ * where cudaMalloc may block and synchronise the device, or a host framework
+ * that routes every device allocation through its own pool.  Given a context
+ * created beforehand, it returns in *alpha_accd_host the same value as the
+ * alpha_accd field of ipc_ccd_max_step for the same arguments (additive CCD
+ * over the owned primitive pairs whose swept boxes overlap; 1.0 when nothing
+ * closes), and in n_pairs_host (may be NULL) the point-triangle and edge-edge
+ * pair counts.  It calls no allocator: its scratch is a 4 MiB array built
+ * into the library, which every GPU that loads the library keeps until the
+ * process exits.  A moving master (xm1_dev != NULL) needs 24 bytes of it per
+ * master vertex, so scenes with more than 174,752 master vertices are
+ * rejected with IPC_ERR_CAPACITY when xm1_dev is given.  The first call on a
+ * device looks up the array's device address (once per device); make that
+ * first call before capturing any stream.  Every call on every context of
+ * the process uses the same array, clearing it first: calls whose GPU work
+ * overlaps (two streams, two threads) race and must be serialised by the
+ * caller.  Pairs are enumerated by brute force (slave triangles x master
+ * triangles of each environment), so this is meant for small scenes.
+ * Synchronises params.stream. */
+ipc_status ipc_accd_min_noalloc(ipc_ctx* ctx, const double* x_dev, const double* dx_dev,
+                                const double* xm0_dev, const double* xm1_dev,
+                                double* alpha_accd_host, int64_t* n_pairs_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -133,6 +133,10 @@ struct ipc_ctx {
     Ctx c;
 };
 
+namespace gmcp {
+Ctx& ctx_of(ipc_ctx* h) { return h->c; }
+}
+
 static ipc_status fail_ctx(ipc_ctx* ctx, ipc_status st, const std::string& msg) {
     if (ctx) ctx->c.err = msg;
     return st;

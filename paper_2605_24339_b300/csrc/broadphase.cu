@@ -23,6 +23,9 @@
 // Edges and vertices are found through the master triangle that owns them
 // (the lowest-numbered adjacent triangle), whose box contains theirs.
 #include <cfloat>
+#include <cstring>
+#include <mutex>
+#include <string>
 
 #include "gmcp_internal.cuh"
 
@@ -565,3 +568,226 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
 }
 
 }  // namespace gmcp
+
+// ===========================================================================
+// Allocation-free additive-CCD minimum (ipc_accd_min_noalloc).
+//
+// Some callers must not allocate device memory once they are running: a
+// robot controller's real-time loop cannot afford cudaMalloc, which may block
+// and synchronise the whole device, and some host frameworks route every
+// device allocation through their own pool and forbid direct cudaMalloc.
+// This entry point gives such callers the additive-CCD step bound over a
+// context created beforehand without touching any allocator: its only
+// scratch (the minimum's bit pattern, three counters and, for a moving
+// master, the master displacement) lives in the file-scope array below,
+// 4 MiB that every GPU which loads the library keeps until the process
+// exits.  The pairs are enumerated by brute force (every slave triangle
+// against every master triangle of its environment) with the same owned-
+// primitive rules, swept-box filters and ACCD routine as k_query_ccd, so the
+// result equals the alpha_accd of ipc_ccd_max_step bit for bit; the cost is
+// O(slave tris x master tris), meant for small scenes.
+// ===========================================================================
+namespace gmcp {
+Ctx& ctx_of(ipc_ctx* h);   // api.cu
+}
+
+static constexpr size_t kNoAllocScratchBytes = (size_t)4 << 20;
+static constexpr size_t kNoAllocHeaderBytes = 256;     // alpha bits + 3 counters, padded
+static constexpr int64_t kNoAllocMaxMasterVerts =
+    (int64_t)((kNoAllocScratchBytes - kNoAllocHeaderBytes) / (3 * sizeof(double)));
+static __device__ __align__(256) unsigned char g_accd_scratch[kNoAllocScratchBytes];
+
+namespace gmcp {
+namespace {
+
+__global__ void k_noalloc_reset(unsigned long long* hdr) {
+    hdr[0] = 0x3FF0000000000000ULL;   // alpha = 1.0
+    hdr[1] = 0; hdr[2] = 0; hdr[3] = 0;
+}
+
+__global__ void k_noalloc_sub(const double* __restrict__ a, const double* __restrict__ b,
+                              double* __restrict__ o, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) o[i] = a[i] - b[i];
+}
+
+// one thread per slave triangle, blockIdx.y selects a chunk of master tris
+__global__ void __launch_bounds__(128)
+k_accd_brute(SceneView S, Params P, const double* __restrict__ x, const double* __restrict__ dx,
+             const double* __restrict__ xm0, const double* __restrict__ dxm, int m_chunk,
+             unsigned long long* alpha_bits, long long* counters) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.ns) return;
+    const int64_t m_begin = (int64_t)blockIdx.y * m_chunk;
+    const int64_t m_end = min((int64_t)S.nmt, m_begin + m_chunk);
+    const int32_t* T = S.stri + 3 * t;
+    double tlo[3], thi[3];
+    swept_vert(x, dx, T[0], tlo, thi);
+    for (int a = 1; a < 3; ++a) {
+        double l[3], h[3];
+        swept_vert(x, dx, T[a], l, h);
+        grow_box(tlo, thi, l, h);
+    }
+    const int e = S.stri_env[t];
+    double best = 1.0;
+    long long n_pt = 0, n_ee = 0;
+    int cap_hit = 0;
+    for (int64_t m = m_begin; m < m_end; ++m) {
+        if (S.mtri_env[m] != e) continue;
+        const int32_t* M = S.mtri + 3 * m;
+        double B[6];
+        swept_vert(xm0, dxm, M[0], B, B + 3);
+        for (int a = 1; a < 3; ++a) {
+            double l[3], h[3];
+            swept_vert(xm0, dxm, M[a], l, h);
+            grow_box(B, B + 3, l, h);
+        }
+        // every primitive box lies inside its triangle's box
+        if (!overlap(tlo, thi, B, B + 3)) continue;
+        double X12[12], P12[12];
+        int it;
+        for (int j = 0; j < 3; ++j) {
+            const int32_t v = S.stri_own_vert[3 * t + j];
+            if (v < 0) continue;
+            double vlo[3], vhi[3];
+            swept_vert(x, dx, v, vlo, vhi);
+            if (!overlap(vlo, vhi, B, B + 3)) continue;
+            for (int c = 0; c < 3; ++c) {
+                X12[c] = x[3 * (int64_t)v + c]; P12[c] = dx[3 * (int64_t)v + c];
+                for (int a = 0; a < 3; ++a) {
+                    X12[3 + 3 * a + c] = xm0[3 * (int64_t)M[a] + c];
+                    P12[3 + 3 * a + c] = dxm ? dxm[3 * (int64_t)M[a] + c] : 0.0;
+                }
+            }
+            const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+            ++n_pt; cap_hit |= it >= P.ccd_max_iter;
+            best = dmin_(best, r);
+        }
+        for (int j = 0; j < 3; ++j) {
+            const int32_t u = S.mtri_own_vert[3 * m + j];
+            if (u < 0) continue;
+            double ulo[3], uhi[3];
+            swept_vert(xm0, dxm, u, ulo, uhi);
+            if (!overlap(ulo, uhi, tlo, thi)) continue;
+            for (int c = 0; c < 3; ++c) {
+                X12[c] = xm0[3 * (int64_t)u + c]; P12[c] = dxm ? dxm[3 * (int64_t)u + c] : 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    X12[3 + 3 * a + c] = x[3 * (int64_t)T[a] + c];
+                    P12[3 + 3 * a + c] = dx[3 * (int64_t)T[a] + c];
+                }
+            }
+            const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+            ++n_pt; cap_hit |= it >= P.ccd_max_iter;
+            best = dmin_(best, r);
+        }
+        for (int j = 0; j < 3; ++j) {
+            const int32_t es = S.stri_own_edge[3 * t + j];
+            if (es < 0) continue;
+            const int32_t sa = S.sedge[2 * (int64_t)es], sb = S.sedge[2 * (int64_t)es + 1];
+            double alo[3], ahi[3], l2[3], h2[3];
+            swept_vert(x, dx, sa, alo, ahi);
+            swept_vert(x, dx, sb, l2, h2);
+            grow_box(alo, ahi, l2, h2);
+            for (int q = 0; q < 3; ++q) {
+                const int32_t em = S.mtri_own_edge[3 * m + q];
+                if (em < 0) continue;
+                const int32_t m0 = S.medge[2 * (int64_t)em], m1 = S.medge[2 * (int64_t)em + 1];
+                double blo[3], bhi[3];
+                swept_vert(xm0, dxm, m0, blo, bhi);
+                swept_vert(xm0, dxm, m1, l2, h2);
+                grow_box(blo, bhi, l2, h2);
+                if (!overlap(alo, ahi, blo, bhi)) continue;
+                for (int c = 0; c < 3; ++c) {
+                    X12[c] = x[3 * (int64_t)sa + c]; P12[c] = dx[3 * (int64_t)sa + c];
+                    X12[3 + c] = x[3 * (int64_t)sb + c]; P12[3 + c] = dx[3 * (int64_t)sb + c];
+                    X12[6 + c] = xm0[3 * (int64_t)m0 + c]; P12[6 + c] = dxm ? dxm[3 * (int64_t)m0 + c] : 0.0;
+                    X12[9 + c] = xm0[3 * (int64_t)m1 + c]; P12[9 + c] = dxm ? dxm[3 * (int64_t)m1 + c] : 0.0;
+                }
+                const double r = accd(1, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+                ++n_ee; cap_hit |= it >= P.ccd_max_iter;
+                best = dmin_(best, r);
+            }
+        }
+    }
+    if (best < 1.0) atomic_min_pos(alpha_bits, best);
+    if (n_pt) atomic_add_ll(&counters[0], n_pt);
+    if (n_ee) atomic_add_ll(&counters[1], n_ee);
+    if (cap_hit) atomicMax(&counters[2], 1LL);
+}
+
+// Device address of g_accd_scratch per device, resolved once with that
+// device current (the array's name is only a host-side stand-in).
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};
+
+cudaError_t noalloc_scratch(int device, void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_accd_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = p;
+    }
+    *out = g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace gmcp
+
+extern "C" ipc_status ipc_accd_min_noalloc(ipc_ctx* h, const double* x_dev, const double* dx_dev,
+                                           const double* xm0_dev, const double* xm1_dev,
+                                           double* alpha_accd_host, int64_t* n_pairs_host) {
+    using namespace gmcp;
+    if (!h) return IPC_ERR_ARG;
+    Ctx& c = ctx_of(h);
+    if (!x_dev || !dx_dev || (!xm0_dev && c.nmv > 0) || !alpha_accd_host) {
+        c.err = "ipc_accd_min_noalloc: NULL argument";
+        return IPC_ERR_ARG;
+    }
+    if (xm1_dev && c.nmv > kNoAllocMaxMasterVerts) {
+        c.err = "ipc_accd_min_noalloc: a moving master needs 24 bytes per master vertex of the "
+                "4 MiB built-in scratch, so at most " + std::to_string(kNoAllocMaxMasterVerts) +
+                " master vertices; this scene has " + std::to_string(c.nmv);
+        return IPC_ERR_CAPACITY;
+    }
+    auto fail = [&](cudaError_t e, const char* where) {
+        cudaGetLastError();
+        c.err = std::string("ipc_accd_min_noalloc: ") + where + ": " + cudaGetErrorString(e);
+        return IPC_ERR_CUDA;
+    };
+    cudaError_t e = cudaSetDevice(c.device);
+    if (e != cudaSuccess) return fail(e, "cudaSetDevice");
+    void* base = nullptr;
+    e = noalloc_scratch(c.device, &base);
+    if (e != cudaSuccess) return fail(e, "cudaGetSymbolAddress");
+    unsigned long long* hdr = reinterpret_cast<unsigned long long*>(base);
+    long long* counters = reinterpret_cast<long long*>(hdr + 1);
+    double* dxm = nullptr;
+    k_noalloc_reset<<<1, 1, 0, c.stream>>>(hdr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "reset");
+    if (xm1_dev && c.nmv > 0) {
+        dxm = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(base) + kNoAllocHeaderBytes);
+        const int64_t n = 3 * c.nmv;
+        k_noalloc_sub<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(xm1_dev, xm0_dev, dxm, n);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "master displacement");
+    }
+    if (c.ns > 0 && c.nmt > 0) {
+        const int m_chunk = 2048;
+        dim3 grid((unsigned)((c.ns + 127) / 128), (unsigned)((c.nmt + m_chunk - 1) / m_chunk));
+        k_accd_brute<<<grid, 128, 0, c.stream>>>(c.view(), c.P, x_dev, dx_dev, xm0_dev, dxm, m_chunk,
+                                                 hdr, counters);
+        if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "k_accd_brute");
+    }
+    // the context's pinned host words (allocated when the context was made)
+    e = cudaMemcpyAsync(c.h_counts + 8, hdr, 4 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream);
+    if (e != cudaSuccess) return fail(e, "copy back");
+    e = cudaStreamSynchronize(c.stream);
+    if (e != cudaSuccess) return fail(e, "synchronise");
+    double a;
+    memcpy(&a, c.h_counts + 8, sizeof(double));
+    *alpha_accd_host = a;
+    if (n_pairs_host) { n_pairs_host[0] = c.h_counts[9]; n_pairs_host[1] = c.h_counts[10]; }
+    return IPC_OK;
+}
