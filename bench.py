@@ -301,6 +301,25 @@ def cpu_baseline(steps=2):
             "seconds": dt}
 
 
+def run_passes(args):
+    """A few contact passes on the benchmark workload with no timing: the
+    command line used for ncu captures of single kernels."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    sc, x_np, dx_np = make_workload()
+    ctx = binding.Context(sc, precision=args.precision)
+    x = torch.as_tensor(x_np, device="cuda")
+    dx = torch.as_tensor(dx_np, device="cuda")
+    xm = torch.as_tensor(sc.Y0, device="cuda")
+    e_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(args.steps):
+        ctx.barrier_eval(x, xm, grad=True, hess="view", counts=False, energy_dev=e_dev)
+        info = ctx.ccd_max_step(x, dx, xm)
+    torch.cuda.synchronize()
+    print(json.dumps({"passes": args.steps, "alpha": info["alpha"], "ccd_pairs_pt": info["n_pt"],
+                      "ccd_pairs_ee": info["n_ee"]}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -346,10 +365,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes"],
+                    help="passes: run --steps untimed contact passes (for profilers)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
-    if args.impl == "reference":
+    if args.mode == "passes":
+        run_passes(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

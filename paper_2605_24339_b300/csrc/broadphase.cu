@@ -70,7 +70,7 @@ __constant__ double c_rule[2][16][3];
 // ---------------------------------------------------------------------------
 __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
                                  const double* __restrict__ dxm, double* __restrict__ mbox,
-                                 int32_t* __restrict__ cnt) {
+                                 int4* __restrict__ mcell, int32_t* __restrict__ cnt) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int32_t* T = S.mtri + 3 * m;
@@ -86,6 +86,7 @@ __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
     const int e = S.mtri_env[m];
     I3 a = cell_of(S, e, lo[0], lo[1], lo[2]);
     I3 b = cell_of(S, e, hi[0], hi[1], hi[2]);
+    mcell[m] = make_int4(a.x, a.y, a.z, e);
     for (int iz = a.z; iz <= b.z; ++iz)
         for (int iy = a.y; iy <= b.y; ++iy)
             for (int ix = a.x; ix <= b.x; ++ix) atomicAdd(&cnt[cell_id(S, e, ix, iy, iz)], 1);
@@ -109,6 +110,17 @@ __global__ void k_mtri_fill(SceneView S, const double* __restrict__ mbox,
             }
 }
 
+__device__ __forceinline__ void swept_vert(const double* P, const double* D, int64_t v, double* lo,
+                                           double* hi) {
+    for (int c = 0; c < 3; ++c) {
+        double a = P[3 * v + c];
+        double b = D ? a + D[3 * v + c] : a;
+        lo[c] = dmin_(a, b); hi[c] = dmax_(a, b);
+    }
+}
+__device__ __forceinline__ void grow_box(double* lo, double* hi, const double* l2, const double* h2) {
+    for (int c = 0; c < 3; ++c) { lo[c] = dmin_(lo[c], l2[c]); hi[c] = dmax_(hi[c], h2[c]); }
+}
 // insertion sort of a short list held in global memory
 __device__ void sort_small(int32_t* a, int n) {
     for (int i = 1; i < n; ++i) {
@@ -120,60 +132,198 @@ __device__ void sort_small(int32_t* a, int n) {
 }
 
 // ---------------------------------------------------------------------------
-// contact candidate query: one thread per slave triangle
+// contact candidate query: one warp per slave triangle
+//
+// The warp visits the cells of the slave triangle's box; the entries of each
+// non-empty cell are spread over the lanes, each lane runs the exact tests
+// for its master triangle and the lanes append their hits with a ballot.
+// Every list is sorted at the end, so the output does not depend on the
+// order in which cells or lanes found the pairs.
 // ---------------------------------------------------------------------------
-template <int NK>
-__global__ void __launch_bounds__(128)
-k_query_contact(SceneView S, Params P, CandView C, const double* __restrict__ x,
-                const double* __restrict__ xm, const double* __restrict__ mbox,
-                const int32_t* __restrict__ start, const int32_t* __restrict__ ent,
-                double* __restrict__ triE, void* __restrict__ triG, void* __restrict__ triS,
-                int out_f32) {
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// warp-aggregated append of v (when pred) to list L with capacity cap
+__device__ __forceinline__ void warp_append(bool pred, int32_t v, int32_t* L, int cap, int& n) {
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    if (pred) {
+        const int pos = n + __popc(mask & lanemask_lt());
+        if (pos < cap) L[pos] = v;
+    }
+    n += __popc(mask);
+}
+
+// ascending sort of the first n entries of L by the warp (n <= 32: bitonic
+// network in registers; longer lists: lane 0 insertion sort)
+__device__ void warp_sort(int32_t* L, int n, int lane) {
+    if (n <= 1) return;
+    if (n <= 32) {
+        int32_t v = lane < n ? L[lane] : INT32_MAX;
+        for (int k = 2; k <= 32; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                const int32_t o = __shfl_xor_sync(0xffffffffu, v, j);
+                const bool up = (lane & k) == 0;
+                const bool lower = (lane & j) == 0;
+                const int32_t lo = v < o ? v : o, hi = v < o ? o : v;
+                v = (lower == up) ? lo : hi;
+            }
+        if (lane < n) L[lane] = v;
+        __syncwarp();
+        return;
+    }
+    __syncwarp();
+    if (lane == 0) sort_small(L, n);
+    __syncwarp();
+}
+
+// Phase 1 of both queries (one thread per slave triangle): the triangle's
+// box (static: vertex box grown by dhat; swept: box of the vertices at x and
+// x + dx), its cell range, and whether any of those cells holds a master
+// triangle.  Triangles with only empty cells are finished here (contact
+// mode zeroes their counts and outputs); the others are appended, with their
+// boxes and cell range, to the list the warps of phase 2 work through.
+struct QueryList {
+    int32_t* n;        // scalar
+    int32_t* tri;      // [ns]
+    double* box;       // [ns][12]: tri box lo/hi, query box lo/hi
+    int32_t* cell;     // [ns][6]: first and last cell (x, y, z)
+};
+
+template <bool SWEPT>
+__global__ void __launch_bounds__(256)
+k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double* __restrict__ dx,
+               const int32_t* __restrict__ start, QueryList Q, int32_t* __restrict__ count,
+               double* __restrict__ triE, void* __restrict__ triG, void* __restrict__ triS,
+               int out_f32) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S.ns) return;
     const int32_t* T = S.stri + 3 * t;
-    double x0[3], x1[3], x2[3];
-    load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
-    const double eps = P.dhat;
-    double slo[3], shi[3];
-    for (int c = 0; c < 3; ++c) {
-        slo[c] = dmin_(x0[c], dmin_(x1[c], x2[c]));
-        shi[c] = dmax_(x0[c], dmax_(x1[c], x2[c]));
+    double lo[3], hi[3];
+    if (SWEPT) {
+        swept_vert(x, dx, T[0], lo, hi);
+        for (int a = 1; a < 3; ++a) {
+            double l[3], h[3];
+            swept_vert(x, dx, T[a], l, h);
+            grow_box(lo, hi, l, h);
+        }
+    } else {
+        double x0[3], x1[3], x2[3];
+        load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = dmin_(x0[c], dmin_(x1[c], x2[c]));
+            hi[c] = dmax_(x0[c], dmax_(x1[c], x2[c]));
+        }
     }
-    // the face samples are convex combinations of the vertices, so the vertex
-    // box grown by dhat (plus the rounding margin) bounds every candidate
-    const double grow = eps + S.margin;
+    const double grow = SWEPT ? S.margin : P.dhat + S.margin;
     double qlo[3], qhi[3];
-    for (int c = 0; c < 3; ++c) { qlo[c] = slo[c] - grow; qhi[c] = shi[c] + grow; }
-    const double (*rule)[3] = c_rule[P.L - 1];
+    for (int c = 0; c < 3; ++c) { qlo[c] = lo[c] - grow; qhi[c] = hi[c] + grow; }
     const int e = S.stri_env[t];
     const I3 ca = cell_of(S, e, qlo[0], qlo[1], qlo[2]);
     const I3 cb = cell_of(S, e, qhi[0], qhi[1], qhi[2]);
+    bool any = false;
+    for (int iz = ca.z; iz <= cb.z && !any; ++iz)
+        for (int iy = ca.y; iy <= cb.y && !any; ++iy) {
+            const int64_t c0 = cell_id(S, e, ca.x, iy, iz);
+            any = start[c0 + (cb.x - ca.x) + 1] > start[c0];   // cells of a row are contiguous
+        }
+    if (any) {
+        const int idx = atomicAdd(Q.n, 1);
+        Q.tri[idx] = (int32_t)t;
+        double* b = Q.box + 12 * (int64_t)idx;
+        for (int c = 0; c < 3; ++c) { b[c] = lo[c]; b[3 + c] = hi[c]; b[6 + c] = qlo[c]; b[9 + c] = qhi[c]; }
+        int32_t* cl = Q.cell + 6 * (int64_t)idx;
+        cl[0] = ca.x; cl[1] = ca.y; cl[2] = ca.z; cl[3] = cb.x; cl[4] = cb.y; cl[5] = cb.z;
+    } else if (!SWEPT) {
+        int32_t* cnt = count + 4 * t;
+        cnt[0] = 0; cnt[1] = 0; cnt[2] = 0; cnt[3] = 0;
+        if (triE) {
+            triE[t] = 0.0;
+            if (out_f32) {
+                float* G = (float*)triG; float* Sm = (float*)triS;
+                for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0f;
+                for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0f;
+            } else {
+                double* G = (double*)triG; double* Sm = (double*)triS;
+                for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0;
+                for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0;
+            }
+        }
+    }
+}
+
+template <int NK>
+__global__ void __launch_bounds__(256)
+k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __restrict__ x,
+                const double* __restrict__ xm, const double* __restrict__ mbox,
+                const int4* __restrict__ mcell, const int32_t* __restrict__ start,
+                const int32_t* __restrict__ ent, double* __restrict__ triE,
+                void* __restrict__ triG, void* __restrict__ triS, int out_f32) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int n_list = *Q.n;
+    const double eps = P.dhat;
+    const double (*rule)[3] = c_rule[P.L - 1];
+    for (int li = warp; li < n_list; li += nwarps) {
+    const int64_t t = Q.tri[li];
+    const int32_t* T = S.stri + 3 * t;
+    double x0[3], x1[3], x2[3];
+    load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
+    const double* qb = Q.box + 12 * (int64_t)li;
+    const double slo[3] = {qb[0], qb[1], qb[2]}, shi[3] = {qb[3], qb[4], qb[5]};
+    const double qlo[3] = {qb[6], qb[7], qb[8]}, qhi[3] = {qb[9], qb[10], qb[11]};
+    const int32_t* ql = Q.cell + 6 * (int64_t)li;
+    const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
+    const int e = S.stri_env[t];
+    const int nx = cb.x - ca.x + 1, ny = cb.y - ca.y + 1, nz = cb.z - ca.z + 1;
+    const int ncell = nx * ny * nz;
     int nf = 0, ne = 0, np = 0;
     int32_t* Lf = C.face + t * C.cap_f;
     int32_t* Le = C.edge + t * C.cap_e;
     int32_t* Lp = C.point + t * C.cap_p;
-    for (int iz = ca.z; iz <= cb.z; ++iz)
-        for (int iy = ca.y; iy <= cb.y; ++iy)
-            for (int ix = ca.x; ix <= cb.x; ++ix) {
-                const int64_t cell = cell_id(S, e, ix, iy, iz);
-                const int k0 = start[cell], k1 = start[cell + 1];
-                for (int k = k0; k < k1; ++k) {
-                    const int32_t m = ent[k];
-                    const double* B = mbox + 6 * (int64_t)m;
-                    const double mlo0 = B[0], mlo1 = B[1], mlo2 = B[2];
-                    const double mhi0 = B[3], mhi1 = B[4], mhi2 = B[5];
+    for (int c0 = 0; c0 < ncell; c0 += 32) {
+        // each lane looks at one cell of this chunk
+        int my_k0 = 0, my_k1 = 0, ix = 0, iy = 0, iz = 0;
+        if (c0 + lane < ncell) {
+            const int q = c0 + lane;
+            ix = ca.x + q % nx; iy = ca.y + (q / nx) % ny; iz = ca.z + q / (nx * ny);
+            const int64_t cell = cell_id(S, e, ix, iy, iz);
+            my_k0 = start[cell]; my_k1 = start[cell + 1];
+        }
+        unsigned busy = __ballot_sync(0xffffffffu, my_k1 > my_k0);
+        while (busy) {
+            const int src = __ffs(busy) - 1;
+            busy &= busy - 1;
+            const int k0 = __shfl_sync(0xffffffffu, my_k0, src);
+            const int k1 = __shfl_sync(0xffffffffu, my_k1, src);
+            const int cx = __shfl_sync(0xffffffffu, ix, src);
+            const int cy = __shfl_sync(0xffffffffu, iy, src);
+            const int cz = __shfl_sync(0xffffffffu, iz, src);
+            for (int kb = k0; kb < k1; kb += 32) {
+                const int k = kb + lane;
+                bool take = false;
+                int32_t m = 0;
+                if (k < k1) {
+                    m = ent[k];
+                    const int4 mc = mcell[m];
                     // report only in the first cell common to both boxes
-                    I3 mc = cell_of(S, e, mlo0, mlo1, mlo2);
-                    if (max(ca.x, mc.x) != ix || max(ca.y, mc.y) != iy || max(ca.z, mc.z) != iz) continue;
-                    if (qlo[0] > mhi0 || mlo0 > qhi[0] || qlo[1] > mhi1 || mlo1 > qhi[1] ||
-                        qlo[2] > mhi2 || mlo2 > qhi[2])
-                        continue;
-                    // face: some sample ((b0 x0 + b1 x1) + b2 x2) inside the
-                    // master box grown by eps
+                    take = max(ca.x, mc.x) == cx && max(ca.y, mc.y) == cy && max(ca.z, mc.z) == cz;
+                }
+                const double* B = mbox + 6 * (int64_t)m;
+                double mlo0 = 0, mlo1 = 0, mlo2 = 0, mhi0 = 0, mhi1 = 0, mhi2 = 0;
+                if (take) {
+                    mlo0 = B[0]; mlo1 = B[1]; mlo2 = B[2]; mhi0 = B[3]; mhi1 = B[4]; mhi2 = B[5];
+                    take = !(qlo[0] > mhi0 || mlo0 > qhi[0] || qlo[1] > mhi1 || mlo1 > qhi[1] ||
+                             qlo[2] > mhi2 || mlo2 > qhi[2]);
+                }
+                // face: some sample ((b0 x0 + b1 x1) + b2 x2) inside the master box grown by eps
+                bool hit = false;
+                if (take) {
                     const double l0 = mlo0 - eps, l1 = mlo1 - eps, l2 = mlo2 - eps;
                     const double h0 = mhi0 + eps, h1 = mhi1 + eps, h2 = mhi2 + eps;
-                    bool hit = false;
                     for (int q = 0; q < NK && !hit; ++q) {
                         const double b0 = rule[q][0], b1 = rule[q][1], b2 = rule[q][2];
                         const double sxq = b0 * x0[0] + b1 * x1[0] + b2 * x2[0];
@@ -183,43 +333,56 @@ k_query_contact(SceneView S, Params P, CandView C, const double* __restrict__ x,
                         const double szq = b0 * x0[2] + b1 * x1[2] + b2 * x2[2];
                         hit = l2 <= szq && szq <= h2;
                     }
-                    if (hit) { if (nf < C.cap_f) Lf[nf] = m; ++nf; }
-                    // owned edges
-                    for (int j = 0; j < 3; ++j) {
-                        const int32_t me = S.mtri_own_edge[3 * (int64_t)m + j];
-                        if (me < 0) continue;
-                        double ya[3], yb[3];
-                        load3(xm, S.medge[2 * (int64_t)me], ya);
-                        load3(xm, S.medge[2 * (int64_t)me + 1], yb);
-                        bool ok = true;
-                        for (int c = 0; c < 3 && ok; ++c) {
-                            double lo = dmin_(ya[c], yb[c]) - eps, hi = dmax_(ya[c], yb[c]) + eps;
-                            ok = slo[c] <= hi && lo <= shi[c];
+                }
+                warp_append(hit, m, Lf, C.cap_f, nf);
+                // owned edges and vertices
+                for (int j = 0; j < 3; ++j) {
+                    bool ok = false;
+                    int32_t me = -1;
+                    if (take) {
+                        me = S.mtri_own_edge[3 * (int64_t)m + j];
+                        if (me >= 0) {
+                            double ya[3], yb[3];
+                            load3(xm, S.medge[2 * (int64_t)me], ya);
+                            load3(xm, S.medge[2 * (int64_t)me + 1], yb);
+                            ok = true;
+                            for (int c = 0; c < 3 && ok; ++c) {
+                                const double lo = dmin_(ya[c], yb[c]) - eps, hi = dmax_(ya[c], yb[c]) + eps;
+                                ok = slo[c] <= hi && lo <= shi[c];
+                            }
                         }
-                        if (ok) { if (ne < C.cap_e) Le[ne] = me; ++ne; }
                     }
-                    // owned vertices
-                    for (int j = 0; j < 3; ++j) {
-                        const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
-                        if (u < 0) continue;
-                        double y[3];
-                        load3(xm, u, y);
-                        bool ok = true;
-                        for (int c = 0; c < 3 && ok; ++c) ok = slo[c] <= y[c] + eps && y[c] - eps <= shi[c];
-                        if (ok) { if (np < C.cap_p) Lp[np] = u; ++np; }
+                    warp_append(ok, me, Le, C.cap_e, ne);
+                }
+                for (int j = 0; j < 3; ++j) {
+                    bool ok = false;
+                    int32_t u = -1;
+                    if (take) {
+                        u = S.mtri_own_vert[3 * (int64_t)m + j];
+                        if (u >= 0) {
+                            double y[3];
+                            load3(xm, u, y);
+                            ok = true;
+                            for (int c = 0; c < 3 && ok; ++c) ok = slo[c] <= y[c] + eps && y[c] - eps <= shi[c];
+                        }
                     }
+                    warp_append(ok, u, Lp, C.cap_p, np);
                 }
             }
-    sort_small(Lf, min(nf, C.cap_f));
-    sort_small(Le, min(ne, C.cap_e));
-    sort_small(Lp, min(np, C.cap_p));
+        }
+    }
+    __syncwarp();
+    warp_sort(Lf, min(nf, C.cap_f), lane);
+    warp_sort(Le, min(ne, C.cap_e), lane);
+    warp_sort(Lp, min(np, C.cap_p), lane);
+    if (lane != 0) continue;
     int32_t* cnt = C.count + 4 * t;
     cnt[0] = nf; cnt[1] = ne; cnt[2] = np; cnt[3] = 0;
     if (nf > C.cap_f) atomicMax(&C.overflow[0], nf);
     if (ne > C.cap_e) atomicMax(&C.overflow[1], ne);
     if (np > C.cap_p) atomicMax(&C.overflow[2], np);
     if (nf + ne + np > 0) {
-        int idx = atomicAdd(C.n_active, 1);
+        const int idx = atomicAdd(C.n_active, 1);
         C.active[idx] = (int32_t)t;
     } else if (triE) {
         // no candidates: this triangle contributes nothing to the gathers
@@ -234,6 +397,7 @@ k_query_contact(SceneView S, Params P, CandView C, const double* __restrict__ x,
             for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0;
         }
     }
+    }  // list loop
 }
 
 // ---------------------------------------------------------------------------
@@ -360,17 +524,6 @@ __device__ __noinline__ double accd(int type, double* x, double* p, double s, do
     return t;
 }
 
-__device__ __forceinline__ void swept_vert(const double* P, const double* D, int64_t v, double* lo,
-                                           double* hi) {
-    for (int c = 0; c < 3; ++c) {
-        double a = P[3 * v + c];
-        double b = D ? a + D[3 * v + c] : a;
-        lo[c] = dmin_(a, b); hi[c] = dmax_(a, b);
-    }
-}
-__device__ __forceinline__ void grow_box(double* lo, double* hi, const double* l2, const double* h2) {
-    for (int c = 0; c < 3; ++c) { lo[c] = dmin_(lo[c], l2[c]); hi[c] = dmax_(hi[c], h2[c]); }
-}
 __device__ __forceinline__ bool overlap(const double* alo, const double* ahi, const double* blo,
                                         const double* bhi) {
     return alo[0] <= bhi[0] && blo[0] <= ahi[0] && alo[1] <= bhi[1] && blo[1] <= ahi[1] &&
@@ -382,109 +535,135 @@ __device__ __forceinline__ void atomic_min_pos(unsigned long long* dst, double v
     atomicMin(dst, (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void __launch_bounds__(128)
-k_query_ccd(SceneView S, Params P, const double* __restrict__ x, const double* __restrict__ dx,
-            const double* __restrict__ xm0, const double* __restrict__ dxm,
-            const double* __restrict__ mbox, const int32_t* __restrict__ start,
+// swept query + ACCD: persistent warps over the filtered slave triangles,
+// lanes over cell entries
+__global__ void __launch_bounds__(256)
+k_query_ccd(SceneView S, Params P, QueryList Q, const double* __restrict__ x,
+            const double* __restrict__ dx, const double* __restrict__ xm0,
+            const double* __restrict__ dxm, const double* __restrict__ mbox,
+            const int4* __restrict__ mcell, const int32_t* __restrict__ start,
             const int32_t* __restrict__ ent, unsigned long long* alpha_bits, long long* counters) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= S.ns) return;
-    const int32_t* T = S.stri + 3 * t;
-    double tlo[3], thi[3];
-    swept_vert(x, dx, T[0], tlo, thi);
-    for (int a = 1; a < 3; ++a) {
-        double l[3], h[3];
-        swept_vert(x, dx, T[a], l, h);
-        grow_box(tlo, thi, l, h);
-    }
-    double qlo[3], qhi[3];
-    for (int c = 0; c < 3; ++c) { qlo[c] = tlo[c] - S.margin; qhi[c] = thi[c] + S.margin; }
-    const int e = S.stri_env[t];
-    const I3 ca = cell_of(S, e, qlo[0], qlo[1], qlo[2]);
-    const I3 cb = cell_of(S, e, qhi[0], qhi[1], qhi[2]);
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int n_list = *Q.n;
     double best = 1.0;
     long long n_pt = 0, n_ee = 0;
     int cap_hit = 0;
-    for (int iz = ca.z; iz <= cb.z; ++iz)
-        for (int iy = ca.y; iy <= cb.y; ++iy)
-            for (int ix = ca.x; ix <= cb.x; ++ix) {
-                const int64_t cell = cell_id(S, e, ix, iy, iz);
-                for (int k = start[cell]; k < start[cell + 1]; ++k) {
-                    const int32_t m = ent[k];
-                    const double* B = mbox + 6 * (int64_t)m;
-                    I3 mc = cell_of(S, e, B[0], B[1], B[2]);
-                    if (max(ca.x, mc.x) != ix || max(ca.y, mc.y) != iy || max(ca.z, mc.z) != iz) continue;
-                    if (!overlap(qlo, qhi, B, B + 3)) continue;
-                    const int32_t* M = S.mtri + 3 * (int64_t)m;
-                    double X12[12], P12[12];
-                    int it;
-                    // slave vertices owned by t vs master triangle m
-                    for (int j = 0; j < 3; ++j) {
-                        const int32_t v = S.stri_own_vert[3 * t + j];
-                        if (v < 0) continue;
-                        double vlo[3], vhi[3];
-                        swept_vert(x, dx, v, vlo, vhi);
-                        if (!overlap(vlo, vhi, B, B + 3)) continue;
-                        for (int c = 0; c < 3; ++c) {
-                            X12[c] = x[3 * (int64_t)v + c]; P12[c] = dx[3 * (int64_t)v + c];
-                            for (int a = 0; a < 3; ++a) {
-                                X12[3 + 3 * a + c] = xm0[3 * (int64_t)M[a] + c];
-                                P12[3 + 3 * a + c] = dxm ? dxm[3 * (int64_t)M[a] + c] : 0.0;
-                            }
+    for (int li = warp; li < n_list; li += nwarps) {
+    const int64_t t = Q.tri[li];
+    const int32_t* T = S.stri + 3 * t;
+    const double* qb = Q.box + 12 * (int64_t)li;
+    const double tlo[3] = {qb[0], qb[1], qb[2]}, thi[3] = {qb[3], qb[4], qb[5]};
+    const double qlo[3] = {qb[6], qb[7], qb[8]}, qhi[3] = {qb[9], qb[10], qb[11]};
+    const int32_t* ql = Q.cell + 6 * (int64_t)li;
+    const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
+    const int e = S.stri_env[t];
+    const int nx = cb.x - ca.x + 1, ny = cb.y - ca.y + 1, nz = cb.z - ca.z + 1;
+    const int ncell = nx * ny * nz;
+    for (int c0 = 0; c0 < ncell; c0 += 32) {
+        int my_k0 = 0, my_k1 = 0, ix = 0, iy = 0, iz = 0;
+        if (c0 + lane < ncell) {
+            const int q = c0 + lane;
+            ix = ca.x + q % nx; iy = ca.y + (q / nx) % ny; iz = ca.z + q / (nx * ny);
+            const int64_t cell = cell_id(S, e, ix, iy, iz);
+            my_k0 = start[cell]; my_k1 = start[cell + 1];
+        }
+        unsigned busy = __ballot_sync(0xffffffffu, my_k1 > my_k0);
+        while (busy) {
+            const int src = __ffs(busy) - 1;
+            busy &= busy - 1;
+            const int k0 = __shfl_sync(0xffffffffu, my_k0, src);
+            const int k1 = __shfl_sync(0xffffffffu, my_k1, src);
+            const int cx = __shfl_sync(0xffffffffu, ix, src);
+            const int cy = __shfl_sync(0xffffffffu, iy, src);
+            const int cz = __shfl_sync(0xffffffffu, iz, src);
+            for (int k = k0 + lane; k < k1; k += 32) {
+                const int32_t m = ent[k];
+                const int4 mc = mcell[m];
+                if (max(ca.x, mc.x) != cx || max(ca.y, mc.y) != cy || max(ca.z, mc.z) != cz) continue;
+                const double* B = mbox + 6 * (int64_t)m;
+                if (!overlap(qlo, qhi, B, B + 3)) continue;
+                const int32_t* M = S.mtri + 3 * (int64_t)m;
+                double X12[12], P12[12];
+                int it;
+                // slave vertices owned by t vs master triangle m
+                for (int j = 0; j < 3; ++j) {
+                    const int32_t v = S.stri_own_vert[3 * t + j];
+                    if (v < 0) continue;
+                    double vlo[3], vhi[3];
+                    swept_vert(x, dx, v, vlo, vhi);
+                    if (!overlap(vlo, vhi, B, B + 3)) continue;
+                    for (int c = 0; c < 3; ++c) {
+                        X12[c] = x[3 * (int64_t)v + c]; P12[c] = dx[3 * (int64_t)v + c];
+                        for (int a = 0; a < 3; ++a) {
+                            X12[3 + 3 * a + c] = xm0[3 * (int64_t)M[a] + c];
+                            P12[3 + 3 * a + c] = dxm ? dxm[3 * (int64_t)M[a] + c] : 0.0;
                         }
-                        double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-                        ++n_pt; cap_hit |= it >= P.ccd_max_iter;
-                        best = dmin_(best, r);
                     }
-                    // master vertices owned by m vs slave triangle t
-                    for (int j = 0; j < 3; ++j) {
-                        const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
-                        if (u < 0) continue;
-                        double ulo[3], uhi[3];
-                        swept_vert(xm0, dxm, u, ulo, uhi);
-                        if (!overlap(ulo, uhi, tlo, thi)) continue;
-                        for (int c = 0; c < 3; ++c) {
-                            X12[c] = xm0[3 * (int64_t)u + c]; P12[c] = dxm ? dxm[3 * (int64_t)u + c] : 0.0;
-                            for (int a = 0; a < 3; ++a) {
-                                X12[3 + 3 * a + c] = x[3 * (int64_t)T[a] + c];
-                                P12[3 + 3 * a + c] = dx[3 * (int64_t)T[a] + c];
-                            }
+                    const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+                    ++n_pt; cap_hit |= it >= P.ccd_max_iter;
+                    best = dmin_(best, r);
+                }
+                // master vertices owned by m vs slave triangle t
+                for (int j = 0; j < 3; ++j) {
+                    const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
+                    if (u < 0) continue;
+                    double ulo[3], uhi[3];
+                    swept_vert(xm0, dxm, u, ulo, uhi);
+                    if (!overlap(ulo, uhi, tlo, thi)) continue;
+                    for (int c = 0; c < 3; ++c) {
+                        X12[c] = xm0[3 * (int64_t)u + c]; P12[c] = dxm ? dxm[3 * (int64_t)u + c] : 0.0;
+                        for (int a = 0; a < 3; ++a) {
+                            X12[3 + 3 * a + c] = x[3 * (int64_t)T[a] + c];
+                            P12[3 + 3 * a + c] = dx[3 * (int64_t)T[a] + c];
                         }
-                        double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-                        ++n_pt; cap_hit |= it >= P.ccd_max_iter;
-                        best = dmin_(best, r);
                     }
-                    // slave edges owned by t vs master edges owned by m
-                    for (int j = 0; j < 3; ++j) {
-                        const int32_t es = S.stri_own_edge[3 * t + j];
-                        if (es < 0) continue;
-                        const int32_t sa = S.sedge[2 * (int64_t)es], sb = S.sedge[2 * (int64_t)es + 1];
-                        double alo[3], ahi[3], l2[3], h2[3];
-                        swept_vert(x, dx, sa, alo, ahi);
-                        swept_vert(x, dx, sb, l2, h2);
-                        grow_box(alo, ahi, l2, h2);
-                        for (int q = 0; q < 3; ++q) {
-                            const int32_t em = S.mtri_own_edge[3 * (int64_t)m + q];
-                            if (em < 0) continue;
-                            const int32_t m0 = S.medge[2 * (int64_t)em], m1 = S.medge[2 * (int64_t)em + 1];
-                            double blo[3], bhi[3];
-                            swept_vert(xm0, dxm, m0, blo, bhi);
-                            swept_vert(xm0, dxm, m1, l2, h2);
-                            grow_box(blo, bhi, l2, h2);
-                            if (!overlap(alo, ahi, blo, bhi)) continue;
-                            for (int c = 0; c < 3; ++c) {
-                                X12[c] = x[3 * (int64_t)sa + c]; P12[c] = dx[3 * (int64_t)sa + c];
-                                X12[3 + c] = x[3 * (int64_t)sb + c]; P12[3 + c] = dx[3 * (int64_t)sb + c];
-                                X12[6 + c] = xm0[3 * (int64_t)m0 + c]; P12[6 + c] = dxm ? dxm[3 * (int64_t)m0 + c] : 0.0;
-                                X12[9 + c] = xm0[3 * (int64_t)m1 + c]; P12[9 + c] = dxm ? dxm[3 * (int64_t)m1 + c] : 0.0;
-                            }
-                            double r = accd(1, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-                            ++n_ee; cap_hit |= it >= P.ccd_max_iter;
-                            best = dmin_(best, r);
+                    const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+                    ++n_pt; cap_hit |= it >= P.ccd_max_iter;
+                    best = dmin_(best, r);
+                }
+                // slave edges owned by t vs master edges owned by m
+                for (int j = 0; j < 3; ++j) {
+                    const int32_t es = S.stri_own_edge[3 * t + j];
+                    if (es < 0) continue;
+                    const int32_t sa = S.sedge[2 * (int64_t)es], sb = S.sedge[2 * (int64_t)es + 1];
+                    double alo[3], ahi[3], l2[3], h2[3];
+                    swept_vert(x, dx, sa, alo, ahi);
+                    swept_vert(x, dx, sb, l2, h2);
+                    grow_box(alo, ahi, l2, h2);
+                    for (int q = 0; q < 3; ++q) {
+                        const int32_t em = S.mtri_own_edge[3 * (int64_t)m + q];
+                        if (em < 0) continue;
+                        const int32_t m0 = S.medge[2 * (int64_t)em], m1 = S.medge[2 * (int64_t)em + 1];
+                        double blo[3], bhi[3];
+                        swept_vert(xm0, dxm, m0, blo, bhi);
+                        swept_vert(xm0, dxm, m1, l2, h2);
+                        grow_box(blo, bhi, l2, h2);
+                        if (!overlap(alo, ahi, blo, bhi)) continue;
+                        for (int c = 0; c < 3; ++c) {
+                            X12[c] = x[3 * (int64_t)sa + c]; P12[c] = dx[3 * (int64_t)sa + c];
+                            X12[3 + c] = x[3 * (int64_t)sb + c]; P12[3 + c] = dx[3 * (int64_t)sb + c];
+                            X12[6 + c] = xm0[3 * (int64_t)m0 + c]; P12[6 + c] = dxm ? dxm[3 * (int64_t)m0 + c] : 0.0;
+                            X12[9 + c] = xm0[3 * (int64_t)m1 + c]; P12[9 + c] = dxm ? dxm[3 * (int64_t)m1 + c] : 0.0;
                         }
+                        const double r = accd(1, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+                        ++n_ee; cap_hit |= it >= P.ccd_max_iter;
+                        best = dmin_(best, r);
                     }
                 }
             }
+        }
+    }
+    }  // list loop
+    // warp reductions (min is exact; counters are integers)
+    for (int o = 16; o > 0; o >>= 1) {
+        best = dmin_(best, __shfl_xor_sync(0xffffffffu, best, o));
+        n_pt += __shfl_xor_sync(0xffffffffu, n_pt, o);
+        n_ee += __shfl_xor_sync(0xffffffffu, n_ee, o);
+        cap_hit |= __shfl_xor_sync(0xffffffffu, cap_hit, o);
+    }
+    if (lane != 0) return;
     if (best < 1.0) atomic_min_pos(alpha_bits, best);
     if (n_pt) atomic_add_ll(&counters[0], n_pt);
     if (n_ee) atomic_add_ll(&counters[1], n_ee);
@@ -505,6 +684,7 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     SceneView S = c.view();
     cudaStream_t s = c.stream;
     GMCP_CUDA_TRY(c.mbox.ensure(6 * (size_t)c.nmt + 6));
+    GMCP_CUDA_TRY(c.mcell.ensure((size_t)c.nmt + 1));
     GMCP_CUDA_TRY(c.cell_cnt.ensure((size_t)c.n_cells + 1));
     GMCP_CUDA_TRY(c.cell_start.ensure((size_t)c.n_cells + 1));
     GMCP_CUDA_TRY(c.scan_tmp.ensure(2 * scan_tmp_size(c.n_cells)));
@@ -512,7 +692,7 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     const int B = 256;
     const unsigned g = (unsigned)((c.nmt + B - 1) / B);
     if (c.nmt > 0) {
-        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mbox.p, c.cell_cnt.p);
+        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mbox.p, c.mcell.p, c.cell_cnt.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     GMCP_CUDA_TRY(exclusive_scan_i32(c.cell_cnt.p, c.cell_start.p, c.n_cells, c.scan_tmp.p,
@@ -531,26 +711,48 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     return cudaSuccess;
 }
 
+static QueryList query_list(Ctx& c) {
+    QueryList Q;
+    Q.n = c.misc_i32.p + 8;
+    Q.tri = c.qlist_tri.p;
+    Q.box = c.qlist_box.p;
+    Q.cell = c.qlist_cell.p;
+    return Q;
+}
+
+static cudaError_t ensure_query_list(Ctx& c) {
+    GMCP_CUDA_TRY(c.qlist_tri.ensure((size_t)c.ns + 1));
+    GMCP_CUDA_TRY(c.qlist_box.ensure(12 * (size_t)c.ns + 12));
+    GMCP_CUDA_TRY(c.qlist_cell.ensure(6 * (size_t)c.ns + 6));
+    return cudaSuccess;
+}
+
+static unsigned persistent_blocks(Ctx& c) { return (unsigned)(sm_count(c.device) * 8); }
+
 cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
     ProfScope ps(c.prof, c.stream, "query");
     SceneView S = c.view();
     Params P = c.P;
     cudaStream_t s = c.stream;
     CandView C = c.cand();
-    GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 4, s));
+    GMCP_CUDA_TRY(ensure_query_list(c));
+    QueryList Q = query_list(c);
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 12, s));
     if (c.ns == 0) return cudaSuccess;
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
     double* triE = c.tri_E.p;
     void* triG = f32 ? (void*)c.tri_G32.p : (void*)c.tri_G64.p;
     void* triS = f32 ? (void*)c.tri_S32.p : (void*)c.tri_S64.p;
-    const int B = 128;
-    const unsigned g = (unsigned)((c.ns + B - 1) / B);
+    k_query_filter<false><<<(unsigned)((c.ns + 255) / 256), 256, 0, s>>>(
+        S, P, x, nullptr, c.cell_start.p, Q, c.cand_count.p, triE, triG, triS, f32);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    const unsigned g = persistent_blocks(c);
     if (P.nk == 4)
-        k_query_contact<4><<<g, B, 0, s>>>(S, P, C, x, xm, c.mbox.p, c.cell_start.p, c.cell_ent.p,
-                                           triE, triG, triS, f32);
+        k_query_contact<4><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mcell.p, c.cell_start.p,
+                                             c.cell_ent.p, triE, triG, triS, f32);
     else
-        k_query_contact<16><<<g, B, 0, s>>>(S, P, C, x, xm, c.mbox.p, c.cell_start.p, c.cell_ent.p,
-                                            triE, triG, triS, f32);
+        k_query_contact<16><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mcell.p, c.cell_start.p,
+                                              c.cell_ent.p, triE, triG, triS, f32);
     return cudaGetLastError();
 }
 
@@ -560,10 +762,15 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
     ProfScope ps(c.prof, c.stream, "accd");
     if (c.ns == 0) return cudaSuccess;
     SceneView S = c.view();
-    const int B = 128;
-    const unsigned g = (unsigned)((c.ns + B - 1) / B);
-    k_query_ccd<<<g, B, 0, c.stream>>>(S, c.P, x, dx, xm0, dxm, c.mbox.p, c.cell_start.p,
-                                       c.cell_ent.p, alpha_bits, counters);
+    GMCP_CUDA_TRY(ensure_query_list(c));
+    QueryList Q = query_list(c);
+    GMCP_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(int32_t), c.stream));
+    k_query_filter<true><<<(unsigned)((c.ns + 255) / 256), 256, 0, c.stream>>>(
+        S, c.P, x, dx, c.cell_start.p, Q, nullptr, nullptr, nullptr, nullptr, 0);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    k_query_ccd<<<persistent_blocks(c), 256, 0, c.stream>>>(S, c.P, Q, x, dx, xm0, dxm, c.mbox.p,
+                                                          c.mcell.p, c.cell_start.p, c.cell_ent.p,
+                                                          alpha_bits, counters);
     return cudaGetLastError();
 }
 

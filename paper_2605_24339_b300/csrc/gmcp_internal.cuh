@@ -209,6 +209,9 @@ struct Ctx {
 
     // per-call broad-phase buffers
     DBuf<double> mbox;                          // [nmt][6]
+    DBuf<int4> mcell;                           // [nmt] lowest cell (x, y, z) and env
+    DBuf<int32_t> qlist_tri, qlist_cell;        // slave tris whose query meets a non-empty cell
+    DBuf<double> qlist_box;
     DBuf<int32_t> cell_cnt, cell_start, cell_ent;
     DBuf<int32_t> scan_tmp;
     DBuf<int32_t> cand_face, cand_edge, cand_point, cand_count, active, misc_i32;
