@@ -1,11 +1,11 @@
 """Benchmark of the GMCP contact pass on one B300 (or N independent replicas).
 
-A step is one full contact pass through the C ABI on the gel-on-terrain
-workload (256x256-quad gel pad, 131,072 slave triangles x 16 face samples =
+A step is one full contact pass (ipc_contact_pass) through the C ABI on the
+gel-on-terrain workload (256x256-quad gel pad, 131,072 slave triangles x 16 face samples =
 2,097,152 samples, against a 199,712-triangle Perlin terrain, dhat = 5e-5 m),
 mixed precision (FP32 barrier, FP64 distance anchors and CCD):
-  ipc_barrier_eval  -- broad phase, samples, energy, gradient, BSR Hessian
-  ipc_ccd_max_step  -- linearised-gap bound and additive CCD for a step dx
+  broad phase, samples, energy, gradient, BSR Hessian (as ipc_barrier_eval)
+  linearised-gap bound and additive CCD for a step dx (as ipc_ccd_max_step)
 The pad state is the terrain pressed 0.15 mm deep (scenes.drape_on_master);
 dx is a seeded downward press of 5 um x U[0.5, 1.5] per vertex plus 1 um
 tangential noise.  Inputs stay resident in HBM; L2 (126 MB) is flushed by
@@ -186,8 +186,8 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
-        ctx.barrier_eval(x, xm, grad=True, hess="view", counts=False, energy_dev=e_dev, grad_out=grad)
-        return ctx.ccd_max_step(x, dx, xm)
+        return ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=False, energy_dev=e_dev,
+                                grad_out=grad)
 
     for _ in range(args.warmup):
         info = step()
@@ -224,8 +224,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         x_e2e.copy_(x_host, non_blocking=True)
-        ctx.barrier_eval(x_e2e, xm, grad=True, hess="view", counts=False, energy_dev=e_dev, grad_out=grad)
-        info = ctx.ccd_max_step(x_e2e, dx, xm)
+        info = ctx.contact_pass(x_e2e, xm, dx, grad=True, hess="view", counts=False,
+                                energy_dev=e_dev, grad_out=grad)
         out_host[:1].copy_(e_dev, non_blocking=False)
         out_host[1] = info["alpha"]
     torch.cuda.synchronize()
@@ -241,8 +241,8 @@ def run_ours(args):
     cand_secs = [s for s in ("samples", "query", "gather_grad") if s in sec_ms]
     top = max(cand_secs, key=lambda s: sec_ms[s])
     achieved = ab[top] / (sec_ms[top] / 1e3) / 1e9
-    n_launch_per_step = {"grid": 5, "query": 1, "samples": 1, "gather_grad": 1, "gather_hess": 1,
-                         "reduce": 2, "alpha_lin": 1, "accd": 1}
+    n_launch_per_step = {"grid": 5, "query": 2, "samples": 1, "gather_grad": 1, "gather_hess": 1,
+                         "reduce": 2, "alpha_lin": 1, "accd": 2}
     launches = 0
     for k, v in prof.items():
         per = n_launch_per_step.get(k, 1)
@@ -313,8 +313,7 @@ def run_passes(args):
     xm = torch.as_tensor(sc.Y0, device="cuda")
     e_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
     for _ in range(args.steps):
-        ctx.barrier_eval(x, xm, grad=True, hess="view", counts=False, energy_dev=e_dev)
-        info = ctx.ccd_max_step(x, dx, xm)
+        info = ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=False, energy_dev=e_dev)
     torch.cuda.synchronize()
     print(json.dumps({"passes": args.steps, "alpha": info["alpha"], "ccd_pairs_pt": info["n_pt"],
                       "ccd_pairs_ee": info["n_ee"]}))

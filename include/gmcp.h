@@ -200,6 +200,23 @@ ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_
                             const double* xm0_dev, const double* xm1_dev, double* alpha_host,
                             ipc_ccd_info* info);
 
+/* One full contact pass for a Newton iteration (Sec. 4.1-4.5 together): the
+ * broad phase at (x_dev, xm0_dev) runs once and serves both
+ *  - the potential, gradient and Hessian of ipc_barrier_eval (energy_dev,
+ *    energy_host, grad_dev, hess, counts: same meaning and may be NULL), and
+ *  - the step bound of ipc_ccd_max_step for the motion x -> x + alpha dx_dev,
+ *    xm0 -> xm0 + alpha (xm1 - xm0) (xm1_dev NULL = static master; then the
+ *    additive CCD reuses the grid of the broad phase).  The linearised-gap
+ *    bound of Eq. (ccd) is computed in the same sample kernel.
+ * dx_dev may be NULL (no step bound; alpha_host and info are then left
+ * untouched).  alpha_host / info (host, may be NULL) receive the bound as in
+ * ipc_ccd_max_step; asking for any host output synchronises the stream.
+ * Results equal those of ipc_barrier_eval followed by ipc_ccd_max_step. */
+ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev,
+                            const double* xm1_dev, const double* dx_dev, double* energy_dev,
+                            double* energy_host, void* grad_dev, ipc_bsr_view* hess,
+                            double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts);
+
 /* One implicit-Euler time step (paper Sec. 2.1 problem statement): x_dev
  * [n_vert][3] holds x^t on entry and x^{t+1} on exit, v_dev the velocity
  * (Dirichlet vertices move to x + h v).  xm_next_dev: master at t+1 (NULL =

@@ -109,6 +109,9 @@ def lib():
                                    C.POINTER(SampleCounts)]
     L.ipc_ccd_max_step.restype = C.c_int
     L.ipc_ccd_max_step.argtypes = [P, P, P, P, P, C.POINTER(C.c_double), C.POINTER(CcdInfo)]
+    L.ipc_contact_pass.restype = C.c_int
+    L.ipc_contact_pass.argtypes = [P, P, P, P, P, P, C.POINTER(C.c_double), P, C.POINTER(BsrView),
+                                   C.POINTER(C.c_double), C.POINTER(CcdInfo), C.POINTER(SampleCounts)]
     L.ipc_profile.restype = C.c_int
     L.ipc_profile.argtypes = [P, C.c_int32, C.c_int32, P, P, P, C.POINTER(C.c_int32)]
     L.ipc_newton_step.restype = C.c_int
@@ -284,6 +287,40 @@ class Context:
                                            C.byref(a), C.byref(info)))
         return dict(alpha=info.alpha, alpha_lin=info.alpha_lin, alpha_accd=info.alpha_accd,
                     n_pt=info.n_pairs_pt, n_ee=info.n_pairs_ee, iter_cap_hit=bool(info.iter_cap_hit))
+
+    def contact_pass(self, x, xm0, dx=None, xm1=None, grad=True, hess=True, counts=True,
+                     energy_dev=None, grad_out=None, host_alpha=True):
+        """ipc_contact_pass: barrier evaluation and step bound sharing one broad
+        phase.  hess="view" returns the raw BsrView (no copy)."""
+        t = self.torch
+        x, xm0, dx, xm1 = self._as(x), self._as(xm0), self._as(dx), self._as(xm1)
+        gdt = t.float32 if self.precision == "mixed" else t.float64
+        g = grad_out
+        if g is None and grad:
+            g = t.empty((self.nv, 3), dtype=gdt, device=self.device)
+        e = C.c_double()
+        bv = BsrView()
+        sc = SampleCounts()
+        a = C.c_double()
+        info = CcdInfo()
+        want_a = dx is not None and host_alpha
+        self._check(lib().ipc_contact_pass(
+            self.h, _ptr(x), _ptr(xm0), _ptr(xm1), _ptr(dx), _ptr(energy_dev),
+            None if energy_dev is not None else C.byref(e), _ptr(g),
+            C.byref(bv) if hess else None, C.byref(a) if want_a else None,
+            C.byref(info) if want_a else None, C.byref(sc) if counts else None))
+        out = dict(energy=e.value if energy_dev is None else None, grad=g)
+        if counts:
+            out["counts"] = dict(face=sc.face, edge=sc.edge, point=sc.point, guard=sc.guard,
+                                 face_evaluated=sc.face_evaluated)
+        if hess == "view":
+            out["hess"] = bv
+        elif hess:
+            out["hess"] = self.bsr(bv)
+        if want_a:
+            out.update(alpha=info.alpha, alpha_lin=info.alpha_lin, alpha_accd=info.alpha_accd,
+                       n_pt=info.n_pairs_pt, n_ee=info.n_pairs_ee)
+        return out
 
     # -- profiling ---------------------------------------------------------
     def profile_start(self):

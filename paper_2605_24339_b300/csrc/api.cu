@@ -625,6 +625,81 @@ ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_
     return IPC_OK;
 }
 
+ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev,
+                            const double* xm1_dev, const double* dx_dev, double* energy_dev,
+                            double* energy_host, void* grad_dev, ipc_bsr_view* hess,
+                            double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!x_dev || (!xm0_dev && c.nmv > 0)) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_contact_pass: NULL positions");
+    API_CK(ctx, cudaSetDevice(c.device));
+    const double* dxm = nullptr;
+    if (dx_dev && xm1_dev) {
+        API_CK(ctx, c.dxm.ensure(3 * (size_t)c.nmv + 3));
+        const int64_t n = 3 * c.nmv;
+        if (n > 0) {
+            k_sub<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(xm1_dev, xm0_dev, c.dxm.p, n);
+            API_CK(ctx, cudaGetLastError());
+        }
+        dxm = c.dxm.p;
+    }
+    if (dx_dev) {
+        const unsigned long long init[2] = {0x7FF0000000000000ULL, 0x3FF0000000000000ULL};
+        API_CK(ctx, cudaMemcpyAsync(c.u64_tmp.p, init, sizeof(init), cudaMemcpyHostToDevice, c.stream));
+        API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
+    }
+    API_CK(ctx, run_candidates(c, x_dev, xm0_dev));
+    long long* ctr = nullptr;
+    if (counts) {
+        API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
+        ctr = c.i64_tmp.p;
+    }
+    double* edev = energy_dev;
+    if (energy_host && !energy_dev) edev = c.scal.p;
+    API_CK(ctx, contact_eval(c, x_dev, xm0_dev, edev, grad_dev, hess != nullptr, ctr, dx_dev, dxm,
+                             dx_dev ? c.u64_tmp.p : nullptr));
+    if (dx_dev)
+        API_CK(ctx, bp_ccd_accd(c, x_dev, dx_dev, xm0_dev, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8, true));
+    const bool want_alpha = dx_dev && (alpha_host || info);
+    unsigned long long bits[2];
+    long long ctr_ccd[4];
+    if (energy_host)
+        API_CK(ctx, cudaMemcpyAsync(c.h_scalars, edev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    if (counts)
+        API_CK(ctx, cudaMemcpyAsync(c.h_counts, c.i64_tmp.p, 4 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+    if (want_alpha) {
+        API_CK(ctx, cudaMemcpyAsync(bits, c.u64_tmp.p, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
+        API_CK(ctx, cudaMemcpyAsync(ctr_ccd, c.i64_tmp.p + 8, sizeof(ctr_ccd), cudaMemcpyDeviceToHost, c.stream));
+    }
+    if (energy_host || counts || want_alpha) API_CK(ctx, cudaStreamSynchronize(c.stream));
+    if (energy_host) *energy_host = c.h_scalars[0];
+    if (counts) {
+        counts->face = c.h_counts[0]; counts->edge = c.h_counts[1]; counts->point = c.h_counts[2];
+        counts->guard = 0; counts->face_evaluated = c.h_counts[3];
+    }
+    if (hess) {
+        const bool f32 = c.P.precision == IPC_PREC_MIXED;
+        hess->n_rows = c.nv; hess->nnzb = c.cb_nnzb;
+        hess->row_ptr_dev = c.cb_row.p; hess->col_idx_dev = c.cb_col.p;
+        hess->vals_dev = f32 ? (const void*)c.cb_val32.p : (const void*)c.cb_val64.p;
+        hess->dtype = f32 ? 1 : 0;
+    }
+    if (want_alpha) {
+        double al, aa;
+        memcpy(&al, &bits[0], 8);
+        memcpy(&aa, &bits[1], 8);
+        if (al < INFINITY) al *= (1.0 - 1e-10);
+        const double a = std::min(1.0, std::min(al, aa));
+        if (alpha_host) *alpha_host = a;
+        if (info) {
+            info->alpha = a; info->alpha_lin = al; info->alpha_accd = aa;
+            info->n_pairs_pt = ctr_ccd[0]; info->n_pairs_ee = ctr_ccd[1];
+            info->iter_cap_hit = (int32_t)(ctr_ccd[2] != 0);
+        }
+    }
+    return IPC_OK;
+}
+
 ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* names_host,
                        double* ms_host, int64_t* calls_host, int32_t* n_sections) {
     if (!ctx) return IPC_ERR_ARG;

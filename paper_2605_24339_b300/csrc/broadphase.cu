@@ -757,8 +757,9 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
 }
 
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
-                        const double* dxm, unsigned long long* alpha_bits, long long* counters) {
-    GMCP_CUDA_TRY(bp_build_grid(c, xm0, dxm, true));
+                        const double* dxm, unsigned long long* alpha_bits, long long* counters,
+                        bool reuse_grid) {
+    if (!(reuse_grid && dxm == nullptr)) GMCP_CUDA_TRY(bp_build_grid(c, xm0, dxm, true));
     ProfScope ps(c.prof, c.stream, "accd");
     if (c.ns == 0) return cudaSuccess;
     SceneView S = c.view();

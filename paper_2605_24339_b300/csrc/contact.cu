@@ -116,6 +116,32 @@ __device__ __forceinline__ bool face_geom(V3<R> xs, V3<R> ns, V3<R> y0, V3<R> y1
     return min3(bm) >= R(0) && g > R(0);
 }
 
+// FP32 pre-test of a face sample in the slave triangle's local frame: false
+// only when the exact FP64 test (face_geom<double> with g < eps <= eps_max)
+// certainly fails.  Near-grazing casts (|N.n_s| < 1e-3 |N|) always go to the
+// FP64 test.  With |den| >= 1e-3 |N| the FP32 gap is within 1e-3 (|d| + |g|)
+// of the FP64 one (inputs rounded once, a handful of operations of relative
+// error 6e-8 each, divided by |den|/|N| >= 1e-3), and the barycentric error
+// is that gap error over the triangle's smallest height plus 1e-2 slack.
+__device__ __forceinline__ bool face_maybe(V3<float> xs, V3<float> ns, V3<float> y0, V3<float> y1,
+                                           V3<float> y2, float eps_max) {
+    const V3<float> e1 = y1 - y0, e2 = y2 - y0, N = cross(e1, e2);
+    const float nN = sqrtf(dot(N, N));
+    const float den = dot(N, ns);
+    if (den >= 1e-3f * nN) return false;          // faces away (facing needs den < 0)
+    if (den > -1e-3f * nN) return true;           // grazing: let FP64 decide
+    const V3<float> d = y0 - xs;
+    const float g = dot(N, d) / den;
+    const float tol_g = 1e-3f * (sqrtf(dot(d, d)) + fabsf(g));
+    if (g > eps_max + tol_g || g < -tol_g) return false;
+    const V3<float> p = xs + g * ns;
+    float b[3];
+    bary(p, y0, y1, y2, b);
+    const float lmax = sqrtf(rmax(dot(e1, e1), rmax(dot(e2, e2), dot(e2 - e1, e2 - e1))));
+    const float tol_b = 1e-2f + 4.0f * tol_g * lmax / nN;
+    return min3(b) >= -tol_b;
+}
+
 // squared distance between two boxes (0 when they overlap)
 __device__ __forceinline__ double box_dist2(const double* alo, const double* ahi, const double* blo,
                                             const double* bhi) {
@@ -215,32 +241,26 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
         Acc<T> A;
         A.zero();
         // ---------------- face samples ----------------
+        // (mixed path: FP32 pre-test, then the exact FP64 cast and decisions)
+        const bool want_alpha = dx != nullptr;
+        V3<double> dx0 = {0, 0, 0}, dx1 = {0, 0, 0}, dx2 = {0, 0, 0};
+        if (want_alpha) { dx0 = ld3(dx, Tt[0]); dx1 = ld3(dx, Tt[1]); dx2 = ld3(dx, Tt[2]); }
         {
             const V3<double> xs = interp(beta_k, x0, x1, x2);
             const V3<float> xs_rel = tof(xs - x0);
             const V3<float> ns_f = tof(ns);
-            const double ell = sqrt(rmin(dot(x1 - x0, x1 - x0), rmin(dot(x2 - x1, x2 - x1), dot(x0 - x2, x0 - x2))));
-            const float g_fp64_below = (float)(1e-2 * ell);
+            const double ds_face = want_alpha ? dot(ns, interp(beta_k, dx0, dx1, dx2)) : 0.0;
             const int32_t* Lf = C.face + t * C.cap_f;
             for (int it = lane; it < nf * NK; it += 32) {
                 const int32_t m = Lf[it / NK];
                 const int32_t* M = S.mtri + 3 * (int64_t)m;
                 const V3<double> y0 = ld3(xm, M[0]), y1 = ld3(xm, M[1]), y2 = ld3(xm, M[2]);
                 ++cnt_eval;
+                if (sizeof(T) == 4 &&
+                    !face_maybe(xs_rel, ns_f, tof(y0 - x0), tof(y1 - x0), tof(y2 - x0), (float)eps_max))
+                    continue;
                 double g, bm[3];
-                bool ok;
-                if (sizeof(T) == 4 && MODE == MODE_EVAL) {
-                    float gf, bmf[3];
-                    ok = face_geom<float>(xs_rel, ns_f, tof(y0 - x0), tof(y1 - x0), tof(y2 - x0), gf, bmf);
-                    if (ok && gf < g_fp64_below) {
-                        ok = face_geom<double>(xs, ns, y0, y1, y2, g, bm);
-                    } else {
-                        g = gf; bm[0] = bmf[0]; bm[1] = bmf[1]; bm[2] = bmf[2];
-                    }
-                } else {
-                    ok = face_geom<double>(xs, ns, y0, y1, y2, g, bm);
-                }
-                if (!ok) continue;
+                if (!face_geom<double>(xs, ns, y0, y1, y2, g, bm)) continue;
                 double eps = eps_max;
                 const double* mb = S.mrest_box + 6 * (int64_t)m;
                 if (!rest_far(sb, sb + 3, mb, mb + 3, eps_max)) {
@@ -253,13 +273,10 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 if (!(g < eps)) continue;
                 const double gamma = hermite(min3(bm), P.delta_T);
                 ++cnt_f;
-                if (MODE == MODE_EVAL) {
-                    sample_add<T>(A, P.kappa, omega * As, gamma, g, eps, beta_k);
-                } else {
-                    const V3<double> dsv = interp(beta_k, ld3(dx, Tt[0]), ld3(dx, Tt[1]), ld3(dx, Tt[2]));
-                    const double ds = dot(ns, dsv);
+                if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa, omega * As, gamma, g, eps, beta_k);
+                if (want_alpha) {
                     const double dm = dxm ? dot(ns, interp(bm, ld3(dxm, M[0]), ld3(dxm, M[1]), ld3(dxm, M[2]))) : 0.0;
-                    const double dg = dm - ds;
+                    const double dg = dm - ds_face;
                     if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
                 }
             }
@@ -314,10 +331,9 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 if (!(g < eps)) continue;
                 ++cnt_e;
                 const double gamma = hermite(eta, P.delta_e) * hermite(1.0 - eta, P.delta_e);
-                if (MODE == MODE_EVAL) {
-                    sample_add<T>(A, P.kappa_edge, 0.5 * ell, gamma, g, eps, bsk);
-                } else {
-                    const double ds = dot(ns, interp(bsk, ld3(dx, Tt[0]), ld3(dx, Tt[1]), ld3(dx, Tt[2])));
+                if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa_edge, 0.5 * ell, gamma, g, eps, bsk);
+                if (want_alpha) {
+                    const double ds = dot(ns, interp(bsk, dx0, dx1, dx2));
                     const double dm = dxm ? dot(ns, (1.0 - eta) * ld3(dxm, ia) + eta * ld3(dxm, ib)) : 0.0;
                     const double dg = dm - ds;
                     if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
@@ -348,10 +364,9 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 }
                 if (!(g < eps)) continue;
                 ++cnt_p;
-                if (MODE == MODE_EVAL) {
-                    sample_add<T>(A, P.kappa_point, 1.0, 1.0, g, eps, bs);
-                } else {
-                    const double ds = dot(ns, interp(bs, ld3(dx, Tt[0]), ld3(dx, Tt[1]), ld3(dx, Tt[2])));
+                if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa_point, 1.0, 1.0, g, eps, bs);
+                if (want_alpha) {
+                    const double ds = dot(ns, interp(bs, dx0, dx1, dx2));
                     const double dm = dxm ? dot(ns, ld3(dxm, u)) : 0.0;
                     const double dg = dm - ds;
                     if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
@@ -374,7 +389,8 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 for (int q = 0; q < 6; ++q) triS[6 * t + q] = A.S[q];
                 triN[3 * t + 0] = (T)ns.x; triN[3 * t + 1] = (T)ns.y; triN[3 * t + 2] = (T)ns.z;
             }
-        } else {
+        }
+        if (want_alpha) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) A.amin = rmin(A.amin, shfl_x(A.amin, o));
             if (lane == 0 && A.amin < INFINITY)
@@ -516,20 +532,21 @@ cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out) {
 }
 
 cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* energy_dev,
-                         void* grad_dev, bool want_hess, long long* counters) {
+                         void* grad_dev, bool want_hess, long long* counters, const double* dx,
+                         const double* dxm, unsigned long long* alpha_bits) {
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
     {
         ProfScope ps(c.prof, c.stream, "samples");
         if (f32) {
             if (c.P.nk == 4)
-                GMCP_CUDA_TRY((launch_samples<4, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, nullptr, nullptr, nullptr)));
+                GMCP_CUDA_TRY((launch_samples<4, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits)));
             else
-                GMCP_CUDA_TRY((launch_samples<16, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, nullptr, nullptr, nullptr)));
+                GMCP_CUDA_TRY((launch_samples<16, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits)));
         } else {
             if (c.P.nk == 4)
-                GMCP_CUDA_TRY((launch_samples<4, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, nullptr, nullptr, nullptr)));
+                GMCP_CUDA_TRY((launch_samples<4, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits)));
             else
-                GMCP_CUDA_TRY((launch_samples<16, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, nullptr, nullptr, nullptr)));
+                GMCP_CUDA_TRY((launch_samples<16, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits)));
         }
     }
     const int B = 256;

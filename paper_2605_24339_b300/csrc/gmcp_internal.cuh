@@ -253,8 +253,11 @@ struct Ctx {
 cudaError_t bp_init_constants(const double* rule_l1l2);
 cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept);
 cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm);
+// ACCD over swept pairs; reuse_grid: the cells already hold the master
+// triangles at xm0 (static master, same call), so the swept grid equals them
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
-                        const double* dxm, unsigned long long* alpha_bits, long long* counters);
+                        const double* dxm, unsigned long long* alpha_bits, long long* counters,
+                        bool reuse_grid = false);
 // scan.cu
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
                                size_t tmp_n, cudaStream_t s);
@@ -263,8 +266,12 @@ size_t scan_tmp_size(int64_t n);
 cudaError_t run_candidates(Ctx& c, const double* x, const double* xm);
 // contact.cu
 cudaError_t contact_init_constants(const double* rule_l1l2);
+// contact_eval also bounds the step (Eq. ccd) along dx / dxm into alpha_bits
+// when dx is non-NULL
 cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* energy_dev,
-                         void* grad_dev, bool want_hess, long long* counters);
+                         void* grad_dev, bool want_hess, long long* counters,
+                         const double* dx = nullptr, const double* dxm = nullptr,
+                         unsigned long long* alpha_bits = nullptr);
 cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const double* dx,
                               const double* dxm, unsigned long long* alpha_bits);
 cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out);

@@ -187,3 +187,45 @@ def test_full_size_terrain_sampled_parity(B, oracle_mod):
         od = np.stack([Ob[(int(v), int(v))] for v in verts])
         assert rel(gd, od) < tol_h
         ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("moving", [False, True])
+def test_contact_pass_fused_matches_separate_and_oracle(B, oracle_mod, prec, moving):
+    sc, x = small_indent(n_quads=10, subdiv=3, press=0.1e-3, L=2, seed=4)
+    ctx = B.Context(sc, precision=prec)
+    O = oracle_mod.Scene(sc)
+    rng = np.random.default_rng(9)
+    dx = np.zeros_like(x)
+    dx[:, 2] = -(1e-5 + 2e-5 * rng.random(x.shape[0]))
+    dx[:, :2] = 2e-6 * rng.normal(size=(x.shape[0], 2))
+    xm1 = sc.Y0 + np.array([0.0, 0.0, 1e-5]) if moving else None
+    r = ctx.contact_pass(x, sc.Y0, dx, xm1)
+    e = ctx.barrier_eval(x, sc.Y0)
+    c = ctx.ccd_max_step(x, dx, sc.Y0, xm1)
+    # same broad phase, same kernels: bitwise equal to the separate calls
+    assert r["energy"] == e["energy"]
+    assert torch.equal(r["grad"], e["grad"])
+    assert torch.equal(r["hess"][2], e["hess"][2])
+    assert (r["alpha"], r["alpha_lin"], r["alpha_accd"]) == (c["alpha"], c["alpha_lin"], c["alpha_accd"])
+    # and against the oracle
+    o = O.contact(x, sc.Y0)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    assert r["energy"] == pytest.approx(o["energy"], rel=tol)
+    assert rel(r["grad"].cpu().numpy(), o["grad"]) < tol
+    a, al, aa = O.ccd_max_step(x, dx, sc.Y0, xm1)
+    assert r["alpha_accd"] == aa
+    assert r["alpha"] <= a and r["alpha"] == pytest.approx(a, rel=1e-9)
+    if np.isfinite(al):
+        assert r["alpha_lin"] <= al and r["alpha_lin"] == pytest.approx(al, rel=1e-9)
+    ctx.close()
+
+
+def test_mixed_decisions_match_fp64(B):
+    """The mixed path makes every sample decision in FP64: the active-sample
+    counts equal the FP64 path's on the full-size terrain."""
+    sc = S.gel_on_terrain()
+    x = S.drape_on_master(sc, 0.15e-3)
+    c64 = B.Context(sc, precision="fp64").barrier_eval(x, sc.Y0, hess=False)["counts"]
+    c32 = B.Context(sc, precision="mixed").barrier_eval(x, sc.Y0, hess=False)["counts"]
+    assert (c32["face"], c32["edge"], c32["point"]) == (c64["face"], c64["edge"], c64["point"])
