@@ -101,8 +101,15 @@ __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b
 
 }  // namespace
 
+cudaError_t grow_candidates(Ctx& c, int32_t need_f, int32_t need_e, int32_t need_p);
+
 // Broad phase with automatic regrowth of the per-triangle capacities.
-cudaError_t run_candidates(Ctx& c, const double* x, const double* xm) {
+cudaError_t run_candidates(Ctx& c, const double* x, const double* xm, bool lazy) {
+    if (lazy) {
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 12, 0, 4 * sizeof(int32_t), c.stream));
+        GMCP_CUDA_TRY(bp_build_grid(c, xm, nullptr, false, true));
+        return bp_query_contact(c, x, xm);
+    }
     for (int attempt = 0; attempt < 6; ++attempt) {
         GMCP_CUDA_TRY(bp_build_grid(c, xm, nullptr, false));
         GMCP_CUDA_TRY(bp_query_contact(c, x, xm));
@@ -110,19 +117,24 @@ cudaError_t run_candidates(Ctx& c, const double* x, const double* xm) {
         GMCP_CUDA_TRY(cudaMemcpyAsync(ov, c.misc_i32.p, sizeof(ov), cudaMemcpyDeviceToHost, c.stream));
         GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
         if (ov[1] == 0 && ov[2] == 0 && ov[3] == 0) return cudaSuccess;
-        auto grow = [](int32_t cap, int32_t need) {
-            int32_t v = cap;
-            while (v < need) v *= 2;
-            return v;
-        };
-        c.cap_f = grow(c.cap_f, ov[1]);
-        c.cap_e = grow(c.cap_e, ov[2]);
-        c.cap_p = grow(c.cap_p, ov[3]);
-        GMCP_CUDA_TRY(c.cand_face.ensure((size_t)c.ns * c.cap_f + 1));
-        GMCP_CUDA_TRY(c.cand_edge.ensure((size_t)c.ns * c.cap_e + 1));
-        GMCP_CUDA_TRY(c.cand_point.ensure((size_t)c.ns * c.cap_p + 1));
+        GMCP_CUDA_TRY(grow_candidates(c, ov[1], ov[2], ov[3]));
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t grow_candidates(Ctx& c, int32_t need_f, int32_t need_e, int32_t need_p) {
+    auto grow = [](int32_t cap, int32_t need) {
+        int32_t v = cap;
+        while (v < need) v *= 2;
+        return v;
+    };
+    c.cap_f = grow(c.cap_f, need_f);
+    c.cap_e = grow(c.cap_e, need_e);
+    c.cap_p = grow(c.cap_p, need_p);
+    GMCP_CUDA_TRY(c.cand_face.ensure((size_t)c.ns * c.cap_f + 1));
+    GMCP_CUDA_TRY(c.cand_edge.ensure((size_t)c.ns * c.cap_e + 1));
+    GMCP_CUDA_TRY(c.cand_point.ensure((size_t)c.ns * c.cap_p + 1));
+    return cudaSuccess;
 }
 
 }  // namespace gmcp
@@ -633,6 +645,10 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
     Ctx& c = ctx->c;
     if (!x_dev || (!xm0_dev && c.nmv > 0)) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_contact_pass: NULL positions");
     API_CK(ctx, cudaSetDevice(c.device));
+    const bool want_alpha = dx_dev && (alpha_host || info);
+    // a call that returns host values synchronises once at the end; it then
+    // also checks the capacity flags and redoes the pass after growing
+    const bool lazy = energy_host || counts || want_alpha;
     const double* dxm = nullptr;
     if (dx_dev && xm1_dev) {
         API_CK(ctx, c.dxm.ensure(3 * (size_t)c.nmv + 3));
@@ -643,35 +659,46 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
         }
         dxm = c.dxm.p;
     }
-    if (dx_dev) {
-        const unsigned long long init[2] = {0x7FF0000000000000ULL, 0x3FF0000000000000ULL};
-        API_CK(ctx, cudaMemcpyAsync(c.u64_tmp.p, init, sizeof(init), cudaMemcpyHostToDevice, c.stream));
-        API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
-    }
-    API_CK(ctx, run_candidates(c, x_dev, xm0_dev));
-    long long* ctr = nullptr;
-    if (counts) {
-        API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
-        ctr = c.i64_tmp.p;
-    }
     double* edev = energy_dev;
     if (energy_host && !energy_dev) edev = c.scal.p;
-    API_CK(ctx, contact_eval(c, x_dev, xm0_dev, edev, grad_dev, hess != nullptr, ctr, dx_dev, dxm,
-                             dx_dev ? c.u64_tmp.p : nullptr));
-    if (dx_dev)
-        API_CK(ctx, bp_ccd_accd(c, x_dev, dx_dev, xm0_dev, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8, true));
-    const bool want_alpha = dx_dev && (alpha_host || info);
-    unsigned long long bits[2];
-    long long ctr_ccd[4];
-    if (energy_host)
-        API_CK(ctx, cudaMemcpyAsync(c.h_scalars, edev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-    if (counts)
-        API_CK(ctx, cudaMemcpyAsync(c.h_counts, c.i64_tmp.p, 4 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
-    if (want_alpha) {
-        API_CK(ctx, cudaMemcpyAsync(bits, c.u64_tmp.p, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
-        API_CK(ctx, cudaMemcpyAsync(ctr_ccd, c.i64_tmp.p + 8, sizeof(ctr_ccd), cudaMemcpyDeviceToHost, c.stream));
+    unsigned long long bits[2] = {0, 0};
+    long long ctr_ccd[4] = {0, 0, 0, 0};
+    for (int attempt = 0;; ++attempt) {
+        if (attempt >= 6) return fail_ctx(ctx, IPC_ERR_CAPACITY, "ipc_contact_pass: capacities did not settle");
+        if (dx_dev) {
+            const unsigned long long init[2] = {0x7FF0000000000000ULL, 0x3FF0000000000000ULL};
+            API_CK(ctx, cudaMemcpyAsync(c.u64_tmp.p, init, sizeof(init), cudaMemcpyHostToDevice, c.stream));
+            API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
+        }
+        API_CK(ctx, run_candidates(c, x_dev, xm0_dev, lazy));
+        long long* ctr = nullptr;
+        if (counts) {
+            API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
+            ctr = c.i64_tmp.p;
+        }
+        API_CK(ctx, contact_eval(c, x_dev, xm0_dev, edev, grad_dev, hess != nullptr, ctr, dx_dev, dxm,
+                                 dx_dev ? c.u64_tmp.p : nullptr));
+        if (dx_dev)
+            API_CK(ctx, bp_ccd_accd(c, x_dev, dx_dev, xm0_dev, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8,
+                                    true, lazy));
+        if (!lazy) break;
+        if (energy_host)
+            API_CK(ctx, cudaMemcpyAsync(c.h_scalars, edev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+        if (counts)
+            API_CK(ctx, cudaMemcpyAsync(c.h_counts, c.i64_tmp.p, 4 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+        if (want_alpha) {
+            API_CK(ctx, cudaMemcpyAsync(bits, c.u64_tmp.p, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
+            API_CK(ctx, cudaMemcpyAsync(ctr_ccd, c.i64_tmp.p + 8, sizeof(ctr_ccd), cudaMemcpyDeviceToHost, c.stream));
+        }
+        int32_t flags[16];
+        API_CK(ctx, cudaMemcpyAsync(flags, c.misc_i32.p, sizeof(flags), cudaMemcpyDeviceToHost, c.stream));
+        API_CK(ctx, cudaStreamSynchronize(c.stream));
+        const bool cand_over = flags[1] || flags[2] || flags[3];
+        const bool grid_over = flags[12] != 0;
+        if (!cand_over && !grid_over) break;
+        if (cand_over) API_CK(ctx, grow_candidates(c, flags[1], flags[2], flags[3]));
+        if (grid_over) API_CK(ctx, c.cell_ent.ensure(2 * c.cell_ent.n));
     }
-    if (energy_host || counts || want_alpha) API_CK(ctx, cudaStreamSynchronize(c.stream));
     if (energy_host) *energy_host = c.h_scalars[0];
     if (counts) {
         counts->face = c.h_counts[0]; counts->edge = c.h_counts[1]; counts->point = c.h_counts[2];

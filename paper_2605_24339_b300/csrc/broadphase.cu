@@ -22,6 +22,7 @@
 //   point (slave tri, master vertex): slave vertex box vs vertex grown by dhat
 // Edges and vertices are found through the master triangle that owns them
 // (the lowest-numbered adjacent triangle), whose box contains theirs.
+#include <algorithm>
 #include <cfloat>
 #include <cstring>
 #include <mutex>
@@ -94,7 +95,7 @@ __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
 
 __global__ void k_mtri_fill(SceneView S, const double* __restrict__ mbox,
                             const int32_t* __restrict__ start, int32_t* __restrict__ cursor,
-                            int32_t* __restrict__ ent) {
+                            int32_t* __restrict__ ent, int64_t cap, int32_t* __restrict__ overflow) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int e = S.mtri_env[m];
@@ -106,7 +107,8 @@ __global__ void k_mtri_fill(SceneView S, const double* __restrict__ mbox,
             for (int ix = a.x; ix <= b.x; ++ix) {
                 int64_t c = cell_id(S, e, ix, iy, iz);
                 int pos = start[c] + atomicAdd(&cursor[c], 1);
-                ent[pos] = (int32_t)m;
+                if (pos < cap) ent[pos] = (int32_t)m;
+                else atomicMax(overflow, 1);
             }
 }
 
@@ -679,7 +681,7 @@ cudaError_t bp_init_constants(const double* rule_l1l2) {
     return cudaMemcpyToSymbol(c_rule, rule_l1l2, sizeof(double) * 2 * 16 * 3);
 }
 
-cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept) {
+cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept, bool lazy) {
     ProfScope ps(c.prof, c.stream, "grid");
     SceneView S = c.view();
     cudaStream_t s = c.stream;
@@ -697,15 +699,22 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     }
     GMCP_CUDA_TRY(exclusive_scan_i32(c.cell_cnt.p, c.cell_start.p, c.n_cells, c.scan_tmp.p,
                                      c.scan_tmp.n, s));
-    // read the total number of (cell, triangle) entries to size the entries
-    int32_t total = 0;
-    GMCP_CUDA_TRY(cudaMemcpyAsync(&total, c.cell_start.p + c.n_cells, sizeof(int32_t),
-                                  cudaMemcpyDeviceToHost, s));
-    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-    GMCP_CUDA_TRY(c.cell_ent.ensure((size_t)total + 1));
+    if (lazy) {
+        // A triangle whose rest extent is at most one cell spans at most 3
+        // cells per axis in any rigid pose; the fill flags any overflow, which
+        // the caller checks when it synchronises and then redoes the pass.
+        GMCP_CUDA_TRY(c.cell_ent.ensure(std::max<size_t>(27 * (size_t)c.nmt + 1, c.cell_ent.n)));
+    } else {
+        int32_t total = 0;
+        GMCP_CUDA_TRY(cudaMemcpyAsync(&total, c.cell_start.p + c.n_cells, sizeof(int32_t),
+                                      cudaMemcpyDeviceToHost, s));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+        GMCP_CUDA_TRY(c.cell_ent.ensure((size_t)total + 1));
+    }
     GMCP_CUDA_TRY(cudaMemsetAsync(c.cell_cnt.p, 0, sizeof(int32_t) * (c.n_cells + 1), s));
     if (c.nmt > 0) {
-        k_mtri_fill<<<g, B, 0, s>>>(S, c.mbox.p, c.cell_start.p, c.cell_cnt.p, c.cell_ent.p);
+        k_mtri_fill<<<g, B, 0, s>>>(S, c.mbox.p, c.cell_start.p, c.cell_cnt.p, c.cell_ent.p,
+                                    (int64_t)c.cell_ent.n, c.misc_i32.p + 12);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -758,8 +767,8 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
 
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
                         const double* dxm, unsigned long long* alpha_bits, long long* counters,
-                        bool reuse_grid) {
-    if (!(reuse_grid && dxm == nullptr)) GMCP_CUDA_TRY(bp_build_grid(c, xm0, dxm, true));
+                        bool reuse_grid, bool lazy) {
+    if (!(reuse_grid && dxm == nullptr)) GMCP_CUDA_TRY(bp_build_grid(c, xm0, dxm, true, lazy));
     ProfScope ps(c.prof, c.stream, "accd");
     if (c.ns == 0) return cudaSuccess;
     SceneView S = c.view();

@@ -251,19 +251,22 @@ struct Ctx {
 // ------------------------------------------------------------------------
 // broadphase.cu
 cudaError_t bp_init_constants(const double* rule_l1l2);
-cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept);
+// lazy: size the entries for the worst rigid pose instead of reading the
+// exact total back (no synchronisation); overflow sets misc_i32[12]
+cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept, bool lazy = false);
 cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm);
 // ACCD over swept pairs; reuse_grid: the cells already hold the master
 // triangles at xm0 (static master, same call), so the swept grid equals them
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
                         const double* dxm, unsigned long long* alpha_bits, long long* counters,
-                        bool reuse_grid = false);
+                        bool reuse_grid = false, bool lazy = false);
 // scan.cu
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
                                size_t tmp_n, cudaStream_t s);
 size_t scan_tmp_size(int64_t n);
 // api.cu
-cudaError_t run_candidates(Ctx& c, const double* x, const double* xm);
+// lazy: no synchronisation; the caller must check misc_i32[1..3] and [12]
+cudaError_t run_candidates(Ctx& c, const double* x, const double* xm, bool lazy = false);
 // contact.cu
 cudaError_t contact_init_constants(const double* rule_l1l2);
 // contact_eval also bounds the step (Eq. ccd) along dx / dxm into alpha_bits
