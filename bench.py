@@ -38,6 +38,10 @@ METRIC = "contact samples/s (barrier E+grad+H+CCD)"
 UNIT = "samples/s"
 WORKLOAD = "gel_on_terrain 256x256 pad (131,072 slave tris x 16 samples) vs 199,712-tri Perlin terrain, pressed 0.15 mm"
 CROP_HALF_WIDTH = 2.0e-3
+# DRAM bytes (read + write) of one k_samples launch on this workload, from the
+# ncu capture summarised in profiles/k_samples_gel_on_terrain.md; null when
+# the kernel changes and the capture is not yet redone
+K_SAMPLES_DRAM_BYTES_PER_LAUNCH = 611584
 
 
 def load_peaks():
@@ -146,30 +150,6 @@ def samples_per_pass(ctx, x, xm, nk):
     return ctx.ns * nk + 2 * c["edge"] + c["point"], c
 
 
-def algorithmic_bytes(ctx, sc, x, cand, precision):
-    """Bytes each section must move at least once (unique inputs, outputs),
-    computed from the candidate lists of the benchmarked state."""
-    face = ctx.candidate_pairs(0)
-    edge = ctx.candidate_pairs(1)
-    point = ctx.candidate_pairs(2)
-    act = np.unique(np.concatenate([face[:, 0], edge[:, 0], point[:, 0]]))
-    sv = np.unique(sc.stris[act])
-    mt = np.unique(face[:, 1])
-    me = np.unique(edge[:, 1])
-    mv = np.unique(np.concatenate([sc.mtris[mt].ravel(), point[:, 1]]))
-    n_pairs = face.shape[0] + edge.shape[0] + point.shape[0]
-    out_per_tri = 8 + (4 if precision == "mixed" else 8) * 12
-    samples = (48 * sv.size + 12 * act.size + 16 * act.size + 4 * n_pairs + 24 * mv.size
-               + 12 * mt.size + 8 * me.size + 48 * mt.size + out_per_tri * act.size)
-    ns = sc.stris.shape[0]
-    nsv = np.unique(sc.stris).size
-    query = 24 * nsv + 12 * ns + 16 * ns + 4 * n_pairs + 48 * sc.mtris.shape[0]
-    gsz = 4 if precision == "mixed" else 8
-    gather_grad = 3 * gsz * sc.X.shape[0] + (gsz * 6) * ns
-    return {"samples": samples, "query": query, "gather_grad": gather_grad,
-            "units": {"active_tris": int(act.size), "pairs": int(n_pairs)}}
-
-
 def run_ours(args):
     import torch
     from paper_2605_24339_b300 import binding
@@ -187,6 +167,7 @@ def run_ours(args):
                        dtype=torch.float32 if args.precision == "mixed" else torch.float64)
     e_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
     units, cand = samples_per_pass(ctx, x, xm, nk)
+    counts_once = ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=True)["counts"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -239,18 +220,23 @@ def run_ours(args):
     if rank != 0:
         return
     peaks, peak_kind = load_peaks()
-    ab = algorithmic_bytes(ctx, sc, x_np, cand, args.precision)
     sec_ms = {k: v["ms"] / max(v["calls"], 1) for k, v in prof.items()}
-    # dominant single-kernel section among those with a byte model
-    cand_secs = [s for s in ("samples", "query", "gather_grad") if s in sec_ms]
-    top = max(cand_secs, key=lambda s: sec_ms[s])
-    achieved = ab[top] / (sec_ms[top] / 1e3) / 1e9
-    n_launch_per_step = {"grid": 5, "query": 2, "samples": 1, "gather_grad": 1, "gather_hess": 1,
-                         "reduce": 2, "alpha_lin": 1, "accd": 2}
+    # Dominant kernel: k_samples ("samples" section, one launch per pass).
+    # Work model (per-unit figure of the contact pass): 160 FP32-equivalent
+    # flops per (sample, candidate) evaluation; units per launch = face
+    # (sample, candidate) pairs evaluated + 2 per edge candidate + 1 per point
+    # candidate.  Peak: FP32 CUDA-core rate from unit counts and the measured
+    # SM clock (148 SMs x 128 lanes x 2 flop x clock).
+    evals = counts_once["face_evaluated"] + 2 * cand["edge"] + cand["point"]
+    flops = 160.0 * evals
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (sec_ms["samples"] / 1e3) / 1e12
+    n_launch_per_step = {"grid": 6, "query": 2, "samples": 1, "gather_grad": 1, "gather_hess": 1,
+                         "reduce": 2, "accd": 2}
     launches = 0
     for k, v in prof.items():
-        per = n_launch_per_step.get(k, 1)
-        launches += per * v["calls"]
+        launches += n_launch_per_step.get(k, 1) * v["calls"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -264,10 +250,11 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_np.nbytes),
                 "d2h_bytes_per_step": 16},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved,
-                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "peak_source": peak_kind, "algorithmic_bytes": int(ab[top])},
+        "roofline": {"bound": "alu", "kernel": "k_samples", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": K_SAMPLES_DRAM_BYTES_PER_LAUNCH,
+                     "peak_source": "FP32 unit counts x measured SM clock",
+                     "work": {"flops_per_eval": 160, "evals_per_launch": int(evals)}},
         "sections_ms": {k: round(v, 4) for k, v in sec_ms.items()},
         "alpha": info["alpha"],
         "clocks": clk,
