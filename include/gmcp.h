@@ -124,11 +124,17 @@ typedef struct {
 } ipc_ccd_info;
 
 typedef struct {
-    int32_t newton_iters, pcg_iters_total, line_search_halvings;
-    double residual;       /* final ||G_free|| / max(||G_free(x~)||, floor) */
-    double alpha0;         /* CCD fraction admitted for the predictor */
-    double energy;
-    double ms_total;
+    int32_t newton_iters;          /* Newton iterations taken (solves) */
+    int32_t pcg_iters_total;       /* PCG iterations summed over the solves */
+    int32_t line_search_halvings;  /* halvings summed over the line searches */
+    double residual;       /* final ||G_free|| / max(||G_free(x~)||, floor), x~ the
+                              CCD-filtered plain predictor, floor = 1e-3 h^2 E lbar^2
+                              (lbar = cube root of the mean tet volume) */
+    double res0;           /* ||G_free(x~)|| (before the floor) */
+    double alpha0;         /* CCD fraction admitted for the Newton start */
+    double last_alpha;     /* step length of the last accepted line search */
+    double energy;         /* incremental potential at the final iterate */
+    double ms_total;       /* host wall time of the call */
 } ipc_step_stats;
 
 /* ---------------------------------------------------------------------- */
@@ -217,12 +223,35 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
                             double* energy_host, void* grad_dev, ipc_bsr_view* hess,
                             double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts);
 
-/* One implicit-Euler time step (paper Sec. 2.1 problem statement): x_dev
- * [n_vert][3] holds x^t on entry and x^{t+1} on exit, v_dev the velocity
- * (Dirichlet vertices move to x + h v).  xm_next_dev: master at t+1 (NULL =
- * unchanged).  dx_pred_dev: a predicted displacement used as the Newton
- * start after CCD filtering (NULL = x + h v).  stats (host) may be NULL.
- * On IPC_ERR_INFEASIBLE / IPC_ERR_LINESEARCH x and v are restored. */
+/* One implicit-Euler time step (paper Sec. 2.1 problem statement): minimises
+ *   E(x) = 1/2 (x - xhat)^T M (x - xhat) + h^2 (Psi_NH(x) + Psi_GMCP(x)),
+ *   xhat = x^t + h v^t + h^2 gravity,
+ * over the free vertices by projected Newton.  Each iteration i evaluates
+ * the contact pass at x_i (Sec. 4.1-4.4) and freezes its samples (normal,
+ * barycentrics, weight, gamma, eps), so the contact term of the line search
+ * is sum kappa w gamma B(g + alpha dg) with the linearised gap change dg;
+ * the system H p = -G (H = M + h^2 (PSD elastic + contact), lumped mass,
+ * Dirichlet rows and columns eliminated) is solved by block-Jacobi PCG to
+ * pcg_rel_tol; the step starts at min(1, alpha_lin, alpha_accd) (Sec. 4.5)
+ * and is halved until E_i(x + alpha p) <= E_i(x) + 1e-4 alpha G^T p (at most
+ * max_halvings times).  Stops when residual <= newton_tol (see
+ * ipc_step_stats).  Elasticity: compressible Neo-Hookean,
+ * mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2 per tet with its 9x9
+ * dP/dF projected onto the PSD cone.
+ *  x_dev [n_vert][3] (device, FP64) holds x^t on entry and x^{t+1} on exit;
+ *  v_dev the velocity, updated to (x^{t+1} - x^t) / h; Dirichlet vertices
+ *  are moved to x + h v (their motion must be admissible);
+ *  xm_next_dev: master at t+1 (NULL = unchanged); the context keeps the
+ *  current master, which starts at m_rest;
+ *  dx_pred_dev: a predicted displacement; the Newton start is then
+ *  x^t + alpha0 dx_pred with alpha0 the CCD-admissible fraction (NULL: the
+ *  plain predictor x^t + h v^t);
+ *  stats (host) may be NULL.
+ * The first call builds the time-stepper state (tet data, mass, the global
+ * block pattern).  The call synchronises params.stream several times per
+ * iteration.  Returns IPC_ERR_NOT_CONVERGED after max_newton iterations
+ * (x and v then hold the last iterate); on IPC_ERR_INFEASIBLE and
+ * IPC_ERR_LINESEARCH x and v are left at x^t, v^t. */
 ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
                            const double* dx_pred_dev, ipc_step_stats* stats);
 

@@ -73,7 +73,12 @@ class CcdInfo(C.Structure):
 class StepStats(C.Structure):
     _fields_ = [("newton_iters", C.c_int32), ("pcg_iters_total", C.c_int32),
                 ("line_search_halvings", C.c_int32), ("residual", C.c_double),
-                ("alpha0", C.c_double), ("energy", C.c_double), ("ms_total", C.c_double)]
+                ("res0", C.c_double), ("alpha0", C.c_double), ("last_alpha", C.c_double),
+                ("energy", C.c_double), ("ms_total", C.c_double)]
+
+
+# ipc_status values a time step may end with without a programming error
+STEP_INFEASIBLE, STEP_NOT_CONVERGED, STEP_LINESEARCH = 4, 6, 7
 
 
 _lib = None
@@ -343,10 +348,19 @@ class Context:
         return out
 
     def newton_step(self, x, v, xm_next=None, dx_pred=None):
-        """In-place implicit-Euler step on x, v (torch FP64 CUDA tensors)."""
+        """In-place implicit-Euler step on x, v (torch FP64 CUDA tensors [n,3]).
+
+        Returns the step statistics with ``status`` (0, or STEP_INFEASIBLE,
+        STEP_NOT_CONVERGED, STEP_LINESEARCH); other failures raise."""
+        t = self.torch
+        for a in (x, v):
+            if not (isinstance(a, t.Tensor) and a.is_cuda and a.dtype == t.float64 and a.is_contiguous()):
+                raise TypeError("x and v must be contiguous FP64 CUDA tensors")
         st = StepStats()
-        self._check(lib().ipc_newton_step(self.h, _ptr(x), _ptr(v), _ptr(self._as(xm_next)),
-                                          _ptr(self._as(dx_pred)), C.byref(st)))
-        return dict(newton_iters=st.newton_iters, pcg_iters=st.pcg_iters_total,
-                    halvings=st.line_search_halvings, residual=st.residual, alpha0=st.alpha0,
-                    energy=st.energy, ms=st.ms_total)
+        r = lib().ipc_newton_step(self.h, _ptr(x), _ptr(v), _ptr(self._as(xm_next)),
+                                  _ptr(self._as(dx_pred)), C.byref(st))
+        if r not in (0, STEP_INFEASIBLE, STEP_NOT_CONVERGED, STEP_LINESEARCH):
+            self._check(r)
+        return dict(status=r, newton_iters=st.newton_iters, pcg_iters=st.pcg_iters_total,
+                    halvings=st.line_search_halvings, residual=st.residual, res0=st.res0,
+                    alpha0=st.alpha0, last_alpha=st.last_alpha, energy=st.energy, ms=st.ms_total)

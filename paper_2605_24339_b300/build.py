@@ -21,7 +21,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # clipping) are not weight-continuous and so must decide exactly as the
 # CPU oracle does on degenerate (coincident) meshes
 NO_FMA = {"broadphase.cu", "contact.cu"}
-SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu"]
+SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu", "newton.cu"]
 
 
 def nvcc() -> str:
@@ -56,7 +56,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
                 print(" ".join(cmd), flush=True)
             subprocess.check_call(cmd)
     if force or _stale(LIB, objs):
-        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart"])
+        subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart",
+                               "-Xlinker", "--no-undefined"])
         os.replace(LIB + ".tmp", LIB)
     return LIB
 

@@ -3,6 +3,7 @@
 // entry points that queue the contact-pass kernels on the caller's stream.
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -134,6 +135,197 @@ cudaError_t grow_candidates(Ctx& c, int32_t need_f, int32_t need_e, int32_t need
     GMCP_CUDA_TRY(c.cand_face.ensure((size_t)c.ns * c.cap_f + 1));
     GMCP_CUDA_TRY(c.cand_edge.ensure((size_t)c.ns * c.cap_e + 1));
     GMCP_CUDA_TRY(c.cand_point.ensure((size_t)c.ns * c.cap_p + 1));
+    return cudaSuccess;
+}
+
+}  // namespace gmcp
+
+// ===========================================================================
+// implicit-Euler time step (paper Sec. 2.1 problem statement; contact
+// potential of Sec. 4.2 with the frozen linearisation of each iterate; step
+// bound of Sec. 4.5)
+// ===========================================================================
+namespace gmcp {
+namespace {
+
+// alpha = min(1, alpha_lin, alpha_accd) for x -> x + alpha dx with the master
+// moving by dxm (NULL = static).  candidates_current: the broad phase of
+// (x, xm0) is the last one run on the context (then it is not repeated and,
+// for a static master, the additive CCD reuses its grid).
+cudaError_t ccd_bound(Ctx& c, const double* x, const double* dx, const double* xm0, const double* dxm,
+                      bool candidates_current, double* alpha) {
+    const unsigned long long init[2] = {0x7FF0000000000000ULL, 0x3FF0000000000000ULL};
+    GMCP_CUDA_TRY(cudaMemcpyAsync(c.u64_tmp.p, init, sizeof(init), cudaMemcpyHostToDevice, c.stream));
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
+    if (!candidates_current) GMCP_CUDA_TRY(run_candidates(c, x, xm0));
+    GMCP_CUDA_TRY(contact_alpha_lin(c, x, xm0, dx, dxm, c.u64_tmp.p));
+    GMCP_CUDA_TRY(bp_ccd_accd(c, x, dx, xm0, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8, dxm == nullptr));
+    unsigned long long bits[2];
+    GMCP_CUDA_TRY(cudaMemcpyAsync(bits, c.u64_tmp.p, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
+    GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    double al, aa;
+    memcpy(&al, &bits[0], 8);
+    memcpy(&aa, &bits[1], 8);
+    if (al < INFINITY) al *= (1.0 - 1e-10);
+    *alpha = std::min(1.0, std::min(al, aa));
+    return cudaSuccess;
+}
+
+// largest k in [0, max_halv] batch: first j with finite elastic energy at
+// xi + (a 2^-j) dP; returns -1 if none up to max_halv
+cudaError_t first_feasible(Ctx& c, const double* xi, const double* dP, double a, int max_halv, int* j_out,
+                           double* a_out) {
+    NewtonState& N = *c.newton;
+    double* hb = c.h_scalars;
+    for (int base = 0; base <= max_halv; base += 8) {
+        const int na = std::min(8, max_halv - base + 1);
+        double al[8];
+        for (int j = 0; j < na; ++j) al[j] = std::ldexp(a, -(base + j));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(N.alphas.p, al, sizeof(double) * na, cudaMemcpyHostToDevice, c.stream));
+        GMCP_CUDA_TRY(nh_energy_multi(c, xi, dP, N.alphas.p, na, N.scal.p + 48));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(hb, N.scal.p + 48, sizeof(double) * na, cudaMemcpyDeviceToHost, c.stream));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        for (int j = 0; j < na; ++j)
+            if (std::isfinite(hb[j])) { *j_out = base + j; *a_out = al[j]; return cudaSuccess; }
+    }
+    *j_out = -1;
+    return cudaSuccess;
+}
+
+// start point: Dirichlet vertices at xhat (their motion must be admissible),
+// free vertices moved toward P by the CCD-limited fraction, halved until
+// every tet keeps J > 0.  x0 may alias neither x nor P.  ok = false: none.
+cudaError_t start_point(Ctx& c, const double* x, const double* P, double* x0, double* alpha0, bool* ok) {
+    NewtonState& N = *c.newton;
+    const int64_t n = 3 * c.nv;
+    *ok = false;
+    bool has_dir = false;
+    for (uint8_t d : c.h_dir) if (d) { has_dir = true; break; }
+    GMCP_CUDA_TRY(cudaMemcpyAsync(N.xi.p, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.stream));
+    if (has_dir) {
+        GMCP_CUDA_TRY(vec_dir_delta(c, x, N.xhat.p, N.dP.p));
+        double a;
+        GMCP_CUDA_TRY(ccd_bound(c, x, N.dP.p, N.xm.p, nullptr, false, &a));
+        if (a < 1.0) return cudaSuccess;
+        GMCP_CUDA_TRY(vec_set_dir(c, N.xhat.p, N.xi.p));
+        int j;
+        double aj;
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.dP.p, 0, sizeof(double) * n, c.stream));
+        GMCP_CUDA_TRY(first_feasible(c, N.xi.p, N.dP.p, 0.0, 0, &j, &aj));
+        if (j < 0) return cudaSuccess;
+    }
+    GMCP_CUDA_TRY(vec_free_delta(c, P, N.xi.p, N.dP.p));
+    double a;
+    GMCP_CUDA_TRY(ccd_bound(c, N.xi.p, N.dP.p, N.xm.p, nullptr, false, &a));
+    int j;
+    double aj;
+    GMCP_CUDA_TRY(first_feasible(c, N.xi.p, N.dP.p, a, c.prm.max_halvings, &j, &aj));
+    if (j < 0) return cudaSuccess;
+    GMCP_CUDA_TRY(vec_axpy(c, n, aj, N.xi.p, N.dP.p, x0));
+    *alpha0 = aj;
+    *ok = true;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// status: 0 converged, 3 infeasible, 5 not converged, 6 line search
+cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, const double* dx_pred,
+                       ipc_step_stats* st, int* status_out) {
+    NewtonState& N = *c.newton;
+    const int64_t n = 3 * c.nv;
+    cudaStream_t s = c.stream;
+    const double h = c.prm.h, h2 = h * h;
+    double* hb = c.h_scalars;
+    double* sc = N.scal.p;   // [56] Ec [57] Ee [58] E [59] |G|^2 [60] G.p
+    int status = 0;
+    GMCP_CUDA_TRY(cudaMemcpyAsync(N.xt.p, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    GMCP_CUDA_TRY(vec_xhat(c, x, v, N.xhat.p));
+    // master motion with the pad held at x^t
+    if (xm_next && c.nmv > 0) {
+        const int64_t m = 3 * c.nmv;
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.tmp.p, 0, sizeof(double) * n, s));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(N.dxm.p, xm_next, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+        GMCP_CUDA_TRY(vec_axpy(c, m, -1.0, N.dxm.p, N.xm.p, N.dxm.p));
+        double a;
+        GMCP_CUDA_TRY(ccd_bound(c, x, N.tmp.p, N.xm.p, N.dxm.p, false, &a));
+        if (a < 1.0) { *status_out = 3; return cudaSuccess; }
+        GMCP_CUDA_TRY(cudaMemcpyAsync(N.xm.p, xm_next, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+    }
+    // residual scale from the CCD-filtered plain predictor (reading R8)
+    double a0 = 0.0, gscale;
+    bool ok;
+    GMCP_CUDA_TRY(start_point(c, x, N.xhat.p, N.tmp.p, &a0, &ok));
+    if (!ok) { *status_out = 3; return cudaSuccess; }
+    GMCP_CUDA_TRY(assemble_system(c, N.tmp.p, false, sc + 56, sc + 57, sc + 58, sc + 59));
+    GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 59, sizeof(double), cudaMemcpyDeviceToHost, s));
+    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+    gscale = std::sqrt(hb[0]);
+    if (dx_pred) {
+        GMCP_CUDA_TRY(vec_axpy(c, n, 1.0, x, dx_pred, N.P.p));
+        GMCP_CUDA_TRY(start_point(c, x, N.P.p, N.tmp.p, &a0, &ok));
+        if (!ok) status = 3;
+    }
+    if (status == 0)
+        GMCP_CUDA_TRY(cudaMemcpyAsync(x, N.tmp.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    st->alpha0 = a0;
+    st->res0 = gscale;
+    // floor: force of a 1e-3 strain on one element, h^2 E lbar^2 1e-3
+    gscale = std::max(gscale, 1e-3 * h2 * c.prm.youngs * N.lbar * N.lbar);
+    for (int it = 0; status == 0; ++it) {
+        GMCP_CUDA_TRY(assemble_system(c, x, true, sc + 56, sc + 57, sc + 58, sc + 59));
+        int32_t bad = 0;
+        GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 56, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(&bad, N.bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (bad || !std::isfinite(hb[2])) { status = 3; break; }
+        st->energy = hb[2];
+        st->residual = std::sqrt(hb[3]) / gscale;
+        if (st->residual <= c.prm.newton_tol) break;
+        if (it >= c.prm.max_newton) { status = 5; break; }
+        st->newton_iters = it + 1;
+        int pit = 0;
+        GMCP_CUDA_TRY(vec_neg(c, n, N.G.p, N.tmp.p));
+        GMCP_CUDA_TRY(pcg_solve(c, N.tmp.p, N.dirn.p, c.prm.pcg_rel_tol, c.prm.max_pcg, &pit));
+        st->pcg_iters_total += pit;
+        GMCP_CUDA_TRY(vec_zero_dir(c, N.dirn.p));
+        GMCP_CUDA_TRY(dot_dev(c, N.G.p, N.dirn.p, n, sc + 60));
+        double al;
+        GMCP_CUDA_TRY(ccd_bound(c, x, N.dirn.p, N.xm.p, nullptr, true, &al));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(hb + 8, sc + 60, sizeof(double), cudaMemcpyDeviceToHost, s));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+        const double gp = hb[8];
+        const double c0 = 1e-4;
+        // backtracking on the frozen-linear energy: slot 0 is alpha = 0 (the
+        // reference), slots 1..7 the next halvings
+        bool accepted = false;
+        for (int hv0 = 0; hv0 <= c.prm.max_halvings && !accepted; hv0 += 7) {
+            const int nk = std::min(7, c.prm.max_halvings - hv0 + 1);
+            double als[8];
+            als[0] = 0.0;
+            for (int j = 0; j < nk; ++j) als[1 + j] = std::ldexp(al, -(hv0 + j));
+            GMCP_CUDA_TRY(cudaMemcpyAsync(N.alphas.p, als, sizeof(double) * (nk + 1), cudaMemcpyHostToDevice, s));
+            GMCP_CUDA_TRY(energy_batch(c, x, N.dirn.p, N.alphas.p, nk + 1, true, sc + 48));
+            GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 48, sizeof(double) * (nk + 1), cudaMemcpyDeviceToHost, s));
+            GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+            const double E0 = hb[0];
+            for (int j = 0; j < nk; ++j)
+                if (hb[1 + j] <= E0 + c0 * als[1 + j] * gp) {
+                    accepted = true;
+                    al = als[1 + j];
+                    st->last_alpha = al;
+                    st->line_search_halvings += hv0 + j;
+                    break;
+                }
+        }
+        if (!accepted) { status = 6; break; }
+        GMCP_CUDA_TRY(vec_axpy(c, n, al, x, N.dirn.p, x));
+    }
+    if (status == 0 || status == 5) GMCP_CUDA_TRY(vec_velocity(c, x, N.xt.p, v));
+    if (status != 0 && status != 5)
+        GMCP_CUDA_TRY(cudaMemcpyAsync(x, N.xt.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+    *status_out = status;
     return cudaSuccess;
 }
 
@@ -311,6 +503,8 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
     src_off.push_back((int32_t)blk.size());
     for (int64_t v = 0; v < nv; ++v) row[v + 1] += row[v];
     c.cb_nnzb = (int64_t)col.size();
+    c.h_cb_row = row;
+    c.h_cb_col = col;
 
     CK(c.stri.upload(sc->s_tris, 3 * ns, s));
     CK(c.mtri.upload(sc->m_tris, 3 * nmt, s));
@@ -472,6 +666,15 @@ ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx*
             CK(bp_init_constants(tab));
             CK(contact_init_constants(tab));
         }
+        if (c.nt > 0 && !scene->tets) throw Fail{IPC_ERR_ARG, "n_tet > 0 but tets is NULL"};
+        for (int64_t i = 0; i < 4 * c.nt; ++i)
+            if (scene->tets[i] < 0 || scene->tets[i] >= c.nv) throw Fail{IPC_ERR_ARG, "tets index out of range"};
+        if (c.nt >= ((int64_t)1 << 27)) throw Fail{IPC_ERR_ARG, "n_tet must be below 2^27"};
+        // kept for the time stepper, whose state is built on its first call
+        c.h_X.assign(scene->pad_rest, scene->pad_rest + 3 * c.nv);
+        if (c.nt > 0) c.h_tets.assign(scene->tets, scene->tets + 4 * c.nt);
+        if (scene->dirichlet) c.h_dir.assign(scene->dirichlet, scene->dirichlet + c.nv);
+        else c.h_dir.assign(c.nv, 0);
         build_topology(c, scene);
         alloc_call_buffers(c);
         CK(cudaStreamSynchronize(c.stream));
@@ -755,8 +958,29 @@ ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* n
 ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
                            const double* dx_pred_dev, ipc_step_stats* stats) {
     if (!ctx) return IPC_ERR_ARG;
-    (void)x_dev; (void)v_dev; (void)xm_next_dev; (void)dx_pred_dev; (void)stats;
-    return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: the time stepper is not part of this build yet");
+    Ctx& c = ctx->c;
+    if (!x_dev || !v_dev) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: NULL x or v");
+    if (c.nt == 0) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: the scene has no tets");
+    if (!(c.prm.h > 0.0) || !(c.prm.density > 0.0) || !(c.prm.youngs > 0.0) ||
+        !(c.prm.poisson > -1.0 && c.prm.poisson < 0.5) || c.prm.max_newton < 0 || c.prm.max_pcg < 1 ||
+        c.prm.max_halvings < 0)
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: invalid h, material or iteration limits");
+    API_CK(ctx, cudaSetDevice(c.device));
+    const auto t_start = std::chrono::steady_clock::now();
+    API_CK(ctx, newton_setup(c));
+    int status = 0;
+    ipc_step_stats st{};
+    const cudaError_t e = newton_run(c, x_dev, v_dev, xm_next_dev, dx_pred_dev, &st, &status);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ipc_newton_step");
+    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = st;
+    switch (status) {
+        case 0: return IPC_OK;
+        case 3: return fail_ctx(ctx, IPC_ERR_INFEASIBLE, "ipc_newton_step: infeasible (master motion blocked, "
+                                                         "inverted tet or no admissible start)");
+        case 5: return fail_ctx(ctx, IPC_ERR_NOT_CONVERGED, "ipc_newton_step: max_newton reached");
+        default: return fail_ctx(ctx, IPC_ERR_LINESEARCH, "ipc_newton_step: line search exhausted max_halvings");
+    }
 }
 
 }  // extern "C"

@@ -37,6 +37,16 @@ namespace {
 
 constexpr int MODE_EVAL = 0;
 constexpr int MODE_ALPHA = 1;
+constexpr int MODE_LAGGED = 2;
+
+// frozen-linear energies of MODE_LAGGED: per active sample, kappa w gamma
+// B(g + a_j dg) for up to 8 step sizes a_j along the direction dx
+struct LagArgs {
+    const double* alphas = nullptr;
+    int na = 0;
+    double* triE8 = nullptr;   // [8][ns]
+    int64_t ns = 0;
+};
 
 template <class R>
 struct V3 { R x, y, z; };
@@ -204,6 +214,25 @@ __device__ __forceinline__ void sample_add(Acc<T>& A, double kq, double w, doubl
 
 template <class T> __device__ __forceinline__ T shfl_x(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 
+// one sample of the frozen-linear potential (lagged energy of the line
+// search, reading R6): g~ = g + a dg; +inf once g~ <= 0, 0 from eps on
+__device__ __forceinline__ void lag_add(double* E8, const double* al, int na, double coef, double g,
+                                        double eps, double dg) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        if (j >= na) break;
+        const double gt = g + al[j] * dg;
+        double e = 0.0;
+        if (!(gt > 0.0)) {
+            e = INFINITY;
+        } else if (gt < eps) {
+            const double d = gt - eps, L = log(gt / eps);
+            e = coef * (-d * d * L);
+        }
+        E8[j] += e;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the sample kernel
 // ---------------------------------------------------------------------------
@@ -213,7 +242,7 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
           const double* __restrict__ xm, double* __restrict__ triE, T* __restrict__ triG,
           T* __restrict__ triS, T* __restrict__ triN, long long* counters,
           const double* __restrict__ dx, const double* __restrict__ dxm,
-          unsigned long long* alpha_bits) {
+          unsigned long long* alpha_bits, LagArgs LG) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
@@ -223,6 +252,9 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
     long long cnt_f = 0, cnt_e = 0, cnt_p = 0, cnt_eval = 0;
     double beta_k[3];
     for (int q = 0; q < 3; ++q) beta_k[q] = c_rule[P.L - 1][lane % NK][q];
+    double al8[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) al8[j] = (MODE == MODE_LAGGED && j < LG.na) ? LG.alphas[j] : 0.0;
     for (int i = warp; i < n_active; i += nwarps) {
         const int64_t t = C.active[i];
         const int32_t* Tt = S.stri + 3 * t;
@@ -240,16 +272,20 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
         const int nf = min(cnt[0], C.cap_f), ne = min(cnt[1], C.cap_e), np = min(cnt[2], C.cap_p);
         Acc<T> A;
         A.zero();
+        double E8[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) E8[j] = 0.0;
         // ---------------- face samples ----------------
         // (mixed path: FP32 pre-test, then the exact FP64 cast and decisions)
-        const bool want_alpha = dx != nullptr;
+        const bool want_dg = dx != nullptr;
+        const bool want_alpha = MODE != MODE_LAGGED && want_dg;
         V3<double> dx0 = {0, 0, 0}, dx1 = {0, 0, 0}, dx2 = {0, 0, 0};
-        if (want_alpha) { dx0 = ld3(dx, Tt[0]); dx1 = ld3(dx, Tt[1]); dx2 = ld3(dx, Tt[2]); }
+        if (want_dg) { dx0 = ld3(dx, Tt[0]); dx1 = ld3(dx, Tt[1]); dx2 = ld3(dx, Tt[2]); }
         {
             const V3<double> xs = interp(beta_k, x0, x1, x2);
             const V3<float> xs_rel = tof(xs - x0);
             const V3<float> ns_f = tof(ns);
-            const double ds_face = want_alpha ? dot(ns, interp(beta_k, dx0, dx1, dx2)) : 0.0;
+            const double ds_face = want_dg ? dot(ns, interp(beta_k, dx0, dx1, dx2)) : 0.0;
             const int32_t* Lf = C.face + t * C.cap_f;
             for (int it = lane; it < nf * NK; it += 32) {
                 const int32_t m = Lf[it / NK];
@@ -274,10 +310,11 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 const double gamma = hermite(min3(bm), P.delta_T);
                 ++cnt_f;
                 if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa, omega * As, gamma, g, eps, beta_k);
-                if (want_alpha) {
+                if (want_dg) {
                     const double dm = dxm ? dot(ns, interp(bm, ld3(dxm, M[0]), ld3(dxm, M[1]), ld3(dxm, M[2]))) : 0.0;
                     const double dg = dm - ds_face;
-                    if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                    if (want_alpha && dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                    if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, P.kappa * (omega * As) * gamma, g, eps, dg);
                 }
             }
         }
@@ -332,11 +369,12 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 ++cnt_e;
                 const double gamma = hermite(eta, P.delta_e) * hermite(1.0 - eta, P.delta_e);
                 if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa_edge, 0.5 * ell, gamma, g, eps, bsk);
-                if (want_alpha) {
+                if (want_dg) {
                     const double ds = dot(ns, interp(bsk, dx0, dx1, dx2));
                     const double dm = dxm ? dot(ns, (1.0 - eta) * ld3(dxm, ia) + eta * ld3(dxm, ib)) : 0.0;
                     const double dg = dm - ds;
-                    if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                    if (want_alpha && dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                    if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, P.kappa_edge * (0.5 * ell) * gamma, g, eps, dg);
                 }
             }
         }
@@ -365,11 +403,12 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 if (!(g < eps)) continue;
                 ++cnt_p;
                 if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa_point, 1.0, 1.0, g, eps, bs);
-                if (want_alpha) {
+                if (want_dg) {
                     const double ds = dot(ns, interp(bs, dx0, dx1, dx2));
                     const double dm = dxm ? dot(ns, ld3(dxm, u)) : 0.0;
                     const double dg = dm - ds;
-                    if (dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                    if (want_alpha && dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
+                    if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, P.kappa_point * 1.0 * 1.0, g, eps, dg);
                 }
             }
         }
@@ -389,6 +428,14 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 for (int q = 0; q < 6; ++q) triS[6 * t + q] = A.S[q];
                 triN[3 * t + 0] = (T)ns.x; triN[3 * t + 1] = (T)ns.y; triN[3 * t + 2] = (T)ns.z;
             }
+        }
+        if (MODE == MODE_LAGGED) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) E8[j] += shfl_x(E8[j], o);
+            if (lane == 0)
+                for (int j = 0; j < LG.na; ++j) LG.triE8[(int64_t)j * LG.ns + t] = E8[j];
         }
         if (want_alpha) {
 #pragma unroll
@@ -496,11 +543,11 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t n, doubl
 template <int NK, class T, int MODE>
 cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* Sm, T* N,
                            long long* counters, const double* dx, const double* dxm,
-                           unsigned long long* alpha_bits) {
+                           unsigned long long* alpha_bits, LagArgs LG = LagArgs()) {
     const int threads = 256;
     const int blocks = sm_count(c.device) * 8;
     k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
-        c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits);
+        c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG);
     return cudaGetLastError();
 }
 
@@ -582,6 +629,21 @@ cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const d
     if (c.P.nk == 4)
         return launch_samples<4, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm, alpha_bits);
     return launch_samples<16, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm, alpha_bits);
+}
+
+cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,
+                           const double* alphas_dev, int na, double* triE8, double* energies_dev) {
+    ProfScope ps(c.prof, c.stream, "lagged");
+    if (na < 1 || na > 8) return cudaErrorInvalidValue;
+    GMCP_CUDA_TRY(cudaMemsetAsync(triE8, 0, sizeof(double) * (size_t)na * (size_t)c.ns, c.stream));
+    LagArgs LG;
+    LG.alphas = alphas_dev; LG.na = na; LG.triE8 = triE8; LG.ns = c.ns;
+    if (c.P.nk == 4)
+        GMCP_CUDA_TRY((launch_samples<4, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, LG)));
+    else
+        GMCP_CUDA_TRY((launch_samples<16, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, LG)));
+    for (int j = 0; j < na; ++j) GMCP_CUDA_TRY(reduce_sum(c, triE8 + (int64_t)j * c.ns, c.ns, energies_dev + j));
+    return cudaSuccess;
 }
 
 }  // namespace gmcp

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -173,6 +174,37 @@ struct ProfScope {
 };
 
 // ------------------------------------------------------------------------
+// time-stepper state (built on the first ipc_newton_step): tet data, the
+// global block pattern (vertex adjacency through tets, plus the diagonal and
+// the contact pattern) with per-block contribution lists, and the solver's
+// vectors
+// ------------------------------------------------------------------------
+struct NewtonState {
+    double mu = 0, lam = 0, lbar = 0;
+    int64_t nnzb = 0;
+    DBuf<int32_t> tets;                  // [nt][4]
+    DBuf<double> Dminv, vol, mass;       // [nt][9], [nt], [nv]
+    DBuf<uint8_t> dir;                   // [nv]
+    DBuf<int32_t> vte_off, vte;          // vertex -> tet corner (t*4+a)
+    DBuf<int32_t> rp, ci, brow, bcol;    // block pattern (CSR and COO)
+    DBuf<int32_t> diag;                  // [nv] index of block (v, v)
+    DBuf<int32_t> bt_off, bt;            // block -> (t*16 + a*4 + b)
+    DBuf<int32_t> cmap;                  // block -> contact block or -1
+    DBuf<double> tE, tG, tH, tE8;        // per-tet energy / gradient / Hessian
+    DBuf<double> A, Pinv;                // [nnzb][9], [nv][9]
+    DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nv]
+    DBuf<double> xhat, xt, G, dirn, tmp, P, dP, xi;   // [3 nv]
+    DBuf<double> cgrad64;                // contact gradient [3 nv] (FP64 path)
+    DBuf<float> cgrad32;                 // contact gradient [3 nv] (mixed path)
+    DBuf<double> xm, dxm;                // current master [nmv][3] and its motion
+    DBuf<double> ein8;                   // [8][nv] inertia energy terms
+    DBuf<double> triE8;                  // [8][ns] lagged contact energies
+    DBuf<double> alphas;                 // [8]
+    DBuf<double> scal;                   // solver scalars
+    DBuf<int32_t> bad;                   // inverted-tet flag
+};
+
+// ------------------------------------------------------------------------
 // the context
 // ------------------------------------------------------------------------
 struct Ctx {
@@ -235,6 +267,13 @@ struct Ctx {
 
     Profiler prof;
 
+    // host copies kept for the time stepper
+    std::vector<int32_t> h_tets;
+    std::vector<uint8_t> h_dir;
+    std::vector<double> h_X;
+    std::vector<int32_t> h_cb_row, h_cb_col;
+    std::unique_ptr<NewtonState> newton;
+
     SceneView view() const;
     CandView cand() {
         CandView c;
@@ -279,6 +318,33 @@ cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const d
                               const double* dxm, unsigned long long* alpha_bits);
 cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out);
 int sm_count(int device);
+// frozen-linear ("lagged") contact energy of the samples active at (x, xm),
+// evaluated at x + alphas[j] p for j < na (na <= 8) into energies_dev[j]
+// (FP64 in both precisions); needs the candidate lists of (x, xm)
+cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,
+                           const double* alphas_dev, int na, double* triE8, double* energies_dev);
+// newton.cu
+cudaError_t newton_setup(Ctx& c);
+cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev, int32_t* bad);
+// elastic energies at x + alphas[j] p (j < na <= 8) into energies_dev[j];
+// +inf where some tet has J <= 0
+cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_dev,
+                            int na, double* energies_dev);
+cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_dev, int na,
+                         bool with_contact, double* out_dev);
+cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess, double* Ec_dev, double* Ee_dev,
+                            double* E_dev, double* gnorm2_dev);
+cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double* out);
+cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters);
+// elementwise helpers
+cudaError_t vec_axpy(Ctx& c, int64_t n, double a, const double* x, const double* p, double* out);
+cudaError_t vec_xhat(Ctx& c, const double* x, const double* v, double* xhat);
+cudaError_t vec_dir_delta(Ctx& c, const double* x, const double* xhat, double* dP);
+cudaError_t vec_set_dir(Ctx& c, const double* src, double* dst);
+cudaError_t vec_free_delta(Ctx& c, const double* P, const double* xi, double* dP);
+cudaError_t vec_zero_dir(Ctx& c, double* p);
+cudaError_t vec_velocity(Ctx& c, const double* x, const double* xt, double* v);
+cudaError_t vec_neg(Ctx& c, int64_t n, const double* a, double* out);
 
 }  // namespace gmcp
 

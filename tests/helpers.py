@@ -37,6 +37,25 @@ def small_indent(n_quads=8, subdiv=2, press=0.15e-3, seed=1, L=1, dhat=1e-4):
     return sc, x
 
 
+def flat_press(nq=4, n_steps=4, pcg_rel_tol=1e-6):
+    """Pad (nq x nq x 2 hexes of 0.5 mm, tetrahedralised) whose top face is
+    driven down 0.3 mm over ``n_steps`` steps onto one large flat master
+    triangle 0.2 mm below (Dirichlet velocity in ``sc.v_dirichlet``)."""
+    sc, _, _ = flat_over_big_triangle(nq=nq, dx=0.5e-3, gap=2e-4, rest_gap=2e-4,
+                                      face_only=False)
+    X, tets, stris, top = S.pad_slab(nq, nq, 2, 0.5e-3, 0.5e-3)
+    sc.X, sc.tets, sc.stris = X, tets, stris
+    sc.dirichlet = top.astype(np.uint8)
+    sc.env_vert_off = np.array([0, sc.X.shape[0]])
+    sc.env_tet_off = np.array([0, sc.tets.shape[0]])
+    sc.env_stri_off = np.array([0, sc.stris.shape[0]])
+    sc.v_dirichlet = np.zeros_like(sc.X)
+    sc.v_dirichlet[top, 2] = -3e-4 / (n_steps * sc.params["h"])
+    sc.n_steps = n_steps
+    sc.params.update(pcg_rel_tol=pcg_rel_tol)
+    return sc
+
+
 def rotation(seed):
     rng = np.random.default_rng(seed)
     q, _ = np.linalg.qr(rng.normal(size=(3, 3)))

@@ -111,20 +111,8 @@ def test_pcg_matches_dense_solve(oracle_mod):
 
 def _flat_press_sim(oracle_mod, nq=4, n_steps=4):
     """pad pressed by its top face onto one large flat master triangle"""
-    from helpers import flat_over_big_triangle
-    sc, x, xm = flat_over_big_triangle(nq=nq, dx=0.5e-3, gap=2e-4, rest_gap=2e-4,
-                                       face_only=False)
-    sc.X = S.pad_slab(nq, nq, 2, 0.5e-3, 0.5e-3)[0]
-    sc.tets = S.pad_slab(nq, nq, 2, 0.5e-3, 0.5e-3)[1]
-    top = S.pad_slab(nq, nq, 2, 0.5e-3, 0.5e-3)[3]
-    sc.stris = S.pad_slab(nq, nq, 2, 0.5e-3, 0.5e-3)[2]
-    sc.dirichlet = top.astype(np.uint8)
-    sc.env_vert_off = np.array([0, sc.X.shape[0]]); sc.env_tet_off = np.array([0, sc.tets.shape[0]])
-    sc.env_stri_off = np.array([0, sc.stris.shape[0]])
-    sc.v_dirichlet = np.zeros_like(sc.X)
-    sc.v_dirichlet[top, 2] = -3e-4 / (n_steps * sc.params["h"])
-    sc.n_steps = n_steps
-    sc.params.update(pcg_rel_tol=1e-6)
+    from helpers import flat_press
+    sc = flat_press(nq=nq, n_steps=n_steps)
     O = oracle_mod.Scene(sc)
     return sc, O, oracle_mod.Sim(O)
 
