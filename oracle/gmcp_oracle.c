@@ -1248,21 +1248,45 @@ ORC_API void orc_psd_project(int n, double* A) {
         }
 }
 
+/* d - log1p(d), without the cancellation of the plain difference when d is
+ * small: its Taylor series d^2/2 - d^3/3 + ... - d^9/9 for |d| < 1e-2
+ * (truncation below 1e-17 relative), else the plain difference. */
+static double d_minus_log1p(double d) {
+    if (fabs(d) < 1e-2)
+        return d * d * (1.0 / 2 - d * (1.0 / 3 - d * (1.0 / 4 - d * (1.0 / 5 - d * (1.0 / 6 - d * (1.0 / 7 - d * (1.0 / 8 - d / 9.0)))))));
+    return d - log1p(d);
+}
+
 /* One tet: energy, gradient [12] (vertex-major), PSD Hessian [12x12] (the
- * 9x9 dP/dF is projected, then mapped by dF/dx).  Returns 0 if J <= 0. */
-ORC_API int orc_nh_tet(const double* Dminv, double vol, double mu, double lam, const double* x4,
-                       double* psi, double* grad, double* hess) {
-    double Ds[9], F[9], Fi[9], G[9];
+ * 9x9 dP/dF is projected, then mapped by dF/dx).  X4 are the rest positions
+ * of the four vertices, x4 the current ones.  Returns 0 if J <= 0.
+ * Reading R15: the energy is evaluated from the displacement gradient
+ * H = F - I = (Ds - Dm) Dm^-1 as
+ *   Psi/V = mu ((J-1) - ln J - q) + mu/2 |H|^2 + lambda/2 (ln J)^2,
+ *   J - 1 = tr H + q,  q = (sum of principal 2x2 minors of H) + det H,
+ * which is the textbook mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2
+ * rearranged (tr F^T F - 3 = 2 tr H + |H|^2) so that its first-order terms
+ * cancel analytically instead of in rounding. */
+ORC_API int orc_nh_tet(const double* Dminv, double vol, double mu, double lam, const double* X4,
+                       const double* x4, double* psi, double* grad, double* hess) {
+    double Du[9], H[9], F[9], Fi[9], G[9];
     for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) Ds[3 * r + c] = x4[3 * (c + 1) + r] - x4[r];
-    mul3(Ds, Dminv, F);
-    double J = det3(F);
-    if (!(J > 0.0)) { *psi = INFINITY; return 0; }
+        for (int c = 0; c < 3; ++c)
+            Du[3 * r + c] = (x4[3 * (c + 1) + r] - X4[3 * (c + 1) + r]) - (x4[r] - X4[r]);
+    mul3(Du, Dminv, H);
+    for (int i = 0; i < 9; ++i) F[i] = H[i];
+    F[0] += 1.0; F[4] += 1.0; F[8] += 1.0;
+    const double trH = H[0] + H[4] + H[8];
+    const double minors = (H[0] * H[4] - H[1] * H[3]) + (H[0] * H[8] - H[2] * H[6]) + (H[4] * H[8] - H[5] * H[7]);
+    const double q = minors + det3(H);
+    const double jm1 = trH + q;
+    if (!(jm1 > -1.0)) { *psi = INFINITY; return 0; }
+    double nH = 0.0;
+    for (int i = 0; i < 9; ++i) nH += H[i] * H[i];
+    const double lnJ = log1p(jm1);
+    *psi = vol * (mu * (d_minus_log1p(jm1) - q) + 0.5 * mu * nH + 0.5 * lam * lnJ * lnJ);
     inv3(F, Fi);
     for (int i = 0; i < 3; ++i) for (int j = 0; j < 3; ++j) G[3 * i + j] = Fi[3 * j + i];
-    double lnJ = log(J), Ic = 0.0;
-    for (int i = 0; i < 9; ++i) Ic += F[i] * F[i];
-    *psi = vol * (0.5 * mu * (Ic - 3.0) - mu * lnJ + 0.5 * lam * lnJ * lnJ);
     double D[12];   /* D[m][j]: dF_ij / dx_{m,i} */
     for (int j = 0; j < 3; ++j) {
         D[3 * 1 + j] = Dminv[0 * 3 + j]; D[3 * 2 + j] = Dminv[1 * 3 + j]; D[3 * 3 + j] = Dminv[2 * 3 + j];
@@ -1397,9 +1421,10 @@ static int elastic_eval(const orc_sim* s, const double* x, double* E, double* gr
     double e = 0.0;
     for (int t = 0; t < s->nt; ++t) {
         const int32_t* T = s->tets + 4 * t;
-        double x4[12], psi, g12[12], h144[144];
-        for (int a = 0; a < 4; ++a) for (int c = 0; c < 3; ++c) x4[3 * a + c] = x[3 * T[a] + c];
-        if (!orc_nh_tet(s->Dminv + 9 * t, s->vol[t], s->mu, s->lam, x4, &psi, grad ? g12 : NULL,
+        double x4[12], X4[12], psi, g12[12], h144[144];
+        for (int a = 0; a < 4; ++a)
+            for (int c = 0; c < 3; ++c) { x4[3 * a + c] = x[3 * T[a] + c]; X4[3 * a + c] = s->X[3 * T[a] + c]; }
+        if (!orc_nh_tet(s->Dminv + 9 * t, s->vol[t], s->mu, s->lam, X4, x4, &psi, grad ? g12 : NULL,
                         blk ? h144 : NULL)) { *E = INFINITY; return 0; }
         e += psi;
         if (grad) for (int a = 0; a < 4; ++a) for (int c = 0; c < 3; ++c) grad[3 * T[a] + c] += g12[3 * a + c];

@@ -88,7 +88,7 @@ def _declare(L):
     L.orc_ccd_max_step.restype = D
     L.orc_ccd_max_step.argtypes = [P, P, P, P, P, D, I, dp, dp]
     L.orc_psd_project.argtypes = [I, P]
-    L.orc_nh_tet.restype = I; L.orc_nh_tet.argtypes = [P, D, D, D, P, dp, P, P]
+    L.orc_nh_tet.restype = I; L.orc_nh_tet.argtypes = [P, D, D, D, P, P, dp, P, P]
     L.orc_sim_create.restype = P
     L.orc_sim_create.argtypes = [P, I, P, I, P, P, D, D, D, D, P, D, D, I, I, I, D, I]
     L.orc_sim_free.argtypes = [P]
@@ -154,11 +154,12 @@ def psd_project(A):
     return A
 
 
-def nh_tet(Dminv, vol, mu, lam, x4):
-    Dminv, x4 = _f64(Dminv).reshape(9), _f64(x4).reshape(12)
+def nh_tet(Dminv, vol, mu, lam, X4, x4):
+    """One tet at rest positions X4 and current positions x4 ([4][3])."""
+    Dminv, X4, x4 = _f64(Dminv).reshape(9), _f64(X4).reshape(12), _f64(x4).reshape(12)
     psi = D()
     g = np.zeros(12); H = np.zeros((12, 12))
-    ok = lib().orc_nh_tet(_p(Dminv), vol, mu, lam, _p(x4), C.byref(psi), _p(g), _p(H))
+    ok = lib().orc_nh_tet(_p(Dminv), vol, mu, lam, _p(X4), _p(x4), C.byref(psi), _p(g), _p(H))
     return bool(ok), psi.value, g, H
 
 

@@ -286,12 +286,18 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
         st->newton_iters = it + 1;
         int pit = 0;
         GMCP_CUDA_TRY(vec_neg(c, n, N.G.p, N.tmp.p));
-        GMCP_CUDA_TRY(pcg_solve(c, N.tmp.p, N.dirn.p, c.prm.pcg_rel_tol, c.prm.max_pcg, &pit));
+        {
+            ProfScope ps(c.prof, s, "pcg");
+            GMCP_CUDA_TRY(pcg_solve(c, N.tmp.p, N.dirn.p, c.prm.pcg_rel_tol, c.prm.max_pcg, &pit));
+        }
         st->pcg_iters_total += pit;
         GMCP_CUDA_TRY(vec_zero_dir(c, N.dirn.p));
         GMCP_CUDA_TRY(dot_dev(c, N.G.p, N.dirn.p, n, sc + 60));
         double al;
-        GMCP_CUDA_TRY(ccd_bound(c, x, N.dirn.p, N.xm.p, nullptr, true, &al));
+        {
+            ProfScope ps(c.prof, s, "step_bound");
+            GMCP_CUDA_TRY(ccd_bound(c, x, N.dirn.p, N.xm.p, nullptr, true, &al));
+        }
         GMCP_CUDA_TRY(cudaMemcpyAsync(hb + 8, sc + 60, sizeof(double), cudaMemcpyDeviceToHost, s));
         GMCP_CUDA_TRY(cudaStreamSynchronize(s));
         const double gp = hb[8];
@@ -305,7 +311,10 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
             als[0] = 0.0;
             for (int j = 0; j < nk; ++j) als[1 + j] = std::ldexp(al, -(hv0 + j));
             GMCP_CUDA_TRY(cudaMemcpyAsync(N.alphas.p, als, sizeof(double) * (nk + 1), cudaMemcpyHostToDevice, s));
-            GMCP_CUDA_TRY(energy_batch(c, x, N.dirn.p, N.alphas.p, nk + 1, true, sc + 48));
+            {
+                ProfScope ps(c.prof, s, "line_search");
+                GMCP_CUDA_TRY(energy_batch(c, x, N.dirn.p, N.alphas.p, nk + 1, true, sc + 48));
+            }
             GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 48, sizeof(double) * (nk + 1), cudaMemcpyDeviceToHost, s));
             GMCP_CUDA_TRY(cudaStreamSynchronize(s));
             const double E0 = hb[0];

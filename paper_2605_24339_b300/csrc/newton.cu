@@ -36,62 +36,12 @@ __device__ __forceinline__ void inv3(const double* A, double* I) {
     I[8] = (A[0] * A[4] - A[1] * A[3]) / d;
 }
 
-// cyclic Jacobi eigen-decomposition of a symmetric 9x9 matrix; on return A
-// holds the eigenvalues on its diagonal and V the eigenvectors in columns
-__device__ void jacobi9(double* A, double* V) {
-    const int n = 9;
-    for (int i = 0; i < n * n; ++i) V[i] = 0.0;
-    for (int i = 0; i < n; ++i) V[i * n + i] = 1.0;
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0, tot = 0.0;
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) {
-                tot += A[i * n + j] * A[i * n + j];
-                if (i != j) off += A[i * n + j] * A[i * n + j];
-            }
-        if (off <= 1e-32 * tot || off == 0.0) break;
-        for (int p = 0; p < n; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[p * n + q];
-                if (apq == 0.0) continue;
-                const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int k = 0; k < n; ++k) {
-                    const double akp = A[k * n + p], akq = A[k * n + q];
-                    A[k * n + p] = c * akp - s * akq;
-                    A[k * n + q] = s * akp + c * akq;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double apk = A[p * n + k], aqk = A[q * n + k];
-                    A[p * n + k] = c * apk - s * aqk;
-                    A[q * n + k] = s * apk + c * aqk;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double vkp = V[k * n + p], vkq = V[k * n + q];
-                    V[k * n + p] = c * vkp - s * vkq;
-                    V[k * n + q] = s * vkp + c * vkq;
-                }
-            }
-    }
-}
-
-// energy of one tet at positions x4 (vertex-major); returns false if J <= 0
-__device__ __forceinline__ bool nh_energy(const double* Dmi, double vol, double mu, double lam,
-                                          const double* x4, double* psi, double* F, double* lnJ) {
-    double Ds[9];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c) Ds[3 * r + c] = x4[3 * (c + 1) + r] - x4[r];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            F[3 * i + j] = Ds[3 * i] * Dmi[j] + Ds[3 * i + 1] * Dmi[3 + j] + Ds[3 * i + 2] * Dmi[6 + j];
-    const double J = det3(F);
-    if (!(J > 0.0)) return false;
-    double Ic = 0.0;
-    for (int i = 0; i < 9; ++i) Ic += F[i] * F[i];
-    *lnJ = log(J);
-    *psi = vol * (0.5 * mu * (Ic - 3.0) - mu * (*lnJ) + 0.5 * lam * (*lnJ) * (*lnJ));
-    return true;
+// (J - 1) - ln J without cancellation: Taylor series for |d| < 1e-2
+// (truncation below 1e-17 relative), else the plain difference
+__device__ __forceinline__ double d_minus_log1p(double d) {
+    if (fabs(d) < 1e-2)
+        return d * d * (1.0 / 2 - d * (1.0 / 3 - d * (1.0 / 4 - d * (1.0 / 5 - d * (1.0 / 6 - d * (1.0 / 7 - d * (1.0 / 8 - d / 9.0)))))));
+    return d - log1p(d);
 }
 
 struct ElasticView {
@@ -99,14 +49,193 @@ struct ElasticView {
     const int32_t* tets;   // [nt][4]
     const double* Dminv;   // [nt][9]
     const double* vol;     // [nt]
+    const double* X;       // rest positions [nv][3]
     double mu, lam;
 };
+
+// Displacement gradient H = (Ds - Dm) Dm^-1 from the vertex displacements
+// u = x - X, F = I + H, and the Neo-Hookean energy of the tet in the form
+//   V [mu ((J-1) - ln J - q) + mu/2 |H|^2 + lambda/2 (ln J)^2],
+//   J - 1 = tr H + q, q = sum of principal 2x2 minors of H + det H,
+// (algebraically mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2, with the
+// first-order terms cancelled exactly so the energy keeps its relative
+// precision at small strain).  Returns false if J <= 0.
+__device__ __forceinline__ bool nh_energy(const double* Dmi, double vol, double mu, double lam,
+                                          const double* x4, const double* X4, double* psi, double* F,
+                                          double* lnJ) {
+    double Du[9], H[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            Du[3 * r + c] = (x4[3 * (c + 1) + r] - X4[3 * (c + 1) + r]) - (x4[r] - X4[r]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            H[3 * i + j] = Du[3 * i] * Dmi[j] + Du[3 * i + 1] * Dmi[3 + j] + Du[3 * i + 2] * Dmi[6 + j];
+    for (int i = 0; i < 9; ++i) F[i] = H[i];
+    F[0] += 1.0; F[4] += 1.0; F[8] += 1.0;
+    const double trH = H[0] + H[4] + H[8];
+    const double minors = (H[0] * H[4] - H[1] * H[3]) + (H[0] * H[8] - H[2] * H[6]) + (H[4] * H[8] - H[5] * H[7]);
+    const double q = minors + det3(H);
+    const double jm1 = trH + q;
+    if (!(jm1 > -1.0)) return false;
+    double nH = 0.0;
+    for (int i = 0; i < 9; ++i) nH += H[i] * H[i];
+    *lnJ = log1p(jm1);
+    *psi = vol * (mu * (d_minus_log1p(jm1) - q) + 0.5 * mu * nH + 0.5 * lam * (*lnJ) * (*lnJ));
+    return true;
+}
 
 __device__ __forceinline__ void load_tet(const ElasticView& E, const double* x, int64_t t, double* x4) {
     for (int a = 0; a < 4; ++a) {
         const int64_t v = E.tets[4 * t + a];
         x4[3 * a] = x[3 * v]; x4[3 * a + 1] = x[3 * v + 1]; x4[3 * a + 2] = x[3 * v + 2];
     }
+}
+
+// cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (row-major,
+// in registers); on return A's diagonal holds the eigenvalues and V's
+// columns the eigenvectors
+__device__ __forceinline__ void jacobi3(double* A, double* V) {
+    for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0 : 0.0;
+#pragma unroll 1
+    for (int sweep = 0; sweep < 32; ++sweep) {
+        const double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        const double tot = off + 0.5 * (A[0] * A[0] + A[4] * A[4] + A[8] * A[8]);
+        if (off <= 1e-33 * tot || off == 0.0) break;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int p = k == 2 ? 1 : 0, q = k == 0 ? 1 : 2;
+            const double apq = A[3 * p + q];
+            if (apq == 0.0) continue;
+            const double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
+            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+            const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double arp = A[3 * r + p], arq = A[3 * r + q];
+                A[3 * r + p] = c * arp - s * arq;
+                A[3 * r + q] = s * arp + c * arq;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double apr = A[3 * p + r], aqr = A[3 * q + r];
+                A[3 * p + r] = c * apr - s * aqr;
+                A[3 * q + r] = s * apr + c * aqr;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const double vrp = V[3 * r + p], vrq = V[3 * r + q];
+                V[3 * r + p] = c * vrp - s * vrq;
+                V[3 * r + q] = s * vrp + c * vrq;
+            }
+        }
+    }
+}
+
+// PSD-projected Neo-Hookean Hessian of one tet, written as its 4x4 blocks
+// of 3x3.  dP/dF of an isotropic energy has a closed-form eigensystem in the
+// singular values of F = U diag(s) V^T (Smith, de Goes, Kim 2019, "Analytic
+// eigensystems for isotropic distortion energies"); for this energy, with
+// c = mu - lambda ln J:
+//   twist modes U (e_i e_j^T - e_j e_i^T) V^T / sqrt 2:  mu - c / (s_i s_j)
+//   flip modes  U (e_i e_j^T + e_j e_i^T) V^T / sqrt 2:  mu + c / (s_i s_j)
+//   scaling modes U diag(e) V^T, e the eigenvectors of the 3x3
+//     A_ii = mu + (c + lambda) / s_i^2, A_ij = lambda / (s_i s_j).
+// Clamping the eigenvalues at zero gives the same (unique) projection as a
+// 9x9 eigen-decomposition.  With D[m] the rows of dF/dx and d_m = V^T D[m],
+// block (m, n) = V_tet U M_mn U^T, M_mn = sum_k max(l_k, 0) (E_k d_m)(E_k d_n)^T.
+__device__ void nh_hessian_blocks(const double* F, double lnJ, double mu, double lam, const double* D,
+                                  double vol, double* out /* [144] */) {
+    // SVD from the eigen-decomposition of F^T F
+    double S[9], V[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) S[3 * i + j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
+    jacobi3(S, V);
+    const double detV = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
+                        V[2] * (V[3] * V[7] - V[4] * V[6]);
+    if (detV < 0.0) { V[2] = -V[2]; V[5] = -V[5]; V[8] = -V[8]; }
+    double B[9];   // F V, columns b_k
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k) B[3 * i + k] = F[3 * i] * V[k] + F[3 * i + 1] * V[3 + k] + F[3 * i + 2] * V[6 + k];
+    double U[9], sg[3];
+    {
+        double n0 = sqrt(B[0] * B[0] + B[3] * B[3] + B[6] * B[6]);
+        double u0[3] = {B[0] / n0, B[3] / n0, B[6] / n0};
+        double pr = u0[0] * B[1] + u0[1] * B[4] + u0[2] * B[7];
+        double w1[3] = {B[1] - pr * u0[0], B[4] - pr * u0[1], B[7] - pr * u0[2]};
+        double n1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2]);
+        double u1[3];
+        if (n1 > 1e-300) {
+            u1[0] = w1[0] / n1; u1[1] = w1[1] / n1; u1[2] = w1[2] / n1;
+        } else {   // any unit vector orthogonal to u0
+            const double ax = fabs(u0[0]), ay = fabs(u0[1]), az = fabs(u0[2]);
+            double e[3] = {0, 0, 0};
+            e[(ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2)] = 1.0;
+            const double d = e[0] * u0[0] + e[1] * u0[1] + e[2] * u0[2];
+            double w[3] = {e[0] - d * u0[0], e[1] - d * u0[1], e[2] - d * u0[2]};
+            const double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+            u1[0] = w[0] / nw; u1[1] = w[1] / nw; u1[2] = w[2] / nw;
+        }
+        double u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2], u0[0] * u1[1] - u0[1] * u1[0]};
+        sg[0] = n0;
+        sg[1] = u1[0] * B[1] + u1[1] * B[4] + u1[2] * B[7];
+        sg[2] = u2[0] * B[2] + u2[1] * B[5] + u2[2] * B[8];
+        for (int i = 0; i < 3; ++i) { U[3 * i] = u0[i]; U[3 * i + 1] = u1[i]; U[3 * i + 2] = u2[i]; }
+    }
+    const double c = mu - lam * lnJ;
+    // scaling block and its projection
+    double A[9], W[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            A[3 * i + j] = (i == j) ? mu + (c + lam) / (sg[i] * sg[i]) : lam / (sg[i] * sg[j]);
+    jacobi3(A, W);
+    double Ah[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double sum = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                const double l = A[4 * k];
+                if (l > 0.0) sum += W[3 * i + k] * l * W[3 * j + k];
+            }
+            Ah[3 * i + j] = sum;
+        }
+    // twist / flip eigenvalues per pair (0,1), (0,2), (1,2), clamped
+    double lp[3], lm[3];   // (lf + lt)/2 and (lf - lt)/2
+    for (int k = 0; k < 3; ++k) {
+        const int i = k == 2 ? 1 : 0, j = k == 0 ? 1 : 2;
+        const double r = c / (sg[i] * sg[j]);
+        const double lt = fmax(mu - r, 0.0), lf = fmax(mu + r, 0.0);
+        lp[k] = 0.5 * (lf + lt);
+        lm[k] = 0.5 * (lf - lt);
+    }
+    // d_m = V^T D[m]
+    double d[12];
+    for (int m = 0; m < 4; ++m)
+        for (int s = 0; s < 3; ++s)
+            d[3 * m + s] = D[3 * m] * V[s] + D[3 * m + 1] * V[3 + s] + D[3 * m + 2] * V[6 + s];
+    for (int m = 0; m < 4; ++m)
+        for (int n = m; n < 4; ++n) {
+            const double* dm = d + 3 * m;
+            const double* dn = d + 3 * n;
+            double M[9];
+            for (int r = 0; r < 3; ++r)
+                for (int s = 0; s < 3; ++s) M[3 * r + s] = dm[r] * dn[s] * Ah[3 * r + s];
+            for (int k = 0; k < 3; ++k) {
+                const int i = k == 2 ? 1 : 0, j = k == 0 ? 1 : 2;
+                M[4 * i] += lp[k] * dm[j] * dn[j];
+                M[4 * j] += lp[k] * dm[i] * dn[i];
+                M[3 * i + j] += lm[k] * dm[j] * dn[i];
+                M[3 * j + i] += lm[k] * dm[i] * dn[j];
+            }
+            double T[9];   // U M
+            for (int a = 0; a < 3; ++a)
+                for (int s = 0; s < 3; ++s) T[3 * a + s] = U[3 * a] * M[s] + U[3 * a + 1] * M[3 + s] + U[3 * a + 2] * M[6 + s];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const double v = vol * (T[3 * a] * U[3 * b] + T[3 * a + 1] * U[3 * b + 1] + T[3 * a + 2] * U[3 * b + 2]);
+                    out[(3 * m + a) * 12 + 3 * n + b] = v;
+                    if (n != m) out[(3 * n + b) * 12 + 3 * m + a] = v;
+                }
+        }
 }
 
 // energy, gradient [nt][12] and (WANT_HESS) PSD Hessian [nt][144] per tet
@@ -116,11 +245,12 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
           double* __restrict__ tG, double* __restrict__ tH, int32_t* __restrict__ bad) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= E.nt) return;
-    double x4[12], F[9], lnJ, psi;
+    double x4[12], X4[12], F[9], lnJ, psi;
     load_tet(E, x, t, x4);
+    load_tet(E, E.X, t, X4);
     const double* Dmi = E.Dminv + 9 * t;
     const double vol = E.vol[t];
-    if (!nh_energy(Dmi, vol, E.mu, E.lam, x4, &psi, F, &lnJ)) {
+    if (!nh_energy(Dmi, vol, E.mu, E.lam, x4, X4, &psi, F, &lnJ)) {
         atomicMax(bad, 1);
         tE[t] = INFINITY;
         for (int q = 0; q < 12; ++q) tG[12 * t + q] = 0.0;
@@ -146,38 +276,7 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
             for (int j = 0; j < 3; ++j) s += P[3 * i + j] * D[3 * m + j];
             tG[12 * t + 3 * m + i] = vol * s;
         }
-    if (!WANT_HESS) return;
-    double H9[81], V9[81];
-    const double cc = E.mu - E.lam * lnJ;
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            for (int l = 0; l < 3; ++l)
-                for (int k = 0; k < 3; ++k)
-                    H9[(3 * i + j) * 9 + 3 * l + k] = (i == l && j == k ? E.mu : 0.0) +
-                                                      cc * G[3 * i + k] * G[3 * l + j] +
-                                                      E.lam * G[3 * i + j] * G[3 * l + k];
-    jacobi9(H9, V9);
-    // projected: sum over positive eigenvalues of l v v^T, mapped by D
-    double Hp[81];
-    for (int i = 0; i < 9; ++i)
-        for (int j = 0; j < 9; ++j) {
-            double s = 0.0;
-            for (int k = 0; k < 9; ++k) {
-                const double l = H9[k * 9 + k];
-                if (l > 0.0) s += V9[i * 9 + k] * l * V9[j * 9 + k];
-            }
-            Hp[i * 9 + j] = s;
-        }
-    for (int m = 0; m < 4; ++m)
-        for (int a = 0; a < 3; ++a)
-            for (int n = 0; n < 4; ++n)
-                for (int b = 0; b < 3; ++b) {
-                    double s = 0.0;
-                    for (int j = 0; j < 3; ++j)
-                        for (int k = 0; k < 3; ++k)
-                            s += D[3 * m + j] * Hp[(3 * a + j) * 9 + 3 * b + k] * D[3 * n + k];
-                    tH[144 * t + (3 * m + a) * 12 + 3 * n + b] = vol * s;
-                }
+    if (WANT_HESS) nh_hessian_blocks(F, lnJ, E.mu, E.lam, D, vol, tH + 144 * t);
 }
 
 // elastic energies at x + alpha_j p for j < na (<= 8), layout [na][nt]
@@ -186,14 +285,15 @@ __global__ void k_nh_energy_multi(ElasticView E, const double* __restrict__ x,
                                   double* __restrict__ tE8) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= E.nt) return;
-    double x4[12], p4[12], y4[12], F[9], lnJ, psi;
+    double x4[12], p4[12], X4[12], y4[12], F[9], lnJ, psi;
     load_tet(E, x, t, x4);
     load_tet(E, p, t, p4);
+    load_tet(E, E.X, t, X4);
     const double* Dmi = E.Dminv + 9 * t;
     for (int j = 0; j < na; ++j) {
         const double a = alphas[j];
         for (int q = 0; q < 12; ++q) y4[q] = x4[q] + a * p4[q];
-        tE8[(int64_t)j * E.nt + t] = nh_energy(Dmi, E.vol[t], E.mu, E.lam, y4, &psi, F, &lnJ) ? psi : INFINITY;
+        tE8[(int64_t)j * E.nt + t] = nh_energy(Dmi, E.vol[t], E.mu, E.lam, y4, X4, &psi, F, &lnJ) ? psi : INFINITY;
     }
 }
 
@@ -416,7 +516,7 @@ static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev, int32_t* bad) {
     NewtonState& N = *c.newton;
-    ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, N.mu, N.lam};
+    ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, c.X.p, N.mu, N.lam};
     if (c.nt == 0) return cudaSuccess;
     if (want_hess)
         k_nh_eval<true><<<nblk(c.nt, 128), 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH.p, bad);
@@ -429,7 +529,7 @@ cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev,
 cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_dev,
                             int na, double* energies_dev) {
     NewtonState& N = *c.newton;
-    ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, N.mu, N.lam};
+    ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, c.X.p, N.mu, N.lam};
     if (c.nt == 0) return cudaMemsetAsync(energies_dev, 0, sizeof(double) * na, c.stream);
     k_nh_energy_multi<<<nblk(c.nt, 128), 128, 0, c.stream>>>(E, x, p, alphas_dev, na, N.tE8.p);
     GMCP_CUDA_TRY(cudaGetLastError());

@@ -18,8 +18,46 @@ MU, LAM = 1e5, 1e6
 
 def test_nh_rest(oracle_mod):
     X, Dmi, V = _tet(np.random.default_rng(0))
-    ok, psi, g, H = oracle_mod.nh_tet(Dmi, V, MU, LAM, X)
+    ok, psi, g, H = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, X)
     assert ok and abs(psi) < 1e-20 and np.abs(g).max() < 1e-12 * MU * V / 1e-3
+
+
+def _nh_exact(Dmi, V, X, x, mu, lam, dps=60):
+    """The textbook energy mu/2 (tr F^T F - 3) - mu ln J + lam/2 (ln J)^2 with
+    F = Ds Dm^-1, evaluated in 60-digit arithmetic (mpmath) from the same
+    FP64 inputs."""
+    import mpmath as mp
+    mp.mp.dps = dps
+    Xm = [[mp.mpf(float(v)) for v in row] for row in np.asarray(X).reshape(4, 3)]
+    xm = [[mp.mpf(float(v)) for v in row] for row in np.asarray(x).reshape(4, 3)]
+    Dm = mp.matrix(3, 3)
+    Ds = mp.matrix(3, 3)
+    for r in range(3):
+        for c in range(3):
+            Dm[r, c] = Xm[c + 1][r] - Xm[0][r]
+            Ds[r, c] = xm[c + 1][r] - xm[0][r]
+    F = Ds * mp.inverse(Dm)
+    Ic = sum(F[i, j] ** 2 for i in range(3) for j in range(3))
+    lnJ = mp.log(mp.det(F))
+    vol = abs(mp.det(Dm)) / 6
+    return float(vol * (mu / 2 * (Ic - 3) - mu * lnJ + lam / 2 * lnJ ** 2))
+
+
+@pytest.mark.parametrize("strain", [1e-8, 1e-6, 1e-4, 1e-2, 0.3])
+def test_nh_energy_relative_precision(oracle_mod, strain):
+    """Reading R15: the oracle's energy keeps ~1e-12 relative precision of
+    the energy itself down to tiny strains (the textbook FP64 evaluation
+    loses ~1e-16 / strain^2 of it), pinned against 60-digit arithmetic."""
+    rng = np.random.default_rng(11)
+    X, Dmi, V = _tet(rng)
+    for _ in range(4):
+        x = X + strain * 1e-3 * rng.normal(size=X.shape)
+        ok, psi, _, _ = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, x)
+        ref = _nh_exact(Dmi, V, X, x, MU, LAM)
+        assert ok and ref > 0
+        # H = (Ds - Dm) Dm^-1 with the FP64 Dm^-1 is H times (1 + O(1e-16)),
+        # so the energy (quadratic in H) stays accurate relative to itself
+        assert psi == pytest.approx(ref, rel=1e-12)
 
 
 def test_nh_gradient_fd(oracle_mod):
@@ -27,13 +65,13 @@ def test_nh_gradient_fd(oracle_mod):
     for _ in range(5):
         X, Dmi, V = _tet(rng)
         x = X + rng.normal(size=X.shape) * 2e-4
-        ok, psi, g, H = oracle_mod.nh_tet(Dmi, V, MU, LAM, x)
+        ok, psi, g, H = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, x)
         assert ok
         h = 1e-9
         for i in range(12):
             e = np.zeros(12); e[i] = h
-            p = oracle_mod.nh_tet(Dmi, V, MU, LAM, x.ravel() + e)[1]
-            m = oracle_mod.nh_tet(Dmi, V, MU, LAM, x.ravel() - e)[1]
+            p = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, x.ravel() + e)[1]
+            m = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, x.ravel() - e)[1]
             assert (p - m) / (2 * h) == pytest.approx(g[i], rel=1e-5, abs=1e-9 * np.abs(g).max())
 
 
@@ -45,12 +83,12 @@ def test_nh_hessian_fd_stretch(oracle_mod):
     rng = np.random.default_rng(2)
     X, Dmi, V = _tet(rng)
     x = (X @ np.diag([1.01, 1.02, 1.015]).T).ravel()
-    ok, psi, g, H = oracle_mod.nh_tet(Dmi, V, MU, LAM, x)
+    ok, psi, g, H = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, x)
     h = 1e-10
     for i in range(12):
         e = np.zeros(12); e[i] = h
-        gp = oracle_mod.nh_tet(Dmi, V, MU, LAM, x + e)[2]
-        gm = oracle_mod.nh_tet(Dmi, V, MU, LAM, x - e)[2]
+        gp = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, x + e)[2]
+        gm = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, x - e)[2]
         np.testing.assert_allclose((gp - gm) / (2 * h), H[:, i], rtol=1e-5,
                                    atol=1e-6 * np.abs(H).max())
 
@@ -60,13 +98,13 @@ def test_nh_hessian_psd_large_strain(oracle_mod):
     X, Dmi, V = _tet(rng)
     # strong stretch makes dP/dF indefinite; the projected Hessian is PSD
     x = X.copy(); x[:, 0] *= 2.5
-    ok, psi, g, H = oracle_mod.nh_tet(Dmi, V, MU, LAM, x)
+    ok, psi, g, H = oracle_mod.nh_tet(Dmi, V, MU, LAM, X, x)
     assert ok
     w = np.linalg.eigvalsh(H)
     assert w.min() >= -1e-9 * w.max()
     # inverted tet is rejected
     xi = X.copy(); xi[3, 2] = -xi[3, 2] - 1e-3
-    assert not oracle_mod.nh_tet(Dmi, V, MU, LAM, xi)[0]
+    assert not oracle_mod.nh_tet(Dmi, V, MU, LAM, X, xi)[0]
 
 
 def test_psd_projection_matches_eigh(oracle_mod):
