@@ -259,9 +259,61 @@ def run_ours(args):
         "alpha": info["alpha"],
         "clocks": clk,
     }
+    if not args.no_newton:
+        line["newton_step"] = newton_measurement(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(steps=2)
     print(json.dumps(line), flush=True)
+
+
+def newton_measurement(dev, start_step=20, n_states=4):
+    """Second half of the metric: wall time of one implicit-Euler step solved
+    to a 1e-6 residual (ipc_newton_step), mixed precision against plain FP64.
+    States: the gel_on_terrain press run from rest in mixed precision; steps
+    ``start_step`` .. ``start_step + n_states - 1`` (contact starts at step 10)
+    are recorded as (x^t, v^t).  Each precision then solves the step from
+    every recorded state (after one untimed step that builds its time-stepper
+    state); the median wall time is reported."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    sc = S.gel_on_terrain()
+    top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
+    vd = torch.as_tensor(sc.v_dirichlet, device="cuda")
+    gen = binding.Context(sc, precision="mixed", device=dev)
+    x = torch.as_tensor(sc.X.copy(), device="cuda")
+    v = vd.clone()
+    states = []
+    for k in range(start_step + n_states):
+        if k >= start_step:
+            states.append((x.clone(), v.clone()))
+        r = gen.newton_step(x, v)
+        v[top] = vd[top]
+        if r["status"] != 0:
+            break
+    gen.close()
+    out = {"workload": f"gel_on_terrain press from rest, steps {start_step}..{start_step + len(states) - 1} "
+                       f"(top face at -0.5 mm/s, h = 10 ms, in contact from step 10)",
+           "n_vert": int(sc.X.shape[0]), "n_tet": int(sc.tets.shape[0]),
+           "newton_tol": sc.params["newton_tol"], "pcg_rel_tol": sc.params["pcg_rel_tol"]}
+    for prec in ("fp64", "mixed"):
+        ctx = binding.Context(sc, precision=prec, device=dev)
+        ctx.newton_step(states[0][0].clone(), states[0][1].clone())
+        times, iters, ok = [], [], True
+        for xs0, vs0 in states:
+            xs, vs = xs0.clone(), vs0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = ctx.newton_step(xs, vs)
+            torch.cuda.synchronize()
+            times.append((time.perf_counter() - t0) * 1e3)
+            iters.append(st["newton_iters"])
+            ok = ok and st["status"] == 0 and st["residual"] <= sc.params["newton_tol"]
+        out[prec] = {"ms_per_step_median": statistics.median(times), "ms_per_step": [round(t, 1) for t in times],
+                     "newton_iters": iters, "all_converged": ok}
+        ctx.close()
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step_median"] / out["mixed"]["ms_per_step_median"]
+    return out
 
 
 def cpu_baseline(steps=2):
@@ -355,6 +407,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-newton", action="store_true",
+                    help="skip the time-step measurement (newton_step key)")
     ap.add_argument("--mode", default="bench", choices=["bench", "passes"],
                     help="passes: run --steps untimed contact passes (for profilers)")
     args = ap.parse_args()

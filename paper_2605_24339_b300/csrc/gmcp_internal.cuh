@@ -186,12 +186,17 @@ struct NewtonState {
     DBuf<double> Dminv, vol, mass;       // [nt][9], [nt], [nv]
     DBuf<uint8_t> dir;                   // [nv]
     DBuf<int32_t> vte_off, vte;          // vertex -> tet corner (t*4+a)
-    DBuf<int32_t> rp, ci, brow, bcol;    // block pattern (CSR and COO)
+    DBuf<int32_t> rp, ci, brow;          // block pattern (CSR, plus the row of each block)
     DBuf<int32_t> diag;                  // [nv] index of block (v, v)
     DBuf<int32_t> bt_off, bt;            // block -> (t*16 + a*4 + b)
     DBuf<int32_t> cmap;                  // block -> contact block or -1
-    DBuf<double> tE, tG, tH, tE8;        // per-tet energy / gradient / Hessian
-    DBuf<double> A, Pinv;                // [nnzb][9], [nv][9]
+    DBuf<double> tE, tG, tE8;            // per-tet energy [nt], gradient [nt][12], energies [8][nt]
+    DBuf<double> tH64;                   // per-tet Hessian, 10 blocks [nt][90] (FP64 path)
+    DBuf<float> tH32;                    // the same in FP32 (mixed path)
+    DBuf<double> A64, Pinv;              // global matrix [nnzb][9] (FP64 path), P^-1 [nv][9]
+    DBuf<float> A32, p32;                // FP32 matrix and search direction (mixed path)
+    DBuf<double> part;                   // PCG per-block partial sums [2][blocks]
+    DBuf<unsigned> counters;             // PCG last-block counters
     DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nv]
     DBuf<double> xhat, xt, G, dirn, tmp, P, dP, xi;   // [3 nv]
     DBuf<double> cgrad64;                // contact gradient [3 nv] (FP64 path)

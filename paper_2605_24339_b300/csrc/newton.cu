@@ -94,36 +94,38 @@ __device__ __forceinline__ void load_tet(const ElasticView& E, const double* x, 
 // cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix (row-major,
 // in registers); on return A's diagonal holds the eigenvalues and V's
 // columns the eigenvectors
-__device__ __forceinline__ void jacobi3(double* A, double* V) {
-    for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? 1.0 : 0.0;
+template <class R>
+__device__ __forceinline__ void jacobi3(R* A, R* V) {
+    const R tol2 = sizeof(R) == 4 ? R(1e-13) : R(1e-33);
+    for (int i = 0; i < 9; ++i) V[i] = (i % 4 == 0) ? R(1) : R(0);
 #pragma unroll 1
     for (int sweep = 0; sweep < 32; ++sweep) {
-        const double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
-        const double tot = off + 0.5 * (A[0] * A[0] + A[4] * A[4] + A[8] * A[8]);
-        if (off <= 1e-33 * tot || off == 0.0) break;
+        const R off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        const R tot = off + R(0.5) * (A[0] * A[0] + A[4] * A[4] + A[8] * A[8]);
+        if (off <= tol2 * tot || off == R(0)) break;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int p = k == 2 ? 1 : 0, q = k == 0 ? 1 : 2;
-            const double apq = A[3 * p + q];
-            if (apq == 0.0) continue;
-            const double theta = (A[3 * q + q] - A[3 * p + p]) / (2.0 * apq);
-            const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-            const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+            const R apq = A[3 * p + q];
+            if (apq == R(0)) continue;
+            const R theta = (A[3 * q + q] - A[3 * p + p]) / (R(2) * apq);
+            const R t = (theta >= R(0) ? R(1) : R(-1)) / (fabs(theta) + sqrt(theta * theta + R(1)));
+            const R c = R(1) / sqrt(t * t + R(1)), s = t * c;
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                const double arp = A[3 * r + p], arq = A[3 * r + q];
+                const R arp = A[3 * r + p], arq = A[3 * r + q];
                 A[3 * r + p] = c * arp - s * arq;
                 A[3 * r + q] = s * arp + c * arq;
             }
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                const double apr = A[3 * p + r], aqr = A[3 * q + r];
+                const R apr = A[3 * p + r], aqr = A[3 * q + r];
                 A[3 * p + r] = c * apr - s * aqr;
                 A[3 * q + r] = s * apr + c * aqr;
             }
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                const double vrp = V[3 * r + p], vrq = V[3 * r + q];
+                const R vrp = V[3 * r + p], vrq = V[3 * r + q];
                 V[3 * r + p] = c * vrp - s * vrq;
                 V[3 * r + q] = s * vrp + c * vrq;
             }
@@ -131,11 +133,15 @@ __device__ __forceinline__ void jacobi3(double* A, double* V) {
     }
 }
 
-// PSD-projected Neo-Hookean Hessian of one tet, written as its 4x4 blocks
-// of 3x3.  dP/dF of an isotropic energy has a closed-form eigensystem in the
-// singular values of F = U diag(s) V^T (Smith, de Goes, Kim 2019, "Analytic
-// eigensystems for isotropic distortion energies"); for this energy, with
-// c = mu - lambda ln J:
+// the 10 distinct 3x3 blocks (m <= n) of a tet's 12x12 Hessian: block
+// (m, n) is stored at kTetBlk[m] + n - m, row-major; (n, m) is its transpose
+__constant__ int kTetBlk[4] = {0, 4, 7, 9};
+
+// PSD-projected Neo-Hookean Hessian of one tet, written as its 10 distinct
+// 3x3 blocks in precision R.  dP/dF of an isotropic energy has a closed-form
+// eigensystem in the singular values of F = U diag(s) V^T (Smith, de Goes,
+// Kim 2019, "Analytic eigensystems for isotropic distortion energies"); for
+// this energy, with c = mu - lambda ln J:
 //   twist modes U (e_i e_j^T - e_j e_i^T) V^T / sqrt 2:  mu - c / (s_i s_j)
 //   flip modes  U (e_i e_j^T + e_j e_i^T) V^T / sqrt 2:  mu + c / (s_i s_j)
 //   scaling modes U diag(e) V^T, e the eigenvectors of the 3x3
@@ -143,80 +149,86 @@ __device__ __forceinline__ void jacobi3(double* A, double* V) {
 // Clamping the eigenvalues at zero gives the same (unique) projection as a
 // 9x9 eigen-decomposition.  With D[m] the rows of dF/dx and d_m = V^T D[m],
 // block (m, n) = V_tet U M_mn U^T, M_mn = sum_k max(l_k, 0) (E_k d_m)(E_k d_n)^T.
-__device__ void nh_hessian_blocks(const double* F, double lnJ, double mu, double lam, const double* D,
-                                  double vol, double* out /* [144] */) {
+template <class R>
+__device__ void nh_hessian_blocks(const double* Fd, double lnJd, double mud, double lamd, const double* Dd,
+                                  double vold, R* out /* [90] */) {
+    R F[9], D[12];
+    for (int i = 0; i < 9; ++i) F[i] = (R)Fd[i];
+    for (int i = 0; i < 12; ++i) D[i] = (R)Dd[i];
+    const R mu = (R)mud, lam = (R)lamd, vol = (R)vold;
     // SVD from the eigen-decomposition of F^T F
-    double S[9], V[9];
+    R S[9], V[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) S[3 * i + j] = F[i] * F[j] + F[3 + i] * F[3 + j] + F[6 + i] * F[6 + j];
     jacobi3(S, V);
-    const double detV = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
-                        V[2] * (V[3] * V[7] - V[4] * V[6]);
-    if (detV < 0.0) { V[2] = -V[2]; V[5] = -V[5]; V[8] = -V[8]; }
-    double B[9];   // F V, columns b_k
+    const R detV = V[0] * (V[4] * V[8] - V[5] * V[7]) - V[1] * (V[3] * V[8] - V[5] * V[6]) +
+                   V[2] * (V[3] * V[7] - V[4] * V[6]);
+    if (detV < R(0)) { V[2] = -V[2]; V[5] = -V[5]; V[8] = -V[8]; }
+    R B[9];   // F V, columns b_k
     for (int i = 0; i < 3; ++i)
         for (int k = 0; k < 3; ++k) B[3 * i + k] = F[3 * i] * V[k] + F[3 * i + 1] * V[3 + k] + F[3 * i + 2] * V[6 + k];
-    double U[9], sg[3];
+    R U[9], sg[3];
     {
-        double n0 = sqrt(B[0] * B[0] + B[3] * B[3] + B[6] * B[6]);
-        double u0[3] = {B[0] / n0, B[3] / n0, B[6] / n0};
-        double pr = u0[0] * B[1] + u0[1] * B[4] + u0[2] * B[7];
-        double w1[3] = {B[1] - pr * u0[0], B[4] - pr * u0[1], B[7] - pr * u0[2]};
-        double n1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2]);
-        double u1[3];
-        if (n1 > 1e-300) {
+        const R n0 = sqrt(B[0] * B[0] + B[3] * B[3] + B[6] * B[6]);
+        const R u0[3] = {B[0] / n0, B[3] / n0, B[6] / n0};
+        const R pr = u0[0] * B[1] + u0[1] * B[4] + u0[2] * B[7];
+        const R w1[3] = {B[1] - pr * u0[0], B[4] - pr * u0[1], B[7] - pr * u0[2]};
+        const R n1 = sqrt(w1[0] * w1[0] + w1[1] * w1[1] + w1[2] * w1[2]);
+        R u1[3];
+        if (n1 > R(1e-30) * n0) {
             u1[0] = w1[0] / n1; u1[1] = w1[1] / n1; u1[2] = w1[2] / n1;
         } else {   // any unit vector orthogonal to u0
-            const double ax = fabs(u0[0]), ay = fabs(u0[1]), az = fabs(u0[2]);
-            double e[3] = {0, 0, 0};
-            e[(ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2)] = 1.0;
-            const double d = e[0] * u0[0] + e[1] * u0[1] + e[2] * u0[2];
-            double w[3] = {e[0] - d * u0[0], e[1] - d * u0[1], e[2] - d * u0[2]};
-            const double nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+            const R ax = fabs(u0[0]), ay = fabs(u0[1]), az = fabs(u0[2]);
+            R e[3] = {R(0), R(0), R(0)};
+            e[(ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2)] = R(1);
+            const R d = e[0] * u0[0] + e[1] * u0[1] + e[2] * u0[2];
+            const R w[3] = {e[0] - d * u0[0], e[1] - d * u0[1], e[2] - d * u0[2]};
+            const R nw = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
             u1[0] = w[0] / nw; u1[1] = w[1] / nw; u1[2] = w[2] / nw;
         }
-        double u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2], u0[0] * u1[1] - u0[1] * u1[0]};
+        const R u2[3] = {u0[1] * u1[2] - u0[2] * u1[1], u0[2] * u1[0] - u0[0] * u1[2], u0[0] * u1[1] - u0[1] * u1[0]};
         sg[0] = n0;
         sg[1] = u1[0] * B[1] + u1[1] * B[4] + u1[2] * B[7];
         sg[2] = u2[0] * B[2] + u2[1] * B[5] + u2[2] * B[8];
         for (int i = 0; i < 3; ++i) { U[3 * i] = u0[i]; U[3 * i + 1] = u1[i]; U[3 * i + 2] = u2[i]; }
     }
-    const double c = mu - lam * lnJ;
+    const R c = (R)(mud - lamd * lnJd);
     // scaling block and its projection
-    double A[9], W[9];
+    R A[9], W[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
             A[3 * i + j] = (i == j) ? mu + (c + lam) / (sg[i] * sg[i]) : lam / (sg[i] * sg[j]);
     jacobi3(A, W);
-    double Ah[9];
+    R Ah[9];
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
-            double sum = 0.0;
+            R sum = R(0);
             for (int k = 0; k < 3; ++k) {
-                const double l = A[4 * k];
-                if (l > 0.0) sum += W[3 * i + k] * l * W[3 * j + k];
+                const R l = A[4 * k];
+                if (l > R(0)) sum += W[3 * i + k] * l * W[3 * j + k];
             }
             Ah[3 * i + j] = sum;
         }
     // twist / flip eigenvalues per pair (0,1), (0,2), (1,2), clamped
-    double lp[3], lm[3];   // (lf + lt)/2 and (lf - lt)/2
+    R lp[3], lm[3];   // (lf + lt)/2 and (lf - lt)/2
     for (int k = 0; k < 3; ++k) {
         const int i = k == 2 ? 1 : 0, j = k == 0 ? 1 : 2;
-        const double r = c / (sg[i] * sg[j]);
-        const double lt = fmax(mu - r, 0.0), lf = fmax(mu + r, 0.0);
-        lp[k] = 0.5 * (lf + lt);
-        lm[k] = 0.5 * (lf - lt);
+        const R r = c / (sg[i] * sg[j]);
+        const R lt = fmax(mu - r, R(0)), lf = fmax(mu + r, R(0));
+        lp[k] = R(0.5) * (lf + lt);
+        lm[k] = R(0.5) * (lf - lt);
     }
     // d_m = V^T D[m]
-    double d[12];
+    R d[12];
     for (int m = 0; m < 4; ++m)
         for (int s = 0; s < 3; ++s)
             d[3 * m + s] = D[3 * m] * V[s] + D[3 * m + 1] * V[3 + s] + D[3 * m + 2] * V[6 + s];
+    int blk = 0;
     for (int m = 0; m < 4; ++m)
-        for (int n = m; n < 4; ++n) {
-            const double* dm = d + 3 * m;
-            const double* dn = d + 3 * n;
-            double M[9];
+        for (int n = m; n < 4; ++n, ++blk) {
+            const R* dm = d + 3 * m;
+            const R* dn = d + 3 * n;
+            R M[9];
             for (int r = 0; r < 3; ++r)
                 for (int s = 0; s < 3; ++s) M[3 * r + s] = dm[r] * dn[s] * Ah[3 * r + s];
             for (int k = 0; k < 3; ++k) {
@@ -226,23 +238,21 @@ __device__ void nh_hessian_blocks(const double* F, double lnJ, double mu, double
                 M[3 * i + j] += lm[k] * dm[j] * dn[i];
                 M[3 * j + i] += lm[k] * dm[i] * dn[j];
             }
-            double T[9];   // U M
+            R T[9];   // U M
             for (int a = 0; a < 3; ++a)
                 for (int s = 0; s < 3; ++s) T[3 * a + s] = U[3 * a] * M[s] + U[3 * a + 1] * M[3 + s] + U[3 * a + 2] * M[6 + s];
             for (int a = 0; a < 3; ++a)
-                for (int b = 0; b < 3; ++b) {
-                    const double v = vol * (T[3 * a] * U[3 * b] + T[3 * a + 1] * U[3 * b + 1] + T[3 * a + 2] * U[3 * b + 2]);
-                    out[(3 * m + a) * 12 + 3 * n + b] = v;
-                    if (n != m) out[(3 * n + b) * 12 + 3 * m + a] = v;
-                }
+                for (int b = 0; b < 3; ++b)
+                    out[9 * blk + 3 * a + b] = vol * (T[3 * a] * U[3 * b] + T[3 * a + 1] * U[3 * b + 1] + T[3 * a + 2] * U[3 * b + 2]);
         }
 }
 
-// energy, gradient [nt][12] and (WANT_HESS) PSD Hessian [nt][144] per tet
-template <bool WANT_HESS>
+// energy, gradient [nt][12] and (WANT_HESS) PSD Hessian [nt][90] (10 blocks,
+// precision TH) per tet
+template <bool WANT_HESS, class TH>
 __global__ void __launch_bounds__(128)
 k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
-          double* __restrict__ tG, double* __restrict__ tH, int32_t* __restrict__ bad) {
+          double* __restrict__ tG, TH* __restrict__ tH, int32_t* __restrict__ bad) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= E.nt) return;
     double x4[12], X4[12], F[9], lnJ, psi;
@@ -255,7 +265,7 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
         tE[t] = INFINITY;
         for (int q = 0; q < 12; ++q) tG[12 * t + q] = 0.0;
         if (WANT_HESS)
-            for (int q = 0; q < 144; ++q) tH[144 * t + q] = 0.0;
+            for (int q = 0; q < 90; ++q) tH[90 * t + q] = TH(0);
         return;
     }
     tE[t] = psi;
@@ -276,7 +286,7 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
             for (int j = 0; j < 3; ++j) s += P[3 * i + j] * D[3 * m + j];
             tG[12 * t + 3 * m + i] = vol * s;
         }
-    if (WANT_HESS) nh_hessian_blocks(F, lnJ, E.mu, E.lam, D, vol, tH + 144 * t);
+    if (WANT_HESS) nh_hessian_blocks<TH>(F, lnJ, E.mu, E.lam, D, vol, tH + 90 * t);
 }
 
 // elastic energies at x + alpha_j p for j < na (<= 8), layout [na][nt]
@@ -327,112 +337,245 @@ __global__ void k_assemble_grad(int64_t nv, const double* __restrict__ x, const 
     G[3 * v + 2] = m * (x[3 * v + 2] - xhat[3 * v + 2]) + h2 * (e2 + c2);
 }
 
-// A = M + h^2 (sum_tets H + contact H) block by block; a block in a
-// Dirichlet row or column is the identity on the diagonal and zero elsewhere
+// A = M + h^2 (sum_tets H + contact H) block by block in precision TA; a
+// block in a Dirichlet row or column is the identity on the diagonal and zero
+// elsewhere
+template <class TH, class TC, class TA>
 __global__ void k_assemble_bsr(int64_t nnzb, const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol,
                                const int32_t* __restrict__ bt_off, const int32_t* __restrict__ bt_ent,
-                               const double* __restrict__ tH, const int32_t* __restrict__ cmap,
-                               const void* __restrict__ cvals, int cvals_f32,
-                               const double* __restrict__ mass, const uint8_t* __restrict__ dir,
-                               double h2, double* __restrict__ A) {
+                               const TH* __restrict__ tH, const int32_t* __restrict__ cmap,
+                               const TC* __restrict__ cvals, const double* __restrict__ mass,
+                               const uint8_t* __restrict__ dir, double h2, TA* __restrict__ A) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nnzb) return;
     const int i = brow[b], j = bcol[b];
-    double* out = A + 9 * b;
+    TA* out = A + 9 * b;
     if (dir[i] || dir[j]) {
-        for (int q = 0; q < 9; ++q) out[q] = (i == j && (q == 0 || q == 4 || q == 8)) ? 1.0 : 0.0;
+        for (int q = 0; q < 9; ++q) out[q] = (i == j && (q == 0 || q == 4 || q == 8)) ? TA(1) : TA(0);
         return;
     }
-    double s[9];
-    for (int q = 0; q < 9; ++q) s[q] = 0.0;
+    TA s[9];
+    for (int q = 0; q < 9; ++q) s[q] = TA(0);
     for (int k = bt_off[b]; k < bt_off[b + 1]; ++k) {
         const int ent = bt_ent[k];
         const int64_t t = ent >> 4;
         const int ma = (ent >> 2) & 3, nb = ent & 3;
-        const double* H = tH + 144 * t;
-        for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q) s[3 * p + q] += H[(3 * ma + p) * 12 + 3 * nb + q];
+        if (ma <= nb) {
+            const TH* H = tH + 90 * t + 9 * (kTetBlk[ma] + nb - ma);
+            for (int q = 0; q < 9; ++q) s[q] += (TA)H[q];
+        } else {
+            const TH* H = tH + 90 * t + 9 * (kTetBlk[nb] + ma - nb);
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q) s[3 * p + q] += (TA)H[3 * q + p];
+        }
     }
     const int cb = cmap[b];
     if (cb >= 0) {
-        if (cvals_f32) {
-            const float* C = (const float*)cvals + 9 * (int64_t)cb;
-            for (int q = 0; q < 9; ++q) s[q] += (double)C[q];
-        } else {
-            const double* C = (const double*)cvals + 9 * (int64_t)cb;
-            for (int q = 0; q < 9; ++q) s[q] += C[q];
-        }
+        const TC* C = cvals + 9 * (int64_t)cb;
+        for (int q = 0; q < 9; ++q) s[q] += (TA)C[q];
     }
-    for (int q = 0; q < 9; ++q) out[q] = h2 * s[q];
-    if (i == j) { out[0] += mass[i]; out[4] += mass[i]; out[8] += mass[i]; }
+    const TA h2a = (TA)h2;
+    for (int q = 0; q < 9; ++q) out[q] = h2a * s[q];
+    if (i == j) {
+        const TA m = (TA)mass[i];
+        out[0] += m; out[4] += m; out[8] += m;
+    }
 }
 
 // ------------------------------------------------------------------ PCG ---
-__global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, const double* __restrict__ A,
+// Fused block-Jacobi PCG: three kernels per iteration; each dot product is
+// finished by the last block to arrive, which sums the per-block partials in
+// block order (deterministic).  Solver scalars (FP64):
+enum : int {
+    kRz0 = 0,        // r.z, double-buffered by iteration parity (slots 0, 1)
+    kPAp = 2, kRr = 3, kBb = 4,
+    kBreak = 5,      // p^T A p <= 0 seen
+    kDone = 6,       // converged
+    kIters = 7,      // iterations taken (valid once kBreak or kDone is set)
+    kThr = 8         // rel_tol |b|
+};
+constexpr int kPcgThreads = 256;
+
+__device__ __forceinline__ double block_sum256(double v, double* sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = threadIdx.x < kPcgThreads / 32 ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;   // valid in warp 0
+}
+
+// Each block contributes (v0, v1); returns true in the last block to
+// arrive, where thread 0 then holds the fixed-order totals in *t0, *t1.
+__device__ bool last_block_sums(double v0, double v1, double* part /* [2][gridDim] */, unsigned* counter,
+                                double* t0, double* t1) {
+    __shared__ double sh[kPcgThreads / 32];
+    __shared__ bool am_last;
+    const double b0 = block_sum256(v0, sh);
+    const double b1 = block_sum256(v1, sh);
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = b0;
+        part[gridDim.x + blockIdx.x] = b1;
+        __threadfence();
+        am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!am_last) return false;
+    __threadfence();
+    const volatile double* vp = part;
+    double s0 = 0.0, s1 = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += kPcgThreads) {
+        s0 += vp[k];
+        s1 += vp[gridDim.x + k];
+    }
+    *t0 = block_sum256(s0, sh);
+    *t1 = block_sum256(s1, sh);
+    if (threadIdx.x == 0) *counter = 0u;
+    return true;
+}
+
+__device__ __forceinline__ void mul33(const double* P, double r0, double r1, double r2, double* z) {
+    z[0] = P[0] * r0 + P[1] * r1 + P[2] * r2;
+    z[1] = P[3] * r0 + P[4] * r1 + P[5] * r2;
+    z[2] = P[6] * r0 + P[7] * r1 + P[8] * r2;
+}
+
+template <class TA>
+__global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, const TA* __restrict__ A,
                            double* __restrict__ Pinv) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
-    inv3(A + 9 * (int64_t)diag_blk[v], Pinv + 9 * v);
+    double D[9];
+    const TA* B = A + 9 * (int64_t)diag_blk[v];
+    for (int q = 0; q < 9; ++q) D[q] = (double)B[q];
+    inv3(D, Pinv + 9 * v);
 }
 
-// y = A x, one thread per block row
-__global__ void k_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                       const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y) {
+// x = 0, r = b, z = P^-1 b, p = z (and its FP32 copy); b.b and r.z
+__global__ void __launch_bounds__(kPcgThreads)
+k_pcg_init(int64_t nv, const double* __restrict__ Pinv, const double* __restrict__ bvec, double* __restrict__ x,
+           double* __restrict__ r, double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32,
+           double* part, unsigned* counter, double* scal, double rel_tol) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv) return;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; ++k) {
-        const double* B = A + 9 * (int64_t)k;
-        const int64_t j = ci[k];
-        const double x0 = x[3 * j], x1 = x[3 * j + 1], x2 = x[3 * j + 2];
-        a0 += B[0] * x0 + B[1] * x1 + B[2] * x2;
-        a1 += B[3] * x0 + B[4] * x1 + B[5] * x2;
-        a2 += B[6] * x0 + B[7] * x1 + B[8] * x2;
+    double bb = 0.0, rz = 0.0;
+    if (i < nv) {
+        const double b0 = bvec[3 * i], b1 = bvec[3 * i + 1], b2 = bvec[3 * i + 2];
+        double zz[3];
+        mul33(Pinv + 9 * i, b0, b1, b2, zz);
+        for (int q = 0; q < 3; ++q) {
+            x[3 * i + q] = 0.0;
+            r[3 * i + q] = bvec[3 * i + q];
+            z[3 * i + q] = zz[q];
+            p[3 * i + q] = zz[q];
+            if (p32) p32[3 * i + q] = (float)zz[q];
+        }
+        bb = b0 * b0 + b1 * b1 + b2 * b2;
+        rz = b0 * zz[0] + b1 * zz[1] + b2 * zz[2];
     }
-    y[3 * i] = a0; y[3 * i + 1] = a1; y[3 * i + 2] = a2;
+    double tb, tr;
+    if (last_block_sums(bb, rz, part, counter, &tb, &tr) && threadIdx.x == 0) {
+        scal[kBb] = tb;
+        scal[kRz0] = tr;
+        scal[kThr] = rel_tol * sqrt(tb);
+        scal[kBreak] = 0.0;
+        scal[kDone] = tb > 0.0 ? 0.0 : 1.0;
+        scal[kIters] = 0.0;
+    }
 }
 
-__global__ void k_precond(int64_t nv, const double* __restrict__ Pinv, const double* __restrict__ r,
-                          double* __restrict__ z) {
+// Ap = A p and p.Ap; one thread per (block row, component).  TA = float:
+// FP32 products of the FP32 matrix and the FP32 copy of p, FP32 row sums.
+template <class TA>
+__global__ void __launch_bounds__(kPcgThreads)
+k_pcg_spmv(int64_t nv, int it, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+           const TA* __restrict__ A, const double* __restrict__ p, const float* __restrict__ p32,
+           double* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
+    if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = tid / 3;
+    const int comp = (int)(tid - 3 * i);
+    double pap = 0.0;
+    if (i < nv) {
+        TA acc = TA(0);
+        for (int k = rp[i]; k < rp[i + 1]; ++k) {
+            const TA* B = A + 9 * (int64_t)k + 3 * comp;
+            const int64_t j = ci[k];
+            if (sizeof(TA) == 4)
+                acc += B[0] * (TA)p32[3 * j] + B[1] * (TA)p32[3 * j + 1] + B[2] * (TA)p32[3 * j + 2];
+            else
+                acc += B[0] * (TA)p[3 * j] + B[1] * (TA)p[3 * j + 1] + B[2] * (TA)p[3 * j + 2];
+        }
+        const double y = (double)acc;
+        Ap[3 * i + comp] = y;
+        pap = p[3 * i + comp] * y;
+    }
+    double t, unused;
+    if (last_block_sums(pap, 0.0, part, counter, &t, &unused) && threadIdx.x == 0) {
+        scal[kPAp] = t;
+        if (!(t > 0.0)) {
+            scal[kBreak] = 1.0;
+            scal[kIters] = (double)it;
+        }
+    }
+}
+
+// x += al p, r -= al Ap, z = P^-1 r, then r.r (convergence) and r.z
+__global__ void __launch_bounds__(kPcgThreads)
+k_pcg_update(int64_t nv, int it, const double* __restrict__ Pinv, double* __restrict__ x, double* __restrict__ r,
+             double* __restrict__ z, const double* __restrict__ p, const double* __restrict__ Ap, double* part,
+             unsigned* counter, double* scal) {
+    if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv) return;
-    const double* P = Pinv + 9 * i;
-    const double r0 = r[3 * i], r1 = r[3 * i + 1], r2 = r[3 * i + 2];
-    z[3 * i] = P[0] * r0 + P[1] * r1 + P[2] * r2;
-    z[3 * i + 1] = P[3] * r0 + P[4] * r1 + P[5] * r2;
-    z[3 * i + 2] = P[6] * r0 + P[7] * r1 + P[8] * r2;
+    const double al = scal[kRz0 + (it & 1)] / scal[kPAp];
+    double rr = 0.0, rz = 0.0;
+    if (i < nv) {
+        double rv[3];
+        for (int q = 0; q < 3; ++q) {
+            x[3 * i + q] += al * p[3 * i + q];
+            rv[q] = r[3 * i + q] - al * Ap[3 * i + q];
+            r[3 * i + q] = rv[q];
+        }
+        double zz[3];
+        mul33(Pinv + 9 * i, rv[0], rv[1], rv[2], zz);
+        for (int q = 0; q < 3; ++q) z[3 * i + q] = zz[q];
+        rr = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+        rz = rv[0] * zz[0] + rv[1] * zz[1] + rv[2] * zz[2];
+    }
+    double trr, trz;
+    if (last_block_sums(rr, rz, part, counter, &trr, &trz) && threadIdx.x == 0) {
+        scal[kRr] = trr;
+        if (sqrt(trr) <= scal[kThr]) {
+            scal[kDone] = 1.0;
+            scal[kIters] = (double)(it + 1);
+        } else {
+            scal[kRz0 + ((it + 1) & 1)] = trz;
+        }
+    }
+}
+
+// p = z + (rz_new / rz_old) p
+__global__ void __launch_bounds__(kPcgThreads)
+k_pcg_dir(int64_t n, int it, const double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32,
+          const double* scal) {
+    if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double be = scal[kRz0 + ((it + 1) & 1)] / scal[kRz0 + (it & 1)];
+    const double v = z[i] + be * p[i];
+    p[i] = v;
+    if (p32) p32[i] = (float)v;
 }
 
 // elementwise products into w (for a fixed-order dot product)
 __global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ w) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) w[i] = a[i] * b[i];
-}
-
-// p = z + (rz_new / rz_old) p
-__global__ void k_cg_dir(int64_t n, const double* __restrict__ scal, const double* __restrict__ z,
-                         double* __restrict__ p) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double be = scal[2] / scal[0];
-    p[i] = z[i] + be * p[i];
-}
-
-__global__ void k_copy_scal(double* __restrict__ scal, int dst, int src) { scal[dst] = scal[src]; }
-
-// x += al p; r -= al Ap, unless p^T A p <= 0 (then flag scal[5] and keep x)
-__global__ void k_cg_update_guarded(int64_t n, double* __restrict__ scal, double* __restrict__ x,
-                                    double* __restrict__ r, const double* __restrict__ p,
-                                    const double* __restrict__ Ap) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (!(scal[1] > 0.0)) {
-        if (i == 0) scal[5] = 1.0;
-        return;
-    }
-    if (i >= n) return;
-    const double al = scal[0] / scal[1];
-    x[i] += al * p[i];
-    r[i] -= al * Ap[i];
 }
 
 // inertia terms 1/2 m |x + a_j p - xhat|^2 per vertex, layout [na][nv]
@@ -518,10 +661,14 @@ cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev,
     NewtonState& N = *c.newton;
     ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, c.X.p, N.mu, N.lam};
     if (c.nt == 0) return cudaSuccess;
-    if (want_hess)
-        k_nh_eval<true><<<nblk(c.nt, 128), 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH.p, bad);
+    const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    const unsigned g = nblk(c.nt, 128);
+    if (!want_hess)
+        k_nh_eval<false, double><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, nullptr, bad);
+    else if (f32)
+        k_nh_eval<true, float><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH32.p, bad);
     else
-        k_nh_eval<false><<<nblk(c.nt, 128), 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH.p, bad);
+        k_nh_eval<true, double><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH64.p, bad);
     GMCP_CUDA_TRY(cudaGetLastError());
     return reduce_sum(c, N.tE.p, c.nt, energy_dev);
 }
@@ -549,11 +696,15 @@ cudaError_t assemble_grad(Ctx& c, const double* x, const double* xhat, const voi
 cudaError_t assemble_bsr(Ctx& c) {
     NewtonState& N = *c.newton;
     const double h2 = c.prm.h * c.prm.h;
-    const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    const void* cv = f32 ? (const void*)c.cb_val32.p : (const void*)c.cb_val64.p;
-    k_assemble_bsr<<<nblk(N.nnzb, 256), 256, 0, c.stream>>>(N.nnzb, N.brow.p, N.bcol.p, N.bt_off.p, N.bt.p,
-                                                           N.tH.p, N.cmap.p, cv, f32 ? 1 : 0, N.mass.p,
-                                                           N.dir.p, h2, N.A.p);
+    const unsigned g = nblk(N.nnzb, 256);
+    if (c.P.precision == IPC_PREC_MIXED)
+        k_assemble_bsr<float, float, float><<<g, 256, 0, c.stream>>>(N.nnzb, N.brow.p, N.ci.p, N.bt_off.p, N.bt.p,
+                                                                    N.tH32.p, N.cmap.p, c.cb_val32.p, N.mass.p,
+                                                                    N.dir.p, h2, N.A32.p);
+    else
+        k_assemble_bsr<double, double, double><<<g, 256, 0, c.stream>>>(N.nnzb, N.brow.p, N.ci.p, N.bt_off.p,
+                                                                       N.bt.p, N.tH64.p, N.cmap.p, c.cb_val64.p,
+                                                                       N.mass.p, N.dir.p, h2, N.A64.p);
     return cudaGetLastError();
 }
 
@@ -565,51 +716,48 @@ cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double*
     return reduce_sum(c, N.w.p, n, out);
 }
 
-// Block-Jacobi PCG for A p = b (A = N.A on the pattern N.rp / N.ci), p = 0
-// start; stops at ||r|| <= rel_tol ||b||, at p^T A p <= 0 or after max_it
-// iterations.  One host readback per iteration.  Returns the iterations.
+// Block-Jacobi PCG for A p = b (A on the pattern N.rp / N.ci; FP32 in the
+// mixed path, FP64 otherwise), p = 0 start; stops at ||r|| <= rel_tol ||b||,
+// at p^T A p <= 0 (that iteration's update is skipped) or after max_it
+// iterations.  The host reads the flags once per 16 iterations; kernels
+// after the stop return at once.  Returns the iterations taken.
 cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters) {
     NewtonState& N = *c.newton;
-    const int64_t n = 3 * c.nv;
+    const int64_t nv = c.nv, n = 3 * nv;
     cudaStream_t s = c.stream;
-    double* r = N.r.p; double* z = N.z.p; double* p = N.p.p; double* Ap = N.Ap.p;
-    double* sc = N.scal.p;   // [0] rz  [1] pAp  [2] rz_new  [3] rr  [4] bb  [5] breakdown flag
+    const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    double* sc = N.scal.p;
     double* hb = c.h_scalars;
-    *iters = 0;
-    GMCP_CUDA_TRY(cudaMemsetAsync(xout, 0, sizeof(double) * n, s));
-    GMCP_CUDA_TRY(cudaMemsetAsync(sc, 0, 8 * sizeof(double), s));
-    GMCP_CUDA_TRY(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    k_diag_inv<<<nblk(c.nv, 256), 256, 0, s>>>(c.nv, N.diag.p, N.A.p, N.Pinv.p);
+    float* p32 = f32 ? N.p32.p : nullptr;
+    if (f32) k_diag_inv<float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A32.p, N.Pinv.p);
+    else k_diag_inv<double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A64.p, N.Pinv.p);
     GMCP_CUDA_TRY(cudaGetLastError());
-    GMCP_CUDA_TRY(dot_dev(c, b, b, n, sc + 4));
-    GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 4, sizeof(double), cudaMemcpyDeviceToHost, s));
-    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-    const double bn = sqrt(hb[0]);
-    if (!(bn > 0.0)) return cudaSuccess;
-    k_precond<<<nblk(c.nv, 256), 256, 0, s>>>(c.nv, N.Pinv.p, r, z);
+    const unsigned g_row = nblk(nv, kPcgThreads), g_comp = nblk(n, kPcgThreads);
+    k_pcg_init<<<g_row, kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, N.r.p, N.z.p, N.p.p, p32, N.part.p,
+                                             N.counters.p, sc, rel_tol);
     GMCP_CUDA_TRY(cudaGetLastError());
-    GMCP_CUDA_TRY(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    GMCP_CUDA_TRY(dot_dev(c, r, z, n, sc + 0));
-    int it = 0;
-    for (it = 0; it < max_it; ++it) {
-        k_spmv<<<nblk(c.nv, 128), 128, 0, s>>>(c.nv, N.rp.p, N.ci.p, N.A.p, p, Ap);
+    *iters = max_it;
+    for (int it = 0; it < max_it;) {
+        const int chunk = std::min(16, max_it - it);
+        for (int j = 0; j < chunk; ++j, ++it) {
+            if (f32)
+                k_pcg_spmv<float><<<g_comp, kPcgThreads, 0, s>>>(nv, it, N.rp.p, N.ci.p, N.A32.p, N.p.p, p32, N.Ap.p,
+                                                                 N.part.p, N.counters.p + 1, sc);
+            else
+                k_pcg_spmv<double><<<g_comp, kPcgThreads, 0, s>>>(nv, it, N.rp.p, N.ci.p, N.A64.p, N.p.p, p32,
+                                                                  N.Ap.p, N.part.p, N.counters.p + 1, sc);
+            k_pcg_update<<<g_row, kPcgThreads, 0, s>>>(nv, it, N.Pinv.p, xout, N.r.p, N.z.p, N.p.p, N.Ap.p,
+                                                       N.part.p, N.counters.p + 2, sc);
+            k_pcg_dir<<<g_comp, kPcgThreads, 0, s>>>(n, it, N.z.p, N.p.p, p32, sc);
+        }
         GMCP_CUDA_TRY(cudaGetLastError());
-        GMCP_CUDA_TRY(dot_dev(c, p, Ap, n, sc + 1));
-        k_cg_update_guarded<<<nblk(n, 256), 256, 0, s>>>(n, sc, xout, r, p, Ap);
-        GMCP_CUDA_TRY(cudaGetLastError());
-        GMCP_CUDA_TRY(dot_dev(c, r, r, n, sc + 3));
-        GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 3, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + kBreak, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
         GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-        if (hb[2] != 0.0) break;                      // p^T A p <= 0: x unchanged
-        if (sqrt(hb[0]) <= rel_tol * bn) { ++it; break; }
-        k_precond<<<nblk(c.nv, 256), 256, 0, s>>>(c.nv, N.Pinv.p, r, z);
-        GMCP_CUDA_TRY(cudaGetLastError());
-        GMCP_CUDA_TRY(dot_dev(c, r, z, n, sc + 2));
-        k_cg_dir<<<nblk(n, 256), 256, 0, s>>>(n, sc, z, p);
-        k_copy_scal<<<1, 1, 0, s>>>(sc, 0, 2);
-        GMCP_CUDA_TRY(cudaGetLastError());
+        if (hb[0] != 0.0 || hb[1] != 0.0) {
+            *iters = (int)hb[2];
+            break;
+        }
     }
-    *iters = it;
     return cudaSuccess;
 }
 
@@ -652,50 +800,7 @@ cudaError_t newton_setup(Ctx& c) {
         for (int a = 0; a < 4; ++a) mass[Tt[a]] += q.density * vol[t] / 4.0;
     }
     N.lbar = nt > 0 ? cbrt(vsum / (double)nt) : 0.0;
-    // block pattern: diagonal, tet adjacency, contact pattern
-    std::vector<int64_t> keys;
-    keys.reserve((size_t)nv + 16 * (size_t)nt + c.h_cb_col.size());
-    auto key = [nv](int64_t i, int64_t j) { return i * nv + j; };
-    for (int64_t v = 0; v < nv; ++v) keys.push_back(key(v, v));
-    for (int64_t t = 0; t < nt; ++t)
-        for (int a = 0; a < 4; ++a)
-            for (int b = 0; b < 4; ++b)
-                if (a != b) keys.push_back(key(T[4 * t + a], T[4 * t + b]));
-    for (int64_t i = 0; i < nv; ++i)
-        for (int k = c.h_cb_row[i]; k < c.h_cb_row[i + 1]; ++k) keys.push_back(key(i, c.h_cb_col[k]));
-    std::sort(keys.begin(), keys.end());
-    keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-    const int64_t nnzb = (int64_t)keys.size();
-    if (nnzb >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
-    N.nnzb = nnzb;
-    std::vector<int32_t> rp(nv + 1, 0), ci(nnzb), brow(nnzb), diag(nv);
-    for (int64_t k = 0; k < nnzb; ++k) {
-        brow[k] = (int32_t)(keys[k] / nv);
-        ci[k] = (int32_t)(keys[k] % nv);
-        rp[brow[k] + 1]++;
-        if (brow[k] == ci[k]) diag[brow[k]] = (int32_t)k;
-    }
-    for (int64_t v = 0; v < nv; ++v) rp[v + 1] += rp[v];
-    auto find = [&](int64_t i, int64_t j) -> int64_t {
-        auto it = std::lower_bound(keys.begin() + rp[i], keys.begin() + rp[i + 1], key(i, j));
-        return (it != keys.begin() + rp[i + 1] && *it == key(i, j)) ? (int64_t)(it - keys.begin()) : -1;
-    };
-    // per-block tet contributions in increasing (tet, a, b)
-    std::vector<int32_t> bt_off(nnzb + 1, 0), bt(16 * (size_t)nt);
-    std::vector<int64_t> tb(16 * (size_t)nt);
-    for (int64_t t = 0; t < nt; ++t)
-        for (int a = 0; a < 4; ++a)
-            for (int b = 0; b < 4; ++b) {
-                const int64_t k = find(T[4 * t + a], T[4 * t + b]);
-                tb[16 * t + 4 * a + b] = k;
-                bt_off[k + 1]++;
-            }
-    for (int64_t k = 0; k < nnzb; ++k) bt_off[k + 1] += bt_off[k];
-    {
-        std::vector<int32_t> cur(bt_off.begin(), bt_off.end() - 1);
-        for (int64_t e = 0; e < 16 * nt; ++e) bt[cur[tb[e]]++] = (int32_t)e;
-    }
-    // vertex -> tet corner, increasing tet
+    // vertex -> tet corner (t*4+a), increasing tet
     std::vector<int32_t> vte_off(nv + 1, 0), vte(4 * (size_t)nt);
     for (int64_t e = 0; e < 4 * nt; ++e) vte_off[T[e] + 1]++;
     for (int64_t v = 0; v < nv; ++v) vte_off[v + 1] += vte_off[v];
@@ -703,10 +808,57 @@ cudaError_t newton_setup(Ctx& c) {
         std::vector<int32_t> cur(vte_off.begin(), vte_off.end() - 1);
         for (int64_t e = 0; e < 4 * nt; ++e) vte[cur[T[e]]++] = (int32_t)e;
     }
+    // block pattern, row by row: the diagonal, every vertex sharing a tet, and
+    // the contact pattern; tb[16 t + 4 a + b] = index of block (T[a], T[b])
+    std::vector<int32_t> rp(nv + 1, 0), ci, brow;
+    std::vector<int64_t> tb(16 * (size_t)nt);
+    ci.reserve(16 * (size_t)nv);
+    brow.reserve(16 * (size_t)nv);
+    std::vector<int32_t> row;
+    for (int64_t i = 0; i < nv; ++i) {
+        row.clear();
+        row.push_back((int32_t)i);
+        for (int k = vte_off[i]; k < vte_off[i + 1]; ++k) {
+            const int64_t t = vte[k] >> 2;
+            for (int q = 0; q < 4; ++q) row.push_back(T[4 * t + q]);
+        }
+        for (int k = c.h_cb_row[i]; k < c.h_cb_row[i + 1]; ++k) row.push_back(c.h_cb_col[k]);
+        std::sort(row.begin(), row.end());
+        row.erase(std::unique(row.begin(), row.end()), row.end());
+        const int64_t base = (int64_t)ci.size();
+        if (base + (int64_t)row.size() >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+        ci.insert(ci.end(), row.begin(), row.end());
+        brow.insert(brow.end(), row.size(), (int32_t)i);
+        rp[i + 1] = (int32_t)ci.size();
+        for (int k = vte_off[i]; k < vte_off[i + 1]; ++k) {
+            const int64_t t = vte[k] >> 2;
+            const int a = vte[k] & 3;
+            for (int q = 0; q < 4; ++q) {
+                const int64_t pos = std::lower_bound(row.begin(), row.end(), T[4 * t + q]) - row.begin();
+                tb[16 * t + 4 * a + q] = base + pos;
+            }
+        }
+    }
+    const int64_t nnzb = (int64_t)ci.size();
+    N.nnzb = nnzb;
+    std::vector<int32_t> diag(nv);
+    for (int64_t i = 0; i < nv; ++i)
+        diag[i] = (int32_t)(std::lower_bound(ci.begin() + rp[i], ci.begin() + rp[i + 1], (int32_t)i) - ci.begin());
+    // per-block tet contributions in increasing (tet, a, b)
+    std::vector<int32_t> bt_off(nnzb + 1, 0), bt(16 * (size_t)nt);
+    for (int64_t e = 0; e < 16 * nt; ++e) bt_off[tb[e] + 1]++;
+    for (int64_t k = 0; k < nnzb; ++k) bt_off[k + 1] += bt_off[k];
+    {
+        std::vector<int32_t> cur(bt_off.begin(), bt_off.end() - 1);
+        for (int64_t e = 0; e < 16 * nt; ++e) bt[cur[tb[e]]++] = (int32_t)e;
+    }
     // global block -> contact block
     std::vector<int32_t> cmap(nnzb, -1);
     for (int64_t i = 0; i < nv; ++i)
-        for (int k = c.h_cb_row[i]; k < c.h_cb_row[i + 1]; ++k) cmap[find(i, c.h_cb_col[k])] = k;
+        for (int k = c.h_cb_row[i]; k < c.h_cb_row[i + 1]; ++k) {
+            const int64_t pos = std::lower_bound(ci.begin() + rp[i], ci.begin() + rp[i + 1], c.h_cb_col[k]) - ci.begin();
+            cmap[pos] = k;
+        }
 
     const size_t n3 = 3 * (size_t)nv;
     GMCP_CUDA_TRY(N.tets.upload(T, 4 * (size_t)nt, s));
@@ -719,20 +871,29 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.rp.upload(rp.data(), rp.size(), s));
     GMCP_CUDA_TRY(N.ci.upload(ci.data(), ci.size(), s));
     GMCP_CUDA_TRY(N.brow.upload(brow.data(), brow.size(), s));
-    GMCP_CUDA_TRY(N.bcol.upload(ci.data(), ci.size(), s));
     GMCP_CUDA_TRY(N.diag.upload(diag.data(), diag.size(), s));
     GMCP_CUDA_TRY(N.bt_off.upload(bt_off.data(), bt_off.size(), s));
     GMCP_CUDA_TRY(N.bt.upload(bt.data(), bt.size(), s));
     GMCP_CUDA_TRY(N.cmap.upload(cmap.data(), cmap.size(), s));
     GMCP_CUDA_TRY(N.tE.ensure((size_t)nt + 1));
     GMCP_CUDA_TRY(N.tG.ensure(12 * (size_t)nt + 12));
-    GMCP_CUDA_TRY(N.tH.ensure(144 * (size_t)nt + 144));
+    const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    if (f32) GMCP_CUDA_TRY(N.tH32.ensure(90 * (size_t)nt + 90));
+    else GMCP_CUDA_TRY(N.tH64.ensure(90 * (size_t)nt + 90));
     GMCP_CUDA_TRY(N.tE8.ensure(8 * (size_t)nt + 8));
-    GMCP_CUDA_TRY(N.A.ensure(9 * (size_t)nnzb));
+    if (f32) {
+        GMCP_CUDA_TRY(N.A32.ensure(9 * (size_t)nnzb));
+        GMCP_CUDA_TRY(N.p32.ensure(3 * (size_t)nv));
+    } else {
+        GMCP_CUDA_TRY(N.A64.ensure(9 * (size_t)nnzb));
+    }
+    GMCP_CUDA_TRY(N.part.ensure(2 * (size_t)nblk(3 * nv, 256) + 2));
+    GMCP_CUDA_TRY(N.counters.ensure(4));
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.counters.p, 0, 4 * sizeof(unsigned), s));
     GMCP_CUDA_TRY(N.Pinv.ensure(9 * (size_t)nv));
     for (DBuf<double>* b : {&N.r, &N.z, &N.p, &N.Ap, &N.w, &N.xhat, &N.xt, &N.G, &N.dirn, &N.tmp, &N.P, &N.dP, &N.xi})
         GMCP_CUDA_TRY(b->ensure(n3));
-    if (c.P.precision == IPC_PREC_MIXED) GMCP_CUDA_TRY(N.cgrad32.ensure(n3));
+    if (f32) GMCP_CUDA_TRY(N.cgrad32.ensure(n3));
     else GMCP_CUDA_TRY(N.cgrad64.ensure(n3));
     GMCP_CUDA_TRY(N.xm.ensure(3 * (size_t)c.nmv + 3));
     GMCP_CUDA_TRY(N.dxm.ensure(3 * (size_t)c.nmv + 3));
