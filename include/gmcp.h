@@ -293,6 +293,72 @@ ipc_status ipc_accd_min_noalloc(ipc_ctx* ctx, const double* x_dev, const double*
                                 const double* xm0_dev, const double* xm1_dev,
                                 double* alpha_accd_host, int64_t* n_pairs_host);
 
+/* ---------------------------------------------------------------------- */
+/* Learned warm start.  The paper has no learned component; this follows
+ * the project's own design: a per-vertex network 32-256-256-256-3 (affine
+ * layers, ReLU between them) predicts the correction of the plain
+ * predictor,
+ *   dx_pred = h v + disp_scale * y(features),
+ * and ipc_newton_step admits dx_pred only through its CCD-filtered start
+ * (so intersection-freedom never depends on the network).  Weights are kept
+ * in FP32 (Adam's master copy) with BF16 copies for the tensor cores; every
+ * matrix product has BF16 operands and FP32 accumulation.  Parameters are a
+ * flattened FP32 vector of IPC_WS_NPARAM values: W1 [256][32], b1 [256],
+ * W2 [256][256], b2, W3 [256][256], b3, W4 [3][256], b4 [3] (row-major).
+ *
+ * Features (BF16 [n][32] per pad vertex): (x - X)/pos_scale, h v /
+ * disp_scale, the rest position mapped to [-1, 1] over the pad's box, the
+ * Dirichlet and slave-surface flags, the contact force at x (the negative
+ * barrier gradient of the contact pass) / force_scale clamped to +-8, a
+ * contact-active flag, sin and cos of pi k Xn (k = 1, 2) per axis, zeros. */
+#define IPC_WS_NPARAM 140803
+
+typedef struct {
+    const float* params_host;   /* [IPC_WS_NPARAM] initial parameters */
+    double lr, beta1, beta2, eps;   /* Adam */
+    double pos_scale;           /* m: displacement feature scale */
+    double disp_scale;          /* m: per-step displacement scale (features and output) */
+    double force_scale;         /* N: contact-force feature scale */
+} ipc_ws_params;
+
+/* Create (or replace) the network of the context.  Allocates activations for
+ * every pad vertex (about 3 KB per vertex). */
+ipc_status ipc_ws_create(ipc_ctx* ctx, const ipc_ws_params* params);
+
+/* Features of state (x_dev, v_dev) with the master at xm_dev (device, FP64
+ * [n][3]); runs a contact pass at (x, xm) for the contact force.  They are
+ * kept in the context for the next ipc_ws_forward / ipc_ws_grads /
+ * ipc_ws_train_step called with feats_dev == NULL; feats_dev (device, may
+ * be NULL) also receives a copy, BF16 [n][32].  Synchronises. */
+ipc_status ipc_ws_features(ipc_ctx* ctx, const double* x_dev, const double* v_dev, const double* xm_dev,
+                           void* feats_dev);
+
+/* Network output y (device FP32 [n][3]) for features feats_dev (BF16
+ * [n][32]; NULL = the context's last features).  Synchronises. */
+ipc_status ipc_ws_forward(ipc_ctx* ctx, const void* feats_dev, float* out_dev);
+
+/* Loss sum_v m_v |y_v - t_v|^2 / (3 sum_v m_v) for target_dev (FP32 [n][3])
+ * and mask_dev (FP32 [n], per-vertex weights), and its gradient with respect
+ * to the parameters (grads_host, FP32 [IPC_WS_NPARAM], may be NULL), without
+ * updating anything.  Synchronises. */
+ipc_status ipc_ws_grads(ipc_ctx* ctx, const void* feats_dev, const float* target_dev, const float* mask_dev,
+                        double* loss_host, float* grads_host);
+
+/* One training step: the loss and gradient of ipc_ws_grads, then one Adam
+ * update (bias-corrected) of the FP32 parameters and of their BF16 copies.
+ * loss_host (may be NULL) receives the loss before the update.  Synchronises. */
+ipc_status ipc_ws_train_step(ipc_ctx* ctx, const void* feats_dev, const float* target_dev,
+                             const float* mask_dev, double* loss_host);
+
+/* Copy the FP32 parameters to params_host [IPC_WS_NPARAM].  Synchronises. */
+ipc_status ipc_ws_get_params(ipc_ctx* ctx, float* params_host);
+
+/* Predicted displacement dx_dev (device FP64 [n][3]) = h v + disp_scale *
+ * y(features(x, v, xm)), the dx_pred argument of ipc_newton_step.
+ * Synchronises.  IPC_ERR_TIMEOUT if a tensor-core wait reached its cap. */
+ipc_status ipc_ws_predict(ipc_ctx* ctx, const double* x_dev, const double* v_dev, const double* xm_dev,
+                          double* dx_dev);
+
 #ifdef __cplusplus
 }
 #endif

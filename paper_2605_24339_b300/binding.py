@@ -77,6 +77,15 @@ class StepStats(C.Structure):
                 ("energy", C.c_double), ("ms_total", C.c_double)]
 
 
+class WsParams(C.Structure):
+    _fields_ = [("params_host", C.c_void_p), ("lr", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("pos_scale", C.c_double),
+                ("disp_scale", C.c_double), ("force_scale", C.c_double)]
+
+
+WS_NPARAM = 140803
+
+
 # ipc_status values a time step may end with without a programming error
 STEP_INFEASIBLE, STEP_NOT_CONVERGED, STEP_LINESEARCH = 4, 6, 7
 
@@ -119,6 +128,20 @@ def lib():
                                    C.POINTER(C.c_double), C.POINTER(CcdInfo), C.POINTER(SampleCounts)]
     L.ipc_profile.restype = C.c_int
     L.ipc_profile.argtypes = [P, C.c_int32, C.c_int32, P, P, P, C.POINTER(C.c_int32)]
+    L.ipc_ws_create.restype = C.c_int
+    L.ipc_ws_create.argtypes = [P, C.POINTER(WsParams)]
+    L.ipc_ws_features.restype = C.c_int
+    L.ipc_ws_features.argtypes = [P, P, P, P, P]
+    L.ipc_ws_forward.restype = C.c_int
+    L.ipc_ws_forward.argtypes = [P, P, P]
+    L.ipc_ws_grads.restype = C.c_int
+    L.ipc_ws_grads.argtypes = [P, P, P, P, C.POINTER(C.c_double), P]
+    L.ipc_ws_train_step.restype = C.c_int
+    L.ipc_ws_train_step.argtypes = [P, P, P, P, C.POINTER(C.c_double)]
+    L.ipc_ws_get_params.restype = C.c_int
+    L.ipc_ws_get_params.argtypes = [P, P]
+    L.ipc_ws_predict.restype = C.c_int
+    L.ipc_ws_predict.argtypes = [P, P, P, P, P]
     L.ipc_newton_step.restype = C.c_int
     L.ipc_newton_step.argtypes = [P, P, P, P, P, C.POINTER(StepStats)]
     _lib = L
@@ -364,3 +387,73 @@ class Context:
         return dict(status=r, newton_iters=st.newton_iters, pcg_iters=st.pcg_iters_total,
                     halvings=st.line_search_halvings, residual=st.residual, res0=st.res0,
                     alpha0=st.alpha0, last_alpha=st.last_alpha, energy=st.energy, ms=st.ms_total)
+
+    # -- learned warm start -------------------------------------------------
+    def ws_create(self, params, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, pos_scale=1e-3,
+                  disp_scale=1e-5, force_scale=1e-3):
+        """Network with the flattened FP32 parameters ``params`` (length
+        WS_NPARAM: W1 b1 W2 b2 W3 b3 W4 b4, row-major)."""
+        p = np.ascontiguousarray(params, dtype=np.float32).ravel()
+        if p.size != WS_NPARAM:
+            raise ValueError(f"expected {WS_NPARAM} parameters, got {p.size}")
+        self._ws_keep = p
+        w = WsParams(p.ctypes.data, lr, beta1, beta2, eps, pos_scale, disp_scale, force_scale)
+        self._check(lib().ipc_ws_create(self.h, C.byref(w)))
+        self.ws_disp_scale = disp_scale
+
+    def ws_features(self, x, v, xm):
+        t = self.torch
+        x, v, xm = self._as(x), self._as(v), self._as(xm)
+        f = t.empty((self.nv, 32), dtype=t.bfloat16, device=self.device)
+        self._check(lib().ipc_ws_features(self.h, _ptr(x), _ptr(v), _ptr(xm), _ptr(f)))
+        return f
+
+    def _feats(self, feats):
+        t = self.torch
+        if feats is None:
+            return None
+        if feats.dtype != t.bfloat16 or not feats.is_cuda or feats.shape != (self.nv, 32):
+            raise TypeError("features must be a CUDA bfloat16 tensor [n_vert, 32]")
+        return feats.contiguous()
+
+    def _f32(self, a, shape):
+        t = self.torch
+        a = t.as_tensor(a).to(device=self.device, dtype=t.float32).contiguous()
+        if tuple(a.shape) != shape:
+            raise ValueError(f"expected shape {shape}, got {tuple(a.shape)}")
+        return a
+
+    def ws_forward(self, feats=None):
+        t = self.torch
+        f = self._feats(feats)
+        y = t.empty((self.nv, 3), dtype=t.float32, device=self.device)
+        self._check(lib().ipc_ws_forward(self.h, _ptr(f), _ptr(y)))
+        return y
+
+    def ws_grads(self, feats, target, mask):
+        f = self._feats(feats)
+        tg, mk = self._f32(target, (self.nv, 3)), self._f32(mask, (self.nv,))
+        loss = C.c_double()
+        g = np.zeros(WS_NPARAM, dtype=np.float32)
+        self._check(lib().ipc_ws_grads(self.h, _ptr(f), _ptr(tg), _ptr(mk), C.byref(loss),
+                                       g.ctypes.data))
+        return loss.value, g
+
+    def ws_train_step(self, feats, target, mask):
+        f = self._feats(feats)
+        tg, mk = self._f32(target, (self.nv, 3)), self._f32(mask, (self.nv,))
+        loss = C.c_double()
+        self._check(lib().ipc_ws_train_step(self.h, _ptr(f), _ptr(tg), _ptr(mk), C.byref(loss)))
+        return loss.value
+
+    def ws_params(self):
+        out = np.zeros(WS_NPARAM, dtype=np.float32)
+        self._check(lib().ipc_ws_get_params(self.h, out.ctypes.data))
+        return out
+
+    def ws_predict(self, x, v, xm):
+        t = self.torch
+        x, v, xm = self._as(x), self._as(v), self._as(xm)
+        dx = t.empty((self.nv, 3), dtype=t.float64, device=self.device)
+        self._check(lib().ipc_ws_predict(self.h, _ptr(x), _ptr(v), _ptr(xm), _ptr(dx)))
+        return dx

@@ -209,6 +209,9 @@ struct NewtonState {
     DBuf<int32_t> bad;                   // inverted-tet flag
 };
 
+struct WarmStart;              // learned warm start (warmstart.cu)
+void ws_destroy(WarmStart* w);
+
 // ------------------------------------------------------------------------
 // the context
 // ------------------------------------------------------------------------
@@ -278,6 +281,7 @@ struct Ctx {
     std::vector<double> h_X;
     std::vector<int32_t> h_cb_row, h_cb_col;
     std::unique_ptr<NewtonState> newton;
+    std::unique_ptr<WarmStart, void (*)(WarmStart*)> ws{nullptr, ws_destroy};
 
     SceneView view() const;
     CandView cand() {
@@ -350,6 +354,8 @@ cudaError_t vec_free_delta(Ctx& c, const double* P, const double* xi, double* dP
 cudaError_t vec_zero_dir(Ctx& c, double* p);
 cudaError_t vec_velocity(Ctx& c, const double* x, const double* xt, double* v);
 cudaError_t vec_neg(Ctx& c, int64_t n, const double* a, double* out);
+// api.cu: the context behind an ABI handle
+Ctx& ctx_of(ipc_ctx* h);
 
 }  // namespace gmcp
 

@@ -1,0 +1,900 @@
+// warmstart.cu -- the learned warm start: a per-vertex MLP 32-256-256-256-3
+// (ReLU) that predicts the correction of the plain predictor,
+//   x^{t+1} ~ x^t + h v^t + s * y(features),
+// trained on states the solver produces.  The two dense contractions per
+// layer run on the 5th-generation tensor cores:
+//   activations  C[m, n] = A[m, :] . W[n, :]   (M = vertices, N = 256, K = 32 | 256)
+//   weight grads dW[o, i] = sum_m dZ[m, o] H[m, i]  (M = 256, N = 256 | 32, K = vertices)
+// as tcgen05.mma kind::f16 (BF16 operands in shared memory, FP32 accumulators
+// in tensor memory), issued by one thread, completion signalled through an
+// mbarrier, accumulators read back with tcgen05.ld.  Operand tiles use the
+// no-swizzle K-major canonical layout: 8 x 16-byte core matrices, K-adjacent
+// core matrices 128 B apart (leading byte offset), 8-row groups (K/8) * 128 B
+// apart (stride byte offset).  The 256 -> 3 head, bias sums and Adam run on
+// the CUDA cores.  Every sum is in a fixed order, so training is deterministic.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gmcp_internal.cuh"
+
+namespace gmcp {
+
+struct WarmStart {
+    int64_t n = 0, mp = 0;                 // vertices, padded to a multiple of 128
+    double lr = 1e-3, beta1 = 0.9, beta2 = 0.999, eps = 1e-8;
+    double pos_scale = 1, disp_scale = 1, force_scale = 1;
+    double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+    int64_t step = 0;
+    // parameters: FP32 master copies, Adam moments, BF16 copies for the
+    // tensor cores (W and W^T)
+    DBuf<float> P, M1, M2, G;              // flattened [W1 b1 W2 b2 W3 b3 W4 b4]
+    DBuf<__nv_bfloat16> W1, W2, W3, W2t, W3t;
+    // activations
+    DBuf<__nv_bfloat16> f, fT, h1, h2, h3, h1T, h2T, dz3, dz3T, dz2, dz2T, dz1T;
+    DBuf<float> y, dy, part;              // FP32 partial sums (split-K weight gradients, head)
+    DBuf<double> dpart;                   // FP64 per-block partial sums (mask, loss)
+    DBuf<uint8_t> surf;
+    DBuf<double> cgrad64;
+    DBuf<float> cgrad32;
+    DBuf<int> err;
+    DBuf<double> scal;
+};
+
+namespace {
+
+constexpr int kHid = 256, kIn = 32, kOut = 3;
+// offsets into the flattened parameter vector
+constexpr int64_t kOffW1 = 0, kOffB1 = kOffW1 + kHid * kIn, kOffW2 = kOffB1 + kHid,
+                  kOffB2 = kOffW2 + kHid * kHid, kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid,
+                  kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kOut * kHid, kNParam = kOffB4 + kOut;
+
+// ------------------------------------------------------------- tcgen05 ---
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// shared-memory matrix descriptor: start address, leading / stride byte
+// offsets (all >> 4), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(mbar)));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+}
+// bounded wait on an mbarrier phase; false when the limit is reached
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t phase) {
+    const uint32_t a = smem_u32(mbar);
+    for (long long it = 0; it < (1ll << 26); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred P1;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, P1;\n\t}\n"
+            : "=r"(done)
+            : "r"(a), "r"(phase));
+        if (done) return true;
+    }
+    return false;
+}
+
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// byte offset of element (r, k) of a K-major no-swizzle tile with K columns
+__device__ __forceinline__ uint32_t tile_off(int r, int k, int K) {
+    return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+// copy rows [row0, row0 + R) x K of a row-major BF16 matrix (row stride ld
+// elements, rows >= nrows read as zero) into a K-major tile; 16-byte chunks,
+// eight consecutive threads fill one core matrix
+__device__ __forceinline__ void stage_tile(uint8_t* tile, const __nv_bfloat16* src, int64_t ld, int64_t row0,
+                                           int64_t nrows, int R, int K, int k0) {
+    const int per_row = K >> 3;
+    const int total = R * per_row;
+    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+        const int rr = idx & 7;
+        const int j = (idx >> 3) % per_row;
+        const int rg = (idx >> 3) / per_row;
+        const int r = rg * 8 + rr;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        const int64_t gr = row0 + r;
+        if (gr < nrows) v = __ldg(reinterpret_cast<const uint4*>(src + gr * ld + k0 + 8 * j));
+        *reinterpret_cast<uint4*>(tile + tile_off(r, 8 * j, K)) = v;
+    }
+}
+
+// ----------------------------------------------------- activation GEMM ---
+// C = epilogue(A W^T), A [mp][K] BF16 row-major (the tile rows of this CTA),
+// W [256][K] BF16 row-major (K-major), persistent over 128-row tiles with W
+// resident in shared memory.  EPI 0: + bias, ReLU.  EPI 1: times
+// (mask > 0), mask [mp][256] BF16 (the previous layer's activation).
+// Writes C [mp][256] (if non-null) and C^T [256][mp] (if non-null).
+template <int K, int EPI>
+__global__ void __launch_bounds__(128, 1)
+k_umma_act(const __nv_bfloat16* __restrict__ A, int64_t mp, const __nv_bfloat16* __restrict__ W,
+           const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ C,
+           __nv_bfloat16* __restrict__ CT, int* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sW = smem;                                  // 256 x K
+    uint8_t* sA = smem + 256 * K * 2;                    // 128 x K
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tmem_alloc(&tslot, 256);
+    if (threadIdx.x == 0) { mbar_init(&mbar, 1); abort_flag = 0; }
+    stage_tile(sW, W, K, 0, 256, 256, K, 0);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    const uint32_t idesc = idesc_bf16(128, 256);
+    const uint32_t sbo = (K / 8) * 128;
+    uint32_t phase = 0;
+    const int64_t ntiles = mp / 128;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t m0 = tile * 128;
+        stage_tile(sA, A, K, m0, mp, 128, K, 0);
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int s = 0; s < K / 16; ++s)
+                umma_bf16(tmem, umma_desc(smem_u32(sA) + 256 * s, 128, sbo), umma_desc(smem_u32(sW) + 256 * s, 128, sbo),
+                          idesc, s > 0 ? 1u : 0u);
+            umma_commit(&mbar);
+        }
+        if (!mbar_wait(&mbar, phase)) {
+            atomicExch(err, 1);
+            abort_flag = 1;
+        }
+        phase ^= 1u;
+        __syncthreads();
+        if (abort_flag) break;
+        tc_fence_after();
+        // epilogue: warp w owns TMEM lanes 32w .. 32w+31 = tile rows
+        const int r = warp * 32 + lane;
+        const int64_t gr = m0 + r;
+        for (int c0 = 0; c0 < 256; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if (EPI == 0) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + bias[c0 + i], 0.0f);
+            } else {
+                const uint4* mk = reinterpret_cast<const uint4*>(mask + gr * 256 + c0);
+                uint4 m0v = __ldg(mk), m1v = __ldg(mk + 1);
+                const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0v);
+                const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1v);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    if (!(__bfloat162float(mb0[i]) > 0.0f)) v[i] = 0.0f;
+                    if (!(__bfloat162float(mb1[i]) > 0.0f)) v[8 + i] = 0.0f;
+                }
+            }
+            __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(v[i]);
+            if (C) {
+                uint4* dst = reinterpret_cast<uint4*>(C + gr * 256 + c0);
+                dst[0] = reinterpret_cast<const uint4*>(o)[0];
+                dst[1] = reinterpret_cast<const uint4*>(o)[1];
+            }
+            if (CT) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) CT[(int64_t)(c0 + i) * mp + gr] = o[i];
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, 256);
+}
+
+// ---------------------------------------------- weight-gradient GEMM ---
+// partial[b][o][n] = sum over this CTA's vertex range of AT[o][m] BT[n][m]
+// (AT [256][mp], BT [NP][mp], BF16 row-major), split-K over vertices in
+// 64-wide chunks; two M = 128 accumulators (o < 128, o >= 128).
+template <int NP>
+__global__ void __launch_bounds__(128, 1)
+k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restrict__ BT, int64_t mp,
+             float* __restrict__ partial, int* __restrict__ err) {
+    constexpr int KC = 64;
+    constexpr uint32_t NCOL = (2 * NP) < 32 ? 32 : 2 * NP;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sA = smem;                     // 256 x 64
+    uint8_t* sB = smem + 256 * KC * 2;      // NP x 64
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tslot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) tmem_alloc(&tslot, NCOL);
+    if (threadIdx.x == 0) { mbar_init(&mbar, 1); abort_flag = 0; }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    const uint32_t idesc = idesc_bf16(128, NP);
+    const uint32_t sbo = (KC / 8) * 128;
+    const int64_t nch = mp / KC;
+    const int64_t c0 = nch * blockIdx.x / gridDim.x, c1 = nch * (blockIdx.x + 1) / gridDim.x;
+    uint32_t phase = 0;
+    for (int64_t ch = c0; ch < c1; ++ch) {
+        // rows o of AT (and n of BT), columns [ch*64, ch*64+64)
+        const int64_t k0 = ch * KC;
+        {
+            const int per_row = KC >> 3;
+            for (int idx = threadIdx.x; idx < 256 * per_row; idx += blockDim.x) {
+                const int rr = idx & 7, j = (idx >> 3) % per_row, rg = (idx >> 3) / per_row;
+                const int r = rg * 8 + rr;
+                *reinterpret_cast<uint4*>(sA + tile_off(r, 8 * j, KC)) =
+                    __ldg(reinterpret_cast<const uint4*>(AT + (int64_t)r * mp + k0 + 8 * j));
+            }
+            for (int idx = threadIdx.x; idx < NP * per_row; idx += blockDim.x) {
+                const int rr = idx & 7, j = (idx >> 3) % per_row, rg = (idx >> 3) / per_row;
+                const int r = rg * 8 + rr;
+                *reinterpret_cast<uint4*>(sB + tile_off(r, 8 * j, KC)) =
+                    __ldg(reinterpret_cast<const uint4*>(BT + (int64_t)r * mp + k0 + 8 * j));
+            }
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int s = 0; s < KC / 16; ++s)
+                    umma_bf16(tmem + (uint32_t)(h * NP),
+                              umma_desc(smem_u32(sA) + (uint32_t)(h * 16) * sbo + 256 * s, 128, sbo),
+                              umma_desc(smem_u32(sB) + 256 * s, 128, sbo), idesc, (ch > c0 || s > 0) ? 1u : 0u);
+            umma_commit(&mbar);
+        }
+        if (!mbar_wait(&mbar, phase)) {
+            atomicExch(err, 1);
+            abort_flag = 1;
+        }
+        phase ^= 1u;
+        __syncthreads();
+        if (abort_flag) break;
+    }
+    tc_fence_after();
+    float* out = partial + (int64_t)blockIdx.x * 256 * NP;
+    for (int h = 0; h < 2; ++h) {
+        const int o = h * 128 + warp * 32 + lane;
+        for (int n0 = 0; n0 < NP; n0 += 16) {
+            float v[16];
+            if (c1 > c0 && !abort_flag) {
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * NP + n0), v);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) out[(int64_t)o * NP + n0 + i] = v[i];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, NCOL);
+}
+
+
+// ------------------------------------------------------- CUDA-core part ---
+// BF16 copies of the weights (W1, W2, W3) and of W2^T, W3^T
+__global__ void k_params_bf16(const float* __restrict__ P, __nv_bfloat16* __restrict__ W1, __nv_bfloat16* __restrict__ W2,
+                              __nv_bfloat16* __restrict__ W3, __nv_bfloat16* __restrict__ W2t,
+                              __nv_bfloat16* __restrict__ W3t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kHid * kIn) W1[i] = __float2bfloat16_rn(P[kOffW1 + i]);
+    if (i < kHid * kHid) {
+        const int o = i / kHid, j = i % kHid;
+        const __nv_bfloat16 a = __float2bfloat16_rn(P[kOffW2 + i]);
+        const __nv_bfloat16 b = __float2bfloat16_rn(P[kOffW3 + i]);
+        W2[i] = a; W3[i] = b;
+        W2t[j * kHid + o] = a; W3t[j * kHid + o] = b;
+    }
+}
+
+// y = h3 W4^T + b4 (FP32), one thread per vertex
+__global__ void __launch_bounds__(256)
+k_head_fwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, int64_t n, float* __restrict__ y) {
+    __shared__ float w4[kOut * kHid];
+    for (int i = threadIdx.x; i < kOut * kHid; i += blockDim.x) w4[i] = P[kOffW4 + i];
+    __syncthreads();
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= n) return;
+    float a0 = P[kOffB4], a1 = P[kOffB4 + 1], a2 = P[kOffB4 + 2];
+    for (int j0 = 0; j0 < kHid; j0 += 8) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4*>(h3 + m * kHid + j0));
+        const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float hv = __bfloat162float(hb[i]);
+            a0 += hv * w4[j0 + i]; a1 += hv * w4[kHid + j0 + i]; a2 += hv * w4[2 * kHid + j0 + i];
+        }
+    }
+    y[3 * m] = a0; y[3 * m + 1] = a1; y[3 * m + 2] = a2;
+}
+
+constexpr int kRedT = 256;
+__device__ __forceinline__ double block_sum_d(double v) {
+    __shared__ double sh[kRedT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x < 32) {
+        r = threadIdx.x < kRedT / 32 ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    }
+    __syncthreads();
+    return r;
+}
+
+// per-block partial sums of the mask (fixed order)
+__global__ void __launch_bounds__(kRedT) k_mask_sum(const float* __restrict__ mask, int64_t n, double* __restrict__ part) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double r = block_sum_d(m < n ? (double)mask[m] : 0.0);
+    if (threadIdx.x == 0) part[blockIdx.x] = r;
+}
+__global__ void k_sum_parts(const double* __restrict__ part, int64_t np, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s = 0.0;
+    for (int64_t i = 0; i < np; ++i) s += part[i];
+    *out = s;
+}
+
+// Head forward and backward, one thread per (padded) vertex: y, the loss
+// term m (y - t)^2 / (3 sum m), dy = 2 m (y - t) / (3 sum m), and
+// dz3 = (dy W4) * (h3 > 0) written row-major and transposed.
+__global__ void __launch_bounds__(kRedT)
+k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, const float* __restrict__ target,
+           const float* __restrict__ mask, int64_t n, int64_t mp, const double* __restrict__ msum,
+           float* __restrict__ y, float* __restrict__ dy, __nv_bfloat16* __restrict__ dz3,
+           __nv_bfloat16* __restrict__ dz3T, double* __restrict__ loss_part) {
+    __shared__ float w4[kOut * kHid];
+    for (int i = threadIdx.x; i < kOut * kHid; i += blockDim.x) w4[i] = P[kOffW4 + i];
+    __syncthreads();
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double den = 3.0 * (*msum);
+    double lterm = 0.0;
+    if (m < mp) {
+        float d[3] = {0.0f, 0.0f, 0.0f};
+        if (m < n && mask[m] != 0.0f && den > 0.0) {
+            float a0 = P[kOffB4], a1 = P[kOffB4 + 1], a2 = P[kOffB4 + 2];
+            for (int j0 = 0; j0 < kHid; j0 += 8) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4*>(h3 + m * kHid + j0));
+                const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float hv = __bfloat162float(hb[i]);
+                    a0 += hv * w4[j0 + i]; a1 += hv * w4[kHid + j0 + i]; a2 += hv * w4[2 * kHid + j0 + i];
+                }
+            }
+            const float yy[3] = {a0, a1, a2};
+            const double mk = (double)mask[m];
+            for (int c = 0; c < 3; ++c) {
+                const double e = (double)yy[c] - (double)target[3 * m + c];
+                lterm += mk * e * e / den;
+                d[c] = (float)(2.0 * mk * e / den);
+                y[3 * m + c] = yy[c];
+            }
+        }
+        for (int c = 0; c < 3; ++c) dy[3 * m + c] = d[c];
+        for (int j0 = 0; j0 < kHid; j0 += 8) {
+            const uint4 u = __ldg(reinterpret_cast<const uint4*>(h3 + m * kHid + j0));
+            const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&u);
+            __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float g = d[0] * w4[j0 + i] + d[1] * w4[kHid + j0 + i] + d[2] * w4[2 * kHid + j0 + i];
+                o[i] = __float2bfloat16_rn(__bfloat162float(hb[i]) > 0.0f ? g : 0.0f);
+                dz3T[(int64_t)(j0 + i) * mp + m] = o[i];
+            }
+            *reinterpret_cast<uint4*>(dz3 + m * kHid + j0) = *reinterpret_cast<const uint4*>(o);
+        }
+    }
+    const double r = block_sum_d(lterm);
+    if (threadIdx.x == 0) loss_part[blockIdx.x] = r;
+}
+
+// partial[b][c][j] = sum over this block's vertex chunk of dy[m][c] h3[m][j]
+// and partial[b][3][j] (j < 3) = sum of dy[m][j]; thread j, rows in order
+__global__ void __launch_bounds__(kHid)
+k_head_wgrad(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ h3, int64_t mp, int64_t chunk,
+             float* __restrict__ partial) {
+    const int j = threadIdx.x;
+    const int64_t m0 = (int64_t)blockIdx.x * chunk, m1 = min(mp, m0 + chunk);
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, s = 0.0f;
+    for (int64_t m = m0; m < m1; ++m) {
+        const float hv = __bfloat162float(h3[m * kHid + j]);
+        const float d0 = dy[3 * m], d1 = dy[3 * m + 1], d2 = dy[3 * m + 2];
+        a0 += d0 * hv; a1 += d1 * hv; a2 += d2 * hv;
+        if (j < 3) s += dy[3 * m + j];
+    }
+    float* out = partial + (int64_t)blockIdx.x * (4 * kHid);
+    out[j] = a0; out[kHid + j] = a1; out[2 * kHid + j] = a2;
+    out[3 * kHid + j] = j < 3 ? s : 0.0f;
+}
+
+// row sums of a [rows][mp] BF16 matrix (bias gradients), one block per row
+__global__ void __launch_bounds__(kRedT)
+k_rowsum(const __nv_bfloat16* __restrict__ A, int64_t mp, float* __restrict__ out) {
+    const __nv_bfloat16* row = A + (int64_t)blockIdx.x * mp;
+    double s = 0.0;
+    for (int64_t m = threadIdx.x; m < mp; m += kRedT) s += (double)__bfloat162float(row[m]);
+    const double r = block_sum_d(s);
+    if (threadIdx.x == 0) out[blockIdx.x] = (float)r;
+}
+
+// out[l] = sum_p partial[p][l] in order p = 0 .. np-1 (optionally strided)
+__global__ void k_reduce_part(const float* __restrict__ partial, int64_t np, int64_t stride, int64_t L,
+                              float* __restrict__ out) {
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= L) return;
+    float s = 0.0f;
+    for (int64_t p = 0; p < np; ++p) s += partial[p * stride + l];
+    out[l] = s;
+}
+
+// Adam (bias-corrected) on the flattened FP32 parameters; omb1 = 1 - beta1
+// and omb2 = 1 - beta2 come from the host in FP64 (1 - 0.999f in FP32 is
+// 1.3e-5 away from 1e-3)
+__global__ void k_adam(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M1,
+                       float* __restrict__ M2, int64_t n, float lr, float b1, float b2, float omb1, float omb2,
+                       float eps, float c1, float c2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float g = G[i];
+    const float a = b1 * M1[i] + omb1 * g;
+    const float b = b2 * M2[i] + omb2 * g * g;
+    M1[i] = a;
+    M2[i] = b;
+    P[i] -= lr * (a / c1) / (sqrtf(b / c2) + eps);
+}
+
+struct FeatScales {
+    float inv_pos, inv_disp, inv_force, h;
+    float lo[3], inv_ext[3];
+};
+
+// 32 features per vertex (rows >= n are zero):
+//  0-2 (x - X) / pos_scale       3-5 h v / disp_scale      6-8 X mapped to [-1, 1]
+//  9 Dirichlet flag              10 slave-surface flag     11-13 contact force / force_scale (clamped +-8)
+//  14 contact active             15-26 sin, cos (pi k Xn), k = 1, 2, per axis      27-31 zero
+template <class TG>
+__global__ void __launch_bounds__(256)
+k_features(const double* __restrict__ x, const double* __restrict__ v, const double* __restrict__ X,
+           const uint8_t* __restrict__ dir, const uint8_t* __restrict__ surf, const TG* __restrict__ cg,
+           int64_t n, int64_t mp, FeatScales S, __nv_bfloat16* __restrict__ f, __nv_bfloat16* __restrict__ fT) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= mp) return;
+    float o[kIn];
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) o[i] = 0.0f;
+    if (m < n) {
+        float xn[3];
+        for (int c = 0; c < 3; ++c) {
+            o[c] = (float)(x[3 * m + c] - X[3 * m + c]) * S.inv_pos;
+            o[3 + c] = (float)(S.h * v[3 * m + c]) * S.inv_disp;
+            xn[c] = 2.0f * ((float)X[3 * m + c] - S.lo[c]) * S.inv_ext[c] - 1.0f;
+            o[6 + c] = xn[c];
+        }
+        o[9] = dir[m] ? 1.0f : 0.0f;
+        o[10] = surf[m] ? 1.0f : 0.0f;
+        float act = 0.0f;
+        for (int c = 0; c < 3; ++c) {
+            const float g = cg ? (float)cg[3 * m + c] : 0.0f;
+            o[11 + c] = fminf(fmaxf(g * S.inv_force, -8.0f), 8.0f);
+            if (g != 0.0f) act = 1.0f;
+        }
+        o[14] = act;
+        for (int c = 0; c < 3; ++c)
+            for (int k = 1; k <= 2; ++k) {
+                const float a = 3.14159265358979f * (float)k * xn[c];
+                o[15 + 4 * c + 2 * (k - 1)] = sinf(a);
+                o[15 + 4 * c + 2 * (k - 1) + 1] = cosf(a);
+            }
+    }
+    __align__(16) __nv_bfloat16 b[kIn];
+#pragma unroll
+    for (int i = 0; i < kIn; ++i) {
+        b[i] = __float2bfloat16_rn(o[i]);
+        fT[(int64_t)i * mp + m] = b[i];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        reinterpret_cast<uint4*>(f + m * kIn)[q] = reinterpret_cast<const uint4*>(b)[q];
+}
+
+// dx = h v + disp_scale y
+__global__ void k_predict(const float* __restrict__ y, const double* __restrict__ v, int64_t n, double h,
+                          double disp, double* __restrict__ dx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    dx[i] = h * v[i] + disp * (double)y[i];
+}
+
+unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+constexpr size_t kActSmem(int K) { return (size_t)256 * K * 2 + (size_t)128 * K * 2; }
+// at least this much dynamic shared memory keeps one CTA per SM, so the
+// tensor-memory allocations of co-resident CTAs never exceed 512 columns
+constexpr size_t kOneCtaSmem = 120 * 1024;
+
+template <int K, int EPI>
+cudaError_t launch_act(Ctx& c, WarmStart& W, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const float* bias,
+                       const __nv_bfloat16* mask, __nv_bfloat16* C, __nv_bfloat16* CT) {
+    const size_t sm = std::max(kActSmem(K), kOneCtaSmem);
+    GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_act<K, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int grid = (int)std::min<int64_t>(sm_count(c.device), W.mp / 128);
+    k_umma_act<K, EPI><<<grid, 128, sm, c.stream>>>(A, W.mp, Wt, bias, mask, C, CT, W.err.p);
+    return cudaGetLastError();
+}
+
+template <int NP>
+cudaError_t launch_wgrad(Ctx& c, WarmStart& W, const __nv_bfloat16* AT, const __nv_bfloat16* BT, float* out) {
+    const size_t sm = std::max((size_t)(256 + NP) * 64 * 2, kOneCtaSmem);
+    GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_wgrad<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    const int grid = sm_count(c.device);
+    k_umma_wgrad<NP><<<grid, 128, sm, c.stream>>>(AT, BT, W.mp, W.part.p, W.err.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    k_reduce_part<<<nb(256 * NP, 256), 256, 0, c.stream>>>(W.part.p, grid, 256 * NP, 256 * NP, out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// forward through the three hidden layers (features already in W.f / W.fT)
+static cudaError_t ws_hidden(Ctx& c, WarmStart& W, bool keep_transposes) {
+    const float* P = W.P.p;
+    GMCP_CUDA_TRY((launch_act<kIn, 0>(c, W, W.f.p, W.W1.p, P + kOffB1, nullptr, W.h1.p, keep_transposes ? W.h1T.p : nullptr)));
+    GMCP_CUDA_TRY((launch_act<kHid, 0>(c, W, W.h1.p, W.W2.p, P + kOffB2, nullptr, W.h2.p, keep_transposes ? W.h2T.p : nullptr)));
+    return launch_act<kHid, 0>(c, W, W.h2.p, W.W3.p, P + kOffB3, nullptr, W.h3.p, nullptr);
+}
+
+static cudaError_t ws_check_err(Ctx& c, WarmStart& W, bool* bad) {
+    int e = 0;
+    GMCP_CUDA_TRY(cudaMemcpyAsync(&e, W.err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+    GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
+    *bad = e != 0;
+    return cudaSuccess;
+}
+
+// forward + backward into W.G; loss into *loss (host, synchronises)
+static cudaError_t ws_backward(Ctx& c, WarmStart& W, const float* target, const float* mask, double* loss) {
+    cudaStream_t s = c.stream;
+    const int64_t n = W.n, mp = W.mp;
+    GMCP_CUDA_TRY(ws_hidden(c, W, true));
+    double* sc = W.scal.p;
+    const unsigned gb = nb(mp, kRedT), gn = nb(n, kRedT);
+    k_mask_sum<<<gn, kRedT, 0, s>>>(mask, n, W.dpart.p);
+    k_sum_parts<<<1, 32, 0, s>>>(W.dpart.p, (int64_t)gn, sc);
+    k_head_bwd<<<gb, kRedT, 0, s>>>(W.h3.p, W.P.p, target, mask, n, mp, sc, W.y.p, W.dy.p, W.dz3.p, W.dz3T.p,
+                                     W.dpart.p);
+    k_sum_parts<<<1, 32, 0, s>>>(W.dpart.p, (int64_t)gb, sc + 1);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    float* G = W.G.p;
+    // layer 4 (CUDA cores)
+    {
+        const int64_t chunk = 4096;
+        const int64_t nblk = (mp + chunk - 1) / chunk;
+        float* pp = W.part.p;
+        k_head_wgrad<<<(unsigned)nblk, kHid, 0, s>>>(W.dy.p, W.h3.p, mp, chunk, pp);
+        k_reduce_part<<<nb(3 * kHid, 256), 256, 0, s>>>(pp, nblk, 4 * kHid, 3 * kHid, G + kOffW4);
+        k_reduce_part<<<1, 32, 0, s>>>(pp + 3 * kHid, nblk, 4 * kHid, 3, G + kOffB4);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    // layer 3: dW3 = dz3^T h2, db3
+    GMCP_CUDA_TRY(launch_wgrad<kHid>(c, W, W.dz3T.p, W.h2T.p, G + kOffW3));
+    k_rowsum<<<kHid, kRedT, 0, s>>>(W.dz3T.p, mp, G + kOffB3);
+    // dz2 = (dz3 W3) * (h2 > 0)
+    GMCP_CUDA_TRY((launch_act<kHid, 1>(c, W, W.dz3.p, W.W3t.p, nullptr, W.h2.p, W.dz2.p, W.dz2T.p)));
+    GMCP_CUDA_TRY(launch_wgrad<kHid>(c, W, W.dz2T.p, W.h1T.p, G + kOffW2));
+    k_rowsum<<<kHid, kRedT, 0, s>>>(W.dz2T.p, mp, G + kOffB2);
+    // dz1 = (dz2 W2) * (h1 > 0)
+    GMCP_CUDA_TRY((launch_act<kHid, 1>(c, W, W.dz2.p, W.W2t.p, nullptr, W.h1.p, nullptr, W.dz1T.p)));
+    GMCP_CUDA_TRY(launch_wgrad<kIn>(c, W, W.dz1T.p, W.fT.p, G + kOffW1));
+    k_rowsum<<<kHid, kRedT, 0, s>>>(W.dz1T.p, mp, G + kOffB1);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    if (loss) {
+        GMCP_CUDA_TRY(cudaMemcpyAsync(loss, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    return cudaSuccess;
+}
+
+void ws_destroy(WarmStart* w) { delete w; }
+
+}  // namespace gmcp
+
+using namespace gmcp;
+
+static ipc_status ws_fail(Ctx& c, ipc_status st, const std::string& m) {
+    c.err = m;
+    return st;
+}
+#define WS_CK(c, expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess) {                                                            \
+            cudaGetLastError();                                                             \
+            return ws_fail(c, _e == cudaErrorMemoryAllocation ? IPC_ERR_OOM : IPC_ERR_CUDA, \
+                           std::string(#expr) + ": " + cudaGetErrorString(_e));             \
+        }                                                                                   \
+    } while (0)
+
+extern "C" {
+
+ipc_status ipc_ws_create(ipc_ctx* ctx, const ipc_ws_params* prm) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx_of(ctx);
+    if (!prm || !prm->params_host || !(prm->lr > 0.0) || !(prm->pos_scale > 0.0) || !(prm->disp_scale > 0.0) ||
+        !(prm->force_scale > 0.0))
+        return ws_fail(c, IPC_ERR_ARG, "ipc_ws_create: NULL parameters or non-positive lr / scales");
+    WS_CK(c, cudaSetDevice(c.device));
+    std::unique_ptr<WarmStart> W(new WarmStart());
+    W->n = c.nv;
+    W->mp = (c.nv + 127) / 128 * 128;
+    W->lr = prm->lr; W->beta1 = prm->beta1; W->beta2 = prm->beta2; W->eps = prm->eps;
+    W->pos_scale = prm->pos_scale; W->disp_scale = prm->disp_scale; W->force_scale = prm->force_scale;
+    for (int q = 0; q < 3; ++q) { W->lo[q] = 1e300; W->hi[q] = -1e300; }
+    for (int64_t v = 0; v < c.nv; ++v)
+        for (int q = 0; q < 3; ++q) {
+            W->lo[q] = std::min(W->lo[q], c.h_X[3 * v + q]);
+            W->hi[q] = std::max(W->hi[q], c.h_X[3 * v + q]);
+        }
+    std::vector<uint8_t> surf(c.nv, 0);
+    {
+        std::vector<int32_t> st((size_t)3 * c.ns);
+        WS_CK(c, cudaMemcpy(st.data(), c.stri.p, sizeof(int32_t) * st.size(), cudaMemcpyDeviceToHost));
+        for (int32_t v : st) surf[v] = 1;
+    }
+    const int64_t mp = W->mp;
+    cudaStream_t s = c.stream;
+    WS_CK(c, W->P.upload(prm->params_host, kNParam, s));
+    WS_CK(c, W->M1.ensure(kNParam)); WS_CK(c, W->M2.ensure(kNParam)); WS_CK(c, W->G.ensure(kNParam));
+    WS_CK(c, cudaMemsetAsync(W->M1.p, 0, sizeof(float) * kNParam, s));
+    WS_CK(c, cudaMemsetAsync(W->M2.p, 0, sizeof(float) * kNParam, s));
+    WS_CK(c, W->W1.ensure(kHid * kIn)); WS_CK(c, W->W2.ensure(kHid * kHid)); WS_CK(c, W->W3.ensure(kHid * kHid));
+    WS_CK(c, W->W2t.ensure(kHid * kHid)); WS_CK(c, W->W3t.ensure(kHid * kHid));
+    WS_CK(c, W->f.ensure(mp * kIn)); WS_CK(c, W->fT.ensure(mp * kIn));
+    for (DBuf<__nv_bfloat16>* b : {&W->h1, &W->h2, &W->h3, &W->h1T, &W->h2T, &W->dz3, &W->dz3T, &W->dz2, &W->dz2T, &W->dz1T})
+        WS_CK(c, b->ensure((size_t)mp * kHid));
+    WS_CK(c, W->y.ensure(3 * mp)); WS_CK(c, W->dy.ensure(3 * mp));
+    // partial sums: split-K weight gradients [SMs][256][256] plus scratch
+    WS_CK(c, W->part.ensure(std::max((size_t)std::max(sm_count(c.device), 1) * kHid * kHid,
+                                     (size_t)4 * kHid * ((mp + 4095) / 4096)) + 1024));
+    WS_CK(c, W->dpart.ensure((size_t)(mp + kRedT - 1) / kRedT + 16));
+    WS_CK(c, W->surf.upload(surf.data(), surf.size(), s));
+    if (c.P.precision == IPC_PREC_MIXED) WS_CK(c, W->cgrad32.ensure(3 * (size_t)c.nv));
+    else WS_CK(c, W->cgrad64.ensure(3 * (size_t)c.nv));
+    WS_CK(c, W->err.ensure(1)); WS_CK(c, cudaMemsetAsync(W->err.p, 0, sizeof(int), s));
+    WS_CK(c, W->scal.ensure(8));
+    WS_CK(c, cudaMemsetAsync(W->f.p, 0, sizeof(__nv_bfloat16) * mp * kIn, s));
+    WS_CK(c, cudaMemsetAsync(W->fT.p, 0, sizeof(__nv_bfloat16) * mp * kIn, s));
+    k_params_bf16<<<nb(kHid * kHid, 256), 256, 0, s>>>(W->P.p, W->W1.p, W->W2.p, W->W3.p, W->W2t.p, W->W3t.p);
+    WS_CK(c, cudaGetLastError());
+    WS_CK(c, cudaStreamSynchronize(s));
+    c.ws = std::unique_ptr<WarmStart, void (*)(WarmStart*)>(W.release(), ws_destroy);
+    return IPC_OK;
+}
+
+ipc_status ipc_ws_features(ipc_ctx* ctx, const double* x_dev, const double* v_dev, const double* xm_dev,
+                           void* feats_dev) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx_of(ctx);
+    if (!c.ws) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_features: call ipc_ws_create first");
+    if (!x_dev || !v_dev || (!xm_dev && c.nmv > 0)) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_features: NULL input");
+    WarmStart& W = *c.ws;
+    WS_CK(c, cudaSetDevice(c.device));
+    // contact force at (x, xm) from the contact pass
+    const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    WS_CK(c, run_candidates(c, x_dev, xm_dev));
+    void* cg = f32 ? (void*)W.cgrad32.p : (void*)W.cgrad64.p;
+    WS_CK(c, contact_eval(c, x_dev, xm_dev, nullptr, cg, false, nullptr));
+    FeatScales S;
+    S.inv_pos = (float)(1.0 / W.pos_scale);
+    S.inv_disp = (float)(1.0 / W.disp_scale);
+    S.inv_force = (float)(1.0 / W.force_scale);
+    S.h = (float)c.prm.h;
+    for (int q = 0; q < 3; ++q) {
+        S.lo[q] = (float)W.lo[q];
+        S.inv_ext[q] = (float)(W.hi[q] > W.lo[q] ? 1.0 / (W.hi[q] - W.lo[q]) : 1.0);
+    }
+    const uint8_t* dir = c.newton ? c.newton->dir.p : nullptr;
+    DBuf<uint8_t> dtmp;
+    if (!dir) {
+        WS_CK(c, dtmp.upload(c.h_dir.data(), c.h_dir.size(), c.stream));
+        dir = dtmp.p;
+    }
+    if (f32)
+        k_features<float><<<nb(W.mp, 256), 256, 0, c.stream>>>(x_dev, v_dev, c.X.p, dir, W.surf.p, W.cgrad32.p, W.n, W.mp, S, W.f.p, W.fT.p);
+    else
+        k_features<double><<<nb(W.mp, 256), 256, 0, c.stream>>>(x_dev, v_dev, c.X.p, dir, W.surf.p, W.cgrad64.p, W.n, W.mp, S, W.f.p, W.fT.p);
+    WS_CK(c, cudaGetLastError());
+    if (feats_dev)
+        WS_CK(c, cudaMemcpyAsync(feats_dev, W.f.p, sizeof(__nv_bfloat16) * W.n * kIn, cudaMemcpyDeviceToDevice, c.stream));
+    WS_CK(c, cudaStreamSynchronize(c.stream));
+    return IPC_OK;
+}
+
+// copy caller features [n][32] BF16 into the padded row-major and transposed buffers
+namespace gmcp {
+namespace {
+__global__ void k_load_feats(const __nv_bfloat16* __restrict__ src, int64_t n, int64_t mp,
+                             __nv_bfloat16* __restrict__ f, __nv_bfloat16* __restrict__ fT) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= mp) return;
+    for (int i = 0; i < kIn; ++i) {
+        const __nv_bfloat16 v = m < n ? src[m * kIn + i] : __float2bfloat16_rn(0.0f);
+        f[m * kIn + i] = v;
+        fT[(int64_t)i * mp + m] = v;
+    }
+}
+}  // namespace
+}  // namespace gmcp
+
+static ipc_status ws_take_feats(Ctx& c, WarmStart& W, const void* feats_dev) {
+    if (!feats_dev) return IPC_OK;
+    k_load_feats<<<nb(W.mp, 256), 256, 0, c.stream>>>((const __nv_bfloat16*)feats_dev, W.n, W.mp, W.f.p, W.fT.p);
+    WS_CK(c, cudaGetLastError());
+    return IPC_OK;
+}
+
+ipc_status ipc_ws_forward(ipc_ctx* ctx, const void* feats_dev, float* out_dev) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx_of(ctx);
+    if (!c.ws) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_forward: call ipc_ws_create first");
+    if (!out_dev) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_forward: NULL output");
+    WarmStart& W = *c.ws;
+    WS_CK(c, cudaSetDevice(c.device));
+    ipc_status st = ws_take_feats(c, W, feats_dev);
+    if (st != IPC_OK) return st;
+    WS_CK(c, ws_hidden(c, W, false));
+    k_head_fwd<<<nb(W.n, 256), 256, 0, c.stream>>>(W.h3.p, W.P.p, W.n, out_dev);
+    WS_CK(c, cudaGetLastError());
+    bool bad = false;
+    WS_CK(c, ws_check_err(c, W, &bad));
+    if (bad) return ws_fail(c, IPC_ERR_TIMEOUT, "ipc_ws_forward: a tensor-core wait hit its iteration cap");
+    return IPC_OK;
+}
+
+ipc_status ipc_ws_grads(ipc_ctx* ctx, const void* feats_dev, const float* target_dev, const float* mask_dev,
+                        double* loss_host, float* grads_host) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx_of(ctx);
+    if (!c.ws) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_grads: call ipc_ws_create first");
+    if (!target_dev || !mask_dev) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_grads: NULL target or mask");
+    WarmStart& W = *c.ws;
+    WS_CK(c, cudaSetDevice(c.device));
+    ipc_status st = ws_take_feats(c, W, feats_dev);
+    if (st != IPC_OK) return st;
+    double loss = 0.0;
+    WS_CK(c, ws_backward(c, W, target_dev, mask_dev, &loss));
+    if (grads_host)
+        WS_CK(c, cudaMemcpyAsync(grads_host, W.G.p, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, c.stream));
+    bool bad = false;
+    WS_CK(c, ws_check_err(c, W, &bad));
+    if (bad) return ws_fail(c, IPC_ERR_TIMEOUT, "ipc_ws_grads: a tensor-core wait hit its iteration cap");
+    if (loss_host) *loss_host = loss;
+    return IPC_OK;
+}
+
+ipc_status ipc_ws_train_step(ipc_ctx* ctx, const void* feats_dev, const float* target_dev, const float* mask_dev,
+                             double* loss_host) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx_of(ctx);
+    if (!c.ws) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_train_step: call ipc_ws_create first");
+    if (!target_dev || !mask_dev) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_train_step: NULL target or mask");
+    WarmStart& W = *c.ws;
+    WS_CK(c, cudaSetDevice(c.device));
+    ipc_status st = ws_take_feats(c, W, feats_dev);
+    if (st != IPC_OK) return st;
+    double loss = 0.0;
+    WS_CK(c, ws_backward(c, W, target_dev, mask_dev, loss_host ? &loss : nullptr));
+    W.step += 1;
+    const float c1 = (float)(1.0 - std::pow(W.beta1, (double)W.step));
+    const float c2 = (float)(1.0 - std::pow(W.beta2, (double)W.step));
+    k_adam<<<nb(kNParam, 256), 256, 0, c.stream>>>(W.P.p, W.G.p, W.M1.p, W.M2.p, kNParam, (float)W.lr, (float)W.beta1,
+                                                   (float)W.beta2, (float)(1.0 - W.beta1), (float)(1.0 - W.beta2),
+                                                   (float)W.eps, c1, c2);
+    k_params_bf16<<<nb(kHid * kHid, 256), 256, 0, c.stream>>>(W.P.p, W.W1.p, W.W2.p, W.W3.p, W.W2t.p, W.W3t.p);
+    WS_CK(c, cudaGetLastError());
+    bool bad = false;
+    WS_CK(c, ws_check_err(c, W, &bad));
+    if (bad) return ws_fail(c, IPC_ERR_TIMEOUT, "ipc_ws_train_step: a tensor-core wait hit its iteration cap");
+    if (loss_host) *loss_host = loss;
+    return IPC_OK;
+}
+
+ipc_status ipc_ws_get_params(ipc_ctx* ctx, float* params_host) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx_of(ctx);
+    if (!c.ws || !params_host) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_get_params: no network or NULL output");
+    WS_CK(c, cudaSetDevice(c.device));
+    WS_CK(c, cudaMemcpyAsync(params_host, c.ws->P.p, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, c.stream));
+    WS_CK(c, cudaStreamSynchronize(c.stream));
+    return IPC_OK;
+}
+
+ipc_status ipc_ws_predict(ipc_ctx* ctx, const double* x_dev, const double* v_dev, const double* xm_dev,
+                          double* dx_dev) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx_of(ctx);
+    if (!c.ws) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_predict: call ipc_ws_create first");
+    if (!dx_dev) return ws_fail(c, IPC_ERR_ARG, "ipc_ws_predict: NULL output");
+    ipc_status st = ipc_ws_features(ctx, x_dev, v_dev, xm_dev, nullptr);
+    if (st != IPC_OK) return st;
+    WarmStart& W = *c.ws;
+    WS_CK(c, ws_hidden(c, W, false));
+    k_head_fwd<<<nb(W.n, 256), 256, 0, c.stream>>>(W.h3.p, W.P.p, W.n, W.y.p);
+    k_predict<<<nb(3 * W.n, 256), 256, 0, c.stream>>>(W.y.p, v_dev, W.n, c.prm.h, W.disp_scale, dx_dev);
+    WS_CK(c, cudaGetLastError());
+    bool bad = false;
+    WS_CK(c, ws_check_err(c, W, &bad));
+    if (bad) return ws_fail(c, IPC_ERR_TIMEOUT, "ipc_ws_predict: a tensor-core wait hit its iteration cap");
+    return IPC_OK;
+}
+
+}  // extern "C"
