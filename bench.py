@@ -261,6 +261,7 @@ def run_ours(args):
     }
     if not args.no_newton:
         line["newton_step"] = newton_measurement(dev)
+        line["warm_start"] = warm_start_measurement(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(steps=2)
     print(json.dumps(line), flush=True)
@@ -314,6 +315,64 @@ def newton_measurement(dev, start_step=20, n_states=4):
         ctx.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step_median"] / out["mixed"]["ms_per_step_median"]
     return out
+
+
+def warm_start_measurement(dev, train_iters=1500, timed_iters=50):
+    """Learned warm start on the terrain press: tensor-core training
+    throughput (one Adam step = forward + backward over all 594,441
+    vertices) and what the trained network gains on held-out steps (start
+    fraction alpha0, Newton iterations, wall time), against the plain
+    predictor from the same states."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    from paper_2605_24339_b300 import warmstart as WS
+    sc = S.gel_on_terrain()
+    sc.params.update(max_newton=60)
+    ctx = binding.Context(sc, precision="mixed", device=dev)
+    p0 = WS.init_params(0)
+    p0[-3 - 3 * 256:] = 0.0
+    ctx.ws_create(p0, lr=3e-4, **WS.default_scales(sc))
+    x = torch.as_tensor(sc.X.copy(), device="cuda")
+    v = torch.as_tensor(sc.v_dirichlet.copy(), device="cuda")
+    WS.rollout(ctx, sc, x, v, 8, record=False)
+    ro = WS.rollout(ctx, sc, x, v, 20, record=True)
+    for smp in ro.samples:
+        big = (smp.target.abs().amax(dim=1) > 0.02).float()
+        smp.mask = (smp.mask * (0.01 + big + smp.feats[:, 14].float())).contiguous()
+    WS.train(ctx, ro.samples[:14], train_iters, seed=1)
+    s0 = ro.samples[0]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(timed_iters):
+        ctx.ws_train_step(s0.feats, s0.target, s0.mask)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / timed_iters
+    n = sc.X.shape[0]
+    macs = 32 * 256 + 2 * 256 * 256 + 256 * 3
+    # forward 2 n macs; backward: activation gradients of layers 2-3 and all
+    # weight gradients, 2 n (macs - 32*256) + 2 n macs
+    flops = 2.0 * n * macs + 2.0 * n * (macs - 32 * 256) + 2.0 * n * macs
+    res = WS.compare_starts(ctx, sc, ro.states[14:20])
+    held = ro.samples[14:20]
+    net = [ctx.ws_grads(sm.feats, sm.target, sm.mask)[0] for sm in held]
+    zero = [float((sm.mask[:, None] * sm.target ** 2).sum() / (3 * sm.mask.sum())) for sm in held]
+    ctx.close()
+    peaks, _ = load_peaks()
+    tf = flops / (ms / 1e3) / 1e12
+    return {
+        "workload": "gel_on_terrain press, train on steps 8-21, held out 22-27",
+        "train_ms_per_step": ms, "train_tflops": tf, "train_flops_per_step": flops,
+        "train_frac_of_bf16_peak": tf / peaks.get("bf16_tflops", 1800.0),
+        "held_out_loss": {"network": net, "plain_predictor": zero},
+        "plain": {"newton_iters": [r["newton_iters"] for r in res["plain"]],
+                  "alpha0": [r["alpha0"] for r in res["plain"]],
+                  "wall_ms": [round(r["wall_ms"], 1) for r in res["plain"]]},
+        "learned": {"newton_iters": [r["newton_iters"] for r in res["learned"]],
+                    "alpha0": [r["alpha0"] for r in res["learned"]],
+                    "pred_used": [r["pred_used"] for r in res["learned"]],
+                    "wall_ms": [round(r["wall_ms"], 1) for r in res["learned"]]},
+    }
 
 
 def cpu_baseline(steps=2):

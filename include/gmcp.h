@@ -135,6 +135,7 @@ typedef struct {
     double last_alpha;     /* step length of the last accepted line search */
     double energy;         /* incremental potential at the final iterate */
     double ms_total;       /* host wall time of the call */
+    int32_t pred_used;     /* 1 if dx_pred gave the Newton start (see ipc_newton_step) */
 } ipc_step_stats;
 
 /* ---------------------------------------------------------------------- */
@@ -243,8 +244,10 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
  *  are moved to x + h v (their motion must be admissible);
  *  xm_next_dev: master at t+1 (NULL = unchanged); the context keeps the
  *  current master, which starts at m_rest;
- *  dx_pred_dev: a predicted displacement; the Newton start is then
- *  x^t + alpha0 dx_pred with alpha0 the CCD-admissible fraction (NULL: the
+ *  dx_pred_dev: a predicted displacement; its start point x^t + alpha0
+ *  dx_pred (alpha0 the CCD-admissible fraction, halved until every tet keeps
+ *  J > 0) replaces the plain predictor's start only if it exists and its
+ *  residual ||G_free|| is not larger than the plain start's (NULL: the
  *  plain predictor x^t + h v^t);
  *  stats (host) may be NULL.
  * The first call builds the time-stepper state (tet data, mass, the global

@@ -1346,6 +1346,7 @@ typedef struct {
     int newton_iters, pcg_iters_total;
     double residual, res0, alpha0, last_alpha;
     double energy;
+    int pred_used;           /* 1 if the predicted start was taken */
 } orc_stats;
 
 ORC_API orc_sim* orc_sim_create(orc_scene* sc, int nv, const double* X, int nt, const int32_t* tets,
@@ -1644,11 +1645,25 @@ ORC_API int orc_newton_step(orc_sim* s, double* x, double* v, const double* xm_n
     if (!start_point(s, x, xhat, xhat, tmp, &a0)) { status = 3; goto done; }
     if (!newton_eval(s, tmp, xhat, &Etmp, G, NULL, &smp)) { status = 3; goto done; }
     gscale = free_norm(s, G);
-    if (dx_pred) {
-        for (int i = 0; i < n; ++i) P[i] = x[i] + dx_pred[i];
-        if (!start_point(s, x, xhat, P, x, &a0)) { status = 3; goto done; }
-    } else {
-        memcpy(x, tmp, sizeof(double) * n);
+    /* a predicted start is admitted through the same CCD-filtered start
+     * point, and kept only if its residual is not worse than the plain
+     * predictor's (reading R16) */
+    {
+        int use_pred = 0;
+        if (dx_pred) {
+            double* xl = (double*)malloc(sizeof(double) * n);
+            double al;
+            for (int i = 0; i < n; ++i) P[i] = x[i] + dx_pred[i];
+            if (start_point(s, x, xhat, P, xl, &al) && newton_eval(s, xl, xhat, &Etmp, G, NULL, &smp) &&
+                free_norm(s, G) <= gscale) {
+                memcpy(x, xl, sizeof(double) * n);
+                a0 = al;
+                use_pred = 1;
+            }
+            free(xl);
+        }
+        if (!use_pred) memcpy(x, tmp, sizeof(double) * n);
+        st->pred_used = use_pred;
     }
     st->alpha0 = a0;
     st->res0 = gscale;

@@ -57,7 +57,7 @@ class AccdInfo(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("status", I), ("newton_iters", I), ("pcg_iters_total", I), ("residual", D),
-                ("res0", D), ("alpha0", D), ("last_alpha", D), ("energy", D)]
+                ("res0", D), ("alpha0", D), ("last_alpha", D), ("energy", D), ("pred_used", I)]
 
 
 def _declare(L):

@@ -74,7 +74,7 @@ class StepStats(C.Structure):
     _fields_ = [("newton_iters", C.c_int32), ("pcg_iters_total", C.c_int32),
                 ("line_search_halvings", C.c_int32), ("residual", C.c_double),
                 ("res0", C.c_double), ("alpha0", C.c_double), ("last_alpha", C.c_double),
-                ("energy", C.c_double), ("ms_total", C.c_double)]
+                ("energy", C.c_double), ("ms_total", C.c_double), ("pred_used", C.c_int32)]
 
 
 class WsParams(C.Structure):
@@ -386,7 +386,8 @@ class Context:
             self._check(r)
         return dict(status=r, newton_iters=st.newton_iters, pcg_iters=st.pcg_iters_total,
                     halvings=st.line_search_halvings, residual=st.residual, res0=st.res0,
-                    alpha0=st.alpha0, last_alpha=st.last_alpha, energy=st.energy, ms=st.ms_total)
+                    alpha0=st.alpha0, last_alpha=st.last_alpha, energy=st.energy, ms=st.ms_total,
+                    pred_used=st.pred_used)
 
     # -- learned warm start -------------------------------------------------
     def ws_create(self, params, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, pos_scale=1e-3,

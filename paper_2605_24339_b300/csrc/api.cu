@@ -261,13 +261,27 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
     GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 59, sizeof(double), cudaMemcpyDeviceToHost, s));
     GMCP_CUDA_TRY(cudaStreamSynchronize(s));
     gscale = std::sqrt(hb[0]);
+    // a predicted start goes through the same CCD-filtered start point and is
+    // kept only if its residual is not worse than the plain predictor's
+    bool use_pred = false;
     if (dx_pred) {
+        double al = 0.0;
         GMCP_CUDA_TRY(vec_axpy(c, n, 1.0, x, dx_pred, N.P.p));
-        GMCP_CUDA_TRY(start_point(c, x, N.P.p, N.tmp.p, &a0, &ok));
-        if (!ok) status = 3;
+        GMCP_CUDA_TRY(start_point(c, x, N.P.p, N.xl.p, &al, &ok));
+        if (ok) {
+            GMCP_CUDA_TRY(assemble_system(c, N.xl.p, false, sc + 56, sc + 57, sc + 58, sc + 59));
+            int32_t bad = 0;
+            GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 59, sizeof(double), cudaMemcpyDeviceToHost, s));
+            GMCP_CUDA_TRY(cudaMemcpyAsync(&bad, N.bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+            if (!bad && std::sqrt(hb[0]) <= gscale) {
+                use_pred = true;
+                a0 = al;
+            }
+        }
     }
-    if (status == 0)
-        GMCP_CUDA_TRY(cudaMemcpyAsync(x, N.tmp.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    st->pred_used = use_pred ? 1 : 0;
+    GMCP_CUDA_TRY(cudaMemcpyAsync(x, use_pred ? N.xl.p : N.tmp.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     st->alpha0 = a0;
     st->res0 = gscale;
     // floor: force of a 1e-3 strain on one element, h^2 E lbar^2 1e-3

@@ -198,7 +198,7 @@ struct NewtonState {
     DBuf<double> part;                   // PCG per-block partial sums [2][blocks]
     DBuf<unsigned> counters;             // PCG last-block counters
     DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nv]
-    DBuf<double> xhat, xt, G, dirn, tmp, P, dP, xi;   // [3 nv]
+    DBuf<double> xhat, xt, G, dirn, tmp, P, dP, xi, xl;   // [3 nv]
     DBuf<double> cgrad64;                // contact gradient [3 nv] (FP64 path)
     DBuf<float> cgrad32;                 // contact gradient [3 nv] (mixed path)
     DBuf<double> xm, dxm;                // current master [nmv][3] and its motion

@@ -891,7 +891,7 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.counters.ensure(4));
     GMCP_CUDA_TRY(cudaMemsetAsync(N.counters.p, 0, 4 * sizeof(unsigned), s));
     GMCP_CUDA_TRY(N.Pinv.ensure(9 * (size_t)nv));
-    for (DBuf<double>* b : {&N.r, &N.z, &N.p, &N.Ap, &N.w, &N.xhat, &N.xt, &N.G, &N.dirn, &N.tmp, &N.P, &N.dP, &N.xi})
+    for (DBuf<double>* b : {&N.r, &N.z, &N.p, &N.Ap, &N.w, &N.xhat, &N.xt, &N.G, &N.dirn, &N.tmp, &N.P, &N.dP, &N.xi, &N.xl})
         GMCP_CUDA_TRY(b->ensure(n3));
     if (f32) GMCP_CUDA_TRY(N.cgrad32.ensure(n3));
     else GMCP_CUDA_TRY(N.cgrad64.ensure(n3));
