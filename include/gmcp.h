@@ -67,6 +67,8 @@ typedef struct {
     double dhat_guard, kappa_guard;  /* primitive guard barrier; kappa_guard 0 = off */
     int32_t device;             /* CUDA device ordinal */
     void* stream;               /* cudaStream_t */
+    int32_t use_graphs;         /* 1: replay repeated contact passes and PCG iteration
+                                   chunks as captured CUDA graphs (same results) */
 } ipc_params;
 
 /* Scene: a batch of independent environments concatenated; indices are
@@ -257,6 +259,21 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
  * IPC_ERR_LINESEARCH x and v are left at x^t, v^t. */
 ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
                            const double* dx_pred_dev, ipc_step_stats* stats);
+
+/* Autotuner (not part of the method): times full contact passes at (x_dev,
+ * xm0_dev) with step dx_dev (may be NULL) for candidate launch shapes -- the
+ * persistent broad-phase / CCD grid (2, 4, 8, 16, 32 blocks per SM), then the
+ * sample kernel's grid (1, 2, 4, 8, 16 blocks per SM) -- by coordinate
+ * search, the median of `reps` passes each (CUDA events), and keeps the
+ * fastest in the context.  Results of every entry point are identical for
+ * every launch shape (each slave triangle's sums have a fixed order); only
+ * the time changes.  Outputs (host, may be NULL): the chosen shapes and the
+ * best pass time in ms.  Synchronises. */
+ipc_status ipc_autotune(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev, const double* dx_dev,
+                        int32_t reps, int32_t* samples_bpsm_out, int32_t* query_bpsm_out, double* ms_out);
+
+/* Set the launch shapes directly (blocks per SM, each in [1, 64]). */
+ipc_status ipc_set_launch_shape(ipc_ctx* ctx, int32_t samples_bpsm, int32_t query_bpsm);
 
 /* Section profiler (not part of the method): CUDA events recorded on the
  * context stream around each group of launches (grid build, candidate

@@ -38,7 +38,8 @@ class Params(C.Structure):
                 ("gravity", C.c_double * 3), ("newton_tol", C.c_double), ("pcg_rel_tol", C.c_double),
                 ("max_newton", C.c_int32), ("max_pcg", C.c_int32), ("max_halvings", C.c_int32),
                 ("ccd_slack", C.c_double), ("ccd_max_iter", C.c_int32), ("dhat_guard", C.c_double),
-                ("kappa_guard", C.c_double), ("device", C.c_int32), ("stream", C.c_void_p)]
+                ("kappa_guard", C.c_double), ("device", C.c_int32), ("stream", C.c_void_p),
+                ("use_graphs", C.c_int32)]
 
 
 class SceneC(C.Structure):
@@ -142,6 +143,11 @@ def lib():
     L.ipc_ws_get_params.argtypes = [P, P]
     L.ipc_ws_predict.restype = C.c_int
     L.ipc_ws_predict.argtypes = [P, P, P, P, P]
+    L.ipc_autotune.restype = C.c_int
+    L.ipc_autotune.argtypes = [P, P, P, P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_double)]
+    L.ipc_set_launch_shape.restype = C.c_int
+    L.ipc_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
     L.ipc_newton_step.restype = C.c_int
     L.ipc_newton_step.argtypes = [P, P, P, P, P, C.POINTER(StepStats)]
     _lib = L
@@ -163,6 +169,7 @@ def make_params(p: dict, precision="fp64", device=0, stream=0) -> Params:
     q.kappa_guard = float(p.get("kappa_guard") or 0.0)
     q.device = int(device)
     q.stream = C.c_void_p(int(stream)) if stream else None
+    q.use_graphs = int(p.get("use_graphs", 1))
     return q
 
 
@@ -458,3 +465,16 @@ class Context:
         dx = t.empty((self.nv, 3), dtype=t.float64, device=self.device)
         self._check(lib().ipc_ws_predict(self.h, _ptr(x), _ptr(v), _ptr(xm), _ptr(dx)))
         return dx
+
+    # -- launch shapes ------------------------------------------------------
+    def autotune(self, x, xm0, dx=None, reps=3):
+        """Pick the launch shapes of the contact pass by timing; returns
+        (samples blocks/SM, query blocks/SM, best ms)."""
+        x, xm0, dx = self._as(x), self._as(xm0), self._as(dx)
+        a, b, ms = C.c_int32(), C.c_int32(), C.c_double()
+        self._check(lib().ipc_autotune(self.h, _ptr(x), _ptr(xm0), _ptr(dx), int(reps), C.byref(a),
+                                       C.byref(b), C.byref(ms)))
+        return a.value, b.value, ms.value
+
+    def set_launch_shape(self, samples_bpsm, query_bpsm):
+        self._check(lib().ipc_set_launch_shape(self.h, int(samples_bpsm), int(query_bpsm)))

@@ -138,6 +138,123 @@ cudaError_t grow_candidates(Ctx& c, int32_t need_f, int32_t need_e, int32_t need
     return cudaSuccess;
 }
 
+// ---------------------------------------------------------------------------
+// the fused contact pass: one enqueue of all its work, captured as a CUDA
+// graph for repeated calls with the same arguments
+// ---------------------------------------------------------------------------
+struct ContactPassArgs {
+    const double *x, *xm0, *xm1, *dx;
+    double* edev;
+    void* grad;
+    bool hess, counts, host_energy, want_alpha, lazy;
+};
+
+// Everything one pass queues (no synchronisation): the master displacement,
+// the step bounds' initial values, the broad phase, samples and gathers, the
+// step bounds, and (lazy) the copies of host-visible results and capacity
+// flags into the pinned area.
+cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
+    const double* dxm = nullptr;
+    if (A.dx && A.xm1) {
+        GMCP_CUDA_TRY(c.dxm.ensure(3 * (size_t)c.nmv + 3));
+        const int64_t n = 3 * c.nmv;
+        if (n > 0) {
+            k_sub<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(A.xm1, A.xm0, c.dxm.p, n);
+            GMCP_CUDA_TRY(cudaGetLastError());
+        }
+        dxm = c.dxm.p;
+    }
+    if (A.dx) {
+        GMCP_CUDA_TRY(cudaMemcpyAsync(c.u64_tmp.p, c.pin->init, 2 * sizeof(unsigned long long),
+                                      cudaMemcpyHostToDevice, c.stream));
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
+    }
+    GMCP_CUDA_TRY(run_candidates(c, A.x, A.xm0, A.lazy));
+    long long* ctr = nullptr;
+    if (A.counts) {
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
+        ctr = c.i64_tmp.p;
+    }
+    GMCP_CUDA_TRY(contact_eval(c, A.x, A.xm0, A.edev, A.grad, A.hess, ctr, A.dx, dxm,
+                               A.dx ? c.u64_tmp.p : nullptr));
+    if (A.dx)
+        GMCP_CUDA_TRY(bp_ccd_accd(c, A.x, A.dx, A.xm0, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8, true, A.lazy));
+    if (!A.lazy) return cudaSuccess;
+    if (A.host_energy)
+        GMCP_CUDA_TRY(cudaMemcpyAsync(&c.pin->energy, A.edev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
+    if (A.counts)
+        GMCP_CUDA_TRY(cudaMemcpyAsync(c.pin->counts, c.i64_tmp.p, 4 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+    if (A.want_alpha) {
+        GMCP_CUDA_TRY(cudaMemcpyAsync(c.pin->bits, c.u64_tmp.p, 2 * sizeof(unsigned long long),
+                                      cudaMemcpyDeviceToHost, c.stream));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(c.pin->ctr_ccd, c.i64_tmp.p + 8, 4 * sizeof(long long),
+                                      cudaMemcpyDeviceToHost, c.stream));
+    }
+    return cudaMemcpyAsync(c.pin->flags, c.misc_i32.p, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream);
+}
+
+// capacity flags of the last lazy pass (valid after a synchronisation)
+bool pass_overflowed(const Ctx& c) {
+    const int32_t* f = c.pin->flags;
+    return f[1] || f[2] || f[3] || f[12];
+}
+
+cudaError_t grow_after_overflow(Ctx& c) {
+    const int32_t* f = c.pin->flags;
+    if (f[1] || f[2] || f[3]) GMCP_CUDA_TRY(grow_candidates(c, f[1], f[2], f[3]));
+    if (f[12]) GMCP_CUDA_TRY(c.cell_ent.ensure(2 * c.cell_ent.n));
+    return cudaSuccess;
+}
+
+// the arguments and capacities a captured pass depends on
+std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) {
+    return {(uintptr_t)A.x, (uintptr_t)A.xm0, (uintptr_t)A.xm1, (uintptr_t)A.dx, (uintptr_t)A.edev,
+            (uintptr_t)A.grad, (uintptr_t)A.hess, (uintptr_t)A.counts, (uintptr_t)A.host_energy,
+            (uintptr_t)A.want_alpha, (uintptr_t)c.cap_f, (uintptr_t)c.cap_e, (uintptr_t)c.cap_p,
+            (uintptr_t)c.cell_ent.n, (uintptr_t)c.stream, (uintptr_t)c.tune_samples_bpsm,
+            (uintptr_t)c.tune_query_bpsm,
+            // every context buffer the pass touches: a reallocation between
+            // capture and replay must not leave a stale address in the graph
+            (uintptr_t)c.red_tmp.p, (uintptr_t)c.red_tmp.n, (uintptr_t)c.cell_ent.p, (uintptr_t)c.cand_face.p,
+            (uintptr_t)c.cand_edge.p, (uintptr_t)c.cand_point.p, (uintptr_t)c.cand_count.p, (uintptr_t)c.active.p,
+            (uintptr_t)c.qlist_tri.p, (uintptr_t)c.qlist_box.p, (uintptr_t)c.qlist_cell.p, (uintptr_t)c.mbox.p,
+            (uintptr_t)c.mcell.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
+            (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
+            (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,
+            (uintptr_t)c.cb_val64.p, (uintptr_t)c.u64_tmp.p, (uintptr_t)c.i64_tmp.p, (uintptr_t)c.misc_i32.p,
+            (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p};
+}
+
+// Capture one pass on the context's private capture stream (nothing runs);
+// on any failure no graph is kept and calls take the plain path.
+void capture_contact_pass(Ctx& c, const ContactPassArgs& A) {
+    c.cp_graph.reset();
+    if (!c.cap_stream && cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c.cap_stream = nullptr;
+        return;
+    }
+    const std::vector<uintptr_t> key = contact_pass_key(c, A);
+    cudaStream_t user = c.stream;
+    c.stream = c.cap_stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t e1 = enqueue_contact_pass(c, A);
+        const cudaError_t e2 = cudaStreamEndCapture(c.stream, &g);
+        e = e1 != cudaSuccess ? e1 : e2;
+    }
+    c.stream = user;
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&c.cp_graph.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c.cp_graph.reset();
+        return;
+    }
+    c.cp_graph.key = key;
+}
+
 }  // namespace gmcp
 
 // ===========================================================================
@@ -617,6 +734,10 @@ static void alloc_call_buffers(Ctx& c) {
     CK(c.scal.ensure(16));
     CK(cudaMallocHost(reinterpret_cast<void**>(&c.h_scalars), 16 * sizeof(double)));
     CK(cudaMallocHost(reinterpret_cast<void**>(&c.h_counts), 16 * sizeof(long long)));
+    CK(cudaMallocHost(reinterpret_cast<void**>(&c.pin), sizeof(PinnedIO)));
+    memset(c.pin, 0, sizeof(PinnedIO));
+    c.pin->init[0] = 0x7FF0000000000000ULL;   // alpha_lin starts at +inf
+    c.pin->init[1] = 0x3FF0000000000000ULL;   // alpha_accd starts at 1
 }
 
 extern "C" {
@@ -672,6 +793,7 @@ ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx*
         c.P.L = params->face_rule_level; c.P.nk = 1 << (2 * c.P.L);
         c.P.dhat_guard = params->dhat_guard; c.P.kappa_guard = params->kappa_guard;
         c.P.ccd_slack = params->ccd_slack; c.P.ccd_max_iter = params->ccd_max_iter;
+        c.graphs = params->use_graphs != 0;
         c.n_env = scene->n_env;
         auto cp = [&](const int64_t* p) { return std::vector<int64_t>(p, p + scene->n_env + 1); };
         c.env_vert_off = cp(scene->env_vert_off); c.env_tet_off = cp(scene->env_tet_off);
@@ -722,6 +844,10 @@ void ipc_destroy(ipc_ctx* ctx) {
     cudaStreamSynchronize(c.stream);
     if (c.h_scalars) cudaFreeHost(c.h_scalars);
     if (c.h_counts) cudaFreeHost(c.h_counts);
+    c.cp_graph.reset();
+    c.pcg_graph.reset();
+    if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+    if (c.pin) cudaFreeHost(c.pin);
     delete ctx;   // every DBuf member frees its device memory
 }
 
@@ -875,60 +1001,36 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
     // a call that returns host values synchronises once at the end; it then
     // also checks the capacity flags and redoes the pass after growing
     const bool lazy = energy_host || counts || want_alpha;
-    const double* dxm = nullptr;
-    if (dx_dev && xm1_dev) {
-        API_CK(ctx, c.dxm.ensure(3 * (size_t)c.nmv + 3));
-        const int64_t n = 3 * c.nmv;
-        if (n > 0) {
-            k_sub<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(xm1_dev, xm0_dev, c.dxm.p, n);
-            API_CK(ctx, cudaGetLastError());
-        }
-        dxm = c.dxm.p;
-    }
     double* edev = energy_dev;
     if (energy_host && !energy_dev) edev = c.scal.p;
-    unsigned long long bits[2] = {0, 0};
-    long long ctr_ccd[4] = {0, 0, 0, 0};
-    for (int attempt = 0;; ++attempt) {
-        if (attempt >= 6) return fail_ctx(ctx, IPC_ERR_CAPACITY, "ipc_contact_pass: capacities did not settle");
-        if (dx_dev) {
-            const unsigned long long init[2] = {0x7FF0000000000000ULL, 0x3FF0000000000000ULL};
-            API_CK(ctx, cudaMemcpyAsync(c.u64_tmp.p, init, sizeof(init), cudaMemcpyHostToDevice, c.stream));
-            API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
+    ContactPassArgs A{x_dev, xm0_dev, xm1_dev, dx_dev, edev, grad_dev, hess != nullptr, counts != nullptr,
+                      energy_host != nullptr, want_alpha, lazy};
+    if (!lazy) {
+        API_CK(ctx, enqueue_contact_pass(c, A));
+    } else {
+        bool done = false;
+        const bool use_graph = c.graphs && !c.prof.on;
+        if (use_graph && c.cp_graph.exec && c.cp_graph.key == contact_pass_key(c, A)) {
+            API_CK(ctx, cudaGraphLaunch(c.cp_graph.exec, c.stream));
+            API_CK(ctx, cudaStreamSynchronize(c.stream));
+            if (!pass_overflowed(c)) done = true;
+            else c.cp_graph.reset();
         }
-        API_CK(ctx, run_candidates(c, x_dev, xm0_dev, lazy));
-        long long* ctr = nullptr;
-        if (counts) {
-            API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
-            ctr = c.i64_tmp.p;
+        if (!done) {
+            for (int attempt = 0;; ++attempt) {
+                if (attempt >= 6) return fail_ctx(ctx, IPC_ERR_CAPACITY, "ipc_contact_pass: capacities did not settle");
+                API_CK(ctx, enqueue_contact_pass(c, A));
+                API_CK(ctx, cudaStreamSynchronize(c.stream));
+                if (!pass_overflowed(c)) break;
+                API_CK(ctx, grow_after_overflow(c));
+            }
+            if (use_graph) capture_contact_pass(c, A);
         }
-        API_CK(ctx, contact_eval(c, x_dev, xm0_dev, edev, grad_dev, hess != nullptr, ctr, dx_dev, dxm,
-                                 dx_dev ? c.u64_tmp.p : nullptr));
-        if (dx_dev)
-            API_CK(ctx, bp_ccd_accd(c, x_dev, dx_dev, xm0_dev, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8,
-                                    true, lazy));
-        if (!lazy) break;
-        if (energy_host)
-            API_CK(ctx, cudaMemcpyAsync(c.h_scalars, edev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
-        if (counts)
-            API_CK(ctx, cudaMemcpyAsync(c.h_counts, c.i64_tmp.p, 4 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
-        if (want_alpha) {
-            API_CK(ctx, cudaMemcpyAsync(bits, c.u64_tmp.p, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
-            API_CK(ctx, cudaMemcpyAsync(ctr_ccd, c.i64_tmp.p + 8, sizeof(ctr_ccd), cudaMemcpyDeviceToHost, c.stream));
-        }
-        int32_t flags[16];
-        API_CK(ctx, cudaMemcpyAsync(flags, c.misc_i32.p, sizeof(flags), cudaMemcpyDeviceToHost, c.stream));
-        API_CK(ctx, cudaStreamSynchronize(c.stream));
-        const bool cand_over = flags[1] || flags[2] || flags[3];
-        const bool grid_over = flags[12] != 0;
-        if (!cand_over && !grid_over) break;
-        if (cand_over) API_CK(ctx, grow_candidates(c, flags[1], flags[2], flags[3]));
-        if (grid_over) API_CK(ctx, c.cell_ent.ensure(2 * c.cell_ent.n));
     }
-    if (energy_host) *energy_host = c.h_scalars[0];
+    if (energy_host) *energy_host = c.pin->energy;
     if (counts) {
-        counts->face = c.h_counts[0]; counts->edge = c.h_counts[1]; counts->point = c.h_counts[2];
-        counts->guard = 0; counts->face_evaluated = c.h_counts[3];
+        counts->face = c.pin->counts[0]; counts->edge = c.pin->counts[1]; counts->point = c.pin->counts[2];
+        counts->guard = 0; counts->face_evaluated = c.pin->counts[3];
     }
     if (hess) {
         const bool f32 = c.P.precision == IPC_PREC_MIXED;
@@ -939,17 +1041,94 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
     }
     if (want_alpha) {
         double al, aa;
-        memcpy(&al, &bits[0], 8);
-        memcpy(&aa, &bits[1], 8);
+        memcpy(&al, &c.pin->bits[0], 8);
+        memcpy(&aa, &c.pin->bits[1], 8);
         if (al < INFINITY) al *= (1.0 - 1e-10);
         const double a = std::min(1.0, std::min(al, aa));
         if (alpha_host) *alpha_host = a;
         if (info) {
             info->alpha = a; info->alpha_lin = al; info->alpha_accd = aa;
-            info->n_pairs_pt = ctr_ccd[0]; info->n_pairs_ee = ctr_ccd[1];
-            info->iter_cap_hit = (int32_t)(ctr_ccd[2] != 0);
+            info->n_pairs_pt = c.pin->ctr_ccd[0]; info->n_pairs_ee = c.pin->ctr_ccd[1];
+            info->iter_cap_hit = (int32_t)(c.pin->ctr_ccd[2] != 0);
         }
     }
+    return IPC_OK;
+}
+
+ipc_status ipc_autotune(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev, const double* dx_dev,
+                        int32_t reps, int32_t* samples_bpsm_out, int32_t* query_bpsm_out, double* ms_out) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!x_dev || (!xm0_dev && c.nmv > 0)) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_autotune: NULL positions");
+    if (reps < 1) reps = 3;
+    API_CK(ctx, cudaSetDevice(c.device));
+    const bool graphs = c.graphs, prof = c.prof.on;
+    c.graphs = false;
+    c.prof.on = false;
+    cudaEvent_t e0, e1;
+    API_CK(ctx, cudaEventCreate(&e0));
+    API_CK(ctx, cudaEventCreate(&e1));
+    double energy = 0.0, alpha = 0.0;
+    ipc_status st = IPC_OK;
+    // median time of `reps` full passes (after one untimed pass)
+    auto time_pass = [&](double* ms) -> ipc_status {
+        std::vector<float> t;
+        for (int r = 0; r <= reps; ++r) {
+            cudaEventRecord(e0, c.stream);
+            ipc_status q = ipc_contact_pass(ctx, x_dev, xm0_dev, nullptr, dx_dev, nullptr, &energy, nullptr,
+                                            nullptr, dx_dev ? &alpha : nullptr, nullptr, nullptr);
+            if (q != IPC_OK) return q;
+            cudaEventRecord(e1, c.stream);
+            cudaEventSynchronize(e1);
+            float m = 0.f;
+            cudaEventElapsedTime(&m, e0, e1);
+            if (r > 0) t.push_back(m);
+        }
+        std::sort(t.begin(), t.end());
+        *ms = t[t.size() / 2];
+        return IPC_OK;
+    };
+    const int cand_q[] = {2, 4, 8, 16, 32};
+    const int cand_s[] = {1, 2, 4, 8, 16};
+    double best = 1e300;
+    int bq = c.tune_query_bpsm, bs = c.tune_samples_bpsm;
+    for (int q : cand_q) {
+        c.tune_query_bpsm = q;
+        double ms;
+        if ((st = time_pass(&ms)) != IPC_OK) break;
+        if (ms < best) { best = ms; bq = q; }
+    }
+    c.tune_query_bpsm = bq;
+    if (st == IPC_OK) {
+        best = 1e300;
+        for (int b : cand_s) {
+            c.tune_samples_bpsm = b;
+            double ms;
+            if ((st = time_pass(&ms)) != IPC_OK) break;
+            if (ms < best) { best = ms; bs = b; }
+        }
+        c.tune_samples_bpsm = bs;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c.graphs = graphs;
+    c.prof.on = prof;
+    c.cp_graph.reset();
+    if (st != IPC_OK) return st;
+    if (samples_bpsm_out) *samples_bpsm_out = bs;
+    if (query_bpsm_out) *query_bpsm_out = bq;
+    if (ms_out) *ms_out = best;
+    return IPC_OK;
+}
+
+ipc_status ipc_set_launch_shape(ipc_ctx* ctx, int32_t samples_bpsm, int32_t query_bpsm) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (samples_bpsm < 1 || samples_bpsm > 64 || query_bpsm < 1 || query_bpsm > 64)
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_set_launch_shape: blocks per SM must be in [1, 64]");
+    c.tune_samples_bpsm = samples_bpsm;
+    c.tune_query_bpsm = query_bpsm;
+    c.cp_graph.reset();
     return IPC_OK;
 }
 

@@ -736,7 +736,7 @@ static cudaError_t ensure_query_list(Ctx& c) {
     return cudaSuccess;
 }
 
-static unsigned persistent_blocks(Ctx& c) { return (unsigned)(sm_count(c.device) * 8); }
+static unsigned persistent_blocks(Ctx& c) { return (unsigned)(sm_count(c.device) * c.tune_query_bpsm); }
 
 cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
     ProfScope ps(c.prof, c.stream, "query");

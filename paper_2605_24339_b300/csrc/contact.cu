@@ -545,7 +545,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
                            long long* counters, const double* dx, const double* dxm,
                            unsigned long long* alpha_bits, LagArgs LG = LagArgs()) {
     const int threads = 256;
-    const int blocks = sm_count(c.device) * 8;
+    const int blocks = sm_count(c.device) * c.tune_samples_bpsm;
     k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
         c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG);
     return cudaGetLastError();

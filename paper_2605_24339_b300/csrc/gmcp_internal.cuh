@@ -209,6 +209,30 @@ struct NewtonState {
     DBuf<int32_t> bad;                   // inverted-tet flag
 };
 
+// A captured CUDA graph and the arguments it was captured with.
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<uintptr_t> key;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
+    }
+    ~GraphCache() { reset(); }
+};
+
+// Pinned host storage for every host <-> device transfer a captured graph
+// performs (a graph replays copies from and to fixed host addresses).
+struct PinnedIO {
+    unsigned long long init[2];   // alpha_lin / alpha_accd initial bits
+    unsigned long long bits[2];
+    long long ctr_ccd[4];
+    long long counts[8];
+    int32_t flags[16];
+    double energy;
+    double pcg[4];
+};
+
 struct WarmStart;              // learned warm start (warmstart.cu)
 void ws_destroy(WarmStart* w);
 
@@ -274,6 +298,18 @@ struct Ctx {
     long long* h_counts = nullptr;
 
     Profiler prof;
+
+    // launch shapes chosen by the autotuner (ipc_autotune); results do not
+    // depend on them
+    int tune_samples_bpsm = 8;     // k_samples blocks per SM (256 threads)
+    int tune_query_bpsm = 8;       // persistent query / CCD blocks per SM
+
+    // CUDA graphs
+    bool graphs = false;
+    GraphCache cp_graph;           // ipc_contact_pass
+    GraphCache pcg_graph;          // one PCG chunk
+    cudaStream_t cap_stream = nullptr;   // private stream graphs are captured on
+    PinnedIO* pin = nullptr;
 
     // host copies kept for the time stepper
     std::vector<int32_t> h_tets;

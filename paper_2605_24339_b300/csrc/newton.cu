@@ -392,7 +392,8 @@ enum : int {
     kBreak = 5,      // p^T A p <= 0 seen
     kDone = 6,       // converged
     kIters = 7,      // iterations taken (valid once kBreak or kDone is set)
-    kThr = 8         // rel_tol |b|
+    kThr = 8,        // rel_tol |b|
+    kIt = 9          // index of the current iteration (advanced by k_pcg_update)
 };
 constexpr int kPcgThreads = 256;
 
@@ -486,6 +487,7 @@ k_pcg_init(int64_t nv, const double* __restrict__ Pinv, const double* __restrict
         scal[kBreak] = 0.0;
         scal[kDone] = tb > 0.0 ? 0.0 : 1.0;
         scal[kIters] = 0.0;
+        scal[kIt] = 0.0;
     }
 }
 
@@ -493,10 +495,11 @@ k_pcg_init(int64_t nv, const double* __restrict__ Pinv, const double* __restrict
 // FP32 products of the FP32 matrix and the FP32 copy of p, FP32 row sums.
 template <class TA>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_spmv(int64_t nv, int it, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
            const TA* __restrict__ A, const double* __restrict__ p, const float* __restrict__ p32,
            double* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
+    const int it = (int)scal[kIt];
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = tid / 3;
     const int comp = (int)(tid - 3 * i);
@@ -527,10 +530,11 @@ k_pcg_spmv(int64_t nv, int it, const int32_t* __restrict__ rp, const int32_t* __
 
 // x += al p, r -= al Ap, z = P^-1 r, then r.r (convergence) and r.z
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_update(int64_t nv, int it, const double* __restrict__ Pinv, double* __restrict__ x, double* __restrict__ r,
+k_pcg_update(int64_t nv, const double* __restrict__ Pinv, double* __restrict__ x, double* __restrict__ r,
              double* __restrict__ z, const double* __restrict__ p, const double* __restrict__ Ap, double* part,
              unsigned* counter, double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
+    const int it = (int)scal[kIt];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double al = scal[kRz0 + (it & 1)] / scal[kPAp];
     double rr = 0.0, rz = 0.0;
@@ -556,17 +560,20 @@ k_pcg_update(int64_t nv, int it, const double* __restrict__ Pinv, double* __rest
         } else {
             scal[kRz0 + ((it + 1) & 1)] = trz;
         }
+        // every block read kIt before it arrived at the counter
+        scal[kIt] = (double)(it + 1);
     }
 }
 
-// p = z + (rz_new / rz_old) p
+// p = z + (rz_new / rz_old) p; kIt already holds the next iteration's index
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_dir(int64_t n, int it, const double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32,
+k_pcg_dir(int64_t n, const double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32,
           const double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double be = scal[kRz0 + ((it + 1) & 1)] / scal[kRz0 + (it & 1)];
+    const int nx = (int)scal[kIt];
+    const double be = scal[kRz0 + (nx & 1)] / scal[kRz0 + ((nx + 1) & 1)];
     const double v = z[i] + be * p[i];
     p[i] = v;
     if (p32) p32[i] = (float)v;
@@ -721,38 +728,95 @@ cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double*
 // at p^T A p <= 0 (that iteration's update is skipped) or after max_it
 // iterations.  The host reads the flags once per 16 iterations; kernels
 // after the stop return at once.  Returns the iterations taken.
-cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters) {
+// queue `count` PCG iterations (each kernel returns at once after a stop)
+static cudaError_t pcg_enqueue_iters(Ctx& c, double* xout, int count) {
     NewtonState& N = *c.newton;
     const int64_t nv = c.nv, n = 3 * nv;
     cudaStream_t s = c.stream;
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    double* sc = N.scal.p;
-    double* hb = c.h_scalars;
+    float* p32 = f32 ? N.p32.p : nullptr;
+    const unsigned g_row = nblk(nv, kPcgThreads), g_comp = nblk(n, kPcgThreads);
+    for (int j = 0; j < count; ++j) {
+        if (f32)
+            k_pcg_spmv<float><<<g_comp, kPcgThreads, 0, s>>>(nv, N.rp.p, N.ci.p, N.A32.p, N.p.p, p32, N.Ap.p,
+                                                             N.part.p, N.counters.p + 1, N.scal.p);
+        else
+            k_pcg_spmv<double><<<g_comp, kPcgThreads, 0, s>>>(nv, N.rp.p, N.ci.p, N.A64.p, N.p.p, p32, N.Ap.p,
+                                                              N.part.p, N.counters.p + 1, N.scal.p);
+        k_pcg_update<<<g_row, kPcgThreads, 0, s>>>(nv, N.Pinv.p, xout, N.r.p, N.z.p, N.p.p, N.Ap.p, N.part.p,
+                                                   N.counters.p + 2, N.scal.p);
+        k_pcg_dir<<<g_comp, kPcgThreads, 0, s>>>(n, N.z.p, N.p.p, p32, N.scal.p);
+    }
+    GMCP_CUDA_TRY(cudaGetLastError());
+    // stop flags and iteration count for the host
+    return cudaMemcpyAsync(c.pin->pcg, N.scal.p + kBreak, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+constexpr int kPcgChunk = 16;
+
+// the chunk of kPcgChunk iterations as a CUDA graph (captured on the
+// context's private stream); false if capture is not possible
+static bool pcg_chunk_graph(Ctx& c, double* xout) {
+    NewtonState& N = *c.newton;
+    const std::vector<uintptr_t> key = {(uintptr_t)xout, (uintptr_t)N.p.p, (uintptr_t)N.p32.p, (uintptr_t)N.A32.p,
+                                        (uintptr_t)N.A64.p, (uintptr_t)N.Ap.p, (uintptr_t)N.r.p, (uintptr_t)N.z.p,
+                                        (uintptr_t)N.Pinv.p, (uintptr_t)N.part.p, (uintptr_t)N.scal.p,
+                                        (uintptr_t)N.counters.p, (uintptr_t)c.pin};
+    if (c.pcg_graph.exec && c.pcg_graph.key == key) return true;
+    c.pcg_graph.reset();
+    if (!c.cap_stream && cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        c.cap_stream = nullptr;
+        return false;
+    }
+    cudaStream_t user = c.stream;
+    c.stream = c.cap_stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t e1 = pcg_enqueue_iters(c, xout, kPcgChunk);
+        const cudaError_t e2 = cudaStreamEndCapture(c.stream, &g);
+        e = e1 != cudaSuccess ? e1 : e2;
+    }
+    c.stream = user;
+    if (e == cudaSuccess && g) e = cudaGraphInstantiate(&c.pcg_graph.exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c.pcg_graph.reset();
+        return false;
+    }
+    c.pcg_graph.key = key;
+    return true;
+}
+
+// Block-Jacobi PCG for A p = b (A on the pattern N.rp / N.ci; FP32 in the
+// mixed path, FP64 otherwise), p = 0 start; stops at ||r|| <= rel_tol ||b||,
+// at p^T A p <= 0 (that iteration's update is skipped) or after max_it
+// iterations.  The host reads the flags once per 16 iterations (a captured
+// graph per chunk when graphs are on); kernels after the stop return at
+// once.  Returns the iterations taken.
+cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters) {
+    NewtonState& N = *c.newton;
+    const int64_t nv = c.nv;
+    cudaStream_t s = c.stream;
+    const bool f32 = c.P.precision == IPC_PREC_MIXED;
     float* p32 = f32 ? N.p32.p : nullptr;
     if (f32) k_diag_inv<float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A32.p, N.Pinv.p);
     else k_diag_inv<double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A64.p, N.Pinv.p);
     GMCP_CUDA_TRY(cudaGetLastError());
-    const unsigned g_row = nblk(nv, kPcgThreads), g_comp = nblk(n, kPcgThreads);
-    k_pcg_init<<<g_row, kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, N.r.p, N.z.p, N.p.p, p32, N.part.p,
-                                             N.counters.p, sc, rel_tol);
+    k_pcg_init<<<nblk(nv, kPcgThreads), kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, N.r.p, N.z.p, N.p.p, p32,
+                                                             N.part.p, N.counters.p, N.scal.p, rel_tol);
     GMCP_CUDA_TRY(cudaGetLastError());
+    const bool graph = c.graphs && !c.prof.on && pcg_chunk_graph(c, xout);
     *iters = max_it;
     for (int it = 0; it < max_it;) {
-        const int chunk = std::min(16, max_it - it);
-        for (int j = 0; j < chunk; ++j, ++it) {
-            if (f32)
-                k_pcg_spmv<float><<<g_comp, kPcgThreads, 0, s>>>(nv, it, N.rp.p, N.ci.p, N.A32.p, N.p.p, p32, N.Ap.p,
-                                                                 N.part.p, N.counters.p + 1, sc);
-            else
-                k_pcg_spmv<double><<<g_comp, kPcgThreads, 0, s>>>(nv, it, N.rp.p, N.ci.p, N.A64.p, N.p.p, p32,
-                                                                  N.Ap.p, N.part.p, N.counters.p + 1, sc);
-            k_pcg_update<<<g_row, kPcgThreads, 0, s>>>(nv, it, N.Pinv.p, xout, N.r.p, N.z.p, N.p.p, N.Ap.p,
-                                                       N.part.p, N.counters.p + 2, sc);
-            k_pcg_dir<<<g_comp, kPcgThreads, 0, s>>>(n, it, N.z.p, N.p.p, p32, sc);
-        }
-        GMCP_CUDA_TRY(cudaGetLastError());
-        GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + kBreak, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        const int chunk = std::min(kPcgChunk, max_it - it);
+        if (graph && chunk == kPcgChunk) GMCP_CUDA_TRY(cudaGraphLaunch(c.pcg_graph.exec, s));
+        else GMCP_CUDA_TRY(pcg_enqueue_iters(c, xout, chunk));
+        it += chunk;
         GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+        const double* hb = c.pin->pcg;
         if (hb[0] != 0.0 || hb[1] != 0.0) {
             *iters = (int)hb[2];
             break;

@@ -448,6 +448,29 @@ def _frame_from_dir(d):
     return np.stack([x, y, z], axis=1)
 
 
+def press_pads(scene: Scene, depth: float) -> np.ndarray:
+    """A pressed state of a batch of pads: every pad (a connected component of
+    the tet mesh) is translated rigidly by ``depth`` along the unit direction
+    of its Dirichlet (top) vertices' scripted velocity.  Returns x [nv,3]."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    nv = scene.X.shape[0]
+    T = scene.tets
+    rows = np.concatenate([T[:, 0], T[:, 0], T[:, 0]])
+    cols = np.concatenate([T[:, 1], T[:, 2], T[:, 3]])
+    g = coo_matrix((np.ones(rows.shape[0], dtype=np.int8), (rows, cols)), shape=(nv, nv))
+    ncomp, lab = connected_components(g, directed=False)
+    top = scene.dirichlet.astype(bool)
+    vd = scene.v_dirichlet
+    nrm = np.linalg.norm(vd, axis=1)
+    u = np.zeros((ncomp, 3))
+    sel = top & (nrm > 0)
+    np.add.at(u, lab[sel], vd[sel] / nrm[sel, None])
+    un = np.linalg.norm(u, axis=1)
+    u[un > 0] /= un[un > 0, None]
+    return scene.X + depth * u[lab]
+
+
 def drape_on_master(scene: Scene, depth: float, gap_lo: float = 0.3,
                     gap_hi: float = 0.9, seed: int = 7) -> np.ndarray:
     """A pressed, intersection-free pad state for a single-env scene whose
