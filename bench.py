@@ -494,6 +494,47 @@ def run_passes(args):
                       "ccd_pairs_ee": info["n_ee"]}))
 
 
+def run_mlp(args):
+    """--steps training steps of the warm-start network on a 594,441-vertex
+    batch of seeded features and targets (the command line for profiling
+    the tensor-core kernels)."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    from paper_2605_24339_b300 import warmstart as WS
+    sc = S.gel_on_terrain()
+    ctx = binding.Context(sc, precision="mixed")
+    ctx.ws_create(WS.init_params(0), lr=1e-3, **WS.default_scales(sc))
+    n = sc.X.shape[0]
+    g = torch.Generator(device="cuda").manual_seed(3)
+    f = torch.randn((n, 32), device="cuda", generator=g).to(torch.bfloat16)
+    t = torch.randn((n, 3), device="cuda", generator=g)
+    m = torch.ones(n, device="cuda")
+    for _ in range(args.steps):
+        loss = ctx.ws_train_step(f, t, m)
+    torch.cuda.synchronize()
+    print(json.dumps({"mlp_train_steps": args.steps, "loss": loss}))
+
+
+def run_newton(args):
+    """--steps time steps of the gel_on_terrain press from rest (the command
+    line for profiling the time-stepper kernels)."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    sc = S.gel_on_terrain()
+    ctx = binding.Context(sc, precision=args.precision)
+    x = torch.as_tensor(sc.X.copy(), device="cuda")
+    v = torch.as_tensor(sc.v_dirichlet.copy(), device="cuda")
+    top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
+    vd = torch.as_tensor(sc.v_dirichlet, device="cuda")
+    for _ in range(args.steps):
+        st = ctx.newton_step(x, v)
+        v[top] = vd[top]
+    torch.cuda.synchronize()
+    print(json.dumps({"newton_steps": args.steps, "last": {k: st[k] for k in ("status", "newton_iters", "pcg_iters")}}))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -542,13 +583,18 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-envs measurement")
     ap.add_argument("--no-newton", action="store_true",
                     help="skip the time-step measurement (newton_step key)")
-    ap.add_argument("--mode", default="bench", choices=["bench", "passes"],
-                    help="passes: run --steps untimed contact passes (for profilers)")
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton"],
+                    help="passes / mlp / newton: run --steps untimed contact passes, network "
+                         "training steps or time steps (command lines for profilers)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
     if args.mode == "passes":
         run_passes(args)
+    elif args.mode == "mlp":
+        run_mlp(args)
+    elif args.mode == "newton":
+        run_newton(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -137,11 +137,18 @@ __device__ __forceinline__ uint32_t tile_off(int r, int k, int K) {
     return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
 }
 
-// copy rows [row0, row0 + R) x K of a row-major BF16 matrix (row stride ld
-// elements, rows >= nrows read as zero) into a K-major tile; 16-byte chunks,
-// eight consecutive threads fill one core matrix
-__device__ __forceinline__ void stage_tile(uint8_t* tile, const __nv_bfloat16* src, int64_t ld, int64_t row0,
-                                           int64_t nrows, int R, int K, int k0) {
+// 16-byte asynchronous global -> shared copy; src_bytes 0 fills zeros
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// queue the copy of rows [row0, row0 + R) x columns [k0, k0 + K) of a
+// row-major BF16 matrix (row stride ld elements; rows >= nrows read as zero)
+// into a K-major tile; eight consecutive threads fill one core matrix
+__device__ __forceinline__ void stage_tile_async(uint8_t* tile, const __nv_bfloat16* src, int64_t ld, int64_t row0,
+                                                 int64_t nrows, int R, int K, int64_t k0) {
     const int per_row = K >> 3;
     const int total = R * per_row;
     for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
@@ -149,19 +156,59 @@ __device__ __forceinline__ void stage_tile(uint8_t* tile, const __nv_bfloat16* s
         const int j = (idx >> 3) % per_row;
         const int rg = (idx >> 3) / per_row;
         const int r = rg * 8 + rr;
-        uint4 v = make_uint4(0, 0, 0, 0);
         const int64_t gr = row0 + r;
-        if (gr < nrows) v = __ldg(reinterpret_cast<const uint4*>(src + gr * ld + k0 + 8 * j));
-        *reinterpret_cast<uint4*>(tile + tile_off(r, 8 * j, K)) = v;
+        const bool ok = gr < nrows;
+        cp_async16(tile + tile_off(r, 8 * j, K), ok ? (const void*)(src + gr * ld + k0 + 8 * j) : (const void*)src,
+                   ok ? 16u : 0u);
     }
 }
 
 // ----------------------------------------------------- activation GEMM ---
-// C = epilogue(A W^T), A [mp][K] BF16 row-major (the tile rows of this CTA),
-// W [256][K] BF16 row-major (K-major), persistent over 128-row tiles with W
-// resident in shared memory.  EPI 0: + bias, ReLU.  EPI 1: times
-// (mask > 0), mask [mp][256] BF16 (the previous layer's activation).
-// Writes C [mp][256] (if non-null) and C^T [256][mp] (if non-null).
+// C = epilogue(A W^T), A [mp][K] BF16 row-major, W [256][K] BF16 row-major
+// (K-major), persistent over 128-row tiles with W resident in shared memory.
+// Two tensor-memory accumulators: the epilogue of tile i-1 runs while the
+// MMAs of tile i execute.  EPI 0: + bias, ReLU.  EPI 1: times (mask > 0),
+// mask [mp][256] BF16 (the previous layer's activation).  Writes C [mp][256]
+// (if non-null) and C^T [256][mp] (if non-null).
+template <int K, int EPI>
+__device__ __forceinline__ void act_epilogue(uint32_t tacc, int64_t m0, int64_t mp, const float* __restrict__ bias,
+                                             const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ C,
+                                             __nv_bfloat16* __restrict__ CT) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = warp * 32 + lane;
+    const int64_t gr = m0 + r;
+    for (int c0 = 0; c0 < 256; c0 += 16) {
+        float v[16];
+        tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        if (EPI == 0) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + bias[c0 + i], 0.0f);
+        } else {
+            const uint4* mk = reinterpret_cast<const uint4*>(mask + gr * 256 + c0);
+            uint4 m0v = __ldg(mk), m1v = __ldg(mk + 1);
+            const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0v);
+            const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1v);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (!(__bfloat162float(mb0[i]) > 0.0f)) v[i] = 0.0f;
+                if (!(__bfloat162float(mb1[i]) > 0.0f)) v[8 + i] = 0.0f;
+            }
+        }
+        __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(v[i]);
+        if (C) {
+            uint4* dst = reinterpret_cast<uint4*>(C + gr * 256 + c0);
+            dst[0] = reinterpret_cast<const uint4*>(o)[0];
+            dst[1] = reinterpret_cast<const uint4*>(o)[1];
+        }
+        if (CT) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) CT[(int64_t)(c0 + i) * mp + gr] = o[i];
+        }
+    }
+}
+
 template <int K, int EPI>
 __global__ void __launch_bounds__(128, 1)
 k_umma_act(const __nv_bfloat16* __restrict__ A, int64_t mp, const __nv_bfloat16* __restrict__ W,
@@ -173,10 +220,12 @@ k_umma_act(const __nv_bfloat16* __restrict__ A, int64_t mp, const __nv_bfloat16*
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0) tmem_alloc(&tslot, 256);
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) tmem_alloc(&tslot, 512);
     if (threadIdx.x == 0) { mbar_init(&mbar, 1); abort_flag = 0; }
-    stage_tile(sW, W, K, 0, 256, 256, K, 0);
+    stage_tile_async(sW, W, K, 0, 256, 256, K, 0);
+    cp_async_commit();
+    cp_async_wait_all();
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
@@ -186,87 +235,71 @@ k_umma_act(const __nv_bfloat16* __restrict__ A, int64_t mp, const __nv_bfloat16*
     const uint32_t sbo = (K / 8) * 128;
     uint32_t phase = 0;
     const int64_t ntiles = mp / 128;
+    int64_t prev = -1;                                   // tile whose epilogue is pending
+    int buf = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t m0 = tile * 128;
-        stage_tile(sA, A, K, m0, mp, 128, K, 0);
+        stage_tile_async(sA, A, K, m0, mp, 128, K, 0);
+        cp_async_commit();
+        cp_async_wait_all();
         fence_async_smem();
+        tc_fence_before();
         __syncthreads();
         if (threadIdx.x == 0) {
             tc_fence_after();
 #pragma unroll
             for (int s = 0; s < K / 16; ++s)
-                umma_bf16(tmem, umma_desc(smem_u32(sA) + 256 * s, 128, sbo), umma_desc(smem_u32(sW) + 256 * s, 128, sbo),
-                          idesc, s > 0 ? 1u : 0u);
+                umma_bf16(tmem + (uint32_t)(buf * 256), umma_desc(smem_u32(sA) + 256 * s, 128, sbo),
+                          umma_desc(smem_u32(sW) + 256 * s, 128, sbo), idesc, s > 0 ? 1u : 0u);
             umma_commit(&mbar);
+        }
+        // the previous tile's epilogue overlaps these MMAs
+        if (prev >= 0) {
+            tc_fence_after();
+            act_epilogue<K, EPI>(tmem + (uint32_t)((buf ^ 1) * 256), prev * 128, mp, bias, mask, C, CT);
         }
         if (!mbar_wait(&mbar, phase)) {
             atomicExch(err, 1);
             abort_flag = 1;
         }
         phase ^= 1u;
-        __syncthreads();
-        if (abort_flag) break;
-        tc_fence_after();
-        // epilogue: warp w owns TMEM lanes 32w .. 32w+31 = tile rows
-        const int r = warp * 32 + lane;
-        const int64_t gr = m0 + r;
-        for (int c0 = 0; c0 < 256; c0 += 16) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if (EPI == 0) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + bias[c0 + i], 0.0f);
-            } else {
-                const uint4* mk = reinterpret_cast<const uint4*>(mask + gr * 256 + c0);
-                uint4 m0v = __ldg(mk), m1v = __ldg(mk + 1);
-                const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0v);
-                const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1v);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    if (!(__bfloat162float(mb0[i]) > 0.0f)) v[i] = 0.0f;
-                    if (!(__bfloat162float(mb1[i]) > 0.0f)) v[8 + i] = 0.0f;
-                }
-            }
-            __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-            for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(v[i]);
-            if (C) {
-                uint4* dst = reinterpret_cast<uint4*>(C + gr * 256 + c0);
-                dst[0] = reinterpret_cast<const uint4*>(o)[0];
-                dst[1] = reinterpret_cast<const uint4*>(o)[1];
-            }
-            if (CT) {
-#pragma unroll
-                for (int i = 0; i < 16; ++i) CT[(int64_t)(c0 + i) * mp + gr] = o[i];
-            }
-        }
         tc_fence_before();
         __syncthreads();
+        if (abort_flag) { prev = -1; break; }
+        prev = tile;
+        buf ^= 1;
     }
+    if (prev >= 0) {
+        tc_fence_after();
+        act_epilogue<K, EPI>(tmem + (uint32_t)((buf ^ 1) * 256), prev * 128, mp, bias, mask, C, CT);
+    }
+    tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 256);
+    if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------- weight-gradient GEMM ---
 // partial[b][o][n] = sum over this CTA's vertex range of AT[o][m] BT[n][m]
 // (AT [256][mp], BT [NP][mp], BF16 row-major), split-K over vertices in
-// 64-wide chunks; two M = 128 accumulators (o < 128, o >= 128).
+// 64-wide chunks, two shared-memory stages (the next chunk loads while the
+// current one multiplies), two M = 128 accumulators (o < 128, o >= 128).
+// The row sums of AT over the same range (the bias gradient) are taken from
+// the staged tiles: bpart[b][o].
 template <int NP>
 __global__ void __launch_bounds__(128, 1)
 k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restrict__ BT, int64_t mp,
-             float* __restrict__ partial, int* __restrict__ err) {
+             float* __restrict__ partial, float* __restrict__ bpart, int* __restrict__ err) {
     constexpr int KC = 64;
     constexpr uint32_t NCOL = (2 * NP) < 32 ? 32 : 2 * NP;
+    constexpr int SA = 256 * KC * 2, SB = NP * KC * 2;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* sA = smem;                     // 256 x 64
-    uint8_t* sB = smem + 256 * KC * 2;      // NP x 64
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tslot;
     __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) tmem_alloc(&tslot, NCOL);
-    if (threadIdx.x == 0) { mbar_init(&mbar, 1); abort_flag = 0; }
+    if (threadIdx.x == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); abort_flag = 0; }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -275,25 +308,20 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
     const uint32_t sbo = (KC / 8) * 128;
     const int64_t nch = mp / KC;
     const int64_t c0 = nch * blockIdx.x / gridDim.x, c1 = nch * (blockIdx.x + 1) / gridDim.x;
-    uint32_t phase = 0;
+    uint32_t ph[2] = {0, 0};
+    bool used[2] = {false, false};
+    float rs0 = 0.0f, rs1 = 0.0f;                       // row sums of rows tid, tid + 128
+    auto stage_of = [&](int st) { return smem + st * (SA + SB); };
+    if (c1 > c0) {
+        stage_tile_async(stage_of(0), AT, mp, 0, 256, 256, KC, c0 * KC);
+        stage_tile_async(stage_of(0) + SA, BT, mp, 0, NP, NP, KC, c0 * KC);
+        cp_async_commit();
+    }
     for (int64_t ch = c0; ch < c1; ++ch) {
-        // rows o of AT (and n of BT), columns [ch*64, ch*64+64)
-        const int64_t k0 = ch * KC;
-        {
-            const int per_row = KC >> 3;
-            for (int idx = threadIdx.x; idx < 256 * per_row; idx += blockDim.x) {
-                const int rr = idx & 7, j = (idx >> 3) % per_row, rg = (idx >> 3) / per_row;
-                const int r = rg * 8 + rr;
-                *reinterpret_cast<uint4*>(sA + tile_off(r, 8 * j, KC)) =
-                    __ldg(reinterpret_cast<const uint4*>(AT + (int64_t)r * mp + k0 + 8 * j));
-            }
-            for (int idx = threadIdx.x; idx < NP * per_row; idx += blockDim.x) {
-                const int rr = idx & 7, j = (idx >> 3) % per_row, rg = (idx >> 3) / per_row;
-                const int r = rg * 8 + rr;
-                *reinterpret_cast<uint4*>(sB + tile_off(r, 8 * j, KC)) =
-                    __ldg(reinterpret_cast<const uint4*>(BT + (int64_t)r * mp + k0 + 8 * j));
-            }
-        }
+        const int st = (int)((ch - c0) & 1);
+        uint8_t* sA = stage_of(st);
+        uint8_t* sB = sA + SA;
+        cp_async_wait_all();
         fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -305,16 +333,47 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
                     umma_bf16(tmem + (uint32_t)(h * NP),
                               umma_desc(smem_u32(sA) + (uint32_t)(h * 16) * sbo + 256 * s, 128, sbo),
                               umma_desc(smem_u32(sB) + 256 * s, 128, sbo), idesc, (ch > c0 || s > 0) ? 1u : 0u);
-            umma_commit(&mbar);
+            umma_commit(&mbar[st]);
         }
-        if (!mbar_wait(&mbar, phase)) {
-            atomicExch(err, 1);
-            abort_flag = 1;
+        used[st] = true;
+        // bias gradient: row sums of the staged AT rows (read-only use of the stage)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int r = threadIdx.x + 128 * q;
+            float acc = 0.0f;
+#pragma unroll
+            for (int j = 0; j < KC / 8; ++j) {
+                const uint4 u = *reinterpret_cast<const uint4*>(sA + tile_off(r, 8 * j, KC));
+                const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&u);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) acc += __bfloat162float(b[i]);
+            }
+            if (q == 0) rs0 += acc; else rs1 += acc;
         }
-        phase ^= 1u;
-        __syncthreads();
-        if (abort_flag) break;
+        // prefetch the next chunk into the other stage once its MMAs finished
+        if (ch + 1 < c1) {
+            const int nst = st ^ 1;
+            if (used[nst]) {
+                if (!mbar_wait(&mbar[nst], ph[nst])) { atomicExch(err, 1); abort_flag = 1; }
+                ph[nst] ^= 1u;
+                used[nst] = false;
+            }
+            __syncthreads();
+            if (abort_flag) break;
+            stage_tile_async(stage_of(nst), AT, mp, 0, 256, 256, KC, (ch + 1) * KC);
+            stage_tile_async(stage_of(nst) + SA, BT, mp, 0, NP, NP, KC, (ch + 1) * KC);
+            cp_async_commit();
+        }
     }
+    cp_async_wait_all();
+    // drain: wait for the MMAs still in flight
+    for (int st = 0; st < 2; ++st)
+        if (used[st] && !abort_flag) {
+            if (!mbar_wait(&mbar[st], ph[st])) { atomicExch(err, 1); abort_flag = 1; }
+            ph[st] ^= 1u;
+        }
+    tc_fence_before();
+    __syncthreads();
     tc_fence_after();
     float* out = partial + (int64_t)blockIdx.x * 256 * NP;
     for (int h = 0; h < 2; ++h) {
@@ -331,12 +390,13 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
             for (int i = 0; i < 16; ++i) out[(int64_t)o * NP + n0 + i] = v[i];
         }
     }
+    bpart[(int64_t)blockIdx.x * 256 + threadIdx.x] = rs0;
+    bpart[(int64_t)blockIdx.x * 256 + 128 + threadIdx.x] = rs1;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0) tmem_dealloc(tmem, NCOL);
 }
-
 
 // ------------------------------------------------------- CUDA-core part ---
 // BF16 copies of the weights (W1, W2, W3) and of W2^T, W3^T
@@ -398,94 +458,147 @@ __global__ void __launch_bounds__(kRedT) k_mask_sum(const float* __restrict__ ma
     const double r = block_sum_d(m < n ? (double)mask[m] : 0.0);
     if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
-__global__ void k_sum_parts(const double* __restrict__ part, int64_t np, double* __restrict__ out) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// out = sum of np partials in a fixed order (strided per thread, then a tree)
+__global__ void __launch_bounds__(1024) k_sum_parts(const double* __restrict__ part, int64_t np, double* __restrict__ out) {
+    __shared__ double sh[32];
     double s = 0.0;
-    for (int64_t i = 0; i < np; ++i) s += part[i];
-    *out = s;
+    for (int64_t i = threadIdx.x; i < np; i += 1024) s += part[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = sh[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) *out = v;
+    }
 }
 
-// Head forward and backward, one thread per (padded) vertex: y, the loss
-// term m (y - t)^2 / (3 sum m), dy = 2 m (y - t) / (3 sum m), and
-// dz3 = (dy W4) * (h3 > 0) written row-major and transposed.
-__global__ void __launch_bounds__(kRedT)
+// Head forward and backward, persistent: each block walks a contiguous range
+// of 32-vertex tiles (8 warps, 4 rows per warp; lane l owns columns l,
+// l + 32, ..., so row accesses are coalesced and W4 reads conflict-free):
+// y, the loss term m (y - t)^2 / (3 sum m), dy = 2 m (y - t) / (3 sum m),
+// dz3 = (dy W4) * (h3 > 0) written row-major and, through a padded shared
+// tile, as dz3^T.  Each lane also accumulates dW4 and db4 over the rows it
+// visits; per block, the warps' sums are combined in warp order into
+// wpart[block][4][256] (rows 0-2 dW4, row 3 db4 in its first 3 entries).
+constexpr int kHeadRows = 32;
+__global__ void __launch_bounds__(256)
 k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, const float* __restrict__ target,
            const float* __restrict__ mask, int64_t n, int64_t mp, const double* __restrict__ msum,
            float* __restrict__ y, float* __restrict__ dy, __nv_bfloat16* __restrict__ dz3,
-           __nv_bfloat16* __restrict__ dz3T, double* __restrict__ loss_part) {
+           __nv_bfloat16* __restrict__ dz3T, double* __restrict__ loss_part, float* __restrict__ wpart) {
     __shared__ float w4[kOut * kHid];
+    __shared__ __nv_bfloat16 tileT[kHeadRows][kHid + 2];
+    __shared__ double lsh[8];
+    __shared__ float wsh[8][4][32];
+    __shared__ double inv_den_s;
     for (int i = threadIdx.x; i < kOut * kHid; i += blockDim.x) w4[i] = P[kOffW4 + i];
+    // one FP64 reciprocal per block (FP64 runs at a small fraction of FP32 here)
+    if (threadIdx.x == 0) inv_den_s = *msum > 0.0 ? 1.0 / (3.0 * (*msum)) : 0.0;
     __syncthreads();
-    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double den = 3.0 * (*msum);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float inv_den = (float)inv_den_s;
+    const float b0 = P[kOffB4], b1 = P[kOffB4 + 1], b2 = P[kOffB4 + 2];
+    const int64_t ntile = mp / kHeadRows;
+    const int64_t t0 = ntile * blockIdx.x / gridDim.x, t1 = ntile * (blockIdx.x + 1) / gridDim.x;
     double lterm = 0.0;
-    if (m < mp) {
-        float d[3] = {0.0f, 0.0f, 0.0f};
-        if (m < n && mask[m] != 0.0f && den > 0.0) {
-            float a0 = P[kOffB4], a1 = P[kOffB4 + 1], a2 = P[kOffB4 + 2];
-            for (int j0 = 0; j0 < kHid; j0 += 8) {
-                const uint4 u = __ldg(reinterpret_cast<const uint4*>(h3 + m * kHid + j0));
-                const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&u);
+    float gw[3][8], gb[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float hv = __bfloat162float(hb[i]);
-                    a0 += hv * w4[j0 + i]; a1 += hv * w4[kHid + j0 + i]; a2 += hv * w4[2 * kHid + j0 + i];
-                }
-            }
-            const float yy[3] = {a0, a1, a2};
-            const double mk = (double)mask[m];
-            for (int c = 0; c < 3; ++c) {
-                const double e = (double)yy[c] - (double)target[3 * m + c];
-                lterm += mk * e * e / den;
-                d[c] = (float)(2.0 * mk * e / den);
-                y[3 * m + c] = yy[c];
-            }
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) gw[c][i] = 0.0f;
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const int64_t m0 = tile * kHeadRows;
+        // the warp's 4 rows together: all their loads are in flight at once
+        constexpr int RW = kHeadRows / 8;
+        float hv[RW][8], acc[RW][3];
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr) {
+            const int64_t m = m0 + warp * RW + rr;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) hv[rr][i] = __bfloat162float(h3[m * kHid + lane + 32 * i]);
         }
-        for (int c = 0; c < 3; ++c) dy[3 * m + c] = d[c];
-        for (int j0 = 0; j0 < kHid; j0 += 8) {
-            const uint4 u = __ldg(reinterpret_cast<const uint4*>(h3 + m * kHid + j0));
-            const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&u);
-            __align__(16) __nv_bfloat16 o[8];
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr) {
+            acc[rr][0] = acc[rr][1] = acc[rr][2] = 0.0f;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const float g = d[0] * w4[j0 + i] + d[1] * w4[kHid + j0 + i] + d[2] * w4[2 * kHid + j0 + i];
-                o[i] = __float2bfloat16_rn(__bfloat162float(hb[i]) > 0.0f ? g : 0.0f);
-                dz3T[(int64_t)(j0 + i) * mp + m] = o[i];
+                const int j = lane + 32 * i;
+                acc[rr][0] += hv[rr][i] * w4[j];
+                acc[rr][1] += hv[rr][i] * w4[kHid + j];
+                acc[rr][2] += hv[rr][i] * w4[2 * kHid + j];
             }
-            *reinterpret_cast<uint4*>(dz3 + m * kHid + j0) = *reinterpret_cast<const uint4*>(o);
         }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int rr = 0; rr < RW; ++rr)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[rr][c] += __shfl_xor_sync(0xffffffffu, acc[rr][c], o);
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr) {
+            const int r = warp * RW + rr;
+            const int64_t m = m0 + r;
+            // every lane holds y; lane c < 3 forms component c of the loss
+            // term and of dy in FP32, lane 0 accumulates the loss in FP64
+            float dc = 0.0f;
+            const bool live = m < n && mask[m] != 0.0f && inv_den > 0.0f;
+            float lt = 0.0f;
+            if (live && lane < 3) {
+                const float yy = acc[rr][lane] + (lane == 0 ? b0 : (lane == 1 ? b1 : b2));
+                const float e = yy - target[3 * m + lane];
+                const float mk = mask[m];
+                lt = mk * e * e * inv_den;
+                dc = 2.0f * mk * e * inv_den;
+                y[3 * m + lane] = yy;
+            }
+            const float d0 = __shfl_sync(0xffffffffu, dc, 0), d1 = __shfl_sync(0xffffffffu, dc, 1),
+                        d2 = __shfl_sync(0xffffffffu, dc, 2);
+            const float l1 = __shfl_sync(0xffffffffu, lt, 1), l2 = __shfl_sync(0xffffffffu, lt, 2);
+            if (lane == 0) lterm += (double)lt + (double)l1 + (double)l2;
+            if (lane < 3) dy[3 * m + lane] = dc;
+            gb[0] += d0; gb[1] += d1; gb[2] += d2;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int j = lane + 32 * i;
+                gw[0][i] += d0 * hv[rr][i]; gw[1][i] += d1 * hv[rr][i]; gw[2][i] += d2 * hv[rr][i];
+                const float g = d0 * w4[j] + d1 * w4[kHid + j] + d2 * w4[2 * kHid + j];
+                const __nv_bfloat16 o = __float2bfloat16_rn(hv[rr][i] > 0.0f ? g : 0.0f);
+                dz3[m * kHid + j] = o;
+                tileT[r][j] = o;
+            }
+        }
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kHeadRows * kHid; idx += blockDim.x) {
+            const int r = idx & (kHeadRows - 1), j = idx / kHeadRows;
+            dz3T[(int64_t)j * mp + m0 + r] = tileT[r][j];
+        }
+        __syncthreads();
     }
-    const double r = block_sum_d(lterm);
-    if (threadIdx.x == 0) loss_part[blockIdx.x] = r;
-}
-
-// partial[b][c][j] = sum over this block's vertex chunk of dy[m][c] h3[m][j]
-// and partial[b][3][j] (j < 3) = sum of dy[m][j]; thread j, rows in order
-__global__ void __launch_bounds__(kHid)
-k_head_wgrad(const float* __restrict__ dy, const __nv_bfloat16* __restrict__ h3, int64_t mp, int64_t chunk,
-             float* __restrict__ partial) {
-    const int j = threadIdx.x;
-    const int64_t m0 = (int64_t)blockIdx.x * chunk, m1 = min(mp, m0 + chunk);
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, s = 0.0f;
-    for (int64_t m = m0; m < m1; ++m) {
-        const float hv = __bfloat162float(h3[m * kHid + j]);
-        const float d0 = dy[3 * m], d1 = dy[3 * m + 1], d2 = dy[3 * m + 2];
-        a0 += d0 * hv; a1 += d1 * hv; a2 += d2 * hv;
-        if (j < 3) s += dy[3 * m + j];
+    // combine the warps' dW4 / db4 sums in warp order, one column slice at a time
+    float* out = wpart + (int64_t)blockIdx.x * 4 * kHid;
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wsh[warp][c][lane] = gw[c][i];
+        wsh[warp][3][lane] = (i == 0 && lane < 3) ? gb[lane] : 0.0f;
+        __syncthreads();
+        if (threadIdx.x < 128) {
+            const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
+            float t = 0.0f;
+            for (int w = 0; w < 8; ++w) t += wsh[w][c][l];
+            out[c * kHid + l + 32 * i] = t;
+        }
+        __syncthreads();
     }
-    float* out = partial + (int64_t)blockIdx.x * (4 * kHid);
-    out[j] = a0; out[kHid + j] = a1; out[2 * kHid + j] = a2;
-    out[3 * kHid + j] = j < 3 ? s : 0.0f;
-}
-
-// row sums of a [rows][mp] BF16 matrix (bias gradients), one block per row
-__global__ void __launch_bounds__(kRedT)
-k_rowsum(const __nv_bfloat16* __restrict__ A, int64_t mp, float* __restrict__ out) {
-    const __nv_bfloat16* row = A + (int64_t)blockIdx.x * mp;
-    double s = 0.0;
-    for (int64_t m = threadIdx.x; m < mp; m += kRedT) s += (double)__bfloat162float(row[m]);
-    const double r = block_sum_d(s);
-    if (threadIdx.x == 0) out[blockIdx.x] = (float)r;
+    if (lane == 0) lsh[warp] = lterm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += lsh[w];
+        loss_part[blockIdx.x] = t;
+    }
 }
 
 // out[l] = sum_p partial[p][l] in order p = 0 .. np-1 (optionally strided)
@@ -594,13 +707,16 @@ cudaError_t launch_act(Ctx& c, WarmStart& W, const __nv_bfloat16* A, const __nv_
 }
 
 template <int NP>
-cudaError_t launch_wgrad(Ctx& c, WarmStart& W, const __nv_bfloat16* AT, const __nv_bfloat16* BT, float* out) {
-    const size_t sm = std::max((size_t)(256 + NP) * 64 * 2, kOneCtaSmem);
+cudaError_t launch_wgrad(Ctx& c, WarmStart& W, const __nv_bfloat16* AT, const __nv_bfloat16* BT, float* out,
+                         float* bias_out) {
+    const size_t sm = std::max((size_t)2 * (256 + NP) * 64 * 2, kOneCtaSmem);
     GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_wgrad<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = sm_count(c.device);
-    k_umma_wgrad<NP><<<grid, 128, sm, c.stream>>>(AT, BT, W.mp, W.part.p, W.err.p);
+    float* bpart = W.part.p + (size_t)grid * 256 * NP;
+    k_umma_wgrad<NP><<<grid, 128, sm, c.stream>>>(AT, BT, W.mp, W.part.p, bpart, W.err.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     k_reduce_part<<<nb(256 * NP, 256), 256, 0, c.stream>>>(W.part.p, grid, 256 * NP, 256 * NP, out);
+    k_reduce_part<<<1, 256, 0, c.stream>>>(bpart, grid, 256, 256, bias_out);
     return cudaGetLastError();
 }
 
@@ -628,35 +744,28 @@ static cudaError_t ws_backward(Ctx& c, WarmStart& W, const float* target, const 
     const int64_t n = W.n, mp = W.mp;
     GMCP_CUDA_TRY(ws_hidden(c, W, true));
     double* sc = W.scal.p;
-    const unsigned gb = nb(mp, kRedT), gn = nb(n, kRedT);
+    const unsigned gn = nb(n, kRedT);
     k_mask_sum<<<gn, kRedT, 0, s>>>(mask, n, W.dpart.p);
-    k_sum_parts<<<1, 32, 0, s>>>(W.dpart.p, (int64_t)gn, sc);
-    k_head_bwd<<<gb, kRedT, 0, s>>>(W.h3.p, W.P.p, target, mask, n, mp, sc, W.y.p, W.dy.p, W.dz3.p, W.dz3T.p,
-                                     W.dpart.p);
-    k_sum_parts<<<1, 32, 0, s>>>(W.dpart.p, (int64_t)gb, sc + 1);
+    k_sum_parts<<<1, 1024, 0, s>>>(W.dpart.p, (int64_t)gn, sc);
+    const unsigned gh = (unsigned)std::min<int64_t>(4 * sm_count(c.device), mp / kHeadRows);
+    float* wp = W.part.p;
+    k_head_bwd<<<gh, 256, 0, s>>>(W.h3.p, W.P.p, target, mask, n, mp, sc, W.y.p, W.dy.p, W.dz3.p, W.dz3T.p,
+                                  W.dpart.p, wp);
+    k_sum_parts<<<1, 1024, 0, s>>>(W.dpart.p, (int64_t)gh, sc + 1);
     GMCP_CUDA_TRY(cudaGetLastError());
     float* G = W.G.p;
-    // layer 4 (CUDA cores)
-    {
-        const int64_t chunk = 4096;
-        const int64_t nblk = (mp + chunk - 1) / chunk;
-        float* pp = W.part.p;
-        k_head_wgrad<<<(unsigned)nblk, kHid, 0, s>>>(W.dy.p, W.h3.p, mp, chunk, pp);
-        k_reduce_part<<<nb(3 * kHid, 256), 256, 0, s>>>(pp, nblk, 4 * kHid, 3 * kHid, G + kOffW4);
-        k_reduce_part<<<1, 32, 0, s>>>(pp + 3 * kHid, nblk, 4 * kHid, 3, G + kOffB4);
-        GMCP_CUDA_TRY(cudaGetLastError());
-    }
+    // layer 4 from the head's per-block partials
+    k_reduce_part<<<nb(3 * kHid, 256), 256, 0, s>>>(wp, gh, 4 * kHid, 3 * kHid, G + kOffW4);
+    k_reduce_part<<<1, 32, 0, s>>>(wp + 3 * kHid, gh, 4 * kHid, 3, G + kOffB4);
+    GMCP_CUDA_TRY(cudaGetLastError());
     // layer 3: dW3 = dz3^T h2, db3
-    GMCP_CUDA_TRY(launch_wgrad<kHid>(c, W, W.dz3T.p, W.h2T.p, G + kOffW3));
-    k_rowsum<<<kHid, kRedT, 0, s>>>(W.dz3T.p, mp, G + kOffB3);
+    GMCP_CUDA_TRY(launch_wgrad<kHid>(c, W, W.dz3T.p, W.h2T.p, G + kOffW3, G + kOffB3));
     // dz2 = (dz3 W3) * (h2 > 0)
     GMCP_CUDA_TRY((launch_act<kHid, 1>(c, W, W.dz3.p, W.W3t.p, nullptr, W.h2.p, W.dz2.p, W.dz2T.p)));
-    GMCP_CUDA_TRY(launch_wgrad<kHid>(c, W, W.dz2T.p, W.h1T.p, G + kOffW2));
-    k_rowsum<<<kHid, kRedT, 0, s>>>(W.dz2T.p, mp, G + kOffB2);
+    GMCP_CUDA_TRY(launch_wgrad<kHid>(c, W, W.dz2T.p, W.h1T.p, G + kOffW2, G + kOffB2));
     // dz1 = (dz2 W2) * (h1 > 0)
     GMCP_CUDA_TRY((launch_act<kHid, 1>(c, W, W.dz2.p, W.W2t.p, nullptr, W.h1.p, nullptr, W.dz1T.p)));
-    GMCP_CUDA_TRY(launch_wgrad<kIn>(c, W, W.dz1T.p, W.fT.p, G + kOffW1));
-    k_rowsum<<<kHid, kRedT, 0, s>>>(W.dz1T.p, mp, G + kOffB1);
+    GMCP_CUDA_TRY(launch_wgrad<kIn>(c, W, W.dz1T.p, W.fT.p, G + kOffW1, G + kOffB1));
     GMCP_CUDA_TRY(cudaGetLastError());
     if (loss) {
         GMCP_CUDA_TRY(cudaMemcpyAsync(loss, sc + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -723,9 +832,9 @@ ipc_status ipc_ws_create(ipc_ctx* ctx, const ipc_ws_params* prm) {
         WS_CK(c, b->ensure((size_t)mp * kHid));
     WS_CK(c, W->y.ensure(3 * mp)); WS_CK(c, W->dy.ensure(3 * mp));
     // partial sums: split-K weight gradients [SMs][256][256] plus scratch
-    WS_CK(c, W->part.ensure(std::max((size_t)std::max(sm_count(c.device), 1) * kHid * kHid,
-                                     (size_t)4 * kHid * ((mp + 4095) / 4096)) + 1024));
-    WS_CK(c, W->dpart.ensure((size_t)(mp + kRedT - 1) / kRedT + 16));
+    WS_CK(c, W->part.ensure(std::max((size_t)std::max(sm_count(c.device), 1) * (kHid * kHid + kHid),
+                                     (size_t)4 * kHid * ((mp + 2047) / 2048)) + 1024));
+    WS_CK(c, W->dpart.ensure((size_t)(mp + 31) / 32 + 16));
     WS_CK(c, W->surf.upload(surf.data(), surf.size(), s));
     if (c.P.precision == IPC_PREC_MIXED) WS_CK(c, W->cgrad32.ensure(3 * (size_t)c.nv));
     else WS_CK(c, W->cgrad64.ensure(3 * (size_t)c.nv));
@@ -786,11 +895,11 @@ __global__ void k_load_feats(const __nv_bfloat16* __restrict__ src, int64_t n, i
                              __nv_bfloat16* __restrict__ f, __nv_bfloat16* __restrict__ fT) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= mp) return;
-    for (int i = 0; i < kIn; ++i) {
-        const __nv_bfloat16 v = m < n ? src[m * kIn + i] : __float2bfloat16_rn(0.0f);
-        f[m * kIn + i] = v;
-        fT[(int64_t)i * mp + m] = v;
-    }
+    __align__(16) __nv_bfloat16 v[kIn];
+    for (int q = 0; q < kIn / 8; ++q)
+        reinterpret_cast<uint4*>(v)[q] = m < n ? reinterpret_cast<const uint4*>(src + m * kIn)[q] : make_uint4(0, 0, 0, 0);
+    for (int q = 0; q < kIn / 8; ++q) reinterpret_cast<uint4*>(f + m * kIn)[q] = reinterpret_cast<const uint4*>(v)[q];
+    for (int i = 0; i < kIn; ++i) fT[(int64_t)i * mp + m] = v[i];
 }
 }  // namespace
 }  // namespace gmcp
