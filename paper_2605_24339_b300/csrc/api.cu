@@ -435,9 +435,11 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
         const double c0 = 1e-4;
         // backtracking on the frozen-linear energy: slot 0 is alpha = 0 (the
         // reference), slots 1..7 the next halvings
+        // the first batch tries the full step only (it is usually taken);
+        // later batches try seven halvings at once
         bool accepted = false;
-        for (int hv0 = 0; hv0 <= c.prm.max_halvings && !accepted; hv0 += 7) {
-            const int nk = std::min(7, c.prm.max_halvings - hv0 + 1);
+        for (int hv0 = 0, nk = 1; hv0 <= c.prm.max_halvings && !accepted; hv0 += nk) {
+            nk = hv0 == 0 ? 1 : std::min(7, c.prm.max_halvings - hv0 + 1);
             double als[8];
             als[0] = 0.0;
             for (int j = 0; j < nk; ++j) als[1 + j] = std::ldexp(al, -(hv0 + j));

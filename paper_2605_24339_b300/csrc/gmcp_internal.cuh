@@ -194,7 +194,7 @@ struct NewtonState {
     DBuf<double> tH64;                   // per-tet Hessian, 10 blocks [nt][90] (FP64 path)
     DBuf<float> tH32;                    // the same in FP32 (mixed path)
     DBuf<double> A64, Pinv;              // global matrix [nnzb][9] (FP64 path), P^-1 [nv][9]
-    DBuf<float> A32, p32;                // FP32 matrix and search direction (mixed path)
+    DBuf<float> A32, p32, r32, z32, Ap32, Pinv32;   // FP32 matrix and PCG vectors (mixed path)
     DBuf<double> part;                   // PCG per-block partial sums [2][blocks]
     DBuf<unsigned> counters;             // PCG last-block counters
     DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nv]

@@ -385,15 +385,19 @@ __global__ void k_assemble_bsr(int64_t nnzb, const int32_t* __restrict__ brow, c
 // ------------------------------------------------------------------ PCG ---
 // Fused block-Jacobi PCG: three kernels per iteration; each dot product is
 // finished by the last block to arrive, which sums the per-block partials in
-// block order (deterministic).  Solver scalars (FP64):
+// block order (deterministic) and forms the iteration's scalars once (alpha
+// in the SpMV kernel, beta in the update kernel), so no thread divides.
+// Vectors r, z, p, Ap and the block inverse are of type V (FP64, or FP32 in
+// the mixed path); the solution and every dot product are FP64.  Solver
+// scalars (FP64):
 enum : int {
-    kRz0 = 0,        // r.z, double-buffered by iteration parity (slots 0, 1)
-    kPAp = 2, kRr = 3, kBb = 4,
-    kBreak = 5,      // p^T A p <= 0 seen
-    kDone = 6,       // converged
-    kIters = 7,      // iterations taken (valid once kBreak or kDone is set)
-    kThr = 8,        // rel_tol |b|
-    kIt = 9          // index of the current iteration (advanced by k_pcg_update)
+    kRz = 0,         // r . z of the current iteration
+    kPAp = 1, kAl = 2, kBe = 3, kRr = 4, kBb = 5,
+    kBreak = 6,      // p^T A p <= 0 seen
+    kDone = 7,       // converged
+    kIters = 8,      // iterations taken (valid once kBreak or kDone is set)
+    kThr = 9,        // rel_tol |b|
+    kIt = 10         // index of the current iteration (advanced by k_pcg_update)
 };
 constexpr int kPcgThreads = 256;
 
@@ -441,48 +445,52 @@ __device__ bool last_block_sums(double v0, double v1, double* part /* [2][gridDi
     return true;
 }
 
-__device__ __forceinline__ void mul33(const double* P, double r0, double r1, double r2, double* z) {
+template <class V>
+__device__ __forceinline__ void mul33(const V* P, V r0, V r1, V r2, V* z) {
     z[0] = P[0] * r0 + P[1] * r1 + P[2] * r2;
     z[1] = P[3] * r0 + P[4] * r1 + P[5] * r2;
     z[2] = P[6] * r0 + P[7] * r1 + P[8] * r2;
 }
 
-template <class TA>
+// inverse of each diagonal block (inverted in FP64, stored as V)
+template <class TA, class V>
 __global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, const TA* __restrict__ A,
-                           double* __restrict__ Pinv) {
+                           V* __restrict__ Pinv) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
-    double D[9];
+    double D[9], I[9];
     const TA* B = A + 9 * (int64_t)diag_blk[v];
     for (int q = 0; q < 9; ++q) D[q] = (double)B[q];
-    inv3(D, Pinv + 9 * v);
+    inv3(D, I);
+    for (int q = 0; q < 9; ++q) Pinv[9 * v + q] = (V)I[q];
 }
 
-// x = 0, r = b, z = P^-1 b, p = z (and its FP32 copy); b.b and r.z
+// x = 0, r = b, z = P^-1 b, p = z; b.b and r.z
+template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_init(int64_t nv, const double* __restrict__ Pinv, const double* __restrict__ bvec, double* __restrict__ x,
-           double* __restrict__ r, double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32,
-           double* part, unsigned* counter, double* scal, double rel_tol) {
+k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bvec, double* __restrict__ x,
+           V* __restrict__ r, V* __restrict__ z, V* __restrict__ p, double* part, unsigned* counter, double* scal,
+           double rel_tol) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double bb = 0.0, rz = 0.0;
     if (i < nv) {
-        const double b0 = bvec[3 * i], b1 = bvec[3 * i + 1], b2 = bvec[3 * i + 2];
-        double zz[3];
+        const V b0 = (V)bvec[3 * i], b1 = (V)bvec[3 * i + 1], b2 = (V)bvec[3 * i + 2];
+        V zz[3];
         mul33(Pinv + 9 * i, b0, b1, b2, zz);
+        const V bv[3] = {b0, b1, b2};
         for (int q = 0; q < 3; ++q) {
             x[3 * i + q] = 0.0;
-            r[3 * i + q] = bvec[3 * i + q];
+            r[3 * i + q] = bv[q];
             z[3 * i + q] = zz[q];
             p[3 * i + q] = zz[q];
-            if (p32) p32[3 * i + q] = (float)zz[q];
+            bb += (double)bv[q] * (double)bv[q];
+            rz += (double)bv[q] * (double)zz[q];
         }
-        bb = b0 * b0 + b1 * b1 + b2 * b2;
-        rz = b0 * zz[0] + b1 * zz[1] + b2 * zz[2];
     }
     double tb, tr;
     if (last_block_sums(bb, rz, part, counter, &tb, &tr) && threadIdx.x == 0) {
         scal[kBb] = tb;
-        scal[kRz0] = tr;
+        scal[kRz] = tr;
         scal[kThr] = rel_tol * sqrt(tb);
         scal[kBreak] = 0.0;
         scal[kDone] = tb > 0.0 ? 0.0 : 1.0;
@@ -491,13 +499,13 @@ k_pcg_init(int64_t nv, const double* __restrict__ Pinv, const double* __restrict
     }
 }
 
-// Ap = A p and p.Ap; one thread per (block row, component).  TA = float:
-// FP32 products of the FP32 matrix and the FP32 copy of p, FP32 row sums.
-template <class TA>
+// Ap = A p and p.Ap; one thread per (block row, component), row sums in TA.
+// The last block sets alpha = r.z / p.Ap (or the breakdown flag).
+template <class TA, class V>
 __global__ void __launch_bounds__(kPcgThreads)
 k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-           const TA* __restrict__ A, const double* __restrict__ p, const float* __restrict__ p32,
-           double* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
+           const TA* __restrict__ A, const V* __restrict__ p, V* __restrict__ Ap, double* part, unsigned* counter,
+           double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int it = (int)scal[kIt];
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -509,47 +517,52 @@ k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict
         for (int k = rp[i]; k < rp[i + 1]; ++k) {
             const TA* B = A + 9 * (int64_t)k + 3 * comp;
             const int64_t j = ci[k];
-            if (sizeof(TA) == 4)
-                acc += B[0] * (TA)p32[3 * j] + B[1] * (TA)p32[3 * j + 1] + B[2] * (TA)p32[3 * j + 2];
-            else
-                acc += B[0] * (TA)p[3 * j] + B[1] * (TA)p[3 * j + 1] + B[2] * (TA)p[3 * j + 2];
+            acc += B[0] * (TA)p[3 * j] + B[1] * (TA)p[3 * j + 1] + B[2] * (TA)p[3 * j + 2];
         }
-        const double y = (double)acc;
+        const V y = (V)acc;
         Ap[3 * i + comp] = y;
-        pap = p[3 * i + comp] * y;
+        pap = (double)p[3 * i + comp] * (double)y;
     }
     double t, unused;
     if (last_block_sums(pap, 0.0, part, counter, &t, &unused) && threadIdx.x == 0) {
         scal[kPAp] = t;
-        if (!(t > 0.0)) {
+        if (t > 0.0) {
+            scal[kAl] = scal[kRz] / t;
+        } else {
             scal[kBreak] = 1.0;
             scal[kIters] = (double)it;
         }
     }
 }
 
-// x += al p, r -= al Ap, z = P^-1 r, then r.r (convergence) and r.z
+// x += al p, r -= al Ap, z = P^-1 r, then r.r (convergence) and r.z; the
+// last block sets beta = r.z_new / r.z and advances the iteration index
+template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_update(int64_t nv, const double* __restrict__ Pinv, double* __restrict__ x, double* __restrict__ r,
-             double* __restrict__ z, const double* __restrict__ p, const double* __restrict__ Ap, double* part,
-             unsigned* counter, double* scal) {
+k_pcg_update(int64_t nv, const V* __restrict__ Pinv, double* __restrict__ x, V* __restrict__ r,
+             V* __restrict__ z, const V* __restrict__ p, const V* __restrict__ Ap, double* part, unsigned* counter,
+             double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int it = (int)scal[kIt];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double al = scal[kRz0 + (it & 1)] / scal[kPAp];
+    const double al = scal[kAl];
+    const V alv = (V)al;
     double rr = 0.0, rz = 0.0;
     if (i < nv) {
-        double rv[3];
+        V rv[3];
         for (int q = 0; q < 3; ++q) {
-            x[3 * i + q] += al * p[3 * i + q];
-            rv[q] = r[3 * i + q] - al * Ap[3 * i + q];
+            const V pq = p[3 * i + q];
+            x[3 * i + q] += (sizeof(V) == 8) ? al * (double)pq : (double)(alv * pq);
+            rv[q] = r[3 * i + q] - alv * Ap[3 * i + q];
             r[3 * i + q] = rv[q];
         }
-        double zz[3];
+        V zz[3];
         mul33(Pinv + 9 * i, rv[0], rv[1], rv[2], zz);
-        for (int q = 0; q < 3; ++q) z[3 * i + q] = zz[q];
-        rr = rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
-        rz = rv[0] * zz[0] + rv[1] * zz[1] + rv[2] * zz[2];
+        for (int q = 0; q < 3; ++q) {
+            z[3 * i + q] = zz[q];
+            rr += (double)rv[q] * (double)rv[q];
+            rz += (double)rv[q] * (double)zz[q];
+        }
     }
     double trr, trz;
     if (last_block_sums(rr, rz, part, counter, &trr, &trz) && threadIdx.x == 0) {
@@ -558,25 +571,23 @@ k_pcg_update(int64_t nv, const double* __restrict__ Pinv, double* __restrict__ x
             scal[kDone] = 1.0;
             scal[kIters] = (double)(it + 1);
         } else {
-            scal[kRz0 + ((it + 1) & 1)] = trz;
+            scal[kBe] = trz / scal[kRz];
+            scal[kRz] = trz;
         }
-        // every block read kIt before it arrived at the counter
+        // every block read kIt and kAl before it arrived at the counter
         scal[kIt] = (double)(it + 1);
     }
 }
 
-// p = z + (rz_new / rz_old) p; kIt already holds the next iteration's index
+// p = z + beta p
+template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_dir(int64_t n, const double* __restrict__ z, double* __restrict__ p, float* __restrict__ p32,
-          const double* scal) {
+k_pcg_dir(int64_t n, const V* __restrict__ z, V* __restrict__ p, const double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int nx = (int)scal[kIt];
-    const double be = scal[kRz0 + (nx & 1)] / scal[kRz0 + ((nx + 1) & 1)];
-    const double v = z[i] + be * p[i];
-    p[i] = v;
-    if (p32) p32[i] = (float)v;
+    const V be = (V)scal[kBe];
+    p[i] = z[i] + be * p[i];
 }
 
 // elementwise products into w (for a fixed-order dot product)
@@ -729,27 +740,30 @@ cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double*
 // iterations.  The host reads the flags once per 16 iterations; kernels
 // after the stop return at once.  Returns the iterations taken.
 // queue `count` PCG iterations (each kernel returns at once after a stop)
-static cudaError_t pcg_enqueue_iters(Ctx& c, double* xout, int count) {
+template <class TA, class V>
+static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* Ap, double* xout, int count) {
     NewtonState& N = *c.newton;
     const int64_t nv = c.nv, n = 3 * nv;
     cudaStream_t s = c.stream;
-    const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    float* p32 = f32 ? N.p32.p : nullptr;
     const unsigned g_row = nblk(nv, kPcgThreads), g_comp = nblk(n, kPcgThreads);
     for (int j = 0; j < count; ++j) {
-        if (f32)
-            k_pcg_spmv<float><<<g_comp, kPcgThreads, 0, s>>>(nv, N.rp.p, N.ci.p, N.A32.p, N.p.p, p32, N.Ap.p,
-                                                             N.part.p, N.counters.p + 1, N.scal.p);
-        else
-            k_pcg_spmv<double><<<g_comp, kPcgThreads, 0, s>>>(nv, N.rp.p, N.ci.p, N.A64.p, N.p.p, p32, N.Ap.p,
-                                                              N.part.p, N.counters.p + 1, N.scal.p);
-        k_pcg_update<<<g_row, kPcgThreads, 0, s>>>(nv, N.Pinv.p, xout, N.r.p, N.z.p, N.p.p, N.Ap.p, N.part.p,
-                                                   N.counters.p + 2, N.scal.p);
-        k_pcg_dir<<<g_comp, kPcgThreads, 0, s>>>(n, N.z.p, N.p.p, p32, N.scal.p);
+        k_pcg_spmv<TA, V><<<g_comp, kPcgThreads, 0, s>>>(nv, N.rp.p, N.ci.p, A, p, Ap, N.part.p,
+                                                         N.counters.p + 1, N.scal.p);
+        k_pcg_update<V><<<g_row, kPcgThreads, 0, s>>>(nv, Pinv, xout, r, z, p, Ap, N.part.p, N.counters.p + 2,
+                                                      N.scal.p);
+        k_pcg_dir<V><<<g_comp, kPcgThreads, 0, s>>>(n, z, p, N.scal.p);
     }
+}
+
+static cudaError_t pcg_enqueue_iters(Ctx& c, double* xout, int count) {
+    NewtonState& N = *c.newton;
+    if (c.P.precision == IPC_PREC_MIXED)
+        pcg_queue<float, float>(c, N.A32.p, N.Pinv32.p, N.r32.p, N.z32.p, N.p32.p, N.Ap32.p, xout, count);
+    else
+        pcg_queue<double, double>(c, N.A64.p, N.Pinv.p, N.r.p, N.z.p, N.p.p, N.Ap.p, xout, count);
     GMCP_CUDA_TRY(cudaGetLastError());
     // stop flags and iteration count for the host
-    return cudaMemcpyAsync(c.pin->pcg, N.scal.p + kBreak, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    return cudaMemcpyAsync(c.pin->pcg, N.scal.p + kBreak, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
 }
 
 constexpr int kPcgChunk = 16;
@@ -759,9 +773,10 @@ constexpr int kPcgChunk = 16;
 static bool pcg_chunk_graph(Ctx& c, double* xout) {
     NewtonState& N = *c.newton;
     const std::vector<uintptr_t> key = {(uintptr_t)xout, (uintptr_t)N.p.p, (uintptr_t)N.p32.p, (uintptr_t)N.A32.p,
-                                        (uintptr_t)N.A64.p, (uintptr_t)N.Ap.p, (uintptr_t)N.r.p, (uintptr_t)N.z.p,
-                                        (uintptr_t)N.Pinv.p, (uintptr_t)N.part.p, (uintptr_t)N.scal.p,
-                                        (uintptr_t)N.counters.p, (uintptr_t)c.pin};
+                                        (uintptr_t)N.A64.p, (uintptr_t)N.Ap.p, (uintptr_t)N.Ap32.p,
+                                        (uintptr_t)N.r.p, (uintptr_t)N.r32.p, (uintptr_t)N.z.p, (uintptr_t)N.z32.p,
+                                        (uintptr_t)N.Pinv.p, (uintptr_t)N.Pinv32.p, (uintptr_t)N.part.p,
+                                        (uintptr_t)N.scal.p, (uintptr_t)N.counters.p, (uintptr_t)c.pin};
     if (c.pcg_graph.exec && c.pcg_graph.key == key) return true;
     c.pcg_graph.reset();
     if (!c.cap_stream && cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -790,23 +805,26 @@ static bool pcg_chunk_graph(Ctx& c, double* xout) {
     return true;
 }
 
-// Block-Jacobi PCG for A p = b (A on the pattern N.rp / N.ci; FP32 in the
-// mixed path, FP64 otherwise), p = 0 start; stops at ||r|| <= rel_tol ||b||,
-// at p^T A p <= 0 (that iteration's update is skipped) or after max_it
-// iterations.  The host reads the flags once per 16 iterations (a captured
-// graph per chunk when graphs are on); kernels after the stop return at
-// once.  Returns the iterations taken.
+// Block-Jacobi PCG for A p = b (A on the pattern N.rp / N.ci; FP32 matrix
+// and vectors in the mixed path, FP64 otherwise; FP64 solution and dots),
+// p = 0 start; stops at ||r|| <= rel_tol ||b||, at p^T A p <= 0 (that
+// iteration's update is skipped) or after max_it iterations.  The host reads
+// the flags once per 16 iterations (a captured graph per chunk when graphs
+// are on); kernels after the stop return at once.  Returns the iterations.
 cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters) {
     NewtonState& N = *c.newton;
     const int64_t nv = c.nv;
     cudaStream_t s = c.stream;
-    const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    float* p32 = f32 ? N.p32.p : nullptr;
-    if (f32) k_diag_inv<float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A32.p, N.Pinv.p);
-    else k_diag_inv<double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A64.p, N.Pinv.p);
-    GMCP_CUDA_TRY(cudaGetLastError());
-    k_pcg_init<<<nblk(nv, kPcgThreads), kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, N.r.p, N.z.p, N.p.p, p32,
-                                                             N.part.p, N.counters.p, N.scal.p, rel_tol);
+    const unsigned gr = nblk(nv, kPcgThreads);
+    if (c.P.precision == IPC_PREC_MIXED) {
+        k_diag_inv<float, float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A32.p, N.Pinv32.p);
+        k_pcg_init<float><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv32.p, b, xout, N.r32.p, N.z32.p, N.p32.p, N.part.p,
+                                                     N.counters.p, N.scal.p, rel_tol);
+    } else {
+        k_diag_inv<double, double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A64.p, N.Pinv.p);
+        k_pcg_init<double><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, N.r.p, N.z.p, N.p.p, N.part.p,
+                                                      N.counters.p, N.scal.p, rel_tol);
+    }
     GMCP_CUDA_TRY(cudaGetLastError());
     const bool graph = c.graphs && !c.prof.on && pcg_chunk_graph(c, xout);
     *iters = max_it;
@@ -947,7 +965,8 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.tE8.ensure(8 * (size_t)nt + 8));
     if (f32) {
         GMCP_CUDA_TRY(N.A32.ensure(9 * (size_t)nnzb));
-        GMCP_CUDA_TRY(N.p32.ensure(3 * (size_t)nv));
+        for (DBuf<float>* b : {&N.p32, &N.r32, &N.z32, &N.Ap32}) GMCP_CUDA_TRY(b->ensure(3 * (size_t)nv));
+        GMCP_CUDA_TRY(N.Pinv32.ensure(9 * (size_t)nv));
     } else {
         GMCP_CUDA_TRY(N.A64.ensure(9 * (size_t)nnzb));
     }
