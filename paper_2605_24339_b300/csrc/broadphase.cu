@@ -192,6 +192,7 @@ struct QueryList {
     int32_t* tri;      // [ns]
     double* box;       // [ns][12]: tri box lo/hi, query box lo/hi
     int32_t* cell;     // [ns][6]: first and last cell (x, y, z)
+    int32_t* work;     // work counter of the persistent query (reset before each launch)
 };
 
 template <bool SWEPT>
@@ -269,7 +270,8 @@ k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __
     const int n_list = *Q.n;
     const double eps = P.dhat;
     const double (*rule)[3] = c_rule[P.L - 1];
-    for (int li = warp; li < n_list; li += nwarps) {
+    (void)warp; (void)nwarps;
+    for (int li = next_item(Q.work, lane); li < n_list; li = next_item(Q.work, lane)) {
     const int64_t t = Q.tri[li];
     const int32_t* T = S.stri + 3 * t;
     double x0[3], x1[3], x2[3];
@@ -552,7 +554,8 @@ k_query_ccd(SceneView S, Params P, QueryList Q, const double* __restrict__ x,
     double best = 1.0;
     long long n_pt = 0, n_ee = 0;
     int cap_hit = 0;
-    for (int li = warp; li < n_list; li += nwarps) {
+    (void)warp; (void)nwarps;
+    for (int li = next_item(Q.work, lane); li < n_list; li = next_item(Q.work, lane)) {
     const int64_t t = Q.tri[li];
     const int32_t* T = S.stri + 3 * t;
     const double* qb = Q.box + 12 * (int64_t)li;
@@ -723,6 +726,7 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
 static QueryList query_list(Ctx& c) {
     QueryList Q;
     Q.n = c.misc_i32.p + 8;
+    Q.work = c.misc_i32.p + 5;
     Q.tri = c.qlist_tri.p;
     Q.box = c.qlist_box.p;
     Q.cell = c.qlist_cell.p;
@@ -756,6 +760,7 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
         S, P, x, nullptr, c.cell_start.p, Q, c.cand_count.p, triE, triG, triS, f32);
     GMCP_CUDA_TRY(cudaGetLastError());
     const unsigned g = persistent_blocks(c);
+    GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), s));
     if (P.nk == 4)
         k_query_contact<4><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mcell.p, c.cell_start.p,
                                              c.cell_ent.p, triE, triG, triS, f32);
@@ -778,6 +783,7 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
     k_query_filter<true><<<(unsigned)((c.ns + 255) / 256), 256, 0, c.stream>>>(
         S, c.P, x, dx, c.cell_start.p, Q, nullptr, nullptr, nullptr, nullptr, 0);
     GMCP_CUDA_TRY(cudaGetLastError());
+    GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), c.stream));
     k_query_ccd<<<persistent_blocks(c), 256, 0, c.stream>>>(S, c.P, Q, x, dx, xm0, dxm, c.mbox.p,
                                                           c.mcell.p, c.cell_start.p, c.cell_ent.p,
                                                           alpha_bits, counters);

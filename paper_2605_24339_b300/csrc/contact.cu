@@ -255,7 +255,8 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
     double al8[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) al8[j] = (MODE == MODE_LAGGED && j < LG.na) ? LG.alphas[j] : 0.0;
-    for (int i = warp; i < n_active; i += nwarps) {
+    (void)warp; (void)nwarps;
+    for (int i = next_item(C.work, lane); i < n_active; i = next_item(C.work, lane)) {
         const int64_t t = C.active[i];
         const int32_t* Tt = S.stri + 3 * t;
         const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
@@ -546,6 +547,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
                            unsigned long long* alpha_bits, LagArgs LG = LagArgs()) {
     const int threads = 256;
     const int blocks = sm_count(c.device) * c.tune_samples_bpsm;
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
     k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
         c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG);
     return cudaGetLastError();

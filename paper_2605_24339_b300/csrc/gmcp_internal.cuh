@@ -105,7 +105,16 @@ struct CandView {
     int32_t* active;    // [ns] slave tris with at least one candidate
     int32_t* n_active;  // scalar
     int32_t* overflow;  // [3] max count seen per kind (for regrowth)
+    int32_t* work;      // work counter of the sample kernel (reset before each launch)
 };
+
+// Dynamic work distribution for persistent warps: lane 0 takes the next item
+// index from a global counter and broadcasts it (all lanes must call).
+__device__ __forceinline__ int next_item(int32_t* counter, int lane) {
+    int i = 0;
+    if (lane == 0) i = atomicAdd(counter, 1);
+    return __shfl_sync(0xffffffffu, i, 0);
+}
 
 // ------------------------------------------------------------------------
 // section profiler: CUDA events around named groups of launches on the
@@ -325,7 +334,7 @@ struct Ctx {
         c.cap_f = cap_f; c.cap_e = cap_e; c.cap_p = cap_p;
         c.face = cand_face.p; c.edge = cand_edge.p; c.point = cand_point.p;
         c.count = cand_count.p; c.active = active.p;
-        c.n_active = misc_i32.p; c.overflow = misc_i32.p + 1;
+        c.n_active = misc_i32.p; c.overflow = misc_i32.p + 1; c.work = misc_i32.p + 4;
         return c;
     }
 };
