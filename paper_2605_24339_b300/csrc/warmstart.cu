@@ -174,12 +174,14 @@ template <int K, int EPI>
 __device__ __forceinline__ void act_epilogue(uint32_t tacc, int64_t m0, int64_t mp, const float* __restrict__ bias,
                                              const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ C,
                                              __nv_bfloat16* __restrict__ CT) {
+    // warp w reads TMEM lanes 32 (w % 4) ..; the two warpgroups split the columns
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = warp * 32 + lane;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = quarter * 32 + lane;
     const int64_t gr = m0 + r;
-    for (int c0 = 0; c0 < 256; c0 += 16) {
+    for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
         float v[16];
-        tmem_ld16(tacc + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+        tmem_ld16(tacc + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
         if (EPI == 0) {
 #pragma unroll
             for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + bias[c0 + i], 0.0f);
@@ -210,7 +212,7 @@ __device__ __forceinline__ void act_epilogue(uint32_t tacc, int64_t m0, int64_t 
 }
 
 template <int K, int EPI>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
 k_umma_act(const __nv_bfloat16* __restrict__ A, int64_t mp, const __nv_bfloat16* __restrict__ W,
            const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ C,
            __nv_bfloat16* __restrict__ CT, int* __restrict__ err) {
@@ -287,7 +289,7 @@ k_umma_act(const __nv_bfloat16* __restrict__ A, int64_t mp, const __nv_bfloat16*
 // The row sums of AT over the same range (the bias gradient) are taken from
 // the staged tiles: bpart[b][o].
 template <int NP>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(256, 1)
 k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restrict__ BT, int64_t mp,
              float* __restrict__ partial, float* __restrict__ bpart, int* __restrict__ err) {
     constexpr int KC = 64;
@@ -310,7 +312,7 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
     const int64_t c0 = nch * blockIdx.x / gridDim.x, c1 = nch * (blockIdx.x + 1) / gridDim.x;
     uint32_t ph[2] = {0, 0};
     bool used[2] = {false, false};
-    float rs0 = 0.0f, rs1 = 0.0f;                       // row sums of rows tid, tid + 128
+    float rs = 0.0f;                                    // row sum of row tid
     auto stage_of = [&](int st) { return smem + st * (SA + SB); };
     if (c1 > c0) {
         stage_tile_async(stage_of(0), AT, mp, 0, 256, 256, KC, c0 * KC);
@@ -337,9 +339,8 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
         }
         used[st] = true;
         // bias gradient: row sums of the staged AT rows (read-only use of the stage)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int r = threadIdx.x + 128 * q;
+        {
+            const int r = threadIdx.x;
             float acc = 0.0f;
 #pragma unroll
             for (int j = 0; j < KC / 8; ++j) {
@@ -348,7 +349,7 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
 #pragma unroll
                 for (int i = 0; i < 8; ++i) acc += __bfloat162float(b[i]);
             }
-            if (q == 0) rs0 += acc; else rs1 += acc;
+            rs += acc;
         }
         // prefetch the next chunk into the other stage once its MMAs finished
         if (ch + 1 < c1) {
@@ -375,13 +376,15 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // warpgroup h reads accumulator h (rows o = 128 h + TMEM lane)
     float* out = partial + (int64_t)blockIdx.x * 256 * NP;
-    for (int h = 0; h < 2; ++h) {
-        const int o = h * 128 + warp * 32 + lane;
+    {
+        const int h = warp >> 2, quarter = warp & 3;
+        const int o = h * 128 + quarter * 32 + lane;
         for (int n0 = 0; n0 < NP; n0 += 16) {
             float v[16];
             if (c1 > c0 && !abort_flag) {
-                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * NP + n0), v);
+                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * NP + n0), v);
             } else {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) v[i] = 0.0f;
@@ -390,8 +393,7 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
             for (int i = 0; i < 16; ++i) out[(int64_t)o * NP + n0 + i] = v[i];
         }
     }
-    bpart[(int64_t)blockIdx.x * 256 + threadIdx.x] = rs0;
-    bpart[(int64_t)blockIdx.x * 256 + 128 + threadIdx.x] = rs1;
+    bpart[(int64_t)blockIdx.x * 256 + threadIdx.x] = rs;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -702,7 +704,7 @@ cudaError_t launch_act(Ctx& c, WarmStart& W, const __nv_bfloat16* A, const __nv_
     const size_t sm = std::max(kActSmem(K), kOneCtaSmem);
     GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_act<K, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = (int)std::min<int64_t>(sm_count(c.device), W.mp / 128);
-    k_umma_act<K, EPI><<<grid, 128, sm, c.stream>>>(A, W.mp, Wt, bias, mask, C, CT, W.err.p);
+    k_umma_act<K, EPI><<<grid, 256, sm, c.stream>>>(A, W.mp, Wt, bias, mask, C, CT, W.err.p);
     return cudaGetLastError();
 }
 
@@ -713,7 +715,7 @@ cudaError_t launch_wgrad(Ctx& c, WarmStart& W, const __nv_bfloat16* AT, const __
     GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_wgrad<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = sm_count(c.device);
     float* bpart = W.part.p + (size_t)grid * 256 * NP;
-    k_umma_wgrad<NP><<<grid, 128, sm, c.stream>>>(AT, BT, W.mp, W.part.p, bpart, W.err.p);
+    k_umma_wgrad<NP><<<grid, 256, sm, c.stream>>>(AT, BT, W.mp, W.part.p, bpart, W.err.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     k_reduce_part<<<nb(256 * NP, 256), 256, 0, c.stream>>>(W.part.p, grid, 256 * NP, 256 * NP, out);
     k_reduce_part<<<1, 256, 0, c.stream>>>(bpart, grid, 256, 256, bias_out);
