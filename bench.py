@@ -271,7 +271,7 @@ def run_ours(args):
         "clocks": clk,
     }
     if not args.no_batch:
-        line["batched"] = batched_measurement(dev)
+        line["batched"] = batched_measurement(dev, n_env=args.batch_envs)
     if not args.no_newton:
         line["newton_step"] = newton_measurement(dev)
         line["warm_start"] = warm_start_measurement(dev)
@@ -319,7 +319,8 @@ def batched_measurement(dev, n_env=64, steps=20):
                                 grad_out=grad)
     for _ in range(3):
         info = step()
-    cnt = ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=True)["counts"]
+    full = ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=True)
+    cnt = full["counts"]
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     total = 0.0
     for _ in range(steps):
@@ -329,14 +330,26 @@ def batched_measurement(dev, n_env=64, steps=20):
         ev1.record(stream)
         ev1.synchronize()
         total += ev0.elapsed_time(ev1)
+    # per-section device times, as for the single-environment pass
+    ctx.profile_start()
+    for _ in range(steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_stop()
+    prof = ctx.profile_read()
     ctx.close()
     ms = total / steps
     return {"workload": f"fingertip_batch {n_env} envs x 5 pads (16-128 quads, 4 samples/tri) vs "
                         f"2k-80k-tri objects, pads pressed 1.5 dhat",
             "n_env": n_env, "slave_tris": int(sc.stris.shape[0]), "master_tris": int(sc.mtris.shape[0]),
             "samples_per_pass": int(units), "active_face_samples": int(cnt["face"]),
+            "candidates": {k: int(c[k]) for k in ("face", "edge", "point")},
+            "face_evaluated": int(cnt["face_evaluated"]), "query_tris": int(cnt["query_tris"]),
+            "swept_tris": int(full["swept_tris"]), "ccd_pairs": [int(full["n_pt"]), int(full["n_ee"])],
             "ms_per_pass": ms, "samples_per_s": units / (ms / 1e3),
             "autotuned_blocks_per_sm": {"samples": tune_s, "query": tune_q},
+            "sections_ms": {k: round(v["ms"] / max(v["calls"], 1), 4) for k, v in prof.items()},
             "alpha": info["alpha"], "scene_build_s": round(gen_s, 1)}
 
 
@@ -583,9 +596,12 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-envs measurement")
     ap.add_argument("--no-newton", action="store_true",
                     help="skip the time-step measurement (newton_step key)")
-    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton"],
+    ap.add_argument("--batch-envs", type=int, default=64,
+                    help="environments in the batched measurement")
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
-                         "training steps or time steps (command lines for profilers)")
+                         "training steps or time steps (command lines for profilers); batch: "
+                         "the batched measurement alone, --steps timed passes")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
@@ -595,6 +611,9 @@ def main():
         run_mlp(args)
     elif args.mode == "newton":
         run_newton(args)
+    elif args.mode == "batch":
+        print(json.dumps(batched_measurement(0, n_env=args.batch_envs,
+                                             steps=args.steps)), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

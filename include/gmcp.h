@@ -103,6 +103,8 @@ typedef struct {
 typedef struct {
     int64_t face, edge, point, guard;
     int64_t face_evaluated;   /* (face sample, candidate) pairs tested */
+    int64_t query_tris;       /* slave tris whose grown box reached a non-empty
+                                 grid cell (the exact candidate tests ran on these) */
 } ipc_sample_counts;
 
 /* View of a context-owned block-sparse (3x3) matrix.  Valid until the next
@@ -123,6 +125,7 @@ typedef struct {
     double alpha_accd;     /* additive CCD minimum over primitive pairs */
     int64_t n_pairs_pt, n_pairs_ee;
     int32_t iter_cap_hit;  /* 1 if some pair stopped at ccd_max_iter */
+    int64_t swept_tris;    /* slave tris whose swept box reached a non-empty grid cell */
 } ipc_ccd_info;
 
 typedef struct {

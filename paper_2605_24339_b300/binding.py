@@ -58,7 +58,7 @@ class CandCounts(C.Structure):
 
 class SampleCounts(C.Structure):
     _fields_ = [("face", C.c_int64), ("edge", C.c_int64), ("point", C.c_int64),
-                ("guard", C.c_int64), ("face_evaluated", C.c_int64)]
+                ("guard", C.c_int64), ("face_evaluated", C.c_int64), ("query_tris", C.c_int64)]
 
 
 class BsrView(C.Structure):
@@ -68,7 +68,8 @@ class BsrView(C.Structure):
 
 class CcdInfo(C.Structure):
     _fields_ = [("alpha", C.c_double), ("alpha_lin", C.c_double), ("alpha_accd", C.c_double),
-                ("n_pairs_pt", C.c_int64), ("n_pairs_ee", C.c_int64), ("iter_cap_hit", C.c_int32)]
+                ("n_pairs_pt", C.c_int64), ("n_pairs_ee", C.c_int64), ("iter_cap_hit", C.c_int32),
+                ("swept_tris", C.c_int64)]
 
 
 class StepStats(C.Structure):
@@ -298,7 +299,7 @@ class Context:
         out = dict(energy=e.value if energy_dev is None else None, grad=g)
         if counts:
             out["counts"] = dict(face=sc.face, edge=sc.edge, point=sc.point, guard=sc.guard,
-                                 face_evaluated=sc.face_evaluated)
+                                 face_evaluated=sc.face_evaluated, query_tris=sc.query_tris)
         if hess == "view":
             out["hess"] = bv
         elif hess:
@@ -321,7 +322,8 @@ class Context:
         self._check(lib().ipc_ccd_max_step(self.h, _ptr(x), _ptr(dx), _ptr(xm0), _ptr(xm1),
                                            C.byref(a), C.byref(info)))
         return dict(alpha=info.alpha, alpha_lin=info.alpha_lin, alpha_accd=info.alpha_accd,
-                    n_pt=info.n_pairs_pt, n_ee=info.n_pairs_ee, iter_cap_hit=bool(info.iter_cap_hit))
+                    n_pt=info.n_pairs_pt, n_ee=info.n_pairs_ee, iter_cap_hit=bool(info.iter_cap_hit),
+                    swept_tris=info.swept_tris)
 
     def contact_pass(self, x, xm0, dx=None, xm1=None, grad=True, hess=True, counts=True,
                      energy_dev=None, grad_out=None, host_alpha=True):
@@ -347,14 +349,14 @@ class Context:
         out = dict(energy=e.value if energy_dev is None else None, grad=g)
         if counts:
             out["counts"] = dict(face=sc.face, edge=sc.edge, point=sc.point, guard=sc.guard,
-                                 face_evaluated=sc.face_evaluated)
+                                 face_evaluated=sc.face_evaluated, query_tris=sc.query_tris)
         if hess == "view":
             out["hess"] = bv
         elif hess:
             out["hess"] = self.bsr(bv)
         if want_a:
             out.update(alpha=info.alpha, alpha_lin=info.alpha_lin, alpha_accd=info.alpha_accd,
-                       n_pt=info.n_pairs_pt, n_ee=info.n_pairs_ee)
+                       n_pt=info.n_pairs_pt, n_ee=info.n_pairs_ee, swept_tris=info.swept_tris)
         return out
 
     # -- profiling ---------------------------------------------------------

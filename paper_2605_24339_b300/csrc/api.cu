@@ -25,6 +25,7 @@ SceneView Ctx::view() const {
     S.stri_env = stri_env.p; S.mtri_env = mtri_env.p;
     S.X = X.p; S.Y0 = Y0.p; S.srest_box = srest_box.p; S.mrest_box = mrest_box.p;
     S.grid_org = grid_org.p; S.grid_inv = grid_inv.p; S.grid_dim = grid_dim.p; S.grid_off = grid_off.p;
+    S.grid_org_f = grid_org_f.p; S.grid_inv_f = grid_inv_f.p;
     S.margin = margin;
     return S;
 }
@@ -218,7 +219,7 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.red_tmp.p, (uintptr_t)c.red_tmp.n, (uintptr_t)c.cell_ent.p, (uintptr_t)c.cand_face.p,
             (uintptr_t)c.cand_edge.p, (uintptr_t)c.cand_point.p, (uintptr_t)c.cand_count.p, (uintptr_t)c.active.p,
             (uintptr_t)c.qlist_tri.p, (uintptr_t)c.qlist_box.p, (uintptr_t)c.qlist_cell.p, (uintptr_t)c.mbox.p,
-            (uintptr_t)c.mcell.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
+            (uintptr_t)c.mcell.p, (uintptr_t)c.mcell_hi.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
             (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
             (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,
             (uintptr_t)c.cb_val64.p, (uintptr_t)c.u64_tmp.p, (uintptr_t)c.i64_tmp.p, (uintptr_t)c.misc_i32.p,
@@ -668,6 +669,9 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
     CK(c.mrest_box.upload(mbox.data(), mbox.size(), s));
     CK(c.grid_org.upload(org.data(), org.size(), s));
     CK(c.grid_inv.upload(inv.data(), inv.size(), s));
+    std::vector<float> org_f(org.begin(), org.end()), inv_f(inv.begin(), inv.end());
+    CK(c.grid_org_f.upload(org_f.data(), org_f.size(), s));
+    CK(c.grid_inv_f.upload(inv_f.data(), inv_f.size(), s));
     CK(c.grid_dim.upload(dim.data(), dim.size(), s));
     CK(c.grid_off.upload(goff.data(), goff.size(), s));
     CK(c.vt_off.upload(vt_off.data(), vt_off.size(), s));
@@ -929,11 +933,14 @@ ipc_status ipc_barrier_eval(ipc_ctx* ctx, const double* x_dev, const double* xm_
         API_CK(ctx, cudaMemcpyAsync(c.h_scalars, edev, sizeof(double), cudaMemcpyDeviceToHost, c.stream));
     if (counts)
         API_CK(ctx, cudaMemcpyAsync(c.h_counts, c.i64_tmp.p, 4 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
+    int32_t n_query = 0;
+    if (counts)
+        API_CK(ctx, cudaMemcpyAsync(&n_query, c.misc_i32.p + 8, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
     if (energy_host || counts) API_CK(ctx, cudaStreamSynchronize(c.stream));
     if (energy_host) *energy_host = c.h_scalars[0];
     if (counts) {
         counts->face = c.h_counts[0]; counts->edge = c.h_counts[1]; counts->point = c.h_counts[2];
-        counts->guard = 0; counts->face_evaluated = c.h_counts[3];
+        counts->guard = 0; counts->face_evaluated = c.h_counts[3]; counts->query_tris = n_query;
     }
     if (hess) {
         const bool f32 = c.P.precision == IPC_PREC_MIXED;
@@ -974,8 +981,10 @@ ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_
     API_CK(ctx, bp_ccd_accd(c, x_dev, dx_dev, xm0_dev, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8));
     unsigned long long bits[2];
     long long ctr[4];
+    int32_t n_swept = 0;
     API_CK(ctx, cudaMemcpyAsync(bits, c.u64_tmp.p, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
     API_CK(ctx, cudaMemcpyAsync(ctr, c.i64_tmp.p + 8, sizeof(ctr), cudaMemcpyDeviceToHost, c.stream));
+    API_CK(ctx, cudaMemcpyAsync(&n_swept, c.misc_i32.p + 9, sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream));
     API_CK(ctx, cudaStreamSynchronize(c.stream));
     double al, aa;
     memcpy(&al, &bits[0], 8);
@@ -987,6 +996,7 @@ ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_
     if (info) {
         info->alpha = a; info->alpha_lin = al; info->alpha_accd = aa;
         info->n_pairs_pt = ctr[0]; info->n_pairs_ee = ctr[1]; info->iter_cap_hit = (int32_t)(ctr[2] != 0);
+        info->swept_tris = n_swept;
     }
     return IPC_OK;
 }
@@ -1033,6 +1043,7 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
     if (counts) {
         counts->face = c.pin->counts[0]; counts->edge = c.pin->counts[1]; counts->point = c.pin->counts[2];
         counts->guard = 0; counts->face_evaluated = c.pin->counts[3];
+        counts->query_tris = c.pin->flags[8];
     }
     if (hess) {
         const bool f32 = c.P.precision == IPC_PREC_MIXED;
@@ -1052,6 +1063,7 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
             info->alpha = a; info->alpha_lin = al; info->alpha_accd = aa;
             info->n_pairs_pt = c.pin->ctr_ccd[0]; info->n_pairs_ee = c.pin->ctr_ccd[1];
             info->iter_cap_hit = (int32_t)(c.pin->ctr_ccd[2] != 0);
+            info->swept_tris = c.pin->flags[9];
         }
     }
     return IPC_OK;

@@ -9,6 +9,8 @@
 // Grid: one dense box of cells per environment, sized at context creation
 // from the rest geometry; cell coordinates are clamped to the box, which
 // keeps the cell map monotone (so overlapping boxes always share a cell).
+// Cell ranges are conservative FP32 ranges (see cell_range_f); the exact
+// FP64 tests decide every pair.
 // Master triangles are counting-sorted into cells (atomic integer counts,
 // exclusive scan, atomic integer cursors).  A query visits the cells of its
 // box and reports a master triangle only in the first cell common to both
@@ -38,24 +40,93 @@ struct I3 { int x, y, z; };
 __device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
 __device__ __forceinline__ double dmax_(double a, double b) { return a > b ? a : b; }
 
-__device__ __forceinline__ int cell_coord(double p, double o, double inv, int dim) {
-    double f = floor((p - o) * inv);
-    f = f < 0.0 ? 0.0 : f;
-    f = f > (double)(dim - 1) ? (double)(dim - 1) : f;
-    return (f == f) ? (int)f : 0;     // NaN maps to cell 0
-}
-
-__device__ __forceinline__ I3 cell_of(const SceneView& S, int e, double px, double py, double pz) {
-    const double* o = S.grid_org + 3 * e;
-    const int* d = S.grid_dim + 3 * e;
-    const double inv = S.grid_inv[e];
-    return I3{cell_coord(px, o[0], inv, d[0]), cell_coord(py, o[1], inv, d[1]),
-              cell_coord(pz, o[2], inv, d[2])};
-}
-
 __device__ __forceinline__ int64_t cell_id(const SceneView& S, int e, int ix, int iy, int iz) {
     const int* d = S.grid_dim + 3 * e;
     return S.grid_off[e] + (int64_t)ix + (int64_t)d[0] * ((int64_t)iy + (int64_t)d[1] * iz);
+}
+
+// ---------------------------------------------------------------------------
+// Conservative cell ranges without the FP64 pipe.
+//
+// B300 issues FP64 at 1/64 of the FP32 rate, and the per-triangle box and
+// cell arithmetic of the filters and the grid build kept that pipe ~75% busy.
+// Cell ranges only have to CONTAIN the cells the exact FP64 map gives: a
+// wider range visits more cells but changes no result, because the exact
+// FP64 box tests decide every pair, and the "first common cell" rule that
+// reports a pair once is evaluated on the same (wider) ranges that are
+// visited.  So the ranges are computed in FP32 from truncated copies of the
+// coordinates, widened by a bound on every rounding involved.
+// ---------------------------------------------------------------------------
+
+// v truncated toward zero to FP32 from its bits (integer pipe only):
+// |result - v| <= 2^-23 |v| for 2^-126 <= |v| < 2^128; +-0 below that (the
+// absolute slack of the cell ranges covers it); +-inf above it; NaN stays NaN.
+__device__ __forceinline__ float trunc_f32(double v) {
+    const unsigned hi = (unsigned)__double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const unsigned sgn = hi & 0x80000000u;
+    const unsigned ex = (hi >> 20) & 0x7FFu;
+    if (ex < 897u) return __uint_as_float(sgn);
+    if (ex > 1150u) {
+        const bool nan = ex == 0x7FFu && ((hi & 0xFFFFFu) | lo) != 0u;
+        return __uint_as_float(sgn | (nan ? 0x7FC00000u : 0x7F800000u));
+    }
+    return __uint_as_float(sgn | ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+// cell index bounds from an FP32 cell coordinate that already includes its
+// slack: NaN and out-of-grid values go to the widest admissible cell
+__device__ __forceinline__ int cell_lo_f(float u, int dim) {
+    if (!(u >= 0.0f)) return 0;
+    if (u >= (float)(dim - 1)) return dim - 1;
+    return (int)u;
+}
+__device__ __forceinline__ int cell_hi_f(float u, int dim) {
+    if (!(u < (float)(dim - 1))) return dim - 1;
+    if (u < 0.0f) return 0;
+    return (int)u;
+}
+
+// Cell range of env e that contains the cells (p - org) * inv (real
+// arithmetic) of every box whose corners differ from lo/hi (FP32) by at most
+// 2^-21 * mag per axis, where mag bounds the sum of the magnitudes of all
+// values combined into the box (vertex coordinates, displacements, growth).
+// With the FP32 rounding of org, inv, the difference and the product, the
+// FP32 cell coordinate is off by at most ~2^-20 (mag + |org|) inv cells; the
+// slack is twice that plus 1e-3 cell, which also covers values flushed to
+// zero by trunc_f32.  Ranges computed this way for two boxes that overlap
+// always share a cell.
+__device__ __forceinline__ void cell_range_f(const SceneView& S, int e, const float* lo, const float* hi,
+                                             const float* mag, I3& a, I3& b) {
+    const float inv = S.grid_inv_f[e];
+    int ra[3], rb[3];
+    for (int q = 0; q < 3; ++q) {
+        const float o = S.grid_org_f[3 * e + q];
+        const int dim = S.grid_dim[3 * e + q];
+        const float sl = (mag[q] + fabsf(o)) * inv * 2e-6f + 1e-3f;
+        ra[q] = cell_lo_f((lo[q] - o) * inv - sl, dim);
+        rb[q] = cell_hi_f((hi[q] - o) * inv + sl, dim);
+    }
+    a = I3{ra[0], ra[1], ra[2]};
+    b = I3{rb[0], rb[1], rb[2]};
+}
+
+// Exact minimum / maximum of doubles by integer comparison of their ordered
+// bit patterns (negative values have their magnitude bits flipped), which
+// keeps the FP64 pipe free.  For non-NaN inputs the result is the IEEE
+// minimum / maximum, except that -0 orders below +0; no box test can tell
+// the two zeros apart.
+__device__ __forceinline__ long long ord_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ double kmin3(double a, double b, double c) {
+    const long long ka = ord_key(a), kb = ord_key(b), kc = ord_key(c);
+    return ka <= kb ? (ka <= kc ? a : c) : (kb <= kc ? b : c);
+}
+__device__ __forceinline__ double kmax3(double a, double b, double c) {
+    const long long ka = ord_key(a), kb = ord_key(b), kc = ord_key(c);
+    return ka >= kb ? (ka >= kc ? a : c) : (kb >= kc ? b : c);
 }
 
 __device__ __forceinline__ void load3(const double* p, int64_t i, double* o) {
@@ -71,37 +142,55 @@ __constant__ double c_rule[2][16][3];
 // ---------------------------------------------------------------------------
 __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
                                  const double* __restrict__ dxm, double* __restrict__ mbox,
-                                 int4* __restrict__ mcell, int32_t* __restrict__ cnt) {
+                                 int4* __restrict__ mcell, int4* __restrict__ mcell_hi,
+                                 int32_t* __restrict__ cnt) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int32_t* T = S.mtri + 3 * m;
-    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    for (int a = 0; a < 3; ++a)
+    double lo[3], hi[3];
+    float flo[3], fhi[3], mag[3];
+    if (dxm) {
+        // swept box: the corners p + dp are FP64 sums
+        for (int c = 0; c < 3; ++c) { lo[c] = DBL_MAX; hi[c] = -DBL_MAX; }
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                double p = xm[3 * (int64_t)T[a] + c];
+                double q = p + dxm[3 * (int64_t)T[a] + c];
+                lo[c] = dmin_(lo[c], dmin_(p, q));
+                hi[c] = dmax_(hi[c], dmax_(p, q));
+            }
         for (int c = 0; c < 3; ++c) {
-            double p = xm[3 * (int64_t)T[a] + c];
-            double q = dxm ? p + dxm[3 * (int64_t)T[a] + c] : p;
-            lo[c] = dmin_(lo[c], dmin_(p, q));
-            hi[c] = dmax_(hi[c], dmax_(p, q));
+            flo[c] = trunc_f32(lo[c]); fhi[c] = trunc_f32(hi[c]);
+            mag[c] = fabsf(flo[c]) + fabsf(fhi[c]);
         }
+    } else {
+        double v[3][3];
+        for (int a = 0; a < 3; ++a) load3(xm, T[a], v[a]);
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = kmin3(v[0][c], v[1][c], v[2][c]);
+            hi[c] = kmax3(v[0][c], v[1][c], v[2][c]);
+            flo[c] = trunc_f32(lo[c]); fhi[c] = trunc_f32(hi[c]);
+            mag[c] = fabsf(flo[c]) + fabsf(fhi[c]);
+        }
+    }
     for (int c = 0; c < 3; ++c) { mbox[6 * m + c] = lo[c]; mbox[6 * m + 3 + c] = hi[c]; }
     const int e = S.mtri_env[m];
-    I3 a = cell_of(S, e, lo[0], lo[1], lo[2]);
-    I3 b = cell_of(S, e, hi[0], hi[1], hi[2]);
+    I3 a, b;
+    cell_range_f(S, e, flo, fhi, mag, a, b);
     mcell[m] = make_int4(a.x, a.y, a.z, e);
+    mcell_hi[m] = make_int4(b.x, b.y, b.z, 0);
     for (int iz = a.z; iz <= b.z; ++iz)
         for (int iy = a.y; iy <= b.y; ++iy)
             for (int ix = a.x; ix <= b.x; ++ix) atomicAdd(&cnt[cell_id(S, e, ix, iy, iz)], 1);
 }
 
-__global__ void k_mtri_fill(SceneView S, const double* __restrict__ mbox,
+__global__ void k_mtri_fill(SceneView S, const int4* __restrict__ mcell, const int4* __restrict__ mcell_hi,
                             const int32_t* __restrict__ start, int32_t* __restrict__ cursor,
                             int32_t* __restrict__ ent, int64_t cap, int32_t* __restrict__ overflow) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
-    const int e = S.mtri_env[m];
-    const double* B = mbox + 6 * m;
-    I3 a = cell_of(S, e, B[0], B[1], B[2]);
-    I3 b = cell_of(S, e, B[3], B[4], B[5]);
+    const int4 a = mcell[m], b = mcell_hi[m];
+    const int e = a.w;
     for (int iz = a.z; iz <= b.z; ++iz)
         for (int iy = a.y; iy <= b.y; ++iy)
             for (int ix = a.x; ix <= b.x; ++ix) {
@@ -204,28 +293,33 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S.ns) return;
     const int32_t* T = S.stri + 3 * t;
-    double lo[3], hi[3];
-    if (SWEPT) {
-        swept_vert(x, dx, T[0], lo, hi);
-        for (int a = 1; a < 3; ++a) {
-            double l[3], h[3];
-            swept_vert(x, dx, T[a], l, h);
-            grow_box(lo, hi, l, h);
-        }
-    } else {
-        double x0[3], x1[3], x2[3];
-        load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
-        for (int c = 0; c < 3; ++c) {
-            lo[c] = dmin_(x0[c], dmin_(x1[c], x2[c]));
-            hi[c] = dmax_(x0[c], dmax_(x1[c], x2[c]));
-        }
+    // The decision (does the grown box reach a non-empty cell?) is taken on a
+    // conservative FP32 box; only the triangles that pass get their exact
+    // FP64 box, which the exact tests of the second phase use.
+    double v[3][3], d[3][3];
+    for (int a = 0; a < 3; ++a) {
+        load3(x, T[a], v[a]);
+        if (SWEPT) load3(dx, T[a], d[a]);
     }
     const double grow = SWEPT ? S.margin : P.dhat + S.margin;
-    double qlo[3], qhi[3];
-    for (int c = 0; c < 3; ++c) { qlo[c] = lo[c] - grow; qhi[c] = hi[c] + grow; }
+    const float grow_f = (float)grow;
+    float flo[3], fhi[3], mag[3];
+    for (int c = 0; c < 3; ++c) {
+        float lo_c = INFINITY, hi_c = -INFINITY, m_c = grow_f;
+        for (int a = 0; a < 3; ++a) {
+            const float p = trunc_f32(v[a][c]);
+            lo_c = fminf(lo_c, p); hi_c = fmaxf(hi_c, p); m_c += fabsf(p);
+            if (SWEPT) {
+                const float dp = trunc_f32(d[a][c]);
+                const float q = p + dp;
+                lo_c = fminf(lo_c, q); hi_c = fmaxf(hi_c, q); m_c += fabsf(dp);
+            }
+        }
+        flo[c] = lo_c - grow_f; fhi[c] = hi_c + grow_f; mag[c] = m_c;
+    }
     const int e = S.stri_env[t];
-    const I3 ca = cell_of(S, e, qlo[0], qlo[1], qlo[2]);
-    const I3 cb = cell_of(S, e, qhi[0], qhi[1], qhi[2]);
+    I3 ca, cb;
+    cell_range_f(S, e, flo, fhi, mag, ca, cb);
     bool any = false;
     for (int iz = ca.z; iz <= cb.z && !any; ++iz)
         for (int iy = ca.y; iy <= cb.y && !any; ++iy) {
@@ -233,6 +327,24 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
             any = start[c0 + (cb.x - ca.x) + 1] > start[c0];   // cells of a row are contiguous
         }
     if (any) {
+        double lo[3], hi[3];
+        if (SWEPT) {
+            // swept box of the vertices at x and x + dx (FP64 sums)
+            for (int c = 0; c < 3; ++c) { lo[c] = DBL_MAX; hi[c] = -DBL_MAX; }
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 3; ++c) {
+                    const double p = v[a][c], q = p + d[a][c];
+                    lo[c] = dmin_(lo[c], dmin_(p, q));
+                    hi[c] = dmax_(hi[c], dmax_(p, q));
+                }
+        } else {
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = kmin3(v[0][c], v[1][c], v[2][c]);
+                hi[c] = kmax3(v[0][c], v[1][c], v[2][c]);
+            }
+        }
+        double qlo[3], qhi[3];
+        for (int c = 0; c < 3; ++c) { qlo[c] = lo[c] - grow; qhi[c] = hi[c] + grow; }
         const int idx = atomicAdd(Q.n, 1);
         Q.tri[idx] = (int32_t)t;
         double* b = Q.box + 12 * (int64_t)idx;
@@ -690,6 +802,7 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     cudaStream_t s = c.stream;
     GMCP_CUDA_TRY(c.mbox.ensure(6 * (size_t)c.nmt + 6));
     GMCP_CUDA_TRY(c.mcell.ensure((size_t)c.nmt + 1));
+    GMCP_CUDA_TRY(c.mcell_hi.ensure((size_t)c.nmt + 1));
     GMCP_CUDA_TRY(c.cell_cnt.ensure((size_t)c.n_cells + 1));
     GMCP_CUDA_TRY(c.cell_start.ensure((size_t)c.n_cells + 1));
     GMCP_CUDA_TRY(c.scan_tmp.ensure(2 * scan_tmp_size(c.n_cells)));
@@ -697,7 +810,8 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     const int B = 256;
     const unsigned g = (unsigned)((c.nmt + B - 1) / B);
     if (c.nmt > 0) {
-        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mbox.p, c.mcell.p, c.cell_cnt.p);
+        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mbox.p, c.mcell.p, c.mcell_hi.p,
+                                         c.cell_cnt.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     GMCP_CUDA_TRY(exclusive_scan_i32(c.cell_cnt.p, c.cell_start.p, c.n_cells, c.scan_tmp.p,
@@ -716,16 +830,18 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     }
     GMCP_CUDA_TRY(cudaMemsetAsync(c.cell_cnt.p, 0, sizeof(int32_t) * (c.n_cells + 1), s));
     if (c.nmt > 0) {
-        k_mtri_fill<<<g, B, 0, s>>>(S, c.mbox.p, c.cell_start.p, c.cell_cnt.p, c.cell_ent.p,
+        k_mtri_fill<<<g, B, 0, s>>>(S, c.mcell.p, c.mcell_hi.p, c.cell_start.p, c.cell_cnt.p, c.cell_ent.p,
                                     (int64_t)c.cell_ent.n, c.misc_i32.p + 12);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
 }
 
-static QueryList query_list(Ctx& c) {
+// the contact and swept queries share the list buffers but keep their
+// lengths apart (slots 8 and 9), so both survive a pass for the statistics
+static QueryList query_list(Ctx& c, bool swept) {
     QueryList Q;
-    Q.n = c.misc_i32.p + 8;
+    Q.n = c.misc_i32.p + (swept ? 9 : 8);
     Q.work = c.misc_i32.p + 5;
     Q.tri = c.qlist_tri.p;
     Q.box = c.qlist_box.p;
@@ -749,7 +865,7 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
     cudaStream_t s = c.stream;
     CandView C = c.cand();
     GMCP_CUDA_TRY(ensure_query_list(c));
-    QueryList Q = query_list(c);
+    QueryList Q = query_list(c, false);
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 12, s));
     if (c.ns == 0) return cudaSuccess;
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
@@ -778,7 +894,7 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
     if (c.ns == 0) return cudaSuccess;
     SceneView S = c.view();
     GMCP_CUDA_TRY(ensure_query_list(c));
-    QueryList Q = query_list(c);
+    QueryList Q = query_list(c, true);
     GMCP_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(int32_t), c.stream));
     k_query_filter<true><<<(unsigned)((c.ns + 255) / 256), 256, 0, c.stream>>>(
         S, c.P, x, dx, c.cell_start.p, Q, nullptr, nullptr, nullptr, nullptr, 0);

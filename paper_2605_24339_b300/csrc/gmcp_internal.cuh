@@ -83,6 +83,8 @@ struct SceneView {
     const double* grid_inv;       // [n_env] 1 / cell size
     const int32_t* grid_dim;      // [n_env][3]
     const int64_t* grid_off;      // [n_env+1] first cell of each env
+    const float* grid_org_f;      // [n_env][3] the same origin and inverse cell size
+    const float* grid_inv_f;      // [n_env]    rounded to FP32 (conservative cell ranges)
     double margin;                // coarse-test slack (covers rounding of grown boxes)
 };
 
@@ -269,6 +271,7 @@ struct Ctx {
     DBuf<int32_t> stri_env, mtri_env;
     DBuf<double> X, Y0, srest_box, mrest_box;
     DBuf<double> grid_org, grid_inv;
+    DBuf<float> grid_org_f, grid_inv_f;
     DBuf<int32_t> grid_dim;
     DBuf<int64_t> grid_off;
     double margin = 0.0;
@@ -283,6 +286,7 @@ struct Ctx {
     // per-call broad-phase buffers
     DBuf<double> mbox;                          // [nmt][6]
     DBuf<int4> mcell;                           // [nmt] lowest cell (x, y, z) and env
+    DBuf<int4> mcell_hi;                        // [nmt] highest cell (x, y, z)
     DBuf<int32_t> qlist_tri, qlist_cell;        // slave tris whose query meets a non-empty cell
     DBuf<double> qlist_box;
     DBuf<int32_t> cell_cnt, cell_start, cell_ent;

@@ -86,6 +86,32 @@ def test_candidates_bit_exact(B, oracle_mod, name, sc, x):
     ctx.close()
 
 
+@pytest.mark.parametrize("offset", [(37.25, -12.5, 5.125), (-1e3, 2e3, -512.0)])
+def test_candidates_far_from_origin(B, oracle_mod, offset):
+    """The grid's cell ranges are computed in FP32 with a slack that grows
+    with the coordinates' magnitude: a scene far from the origin (cells of
+    ~0.1 mm at 40 m and at 2 km) must still give the oracle's exact candidate
+    sets, and the swept query the oracle's additive-CCD step."""
+    sc, x = small_indent(n_quads=8, subdiv=2, press=0.1e-3, seed=5)
+    off = np.asarray(offset)
+    import dataclasses
+    sc = dataclasses.replace(sc, X=sc.X + off, Y0=sc.Y0 + off)
+    x = x + off
+    ctx = B.Context(sc, precision="fp64")
+    O = oracle_mod.Scene(sc)
+    cnt = ctx.candidates(x, sc.Y0)
+    for kind in range(3):
+        np.testing.assert_array_equal(ctx.candidate_pairs(kind), O.candidates(kind, x, sc.Y0),
+                                      err_msg=f"kind {kind}")
+    assert cnt["face"] > 0
+    dx = np.zeros_like(x)
+    dx[:, 2] = -2e-4
+    g = ctx.ccd_max_step(x, dx, sc.Y0)
+    assert g["alpha_accd"] == O.ccd_max_step(x, dx, sc.Y0)[2]
+    assert g["n_pt"] + g["n_ee"] > 0
+    ctx.close()
+
+
 @pytest.mark.parametrize("name,sc,x", SCENES, ids=IDS)
 def test_barrier_eval_fp64_parity(B, oracle_mod, name, sc, x):
     ctx = B.Context(sc, precision="fp64")
