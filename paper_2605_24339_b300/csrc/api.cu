@@ -568,7 +568,9 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
     for (int64_t t = 0; t < ns; ++t) box(sc->pad_rest, sc->s_tris + 3 * t, &sbox[6 * t]);
     for (int64_t t = 0; t < nmt; ++t) box(sc->m_rest, sc->m_tris + 3 * t, &mbox[6 * t]);
     // --- grid per env: master rest box grown by 2 dhat + 5 % of its extent;
-    // cell size = max(largest master tri extent, mean slave tri extent + 2 dhat)
+    // cell size = max(mean master tri extent, mean slave tri extent + 2 dhat).
+    // (The largest master extent made cells up to ~1.5x coarser on meshes of
+    // uneven triangles, and a query visits entries ~ cell size^2.)
     const double dhat = c.P.dhat;
     std::vector<double> org(3 * c.n_env), inv(c.n_env);
     std::vector<int32_t> dim(3 * c.n_env);
@@ -583,8 +585,14 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
             for (int q = 0; q < 3; ++q) {
                 lo[q] = std::min(lo[q], mbox[6 * t + q]);
                 hi[q] = std::max(hi[q], mbox[6 * t + 3 + q]);
-                mext = std::max(mext, mbox[6 * t + 3 + q] - mbox[6 * t + q]);
             }
+        const int64_t nme_ = c.env_mtri_off[e + 1] - c.env_mtri_off[e];
+        for (int64_t t = c.env_mtri_off[e]; t < c.env_mtri_off[e + 1]; ++t) {
+            double m = 0.0;
+            for (int q = 0; q < 3; ++q) m = std::max(m, mbox[6 * t + 3 + q] - mbox[6 * t + q]);
+            mext += m;
+        }
+        if (nme_ > 0) mext /= (double)nme_;
         const int64_t nse_ = c.env_stri_off[e + 1] - c.env_stri_off[e];
         for (int64_t t = c.env_stri_off[e]; t < c.env_stri_off[e + 1]; ++t) {
             double m = 0.0;

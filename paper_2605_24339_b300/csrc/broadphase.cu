@@ -369,20 +369,72 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
     }
 }
 
+// Entries of the cells in one x-row of the query range are contiguous in the
+// cell lists (cells of a row are consecutive and the lists are a prefix sum
+// over cells), so the warp walks each row's entries 32 at a time whatever
+// the cells' occupancy.  A pair is kept only in the first cell common to the
+// two cell ranges: in row (iy, iz) that is the entry at position k of cell
+// cx = max(ca.x, mc.x) when start[cx] <= k < start[cx + 1].
+__device__ __forceinline__ bool first_common_cell(const SceneView& S, const int32_t* __restrict__ start,
+                                                  int e, I3 ca, int4 mc, int iy, int iz, int k) {
+    if (max(ca.y, mc.y) != iy || max(ca.z, mc.z) != iz) return false;
+    const int64_t cell = cell_id(S, e, max(ca.x, mc.x), iy, iz);
+    return start[cell] <= k && k < start[cell + 1];
+}
+
+// Walk over the rows (iy, iz) of a cell range, 32 entries at a time.  While
+// more() holds, [kb, kb + 32) intersected with [kb, k1) is the current chunk
+// of row (iy, iz); empty rows are skipped.
+struct RowWalk {
+    const int32_t* __restrict__ start;
+    int64_t off;           // first cell of the env
+    int dx, dy;            // env grid dimensions in x and y
+    int x0, nx, y0, y1, z1;
+    int iy, iz, kb, k1;
+    __device__ RowWalk(const SceneView& S, const int32_t* __restrict__ st, int e, I3 ca, I3 cb)
+        : start(st), off(S.grid_off[e]), dx(S.grid_dim[3 * e]), dy(S.grid_dim[3 * e + 1]),
+          x0(ca.x), nx(cb.x - ca.x + 1), y0(ca.y), y1(cb.y), z1(cb.z), iy(ca.y), iz(ca.z) {
+        load_row();
+        skip_empty();
+    }
+    __device__ void load_row() {
+        const int64_t c0 = off + (int64_t)x0 + (int64_t)dx * ((int64_t)iy + (int64_t)dy * iz);
+        kb = start[c0];
+        k1 = start[c0 + nx];
+    }
+    __device__ void skip_empty() {
+        while (kb >= k1) {
+            if (++iy > y1) { iy = y0; ++iz; }
+            if (iz > z1) return;
+            load_row();
+        }
+    }
+    __device__ bool more() const { return iz <= z1; }
+    __device__ void next() { kb += 32; skip_empty(); }
+};
+
+// Per-warp queue of the masters that passed the coarse box test: the exact
+// tests then run 32 masters at a time (every lane busy) instead of once per
+// 32 cell entries.
+constexpr int kQueue = 64;
+
+// contact candidate query: persistent warps over the filtered slave
+// triangles.  Per master: the coarse test (query box = slave box grown by
+// dhat + margin) against the master box, then the exact tests of the face,
+// edge and point kinds; every list is sorted at the end.
 template <int NK>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __restrict__ x,
                 const double* __restrict__ xm, const double* __restrict__ mbox,
                 const int4* __restrict__ mcell, const int32_t* __restrict__ start,
                 const int32_t* __restrict__ ent, double* __restrict__ triE,
                 void* __restrict__ triG, void* __restrict__ triS, int out_f32) {
+    __shared__ int32_t s_queue[8][kQueue];
     const int lane = threadIdx.x & 31;
-    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    int32_t* queue = s_queue[threadIdx.x >> 5];
     const int n_list = *Q.n;
     const double eps = P.dhat;
     const double (*rule)[3] = c_rule[P.L - 1];
-    (void)warp; (void)nwarps;
     for (int li = next_item(Q.work, lane); li < n_list; li = next_item(Q.work, lane)) {
     const int64_t t = Q.tri[li];
     const int32_t* T = S.stri + 3 * t;
@@ -394,100 +446,97 @@ k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __
     const int32_t* ql = Q.cell + 6 * (int64_t)li;
     const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
     const int e = S.stri_env[t];
-    const int nx = cb.x - ca.x + 1, ny = cb.y - ca.y + 1, nz = cb.z - ca.z + 1;
-    const int ncell = nx * ny * nz;
     int nf = 0, ne = 0, np = 0;
     int32_t* Lf = C.face + t * C.cap_f;
     int32_t* Le = C.edge + t * C.cap_e;
     int32_t* Lp = C.point + t * C.cap_p;
-    for (int c0 = 0; c0 < ncell; c0 += 32) {
-        // each lane looks at one cell of this chunk
-        int my_k0 = 0, my_k1 = 0, ix = 0, iy = 0, iz = 0;
-        if (c0 + lane < ncell) {
-            const int q = c0 + lane;
-            ix = ca.x + q % nx; iy = ca.y + (q / nx) % ny; iz = ca.z + q / (nx * ny);
-            const int64_t cell = cell_id(S, e, ix, iy, iz);
-            my_k0 = start[cell]; my_k1 = start[cell + 1];
-        }
-        unsigned busy = __ballot_sync(0xffffffffu, my_k1 > my_k0);
-        while (busy) {
-            const int src = __ffs(busy) - 1;
-            busy &= busy - 1;
-            const int k0 = __shfl_sync(0xffffffffu, my_k0, src);
-            const int k1 = __shfl_sync(0xffffffffu, my_k1, src);
-            const int cx = __shfl_sync(0xffffffffu, ix, src);
-            const int cy = __shfl_sync(0xffffffffu, iy, src);
-            const int cz = __shfl_sync(0xffffffffu, iz, src);
-            for (int kb = k0; kb < k1; kb += 32) {
-                const int k = kb + lane;
-                bool take = false;
-                int32_t m = 0;
-                if (k < k1) {
-                    m = ent[k];
-                    const int4 mc = mcell[m];
-                    // report only in the first cell common to both boxes
-                    take = max(ca.x, mc.x) == cx && max(ca.y, mc.y) == cy && max(ca.z, mc.z) == cz;
-                }
-                const double* B = mbox + 6 * (int64_t)m;
-                double mlo0 = 0, mlo1 = 0, mlo2 = 0, mhi0 = 0, mhi1 = 0, mhi2 = 0;
-                if (take) {
-                    mlo0 = B[0]; mlo1 = B[1]; mlo2 = B[2]; mhi0 = B[3]; mhi1 = B[4]; mhi2 = B[5];
-                    take = !(qlo[0] > mhi0 || mlo0 > qhi[0] || qlo[1] > mhi1 || mlo1 > qhi[1] ||
-                             qlo[2] > mhi2 || mlo2 > qhi[2]);
-                }
-                // face: some sample ((b0 x0 + b1 x1) + b2 x2) inside the master box grown by eps
-                bool hit = false;
-                if (take) {
-                    const double l0 = mlo0 - eps, l1 = mlo1 - eps, l2 = mlo2 - eps;
-                    const double h0 = mhi0 + eps, h1 = mhi1 + eps, h2 = mhi2 + eps;
-                    for (int q = 0; q < NK && !hit; ++q) {
-                        const double b0 = rule[q][0], b1 = rule[q][1], b2 = rule[q][2];
-                        const double sxq = b0 * x0[0] + b1 * x1[0] + b2 * x2[0];
-                        if (!(l0 <= sxq && sxq <= h0)) continue;
-                        const double syq = b0 * x0[1] + b1 * x1[1] + b2 * x2[1];
-                        if (!(l1 <= syq && syq <= h1)) continue;
-                        const double szq = b0 * x0[2] + b1 * x1[2] + b2 * x2[2];
-                        hit = l2 <= szq && szq <= h2;
-                    }
-                }
-                warp_append(hit, m, Lf, C.cap_f, nf);
-                // owned edges and vertices
-                for (int j = 0; j < 3; ++j) {
-                    bool ok = false;
-                    int32_t me = -1;
-                    if (take) {
-                        me = S.mtri_own_edge[3 * (int64_t)m + j];
-                        if (me >= 0) {
-                            double ya[3], yb[3];
-                            load3(xm, S.medge[2 * (int64_t)me], ya);
-                            load3(xm, S.medge[2 * (int64_t)me + 1], yb);
-                            ok = true;
-                            for (int c = 0; c < 3 && ok; ++c) {
-                                const double lo = dmin_(ya[c], yb[c]) - eps, hi = dmax_(ya[c], yb[c]) + eps;
-                                ok = slo[c] <= hi && lo <= shi[c];
-                            }
-                        }
-                    }
-                    warp_append(ok, me, Le, C.cap_e, ne);
-                }
-                for (int j = 0; j < 3; ++j) {
-                    bool ok = false;
-                    int32_t u = -1;
-                    if (take) {
-                        u = S.mtri_own_vert[3 * (int64_t)m + j];
-                        if (u >= 0) {
-                            double y[3];
-                            load3(xm, u, y);
-                            ok = true;
-                            for (int c = 0; c < 3 && ok; ++c) ok = slo[c] <= y[c] + eps && y[c] - eps <= shi[c];
-                        }
-                    }
-                    warp_append(ok, u, Lp, C.cap_p, np);
-                }
+
+    // exact tests of the first n queued masters, one per lane
+    auto run_exact = [&](int n) {
+        const bool have = lane < n;
+        const int32_t m = have ? queue[lane] : 0;
+        // face: some sample ((b0 x0 + b1 x1) + b2 x2) inside the master box grown by eps
+        bool hit = false;
+        if (have) {
+            const double* B = mbox + 6 * (int64_t)m;
+            const double l0 = B[0] - eps, l1 = B[1] - eps, l2 = B[2] - eps;
+            const double h0 = B[3] + eps, h1 = B[4] + eps, h2 = B[5] + eps;
+            for (int q = 0; q < NK && !hit; ++q) {
+                const double b0 = rule[q][0], b1 = rule[q][1], b2 = rule[q][2];
+                const double sxq = b0 * x0[0] + b1 * x1[0] + b2 * x2[0];
+                if (!(l0 <= sxq && sxq <= h0)) continue;
+                const double syq = b0 * x0[1] + b1 * x1[1] + b2 * x2[1];
+                if (!(l1 <= syq && syq <= h1)) continue;
+                const double szq = b0 * x0[2] + b1 * x1[2] + b2 * x2[2];
+                hit = l2 <= szq && szq <= h2;
             }
         }
+        warp_append(hit, m, Lf, C.cap_f, nf);
+        // owned edges and vertices: slave tri box vs their boxes grown by eps
+        for (int j = 0; j < 3; ++j) {
+            bool ok = false;
+            int32_t me = -1;
+            if (have) {
+                me = S.mtri_own_edge[3 * (int64_t)m + j];
+                if (me >= 0) {
+                    double ya[3], yb[3];
+                    load3(xm, S.medge[2 * (int64_t)me], ya);
+                    load3(xm, S.medge[2 * (int64_t)me + 1], yb);
+                    ok = true;
+                    for (int c = 0; c < 3 && ok; ++c) {
+                        const double lo = dmin_(ya[c], yb[c]) - eps, hi = dmax_(ya[c], yb[c]) + eps;
+                        ok = slo[c] <= hi && lo <= shi[c];
+                    }
+                }
+            }
+            warp_append(ok, me, Le, C.cap_e, ne);
+        }
+        for (int j = 0; j < 3; ++j) {
+            bool ok = false;
+            int32_t u = -1;
+            if (have) {
+                u = S.mtri_own_vert[3 * (int64_t)m + j];
+                if (u >= 0) {
+                    double y[3];
+                    load3(xm, u, y);
+                    ok = true;
+                    for (int c = 0; c < 3 && ok; ++c) ok = slo[c] <= y[c] + eps && y[c] - eps <= shi[c];
+                }
+            }
+            warp_append(ok, u, Lp, C.cap_p, np);
+        }
+    };
+
+    RowWalk W(S, start, e, ca, cb);
+    for (int nq = 0;;) {
+        // queue coarse-test survivors until 32 are waiting or the rows are done
+        while (nq < 32 && W.more()) {
+            const int k = W.kb + lane;
+            bool take = false;
+            int32_t m = 0;
+            if (k < W.k1) {
+                m = ent[k];
+                take = first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
+                if (take) {
+                    const double* B = mbox + 6 * (int64_t)m;
+                    take = !(qlo[0] > B[3] || B[0] > qhi[0] || qlo[1] > B[4] || B[1] > qhi[1] ||
+                             qlo[2] > B[5] || B[2] > qhi[2]);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            if (take) queue[nq + __popc(bal & lanemask_lt())] = m;
+            nq += __popc(bal);
+            W.next();
+        }
+        if (nq == 0) break;
+        __syncwarp();
+        const int n = min(nq, 32);
+        run_exact(n);
+        __syncwarp();
+        if (lane < nq - n) queue[lane] = queue[n + lane];
+        nq -= n;
+        __syncwarp();
     }
-    __syncwarp();
     warp_sort(Lf, min(nf, C.cap_f), lane);
     warp_sort(Le, min(ne, C.cap_e), lane);
     warp_sort(Lp, min(np, C.cap_p), lane);
@@ -651,22 +700,27 @@ __device__ __forceinline__ void atomic_min_pos(unsigned long long* dst, double v
     atomicMin(dst, (unsigned long long)__double_as_longlong(v));
 }
 
-// swept query + ACCD: persistent warps over the filtered slave triangles,
-// lanes over cell entries
-__global__ void __launch_bounds__(256)
+// swept query + ACCD: persistent warps over the filtered slave triangles.
+// Cell entries are walked row by row and the masters that pass the coarse
+// swept-box test are queued, as in the contact query.  The swept boxes of
+// the slave triangle's owned vertices and edges are formed once per
+// triangle (per-warp shared memory); a master edge's box once per master.
+__global__ void __launch_bounds__(256, 2)
 k_query_ccd(SceneView S, Params P, QueryList Q, const double* __restrict__ x,
             const double* __restrict__ dx, const double* __restrict__ xm0,
             const double* __restrict__ dxm, const double* __restrict__ mbox,
             const int4* __restrict__ mcell, const int32_t* __restrict__ start,
             const int32_t* __restrict__ ent, unsigned long long* alpha_bits, long long* counters) {
+    __shared__ int32_t s_queue[8][kQueue];
+    __shared__ double s_box[8][6][6];      // owned slave vertices 0-2, edges 3-5: lo xyz, hi xyz
+    __shared__ int32_t s_own[8][6];        // their ids (-1: not owned)
     const int lane = threadIdx.x & 31;
-    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int wib = threadIdx.x >> 5;
+    int32_t* queue = s_queue[wib];
     const int n_list = *Q.n;
     double best = 1.0;
     long long n_pt = 0, n_ee = 0;
     int cap_hit = 0;
-    (void)warp; (void)nwarps;
     for (int li = next_item(Q.work, lane); li < n_list; li = next_item(Q.work, lane)) {
     const int64_t t = Q.tri[li];
     const int32_t* T = S.stri + 3 * t;
@@ -676,101 +730,124 @@ k_query_ccd(SceneView S, Params P, QueryList Q, const double* __restrict__ x,
     const int32_t* ql = Q.cell + 6 * (int64_t)li;
     const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
     const int e = S.stri_env[t];
-    const int nx = cb.x - ca.x + 1, ny = cb.y - ca.y + 1, nz = cb.z - ca.z + 1;
-    const int ncell = nx * ny * nz;
-    for (int c0 = 0; c0 < ncell; c0 += 32) {
-        int my_k0 = 0, my_k1 = 0, ix = 0, iy = 0, iz = 0;
-        if (c0 + lane < ncell) {
-            const int q = c0 + lane;
-            ix = ca.x + q % nx; iy = ca.y + (q / nx) % ny; iz = ca.z + q / (nx * ny);
-            const int64_t cell = cell_id(S, e, ix, iy, iz);
-            my_k0 = start[cell]; my_k1 = start[cell + 1];
-        }
-        unsigned busy = __ballot_sync(0xffffffffu, my_k1 > my_k0);
-        while (busy) {
-            const int src = __ffs(busy) - 1;
-            busy &= busy - 1;
-            const int k0 = __shfl_sync(0xffffffffu, my_k0, src);
-            const int k1 = __shfl_sync(0xffffffffu, my_k1, src);
-            const int cx = __shfl_sync(0xffffffffu, ix, src);
-            const int cy = __shfl_sync(0xffffffffu, iy, src);
-            const int cz = __shfl_sync(0xffffffffu, iz, src);
-            for (int k = k0 + lane; k < k1; k += 32) {
-                const int32_t m = ent[k];
-                const int4 mc = mcell[m];
-                if (max(ca.x, mc.x) != cx || max(ca.y, mc.y) != cy || max(ca.z, mc.z) != cz) continue;
-                const double* B = mbox + 6 * (int64_t)m;
-                if (!overlap(qlo, qhi, B, B + 3)) continue;
-                const int32_t* M = S.mtri + 3 * (int64_t)m;
-                double X12[12], P12[12];
-                int it;
-                // slave vertices owned by t vs master triangle m
-                for (int j = 0; j < 3; ++j) {
-                    const int32_t v = S.stri_own_vert[3 * t + j];
-                    if (v < 0) continue;
-                    double vlo[3], vhi[3];
-                    swept_vert(x, dx, v, vlo, vhi);
-                    if (!overlap(vlo, vhi, B, B + 3)) continue;
-                    for (int c = 0; c < 3; ++c) {
-                        X12[c] = x[3 * (int64_t)v + c]; P12[c] = dx[3 * (int64_t)v + c];
-                        for (int a = 0; a < 3; ++a) {
-                            X12[3 + 3 * a + c] = xm0[3 * (int64_t)M[a] + c];
-                            P12[3 + 3 * a + c] = dxm ? dxm[3 * (int64_t)M[a] + c] : 0.0;
-                        }
-                    }
-                    const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-                    ++n_pt; cap_hit |= it >= P.ccd_max_iter;
-                    best = dmin_(best, r);
-                }
-                // master vertices owned by m vs slave triangle t
-                for (int j = 0; j < 3; ++j) {
-                    const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
-                    if (u < 0) continue;
-                    double ulo[3], uhi[3];
-                    swept_vert(xm0, dxm, u, ulo, uhi);
-                    if (!overlap(ulo, uhi, tlo, thi)) continue;
-                    for (int c = 0; c < 3; ++c) {
-                        X12[c] = xm0[3 * (int64_t)u + c]; P12[c] = dxm ? dxm[3 * (int64_t)u + c] : 0.0;
-                        for (int a = 0; a < 3; ++a) {
-                            X12[3 + 3 * a + c] = x[3 * (int64_t)T[a] + c];
-                            P12[3 + 3 * a + c] = dx[3 * (int64_t)T[a] + c];
-                        }
-                    }
-                    const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-                    ++n_pt; cap_hit |= it >= P.ccd_max_iter;
-                    best = dmin_(best, r);
-                }
-                // slave edges owned by t vs master edges owned by m
-                for (int j = 0; j < 3; ++j) {
-                    const int32_t es = S.stri_own_edge[3 * t + j];
-                    if (es < 0) continue;
-                    const int32_t sa = S.sedge[2 * (int64_t)es], sb = S.sedge[2 * (int64_t)es + 1];
-                    double alo[3], ahi[3], l2[3], h2[3];
-                    swept_vert(x, dx, sa, alo, ahi);
-                    swept_vert(x, dx, sb, l2, h2);
-                    grow_box(alo, ahi, l2, h2);
-                    for (int q = 0; q < 3; ++q) {
-                        const int32_t em = S.mtri_own_edge[3 * (int64_t)m + q];
-                        if (em < 0) continue;
-                        const int32_t m0 = S.medge[2 * (int64_t)em], m1 = S.medge[2 * (int64_t)em + 1];
-                        double blo[3], bhi[3];
-                        swept_vert(xm0, dxm, m0, blo, bhi);
-                        swept_vert(xm0, dxm, m1, l2, h2);
-                        grow_box(blo, bhi, l2, h2);
-                        if (!overlap(alo, ahi, blo, bhi)) continue;
-                        for (int c = 0; c < 3; ++c) {
-                            X12[c] = x[3 * (int64_t)sa + c]; P12[c] = dx[3 * (int64_t)sa + c];
-                            X12[3 + c] = x[3 * (int64_t)sb + c]; P12[3 + c] = dx[3 * (int64_t)sb + c];
-                            X12[6 + c] = xm0[3 * (int64_t)m0 + c]; P12[6 + c] = dxm ? dxm[3 * (int64_t)m0 + c] : 0.0;
-                            X12[9 + c] = xm0[3 * (int64_t)m1 + c]; P12[9 + c] = dxm ? dxm[3 * (int64_t)m1 + c] : 0.0;
-                        }
-                        const double r = accd(1, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-                        ++n_ee; cap_hit |= it >= P.ccd_max_iter;
-                        best = dmin_(best, r);
-                    }
-                }
+    __syncwarp();
+    if (lane < 6) {
+        double* bx = s_box[wib][lane];
+        int32_t id;
+        if (lane < 3) {
+            id = S.stri_own_vert[3 * t + lane];
+            if (id >= 0) swept_vert(x, dx, id, bx, bx + 3);
+        } else {
+            id = S.stri_own_edge[3 * t + lane - 3];
+            if (id >= 0) {
+                double l2[3], h2[3];
+                swept_vert(x, dx, S.sedge[2 * (int64_t)id], bx, bx + 3);
+                swept_vert(x, dx, S.sedge[2 * (int64_t)id + 1], l2, h2);
+                grow_box(bx, bx + 3, l2, h2);
             }
         }
+        s_own[wib][lane] = id;
+    }
+    __syncwarp();
+
+    // exact tests and ACCD of the first n queued masters, one per lane
+    auto run_exact = [&](int n) {
+        if (lane >= n) return;
+        const int32_t m = queue[lane];
+        const double* B = mbox + 6 * (int64_t)m;
+        const int32_t* M = S.mtri + 3 * (int64_t)m;
+        double X12[12], P12[12];
+        int it;
+        // slave vertices owned by t vs master triangle m
+        for (int j = 0; j < 3; ++j) {
+            const int32_t v = s_own[wib][j];
+            if (v < 0) continue;
+            const double* vb = s_box[wib][j];
+            if (!overlap(vb, vb + 3, B, B + 3)) continue;
+            for (int c = 0; c < 3; ++c) {
+                X12[c] = x[3 * (int64_t)v + c]; P12[c] = dx[3 * (int64_t)v + c];
+                for (int a = 0; a < 3; ++a) {
+                    X12[3 + 3 * a + c] = xm0[3 * (int64_t)M[a] + c];
+                    P12[3 + 3 * a + c] = dxm ? dxm[3 * (int64_t)M[a] + c] : 0.0;
+                }
+            }
+            const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+            ++n_pt; cap_hit |= it >= P.ccd_max_iter;
+            best = dmin_(best, r);
+        }
+        // master vertices owned by m vs slave triangle t
+        for (int j = 0; j < 3; ++j) {
+            const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
+            if (u < 0) continue;
+            double ulo[3], uhi[3];
+            swept_vert(xm0, dxm, u, ulo, uhi);
+            if (!overlap(ulo, uhi, tlo, thi)) continue;
+            for (int c = 0; c < 3; ++c) {
+                X12[c] = xm0[3 * (int64_t)u + c]; P12[c] = dxm ? dxm[3 * (int64_t)u + c] : 0.0;
+                for (int a = 0; a < 3; ++a) {
+                    X12[3 + 3 * a + c] = x[3 * (int64_t)T[a] + c];
+                    P12[3 + 3 * a + c] = dx[3 * (int64_t)T[a] + c];
+                }
+            }
+            const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+            ++n_pt; cap_hit |= it >= P.ccd_max_iter;
+            best = dmin_(best, r);
+        }
+        // master edges owned by m vs slave edges owned by t
+        for (int q = 0; q < 3; ++q) {
+            const int32_t em = S.mtri_own_edge[3 * (int64_t)m + q];
+            if (em < 0) continue;
+            const int32_t m0 = S.medge[2 * (int64_t)em], m1 = S.medge[2 * (int64_t)em + 1];
+            double blo[3], bhi[3], l2[3], h2[3];
+            swept_vert(xm0, dxm, m0, blo, bhi);
+            swept_vert(xm0, dxm, m1, l2, h2);
+            grow_box(blo, bhi, l2, h2);
+            for (int j = 0; j < 3; ++j) {
+                const int32_t es = s_own[wib][3 + j];
+                if (es < 0) continue;
+                const double* ab = s_box[wib][3 + j];
+                if (!overlap(ab, ab + 3, blo, bhi)) continue;
+                const int32_t sa = S.sedge[2 * (int64_t)es], sb = S.sedge[2 * (int64_t)es + 1];
+                for (int c = 0; c < 3; ++c) {
+                    X12[c] = x[3 * (int64_t)sa + c]; P12[c] = dx[3 * (int64_t)sa + c];
+                    X12[3 + c] = x[3 * (int64_t)sb + c]; P12[3 + c] = dx[3 * (int64_t)sb + c];
+                    X12[6 + c] = xm0[3 * (int64_t)m0 + c]; P12[6 + c] = dxm ? dxm[3 * (int64_t)m0 + c] : 0.0;
+                    X12[9 + c] = xm0[3 * (int64_t)m1 + c]; P12[9 + c] = dxm ? dxm[3 * (int64_t)m1 + c] : 0.0;
+                }
+                const double r = accd(1, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+                ++n_ee; cap_hit |= it >= P.ccd_max_iter;
+                best = dmin_(best, r);
+            }
+        }
+    };
+
+    RowWalk W(S, start, e, ca, cb);
+    for (int nq = 0;;) {
+        while (nq < 32 && W.more()) {
+            const int k = W.kb + lane;
+            bool take = false;
+            int32_t m = 0;
+            if (k < W.k1) {
+                m = ent[k];
+                take = first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
+                if (take) {
+                    const double* B = mbox + 6 * (int64_t)m;
+                    take = overlap(qlo, qhi, B, B + 3);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            if (take) queue[nq + __popc(bal & lanemask_lt())] = m;
+            nq += __popc(bal);
+            W.next();
+        }
+        if (nq == 0) break;
+        __syncwarp();
+        const int n = min(nq, 32);
+        run_exact(n);
+        __syncwarp();
+        if (lane < nq - n) queue[lane] = queue[n + lane];
+        nq -= n;
+        __syncwarp();
     }
     }  // list loop
     // warp reductions (min is exact; counters are integers)
@@ -817,9 +894,10 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     GMCP_CUDA_TRY(exclusive_scan_i32(c.cell_cnt.p, c.cell_start.p, c.n_cells, c.scan_tmp.p,
                                      c.scan_tmp.n, s));
     if (lazy) {
-        // A triangle whose rest extent is at most one cell spans at most 3
-        // cells per axis in any rigid pose; the fill flags any overflow, which
-        // the caller checks when it synchronises and then redoes the pass.
+        // Cells are at least the mean master extent, so a triangle spans a few
+        // cells per axis and 27 entries per triangle is ample on average; the
+        // fill flags any overflow, which the caller checks when it
+        // synchronises and then redoes the pass with a larger list.
         GMCP_CUDA_TRY(c.cell_ent.ensure(std::max<size_t>(27 * (size_t)c.nmt + 1, c.cell_ent.n)));
     } else {
         int32_t total = 0;
