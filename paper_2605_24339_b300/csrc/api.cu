@@ -197,13 +197,21 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
 // capacity flags of the last lazy pass (valid after a synchronisation)
 bool pass_overflowed(const Ctx& c) {
     const int32_t* f = c.pin->flags;
-    return f[1] || f[2] || f[3] || f[12];
+    return f[1] || f[2] || f[3] || f[12] || f[13] || f[14];
 }
 
 cudaError_t grow_after_overflow(Ctx& c) {
     const int32_t* f = c.pin->flags;
     if (f[1] || f[2] || f[3]) GMCP_CUDA_TRY(grow_candidates(c, f[1], f[2], f[3]));
     if (f[12]) GMCP_CUDA_TRY(c.cell_ent.ensure(2 * c.cell_ent.n));
+    if (f[13]) {
+        c.cap_ccd = std::max(c.cap_ccd, f[13]);
+        GMCP_CUDA_TRY(c.ccd_pairs.ensure((size_t)c.cap_ccd));
+    }
+    if (f[14]) {
+        c.cap_coarse = std::max(c.cap_coarse, f[14]);
+        GMCP_CUDA_TRY(c.coarse_pairs.ensure((size_t)c.cap_coarse));
+    }
     return cudaSuccess;
 }
 
@@ -218,9 +226,11 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             // capture and replay must not leave a stale address in the graph
             (uintptr_t)c.red_tmp.p, (uintptr_t)c.red_tmp.n, (uintptr_t)c.cell_ent.p, (uintptr_t)c.cand_face.p,
             (uintptr_t)c.cand_edge.p, (uintptr_t)c.cand_point.p, (uintptr_t)c.cand_count.p, (uintptr_t)c.active.p,
-            (uintptr_t)c.qlist_tri.p, (uintptr_t)c.qlist_box.p, (uintptr_t)c.qlist_cell.p, (uintptr_t)c.mbox.p,
+            (uintptr_t)c.qlist_tri.p, (uintptr_t)c.qlist_box.p, (uintptr_t)c.qlist_boxf.p, (uintptr_t)c.mboxf.p,
+            (uintptr_t)c.ccd_pairs.p, (uintptr_t)c.cap_ccd, (uintptr_t)c.coarse_pairs.p,
+            (uintptr_t)c.cap_coarse, (uintptr_t)c.qlist_vboxf.p, (uintptr_t)c.qlist_cell.p, (uintptr_t)c.mbox.p,
             (uintptr_t)c.mcell.p, (uintptr_t)c.mcell_hi.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
-            (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
+            (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_frame.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
             (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,
             (uintptr_t)c.cb_val64.p, (uintptr_t)c.u64_tmp.p, (uintptr_t)c.i64_tmp.p, (uintptr_t)c.misc_i32.p,
             (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p};

@@ -129,6 +129,43 @@ __device__ __forceinline__ double kmax3(double a, double b, double c) {
     return ka >= kb ? (ka >= kc ? a : c) : (kb >= kc ? b : c);
 }
 
+// Conservative FP32 bounds of a double: lo_f32(v) <= v <= hi_f32(v), within
+// ~2^-21 |v| + 1e-30 of v, from trunc_f32 and FP32 arithmetic with directed
+// rounding (no FP64 instruction).  Each bound keeps a slack of at least
+// ~2^-23 |v| beyond the truncation error, which also covers the FP64
+// rounding of a sum of two such values (2^-53 of their magnitudes).
+__device__ __forceinline__ float f32_slack(float t) { return __fadd_ru(fabsf(t) * 0x1p-22f, 1e-30f); }
+__device__ __forceinline__ float lo_f32(double v) {
+    const float t = trunc_f32(v);
+    return __fsub_rd(t, f32_slack(t));
+}
+__device__ __forceinline__ float hi_f32(double v) {
+    const float t = trunc_f32(v);
+    return __fadd_ru(t, f32_slack(t));
+}
+// FP32 box test that keeps a pair unless the boxes are certainly apart
+// (NaN compares false, so it keeps)
+__device__ __forceinline__ bool overlap_keep(const float* alo, const float* ahi, const float* blo,
+                                             const float* bhi) {
+    return !(alo[0] > bhi[0] || blo[0] > ahi[0] || alo[1] > bhi[1] || blo[1] > ahi[1] ||
+             alo[2] > bhi[2] || blo[2] > ahi[2]);
+}
+// conservative FP32 box of a vertex swept from p to p + d (d may be NULL);
+// contains the FP64 box of swept_vert
+__device__ __forceinline__ void swept_vert_f(const double* P, const double* D, int64_t v, float* lo,
+                                             float* hi) {
+    for (int c = 0; c < 3; ++c) {
+        const double a = P[3 * v + c];
+        float l = lo_f32(a), h = hi_f32(a);
+        if (D) {
+            const double b = D[3 * v + c];
+            l = fminf(l, __fadd_rd(l, lo_f32(b)));
+            h = fmaxf(h, __fadd_ru(h, hi_f32(b)));
+        }
+        lo[c] = l; hi[c] = h;
+    }
+}
+
 __device__ __forceinline__ void load3(const double* p, int64_t i, double* o) {
     o[0] = p[3 * i]; o[1] = p[3 * i + 1]; o[2] = p[3 * i + 2];
 }
@@ -142,8 +179,8 @@ __constant__ double c_rule[2][16][3];
 // ---------------------------------------------------------------------------
 __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
                                  const double* __restrict__ dxm, double* __restrict__ mbox,
-                                 int4* __restrict__ mcell, int4* __restrict__ mcell_hi,
-                                 int32_t* __restrict__ cnt) {
+                                 float* __restrict__ mboxf, int4* __restrict__ mcell,
+                                 int4* __restrict__ mcell_hi, int32_t* __restrict__ cnt) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int32_t* T = S.mtri + 3 * m;
@@ -159,21 +196,21 @@ __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
                 lo[c] = dmin_(lo[c], dmin_(p, q));
                 hi[c] = dmax_(hi[c], dmax_(p, q));
             }
-        for (int c = 0; c < 3; ++c) {
-            flo[c] = trunc_f32(lo[c]); fhi[c] = trunc_f32(hi[c]);
-            mag[c] = fabsf(flo[c]) + fabsf(fhi[c]);
-        }
     } else {
         double v[3][3];
         for (int a = 0; a < 3; ++a) load3(xm, T[a], v[a]);
         for (int c = 0; c < 3; ++c) {
             lo[c] = kmin3(v[0][c], v[1][c], v[2][c]);
             hi[c] = kmax3(v[0][c], v[1][c], v[2][c]);
-            flo[c] = trunc_f32(lo[c]); fhi[c] = trunc_f32(hi[c]);
-            mag[c] = fabsf(flo[c]) + fabsf(fhi[c]);
         }
     }
-    for (int c = 0; c < 3; ++c) { mbox[6 * m + c] = lo[c]; mbox[6 * m + 3 + c] = hi[c]; }
+    // exact FP64 box, and its conservative FP32 bounds for the coarse tests
+    for (int c = 0; c < 3; ++c) {
+        flo[c] = lo_f32(lo[c]); fhi[c] = hi_f32(hi[c]);
+        mag[c] = fabsf(flo[c]) + fabsf(fhi[c]);
+        mbox[6 * m + c] = lo[c]; mbox[6 * m + 3 + c] = hi[c];
+        mboxf[6 * m + c] = flo[c]; mboxf[6 * m + 3 + c] = fhi[c];
+    }
     const int e = S.mtri_env[m];
     I3 a, b;
     cell_range_f(S, e, flo, fhi, mag, a, b);
@@ -279,7 +316,9 @@ __device__ void warp_sort(int32_t* L, int n, int lane) {
 struct QueryList {
     int32_t* n;        // scalar
     int32_t* tri;      // [ns]
-    double* box;       // [ns][12]: tri box lo/hi, query box lo/hi
+    float* boxf;       // [ns][6]: query box lo/hi (conservative FP32: contains the exact grown box)
+    float* vboxf;      // [ns][3][6]: swept query only, conservative FP32 box of each corner
+    double* box;       // [ns][6]: exact slave tri box lo/hi (contact query only)
     int32_t* cell;     // [ns][6]: first and last cell (x, y, z)
     int32_t* work;     // work counter of the persistent query (reset before each launch)
 };
@@ -293,29 +332,32 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S.ns) return;
     const int32_t* T = S.stri + 3 * t;
-    // The decision (does the grown box reach a non-empty cell?) is taken on a
-    // conservative FP32 box; only the triangles that pass get their exact
-    // FP64 box, which the exact tests of the second phase use.
+    // The decision (does the grown box reach a non-empty cell?) and the
+    // coarse box of the second phase are conservative FP32 bounds; no FP64
+    // instruction runs here except the exact slave box of contact survivors.
     double v[3][3], d[3][3];
     for (int a = 0; a < 3; ++a) {
         load3(x, T[a], v[a]);
         if (SWEPT) load3(dx, T[a], d[a]);
     }
     const double grow = SWEPT ? S.margin : P.dhat + S.margin;
-    const float grow_f = (float)grow;
+    const float grow_up = __double2float_ru(grow);
     float flo[3], fhi[3], mag[3];
+    float vb[3][6];        // swept: conservative FP32 box of each corner (as swept_vert_f)
     for (int c = 0; c < 3; ++c) {
-        float lo_c = INFINITY, hi_c = -INFINITY, m_c = grow_f;
+        float lo_c = INFINITY, hi_c = -INFINITY, m_c = grow_up;
         for (int a = 0; a < 3; ++a) {
-            const float p = trunc_f32(v[a][c]);
-            lo_c = fminf(lo_c, p); hi_c = fmaxf(hi_c, p); m_c += fabsf(p);
+            float pl = lo_f32(v[a][c]), ph = hi_f32(v[a][c]);
+            m_c += fmaxf(fabsf(pl), fabsf(ph));
             if (SWEPT) {
-                const float dp = trunc_f32(d[a][c]);
-                const float q = p + dp;
-                lo_c = fminf(lo_c, q); hi_c = fmaxf(hi_c, q); m_c += fabsf(dp);
+                const float dl = lo_f32(d[a][c]), dh = hi_f32(d[a][c]);
+                m_c += fmaxf(fabsf(dl), fabsf(dh));
+                pl = fminf(pl, __fadd_rd(pl, dl)); ph = fmaxf(ph, __fadd_ru(ph, dh));
+                vb[a][c] = pl; vb[a][3 + c] = ph;
             }
+            lo_c = fminf(lo_c, pl); hi_c = fmaxf(hi_c, ph);
         }
-        flo[c] = lo_c - grow_f; fhi[c] = hi_c + grow_f; mag[c] = m_c;
+        flo[c] = __fsub_rd(lo_c, grow_up); fhi[c] = __fadd_ru(hi_c, grow_up); mag[c] = m_c;
     }
     const int e = S.stri_env[t];
     I3 ca, cb;
@@ -327,28 +369,22 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
             any = start[c0 + (cb.x - ca.x) + 1] > start[c0];   // cells of a row are contiguous
         }
     if (any) {
-        double lo[3], hi[3];
-        if (SWEPT) {
-            // swept box of the vertices at x and x + dx (FP64 sums)
-            for (int c = 0; c < 3; ++c) { lo[c] = DBL_MAX; hi[c] = -DBL_MAX; }
-            for (int a = 0; a < 3; ++a)
-                for (int c = 0; c < 3; ++c) {
-                    const double p = v[a][c], q = p + d[a][c];
-                    lo[c] = dmin_(lo[c], dmin_(p, q));
-                    hi[c] = dmax_(hi[c], dmax_(p, q));
-                }
-        } else {
-            for (int c = 0; c < 3; ++c) {
-                lo[c] = kmin3(v[0][c], v[1][c], v[2][c]);
-                hi[c] = kmax3(v[0][c], v[1][c], v[2][c]);
-            }
-        }
-        double qlo[3], qhi[3];
-        for (int c = 0; c < 3; ++c) { qlo[c] = lo[c] - grow; qhi[c] = hi[c] + grow; }
         const int idx = atomicAdd(Q.n, 1);
         Q.tri[idx] = (int32_t)t;
-        double* b = Q.box + 12 * (int64_t)idx;
-        for (int c = 0; c < 3; ++c) { b[c] = lo[c]; b[3 + c] = hi[c]; b[6 + c] = qlo[c]; b[9 + c] = qhi[c]; }
+        float* bf = Q.boxf + 6 * (int64_t)idx;
+        for (int c = 0; c < 3; ++c) { bf[c] = flo[c]; bf[3 + c] = fhi[c]; }
+        if (SWEPT) {
+            float* w = Q.vboxf + 18 * (int64_t)idx;
+            for (int a = 0; a < 3; ++a)
+                for (int q = 0; q < 6; ++q) w[6 * a + q] = vb[a][q];
+        } else {
+            // exact slave box for the edge and point tests
+            double* b = Q.box + 6 * (int64_t)idx;
+            for (int c = 0; c < 3; ++c) {
+                b[c] = kmin3(v[0][c], v[1][c], v[2][c]);
+                b[3 + c] = kmax3(v[0][c], v[1][c], v[2][c]);
+            }
+        }
         int32_t* cl = Q.cell + 6 * (int64_t)idx;
         cl[0] = ca.x; cl[1] = ca.y; cl[2] = ca.z; cl[3] = cb.x; cl[4] = cb.y; cl[5] = cb.z;
     } else if (!SWEPT) {
@@ -426,7 +462,8 @@ template <int NK>
 __global__ void __launch_bounds__(256, 3)
 k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __restrict__ x,
                 const double* __restrict__ xm, const double* __restrict__ mbox,
-                const int4* __restrict__ mcell, const int32_t* __restrict__ start,
+                const float* __restrict__ mboxf, const int4* __restrict__ mcell,
+                const int32_t* __restrict__ start,
                 const int32_t* __restrict__ ent, double* __restrict__ triE,
                 void* __restrict__ triG, void* __restrict__ triS, int out_f32) {
     __shared__ int32_t s_queue[8][kQueue];
@@ -440,9 +477,10 @@ k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __
     const int32_t* T = S.stri + 3 * t;
     double x0[3], x1[3], x2[3];
     load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
-    const double* qb = Q.box + 12 * (int64_t)li;
+    const double* qb = Q.box + 6 * (int64_t)li;
     const double slo[3] = {qb[0], qb[1], qb[2]}, shi[3] = {qb[3], qb[4], qb[5]};
-    const double qlo[3] = {qb[6], qb[7], qb[8]}, qhi[3] = {qb[9], qb[10], qb[11]};
+    const float* qf = Q.boxf + 6 * (int64_t)li;
+    const float qlo[3] = {qf[0], qf[1], qf[2]}, qhi[3] = {qf[3], qf[4], qf[5]};
     const int32_t* ql = Q.cell + 6 * (int64_t)li;
     const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
     const int e = S.stri_env[t];
@@ -515,13 +553,12 @@ k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __
             bool take = false;
             int32_t m = 0;
             if (k < W.k1) {
+                // coarse test on conservative FP32 boxes (the exact tests decide),
+                // then the first-common-cell rule
                 m = ent[k];
-                take = first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
-                if (take) {
-                    const double* B = mbox + 6 * (int64_t)m;
-                    take = !(qlo[0] > B[3] || B[0] > qhi[0] || qlo[1] > B[4] || B[1] > qhi[1] ||
-                             qlo[2] > B[5] || B[2] > qhi[2]);
-                }
+                const float* B = mboxf + 6 * (int64_t)m;
+                take = overlap_keep(qlo, qhi, B, B + 3) &&
+                       first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, take);
             if (take) queue[nq + __popc(bal & lanemask_lt())] = m;
@@ -700,156 +737,197 @@ __device__ __forceinline__ void atomic_min_pos(unsigned long long* dst, double v
     atomicMin(dst, (unsigned long long)__double_as_longlong(v));
 }
 
-// swept query + ACCD: persistent warps over the filtered slave triangles.
-// Cell entries are walked row by row and the masters that pass the coarse
-// swept-box test are queued, as in the contact query.  The swept boxes of
-// the slave triangle's owned vertices and edges are formed once per
-// triangle (per-warp shared memory); a master edge's box once per master.
-__global__ void __launch_bounds__(256, 2)
-k_query_ccd(SceneView S, Params P, QueryList Q, const double* __restrict__ x,
-            const double* __restrict__ dx, const double* __restrict__ xm0,
-            const double* __restrict__ dxm, const double* __restrict__ mbox,
-            const int4* __restrict__ mcell, const int32_t* __restrict__ start,
-            const int32_t* __restrict__ ent, unsigned long long* alpha_bits, long long* counters) {
-    __shared__ int32_t s_queue[8][kQueue];
-    __shared__ double s_box[8][6][6];      // owned slave vertices 0-2, edges 3-5: lo xyz, hi xyz
-    __shared__ int32_t s_own[8][6];        // their ids (-1: not owned)
+// Primitive pairs that ACCD must test, emitted by k_query_ccd and consumed
+// by k_accd_pairs: x = first id | kind << 30, y = second id.  Kinds:
+// 0 slave vertex / master tri, 1 master vertex / slave tri, 2 slave edge /
+// master edge.
+struct PairList {
+    int2* p;
+    int32_t* n;          // pairs emitted (may exceed cap)
+    int32_t* overflow;   // needed capacity when it does
+    int32_t cap;
+};
+__device__ __forceinline__ void emit_pair(const PairList& L, int kind, int32_t a, int32_t b) {
+    const int pos = atomicAdd(L.n, 1);
+    if (pos < L.cap) L.p[pos] = make_int2(a | (kind << 30), b);
+    else atomicMax(L.overflow, pos + 1);
+}
+
+// Swept query, in three launches so that each stays light: the walk over
+// cell entries (k_query_ccd, warp per filtered slave triangle) emits the
+// (triangle, master) pairs that pass the coarse test on conservative FP32
+// boxes and the first-common-cell rule; k_ccd_exact (thread per such pair)
+// tests the owned primitives, first on FP32 boxes, then, for the pairs that
+// pass, on their exact FP64 boxes, and emits the primitive pairs that
+// overlap; k_accd_pairs runs ACCD on those.  The primitive pairs are exactly
+// those of the plain FP64 box tests.
+__global__ void __launch_bounds__(256)
+k_query_ccd(SceneView S, QueryList Q, const float* __restrict__ mboxf, const int4* __restrict__ mcell,
+            const int32_t* __restrict__ start, const int32_t* __restrict__ ent, PairList L) {
     const int lane = threadIdx.x & 31;
-    const int wib = threadIdx.x >> 5;
-    int32_t* queue = s_queue[wib];
     const int n_list = *Q.n;
-    double best = 1.0;
-    long long n_pt = 0, n_ee = 0;
-    int cap_hit = 0;
     for (int li = next_item(Q.work, lane); li < n_list; li = next_item(Q.work, lane)) {
-    const int64_t t = Q.tri[li];
-    const int32_t* T = S.stri + 3 * t;
-    const double* qb = Q.box + 12 * (int64_t)li;
-    const double tlo[3] = {qb[0], qb[1], qb[2]}, thi[3] = {qb[3], qb[4], qb[5]};
-    const double qlo[3] = {qb[6], qb[7], qb[8]}, qhi[3] = {qb[9], qb[10], qb[11]};
-    const int32_t* ql = Q.cell + 6 * (int64_t)li;
-    const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
-    const int e = S.stri_env[t];
-    __syncwarp();
-    if (lane < 6) {
-        double* bx = s_box[wib][lane];
-        int32_t id;
-        if (lane < 3) {
-            id = S.stri_own_vert[3 * t + lane];
-            if (id >= 0) swept_vert(x, dx, id, bx, bx + 3);
-        } else {
-            id = S.stri_own_edge[3 * t + lane - 3];
-            if (id >= 0) {
-                double l2[3], h2[3];
-                swept_vert(x, dx, S.sedge[2 * (int64_t)id], bx, bx + 3);
-                swept_vert(x, dx, S.sedge[2 * (int64_t)id + 1], l2, h2);
-                grow_box(bx, bx + 3, l2, h2);
-            }
-        }
-        s_own[wib][lane] = id;
-    }
-    __syncwarp();
-
-    // exact tests and ACCD of the first n queued masters, one per lane
-    auto run_exact = [&](int n) {
-        if (lane >= n) return;
-        const int32_t m = queue[lane];
-        const double* B = mbox + 6 * (int64_t)m;
-        const int32_t* M = S.mtri + 3 * (int64_t)m;
-        double X12[12], P12[12];
-        int it;
-        // slave vertices owned by t vs master triangle m
-        for (int j = 0; j < 3; ++j) {
-            const int32_t v = s_own[wib][j];
-            if (v < 0) continue;
-            const double* vb = s_box[wib][j];
-            if (!overlap(vb, vb + 3, B, B + 3)) continue;
-            for (int c = 0; c < 3; ++c) {
-                X12[c] = x[3 * (int64_t)v + c]; P12[c] = dx[3 * (int64_t)v + c];
-                for (int a = 0; a < 3; ++a) {
-                    X12[3 + 3 * a + c] = xm0[3 * (int64_t)M[a] + c];
-                    P12[3 + 3 * a + c] = dxm ? dxm[3 * (int64_t)M[a] + c] : 0.0;
-                }
-            }
-            const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-            ++n_pt; cap_hit |= it >= P.ccd_max_iter;
-            best = dmin_(best, r);
-        }
-        // master vertices owned by m vs slave triangle t
-        for (int j = 0; j < 3; ++j) {
-            const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
-            if (u < 0) continue;
-            double ulo[3], uhi[3];
-            swept_vert(xm0, dxm, u, ulo, uhi);
-            if (!overlap(ulo, uhi, tlo, thi)) continue;
-            for (int c = 0; c < 3; ++c) {
-                X12[c] = xm0[3 * (int64_t)u + c]; P12[c] = dxm ? dxm[3 * (int64_t)u + c] : 0.0;
-                for (int a = 0; a < 3; ++a) {
-                    X12[3 + 3 * a + c] = x[3 * (int64_t)T[a] + c];
-                    P12[3 + 3 * a + c] = dx[3 * (int64_t)T[a] + c];
-                }
-            }
-            const double r = accd(0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-            ++n_pt; cap_hit |= it >= P.ccd_max_iter;
-            best = dmin_(best, r);
-        }
-        // master edges owned by m vs slave edges owned by t
-        for (int q = 0; q < 3; ++q) {
-            const int32_t em = S.mtri_own_edge[3 * (int64_t)m + q];
-            if (em < 0) continue;
-            const int32_t m0 = S.medge[2 * (int64_t)em], m1 = S.medge[2 * (int64_t)em + 1];
-            double blo[3], bhi[3], l2[3], h2[3];
-            swept_vert(xm0, dxm, m0, blo, bhi);
-            swept_vert(xm0, dxm, m1, l2, h2);
-            grow_box(blo, bhi, l2, h2);
-            for (int j = 0; j < 3; ++j) {
-                const int32_t es = s_own[wib][3 + j];
-                if (es < 0) continue;
-                const double* ab = s_box[wib][3 + j];
-                if (!overlap(ab, ab + 3, blo, bhi)) continue;
-                const int32_t sa = S.sedge[2 * (int64_t)es], sb = S.sedge[2 * (int64_t)es + 1];
-                for (int c = 0; c < 3; ++c) {
-                    X12[c] = x[3 * (int64_t)sa + c]; P12[c] = dx[3 * (int64_t)sa + c];
-                    X12[3 + c] = x[3 * (int64_t)sb + c]; P12[3 + c] = dx[3 * (int64_t)sb + c];
-                    X12[6 + c] = xm0[3 * (int64_t)m0 + c]; P12[6 + c] = dxm ? dxm[3 * (int64_t)m0 + c] : 0.0;
-                    X12[9 + c] = xm0[3 * (int64_t)m1 + c]; P12[9 + c] = dxm ? dxm[3 * (int64_t)m1 + c] : 0.0;
-                }
-                const double r = accd(1, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
-                ++n_ee; cap_hit |= it >= P.ccd_max_iter;
-                best = dmin_(best, r);
-            }
-        }
-    };
-
-    RowWalk W(S, start, e, ca, cb);
-    for (int nq = 0;;) {
-        while (nq < 32 && W.more()) {
+        const float* qf = Q.boxf + 6 * (int64_t)li;
+        const float qlo[3] = {qf[0], qf[1], qf[2]}, qhi[3] = {qf[3], qf[4], qf[5]};
+        const int32_t* ql = Q.cell + 6 * (int64_t)li;
+        const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
+        const int e = S.stri_env[Q.tri[li]];
+        for (RowWalk W(S, start, e, ca, cb); W.more(); W.next()) {
             const int k = W.kb + lane;
             bool take = false;
             int32_t m = 0;
             if (k < W.k1) {
                 m = ent[k];
-                take = first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
-                if (take) {
-                    const double* B = mbox + 6 * (int64_t)m;
-                    take = overlap(qlo, qhi, B, B + 3);
-                }
+                const float* B = mboxf + 6 * (int64_t)m;
+                take = overlap_keep(qlo, qhi, B, B + 3) &&
+                       first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
             }
             const unsigned bal = __ballot_sync(0xffffffffu, take);
-            if (take) queue[nq + __popc(bal & lanemask_lt())] = m;
-            nq += __popc(bal);
-            W.next();
+            if (bal == 0u) continue;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(L.n, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) {
+                const int pos = base + __popc(bal & lanemask_lt());
+                if (pos < L.cap) L.p[pos] = make_int2(li, m);
+                else atomicMax(L.overflow, pos + 1);
+            }
         }
-        if (nq == 0) break;
-        __syncwarp();
-        const int n = min(nq, 32);
-        run_exact(n);
-        __syncwarp();
-        if (lane < nq - n) queue[lane] = queue[n + lane];
-        nq -= n;
-        __syncwarp();
     }
-    }  // list loop
+}
+
+// corner of slave tri T holding vertex v (v is one of T's vertices)
+__device__ __forceinline__ int corner_of(const int32_t* T, int32_t v) {
+    return T[0] == v ? 0 : (T[1] == v ? 1 : 2);
+}
+
+// the exact primitive tests of one (filtered slave triangle, master) pair
+__global__ void __launch_bounds__(256)
+k_ccd_exact(SceneView S, QueryList Q, PairList C, const double* __restrict__ x,
+            const double* __restrict__ dx, const double* __restrict__ xm0,
+            const double* __restrict__ dxm, const double* __restrict__ mbox,
+            const float* __restrict__ mboxf, PairList L) {
+    const int n = min(*C.n, C.cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int2 pr = C.p[i];
+        const int li = pr.x;
+        const int32_t m = pr.y;
+        const int64_t t = Q.tri[li];
+        const int32_t* T = S.stri + 3 * t;
+        const float* vb = Q.vboxf + 18 * (int64_t)li;     // swept boxes of T's corners
+        const float* qf = Q.boxf + 6 * (int64_t)li;
+        const float* Bf = mboxf + 6 * (int64_t)m;
+        // slave vertices owned by t vs master triangle m
+        for (int j = 0; j < 3; ++j) {
+            const int32_t v = S.stri_own_vert[3 * t + j];
+            if (v < 0) continue;
+            const float* b = vb + 6 * corner_of(T, v);
+            if (!overlap_keep(b, b + 3, Bf, Bf + 3)) continue;
+            double vlo[3], vhi[3];
+            swept_vert(x, dx, v, vlo, vhi);
+            const double* B = mbox + 6 * (int64_t)m;
+            if (overlap(vlo, vhi, B, B + 3)) emit_pair(L, 0, v, m);
+        }
+        // master vertices owned by m vs slave triangle t
+        for (int j = 0; j < 3; ++j) {
+            const int32_t u = S.mtri_own_vert[3 * (int64_t)m + j];
+            if (u < 0) continue;
+            float uf_lo[3], uf_hi[3];
+            swept_vert_f(xm0, dxm, u, uf_lo, uf_hi);
+            if (!overlap_keep(uf_lo, uf_hi, qf, qf + 3)) continue;
+            double ulo[3], uhi[3], tlo[3], thi[3], l2[3], h2[3];
+            swept_vert(xm0, dxm, u, ulo, uhi);
+            swept_vert(x, dx, T[0], tlo, thi);
+            swept_vert(x, dx, T[1], l2, h2);
+            grow_box(tlo, thi, l2, h2);
+            swept_vert(x, dx, T[2], l2, h2);
+            grow_box(tlo, thi, l2, h2);
+            if (overlap(ulo, uhi, tlo, thi)) emit_pair(L, 1, u, (int32_t)t);
+        }
+        // slave edges owned by t vs master edges owned by m
+        float se_lo[3][3], se_hi[3][3];
+        int32_t se[3];
+        for (int j = 0; j < 3; ++j) {
+            se[j] = S.stri_own_edge[3 * t + j];
+            if (se[j] < 0) continue;
+            const float* b0 = vb + 6 * corner_of(T, S.sedge[2 * (int64_t)se[j]]);
+            const float* b1 = vb + 6 * corner_of(T, S.sedge[2 * (int64_t)se[j] + 1]);
+            for (int c = 0; c < 3; ++c) {
+                se_lo[j][c] = fminf(b0[c], b1[c]);
+                se_hi[j][c] = fmaxf(b0[3 + c], b1[3 + c]);
+            }
+        }
+        for (int q = 0; q < 3; ++q) {
+            const int32_t em = S.mtri_own_edge[3 * (int64_t)m + q];
+            if (em < 0) continue;
+            const int32_t m0 = S.medge[2 * (int64_t)em], m1 = S.medge[2 * (int64_t)em + 1];
+            float bf_lo[3], bf_hi[3], fl2[3], fh2[3];
+            swept_vert_f(xm0, dxm, m0, bf_lo, bf_hi);
+            swept_vert_f(xm0, dxm, m1, fl2, fh2);
+            for (int c = 0; c < 3; ++c) { bf_lo[c] = fminf(bf_lo[c], fl2[c]); bf_hi[c] = fmaxf(bf_hi[c], fh2[c]); }
+            for (int j = 0; j < 3; ++j) {
+                if (se[j] < 0) continue;
+                if (!overlap_keep(se_lo[j], se_hi[j], bf_lo, bf_hi)) continue;
+                const int32_t sa = S.sedge[2 * (int64_t)se[j]], sb = S.sedge[2 * (int64_t)se[j] + 1];
+                double alo[3], ahi[3], blo[3], bhi[3], l2[3], h2[3];
+                swept_vert(x, dx, sa, alo, ahi);
+                swept_vert(x, dx, sb, l2, h2);
+                grow_box(alo, ahi, l2, h2);
+                swept_vert(xm0, dxm, m0, blo, bhi);
+                swept_vert(xm0, dxm, m1, l2, h2);
+                grow_box(blo, bhi, l2, h2);
+                if (overlap(alo, ahi, blo, bhi)) emit_pair(L, 2, se[j], em);
+            }
+        }
+    }
+}
+
+// ACCD of the emitted pairs, one thread per pair; the minimum and the
+// counters do not depend on the order (exact minimum, integer sums).
+__global__ void __launch_bounds__(256)
+k_accd_pairs(SceneView S, Params P, PairList L, const double* __restrict__ x,
+             const double* __restrict__ dx, const double* __restrict__ xm0,
+             const double* __restrict__ dxm, unsigned long long* alpha_bits, long long* counters) {
+    const int n = min(*L.n, L.cap);
+    double best = 1.0;
+    long long n_pt = 0, n_ee = 0;
+    int cap_hit = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int2 pr = L.p[i];
+        const int kind = (int)((unsigned)pr.x >> 30);
+        const int32_t a = pr.x & 0x3FFFFFFF, b = pr.y;
+        double X12[12], P12[12];
+        int32_t va[4];          // the four vertices: first primitive's, then the second's
+        bool first_slave;
+        if (kind == 0) {        // slave vertex a, master tri b
+            const int32_t* M = S.mtri + 3 * (int64_t)b;
+            va[0] = a; va[1] = M[0]; va[2] = M[1]; va[3] = M[2];
+            first_slave = true;
+        } else if (kind == 1) { // master vertex a, slave tri b
+            const int32_t* T = S.stri + 3 * (int64_t)b;
+            va[0] = a; va[1] = T[0]; va[2] = T[1]; va[3] = T[2];
+            first_slave = false;
+        } else {                // slave edge a, master edge b
+            va[0] = S.sedge[2 * (int64_t)a]; va[1] = S.sedge[2 * (int64_t)a + 1];
+            va[2] = S.medge[2 * (int64_t)b]; va[3] = S.medge[2 * (int64_t)b + 1];
+            first_slave = true;
+        }
+        const int n_first = kind == 2 ? 2 : 1;
+        for (int q = 0; q < 4; ++q) {
+            const bool slave = (q < n_first) == first_slave;
+            const double* Px = slave ? x : xm0;
+            const double* Pd = slave ? dx : dxm;
+            for (int c = 0; c < 3; ++c) {
+                X12[3 * q + c] = Px[3 * (int64_t)va[q] + c];
+                P12[3 * q + c] = Pd ? Pd[3 * (int64_t)va[q] + c] : 0.0;
+            }
+        }
+        int it;
+        const double r = accd(kind == 2 ? 1 : 0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+        if (kind == 2) ++n_ee; else ++n_pt;
+        cap_hit |= it >= P.ccd_max_iter;
+        best = dmin_(best, r);
+    }
     // warp reductions (min is exact; counters are integers)
     for (int o = 16; o > 0; o >>= 1) {
         best = dmin_(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -857,7 +935,7 @@ k_query_ccd(SceneView S, Params P, QueryList Q, const double* __restrict__ x,
         n_ee += __shfl_xor_sync(0xffffffffu, n_ee, o);
         cap_hit |= __shfl_xor_sync(0xffffffffu, cap_hit, o);
     }
-    if (lane != 0) return;
+    if ((threadIdx.x & 31) != 0) return;
     if (best < 1.0) atomic_min_pos(alpha_bits, best);
     if (n_pt) atomic_add_ll(&counters[0], n_pt);
     if (n_ee) atomic_add_ll(&counters[1], n_ee);
@@ -880,6 +958,7 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     GMCP_CUDA_TRY(c.mbox.ensure(6 * (size_t)c.nmt + 6));
     GMCP_CUDA_TRY(c.mcell.ensure((size_t)c.nmt + 1));
     GMCP_CUDA_TRY(c.mcell_hi.ensure((size_t)c.nmt + 1));
+    GMCP_CUDA_TRY(c.mboxf.ensure(6 * (size_t)c.nmt + 6));
     GMCP_CUDA_TRY(c.cell_cnt.ensure((size_t)c.n_cells + 1));
     GMCP_CUDA_TRY(c.cell_start.ensure((size_t)c.n_cells + 1));
     GMCP_CUDA_TRY(c.scan_tmp.ensure(2 * scan_tmp_size(c.n_cells)));
@@ -887,8 +966,8 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     const int B = 256;
     const unsigned g = (unsigned)((c.nmt + B - 1) / B);
     if (c.nmt > 0) {
-        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mbox.p, c.mcell.p, c.mcell_hi.p,
-                                         c.cell_cnt.p);
+        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mbox.p, c.mboxf.p, c.mcell.p,
+                                         c.mcell_hi.p, c.cell_cnt.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     GMCP_CUDA_TRY(exclusive_scan_i32(c.cell_cnt.p, c.cell_start.p, c.n_cells, c.scan_tmp.p,
@@ -923,13 +1002,17 @@ static QueryList query_list(Ctx& c, bool swept) {
     Q.work = c.misc_i32.p + 5;
     Q.tri = c.qlist_tri.p;
     Q.box = c.qlist_box.p;
+    Q.boxf = c.qlist_boxf.p;
+    Q.vboxf = c.qlist_vboxf.p;
     Q.cell = c.qlist_cell.p;
     return Q;
 }
 
 static cudaError_t ensure_query_list(Ctx& c) {
     GMCP_CUDA_TRY(c.qlist_tri.ensure((size_t)c.ns + 1));
-    GMCP_CUDA_TRY(c.qlist_box.ensure(12 * (size_t)c.ns + 12));
+    GMCP_CUDA_TRY(c.qlist_box.ensure(6 * (size_t)c.ns + 6));
+    GMCP_CUDA_TRY(c.qlist_boxf.ensure(6 * (size_t)c.ns + 6));
+    GMCP_CUDA_TRY(c.qlist_vboxf.ensure(18 * (size_t)c.ns + 18));
     GMCP_CUDA_TRY(c.qlist_cell.ensure(6 * (size_t)c.ns + 6));
     return cudaSuccess;
 }
@@ -956,10 +1039,10 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
     const unsigned g = persistent_blocks(c);
     GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), s));
     if (P.nk == 4)
-        k_query_contact<4><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mcell.p, c.cell_start.p,
+        k_query_contact<4><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mboxf.p, c.mcell.p, c.cell_start.p,
                                              c.cell_ent.p, triE, triG, triS, f32);
     else
-        k_query_contact<16><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mcell.p, c.cell_start.p,
+        k_query_contact<16><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mboxf.p, c.mcell.p, c.cell_start.p,
                                               c.cell_ent.p, triE, triG, triS, f32);
     return cudaGetLastError();
 }
@@ -977,11 +1060,38 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
     k_query_filter<true><<<(unsigned)((c.ns + 255) / 256), 256, 0, c.stream>>>(
         S, c.P, x, dx, c.cell_start.p, Q, nullptr, nullptr, nullptr, nullptr, 0);
     GMCP_CUDA_TRY(cudaGetLastError());
-    GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), c.stream));
-    k_query_ccd<<<persistent_blocks(c), 256, 0, c.stream>>>(S, c.P, Q, x, dx, xm0, dxm, c.mbox.p,
-                                                          c.mcell.p, c.cell_start.p, c.cell_ent.p,
-                                                          alpha_bits, counters);
-    return cudaGetLastError();
+    if (c.cap_ccd == 0) c.cap_ccd = (int32_t)std::min<int64_t>((1 << 16) + c.ns / 4, 1 << 30);
+    if (c.cap_coarse == 0) c.cap_coarse = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);
+    const unsigned flat = (unsigned)(sm_count(c.device) * 8);
+    for (int attempt = 0;; ++attempt) {
+        GMCP_CUDA_TRY(c.ccd_pairs.ensure((size_t)c.cap_ccd));
+        GMCP_CUDA_TRY(c.coarse_pairs.ensure((size_t)c.cap_coarse));
+        // coarse pairs: count in slot 11, needed capacity in slot 14;
+        // primitive pairs: count in slot 10, needed capacity in slot 13
+        PairList C{c.coarse_pairs.p, c.misc_i32.p + 11, c.misc_i32.p + 14, c.cap_coarse};
+        PairList L{c.ccd_pairs.p, c.misc_i32.p + 10, c.misc_i32.p + 13, c.cap_ccd};
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 10, 0, 2 * sizeof(int32_t), c.stream));
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 13, 0, 2 * sizeof(int32_t), c.stream));
+        GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), c.stream));
+        k_query_ccd<<<persistent_blocks(c), 256, 0, c.stream>>>(S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
+                                                              c.cell_ent.p, C);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        k_ccd_exact<<<flat, 256, 0, c.stream>>>(S, Q, C, x, dx, xm0, dxm, c.mbox.p, c.mboxf.p, L);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        k_accd_pairs<<<flat, 256, 0, c.stream>>>(S, c.P, L, x, dx, xm0, dxm, alpha_bits, counters);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        // a lazy caller reads the overflow slots after it synchronises and redoes the pass
+        if (lazy) return cudaSuccess;
+        int32_t need[2] = {0, 0};
+        GMCP_CUDA_TRY(cudaMemcpyAsync(need, c.misc_i32.p + 13, sizeof(need), cudaMemcpyDeviceToHost, c.stream));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        if (need[0] == 0 && need[1] == 0) return cudaSuccess;
+        if (attempt >= 4) return cudaErrorInvalidValue;
+        // the minimum over the pairs seen so far stays valid; the counters restart
+        c.cap_ccd = std::max(c.cap_ccd, need[0]);
+        c.cap_coarse = std::max(c.cap_coarse, need[1]);
+        GMCP_CUDA_TRY(cudaMemsetAsync(counters, 0, 3 * sizeof(long long), c.stream));
+    }
 }
 
 }  // namespace gmcp

@@ -1,7 +1,8 @@
 // contact.cu -- GMCP samples, barrier, gradient / Hessian coefficients,
 // deterministic gathers, and the linearised-gap step bound.
 //
-// Work decomposition (one warp per active slave triangle, persistent grid):
+// Work decomposition (one warp per active slave triangle, persistent grid;
+// the triangles' frames come from a thread-per-triangle pass):
 //   face items  = (sample k, candidate master tri)  -> lane handles items
 //                 lane, lane+32, ...; since 32 is a multiple of the 4 or 16
 //                 samples per triangle, each lane keeps one fixed sample k
@@ -21,13 +22,13 @@
 // the weight for point samples and for edges lying on slave edges) come out
 // identical to a plain IEEE evaluation even on coincident meshes.
 //
-// Precision.  FP64 path: everything in double.  Mixed path: face samples are
-// cast in FP32 in a local frame anchored at the slave triangle's first
-// vertex (coordinate differences formed in FP64, then rounded); a sample
-// whose FP32 gap falls below 1e-2 of the shortest slave edge is recomputed
-// in FP64.  Barrier, gradient and Hessian coefficients are FP32; the energy
-// sum stays FP64; edge and point samples, whose point-sample membership test
-// is not weight-continuous, are always built in FP64.
+// Precision.  FP64 path: everything in double.  Mixed path: every sample is
+// first pre-tested in FP32 in a local frame anchored at the slave
+// triangle's first vertex (coordinate differences formed in FP64, then
+// rounded), with slacks that bound the FP32 error, so only samples that
+// cannot be active are dropped; the survivors are built and decided in FP64
+// exactly as in the FP64 path.  Barrier, gradient and Hessian coefficients
+// are FP32; the energy sum stays FP64.
 #include <cfloat>
 
 #include "gmcp_internal.cuh"
@@ -152,6 +153,22 @@ __device__ __forceinline__ bool face_maybe(V3<float> xs, V3<float> ns, V3<float>
     return min3(b) >= -tol_b;
 }
 
+// FP32 pre-test of edge and point samples.  Their gap is g = n_s . (x_m -
+// x_s) with x_s on the slave plane, i.e. the plane distance n_s . (y - x0)
+// of a point y on the master edge [a, b] (a = b for a vertex), an affine
+// mix of the end values.  False only when that distance is certainly >=
+// eps_max (no sample can be active) or certainly <= 0 at both ends; the FP32
+// error of each end value is below 1e-6 |y - x0|_1, the slack is ten times
+// that plus tol_abs for the rounding of the FP64 gap itself (and eps_max is
+// raised by 1e-6 relative for its own rounding to FP32).
+__device__ __forceinline__ bool plane_gap_maybe(V3<float> ns, V3<float> a, V3<float> b, float eps_max,
+                                                float tol_abs) {
+    const float da = dot(ns, a), db = dot(ns, b);
+    const float tol = 1e-5f * (fabsf(a.x) + fabsf(a.y) + fabsf(a.z) + fabsf(b.x) + fabsf(b.y) + fabsf(b.z)) +
+                      tol_abs;
+    return !(rmin(da, db) > eps_max * (1.0f + 1e-6f) + tol || rmax(da, db) < -tol);
+}
+
 // squared distance between two boxes (0 when they overlap)
 __device__ __forceinline__ double box_dist2(const double* alo, const double* ahi, const double* blo,
                                             const double* bhi) {
@@ -236,13 +253,38 @@ __device__ __forceinline__ void lag_add(double* E8, const double* al, int na, do
 // ---------------------------------------------------------------------------
 // the sample kernel
 // ---------------------------------------------------------------------------
+// Frames of the active slave triangles, one thread per triangle, so that
+// the FP64 square roots and divisions run once per triangle rather than on
+// every lane of the triangle's warp in k_samples: unit normal and area at x,
+// unit normal at rest, and the absolute slack of the FP32 plane-distance
+// pre-tests (which covers the FP64 rounding of gaps formed from coordinates
+// of this magnitude).  frame[8 i ...] belongs to active[i].
+__global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ x,
+                            double* __restrict__ frame) {
+    const int n_active = *C.n_active;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_active; i += gridDim.x * blockDim.x) {
+        const int32_t* Tt = S.stri + 3 * (int64_t)C.active[i];
+        const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
+        const V3<double> X0 = ld3(S.X, Tt[0]), X1 = ld3(S.X, Tt[1]), X2 = ld3(S.X, Tt[2]);
+        const V3<double> cr = cross(x1 - x0, x2 - x0);
+        const double clen = sqrt(dot(cr, cr));
+        const V3<double> cr0 = cross(X1 - X0, X2 - X0);
+        const double clen0 = sqrt(dot(cr0, cr0));
+        double* f = frame + 8 * (int64_t)i;
+        f[0] = cr.x / clen; f[1] = cr.y / clen; f[2] = cr.z / clen;
+        f[3] = 0.5 * clen;
+        f[4] = cr0.x / clen0; f[5] = cr0.y / clen0; f[6] = cr0.z / clen0;
+        f[7] = 1e-12 * (fabs(x0.x) + fabs(x0.y) + fabs(x0.z)) + 1e-30;
+    }
+}
+
 template <int NK, class T, int MODE>
 __global__ void __launch_bounds__(256)
 k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
           const double* __restrict__ xm, double* __restrict__ triE, T* __restrict__ triG,
           T* __restrict__ triS, T* __restrict__ triN, long long* counters,
           const double* __restrict__ dx, const double* __restrict__ dxm,
-          unsigned long long* alpha_bits, LagArgs LG) {
+          unsigned long long* alpha_bits, LagArgs LG, const double* __restrict__ frame) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
@@ -256,18 +298,18 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
 #pragma unroll
     for (int j = 0; j < 8; ++j) al8[j] = (MODE == MODE_LAGGED && j < LG.na) ? LG.alphas[j] : 0.0;
     (void)warp; (void)nwarps;
+    const bool pre = P.precision == IPC_PREC_MIXED;   // FP32 pre-tests (exact decisions unchanged)
     for (int i = next_item(C.work, lane); i < n_active; i = next_item(C.work, lane)) {
         const int64_t t = C.active[i];
         const int32_t* Tt = S.stri + 3 * t;
         const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
         const V3<double> X0 = ld3(S.X, Tt[0]), X1 = ld3(S.X, Tt[1]), X2 = ld3(S.X, Tt[2]);
-        const V3<double> cr = cross(x1 - x0, x2 - x0);
-        const double clen = sqrt(dot(cr, cr));
-        const V3<double> ns = {cr.x / clen, cr.y / clen, cr.z / clen};
-        const double As = 0.5 * clen;
-        const V3<double> cr0 = cross(X1 - X0, X2 - X0);
-        const double clen0 = sqrt(dot(cr0, cr0));
-        const V3<double> ns0 = {cr0.x / clen0, cr0.y / clen0, cr0.z / clen0};
+        const double* fr = frame + 8 * (int64_t)i;
+        const V3<double> ns = {fr[0], fr[1], fr[2]};
+        const double As = fr[3];
+        const V3<double> ns0 = {fr[4], fr[5], fr[6]};
+        const float tol_abs = (float)fr[7];
+        const V3<float> ns_f = tof(ns);
         const double* sb = S.srest_box + 6 * t;
         const int32_t* cnt = C.count + 4 * t;
         const int nf = min(cnt[0], C.cap_f), ne = min(cnt[1], C.cap_e), np = min(cnt[2], C.cap_p);
@@ -285,7 +327,6 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
         {
             const V3<double> xs = interp(beta_k, x0, x1, x2);
             const V3<float> xs_rel = tof(xs - x0);
-            const V3<float> ns_f = tof(ns);
             const double ds_face = want_dg ? dot(ns, interp(beta_k, dx0, dx1, dx2)) : 0.0;
             const int32_t* Lf = C.face + t * C.cap_f;
             for (int it = lane; it < nf * NK; it += 32) {
@@ -293,8 +334,7 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 const int32_t* M = S.mtri + 3 * (int64_t)m;
                 const V3<double> y0 = ld3(xm, M[0]), y1 = ld3(xm, M[1]), y2 = ld3(xm, M[2]);
                 ++cnt_eval;
-                if (sizeof(T) == 4 &&
-                    !face_maybe(xs_rel, ns_f, tof(y0 - x0), tof(y1 - x0), tof(y2 - x0), (float)eps_max))
+                if (pre && !face_maybe(xs_rel, ns_f, tof(y0 - x0), tof(y1 - x0), tof(y2 - x0), (float)eps_max))
                     continue;
                 double g, bm[3];
                 if (!face_geom<double>(xs, ns, y0, y1, y2, g, bm)) continue;
@@ -327,9 +367,10 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 const int32_t me = Le[it >> 1];
                 const int q = it & 1;
                 const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
+                const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
+                if (pre && !plane_gap_maybe(ns_f, tof(ya - x0), tof(yb - x0), (float)eps_max, tol_abs)) continue;
                 const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
                 if (!any_facing(S, xm, S.me_tri + a0, a1 - a0, ns)) continue;
-                const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
                 double bA[3], bB[3];
                 bary(ya, x0, x1, x2, bA);
                 bary(yb, x0, x1, x2, bB);
@@ -384,9 +425,13 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
             const int32_t* Lp = C.point + t * C.cap_p;
             for (int it = lane; it < np; it += 32) {
                 const int32_t u = Lp[it];
+                const V3<double> y = ld3(xm, u);
+                if (pre) {
+                    const V3<float> d = tof(y - x0);
+                    if (!plane_gap_maybe(ns_f, d, d, (float)eps_max, tol_abs)) continue;
+                }
                 const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
                 if (!any_facing(S, xm, S.mv_tri + a0, a1 - a0, ns)) continue;
-                const V3<double> y = ld3(xm, u);
                 double bs[3];
                 bary(y, x0, x1, x2, bs);
                 if (!(min3(bs) >= 0.0)) continue;
@@ -547,9 +592,13 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
                            unsigned long long* alpha_bits, LagArgs LG = LagArgs()) {
     const int threads = 256;
     const int blocks = sm_count(c.device) * c.tune_samples_bpsm;
+    GMCP_CUDA_TRY(c.tri_frame.ensure(8 * (size_t)c.ns + 8));
+    k_tri_frame<<<sm_count(c.device) * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
     k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
-        c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG);
+        c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG,
+        c.tri_frame.p);
     return cudaGetLastError();
 }
 

@@ -289,6 +289,11 @@ struct Ctx {
     DBuf<int4> mcell_hi;                        // [nmt] highest cell (x, y, z)
     DBuf<int32_t> qlist_tri, qlist_cell;        // slave tris whose query meets a non-empty cell
     DBuf<double> qlist_box;
+    DBuf<float> qlist_boxf, mboxf;              // conservative FP32 boxes (query list, master tris)
+    DBuf<int2> ccd_pairs;                       // primitive pairs for ACCD
+    DBuf<int2> coarse_pairs;                    // (swept query entry, master) pairs
+    DBuf<float> qlist_vboxf;                    // swept query: corner boxes
+    int32_t cap_ccd = 0, cap_coarse = 0;
     DBuf<int32_t> cell_cnt, cell_start, cell_ent;
     DBuf<int32_t> scan_tmp;
     DBuf<int32_t> cand_face, cand_edge, cand_point, cand_count, active, misc_i32;
@@ -296,6 +301,7 @@ struct Ctx {
 
     // per-call sample outputs
     DBuf<double> tri_E;
+    DBuf<double> tri_frame;                     // [n_active][8] frames of the active slave tris
     DBuf<double> tri_G64, tri_S64, tri_n64;
     DBuf<float> tri_G32, tri_S32, tri_n32;
     DBuf<double> cb_val64;
