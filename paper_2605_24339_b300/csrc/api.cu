@@ -110,7 +110,7 @@ cudaError_t run_candidates(Ctx& c, const double* x, const double* xm, bool lazy)
     if (lazy) {
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 12, 0, 4 * sizeof(int32_t), c.stream));
         GMCP_CUDA_TRY(bp_build_grid(c, xm, nullptr, false, true));
-        return bp_query_contact(c, x, xm);
+        return bp_query_contact(c, x, xm, true);
     }
     for (int attempt = 0; attempt < 6; ++attempt) {
         GMCP_CUDA_TRY(bp_build_grid(c, xm, nullptr, false));
@@ -171,6 +171,24 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
         GMCP_CUDA_TRY(cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
     }
     GMCP_CUDA_TRY(run_candidates(c, A.x, A.xm0, A.lazy));
+    // With a static master the swept query reads the same grid and nothing
+    // else of the contact evaluation: it runs on a second stream, forked
+    // after the grid build and joined before the results are read (the
+    // profiler keeps one stream so that its sections stay separate).
+    const bool fork = A.dx && !dxm && A.lazy && !c.prof.on;
+    if (fork) {
+        if (!c.ccd_stream) GMCP_CUDA_TRY(cudaStreamCreateWithFlags(&c.ccd_stream, cudaStreamNonBlocking));
+        if (!c.ev_fork) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_fork, cudaEventDisableTiming));
+        if (!c.ev_join) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
+        GMCP_CUDA_TRY(cudaEventRecord(c.ev_fork, c.stream));
+        GMCP_CUDA_TRY(cudaStreamWaitEvent(c.ccd_stream, c.ev_fork, 0));
+        cudaStream_t main = c.stream;
+        c.stream = c.ccd_stream;
+        const cudaError_t e = bp_ccd_accd(c, A.x, A.dx, A.xm0, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8, true, true);
+        c.stream = main;
+        GMCP_CUDA_TRY(e);
+        GMCP_CUDA_TRY(cudaEventRecord(c.ev_join, c.ccd_stream));
+    }
     long long* ctr = nullptr;
     if (A.counts) {
         GMCP_CUDA_TRY(cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
@@ -178,7 +196,9 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
     }
     GMCP_CUDA_TRY(contact_eval(c, A.x, A.xm0, A.edev, A.grad, A.hess, ctr, A.dx, dxm,
                                A.dx ? c.u64_tmp.p : nullptr));
-    if (A.dx)
+    if (fork)
+        GMCP_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.ev_join, 0));
+    else if (A.dx)
         GMCP_CUDA_TRY(bp_ccd_accd(c, A.x, A.dx, A.xm0, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8, true, A.lazy));
     if (!A.lazy) return cudaSuccess;
     if (A.host_energy)
@@ -197,7 +217,7 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
 // capacity flags of the last lazy pass (valid after a synchronisation)
 bool pass_overflowed(const Ctx& c) {
     const int32_t* f = c.pin->flags;
-    return f[1] || f[2] || f[3] || f[12] || f[13] || f[14];
+    return f[1] || f[2] || f[3] || f[12] || f[13] || f[14] || f[15];
 }
 
 cudaError_t grow_after_overflow(Ctx& c) {
@@ -209,7 +229,11 @@ cudaError_t grow_after_overflow(Ctx& c) {
         GMCP_CUDA_TRY(c.ccd_pairs.ensure((size_t)c.cap_ccd));
     }
     if (f[14]) {
-        c.cap_coarse = std::max(c.cap_coarse, f[14]);
+        c.cap_coarse_swept = std::max(c.cap_coarse_swept, f[14]);
+        GMCP_CUDA_TRY(c.coarse_swept.ensure((size_t)c.cap_coarse_swept));
+    }
+    if (f[15]) {
+        c.cap_coarse = std::max(c.cap_coarse, f[15]);
         GMCP_CUDA_TRY(c.coarse_pairs.ensure((size_t)c.cap_coarse));
     }
     return cudaSuccess;
@@ -226,9 +250,12 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             // capture and replay must not leave a stale address in the graph
             (uintptr_t)c.red_tmp.p, (uintptr_t)c.red_tmp.n, (uintptr_t)c.cell_ent.p, (uintptr_t)c.cand_face.p,
             (uintptr_t)c.cand_edge.p, (uintptr_t)c.cand_point.p, (uintptr_t)c.cand_count.p, (uintptr_t)c.active.p,
-            (uintptr_t)c.qlist_tri.p, (uintptr_t)c.qlist_box.p, (uintptr_t)c.qlist_boxf.p, (uintptr_t)c.mboxf.p,
-            (uintptr_t)c.ccd_pairs.p, (uintptr_t)c.cap_ccd, (uintptr_t)c.coarse_pairs.p,
-            (uintptr_t)c.cap_coarse, (uintptr_t)c.qlist_vboxf.p, (uintptr_t)c.qlist_cell.p, (uintptr_t)c.mbox.p,
+            (uintptr_t)c.qcontact.tri.p, (uintptr_t)c.qcontact.box.p, (uintptr_t)c.qcontact.boxf.p,
+            (uintptr_t)c.qcontact.vboxf.p, (uintptr_t)c.qcontact.cell.p, (uintptr_t)c.qswept.tri.p,
+            (uintptr_t)c.qswept.boxf.p, (uintptr_t)c.qswept.vboxf.p, (uintptr_t)c.qswept.cell.p,
+            (uintptr_t)c.mboxf.p, (uintptr_t)c.ccd_pairs.p, (uintptr_t)c.cap_ccd, (uintptr_t)c.coarse_pairs.p,
+            (uintptr_t)c.cap_coarse, (uintptr_t)c.coarse_swept.p, (uintptr_t)c.cap_coarse_swept,
+            (uintptr_t)c.ccd_stream, (uintptr_t)c.mbox.p,
             (uintptr_t)c.mcell.p, (uintptr_t)c.mcell_hi.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
             (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_frame.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
             (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,
@@ -871,6 +898,9 @@ void ipc_destroy(ipc_ctx* ctx) {
     c.cp_graph.reset();
     c.pcg_graph.reset();
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+    if (c.ccd_stream) cudaStreamDestroy(c.ccd_stream);
+    if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+    if (c.ev_join) cudaEventDestroy(c.ev_join);
     if (c.pin) cudaFreeHost(c.pin);
     delete ctx;   // every DBuf member frees its device memory
 }

@@ -26,6 +26,7 @@
 // (the lowest-numbered adjacent triangle), whose box contains theirs.
 #include <algorithm>
 #include <cfloat>
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -173,6 +174,8 @@ __device__ __forceinline__ void load3(const double* p, int64_t i, double* o) {
 // face-rule barycentrics per level (index L-1), filled at context creation
 // with the exact quotients (3i+1)/(3n), (3i+2)/(3n) of the fixed rule
 __constant__ double c_rule[2][16][3];
+// FP32 brackets of the same values: [l][k][0..2] <= c_rule[l][k][0..2] <= [l][k][3..5]
+__constant__ float c_rule_f[2][16][6];
 
 // ---------------------------------------------------------------------------
 // grid build
@@ -274,18 +277,10 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
-// warp-aggregated append of v (when pred) to list L with capacity cap
-__device__ __forceinline__ void warp_append(bool pred, int32_t v, int32_t* L, int cap, int& n) {
-    const unsigned mask = __ballot_sync(0xffffffffu, pred);
-    if (pred) {
-        const int pos = n + __popc(mask & lanemask_lt());
-        if (pos < cap) L[pos] = v;
-    }
-    n += __popc(mask);
-}
-
-// ascending sort of the first n entries of L by the warp (n <= 32: bitonic
-// network in registers; longer lists: lane 0 insertion sort)
+// ascending sort of the first n entries of L by the warp (entries are
+// distinct ids).  n <= 32: bitonic network in registers; n <= 128: each
+// lane ranks up to four entries against all n and stores them at their
+// ranks; longer lists (rare): lane 0 insertion sort.
 __device__ void warp_sort(int32_t* L, int n, int lane) {
     if (n <= 1) return;
     if (n <= 32) {
@@ -303,6 +298,24 @@ __device__ void warp_sort(int32_t* L, int n, int lane) {
         return;
     }
     __syncwarp();
+    if (n <= 128) {
+        int32_t v[4];
+        int r[4];
+        for (int q = 0; q < 4; ++q) {
+            const int j = lane + 32 * q;
+            v[q] = j < n ? L[j] : 0;
+            r[q] = 0;
+        }
+        for (int i = 0; i < n; ++i) {
+            const int32_t w = L[i];
+            for (int q = 0; q < 4; ++q) r[q] += w < v[q];
+        }
+        __syncwarp();
+        for (int q = 0; q < 4; ++q)
+            if (lane + 32 * q < n) L[r[q]] = v[q];
+        __syncwarp();
+        return;
+    }
     if (lane == 0) sort_small(L, n);
     __syncwarp();
 }
@@ -317,7 +330,7 @@ struct QueryList {
     int32_t* n;        // scalar
     int32_t* tri;      // [ns]
     float* boxf;       // [ns][6]: query box lo/hi (conservative FP32: contains the exact grown box)
-    float* vboxf;      // [ns][3][6]: swept query only, conservative FP32 box of each corner
+    float* vboxf;      // [ns][3][6]: conservative FP32 box of each corner (swept: of its motion)
     double* box;       // [ns][6]: exact slave tri box lo/hi (contact query only)
     int32_t* cell;     // [ns][6]: first and last cell (x, y, z)
     int32_t* work;     // work counter of the persistent query (reset before each launch)
@@ -343,7 +356,7 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
     const double grow = SWEPT ? S.margin : P.dhat + S.margin;
     const float grow_up = __double2float_ru(grow);
     float flo[3], fhi[3], mag[3];
-    float vb[3][6];        // swept: conservative FP32 box of each corner (as swept_vert_f)
+    float vb[3][6];        // conservative FP32 box of each corner (swept: as swept_vert_f)
     for (int c = 0; c < 3; ++c) {
         float lo_c = INFINITY, hi_c = -INFINITY, m_c = grow_up;
         for (int a = 0; a < 3; ++a) {
@@ -353,8 +366,8 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
                 const float dl = lo_f32(d[a][c]), dh = hi_f32(d[a][c]);
                 m_c += fmaxf(fabsf(dl), fabsf(dh));
                 pl = fminf(pl, __fadd_rd(pl, dl)); ph = fmaxf(ph, __fadd_ru(ph, dh));
-                vb[a][c] = pl; vb[a][3 + c] = ph;
             }
+            vb[a][c] = pl; vb[a][3 + c] = ph;
             lo_c = fminf(lo_c, pl); hi_c = fmaxf(hi_c, ph);
         }
         flo[c] = __fsub_rd(lo_c, grow_up); fhi[c] = __fadd_ru(hi_c, grow_up); mag[c] = m_c;
@@ -368,16 +381,20 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
             const int64_t c0 = cell_id(S, e, ca.x, iy, iz);
             any = start[c0 + (cb.x - ca.x) + 1] > start[c0];   // cells of a row are contiguous
         }
+    if (!SWEPT) {
+        // the candidate counts start at zero (the exact tests append to them)
+        int32_t* cnt = count + 4 * t;
+        cnt[0] = 0; cnt[1] = 0; cnt[2] = 0; cnt[3] = 0;
+    }
     if (any) {
         const int idx = atomicAdd(Q.n, 1);
         Q.tri[idx] = (int32_t)t;
         float* bf = Q.boxf + 6 * (int64_t)idx;
         for (int c = 0; c < 3; ++c) { bf[c] = flo[c]; bf[3 + c] = fhi[c]; }
-        if (SWEPT) {
-            float* w = Q.vboxf + 18 * (int64_t)idx;
-            for (int a = 0; a < 3; ++a)
-                for (int q = 0; q < 6; ++q) w[6 * a + q] = vb[a][q];
-        } else {
+        float* w = Q.vboxf + 18 * (int64_t)idx;
+        for (int a = 0; a < 3; ++a)
+            for (int q = 0; q < 6; ++q) w[6 * a + q] = vb[a][q];
+        if (!SWEPT) {
             // exact slave box for the edge and point tests
             double* b = Q.box + 6 * (int64_t)idx;
             for (int c = 0; c < 3; ++c) {
@@ -388,8 +405,6 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
         int32_t* cl = Q.cell + 6 * (int64_t)idx;
         cl[0] = ca.x; cl[1] = ca.y; cl[2] = ca.z; cl[3] = cb.x; cl[4] = cb.y; cl[5] = cb.z;
     } else if (!SWEPT) {
-        int32_t* cnt = count + 4 * t;
-        cnt[0] = 0; cnt[1] = 0; cnt[2] = 0; cnt[3] = 0;
         if (triE) {
             triE[t] = 0.0;
             if (out_f32) {
@@ -449,56 +464,122 @@ struct RowWalk {
     __device__ void next() { kb += 32; skip_empty(); }
 };
 
-// Per-warp queue of the masters that passed the coarse box test: the exact
-// tests then run 32 masters at a time (every lane busy) instead of once per
-// 32 cell entries.
-constexpr int kQueue = 64;
+// Primitive or (triangle, master) pairs passed between the launches of a
+// query: p[i] = (x, y), n = pairs emitted (may exceed cap), overflow = the
+// capacity needed when it does.
+struct PairList {
+    int2* p;
+    int32_t* n;
+    int32_t* overflow;
+    int32_t cap;
+};
 
-// contact candidate query: persistent warps over the filtered slave
-// triangles.  Per master: the coarse test (query box = slave box grown by
-// dhat + margin) against the master box, then the exact tests of the face,
-// edge and point kinds; every list is sorted at the end.
-template <int NK>
-__global__ void __launch_bounds__(256, 3)
-k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __restrict__ x,
-                const double* __restrict__ xm, const double* __restrict__ mbox,
-                const float* __restrict__ mboxf, const int4* __restrict__ mcell,
-                const int32_t* __restrict__ start,
-                const int32_t* __restrict__ ent, double* __restrict__ triE,
-                void* __restrict__ triG, void* __restrict__ triS, int out_f32) {
-    __shared__ int32_t s_queue[8][kQueue];
+// Walk of the cell entries of the filtered slave triangles (warp per
+// triangle): emits (query-list index, master) for every entry that passes
+// the coarse test on conservative FP32 boxes and the first-common-cell
+// rule.  Shared by the contact and the swept query.
+__global__ void __launch_bounds__(256)
+k_query_walk(SceneView S, QueryList Q, const float* __restrict__ mboxf, const int4* __restrict__ mcell,
+             const int32_t* __restrict__ start, const int32_t* __restrict__ ent, PairList L) {
     const int lane = threadIdx.x & 31;
-    int32_t* queue = s_queue[threadIdx.x >> 5];
     const int n_list = *Q.n;
-    const double eps = P.dhat;
-    const double (*rule)[3] = c_rule[P.L - 1];
     for (int li = next_item(Q.work, lane); li < n_list; li = next_item(Q.work, lane)) {
-    const int64_t t = Q.tri[li];
-    const int32_t* T = S.stri + 3 * t;
-    double x0[3], x1[3], x2[3];
-    load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
-    const double* qb = Q.box + 6 * (int64_t)li;
-    const double slo[3] = {qb[0], qb[1], qb[2]}, shi[3] = {qb[3], qb[4], qb[5]};
-    const float* qf = Q.boxf + 6 * (int64_t)li;
-    const float qlo[3] = {qf[0], qf[1], qf[2]}, qhi[3] = {qf[3], qf[4], qf[5]};
-    const int32_t* ql = Q.cell + 6 * (int64_t)li;
-    const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
-    const int e = S.stri_env[t];
-    int nf = 0, ne = 0, np = 0;
-    int32_t* Lf = C.face + t * C.cap_f;
-    int32_t* Le = C.edge + t * C.cap_e;
-    int32_t* Lp = C.point + t * C.cap_p;
+        const float* qf = Q.boxf + 6 * (int64_t)li;
+        const float qlo[3] = {qf[0], qf[1], qf[2]}, qhi[3] = {qf[3], qf[4], qf[5]};
+        const int32_t* ql = Q.cell + 6 * (int64_t)li;
+        const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
+        const int e = S.stri_env[Q.tri[li]];
+        for (RowWalk W(S, start, e, ca, cb); W.more(); W.next()) {
+            const int k = W.kb + lane;
+            bool take = false;
+            int32_t m = 0;
+            if (k < W.k1) {
+                m = ent[k];
+                const float* B = mboxf + 6 * (int64_t)m;
+                take = overlap_keep(qlo, qhi, B, B + 3) &&
+                       first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, take);
+            if (bal == 0u) continue;
+            int base = 0;
+            if (lane == 0) base = atomicAdd(L.n, __popc(bal));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (take) {
+                const int pos = base + __popc(bal & lanemask_lt());
+                if (pos < L.cap) L.p[pos] = make_int2(li, m);
+                else atomicMax(L.overflow, pos + 1);
+            }
+        }
+    }
+}
 
-    // exact tests of the first n queued masters, one per lane
-    auto run_exact = [&](int n) {
-        const bool have = lane < n;
-        const int32_t m = have ? queue[lane] : 0;
-        // face: some sample ((b0 x0 + b1 x1) + b2 x2) inside the master box grown by eps
-        bool hit = false;
-        if (have) {
+// append v to the list of kind q of slave tri t (counts may exceed the
+// capacity; the finishing pass flags that)
+__device__ __forceinline__ void cand_append(const CandView& C, int64_t t, int q, int32_t v) {
+    const int pos = atomicAdd(&C.count[4 * t + q], 1);
+    const int cap = q == 0 ? C.cap_f : (q == 1 ? C.cap_e : C.cap_p);
+    int32_t* L = q == 0 ? C.face : (q == 1 ? C.edge : C.point);
+    if (pos < cap) L[t * cap + pos] = v;
+}
+
+// Exact candidate tests of one (filtered slave triangle, master triangle)
+// pair: face (some sample ((b0 x0 + b1 x1) + b2 x2) inside the master box
+// grown by eps), owned master edges and vertices (slave tri box vs their
+// boxes grown by eps; FP32 pre-test on conservative boxes first).
+template <int NK>
+__global__ void __launch_bounds__(256)
+k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
+                const double* __restrict__ x, const double* __restrict__ xm,
+                const double* __restrict__ mbox, const float* __restrict__ mboxf) {
+    const int n = min(*W.n, W.cap);
+    const double eps = P.dhat;
+    // eps rounded up, with a relative slack that covers the FP64 rounding of
+    // the grown master box
+    const float eps_up = __double2float_ru(eps * (1.0 + 0x1p-20));
+    const double (*rule)[3] = c_rule[P.L - 1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int2 pr = W.p[i];
+        const int li = pr.x;
+        const int32_t m = pr.y;
+        // everything that depends only on the pair, loaded up front
+        const int64_t t = Q.tri[li];
+        const float* qf = Q.boxf + 6 * (int64_t)li;      // contains the slave box grown by eps
+        const float* vb = Q.vboxf + 18 * (int64_t)li;
+        const float* Bf = mboxf + 6 * (int64_t)m;
+        int32_t own_e[3], own_v[3];
+        for (int j = 0; j < 3; ++j) {
+            own_e[j] = S.mtri_own_edge[3 * (int64_t)m + j];
+            own_v[j] = S.mtri_own_vert[3 * (int64_t)m + j];
+        }
+        const int32_t* T = S.stri + 3 * t;
+        // face: FP32 pre-test on conservative sample bounds, then the exact test
+        bool maybe = false;
+        {
+            float L[3], H[3];
+            for (int c = 0; c < 3; ++c) { L[c] = __fsub_rd(Bf[c], eps_up); H[c] = __fadd_ru(Bf[3 + c], eps_up); }
+            const float (*rf)[6] = c_rule_f[P.L - 1];
+            for (int q = 0; q < NK && !maybe; ++q) {
+                bool in = true;
+                for (int c = 0; c < 3 && in; ++c) {
+                    // bounds of ((b0 x0 + b1 x1) + b2 x2) with b >= 0
+                    float lo = 0.0f, hi = 0.0f;
+                    for (int a = 0; a < 3; ++a) {
+                        const float xl = vb[6 * a + c], xh = vb[6 * a + 3 + c];
+                        lo = __fadd_rd(lo, __fmul_rd(xl >= 0.0f ? rf[q][a] : rf[q][3 + a], xl));
+                        hi = __fadd_ru(hi, __fmul_ru(xh >= 0.0f ? rf[q][3 + a] : rf[q][a], xh));
+                    }
+                    in = !(hi < L[c] || lo > H[c]);
+                }
+                maybe = in;
+            }
+        }
+        if (maybe) {
+            double x0[3], x1[3], x2[3];
+            load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
             const double* B = mbox + 6 * (int64_t)m;
             const double l0 = B[0] - eps, l1 = B[1] - eps, l2 = B[2] - eps;
             const double h0 = B[3] + eps, h1 = B[4] + eps, h2 = B[5] + eps;
+            bool hit = false;
             for (int q = 0; q < NK && !hit; ++q) {
                 const double b0 = rule[q][0], b1 = rule[q][1], b2 = rule[q][2];
                 const double sxq = b0 * x0[0] + b1 * x1[0] + b2 * x2[0];
@@ -508,98 +589,83 @@ k_query_contact(SceneView S, Params P, CandView C, QueryList Q, const double* __
                 const double szq = b0 * x0[2] + b1 * x1[2] + b2 * x2[2];
                 hit = l2 <= szq && szq <= h2;
             }
+            if (hit) cand_append(C, t, 0, m);
         }
-        warp_append(hit, m, Lf, C.cap_f, nf);
-        // owned edges and vertices: slave tri box vs their boxes grown by eps
+        const double* qb = Q.box + 6 * (int64_t)li;       // exact slave box
         for (int j = 0; j < 3; ++j) {
-            bool ok = false;
-            int32_t me = -1;
-            if (have) {
-                me = S.mtri_own_edge[3 * (int64_t)m + j];
-                if (me >= 0) {
-                    double ya[3], yb[3];
-                    load3(xm, S.medge[2 * (int64_t)me], ya);
-                    load3(xm, S.medge[2 * (int64_t)me + 1], yb);
-                    ok = true;
-                    for (int c = 0; c < 3 && ok; ++c) {
-                        const double lo = dmin_(ya[c], yb[c]) - eps, hi = dmax_(ya[c], yb[c]) + eps;
-                        ok = slo[c] <= hi && lo <= shi[c];
-                    }
-                }
+            const int32_t me = own_e[j];
+            if (me < 0) continue;
+            const int32_t ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
+            double ya[3], yb[3];
+            load3(xm, ia, ya);
+            load3(xm, ib, yb);
+            float flo[3], fhi[3];
+            for (int c = 0; c < 3; ++c) {
+                flo[c] = fminf(lo_f32(ya[c]), lo_f32(yb[c]));
+                fhi[c] = fmaxf(hi_f32(ya[c]), hi_f32(yb[c]));
             }
-            warp_append(ok, me, Le, C.cap_e, ne);
+            if (!overlap_keep(qf, qf + 3, flo, fhi)) continue;
+            bool ok = true;
+            for (int c = 0; c < 3 && ok; ++c) {
+                const double lo = dmin_(ya[c], yb[c]) - eps, hi = dmax_(ya[c], yb[c]) + eps;
+                ok = qb[c] <= hi && lo <= qb[3 + c];
+            }
+            if (ok) cand_append(C, t, 1, me);
         }
         for (int j = 0; j < 3; ++j) {
-            bool ok = false;
-            int32_t u = -1;
-            if (have) {
-                u = S.mtri_own_vert[3 * (int64_t)m + j];
-                if (u >= 0) {
-                    double y[3];
-                    load3(xm, u, y);
-                    ok = true;
-                    for (int c = 0; c < 3 && ok; ++c) ok = slo[c] <= y[c] + eps && y[c] - eps <= shi[c];
-                }
-            }
-            warp_append(ok, u, Lp, C.cap_p, np);
+            const int32_t u = own_v[j];
+            if (u < 0) continue;
+            double y[3];
+            load3(xm, u, y);
+            float flo[3], fhi[3];
+            for (int c = 0; c < 3; ++c) { flo[c] = lo_f32(y[c]); fhi[c] = hi_f32(y[c]); }
+            if (!overlap_keep(qf, qf + 3, flo, fhi)) continue;
+            bool ok = true;
+            for (int c = 0; c < 3 && ok; ++c) ok = qb[c] <= y[c] + eps && y[c] - eps <= qb[3 + c];
+            if (ok) cand_append(C, t, 2, u);
         }
-    };
+    }
+}
 
-    RowWalk W(S, start, e, ca, cb);
-    for (int nq = 0;;) {
-        // queue coarse-test survivors until 32 are waiting or the rows are done
-        while (nq < 32 && W.more()) {
-            const int k = W.kb + lane;
-            bool take = false;
-            int32_t m = 0;
-            if (k < W.k1) {
-                // coarse test on conservative FP32 boxes (the exact tests decide),
-                // then the first-common-cell rule
-                m = ent[k];
-                const float* B = mboxf + 6 * (int64_t)m;
-                take = overlap_keep(qlo, qhi, B, B + 3) &&
-                       first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
+// Finishing pass of the contact query (warp per filtered slave triangle):
+// sort each list (the order of the appends depends on scheduling), flag
+// overflowing lists, add the triangle to the active list or zero its
+// outputs.
+__global__ void __launch_bounds__(256)
+k_contact_finish(CandView C, QueryList Q, double* __restrict__ triE, void* __restrict__ triG,
+                 void* __restrict__ triS, int out_f32) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int n_list = *Q.n;
+    for (int li = warp; li < n_list; li += nwarps) {
+        const int64_t t = Q.tri[li];
+        int32_t* cnt = C.count + 4 * t;
+        const int nf = cnt[0], ne = cnt[1], np = cnt[2];
+        warp_sort(C.face + t * C.cap_f, min(nf, C.cap_f), lane);
+        warp_sort(C.edge + t * C.cap_e, min(ne, C.cap_e), lane);
+        warp_sort(C.point + t * C.cap_p, min(np, C.cap_p), lane);
+        if (lane != 0) continue;
+        if (nf > C.cap_f) atomicMax(&C.overflow[0], nf);
+        if (ne > C.cap_e) atomicMax(&C.overflow[1], ne);
+        if (np > C.cap_p) atomicMax(&C.overflow[2], np);
+        if (nf + ne + np > 0) {
+            const int idx = atomicAdd(C.n_active, 1);
+            C.active[idx] = (int32_t)t;
+        } else if (triE) {
+            // no candidates: this triangle contributes nothing to the gathers
+            triE[t] = 0.0;
+            if (out_f32) {
+                float* G = (float*)triG; float* Sm = (float*)triS;
+                for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0f;
+                for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0f;
+            } else {
+                double* G = (double*)triG; double* Sm = (double*)triS;
+                for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0;
+                for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, take);
-            if (take) queue[nq + __popc(bal & lanemask_lt())] = m;
-            nq += __popc(bal);
-            W.next();
-        }
-        if (nq == 0) break;
-        __syncwarp();
-        const int n = min(nq, 32);
-        run_exact(n);
-        __syncwarp();
-        if (lane < nq - n) queue[lane] = queue[n + lane];
-        nq -= n;
-        __syncwarp();
-    }
-    warp_sort(Lf, min(nf, C.cap_f), lane);
-    warp_sort(Le, min(ne, C.cap_e), lane);
-    warp_sort(Lp, min(np, C.cap_p), lane);
-    if (lane != 0) continue;
-    int32_t* cnt = C.count + 4 * t;
-    cnt[0] = nf; cnt[1] = ne; cnt[2] = np; cnt[3] = 0;
-    if (nf > C.cap_f) atomicMax(&C.overflow[0], nf);
-    if (ne > C.cap_e) atomicMax(&C.overflow[1], ne);
-    if (np > C.cap_p) atomicMax(&C.overflow[2], np);
-    if (nf + ne + np > 0) {
-        const int idx = atomicAdd(C.n_active, 1);
-        C.active[idx] = (int32_t)t;
-    } else if (triE) {
-        // no candidates: this triangle contributes nothing to the gathers
-        triE[t] = 0.0;
-        if (out_f32) {
-            float* G = (float*)triG; float* Sm = (float*)triS;
-            for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0f;
-            for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0f;
-        } else {
-            double* G = (double*)triG; double* Sm = (double*)triS;
-            for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0;
-            for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0;
         }
     }
-    }  // list loop
 }
 
 // ---------------------------------------------------------------------------
@@ -737,16 +803,10 @@ __device__ __forceinline__ void atomic_min_pos(unsigned long long* dst, double v
     atomicMin(dst, (unsigned long long)__double_as_longlong(v));
 }
 
-// Primitive pairs that ACCD must test, emitted by k_query_ccd and consumed
-// by k_accd_pairs: x = first id | kind << 30, y = second id.  Kinds:
-// 0 slave vertex / master tri, 1 master vertex / slave tri, 2 slave edge /
-// master edge.
-struct PairList {
-    int2* p;
-    int32_t* n;          // pairs emitted (may exceed cap)
-    int32_t* overflow;   // needed capacity when it does
-    int32_t cap;
-};
+// Primitive pairs that ACCD must test (PairList), emitted by k_ccd_exact
+// and consumed by k_accd_pairs: x = first id | kind << 30, y = second id.
+// Kinds: 0 slave vertex / master tri, 1 master vertex / slave tri, 2 slave
+// edge / master edge.
 __device__ __forceinline__ void emit_pair(const PairList& L, int kind, int32_t a, int32_t b) {
     const int pos = atomicAdd(L.n, 1);
     if (pos < L.cap) L.p[pos] = make_int2(a | (kind << 30), b);
@@ -754,47 +814,13 @@ __device__ __forceinline__ void emit_pair(const PairList& L, int kind, int32_t a
 }
 
 // Swept query, in three launches so that each stays light: the walk over
-// cell entries (k_query_ccd, warp per filtered slave triangle) emits the
-// (triangle, master) pairs that pass the coarse test on conservative FP32
-// boxes and the first-common-cell rule; k_ccd_exact (thread per such pair)
-// tests the owned primitives, first on FP32 boxes, then, for the pairs that
-// pass, on their exact FP64 boxes, and emits the primitive pairs that
-// overlap; k_accd_pairs runs ACCD on those.  The primitive pairs are exactly
-// those of the plain FP64 box tests.
-__global__ void __launch_bounds__(256)
-k_query_ccd(SceneView S, QueryList Q, const float* __restrict__ mboxf, const int4* __restrict__ mcell,
-            const int32_t* __restrict__ start, const int32_t* __restrict__ ent, PairList L) {
-    const int lane = threadIdx.x & 31;
-    const int n_list = *Q.n;
-    for (int li = next_item(Q.work, lane); li < n_list; li = next_item(Q.work, lane)) {
-        const float* qf = Q.boxf + 6 * (int64_t)li;
-        const float qlo[3] = {qf[0], qf[1], qf[2]}, qhi[3] = {qf[3], qf[4], qf[5]};
-        const int32_t* ql = Q.cell + 6 * (int64_t)li;
-        const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
-        const int e = S.stri_env[Q.tri[li]];
-        for (RowWalk W(S, start, e, ca, cb); W.more(); W.next()) {
-            const int k = W.kb + lane;
-            bool take = false;
-            int32_t m = 0;
-            if (k < W.k1) {
-                m = ent[k];
-                const float* B = mboxf + 6 * (int64_t)m;
-                take = overlap_keep(qlo, qhi, B, B + 3) &&
-                       first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
-            }
-            const unsigned bal = __ballot_sync(0xffffffffu, take);
-            if (bal == 0u) continue;
-            int base = 0;
-            if (lane == 0) base = atomicAdd(L.n, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) {
-                const int pos = base + __popc(bal & lanemask_lt());
-                if (pos < L.cap) L.p[pos] = make_int2(li, m);
-                else atomicMax(L.overflow, pos + 1);
-            }
-        }
-    }
-}
+// cell entries (k_query_walk) emits the (triangle, master) pairs that pass
+// the coarse test on conservative FP32 boxes and the first-common-cell
+// rule; k_ccd_exact (thread per such pair) tests the owned primitives,
+// first on FP32 boxes, then, for the pairs that pass, on their exact FP64
+// boxes, and emits the primitive pairs that overlap; k_accd_pairs runs ACCD
+// on those.  The primitive pairs are exactly those of the plain FP64 box
+// tests.
 
 // corner of slave tri T holding vertex v (v is one of T's vertices)
 __device__ __forceinline__ int corner_of(const int32_t* T, int32_t v) {
@@ -948,6 +974,17 @@ k_accd_pairs(SceneView S, Params P, PairList L, const double* __restrict__ x,
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t bp_init_constants(const double* rule_l1l2) {
+    // FP32 brackets of the rule's barycentrics: lo <= b <= hi
+    float f[2][16][6];
+    for (int l = 0; l < 2; ++l)
+        for (int k = 0; k < 16; ++k)
+            for (int a = 0; a < 3; ++a) {
+                const double b = rule_l1l2[(l * 16 + k) * 3 + a];
+                const float r = (float)b;
+                f[l][k][a] = (double)r > b ? std::nextafter(r, -INFINITY) : r;
+                f[l][k][3 + a] = (double)r < b ? std::nextafter(r, INFINITY) : r;
+            }
+    GMCP_CUDA_TRY(cudaMemcpyToSymbol(c_rule_f, f, sizeof(f)));
     return cudaMemcpyToSymbol(c_rule, rule_l1l2, sizeof(double) * 2 * 16 * 3);
 }
 
@@ -996,36 +1033,40 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
 
 // the contact and swept queries share the list buffers but keep their
 // lengths apart (slots 8 and 9), so both survive a pass for the statistics
+// The contact and the swept query keep separate lists, counters and work
+// counters (slots 8 / 5 and 9 / 7), so that the two can run concurrently.
 static QueryList query_list(Ctx& c, bool swept) {
+    QueryBufs& B = swept ? c.qswept : c.qcontact;
     QueryList Q;
     Q.n = c.misc_i32.p + (swept ? 9 : 8);
-    Q.work = c.misc_i32.p + 5;
-    Q.tri = c.qlist_tri.p;
-    Q.box = c.qlist_box.p;
-    Q.boxf = c.qlist_boxf.p;
-    Q.vboxf = c.qlist_vboxf.p;
-    Q.cell = c.qlist_cell.p;
+    Q.work = c.misc_i32.p + (swept ? 7 : 5);
+    Q.tri = B.tri.p;
+    Q.box = B.box.p;
+    Q.boxf = B.boxf.p;
+    Q.vboxf = B.vboxf.p;
+    Q.cell = B.cell.p;
     return Q;
 }
 
-static cudaError_t ensure_query_list(Ctx& c) {
-    GMCP_CUDA_TRY(c.qlist_tri.ensure((size_t)c.ns + 1));
-    GMCP_CUDA_TRY(c.qlist_box.ensure(6 * (size_t)c.ns + 6));
-    GMCP_CUDA_TRY(c.qlist_boxf.ensure(6 * (size_t)c.ns + 6));
-    GMCP_CUDA_TRY(c.qlist_vboxf.ensure(18 * (size_t)c.ns + 18));
-    GMCP_CUDA_TRY(c.qlist_cell.ensure(6 * (size_t)c.ns + 6));
+static cudaError_t ensure_query_list(Ctx& c, bool swept) {
+    QueryBufs& B = swept ? c.qswept : c.qcontact;
+    GMCP_CUDA_TRY(B.tri.ensure((size_t)c.ns + 1));
+    if (!swept) GMCP_CUDA_TRY(B.box.ensure(6 * (size_t)c.ns + 6));
+    GMCP_CUDA_TRY(B.boxf.ensure(6 * (size_t)c.ns + 6));
+    GMCP_CUDA_TRY(B.vboxf.ensure(18 * (size_t)c.ns + 18));
+    GMCP_CUDA_TRY(B.cell.ensure(6 * (size_t)c.ns + 6));
     return cudaSuccess;
 }
 
 static unsigned persistent_blocks(Ctx& c) { return (unsigned)(sm_count(c.device) * c.tune_query_bpsm); }
 
-cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
+cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool lazy) {
     ProfScope ps(c.prof, c.stream, "query");
     SceneView S = c.view();
     Params P = c.P;
     cudaStream_t s = c.stream;
     CandView C = c.cand();
-    GMCP_CUDA_TRY(ensure_query_list(c));
+    GMCP_CUDA_TRY(ensure_query_list(c, false));
     QueryList Q = query_list(c, false);
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 12, s));
     if (c.ns == 0) return cudaSuccess;
@@ -1036,14 +1077,34 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm) {
     k_query_filter<false><<<(unsigned)((c.ns + 255) / 256), 256, 0, s>>>(
         S, P, x, nullptr, c.cell_start.p, Q, c.cand_count.p, triE, triG, triS, f32);
     GMCP_CUDA_TRY(cudaGetLastError());
-    const unsigned g = persistent_blocks(c);
-    GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), s));
-    if (P.nk == 4)
-        k_query_contact<4><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mboxf.p, c.mcell.p, c.cell_start.p,
-                                             c.cell_ent.p, triE, triG, triS, f32);
-    else
-        k_query_contact<16><<<g, 256, 0, s>>>(S, P, C, Q, x, xm, c.mbox.p, c.mboxf.p, c.mcell.p, c.cell_start.p,
-                                              c.cell_ent.p, triE, triG, triS, f32);
+    if (c.cap_coarse == 0) c.cap_coarse = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);
+    const unsigned flat = (unsigned)(sm_count(c.device) * 8);
+    for (int attempt = 0;; ++attempt) {
+        GMCP_CUDA_TRY(c.coarse_pairs.ensure((size_t)c.cap_coarse));
+        // (triangle, master) pairs: count in slot 6, needed capacity in slot 15
+        PairList W{c.coarse_pairs.p, c.misc_i32.p + 6, c.misc_i32.p + 15, c.cap_coarse};
+        GMCP_CUDA_TRY(cudaMemsetAsync(W.n, 0, sizeof(int32_t), s));
+        GMCP_CUDA_TRY(cudaMemsetAsync(W.overflow, 0, sizeof(int32_t), s));
+        GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), s));
+        k_query_walk<<<persistent_blocks(c), 256, 0, s>>>(S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
+                                                          c.cell_ent.p, W);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        if (P.nk == 4)
+            k_contact_exact<4><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mbox.p, c.mboxf.p);
+        else
+            k_contact_exact<16><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mbox.p, c.mboxf.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        if (lazy) break;   // the caller reads the overflow slot after it synchronises
+        int32_t need = 0;
+        GMCP_CUDA_TRY(cudaMemcpyAsync(&need, W.overflow, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+        if (need == 0) break;
+        if (attempt >= 4) return cudaErrorInvalidValue;
+        c.cap_coarse = std::max(c.cap_coarse, need);
+        // the lists restart empty
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.cand_count.p, 0, sizeof(int32_t) * 4 * c.ns, s));
+    }
+    k_contact_finish<<<persistent_blocks(c), 256, 0, s>>>(C, Q, triE, triG, triS, f32);
     return cudaGetLastError();
 }
 
@@ -1054,27 +1115,27 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
     ProfScope ps(c.prof, c.stream, "accd");
     if (c.ns == 0) return cudaSuccess;
     SceneView S = c.view();
-    GMCP_CUDA_TRY(ensure_query_list(c));
+    GMCP_CUDA_TRY(ensure_query_list(c, true));
     QueryList Q = query_list(c, true);
     GMCP_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(int32_t), c.stream));
     k_query_filter<true><<<(unsigned)((c.ns + 255) / 256), 256, 0, c.stream>>>(
         S, c.P, x, dx, c.cell_start.p, Q, nullptr, nullptr, nullptr, nullptr, 0);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.cap_ccd == 0) c.cap_ccd = (int32_t)std::min<int64_t>((1 << 16) + c.ns / 4, 1 << 30);
-    if (c.cap_coarse == 0) c.cap_coarse = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);
+    if (c.cap_coarse_swept == 0) c.cap_coarse_swept = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);
     const unsigned flat = (unsigned)(sm_count(c.device) * 8);
     for (int attempt = 0;; ++attempt) {
         GMCP_CUDA_TRY(c.ccd_pairs.ensure((size_t)c.cap_ccd));
-        GMCP_CUDA_TRY(c.coarse_pairs.ensure((size_t)c.cap_coarse));
+        GMCP_CUDA_TRY(c.coarse_swept.ensure((size_t)c.cap_coarse_swept));
         // coarse pairs: count in slot 11, needed capacity in slot 14;
         // primitive pairs: count in slot 10, needed capacity in slot 13
-        PairList C{c.coarse_pairs.p, c.misc_i32.p + 11, c.misc_i32.p + 14, c.cap_coarse};
+        PairList C{c.coarse_swept.p, c.misc_i32.p + 11, c.misc_i32.p + 14, c.cap_coarse_swept};
         PairList L{c.ccd_pairs.p, c.misc_i32.p + 10, c.misc_i32.p + 13, c.cap_ccd};
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 10, 0, 2 * sizeof(int32_t), c.stream));
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 13, 0, 2 * sizeof(int32_t), c.stream));
         GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), c.stream));
-        k_query_ccd<<<persistent_blocks(c), 256, 0, c.stream>>>(S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
-                                                              c.cell_ent.p, C);
+        k_query_walk<<<persistent_blocks(c), 256, 0, c.stream>>>(S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
+                                                               c.cell_ent.p, C);
         GMCP_CUDA_TRY(cudaGetLastError());
         k_ccd_exact<<<flat, 256, 0, c.stream>>>(S, Q, C, x, dx, xm0, dxm, c.mbox.p, c.mboxf.p, L);
         GMCP_CUDA_TRY(cudaGetLastError());
@@ -1089,7 +1150,7 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
         if (attempt >= 4) return cudaErrorInvalidValue;
         // the minimum over the pairs seen so far stays valid; the counters restart
         c.cap_ccd = std::max(c.cap_ccd, need[0]);
-        c.cap_coarse = std::max(c.cap_coarse, need[1]);
+        c.cap_coarse_swept = std::max(c.cap_coarse_swept, need[1]);
         GMCP_CUDA_TRY(cudaMemsetAsync(counters, 0, 3 * sizeof(long long), c.stream));
     }
 }

@@ -244,6 +244,13 @@ struct PinnedIO {
     double pcg[4];
 };
 
+// slave tris whose query box meets a non-empty cell, with their boxes
+struct QueryBufs {
+    DBuf<int32_t> tri, cell;
+    DBuf<double> box;
+    DBuf<float> boxf, vboxf;
+};
+
 struct WarmStart;              // learned warm start (warmstart.cu)
 void ws_destroy(WarmStart* w);
 
@@ -287,13 +294,13 @@ struct Ctx {
     DBuf<double> mbox;                          // [nmt][6]
     DBuf<int4> mcell;                           // [nmt] lowest cell (x, y, z) and env
     DBuf<int4> mcell_hi;                        // [nmt] highest cell (x, y, z)
-    DBuf<int32_t> qlist_tri, qlist_cell;        // slave tris whose query meets a non-empty cell
-    DBuf<double> qlist_box;
-    DBuf<float> qlist_boxf, mboxf;              // conservative FP32 boxes (query list, master tris)
+    DBuf<float> mboxf;                          // conservative FP32 master boxes
     DBuf<int2> ccd_pairs;                       // primitive pairs for ACCD
-    DBuf<int2> coarse_pairs;                    // (swept query entry, master) pairs
-    DBuf<float> qlist_vboxf;                    // swept query: corner boxes
-    int32_t cap_ccd = 0, cap_coarse = 0;
+    DBuf<int2> coarse_pairs, coarse_swept;      // (query entry, master) pairs: contact, swept
+    int32_t cap_ccd = 0, cap_coarse = 0, cap_coarse_swept = 0;
+    QueryBufs qcontact, qswept;                 // filtered slave tris of the two queries
+    cudaStream_t ccd_stream = nullptr;          // the swept query's branch of a contact pass
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     DBuf<int32_t> cell_cnt, cell_start, cell_ent;
     DBuf<int32_t> scan_tmp;
     DBuf<int32_t> cand_face, cand_edge, cand_point, cand_count, active, misc_i32;
@@ -357,7 +364,7 @@ cudaError_t bp_init_constants(const double* rule_l1l2);
 // lazy: size the entries for the worst rigid pose instead of reading the
 // exact total back (no synchronisation); overflow sets misc_i32[12]
 cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swept, bool lazy = false);
-cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm);
+cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool lazy = false);
 // ACCD over swept pairs; reuse_grid: the cells already hold the master
 // triangles at xm0 (static master, same call), so the swept grid equals them
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
