@@ -41,7 +41,7 @@ CROP_HALF_WIDTH = 2.0e-3
 # DRAM bytes (read + write) of one k_samples launch on this workload, from the
 # ncu capture summarised in profiles/k_samples_gel_on_terrain.md; null when
 # the kernel changes and the capture is not yet redone
-K_SAMPLES_DRAM_BYTES_PER_LAUNCH = 604331
+K_SAMPLES_DRAM_BYTES_PER_LAUNCH = None
 
 
 def load_peaks():
