@@ -211,13 +211,27 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
         GMCP_CUDA_TRY(cudaMemcpyAsync(c.pin->ctr_ccd, c.i64_tmp.p + 8, 4 * sizeof(long long),
                                       cudaMemcpyDeviceToHost, c.stream));
     }
-    return cudaMemcpyAsync(c.pin->flags, c.misc_i32.p, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream);
+    return cudaMemcpyAsync(c.pin->flags, c.misc_i32.p, 32 * sizeof(int32_t), cudaMemcpyDeviceToHost, c.stream);
 }
 
 // capacity flags of the last lazy pass (valid after a synchronisation)
 bool pass_overflowed(const Ctx& c) {
     const int32_t* f = c.pin->flags;
     return f[1] || f[2] || f[3] || f[12] || f[13] || f[14] || f[15];
+}
+
+// The sample items of the last lazy pass did not fit their buffer (the
+// pass then took the warp-per-triangle kernel, with the same results):
+// make room for the next passes.
+cudaError_t grow_items(Ctx& c) {
+    const int64_t need = c.pin->flags[16];
+    if (need <= c.cap_items) return cudaSuccess;
+    c.cap_items = need + need / 2;
+    GMCP_CUDA_TRY(c.item_owner.ensure((size_t)c.cap_items));
+    GMCP_CUDA_TRY(c.item_rd.ensure(2 * (size_t)c.cap_items));
+    GMCP_CUDA_TRY(c.item_rt.ensure(5 * sizeof(double) * (size_t)c.cap_items));
+    c.cp_graph.reset();
+    return cudaSuccess;
 }
 
 cudaError_t grow_after_overflow(Ctx& c) {
@@ -257,7 +271,8 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.cap_coarse, (uintptr_t)c.coarse_swept.p, (uintptr_t)c.cap_coarse_swept,
             (uintptr_t)c.ccd_stream, (uintptr_t)c.mbox.p,
             (uintptr_t)c.mcell.p, (uintptr_t)c.mcell_hi.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
-            (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_frame.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
+            (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_frame.p, (uintptr_t)c.tri_items.p, (uintptr_t)c.item_owner.p,
+            (uintptr_t)c.item_rd.p, (uintptr_t)c.item_rt.p, (uintptr_t)c.cap_items, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
             (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,
             (uintptr_t)c.cb_val64.p, (uintptr_t)c.u64_tmp.p, (uintptr_t)c.i64_tmp.p, (uintptr_t)c.misc_i32.p,
             (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p};
@@ -764,7 +779,8 @@ static void alloc_call_buffers(Ctx& c) {
     CK(c.cand_point.ensure((size_t)ns * c.cap_p + 1));
     CK(c.cand_count.ensure((size_t)ns * 4 + 4));
     CK(c.active.ensure((size_t)ns + 1));
-    CK(c.misc_i32.ensure(16));
+    CK(c.misc_i32.ensure(32));
+    CK(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 32, s));
     CK(c.tri_E.ensure((size_t)ns + 1));
     CK(cudaMemsetAsync(c.tri_E.p, 0, sizeof(double) * (ns + 1), s));
     if (c.P.precision == IPC_PREC_MIXED) {
@@ -780,6 +796,26 @@ static void alloc_call_buffers(Ctx& c) {
         CK(cudaMemsetAsync(c.tri_S64.p, 0, sizeof(double) * (6 * ns + 6), s));
         CK(cudaMemsetAsync(c.tri_n64.p, 0, sizeof(double) * (3 * ns + 3), s));
     }
+    // touched-output lists: stamps start below the first pass number, the
+    // Hessian blocks start at zero
+    CK(c.tri_stamp.ensure((size_t)ns + 1));
+    CK(c.v_stamp.ensure((size_t)c.nv + 1));
+    CK(c.b_stamp.ensure((size_t)c.cb_nnzb + 1));
+    CK(c.v_list.ensure((size_t)c.nv + 1));
+    CK(c.b_list0.ensure((size_t)c.cb_nnzb + 1));
+    CK(c.b_list1.ensure((size_t)c.cb_nnzb + 1));
+    CK(cudaMemsetAsync(c.tri_stamp.p, 0, sizeof(int32_t) * (ns + 1), s));
+    CK(cudaMemsetAsync(c.v_stamp.p, 0, sizeof(int32_t) * (c.nv + 1), s));
+    CK(cudaMemsetAsync(c.b_stamp.p, 0, sizeof(int32_t) * (c.cb_nnzb + 1), s));
+    {
+        int32_t* lists[2] = {c.b_list0.p, c.b_list1.p};
+        CK(c.b_lists.upload(lists, 2, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    if (c.P.precision == IPC_PREC_MIXED)
+        CK(cudaMemsetAsync(c.cb_val32.p, 0, sizeof(float) * 9 * (c.cb_nnzb + 1), s));
+    else
+        CK(cudaMemsetAsync(c.cb_val64.p, 0, sizeof(double) * 9 * (c.cb_nnzb + 1), s));
     CK(c.u64_tmp.ensure(8));
     CK(c.i64_tmp.ensure(16));
     CK(c.scal.ensure(16));
@@ -1084,7 +1120,10 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
                 if (!pass_overflowed(c)) break;
                 API_CK(ctx, grow_after_overflow(c));
             }
+            API_CK(ctx, grow_items(c));
             if (use_graph) capture_contact_pass(c, A);
+        } else if (c.pin->flags[16] > c.cap_items) {
+            API_CK(ctx, grow_items(c));
         }
     }
     if (energy_host) *energy_host = c.pin->energy;

@@ -323,9 +323,9 @@ __device__ void warp_sort(int32_t* L, int n, int lane) {
 // Phase 1 of both queries (one thread per slave triangle): the triangle's
 // box (static: vertex box grown by dhat; swept: box of the vertices at x and
 // x + dx), its cell range, and whether any of those cells holds a master
-// triangle.  Triangles with only empty cells are finished here (contact
-// mode zeroes their counts and outputs); the others are appended, with their
-// boxes and cell range, to the list the warps of phase 2 work through.
+// triangle.  Contact mode zeroes every triangle's candidate counts; the
+// triangles that reach a non-empty cell are appended, with their boxes and
+// cell range, to the list that the later launches work through.
 struct QueryList {
     int32_t* n;        // scalar
     int32_t* tri;      // [ns]
@@ -339,9 +339,7 @@ struct QueryList {
 template <bool SWEPT>
 __global__ void __launch_bounds__(256)
 k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double* __restrict__ dx,
-               const int32_t* __restrict__ start, QueryList Q, int32_t* __restrict__ count,
-               double* __restrict__ triE, void* __restrict__ triG, void* __restrict__ triS,
-               int out_f32) {
+               const int32_t* __restrict__ start, QueryList Q, int32_t* __restrict__ count) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S.ns) return;
     const int32_t* T = S.stri + 3 * t;
@@ -404,19 +402,6 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
         }
         int32_t* cl = Q.cell + 6 * (int64_t)idx;
         cl[0] = ca.x; cl[1] = ca.y; cl[2] = ca.z; cl[3] = cb.x; cl[4] = cb.y; cl[5] = cb.z;
-    } else if (!SWEPT) {
-        if (triE) {
-            triE[t] = 0.0;
-            if (out_f32) {
-                float* G = (float*)triG; float* Sm = (float*)triS;
-                for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0f;
-                for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0f;
-            } else {
-                double* G = (double*)triG; double* Sm = (double*)triS;
-                for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0;
-                for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0;
-            }
-        }
     }
 }
 
@@ -632,8 +617,7 @@ k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
 // overflowing lists, add the triangle to the active list or zero its
 // outputs.
 __global__ void __launch_bounds__(256)
-k_contact_finish(CandView C, QueryList Q, double* __restrict__ triE, void* __restrict__ triG,
-                 void* __restrict__ triS, int out_f32) {
+k_contact_finish(CandView C, QueryList Q) {
     const int lane = threadIdx.x & 31;
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
@@ -649,21 +633,11 @@ k_contact_finish(CandView C, QueryList Q, double* __restrict__ triE, void* __res
         if (nf > C.cap_f) atomicMax(&C.overflow[0], nf);
         if (ne > C.cap_e) atomicMax(&C.overflow[1], ne);
         if (np > C.cap_p) atomicMax(&C.overflow[2], np);
+        // triangles without candidates are not stamped by the evaluation, so
+        // their stored outputs are never read
         if (nf + ne + np > 0) {
             const int idx = atomicAdd(C.n_active, 1);
             C.active[idx] = (int32_t)t;
-        } else if (triE) {
-            // no candidates: this triangle contributes nothing to the gathers
-            triE[t] = 0.0;
-            if (out_f32) {
-                float* G = (float*)triG; float* Sm = (float*)triS;
-                for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0f;
-                for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0f;
-            } else {
-                double* G = (double*)triG; double* Sm = (double*)triS;
-                for (int q = 0; q < 3; ++q) G[3 * t + q] = 0.0;
-                for (int q = 0; q < 6; ++q) Sm[6 * t + q] = 0.0;
-            }
         }
     }
 }
@@ -1070,12 +1044,8 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
     QueryList Q = query_list(c, false);
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 12, s));
     if (c.ns == 0) return cudaSuccess;
-    const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    double* triE = c.tri_E.p;
-    void* triG = f32 ? (void*)c.tri_G32.p : (void*)c.tri_G64.p;
-    void* triS = f32 ? (void*)c.tri_S32.p : (void*)c.tri_S64.p;
     k_query_filter<false><<<(unsigned)((c.ns + 255) / 256), 256, 0, s>>>(
-        S, P, x, nullptr, c.cell_start.p, Q, c.cand_count.p, triE, triG, triS, f32);
+        S, P, x, nullptr, c.cell_start.p, Q, c.cand_count.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.cap_coarse == 0) c.cap_coarse = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);
     const unsigned flat = (unsigned)(sm_count(c.device) * 8);
@@ -1104,7 +1074,7 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
         // the lists restart empty
         GMCP_CUDA_TRY(cudaMemsetAsync(c.cand_count.p, 0, sizeof(int32_t) * 4 * c.ns, s));
     }
-    k_contact_finish<<<persistent_blocks(c), 256, 0, s>>>(C, Q, triE, triG, triS, f32);
+    k_contact_finish<<<persistent_blocks(c), 256, 0, s>>>(C, Q);
     return cudaGetLastError();
 }
 
@@ -1119,7 +1089,7 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
     QueryList Q = query_list(c, true);
     GMCP_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(int32_t), c.stream));
     k_query_filter<true><<<(unsigned)((c.ns + 255) / 256), 256, 0, c.stream>>>(
-        S, c.P, x, dx, c.cell_start.p, Q, nullptr, nullptr, nullptr, nullptr, 0);
+        S, c.P, x, dx, c.cell_start.p, Q, nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.cap_ccd == 0) c.cap_ccd = (int32_t)std::min<int64_t>((1 << 16) + c.ns / 4, 1 << 30);
     if (c.cap_coarse_swept == 0) c.cap_coarse_swept = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);

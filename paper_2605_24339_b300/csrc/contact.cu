@@ -251,19 +251,81 @@ __device__ __forceinline__ void lag_add(double* E8, const double* al, int na, do
 }
 
 // ---------------------------------------------------------------------------
-// the sample kernel
+// the samples
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Outputs touched by the active triangles only.  A contact evaluation
+// numbers itself (slot kSlotPass) and stamps its active triangles; the
+// frame pass also lists the vertices and contact blocks of those triangles
+// once each (stamps make the lists duplicate-free).  Gradient rows and
+// blocks are then gathered in a fixed order over their contributing
+// triangles, skipping those not active in this evaluation (their stored
+// outputs are stale), so the result does not depend on the lists' order.
+// The gradient is written whole (zero rows first); the Hessian blocks live
+// in the context, so only the blocks listed by the previous Hessian pass and
+// not by this one are cleared.  The block lists of consecutive Hessian
+// passes alternate by the parity of the Hessian-pass number (kSlotHPass).
+// ---------------------------------------------------------------------------
+__global__ void k_pass_begin(int32_t* misc, int hess) {
+    const int32_t p = ++misc[kSlotPass];
+    (void)p;
+    misc[kSlotVCount] = 0;
+    if (hess) {
+        const int32_t h = ++misc[kSlotHPass];
+        misc[kSlotBCount + (h & 1)] = 0;
+    }
+}
+
+struct TouchArgs {
+    const int32_t* misc;
+    int32_t* v_stamp;
+    int32_t* v_list;
+    int32_t* v_count;
+    int32_t* b_stamp;
+    int32_t* b_list[2];
+    int32_t* b_count;      // [2], by Hessian-pass parity
+    const int32_t* row;    // contact BSR pattern
+    const int32_t* col;
+    int grad, hess;
+};
+
+// list the vertices and contact blocks of slave tri T once each (stamps)
+__device__ __forceinline__ void touch_tri(const TouchArgs& A, const int32_t* T) {
+    const int32_t ps = A.misc[kSlotPass], hs = A.misc[kSlotHPass];
+    for (int a = 0; a < 3; ++a) {
+        const int32_t v = T[a];
+        if (A.grad && atomicExch(&A.v_stamp[v], ps) != ps) A.v_list[atomicAdd(A.v_count, 1)] = v;
+        if (!A.hess) continue;
+        for (int b = 0; b < 3; ++b) {
+            int32_t k = A.row[v];
+            while (A.col[k] != T[b]) ++k;        // the pattern holds every (T[a], T[b])
+            if (atomicExch(&A.b_stamp[k], hs) != hs) A.b_list[hs & 1][atomicAdd(&A.b_count[hs & 1], 1)] = k;
+        }
+    }
+}
+
 // Frames of the active slave triangles, one thread per triangle, so that
-// the FP64 square roots and divisions run once per triangle rather than on
-// every lane of the triangle's warp in k_samples: unit normal and area at x,
-// unit normal at rest, and the absolute slack of the FP32 plane-distance
-// pre-tests (which covers the FP64 rounding of gaps formed from coordinates
-// of this magnitude).  frame[8 i ...] belongs to active[i].
+// the FP64 square roots and divisions run once per triangle: unit normal
+// and area at x, unit normal at rest, and the absolute slack of the FP32
+// plane-distance pre-tests (which covers the FP64 rounding of gaps formed
+// from coordinates of this magnitude).  frame[8 i ...] belongs to active[i].
+// With items != NULL it also counts the triangle's sample items (face:
+// candidate x sample, edge: candidate x Gauss point, point: candidate),
+// reserves a contiguous range of slots for them (items[2 i] = first slot,
+// items[2 i + 1] = count; the ranges' order depends on scheduling, the
+// per-triangle results do not) and adds them to *n_items.
 __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ x,
-                            double* __restrict__ frame) {
+                            double* __restrict__ frame, int nk, int32_t* __restrict__ items,
+                            int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp, TouchArgs TA) {
     const int n_active = *C.n_active;
+    const int32_t ps = tri_stamp ? TA.misc[kSlotPass] : 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_active; i += gridDim.x * blockDim.x) {
-        const int32_t* Tt = S.stri + 3 * (int64_t)C.active[i];
+        const int64_t t = C.active[i];
+        const int32_t* Tt = S.stri + 3 * t;
+        if (tri_stamp) {
+            tri_stamp[t] = ps;
+            touch_tri(TA, Tt);
+        }
         const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
         const V3<double> X0 = ld3(S.X, Tt[0]), X1 = ld3(S.X, Tt[1]), X2 = ld3(S.X, Tt[2]);
         const V3<double> cr = cross(x1 - x0, x2 - x0);
@@ -275,187 +337,267 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
         f[3] = 0.5 * clen;
         f[4] = cr0.x / clen0; f[5] = cr0.y / clen0; f[6] = cr0.z / clen0;
         f[7] = 1e-12 * (fabs(x0.x) + fabs(x0.y) + fabs(x0.z)) + 1e-30;
+        if (items) {
+            const int32_t* cnt = C.count + 4 * t;
+            const int n = min(cnt[0], C.cap_f) * nk + 2 * min(cnt[1], C.cap_e) + min(cnt[2], C.cap_p);
+            items[2 * i] = atomicAdd(n_items, n);
+            items[2 * i + 1] = n;
+        }
     }
 }
 
+// what the slave triangle's samples share
+struct TriData {
+    int64_t t;
+    V3<double> x0, x1, x2, X0, X1, X2, dx0, dx1, dx2, ns, ns0;
+    V3<float> ns_f;
+    double As;
+    float tol_abs;
+    const double* sb;      // rest box of the slave tri
+    int nf, ne, np;        // candidates (capped)
+};
+
+__device__ __forceinline__ TriData load_tri(const SceneView& S, const CandView& C, const double* x,
+                                            const double* dx, const double* frame, int i) {
+    TriData D;
+    D.t = C.active[i];
+    const int32_t* Tt = S.stri + 3 * D.t;
+    D.x0 = ld3(x, Tt[0]); D.x1 = ld3(x, Tt[1]); D.x2 = ld3(x, Tt[2]);
+    D.X0 = ld3(S.X, Tt[0]); D.X1 = ld3(S.X, Tt[1]); D.X2 = ld3(S.X, Tt[2]);
+    const double* fr = frame + 8 * (int64_t)i;
+    D.ns = {fr[0], fr[1], fr[2]};
+    D.As = fr[3];
+    D.ns0 = {fr[4], fr[5], fr[6]};
+    D.tol_abs = (float)fr[7];
+    D.ns_f = tof(D.ns);
+    D.sb = S.srest_box + 6 * D.t;
+    const int32_t* cnt = C.count + 4 * D.t;
+    D.nf = min(cnt[0], C.cap_f); D.ne = min(cnt[1], C.cap_e); D.np = min(cnt[2], C.cap_p);
+    D.dx0 = {0, 0, 0}; D.dx1 = {0, 0, 0}; D.dx2 = {0, 0, 0};
+    if (dx) { D.dx0 = ld3(dx, Tt[0]); D.dx1 = ld3(dx, Tt[1]); D.dx2 = ld3(dx, Tt[2]); }
+    return D;
+}
+
+// an active sample: kappa_q, weight w, gamma, gap g, eps, slave
+// barycentrics b and the linearised gap change dg along (dx, dxm)
+struct ItemOut {
+    double kq, w, gamma, g, eps, dg;
+    double b[3];
+};
+
+// what a face sample k shares over its candidates: its position, the
+// position relative to x0 in FP32 and the slave-side gap change
+struct FaceSample {
+    double beta[3];
+    V3<double> xs;
+    V3<float> xs_rel;
+    double ds;
+};
+__device__ __forceinline__ FaceSample face_sample(const Params& P, const TriData& D, int k, bool want_dg) {
+    FaceSample F;
+    for (int q = 0; q < 3; ++q) F.beta[q] = c_rule[P.L - 1][k][q];
+    F.xs = interp(F.beta, D.x0, D.x1, D.x2);
+    F.xs_rel = tof(F.xs - D.x0);
+    F.ds = want_dg ? dot(D.ns, interp(F.beta, D.dx0, D.dx1, D.dx2)) : 0.0;
+    return F;
+}
+
+// face sample F of slave tri D against master tri m (Sec. 4.1, reading R1)
+template <int NK>
+__device__ __forceinline__ bool face_item(const SceneView& S, const Params& P, const TriData& D,
+                                          const FaceSample& F, const double* xm, const double* dxm,
+                                          int32_t m, bool pre, bool want_dg, ItemOut& o) {
+    const double eps_max = P.dhat;
+    const int32_t* M = S.mtri + 3 * (int64_t)m;
+    const V3<double> y0 = ld3(xm, M[0]), y1 = ld3(xm, M[1]), y2 = ld3(xm, M[2]);
+    if (pre && !face_maybe(F.xs_rel, D.ns_f, tof(y0 - D.x0), tof(y1 - D.x0), tof(y2 - D.x0), (float)eps_max))
+        return false;
+    double g, bm[3];
+    if (!face_geom<double>(F.xs, D.ns, y0, y1, y2, g, bm)) return false;
+    double eps = eps_max;
+    const double* mb = S.mrest_box + 6 * (int64_t)m;
+    if (!rest_far(D.sb, D.sb + 3, mb, mb + 3, eps_max)) {
+        const V3<double> xs0 = interp(F.beta, D.X0, D.X1, D.X2);
+        double g0, bm0[3];
+        const bool ok0 = face_geom<double>(xs0, D.ns0, ld3(S.Y0, M[0]), ld3(S.Y0, M[1]), ld3(S.Y0, M[2]), g0, bm0);
+        if (ok0) eps = rmin(0.9 * g0, eps_max);
+    }
+    if (!(g < eps)) return false;
+    o.kq = P.kappa; o.w = (1.0 / (double)NK) * D.As; o.gamma = hermite(min3(bm), P.delta_T);
+    o.g = g; o.eps = eps;
+    for (int q = 0; q < 3; ++q) o.b[q] = F.beta[q];
+    o.dg = 0.0;
+    if (want_dg) {
+        const double dm = dxm ? dot(D.ns, interp(bm, ld3(dxm, M[0]), ld3(dxm, M[1]), ld3(dxm, M[2]))) : 0.0;
+        o.dg = dm - F.ds;
+    }
+    return true;
+}
+
+// Gauss point q of master edge me projected on slave tri D (Sec. 4.1,
+// reading R3)
+__device__ __forceinline__ bool edge_item(const SceneView& S, const Params& P, const TriData& D,
+                                          const double* xm, const double* dxm, int32_t me, int q,
+                                          bool pre, bool want_dg, ItemOut& o) {
+    const double eps_max = P.dhat;
+    const double gp = 1.0 / sqrt(3.0);
+    const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
+    const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
+    if (pre && !plane_gap_maybe(D.ns_f, tof(ya - D.x0), tof(yb - D.x0), (float)eps_max, D.tol_abs)) return false;
+    const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
+    if (!any_facing(S, xm, S.me_tri + a0, a1 - a0, D.ns)) return false;
+    double bA[3], bB[3];
+    bary(ya, D.x0, D.x1, D.x2, bA);
+    bary(yb, D.x0, D.x1, D.x2, bB);
+    // clip the projected edge by the slave triangle: all beta >= 0
+    double lo = 0.0, hi = 1.0;
+    bool empty = false;
+    for (int a = 0; a < 3; ++a) {
+        const double Dd = bB[a] - bA[a];
+        if (Dd > 0.0) lo = rmax(lo, -bA[a] / Dd);
+        else if (Dd < 0.0) hi = rmin(hi, -bA[a] / Dd);
+        else if (bA[a] < 0.0) empty = true;
+    }
+    if (empty || !(hi > lo)) return false;
+    const V3<double> tv = yb - ya;
+    const double tn = dot(tv, D.ns);
+    const V3<double> tp = tv - tn * D.ns;
+    const double ell = (hi - lo) * sqrt(dot(tp, tp));
+    const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
+    const double eta = q == 0 ? mid - half * gp : mid + half * gp;
+    const V3<double> xmk = (1.0 - eta) * ya + eta * yb;
+    double bsk[3];
+    bary(xmk, D.x0, D.x1, D.x2, bsk);
+    const V3<double> xs = interp(bsk, D.x0, D.x1, D.x2);
+    const double g = dot(D.ns, xmk - xs);
+    if (!(g > 0.0)) return false;
+    double eps = eps_max;
+    const V3<double> Ya = ld3(S.Y0, ia), Yb = ld3(S.Y0, ib);
+    const double elo[3] = {rmin(Ya.x, Yb.x), rmin(Ya.y, Yb.y), rmin(Ya.z, Yb.z)};
+    const double ehi[3] = {rmax(Ya.x, Yb.x), rmax(Ya.y, Yb.y), rmax(Ya.z, Yb.z)};
+    if (!rest_far(D.sb, D.sb + 3, elo, ehi, eps_max)) {
+        const V3<double> xm0 = (1.0 - eta) * Ya + eta * Yb;
+        double bs0[3];
+        bary(xm0, D.X0, D.X1, D.X2, bs0);
+        const double g0 = dot(D.ns0, xm0 - interp(bs0, D.X0, D.X1, D.X2));
+        if (min3(bs0) >= 0.0 && g0 > 0.0) eps = rmin(0.9 * g0, eps_max);
+    }
+    if (!(g < eps)) return false;
+    o.kq = P.kappa_edge; o.w = 0.5 * ell; o.gamma = hermite(eta, P.delta_e) * hermite(1.0 - eta, P.delta_e);
+    o.g = g; o.eps = eps;
+    for (int c = 0; c < 3; ++c) o.b[c] = bsk[c];
+    o.dg = 0.0;
+    if (want_dg) {
+        const double ds = dot(D.ns, interp(bsk, D.dx0, D.dx1, D.dx2));
+        const double dm = dxm ? dot(D.ns, (1.0 - eta) * ld3(dxm, ia) + eta * ld3(dxm, ib)) : 0.0;
+        o.dg = dm - ds;
+    }
+    return true;
+}
+
+// master vertex u projected on slave tri D (Sec. 4.1, reading R3)
+__device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, const TriData& D,
+                                           const double* xm, const double* dxm, int32_t u, bool pre,
+                                           bool want_dg, ItemOut& o) {
+    const double eps_max = P.dhat;
+    const V3<double> y = ld3(xm, u);
+    if (pre) {
+        const V3<float> d = tof(y - D.x0);
+        if (!plane_gap_maybe(D.ns_f, d, d, (float)eps_max, D.tol_abs)) return false;
+    }
+    const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
+    if (!any_facing(S, xm, S.mv_tri + a0, a1 - a0, D.ns)) return false;
+    double bs[3];
+    bary(y, D.x0, D.x1, D.x2, bs);
+    if (!(min3(bs) >= 0.0)) return false;
+    const double g = dot(D.ns, y - interp(bs, D.x0, D.x1, D.x2));
+    if (!(g > 0.0)) return false;
+    double eps = eps_max;
+    const V3<double> Y = ld3(S.Y0, u);
+    const double yb[3] = {Y.x, Y.y, Y.z};
+    if (!rest_far(D.sb, D.sb + 3, yb, yb, eps_max)) {
+        double bs0[3];
+        bary(Y, D.X0, D.X1, D.X2, bs0);
+        const double g0 = dot(D.ns0, Y - interp(bs0, D.X0, D.X1, D.X2));
+        if (min3(bs0) >= 0.0 && g0 > 0.0) eps = rmin(0.9 * g0, eps_max);
+    }
+    if (!(g < eps)) return false;
+    o.kq = P.kappa_point; o.w = 1.0; o.gamma = 1.0;
+    o.g = g; o.eps = eps;
+    for (int c = 0; c < 3; ++c) o.b[c] = bs[c];
+    o.dg = 0.0;
+    if (want_dg) {
+        const double ds = dot(D.ns, interp(bs, D.dx0, D.dx1, D.dx2));
+        const double dm = dxm ? dot(D.ns, ld3(dxm, u)) : 0.0;
+        o.dg = dm - ds;
+    }
+    return true;
+}
+
+// Warp per active triangle (persistent grid).  Used for the step bound and
+// the lagged energies of the line search, and for the contact evaluation
+// when the item buffer is too small (then run_if_over selects it).
 template <int NK, class T, int MODE>
 __global__ void __launch_bounds__(256)
 k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
           const double* __restrict__ xm, double* __restrict__ triE, T* __restrict__ triG,
           T* __restrict__ triS, T* __restrict__ triN, long long* counters,
           const double* __restrict__ dx, const double* __restrict__ dxm,
-          unsigned long long* alpha_bits, LagArgs LG, const double* __restrict__ frame) {
+          unsigned long long* alpha_bits, LagArgs LG, const double* __restrict__ frame,
+          const int32_t* __restrict__ run_if_over, int64_t item_cap) {
+    if (run_if_over && (int64_t)*run_if_over <= item_cap) return;
     const int lane = threadIdx.x & 31;
-    const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
     const int n_active = *C.n_active;
-    const double eps_max = P.dhat;
-    const double omega = 1.0 / (double)NK;
     long long cnt_f = 0, cnt_e = 0, cnt_p = 0, cnt_eval = 0;
-    double beta_k[3];
-    for (int q = 0; q < 3; ++q) beta_k[q] = c_rule[P.L - 1][lane % NK][q];
     double al8[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) al8[j] = (MODE == MODE_LAGGED && j < LG.na) ? LG.alphas[j] : 0.0;
-    (void)warp; (void)nwarps;
     const bool pre = P.precision == IPC_PREC_MIXED;   // FP32 pre-tests (exact decisions unchanged)
+    const bool want_dg = dx != nullptr;
+    const bool want_alpha = MODE != MODE_LAGGED && want_dg;
     for (int i = next_item(C.work, lane); i < n_active; i = next_item(C.work, lane)) {
-        const int64_t t = C.active[i];
-        const int32_t* Tt = S.stri + 3 * t;
-        const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
-        const V3<double> X0 = ld3(S.X, Tt[0]), X1 = ld3(S.X, Tt[1]), X2 = ld3(S.X, Tt[2]);
-        const double* fr = frame + 8 * (int64_t)i;
-        const V3<double> ns = {fr[0], fr[1], fr[2]};
-        const double As = fr[3];
-        const V3<double> ns0 = {fr[4], fr[5], fr[6]};
-        const float tol_abs = (float)fr[7];
-        const V3<float> ns_f = tof(ns);
-        const double* sb = S.srest_box + 6 * t;
-        const int32_t* cnt = C.count + 4 * t;
-        const int nf = min(cnt[0], C.cap_f), ne = min(cnt[1], C.cap_e), np = min(cnt[2], C.cap_p);
+        const TriData D = load_tri(S, C, x, dx, frame, i);
         Acc<T> A;
         A.zero();
         double E8[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) E8[j] = 0.0;
-        // ---------------- face samples ----------------
-        // (mixed path: FP32 pre-test, then the exact FP64 cast and decisions)
-        const bool want_dg = dx != nullptr;
-        const bool want_alpha = MODE != MODE_LAGGED && want_dg;
-        V3<double> dx0 = {0, 0, 0}, dx1 = {0, 0, 0}, dx2 = {0, 0, 0};
-        if (want_dg) { dx0 = ld3(dx, Tt[0]); dx1 = ld3(dx, Tt[1]); dx2 = ld3(dx, Tt[2]); }
+        auto consume = [&](const ItemOut& o) {
+            if (MODE == MODE_EVAL) sample_add<T>(A, o.kq, o.w, o.gamma, o.g, o.eps, o.b);
+            if (want_dg) {
+                if (want_alpha && o.dg < 0.0) A.amin = rmin(A.amin, 0.9 * o.g / (-o.dg));
+                if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, o.kq * o.w * o.gamma, o.g, o.eps, o.dg);
+            }
+        };
+        // face items (lane, lane + 32, ...): 32 is a multiple of NK, so each
+        // lane keeps one sample
         {
-            const V3<double> xs = interp(beta_k, x0, x1, x2);
-            const V3<float> xs_rel = tof(xs - x0);
-            const double ds_face = want_dg ? dot(ns, interp(beta_k, dx0, dx1, dx2)) : 0.0;
-            const int32_t* Lf = C.face + t * C.cap_f;
-            for (int it = lane; it < nf * NK; it += 32) {
-                const int32_t m = Lf[it / NK];
-                const int32_t* M = S.mtri + 3 * (int64_t)m;
-                const V3<double> y0 = ld3(xm, M[0]), y1 = ld3(xm, M[1]), y2 = ld3(xm, M[2]);
+            const FaceSample F = face_sample(P, D, lane % NK, want_dg);
+            const int32_t* Lf = C.face + D.t * C.cap_f;
+            for (int it = lane; it < D.nf * NK; it += 32) {
                 ++cnt_eval;
-                if (pre && !face_maybe(xs_rel, ns_f, tof(y0 - x0), tof(y1 - x0), tof(y2 - x0), (float)eps_max))
-                    continue;
-                double g, bm[3];
-                if (!face_geom<double>(xs, ns, y0, y1, y2, g, bm)) continue;
-                double eps = eps_max;
-                const double* mb = S.mrest_box + 6 * (int64_t)m;
-                if (!rest_far(sb, sb + 3, mb, mb + 3, eps_max)) {
-                    const V3<double> xs0 = interp(beta_k, X0, X1, X2);
-                    double g0, bm0[3];
-                    bool ok0 = face_geom<double>(xs0, ns0, ld3(S.Y0, M[0]), ld3(S.Y0, M[1]),
-                                                 ld3(S.Y0, M[2]), g0, bm0);
-                    if (ok0) eps = rmin(0.9 * g0, eps_max);
-                }
-                if (!(g < eps)) continue;
-                const double gamma = hermite(min3(bm), P.delta_T);
+                ItemOut o;
+                if (!face_item<NK>(S, P, D, F, xm, dxm, Lf[it / NK], pre, want_dg, o)) continue;
                 ++cnt_f;
-                if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa, omega * As, gamma, g, eps, beta_k);
-                if (want_dg) {
-                    const double dm = dxm ? dot(ns, interp(bm, ld3(dxm, M[0]), ld3(dxm, M[1]), ld3(dxm, M[2]))) : 0.0;
-                    const double dg = dm - ds_face;
-                    if (want_alpha && dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
-                    if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, P.kappa * (omega * As) * gamma, g, eps, dg);
-                }
+                consume(o);
             }
         }
-        // ---------------- edge samples (FP64 geometry) ----------------
         {
-            const int32_t* Le = C.edge + t * C.cap_e;
-            const double gp = 1.0 / sqrt(3.0);
-            for (int it = lane; it < ne * 2; it += 32) {
-                const int32_t me = Le[it >> 1];
-                const int q = it & 1;
-                const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
-                const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
-                if (pre && !plane_gap_maybe(ns_f, tof(ya - x0), tof(yb - x0), (float)eps_max, tol_abs)) continue;
-                const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
-                if (!any_facing(S, xm, S.me_tri + a0, a1 - a0, ns)) continue;
-                double bA[3], bB[3];
-                bary(ya, x0, x1, x2, bA);
-                bary(yb, x0, x1, x2, bB);
-                // clip the projected edge by the slave triangle: all beta >= 0
-                double lo = 0.0, hi = 1.0;
-                bool empty = false;
-                for (int a = 0; a < 3; ++a) {
-                    const double D = bB[a] - bA[a];
-                    if (D > 0.0) lo = rmax(lo, -bA[a] / D);
-                    else if (D < 0.0) hi = rmin(hi, -bA[a] / D);
-                    else if (bA[a] < 0.0) empty = true;
-                }
-                if (empty || !(hi > lo)) continue;
-                const V3<double> tv = yb - ya;
-                const double tn = dot(tv, ns);
-                const V3<double> tp = tv - tn * ns;
-                const double ell = (hi - lo) * sqrt(dot(tp, tp));
-                const double mid = 0.5 * (lo + hi), half = 0.5 * (hi - lo);
-                const double eta = q == 0 ? mid - half * gp : mid + half * gp;
-                const V3<double> xmk = (1.0 - eta) * ya + eta * yb;
-                double bsk[3];
-                bary(xmk, x0, x1, x2, bsk);
-                const V3<double> xs = interp(bsk, x0, x1, x2);
-                const double g = dot(ns, xmk - xs);
-                if (!(g > 0.0)) continue;
-                double eps = eps_max;
-                const V3<double> Ya = ld3(S.Y0, ia), Yb = ld3(S.Y0, ib);
-                const double elo[3] = {rmin(Ya.x, Yb.x), rmin(Ya.y, Yb.y), rmin(Ya.z, Yb.z)};
-                const double ehi[3] = {rmax(Ya.x, Yb.x), rmax(Ya.y, Yb.y), rmax(Ya.z, Yb.z)};
-                if (!rest_far(sb, sb + 3, elo, ehi, eps_max)) {
-                    const V3<double> xm0 = (1.0 - eta) * Ya + eta * Yb;
-                    double bs0[3];
-                    bary(xm0, X0, X1, X2, bs0);
-                    const double g0 = dot(ns0, xm0 - interp(bs0, X0, X1, X2));
-                    if (min3(bs0) >= 0.0 && g0 > 0.0) eps = rmin(0.9 * g0, eps_max);
-                }
-                if (!(g < eps)) continue;
+            const int32_t* Le = C.edge + D.t * C.cap_e;
+            for (int it = lane; it < D.ne * 2; it += 32) {
+                ItemOut o;
+                if (!edge_item(S, P, D, xm, dxm, Le[it >> 1], it & 1, pre, want_dg, o)) continue;
                 ++cnt_e;
-                const double gamma = hermite(eta, P.delta_e) * hermite(1.0 - eta, P.delta_e);
-                if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa_edge, 0.5 * ell, gamma, g, eps, bsk);
-                if (want_dg) {
-                    const double ds = dot(ns, interp(bsk, dx0, dx1, dx2));
-                    const double dm = dxm ? dot(ns, (1.0 - eta) * ld3(dxm, ia) + eta * ld3(dxm, ib)) : 0.0;
-                    const double dg = dm - ds;
-                    if (want_alpha && dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
-                    if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, P.kappa_edge * (0.5 * ell) * gamma, g, eps, dg);
-                }
+                consume(o);
             }
         }
-        // ---------------- point samples (FP64 geometry) ----------------
         {
-            const int32_t* Lp = C.point + t * C.cap_p;
-            for (int it = lane; it < np; it += 32) {
-                const int32_t u = Lp[it];
-                const V3<double> y = ld3(xm, u);
-                if (pre) {
-                    const V3<float> d = tof(y - x0);
-                    if (!plane_gap_maybe(ns_f, d, d, (float)eps_max, tol_abs)) continue;
-                }
-                const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
-                if (!any_facing(S, xm, S.mv_tri + a0, a1 - a0, ns)) continue;
-                double bs[3];
-                bary(y, x0, x1, x2, bs);
-                if (!(min3(bs) >= 0.0)) continue;
-                const double g = dot(ns, y - interp(bs, x0, x1, x2));
-                if (!(g > 0.0)) continue;
-                double eps = eps_max;
-                const V3<double> Y = ld3(S.Y0, u);
-                const double yb[3] = {Y.x, Y.y, Y.z};
-                if (!rest_far(sb, sb + 3, yb, yb, eps_max)) {
-                    double bs0[3];
-                    bary(Y, X0, X1, X2, bs0);
-                    const double g0 = dot(ns0, Y - interp(bs0, X0, X1, X2));
-                    if (min3(bs0) >= 0.0 && g0 > 0.0) eps = rmin(0.9 * g0, eps_max);
-                }
-                if (!(g < eps)) continue;
+            const int32_t* Lp = C.point + D.t * C.cap_p;
+            for (int it = lane; it < D.np; it += 32) {
+                ItemOut o;
+                if (!point_item(S, P, D, xm, dxm, Lp[it], pre, want_dg, o)) continue;
                 ++cnt_p;
-                if (MODE == MODE_EVAL) sample_add<T>(A, P.kappa_point, 1.0, 1.0, g, eps, bs);
-                if (want_dg) {
-                    const double ds = dot(ns, interp(bs, dx0, dx1, dx2));
-                    const double dm = dxm ? dot(ns, ld3(dxm, u)) : 0.0;
-                    const double dg = dm - ds;
-                    if (want_alpha && dg < 0.0) A.amin = rmin(A.amin, 0.9 * g / (-dg));
-                    if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, P.kappa_point * 1.0 * 1.0, g, eps, dg);
-                }
+                consume(o);
             }
         }
         // ---------------- fixed-order warp reduction ----------------
@@ -469,10 +611,11 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                 for (int q = 0; q < 6; ++q) A.S[q] += shfl_x(A.S[q], o);
             }
             if (lane == 0) {
+                const int64_t t = D.t;
                 triE[t] = A.E;
                 for (int q = 0; q < 3; ++q) triG[3 * t + q] = A.G[q];
                 for (int q = 0; q < 6; ++q) triS[6 * t + q] = A.S[q];
-                triN[3 * t + 0] = (T)ns.x; triN[3 * t + 1] = (T)ns.y; triN[3 * t + 2] = (T)ns.z;
+                triN[3 * t + 0] = (T)D.ns.x; triN[3 * t + 1] = (T)D.ns.y; triN[3 * t + 2] = (T)D.ns.z;
             }
         }
         if (MODE == MODE_LAGGED) {
@@ -481,7 +624,7 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) E8[j] += shfl_x(E8[j], o);
             if (lane == 0)
-                for (int j = 0; j < LG.na; ++j) LG.triE8[(int64_t)j * LG.ns + t] = E8[j];
+                for (int j = 0; j < LG.na; ++j) LG.triE8[(int64_t)j * LG.ns + D.t] = E8[j];
         }
         if (want_alpha) {
 #pragma unroll
@@ -505,22 +648,168 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
 }
 
 // ---------------------------------------------------------------------------
+// the contact evaluation, one thread per sample item
+//
+// The warp-per-triangle kernel leaves most lanes idle when a triangle has
+// few candidates and hides little latency.  Here k_fill_owner maps every
+// item slot to its triangle, k_items evaluates one item per thread and
+// stores its contribution (energy, c1, c2, slave barycentrics, step bound),
+// and k_tri_reduce sums each triangle's items with exactly the lane
+// assignment and shuffle tree of the warp-per-triangle kernel, so the
+// results are bitwise the same.
+// ---------------------------------------------------------------------------
+struct ItemBufs {
+    int32_t* owner;      // [cap] active index of the slot's triangle
+    double* rd;          // [cap][2] energy, step bound
+    void* rt;            // [cap][5] c1, c2, b0, b1, b2 (T)
+    const int32_t* n;    // items requested
+    int64_t cap;
+};
+
+__global__ void k_fill_owner(CandView C, const int32_t* __restrict__ items, ItemBufs B) {
+    if ((int64_t)*B.n > B.cap) return;
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int n_active = *C.n_active;
+    for (int i = warp; i < n_active; i += nwarps) {
+        const int off = items[2 * i], n = items[2 * i + 1];
+        for (int q = lane; q < n; q += 32) B.owner[off + q] = i;
+    }
+}
+
+template <int NK, class T>
+__global__ void __launch_bounds__(64)
+k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
+        const double* __restrict__ dx, const double* __restrict__ dxm, const double* __restrict__ frame,
+        const int32_t* __restrict__ items, ItemBufs B, long long* counters) {
+    const int64_t n = *B.n;
+    if (n > B.cap) return;
+    const bool pre = P.precision == IPC_PREC_MIXED;
+    const bool want_dg = dx != nullptr;
+    long long cnt_f = 0, cnt_e = 0, cnt_p = 0, cnt_eval = 0;
+    T* rt = (T*)B.rt;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        const int i = B.owner[s];
+        const int q = (int)(s - items[2 * i]);
+        const TriData D = load_tri(S, C, x, dx, frame, i);
+        ItemOut o;
+        bool on;
+        if (q < D.nf * NK) {
+            ++cnt_eval;
+            // lane q % 32 of the warp-per-triangle kernel holds sample q % NK
+            const FaceSample F = face_sample(P, D, q % NK, want_dg);
+            on = face_item<NK>(S, P, D, F, xm, dxm, C.face[D.t * C.cap_f + q / NK], pre, want_dg, o);
+            cnt_f += on;
+        } else if (q < D.nf * NK + 2 * D.ne) {
+            const int r = q - D.nf * NK;
+            on = edge_item(S, P, D, xm, dxm, C.edge[D.t * C.cap_e + (r >> 1)], r & 1, pre, want_dg, o);
+            cnt_e += on;
+        } else {
+            const int r = q - D.nf * NK - 2 * D.ne;
+            on = point_item(S, P, D, xm, dxm, C.point[D.t * C.cap_p + r], pre, want_dg, o);
+            cnt_p += on;
+        }
+        double e = 0.0, amin = INFINITY;
+        T c1 = T(0), c2 = T(0), b[3] = {T(0), T(0), T(0)};
+        if (on) {
+            // the arithmetic of sample_add
+            T Bv, dB, d2B;
+            barrier((T)o.g, (T)o.eps, Bv, dB, d2B);
+            const T coef = (T)(o.kq * o.w * o.gamma);
+            e = (double)(coef * Bv);
+            c1 = coef * dB;
+            c2 = rmax(coef * d2B, T(0));
+            for (int c = 0; c < 3; ++c) b[c] = (T)o.b[c];
+            if (want_dg && o.dg < 0.0) amin = 0.9 * o.g / (-o.dg);
+        }
+        B.rd[2 * s] = e;
+        B.rd[2 * s + 1] = amin;
+        rt[5 * s] = c1; rt[5 * s + 1] = c2;
+        rt[5 * s + 2] = b[0]; rt[5 * s + 3] = b[1]; rt[5 * s + 4] = b[2];
+    }
+    if (counters) {
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt_f += shfl_x(cnt_f, o); cnt_e += shfl_x(cnt_e, o);
+            cnt_p += shfl_x(cnt_p, o); cnt_eval += shfl_x(cnt_eval, o);
+        }
+        if ((threadIdx.x & 31) == 0 && (cnt_f | cnt_e | cnt_p | cnt_eval)) {
+            atomic_add_ll(&counters[0], cnt_f); atomic_add_ll(&counters[1], cnt_e);
+            atomic_add_ll(&counters[2], cnt_p); atomic_add_ll(&counters[3], cnt_eval);
+        }
+    }
+}
+
+template <int NK, class T>
+__global__ void __launch_bounds__(256)
+k_tri_reduce(CandView C, const double* __restrict__ frame, const int32_t* __restrict__ items, ItemBufs B,
+             double* __restrict__ triE, T* __restrict__ triG, T* __restrict__ triS, T* __restrict__ triN,
+             unsigned long long* alpha_bits) {
+    if ((int64_t)*B.n > B.cap) return;
+    const int lane = threadIdx.x & 31;
+    const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int n_active = *C.n_active;
+    const T* rt = (const T*)B.rt;
+    for (int i = warp; i < n_active; i += nwarps) {
+        const int64_t t = C.active[i];
+        const int32_t* cnt = C.count + 4 * t;
+        const int nf = min(cnt[0], C.cap_f), ne = min(cnt[1], C.cap_e), np = min(cnt[2], C.cap_p);
+        const int64_t off = items[2 * i];
+        Acc<T> A;
+        A.zero();
+        auto take = [&](int64_t s) {
+            const T b[3] = {rt[5 * s + 2], rt[5 * s + 3], rt[5 * s + 4]};
+            A.add(B.rd[2 * s], rt[5 * s], rt[5 * s + 1], b);
+            A.amin = rmin(A.amin, B.rd[2 * s + 1]);
+        };
+        for (int it = lane; it < nf * NK; it += 32) take(off + it);
+        for (int it = lane; it < ne * 2; it += 32) take(off + nf * NK + it);
+        for (int it = lane; it < np; it += 32) take(off + nf * NK + 2 * ne + it);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            A.E += shfl_x(A.E, o);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) A.G[q] += shfl_x(A.G[q], o);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) A.S[q] += shfl_x(A.S[q], o);
+            A.amin = rmin(A.amin, shfl_x(A.amin, o));
+        }
+        if (lane == 0) {
+            const double* fr = frame + 8 * (int64_t)i;
+            triE[t] = A.E;
+            for (int q = 0; q < 3; ++q) triG[3 * t + q] = A.G[q];
+            for (int q = 0; q < 6; ++q) triS[6 * t + q] = A.S[q];
+            triN[3 * t + 0] = (T)fr[0]; triN[3 * t + 1] = (T)fr[1]; triN[3 * t + 2] = (T)fr[2];
+            if (alpha_bits && A.amin < INFINITY)
+                atomicMin(alpha_bits, (unsigned long long)__double_as_longlong(A.amin));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // deterministic gathers
 // ---------------------------------------------------------------------------
 template <class T, class TO>
-__global__ void k_gather_grad(int64_t nv, const int32_t* __restrict__ off, const int32_t* __restrict__ ent,
-                              const T* __restrict__ triG, const T* __restrict__ triN, TO* __restrict__ out) {
-    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    T g0 = T(0), g1 = T(0), g2 = T(0);
-    for (int k = off[v]; k < off[v + 1]; ++k) {
-        const int e = ent[k];
-        const int64_t t = e >> 2;
-        const int a = e & 3;
-        const T c = triG[3 * t + a];
-        g0 -= c * triN[3 * t]; g1 -= c * triN[3 * t + 1]; g2 -= c * triN[3 * t + 2];
+__global__ void k_gather_grad(const int32_t* __restrict__ off, const int32_t* __restrict__ ent,
+                              const T* __restrict__ triG, const T* __restrict__ triN,
+                              const int32_t* __restrict__ tri_stamp, const int32_t* __restrict__ misc,
+                              const int32_t* __restrict__ v_list, TO* __restrict__ out) {
+    const int n = misc[kSlotVCount];
+    const int32_t ps = misc[kSlotPass];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int64_t v = v_list[i];
+        T g0 = T(0), g1 = T(0), g2 = T(0);
+        for (int k = off[v]; k < off[v + 1]; ++k) {
+            const int e = ent[k];
+            const int64_t t = e >> 2;
+            if (tri_stamp[t] != ps) continue;
+            const int a = e & 3;
+            const T c = triG[3 * t + a];
+            g0 -= c * triN[3 * t]; g1 -= c * triN[3 * t + 1]; g2 -= c * triN[3 * t + 2];
+        }
+        out[3 * v] = (TO)g0; out[3 * v + 1] = (TO)g1; out[3 * v + 2] = (TO)g2;
     }
-    out[3 * v] = (TO)g0; out[3 * v + 1] = (TO)g1; out[3 * v + 2] = (TO)g2;
 }
 
 __device__ __forceinline__ int sym_idx(int a, int b) {
@@ -530,38 +819,57 @@ __device__ __forceinline__ int sym_idx(int a, int b) {
 }
 
 template <class T>
-__global__ void k_gather_hess(int64_t nnzb, const int32_t* __restrict__ off, const int32_t* __restrict__ ent,
-                              const T* __restrict__ triS, const T* __restrict__ triN, T* __restrict__ out) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnzb) return;
-    T h[9];
+__global__ void k_gather_hess(const int32_t* __restrict__ off, const int32_t* __restrict__ ent,
+                              const T* __restrict__ triS, const T* __restrict__ triN,
+                              const int32_t* __restrict__ tri_stamp, const int32_t* __restrict__ misc,
+                              int32_t* const* __restrict__ b_list, const int32_t* __restrict__ b_stamp,
+                              T* __restrict__ out) {
+    const int32_t ps = misc[kSlotPass], hs = misc[kSlotHPass];
+    const int n_cur = misc[kSlotBCount + (hs & 1)], n_prev = misc[kSlotBCount + ((hs + 1) & 1)];
+    const int32_t* cur = b_list[hs & 1];
+    const int32_t* prev = b_list[(hs + 1) & 1];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_cur + n_prev; i += gridDim.x * blockDim.x) {
+        if (i >= n_cur) {
+            // listed by the previous Hessian pass: clear it unless this pass listed it too
+            const int64_t b = prev[i - n_cur];
+            if (b_stamp[b] != hs)
+                for (int q = 0; q < 9; ++q) out[9 * b + q] = T(0);
+            continue;
+        }
+        const int64_t b = cur[i];
+        T h[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) h[q] = T(0);
-    for (int k = off[b]; k < off[b + 1]; ++k) {
-        const int e = ent[k];
-        const int64_t t = e >> 4;
-        const int a = (e >> 2) & 3, c = e & 3;
-        const T s = triS[6 * t + sym_idx(a, c)];
-        const T nn[3] = {triN[3 * t], triN[3 * t + 1], triN[3 * t + 2]};
+        for (int q = 0; q < 9; ++q) h[q] = T(0);
+        for (int k = off[b]; k < off[b + 1]; ++k) {
+            const int e = ent[k];
+            const int64_t t = e >> 4;
+            if (tri_stamp[t] != ps) continue;
+            const int a = (e >> 2) & 3, c = e & 3;
+            const T sv = triS[6 * t + sym_idx(a, c)];
+            const T nn[3] = {triN[3 * t], triN[3 * t + 1], triN[3 * t + 2]};
 #pragma unroll
-        for (int p = 0; p < 3; ++p)
+            for (int p = 0; p < 3; ++p)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) h[3 * p + q] += s * nn[p] * nn[q];
+                for (int q = 0; q < 3; ++q) h[3 * p + q] += sv * nn[p] * nn[q];
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) out[9 * b + q] = h[q];
     }
-#pragma unroll
-    for (int q = 0; q < 9; ++q) out[9 * b + q] = h[q];
 }
 
 // two-pass fixed-order sum of n doubles
 constexpr int kRedThreads = 256;
 constexpr int kRedPer = 8;
-__global__ void k_reduce_partial(const double* __restrict__ in, int64_t n, double* __restrict__ part) {
+// (with stamp: only the entries whose stamp equals *pass count)
+__global__ void k_reduce_partial(const double* __restrict__ in, int64_t n, double* __restrict__ part,
+                                 const int32_t* __restrict__ stamp, const int32_t* __restrict__ pass) {
     __shared__ double sh[kRedThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kRedThreads * kRedPer;
+    const int32_t ps = pass ? *pass : 0;
     double s = 0.0;
     for (int i = 0; i < kRedPer; ++i) {
         const int64_t k = base + (int64_t)i * kRedThreads + threadIdx.x;
-        if (k < n) s += in[k];
+        if (k < n && (!stamp || stamp[k] == ps)) s += in[k];
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
@@ -589,16 +897,49 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t n, doubl
 template <int NK, class T, int MODE>
 cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* Sm, T* N,
                            long long* counters, const double* dx, const double* dxm,
-                           unsigned long long* alpha_bits, LagArgs LG = LagArgs()) {
+                           unsigned long long* alpha_bits, LagArgs LG = LagArgs(), TouchArgs TA = TouchArgs{}) {
     const int threads = 256;
-    const int blocks = sm_count(c.device) * c.tune_samples_bpsm;
+    const int sms = sm_count(c.device);
+    const int blocks = sms * c.tune_samples_bpsm;
     GMCP_CUDA_TRY(c.tri_frame.ensure(8 * (size_t)c.ns + 8));
-    k_tri_frame<<<sm_count(c.device) * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p);
+    if (MODE != MODE_EVAL) {
+        k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
+                                                   nullptr, TouchArgs{});
+        GMCP_CUDA_TRY(cudaGetLastError());
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
+        k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
+            c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG,
+            c.tri_frame.p, nullptr, 0);
+        return cudaGetLastError();
+    }
+    // contact evaluation: one thread per sample item, and the warp-per-
+    // triangle kernel only when the items do not fit the buffer (the
+    // count is known on the device alone; the caller grows the buffer)
+    if (c.cap_items == 0) c.cap_items = std::max<int64_t>((int64_t)1 << 20, c.ns);
+    GMCP_CUDA_TRY(c.tri_items.ensure(2 * (size_t)c.ns + 2));
+    GMCP_CUDA_TRY(c.item_owner.ensure((size_t)c.cap_items));
+    GMCP_CUDA_TRY(c.item_rd.ensure(2 * (size_t)c.cap_items));
+    GMCP_CUDA_TRY(c.item_rt.ensure(5 * sizeof(T) * (size_t)c.cap_items));
+    int32_t* n_items = c.misc_i32.p + 16;
+    GMCP_CUDA_TRY(cudaMemsetAsync(n_items, 0, sizeof(int32_t), c.stream));
+    k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, c.tri_items.p, n_items,
+                                               c.tri_stamp.p, TA);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items};
+    k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    // 64-thread blocks: at ~160 registers a thread, 12 warps fit an SM
+    // (8 with 256-thread blocks)
+    k_items<NK, T><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
+                                                   c.tri_items.p, B, counters);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    k_tri_reduce<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_frame.p, c.tri_items.p, B, c.tri_E.p,
+                                                        G, Sm, N, alpha_bits);
     GMCP_CUDA_TRY(cudaGetLastError());
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
     k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
         c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG,
-        c.tri_frame.p);
+        c.tri_frame.p, n_items, c.cap_items);
     return cudaGetLastError();
 }
 
@@ -617,12 +958,13 @@ int sm_count(int device) {
     return n;
 }
 
-cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out) {
+cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out, const int32_t* stamp,
+                       const int32_t* pass) {
     const int64_t per = (int64_t)kRedThreads * kRedPer;
     const int64_t nb = (n + per - 1) / per;
     GMCP_CUDA_TRY(c.red_tmp.ensure((size_t)nb + 2));
     if (nb > 0) {
-        k_reduce_partial<<<(unsigned)nb, kRedThreads, 0, c.stream>>>(in, n, c.red_tmp.p);
+        k_reduce_partial<<<(unsigned)nb, kRedThreads, 0, c.stream>>>(in, n, c.red_tmp.p, stamp, pass);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     k_reduce_final<<<1, 1024, 0, c.stream>>>(c.red_tmp.p, nb, out);
@@ -633,42 +975,58 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
                          void* grad_dev, bool want_hess, long long* counters, const double* dx,
                          const double* dxm, unsigned long long* alpha_bits) {
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    const bool grad = grad_dev != nullptr, hess = want_hess && c.cb_nnzb > 0;
+    const int sms = sm_count(c.device);
+    const unsigned flat = (unsigned)(sms * 8);
+    int32_t* misc = c.misc_i32.p;
+    k_pass_begin<<<1, 1, 0, c.stream>>>(misc, hess ? 1 : 0);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    const TouchArgs TA{misc, c.v_stamp.p, c.v_list.p, misc + kSlotVCount, c.b_stamp.p,
+                       {c.b_list0.p, c.b_list1.p}, misc + kSlotBCount, c.cb_row.p, c.cb_col.p,
+                       grad ? 1 : 0, hess ? 1 : 0};
     {
         ProfScope ps(c.prof, c.stream, "samples");
         if (f32) {
             if (c.P.nk == 4)
-                GMCP_CUDA_TRY((launch_samples<4, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits)));
+                GMCP_CUDA_TRY((launch_samples<4, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits, LagArgs(), TA)));
             else
-                GMCP_CUDA_TRY((launch_samples<16, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits)));
+                GMCP_CUDA_TRY((launch_samples<16, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits, LagArgs(), TA)));
         } else {
             if (c.P.nk == 4)
-                GMCP_CUDA_TRY((launch_samples<4, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits)));
+                GMCP_CUDA_TRY((launch_samples<4, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits, LagArgs(), TA)));
             else
-                GMCP_CUDA_TRY((launch_samples<16, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits)));
+                GMCP_CUDA_TRY((launch_samples<16, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits, LagArgs(), TA)));
         }
     }
-    const int B = 256;
-    if (grad_dev) {
+    if (grad) {
         ProfScope ps(c.prof, c.stream, "gather_grad");
-        const unsigned g = (unsigned)((c.nv + B - 1) / B);
-        if (f32)
-            k_gather_grad<float, float><<<g, B, 0, c.stream>>>(c.nv, c.vt_off.p, c.vt_ent.p, c.tri_G32.p, c.tri_n32.p, (float*)grad_dev);
-        else
-            k_gather_grad<double, double><<<g, B, 0, c.stream>>>(c.nv, c.vt_off.p, c.vt_ent.p, c.tri_G64.p, c.tri_n64.p, (double*)grad_dev);
-        GMCP_CUDA_TRY(cudaGetLastError());
+        {
+            GMCP_CUDA_TRY(cudaMemsetAsync(grad_dev, 0, (f32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)c.nv,
+                                          c.stream));
+            if (f32)
+                k_gather_grad<float, float><<<flat, 256, 0, c.stream>>>(c.vt_off.p, c.vt_ent.p, c.tri_G32.p, c.tri_n32.p,
+                                                                     c.tri_stamp.p, misc, c.v_list.p, (float*)grad_dev);
+            else
+                k_gather_grad<double, double><<<flat, 256, 0, c.stream>>>(c.vt_off.p, c.vt_ent.p, c.tri_G64.p,
+                                                                       c.tri_n64.p, c.tri_stamp.p, misc, c.v_list.p,
+                                                                       (double*)grad_dev);
+            GMCP_CUDA_TRY(cudaGetLastError());
+        }
     }
-    if (want_hess && c.cb_nnzb > 0) {
+    if (hess) {
         ProfScope ps(c.prof, c.stream, "gather_hess");
-        const unsigned g = (unsigned)((c.cb_nnzb + B - 1) / B);
+        int32_t* const* lists = c.b_lists.p;
         if (f32)
-            k_gather_hess<float><<<g, B, 0, c.stream>>>(c.cb_nnzb, c.cb_src_off.p, c.cb_src.p, c.tri_S32.p, c.tri_n32.p, c.cb_val32.p);
+            k_gather_hess<float><<<flat, 256, 0, c.stream>>>(c.cb_src_off.p, c.cb_src.p, c.tri_S32.p, c.tri_n32.p,
+                                                             c.tri_stamp.p, misc, lists, c.b_stamp.p, c.cb_val32.p);
         else
-            k_gather_hess<double><<<g, B, 0, c.stream>>>(c.cb_nnzb, c.cb_src_off.p, c.cb_src.p, c.tri_S64.p, c.tri_n64.p, c.cb_val64.p);
+            k_gather_hess<double><<<flat, 256, 0, c.stream>>>(c.cb_src_off.p, c.cb_src.p, c.tri_S64.p, c.tri_n64.p,
+                                                              c.tri_stamp.p, misc, lists, c.b_stamp.p, c.cb_val64.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     if (energy_dev) {
         ProfScope ps(c.prof, c.stream, "reduce");
-        GMCP_CUDA_TRY(reduce_sum(c, c.tri_E.p, c.ns, energy_dev));
+        GMCP_CUDA_TRY(reduce_sum(c, c.tri_E.p, c.ns, energy_dev, c.tri_stamp.p, misc + kSlotPass));
     }
     return cudaSuccess;
 }

@@ -239,7 +239,7 @@ struct PinnedIO {
     unsigned long long bits[2];
     long long ctr_ccd[4];
     long long counts[8];
-    int32_t flags[16];
+    int32_t flags[32];
     double energy;
     double pcg[4];
 };
@@ -253,6 +253,12 @@ struct QueryBufs {
 
 struct WarmStart;              // learned warm start (warmstart.cu)
 void ws_destroy(WarmStart* w);
+
+// misc_i32 slots used by the contact evaluation's touched-output lists
+constexpr int kSlotPass = 18;    // contact evaluations so far (stamps of this one)
+constexpr int kSlotHPass = 19;   // those that assembled the Hessian
+constexpr int kSlotVCount = 20;  // vertices listed in this evaluation
+constexpr int kSlotBCount = 21;  // [2] blocks listed, by Hessian-pass parity
 
 // ------------------------------------------------------------------------
 // the context
@@ -309,6 +315,15 @@ struct Ctx {
     // per-call sample outputs
     DBuf<double> tri_E;
     DBuf<double> tri_frame;                     // [n_active][8] frames of the active slave tris
+    DBuf<int32_t> tri_items;                    // [n_active][2] first item slot, item count
+    DBuf<int32_t> item_owner;                   // [cap_items] active index of each item slot
+    DBuf<double> item_rd;                       // [cap_items][2] energy, step bound
+    DBuf<unsigned char> item_rt;                // [cap_items][5] c1, c2, b (FP32 or FP64)
+    int64_t cap_items = 0;
+    // outputs touched by the active triangles (pass stamps and lists)
+    DBuf<int32_t> tri_stamp, v_stamp, b_stamp;  // [ns], [nv], [cb_nnzb]
+    DBuf<int32_t> v_list, b_list0, b_list1;     // [nv], [cb_nnzb] x 2
+    DBuf<int32_t*> b_lists;                     // device copy of {b_list0, b_list1}
     DBuf<double> tri_G64, tri_S64, tri_n64;
     DBuf<float> tri_G32, tri_S32, tri_n32;
     DBuf<double> cb_val64;
@@ -387,7 +402,8 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
                          unsigned long long* alpha_bits = nullptr);
 cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const double* dx,
                               const double* dxm, unsigned long long* alpha_bits);
-cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out);
+cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out, const int32_t* stamp = nullptr,
+                       const int32_t* pass = nullptr);
 int sm_count(int device);
 // frozen-linear ("lagged") contact energy of the samples active at (x, xm),
 // evaluated at x + alphas[j] p for j < na (na <= 8) into energies_dev[j]
