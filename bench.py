@@ -280,28 +280,30 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
-def batched_measurement(dev, n_env=64, steps=20):
+def batched_measurement(dev, n_env=512, steps=20):
     """Batched contact pass: n_env fingertip environments (5 pads of 16-128
     quads of 0.25 mm, 4 samples per slave triangle, around a perturbed convex
     object of 2k-80k triangles), every pad pressed 1.5 dhat toward its
     object, in one pass per step (one grid per environment, persistent
     kernels over all of them, captured CUDA graph, autotuned launch shapes).
-    L2 is flushed between steps."""
-    import dataclasses
+    L2 is flushed between steps.  The environments are generated in worker
+    processes (spawn) and without tetrahedra: the contact pass reads the
+    surfaces only."""
     import torch
     from paper_2605_24339_b300 import binding
     from paper_2605_24339_b300 import scenes as S
     t0 = time.perf_counter()
-    sc = S.fingertip_batch(n_env=n_env)
-    x_np = S.press_pads(sc, 1.5 * sc.params["dhat"])
-    # the contact pass needs the surfaces only
-    sc = dataclasses.replace(sc, tets=np.zeros((0, 4), dtype=np.int32),
-                             env_tet_off=np.zeros(sc.n_env + 1, dtype=np.int64))
+    dhat = 1e-4
+    sc, x_np = S.fingertip_batch(n_env=n_env, dhat=dhat, pressed=1.5 * dhat, with_tets=False,
+                                 workers=max(1, min(32, os.cpu_count() or 1)))
     gen_s = time.perf_counter() - t0
     rng = np.random.default_rng(5)
     dx_np = np.zeros_like(x_np)
     dx_np[:, :] = -1e-6 * (x_np - x_np.mean(axis=0)) / np.linalg.norm(x_np - x_np.mean(axis=0), axis=1)[:, None]
+    t1 = time.perf_counter()
     ctx = binding.Context(sc, precision="mixed", device=dev)
+    torch.cuda.synchronize()
+    create_s = time.perf_counter() - t1
     x = torch.as_tensor(x_np, device="cuda")
     dx = torch.as_tensor(dx_np, device="cuda")
     xm = torch.as_tensor(sc.Y0, device="cuda")
@@ -338,6 +340,7 @@ def batched_measurement(dev, n_env=64, steps=20):
     torch.cuda.synchronize()
     ctx.profile_stop()
     prof = ctx.profile_read()
+    free_b, total_b = torch.cuda.mem_get_info()
     ctx.close()
     ms = total / steps
     return {"workload": f"fingertip_batch {n_env} envs x 5 pads (16-128 quads, 4 samples/tri) vs "
@@ -350,7 +353,8 @@ def batched_measurement(dev, n_env=64, steps=20):
             "ms_per_pass": ms, "samples_per_s": units / (ms / 1e3),
             "autotuned_blocks_per_sm": {"samples": tune_s, "query": tune_q},
             "sections_ms": {k: round(v["ms"] / max(v["calls"], 1), 4) for k, v in prof.items()},
-            "alpha": info["alpha"], "scene_build_s": round(gen_s, 1)}
+            "alpha": info["alpha"], "scene_build_s": round(gen_s, 1), "context_create_s": round(create_s, 1),
+            "gpu_mem_used_gb": round((total_b - free_b) / 1e9, 1)}
 
 
 def newton_measurement(dev, start_step=20, n_states=4):
@@ -596,7 +600,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-envs measurement")
     ap.add_argument("--no-newton", action="store_true",
                     help="skip the time-step measurement (newton_step key)")
-    ap.add_argument("--batch-envs", type=int, default=64,
+    ap.add_argument("--batch-envs", type=int, default=512,
                     help="environments in the batched measurement")
     ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "

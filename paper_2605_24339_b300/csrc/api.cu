@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "gmcp_internal.cuh"
@@ -57,22 +58,37 @@ int32_t env_of(const std::vector<int64_t>& off, int64_t i) {
 // in increasing triangle id
 void tri_edges(const int32_t* tris, int64_t n, std::vector<int32_t>& edges,
                std::vector<int32_t>& off, std::vector<int32_t>& adj) {
-    std::vector<std::array<int32_t, 3>> tr((size_t)n * 3);
+    // every (min vertex, max vertex, tri) triple, in lexicographic order:
+    // bucketed by the min vertex (counting sort), each bucket sorted by (max
+    // vertex, tri); buckets are short (the vertex's incident edges)
+    int32_t nvert = 0;
+    for (int64_t i = 0; i < 3 * n; ++i) nvert = std::max(nvert, tris[i] + 1);
+    std::vector<int64_t> boff((size_t)nvert + 1, 0);
     for (int64_t t = 0; t < n; ++t)
-        for (int k = 0; k < 3; ++k) {
-            int32_t a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
-            tr[3 * t + k] = {std::min(a, b), std::max(a, b), (int32_t)t};
-        }
-    std::sort(tr.begin(), tr.end());
-    edges.clear(); off.clear(); adj.clear();
-    for (size_t i = 0; i < tr.size(); ++i) {
-        if (i == 0 || tr[i][0] != tr[i - 1][0] || tr[i][1] != tr[i - 1][1]) {
-            edges.push_back(tr[i][0]); edges.push_back(tr[i][1]);
-            off.push_back((int32_t)i);
-        }
-        adj.push_back(tr[i][2]);
+        for (int k = 0; k < 3; ++k) boff[(size_t)std::min(tris[3 * t + k], tris[3 * t + (k + 1) % 3]) + 1]++;
+    for (int32_t v = 0; v < nvert; ++v) boff[v + 1] += boff[v];
+    std::vector<std::pair<int32_t, int32_t>> tr((size_t)n * 3);   // (max vertex, tri)
+    {
+        std::vector<int64_t> cur(boff.begin(), boff.end() - 1);
+        for (int64_t t = 0; t < n; ++t)
+            for (int k = 0; k < 3; ++k) {
+                const int32_t a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+                tr[(size_t)cur[std::min(a, b)]++] = {std::max(a, b), (int32_t)t};
+            }
     }
-    off.push_back((int32_t)tr.size());
+    edges.clear(); off.clear(); adj.clear();
+    adj.reserve(tr.size());
+    for (int32_t v = 0; v < nvert; ++v) {
+        std::sort(tr.begin() + boff[v], tr.begin() + boff[v + 1]);
+        for (int64_t i = boff[v]; i < boff[v + 1]; ++i) {
+            if (i == boff[v] || tr[i].first != tr[i - 1].first) {
+                edges.push_back(v); edges.push_back(tr[i].first);
+                off.push_back((int32_t)adj.size());
+            }
+            adj.push_back(tr[i].second);
+        }
+    }
+    off.push_back((int32_t)adj.size());
 }
 
 __global__ void k_count_sum(const int32_t* __restrict__ cnt, int64_t ns, long long* out) {
@@ -687,23 +703,37 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
             for (int k = 0; k < 3; ++k) vt_ent[cur[sc->s_tris[3 * t + k]]++] = (int32_t)(t * 4 + k);
     }
     // --- contact BSR pattern: blocks (T[a], T[b]) of every slave tri, with
-    // the contributing (tri, a, b) in increasing order
-    std::vector<std::array<int64_t, 3>> blk((size_t)ns * 9);
+    // the contributing (tri, a, b) in increasing order.  The 9 entries of
+    // every tri are bucketed by row T[a] (counting sort) and each row sorted
+    // by (column, source), which is the lexicographic order of (row, column,
+    // source); rows are short (the vertex's incident tris).
+    std::vector<int64_t> boff(nv + 1, 0);
     for (int64_t t = 0; t < ns; ++t)
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b)
-                blk[9 * t + 3 * a + b] = {sc->s_tris[3 * t + a], sc->s_tris[3 * t + b], t * 16 + a * 4 + b};
-    std::sort(blk.begin(), blk.end());
-    std::vector<int32_t> row(nv + 1, 0), col, src_off, src;
-    for (size_t i = 0; i < blk.size(); ++i) {
-        if (i == 0 || blk[i][0] != blk[i - 1][0] || blk[i][1] != blk[i - 1][1]) {
-            col.push_back((int32_t)blk[i][1]);
-            src_off.push_back((int32_t)i);
-            row[blk[i][0] + 1]++;
-        }
-        src.push_back((int32_t)blk[i][2]);
+        for (int a = 0; a < 3; ++a) boff[sc->s_tris[3 * t + a] + 1] += 3;
+    for (int64_t v = 0; v < nv; ++v) boff[v + 1] += boff[v];
+    std::vector<std::pair<int32_t, int32_t>> be((size_t)ns * 9);   // (column, source)
+    {
+        std::vector<int64_t> cur(boff.begin(), boff.end() - 1);
+        for (int64_t t = 0; t < ns; ++t)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    be[(size_t)cur[sc->s_tris[3 * t + a]]++] = {sc->s_tris[3 * t + b], (int32_t)(t * 16 + a * 4 + b)};
     }
-    src_off.push_back((int32_t)blk.size());
+    std::vector<int32_t> row(nv + 1, 0), col, src_off, src;
+    src.reserve(be.size());
+    for (int64_t v = 0; v < nv; ++v) {
+        std::sort(be.begin() + boff[v], be.begin() + boff[v + 1]);
+        for (int64_t i = boff[v]; i < boff[v + 1]; ++i) {
+            if (i == boff[v] || be[i].first != be[i - 1].first) {
+                col.push_back(be[i].first);
+                src_off.push_back((int32_t)src.size());
+                row[v + 1]++;
+            }
+            src.push_back(be[i].second);
+        }
+    }
+    src_off.push_back((int32_t)src.size());
+    std::vector<std::pair<int32_t, int32_t>>().swap(be);
     for (int64_t v = 0; v < nv; ++v) row[v + 1] += row[v];
     c.cb_nnzb = (int64_t)col.size();
     c.h_cb_row = row;

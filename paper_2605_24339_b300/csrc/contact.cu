@@ -169,6 +169,24 @@ __device__ __forceinline__ bool plane_gap_maybe(V3<float> ns, V3<float> a, V3<fl
     return !(rmin(da, db) > eps_max * (1.0f + 1e-6f) + tol || rmax(da, db) < -tol);
 }
 
+// FP32 barycentric coordinates of p (relative to x0) in the slave frame
+// (e1, e2 = x1 - x0, x2 - x0), with a bound on their error: Gram formula
+// (as bary), each rounding 2^-24 relative; tol below exceeds 100 times the
+// first-order error bound, plus 1e-3.  ok is false for a degenerate frame.
+__device__ __forceinline__ void bary_f(V3<float> p, V3<float> e1, V3<float> e2, float* b, float& tol,
+                                       bool& ok) {
+    const float a = dot(e1, e1), bb = dot(e1, e2), c = dot(e2, e2);
+    const float r1 = dot(p, e1), r2 = dot(p, e2);
+    const float det = a * c - bb * bb;
+    ok = det > 1e-6f * a * c;
+    const float v = (c * r1 - bb * r2) / det;
+    const float w = (a * r2 - bb * r1) / det;
+    b[0] = 1.0f - v - w; b[1] = v; b[2] = w;
+    const float mag = c * fabsf(r1) + fabsf(bb * r2) + a * fabsf(r2) + fabsf(bb * r1) +
+                      (a * c + bb * bb) * (fabsf(v) + fabsf(w));
+    tol = 1e-3f + 1e-5f * mag / det;
+}
+
 // squared distance between two boxes (0 when they overlap)
 __device__ __forceinline__ double box_dist2(const double* alo, const double* ahi, const double* blo,
                                             const double* bhi) {
@@ -351,6 +369,7 @@ struct TriData {
     int64_t t;
     V3<double> x0, x1, x2, X0, X1, X2, dx0, dx1, dx2, ns, ns0;
     V3<float> ns_f;
+    V3<float> e1_f, e2_f;  // x1 - x0, x2 - x0 (FP64 differences, rounded)
     double As;
     float tol_abs;
     const double* sb;      // rest box of the slave tri
@@ -370,6 +389,8 @@ __device__ __forceinline__ TriData load_tri(const SceneView& S, const CandView& 
     D.ns0 = {fr[4], fr[5], fr[6]};
     D.tol_abs = (float)fr[7];
     D.ns_f = tof(D.ns);
+    D.e1_f = tof(D.x1 - D.x0);
+    D.e2_f = tof(D.x2 - D.x0);
     D.sb = S.srest_box + 6 * D.t;
     const int32_t* cnt = C.count + 4 * D.t;
     D.nf = min(cnt[0], C.cap_f); D.ne = min(cnt[1], C.cap_e); D.np = min(cnt[2], C.cap_p);
@@ -443,7 +464,19 @@ __device__ __forceinline__ bool edge_item(const SceneView& S, const Params& P, c
     const double gp = 1.0 / sqrt(3.0);
     const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
     const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
-    if (pre && !plane_gap_maybe(D.ns_f, tof(ya - D.x0), tof(yb - D.x0), (float)eps_max, D.tol_abs)) return false;
+    if (pre) {
+        const V3<float> da = tof(ya - D.x0), db = tof(yb - D.x0);
+        if (!plane_gap_maybe(D.ns_f, da, db, (float)eps_max, D.tol_abs)) return false;
+        // the projected edge misses the slave tri when both ends are certainly
+        // on the outer side of one of its edges (beta_a is affine along it)
+        float fa[3], fb[3], ta, tb;
+        bool oka, okb;
+        bary_f(da, D.e1_f, D.e2_f, fa, ta, oka);
+        bary_f(db, D.e1_f, D.e2_f, fb, tb, okb);
+        if (oka && okb)
+            for (int a = 0; a < 3; ++a)
+                if (fa[a] < -ta && fb[a] < -tb) return false;
+    }
     const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
     if (!any_facing(S, xm, S.me_tri + a0, a1 - a0, D.ns)) return false;
     double bA[3], bB[3];
@@ -504,6 +537,10 @@ __device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, 
     if (pre) {
         const V3<float> d = tof(y - D.x0);
         if (!plane_gap_maybe(D.ns_f, d, d, (float)eps_max, D.tol_abs)) return false;
+        float f[3], tf;
+        bool ok;
+        bary_f(d, D.e1_f, D.e2_f, f, tf, ok);
+        if (ok && min3(f) < -tf) return false;
     }
     const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
     if (!any_facing(S, xm, S.mv_tri + a0, a1 - a0, D.ns)) return false;

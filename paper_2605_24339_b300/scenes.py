@@ -63,7 +63,7 @@ _PERMS = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
 
 
 def pad_slab(nx: int, ny: int, nz: int, dx: float, dz: float,
-             origin=(0.0, 0.0, 0.0)):
+             origin=(0.0, 0.0, 0.0), with_tets: bool = True):
     """Structured tetrahedral slab.
 
     Returns ``(X, tets, bottom_tris, top_mask)``: rest positions ``[nv,3]``
@@ -71,6 +71,7 @@ def pad_slab(nx: int, ny: int, nz: int, dx: float, dz: float,
     triangles ``[2*nx*ny,3]`` int32 oriented so that ``(x1-x0)x(x2-x0)``
     points to -z (out of the slab), and a bool mask of the top-face vertices.
     Vertex (i,j,k) has index ``i + (nx+1)*(j + (ny+1)*k)``; k=0 is the bottom.
+    ``with_tets=False`` returns an empty tet array (surface-only workloads).
     """
     ox, oy, oz = origin
     i = np.arange(nx + 1)
@@ -85,8 +86,8 @@ def pad_slab(nx: int, ny: int, nz: int, dx: float, dz: float,
 
     ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
     ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
-    tets = []
-    for p in _PERMS:
+    tets = [np.zeros((0, 4), dtype=np.int64)]
+    for p in (_PERMS if with_tets else []):
         off = np.zeros((4, 3), dtype=np.int64)
         for s in range(1, 4):
             off[s] = off[s - 1]
@@ -390,42 +391,68 @@ def gel_on_terrain(n_quads=256, dx=1e-4, nz=8, thick=2e-3, terrain_quads=316,
                        "gel_on_terrain", n_steps)
 
 
+def _fingertip_env(e, pads_per_env, quad_range, dx, nz, thick, tri_range, radius, dhat, kappa, h,
+                   press_speed, n_steps, seed, face_rule_level, pressed, with_tets):
+    """Environment e of fingertip_batch (a function of its arguments only, so
+    that environments can be built in worker processes); with ``pressed``
+    also the pad positions moved that far toward the object."""
+    rng = np.random.Generator(np.random.PCG64(seed + e))
+    T = int(rng.integers(tri_range[0], tri_range[1] + 1))
+    Y, F = _fib_hull_sphere(T // 2 + 2, radius, (0.0, 0.0, 0.0), rng)
+    rmax = float(np.linalg.norm(Y, axis=1).max())
+    Xs, Ts, Ss, Ds, Vd, Xq = [], [], [], [], [], []
+    nvo = 0
+    dirs = _pad_dirs(pads_per_env)
+    for k in range(pads_per_env):
+        nq = int(rng.integers(quad_range[0], quad_range[1] + 1))
+        side = nq * dx
+        Xp, tp, bp, topm = pad_slab(nq, nq, nz, dx, thick / nz,
+                                    origin=(-side / 2, -side / 2, 0.0), with_tets=with_tets)
+        # rotate the pad so its bottom normal (-z) points at the centre
+        R = _frame_from_dir(dirs[k])
+        Xr = Xp @ R.T
+        Xp = Xr + dirs[k] * (rmax + 2 * dhat)
+        if pressed is not None:
+            Xq.append(Xr + dirs[k] * (rmax + 2 * dhat) - dirs[k] * pressed)
+        vd = np.zeros_like(Xp)
+        vd[topm] = -dirs[k] * press_speed
+        Xs.append(Xp); Ts.append(tp + nvo); Ss.append(bp + nvo)
+        Ds.append(topm.astype(np.uint8)); Vd.append(vd)
+        nvo += Xp.shape[0]
+    X = np.concatenate(Xs)
+    S = np.concatenate(Ss)
+    p = _finish_params(default_params(dhat=dhat, kappa=kappa, h=h,
+                                      face_rule_level=face_rule_level), X, S)
+    sc = _single_env(X, np.concatenate(Ts), S, np.concatenate(Ds), Y, F,
+                     np.concatenate(Vd), p, f"env{e}", n_steps)
+    return sc if pressed is None else (sc, np.concatenate(Xq))
+
+
 def fingertip_batch(n_env=512, pads_per_env=5, quad_range=(16, 128), dx=0.25e-3,
                     nz=2, thick=0.5e-3, tri_range=(2000, 80000), radius=15e-3,
                     dhat=1e-4, kappa=1e5, h=1e-3, press_speed=0.5e-3,
-                    n_steps=100, seed=3, face_rule_level=1) -> Scene:
+                    n_steps=100, seed=3, face_rule_level=1, pressed=None,
+                    with_tets=True, workers=1):
     """Many independent envs: each has ``pads_per_env`` square pads of side
     U{quad_range} quads facing the centre of a perturbed convex sphere with
-    U[tri_range] triangles, 2*dhat away from its surface."""
-    envs = []
-    for e in range(n_env):
-        rng = np.random.Generator(np.random.PCG64(seed + e))
-        T = int(rng.integers(tri_range[0], tri_range[1] + 1))
-        Y, F = _fib_hull_sphere(T // 2 + 2, radius, (0.0, 0.0, 0.0), rng)
-        rmax = float(np.linalg.norm(Y, axis=1).max())
-        Xs, Ts, Ss, Ds, Vd = [], [], [], [], []
-        nvo = 0
-        dirs = _pad_dirs(pads_per_env)
-        for k in range(pads_per_env):
-            nq = int(rng.integers(quad_range[0], quad_range[1] + 1))
-            side = nq * dx
-            Xp, tp, bp, topm = pad_slab(nq, nq, nz, dx, thick / nz,
-                                        origin=(-side / 2, -side / 2, 0.0))
-            # rotate the pad so its bottom normal (-z) points at the centre
-            R = _frame_from_dir(dirs[k])
-            Xp = Xp @ R.T + dirs[k] * (rmax + 2 * dhat)
-            vd = np.zeros_like(Xp)
-            vd[topm] = -dirs[k] * press_speed
-            Xs.append(Xp); Ts.append(tp + nvo); Ss.append(bp + nvo)
-            Ds.append(topm.astype(np.uint8)); Vd.append(vd)
-            nvo += Xp.shape[0]
-        X = np.concatenate(Xs)
-        S = np.concatenate(Ss)
-        p = _finish_params(default_params(dhat=dhat, kappa=kappa, h=h,
-                                          face_rule_level=face_rule_level), X, S)
-        envs.append(_single_env(X, np.concatenate(Ts), S, np.concatenate(Ds), Y, F,
-                                np.concatenate(Vd), p, f"env{e}", n_steps))
-    return concat_envs(envs, name="fingertip_batch")
+    U[tri_range] triangles, 2*dhat away from the sphere's largest radius.
+    With ``pressed`` (a distance) returns ``(scene, x)``, x the pads moved
+    that far toward their objects (what press_pads gives, without needing
+    the tets).  ``workers > 1`` builds the envs in that many worker processes
+    (started with spawn); the result does not depend on it."""
+    args = (pads_per_env, quad_range, dx, nz, thick, tri_range, radius, dhat, kappa, h,
+            press_speed, n_steps, seed, face_rule_level, pressed, with_tets)
+    if workers > 1 and n_env > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            out = list(ex.map(_fingertip_env, range(n_env), *[[a] * n_env for a in args],
+                              chunksize=max(1, n_env // (4 * workers))))
+    else:
+        out = [_fingertip_env(e, *args) for e in range(n_env)]
+    if pressed is None:
+        return concat_envs(out, name="fingertip_batch")
+    return concat_envs([o[0] for o in out], name="fingertip_batch"), np.concatenate([o[1] for o in out])
 
 
 def _pad_dirs(n):
