@@ -285,8 +285,8 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.qswept.boxf.p, (uintptr_t)c.qswept.vboxf.p, (uintptr_t)c.qswept.cell.p,
             (uintptr_t)c.mboxf.p, (uintptr_t)c.ccd_pairs.p, (uintptr_t)c.cap_ccd, (uintptr_t)c.coarse_pairs.p,
             (uintptr_t)c.cap_coarse, (uintptr_t)c.coarse_swept.p, (uintptr_t)c.cap_coarse_swept,
-            (uintptr_t)c.ccd_stream, (uintptr_t)c.mbox.p,
-            (uintptr_t)c.mcell.p, (uintptr_t)c.mcell_hi.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
+            (uintptr_t)c.ccd_stream,
+            (uintptr_t)c.mcell.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
             (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_frame.p, (uintptr_t)c.tri_items.p, (uintptr_t)c.item_owner.p,
             (uintptr_t)c.item_rd.p, (uintptr_t)c.item_rt.p, (uintptr_t)c.cap_items, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
             (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,

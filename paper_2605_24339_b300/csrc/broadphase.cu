@@ -181,9 +181,8 @@ __constant__ float c_rule_f[2][16][6];
 // grid build
 // ---------------------------------------------------------------------------
 __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
-                                 const double* __restrict__ dxm, double* __restrict__ mbox,
-                                 float* __restrict__ mboxf, int4* __restrict__ mcell,
-                                 int4* __restrict__ mcell_hi, int32_t* __restrict__ cnt) {
+                                 const double* __restrict__ dxm, float* __restrict__ mboxf,
+                                 int4* __restrict__ mcell, int32_t* __restrict__ cnt) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int32_t* T = S.mtri + 3 * m;
@@ -207,35 +206,44 @@ __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
             hi[c] = kmax3(v[0][c], v[1][c], v[2][c]);
         }
     }
-    // exact FP64 box, and its conservative FP32 bounds for the coarse tests
+    // conservative FP32 bounds of the exact FP64 box (the exact box itself is
+    // formed again, from the vertices, for the few pairs the exact tests see)
     for (int c = 0; c < 3; ++c) {
         flo[c] = lo_f32(lo[c]); fhi[c] = hi_f32(hi[c]);
         mag[c] = fabsf(flo[c]) + fabsf(fhi[c]);
-        mbox[6 * m + c] = lo[c]; mbox[6 * m + 3 + c] = hi[c];
         mboxf[6 * m + c] = flo[c]; mboxf[6 * m + 3 + c] = fhi[c];
     }
     const int e = S.mtri_env[m];
     I3 a, b;
     cell_range_f(S, e, flo, fhi, mag, a, b);
     mcell[m] = make_int4(a.x, a.y, a.z, e);
-    mcell_hi[m] = make_int4(b.x, b.y, b.z, 0);
     for (int iz = a.z; iz <= b.z; ++iz)
         for (int iy = a.y; iy <= b.y; ++iy)
             for (int ix = a.x; ix <= b.x; ++ix) atomicAdd(&cnt[cell_id(S, e, ix, iy, iz)], 1);
 }
 
-__global__ void k_mtri_fill(SceneView S, const int4* __restrict__ mcell, const int4* __restrict__ mcell_hi,
-                            const int32_t* __restrict__ start, int32_t* __restrict__ cursor,
-                            int32_t* __restrict__ ent, int64_t cap, int32_t* __restrict__ overflow) {
+// Fill: the same cell range as the count (recomputed from the same FP32
+// box), each entry at the next free position of its cell.  cur holds the
+// exclusive scan of the counts and is advanced in place, so that afterwards
+// cur[c] is the end of cell c; the cell start array is cur shifted by one
+// (start[0] = 0, start[c + 1] = cur[c]).
+__global__ void k_mtri_fill(SceneView S, const float* __restrict__ mboxf, const int4* __restrict__ mcell,
+                            int32_t* __restrict__ cur, int32_t* __restrict__ ent, int64_t cap,
+                            int32_t* __restrict__ overflow) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
-    const int4 a = mcell[m], b = mcell_hi[m];
-    const int e = a.w;
+    const int e = mcell[m].w;
+    float flo[3], fhi[3], mag[3];
+    for (int c = 0; c < 3; ++c) {
+        flo[c] = mboxf[6 * m + c]; fhi[c] = mboxf[6 * m + 3 + c];
+        mag[c] = fabsf(flo[c]) + fabsf(fhi[c]);
+    }
+    I3 a, b;
+    cell_range_f(S, e, flo, fhi, mag, a, b);
     for (int iz = a.z; iz <= b.z; ++iz)
         for (int iy = a.y; iy <= b.y; ++iy)
             for (int ix = a.x; ix <= b.x; ++ix) {
-                int64_t c = cell_id(S, e, ix, iy, iz);
-                int pos = start[c] + atomicAdd(&cursor[c], 1);
+                const int pos = atomicAdd(&cur[cell_id(S, e, ix, iy, iz)], 1);
                 if (pos < cap) ent[pos] = (int32_t)m;
                 else atomicMax(overflow, 1);
             }
@@ -252,6 +260,28 @@ __device__ __forceinline__ void swept_vert(const double* P, const double* D, int
 __device__ __forceinline__ void grow_box(double* lo, double* hi, const double* l2, const double* h2) {
     for (int c = 0; c < 3; ++c) { lo[c] = dmin_(lo[c], l2[c]); hi[c] = dmax_(hi[c], h2[c]); }
 }
+// exact FP64 box of master tri m: of its vertices, or of their motion from
+// xm to xm + dxm when dxm is given (the box the grid build bounds in FP32)
+__device__ __forceinline__ void exact_mbox(const SceneView& S, const double* xm, const double* dxm,
+                                           int64_t m, double* lo, double* hi) {
+    const int32_t* T = S.mtri + 3 * m;
+    if (dxm) {
+        double l2[3], h2[3];
+        swept_vert(xm, dxm, T[0], lo, hi);
+        swept_vert(xm, dxm, T[1], l2, h2);
+        grow_box(lo, hi, l2, h2);
+        swept_vert(xm, dxm, T[2], l2, h2);
+        grow_box(lo, hi, l2, h2);
+    } else {
+        double v[3][3];
+        for (int a = 0; a < 3; ++a) load3(xm, T[a], v[a]);
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = kmin3(v[0][c], v[1][c], v[2][c]);
+            hi[c] = kmax3(v[0][c], v[1][c], v[2][c]);
+        }
+    }
+}
+
 // insertion sort of a short list held in global memory
 __device__ void sort_small(int32_t* a, int n) {
     for (int i = 1; i < n; ++i) {
@@ -515,7 +545,7 @@ template <int NK>
 __global__ void __launch_bounds__(256)
 k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
                 const double* __restrict__ x, const double* __restrict__ xm,
-                const double* __restrict__ mbox, const float* __restrict__ mboxf) {
+                const float* __restrict__ mboxf) {
     const int n = min(*W.n, W.cap);
     const double eps = P.dhat;
     // eps rounded up, with a relative slack that covers the FP64 rounding of
@@ -561,7 +591,8 @@ k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
         if (maybe) {
             double x0[3], x1[3], x2[3];
             load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
-            const double* B = mbox + 6 * (int64_t)m;
+            double B[6];
+            exact_mbox(S, xm, nullptr, m, B, B + 3);
             const double l0 = B[0] - eps, l1 = B[1] - eps, l2 = B[2] - eps;
             const double h0 = B[3] + eps, h1 = B[4] + eps, h2 = B[5] + eps;
             bool hit = false;
@@ -805,8 +836,7 @@ __device__ __forceinline__ int corner_of(const int32_t* T, int32_t v) {
 __global__ void __launch_bounds__(256)
 k_ccd_exact(SceneView S, QueryList Q, PairList C, const double* __restrict__ x,
             const double* __restrict__ dx, const double* __restrict__ xm0,
-            const double* __restrict__ dxm, const double* __restrict__ mbox,
-            const float* __restrict__ mboxf, PairList L) {
+            const double* __restrict__ dxm, const float* __restrict__ mboxf, PairList L) {
     const int n = min(*C.n, C.cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int2 pr = C.p[i];
@@ -823,9 +853,9 @@ k_ccd_exact(SceneView S, QueryList Q, PairList C, const double* __restrict__ x,
             if (v < 0) continue;
             const float* b = vb + 6 * corner_of(T, v);
             if (!overlap_keep(b, b + 3, Bf, Bf + 3)) continue;
-            double vlo[3], vhi[3];
+            double vlo[3], vhi[3], B[6];
             swept_vert(x, dx, v, vlo, vhi);
-            const double* B = mbox + 6 * (int64_t)m;
+            exact_mbox(S, xm0, dxm, m, B, B + 3);
             if (overlap(vlo, vhi, B, B + 3)) emit_pair(L, 0, v, m);
         }
         // master vertices owned by m vs slave triangle t
@@ -966,22 +996,21 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     ProfScope ps(c.prof, c.stream, "grid");
     SceneView S = c.view();
     cudaStream_t s = c.stream;
-    GMCP_CUDA_TRY(c.mbox.ensure(6 * (size_t)c.nmt + 6));
     GMCP_CUDA_TRY(c.mcell.ensure((size_t)c.nmt + 1));
-    GMCP_CUDA_TRY(c.mcell_hi.ensure((size_t)c.nmt + 1));
     GMCP_CUDA_TRY(c.mboxf.ensure(6 * (size_t)c.nmt + 6));
     GMCP_CUDA_TRY(c.cell_cnt.ensure((size_t)c.n_cells + 1));
-    GMCP_CUDA_TRY(c.cell_start.ensure((size_t)c.n_cells + 1));
+    GMCP_CUDA_TRY(c.cell_start.ensure((size_t)c.n_cells + 2));
     GMCP_CUDA_TRY(c.scan_tmp.ensure(2 * scan_tmp_size(c.n_cells)));
     GMCP_CUDA_TRY(cudaMemsetAsync(c.cell_cnt.p, 0, sizeof(int32_t) * (c.n_cells + 1), s));
     const int B = 256;
     const unsigned g = (unsigned)((c.nmt + B - 1) / B);
     if (c.nmt > 0) {
-        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mbox.p, c.mboxf.p, c.mcell.p,
-                                         c.mcell_hi.p, c.cell_cnt.p);
+        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mboxf.p, c.mcell.p, c.cell_cnt.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
-    GMCP_CUDA_TRY(exclusive_scan_i32(c.cell_cnt.p, c.cell_start.p, c.n_cells, c.scan_tmp.p,
+    // scan into start + 1 (start[0] = 0), which the fill advances in place
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.cell_start.p, 0, sizeof(int32_t), s));
+    GMCP_CUDA_TRY(exclusive_scan_i32(c.cell_cnt.p, c.cell_start.p + 1, c.n_cells, c.scan_tmp.p,
                                      c.scan_tmp.n, s));
     if (lazy) {
         // Cells are at least the mean master extent, so a triangle spans a few
@@ -991,14 +1020,13 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
         GMCP_CUDA_TRY(c.cell_ent.ensure(std::max<size_t>(27 * (size_t)c.nmt + 1, c.cell_ent.n)));
     } else {
         int32_t total = 0;
-        GMCP_CUDA_TRY(cudaMemcpyAsync(&total, c.cell_start.p + c.n_cells, sizeof(int32_t),
+        GMCP_CUDA_TRY(cudaMemcpyAsync(&total, c.cell_start.p + 1 + c.n_cells, sizeof(int32_t),
                                       cudaMemcpyDeviceToHost, s));
         GMCP_CUDA_TRY(cudaStreamSynchronize(s));
         GMCP_CUDA_TRY(c.cell_ent.ensure((size_t)total + 1));
     }
-    GMCP_CUDA_TRY(cudaMemsetAsync(c.cell_cnt.p, 0, sizeof(int32_t) * (c.n_cells + 1), s));
     if (c.nmt > 0) {
-        k_mtri_fill<<<g, B, 0, s>>>(S, c.mcell.p, c.mcell_hi.p, c.cell_start.p, c.cell_cnt.p, c.cell_ent.p,
+        k_mtri_fill<<<g, B, 0, s>>>(S, c.mboxf.p, c.mcell.p, c.cell_start.p + 1, c.cell_ent.p,
                                     (int64_t)c.cell_ent.n, c.misc_i32.p + 12);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
@@ -1060,9 +1088,9 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
                                                           c.cell_ent.p, W);
         GMCP_CUDA_TRY(cudaGetLastError());
         if (P.nk == 4)
-            k_contact_exact<4><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mbox.p, c.mboxf.p);
+            k_contact_exact<4><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mboxf.p);
         else
-            k_contact_exact<16><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mbox.p, c.mboxf.p);
+            k_contact_exact<16><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mboxf.p);
         GMCP_CUDA_TRY(cudaGetLastError());
         if (lazy) break;   // the caller reads the overflow slot after it synchronises
         int32_t need = 0;
@@ -1107,7 +1135,7 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
         k_query_walk<<<persistent_blocks(c), 256, 0, c.stream>>>(S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
                                                                c.cell_ent.p, C);
         GMCP_CUDA_TRY(cudaGetLastError());
-        k_ccd_exact<<<flat, 256, 0, c.stream>>>(S, Q, C, x, dx, xm0, dxm, c.mbox.p, c.mboxf.p, L);
+        k_ccd_exact<<<flat, 256, 0, c.stream>>>(S, Q, C, x, dx, xm0, dxm, c.mboxf.p, L);
         GMCP_CUDA_TRY(cudaGetLastError());
         k_accd_pairs<<<flat, 256, 0, c.stream>>>(S, c.P, L, x, dx, xm0, dxm, alpha_bits, counters);
         GMCP_CUDA_TRY(cudaGetLastError());

@@ -297,9 +297,7 @@ struct Ctx {
     int64_t cb_nnzb = 0;
 
     // per-call broad-phase buffers
-    DBuf<double> mbox;                          // [nmt][6]
     DBuf<int4> mcell;                           // [nmt] lowest cell (x, y, z) and env
-    DBuf<int4> mcell_hi;                        // [nmt] highest cell (x, y, z)
     DBuf<float> mboxf;                          // conservative FP32 master boxes
     DBuf<int2> ccd_pairs;                       // primitive pairs for ACCD
     DBuf<int2> coarse_pairs, coarse_swept;      // (query entry, master) pairs: contact, swept
