@@ -307,6 +307,19 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// Slots for the lanes with pred set, reserved by one atomic for the whole
+// warp (a counter that every thread bumps serialises at its L2 slice).
+// All 32 lanes must call it.
+__device__ __forceinline__ int warp_reserve(bool pred, int32_t* counter) {
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    if (mask == 0u) return 0;
+    const int leader = __ffs(mask) - 1;
+    int base = 0;
+    if ((int)(threadIdx.x & 31) == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    return base + __popc(mask & lanemask_lt());
+}
+
 // ascending sort of the first n entries of L by the warp (entries are
 // distinct ids).  n <= 32: bitonic network in registers; n <= 128: each
 // lane ranks up to four entries against all n and stores them at their
@@ -370,8 +383,11 @@ template <bool SWEPT>
 __global__ void __launch_bounds__(256)
 k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double* __restrict__ dx,
                const int32_t* __restrict__ start, QueryList Q, int32_t* __restrict__ count) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= S.ns) return;
+    // every lane runs to the warp-wide append at the end (lanes past the last
+    // triangle work on triangle 0 and append nothing)
+    const int64_t t_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = t_raw < S.ns;
+    const int64_t t = valid ? t_raw : 0;
     const int32_t* T = S.stri + 3 * t;
     // The decision (does the grown box reach a non-empty cell?) and the
     // coarse box of the second phase are conservative FP32 bounds; no FP64
@@ -409,13 +425,14 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
             const int64_t c0 = cell_id(S, e, ca.x, iy, iz);
             any = start[c0 + (cb.x - ca.x) + 1] > start[c0];   // cells of a row are contiguous
         }
-    if (!SWEPT) {
+    if (!SWEPT && valid) {
         // the candidate counts start at zero (the exact tests append to them)
-        int32_t* cnt = count + 4 * t;
-        cnt[0] = 0; cnt[1] = 0; cnt[2] = 0; cnt[3] = 0;
+        *reinterpret_cast<int4*>(count + 4 * t) = make_int4(0, 0, 0, 0);
     }
+    any = any && valid;
+    // one atomic per warp for the survivors' slots
+    const int idx = warp_reserve(any, Q.n);
     if (any) {
-        const int idx = atomicAdd(Q.n, 1);
         Q.tri[idx] = (int32_t)t;
         float* bf = Q.boxf + 6 * (int64_t)idx;
         for (int c = 0; c < 3; ++c) { bf[c] = flo[c]; bf[3 + c] = fhi[c]; }
@@ -496,36 +513,93 @@ struct PairList {
 __global__ void __launch_bounds__(256)
 k_query_walk(SceneView S, QueryList Q, const float* __restrict__ mboxf, const int4* __restrict__ mcell,
              const int32_t* __restrict__ start, const int32_t* __restrict__ ent, PairList L) {
+    // pairs are staged per warp in shared memory and written out kWalkStage
+    // at a time, one atomic per batch (a counter bumped per chunk serialises)
+    constexpr int kWalkStage = 128;
+    __shared__ int2 s_stage[8][kWalkStage];
     const int lane = threadIdx.x & 31;
+    int2* stage = s_stage[threadIdx.x >> 5];
+    int ns = 0;
+    auto flush = [&]() {
+        int base = 0;
+        if (lane == 0) {
+            base = atomicAdd(L.n, ns);
+            if (base + ns > L.cap) atomicMax(L.overflow, base + ns);
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        __syncwarp();
+        for (int j = lane; j < ns; j += 32)
+            if (base + j < L.cap) L.p[base + j] = stage[j];
+        __syncwarp();
+        ns = 0;
+    };
     const int n_list = *Q.n;
-    for (int li = next_item(Q.work, lane); li < n_list; li = next_item(Q.work, lane)) {
+    // Items per atomic on the shared work counter: one while the list is
+    // short against the grid (balance matters), up to 16 for long lists (a
+    // counter bumped millions of times serialises).
+    const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
+    const int grab = max(1, min(16, n_list / (16 * nwarps)));
+    for (int lb = next_items(Q.work, lane, grab); lb < n_list; lb = next_items(Q.work, lane, grab))
+    for (int li = lb; li < min(lb + grab, n_list); ++li) {
         const float* qf = Q.boxf + 6 * (int64_t)li;
         const float qlo[3] = {qf[0], qf[1], qf[2]}, qhi[3] = {qf[3], qf[4], qf[5]};
         const int32_t* ql = Q.cell + 6 * (int64_t)li;
         const I3 ca = {ql[0], ql[1], ql[2]}, cb = {ql[3], ql[4], ql[5]};
         const int e = S.stri_env[Q.tri[li]];
-        for (RowWalk W(S, start, e, ca, cb); W.more(); W.next()) {
-            const int k = W.kb + lane;
-            bool take = false;
-            int32_t m = 0;
-            if (k < W.k1) {
-                m = ent[k];
-                const float* B = mboxf + 6 * (int64_t)m;
-                take = overlap_keep(qlo, qhi, B, B + 3) &&
-                       first_common_cell(S, start, e, ca, mcell[m], W.iy, W.iz, k);
+        const int nx = cb.x - ca.x + 1, ny = cb.y - ca.y + 1;
+        const int nrows = ny * (cb.z - ca.z + 1);
+        const int64_t off = S.grid_off[e];
+        const int dx = S.grid_dim[3 * e], dy = S.grid_dim[3 * e + 1];
+        // rows (iy, iz) in batches of 32, one per lane: their entry ranges,
+        // then their entries as one flat range walked 32 at a time
+        for (int rb = 0; rb < nrows; rb += 32) {
+            const int r = rb + lane;
+            int k0 = 0, len = 0, iy = 0, iz = 0;
+            if (r < nrows) {
+                iy = ca.y + r % ny; iz = ca.z + r / ny;
+                const int64_t c0 = off + (int64_t)ca.x + (int64_t)dx * ((int64_t)iy + (int64_t)dy * iz);
+                k0 = start[c0];
+                len = start[c0 + nx] - k0;
             }
-            const unsigned bal = __ballot_sync(0xffffffffu, take);
-            if (bal == 0u) continue;
-            int base = 0;
-            if (lane == 0) base = atomicAdd(L.n, __popc(bal));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (take) {
-                const int pos = base + __popc(bal & lanemask_lt());
-                if (pos < L.cap) L.p[pos] = make_int2(li, m);
-                else atomicMax(L.overflow, pos + 1);
+            int incl = len;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int excl = incl - len;
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int jb = 0; jb < total; jb += 32) {
+                const int j = jb + lane;
+                // the row holding flat entry j: the last lane whose prefix is
+                // <= j (empty rows share the next row's prefix); every lane
+                // searches, so the shuffles stay convergent
+                int lo = 0;
+                for (int step = 16; step > 0; step >>= 1) {
+                    const int probe = __shfl_sync(0xffffffffu, excl, (lo + step) & 31);
+                    if (lo + step < 32 && probe <= j) lo += step;
+                }
+                const int rk0 = __shfl_sync(0xffffffffu, k0, lo);
+                const int rex = __shfl_sync(0xffffffffu, excl, lo);
+                const int riy = __shfl_sync(0xffffffffu, iy, lo);
+                const int riz = __shfl_sync(0xffffffffu, iz, lo);
+                bool take = false;
+                int32_t m = 0;
+                if (j < total) {
+                    const int k = rk0 + (j - rex);
+                    m = ent[k];
+                    const float* B = mboxf + 6 * (int64_t)m;
+                    take = overlap_keep(qlo, qhi, B, B + 3) &&
+                           first_common_cell(S, start, e, ca, mcell[m], riy, riz, k);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, take);
+                if (bal == 0u) continue;
+                if (ns + __popc(bal) > kWalkStage) flush();
+                if (take) stage[ns + __popc(bal & lanemask_lt())] = make_int2(li, m);
+                ns += __popc(bal);
             }
         }
     }
+    if (ns > 0) flush();
 }
 
 // append v to the list of kind q of slave tri t (counts may exceed the

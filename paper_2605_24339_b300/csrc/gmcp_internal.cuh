@@ -117,6 +117,12 @@ __device__ __forceinline__ int next_item(int32_t* counter, int lane) {
     if (lane == 0) i = atomicAdd(counter, 1);
     return __shfl_sync(0xffffffffu, i, 0);
 }
+// the same, g consecutive items at a time (returns the first)
+__device__ __forceinline__ int next_items(int32_t* counter, int lane, int g) {
+    int i = 0;
+    if (lane == 0) i = atomicAdd(counter, g);
+    return __shfl_sync(0xffffffffu, i, 0);
+}
 
 // ------------------------------------------------------------------------
 // section profiler: CUDA events around named groups of launches on the
