@@ -727,24 +727,38 @@ k_contact_finish(CandView C, QueryList Q) {
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
     const int n_list = *Q.n;
+    // one triangle at a time per warp; the triangles with candidates wait in
+    // a lane register (lane j holds the j-th) and join the active list 32 at
+    // a time, one atomic each time
+    int32_t held = 0;
+    int nheld = 0;
+    auto flush = [&]() {
+        int base = 0;
+        if (lane == 0) base = atomicAdd(C.n_active, nheld);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane < nheld) C.active[base + lane] = held;
+        nheld = 0;
+    };
     for (int li = warp; li < n_list; li += nwarps) {
         const int64_t t = Q.tri[li];
-        int32_t* cnt = C.count + 4 * t;
-        const int nf = cnt[0], ne = cnt[1], np = cnt[2];
+        const int4 cn = *reinterpret_cast<const int4*>(C.count + 4 * t);
+        const int nf = cn.x, ne = cn.y, np = cn.z;
         warp_sort(C.face + t * C.cap_f, min(nf, C.cap_f), lane);
         warp_sort(C.edge + t * C.cap_e, min(ne, C.cap_e), lane);
         warp_sort(C.point + t * C.cap_p, min(np, C.cap_p), lane);
-        if (lane != 0) continue;
-        if (nf > C.cap_f) atomicMax(&C.overflow[0], nf);
-        if (ne > C.cap_e) atomicMax(&C.overflow[1], ne);
-        if (np > C.cap_p) atomicMax(&C.overflow[2], np);
+        if (lane == 0) {
+            if (nf > C.cap_f) atomicMax(&C.overflow[0], nf);
+            if (ne > C.cap_e) atomicMax(&C.overflow[1], ne);
+            if (np > C.cap_p) atomicMax(&C.overflow[2], np);
+        }
         // triangles without candidates are not stamped by the evaluation, so
         // their stored outputs are never read
         if (nf + ne + np > 0) {
-            const int idx = atomicAdd(C.n_active, 1);
-            C.active[idx] = (int32_t)t;
+            if (lane == nheld) held = (int32_t)t;
+            if (++nheld == 32) flush();
         }
     }
+    if (nheld > 0) flush();
 }
 
 // ---------------------------------------------------------------------------

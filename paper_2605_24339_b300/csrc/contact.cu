@@ -337,29 +337,50 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
                             int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp, TouchArgs TA) {
     const int n_active = *C.n_active;
     const int32_t ps = tri_stamp ? TA.misc[kSlotPass] : 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_active; i += gridDim.x * blockDim.x) {
-        const int64_t t = C.active[i];
-        const int32_t* Tt = S.stri + 3 * t;
-        if (tri_stamp) {
-            tri_stamp[t] = ps;
-            touch_tri(TA, Tt);
+    const int lane = threadIdx.x & 31;
+    // whole warps iterate together (the item slots are reserved per warp)
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t ib = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); ib < n_active; ib += stride) {
+        const int i = (int)(ib + lane);
+        const bool valid = i < n_active;
+        int n = 0;
+        if (valid) {
+            const int64_t t = C.active[i];
+            const int32_t* Tt = S.stri + 3 * t;
+            if (tri_stamp) {
+                tri_stamp[t] = ps;
+                touch_tri(TA, Tt);
+            }
+            const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
+            const V3<double> X0 = ld3(S.X, Tt[0]), X1 = ld3(S.X, Tt[1]), X2 = ld3(S.X, Tt[2]);
+            const V3<double> cr = cross(x1 - x0, x2 - x0);
+            const double clen = sqrt(dot(cr, cr));
+            const V3<double> cr0 = cross(X1 - X0, X2 - X0);
+            const double clen0 = sqrt(dot(cr0, cr0));
+            double* f = frame + 8 * (int64_t)i;
+            f[0] = cr.x / clen; f[1] = cr.y / clen; f[2] = cr.z / clen;
+            f[3] = 0.5 * clen;
+            f[4] = cr0.x / clen0; f[5] = cr0.y / clen0; f[6] = cr0.z / clen0;
+            f[7] = 1e-12 * (fabs(x0.x) + fabs(x0.y) + fabs(x0.z)) + 1e-30;
+            if (items) {
+                const int32_t* cnt = C.count + 4 * t;
+                n = min(cnt[0], C.cap_f) * nk + 2 * min(cnt[1], C.cap_e) + min(cnt[2], C.cap_p);
+            }
         }
-        const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
-        const V3<double> X0 = ld3(S.X, Tt[0]), X1 = ld3(S.X, Tt[1]), X2 = ld3(S.X, Tt[2]);
-        const V3<double> cr = cross(x1 - x0, x2 - x0);
-        const double clen = sqrt(dot(cr, cr));
-        const V3<double> cr0 = cross(X1 - X0, X2 - X0);
-        const double clen0 = sqrt(dot(cr0, cr0));
-        double* f = frame + 8 * (int64_t)i;
-        f[0] = cr.x / clen; f[1] = cr.y / clen; f[2] = cr.z / clen;
-        f[3] = 0.5 * clen;
-        f[4] = cr0.x / clen0; f[5] = cr0.y / clen0; f[6] = cr0.z / clen0;
-        f[7] = 1e-12 * (fabs(x0.x) + fabs(x0.y) + fabs(x0.z)) + 1e-30;
         if (items) {
-            const int32_t* cnt = C.count + 4 * t;
-            const int n = min(cnt[0], C.cap_f) * nk + 2 * min(cnt[1], C.cap_e) + min(cnt[2], C.cap_p);
-            items[2 * i] = atomicAdd(n_items, n);
-            items[2 * i + 1] = n;
+            // the warp's ranges are consecutive: one atomic per warp
+            int incl = n;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += v;
+            }
+            int base = 0;
+            if (lane == 31) base = atomicAdd(n_items, incl);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            if (valid) {
+                items[2 * i] = base + incl - n;
+                items[2 * i + 1] = n;
+            }
         }
     }
 }
