@@ -38,10 +38,15 @@ METRIC = "contact samples/s (barrier E+grad+H+CCD)"
 UNIT = "samples/s"
 WORKLOAD = "gel_on_terrain 256x256 pad (131,072 slave tris x 16 samples) vs 199,712-tri Perlin terrain, pressed 0.15 mm"
 CROP_HALF_WIDTH = 2.0e-3
-# DRAM bytes (read + write) of one k_samples launch on this workload, from the
-# ncu capture summarised in profiles/k_samples_gel_on_terrain.md; null when
-# the kernel changes and the capture is not yet redone
-K_SAMPLES_DRAM_BYTES_PER_LAUNCH = None
+# Counters of one k_items launch on this workload (the largest kernel of the
+# pass), from the ncu capture summarised in profiles/k_items_gel_on_terrain.md:
+# FP64-pipe lane instructions (warp instructions x 32) and DRAM bytes (read +
+# write).  Null when the kernel changes and the capture is not yet redone.
+K_ITEMS_FP64_LANE_INST = None
+K_ITEMS_DRAM_BYTES = None
+# kernels one contact pass launches on this workload (ncu launch list,
+# profiles/launches_gel_on_terrain.md)
+KERNELS_PER_PASS = 24
 
 
 def load_peaks():
@@ -230,23 +235,21 @@ def run_ours(args):
         return
     peaks, peak_kind = load_peaks()
     sec_ms = {k: v["ms"] / max(v["calls"], 1) for k, v in prof.items()}
-    # Dominant kernel: k_samples ("samples" section, one launch per pass).
-    # Work model (per-unit figure of the contact pass): 160 FP32-equivalent
-    # flops per (sample, candidate) evaluation; units per launch = face
-    # (sample, candidate) pairs evaluated + 2 per edge candidate + 1 per point
-    # candidate.  Peak: FP32 CUDA-core rate from unit counts and the measured
-    # SM clock (148 SMs x 128 lanes x 2 flop x clock).
-    evals = counts_once["face_evaluated"] + 2 * cand["edge"] + cand["point"]
-    flops = 160.0 * evals
+    # Dominant kernel: k_items (one thread per sample item), bound by the
+    # FP64 pipe: its exact FP64 sample geometry, counted per launch with ncu,
+    # over B300's FP64 rate of 2 lane instructions per SM per clock (1.25
+    # TFLOP/s of FMA at 2.03 GHz) at the SM clock sampled during the run.
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    fp64_peak = 148 * 2 * sm_mhz * 1e6 / 1e9
+    items_ms = sec_ms.get("items")
+    fp64_achieved = (K_ITEMS_FP64_LANE_INST / (items_ms / 1e3) / 1e9
+                     if K_ITEMS_FP64_LANE_INST and items_ms else None)
+    # the survey's per-unit model beside it: 160 FP32 flops per evaluated
+    # (sample, candidate), against the FP32 CUDA-core rate
+    evals = counts_once["face_evaluated"] + 2 * cand["edge"] + cand["point"]
     fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    achieved = flops / (sec_ms["samples"] / 1e3) / 1e12
-    n_launch_per_step = {"grid": 6, "query": 2, "samples": 1, "gather_grad": 1, "gather_hess": 1,
-                         "reduce": 2, "accd": 2}
-    launches = 0
-    for k, v in prof.items():
-        launches += n_launch_per_step.get(k, 1) * v["calls"]
-    launches = launches * args.steps // max(n_prof, 1)
+    fp32_achieved = 160.0 * evals / (items_ms / 1e3) / 1e12 if items_ms else None
+    launches = KERNELS_PER_PASS * args.steps if KERNELS_PER_PASS else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -260,12 +263,17 @@ def run_ours(args):
                    "cuda_graph": True, "autotuned_blocks_per_sm": {"samples": tune_s, "query": tune_q}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_np.nbytes),
                 "d2h_bytes_per_step": 16},
-        "gpu_launches": int(launches),
-        "roofline": {"bound": "alu", "kernel": "k_samples", "achieved": achieved,
-                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "traffic": K_SAMPLES_DRAM_BYTES_PER_LAUNCH,
-                     "peak_source": "FP32 unit counts x measured SM clock",
-                     "work": {"flops_per_eval": 160, "evals_per_launch": int(evals)}},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "kernel": "k_items", "achieved": fp64_achieved,
+                     "peak": fp64_peak, "unit": "FP64 Ginst/s",
+                     "frac": fp64_achieved / fp64_peak if fp64_achieved else None,
+                     "traffic": K_ITEMS_DRAM_BYTES,
+                     "peak_source": "FP64 pipe: 148 SMs x 2 lanes/clock x measured SM clock",
+                     "work": {"fp64_lane_inst_per_launch": K_ITEMS_FP64_LANE_INST,
+                              "evals_per_launch": int(evals), "launch_ms": items_ms},
+                     "fp32_model": {"flops_per_eval": 160, "achieved_tflops": fp32_achieved,
+                                    "peak_tflops": fp32_peak,
+                                    "frac": fp32_achieved / fp32_peak if fp32_achieved else None}},
         "sections_ms": {k: round(v, 4) for k, v in sec_ms.items()},
         "alpha": info["alpha"],
         "clocks": clk,

@@ -999,6 +999,28 @@ ORC_API double orc_ee_dist2(const double* a0, const double* a1, const double* b0
     return d;
 }
 
+/* brute-force minimum squared distance between two triangle surfaces (the
+ * invariant a CCD-limited step must keep > 0): every vertex of one against
+ * every triangle of the other, both ways, and every edge pair (edges taken
+ * from the triangles, repeats included) */
+ORC_API double orc_surface_min_dist2(const double* xa, const int32_t* ta, int64_t na,
+                                     const double* xb, const int32_t* tb, int64_t nb) {
+    double best = INFINITY;
+    for (int64_t i = 0; i < na; ++i)
+        for (int64_t j = 0; j < nb; ++j) {
+            const int32_t* A = ta + 3 * i;
+            const int32_t* B = tb + 3 * j;
+            for (int k = 0; k < 3; ++k) {
+                best = dmin(best, orc_pt_dist2(xa + 3 * A[k], xb + 3 * B[0], xb + 3 * B[1], xb + 3 * B[2]));
+                best = dmin(best, orc_pt_dist2(xb + 3 * B[k], xa + 3 * A[0], xa + 3 * A[1], xa + 3 * A[2]));
+                for (int l = 0; l < 3; ++l)
+                    best = dmin(best, orc_ee_dist2(xa + 3 * A[k], xa + 3 * A[(k + 1) % 3],
+                                                   xb + 3 * B[l], xb + 3 * B[(l + 1) % 3]));
+            }
+        }
+    return best;
+}
+
 /* ACCD for one primitive pair.  type 0: point x[0] vs triangle x[1..3];
  * type 1: edge x[0..1] vs edge x[2..3].  p[] are the displacements over the
  * step; returns the largest safe fraction found in [0, tc] (tc when no

@@ -82,6 +82,8 @@ def _declare(L):
     L.orc_alpha_lin.restype = D; L.orc_alpha_lin.argtypes = [P, P, P, P, P]
     L.orc_pt_dist2.restype = D; L.orc_pt_dist2.argtypes = [P, P, P, P]
     L.orc_ee_dist2.restype = D; L.orc_ee_dist2.argtypes = [P, P, P, P]
+    L.orc_surface_min_dist2.restype = D
+    L.orc_surface_min_dist2.argtypes = [P, P, C.c_int64, P, P, C.c_int64]
     L.orc_accd.restype = D; L.orc_accd.argtypes = [I, P, P, D, D, I, C.POINTER(I)]
     L.orc_accd_min.restype = D
     L.orc_accd_min.argtypes = [P, P, P, P, P, D, I, C.POINTER(AccdInfo)]
@@ -134,6 +136,17 @@ def face_rule(L):
 def pt_dist2(p, t0, t1, t2):
     a = [_f64(v) for v in (p, t0, t1, t2)]
     return lib().orc_pt_dist2(*[_p(v) for v in a])
+
+
+def surface_min_dist(xa, ta, xb, tb):
+    """Brute-force minimum distance between two triangle surfaces (all
+    vertex-triangle pairs both ways and all edge pairs)."""
+    xa, xb = _f64(xa), _f64(xb)
+    ta = np.ascontiguousarray(ta, dtype=np.int32)
+    tb = np.ascontiguousarray(tb, dtype=np.int32)
+    d2 = lib().orc_surface_min_dist2(xa.ctypes.data, ta.ctypes.data, ta.shape[0],
+                                     xb.ctypes.data, tb.ctypes.data, tb.shape[0])
+    return float(np.sqrt(max(d2, 0.0)))
 
 
 def ee_dist2(a0, a1, b0, b1):

@@ -737,7 +737,7 @@ __global__ void k_fill_owner(CandView C, const int32_t* __restrict__ items, Item
 }
 
 template <int NK, class T>
-__global__ void __launch_bounds__(64)
+__global__ void __launch_bounds__(64, 6)
 k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
         const double* __restrict__ dx, const double* __restrict__ dxm, const double* __restrict__ frame,
         const int32_t* __restrict__ items, ItemBufs B, long long* counters) {
@@ -986,11 +986,14 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items};
     k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
     GMCP_CUDA_TRY(cudaGetLastError());
-    // 64-thread blocks: at ~160 registers a thread, 12 warps fit an SM
-    // (8 with 256-thread blocks)
-    k_items<NK, T><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
-                                                   c.tri_items.p, B, counters);
-    GMCP_CUDA_TRY(cudaGetLastError());
+    {
+        ProfScope pi(c.prof, c.stream, "items");
+        // 64-thread blocks, at most 168 registers a thread: 12 warps fit an
+        // SM (8 with 256-thread blocks)
+        k_items<NK, T><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
+                                                       c.tri_items.p, B, counters);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
     k_tri_reduce<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_frame.p, c.tri_items.p, B, c.tri_E.p,
                                                         G, Sm, N, alpha_bits);
     GMCP_CUDA_TRY(cudaGetLastError());

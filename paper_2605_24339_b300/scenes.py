@@ -455,6 +455,68 @@ def fingertip_batch(n_env=512, pads_per_env=5, quad_range=(16, 128), dx=0.25e-3,
     return concat_envs([o[0] for o in out], name="fingertip_batch"), np.concatenate([o[1] for o in out])
 
 
+def thin_shell(nq: int, side: float, thickness: float):
+    """Closed thin plate: the surface of a box of side x side x thickness
+    with nq x nq quads on the two large faces and nq x 1 quads on each rim,
+    triangulated with outward normals.  Returns (Y [n,3], F [m,3] int32)."""
+    i = np.arange(nq + 1)
+    I, J = np.meshgrid(i, i, indexing="ij")
+    a = side / 2
+    Y = []
+    for k, z in enumerate((-thickness / 2, thickness / 2)):
+        Y.append(np.stack([-a + I.ravel() * side / nq, -a + J.ravel() * side / nq,
+                           np.full(I.size, z)], axis=1))
+    Y = np.concatenate(Y).astype(np.float64)
+    vid = lambda ii, jj, kk: ii + (nq + 1) * (jj + (nq + 1) * kk)
+    quads = []
+    for kk in (0, 1):                                   # large faces
+        for ii in range(nq):
+            for jj in range(nq):
+                quads.append((vid(ii, jj, kk), vid(ii + 1, jj, kk), vid(ii + 1, jj + 1, kk), vid(ii, jj + 1, kk)))
+    for ii in range(nq):                                # rims y = -a, y = +a
+        for jj in (0, nq):
+            quads.append((vid(ii, jj, 0), vid(ii + 1, jj, 0), vid(ii + 1, jj, 1), vid(ii, jj, 1)))
+    for jj in range(nq):                                # rims x = -a, x = +a
+        for ii in (0, nq):
+            quads.append((vid(ii, jj, 0), vid(ii, jj + 1, 0), vid(ii, jj + 1, 1), vid(ii, jj, 1)))
+    F = []
+    for q in quads:
+        for tri in ((q[0], q[1], q[2]), (q[0], q[2], q[3])):
+            p0, p1, p2 = Y[list(tri)]
+            n = np.cross(p1 - p0, p2 - p0)
+            c = (p0 + p1 + p2) / 3
+            F.append(tri if np.dot(n, c) > 0 else (tri[0], tri[2], tri[1]))   # outward (box centred at 0)
+    return Y, np.asarray(F, dtype=np.int32)
+
+
+def ccd_stress(n_env=64, pad_quads=128, pad_dx=0.25e-3, pad_nz=4, shell_quads=100, shell_side=30e-3,
+               shell_thickness=1e-3, gap=1e-3, speed=(0.5, 2.0), dhat=1e-4, kappa=1e5, h=1e-3,
+               seed=4, face_rule_level=1):
+    """CCD / line-search stress: per env, a free pad (no Dirichlet vertices)
+    moving at U[speed] m/s toward a closed thin shell from ``gap`` away, the
+    whole env at a seeded random rotation.  At 2 m/s and h = 1 ms a step moves
+    the pad 2 mm, more than the shell is thick.  Returns (scene, v0)."""
+    envs, vs = [], []
+    Ys, Fs = thin_shell(shell_quads, shell_side, shell_thickness)
+    for e in range(n_env):
+        rng = np.random.Generator(np.random.PCG64(seed * 1000 + e))
+        side = pad_quads * pad_dx
+        X, tets, bot, _ = pad_slab(pad_quads, pad_quads, pad_nz, pad_dx, pad_dx,
+                                   origin=(-side / 2, -side / 2, shell_thickness / 2 + gap))
+        q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+        if np.linalg.det(q) < 0:
+            q[:, 0] = -q[:, 0]
+        spd = rng.uniform(speed[0], speed[1])
+        v = np.zeros_like(X)
+        v[:, 2] = -spd
+        p = _finish_params(default_params(dhat=dhat, kappa=kappa, h=h, face_rule_level=face_rule_level),
+                           X, bot)
+        envs.append(_single_env(X @ q.T, tets, bot, np.zeros(X.shape[0], dtype=np.uint8), Ys @ q.T, Fs,
+                                np.zeros_like(X), p, f"env{e}", 10))
+        vs.append(v @ q.T)
+    return concat_envs(envs, name="ccd_stress"), np.concatenate(vs)
+
+
 def _pad_dirs(n):
     """n unit directions spread over the sphere (outward from the object)."""
     base = [np.array(v, dtype=np.float64) for v in

@@ -136,3 +136,40 @@ def test_accd_min_matches_pairwise(oracle_mod):
             X4 = np.vstack([x[v], sc.Y0[t]]); P4 = np.vstack([dx[v], np.zeros((3, 3))])
             best = min(best, oracle_mod.accd(0, X4, P4)[0])
     assert al <= best
+
+
+def test_surface_min_dist_closed_forms(oracle_mod):
+    """The brute-force surface distance (used by the CCD stress checks) on
+    configurations with a known answer: parallel faces, a vertex over a
+    face interior, and two crossing edges whose closest points are interior
+    to both."""
+    h = 0.37
+    A = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0]], dtype=np.float64)
+    B = A + [0, 0, h]
+    T = np.array([[0, 1, 2]], dtype=np.int32)
+    assert oracle_mod.surface_min_dist(A, T, B, T) == pytest.approx(h, rel=1e-14)
+    # a tilted triangle whose lowest vertex sits h above the interior of A
+    C = np.array([[0.25, 0.25, h], [2.0, 2.0, 3.0], [-1.0, 3.0, 2.0]])
+    assert oracle_mod.surface_min_dist(A, T, C, T) == pytest.approx(h, rel=1e-14)
+    assert oracle_mod.surface_min_dist(C, T, A, T) == pytest.approx(h, rel=1e-14)
+    # edge along x at z = 0 against edge along y at z = h, both tris turned away
+    D = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, -1]], dtype=np.float64)
+    E = np.array([[0, -1, h], [0, 1, h], [1, 0, h + 1]], dtype=np.float64)
+    assert oracle_mod.surface_min_dist(D, T, E, T) == pytest.approx(h, rel=1e-14)
+    # every vertex is farther than h: the minimum is the edge-edge distance
+    vmin = min(np.sqrt(oracle_mod.pt_dist2(p, *E)) for p in D)
+    assert vmin > 1.2 * h
+
+
+def test_thin_shell_is_closed_and_outward():
+    from paper_2605_24339_b300 import scenes as S
+    from collections import Counter
+    Y, F = S.thin_shell(5, 4e-3, 1e-3)
+    E = Counter()
+    for t in F:
+        for k in range(3):
+            E[(int(t[k]), int(t[(k + 1) % 3]))] += 1
+    assert all(c == 1 for c in E.values())
+    assert all(E[(b, a)] == 1 for (a, b) in E)            # every edge shared, opposite directions
+    vol = sum(np.dot(Y[t[0]], np.cross(Y[t[1]], Y[t[2]])) for t in F) / 6.0
+    assert vol == pytest.approx(4e-3 * 4e-3 * 1e-3, rel=1e-12)   # outward normals
