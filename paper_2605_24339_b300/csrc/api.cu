@@ -246,6 +246,7 @@ cudaError_t grow_items(Ctx& c) {
     GMCP_CUDA_TRY(c.item_owner.ensure((size_t)c.cap_items));
     GMCP_CUDA_TRY(c.item_rd.ensure(2 * (size_t)c.cap_items));
     GMCP_CUDA_TRY(c.item_rt.ensure(5 * sizeof(double) * (size_t)c.cap_items));
+    GMCP_CUDA_TRY(c.item_list.ensure((size_t)c.cap_items));
     c.cp_graph.reset();
     return cudaSuccess;
 }
@@ -288,7 +289,7 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.ccd_stream,
             (uintptr_t)c.mcell.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
             (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_frame.p, (uintptr_t)c.tri_items.p, (uintptr_t)c.item_owner.p,
-            (uintptr_t)c.item_rd.p, (uintptr_t)c.item_rt.p, (uintptr_t)c.cap_items, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
+            (uintptr_t)c.item_rd.p, (uintptr_t)c.item_rt.p, (uintptr_t)c.cap_items, (uintptr_t)c.item_list.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
             (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,
             (uintptr_t)c.cb_val64.p, (uintptr_t)c.u64_tmp.p, (uintptr_t)c.i64_tmp.p, (uintptr_t)c.misc_i32.p,
             (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p};

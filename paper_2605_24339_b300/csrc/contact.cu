@@ -249,6 +249,20 @@ __device__ __forceinline__ void sample_add(Acc<T>& A, double kq, double w, doubl
 
 template <class T> __device__ __forceinline__ T shfl_x(T v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
 
+// slots for the lanes with pred set, one atomic for the warp (all 32 lanes call it)
+__device__ __forceinline__ int warp_reserve_c(bool pred, int32_t* counter) {
+    const unsigned mask = __ballot_sync(0xffffffffu, pred);
+    if (mask == 0u) return 0;
+    const int leader = __ffs(mask) - 1;
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    unsigned lt;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(lt));
+    return base + __popc(mask & lt);
+}
+
 // one sample of the frozen-linear potential (lagged energy of the line
 // search, reading R6): g~ = g + a dg; +inf once g~ <= 0, 0 from eps on
 __device__ __forceinline__ void lag_add(double* E8, const double* al, int na, double coef, double g,
@@ -288,6 +302,7 @@ __global__ void k_pass_begin(int32_t* misc, int hess) {
     const int32_t p = ++misc[kSlotPass];
     (void)p;
     misc[kSlotVCount] = 0;
+    misc[kSlotItemList] = 0;
     if (hess) {
         const int32_t h = ++misc[kSlotHPass];
         misc[kSlotBCount + (h & 1)] = 0;
@@ -444,6 +459,36 @@ __device__ __forceinline__ FaceSample face_sample(const Params& P, const TriData
     return F;
 }
 
+// FP32 pre-tests of the mixed path: false only when the exact FP64 test of
+// the item certainly fails (the bounds are stated at face_maybe,
+// plane_gap_maybe and bary_f)
+__device__ __forceinline__ bool face_pre(const Params& P, const TriData& D, const FaceSample& F,
+                                         V3<double> y0, V3<double> y1, V3<double> y2) {
+    return face_maybe(F.xs_rel, D.ns_f, tof(y0 - D.x0), tof(y1 - D.x0), tof(y2 - D.x0), (float)P.dhat);
+}
+__device__ __forceinline__ bool edge_pre(const Params& P, const TriData& D, V3<double> ya, V3<double> yb) {
+    const V3<float> da = tof(ya - D.x0), db = tof(yb - D.x0);
+    if (!plane_gap_maybe(D.ns_f, da, db, (float)P.dhat, D.tol_abs)) return false;
+    // the projected edge misses the slave tri when both ends are certainly
+    // on the outer side of one of its edges (beta_a is affine along it)
+    float fa[3], fb[3], ta, tb;
+    bool oka, okb;
+    bary_f(da, D.e1_f, D.e2_f, fa, ta, oka);
+    bary_f(db, D.e1_f, D.e2_f, fb, tb, okb);
+    if (oka && okb)
+        for (int a = 0; a < 3; ++a)
+            if (fa[a] < -ta && fb[a] < -tb) return false;
+    return true;
+}
+__device__ __forceinline__ bool point_pre(const Params& P, const TriData& D, V3<double> y) {
+    const V3<float> d = tof(y - D.x0);
+    if (!plane_gap_maybe(D.ns_f, d, d, (float)P.dhat, D.tol_abs)) return false;
+    float f[3], tf;
+    bool ok;
+    bary_f(d, D.e1_f, D.e2_f, f, tf, ok);
+    return !(ok && min3(f) < -tf);
+}
+
 // face sample F of slave tri D against master tri m (Sec. 4.1, reading R1)
 template <int NK>
 __device__ __forceinline__ bool face_item(const SceneView& S, const Params& P, const TriData& D,
@@ -452,8 +497,7 @@ __device__ __forceinline__ bool face_item(const SceneView& S, const Params& P, c
     const double eps_max = P.dhat;
     const int32_t* M = S.mtri + 3 * (int64_t)m;
     const V3<double> y0 = ld3(xm, M[0]), y1 = ld3(xm, M[1]), y2 = ld3(xm, M[2]);
-    if (pre && !face_maybe(F.xs_rel, D.ns_f, tof(y0 - D.x0), tof(y1 - D.x0), tof(y2 - D.x0), (float)eps_max))
-        return false;
+    if (pre && !face_pre(P, D, F, y0, y1, y2)) return false;
     double g, bm[3];
     if (!face_geom<double>(F.xs, D.ns, y0, y1, y2, g, bm)) return false;
     double eps = eps_max;
@@ -485,19 +529,7 @@ __device__ __forceinline__ bool edge_item(const SceneView& S, const Params& P, c
     const double gp = 1.0 / sqrt(3.0);
     const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
     const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
-    if (pre) {
-        const V3<float> da = tof(ya - D.x0), db = tof(yb - D.x0);
-        if (!plane_gap_maybe(D.ns_f, da, db, (float)eps_max, D.tol_abs)) return false;
-        // the projected edge misses the slave tri when both ends are certainly
-        // on the outer side of one of its edges (beta_a is affine along it)
-        float fa[3], fb[3], ta, tb;
-        bool oka, okb;
-        bary_f(da, D.e1_f, D.e2_f, fa, ta, oka);
-        bary_f(db, D.e1_f, D.e2_f, fb, tb, okb);
-        if (oka && okb)
-            for (int a = 0; a < 3; ++a)
-                if (fa[a] < -ta && fb[a] < -tb) return false;
-    }
+    if (pre && !edge_pre(P, D, ya, yb)) return false;
     const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
     if (!any_facing(S, xm, S.me_tri + a0, a1 - a0, D.ns)) return false;
     double bA[3], bB[3];
@@ -555,14 +587,7 @@ __device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, 
                                            bool want_dg, ItemOut& o) {
     const double eps_max = P.dhat;
     const V3<double> y = ld3(xm, u);
-    if (pre) {
-        const V3<float> d = tof(y - D.x0);
-        if (!plane_gap_maybe(D.ns_f, d, d, (float)eps_max, D.tol_abs)) return false;
-        float f[3], tf;
-        bool ok;
-        bary_f(d, D.e1_f, D.e2_f, f, tf, ok);
-        if (ok && min3(f) < -tf) return false;
-    }
+    if (pre && !point_pre(P, D, y)) return false;
     const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
     if (!any_facing(S, xm, S.mv_tri + a0, a1 - a0, D.ns)) return false;
     double bs[3];
@@ -736,64 +761,133 @@ __global__ void k_fill_owner(CandView C, const int32_t* __restrict__ items, Item
     }
 }
 
+// where item slot s of active triangle i points: kind 0 face (candidate j,
+// sample k), 1 edge (candidate j, Gauss point k), 2 point (candidate j)
+struct ItemRef { int kind, j, k; };
+template <int NK>
+__device__ __forceinline__ ItemRef item_ref(const TriData& D, int q) {
+    if (q < D.nf * NK) return ItemRef{0, q / NK, q % NK};
+    const int r = q - D.nf * NK;
+    if (r < 2 * D.ne) return ItemRef{1, r >> 1, r & 1};
+    return ItemRef{2, r - 2 * D.ne, 0};
+}
+
+template <class T>
+__device__ __forceinline__ void item_store(const ItemBufs& B, int64_t s, double e, double amin, T c1, T c2,
+                                           const T* b) {
+    T* rt = (T*)B.rt;
+    B.rd[2 * s] = e;
+    B.rd[2 * s + 1] = amin;
+    rt[5 * s] = c1; rt[5 * s + 1] = c2;
+    rt[5 * s + 2] = b[0]; rt[5 * s + 3] = b[1]; rt[5 * s + 4] = b[2];
+}
+
+// Phase 1, one thread per item slot: the FP32 pre-test only.  Items that
+// fail it get their (empty) contribution here; the others are listed for
+// phase 2, which then runs the FP64 geometry on full warps (most of the
+// slots fail the pre-test, and a warp instruction on the FP64 pipe costs
+// the same however few of its lanes are active).
+template <int NK, class T>
+__global__ void __launch_bounds__(256)
+k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
+            const double* __restrict__ frame, const int32_t* __restrict__ items, ItemBufs B,
+            int32_t* __restrict__ list, int32_t* __restrict__ n_list, long long* counters) {
+    const int64_t n = *B.n;
+    if (n > B.cap) return;
+    const bool pre = P.precision == IPC_PREC_MIXED;
+    long long cnt_eval = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together (the list append is per warp)
+    for (int64_t sb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); sb < n; sb += stride) {
+        const int64_t s = sb + (threadIdx.x & 31);
+        bool keep = false;
+        if (s < n) {
+            const int i = B.owner[s];
+            const int q = (int)(s - items[2 * i]);
+            const TriData D = load_tri(S, C, x, nullptr, frame, i);
+            const ItemRef R = item_ref<NK>(D, q);
+            keep = true;
+            if (R.kind == 0) {
+                ++cnt_eval;
+                if (pre) {
+                    const FaceSample F = face_sample(P, D, R.k, false);
+                    const int32_t* M = S.mtri + 3 * (int64_t)C.face[D.t * C.cap_f + R.j];
+                    keep = face_pre(P, D, F, ld3(xm, M[0]), ld3(xm, M[1]), ld3(xm, M[2]));
+                }
+            } else if (R.kind == 1) {
+                if (pre) {
+                    const int32_t me = C.edge[D.t * C.cap_e + R.j];
+                    keep = edge_pre(P, D, ld3(xm, S.medge[2 * (int64_t)me]), ld3(xm, S.medge[2 * (int64_t)me + 1]));
+                }
+            } else if (pre) {
+                keep = point_pre(P, D, ld3(xm, C.point[D.t * C.cap_p + R.j]));
+            }
+            if (!keep) {
+                const T z[3] = {T(0), T(0), T(0)};
+                item_store<T>(B, s, 0.0, INFINITY, T(0), T(0), z);
+            }
+        }
+        const int at = warp_reserve_c(keep, n_list);
+        if (keep) list[at] = (int32_t)s;
+    }
+    if (counters) {
+        for (int o = 16; o > 0; o >>= 1) cnt_eval += shfl_x(cnt_eval, o);
+        if ((threadIdx.x & 31) == 0 && cnt_eval) atomic_add_ll(&counters[3], cnt_eval);
+    }
+}
+
+// Phase 2, one thread per listed item: the exact FP64 geometry and the
+// contribution (the arithmetic of sample_add).
 template <int NK, class T>
 __global__ void __launch_bounds__(64, 6)
 k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
         const double* __restrict__ dx, const double* __restrict__ dxm, const double* __restrict__ frame,
-        const int32_t* __restrict__ items, ItemBufs B, long long* counters) {
-    const int64_t n = *B.n;
-    if (n > B.cap) return;
-    const bool pre = P.precision == IPC_PREC_MIXED;
+        const int32_t* __restrict__ items, ItemBufs B, const int32_t* __restrict__ list,
+        const int32_t* __restrict__ n_list, long long* counters) {
+    if ((int64_t)*B.n > B.cap) return;
+    const int n = *n_list;
     const bool want_dg = dx != nullptr;
-    long long cnt_f = 0, cnt_e = 0, cnt_p = 0, cnt_eval = 0;
-    T* rt = (T*)B.rt;
-    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+    long long cnt_f = 0, cnt_e = 0, cnt_p = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const int64_t s = list[c];
         const int i = B.owner[s];
         const int q = (int)(s - items[2 * i]);
         const TriData D = load_tri(S, C, x, dx, frame, i);
+        const ItemRef R = item_ref<NK>(D, q);
         ItemOut o;
         bool on;
-        if (q < D.nf * NK) {
-            ++cnt_eval;
-            // lane q % 32 of the warp-per-triangle kernel holds sample q % NK
-            const FaceSample F = face_sample(P, D, q % NK, want_dg);
-            on = face_item<NK>(S, P, D, F, xm, dxm, C.face[D.t * C.cap_f + q / NK], pre, want_dg, o);
+        if (R.kind == 0) {
+            const FaceSample F = face_sample(P, D, R.k, want_dg);
+            on = face_item<NK>(S, P, D, F, xm, dxm, C.face[D.t * C.cap_f + R.j], false, want_dg, o);
             cnt_f += on;
-        } else if (q < D.nf * NK + 2 * D.ne) {
-            const int r = q - D.nf * NK;
-            on = edge_item(S, P, D, xm, dxm, C.edge[D.t * C.cap_e + (r >> 1)], r & 1, pre, want_dg, o);
+        } else if (R.kind == 1) {
+            on = edge_item(S, P, D, xm, dxm, C.edge[D.t * C.cap_e + R.j], R.k, false, want_dg, o);
             cnt_e += on;
         } else {
-            const int r = q - D.nf * NK - 2 * D.ne;
-            on = point_item(S, P, D, xm, dxm, C.point[D.t * C.cap_p + r], pre, want_dg, o);
+            on = point_item(S, P, D, xm, dxm, C.point[D.t * C.cap_p + R.j], false, want_dg, o);
             cnt_p += on;
         }
         double e = 0.0, amin = INFINITY;
         T c1 = T(0), c2 = T(0), b[3] = {T(0), T(0), T(0)};
         if (on) {
-            // the arithmetic of sample_add
             T Bv, dB, d2B;
             barrier((T)o.g, (T)o.eps, Bv, dB, d2B);
             const T coef = (T)(o.kq * o.w * o.gamma);
             e = (double)(coef * Bv);
             c1 = coef * dB;
             c2 = rmax(coef * d2B, T(0));
-            for (int c = 0; c < 3; ++c) b[c] = (T)o.b[c];
+            for (int cc = 0; cc < 3; ++cc) b[cc] = (T)o.b[cc];
             if (want_dg && o.dg < 0.0) amin = 0.9 * o.g / (-o.dg);
         }
-        B.rd[2 * s] = e;
-        B.rd[2 * s + 1] = amin;
-        rt[5 * s] = c1; rt[5 * s + 1] = c2;
-        rt[5 * s + 2] = b[0]; rt[5 * s + 3] = b[1]; rt[5 * s + 4] = b[2];
+        item_store<T>(B, s, e, amin, c1, c2, b);
     }
     if (counters) {
         for (int o = 16; o > 0; o >>= 1) {
-            cnt_f += shfl_x(cnt_f, o); cnt_e += shfl_x(cnt_e, o);
-            cnt_p += shfl_x(cnt_p, o); cnt_eval += shfl_x(cnt_eval, o);
+            cnt_f += shfl_x(cnt_f, o); cnt_e += shfl_x(cnt_e, o); cnt_p += shfl_x(cnt_p, o);
         }
-        if ((threadIdx.x & 31) == 0 && (cnt_f | cnt_e | cnt_p | cnt_eval)) {
+        if ((threadIdx.x & 31) == 0 && (cnt_f | cnt_e | cnt_p)) {
             atomic_add_ll(&counters[0], cnt_f); atomic_add_ll(&counters[1], cnt_e);
-            atomic_add_ll(&counters[2], cnt_p); atomic_add_ll(&counters[3], cnt_eval);
+            atomic_add_ll(&counters[2], cnt_p);
         }
     }
 }
@@ -978,6 +1072,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     GMCP_CUDA_TRY(c.item_owner.ensure((size_t)c.cap_items));
     GMCP_CUDA_TRY(c.item_rd.ensure(2 * (size_t)c.cap_items));
     GMCP_CUDA_TRY(c.item_rt.ensure(5 * sizeof(T) * (size_t)c.cap_items));
+    GMCP_CUDA_TRY(c.item_list.ensure((size_t)c.cap_items));
     int32_t* n_items = c.misc_i32.p + 16;
     GMCP_CUDA_TRY(cudaMemsetAsync(n_items, 0, sizeof(int32_t), c.stream));
     k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, c.tri_items.p, n_items,
@@ -986,12 +1081,16 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items};
     k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
     GMCP_CUDA_TRY(cudaGetLastError());
+    int32_t* n_list = c.misc_i32.p + kSlotItemList;
+    k_items_pre<NK, T><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, c.tri_frame.p,
+                                                       c.tri_items.p, B, c.item_list.p, n_list, counters);
+    GMCP_CUDA_TRY(cudaGetLastError());
     {
         ProfScope pi(c.prof, c.stream, "items");
         // 64-thread blocks, at most 168 registers a thread: 12 warps fit an
         // SM (8 with 256-thread blocks)
         k_items<NK, T><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
-                                                       c.tri_items.p, B, counters);
+                                                       c.tri_items.p, B, c.item_list.p, n_list, counters);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     k_tri_reduce<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_frame.p, c.tri_items.p, B, c.tri_E.p,

@@ -265,6 +265,7 @@ constexpr int kSlotPass = 18;    // contact evaluations so far (stamps of this o
 constexpr int kSlotHPass = 19;   // those that assembled the Hessian
 constexpr int kSlotVCount = 20;  // vertices listed in this evaluation
 constexpr int kSlotBCount = 21;  // [2] blocks listed, by Hessian-pass parity
+constexpr int kSlotItemList = 23; // items that passed the FP32 pre-tests
 
 // ------------------------------------------------------------------------
 // the context
@@ -323,6 +324,7 @@ struct Ctx {
     DBuf<int32_t> item_owner;                   // [cap_items] active index of each item slot
     DBuf<double> item_rd;                       // [cap_items][2] energy, step bound
     DBuf<unsigned char> item_rt;                // [cap_items][5] c1, c2, b (FP32 or FP64)
+    DBuf<int32_t> item_list;                    // [cap_items] slots that passed the pre-tests
     int64_t cap_items = 0;
     // outputs touched by the active triangles (pass stamps and lists)
     DBuf<int32_t> tri_stamp, v_stamp, b_stamp;  // [ns], [nv], [cb_nnzb]
