@@ -42,11 +42,11 @@ CROP_HALF_WIDTH = 2.0e-3
 # pass), from the ncu capture summarised in profiles/k_items_gel_on_terrain.md:
 # FP64-pipe lane instructions (warp instructions x 32) and DRAM bytes (read +
 # write).  Null when the kernel changes and the capture is not yet redone.
-K_ITEMS_FP64_LANE_INST = None
-K_ITEMS_DRAM_BYTES = None
+K_ITEMS_FP64_LANE_INST = 6722592
+K_ITEMS_DRAM_BYTES = 918528
 # kernels one contact pass launches on this workload (ncu launch list,
 # profiles/launches_gel_on_terrain.md)
-KERNELS_PER_PASS = 24
+KERNELS_PER_PASS = 25
 
 
 def load_peaks():
