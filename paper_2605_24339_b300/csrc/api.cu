@@ -286,7 +286,7 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.qswept.boxf.p, (uintptr_t)c.qswept.vboxf.p, (uintptr_t)c.qswept.cell.p,
             (uintptr_t)c.mboxf.p, (uintptr_t)c.ccd_pairs.p, (uintptr_t)c.cap_ccd, (uintptr_t)c.coarse_pairs.p,
             (uintptr_t)c.cap_coarse, (uintptr_t)c.coarse_swept.p, (uintptr_t)c.cap_coarse_swept,
-            (uintptr_t)c.ccd_stream,
+            (uintptr_t)c.ccd_stream, (uintptr_t)c.aux_stream,
             (uintptr_t)c.mcell.p, (uintptr_t)c.cell_cnt.p, (uintptr_t)c.cell_start.p, (uintptr_t)c.scan_tmp.p,
             (uintptr_t)c.tri_E.p, (uintptr_t)c.tri_frame.p, (uintptr_t)c.tri_items.p, (uintptr_t)c.item_owner.p,
             (uintptr_t)c.item_rd.p, (uintptr_t)c.item_rt.p, (uintptr_t)c.cap_items, (uintptr_t)c.item_list.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
@@ -966,6 +966,10 @@ void ipc_destroy(ipc_ctx* ctx) {
     c.pcg_graph.reset();
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     if (c.ccd_stream) cudaStreamDestroy(c.ccd_stream);
+    if (c.aux_stream) cudaStreamDestroy(c.aux_stream);
+    if (c.ev_touch0) cudaEventDestroy(c.ev_touch0);
+    if (c.ev_touch1) cudaEventDestroy(c.ev_touch1);
+    if (c.ev_samples) cudaEventDestroy(c.ev_samples);
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_join) cudaEventDestroy(c.ev_join);
     if (c.pin) cudaFreeHost(c.pin);

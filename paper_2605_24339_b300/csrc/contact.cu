@@ -322,10 +322,15 @@ struct TouchArgs {
     int grad, hess;
 };
 
-// list the vertices and contact blocks of slave tri T once each (stamps)
-__device__ __forceinline__ void touch_tri(const TouchArgs& A, const int32_t* T) {
+// List the vertices and contact blocks of the active slave triangles once
+// each (stamps), one thread per (triangle, corner a): vertex T[a] and the
+// blocks (T[a], T[b]) of its row.  Runs beside the sample evaluation.
+__global__ void k_touch(SceneView S, CandView C, TouchArgs A) {
+    const int n = 3 * *C.n_active;
     const int32_t ps = A.misc[kSlotPass], hs = A.misc[kSlotHPass];
-    for (int a = 0; a < 3; ++a) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
+        const int32_t* T = S.stri + 3 * (int64_t)C.active[idx / 3];
+        const int a = idx % 3;
         const int32_t v = T[a];
         if (A.grad && atomicExch(&A.v_stamp[v], ps) != ps) A.v_list[atomicAdd(A.v_count, 1)] = v;
         if (!A.hess) continue;
@@ -349,9 +354,10 @@ __device__ __forceinline__ void touch_tri(const TouchArgs& A, const int32_t* T) 
 // per-triangle results do not) and adds them to *n_items.
 __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ x,
                             double* __restrict__ frame, int nk, int32_t* __restrict__ items,
-                            int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp, TouchArgs TA) {
+                            int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp,
+                            const int32_t* __restrict__ misc) {
     const int n_active = *C.n_active;
-    const int32_t ps = tri_stamp ? TA.misc[kSlotPass] : 0;
+    const int32_t ps = tri_stamp ? misc[kSlotPass] : 0;
     const int lane = threadIdx.x & 31;
     // whole warps iterate together (the item slots are reserved per warp)
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -362,10 +368,7 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
         if (valid) {
             const int64_t t = C.active[i];
             const int32_t* Tt = S.stri + 3 * t;
-            if (tri_stamp) {
-                tri_stamp[t] = ps;
-                touch_tri(TA, Tt);
-            }
+            if (tri_stamp) tri_stamp[t] = ps;
             const V3<double> x0 = ld3(x, Tt[0]), x1 = ld3(x, Tt[1]), x2 = ld3(x, Tt[2]);
             const V3<double> X0 = ld3(S.X, Tt[0]), X1 = ld3(S.X, Tt[1]), X2 = ld3(S.X, Tt[2]);
             const V3<double> cr = cross(x1 - x0, x2 - x0);
@@ -1049,14 +1052,14 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t n, doubl
 template <int NK, class T, int MODE>
 cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* Sm, T* N,
                            long long* counters, const double* dx, const double* dxm,
-                           unsigned long long* alpha_bits, LagArgs LG = LagArgs(), TouchArgs TA = TouchArgs{}) {
+                           unsigned long long* alpha_bits, LagArgs LG = LagArgs()) {
     const int threads = 256;
     const int sms = sm_count(c.device);
     const int blocks = sms * c.tune_samples_bpsm;
     GMCP_CUDA_TRY(c.tri_frame.ensure(8 * (size_t)c.ns + 8));
     if (MODE != MODE_EVAL) {
         k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
-                                                   nullptr, TouchArgs{});
+                                                   nullptr, nullptr);
         GMCP_CUDA_TRY(cudaGetLastError());
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
         k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
@@ -1076,7 +1079,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     int32_t* n_items = c.misc_i32.p + 16;
     GMCP_CUDA_TRY(cudaMemsetAsync(n_items, 0, sizeof(int32_t), c.stream));
     k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, c.tri_items.p, n_items,
-                                               c.tri_stamp.p, TA);
+                                               c.tri_stamp.p, c.misc_i32.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items};
     k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
@@ -1141,52 +1144,87 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
     int32_t* misc = c.misc_i32.p;
     k_pass_begin<<<1, 1, 0, c.stream>>>(misc, hess ? 1 : 0);
     GMCP_CUDA_TRY(cudaGetLastError());
-    const TouchArgs TA{misc, c.v_stamp.p, c.v_list.p, misc + kSlotVCount, c.b_stamp.p,
-                       {c.b_list0.p, c.b_list1.p}, misc + kSlotBCount, c.cb_row.p, c.cb_col.p,
-                       grad ? 1 : 0, hess ? 1 : 0};
+    // The touched vertices and blocks depend on the active list alone: they
+    // are listed on a third stream beside the sample evaluation (the
+    // profiler keeps one stream) and joined before the gathers.
+    const bool fork = (grad || hess) && !c.prof.on;
+    if (grad || hess) {
+        const TouchArgs TA{misc, c.v_stamp.p, c.v_list.p, misc + kSlotVCount, c.b_stamp.p,
+                           {c.b_list0.p, c.b_list1.p}, misc + kSlotBCount, c.cb_row.p, c.cb_col.p,
+                           grad ? 1 : 0, hess ? 1 : 0};
+        cudaStream_t ts = c.stream;
+        if (fork) {
+            if (!c.aux_stream) GMCP_CUDA_TRY(cudaStreamCreateWithFlags(&c.aux_stream, cudaStreamNonBlocking));
+            if (!c.ev_touch0) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_touch0, cudaEventDisableTiming));
+            if (!c.ev_touch1) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_touch1, cudaEventDisableTiming));
+            if (!c.ev_samples) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_samples, cudaEventDisableTiming));
+            GMCP_CUDA_TRY(cudaEventRecord(c.ev_touch0, c.stream));
+            GMCP_CUDA_TRY(cudaStreamWaitEvent(c.aux_stream, c.ev_touch0, 0));
+            ts = c.aux_stream;
+        }
+        k_touch<<<flat, 256, 0, ts>>>(c.view(), c.cand(), TA);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        if (fork) GMCP_CUDA_TRY(cudaEventRecord(c.ev_touch1, c.aux_stream));
+    }
     {
         ProfScope ps(c.prof, c.stream, "samples");
         if (f32) {
             if (c.P.nk == 4)
-                GMCP_CUDA_TRY((launch_samples<4, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits, LagArgs(), TA)));
+                GMCP_CUDA_TRY((launch_samples<4, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits)));
             else
-                GMCP_CUDA_TRY((launch_samples<16, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits, LagArgs(), TA)));
+                GMCP_CUDA_TRY((launch_samples<16, float, MODE_EVAL>(c, x, xm, c.tri_G32.p, c.tri_S32.p, c.tri_n32.p, counters, dx, dxm, alpha_bits)));
         } else {
             if (c.P.nk == 4)
-                GMCP_CUDA_TRY((launch_samples<4, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits, LagArgs(), TA)));
+                GMCP_CUDA_TRY((launch_samples<4, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits)));
             else
-                GMCP_CUDA_TRY((launch_samples<16, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits, LagArgs(), TA)));
+                GMCP_CUDA_TRY((launch_samples<16, double, MODE_EVAL>(c, x, xm, c.tri_G64.p, c.tri_S64.p, c.tri_n64.p, counters, dx, dxm, alpha_bits)));
         }
+    }
+    // After the samples: the gradient gather on the main stream, the Hessian
+    // gather and the energy sum on the third stream (behind the touch lists),
+    // joined at the end.
+    cudaStream_t hs_stream = c.stream;
+    if (fork) {
+        GMCP_CUDA_TRY(cudaEventRecord(c.ev_samples, c.stream));
+        GMCP_CUDA_TRY(cudaStreamWaitEvent(c.aux_stream, c.ev_samples, 0));
+        GMCP_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.ev_touch1, 0));
+        hs_stream = c.aux_stream;
     }
     if (grad) {
         ProfScope ps(c.prof, c.stream, "gather_grad");
-        {
-            GMCP_CUDA_TRY(cudaMemsetAsync(grad_dev, 0, (f32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)c.nv,
-                                          c.stream));
-            if (f32)
-                k_gather_grad<float, float><<<flat, 256, 0, c.stream>>>(c.vt_off.p, c.vt_ent.p, c.tri_G32.p, c.tri_n32.p,
-                                                                     c.tri_stamp.p, misc, c.v_list.p, (float*)grad_dev);
-            else
-                k_gather_grad<double, double><<<flat, 256, 0, c.stream>>>(c.vt_off.p, c.vt_ent.p, c.tri_G64.p,
-                                                                       c.tri_n64.p, c.tri_stamp.p, misc, c.v_list.p,
-                                                                       (double*)grad_dev);
-            GMCP_CUDA_TRY(cudaGetLastError());
-        }
+        GMCP_CUDA_TRY(cudaMemsetAsync(grad_dev, 0, (f32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)c.nv,
+                                      c.stream));
+        if (f32)
+            k_gather_grad<float, float><<<flat, 256, 0, c.stream>>>(c.vt_off.p, c.vt_ent.p, c.tri_G32.p, c.tri_n32.p,
+                                                                 c.tri_stamp.p, misc, c.v_list.p, (float*)grad_dev);
+        else
+            k_gather_grad<double, double><<<flat, 256, 0, c.stream>>>(c.vt_off.p, c.vt_ent.p, c.tri_G64.p,
+                                                                   c.tri_n64.p, c.tri_stamp.p, misc, c.v_list.p,
+                                                                   (double*)grad_dev);
+        GMCP_CUDA_TRY(cudaGetLastError());
     }
     if (hess) {
-        ProfScope ps(c.prof, c.stream, "gather_hess");
+        ProfScope ps(c.prof, hs_stream, "gather_hess");
         int32_t* const* lists = c.b_lists.p;
         if (f32)
-            k_gather_hess<float><<<flat, 256, 0, c.stream>>>(c.cb_src_off.p, c.cb_src.p, c.tri_S32.p, c.tri_n32.p,
-                                                             c.tri_stamp.p, misc, lists, c.b_stamp.p, c.cb_val32.p);
+            k_gather_hess<float><<<flat, 256, 0, hs_stream>>>(c.cb_src_off.p, c.cb_src.p, c.tri_S32.p, c.tri_n32.p,
+                                                              c.tri_stamp.p, misc, lists, c.b_stamp.p, c.cb_val32.p);
         else
-            k_gather_hess<double><<<flat, 256, 0, c.stream>>>(c.cb_src_off.p, c.cb_src.p, c.tri_S64.p, c.tri_n64.p,
-                                                              c.tri_stamp.p, misc, lists, c.b_stamp.p, c.cb_val64.p);
+            k_gather_hess<double><<<flat, 256, 0, hs_stream>>>(c.cb_src_off.p, c.cb_src.p, c.tri_S64.p, c.tri_n64.p,
+                                                               c.tri_stamp.p, misc, lists, c.b_stamp.p, c.cb_val64.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     if (energy_dev) {
-        ProfScope ps(c.prof, c.stream, "reduce");
-        GMCP_CUDA_TRY(reduce_sum(c, c.tri_E.p, c.ns, energy_dev, c.tri_stamp.p, misc + kSlotPass));
+        ProfScope ps(c.prof, hs_stream, "reduce");
+        cudaStream_t main = c.stream;
+        c.stream = hs_stream;
+        const cudaError_t e = reduce_sum(c, c.tri_E.p, c.ns, energy_dev, c.tri_stamp.p, misc + kSlotPass);
+        c.stream = main;
+        GMCP_CUDA_TRY(e);
+    }
+    if (fork) {
+        GMCP_CUDA_TRY(cudaEventRecord(c.ev_touch1, c.aux_stream));
+        GMCP_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.ev_touch1, 0));
     }
     return cudaSuccess;
 }

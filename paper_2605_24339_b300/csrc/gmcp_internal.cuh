@@ -312,6 +312,8 @@ struct Ctx {
     QueryBufs qcontact, qswept;                 // filtered slave tris of the two queries
     cudaStream_t ccd_stream = nullptr;          // the swept query's branch of a contact pass
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t aux_stream = nullptr;          // touched-output lists beside the sample evaluation
+    cudaEvent_t ev_touch0 = nullptr, ev_touch1 = nullptr, ev_samples = nullptr;
     DBuf<int32_t> cell_cnt, cell_start, cell_ent;
     DBuf<int32_t> scan_tmp;
     DBuf<int32_t> cand_face, cand_edge, cand_point, cand_count, active, misc_i32;
