@@ -203,18 +203,23 @@ struct NewtonState {
     DBuf<double> Dminv, vol, mass;       // [nt][9], [nt], [nv]
     DBuf<uint8_t> dir;                   // [nv]
     DBuf<int32_t> vte_off, vte;          // vertex -> tet corner (t*4+a)
-    DBuf<int32_t> rp, ci, brow;          // block pattern (CSR, plus the row of each block)
+    DBuf<int32_t> rp, ci;                // block pattern (CSR)
+    int64_t nslice = 0, ngroups = 0;     // sliced-ELL storage of the matrix: 32 rows per slice
+    DBuf<int32_t> goff;                  // [nslice + 1] first group (32 stored blocks) of each slice
+    DBuf<int32_t> gslice;                // [ngroups] slice of each group
+    DBuf<int32_t> sci;                   // [ngroups][32] column of each stored block, -1 for padding
     DBuf<int32_t> diag;                  // [nv] index of block (v, v)
     DBuf<int32_t> bt_off, bt;            // block -> (t*16 + a*4 + b)
     DBuf<int32_t> cmap;                  // block -> contact block or -1
     DBuf<double> tE, tG, tE8;            // per-tet energy [nt], gradient [nt][12], energies [8][nt]
     DBuf<double> tH64;                   // per-tet Hessian, 10 blocks [nt][90] (FP64 path)
     DBuf<float> tH32;                    // the same in FP32 (mixed path)
-    DBuf<double> A64, Pinv;              // global matrix [nnzb][9] (FP64 path), P^-1 [nv][9]
+    DBuf<double> A64, Pinv;              // global matrix [ngroups][9][32] (FP64 path), P^-1 [nv][9]
     DBuf<float> A32, p32, r32, z32, Ap32, Pinv32;   // FP32 matrix and PCG vectors (mixed path)
+    DBuf<float> xh32, xl32;              // mixed-path PCG solution as a float pair hi + lo [3 nv]
     DBuf<double> part;                   // PCG per-block partial sums [2][blocks]
     DBuf<unsigned> counters;             // PCG last-block counters
-    DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nv]
+    DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nv] (p: [nv][4])
     DBuf<double> xhat, xt, G, dirn, tmp, P, dP, xi, xl;   // [3 nv]
     DBuf<double> cgrad64;                // contact gradient [3 nv] (FP64 path)
     DBuf<float> cgrad32;                 // contact gradient [3 nv] (mixed path)

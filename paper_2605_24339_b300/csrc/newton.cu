@@ -339,32 +339,49 @@ __global__ void k_assemble_grad(int64_t nv, const double* __restrict__ x, const 
 
 // A = M + h^2 (sum_tets H + contact H) block by block in precision TA; a
 // block in a Dirichlet row or column is the identity on the diagonal and zero
-// elsewhere
+// elsewhere.  Storage is sliced ELL: rows are taken 32 at a time (a slice),
+// each slice holds as many groups as its longest row has blocks, and group g
+// stores, for its 32 rows, element q of the rows' k-th blocks at
+// A[288 g + 32 q + lane].  One thread per stored block, in storage order, so
+// every store is coalesced; padding blocks are zero.
 template <class TH, class TC, class TA>
-__global__ void k_assemble_bsr(int64_t nnzb, const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol,
-                               const int32_t* __restrict__ bt_off, const int32_t* __restrict__ bt_ent,
-                               const TH* __restrict__ tH, const int32_t* __restrict__ cmap,
-                               const TC* __restrict__ cvals, const double* __restrict__ mass,
-                               const uint8_t* __restrict__ dir, double h2, TA* __restrict__ A) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nnzb) return;
-    const int i = brow[b], j = bcol[b];
-    TA* out = A + 9 * b;
+__global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __restrict__ goff,
+                                const int32_t* __restrict__ gslice, const int32_t* __restrict__ rp,
+                                const int32_t* __restrict__ bcol, const int32_t* __restrict__ bt_off,
+                                const int32_t* __restrict__ bt_ent, const TH* __restrict__ tH,
+                                const int32_t* __restrict__ cmap, const TC* __restrict__ cvals,
+                                const double* __restrict__ mass, const uint8_t* __restrict__ dir, double h2,
+                                TA* __restrict__ A) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = t >> 5;
+    if (g >= ngroups) return;
+    const int lane = (int)(t & 31);
+    const int sl = gslice[g];
+    const int k = (int)(g - goff[sl]);
+    const int64_t i = 32 * (int64_t)sl + lane;
+    TA* out = A + 288 * g + lane;
+    const int len = i < nv ? rp[i + 1] - rp[i] : 0;
+    if (k >= len) {
+        for (int q = 0; q < 9; ++q) out[32 * q] = TA(0);
+        return;
+    }
+    const int64_t b = rp[i] + k;
+    const int64_t j = bcol[b];
     if (dir[i] || dir[j]) {
-        for (int q = 0; q < 9; ++q) out[q] = (i == j && (q == 0 || q == 4 || q == 8)) ? TA(1) : TA(0);
+        for (int q = 0; q < 9; ++q) out[32 * q] = (i == j && (q == 0 || q == 4 || q == 8)) ? TA(1) : TA(0);
         return;
     }
     TA s[9];
     for (int q = 0; q < 9; ++q) s[q] = TA(0);
-    for (int k = bt_off[b]; k < bt_off[b + 1]; ++k) {
-        const int ent = bt_ent[k];
-        const int64_t t = ent >> 4;
+    for (int e = bt_off[b]; e < bt_off[b + 1]; ++e) {
+        const int ent = bt_ent[e];
+        const int64_t tt = ent >> 4;
         const int ma = (ent >> 2) & 3, nb = ent & 3;
         if (ma <= nb) {
-            const TH* H = tH + 90 * t + 9 * (kTetBlk[ma] + nb - ma);
+            const TH* H = tH + 90 * tt + 9 * (kTetBlk[ma] + nb - ma);
             for (int q = 0; q < 9; ++q) s[q] += (TA)H[q];
         } else {
-            const TH* H = tH + 90 * t + 9 * (kTetBlk[nb] + ma - nb);
+            const TH* H = tH + 90 * tt + 9 * (kTetBlk[nb] + ma - nb);
             for (int p = 0; p < 3; ++p)
                 for (int q = 0; q < 3; ++q) s[3 * p + q] += (TA)H[3 * q + p];
         }
@@ -375,21 +392,27 @@ __global__ void k_assemble_bsr(int64_t nnzb, const int32_t* __restrict__ brow, c
         for (int q = 0; q < 9; ++q) s[q] += (TA)C[q];
     }
     const TA h2a = (TA)h2;
-    for (int q = 0; q < 9; ++q) out[q] = h2a * s[q];
+    for (int q = 0; q < 9; ++q) s[q] *= h2a;
     if (i == j) {
         const TA m = (TA)mass[i];
-        out[0] += m; out[4] += m; out[8] += m;
+        s[0] += m; s[4] += m; s[8] += m;
     }
+    for (int q = 0; q < 9; ++q) out[32 * q] = s[q];
 }
 
 // ------------------------------------------------------------------ PCG ---
-// Fused block-Jacobi PCG: three kernels per iteration; each dot product is
-// finished by the last block to arrive, which sums the per-block partials in
-// block order (deterministic) and forms the iteration's scalars once (alpha
-// in the SpMV kernel, beta in the update kernel), so no thread divides.
-// Vectors r, z, p, Ap and the block inverse are of type V (FP64, or FP32 in
-// the mixed path); the solution and every dot product are FP64.  Solver
-// scalars (FP64):
+// Fused block-Jacobi PCG: three kernels per iteration, one thread per block
+// row in each; each dot product is finished by the last block to arrive,
+// which sums the per-block partials in block order (deterministic) and forms
+// the iteration's scalars once (alpha in the SpMV kernel, beta in the update
+// kernel), so no thread divides.  Vectors r, z, Ap ([nv][3]), the search
+// direction p ([nv][4], the fourth entry unused, so a neighbour's three
+// entries are one aligned load) and the block inverse are of type V (FP64,
+// or FP32 in the mixed path).  Dot products are formed per thread and per
+// warp in V and summed across warps and blocks in FP64 (the B300 FP64 pipe
+// runs at 1/64 of FP32, so FP64 per element would dominate the mixed path).
+// The solution is FP64 in the FP64 path and an unevaluated pair of floats
+// (hi + lo, compensated summation) in the mixed path.  Solver scalars (FP64):
 enum : int {
     kRz = 0,         // r . z of the current iteration
     kPAp = 1, kAl = 2, kBe = 3, kRr = 4, kBb = 5,
@@ -401,32 +424,36 @@ enum : int {
 };
 constexpr int kPcgThreads = 256;
 
-__device__ __forceinline__ double block_sum256(double v, double* sh) {
+// block sum: a shuffle tree in R within each warp, then the eight warp sums
+// in FP64 (fixed order); the result is valid in warp 0
+template <class R>
+__device__ __forceinline__ double block_sum256(R v, double* sh) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)v;
     __syncthreads();
     double r = 0.0;
     if (threadIdx.x < 32) {
         r = threadIdx.x < kPcgThreads / 32 ? sh[threadIdx.x] : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        for (int o = kPcgThreads / 64; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
     }
     __syncthreads();
-    return r;   // valid in warp 0
+    return r;
 }
 
-// Each block contributes (v0, v1); returns true in the last block to
-// arrive, where thread 0 then holds the fixed-order totals in *t0, *t1.
-__device__ bool last_block_sums(double v0, double v1, double* part /* [2][gridDim] */, unsigned* counter,
-                                double* t0, double* t1) {
+// Each block contributes NV values (v0, v1); returns true in the last block
+// to arrive, where thread 0 then holds the fixed-order totals in *t0, *t1.
+template <int NV, class R>
+__device__ bool last_block_sums(R v0, R v1, double* part /* [2][gridDim] */, unsigned* counter, double* t0,
+                                double* t1) {
     __shared__ double sh[kPcgThreads / 32];
     __shared__ bool am_last;
-    const double b0 = block_sum256(v0, sh);
-    const double b1 = block_sum256(v1, sh);
+    const double b0 = block_sum256<R>(v0, sh);
+    const double b1 = NV > 1 ? block_sum256<R>(v1, sh) : 0.0;
     if (threadIdx.x == 0) {
         part[blockIdx.x] = b0;
-        part[gridDim.x + blockIdx.x] = b1;
+        if (NV > 1) part[gridDim.x + blockIdx.x] = b1;
         __threadfence();
         am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
     }
@@ -437,10 +464,10 @@ __device__ bool last_block_sums(double v0, double v1, double* part /* [2][gridDi
     double s0 = 0.0, s1 = 0.0;
     for (unsigned k = threadIdx.x; k < gridDim.x; k += kPcgThreads) {
         s0 += vp[k];
-        s1 += vp[gridDim.x + k];
+        if (NV > 1) s1 += vp[gridDim.x + k];
     }
-    *t0 = block_sum256(s0, sh);
-    *t1 = block_sum256(s1, sh);
+    *t0 = block_sum256<double>(s0, sh);
+    *t1 = NV > 1 ? block_sum256<double>(s1, sh) : 0.0;
     if (threadIdx.x == 0) *counter = 0u;
     return true;
 }
@@ -452,15 +479,26 @@ __device__ __forceinline__ void mul33(const V* P, V r0, V r1, V r2, V* z) {
     z[2] = P[6] * r0 + P[7] * r1 + P[8] * r2;
 }
 
+// the three used entries of p[i] (stride 4): one 16-byte load in FP32
+__device__ __forceinline__ void load_p(const float* p, int64_t i, float& a, float& b, float& c) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+    a = v.x; b = v.y; c = v.z;
+}
+__device__ __forceinline__ void load_p(const double* p, int64_t i, double& a, double& b, double& c) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p + 4 * i));
+    a = v.x; b = v.y; c = __ldg(p + 4 * i + 2);
+}
+
 // inverse of each diagonal block (inverted in FP64, stored as V)
 template <class TA, class V>
-__global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, const TA* __restrict__ A,
-                           V* __restrict__ Pinv) {
+__global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, const int32_t* __restrict__ rp,
+                           const int32_t* __restrict__ goff, const TA* __restrict__ A, V* __restrict__ Pinv) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     double D[9], I[9];
-    const TA* B = A + 9 * (int64_t)diag_blk[v];
-    for (int q = 0; q < 9; ++q) D[q] = (double)B[q];
+    const int64_t g = goff[v >> 5] + (diag_blk[v] - rp[v]);
+    const TA* B = A + 288 * g + (v & 31);
+    for (int q = 0; q < 9; ++q) D[q] = (double)B[32 * q];
     inv3(D, I);
     for (int q = 0; q < 9; ++q) Pinv[9 * v + q] = (V)I[q];
 }
@@ -469,26 +507,32 @@ __global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, con
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
 k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bvec, double* __restrict__ x,
-           V* __restrict__ r, V* __restrict__ z, V* __restrict__ p, double* part, unsigned* counter, double* scal,
-           double rel_tol) {
+           V* __restrict__ xh, V* __restrict__ xl, V* __restrict__ r, V* __restrict__ z, V* __restrict__ p, double* part,
+           unsigned* counter, double* scal, double rel_tol) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    double bb = 0.0, rz = 0.0;
+    V bb = V(0), rz = V(0);
     if (i < nv) {
         const V b0 = (V)bvec[3 * i], b1 = (V)bvec[3 * i + 1], b2 = (V)bvec[3 * i + 2];
         V zz[3];
         mul33(Pinv + 9 * i, b0, b1, b2, zz);
         const V bv[3] = {b0, b1, b2};
         for (int q = 0; q < 3; ++q) {
-            x[3 * i + q] = 0.0;
+            if (sizeof(V) == 8) {
+                x[3 * i + q] = 0.0;
+            } else {
+                xh[3 * i + q] = V(0);
+                xl[3 * i + q] = V(0);
+            }
             r[3 * i + q] = bv[q];
             z[3 * i + q] = zz[q];
-            p[3 * i + q] = zz[q];
-            bb += (double)bv[q] * (double)bv[q];
-            rz += (double)bv[q] * (double)zz[q];
+            p[4 * i + q] = zz[q];
+            bb += bv[q] * bv[q];
+            rz += bv[q] * zz[q];
         }
+        p[4 * i + 3] = V(0);
     }
     double tb, tr;
-    if (last_block_sums(bb, rz, part, counter, &tb, &tr) && threadIdx.x == 0) {
+    if (last_block_sums<2, V>(bb, rz, part, counter, &tb, &tr) && threadIdx.x == 0) {
         scal[kBb] = tb;
         scal[kRz] = tr;
         scal[kThr] = rel_tol * sqrt(tb);
@@ -499,32 +543,45 @@ k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bv
     }
 }
 
-// Ap = A p and p.Ap; one thread per (block row, component), row sums in TA.
-// The last block sets alpha = r.z / p.Ap (or the breakdown flag).
+// Ap = A p and p.Ap; one thread per block row, over the row's blocks in
+// column order, sums in TA.  The last block sets alpha = r.z / p.Ap (or the
+// breakdown flag).
 template <class TA, class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-           const TA* __restrict__ A, const V* __restrict__ p, V* __restrict__ Ap, double* part, unsigned* counter,
-           double* scal) {
+k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ goff,
+           const int32_t* __restrict__ sci, const TA* __restrict__ A, const V* __restrict__ p, V* __restrict__ Ap,
+           double* part, unsigned* counter, double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int it = (int)scal[kIt];
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = tid / 3;
-    const int comp = (int)(tid - 3 * i);
-    double pap = 0.0;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    V pap = V(0);
     if (i < nv) {
-        TA acc = TA(0);
-        for (int k = rp[i]; k < rp[i + 1]; ++k) {
-            const TA* B = A + 9 * (int64_t)k + 3 * comp;
-            const int64_t j = ci[k];
-            acc += B[0] * (TA)p[3 * j] + B[1] * (TA)p[3 * j + 1] + B[2] * (TA)p[3 * j + 2];
+        const int64_t g0 = goff[i >> 5];
+        const int len = rp[i + 1] - rp[i];
+        const TA* B = A + 288 * g0 + (i & 31);
+        const int32_t* cj = sci + 32 * g0 + (i & 31);
+        TA a0 = TA(0), a1 = TA(0), a2 = TA(0);
+#pragma unroll 3
+        for (int k = 0; k < len; ++k) {
+            const int64_t j = __ldg(cj + 32 * k);
+            V q0, q1, q2;
+            load_p(p, j, q0, q1, q2);
+            const TA p0 = (TA)q0, p1 = (TA)q1, p2 = (TA)q2;
+            const TA* Bk = B + 288 * k;
+            a0 += __ldg(Bk) * p0 + __ldg(Bk + 32) * p1 + __ldg(Bk + 64) * p2;
+            a1 += __ldg(Bk + 96) * p0 + __ldg(Bk + 128) * p1 + __ldg(Bk + 160) * p2;
+            a2 += __ldg(Bk + 192) * p0 + __ldg(Bk + 224) * p1 + __ldg(Bk + 256) * p2;
         }
-        const V y = (V)acc;
-        Ap[3 * i + comp] = y;
-        pap = (double)p[3 * i + comp] * (double)y;
+        const V y0 = (V)a0, y1 = (V)a1, y2 = (V)a2;
+        Ap[3 * i] = y0;
+        Ap[3 * i + 1] = y1;
+        Ap[3 * i + 2] = y2;
+        V q0, q1, q2;
+        load_p(p, i, q0, q1, q2);
+        pap = q0 * y0 + q1 * y1 + q2 * y2;
     }
     double t, unused;
-    if (last_block_sums(pap, 0.0, part, counter, &t, &unused) && threadIdx.x == 0) {
+    if (last_block_sums<1, V>(pap, V(0), part, counter, &t, &unused) && threadIdx.x == 0) {
         scal[kPAp] = t;
         if (t > 0.0) {
             scal[kAl] = scal[kRz] / t;
@@ -535,24 +592,42 @@ k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict
     }
 }
 
+// hi + lo += v (Knuth's two-sum; |lo| stays below half an ulp of hi)
+__device__ __forceinline__ void add_pair(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (v - bv);
+    hi = s;
+    lo += e;
+}
+
 // x += al p, r -= al Ap, z = P^-1 r, then r.r (convergence) and r.z; the
-// last block sets beta = r.z_new / r.z and advances the iteration index
+// last block sets beta = r.z_new / r.z and advances the iteration index.
+// x is FP64 when V is FP64, else the float pair (xh, xl).
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_update(int64_t nv, const V* __restrict__ Pinv, double* __restrict__ x, V* __restrict__ r,
-             V* __restrict__ z, const V* __restrict__ p, const V* __restrict__ Ap, double* part, unsigned* counter,
-             double* scal) {
+k_pcg_update(int64_t nv, const V* __restrict__ Pinv, double* __restrict__ x, V* __restrict__ xh, V* __restrict__ xl,
+             V* __restrict__ r, V* __restrict__ z, const V* __restrict__ p, const V* __restrict__ Ap, double* part,
+             unsigned* counter, double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int it = (int)scal[kIt];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const double al = scal[kAl];
     const V alv = (V)al;
-    double rr = 0.0, rz = 0.0;
+    V rr = V(0), rz = V(0);
     if (i < nv) {
+        V pv[3];
+        load_p(p, i, pv[0], pv[1], pv[2]);
         V rv[3];
         for (int q = 0; q < 3; ++q) {
-            const V pq = p[3 * i + q];
-            x[3 * i + q] += (sizeof(V) == 8) ? al * (double)pq : (double)(alv * pq);
+            if (sizeof(V) == 8) {
+                x[3 * i + q] += al * (double)pv[q];
+            } else {
+                float hi = (float)xh[3 * i + q], lo = (float)xl[3 * i + q];
+                add_pair(hi, lo, (float)(alv * pv[q]));
+                xh[3 * i + q] = (V)hi;
+                xl[3 * i + q] = (V)lo;
+            }
             rv[q] = r[3 * i + q] - alv * Ap[3 * i + q];
             r[3 * i + q] = rv[q];
         }
@@ -560,12 +635,12 @@ k_pcg_update(int64_t nv, const V* __restrict__ Pinv, double* __restrict__ x, V* 
         mul33(Pinv + 9 * i, rv[0], rv[1], rv[2], zz);
         for (int q = 0; q < 3; ++q) {
             z[3 * i + q] = zz[q];
-            rr += (double)rv[q] * (double)rv[q];
-            rz += (double)rv[q] * (double)zz[q];
+            rr += rv[q] * rv[q];
+            rz += rv[q] * zz[q];
         }
     }
     double trr, trz;
-    if (last_block_sums(rr, rz, part, counter, &trr, &trz) && threadIdx.x == 0) {
+    if (last_block_sums<2, V>(rr, rz, part, counter, &trr, &trz) && threadIdx.x == 0) {
         scal[kRr] = trr;
         if (sqrt(trr) <= scal[kThr]) {
             scal[kDone] = 1.0;
@@ -579,15 +654,22 @@ k_pcg_update(int64_t nv, const V* __restrict__ Pinv, double* __restrict__ x, V* 
     }
 }
 
-// p = z + beta p
+// p = z + beta p, one thread per block row
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_dir(int64_t n, const V* __restrict__ z, V* __restrict__ p, const double* scal) {
+k_pcg_dir(int64_t nv, const V* __restrict__ z, V* __restrict__ p, const double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= nv) return;
     const V be = (V)scal[kBe];
-    p[i] = z[i] + be * p[i];
+    for (int q = 0; q < 3; ++q) p[4 * i + q] = z[3 * i + q] + be * p[4 * i + q];
+}
+
+// x = hi + lo in FP64 (mixed path, after the solve)
+__global__ void k_pair_to_f64(int64_t n, const float* __restrict__ hi, const float* __restrict__ lo,
+                              double* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (double)hi[i] + (double)lo[i];
 }
 
 // elementwise products into w (for a fixed-order dot product)
@@ -714,15 +796,16 @@ cudaError_t assemble_grad(Ctx& c, const double* x, const double* xhat, const voi
 cudaError_t assemble_bsr(Ctx& c) {
     NewtonState& N = *c.newton;
     const double h2 = c.prm.h * c.prm.h;
-    const unsigned g = nblk(N.nnzb, 256);
+    const unsigned g = nblk(32 * N.ngroups, 256);
+    if (g == 0) return cudaSuccess;
     if (c.P.precision == IPC_PREC_MIXED)
-        k_assemble_bsr<float, float, float><<<g, 256, 0, c.stream>>>(N.nnzb, N.brow.p, N.ci.p, N.bt_off.p, N.bt.p,
-                                                                    N.tH32.p, N.cmap.p, c.cb_val32.p, N.mass.p,
-                                                                    N.dir.p, h2, N.A32.p);
+        k_assemble_sell<float, float, float><<<g, 256, 0, c.stream>>>(
+            c.nv, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH32.p, N.cmap.p,
+            c.cb_val32.p, N.mass.p, N.dir.p, h2, N.A32.p);
     else
-        k_assemble_bsr<double, double, double><<<g, 256, 0, c.stream>>>(N.nnzb, N.brow.p, N.ci.p, N.bt_off.p,
-                                                                       N.bt.p, N.tH64.p, N.cmap.p, c.cb_val64.p,
-                                                                       N.mass.p, N.dir.p, h2, N.A64.p);
+        k_assemble_sell<double, double, double><<<g, 256, 0, c.stream>>>(
+            c.nv, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH64.p, N.cmap.p,
+            c.cb_val64.p, N.mass.p, N.dir.p, h2, N.A64.p);
     return cudaGetLastError();
 }
 
@@ -741,26 +824,29 @@ cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double*
 // after the stop return at once.  Returns the iterations taken.
 // queue `count` PCG iterations (each kernel returns at once after a stop)
 template <class TA, class V>
-static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* Ap, double* xout, int count) {
+static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* Ap, double* xout, V* xh, V* xl,
+                      int count) {
     NewtonState& N = *c.newton;
-    const int64_t nv = c.nv, n = 3 * nv;
+    const int64_t nv = c.nv;
     cudaStream_t s = c.stream;
-    const unsigned g_row = nblk(nv, kPcgThreads), g_comp = nblk(n, kPcgThreads);
+    const unsigned g_row = nblk(nv, kPcgThreads);
     for (int j = 0; j < count; ++j) {
-        k_pcg_spmv<TA, V><<<g_comp, kPcgThreads, 0, s>>>(nv, N.rp.p, N.ci.p, A, p, Ap, N.part.p,
-                                                         N.counters.p + 1, N.scal.p);
-        k_pcg_update<V><<<g_row, kPcgThreads, 0, s>>>(nv, Pinv, xout, r, z, p, Ap, N.part.p, N.counters.p + 2,
-                                                      N.scal.p);
-        k_pcg_dir<V><<<g_comp, kPcgThreads, 0, s>>>(n, z, p, N.scal.p);
+        k_pcg_spmv<TA, V><<<g_row, kPcgThreads, 0, s>>>(nv, N.rp.p, N.goff.p, N.sci.p, A, p, Ap, N.part.p,
+                                                        N.counters.p + 1, N.scal.p);
+        k_pcg_update<V><<<g_row, kPcgThreads, 0, s>>>(nv, Pinv, xout, xh, xl, r, z, p, Ap, N.part.p,
+                                                      N.counters.p + 2, N.scal.p);
+        k_pcg_dir<V><<<g_row, kPcgThreads, 0, s>>>(nv, z, p, N.scal.p);
     }
 }
 
 static cudaError_t pcg_enqueue_iters(Ctx& c, double* xout, int count) {
     NewtonState& N = *c.newton;
     if (c.P.precision == IPC_PREC_MIXED)
-        pcg_queue<float, float>(c, N.A32.p, N.Pinv32.p, N.r32.p, N.z32.p, N.p32.p, N.Ap32.p, xout, count);
+        pcg_queue<float, float>(c, N.A32.p, N.Pinv32.p, N.r32.p, N.z32.p, N.p32.p, N.Ap32.p, xout, N.xh32.p,
+                                N.xl32.p, count);
     else
-        pcg_queue<double, double>(c, N.A64.p, N.Pinv.p, N.r.p, N.z.p, N.p.p, N.Ap.p, xout, count);
+        pcg_queue<double, double>(c, N.A64.p, N.Pinv.p, N.r.p, N.z.p, N.p.p, N.Ap.p, xout, nullptr, nullptr,
+                                  count);
     GMCP_CUDA_TRY(cudaGetLastError());
     // stop flags and iteration count for the host
     return cudaMemcpyAsync(c.pin->pcg, N.scal.p + kBreak, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
@@ -776,7 +862,9 @@ static bool pcg_chunk_graph(Ctx& c, double* xout) {
                                         (uintptr_t)N.A64.p, (uintptr_t)N.Ap.p, (uintptr_t)N.Ap32.p,
                                         (uintptr_t)N.r.p, (uintptr_t)N.r32.p, (uintptr_t)N.z.p, (uintptr_t)N.z32.p,
                                         (uintptr_t)N.Pinv.p, (uintptr_t)N.Pinv32.p, (uintptr_t)N.part.p,
-                                        (uintptr_t)N.scal.p, (uintptr_t)N.counters.p, (uintptr_t)c.pin};
+                                        (uintptr_t)N.scal.p, (uintptr_t)N.counters.p, (uintptr_t)c.pin,
+                                        (uintptr_t)N.xh32.p, (uintptr_t)N.xl32.p, (uintptr_t)N.sci.p,
+                                        (uintptr_t)N.goff.p};
     if (c.pcg_graph.exec && c.pcg_graph.key == key) return true;
     c.pcg_graph.reset();
     if (!c.cap_stream && cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -817,13 +905,15 @@ cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int
     cudaStream_t s = c.stream;
     const unsigned gr = nblk(nv, kPcgThreads);
     if (c.P.precision == IPC_PREC_MIXED) {
-        k_diag_inv<float, float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A32.p, N.Pinv32.p);
-        k_pcg_init<float><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv32.p, b, xout, N.r32.p, N.z32.p, N.p32.p, N.part.p,
-                                                     N.counters.p, N.scal.p, rel_tol);
+        k_diag_inv<float, float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.rp.p, N.goff.p, N.A32.p,
+                                                                N.Pinv32.p);
+        k_pcg_init<float><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv32.p, b, xout, N.xh32.p, N.xl32.p, N.r32.p,
+                                                     N.z32.p, N.p32.p, N.part.p, N.counters.p, N.scal.p, rel_tol);
     } else {
-        k_diag_inv<double, double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.A64.p, N.Pinv.p);
-        k_pcg_init<double><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, N.r.p, N.z.p, N.p.p, N.part.p,
-                                                      N.counters.p, N.scal.p, rel_tol);
+        k_diag_inv<double, double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.rp.p, N.goff.p, N.A64.p,
+                                                                  N.Pinv.p);
+        k_pcg_init<double><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, nullptr, nullptr, N.r.p, N.z.p,
+                                                      N.p.p, N.part.p, N.counters.p, N.scal.p, rel_tol);
     }
     GMCP_CUDA_TRY(cudaGetLastError());
     const bool graph = c.graphs && !c.prof.on && pcg_chunk_graph(c, xout);
@@ -839,6 +929,10 @@ cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int
             *iters = (int)hb[2];
             break;
         }
+    }
+    if (c.P.precision == IPC_PREC_MIXED) {
+        k_pair_to_f64<<<nblk(3 * nv, 256), 256, 0, s>>>(3 * nv, N.xh32.p, N.xl32.p, xout);
+        GMCP_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
 }
@@ -892,10 +986,9 @@ cudaError_t newton_setup(Ctx& c) {
     }
     // block pattern, row by row: the diagonal, every vertex sharing a tet, and
     // the contact pattern; tb[16 t + 4 a + b] = index of block (T[a], T[b])
-    std::vector<int32_t> rp(nv + 1, 0), ci, brow;
+    std::vector<int32_t> rp(nv + 1, 0), ci;
     std::vector<int64_t> tb(16 * (size_t)nt);
     ci.reserve(16 * (size_t)nv);
-    brow.reserve(16 * (size_t)nv);
     std::vector<int32_t> row;
     for (int64_t i = 0; i < nv; ++i) {
         row.clear();
@@ -910,7 +1003,6 @@ cudaError_t newton_setup(Ctx& c) {
         const int64_t base = (int64_t)ci.size();
         if (base + (int64_t)row.size() >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
         ci.insert(ci.end(), row.begin(), row.end());
-        brow.insert(brow.end(), row.size(), (int32_t)i);
         rp[i + 1] = (int32_t)ci.size();
         for (int k = vte_off[i]; k < vte_off[i + 1]; ++k) {
             const int64_t t = vte[k] >> 2;
@@ -942,7 +1034,34 @@ cudaError_t newton_setup(Ctx& c) {
             cmap[pos] = k;
         }
 
+    // sliced-ELL layout: slice sl holds rows 32 sl .. 32 sl + 31 and as many
+    // groups of 32 blocks as its longest row; padding columns are -1
+    const int64_t nslice = (nv + 31) / 32;
+    std::vector<int32_t> goff(nslice + 1, 0);
+    for (int64_t sl = 0; sl < nslice; ++sl) {
+        int32_t w = 0;
+        for (int64_t i = 32 * sl; i < std::min<int64_t>(nv, 32 * sl + 32); ++i) w = std::max(w, rp[i + 1] - rp[i]);
+        if ((int64_t)goff[sl] + w >= ((int64_t)1 << 31) / 288) return cudaErrorInvalidValue;
+        goff[sl + 1] = goff[sl] + w;
+    }
+    const int64_t ngroups = goff[nslice];
+    std::vector<int32_t> gslice(ngroups), sci(32 * (size_t)ngroups, -1);
+    for (int64_t sl = 0; sl < nslice; ++sl)
+        for (int32_t g = goff[sl]; g < goff[sl + 1]; ++g) {
+            gslice[g] = (int32_t)sl;
+            const int k = g - goff[sl];
+            for (int lane = 0; lane < 32; ++lane) {
+                const int64_t i = 32 * sl + lane;
+                if (i < nv && k < rp[i + 1] - rp[i]) sci[32 * (size_t)g + lane] = ci[rp[i] + k];
+            }
+        }
+    N.nslice = nslice;
+    N.ngroups = ngroups;
+
     const size_t n3 = 3 * (size_t)nv;
+    GMCP_CUDA_TRY(N.goff.upload(goff.data(), goff.size(), s));
+    GMCP_CUDA_TRY(N.gslice.upload(gslice.data(), gslice.size(), s));
+    GMCP_CUDA_TRY(N.sci.upload(sci.data(), sci.size(), s));
     GMCP_CUDA_TRY(N.tets.upload(T, 4 * (size_t)nt, s));
     GMCP_CUDA_TRY(N.Dminv.upload(Dminv.data(), Dminv.size(), s));
     GMCP_CUDA_TRY(N.vol.upload(vol.data(), vol.size(), s));
@@ -952,7 +1071,6 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.vte.upload(vte.data(), vte.size(), s));
     GMCP_CUDA_TRY(N.rp.upload(rp.data(), rp.size(), s));
     GMCP_CUDA_TRY(N.ci.upload(ci.data(), ci.size(), s));
-    GMCP_CUDA_TRY(N.brow.upload(brow.data(), brow.size(), s));
     GMCP_CUDA_TRY(N.diag.upload(diag.data(), diag.size(), s));
     GMCP_CUDA_TRY(N.bt_off.upload(bt_off.data(), bt_off.size(), s));
     GMCP_CUDA_TRY(N.bt.upload(bt.data(), bt.size(), s));
@@ -964,18 +1082,20 @@ cudaError_t newton_setup(Ctx& c) {
     else GMCP_CUDA_TRY(N.tH64.ensure(90 * (size_t)nt + 90));
     GMCP_CUDA_TRY(N.tE8.ensure(8 * (size_t)nt + 8));
     if (f32) {
-        GMCP_CUDA_TRY(N.A32.ensure(9 * (size_t)nnzb));
-        for (DBuf<float>* b : {&N.p32, &N.r32, &N.z32, &N.Ap32}) GMCP_CUDA_TRY(b->ensure(3 * (size_t)nv));
+        GMCP_CUDA_TRY(N.A32.ensure(288 * (size_t)ngroups + 288));
+        for (DBuf<float>* b : {&N.r32, &N.z32, &N.Ap32, &N.xh32, &N.xl32}) GMCP_CUDA_TRY(b->ensure(3 * (size_t)nv));
+        GMCP_CUDA_TRY(N.p32.ensure(4 * (size_t)nv));
         GMCP_CUDA_TRY(N.Pinv32.ensure(9 * (size_t)nv));
     } else {
-        GMCP_CUDA_TRY(N.A64.ensure(9 * (size_t)nnzb));
+        GMCP_CUDA_TRY(N.A64.ensure(288 * (size_t)ngroups + 288));
     }
-    GMCP_CUDA_TRY(N.part.ensure(2 * (size_t)nblk(3 * nv, 256) + 2));
+    GMCP_CUDA_TRY(N.part.ensure(2 * (size_t)nblk(nv, kPcgThreads) + 2));
     GMCP_CUDA_TRY(N.counters.ensure(4));
     GMCP_CUDA_TRY(cudaMemsetAsync(N.counters.p, 0, 4 * sizeof(unsigned), s));
     GMCP_CUDA_TRY(N.Pinv.ensure(9 * (size_t)nv));
-    for (DBuf<double>* b : {&N.r, &N.z, &N.p, &N.Ap, &N.w, &N.xhat, &N.xt, &N.G, &N.dirn, &N.tmp, &N.P, &N.dP, &N.xi, &N.xl})
+    for (DBuf<double>* b : {&N.r, &N.z, &N.Ap, &N.w, &N.xhat, &N.xt, &N.G, &N.dirn, &N.tmp, &N.P, &N.dP, &N.xi, &N.xl})
         GMCP_CUDA_TRY(b->ensure(n3));
+    GMCP_CUDA_TRY(N.p.ensure(4 * (size_t)nv));
     if (f32) GMCP_CUDA_TRY(N.cgrad32.ensure(n3));
     else GMCP_CUDA_TRY(N.cgrad64.ensure(n3));
     GMCP_CUDA_TRY(N.xm.ensure(3 * (size_t)c.nmv + 3));
