@@ -543,11 +543,12 @@ def run_mlp(args):
 
 def run_newton(args):
     """--steps time steps of the gel_on_terrain press from rest (the command
-    line for profiling the time-stepper kernels)."""
+    line for profiling the time-stepper kernels); --newton-quads sets the
+    pad's quads per side (256 in the measured workload)."""
     import torch
     from paper_2605_24339_b300 import binding
     from paper_2605_24339_b300 import scenes as S
-    sc = S.gel_on_terrain()
+    sc = S.gel_on_terrain(n_quads=args.newton_quads)
     ctx = binding.Context(sc, precision=args.precision)
     x = torch.as_tensor(sc.X.copy(), device="cuda")
     v = torch.as_tensor(sc.v_dirichlet.copy(), device="cuda")
@@ -610,6 +611,8 @@ def main():
                     help="skip the time-step measurement (newton_step key)")
     ap.add_argument("--batch-envs", type=int, default=512,
                     help="environments in the batched measurement")
+    ap.add_argument("--newton-quads", type=int, default=256,
+                    help="--mode newton: gel pad quads per side (256 = the measured workload)")
     ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
                          "training steps or time steps (command lines for profilers); batch: "

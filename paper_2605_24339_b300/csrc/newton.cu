@@ -337,13 +337,23 @@ __global__ void k_assemble_grad(int64_t nv, const double* __restrict__ x, const 
     G[3 * v + 2] = m * (x[3 * v + 2] - xhat[3 * v + 2]) + h2 * (e2 + c2);
 }
 
+// Sliced-ELL storage of the matrix: rows are taken 32 at a time (a slice),
+// each slice holds as many groups as its longest row has blocks, and group g
+// holds the k-th blocks of its 32 rows (lane = row mod 32) in 288 entries.
+// Entries 0..7 of a block sit in 16-byte vectors of VW = 16 / sizeof(TA)
+// entries, vector c of all 32 lanes side by side; entry 8 follows for all
+// lanes.  A warp thus reads a group with two (FP32) or four (FP64) coalesced
+// 16-byte loads and one 4- or 8-byte load per thread.
+template <class TA>
+__host__ __device__ __forceinline__ int64_t sell_idx(int64_t g, int lane, int q) {
+    constexpr int VW = 16 / (int)sizeof(TA);
+    return q < 8 ? 288 * g + 32 * VW * (q / VW) + VW * lane + q % VW : 288 * g + 256 + lane;
+}
+
 // A = M + h^2 (sum_tets H + contact H) block by block in precision TA; a
 // block in a Dirichlet row or column is the identity on the diagonal and zero
-// elsewhere.  Storage is sliced ELL: rows are taken 32 at a time (a slice),
-// each slice holds as many groups as its longest row has blocks, and group g
-// stores, for its 32 rows, element q of the rows' k-th blocks at
-// A[288 g + 32 q + lane].  One thread per stored block, in storage order, so
-// every store is coalesced; padding blocks are zero.
+// elsewhere.  One thread per stored block, in storage order, so every store
+// is coalesced; padding blocks are zero.
 template <class TH, class TC, class TA>
 __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __restrict__ goff,
                                 const int32_t* __restrict__ gslice, const int32_t* __restrict__ rp,
@@ -359,16 +369,16 @@ __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __re
     const int sl = gslice[g];
     const int k = (int)(g - goff[sl]);
     const int64_t i = 32 * (int64_t)sl + lane;
-    TA* out = A + 288 * g + lane;
     const int len = i < nv ? rp[i + 1] - rp[i] : 0;
     if (k >= len) {
-        for (int q = 0; q < 9; ++q) out[32 * q] = TA(0);
+        for (int q = 0; q < 9; ++q) A[sell_idx<TA>(g, lane, q)] = TA(0);
         return;
     }
     const int64_t b = rp[i] + k;
     const int64_t j = bcol[b];
     if (dir[i] || dir[j]) {
-        for (int q = 0; q < 9; ++q) out[32 * q] = (i == j && (q == 0 || q == 4 || q == 8)) ? TA(1) : TA(0);
+        for (int q = 0; q < 9; ++q)
+            A[sell_idx<TA>(g, lane, q)] = (i == j && (q == 0 || q == 4 || q == 8)) ? TA(1) : TA(0);
         return;
     }
     TA s[9];
@@ -397,7 +407,7 @@ __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __re
         const TA m = (TA)mass[i];
         s[0] += m; s[4] += m; s[8] += m;
     }
-    for (int q = 0; q < 9; ++q) out[32 * q] = s[q];
+    for (int q = 0; q < 9; ++q) A[sell_idx<TA>(g, lane, q)] = s[q];
 }
 
 // ------------------------------------------------------------------ PCG ---
@@ -424,22 +434,32 @@ enum : int {
 };
 constexpr int kPcgThreads = 256;
 
-// block sum: a shuffle tree in R within each warp, then the eight warp sums
-// in FP64 (fixed order); the result is valid in warp 0
-template <class R>
-__device__ __forceinline__ double block_sum256(R v, double* sh) {
+// block sums of v0 and v1 (NV = 1 or 2): a shuffle tree in R within each
+// warp, then the eight warp sums in FP64 (fixed order); valid in warp 0
+template <int NV, class R>
+__device__ __forceinline__ void block_sums256(R v0, R v1, double (*sh)[kPcgThreads / 32], double* b0, double* b1) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = (double)v;
-    __syncthreads();
-    double r = 0.0;
-    if (threadIdx.x < 32) {
-        r = threadIdx.x < kPcgThreads / 32 ? sh[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = kPcgThreads / 64; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        if (NV > 1) v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = (double)v0;
+        if (NV > 1) sh[1][threadIdx.x >> 5] = (double)v1;
     }
     __syncthreads();
-    return r;
+    if (threadIdx.x < 32) {
+        const bool in = threadIdx.x < kPcgThreads / 32;
+        double r0 = in ? sh[0][threadIdx.x] : 0.0;
+        double r1 = (NV > 1 && in) ? sh[1][threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = kPcgThreads / 64; o > 0; o >>= 1) {
+            r0 += __shfl_xor_sync(0xffffffffu, r0, o);
+            if (NV > 1) r1 += __shfl_xor_sync(0xffffffffu, r1, o);
+        }
+        *b0 = r0;
+        *b1 = r1;
+    }
 }
 
 // Each block contributes NV values (v0, v1); returns true in the last block
@@ -447,10 +467,10 @@ __device__ __forceinline__ double block_sum256(R v, double* sh) {
 template <int NV, class R>
 __device__ bool last_block_sums(R v0, R v1, double* part /* [2][gridDim] */, unsigned* counter, double* t0,
                                 double* t1) {
-    __shared__ double sh[kPcgThreads / 32];
+    __shared__ double sh[2][kPcgThreads / 32];
     __shared__ bool am_last;
-    const double b0 = block_sum256<R>(v0, sh);
-    const double b1 = NV > 1 ? block_sum256<R>(v1, sh) : 0.0;
+    double b0 = 0.0, b1 = 0.0;
+    block_sums256<NV, R>(v0, v1, sh, &b0, &b1);
     if (threadIdx.x == 0) {
         part[blockIdx.x] = b0;
         if (NV > 1) part[gridDim.x + blockIdx.x] = b1;
@@ -466,8 +486,8 @@ __device__ bool last_block_sums(R v0, R v1, double* part /* [2][gridDim] */, uns
         s0 += vp[k];
         if (NV > 1) s1 += vp[gridDim.x + k];
     }
-    *t0 = block_sum256<double>(s0, sh);
-    *t1 = NV > 1 ? block_sum256<double>(s1, sh) : 0.0;
+    __syncthreads();   // the first pass's readers of sh are done
+    block_sums256<NV, double>(s0, s1, sh, t0, t1);
     if (threadIdx.x == 0) *counter = 0u;
     return true;
 }
@@ -489,6 +509,23 @@ __device__ __forceinline__ void load_p(const double* p, int64_t i, double& a, do
     a = v.x; b = v.y; c = __ldg(p + 4 * i + 2);
 }
 
+// the nine entries of the stored block (g, lane)
+__device__ __forceinline__ void load_blk(const float* A, int64_t g, int lane, float* b) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(A + sell_idx<float>(g, lane, 0)));
+    const float4 v = __ldg(reinterpret_cast<const float4*>(A + sell_idx<float>(g, lane, 4)));
+    b[0] = u.x; b[1] = u.y; b[2] = u.z; b[3] = u.w;
+    b[4] = v.x; b[5] = v.y; b[6] = v.z; b[7] = v.w;
+    b[8] = __ldg(A + sell_idx<float>(g, lane, 8));
+}
+__device__ __forceinline__ void load_blk(const double* A, int64_t g, int lane, double* b) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double2 u = __ldg(reinterpret_cast<const double2*>(A + sell_idx<double>(g, lane, 2 * c)));
+        b[2 * c] = u.x; b[2 * c + 1] = u.y;
+    }
+    b[8] = __ldg(A + sell_idx<double>(g, lane, 8));
+}
+
 // inverse of each diagonal block (inverted in FP64, stored as V)
 template <class TA, class V>
 __global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, const int32_t* __restrict__ rp,
@@ -497,8 +534,7 @@ __global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, con
     if (v >= nv) return;
     double D[9], I[9];
     const int64_t g = goff[v >> 5] + (diag_blk[v] - rp[v]);
-    const TA* B = A + 288 * g + (v & 31);
-    for (int q = 0; q < 9; ++q) D[q] = (double)B[32 * q];
+    for (int q = 0; q < 9; ++q) D[q] = (double)A[sell_idx<TA>(g, (int)(v & 31), q)];
     inv3(D, I);
     for (int q = 0; q < 9; ++q) Pinv[9 * v + q] = (V)I[q];
 }
@@ -557,20 +593,33 @@ k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict
     V pap = V(0);
     if (i < nv) {
         const int64_t g0 = goff[i >> 5];
+        const int lane = (int)(i & 31);
         const int len = rp[i + 1] - rp[i];
-        const TA* B = A + 288 * g0 + (i & 31);
-        const int32_t* cj = sci + 32 * g0 + (i & 31);
+        const int32_t* cj = sci + 32 * g0 + lane;
         TA a0 = TA(0), a1 = TA(0), a2 = TA(0);
-#pragma unroll 3
+        // software pipeline: the column two blocks ahead, the block and p one
+        // block ahead are in flight while a block is multiplied
+        TA bn[9];
+        V qn0 = V(0), qn1 = V(0), qn2 = V(0);
+        int64_t j2 = 0;
+        if (len > 0) {
+            load_blk(A, g0, lane, bn);
+            load_p(p, __ldg(cj), qn0, qn1, qn2);
+        }
+        if (len > 1) j2 = __ldg(cj + 32);
         for (int k = 0; k < len; ++k) {
-            const int64_t j = __ldg(cj + 32 * k);
-            V q0, q1, q2;
-            load_p(p, j, q0, q1, q2);
-            const TA p0 = (TA)q0, p1 = (TA)q1, p2 = (TA)q2;
-            const TA* Bk = B + 288 * k;
-            a0 += __ldg(Bk) * p0 + __ldg(Bk + 32) * p1 + __ldg(Bk + 64) * p2;
-            a1 += __ldg(Bk + 96) * p0 + __ldg(Bk + 128) * p1 + __ldg(Bk + 160) * p2;
-            a2 += __ldg(Bk + 192) * p0 + __ldg(Bk + 224) * p1 + __ldg(Bk + 256) * p2;
+            TA b[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) b[q] = bn[q];
+            const TA p0 = (TA)qn0, p1 = (TA)qn1, p2 = (TA)qn2;
+            if (k + 1 < len) {
+                load_blk(A, g0 + k + 1, lane, bn);
+                load_p(p, j2, qn0, qn1, qn2);
+                if (k + 2 < len) j2 = __ldg(cj + 32 * (k + 2));
+            }
+            a0 += b[0] * p0 + b[1] * p1 + b[2] * p2;
+            a1 += b[3] * p0 + b[4] * p1 + b[5] * p2;
+            a2 += b[6] * p0 + b[7] * p1 + b[8] * p2;
         }
         const V y0 = (V)a0, y1 = (V)a1, y2 = (V)a2;
         Ap[3 * i] = y0;
