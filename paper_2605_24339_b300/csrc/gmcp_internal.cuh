@@ -205,6 +205,7 @@ struct NewtonState {
     DBuf<int32_t> vte_off, vte;          // vertex -> tet corner (t*4+a)
     DBuf<int32_t> rp, ci;                // block pattern (CSR)
     int64_t nslice = 0, ngroups = 0;     // sliced-ELL storage of the matrix: 32 rows per slice
+    int64_t nvp = 0;                     // PCG vector rows: nv padded to a multiple of 4 (padding zero)
     DBuf<int32_t> goff;                  // [nslice + 1] first group (32 stored blocks) of each slice
     DBuf<int32_t> gslice;                // [ngroups] slice of each group
     DBuf<int32_t> sci;                   // [ngroups][32] column of each stored block, -1 for padding
@@ -214,12 +215,12 @@ struct NewtonState {
     DBuf<double> tE, tG, tE8;            // per-tet energy [nt], gradient [nt][12], energies [8][nt]
     DBuf<double> tH64;                   // per-tet Hessian, 10 blocks [nt][90] (FP64 path)
     DBuf<float> tH32;                    // the same in FP32 (mixed path)
-    DBuf<double> A64, Pinv;              // global matrix [ngroups][9][32] (FP64 path), P^-1 [nv][9]
+    DBuf<double> A64, Pinv;              // global matrix [ngroups][288] (FP64 path), P^-1 [nvp][9]
     DBuf<float> A32, p32, r32, z32, Ap32, Pinv32;   // FP32 matrix and PCG vectors (mixed path)
-    DBuf<float> xh32, xl32;              // mixed-path PCG solution as a float pair hi + lo [3 nv]
+    DBuf<float> xh32, xl32;              // mixed-path PCG solution as a float pair hi + lo [3 nvp]
     DBuf<double> part;                   // PCG per-block partial sums [2][blocks]
     DBuf<unsigned> counters;             // PCG last-block counters
-    DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nv] (p: [nv][4])
+    DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nvp] (p: [nvp][4]); w [3 nv]
     DBuf<double> xhat, xt, G, dirn, tmp, P, dP, xi, xl;   // [3 nv]
     DBuf<double> cgrad64;                // contact gradient [3 nv] (FP64 path)
     DBuf<float> cgrad32;                 // contact gradient [3 nv] (mixed path)

@@ -650,42 +650,110 @@ __device__ __forceinline__ void add_pair(float& hi, float& lo, float v) {
     lo += e;
 }
 
+// rows handled by one thread of the update and direction kernels: four in
+// FP32, two in FP64, so that a thread's rows of every vector are whole
+// 16-byte vectors (the vectors are padded to a multiple of four rows)
+template <class V>
+struct PcgRows {
+    static constexpr int R = sizeof(V) == 4 ? 4 : 2;
+};
+
+// n consecutive values of V (n * sizeof(V) a multiple of 16, 16-byte aligned)
+template <class V, int N>
+__device__ __forceinline__ void ldv(const V* __restrict__ src, V* dst) {
+    if constexpr (sizeof(V) == 4) {
+#pragma unroll
+        for (int c = 0; c < N / 4; ++c) {
+            const float4 u = __ldg(reinterpret_cast<const float4*>(src) + c);
+            dst[4 * c] = u.x; dst[4 * c + 1] = u.y; dst[4 * c + 2] = u.z; dst[4 * c + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) {
+            const double2 u = __ldg(reinterpret_cast<const double2*>(src) + c);
+            dst[2 * c] = u.x; dst[2 * c + 1] = u.y;
+        }
+    }
+}
+template <class V, int N>
+__device__ __forceinline__ void ldv_rw(const V* src, V* dst) {   // for buffers the kernel also writes
+    if constexpr (sizeof(V) == 4) {
+#pragma unroll
+        for (int c = 0; c < N / 4; ++c) {
+            const float4 u = reinterpret_cast<const float4*>(src)[c];
+            dst[4 * c] = u.x; dst[4 * c + 1] = u.y; dst[4 * c + 2] = u.z; dst[4 * c + 3] = u.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) {
+            const double2 u = reinterpret_cast<const double2*>(src)[c];
+            dst[2 * c] = u.x; dst[2 * c + 1] = u.y;
+        }
+    }
+}
+template <class V, int N>
+__device__ __forceinline__ void stv(V* dst, const V* src) {
+    if constexpr (sizeof(V) == 4) {
+#pragma unroll
+        for (int c = 0; c < N / 4; ++c)
+            reinterpret_cast<float4*>(dst)[c] = make_float4(src[4 * c], src[4 * c + 1], src[4 * c + 2], src[4 * c + 3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c)
+            reinterpret_cast<double2*>(dst)[c] = make_double2(src[2 * c], src[2 * c + 1]);
+    }
+}
+
 // x += al p, r -= al Ap, z = P^-1 r, then r.r (convergence) and r.z; the
 // last block sets beta = r.z_new / r.z and advances the iteration index.
-// x is FP64 when V is FP64, else the float pair (xh, xl).
+// PcgRows<V>::R rows per thread over the padded rows nvp; x is FP64 (rows
+// below nv) when V is FP64, else the float pair (xh, xl).
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_update(int64_t nv, const V* __restrict__ Pinv, double* __restrict__ x, V* __restrict__ xh, V* __restrict__ xl,
-             V* __restrict__ r, V* __restrict__ z, const V* __restrict__ p, const V* __restrict__ Ap, double* part,
-             unsigned* counter, double* scal) {
+k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __restrict__ x, V* __restrict__ xh,
+             V* __restrict__ xl, V* __restrict__ r, V* __restrict__ z, const V* __restrict__ p,
+             const V* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
+    constexpr int R = PcgRows<V>::R;
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int it = (int)scal[kIt];
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = R * t;
     const double al = scal[kAl];
     const V alv = (V)al;
     V rr = V(0), rz = V(0);
-    if (i < nv) {
-        V pv[3];
-        load_p(p, i, pv[0], pv[1], pv[2]);
-        V rv[3];
-        for (int q = 0; q < 3; ++q) {
-            if (sizeof(V) == 8) {
-                x[3 * i + q] += al * (double)pv[q];
-            } else {
-                float hi = (float)xh[3 * i + q], lo = (float)xl[3 * i + q];
-                add_pair(hi, lo, (float)(alv * pv[q]));
-                xh[3 * i + q] = (V)hi;
-                xl[3 * i + q] = (V)lo;
-            }
-            rv[q] = r[3 * i + q] - alv * Ap[3 * i + q];
-            r[3 * i + q] = rv[q];
+    if (i0 < nvp) {
+        V pv[4 * R], av[3 * R], rv[3 * R];
+        ldv<V, 4 * R>(p + 4 * i0, pv);
+        ldv<V, 3 * R>(Ap + 3 * i0, av);
+        ldv_rw<V, 3 * R>(r + 3 * i0, rv);
+        if constexpr (sizeof(V) == 4) {
+            V hv[3 * R], lv[3 * R];
+            ldv_rw<V, 3 * R>(xh + 3 * i0, hv);
+            ldv_rw<V, 3 * R>(xl + 3 * i0, lv);
+#pragma unroll
+            for (int a = 0; a < R; ++a)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) add_pair(hv[3 * a + q], lv[3 * a + q], alv * pv[4 * a + q]);
+            stv<V, 3 * R>(xh + 3 * i0, hv);
+            stv<V, 3 * R>(xl + 3 * i0, lv);
+        } else {
+#pragma unroll
+            for (int a = 0; a < R; ++a)
+                if (i0 + a < nv)
+                    for (int q = 0; q < 3; ++q) x[3 * (i0 + a) + q] += al * (double)pv[4 * a + q];
         }
-        V zz[3];
-        mul33(Pinv + 9 * i, rv[0], rv[1], rv[2], zz);
-        for (int q = 0; q < 3; ++q) {
-            z[3 * i + q] = zz[q];
-            rr += rv[q] * rv[q];
-            rz += rv[q] * zz[q];
+#pragma unroll
+        for (int e = 0; e < 3 * R; ++e) rv[e] -= alv * av[e];
+        stv<V, 3 * R>(r + 3 * i0, rv);
+        V P[9 * R], zz[3 * R];
+        ldv<V, 9 * R>(Pinv + 9 * i0, P);
+#pragma unroll
+        for (int a = 0; a < R; ++a) mul33(P + 9 * a, rv[3 * a], rv[3 * a + 1], rv[3 * a + 2], zz + 3 * a);
+        stv<V, 3 * R>(z + 3 * i0, zz);
+#pragma unroll
+        for (int e = 0; e < 3 * R; ++e) {
+            rr += rv[e] * rv[e];
+            rz += rv[e] * zz[e];
         }
     }
     double trr, trz;
@@ -703,15 +771,23 @@ k_pcg_update(int64_t nv, const V* __restrict__ Pinv, double* __restrict__ x, V* 
     }
 }
 
-// p = z + beta p, one thread per block row
+// p = z + beta p, PcgRows<V>::R rows per thread over the padded rows
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_dir(int64_t nv, const V* __restrict__ z, V* __restrict__ p, const double* scal) {
+k_pcg_dir(int64_t nvp, const V* __restrict__ z, V* __restrict__ p, const double* scal) {
+    constexpr int R = PcgRows<V>::R;
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nv) return;
+    const int64_t i0 = R * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= nvp) return;
     const V be = (V)scal[kBe];
-    for (int q = 0; q < 3; ++q) p[4 * i + q] = z[3 * i + q] + be * p[4 * i + q];
+    V zv[3 * R], pv[4 * R];
+    ldv<V, 3 * R>(z + 3 * i0, zv);
+    ldv_rw<V, 4 * R>(p + 4 * i0, pv);
+#pragma unroll
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) pv[4 * a + q] = zv[3 * a + q] + be * pv[4 * a + q];
+    stv<V, 4 * R>(p + 4 * i0, pv);
 }
 
 // x = hi + lo in FP64 (mixed path, after the solve)
@@ -879,12 +955,14 @@ static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* A
     const int64_t nv = c.nv;
     cudaStream_t s = c.stream;
     const unsigned g_row = nblk(nv, kPcgThreads);
+    const int64_t nvp = N.nvp;
+    const unsigned g_multi = nblk(nvp / PcgRows<V>::R, kPcgThreads);
     for (int j = 0; j < count; ++j) {
         k_pcg_spmv<TA, V><<<g_row, kPcgThreads, 0, s>>>(nv, N.rp.p, N.goff.p, N.sci.p, A, p, Ap, N.part.p,
                                                         N.counters.p + 1, N.scal.p);
-        k_pcg_update<V><<<g_row, kPcgThreads, 0, s>>>(nv, Pinv, xout, xh, xl, r, z, p, Ap, N.part.p,
-                                                      N.counters.p + 2, N.scal.p);
-        k_pcg_dir<V><<<g_row, kPcgThreads, 0, s>>>(nv, z, p, N.scal.p);
+        k_pcg_update<V><<<g_multi, kPcgThreads, 0, s>>>(nv, nvp, Pinv, xout, xh, xl, r, z, p, Ap, N.part.p,
+                                                        N.counters.p + 2, N.scal.p);
+        k_pcg_dir<V><<<g_multi, kPcgThreads, 0, s>>>(nvp, z, p, N.scal.p);
     }
 }
 
@@ -1130,21 +1208,35 @@ cudaError_t newton_setup(Ctx& c) {
     if (f32) GMCP_CUDA_TRY(N.tH32.ensure(90 * (size_t)nt + 90));
     else GMCP_CUDA_TRY(N.tH64.ensure(90 * (size_t)nt + 90));
     GMCP_CUDA_TRY(N.tE8.ensure(8 * (size_t)nt + 8));
+    // PCG vectors: rows padded to a multiple of four, the padding zero
+    const int64_t nvp = (nv + 3) / 4 * 4;
+    N.nvp = nvp;
     if (f32) {
         GMCP_CUDA_TRY(N.A32.ensure(288 * (size_t)ngroups + 288));
-        for (DBuf<float>* b : {&N.r32, &N.z32, &N.Ap32, &N.xh32, &N.xl32}) GMCP_CUDA_TRY(b->ensure(3 * (size_t)nv));
-        GMCP_CUDA_TRY(N.p32.ensure(4 * (size_t)nv));
-        GMCP_CUDA_TRY(N.Pinv32.ensure(9 * (size_t)nv));
+        for (DBuf<float>* b : {&N.r32, &N.z32, &N.Ap32, &N.xh32, &N.xl32}) {
+            GMCP_CUDA_TRY(b->ensure(3 * (size_t)nvp));
+            GMCP_CUDA_TRY(cudaMemsetAsync(b->p, 0, sizeof(float) * 3 * nvp, s));
+        }
+        GMCP_CUDA_TRY(N.p32.ensure(4 * (size_t)nvp));
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.p32.p, 0, sizeof(float) * 4 * nvp, s));
+        GMCP_CUDA_TRY(N.Pinv32.ensure(9 * (size_t)nvp));
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.Pinv32.p, 0, sizeof(float) * 9 * nvp, s));
     } else {
         GMCP_CUDA_TRY(N.A64.ensure(288 * (size_t)ngroups + 288));
+        for (DBuf<double>* b : {&N.r, &N.z, &N.Ap}) {
+            GMCP_CUDA_TRY(b->ensure(3 * (size_t)nvp));
+            GMCP_CUDA_TRY(cudaMemsetAsync(b->p, 0, sizeof(double) * 3 * nvp, s));
+        }
+        GMCP_CUDA_TRY(N.p.ensure(4 * (size_t)nvp));
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.p.p, 0, sizeof(double) * 4 * nvp, s));
+        GMCP_CUDA_TRY(N.Pinv.ensure(9 * (size_t)nvp));
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.Pinv.p, 0, sizeof(double) * 9 * nvp, s));
     }
     GMCP_CUDA_TRY(N.part.ensure(2 * (size_t)nblk(nv, kPcgThreads) + 2));
     GMCP_CUDA_TRY(N.counters.ensure(4));
     GMCP_CUDA_TRY(cudaMemsetAsync(N.counters.p, 0, 4 * sizeof(unsigned), s));
-    GMCP_CUDA_TRY(N.Pinv.ensure(9 * (size_t)nv));
-    for (DBuf<double>* b : {&N.r, &N.z, &N.Ap, &N.w, &N.xhat, &N.xt, &N.G, &N.dirn, &N.tmp, &N.P, &N.dP, &N.xi, &N.xl})
+    for (DBuf<double>* b : {&N.w, &N.xhat, &N.xt, &N.G, &N.dirn, &N.tmp, &N.P, &N.dP, &N.xi, &N.xl})
         GMCP_CUDA_TRY(b->ensure(n3));
-    GMCP_CUDA_TRY(N.p.ensure(4 * (size_t)nv));
     if (f32) GMCP_CUDA_TRY(N.cgrad32.ensure(n3));
     else GMCP_CUDA_TRY(N.cgrad64.ensure(n3));
     GMCP_CUDA_TRY(N.xm.ensure(3 * (size_t)c.nmv + 3));
