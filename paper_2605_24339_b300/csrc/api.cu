@@ -516,7 +516,7 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
             GMCP_CUDA_TRY(cudaMemcpyAsync(N.alphas.p, als, sizeof(double) * (nk + 1), cudaMemcpyHostToDevice, s));
             {
                 ProfScope ps(c.prof, s, "line_search");
-                GMCP_CUDA_TRY(energy_batch(c, x, N.dirn.p, N.alphas.p, nk + 1, true, sc + 48));
+                GMCP_CUDA_TRY(energy_batch(c, x, N.dirn.p, N.alphas.p, nk + 1, true, sc + 48, sc + 57));
             }
             GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 48, sizeof(double) * (nk + 1), cudaMemcpyDeviceToHost, s));
             GMCP_CUDA_TRY(cudaStreamSynchronize(s));

@@ -431,8 +431,11 @@ cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev,
 // +inf where some tet has J <= 0
 cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_dev,
                             int na, double* energies_dev);
+// total energies at x + alphas[j] p into out_dev[j]; with ee0_dev (alphas[0]
+// = 0 and the elastic energy at x already summed there) the elastic energy
+// of slot 0 is taken from it instead of being evaluated again
 cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_dev, int na,
-                         bool with_contact, double* out_dev);
+                         bool with_contact, double* out_dev, const double* ee0_dev = nullptr);
 cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess, double* Ec_dev, double* Ee_dev,
                             double* E_dev, double* gnorm2_dev);
 cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double* out);

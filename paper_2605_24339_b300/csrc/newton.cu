@@ -1261,10 +1261,17 @@ cudaError_t newton_setup(Ctx& c) {
 // out_dev[j]; the contact term is the frozen-linear potential of the samples
 // active at x (requires the candidate lists of x)
 cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_dev, int na,
-                         bool with_contact, double* out_dev) {
+                         bool with_contact, double* out_dev, const double* ee0_dev) {
     NewtonState& N = *c.newton;
     double* sc = N.scal.p;   // [16..23] Ein  [24..31] Ee  [32..39] Ec
-    GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_dev, na, sc + 24));
+    if (ee0_dev && na > 1) {
+        // alphas[0] = 0: the elastic energy at x is known (same per-tet
+        // values and the same fixed-order sum)
+        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_dev + 1, na - 1, sc + 25));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(sc + 24, ee0_dev, sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    } else {
+        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_dev, na, sc + 24));
+    }
     k_inertia_multi<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, p, N.xhat.p, N.mass.p, alphas_dev, na, N.ein8.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     for (int j = 0; j < na; ++j) GMCP_CUDA_TRY(reduce_sum(c, N.ein8.p + (int64_t)j * c.nv, c.nv, sc + 16 + j));
