@@ -216,11 +216,11 @@ struct NewtonState {
     DBuf<double> tH64;                   // per-tet Hessian, 10 blocks [nt][90] (FP64 path)
     DBuf<float> tH32;                    // the same in FP32 (mixed path)
     DBuf<double> A64, Pinv;              // global matrix [ngroups][288] (FP64 path), P^-1 [nvp][9]
-    DBuf<float> A32, p32, r32, z32, Ap32, Pinv32;   // FP32 matrix and PCG vectors (mixed path)
+    DBuf<float> A32, p32, r32, z32, Ap32, Pinv32;   // FP32 matrix and PCG vectors (mixed path; z [nvp][4], p [2][nvp][4])
     DBuf<float> xh32, xl32;              // mixed-path PCG solution as a float pair hi + lo [3 nvp]
     DBuf<double> part;                   // PCG per-block partial sums [2][blocks]
     DBuf<unsigned> counters;             // PCG last-block counters
-    DBuf<double> r, z, p, Ap, w;         // PCG vectors [3 nvp] (p: [nvp][4]); w [3 nv]
+    DBuf<double> r, z, p, Ap, w;         // PCG vectors r, z, Ap [3 nvp], p [nvp][4]; w [3 nv]
     DBuf<double> xhat, xt, G, dirn, tmp, P, dP, xi, xl;   // [3 nv]
     DBuf<double> cgrad64;                // contact gradient [3 nv] (FP64 path)
     DBuf<float> cgrad32;                 // contact gradient [3 nv] (mixed path)

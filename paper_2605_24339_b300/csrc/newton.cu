@@ -434,6 +434,13 @@ enum : int {
 };
 constexpr int kPcgThreads = 256;
 
+// whether the SpMV forms the search direction itself (FP32; see k_pcg_spmv)
+template <class V>
+struct PcgDir {
+    static constexpr bool kFused = sizeof(V) == 4;
+    static constexpr int kZs = kFused ? 4 : 3;   // row stride of z (4: gathered by the SpMV)
+};
+
 // block sums of v0 and v1 (NV = 1 or 2): a shuffle tree in R within each
 // warp, then the eight warp sums in FP64 (fixed order); valid in warp 0
 template <int NV, class R>
@@ -539,7 +546,9 @@ __global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, con
     for (int q = 0; q < 9; ++q) Pinv[9 * v + q] = (V)I[q];
 }
 
-// x = 0, r = b, z = P^-1 b, p = z; b.b and r.z
+// x = 0, r = b, z = P^-1 b; p = z (FP64), or, where the SpMV forms the
+// direction, p (first of the pair) = 0 and beta = 0 so that it forms p = z;
+// b.b and r.z
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
 k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bvec, double* __restrict__ x,
@@ -560,11 +569,12 @@ k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bv
                 xl[3 * i + q] = V(0);
             }
             r[3 * i + q] = bv[q];
-            z[3 * i + q] = zz[q];
-            p[4 * i + q] = zz[q];
+            z[PcgDir<V>::kZs * i + q] = zz[q];
+            p[4 * i + q] = PcgDir<V>::kFused ? V(0) : zz[q];
             bb += bv[q] * bv[q];
             rz += bv[q] * zz[q];
         }
+        if (PcgDir<V>::kZs == 4) z[4 * i + 3] = V(0);
         p[4 * i + 3] = V(0);
     }
     double tb, tr;
@@ -576,19 +586,45 @@ k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bv
         scal[kDone] = tb > 0.0 ? 0.0 : 1.0;
         scal[kIters] = 0.0;
         scal[kIt] = 0.0;
+        scal[kBe] = 0.0;   // a fused first SpMV forms p = z + 0 * p (p zero)
     }
 }
 
-// Ap = A p and p.Ap; one thread per block row, over the row's blocks in
-// column order, sums in TA.  The last block sets alpha = r.z / p.Ap (or the
-// breakdown flag).
+// In FP32 the search direction is kept as a pair of buffers [2][nvp][4]:
+// iteration it reads p_old = pair[it mod 2] and writes p_new = pair[(it + 1)
+// mod 2].  p_new = z + beta p_old is formed by the SpMV itself, for its own
+// row (stored) and for every neighbour it multiplies (recomputed from z and
+// p_old, bitwise the same value), so no separate direction pass is needed:
+// the extra neighbour reads hit L2 and cost less than a pass over p and z.
+// In FP64 the recomputation would load the FP64 pipe (the B300's is 1/64
+// of FP32), so there p is one buffer, updated by k_pcg_dir.
+template <class V>
+__device__ __forceinline__ void dir_row(const V* p_old, const V* z, int64_t j, V be, V& a, V& b, V& c) {
+    V p0, p1, p2;
+    load_p(p_old, j, p0, p1, p2);
+    if constexpr (PcgDir<V>::kFused) {
+        V z0, z1, z2;
+        load_p(z, j, z0, z1, z2);
+        a = fmaf(be, p0, z0); b = fmaf(be, p1, z1); c = fmaf(be, p2, z2);
+    } else {
+        a = p0; b = p1; c = p2;
+    }
+}
+
+// Ap = A p_new and p_new.Ap; one thread per block row, over the row's blocks
+// in column order, sums in TA.  The last block sets alpha = r.z / p.Ap (or
+// the breakdown flag).
 template <class TA, class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict__ goff,
-           const int32_t* __restrict__ sci, const TA* __restrict__ A, const V* __restrict__ p, V* __restrict__ Ap,
-           double* part, unsigned* counter, double* scal) {
+k_pcg_spmv(int64_t nv, int64_t nvp, const int32_t* __restrict__ rp, const int32_t* __restrict__ goff,
+           const int32_t* __restrict__ sci, const TA* __restrict__ A, V* __restrict__ ppair,
+           const V* __restrict__ z, V* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int it = (int)scal[kIt];
+    constexpr bool kFused = PcgDir<V>::kFused;
+    const V be = (V)scal[kBe];
+    const V* p_old = kFused ? ppair + 4 * nvp * (it & 1) : ppair;
+    V* p_new = ppair + 4 * nvp * ((it + 1) & 1);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     V pap = V(0);
     if (i < nv) {
@@ -597,14 +633,15 @@ k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict
         const int len = rp[i + 1] - rp[i];
         const int32_t* cj = sci + 32 * g0 + lane;
         TA a0 = TA(0), a1 = TA(0), a2 = TA(0);
-        // software pipeline: the column two blocks ahead, the block and p one
-        // block ahead are in flight while a block is multiplied
+        // software pipeline: the column two blocks ahead, the block and the
+        // neighbour's direction one block ahead are in flight while a block
+        // is multiplied
         TA bn[9];
         V qn0 = V(0), qn1 = V(0), qn2 = V(0);
         int64_t j2 = 0;
         if (len > 0) {
             load_blk(A, g0, lane, bn);
-            load_p(p, __ldg(cj), qn0, qn1, qn2);
+            dir_row(p_old, z, __ldg(cj), be, qn0, qn1, qn2);
         }
         if (len > 1) j2 = __ldg(cj + 32);
         for (int k = 0; k < len; ++k) {
@@ -614,7 +651,7 @@ k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict
             const TA p0 = (TA)qn0, p1 = (TA)qn1, p2 = (TA)qn2;
             if (k + 1 < len) {
                 load_blk(A, g0 + k + 1, lane, bn);
-                load_p(p, j2, qn0, qn1, qn2);
+                dir_row(p_old, z, j2, be, qn0, qn1, qn2);
                 if (k + 2 < len) j2 = __ldg(cj + 32 * (k + 2));
             }
             a0 += b[0] * p0 + b[1] * p1 + b[2] * p2;
@@ -626,7 +663,8 @@ k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict
         Ap[3 * i + 1] = y1;
         Ap[3 * i + 2] = y2;
         V q0, q1, q2;
-        load_p(p, i, q0, q1, q2);
+        dir_row(p_old, z, i, be, q0, q1, q2);
+        if constexpr (kFused) reinterpret_cast<float4*>(p_new)[i] = make_float4(q0, q1, q2, 0.f);
         pap = q0 * y0 + q1 * y1 + q2 * y2;
     }
     double t, unused;
@@ -641,16 +679,7 @@ k_pcg_spmv(int64_t nv, const int32_t* __restrict__ rp, const int32_t* __restrict
     }
 }
 
-// hi + lo += v (Knuth's two-sum; |lo| stays below half an ulp of hi)
-__device__ __forceinline__ void add_pair(float& hi, float& lo, float v) {
-    const float s = hi + v;
-    const float bv = s - hi;
-    const float e = (hi - (s - bv)) + (v - bv);
-    hi = s;
-    lo += e;
-}
-
-// rows handled by one thread of the update and direction kernels: four in
+// rows handled by one thread of the update kernel: four in
 // FP32, two in FP64, so that a thread's rows of every vector are whole
 // 16-byte vectors (the vectors are padded to a multiple of four rows)
 template <class V>
@@ -704,18 +733,29 @@ __device__ __forceinline__ void stv(V* dst, const V* src) {
     }
 }
 
-// x += al p, r -= al Ap, z = P^-1 r, then r.r (convergence) and r.z; the
-// last block sets beta = r.z_new / r.z and advances the iteration index.
+// hi + lo += v (Knuth's two-sum; |lo| stays below half an ulp of hi)
+__device__ __forceinline__ void add_pair(float& hi, float& lo, float v) {
+    const float s = hi + v;
+    const float bv = s - hi;
+    const float e = (hi - (s - bv)) + (v - bv);
+    hi = s;
+    lo += e;
+}
+
+// x += al p, r -= al Ap, z = P^-1 r (z: [nvp][4], the fourth entry zero),
+// then r.r (convergence) and r.z; the last block sets beta = r.z_new / r.z
+// and advances the iteration index.
 // PcgRows<V>::R rows per thread over the padded rows nvp; x is FP64 (rows
 // below nv) when V is FP64, else the float pair (xh, xl).
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
 k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __restrict__ x, V* __restrict__ xh,
-             V* __restrict__ xl, V* __restrict__ r, V* __restrict__ z, const V* __restrict__ p,
+             V* __restrict__ xl, V* __restrict__ r, V* __restrict__ z, const V* __restrict__ ppair,
              const V* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
     constexpr int R = PcgRows<V>::R;
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
     const int it = (int)scal[kIt];
+    const V* p = PcgDir<V>::kFused ? ppair + 4 * nvp * ((it + 1) & 1) : ppair;   // this iteration's direction
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i0 = R * t;
     const double al = scal[kAl];
@@ -745,16 +785,22 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
 #pragma unroll
         for (int e = 0; e < 3 * R; ++e) rv[e] -= alv * av[e];
         stv<V, 3 * R>(r + 3 * i0, rv);
-        V P[9 * R], zz[3 * R];
+        constexpr int ZS = PcgDir<V>::kZs;
+        V P[9 * R], zz[ZS * R];
         ldv<V, 9 * R>(Pinv + 9 * i0, P);
 #pragma unroll
-        for (int a = 0; a < R; ++a) mul33(P + 9 * a, rv[3 * a], rv[3 * a + 1], rv[3 * a + 2], zz + 3 * a);
-        stv<V, 3 * R>(z + 3 * i0, zz);
-#pragma unroll
-        for (int e = 0; e < 3 * R; ++e) {
-            rr += rv[e] * rv[e];
-            rz += rv[e] * zz[e];
+        for (int a = 0; a < R; ++a) {
+            mul33(P + 9 * a, rv[3 * a], rv[3 * a + 1], rv[3 * a + 2], zz + ZS * a);
+            if (ZS == 4) zz[ZS * a + ZS - 1] = V(0);
         }
+        stv<V, ZS * R>(z + ZS * i0, zz);
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                rr += rv[3 * a + q] * rv[3 * a + q];
+                rz += rv[3 * a + q] * zz[ZS * a + q];
+            }
     }
     double trr, trz;
     if (last_block_sums<2, V>(rr, rz, part, counter, &trr, &trz) && threadIdx.x == 0) {
@@ -771,23 +817,22 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
     }
 }
 
-// p = z + beta p, PcgRows<V>::R rows per thread over the padded rows
+// p = z + beta p (FP64 path; z [nvp][3], p [nvp][4]), two rows per thread
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
 k_pcg_dir(int64_t nvp, const V* __restrict__ z, V* __restrict__ p, const double* scal) {
-    constexpr int R = PcgRows<V>::R;
     if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
-    const int64_t i0 = R * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    const int64_t i0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (i0 >= nvp) return;
     const V be = (V)scal[kBe];
-    V zv[3 * R], pv[4 * R];
-    ldv<V, 3 * R>(z + 3 * i0, zv);
-    ldv_rw<V, 4 * R>(p + 4 * i0, pv);
+    V zv[6], pv[8];
+    ldv<V, 6>(z + 3 * i0, zv);
+    ldv_rw<V, 8>(p + 4 * i0, pv);
 #pragma unroll
-    for (int a = 0; a < R; ++a)
+    for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int q = 0; q < 3; ++q) pv[4 * a + q] = zv[3 * a + q] + be * pv[4 * a + q];
-    stv<V, 4 * R>(p + 4 * i0, pv);
+    stv<V, 8>(p + 4 * i0, pv);
 }
 
 // x = hi + lo in FP64 (mixed path, after the solve)
@@ -958,11 +1003,11 @@ static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* A
     const int64_t nvp = N.nvp;
     const unsigned g_multi = nblk(nvp / PcgRows<V>::R, kPcgThreads);
     for (int j = 0; j < count; ++j) {
-        k_pcg_spmv<TA, V><<<g_row, kPcgThreads, 0, s>>>(nv, N.rp.p, N.goff.p, N.sci.p, A, p, Ap, N.part.p,
-                                                        N.counters.p + 1, N.scal.p);
+        k_pcg_spmv<TA, V><<<g_row, kPcgThreads, 0, s>>>(nv, nvp, N.rp.p, N.goff.p, N.sci.p, A, p, z, Ap,
+                                                        N.part.p, N.counters.p + 1, N.scal.p);
         k_pcg_update<V><<<g_multi, kPcgThreads, 0, s>>>(nv, nvp, Pinv, xout, xh, xl, r, z, p, Ap, N.part.p,
                                                         N.counters.p + 2, N.scal.p);
-        k_pcg_dir<V><<<g_multi, kPcgThreads, 0, s>>>(nvp, z, p, N.scal.p);
+        if (!PcgDir<V>::kFused) k_pcg_dir<V><<<nblk(nvp / 2, kPcgThreads), kPcgThreads, 0, s>>>(nvp, z, p, N.scal.p);
     }
 }
 
@@ -1213,20 +1258,24 @@ cudaError_t newton_setup(Ctx& c) {
     N.nvp = nvp;
     if (f32) {
         GMCP_CUDA_TRY(N.A32.ensure(288 * (size_t)ngroups + 288));
-        for (DBuf<float>* b : {&N.r32, &N.z32, &N.Ap32, &N.xh32, &N.xl32}) {
+        for (DBuf<float>* b : {&N.r32, &N.Ap32, &N.xh32, &N.xl32}) {
             GMCP_CUDA_TRY(b->ensure(3 * (size_t)nvp));
             GMCP_CUDA_TRY(cudaMemsetAsync(b->p, 0, sizeof(float) * 3 * nvp, s));
         }
-        GMCP_CUDA_TRY(N.p32.ensure(4 * (size_t)nvp));
-        GMCP_CUDA_TRY(cudaMemsetAsync(N.p32.p, 0, sizeof(float) * 4 * nvp, s));
+        GMCP_CUDA_TRY(N.z32.ensure(4 * (size_t)nvp));
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.z32.p, 0, sizeof(float) * 4 * nvp, s));
+        GMCP_CUDA_TRY(N.p32.ensure(8 * (size_t)nvp));
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.p32.p, 0, sizeof(float) * 8 * nvp, s));
         GMCP_CUDA_TRY(N.Pinv32.ensure(9 * (size_t)nvp));
         GMCP_CUDA_TRY(cudaMemsetAsync(N.Pinv32.p, 0, sizeof(float) * 9 * nvp, s));
     } else {
         GMCP_CUDA_TRY(N.A64.ensure(288 * (size_t)ngroups + 288));
-        for (DBuf<double>* b : {&N.r, &N.z, &N.Ap}) {
+        for (DBuf<double>* b : {&N.r, &N.Ap}) {
             GMCP_CUDA_TRY(b->ensure(3 * (size_t)nvp));
             GMCP_CUDA_TRY(cudaMemsetAsync(b->p, 0, sizeof(double) * 3 * nvp, s));
         }
+        GMCP_CUDA_TRY(N.z.ensure(3 * (size_t)nvp));
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.z.p, 0, sizeof(double) * 3 * nvp, s));
         GMCP_CUDA_TRY(N.p.ensure(4 * (size_t)nvp));
         GMCP_CUDA_TRY(cudaMemsetAsync(N.p.p, 0, sizeof(double) * 4 * nvp, s));
         GMCP_CUDA_TRY(N.Pinv.ensure(9 * (size_t)nvp));
