@@ -430,8 +430,21 @@ enum : int {
     kDone = 7,       // converged
     kIters = 8,      // iterations taken (valid once kBreak or kDone is set)
     kThr = 9,        // rel_tol |b|
-    kIt = 10         // index of the current iteration (advanced by k_pcg_update)
+    kIt = 10,        // index of the current iteration (advanced by k_pcg_update)
+    kCtlI = 11,      // two int32: stop (break or done), iteration index
+    kCtlF = 12       // two float: alpha, beta (FP32 copies)
 };
+// The control words repeat the stop flags, the iteration index and alpha,
+// beta in int32 / FP32, so that the per-iteration kernels test and read them
+// without FP64 instructions (each costs a full warp issue on the B300's
+// narrow FP64 pipe).
+__device__ __forceinline__ int* pcg_ictl(double* scal) { return reinterpret_cast<int*>(scal + kCtlI); }
+__device__ __forceinline__ float* pcg_fctl(double* scal) { return reinterpret_cast<float*>(scal + kCtlF); }
+template <class V>
+__device__ __forceinline__ V pcg_scalar(double* scal, int k /* kAl or kBe */) {
+    if constexpr (sizeof(V) == 4) return pcg_fctl(scal)[k == kAl ? 0 : 1];
+    else return scal[k];
+}
 constexpr int kPcgThreads = 256;
 
 // whether the SpMV forms the search direction itself (FP32; see k_pcg_spmv)
@@ -587,6 +600,9 @@ k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bv
         scal[kIters] = 0.0;
         scal[kIt] = 0.0;
         scal[kBe] = 0.0;   // a fused first SpMV forms p = z + 0 * p (p zero)
+        pcg_ictl(scal)[0] = tb > 0.0 ? 0 : 1;
+        pcg_ictl(scal)[1] = 0;
+        pcg_fctl(scal)[1] = 0.f;
     }
 }
 
@@ -619,10 +635,10 @@ __global__ void __launch_bounds__(kPcgThreads)
 k_pcg_spmv(int64_t nv, int64_t nvp, const int32_t* __restrict__ rp, const int32_t* __restrict__ goff,
            const int32_t* __restrict__ sci, const TA* __restrict__ A, V* __restrict__ ppair,
            const V* __restrict__ z, V* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
-    if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
-    const int it = (int)scal[kIt];
+    if (pcg_ictl(scal)[0] != 0) return;
+    const int it = pcg_ictl(scal)[1];
     constexpr bool kFused = PcgDir<V>::kFused;
-    const V be = (V)scal[kBe];
+    const V be = pcg_scalar<V>(scal, kBe);
     const V* p_old = kFused ? ppair + 4 * nvp * (it & 1) : ppair;
     V* p_new = ppair + 4 * nvp * ((it + 1) & 1);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -672,25 +688,34 @@ k_pcg_spmv(int64_t nv, int64_t nvp, const int32_t* __restrict__ rp, const int32_
         scal[kPAp] = t;
         if (t > 0.0) {
             scal[kAl] = scal[kRz] / t;
+            pcg_fctl(scal)[0] = (float)scal[kAl];
         } else {
             scal[kBreak] = 1.0;
             scal[kIters] = (double)it;
+            pcg_ictl(scal)[0] = 1;
         }
     }
 }
 
-// rows handled by one thread of the update kernel: four in
-// FP32, two in FP64, so that a thread's rows of every vector are whole
-// 16-byte vectors (the vectors are padded to a multiple of four rows)
+// rows handled by one thread of the update kernel: two, so that a thread's
+// rows of every vector are whole 8-byte (FP32) or 16-byte (FP64) vectors
+// (the vectors are padded to a multiple of four rows)
 template <class V>
 struct PcgRows {
-    static constexpr int R = sizeof(V) == 4 ? 4 : 2;
+    static constexpr int R = 2;
 };
 
-// n consecutive values of V (n * sizeof(V) a multiple of 16, 16-byte aligned)
+// n consecutive values of V: 16-byte vectors when n * sizeof(V) is a
+// multiple of 16 (the address then 16-byte aligned), else 8-byte ones
 template <class V, int N>
 __device__ __forceinline__ void ldv(const V* __restrict__ src, V* dst) {
-    if constexpr (sizeof(V) == 4) {
+    if constexpr (sizeof(V) == 4 && (N * 4) % 16 != 0) {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) {
+            const float2 u = __ldg(reinterpret_cast<const float2*>(src) + c);
+            dst[2 * c] = u.x; dst[2 * c + 1] = u.y;
+        }
+    } else if constexpr (sizeof(V) == 4) {
 #pragma unroll
         for (int c = 0; c < N / 4; ++c) {
             const float4 u = __ldg(reinterpret_cast<const float4*>(src) + c);
@@ -706,7 +731,13 @@ __device__ __forceinline__ void ldv(const V* __restrict__ src, V* dst) {
 }
 template <class V, int N>
 __device__ __forceinline__ void ldv_rw(const V* src, V* dst) {   // for buffers the kernel also writes
-    if constexpr (sizeof(V) == 4) {
+    if constexpr (sizeof(V) == 4 && (N * 4) % 16 != 0) {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c) {
+            const float2 u = reinterpret_cast<const float2*>(src)[c];
+            dst[2 * c] = u.x; dst[2 * c + 1] = u.y;
+        }
+    } else if constexpr (sizeof(V) == 4) {
 #pragma unroll
         for (int c = 0; c < N / 4; ++c) {
             const float4 u = reinterpret_cast<const float4*>(src)[c];
@@ -722,7 +753,11 @@ __device__ __forceinline__ void ldv_rw(const V* src, V* dst) {   // for buffers 
 }
 template <class V, int N>
 __device__ __forceinline__ void stv(V* dst, const V* src) {
-    if constexpr (sizeof(V) == 4) {
+    if constexpr (sizeof(V) == 4 && (N * 4) % 16 != 0) {
+#pragma unroll
+        for (int c = 0; c < N / 2; ++c)
+            reinterpret_cast<float2*>(dst)[c] = make_float2(src[2 * c], src[2 * c + 1]);
+    } else if constexpr (sizeof(V) == 4) {
 #pragma unroll
         for (int c = 0; c < N / 4; ++c)
             reinterpret_cast<float4*>(dst)[c] = make_float4(src[4 * c], src[4 * c + 1], src[4 * c + 2], src[4 * c + 3]);
@@ -753,13 +788,12 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
              V* __restrict__ xl, V* __restrict__ r, V* __restrict__ z, const V* __restrict__ ppair,
              const V* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
     constexpr int R = PcgRows<V>::R;
-    if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
-    const int it = (int)scal[kIt];
+    if (pcg_ictl(scal)[0] != 0) return;
+    const int it = pcg_ictl(scal)[1];
     const V* p = PcgDir<V>::kFused ? ppair + 4 * nvp * ((it + 1) & 1) : ppair;   // this iteration's direction
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i0 = R * t;
-    const double al = scal[kAl];
-    const V alv = (V)al;
+    const V alv = pcg_scalar<V>(scal, kAl);
     V rr = V(0), rz = V(0);
     if (i0 < nvp) {
         V pv[4 * R], av[3 * R], rv[3 * R];
@@ -780,7 +814,7 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
 #pragma unroll
             for (int a = 0; a < R; ++a)
                 if (i0 + a < nv)
-                    for (int q = 0; q < 3; ++q) x[3 * (i0 + a) + q] += al * (double)pv[4 * a + q];
+                    for (int q = 0; q < 3; ++q) x[3 * (i0 + a) + q] += (double)alv * (double)pv[4 * a + q];
         }
 #pragma unroll
         for (int e = 0; e < 3 * R; ++e) rv[e] -= alv * av[e];
@@ -808,20 +842,24 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
         if (sqrt(trr) <= scal[kThr]) {
             scal[kDone] = 1.0;
             scal[kIters] = (double)(it + 1);
+            pcg_ictl(scal)[0] = 1;
         } else {
             scal[kBe] = trz / scal[kRz];
             scal[kRz] = trz;
+            pcg_fctl(scal)[1] = (float)scal[kBe];
         }
-        // every block read kIt and kAl before it arrived at the counter
+        // every block read the iteration index and alpha before it arrived
+        // at the counter
         scal[kIt] = (double)(it + 1);
+        pcg_ictl(scal)[1] = it + 1;
     }
 }
 
 // p = z + beta p (FP64 path; z [nvp][3], p [nvp][4]), two rows per thread
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_dir(int64_t nvp, const V* __restrict__ z, V* __restrict__ p, const double* scal) {
-    if (scal[kDone] != 0.0 || scal[kBreak] != 0.0) return;
+k_pcg_dir(int64_t nvp, const V* __restrict__ z, V* __restrict__ p, double* scal) {
+    if (pcg_ictl(scal)[0] != 0) return;
     const int64_t i0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (i0 >= nvp) return;
     const V be = (V)scal[kBe];
