@@ -213,8 +213,8 @@ struct NewtonState {
     DBuf<int32_t> bt_off, bt;            // block -> (t*16 + a*4 + b)
     DBuf<int32_t> cmap;                  // block -> contact block or -1
     DBuf<double> tE, tG, tE8;            // per-tet energy [nt], gradient [nt][12], energies [8][nt]
-    DBuf<double> tH64;                   // per-tet Hessian, 10 blocks [nt][90] (FP64 path)
-    DBuf<float> tH32;                    // the same in FP32 (mixed path)
+    DBuf<double> tH64;                   // per-tet Hessian, 10 blocks [nt][10][10] (FP64 path)
+    DBuf<float> tH32;                    // the same in FP32, [nt][10][12] (mixed path)
     DBuf<double> A64, Pinv;              // global matrix [ngroups][288] (FP64 path), P^-1 [nvp][9]
     DBuf<float> A32, p32, r32, z32, Ap32, Pinv32;   // FP32 matrix and PCG vectors (mixed path; z [nvp][4], p [2][nvp][4])
     DBuf<float> xh32, xl32;              // mixed-path PCG solution as a float pair hi + lo [3 nvp]

@@ -137,6 +137,30 @@ __device__ __forceinline__ void jacobi3(R* A, R* V) {
 // (m, n) is stored at kTetBlk[m] + n - m, row-major; (n, m) is its transpose
 __constant__ int kTetBlk[4] = {0, 4, 7, 9};
 
+// Each 3x3 block of the per-tet Hessian is stored with a stride of 48 bytes
+// (12 FP32 or, rounded up, 10 FP64 entries; the tail unused), so that the
+// assembly reads a block with 16-byte loads: [nt][10][kStride]
+template <class T>
+struct HBlk {
+    static constexpr int kStride = sizeof(T) == 4 ? 12 : 10;
+    static constexpr int kPerTet = 10 * kStride;
+};
+__device__ __forceinline__ void load_hblk(const float* H, float* h) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(H));
+    const float4 v = __ldg(reinterpret_cast<const float4*>(H) + 1);
+    h[0] = u.x; h[1] = u.y; h[2] = u.z; h[3] = u.w;
+    h[4] = v.x; h[5] = v.y; h[6] = v.z; h[7] = v.w;
+    h[8] = __ldg(H + 8);
+}
+__device__ __forceinline__ void load_hblk(const double* H, double* h) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const double2 u = __ldg(reinterpret_cast<const double2*>(H) + c);
+        h[2 * c] = u.x; h[2 * c + 1] = u.y;
+    }
+    h[8] = __ldg(H + 8);
+}
+
 // PSD-projected Neo-Hookean Hessian of one tet, written as its 10 distinct
 // 3x3 blocks in precision R.  dP/dF of an isotropic energy has a closed-form
 // eigensystem in the singular values of F = U diag(s) V^T (Smith, de Goes,
@@ -151,7 +175,7 @@ __constant__ int kTetBlk[4] = {0, 4, 7, 9};
 // block (m, n) = V_tet U M_mn U^T, M_mn = sum_k max(l_k, 0) (E_k d_m)(E_k d_n)^T.
 template <class R>
 __device__ void nh_hessian_blocks(const double* Fd, double lnJd, double mud, double lamd, const double* Dd,
-                                  double vold, R* out /* [90] */) {
+                                  double vold, R* out /* [10][HBlk<R>::kStride] */) {
     R F[9], D[12];
     for (int i = 0; i < 9; ++i) F[i] = (R)Fd[i];
     for (int i = 0; i < 12; ++i) D[i] = (R)Dd[i];
@@ -243,11 +267,11 @@ __device__ void nh_hessian_blocks(const double* Fd, double lnJd, double mud, dou
                 for (int s = 0; s < 3; ++s) T[3 * a + s] = U[3 * a] * M[s] + U[3 * a + 1] * M[3 + s] + U[3 * a + 2] * M[6 + s];
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b)
-                    out[9 * blk + 3 * a + b] = vol * (T[3 * a] * U[3 * b] + T[3 * a + 1] * U[3 * b + 1] + T[3 * a + 2] * U[3 * b + 2]);
+                    out[HBlk<R>::kStride * blk + 3 * a + b] = vol * (T[3 * a] * U[3 * b] + T[3 * a + 1] * U[3 * b + 1] + T[3 * a + 2] * U[3 * b + 2]);
         }
 }
 
-// energy, gradient [nt][12] and (WANT_HESS) PSD Hessian [nt][90] (10 blocks,
+// energy, gradient [nt][12] and (WANT_HESS) PSD Hessian [nt][10][stride] (10 blocks,
 // precision TH) per tet
 template <bool WANT_HESS, class TH>
 __global__ void __launch_bounds__(128)
@@ -265,7 +289,7 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
         tE[t] = INFINITY;
         for (int q = 0; q < 12; ++q) tG[12 * t + q] = 0.0;
         if (WANT_HESS)
-            for (int q = 0; q < 90; ++q) tH[90 * t + q] = TH(0);
+            for (int q = 0; q < HBlk<TH>::kPerTet; ++q) tH[HBlk<TH>::kPerTet * t + q] = TH(0);
         return;
     }
     tE[t] = psi;
@@ -286,7 +310,7 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
             for (int j = 0; j < 3; ++j) s += P[3 * i + j] * D[3 * m + j];
             tG[12 * t + 3 * m + i] = vol * s;
         }
-    if (WANT_HESS) nh_hessian_blocks<TH>(F, lnJ, E.mu, E.lam, D, vol, tH + 90 * t);
+    if (WANT_HESS) nh_hessian_blocks<TH>(F, lnJ, E.mu, E.lam, D, vol, tH + HBlk<TH>::kPerTet * t);
 }
 
 // elastic energies at x + alpha_j p for j < na (<= 8), layout [na][nt]
@@ -387,13 +411,15 @@ __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __re
         const int ent = bt_ent[e];
         const int64_t tt = ent >> 4;
         const int ma = (ent >> 2) & 3, nb = ent & 3;
+        constexpr int HS = HBlk<TH>::kStride;
+        TH h[9];
         if (ma <= nb) {
-            const TH* H = tH + 90 * tt + 9 * (kTetBlk[ma] + nb - ma);
-            for (int q = 0; q < 9; ++q) s[q] += (TA)H[q];
+            load_hblk(tH + HBlk<TH>::kPerTet * tt + HS * (kTetBlk[ma] + nb - ma), h);
+            for (int q = 0; q < 9; ++q) s[q] += (TA)h[q];
         } else {
-            const TH* H = tH + 90 * tt + 9 * (kTetBlk[nb] + ma - nb);
+            load_hblk(tH + HBlk<TH>::kPerTet * tt + HS * (kTetBlk[nb] + ma - nb), h);
             for (int p = 0; p < 3; ++p)
-                for (int q = 0; q < 3; ++q) s[3 * p + q] += (TA)H[3 * q + p];
+                for (int q = 0; q < 3; ++q) s[3 * p + q] += (TA)h[3 * q + p];
         }
     }
     const int cb = cmap[b];
@@ -1288,8 +1314,8 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.tE.ensure((size_t)nt + 1));
     GMCP_CUDA_TRY(N.tG.ensure(12 * (size_t)nt + 12));
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    if (f32) GMCP_CUDA_TRY(N.tH32.ensure(90 * (size_t)nt + 90));
-    else GMCP_CUDA_TRY(N.tH64.ensure(90 * (size_t)nt + 90));
+    if (f32) GMCP_CUDA_TRY(N.tH32.ensure(HBlk<float>::kPerTet * ((size_t)nt + 1)));
+    else GMCP_CUDA_TRY(N.tH64.ensure(HBlk<double>::kPerTet * ((size_t)nt + 1)));
     GMCP_CUDA_TRY(N.tE8.ensure(8 * (size_t)nt + 8));
     // PCG vectors: rows padded to a multiple of four, the padding zero
     const int64_t nvp = (nv + 3) / 4 * 4;
