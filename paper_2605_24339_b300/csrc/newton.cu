@@ -145,6 +145,15 @@ struct HBlk {
     static constexpr int kStride = sizeof(T) == 4 ? 12 : 10;
     static constexpr int kPerTet = 10 * kStride;
 };
+__device__ __forceinline__ void store_hblk(float* H, const float* h) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        reinterpret_cast<float4*>(H)[c] = make_float4(h[4 * c], h[4 * c + 1], h[4 * c + 2], h[4 * c + 3]);
+}
+__device__ __forceinline__ void store_hblk(double* H, const double* h) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) reinterpret_cast<double2*>(H)[c] = make_double2(h[2 * c], h[2 * c + 1]);
+}
 __device__ __forceinline__ void load_hblk(const float* H, float* h) {
     const float4 u = __ldg(reinterpret_cast<const float4*>(H));
     const float4 v = __ldg(reinterpret_cast<const float4*>(H) + 1);
@@ -265,9 +274,12 @@ __device__ void nh_hessian_blocks(const double* Fd, double lnJd, double mud, dou
             R T[9];   // U M
             for (int a = 0; a < 3; ++a)
                 for (int s = 0; s < 3; ++s) T[3 * a + s] = U[3 * a] * M[s] + U[3 * a + 1] * M[3 + s] + U[3 * a + 2] * M[6 + s];
+            R hb[HBlk<R>::kStride];
             for (int a = 0; a < 3; ++a)
                 for (int b = 0; b < 3; ++b)
-                    out[HBlk<R>::kStride * blk + 3 * a + b] = vol * (T[3 * a] * U[3 * b] + T[3 * a + 1] * U[3 * b + 1] + T[3 * a + 2] * U[3 * b + 2]);
+                    hb[3 * a + b] = vol * (T[3 * a] * U[3 * b] + T[3 * a + 1] * U[3 * b + 1] + T[3 * a + 2] * U[3 * b + 2]);
+            for (int q = 9; q < HBlk<R>::kStride; ++q) hb[q] = R(0);   // whole sectors are written
+            store_hblk(out + HBlk<R>::kStride * blk, hb);
         }
 }
 
