@@ -204,12 +204,15 @@ struct NewtonState {
     DBuf<uint8_t> dir;                   // [nv]
     DBuf<int32_t> vte_off, vte;          // vertex -> tet corner (t*4+a)
     DBuf<int32_t> rp, ci;                // block pattern (CSR)
-    int64_t nslice = 0, ngroups = 0;     // sliced-ELL storage of the matrix: 32 rows per slice
+    int64_t nslice = 0, ngroups = 0;     // sliced-ELL storage of the blocks (i, j >= i): 32 rows per slice
+    int64_t nlgroups = 0;                // groups of the lower lists (blocks j < i, read transposed)
     int64_t nvp = 0;                     // PCG vector rows: nv padded to a multiple of 4 (padding zero)
     DBuf<int32_t> goff;                  // [nslice + 1] first group (32 stored blocks) of each slice
     DBuf<int32_t> gslice;                // [ngroups] slice of each group
     DBuf<int32_t> sci;                   // [ngroups][32] column of each stored block, -1 for padding
-    DBuf<int32_t> diag;                  // [nv] index of block (v, v)
+    DBuf<int32_t> llen;                  // [nv] blocks j < i of each row
+    DBuf<int32_t> lgoff;                 // [nslice + 1] first lower group of each slice
+    DBuf<int32_t> lcol, lmir;            // [nlgroups + 1][32] column j, and group * 32 + lane of block (j, i)
     DBuf<int32_t> bt_off, bt;            // block -> (t*16 + a*4 + b)
     DBuf<int32_t> cmap;                  // block -> contact block or -1
     DBuf<double> tE, tG, tE8;            // per-tet energy [nt], gradient [nt][12], energies [8][nt]

@@ -388,12 +388,14 @@ __host__ __device__ __forceinline__ int64_t sell_idx(int64_t g, int lane, int q)
 
 // A = M + h^2 (sum_tets H + contact H) block by block in precision TA; a
 // block in a Dirichlet row or column is the identity on the diagonal and zero
-// elsewhere.  One thread per stored block, in storage order, so every store
-// is coalesced; padding blocks are zero.
+// elsewhere.  Only the blocks (i, j >= i) are stored (A is symmetric).  One
+// thread per stored block, in storage order, so every store is coalesced;
+// padding blocks are zero.
 template <class TH, class TC, class TA>
 __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __restrict__ goff,
                                 const int32_t* __restrict__ gslice, const int32_t* __restrict__ rp,
-                                const int32_t* __restrict__ bcol, const int32_t* __restrict__ bt_off,
+                                const int32_t* __restrict__ llen, const int32_t* __restrict__ bcol,
+                                const int32_t* __restrict__ bt_off,
                                 const int32_t* __restrict__ bt_ent, const TH* __restrict__ tH,
                                 const int32_t* __restrict__ cmap, const TC* __restrict__ cvals,
                                 const double* __restrict__ mass, const uint8_t* __restrict__ dir, double h2,
@@ -405,12 +407,13 @@ __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __re
     const int sl = gslice[g];
     const int k = (int)(g - goff[sl]);
     const int64_t i = 32 * (int64_t)sl + lane;
-    const int len = i < nv ? rp[i + 1] - rp[i] : 0;
+    const int ll = i < nv ? llen[i] : 0;
+    const int len = i < nv ? rp[i + 1] - rp[i] - ll : 0;
     if (k >= len) {
         for (int q = 0; q < 9; ++q) A[sell_idx<TA>(g, lane, q)] = TA(0);
         return;
     }
-    const int64_t b = rp[i] + k;
+    const int64_t b = rp[i] + ll + k;   // the k-th stored (j >= i) block of row i
     const int64_t j = bcol[b];
     if (dir[i] || dir[j]) {
         for (int q = 0; q < 9; ++q)
@@ -584,14 +587,15 @@ __device__ __forceinline__ void load_blk(const double* A, int64_t g, int lane, d
     b[8] = __ldg(A + sell_idx<double>(g, lane, 8));
 }
 
-// inverse of each diagonal block (inverted in FP64, stored as V)
+// inverse of each diagonal block (inverted in FP64, stored as V); the
+// diagonal is the first stored block of its row
 template <class TA, class V>
-__global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ diag_blk, const int32_t* __restrict__ rp,
-                           const int32_t* __restrict__ goff, const TA* __restrict__ A, V* __restrict__ Pinv) {
+__global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ goff, const TA* __restrict__ A,
+                           V* __restrict__ Pinv) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     double D[9], I[9];
-    const int64_t g = goff[v >> 5] + (diag_blk[v] - rp[v]);
+    const int64_t g = goff[v >> 5];
     for (int q = 0; q < 9; ++q) D[q] = (double)A[sell_idx<TA>(g, (int)(v & 31), q)];
     inv3(D, I);
     for (int q = 0; q < 9; ++q) Pinv[9 * v + q] = (V)I[q];
@@ -666,13 +670,16 @@ __device__ __forceinline__ void dir_row(const V* p_old, const V* z, int64_t j, V
 }
 
 // Ap = A p_new and p_new.Ap; one thread per block row, over the row's blocks
-// in column order, sums in TA.  The last block sets alpha = r.z / p.Ap (or
+// in column order (the transposed blocks j < i, then the stored ones), sums
+// in TA.  The last block sets alpha = r.z / p.Ap (or
 // the breakdown flag).
 template <class TA, class V>
 __global__ void __launch_bounds__(kPcgThreads)
 k_pcg_spmv(int64_t nv, int64_t nvp, const int32_t* __restrict__ rp, const int32_t* __restrict__ goff,
-           const int32_t* __restrict__ sci, const TA* __restrict__ A, V* __restrict__ ppair,
-           const V* __restrict__ z, V* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
+           const int32_t* __restrict__ sci, const int32_t* __restrict__ llen, const int32_t* __restrict__ lgoff,
+           const int32_t* __restrict__ lcol, const int32_t* __restrict__ lmir, const TA* __restrict__ A,
+           V* __restrict__ ppair, const V* __restrict__ z, V* __restrict__ Ap, double* part, unsigned* counter,
+           double* scal) {
     if (pcg_ictl(scal)[0] != 0) return;
     const int it = pcg_ictl(scal)[1];
     constexpr bool kFused = PcgDir<V>::kFused;
@@ -684,12 +691,45 @@ k_pcg_spmv(int64_t nv, int64_t nvp, const int32_t* __restrict__ rp, const int32_
     if (i < nv) {
         const int64_t g0 = goff[i >> 5];
         const int lane = (int)(i & 31);
-        const int len = rp[i + 1] - rp[i];
+        const int ll = llen[i];
+        const int len = rp[i + 1] - rp[i] - ll;
         const int32_t* cj = sci + 32 * g0 + lane;
         TA a0 = TA(0), a1 = TA(0), a2 = TA(0);
-        // software pipeline: the column two blocks ahead, the block and the
-        // neighbour's direction one block ahead are in flight while a block
-        // is multiplied
+        // the blocks j < i first (column order): transposes of block (j, i)
+        // in row j's storage, gathered (they were streamed by row j's slice
+        // and are read from L2); the same pipeline as below
+        if (ll > 0) {
+            const int64_t lg0 = lgoff[i >> 5];
+            const int32_t* lc = lcol + 32 * lg0 + lane;
+            const int32_t* lm = lmir + 32 * lg0 + lane;
+            TA bn[9];
+            V qn0, qn1, qn2;
+            int32_t m2 = 0;
+            int64_t j2 = 0;
+            {
+                const int32_t m = __ldg(lm);
+                load_blk(A, m >> 5, m & 31, bn);
+                dir_row(p_old, z, __ldg(lc), be, qn0, qn1, qn2);
+            }
+            if (ll > 1) { j2 = __ldg(lc + 32); m2 = __ldg(lm + 32); }
+            for (int k = 0; k < ll; ++k) {
+                TA b[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) b[q] = bn[q];
+                const TA p0 = (TA)qn0, p1 = (TA)qn1, p2 = (TA)qn2;
+                if (k + 1 < ll) {
+                    load_blk(A, m2 >> 5, m2 & 31, bn);
+                    dir_row(p_old, z, j2, be, qn0, qn1, qn2);
+                    if (k + 2 < ll) { j2 = __ldg(lc + 32 * (k + 2)); m2 = __ldg(lm + 32 * (k + 2)); }
+                }
+                a0 += b[0] * p0 + b[3] * p1 + b[6] * p2;
+                a1 += b[1] * p0 + b[4] * p1 + b[7] * p2;
+                a2 += b[2] * p0 + b[5] * p1 + b[8] * p2;
+            }
+        }
+        // the stored blocks j >= i: software pipeline, the column two blocks
+        // ahead, the block and the neighbour's direction one block ahead are
+        // in flight while a block is multiplied
         TA bn[9];
         V qn0 = V(0), qn1 = V(0), qn2 = V(0);
         int64_t j2 = 0;
@@ -1046,11 +1086,11 @@ cudaError_t assemble_bsr(Ctx& c) {
     if (g == 0) return cudaSuccess;
     if (c.P.precision == IPC_PREC_MIXED)
         k_assemble_sell<float, float, float><<<g, 256, 0, c.stream>>>(
-            c.nv, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH32.p, N.cmap.p,
+            c.nv, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.llen.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH32.p, N.cmap.p,
             c.cb_val32.p, N.mass.p, N.dir.p, h2, N.A32.p);
     else
         k_assemble_sell<double, double, double><<<g, 256, 0, c.stream>>>(
-            c.nv, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH64.p, N.cmap.p,
+            c.nv, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.llen.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH64.p, N.cmap.p,
             c.cb_val64.p, N.mass.p, N.dir.p, h2, N.A64.p);
     return cudaGetLastError();
 }
@@ -1079,8 +1119,9 @@ static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* A
     const int64_t nvp = N.nvp;
     const unsigned g_multi = nblk(nvp / PcgRows<V>::R, kPcgThreads);
     for (int j = 0; j < count; ++j) {
-        k_pcg_spmv<TA, V><<<g_row, kPcgThreads, 0, s>>>(nv, nvp, N.rp.p, N.goff.p, N.sci.p, A, p, z, Ap,
-                                                        N.part.p, N.counters.p + 1, N.scal.p);
+        k_pcg_spmv<TA, V><<<g_row, kPcgThreads, 0, s>>>(nv, nvp, N.rp.p, N.goff.p, N.sci.p, N.llen.p, N.lgoff.p,
+                                                        N.lcol.p, N.lmir.p, A, p, z, Ap, N.part.p,
+                                                        N.counters.p + 1, N.scal.p);
         k_pcg_update<V><<<g_multi, kPcgThreads, 0, s>>>(nv, nvp, Pinv, xout, xh, xl, r, z, p, Ap, N.part.p,
                                                         N.counters.p + 2, N.scal.p);
         if (!PcgDir<V>::kFused) k_pcg_dir<V><<<nblk(nvp / 2, kPcgThreads), kPcgThreads, 0, s>>>(nvp, z, p, N.scal.p);
@@ -1112,7 +1153,8 @@ static bool pcg_chunk_graph(Ctx& c, double* xout) {
                                         (uintptr_t)N.Pinv.p, (uintptr_t)N.Pinv32.p, (uintptr_t)N.part.p,
                                         (uintptr_t)N.scal.p, (uintptr_t)N.counters.p, (uintptr_t)c.pin,
                                         (uintptr_t)N.xh32.p, (uintptr_t)N.xl32.p, (uintptr_t)N.sci.p,
-                                        (uintptr_t)N.goff.p};
+                                        (uintptr_t)N.goff.p, (uintptr_t)N.llen.p, (uintptr_t)N.lgoff.p,
+                                        (uintptr_t)N.lcol.p, (uintptr_t)N.lmir.p};
     if (c.pcg_graph.exec && c.pcg_graph.key == key) return true;
     c.pcg_graph.reset();
     if (!c.cap_stream && cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1153,13 +1195,11 @@ cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int
     cudaStream_t s = c.stream;
     const unsigned gr = nblk(nv, kPcgThreads);
     if (c.P.precision == IPC_PREC_MIXED) {
-        k_diag_inv<float, float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.rp.p, N.goff.p, N.A32.p,
-                                                                N.Pinv32.p);
+        k_diag_inv<float, float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.goff.p, N.A32.p, N.Pinv32.p);
         k_pcg_init<float><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv32.p, b, xout, N.xh32.p, N.xl32.p, N.r32.p,
                                                      N.z32.p, N.p32.p, N.part.p, N.counters.p, N.scal.p, rel_tol);
     } else {
-        k_diag_inv<double, double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.diag.p, N.rp.p, N.goff.p, N.A64.p,
-                                                                  N.Pinv.p);
+        k_diag_inv<double, double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.goff.p, N.A64.p, N.Pinv.p);
         k_pcg_init<double><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, nullptr, nullptr, N.r.p, N.z.p,
                                                       N.p.p, N.part.p, N.counters.p, N.scal.p, rel_tol);
     }
@@ -1263,9 +1303,6 @@ cudaError_t newton_setup(Ctx& c) {
     }
     const int64_t nnzb = (int64_t)ci.size();
     N.nnzb = nnzb;
-    std::vector<int32_t> diag(nv);
-    for (int64_t i = 0; i < nv; ++i)
-        diag[i] = (int32_t)(std::lower_bound(ci.begin() + rp[i], ci.begin() + rp[i + 1], (int32_t)i) - ci.begin());
     // per-block tet contributions in increasing (tet, a, b)
     std::vector<int32_t> bt_off(nnzb + 1, 0), bt(16 * (size_t)nt);
     for (int64_t e = 0; e < 16 * nt; ++e) bt_off[tb[e] + 1]++;
@@ -1282,34 +1319,68 @@ cudaError_t newton_setup(Ctx& c) {
             cmap[pos] = k;
         }
 
-    // sliced-ELL layout: slice sl holds rows 32 sl .. 32 sl + 31 and as many
-    // groups of 32 blocks as its longest row; padding columns are -1
+    // Symmetric sliced-ELL storage.  Row i stores its blocks (i, j), j >= i
+    // (the diagonal first), in sliced ELL: slice sl holds rows 32 sl ..
+    // 32 sl + 31 and as many groups of 32 blocks as its longest stored row;
+    // padding columns are -1.  Its blocks j < i are the transposes of block
+    // (j, i), stored in row j: the lower lists give, per row and in column
+    // order, j and that block's position (group * 32 + lane).
     const int64_t nslice = (nv + 31) / 32;
-    std::vector<int32_t> goff(nslice + 1, 0);
+    std::vector<int32_t> llen(nv);
+    for (int64_t i = 0; i < nv; ++i)
+        llen[i] = (int32_t)(std::lower_bound(ci.begin() + rp[i], ci.begin() + rp[i + 1], (int32_t)i) -
+                            (ci.begin() + rp[i]));
+    std::vector<int32_t> goff(nslice + 1, 0), lgoff(nslice + 1, 0);
     for (int64_t sl = 0; sl < nslice; ++sl) {
-        int32_t w = 0;
-        for (int64_t i = 32 * sl; i < std::min<int64_t>(nv, 32 * sl + 32); ++i) w = std::max(w, rp[i + 1] - rp[i]);
-        if ((int64_t)goff[sl] + w >= ((int64_t)1 << 31) / 288) return cudaErrorInvalidValue;
+        int32_t w = 0, lw = 0;
+        for (int64_t i = 32 * sl; i < std::min<int64_t>(nv, 32 * sl + 32); ++i) {
+            w = std::max(w, rp[i + 1] - rp[i] - llen[i]);
+            lw = std::max(lw, llen[i]);
+        }
+        if ((int64_t)goff[sl] + w >= ((int64_t)1 << 31) / 288 || (int64_t)lgoff[sl] + lw >= ((int64_t)1 << 26))
+            return cudaErrorInvalidValue;
         goff[sl + 1] = goff[sl] + w;
+        lgoff[sl + 1] = lgoff[sl] + lw;
     }
-    const int64_t ngroups = goff[nslice];
+    const int64_t ngroups = goff[nslice], nlgroups = lgoff[nslice];
     std::vector<int32_t> gslice(ngroups), sci(32 * (size_t)ngroups, -1);
-    for (int64_t sl = 0; sl < nslice; ++sl)
+    std::vector<int32_t> lcol(32 * (size_t)nlgroups + 32, -1), lmir(32 * (size_t)nlgroups + 32, 0);
+    for (int64_t sl = 0; sl < nslice; ++sl) {
         for (int32_t g = goff[sl]; g < goff[sl + 1]; ++g) {
             gslice[g] = (int32_t)sl;
             const int k = g - goff[sl];
             for (int lane = 0; lane < 32; ++lane) {
                 const int64_t i = 32 * sl + lane;
-                if (i < nv && k < rp[i + 1] - rp[i]) sci[32 * (size_t)g + lane] = ci[rp[i] + k];
+                if (i < nv && k < rp[i + 1] - rp[i] - llen[i]) sci[32 * (size_t)g + lane] = ci[rp[i] + llen[i] + k];
             }
         }
+        for (int32_t g = lgoff[sl]; g < lgoff[sl + 1]; ++g) {
+            const int k = g - lgoff[sl];
+            for (int lane = 0; lane < 32; ++lane) {
+                const int64_t i = 32 * sl + lane;
+                if (i >= nv || k >= llen[i]) continue;
+                const int32_t j = ci[rp[i] + k];
+                const int64_t pos =
+                    std::lower_bound(ci.begin() + rp[j], ci.begin() + rp[j + 1], (int32_t)i) - ci.begin();
+                if (pos >= rp[j + 1] || ci[pos] != (int32_t)i) return cudaErrorInvalidValue;   // pattern not symmetric
+                const int64_t ku = pos - rp[j] - llen[j];
+                lcol[32 * (size_t)g + lane] = j;
+                lmir[32 * (size_t)g + lane] = (int32_t)((goff[j >> 5] + ku) * 32 + (j & 31));
+            }
+        }
+    }
     N.nslice = nslice;
     N.ngroups = ngroups;
+    N.nlgroups = nlgroups;
 
     const size_t n3 = 3 * (size_t)nv;
     GMCP_CUDA_TRY(N.goff.upload(goff.data(), goff.size(), s));
     GMCP_CUDA_TRY(N.gslice.upload(gslice.data(), gslice.size(), s));
     GMCP_CUDA_TRY(N.sci.upload(sci.data(), sci.size(), s));
+    GMCP_CUDA_TRY(N.llen.upload(llen.data(), llen.size(), s));
+    GMCP_CUDA_TRY(N.lgoff.upload(lgoff.data(), lgoff.size(), s));
+    GMCP_CUDA_TRY(N.lcol.upload(lcol.data(), lcol.size(), s));
+    GMCP_CUDA_TRY(N.lmir.upload(lmir.data(), lmir.size(), s));
     GMCP_CUDA_TRY(N.tets.upload(T, 4 * (size_t)nt, s));
     GMCP_CUDA_TRY(N.Dminv.upload(Dminv.data(), Dminv.size(), s));
     GMCP_CUDA_TRY(N.vol.upload(vol.data(), vol.size(), s));
@@ -1319,7 +1390,6 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.vte.upload(vte.data(), vte.size(), s));
     GMCP_CUDA_TRY(N.rp.upload(rp.data(), rp.size(), s));
     GMCP_CUDA_TRY(N.ci.upload(ci.data(), ci.size(), s));
-    GMCP_CUDA_TRY(N.diag.upload(diag.data(), diag.size(), s));
     GMCP_CUDA_TRY(N.bt_off.upload(bt_off.data(), bt_off.size(), s));
     GMCP_CUDA_TRY(N.bt.upload(bt.data(), bt.size(), s));
     GMCP_CUDA_TRY(N.cmap.upload(cmap.data(), cmap.size(), s));
