@@ -604,7 +604,7 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
     std::vector<int32_t> sedge, se_off, se_adj;
     tri_edges(sc->s_tris, ns, sedge, se_off, se_adj);
     c.nse = (int64_t)sedge.size() / 2;
-    std::vector<int32_t> sown_e(3 * ns, -1), sown_v(3 * ns, -1);
+    std::vector<int32_t> sown_e(3 * ns, -1), sown_v(3 * ns, -1), svert;   // svert: vertices of slave tris
     {
         std::vector<int> slot(ns, 0);
         for (int64_t e = 0; e < c.nse; ++e) {
@@ -619,7 +619,10 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
             }
         std::fill(slot.begin(), slot.end(), 0);
         for (int64_t v = 0; v < nv; ++v)
-            if (vowner[v] >= 0) sown_v[3 * vowner[v] + slot[vowner[v]]++] = (int32_t)v;
+            if (vowner[v] >= 0) {
+                sown_v[3 * vowner[v] + slot[vowner[v]]++] = (int32_t)v;
+                svert.push_back((int32_t)v);
+            }
     }
     // --- env of each tri
     std::vector<int32_t> s_env(ns), m_env(nmt);
@@ -750,6 +753,10 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
     CK(c.mtri_own_edge.upload(own_e.data(), own_e.size(), s));
     CK(c.mtri_own_vert.upload(own_v.data(), own_v.size(), s));
     CK(c.stri_own_vert.upload(sown_v.data(), sown_v.size(), s));
+    c.n_svert = (int64_t)svert.size();
+    CK(c.svert.upload(svert.data(), svert.size(), s));
+    CK(c.vbound_c.ensure(8 * (size_t)nv + 8));
+    CK(c.vbound_s.ensure(12 * (size_t)nv + 12));
     CK(c.stri_own_edge.upload(sown_e.data(), sown_e.size(), s));
     CK(c.sedge.upload(sedge.data(), sedge.size(), s));
     CK(c.stri_env.upload(s_env.data(), s_env.size(), s));

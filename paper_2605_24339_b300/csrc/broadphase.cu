@@ -379,9 +379,49 @@ struct QueryList {
     int32_t* work;     // work counter of the persistent query (reset before each launch)
 };
 
+// Per-vertex conservative FP32 bounds for the query filter, once per slave
+// vertex instead of once per triangle corner (a vertex is shared by about
+// six triangles).  Contact, [nv][8]: lo_f32 and hi_f32 of the position.
+// Swept, [nv][12]: the swept corner box (lo xyz, hi xyz) and the two
+// magnitude terms of each axis (position, displacement).  The filter combines
+// them in the same order as it would per corner, so its results are
+// unchanged.
+template <bool SWEPT>
+__global__ void k_vert_bounds(int64_t n, const int32_t* __restrict__ svert, const double* __restrict__ x,
+                              const double* __restrict__ dx, float* __restrict__ out) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t v = svert[k];
+    float pl[3], ph[3];
+    for (int c = 0; c < 3; ++c) {
+        const double p = x[3 * v + c];
+        pl[c] = lo_f32(p);
+        ph[c] = hi_f32(p);
+    }
+    if (!SWEPT) {
+        float4* o = reinterpret_cast<float4*>(out + 8 * v);
+        o[0] = make_float4(pl[0], pl[1], pl[2], 0.f);
+        o[1] = make_float4(ph[0], ph[1], ph[2], 0.f);
+        return;
+    }
+    float l[3], h[3], tx[3], td[3];
+    for (int c = 0; c < 3; ++c) {
+        const double d = dx[3 * v + c];
+        const float dl = lo_f32(d), dh = hi_f32(d);
+        tx[c] = fmaxf(fabsf(pl[c]), fabsf(ph[c]));
+        td[c] = fmaxf(fabsf(dl), fabsf(dh));
+        l[c] = fminf(pl[c], __fadd_rd(pl[c], dl));
+        h[c] = fmaxf(ph[c], __fadd_ru(ph[c], dh));
+    }
+    float4* o = reinterpret_cast<float4*>(out + 12 * v);
+    o[0] = make_float4(l[0], l[1], l[2], h[0]);
+    o[1] = make_float4(h[1], h[2], tx[0], tx[1]);
+    o[2] = make_float4(tx[2], td[0], td[1], td[2]);
+}
+
 template <bool SWEPT>
 __global__ void __launch_bounds__(256)
-k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double* __restrict__ dx,
+k_query_filter(SceneView S, Params P, const double* __restrict__ x, const float* __restrict__ vb_in,
                const int32_t* __restrict__ start, QueryList Q, int32_t* __restrict__ count) {
     // every lane runs to the warp-wide append at the end (lanes past the last
     // triangle work on triangle 0 and append nothing)
@@ -392,10 +432,15 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
     // The decision (does the grown box reach a non-empty cell?) and the
     // coarse box of the second phase are conservative FP32 bounds; no FP64
     // instruction runs here except the exact slave box of contact survivors.
-    double v[3][3], d[3][3];
+    // the corners' bounds from the per-vertex pass (k_vert_bounds)
+    constexpr int VS = SWEPT ? 12 : 8;
+    float r[3][VS];
     for (int a = 0; a < 3; ++a) {
-        load3(x, T[a], v[a]);
-        if (SWEPT) load3(dx, T[a], d[a]);
+        const float4* src = reinterpret_cast<const float4*>(vb_in + VS * (int64_t)T[a]);
+        for (int q = 0; q < VS / 4; ++q) {
+            const float4 u = __ldg(src + q);
+            r[a][4 * q] = u.x; r[a][4 * q + 1] = u.y; r[a][4 * q + 2] = u.z; r[a][4 * q + 3] = u.w;
+        }
     }
     const double grow = SWEPT ? S.margin : P.dhat + S.margin;
     const float grow_up = __double2float_ru(grow);
@@ -404,12 +449,14 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
     for (int c = 0; c < 3; ++c) {
         float lo_c = INFINITY, hi_c = -INFINITY, m_c = grow_up;
         for (int a = 0; a < 3; ++a) {
-            float pl = lo_f32(v[a][c]), ph = hi_f32(v[a][c]);
-            m_c += fmaxf(fabsf(pl), fabsf(ph));
+            float pl, ph;
             if (SWEPT) {
-                const float dl = lo_f32(d[a][c]), dh = hi_f32(d[a][c]);
-                m_c += fmaxf(fabsf(dl), fabsf(dh));
-                pl = fminf(pl, __fadd_rd(pl, dl)); ph = fmaxf(ph, __fadd_ru(ph, dh));
+                pl = r[a][c]; ph = r[a][3 + c];
+                m_c += r[a][6 + c];   // position term
+                m_c += r[a][9 + c];   // displacement term
+            } else {
+                pl = r[a][c]; ph = r[a][4 + c];
+                m_c += fmaxf(fabsf(pl), fabsf(ph));
             }
             vb[a][c] = pl; vb[a][3 + c] = ph;
             lo_c = fminf(lo_c, pl); hi_c = fmaxf(hi_c, ph);
@@ -441,6 +488,8 @@ k_query_filter(SceneView S, Params P, const double* __restrict__ x, const double
             for (int q = 0; q < 6; ++q) w[6 * a + q] = vb[a][q];
         if (!SWEPT) {
             // exact slave box for the edge and point tests
+            double v[3][3];
+            for (int a = 0; a < 3; ++a) load3(x, T[a], v[a]);
             double* b = Q.box + 6 * (int64_t)idx;
             for (int c = 0; c < 3; ++c) {
                 b[c] = kmin3(v[0][c], v[1][c], v[2][c]);
@@ -1160,8 +1209,11 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
     QueryList Q = query_list(c, false);
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 12, s));
     if (c.ns == 0) return cudaSuccess;
+    k_vert_bounds<false><<<(unsigned)((c.n_svert + 255) / 256), 256, 0, s>>>(c.n_svert, c.svert.p, x, nullptr,
+                                                                           c.vbound_c.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
     k_query_filter<false><<<(unsigned)((c.ns + 255) / 256), 256, 0, s>>>(
-        S, P, x, nullptr, c.cell_start.p, Q, c.cand_count.p);
+        S, P, x, c.vbound_c.p, c.cell_start.p, Q, c.cand_count.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.cap_coarse == 0) c.cap_coarse = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);
     const unsigned flat = (unsigned)(sm_count(c.device) * 8);
@@ -1204,8 +1256,11 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
     GMCP_CUDA_TRY(ensure_query_list(c, true));
     QueryList Q = query_list(c, true);
     GMCP_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(int32_t), c.stream));
+    k_vert_bounds<true><<<(unsigned)((c.n_svert + 255) / 256), 256, 0, c.stream>>>(c.n_svert, c.svert.p, x, dx,
+                                                                                 c.vbound_s.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
     k_query_filter<true><<<(unsigned)((c.ns + 255) / 256), 256, 0, c.stream>>>(
-        S, c.P, x, dx, c.cell_start.p, Q, nullptr);
+        S, c.P, x, c.vbound_s.p, c.cell_start.p, Q, nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.cap_ccd == 0) c.cap_ccd = (int32_t)std::min<int64_t>((1 << 16) + c.ns / 4, 1 << 30);
     if (c.cap_coarse_swept == 0) c.cap_coarse_swept = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);

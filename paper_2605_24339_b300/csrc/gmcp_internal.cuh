@@ -319,6 +319,10 @@ struct Ctx {
     DBuf<int2> coarse_pairs, coarse_swept;      // (query entry, master) pairs: contact, swept
     int32_t cap_ccd = 0, cap_coarse = 0, cap_coarse_swept = 0;
     QueryBufs qcontact, qswept;                 // filtered slave tris of the two queries
+    int64_t n_svert = 0;
+    DBuf<int32_t> svert;                        // [n_svert] vertices of slave tris (ascending)
+    DBuf<float> vbound_c;                       // [nv][8] per-vertex FP32 bounds for the contact query
+    DBuf<float> vbound_s;                       // [nv][12] per-vertex FP32 swept bounds for the swept query
     cudaStream_t ccd_stream = nullptr;          // the swept query's branch of a contact pass
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t aux_stream = nullptr;          // touched-output lists beside the sample evaluation
