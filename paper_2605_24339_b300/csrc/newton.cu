@@ -488,6 +488,15 @@ __device__ __forceinline__ V pcg_scalar(double* scal, int k /* kAl or kBe */) {
 }
 constexpr int kPcgThreads = 256;
 
+// Programmatic dependent launch: the PCG kernels are launched so that the
+// next one may start while the previous one drains (its last block forms
+// the iteration's scalars).  Each kernel waits for its predecessor's memory
+// before reading anything the predecessor writes, and lets its successor
+// launch as soon as it has passed that point.  Launched without the
+// attribute, both instructions are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // whether the SpMV forms the search direction itself (FP32; see k_pcg_spmv)
 template <class V>
 struct PcgDir {
@@ -680,6 +689,8 @@ k_pcg_spmv(int64_t nv, int64_t nvp, const int32_t* __restrict__ rp, const int32_
            const int32_t* __restrict__ lcol, const int32_t* __restrict__ lmir, const TA* __restrict__ A,
            V* __restrict__ ppair, const V* __restrict__ z, V* __restrict__ Ap, double* part, unsigned* counter,
            double* scal) {
+    pdl_wait();
+    pdl_trigger();
     if (pcg_ictl(scal)[0] != 0) return;
     const int it = pcg_ictl(scal)[1];
     constexpr bool kFused = PcgDir<V>::kFused;
@@ -866,6 +877,8 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
              V* __restrict__ xl, V* __restrict__ r, V* __restrict__ z, const V* __restrict__ ppair,
              const V* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
     constexpr int R = PcgRows<V>::R;
+    pdl_wait();
+    pdl_trigger();
     if (pcg_ictl(scal)[0] != 0) return;
     const int it = pcg_ictl(scal)[1];
     const V* p = PcgDir<V>::kFused ? ppair + 4 * nvp * ((it + 1) & 1) : ppair;   // this iteration's direction
@@ -937,6 +950,8 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
 k_pcg_dir(int64_t nvp, const V* __restrict__ z, V* __restrict__ p, double* scal) {
+    pdl_wait();
+    pdl_trigger();
     if (pcg_ictl(scal)[0] != 0) return;
     const int64_t i0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
     if (i0 >= nvp) return;
@@ -1109,6 +1124,22 @@ cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double*
 // iterations.  The host reads the flags once per 16 iterations; kernels
 // after the stop return at once.  Returns the iterations taken.
 // queue `count` PCG iterations (each kernel returns at once after a stop)
+// launch with programmatic stream serialisation (see pdl_wait)
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*k)(KArgs...), unsigned grid, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kPcgThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 template <class TA, class V>
 static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* Ap, double* xout, V* xh, V* xl,
                       int count) {
@@ -1119,12 +1150,14 @@ static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* A
     const int64_t nvp = N.nvp;
     const unsigned g_multi = nblk(nvp / PcgRows<V>::R, kPcgThreads);
     for (int j = 0; j < count; ++j) {
-        k_pcg_spmv<TA, V><<<g_row, kPcgThreads, 0, s>>>(nv, nvp, N.rp.p, N.goff.p, N.sci.p, N.llen.p, N.lgoff.p,
-                                                        N.lcol.p, N.lmir.p, A, p, z, Ap, N.part.p,
-                                                        N.counters.p + 1, N.scal.p);
-        k_pcg_update<V><<<g_multi, kPcgThreads, 0, s>>>(nv, nvp, Pinv, xout, xh, xl, r, z, p, Ap, N.part.p,
-                                                        N.counters.p + 2, N.scal.p);
-        if (!PcgDir<V>::kFused) k_pcg_dir<V><<<nblk(nvp / 2, kPcgThreads), kPcgThreads, 0, s>>>(nvp, z, p, N.scal.p);
+        launch_pdl(k_pcg_spmv<TA, V>, g_row, s, nv, nvp, (const int32_t*)N.rp.p, (const int32_t*)N.goff.p,
+                   (const int32_t*)N.sci.p, (const int32_t*)N.llen.p, (const int32_t*)N.lgoff.p,
+                   (const int32_t*)N.lcol.p, (const int32_t*)N.lmir.p, A, p, (const V*)z, Ap, N.part.p,
+                   N.counters.p + 1, N.scal.p);
+        launch_pdl(k_pcg_update<V>, g_multi, s, nv, nvp, Pinv, xout, xh, xl, r, z, (const V*)p, (const V*)Ap,
+                   N.part.p, N.counters.p + 2, N.scal.p);
+        if (!PcgDir<V>::kFused)
+            launch_pdl(k_pcg_dir<V>, nblk(nvp / 2, kPcgThreads), s, nvp, (const V*)z, p, N.scal.p);
     }
 }
 
