@@ -26,6 +26,8 @@
  *   Newton step ............. IPC problem statement, Sec. 2.1: minimise
  *                              inertia + elastic + contact over x with an
  *                              intersection-free line search
+ *   dual-mesh mapper ........ Sec. 3.2, Eqs. (bary_proj), (decomp), (gram),
+ *                              (bary_interp); nearest triangle by brute force
  *   warm-start MLP .......... not in the paper (a plain 4-layer perceptron)
  *
  * Parity pins live in tests/test_oracle_*.py.  Parts with no pin other than
@@ -1755,4 +1757,71 @@ ORC_API void orc_sim_pattern(const orc_sim* s, int32_t* rp, int32_t* ci) {
 }
 ORC_API int orc_pcg_solve(const orc_sim* s, const double* A, const double* b, double* x, double tol, int max_it) {
     return pcg(s, A, b, x, tol, max_it);
+}
+
+/* ------------------------------------------------------------------------
+ * Dual-mesh mapper, Sec. 3.2 (Eqs. bary_proj, decomp, gram, bary_interp).
+ *
+ * Precomputation: every visual vertex p is embedded on the simulation
+ * surface.  Its triangle is the nearest one (smallest point-triangle
+ * distance, orc_pt_dist2; on a tie the lowest index).  With e1 = v1 - v0,
+ * e2 = v2 - v0, n = e1 x e2 / |e1 x e2| and d = p - v0, the offset is
+ * delta = d . n (Eq. decomp), and (v, w) solve the 2x2 Gram system of
+ * Eq. (gram), written out by Cramer's rule; u = 1 - v - w.
+ * Per-frame update: p' = u v0' + v v1' + w v2' + delta n' (Eq. bary_interp),
+ * n' the unit normal of the deformed triangle.
+ * ------------------------------------------------------------------------ */
+ORC_API void orc_dual_map_coords(const double* p, const double* v0, const double* v1, const double* v2,
+                                 double* uvwd) {
+    double e1[3], e2[3], n[3], d[3];
+    sub3(v1, v0, e1);
+    sub3(v2, v0, e2);
+    cross3(e1, e2, n);
+    const double len = sqrt(dot3(n, n));
+    for (int c = 0; c < 3; ++c) n[c] = n[c] / len;
+    sub3(p, v0, d);
+    const double g11 = dot3(e1, e1), g12 = dot3(e1, e2), g22 = dot3(e2, e2);
+    const double r1 = dot3(d, e1), r2 = dot3(d, e2);
+    const double det = g11 * g22 - g12 * g12;
+    const double v = (r1 * g22 - g12 * r2) / det;
+    const double w = (g11 * r2 - g12 * r1) / det;
+    uvwd[0] = 1.0 - v - w;
+    uvwd[1] = v;
+    uvwd[2] = w;
+    uvwd[3] = dot3(d, n);
+}
+
+ORC_API void orc_dual_map_build(const double* V, const int32_t* T, int64_t nt, const double* P, int64_t np,
+                                int32_t* tri, double* uvwd, double* dist2) {
+    for (int64_t i = 0; i < np; ++i) {
+        const double* p = P + 3 * i;
+        double best = INFINITY;
+        int64_t bt = -1;
+        for (int64_t t = 0; t < nt; ++t) {
+            const int32_t* F = T + 3 * t;
+            const double d2 = orc_pt_dist2(p, V + 3 * F[0], V + 3 * F[1], V + 3 * F[2]);
+            if (d2 < best) { best = d2; bt = t; }
+        }
+        tri[i] = (int32_t)bt;
+        if (dist2) dist2[i] = best;
+        if (bt < 0) { uvwd[4 * i] = uvwd[4 * i + 1] = uvwd[4 * i + 2] = uvwd[4 * i + 3] = NAN; continue; }
+        const int32_t* F = T + 3 * bt;
+        orc_dual_map_coords(p, V + 3 * F[0], V + 3 * F[1], V + 3 * F[2], uvwd + 4 * i);
+    }
+}
+
+ORC_API void orc_dual_map_apply(const double* V, const int32_t* T, const int32_t* tri, const double* uvwd,
+                                int64_t np, double* out) {
+    for (int64_t i = 0; i < np; ++i) {
+        const int32_t* F = T + 3 * (int64_t)tri[i];
+        const double *v0 = V + 3 * F[0], *v1 = V + 3 * F[1], *v2 = V + 3 * F[2];
+        double e1[3], e2[3], n[3];
+        sub3(v1, v0, e1);
+        sub3(v2, v0, e2);
+        cross3(e1, e2, n);
+        const double len = sqrt(dot3(n, n));
+        const double* c4 = uvwd + 4 * i;
+        for (int c = 0; c < 3; ++c)
+            out[3 * i + c] = c4[0] * v0[c] + c4[1] * v1[c] + c4[2] * v2[c] + c4[3] * (n[c] / len);
+    }
 }

@@ -82,6 +82,9 @@ def _declare(L):
     L.orc_alpha_lin.restype = D; L.orc_alpha_lin.argtypes = [P, P, P, P, P]
     L.orc_pt_dist2.restype = D; L.orc_pt_dist2.argtypes = [P, P, P, P]
     L.orc_ee_dist2.restype = D; L.orc_ee_dist2.argtypes = [P, P, P, P]
+    L.orc_dual_map_coords.argtypes = [P, P, P, P, P]
+    L.orc_dual_map_build.argtypes = [P, P, C.c_int64, P, C.c_int64, P, P, P]
+    L.orc_dual_map_apply.argtypes = [P, P, P, P, C.c_int64, P]
     L.orc_surface_min_dist2.restype = D
     L.orc_surface_min_dist2.argtypes = [P, P, C.c_int64, P, P, C.c_int64]
     L.orc_accd.restype = D; L.orc_accd.argtypes = [I, P, P, D, D, I, C.POINTER(I)]
@@ -147,6 +150,41 @@ def surface_min_dist(xa, ta, xb, tb):
     d2 = lib().orc_surface_min_dist2(xa.ctypes.data, ta.ctypes.data, ta.shape[0],
                                      xb.ctypes.data, tb.ctypes.data, tb.shape[0])
     return float(np.sqrt(max(d2, 0.0)))
+
+
+def dual_map_coords(p, v0, v1, v2):
+    """(u, v, w, delta) of point p on triangle (v0, v1, v2): Sec. 3.2,
+    Eqs. (decomp), (gram)."""
+    a = [_f64(q) for q in (p, v0, v1, v2)]
+    out = np.zeros(4)
+    lib().orc_dual_map_coords(*[_p(q) for q in a], _p(out))
+    return out
+
+
+def dual_map_build(V, T, P):
+    """Dual-mesh mapper precomputation, Sec. 3.2 (Eq. bary_proj): for each
+    visual vertex the nearest simulation triangle (brute force, ties to the
+    lowest index), its (u, v, w, delta) and the squared distance."""
+    V, P = _f64(V).reshape(-1, 3), _f64(P).reshape(-1, 3)
+    T = np.ascontiguousarray(T, dtype=np.int32).reshape(-1, 3)
+    tri = np.zeros(P.shape[0], dtype=np.int32)
+    uvwd = np.zeros((P.shape[0], 4))
+    d2 = np.zeros(P.shape[0])
+    lib().orc_dual_map_build(V.ctypes.data, T.ctypes.data, T.shape[0], P.ctypes.data, P.shape[0],
+                             tri.ctypes.data, uvwd.ctypes.data, d2.ctypes.data)
+    return tri, uvwd, d2
+
+
+def dual_map_apply(V, T, tri, uvwd):
+    """Per-frame update, Sec. 3.2, Eq. (bary_interp)."""
+    V = _f64(V).reshape(-1, 3)
+    T = np.ascontiguousarray(T, dtype=np.int32).reshape(-1, 3)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    uvwd = _f64(uvwd).reshape(-1, 4)
+    out = np.zeros((tri.shape[0], 3))
+    lib().orc_dual_map_apply(V.ctypes.data, T.ctypes.data, tri.ctypes.data, uvwd.ctypes.data, tri.shape[0],
+                             out.ctypes.data)
+    return out
 
 
 def ee_dist2(a0, a1, b0, b1):
