@@ -382,6 +382,36 @@ ipc_status ipc_ws_get_params(ipc_ctx* ctx, float* params_host);
 ipc_status ipc_ws_predict(ipc_ctx* ctx, const double* x_dev, const double* v_dev, const double* xm_dev,
                           double* dx_dev);
 
+/* ------------------------------------------------------------------------
+ * Dual-mesh mapper (Sec. 3.2, Eqs. bary_proj, decomp, gram, bary_interp).
+ * Context-free: errors are reported through ipc_last_error(NULL).
+ * ------------------------------------------------------------------------ */
+
+/* Embed the visual vertices P_dev (device FP64 [np][3]) on the simulation
+ * surface (V_dev device FP64 [nv][3], triangles T_dev device int32 [nt][3]):
+ * for each vertex the nearest triangle (smallest point-triangle distance; on
+ * a tie the lowest index) into tri_dev (device int32 [np]), and into
+ * uvwd_dev (device FP64 [np][4], 16-byte aligned) the barycentric
+ * coordinates (u, v, w) of its projection onto that triangle's plane (the
+ * 2x2 Gram system of Eq. gram; they may be negative when the projection
+ * falls outside the triangle) and the signed offset delta = (p - v0) . n,
+ * n = (v1 - v0) x (v2 - v0) normalised.  dist2_dev (device FP64 [np], may be
+ * NULL) receives the squared distances.  Allocates and frees its scratch (a
+ * uniform grid of the triangles' boxes) and synchronises stream (a
+ * cudaStream_t).  IPC_ERR_ARG for NULL pointers, an empty mesh or a
+ * non-finite vertex. */
+ipc_status ipc_dual_map_build(const double* V_dev, int64_t nv, const int32_t* T_dev, int64_t nt,
+                              const double* P_dev, int64_t np, int32_t* tri_dev, double* uvwd_dev,
+                              double* dist2_dev, void* stream);
+
+/* Per-frame update, Eq. (bary_interp): out_dev[i] (device FP64 [np][3]) =
+ * u v0' + v v1' + w v2' + delta n' for the deformed simulation vertices
+ * V_dev (same vertex count and triangles T_dev [nt][3] as the build) and the
+ * triangles and coordinates of ipc_dual_map_build.  A triangle index
+ * outside [0, nt) gives NaN.  Queued on stream, no synchronisation. */
+ipc_status ipc_dual_map_apply(const double* V_dev, const int32_t* T_dev, int64_t nt, const int32_t* tri_dev,
+                              const double* uvwd_dev, int64_t np, double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -151,8 +151,44 @@ def lib():
     L.ipc_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
     L.ipc_newton_step.restype = C.c_int
     L.ipc_newton_step.argtypes = [P, P, P, P, P, C.POINTER(StepStats)]
+    L.ipc_dual_map_build.restype = C.c_int
+    L.ipc_dual_map_build.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, P, P, P, P]
+    L.ipc_dual_map_apply.restype = C.c_int
+    L.ipc_dual_map_apply.argtypes = [P, P, C.c_int64, P, P, C.c_int64, P, P]
     _lib = L
     return L
+
+
+def _dm_check(st):
+    if st != 0:
+        raise GmcpError(st, lib().ipc_last_error(None).decode())
+
+
+def dual_map_build(V, T, P, stream=0):
+    """ipc_dual_map_build on CUDA tensors: V float64 [nv, 3], T int32
+    [nt, 3] (simulation surface), P float64 [np, 3] (visual vertices).
+    Returns (tri int32 [np], uvwd float64 [np, 4], dist2 float64 [np])."""
+    import torch
+    V = V.contiguous(); T = T.contiguous(); P = P.contiguous()
+    n = P.shape[0]
+    tri = torch.empty(n, dtype=torch.int32, device=P.device)
+    uvwd = torch.empty((n, 4), dtype=torch.float64, device=P.device)
+    d2 = torch.empty(n, dtype=torch.float64, device=P.device)
+    _dm_check(lib().ipc_dual_map_build(_ptr(V), V.shape[0], _ptr(T), T.shape[0], _ptr(P), n, _ptr(tri),
+                                       _ptr(uvwd), _ptr(d2), C.c_void_p(stream)))
+    return tri, uvwd, d2
+
+
+def dual_map_apply(V, T, tri, uvwd, out=None, stream=0):
+    """ipc_dual_map_apply: the visual vertices for the deformed simulation
+    vertices V (float64 [nv, 3]); returns out (float64 [np, 3])."""
+    import torch
+    V = V.contiguous()
+    if out is None:
+        out = torch.empty((tri.shape[0], 3), dtype=torch.float64, device=V.device)
+    _dm_check(lib().ipc_dual_map_apply(_ptr(V), _ptr(T), T.shape[0], _ptr(tri), _ptr(uvwd), tri.shape[0],
+                                       _ptr(out), C.c_void_p(stream)))
+    return out
 
 
 def make_params(p: dict, precision="fp64", device=0, stream=0) -> Params:

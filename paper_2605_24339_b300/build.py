@@ -21,7 +21,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # clipping) are not weight-continuous and so must decide exactly as the
 # CPU oracle does on degenerate (coincident) meshes
 NO_FMA = {"broadphase.cu", "contact.cu"}
-SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu", "newton.cu", "warmstart.cu"]
+SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu", "newton.cu", "warmstart.cu", "dualmap.cu"]
 
 
 def nvcc() -> str:

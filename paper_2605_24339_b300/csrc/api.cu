@@ -1329,3 +1329,9 @@ ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const dou
 }
 
 }  // extern "C"
+
+namespace gmcp {
+// errors of the context-free entry points (the dual-mesh mapper), read by
+// ipc_last_error(NULL)
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace gmcp
