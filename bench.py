@@ -341,14 +341,14 @@ def dual_mesh_measurement(dev, n_points=2_000_000, reps=50):
     peaks, src = load_peaks()
     byts = n_points * (4 + 32 + 24) + V.nbytes + T.nbytes
     gbs = byts / (ms * 1e-3) / 1e9
-    fp64_ops = 33 * n_points
+    fp64_ops = 32 * n_points
     fp64_peak = 148 * 2 * 2032e6
     return {"workload": f"{n_points} visual points near the 131,072-triangle tactile surface of gel_on_terrain",
             "build_s": round(build_s, 3), "apply_ms": round(ms, 4),
             "points_per_s": n_points / (ms * 1e-3),
             "undeformed_max_err_m": err, "max_dist_m": float(np.sqrt(d2.max().item())),
             "roofline": {"hbm_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"], "hbm_frac": gbs / peaks["hbm_gbs"],
-                         "peak_source": src, "bytes_per_apply": byts, "fp64_ops_per_point": 33,
+                         "peak_source": src, "bytes_per_apply": byts, "fp64_ops_per_point": 32,
                          "fp64_frac": fp64_ops / (ms * 1e-3) / fp64_peak,
                          "fp64_peak_note": "148 SMs x 2 FP64 lanes/clock x 2032 MHz"},
             "l2": "flushed (256 MB write) between frames"}
@@ -674,13 +674,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-envs measurement")
     ap.add_argument("--no-dual-map", action="store_true", help="skip the dual-mesh mapper measurement")
+    ap.add_argument("--dual-points", type=int, default=2_000_000,
+                    help="--mode dualmap: visual points of the dual-mesh measurement")
     ap.add_argument("--no-newton", action="store_true",
                     help="skip the time-step measurement (newton_step key)")
     ap.add_argument("--batch-envs", type=int, default=512,
                     help="environments in the batched measurement")
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
-    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "dualmap"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
                          "training steps or time steps (command lines for profilers); batch: "
                          "the batched measurement alone, --steps timed passes")
@@ -693,6 +695,9 @@ def main():
         run_mlp(args)
     elif args.mode == "newton":
         run_newton(args)
+    elif args.mode == "dualmap":
+        import torch
+        print(json.dumps(dual_mesh_measurement("cuda", n_points=args.dual_points, reps=max(3, args.steps))))
     elif args.mode == "batch":
         print(json.dumps(batched_measurement(0, n_env=args.batch_envs,
                                              steps=args.steps)), flush=True)

@@ -259,14 +259,18 @@ __global__ void k_dm_apply(const double* __restrict__ V, const int32_t* __restri
         out[3 * i] = out[3 * i + 1] = out[3 * i + 2] = NAN;
         return;
     }
-    const double2 uv = __ldg(reinterpret_cast<const double2*>(uvwd) + 2 * i);
+    const double2 uv = __ldg(reinterpret_cast<const double2*>(uvwd) + 2 * i);   // (u, v); u is implied
     const double2 wd = __ldg(reinterpret_cast<const double2*>(uvwd) + 2 * i + 1);
     const D3 v0 = ld3(V, __ldg(T + 3 * t)), v1 = ld3(V, __ldg(T + 3 * t + 1)), v2 = ld3(V, __ldg(T + 3 * t + 2));
-    const D3 n = cross(sub(v1, v0), sub(v2, v0));
-    const double s = wd.y / sqrt(norm2(n));
-    out[3 * i] = uv.x * v0.x + uv.y * v1.x + wd.x * v2.x + s * n.x;
-    out[3 * i + 1] = uv.x * v0.y + uv.y * v1.y + wd.x * v2.y + s * n.y;
-    out[3 * i + 2] = uv.x * v0.z + uv.y * v1.z + wd.x * v2.z + s * n.z;
+    // the same point written as v0 + v e1 + w e2 + delta n (u = 1 - v - w),
+    // reusing the edges of the normal: fewer FP64 operations, the kernel's
+    // bound on this part
+    const D3 e1 = sub(v1, v0), e2 = sub(v2, v0);
+    const D3 n = cross(e1, e2);
+    const double s = wd.y * rsqrt(norm2(n));
+    out[3 * i] = v0.x + uv.y * e1.x + wd.x * e2.x + s * n.x;
+    out[3 * i + 1] = v0.y + uv.y * e1.y + wd.x * e2.y + s * n.y;
+    out[3 * i + 2] = v0.z + uv.y * e1.z + wd.x * e2.z + s * n.z;
 }
 
 ipc_status dm_fail(ipc_status st, const std::string& msg) {
