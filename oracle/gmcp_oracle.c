@@ -13,7 +13,9 @@
  *
  * What each part follows (paper: IsaacIPC / GMCP, arXiv 2605.24339):
  *   face samples ............ Sec. 4.1 "Face samples", Eq. (gap); fixed
- *                              slave-side centroid rule (reading R1)
+ *                              slave-side centroid rule (reading R1); the
+ *                              paper's clipped-polygon rule separately
+ *                              (orc_face_clip_samples, reading R18)
  *   edge samples ............ Sec. 4.1 "Edge samples", Eqs. (edge_pos, gap_edge)
  *   point samples ........... Sec. 4.1 "Point samples"
  *   barycentric projection .. Sec. 3.2, Eq. (gram)
@@ -1824,4 +1826,113 @@ ORC_API void orc_dual_map_apply(const double* V, const int32_t* T, const int32_t
         for (int c = 0; c < 3; ++c)
             out[3 * i + c] = c4[0] * v0[c] + c4[1] * v1[c] + c4[2] * v2[c] + c4[3] * (n[c] / len);
     }
+}
+
+/* ------------------------------------------------------------------------
+ * Paper-exact face samples, Sec. 4.1 "Face samples": both triangles are
+ * projected onto the tangent plane of the slave triangle T_s, the projected
+ * master triangle is clipped by T_s (Sutherland-Hodgman), the clipped polygon
+ * is fan-triangulated from its first vertex, and each sub-triangle gets the
+ * 3-point, degree-2 Gauss rule (interior points with barycentric coordinates
+ * (2/3, 1/6, 1/6) and permutations, weight one third of the area; reading
+ * R18).  Each sample is a point x_s on T_s (slave barycentrics beta^s); it
+ * is cast along the slave normal n_s onto the master plane, which gives the
+ * gap g (Eq. gap) and the master barycentrics beta^m (Eq. gram).
+ *
+ * Plane coordinates: origin x_s0, t1 = (x_s1 - x_s0)/|.|, t2 = n_s x t1,
+ * n_s = (x_s1 - x_s0) x (x_s2 - x_s0) normalised; T_s is counter-clockwise
+ * there.  Output per sample, 8 doubles: beta^s[3], beta^m[3], g, w.
+ * Returns the sample count (0 when the overlap has no area or the master
+ * plane is parallel to n_s), at most 12.
+ * ------------------------------------------------------------------------ */
+static double cross2(const double* a, const double* b, const double* p) {
+    return (b[0] - a[0]) * (p[1] - a[1]) - (b[1] - a[1]) * (p[0] - a[0]);
+}
+
+ORC_API int orc_face_clip_samples(const double* xs, const double* xm, double* out) {
+    const double *s0 = xs, *s1 = xs + 3, *s2 = xs + 6;
+    double e1[3], e2[3], n[3], t1[3], t2[3];
+    sub3(s1, s0, e1);
+    sub3(s2, s0, e2);
+    cross3(e1, e2, n);
+    const double nl = sqrt(dot3(n, n));
+    for (int c = 0; c < 3; ++c) n[c] = n[c] / nl;
+    const double l1 = sqrt(dot3(e1, e1));
+    for (int c = 0; c < 3; ++c) t1[c] = e1[c] / l1;
+    cross3(n, t1, t2);
+    /* slave triangle and projected master triangle in plane coordinates */
+    double A[3][2], P[3][2];
+    for (int k = 0; k < 3; ++k) {
+        double d[3];
+        sub3(xs + 3 * k, s0, d);
+        A[k][0] = dot3(d, t1); A[k][1] = dot3(d, t2);
+        sub3(xm + 3 * k, s0, d);
+        P[k][0] = dot3(d, t1); P[k][1] = dot3(d, t2);
+    }
+    /* Sutherland-Hodgman: keep the part on the left of each directed edge */
+    double poly[12][2], tmp[12][2];
+    int m = 3;
+    for (int k = 0; k < 3; ++k) { poly[k][0] = P[k][0]; poly[k][1] = P[k][1]; }
+    for (int e = 0; e < 3 && m > 0; ++e) {
+        const double* a = A[e];
+        const double* b = A[(e + 1) % 3];
+        int mo = 0;
+        for (int k = 0; k < m; ++k) {
+            const double* p = poly[(k + m - 1) % m];
+            const double* q = poly[k];
+            const double sp = cross2(a, b, p), sq = cross2(a, b, q);
+            if (sq >= 0.0) {
+                if (sp < 0.0) {
+                    const double t = sp / (sp - sq);
+                    tmp[mo][0] = p[0] + t * (q[0] - p[0]); tmp[mo][1] = p[1] + t * (q[1] - p[1]); ++mo;
+                }
+                tmp[mo][0] = q[0]; tmp[mo][1] = q[1]; ++mo;
+            } else if (sp >= 0.0) {
+                const double t = sp / (sp - sq);
+                tmp[mo][0] = p[0] + t * (q[0] - p[0]); tmp[mo][1] = p[1] + t * (q[1] - p[1]); ++mo;
+            }
+        }
+        m = mo;
+        for (int k = 0; k < m; ++k) { poly[k][0] = tmp[k][0]; poly[k][1] = tmp[k][1]; }
+    }
+    if (m < 3) return 0;
+    /* master plane */
+    double f1[3], f2[3], N[3];
+    sub3(xm + 3, xm, f1);
+    sub3(xm + 6, xm, f2);
+    cross3(f1, f2, N);
+    const double den = dot3(N, n);
+    if (den == 0.0) return 0;
+    /* slave barycentrics of a plane point: 2x2 solve in the plane */
+    const double a11 = A[1][0] - A[0][0], a12 = A[2][0] - A[0][0];
+    const double a21 = A[1][1] - A[0][1], a22 = A[2][1] - A[0][1];
+    const double det = a11 * a22 - a12 * a21;
+    static const double G[3][3] = {{2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0},
+                                   {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0},
+                                   {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}};
+    int ns = 0;
+    for (int k = 1; k + 1 < m; ++k) {
+        const double *q0 = poly[0], *q1 = poly[k], *q2 = poly[k + 1];
+        const double area = 0.5 * fabs((q1[0] - q0[0]) * (q2[1] - q0[1]) - (q1[1] - q0[1]) * (q2[0] - q0[0]));
+        if (!(area > 0.0)) continue;
+        for (int gp = 0; gp < 3; ++gp) {
+            const double u = G[gp][0] * q0[0] + G[gp][1] * q1[0] + G[gp][2] * q2[0];
+            const double v = G[gp][0] * q0[1] + G[gp][1] * q1[1] + G[gp][2] * q2[1];
+            const double ru = u - A[0][0], rv = v - A[0][1];
+            const double b1 = (a22 * ru - a12 * rv) / det;
+            const double b2 = (a11 * rv - a21 * ru) / det;
+            double* o = out + 8 * ns;
+            o[0] = 1.0 - b1 - b2; o[1] = b1; o[2] = b2;
+            double x[3], d[3], hit[3];
+            for (int c = 0; c < 3; ++c) x[c] = o[0] * s0[c] + o[1] * s1[c] + o[2] * s2[c];
+            sub3(xm, x, d);
+            const double g = dot3(N, d) / den;
+            for (int c = 0; c < 3; ++c) hit[c] = x[c] + g * n[c];
+            bary_gram(hit, xm, xm + 3, xm + 6, o + 3);
+            o[6] = g;
+            o[7] = area / 3.0;
+            ++ns;
+        }
+    }
+    return ns;
 }

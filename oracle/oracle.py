@@ -82,6 +82,7 @@ def _declare(L):
     L.orc_alpha_lin.restype = D; L.orc_alpha_lin.argtypes = [P, P, P, P, P]
     L.orc_pt_dist2.restype = D; L.orc_pt_dist2.argtypes = [P, P, P, P]
     L.orc_ee_dist2.restype = D; L.orc_ee_dist2.argtypes = [P, P, P, P]
+    L.orc_face_clip_samples.restype = I; L.orc_face_clip_samples.argtypes = [P, P, P]
     L.orc_dual_map_coords.argtypes = [P, P, P, P, P]
     L.orc_dual_map_build.argtypes = [P, P, C.c_int64, P, C.c_int64, P, P, P]
     L.orc_dual_map_apply.argtypes = [P, P, P, P, C.c_int64, P]
@@ -150,6 +151,17 @@ def surface_min_dist(xa, ta, xb, tb):
     d2 = lib().orc_surface_min_dist2(xa.ctypes.data, ta.ctypes.data, ta.shape[0],
                                      xb.ctypes.data, tb.ctypes.data, tb.shape[0])
     return float(np.sqrt(max(d2, 0.0)))
+
+
+def face_clip_samples(xs, xm):
+    """Paper-exact face samples of slave triangle xs [3,3] against master
+    triangle xm [3,3] (Sec. 4.1: projection, Sutherland-Hodgman clip, fan,
+    3-point Gauss per sub-triangle).  Returns [n, 8]: beta_s[3], beta_m[3],
+    g, w."""
+    xs, xm = _f64(xs).reshape(9), _f64(xm).reshape(9)
+    out = np.zeros((12, 8))
+    n = lib().orc_face_clip_samples(_p(xs), _p(xm), _p(out))
+    return out[:n].copy()
 
 
 def dual_map_coords(p, v0, v1, v2):
