@@ -412,6 +412,28 @@ ipc_status ipc_dual_map_build(const double* V_dev, int64_t nv, const int32_t* T_
 ipc_status ipc_dual_map_apply(const double* V_dev, const int32_t* T_dev, int64_t nt, const int32_t* tri_dev,
                               const double* uvwd_dev, int64_t np, double* out_dev, void* stream);
 
+/* Paper-exact face samples (Sec. 4.1 "Face samples"), for a list of pairs
+ * pairs_dev (device int32 [n][2]: slave triangle, master triangle) of the
+ * slave mesh (xs_dev FP64 [nvs][3], ts_dev int32 [nts][3]) and the master
+ * mesh (xm_dev FP64 [nvm][3], tm_dev int32 [ntm][3]), all device memory.
+ * Both triangles are projected onto the slave triangle's tangent plane, the
+ * projected master triangle is clipped by the slave triangle
+ * (Sutherland-Hodgman), the polygon is fan-triangulated from its first
+ * vertex and each sub-triangle gets the 3-point degree-2 Gauss rule (points
+ * (2/3, 1/6, 1/6) and permutations, weight area/3).  Each sample is cast
+ * along the slave normal n_s = (xs1 - xs0) x (xs2 - xs0) normalised onto the
+ * master plane.  samples_dev (device FP64 [n][12][8]) receives per sample
+ * beta^s[3], beta^m[3], the gap g and the weight w; count_dev (device int32
+ * [n]) the number of samples (0 to 12; 0 when the overlap has no area or
+ * the master plane contains n_s).  The contact pass does not use it (it keeps
+ * the fixed slave-side rule).  Context-free (errors through
+ * ipc_last_error(NULL)); synchronises stream.  IPC_ERR_ARG for an index out
+ * of range. */
+ipc_status ipc_face_clip_samples(const double* xs_dev, int64_t nvs, const int32_t* ts_dev, int64_t nts,
+                                 const double* xm_dev, int64_t nvm, const int32_t* tm_dev, int64_t ntm,
+                                 const int32_t* pairs_dev, int64_t n, double* samples_dev, int32_t* count_dev,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

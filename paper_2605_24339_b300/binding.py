@@ -153,6 +153,9 @@ def lib():
     L.ipc_newton_step.argtypes = [P, P, P, P, P, C.POINTER(StepStats)]
     L.ipc_dual_map_build.restype = C.c_int
     L.ipc_dual_map_build.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, P, P, P, P]
+    L.ipc_face_clip_samples.restype = C.c_int
+    L.ipc_face_clip_samples.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, P, C.c_int64, P, C.c_int64,
+                                        P, P, P]
     L.ipc_dual_map_apply.restype = C.c_int
     L.ipc_dual_map_apply.argtypes = [P, P, C.c_int64, P, P, C.c_int64, P, P]
     _lib = L
@@ -177,6 +180,20 @@ def dual_map_build(V, T, P, stream=0):
     _dm_check(lib().ipc_dual_map_build(_ptr(V), V.shape[0], _ptr(T), T.shape[0], _ptr(P), n, _ptr(tri),
                                        _ptr(uvwd), _ptr(d2), C.c_void_p(stream)))
     return tri, uvwd, d2
+
+
+def face_clip_samples(xs, ts, xm, tm, pairs, stream=0):
+    """ipc_face_clip_samples on CUDA tensors; returns (samples float64
+    [n, 12, 8], count int32 [n])."""
+    import torch
+    xs, ts, xm, tm, pairs = (a.contiguous() for a in (xs, ts, xm, tm, pairs))
+    n = pairs.shape[0]
+    smp = torch.zeros((n, 12, 8), dtype=torch.float64, device=xs.device)
+    cnt = torch.zeros(n, dtype=torch.int32, device=xs.device)
+    _dm_check(lib().ipc_face_clip_samples(_ptr(xs), xs.shape[0], _ptr(ts), ts.shape[0], _ptr(xm), xm.shape[0],
+                                          _ptr(tm), tm.shape[0], _ptr(pairs), n, _ptr(smp), _ptr(cnt),
+                                          C.c_void_p(stream)))
+    return smp, cnt
 
 
 def dual_map_apply(V, T, tri, uvwd, out=None, stream=0):

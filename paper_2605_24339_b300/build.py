@@ -20,8 +20,9 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # geometry whose membership tests (point inside a slave triangle, edge
 # clipping) are not weight-continuous and so must decide exactly as the
 # CPU oracle does on degenerate (coincident) meshes
-NO_FMA = {"broadphase.cu", "contact.cu"}
-SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu", "newton.cu", "warmstart.cu", "dualmap.cu"]
+NO_FMA = {"broadphase.cu", "contact.cu", "faceclip.cu"}
+SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu", "newton.cu", "warmstart.cu", "dualmap.cu",
+           "faceclip.cu"]
 
 
 def nvcc() -> str:
