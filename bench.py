@@ -285,9 +285,42 @@ def run_ours(args):
         line["warm_start"] = warm_start_measurement(dev)
     if not args.no_dual_map:
         line["dual_mesh"] = dual_mesh_measurement(dev)
+        line["face_clip"] = face_clip_measurement(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(steps=2)
     print(json.dumps(line), flush=True)
+
+
+def face_clip_measurement(dev, n_pairs=2_000_000, reps=20):
+    """Paper-exact face samples (Sec. 4.1, ipc_face_clip_samples) on
+    n_pairs seeded (slave, master) triangle pairs of unit size: slaves near
+    z = 0, masters 0.05-0.3 above with random tilt and offset (about half of
+    the pairs overlap in projection).  Throughput of the sampler in pairs/s
+    and samples/s (CUDA events, L2 flushed between launches)."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    rng = np.random.default_rng(12)
+    xs = np.c_[rng.uniform(0, 1, (3 * n_pairs, 2)), rng.uniform(-0.05, 0.05, 3 * n_pairs)]
+    xm = np.c_[rng.uniform(0, 1, (3 * n_pairs, 2)), rng.uniform(0.05, 0.3, 3 * n_pairs)]
+    T = np.arange(3 * n_pairs, dtype=np.int32).reshape(n_pairs, 3)
+    pairs = np.c_[np.arange(n_pairs), np.arange(n_pairs)].astype(np.int32)
+    a = [torch.as_tensor(v, device=dev) for v in (xs, T, xm, T, pairs)]
+    smp, cnt = binding.face_clip_samples(*a)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    times = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        smp, cnt = binding.face_clip_samples(*a)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    s = statistics.median(times)
+    n_samples = int(cnt.sum().item())
+    return {"workload": f"{n_pairs} seeded unit-size triangle pairs (slave near z = 0, tilted masters above)",
+            "ms_per_call": round(s * 1e3, 3), "pairs_per_s": n_pairs / s, "samples_per_call": n_samples,
+            "samples_per_s": n_samples / s, "overlapping_pairs": int((cnt > 0).sum().item()),
+            "note": "wall time of the synchronising call (allocation of its 4-byte flag included)"}
 
 
 def dual_mesh_measurement(dev, n_points=2_000_000, reps=50):
@@ -682,7 +715,7 @@ def main():
                     help="environments in the batched measurement")
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
-    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "dualmap"],
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "dualmap", "faceclip"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
                          "training steps or time steps (command lines for profilers); batch: "
                          "the batched measurement alone, --steps timed passes")
@@ -698,6 +731,9 @@ def main():
     elif args.mode == "dualmap":
         import torch
         print(json.dumps(dual_mesh_measurement("cuda", n_points=args.dual_points, reps=max(3, args.steps))))
+    elif args.mode == "faceclip":
+        import torch
+        print(json.dumps(face_clip_measurement("cuda", reps=max(3, args.steps))))
     elif args.mode == "batch":
         print(json.dumps(batched_measurement(0, n_env=args.batch_envs,
                                              steps=args.steps)), flush=True)
