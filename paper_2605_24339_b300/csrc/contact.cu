@@ -303,6 +303,7 @@ __global__ void k_pass_begin(int32_t* misc, int hess) {
     (void)p;
     misc[kSlotVCount] = 0;
     misc[kSlotItemList] = 0;
+    misc[kSlotItemList2] = 0;
     if (hess) {
         const int32_t h = ++misc[kSlotHPass];
         misc[kSlotBCount + (h & 1)] = 0;
@@ -794,7 +795,8 @@ template <int NK, class T>
 __global__ void __launch_bounds__(256)
 k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
             const double* __restrict__ frame, const int32_t* __restrict__ items, ItemBufs B,
-            int32_t* __restrict__ list, int32_t* __restrict__ n_list, long long* counters) {
+            int32_t* __restrict__ list, int32_t* __restrict__ n_list, int32_t* __restrict__ n_list2,
+            long long* counters) {
     const int64_t n = *B.n;
     if (n > B.cap) return;
     const bool pre = P.precision == IPC_PREC_MIXED;
@@ -803,13 +805,14 @@ k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, con
     // whole warps iterate together (the list append is per warp)
     for (int64_t sb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); sb < n; sb += stride) {
         const int64_t s = sb + (threadIdx.x & 31);
-        bool keep = false;
+        bool keep = false, face = false;
         if (s < n) {
             const int i = B.owner[s];
             const int q = (int)(s - items[2 * i]);
             const TriData D = load_tri(S, C, x, nullptr, frame, i);
             const ItemRef R = item_ref<NK>(D, q);
             keep = true;
+            face = R.kind == 0;
             if (R.kind == 0) {
                 ++cnt_eval;
                 if (pre) {
@@ -830,8 +833,11 @@ k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, con
                 item_store<T>(B, s, 0.0, INFINITY, T(0), T(0), z);
             }
         }
-        const int at = warp_reserve_c(keep, n_list);
-        if (keep) list[at] = (int32_t)s;
+        // face survivors from the front of the list, edge and point survivors
+        // from the back, so that the FP64 phase runs warps of one kind
+        const int at_f = warp_reserve_c(keep && face, n_list);
+        const int at_o = warp_reserve_c(keep && !face, n_list2);
+        if (keep) list[face ? (int64_t)at_f : B.cap - 1 - at_o] = (int32_t)s;
     }
     if (counters) {
         for (int o = 16; o > 0; o >>= 1) cnt_eval += shfl_x(cnt_eval, o);
@@ -846,13 +852,14 @@ __global__ void __launch_bounds__(64, 6)
 k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
         const double* __restrict__ dx, const double* __restrict__ dxm, const double* __restrict__ frame,
         const int32_t* __restrict__ items, ItemBufs B, const int32_t* __restrict__ list,
-        const int32_t* __restrict__ n_list, long long* counters) {
+        const int32_t* __restrict__ n_list, const int32_t* __restrict__ n_list2, long long* counters) {
     if ((int64_t)*B.n > B.cap) return;
-    const int n = *n_list;
+    const int nf = *n_list;
+    const int n = nf + *n_list2;
     const bool want_dg = dx != nullptr;
     long long cnt_f = 0, cnt_e = 0, cnt_p = 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
-        const int64_t s = list[c];
+        const int64_t s = c < nf ? list[c] : list[B.cap - 1 - (c - nf)];
         const int i = B.owner[s];
         const int q = (int)(s - items[2 * i]);
         const TriData D = load_tri(S, C, x, dx, frame, i);
@@ -1085,15 +1092,16 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
     GMCP_CUDA_TRY(cudaGetLastError());
     int32_t* n_list = c.misc_i32.p + kSlotItemList;
+    int32_t* n_list2 = c.misc_i32.p + kSlotItemList2;
     k_items_pre<NK, T><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, c.tri_frame.p,
-                                                       c.tri_items.p, B, c.item_list.p, n_list, counters);
+                                                       c.tri_items.p, B, c.item_list.p, n_list, n_list2, counters);
     GMCP_CUDA_TRY(cudaGetLastError());
     {
         ProfScope pi(c.prof, c.stream, "items");
         // 64-thread blocks, at most 168 registers a thread: 12 warps fit an
         // SM (8 with 256-thread blocks)
         k_items<NK, T><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
-                                                       c.tri_items.p, B, c.item_list.p, n_list, counters);
+                                                       c.tri_items.p, B, c.item_list.p, n_list, n_list2, counters);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     k_tri_reduce<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_frame.p, c.tri_items.p, B, c.tri_E.p,

@@ -274,7 +274,8 @@ constexpr int kSlotPass = 18;    // contact evaluations so far (stamps of this o
 constexpr int kSlotHPass = 19;   // those that assembled the Hessian
 constexpr int kSlotVCount = 20;  // vertices listed in this evaluation
 constexpr int kSlotBCount = 21;  // [2] blocks listed, by Hessian-pass parity
-constexpr int kSlotItemList = 23; // items that passed the FP32 pre-tests
+constexpr int kSlotItemList = 23; // face items that passed the FP32 pre-tests (listed from the front)
+constexpr int kSlotItemList2 = 24; // edge and point items that passed (listed from the back)
 
 // ------------------------------------------------------------------------
 // the context
