@@ -38,12 +38,15 @@ METRIC = "contact samples/s (barrier E+grad+H+CCD)"
 UNIT = "samples/s"
 WORKLOAD = "gel_on_terrain 256x256 pad (131,072 slave tris x 16 samples) vs 199,712-tri Perlin terrain, pressed 0.15 mm"
 CROP_HALF_WIDTH = 2.0e-3
-# Counters of one k_items launch on this workload (the largest kernel of the
-# pass), from the ncu capture summarised in profiles/k_items_gel_on_terrain.md:
-# FP64-pipe lane instructions (warp instructions x 32) and DRAM bytes (read +
-# write).  Null when the kernel changes and the capture is not yet redone.
-K_ITEMS_FP64_LANE_INST = 6722592
-K_ITEMS_DRAM_BYTES = 918528
+# Counters of one k_items launch on this workload (the FP64 phase of the
+# sample evaluation), from the ncu capture summarised in
+# profiles/k_items_gel_on_terrain.md: the FP64 thread instructions executed
+# (sm__sass_thread_inst_executed_op_fp64_pred_on: the work of the lanes that
+# have an item, not the issue slots of partly filled warps) and DRAM bytes
+# (read + write).  Null when the kernel changes and the capture is not yet
+# redone.
+K_ITEMS_FP64_LANE_INST = 3071471
+K_ITEMS_DRAM_BYTES = 917845
 # kernels one contact pass launches on this workload (ncu launch list,
 # profiles/launches_gel_on_terrain.md)
 KERNELS_PER_PASS = 28
