@@ -128,24 +128,35 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_setup(n_gpus):
+def dist_setup(n_gpus, backend="nccl"):
+    """One process per GPU (torchrun sets RANK / WORLD_SIZE / MASTER_*):
+    every rank runs an independent replica of the workload (the benchmark
+    workload is one environment and does not shard); only the timing is
+    reduced across ranks.  backend "gloo" serves the CPU tests."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
         import torch.distributed as dist
-        backend = "nccl"
         dist.init_process_group(backend=backend)
         return rank, world, dist
     return 0, 1, None
 
 
 def max_over_ranks(v, dist):
+    """The slowest rank's value (the whole job ends with it)."""
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(units_per_step, steps, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank has the same per-step work)."""
+    return units_per_step * steps * world / seconds
 
 
 def barrier(dist):
@@ -215,7 +226,7 @@ def run_ours(args):
     prof = ctx.profile_read()
     total_ms = max_over_ranks(total_ms, dist)
     ms_step = total_ms / args.steps
-    value = units * args.steps * world / (total_ms / 1e3)
+    value = job_throughput(units, args.steps, world, total_ms / 1e3)
 
     # end to end: host positions copied in from pinned memory, energy and
     # alpha read back, every step
@@ -232,7 +243,7 @@ def run_ours(args):
         out_host[1] = info["alpha"]
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, dist)
-    e2e_value = units * args.steps * world / e2e_s
+    e2e_value = job_throughput(units, args.steps, world, e2e_s)
 
     if rank != 0:
         return
