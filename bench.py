@@ -258,7 +258,7 @@ def run_ours(args):
     items_ms = sec_ms.get("items")
     fp64_achieved = (K_ITEMS_FP64_LANE_INST / (items_ms / 1e3) / 1e9
                      if K_ITEMS_FP64_LANE_INST and items_ms else None)
-    # the survey's per-unit model beside it: 160 FP32 flops per evaluated
+    # a per-unit model beside it: 160 FP32 flops per evaluated
     # (sample, candidate), against the FP32 CUDA-core rate
     evals = counts_once["face_evaluated"] + 2 * cand["edge"] + cand["point"]
     fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
