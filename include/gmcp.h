@@ -278,6 +278,18 @@ ipc_status ipc_autotune(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev
 /* Set the launch shapes directly (blocks per SM, each in [1, 64]). */
 ipc_status ipc_set_launch_shape(ipc_ctx* ctx, int32_t samples_bpsm, int32_t query_bpsm);
 
+/* The contact pass reads the pad positions and displacements of the slave
+ * (tactile) surface vertices only.  ipc_slave_vertices writes their ids
+ * (ascending; ids_host int32 [n], may be NULL) and *n_host their count.
+ * Synchronises (a device-to-host copy). */
+ipc_status ipc_slave_vertices(ipc_ctx* ctx, int32_t* ids_host, int64_t* n_host);
+
+/* x_dev[ids[k]] = xs_dev[k] (device FP64 [n][3] into [nv][3]) for the slave
+ * vertices of ipc_slave_vertices: a caller that streams only the surface
+ * positions (or displacements) from the host scatters them into its full
+ * device arrays.  Queued on params.stream. */
+ipc_status ipc_scatter_slave(ipc_ctx* ctx, const double* xs_dev, double* x_dev);
+
 /* Section profiler (not part of the method): CUDA events recorded on the
  * context stream around each group of launches (grid build, candidate
  * query, sample kernel, gathers, reductions, step bounds).

@@ -147,6 +147,10 @@ def lib():
     L.ipc_autotune.restype = C.c_int
     L.ipc_autotune.argtypes = [P, P, P, P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_double)]
+    L.ipc_slave_vertices.restype = C.c_int
+    L.ipc_slave_vertices.argtypes = [P, P, C.POINTER(C.c_int64)]
+    L.ipc_scatter_slave.restype = C.c_int
+    L.ipc_scatter_slave.argtypes = [P, P, P]
     L.ipc_set_launch_shape.restype = C.c_int
     L.ipc_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
     L.ipc_newton_step.restype = C.c_int
@@ -530,6 +534,20 @@ class Context:
         self._check(lib().ipc_autotune(self.h, _ptr(x), _ptr(xm0), _ptr(dx), int(reps), C.byref(a),
                                        C.byref(b), C.byref(ms)))
         return a.value, b.value, ms.value
+
+    def slave_vertices(self):
+        """Ids of the slave (tactile) surface vertices, ascending (numpy int32)."""
+        n = C.c_int64()
+        self._check(lib().ipc_slave_vertices(self.h, None, C.byref(n)))
+        ids = np.zeros(n.value, dtype=np.int32)
+        self._check(lib().ipc_slave_vertices(self.h, ids.ctypes.data, C.byref(n)))
+        return ids
+
+    def scatter_slave(self, xs, x):
+        """x[ids] = xs on the device (xs [n_slave, 3], x [nv, 3], FP64)."""
+        xs, x = self._as(xs), self._as(x)
+        self._check(lib().ipc_scatter_slave(self.h, _ptr(xs), _ptr(x)))
+        return x
 
     def set_launch_shape(self, samples_bpsm, query_bpsm):
         self._check(lib().ipc_set_launch_shape(self.h, int(samples_bpsm), int(query_bpsm)))

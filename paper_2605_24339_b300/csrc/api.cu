@@ -112,6 +112,17 @@ __global__ void k_count_sum(const int32_t* __restrict__ cnt, int64_t ns, long lo
     }
 }
 
+// x[svert[k]] = xs[k] for the slave vertices (ipc_scatter_slave)
+__global__ void k_scatter_slave(const int32_t* __restrict__ svert, int64_t n, const double* __restrict__ xs,
+                                double* __restrict__ x) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int64_t v = svert[k];
+    x[3 * v] = xs[3 * k];
+    x[3 * v + 1] = xs[3 * k + 1];
+    x[3 * v + 2] = xs[3 * k + 2];
+}
+
 __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o, int64_t n) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) o[i] = a[i] - b[i];
@@ -1261,6 +1272,26 @@ ipc_status ipc_autotune(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev
     if (samples_bpsm_out) *samples_bpsm_out = bs;
     if (query_bpsm_out) *query_bpsm_out = bq;
     if (ms_out) *ms_out = best;
+    return IPC_OK;
+}
+
+ipc_status ipc_slave_vertices(ipc_ctx* ctx, int32_t* ids_host, int64_t* n_host) {
+    if (!ctx || !n_host) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    *n_host = c.n_svert;
+    if (ids_host && c.n_svert > 0) {
+        API_CK(ctx, cudaMemcpy(ids_host, c.svert.p, sizeof(int32_t) * c.n_svert, cudaMemcpyDeviceToHost));
+    }
+    return IPC_OK;
+}
+
+ipc_status ipc_scatter_slave(ipc_ctx* ctx, const double* xs_dev, double* x_dev) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (c.n_svert == 0) return IPC_OK;
+    if (!xs_dev || !x_dev) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_scatter_slave: NULL pointer");
+    k_scatter_slave<<<(unsigned)((c.n_svert + 255) / 256), 256, 0, c.stream>>>(c.svert.p, c.n_svert, xs_dev, x_dev);
+    API_CK(ctx, cudaGetLastError());
     return IPC_OK;
 }
 

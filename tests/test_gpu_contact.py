@@ -255,3 +255,33 @@ def test_mixed_decisions_match_fp64(B):
     c64 = B.Context(sc, precision="fp64").barrier_eval(x, sc.Y0, hess=False)["counts"]
     c32 = B.Context(sc, precision="mixed").barrier_eval(x, sc.Y0, hess=False)["counts"]
     assert (c32["face"], c32["edge"], c32["point"]) == (c64["face"], c64["edge"], c64["point"])
+
+
+def test_scattered_surface_inputs_give_the_same_pass(B):
+    """ipc_slave_vertices / ipc_scatter_slave: a pass on arrays that hold
+    only the slave surface vertices' positions and displacements (the rest
+    zero) equals the pass on the full arrays, bitwise."""
+    from paper_2605_24339_b300 import scenes as S
+    sc = S.gel_on_terrain(n_quads=16, nz=2, terrain_quads=24)
+    rng = np.random.default_rng(3)
+    x = sc.X.copy()
+    x[:, 2] -= 1.5 * sc.params["dhat"]
+    dx = rng.normal(scale=1e-5, size=x.shape)
+    ctx = B.Context(sc, precision="mixed")
+    try:
+        xd = torch.as_tensor(x, device="cuda")
+        dxd = torch.as_tensor(dx, device="cuda")
+        xm = torch.as_tensor(sc.Y0, device="cuda")
+        ids = ctx.slave_vertices()
+        assert (np.diff(ids) > 0).all() and np.isin(ids, sc.stris.ravel()).all()
+        assert len(np.unique(sc.stris)) == len(ids)
+        a = ctx.contact_pass(xd, xm, dxd, grad=True, hess=False)
+        xs = torch.zeros_like(xd)
+        dxs = torch.zeros_like(dxd)
+        ctx.scatter_slave(torch.as_tensor(x[ids], device="cuda"), xs)
+        ctx.scatter_slave(torch.as_tensor(dx[ids], device="cuda"), dxs)
+        b = ctx.contact_pass(xs, xm, dxs, grad=True, hess=False)
+        assert a["energy"] == b["energy"] and a["alpha"] == b["alpha"]
+        assert torch.equal(a["grad"], b["grad"])
+    finally:
+        ctx.close()
