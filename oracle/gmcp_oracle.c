@@ -23,6 +23,8 @@
  *   gradient / Hessian ...... Sec. 4.2 (approximation with per-sample PSD clamp)
  *   gamma ................... Sec. 4.3, Eqs. (smoothstep, gamma)
  *   support radius .......... Sec. 4.4, Eq. (adaptive_eps)
+ *   master rows ............. Sec. 4.3 with Eq. (gap): gradient with respect
+ *                              to the master vertices (orc_master_grad)
  *   linearised step ......... Sec. 4.5, Eqs. (ccd, global_ccd)
  *   additive CCD ............ Li, Kaufman, Jiang 2021 (Codimensional IPC), Alg. 1
  *   Newton step ............. IPC problem statement, Sec. 2.1: minimise
@@ -937,6 +939,30 @@ ORC_API double orc_alpha_lin(const orc_scene* s, const double* x, const double* 
 
 /* frozen-linear ("lagged") potential of the samples active at x, evaluated
  * at x + a dx for each a in alphas (reading R6): g~ = g + a (grad g . dx) */
+/* Master rows of two-sided GMCP (Sec. 4.3 with Eq. gap): each sample's gap
+ * is g = n_s . (x_m - x_s) with x_m = sum_j bm_j y_j, so with the sample's
+ * normal and weights held fixed (as for the slave rows of orc_contact_eval)
+ * master vertex y_j gets kappa_q w gamma B'(g) bm_j n_s.  GMCP samples only
+ * (the primitive guard pairs are not included).  grad_m [nmv][3] is
+ * overwritten. */
+ORC_API void orc_master_grad(const orc_scene* s, const double* x, const double* xm, double* grad_m) {
+    svec v = {0, 0, 0};
+    collect_samples(s, x, xm, 0, NULL, &v);
+    memset(grad_m, 0, sizeof(double) * 3 * (size_t)s->nmv);
+    for (int64_t i = 0; i < v.n; ++i) {
+        const orc_sample* k = v.a + i;
+        if (k->type > 2) continue;
+        double B, dB, d2B;
+        orc_barrier(k->g, k->eps, &B, &dB, &d2B);
+        const double c1 = k->kq * k->w * k->gamma * dB;
+        for (int j = 0; j < 3; ++j) {
+            if (k->mv[j] < 0) continue;
+            for (int c = 0; c < 3; ++c) grad_m[3 * (size_t)k->mv[j] + c] += c1 * k->bm[j] * k->ns[c];
+        }
+    }
+    free(v.a);
+}
+
 ORC_API void orc_contact_lagged(const orc_scene* s, const double* x, const double* xm,
                                 const double* dx, int n_alpha, const double* alphas, double* out) {
     svec v = {0, 0, 0};

@@ -80,6 +80,7 @@ def _declare(L):
     L.orc_contact_result_free.argtypes = [C.POINTER(ContactResult)]
     L.orc_samples.restype = I64; L.orc_samples.argtypes = [P, P, P, I, P, C.POINTER(dp)]
     L.orc_alpha_lin.restype = D; L.orc_alpha_lin.argtypes = [P, P, P, P, P]
+    L.orc_master_grad.argtypes = [P, P, P, P]
     L.orc_pt_dist2.restype = D; L.orc_pt_dist2.argtypes = [P, P, P, P]
     L.orc_ee_dist2.restype = D; L.orc_ee_dist2.argtypes = [P, P, P, P]
     L.orc_face_clip_samples.restype = I; L.orc_face_clip_samples.argtypes = [P, P, P]
@@ -290,6 +291,14 @@ class Scene:
             blk_ij=np.ctypeslib.as_array(R.blk_ij, shape=(max(nb, 1), 2))[:nb].copy(),
             blk=np.ctypeslib.as_array(R.blk, shape=(max(nb, 1), 3, 3))[:nb].copy())
         lib().orc_contact_result_free(r)
+        return out
+
+    def master_grad(self, x, xm):
+        """dPsi/dx_m over the master vertices with each sample's normal and
+        weights held fixed (Sec. 4.3, Eq. gap), [nmv, 3]."""
+        x, xm = _f64(x), _f64(xm)
+        out = np.zeros((xm.shape[0], 3))
+        lib().orc_master_grad(self.h, _p(x), _p(xm), _p(out))
         return out
 
     def set_all_pairs(self, flag: bool):
