@@ -199,6 +199,21 @@ ipc_status ipc_barrier_eval(ipc_ctx* ctx, const double* x_dev, const double* xm_
                             double* energy_dev, double* energy_host, void* grad_dev,
                             ipc_bsr_view* hess, ipc_sample_counts* counts);
 
+/* Gradient of the contact potential Psi with respect to the master vertex
+ * positions: the master rows of two-sided GMCP (Sec. 4.3, Eq. gap).  Each
+ * active sample has x_m = sum_j bm_j y_j (face: the master barycentrics of
+ * the cast point, Eq. gram; edge: (1 - eta, eta) at its Gauss point; point:
+ * the vertex itself) and g = n_s . (x_m - x_s) with n_s and the weights held
+ * fixed, as for the slave rows of ipc_barrier_eval, so vertex y_j gets
+ * kappa_q w gamma B'(g) bm_j n_s.  The rows of one sample sum to the negative
+ * of its slave rows (equal and opposite forces, zero net torque).
+ *  x_dev [n_vert][3], xm_dev [n_mvert][3] (device, FP64): the state;
+ *  grad_m_dev [n_mvert][3] (device, FP64, caller-owned): overwritten.
+ * Samples are evaluated in FP64 in both precision modes; the rows are summed
+ * with FP64 atomics, so repeated calls agree to rounding, not bitwise.
+ * Asynchronous on params.stream. */
+ipc_status ipc_master_grad(ipc_ctx* ctx, const double* x_dev, const double* xm_dev, double* grad_m_dev);
+
 /* Largest admissible step for the motion x -> x + alpha dx (pad) and
  * xm0 -> xm0 + alpha (xm1 - xm0) (master; xm1_dev NULL = static master):
  * alpha = min(1, alpha_lin, alpha_accd), alpha_lin from Eqs. (ccd) and

@@ -123,6 +123,8 @@ def lib():
     L.ipc_barrier_eval.restype = C.c_int
     L.ipc_barrier_eval.argtypes = [P, P, P, P, C.POINTER(C.c_double), P, C.POINTER(BsrView),
                                    C.POINTER(SampleCounts)]
+    L.ipc_master_grad.restype = C.c_int
+    L.ipc_master_grad.argtypes = [P, P, P, P]
     L.ipc_ccd_max_step.restype = C.c_int
     L.ipc_ccd_max_step.argtypes = [P, P, P, P, P, C.POINTER(C.c_double), C.POINTER(CcdInfo)]
     L.ipc_contact_pass.restype = C.c_int
@@ -371,6 +373,15 @@ class Context:
         ts = "<f4" if bv.dtype == 1 else "<f8"
         vals = t.as_tensor(_CudaArray(bv.vals_dev, (bv.nnzb, 3, 3), ts), device=self.device).clone()
         return rp, ci, vals
+
+    def master_grad(self, x, xm, out=None):
+        """dPsi/dx_m over the master vertices, [n_mvert, 3] FP64 (ipc_master_grad)."""
+        t = self.torch
+        x, xm = self._as(x), self._as(xm)
+        if out is None:
+            out = t.empty((self.nmv, 3), dtype=t.float64, device=self.device)
+        self._check(lib().ipc_master_grad(self.h, _ptr(x), _ptr(xm), _ptr(out)))
+        return out
 
     def ccd_max_step(self, x, dx, xm0, xm1=None):
         x, dx, xm0, xm1 = self._as(x), self._as(dx), self._as(xm0), self._as(xm1)

@@ -1091,6 +1091,18 @@ ipc_status ipc_barrier_eval(ipc_ctx* ctx, const double* x_dev, const double* xm_
     return IPC_OK;
 }
 
+ipc_status ipc_master_grad(ipc_ctx* ctx, const double* x_dev, const double* xm_dev, double* grad_m_dev) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!x_dev || (c.nmv > 0 && (!xm_dev || !grad_m_dev)))
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_master_grad: NULL pointer");
+    if (c.nmv == 0) return IPC_OK;
+    API_CK(ctx, cudaSetDevice(c.device));
+    API_CK(ctx, run_candidates(c, x_dev, xm_dev));
+    API_CK(ctx, contact_master_grad(c, x_dev, xm_dev, grad_m_dev));
+    return IPC_OK;
+}
+
 ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_dev,
                             const double* xm0_dev, const double* xm1_dev, double* alpha_host,
                             ipc_ccd_info* info) {

@@ -39,6 +39,7 @@ namespace {
 constexpr int MODE_EVAL = 0;
 constexpr int MODE_ALPHA = 1;
 constexpr int MODE_LAGGED = 2;
+constexpr int MODE_MASTER = 3;   // gradient rows of the master vertices
 
 // frozen-linear energies of MODE_LAGGED: per active sample, kappa w gamma
 // B(g + a_j dg) for up to 8 step sizes a_j along the direction dx
@@ -47,6 +48,7 @@ struct LagArgs {
     int na = 0;
     double* triE8 = nullptr;   // [8][ns]
     int64_t ns = 0;
+    double* grad_m = nullptr;  // MODE_MASTER: [nmv][3], accumulated
 };
 
 template <class R>
@@ -444,6 +446,8 @@ __device__ __forceinline__ TriData load_tri(const SceneView& S, const CandView& 
 struct ItemOut {
     double kq, w, gamma, g, eps, dg;
     double b[3];
+    int32_t mv[3];   // master vertices of x_m (-1 unused) and their weights
+    double bm[3];
 };
 
 // what a face sample k shares over its candidates: its position, the
@@ -515,7 +519,7 @@ __device__ __forceinline__ bool face_item(const SceneView& S, const Params& P, c
     if (!(g < eps)) return false;
     o.kq = P.kappa; o.w = (1.0 / (double)NK) * D.As; o.gamma = hermite(min3(bm), P.delta_T);
     o.g = g; o.eps = eps;
-    for (int q = 0; q < 3; ++q) o.b[q] = F.beta[q];
+    for (int q = 0; q < 3; ++q) { o.b[q] = F.beta[q]; o.mv[q] = M[q]; o.bm[q] = bm[q]; }
     o.dg = 0.0;
     if (want_dg) {
         const double dm = dxm ? dot(D.ns, interp(bm, ld3(dxm, M[0]), ld3(dxm, M[1]), ld3(dxm, M[2]))) : 0.0;
@@ -576,6 +580,8 @@ __device__ __forceinline__ bool edge_item(const SceneView& S, const Params& P, c
     o.kq = P.kappa_edge; o.w = 0.5 * ell; o.gamma = hermite(eta, P.delta_e) * hermite(1.0 - eta, P.delta_e);
     o.g = g; o.eps = eps;
     for (int c = 0; c < 3; ++c) o.b[c] = bsk[c];
+    o.mv[0] = ia; o.mv[1] = ib; o.mv[2] = -1;
+    o.bm[0] = 1.0 - eta; o.bm[1] = eta; o.bm[2] = 0.0;
     o.dg = 0.0;
     if (want_dg) {
         const double ds = dot(D.ns, interp(bsk, D.dx0, D.dx1, D.dx2));
@@ -612,6 +618,8 @@ __device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, 
     o.kq = P.kappa_point; o.w = 1.0; o.gamma = 1.0;
     o.g = g; o.eps = eps;
     for (int c = 0; c < 3; ++c) o.b[c] = bs[c];
+    o.mv[0] = u; o.mv[1] = -1; o.mv[2] = -1;
+    o.bm[0] = 1.0; o.bm[1] = 0.0; o.bm[2] = 0.0;
     o.dg = 0.0;
     if (want_dg) {
         const double ds = dot(D.ns, interp(bs, D.dx0, D.dx1, D.dx2));
@@ -651,6 +659,20 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
         for (int j = 0; j < 8; ++j) E8[j] = 0.0;
         auto consume = [&](const ItemOut& o) {
             if (MODE == MODE_EVAL) sample_add<T>(A, o.kq, o.w, o.gamma, o.g, o.eps, o.b);
+            if (MODE == MODE_MASTER) {
+                // g = n_s . (x_m - x_s) with x_m = sum_j bm_j y_j: the row of
+                // master vertex y_j is kappa w gamma B'(g) bm_j n_s, the
+                // counterpart of the slave rows -kappa w gamma B'(g) beta_i n_s
+                double Bv, dB, d2B;
+                barrier(o.g, o.eps, Bv, dB, d2B);
+                const double c1 = o.kq * o.w * o.gamma * dB;
+                for (int j = 0; j < 3; ++j) {
+                    if (o.mv[j] < 0) continue;
+                    double* gm = LG.grad_m + 3 * (int64_t)o.mv[j];
+                    const double f = c1 * o.bm[j];
+                    atomicAdd(gm, f * D.ns.x); atomicAdd(gm + 1, f * D.ns.y); atomicAdd(gm + 2, f * D.ns.z);
+                }
+            }
             if (want_dg) {
                 if (want_alpha && o.dg < 0.0) A.amin = rmin(A.amin, 0.9 * o.g / (-o.dg));
                 if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, o.kq * o.w * o.gamma, o.g, o.eps, o.dg);
@@ -1244,6 +1266,18 @@ cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const d
     if (c.P.nk == 4)
         return launch_samples<4, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm, alpha_bits);
     return launch_samples<16, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm, alpha_bits);
+}
+
+cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m) {
+    ProfScope ps(c.prof, c.stream, "master_grad");
+    GMCP_CUDA_TRY(cudaMemsetAsync(grad_m, 0, sizeof(double) * 3 * (size_t)c.nmv, c.stream));
+    LagArgs LG;
+    LG.grad_m = grad_m;
+    if (c.P.nk == 4)
+        return launch_samples<4, double, MODE_MASTER>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                       nullptr, nullptr, LG);
+    return launch_samples<16, double, MODE_MASTER>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                    nullptr, nullptr, LG);
 }
 
 cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,

@@ -432,6 +432,9 @@ int sm_count(int device);
 // (FP64 in both precisions); needs the candidate lists of (x, xm)
 cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,
                            const double* alphas_dev, int na, double* triE8, double* energies_dev);
+// gradient of the contact potential with respect to the master vertices,
+// [nmv][3] FP64 (zeroed first; FP64 atomics, so the summation order varies)
+cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m);
 // newton.cu
 cudaError_t newton_setup(Ctx& c);
 cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev, int32_t* bad);

@@ -1,0 +1,71 @@
+"""GPU master rows (ipc_master_grad through the C ABI) against the oracle's
+(Sec. 4.3 with Eq. gap).  Both evaluate the samples in FP64; the GPU sums
+the rows with FP64 atomics, so the comparison is relative 1e-11 of the
+largest row, not bitwise."""
+import numpy as np
+import pytest
+
+from helpers import flat_over_big_triangle, small_indent
+from paper_2605_24339_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_24339_b300 import binding
+    binding.lib()
+    return binding
+
+
+def _scenes():
+    out = []
+    for L in (1, 2):
+        sc, x = small_indent(n_quads=10, subdiv=3, press=0.12e-3, L=L)
+        out.append((f"indent_L{L}", sc, x))
+    parts, xs = [], []
+    for k, (nq, press) in enumerate([(6, 0.08e-3), (9, 0.15e-3), (4, 0.05e-3)]):
+        s, xx = small_indent(n_quads=nq, subdiv=2 + (k % 2), press=press, seed=20 + k)
+        parts.append(s)
+        xs.append(xx)
+    out.append(("batch3", S.concat_envs(parts), np.concatenate(xs)))
+    return out
+
+
+SCENES = _scenes()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name,sc,x", SCENES, ids=[s[0] for s in SCENES])
+def test_master_grad_matches_oracle(B, oracle_mod, name, sc, x, prec):
+    ctx = B.Context(sc, precision=prec)
+    O = oracle_mod.Scene(sc)
+    g = ctx.master_grad(x, sc.Y0).cpu().numpy()
+    o = O.master_grad(x, sc.Y0)
+    scale = np.abs(o).max()
+    assert scale > 0
+    np.testing.assert_allclose(g, o, rtol=0, atol=1e-11 * scale)
+    # rows only where the oracle has them
+    assert np.array_equal(np.any(g != 0, axis=1), np.any(o != 0, axis=1))
+    # balance with the slave rows of the same pass (FP64 context)
+    if prec == "fp64":
+        gs = ctx.barrier_eval(x, sc.Y0, hess=False, counts=False)["grad"].cpu().numpy()
+        np.testing.assert_allclose(g.sum(axis=0), -gs.sum(axis=0), rtol=0, atol=1e-11 * np.abs(gs).sum())
+    ctx.close()
+
+
+def test_master_grad_no_contact_and_repeat(B):
+    sc, x, xm = flat_over_big_triangle(nq=2, gap=2e-4)
+    ctx = B.Context(sc, precision="fp64")
+    assert np.all(ctx.master_grad(x, xm).cpu().numpy() == 0.0)
+    sc2, x2 = small_indent(n_quads=8, subdiv=2, press=0.12e-3)
+    ctx2 = B.Context(sc2, precision="fp64")
+    a = ctx2.master_grad(x2, sc2.Y0).cpu().numpy()
+    b = ctx2.master_grad(x2, sc2.Y0).cpu().numpy()
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * np.abs(a).max())
+    ctx.close()
+    ctx2.close()
