@@ -943,11 +943,13 @@ ORC_API double orc_alpha_lin(const orc_scene* s, const double* x, const double* 
  * is g = n_s . (x_m - x_s) with x_m = sum_j bm_j y_j, so with the sample's
  * normal and weights held fixed (as for the slave rows of orc_contact_eval)
  * master vertex y_j gets kappa_q w gamma B'(g) bm_j n_s.  GMCP samples only
- * (the primitive guard pairs are not included).  grad_m [nmv][3] is
+ * (the primitive guard pairs are not included); n_sub > 0 restricts the
+ * samples to the slave triangles sub[0..n_sub).  grad_m [nmv][3] is
  * overwritten. */
-ORC_API void orc_master_grad(const orc_scene* s, const double* x, const double* xm, double* grad_m) {
+ORC_API void orc_master_grad(const orc_scene* s, const double* x, const double* xm, int n_sub,
+                             const int32_t* sub, double* grad_m) {
     svec v = {0, 0, 0};
-    collect_samples(s, x, xm, 0, NULL, &v);
+    collect_samples(s, x, xm, n_sub, sub, &v);
     memset(grad_m, 0, sizeof(double) * 3 * (size_t)s->nmv);
     for (int64_t i = 0; i < v.n; ++i) {
         const orc_sample* k = v.a + i;

@@ -80,7 +80,7 @@ def _declare(L):
     L.orc_contact_result_free.argtypes = [C.POINTER(ContactResult)]
     L.orc_samples.restype = I64; L.orc_samples.argtypes = [P, P, P, I, P, C.POINTER(dp)]
     L.orc_alpha_lin.restype = D; L.orc_alpha_lin.argtypes = [P, P, P, P, P]
-    L.orc_master_grad.argtypes = [P, P, P, P]
+    L.orc_master_grad.argtypes = [P, P, P, I, P, P]
     L.orc_pt_dist2.restype = D; L.orc_pt_dist2.argtypes = [P, P, P, P]
     L.orc_ee_dist2.restype = D; L.orc_ee_dist2.argtypes = [P, P, P, P]
     L.orc_face_clip_samples.restype = I; L.orc_face_clip_samples.argtypes = [P, P, P]
@@ -293,12 +293,14 @@ class Scene:
         lib().orc_contact_result_free(r)
         return out
 
-    def master_grad(self, x, xm):
+    def master_grad(self, x, xm, subset=None):
         """dPsi/dx_m over the master vertices with each sample's normal and
-        weights held fixed (Sec. 4.3, Eq. gap), [nmv, 3]."""
+        weights held fixed (Sec. 4.3, Eq. gap), [nmv, 3]; subset: only the
+        samples of these slave triangles."""
         x, xm = _f64(x), _f64(xm)
+        sub = None if subset is None else np.ascontiguousarray(subset, dtype=np.int32)
         out = np.zeros((xm.shape[0], 3))
-        lib().orc_master_grad(self.h, _p(x), _p(xm), _p(out))
+        lib().orc_master_grad(self.h, _p(x), _p(xm), 0 if sub is None else len(sub), _p(sub), _p(out))
         return out
 
     def set_all_pairs(self, flag: bool):

@@ -69,3 +69,40 @@ def test_master_grad_no_contact_and_repeat(B):
     np.testing.assert_allclose(a, b, rtol=0, atol=1e-13 * np.abs(a).max())
     ctx.close()
     ctx2.close()
+
+
+def test_full_size_terrain_sampled_master_rows(B, oracle_mod):
+    """gel_on_terrain at full size (131,072 slave tris x 16 samples, 199,712
+    master tris) in the mixed mode the benchmark times: sampled master rows
+    against the oracle evaluated on every slave triangle near the sampled
+    vertices (a superset of the triangles that can reach them), and the
+    force balance with the slave rows over the whole pass."""
+    sc = S.gel_on_terrain()
+    x = S.drape_on_master(sc, 0.15e-3)
+    ctx = B.Context(sc, precision="mixed")
+    g = ctx.master_grad(x, sc.Y0).cpu().numpy()
+    assert np.any(g != 0, axis=1).sum() > 100
+    Y, M, T = sc.Y0, sc.mtris, sc.stris
+    lm = np.linalg.norm(Y[M] - Y[M[:, [1, 2, 0]]], axis=2).max()
+    ls = np.linalg.norm(x[T] - x[T[:, [1, 2, 0]]], axis=2).max()
+    radius = 2.0 * (lm + ls) + sc.params["dhat"]
+    cen = x[T].mean(axis=1)
+    from scipy.spatial import cKDTree
+    tree = cKDTree(cen)
+    # master vertices closer than half a slave edge to a slave centroid
+    # (geometry only: most of them carry contact)
+    near = np.flatnonzero(tree.query(Y)[0] < 0.5 * ls)
+    rng = np.random.default_rng(3)
+    O = oracle_mod.Scene(sc)
+    n_nonzero = 0
+    for u in rng.choice(near, 12, replace=False):
+        sub = np.array(sorted(tree.query_ball_point(Y[u], radius)), dtype=np.int32)
+        o = O.master_grad(x, sc.Y0, subset=sub)
+        np.testing.assert_allclose(g[u], o[u], rtol=0, atol=1e-11 * max(np.abs(o[u]).max(), 1e-300))
+        n_nonzero += bool(np.any(o[u] != 0))
+    assert n_nonzero >= 5
+    ctx64 = B.Context(sc, precision="fp64")
+    gs = ctx64.barrier_eval(x, sc.Y0, hess=False, counts=False)["grad"].cpu().numpy()
+    np.testing.assert_allclose(g.sum(axis=0), -gs.sum(axis=0), rtol=0, atol=1e-11 * np.abs(gs).sum())
+    ctx.close()
+    ctx64.close()
