@@ -312,6 +312,7 @@ def run_ours(args):
     if not args.no_dual_map:
         line["dual_mesh"] = dual_mesh_measurement(dev)
         line["face_clip"] = face_clip_measurement(dev)
+        line["master_rows"] = master_grad_measurement(dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(steps=2)
     print(json.dumps(line), flush=True)
@@ -770,7 +771,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-envs measurement")
-    ap.add_argument("--no-dual-map", action="store_true", help="skip the dual-mesh mapper measurement")
+    ap.add_argument("--no-dual-map", action="store_true", help="skip the dual-mesh mapper, face-clip and master-row measurements")
     ap.add_argument("--dual-points", type=int, default=2_000_000,
                     help="--mode dualmap: visual points of the dual-mesh measurement")
     ap.add_argument("--no-newton", action="store_true",
