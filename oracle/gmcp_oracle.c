@@ -24,7 +24,8 @@
  *   gamma ................... Sec. 4.3, Eqs. (smoothstep, gamma)
  *   support radius .......... Sec. 4.4, Eq. (adaptive_eps)
  *   master rows ............. Sec. 4.3 with Eq. (gap): gradient with respect
- *                              to the master vertices (orc_master_grad)
+ *                              to the master vertices (orc_master_grad) and
+ *                              the blocks with master vertices (orc_master_hess)
  *   linearised step ......... Sec. 4.5, Eqs. (ccd, global_ccd)
  *   additive CCD ............ Li, Kaufman, Jiang 2021 (Codimensional IPC), Alg. 1
  *   Newton step ............. IPC problem statement, Sec. 2.1: minimise
@@ -963,6 +964,50 @@ ORC_API void orc_master_grad(const orc_scene* s, const double* x, const double* 
         }
     }
     free(v.a);
+}
+
+/* Hessian blocks of two-sided GMCP that involve master vertices (Sec. 4.2
+ * approximation, Sec. 4.3 with Eq. gap): a sample's gap gradient is
+ * -bs_a n_s on slave vertex a and bm_j n_s on master vertex j; the block
+ * (u, v) of two of them is max(kappa w gamma B''(g), 0) w_u w_v n_s n_s^T,
+ * the same clamped curvature as the slave-slave blocks of orc_contact_eval.
+ * Joint numbering: master vertex j is nv + j.  Written: (slave a, master j)
+ * and (master i, master j) for every sample, unsorted, with repeats; at most
+ * cap entries.  Returns the number of entries. */
+ORC_API int64_t orc_master_hess(const orc_scene* s, const double* x, const double* xm, int n_sub,
+                                const int32_t* sub, int64_t cap, int32_t* ij, double* blk) {
+    svec v = {0, 0, 0};
+    collect_samples(s, x, xm, n_sub, sub, &v);
+    int64_t n = 0;
+    for (int64_t i = 0; i < v.n; ++i) {
+        const orc_sample* k = v.a + i;
+        if (k->type > 2) continue;
+        double B, dB, d2B;
+        orc_barrier(k->g, k->eps, &B, &dB, &d2B);
+        const double c2 = dmax(k->kq * k->w * k->gamma * d2B, 0.0);
+        const int32_t* T = s->stri + 3 * (size_t)k->stri;
+        for (int j = 0; j < 3; ++j) {
+            if (k->mv[j] < 0) continue;
+            /* rows: the three slave vertices, then the master vertices */
+            for (int r = 0; r < 6; ++r) {
+                int row;
+                double wr;
+                if (r < 3) { row = T[r]; wr = -k->bs[r]; }
+                else {
+                    if (k->mv[r - 3] < 0) continue;
+                    row = s->nv + k->mv[r - 3]; wr = k->bm[r - 3];
+                }
+                if (n < cap) {
+                    ij[2 * n] = row; ij[2 * n + 1] = s->nv + k->mv[j];
+                    for (int p = 0; p < 3; ++p)
+                        for (int q = 0; q < 3; ++q) blk[9 * n + 3 * p + q] = c2 * wr * k->bm[j] * k->ns[p] * k->ns[q];
+                }
+                ++n;
+            }
+        }
+    }
+    free(v.a);
+    return n;
 }
 
 ORC_API void orc_contact_lagged(const orc_scene* s, const double* x, const double* xm,

@@ -81,6 +81,8 @@ def _declare(L):
     L.orc_samples.restype = I64; L.orc_samples.argtypes = [P, P, P, I, P, C.POINTER(dp)]
     L.orc_alpha_lin.restype = D; L.orc_alpha_lin.argtypes = [P, P, P, P, P]
     L.orc_master_grad.argtypes = [P, P, P, I, P, P]
+    L.orc_master_hess.restype = I64
+    L.orc_master_hess.argtypes = [P, P, P, I, P, I64, P, P]
     L.orc_pt_dist2.restype = D; L.orc_pt_dist2.argtypes = [P, P, P, P]
     L.orc_ee_dist2.restype = D; L.orc_ee_dist2.argtypes = [P, P, P, P]
     L.orc_face_clip_samples.restype = I; L.orc_face_clip_samples.argtypes = [P, P, P]
@@ -301,6 +303,22 @@ class Scene:
         sub = None if subset is None else np.ascontiguousarray(subset, dtype=np.int32)
         out = np.zeros((xm.shape[0], 3))
         lib().orc_master_grad(self.h, _p(x), _p(xm), 0 if sub is None else len(sub), _p(sub), _p(out))
+        return out
+
+    def master_hess(self, x, xm, subset=None):
+        """Slave-master and master-master blocks (Sec. 4.2-4.3), summed over
+        repeats: dict (row, col) -> 3x3, master vertex j numbered nv + j."""
+        x, xm = _f64(x), _f64(xm)
+        sub = None if subset is None else np.ascontiguousarray(subset, dtype=np.int32)
+        ns = 0 if sub is None else len(sub)
+        n = lib().orc_master_hess(self.h, _p(x), _p(xm), ns, _p(sub), 0, None, None)
+        ij = np.zeros((max(n, 1), 2), dtype=np.int32)
+        blk = np.zeros((max(n, 1), 3, 3))
+        lib().orc_master_hess(self.h, _p(x), _p(xm), ns, _p(sub), n, _p(ij), _p(blk))
+        out = {}
+        for (r, c), b in zip(ij[:n], blk[:n]):
+            key = (int(r), int(c))
+            out[key] = out.get(key, 0.0) + b
         return out
 
     def set_all_pairs(self, flag: bool):

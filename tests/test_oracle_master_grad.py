@@ -59,3 +59,65 @@ def test_no_contact_gives_zero_master_rows(oracle_mod):
     sc, x, xm = flat_over_big_triangle(nq=2, gap=2e-4)   # beyond dhat = 1e-4
     O = oracle_mod.Scene(sc)
     assert np.all(O.master_grad(x, xm) == 0.0)
+
+
+def test_flat_master_blocks_match_finite_differences(oracle_mod):
+    # Same parallel-plane scene: the master rows and the slave rows are exact
+    # there, so their derivatives with respect to a master vertex are the
+    # master-master and slave-master blocks.  Along the normal (z) the
+    # Gauss-Newton form is exact.  An in-plane move of a master vertex
+    # changes no gap but does change the master weights bm_j of the cast
+    # points, a term B'(g) dbm_j/dy that the Gauss-Newton form leaves out
+    # (as the slave side leaves out its own weight derivatives), so the
+    # master-master blocks are compared on their z column only.
+    sc, x, xm = flat_over_big_triangle(nq=3, gap=3e-5, L=1)
+    O = oracle_mod.Scene(sc)
+    nv = x.shape[0]
+    H = O.master_hess(x, xm)
+    assert H
+    h = 1e-10
+    fd_m = np.zeros((3, 3, 3, 3))            # [row master j][col master i][p][q]
+    fd_s = np.zeros((nv, 3, 3, 3))           # [slave a][col master i][p][q]
+    for i in range(3):
+        for q in range(3):
+            p_, m_ = xm.copy(), xm.copy()
+            p_[i, q] += h
+            m_[i, q] -= h
+            fd_m[:, i, :, q] = (O.master_grad(x, p_) - O.master_grad(x, m_)) / (2 * h)
+            fd_s[:, i, :, q] = (O.contact(x, p_)["grad"] - O.contact(x, m_)["grad"]) / (2 * h)
+    scale = max(np.abs(b).max() for b in H.values())
+    for j in range(3):
+        for i in range(3):
+            np.testing.assert_allclose(H.get((nv + j, nv + i), np.zeros((3, 3)))[:, 2], fd_m[j, i][:, 2],
+                                       rtol=0, atol=1e-6 * scale)
+            # the in-plane columns of the exact derivative are the weight term
+            assert np.abs(fd_m[j, i][:, :2]).max() < 1e-3 * scale
+    for a in range(nv):
+        for i in range(3):
+            np.testing.assert_allclose(H.get((a, nv + i), np.zeros((3, 3))), fd_s[a, i],
+                                       rtol=0, atol=1e-6 * scale)
+
+
+@pytest.mark.parametrize("L,subdiv", [(1, 2), (2, 3)])
+def test_joint_hessian_annihilates_translations(oracle_mod, L, subdiv):
+    # Moving slave and master together changes no gap, so every block row of
+    # the joint Hessian (slave-slave from the contact evaluation, slave-master
+    # and its transpose, master-master) sums to zero.
+    sc, x = small_indent(n_quads=10, subdiv=subdiv, press=0.15e-3, L=L)
+    O = oracle_mod.Scene(sc)
+    r = O.contact(x, sc.Y0)
+    H = O.master_hess(x, sc.Y0)
+    rows = {}
+    def add(u, b):
+        rows[u] = rows.get(u, np.zeros((3, 3))) + b
+    for (u, v), b in zip(r["blk_ij"], r["blk"]):
+        add(int(u), b)
+    nv = x.shape[0]
+    for (u, v), b in H.items():
+        add(u, b)
+        if u < nv:          # slave-master: its transpose is the master-slave block
+            add(v, b.T)
+    scale = max(np.abs(b).max() for b in r["blk"])
+    assert any(u >= nv for u in rows)
+    for u, b in rows.items():
+        assert np.abs(b).max() < 1e-10 * scale, (u, b)
