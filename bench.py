@@ -21,6 +21,7 @@ around the highest terrain peak) with the same metric.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -375,6 +376,21 @@ def master_grad_measurement(dev, reps=50):
         e1.record()
     torch.cuda.synchronize()
     ms = statistics.median([e0.elapsed_time(e1) for e0, e1 in ev])
+    # the Hessian blocks with master vertices (synchronising call: wall time)
+    ij, blk = ctx.master_hess(xd, xm)
+    cap = ij.shape[0]
+    ij = torch.empty((max(cap, 1), 2), dtype=torch.int32, device="cuda")
+    blk = torch.empty((max(cap, 1), 9), dtype=torch.float64, device="cuda")
+    n = ctypes.c_int64()
+    hts = []
+    for _ in range(reps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = binding.lib().ipc_master_hess(ctx.h, binding._ptr(xd), binding._ptr(xm), cap, binding._ptr(ij),
+                                           binding._ptr(blk), ctypes.byref(n))
+        hts.append(time.perf_counter() - t0)
+        assert st == 0
     ctx64 = binding.Context(sc, precision="fp64", device=dev)
     gm = ctx64.master_grad(xd, xm).cpu().numpy()
     gs = ctx64.barrier_eval(xd, xm, hess=False, counts=False)["grad"].cpu().numpy()
@@ -384,6 +400,7 @@ def master_grad_measurement(dev, reps=50):
     ctx64.close()
     return {"workload": "gel_on_terrain pad draped 0.15 mm onto the terrain (master rows of every active sample)",
             "ms_per_call": round(ms, 4), "master_rows": rows, "balance_rel": bal,
+            "hess_ms_per_call": round(statistics.median(hts) * 1e3, 4), "hess_blocks": int(n.value),
             "l2": "flushed (256 MB write) between calls",
             "note": "broad phase + warp-per-triangle FP64 sample kernel with FP64 atomics"}
 

@@ -214,6 +214,29 @@ ipc_status ipc_barrier_eval(ipc_ctx* ctx, const double* x_dev, const double* xm_
  * Asynchronous on params.stream. */
 ipc_status ipc_master_grad(ipc_ctx* ctx, const double* x_dev, const double* xm_dev, double* grad_m_dev);
 
+/* Hessian blocks of the contact potential that involve master vertices
+ * (two-sided GMCP, Sec. 4.2-4.3 with Eq. gap), in the Gauss-Newton form of
+ * the slave-slave blocks of ipc_barrier_eval: a sample with slave weights
+ * beta_a and master weights bm_j has the gap gradient -beta_a n_s on slave
+ * vertex a and bm_j n_s on master vertex j, and adds
+ * max(kappa_q w gamma B''(g), 0) w_u w_v n_s n_s^T to the block (u, v).
+ * Vertices are numbered jointly: pad vertex i is i, master vertex j is
+ * n_vert + j.  Written are the slave-master blocks (row a pad vertex, column
+ * a master vertex; their transposes are the master-slave blocks) and the
+ * master-master blocks, one entry per sample and vertex pair, unsorted and
+ * with repeats (sum repeated (row, col) entries); together with the pad
+ * blocks of ipc_barrier_eval every block row sums to zero.
+ *  x_dev, xm_dev (device, FP64): the state;
+ *  capacity: entries the caller's arrays hold;
+ *  ij_dev [capacity][2] int32 (row, col) and blk_dev [capacity][9] FP64
+ *  row-major 3x3 (device, caller-owned);
+ *  n_host (host): the number of entries.
+ * Samples are evaluated in FP64 in both precision modes.  Synchronises
+ * params.stream.  IPC_ERR_CAPACITY when *n_host > capacity (nothing past
+ * capacity is written; call again with room for *n_host). */
+ipc_status ipc_master_hess(ipc_ctx* ctx, const double* x_dev, const double* xm_dev, int64_t capacity,
+                           int32_t* ij_dev, double* blk_dev, int64_t* n_host);
+
 /* Largest admissible step for the motion x -> x + alpha dx (pad) and
  * xm0 -> xm0 + alpha (xm1 - xm0) (master; xm1_dev NULL = static master):
  * alpha = min(1, alpha_lin, alpha_accd), alpha_lin from Eqs. (ccd) and

@@ -125,6 +125,8 @@ def lib():
                                    C.POINTER(SampleCounts)]
     L.ipc_master_grad.restype = C.c_int
     L.ipc_master_grad.argtypes = [P, P, P, P]
+    L.ipc_master_hess.restype = C.c_int
+    L.ipc_master_hess.argtypes = [P, P, P, C.c_int64, P, P, C.POINTER(C.c_int64)]
     L.ipc_ccd_max_step.restype = C.c_int
     L.ipc_ccd_max_step.argtypes = [P, P, P, P, P, C.POINTER(C.c_double), C.POINTER(CcdInfo)]
     L.ipc_contact_pass.restype = C.c_int
@@ -382,6 +384,24 @@ class Context:
             out = t.empty((self.nmv, 3), dtype=t.float64, device=self.device)
         self._check(lib().ipc_master_grad(self.h, _ptr(x), _ptr(xm), _ptr(out)))
         return out
+
+    def master_hess(self, x, xm, capacity=None):
+        """Slave-master and master-master Hessian blocks (ipc_master_hess):
+        (ij [n, 2] int32 in the joint numbering, blk [n, 3, 3] FP64), with
+        repeated (row, col) entries; grows the arrays once if needed."""
+        t = self.torch
+        x, xm = self._as(x), self._as(xm)
+        cap = int(capacity) if capacity is not None else 1 << 16
+        n = C.c_int64()
+        while True:
+            ij = t.empty((max(cap, 1), 2), dtype=t.int32, device=self.device)
+            blk = t.empty((max(cap, 1), 3, 3), dtype=t.float64, device=self.device)
+            st = lib().ipc_master_hess(self.h, _ptr(x), _ptr(xm), cap, _ptr(ij), _ptr(blk), C.byref(n))
+            if st == 5 and n.value > cap:   # IPC_ERR_CAPACITY
+                cap = n.value
+                continue
+            self._check(st)
+            return ij[: n.value], blk[: n.value]
 
     def ccd_max_step(self, x, dx, xm0, xm1=None):
         x, dx, xm0, xm1 = self._as(x), self._as(dx), self._as(xm0), self._as(xm1)

@@ -1103,6 +1103,26 @@ ipc_status ipc_master_grad(ipc_ctx* ctx, const double* x_dev, const double* xm_d
     return IPC_OK;
 }
 
+ipc_status ipc_master_hess(ipc_ctx* ctx, const double* x_dev, const double* xm_dev, int64_t capacity,
+                           int32_t* ij_dev, double* blk_dev, int64_t* n_host) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!x_dev || !n_host || capacity < 0 || (capacity > 0 && (!ij_dev || !blk_dev)) || (c.nmv > 0 && !xm_dev))
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_master_hess: NULL pointer or negative capacity");
+    *n_host = 0;
+    if (c.nmv == 0) return IPC_OK;
+    API_CK(ctx, cudaSetDevice(c.device));
+    API_CK(ctx, run_candidates(c, x_dev, xm_dev));
+    API_CK(ctx, contact_master_hess(c, x_dev, xm_dev, ij_dev, blk_dev, capacity, c.u64_tmp.p + 2));
+    unsigned long long n = 0;
+    API_CK(ctx, cudaMemcpyAsync(&n, c.u64_tmp.p + 2, sizeof(n), cudaMemcpyDeviceToHost, c.stream));
+    API_CK(ctx, cudaStreamSynchronize(c.stream));
+    *n_host = (int64_t)n;
+    if ((int64_t)n > capacity)
+        return fail_ctx(ctx, IPC_ERR_CAPACITY, "ipc_master_hess: more blocks than capacity (*n_host holds the count)");
+    return IPC_OK;
+}
+
 ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_dev,
                             const double* xm0_dev, const double* xm1_dev, double* alpha_host,
                             ipc_ccd_info* info) {

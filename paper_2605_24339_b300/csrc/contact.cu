@@ -40,6 +40,7 @@ constexpr int MODE_EVAL = 0;
 constexpr int MODE_ALPHA = 1;
 constexpr int MODE_LAGGED = 2;
 constexpr int MODE_MASTER = 3;   // gradient rows of the master vertices
+constexpr int MODE_MASTER_HESS = 4;   // slave-master and master-master Hessian blocks
 
 // frozen-linear energies of MODE_LAGGED: per active sample, kappa w gamma
 // B(g + a_j dg) for up to 8 step sizes a_j along the direction dx
@@ -49,7 +50,15 @@ struct LagArgs {
     double* triE8 = nullptr;   // [8][ns]
     int64_t ns = 0;
     double* grad_m = nullptr;  // MODE_MASTER: [nmv][3], accumulated
+    // MODE_MASTER_HESS: blocks (row, col) with value coef n n^T, appended at
+    // *h_count (entries past h_cap are counted, not written)
+    int32_t* h_ij = nullptr;   // [h_cap][2]
+    double* h_blk = nullptr;   // [h_cap][9]
+    unsigned long long* h_count = nullptr;
+    int64_t h_cap = 0;
+    int32_t m_off = 0;         // index of master vertex 0 in the joint numbering
 };
+
 
 template <class R>
 struct V3 { R x, y, z; };
@@ -632,6 +641,16 @@ __device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, 
 // Warp per active triangle (persistent grid).  Used for the step bound and
 // the lagged energies of the line search, and for the contact evaluation
 // when the item buffer is too small (then run_if_over selects it).
+__device__ __forceinline__ void put_block(const LagArgs& LG, int32_t r, int32_t c, double coef, const V3<double>& n) {
+    const unsigned long long at = atomicAdd(LG.h_count, 1ull);
+    if ((int64_t)at >= LG.h_cap) return;
+    LG.h_ij[2 * at] = r; LG.h_ij[2 * at + 1] = c;
+    double* b = LG.h_blk + 9 * at;
+    const double nn[3] = {n.x, n.y, n.z};
+    for (int p = 0; p < 3; ++p)
+        for (int q = 0; q < 3; ++q) b[3 * p + q] = coef * nn[p] * nn[q];
+}
+
 template <int NK, class T, int MODE>
 __global__ void __launch_bounds__(256)
 k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
@@ -671,6 +690,23 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
                     double* gm = LG.grad_m + 3 * (int64_t)o.mv[j];
                     const double f = c1 * o.bm[j];
                     atomicAdd(gm, f * D.ns.x); atomicAdd(gm + 1, f * D.ns.y); atomicAdd(gm + 2, f * D.ns.z);
+                }
+            }
+            if (MODE == MODE_MASTER_HESS) {
+                // the sample's gap gradient is (-beta_a n_s) on its slave
+                // vertices and (bm_j n_s) on its master vertices; its
+                // Gauss-Newton block between two of them is
+                // max(kappa w gamma B''(g), 0) w_u w_v n_s n_s^T
+                double Bv, dB, d2B;
+                barrier(o.g, o.eps, Bv, dB, d2B);
+                const double c2 = rmax(o.kq * o.w * o.gamma * d2B, 0.0);
+                const int32_t* Ts = S.stri + 3 * D.t;
+                for (int j = 0; j < 3; ++j) {
+                    if (o.mv[j] < 0) continue;
+                    const int32_t cj = LG.m_off + o.mv[j];
+                    for (int a = 0; a < 3; ++a) put_block(LG, Ts[a], cj, -c2 * o.b[a] * o.bm[j], D.ns);
+                    for (int i = 0; i < 3; ++i)
+                        if (o.mv[i] >= 0) put_block(LG, LG.m_off + o.mv[i], cj, c2 * o.bm[i] * o.bm[j], D.ns);
                 }
             }
             if (want_dg) {
@@ -1278,6 +1314,19 @@ cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, doubl
                                                        nullptr, nullptr, LG);
     return launch_samples<16, double, MODE_MASTER>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                     nullptr, nullptr, LG);
+}
+
+cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32_t* ij, double* blk,
+                                int64_t cap, unsigned long long* count) {
+    ProfScope ps(c.prof, c.stream, "master_hess");
+    GMCP_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), c.stream));
+    LagArgs LG;
+    LG.h_ij = ij; LG.h_blk = blk; LG.h_count = count; LG.h_cap = cap; LG.m_off = (int32_t)c.nv;
+    if (c.P.nk == 4)
+        return launch_samples<4, double, MODE_MASTER_HESS>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                            nullptr, nullptr, LG);
+    return launch_samples<16, double, MODE_MASTER_HESS>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                         nullptr, nullptr, LG);
 }
 
 cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,

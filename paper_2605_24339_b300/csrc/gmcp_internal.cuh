@@ -435,6 +435,10 @@ cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const doub
 // gradient of the contact potential with respect to the master vertices,
 // [nmv][3] FP64 (zeroed first; FP64 atomics, so the summation order varies)
 cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m);
+// slave-master (slave row) and master-master Hessian blocks of the active
+// samples, appended in arbitrary order; *count receives the number needed
+cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32_t* ij, double* blk,
+                                int64_t cap, unsigned long long* count);
 // newton.cu
 cudaError_t newton_setup(Ctx& c);
 cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev, int32_t* bad);

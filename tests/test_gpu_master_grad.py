@@ -106,3 +106,50 @@ def test_full_size_terrain_sampled_master_rows(B, oracle_mod):
     np.testing.assert_allclose(g.sum(axis=0), -gs.sum(axis=0), rtol=0, atol=1e-11 * np.abs(gs).sum())
     ctx.close()
     ctx64.close()
+
+
+def _sum_blocks(ij, blk):
+    out = {}
+    for (r, c), b in zip(ij.cpu().numpy(), blk.cpu().numpy()):
+        key = (int(r), int(c))
+        out[key] = out.get(key, 0.0) + b
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("name,sc,x", SCENES, ids=[s[0] for s in SCENES])
+def test_master_hess_matches_oracle(B, oracle_mod, name, sc, x, prec):
+    ctx = B.Context(sc, precision=prec)
+    O = oracle_mod.Scene(sc)
+    G = _sum_blocks(*ctx.master_hess(x, sc.Y0, capacity=16))   # grows once
+    H = O.master_hess(x, sc.Y0)
+    assert set(G) == set(H)
+    scale = max(np.abs(b).max() for b in H.values())
+    for k, b in H.items():
+        np.testing.assert_allclose(G[k], b, rtol=0, atol=1e-11 * scale)
+    ctx.close()
+
+
+def test_master_hess_capacity_and_empty(B):
+    sc, x = small_indent(n_quads=8, subdiv=2, press=0.12e-3)
+    ctx = B.Context(sc, precision="fp64")
+    ij, blk = ctx.master_hess(x, sc.Y0)
+    n = ij.shape[0]
+    assert n > 0
+    # too small: IPC_ERR_CAPACITY with the count, nothing past capacity written
+    import ctypes
+    from paper_2605_24339_b300 import binding as Bm
+    xs, xm = ctx._as(x), ctx._as(sc.Y0)
+    ij2 = torch.full((4, 2), -7, dtype=torch.int32, device="cuda")
+    blk2 = torch.zeros((4, 3, 3), dtype=torch.float64, device="cuda")
+    cnt = ctypes.c_int64()
+    st = Bm.lib().ipc_master_hess(ctx.h, Bm._ptr(xs), Bm._ptr(xm), 2, Bm._ptr(ij2), Bm._ptr(blk2), ctypes.byref(cnt))
+    assert st == 5 and cnt.value == n
+    assert (ij2[2:].cpu().numpy() == -7).all()
+    # no contact: no blocks
+    sc3, x3, xm3 = flat_over_big_triangle(nq=2, gap=2e-4)
+    ctx3 = B.Context(sc3, precision="fp64")
+    ij3, _ = ctx3.master_hess(x3, xm3)
+    assert ij3.shape[0] == 0
+    ctx.close()
+    ctx3.close()
