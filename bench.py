@@ -353,9 +353,10 @@ def face_clip_measurement(dev, n_pairs=2_000_000, reps=20):
 
 def master_grad_measurement(dev, reps=50):
     """Master rows of two-sided GMCP (Sec. 4.3 with Eq. gap, ipc_master_grad)
-    on the pressed gel_on_terrain state: the broad phase plus the FP64
-    sample kernel that adds kappa w gamma B'(g) bm_j n_s to each master
-    vertex.  CUDA events on the context's stream, L2 flushed between calls.
+    on the pressed gel_on_terrain state: the broad phase plus the
+    item-parallel FP64 sample kernels, which add kappa w gamma B'(g) bm_j n_s
+    to each master vertex (ipc_master_hess: the blocks with master vertices,
+    wall time of the synchronising call).  CUDA events on the context's stream, L2 flushed between calls.
     The balance check (net master force + net slave force, relative to the
     total slave force) holds at any size."""
     import torch
@@ -402,7 +403,7 @@ def master_grad_measurement(dev, reps=50):
             "ms_per_call": round(ms, 4), "master_rows": rows, "balance_rel": bal,
             "hess_ms_per_call": round(statistics.median(hts) * 1e3, 4), "hess_blocks": int(n.value),
             "l2": "flushed (256 MB write) between calls",
-            "note": "broad phase + warp-per-triangle FP64 sample kernel with FP64 atomics"}
+            "note": "broad phase + item-parallel FP64 sample kernels (k_items_pre, k_items) with FP64 atomics"}
 
 
 def dual_mesh_measurement(dev, n_points=2_000_000, reps=50):

@@ -641,7 +641,7 @@ __device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, 
 // Warp per active triangle (persistent grid).  Used for the step bound and
 // the lagged energies of the line search, and for the contact evaluation
 // when the item buffer is too small (then run_if_over selects it).
-__device__ __forceinline__ void put_block(const LagArgs& LG, int32_t r, int32_t c, double coef, const V3<double>& n) {
+__device__ void put_block(const LagArgs& LG, int32_t r, int32_t c, double coef, const V3<double>& n) {
     const unsigned long long at = atomicAdd(LG.h_count, 1ull);
     if ((int64_t)at >= LG.h_cap) return;
     LG.h_ij[2 * at] = r; LG.h_ij[2 * at + 1] = c;
@@ -649,6 +649,37 @@ __device__ __forceinline__ void put_block(const LagArgs& LG, int32_t r, int32_t 
     const double nn[3] = {n.x, n.y, n.z};
     for (int p = 0; p < 3; ++p)
         for (int q = 0; q < 3; ++q) b[3 * p + q] = coef * nn[p] * nn[q];
+}
+
+// g = n_s . (x_m - x_s) with x_m = sum_j bm_j y_j: the row of master vertex
+// y_j is kappa w gamma B'(g) bm_j n_s, the counterpart of the slave rows
+// -kappa w gamma B'(g) beta_i n_s
+__device__ void master_rows(const LagArgs& LG, const ItemOut& o, const V3<double>& ns) {
+    double Bv, dB, d2B;
+    barrier(o.g, o.eps, Bv, dB, d2B);
+    const double c1 = o.kq * o.w * o.gamma * dB;
+    for (int j = 0; j < 3; ++j) {
+        if (o.mv[j] < 0) continue;
+        double* gm = LG.grad_m + 3 * (int64_t)o.mv[j];
+        const double f = c1 * o.bm[j];
+        atomicAdd(gm, f * ns.x); atomicAdd(gm + 1, f * ns.y); atomicAdd(gm + 2, f * ns.z);
+    }
+}
+
+// the sample's gap gradient is (-beta_a n_s) on its slave vertices Ts[a] and
+// (bm_j n_s) on its master vertices; its Gauss-Newton block between two of
+// them is max(kappa w gamma B''(g), 0) w_u w_v n_s n_s^T
+__device__ void master_blocks(const LagArgs& LG, const ItemOut& o, const int32_t* Ts, const V3<double>& ns) {
+    double Bv, dB, d2B;
+    barrier(o.g, o.eps, Bv, dB, d2B);
+    const double c2 = rmax(o.kq * o.w * o.gamma * d2B, 0.0);
+    for (int j = 0; j < 3; ++j) {
+        if (o.mv[j] < 0) continue;
+        const int32_t cj = LG.m_off + o.mv[j];
+        for (int a = 0; a < 3; ++a) put_block(LG, Ts[a], cj, -c2 * o.b[a] * o.bm[j], ns);
+        for (int i = 0; i < 3; ++i)
+            if (o.mv[i] >= 0) put_block(LG, LG.m_off + o.mv[i], cj, c2 * o.bm[i] * o.bm[j], ns);
+    }
 }
 
 template <int NK, class T, int MODE>
@@ -678,37 +709,8 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
         for (int j = 0; j < 8; ++j) E8[j] = 0.0;
         auto consume = [&](const ItemOut& o) {
             if (MODE == MODE_EVAL) sample_add<T>(A, o.kq, o.w, o.gamma, o.g, o.eps, o.b);
-            if (MODE == MODE_MASTER) {
-                // g = n_s . (x_m - x_s) with x_m = sum_j bm_j y_j: the row of
-                // master vertex y_j is kappa w gamma B'(g) bm_j n_s, the
-                // counterpart of the slave rows -kappa w gamma B'(g) beta_i n_s
-                double Bv, dB, d2B;
-                barrier(o.g, o.eps, Bv, dB, d2B);
-                const double c1 = o.kq * o.w * o.gamma * dB;
-                for (int j = 0; j < 3; ++j) {
-                    if (o.mv[j] < 0) continue;
-                    double* gm = LG.grad_m + 3 * (int64_t)o.mv[j];
-                    const double f = c1 * o.bm[j];
-                    atomicAdd(gm, f * D.ns.x); atomicAdd(gm + 1, f * D.ns.y); atomicAdd(gm + 2, f * D.ns.z);
-                }
-            }
-            if (MODE == MODE_MASTER_HESS) {
-                // the sample's gap gradient is (-beta_a n_s) on its slave
-                // vertices and (bm_j n_s) on its master vertices; its
-                // Gauss-Newton block between two of them is
-                // max(kappa w gamma B''(g), 0) w_u w_v n_s n_s^T
-                double Bv, dB, d2B;
-                barrier(o.g, o.eps, Bv, dB, d2B);
-                const double c2 = rmax(o.kq * o.w * o.gamma * d2B, 0.0);
-                const int32_t* Ts = S.stri + 3 * D.t;
-                for (int j = 0; j < 3; ++j) {
-                    if (o.mv[j] < 0) continue;
-                    const int32_t cj = LG.m_off + o.mv[j];
-                    for (int a = 0; a < 3; ++a) put_block(LG, Ts[a], cj, -c2 * o.b[a] * o.bm[j], D.ns);
-                    for (int i = 0; i < 3; ++i)
-                        if (o.mv[i] >= 0) put_block(LG, LG.m_off + o.mv[i], cj, c2 * o.bm[i] * o.bm[j], D.ns);
-                }
-            }
+            if (MODE == MODE_MASTER) master_rows(LG, o, D.ns);
+            if (MODE == MODE_MASTER_HESS) master_blocks(LG, o, S.stri + 3 * D.t, D.ns);
             if (want_dg) {
                 if (want_alpha && o.dg < 0.0) A.amin = rmin(A.amin, 0.9 * o.g / (-o.dg));
                 if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, o.kq * o.w * o.gamma, o.g, o.eps, o.dg);
@@ -905,12 +907,13 @@ k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, con
 
 // Phase 2, one thread per listed item: the exact FP64 geometry and the
 // contribution (the arithmetic of sample_add).
-template <int NK, class T>
+template <int NK, class T, int MODE = MODE_EVAL>
 __global__ void __launch_bounds__(64, 6)
 k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
         const double* __restrict__ dx, const double* __restrict__ dxm, const double* __restrict__ frame,
         const int32_t* __restrict__ items, ItemBufs B, const int32_t* __restrict__ list,
-        const int32_t* __restrict__ n_list, const int32_t* __restrict__ n_list2, long long* counters) {
+        const int32_t* __restrict__ n_list, const int32_t* __restrict__ n_list2, long long* counters,
+        LagArgs LG = LagArgs()) {
     if ((int64_t)*B.n > B.cap) return;
     const int nf = *n_list;
     const int n = nf + *n_list2;
@@ -934,6 +937,14 @@ k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const d
         } else {
             on = point_item(S, P, D, xm, dxm, C.point[D.t * C.cap_p + R.j], false, want_dg, o);
             cnt_p += on;
+        }
+        if (MODE == MODE_MASTER) {
+            if (on) master_rows(LG, o, D.ns);
+            continue;
+        }
+        if (MODE == MODE_MASTER_HESS) {
+            if (on) master_blocks(LG, o, S.stri + 3 * D.t, D.ns);
+            continue;
         }
         double e = 0.0, amin = INFINITY;
         T c1 = T(0), c2 = T(0), b[3] = {T(0), T(0), T(0)};
@@ -1122,7 +1133,8 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     const int sms = sm_count(c.device);
     const int blocks = sms * c.tune_samples_bpsm;
     GMCP_CUDA_TRY(c.tri_frame.ensure(8 * (size_t)c.ns + 8));
-    if (MODE != MODE_EVAL) {
+    constexpr bool kMaster = MODE == MODE_MASTER || MODE == MODE_MASTER_HESS;
+    if (MODE != MODE_EVAL && !kMaster) {
         k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
                                                    nullptr, nullptr);
         GMCP_CUDA_TRY(cudaGetLastError());
@@ -1143,8 +1155,13 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     GMCP_CUDA_TRY(c.item_list.ensure((size_t)c.cap_items));
     int32_t* n_items = c.misc_i32.p + 16;
     GMCP_CUDA_TRY(cudaMemsetAsync(n_items, 0, sizeof(int32_t), c.stream));
+    if (kMaster) {
+        // outside a contact pass: fresh item lists, and no pass stamps
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + kSlotItemList, 0, sizeof(int32_t), c.stream));
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + kSlotItemList2, 0, sizeof(int32_t), c.stream));
+    }
     k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, c.tri_items.p, n_items,
-                                               c.tri_stamp.p, c.misc_i32.p);
+                                               kMaster ? nullptr : c.tri_stamp.p, c.misc_i32.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items};
     k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
@@ -1154,6 +1171,18 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     k_items_pre<NK, T><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, c.tri_frame.p,
                                                        c.tri_items.p, B, c.item_list.p, n_list, n_list2, counters);
     GMCP_CUDA_TRY(cudaGetLastError());
+    if (kMaster) {
+        k_items<NK, T, MODE><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
+                                                             c.tri_items.p, B, c.item_list.p, n_list, n_list2,
+                                                             counters, LG);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        // oversized item sets: the warp-per-triangle kernel instead
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
+        k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
+            c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG,
+            c.tri_frame.p, n_items, c.cap_items);
+        return cudaGetLastError();
+    }
     {
         ProfScope pi(c.prof, c.stream, "items");
         // 64-thread blocks, at most 168 registers a thread: 12 warps fit an
