@@ -316,6 +316,14 @@ ipc_status ipc_autotune(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev
 /* Set the launch shapes directly (blocks per SM, each in [1, 64]). */
 ipc_status ipc_set_launch_shape(ipc_ctx* ctx, int32_t samples_bpsm, int32_t query_bpsm);
 
+/* Capacity of the sample-item buffer of the item-parallel evaluation (items
+ * = face candidates x samples + 2 x edge candidates + point candidates).  A
+ * set of items larger than the capacity is evaluated by the warp-per-
+ * triangle kernel instead, with the same results; ipc_contact_pass then
+ * grows the buffer for its next calls.  capacity in [1, 2^31 - 1]; the
+ * buffers themselves only grow.  Invalidates the captured pass graph. */
+ipc_status ipc_set_item_capacity(ipc_ctx* ctx, int64_t capacity);
+
 /* The contact pass reads the pad positions and displacements of the slave
  * (tactile) surface vertices only.  ipc_slave_vertices writes their ids
  * (ascending; ids_host int32 [n], may be NULL) and *n_host their count.

@@ -125,6 +125,8 @@ def lib():
                                    C.POINTER(SampleCounts)]
     L.ipc_master_grad.restype = C.c_int
     L.ipc_master_grad.argtypes = [P, P, P, P]
+    L.ipc_set_item_capacity.restype = C.c_int
+    L.ipc_set_item_capacity.argtypes = [P, C.c_int64]
     L.ipc_master_hess.restype = C.c_int
     L.ipc_master_hess.argtypes = [P, P, P, C.c_int64, P, P, C.POINTER(C.c_int64)]
     L.ipc_ccd_max_step.restype = C.c_int
@@ -375,6 +377,11 @@ class Context:
         ts = "<f4" if bv.dtype == 1 else "<f8"
         vals = t.as_tensor(_CudaArray(bv.vals_dev, (bv.nnzb, 3, 3), ts), device=self.device).clone()
         return rp, ci, vals
+
+    def set_item_capacity(self, capacity: int):
+        """Item-buffer capacity (ipc_set_item_capacity): smaller item sets take
+        the item-parallel kernels, larger ones the warp-per-triangle kernel."""
+        self._check(lib().ipc_set_item_capacity(self.h, int(capacity)))
 
     def master_grad(self, x, xm, out=None):
         """dPsi/dx_m over the master vertices, [n_mvert, 3] FP64 (ipc_master_grad)."""

@@ -1338,6 +1338,16 @@ ipc_status ipc_set_launch_shape(ipc_ctx* ctx, int32_t samples_bpsm, int32_t quer
     return IPC_OK;
 }
 
+ipc_status ipc_set_item_capacity(ipc_ctx* ctx, int64_t capacity) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (capacity < 1 || capacity > ((int64_t)1 << 31) - 1)
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_set_item_capacity: capacity must be in [1, 2^31 - 1]");
+    c.cap_items = capacity;
+    c.cp_graph.reset();
+    return IPC_OK;
+}
+
 ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* names_host,
                        double* ms_host, int64_t* calls_host, int32_t* n_sections) {
     if (!ctx) return IPC_ERR_ARG;

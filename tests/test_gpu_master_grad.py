@@ -153,3 +153,37 @@ def test_master_hess_capacity_and_empty(B):
     assert ij3.shape[0] == 0
     ctx.close()
     ctx3.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_warp_per_triangle_path_gives_the_same_results(B, oracle_mod, prec):
+    """An item buffer too small for the items sends the evaluation and both
+    master modes to the warp-per-triangle kernel: the same results as the
+    item-parallel kernels, and the oracle's."""
+    sc, x = small_indent(n_quads=10, subdiv=3, press=0.12e-3, L=2)
+    O = oracle_mod.Scene(sc)
+    a = B.Context(sc, precision=prec)
+    b = B.Context(sc, precision=prec)
+    b.set_item_capacity(1)
+    ra = a.barrier_eval(x, sc.Y0, hess=False)
+    rb = b.barrier_eval(x, sc.Y0, hess=False)
+    assert all(rb["counts"][k] == ra["counts"][k] for k in ("face", "edge", "point"))
+    ga, gb = ra["grad"].cpu().numpy(), rb["grad"].cpu().numpy()
+    if prec == "fp64":
+        np.testing.assert_array_equal(gb, ga)     # same sums in the same order
+    else:
+        np.testing.assert_allclose(gb, ga, rtol=0, atol=1e-6 * np.abs(ga).max())
+    o = O.master_grad(x, sc.Y0)
+    for ctx in (a, b):
+        np.testing.assert_allclose(ctx.master_grad(x, sc.Y0).cpu().numpy(), o, rtol=0,
+                                   atol=1e-11 * np.abs(o).max())
+    H = O.master_hess(x, sc.Y0)
+    G = _sum_blocks(*b.master_hess(x, sc.Y0))
+    assert set(G) == set(H)
+    scale = max(np.abs(v).max() for v in H.values())
+    for k, v in H.items():
+        np.testing.assert_allclose(G[k], v, rtol=0, atol=1e-11 * scale)
+    with pytest.raises(B.GmcpError):
+        b.set_item_capacity(0)
+    a.close()
+    b.close()
