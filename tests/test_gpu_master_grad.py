@@ -187,3 +187,27 @@ def test_warp_per_triangle_path_gives_the_same_results(B, oracle_mod, prec):
         b.set_item_capacity(0)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_master_rows_with_a_deformed_master(B, oracle_mod, prec):
+    """The master away from its rest shape (rest gaps and eps from Y0, the
+    geometry from the current master): rows and blocks as the oracle's."""
+    sc, x = small_indent(n_quads=10, subdiv=3, press=0.10e-3, L=1)
+    rng = np.random.default_rng(5)
+    Y = sc.Y0
+    c = Y.mean(axis=0)
+    xm = c + (Y - c) * np.array([1.01, 0.99, 1.0]) + rng.normal(scale=2e-6, size=Y.shape)
+    xm[:, 2] += 0.02e-3
+    O = oracle_mod.Scene(sc)
+    o = O.master_grad(x, xm)
+    assert np.abs(o).max() > 0
+    ctx = B.Context(sc, precision=prec)
+    np.testing.assert_allclose(ctx.master_grad(x, xm).cpu().numpy(), o, rtol=0, atol=1e-11 * np.abs(o).max())
+    H = O.master_hess(x, xm)
+    G = _sum_blocks(*ctx.master_hess(x, xm))
+    assert set(G) == set(H)
+    scale = max(np.abs(v).max() for v in H.values())
+    for k, v in H.items():
+        np.testing.assert_allclose(G[k], v, rtol=0, atol=1e-11 * scale)
+    ctx.close()
