@@ -146,6 +146,13 @@ def test_master_hess_capacity_and_empty(B):
     st = Bm.lib().ipc_master_hess(ctx.h, Bm._ptr(xs), Bm._ptr(xm), 2, Bm._ptr(ij2), Bm._ptr(blk2), ctypes.byref(cnt))
     assert st == 5 and cnt.value == n
     assert (ij2[2:].cpu().numpy() == -7).all()
+    # argument errors are statuses, not faults
+    st = Bm.lib().ipc_master_hess(ctx.h, Bm._ptr(xs), Bm._ptr(xm), -1, Bm._ptr(ij2), Bm._ptr(blk2), ctypes.byref(cnt))
+    assert st == 1
+    st = Bm.lib().ipc_master_hess(ctx.h, Bm._ptr(xs), None, 4, Bm._ptr(ij2), Bm._ptr(blk2), ctypes.byref(cnt))
+    assert st == 1
+    st = Bm.lib().ipc_master_grad(ctx.h, Bm._ptr(xs), Bm._ptr(xm), None)
+    assert st == 1
     # no contact: no blocks
     sc3, x3, xm3 = flat_over_big_triangle(nq=2, gap=2e-4)
     ctx3 = B.Context(sc3, precision="fp64")
