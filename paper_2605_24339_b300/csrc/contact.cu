@@ -42,9 +42,11 @@ constexpr int MODE_LAGGED = 2;
 constexpr int MODE_MASTER = 3;   // gradient rows of the master vertices
 constexpr int MODE_MASTER_HESS = 4;   // slave-master and master-master Hessian blocks
 
-// frozen-linear energies of MODE_LAGGED: per active sample, kappa w gamma
-// B(g + a_j dg) for up to 8 step sizes a_j along the direction dx
-struct LagArgs {
+// outputs of the modes beyond the evaluation.  MODE_LAGGED: the frozen-
+// linear energies, per active sample kappa w gamma B(g + a_j dg) for up to 8
+// step sizes a_j along the direction dx.  MODE_MASTER / MODE_MASTER_HESS:
+// the master rows and blocks.
+struct ModeArgs {
     const double* alphas = nullptr;
     int na = 0;
     double* triE8 = nullptr;   // [8][ns]
@@ -641,7 +643,7 @@ __device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, 
 // Warp per active triangle (persistent grid).  Used for the step bound and
 // the lagged energies of the line search, and for the contact evaluation
 // when the item buffer is too small (then run_if_over selects it).
-__device__ void put_block(const LagArgs& LG, int32_t r, int32_t c, double coef, const V3<double>& n) {
+__device__ void put_block(const ModeArgs& LG, int32_t r, int32_t c, double coef, const V3<double>& n) {
     const unsigned long long at = atomicAdd(LG.h_count, 1ull);
     if ((int64_t)at >= LG.h_cap) return;
     LG.h_ij[2 * at] = r; LG.h_ij[2 * at + 1] = c;
@@ -654,7 +656,7 @@ __device__ void put_block(const LagArgs& LG, int32_t r, int32_t c, double coef, 
 // g = n_s . (x_m - x_s) with x_m = sum_j bm_j y_j: the row of master vertex
 // y_j is kappa w gamma B'(g) bm_j n_s, the counterpart of the slave rows
 // -kappa w gamma B'(g) beta_i n_s
-__device__ void master_rows(const LagArgs& LG, const ItemOut& o, const V3<double>& ns) {
+__device__ void master_rows(const ModeArgs& LG, const ItemOut& o, const V3<double>& ns) {
     double Bv, dB, d2B;
     barrier(o.g, o.eps, Bv, dB, d2B);
     const double c1 = o.kq * o.w * o.gamma * dB;
@@ -669,7 +671,7 @@ __device__ void master_rows(const LagArgs& LG, const ItemOut& o, const V3<double
 // the sample's gap gradient is (-beta_a n_s) on its slave vertices Ts[a] and
 // (bm_j n_s) on its master vertices; its Gauss-Newton block between two of
 // them is max(kappa w gamma B''(g), 0) w_u w_v n_s n_s^T
-__device__ void master_blocks(const LagArgs& LG, const ItemOut& o, const int32_t* Ts, const V3<double>& ns) {
+__device__ void master_blocks(const ModeArgs& LG, const ItemOut& o, const int32_t* Ts, const V3<double>& ns) {
     double Bv, dB, d2B;
     barrier(o.g, o.eps, Bv, dB, d2B);
     const double c2 = rmax(o.kq * o.w * o.gamma * d2B, 0.0);
@@ -688,7 +690,7 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
           const double* __restrict__ xm, double* __restrict__ triE, T* __restrict__ triG,
           T* __restrict__ triS, T* __restrict__ triN, long long* counters,
           const double* __restrict__ dx, const double* __restrict__ dxm,
-          unsigned long long* alpha_bits, LagArgs LG, const double* __restrict__ frame,
+          unsigned long long* alpha_bits, ModeArgs LG, const double* __restrict__ frame,
           const int32_t* __restrict__ run_if_over, int64_t item_cap) {
     if (run_if_over && (int64_t)*run_if_over <= item_cap) return;
     const int lane = threadIdx.x & 31;
@@ -913,7 +915,7 @@ k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const d
         const double* __restrict__ dx, const double* __restrict__ dxm, const double* __restrict__ frame,
         const int32_t* __restrict__ items, ItemBufs B, const int32_t* __restrict__ list,
         const int32_t* __restrict__ n_list, const int32_t* __restrict__ n_list2, long long* counters,
-        LagArgs LG = LagArgs()) {
+        ModeArgs LG = ModeArgs()) {
     if ((int64_t)*B.n > B.cap) return;
     const int nf = *n_list;
     const int n = nf + *n_list2;
@@ -1128,7 +1130,7 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t n, doubl
 template <int NK, class T, int MODE>
 cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* Sm, T* N,
                            long long* counters, const double* dx, const double* dxm,
-                           unsigned long long* alpha_bits, LagArgs LG = LagArgs()) {
+                           unsigned long long* alpha_bits, ModeArgs LG = ModeArgs()) {
     const int threads = 256;
     const int sms = sm_count(c.device);
     const int blocks = sms * c.tune_samples_bpsm;
@@ -1336,7 +1338,7 @@ cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const d
 cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m) {
     ProfScope ps(c.prof, c.stream, "master_grad");
     GMCP_CUDA_TRY(cudaMemsetAsync(grad_m, 0, sizeof(double) * 3 * (size_t)c.nmv, c.stream));
-    LagArgs LG;
+    ModeArgs LG;
     LG.grad_m = grad_m;
     if (c.P.nk == 4)
         return launch_samples<4, double, MODE_MASTER>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -1349,7 +1351,7 @@ cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32
                                 int64_t cap, unsigned long long* count) {
     ProfScope ps(c.prof, c.stream, "master_hess");
     GMCP_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), c.stream));
-    LagArgs LG;
+    ModeArgs LG;
     LG.h_ij = ij; LG.h_blk = blk; LG.h_count = count; LG.h_cap = cap; LG.m_off = (int32_t)c.nv;
     if (c.P.nk == 4)
         return launch_samples<4, double, MODE_MASTER_HESS>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
@@ -1363,7 +1365,7 @@ cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const doub
     ProfScope ps(c.prof, c.stream, "lagged");
     if (na < 1 || na > 8) return cudaErrorInvalidValue;
     GMCP_CUDA_TRY(cudaMemsetAsync(triE8, 0, sizeof(double) * (size_t)na * (size_t)c.ns, c.stream));
-    LagArgs LG;
+    ModeArgs LG;
     LG.alphas = alphas_dev; LG.na = na; LG.triE8 = triE8; LG.ns = c.ns;
     if (c.P.nk == 4)
         GMCP_CUDA_TRY((launch_samples<4, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, LG)));
