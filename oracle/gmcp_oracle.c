@@ -35,8 +35,13 @@
  *                              (bary_interp); nearest triangle by brute force
  *   warm-start MLP .......... not in the paper (a plain 4-layer perceptron)
  *
- * Parity pins live in tests/test_oracle_*.py.  Parts with no pin other than
- * self-consistency are marked "parity unpinned" below: none at present.
+ * Parity pins live in tests/test_oracle_*.py.  The sample weights, the
+ * smoothing factors gamma of faces and edges, the edge Gauss points and the
+ * support radius of each sample kind are pinned by hand-worked closed forms
+ * (tests/test_oracle_closed_forms.py, derivations in tests/golden/); the
+ * derivatives by finite differences; candidates by brute force; CCD by
+ * analytic times of impact.  Parts with no pin other than self-consistency
+ * would be marked "parity unpinned" below: none at present.
  */
 #include <math.h>
 #include <stdint.h>

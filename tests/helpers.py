@@ -74,3 +74,70 @@ def load_golden(name):
                 continue
             rows.append([float(v) for v in line.split()])
     return np.array(rows)
+
+
+MM = 1e-3
+
+
+def one_slave_triangle(Y, F, gap_rest=1e-3, kappa=1e5, kappa_edge=1e2, kappa_point=1e-1,
+                       dhat=1e-4, L=1):
+    """One tet whose bottom face is the only slave triangle: S0=(0,0,0),
+    S1=(0,1,0), S2=(1,0,0) mm, normal -z; a point (x, y) of it has
+    beta^s = (1-x-y, y, x).  ``Y`` [n,3] (metres) is the current master, ``F``
+    its outward triangles; at rest (Y0) the master sits ``gap_rest`` lower,
+    so that 0.9 g_ref > dhat and every sample takes eps = dhat (Eq.
+    adaptive_eps).  Returns (scene, x, xm)."""
+    X = np.array([[0, 0, 0], [0, 1, 0], [1, 0, 0], [0, 0, 1]], dtype=np.float64) * MM
+    tets = np.array([[0, 2, 1, 3]], dtype=np.int32)
+    stris = np.array([[0, 1, 2]], dtype=np.int32)
+    Y = np.asarray(Y, dtype=np.float64)
+    Y0 = Y.copy()
+    Y0[:, 2] -= gap_rest
+    p = S.default_params(dhat=dhat, kappa=kappa, kappa_edge=kappa_edge, kappa_point=kappa_point,
+                         face_rule_level=L)
+    p = S._finish_params(p, X, stris)
+    dirichlet = np.array([0, 0, 0, 1], dtype=np.uint8)
+    sc = S._single_env(X, tets, stris, dirichlet, Y0, np.asarray(F, dtype=np.int32),
+                       np.zeros_like(X), p, "one_slave_triangle", 1)
+    return sc, X.copy(), Y
+
+
+def outward_up(Y, F):
+    """Orient each triangle of F so that its normal has a positive z part."""
+    F = np.array(F, dtype=np.int32)
+    for t in F:
+        n = np.cross(Y[t[1]] - Y[t[0]], Y[t[2]] - Y[t[0]])
+        if n[2] < 0:
+            t[1], t[2] = t[2], t[1]
+    return F
+
+
+def spike_master(apex_xy, gap, radius=1.0, depth=10.0):
+    """An upward spike: apex at (apex_xy, -gap), three base vertices
+    ``radius`` mm away horizontally and ``depth`` mm lower; three faces."""
+    ax, ay = apex_xy
+    Y = [[ax * MM, ay * MM, -gap]]
+    for th in (90.0, 210.0, 330.0):
+        r = np.deg2rad(th)
+        Y.append([(ax + radius * np.cos(r)) * MM, (ay + radius * np.sin(r)) * MM,
+                  -gap - depth * MM])
+    Y = np.array(Y)
+    return Y, outward_up(Y, [[0, 1, 2], [0, 2, 3], [0, 3, 1]])
+
+
+def edge_master(gap_a, gap_b):
+    """One master triangle whose edge A-B runs along y = 0.25 mm from
+    x = -0.01 mm to x = 9.99 mm (A at depth gap_a, B at gap_b); its third
+    vertex C = (-0.01, 1.25) mm lies 10 mm below A, so the face rises steeply
+    away from A-B and the edges A-C and B-C miss the slave triangle."""
+    Y = np.array([[-0.01 * MM, 0.25 * MM, -gap_a], [9.99 * MM, 0.25 * MM, -gap_b],
+                  [-0.01 * MM, 1.25 * MM, -gap_a - 10.0 * MM]])
+    return Y, outward_up(Y, [[0, 1, 2]])
+
+
+def face_master(gap):
+    """One master triangle parallel to the slave at depth gap:
+    M0=(0.18,-1), M1=(2.5,-1), M2=(0.18,2.5) mm."""
+    Y = np.array([[0.18, -1.0, 0.0], [2.5, -1.0, 0.0], [0.18, 2.5, 0.0]]) * MM
+    Y[:, 2] = -gap
+    return Y, outward_up(Y, [[0, 1, 2]])
