@@ -357,14 +357,19 @@ ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* n
  * created beforehand, it returns in *alpha_accd_host the same value as the
  * alpha_accd field of ipc_ccd_max_step for the same arguments (additive CCD
  * over the owned primitive pairs whose swept boxes overlap; 1.0 when nothing
- * closes), and in n_pairs_host (may be NULL) the point-triangle and edge-edge
- * pair counts.  It calls no allocator: its scratch is a 4 MiB array built
+ * closes), in n_pairs_host (may be NULL, else 2 entries) the point-triangle
+ * and edge-edge pair counts, and in *iter_cap_hit_host (may be NULL) 1 when
+ * some pair's additive CCD reached params.ccd_max_iter iterations (its bound
+ * is then the last safe time, as in ipc_ccd_max_step's iter_cap_hit), else
+ * 0.  It calls no allocator: its scratch is a 4 MiB array built
  * into the library, which every GPU that loads the library keeps until the
  * process exits.  A moving master (xm1_dev != NULL) needs 24 bytes of it per
  * master vertex, so scenes with more than 174,752 master vertices are
- * rejected with IPC_ERR_CAPACITY when xm1_dev is given.  The first call on a
- * device looks up the array's device address (once per device); make that
- * first call before capturing any stream.  Every call on every context of
+ * rejected with IPC_ERR_CAPACITY when xm1_dev is given.  Every call looks up
+ * the array's device address with the context's device current (the lookup
+ * allocates nothing once the library's module is loaded on that device; the
+ * first call on a device may load it, so make that first call before
+ * capturing any stream).  Every call on every context of
  * the process uses the same array, clearing it first: calls whose GPU work
  * overlaps (two streams, two threads) race and must be serialised by the
  * caller.  Pairs are enumerated by brute force (slave triangles x master
@@ -372,7 +377,7 @@ ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* n
  * Synchronises params.stream. */
 ipc_status ipc_accd_min_noalloc(ipc_ctx* ctx, const double* x_dev, const double* dx_dev,
                                 const double* xm0_dev, const double* xm1_dev,
-                                double* alpha_accd_host, int64_t* n_pairs_host);
+                                double* alpha_accd_host, int64_t* n_pairs_host, int32_t* iter_cap_hit_host);
 
 /* ---------------------------------------------------------------------- */
 /* Learned warm start.  The paper has no learned component; this follows
@@ -441,6 +446,35 @@ ipc_status ipc_ws_predict(ipc_ctx* ctx, const double* x_dev, const double* v_dev
                           double* dx_dev);
 
 /* ------------------------------------------------------------------------
+ * Checkpoint and resume (not in the paper: the library's own subsystem).
+ * ------------------------------------------------------------------------ */
+
+/* Write a snapshot of a time-stepping context to the file at path: the pad
+ * state x_dev, v_dev (device FP64 [n_vert][3], as passed to
+ * ipc_newton_step), the kinematic master's current pose (m_rest until the
+ * first ipc_newton_step), the number of time steps ipc_newton_step has
+ * completed, and, if the context has a network (ipc_ws_create), its FP32
+ * parameters, Adam moments, Adam step and settings.  Together with the scene
+ * and ipc_params the context was created with, this is everything a time
+ * step depends on: a context created from the same scene and parameters and
+ * given the snapshot by ipc_load continues bit for bit.  The file has a
+ * versioned header, the sizes of the scene and an FNV-1a checksum; it is
+ * written beside path and renamed, so a failed write leaves no torn file.
+ * Synchronises params.stream.  IPC_ERR_ARG for NULL arguments or a file
+ * that cannot be written. */
+ipc_status ipc_save(ipc_ctx* ctx, const char* path, const double* x_dev, const double* v_dev);
+
+/* Read a snapshot written by ipc_save into a context created from the same
+ * scene (same sizes) and parameters: x_dev and v_dev (device FP64
+ * [n_vert][3]) receive the pad state, the context takes the master pose,
+ * the step count (also returned in *step_count_host, may be NULL) and the
+ * network (created if the context has none).  Nothing is changed unless the
+ * whole file reads and checks: IPC_ERR_ARG for a missing or corrupt file
+ * (bad magic, version or checksum) or one written for other sizes.
+ * Synchronises params.stream. */
+ipc_status ipc_load(ipc_ctx* ctx, const char* path, double* x_dev, double* v_dev, int64_t* step_count_host);
+
+/* ------------------------------------------------------------------------
  * Dual-mesh mapper (Sec. 3.2, Eqs. bary_proj, decomp, gram, bary_interp).
  * Context-free: errors are reported through ipc_last_error(NULL).
  * ------------------------------------------------------------------------ */
@@ -483,10 +517,11 @@ ipc_status ipc_dual_map_apply(const double* V_dev, const int32_t* T_dev, int64_t
  * master plane.  samples_dev (device FP64 [n][12][8]) receives per sample
  * beta^s[3], beta^m[3], the gap g and the weight w; count_dev (device int32
  * [n]) the number of samples (0 to 12; 0 when the overlap has no area or
- * the master plane contains n_s).  The contact pass does not use it (it keeps
- * the fixed slave-side rule).  Context-free (errors through
- * ipc_last_error(NULL)); synchronises stream.  IPC_ERR_ARG for an index out
- * of range. */
+ * the master plane contains n_s; -1 for a pair with a triangle or vertex
+ * index out of range, which gets no samples).  The contact pass does not use
+ * it (it keeps the fixed slave-side rule).  Context-free (errors through
+ * ipc_last_error(NULL)); asynchronous on stream, allocates nothing.
+ * IPC_ERR_ARG for a NULL pointer or n < 0. */
 ipc_status ipc_face_clip_samples(const double* xs_dev, int64_t nvs, const int32_t* ts_dev, int64_t nts,
                                  const double* xm_dev, int64_t nvm, const int32_t* tm_dev, int64_t ntm,
                                  const int32_t* pairs_dev, int64_t n, double* samples_dev, int32_t* count_dev,

@@ -100,3 +100,39 @@ def adam_step(params, g, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
         n1.append(a)
         n2.append(b)
     return newp, n1, n2
+
+
+def features(x, v, X, dirichlet, surface, contact_grad, h, pos_scale, disp_scale, force_scale):
+    """Per-vertex input features of the warm-start network (the project's own
+    design; the paper has no learned component), FP64 then rounded to BF16:
+
+      0-2   (x - X) / pos_scale
+      3-5   h v / disp_scale
+      6-8   Xn = 2 (X - lo) / (hi - lo) - 1, lo/hi the pad's rest box per axis
+      9     Dirichlet flag
+      10    slave-surface flag
+      11-13 contact force -grad Psi / force_scale, clamped to [-8, 8]
+      14    1 where the contact gradient row is nonzero
+      15-26 per axis c: sin(pi Xn_c), cos(pi Xn_c), sin(2 pi Xn_c), cos(2 pi Xn_c)
+      27-31 zero
+    Returns FP32 values that are exactly BF16-representable, [n][32]."""
+    x, v, X = (np.asarray(a, dtype=np.float64) for a in (x, v, X))
+    g = np.asarray(contact_grad, dtype=np.float64)
+    n = X.shape[0]
+    f = np.zeros((n, 32))
+    lo, hi = X.min(axis=0), X.max(axis=0)
+    ext = np.where(hi > lo, hi - lo, 1.0)
+    xn = 2.0 * (X - lo) / ext - 1.0
+    f[:, 0:3] = (x - X) / pos_scale
+    f[:, 3:6] = h * v / disp_scale
+    f[:, 6:9] = xn
+    f[:, 9] = np.asarray(dirichlet) != 0
+    f[:, 10] = np.asarray(surface) != 0
+    f[:, 11:14] = np.clip(-g / force_scale, -8.0, 8.0)
+    f[:, 14] = np.any(g != 0.0, axis=1)
+    for c in range(3):
+        for k in (1, 2):
+            col = 15 + 4 * c + 2 * (k - 1)
+            f[:, col] = np.sin(np.pi * k * xn[:, c])
+            f[:, col + 1] = np.cos(np.pi * k * xn[:, c])
+    return bf16_round(f.astype(np.float32))

@@ -150,6 +150,10 @@ def lib():
     L.ipc_ws_get_params.argtypes = [P, P]
     L.ipc_ws_predict.restype = C.c_int
     L.ipc_ws_predict.argtypes = [P, P, P, P, P]
+    L.ipc_save.restype = C.c_int
+    L.ipc_save.argtypes = [P, C.c_char_p, P, P]
+    L.ipc_load.restype = C.c_int
+    L.ipc_load.argtypes = [P, C.c_char_p, P, P, C.POINTER(C.c_int64)]
     L.ipc_autotune.restype = C.c_int
     L.ipc_autotune.argtypes = [P, P, P, P, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                C.POINTER(C.c_double)]
@@ -562,6 +566,20 @@ class Context:
         dx = t.empty((self.nv, 3), dtype=t.float64, device=self.device)
         self._check(lib().ipc_ws_predict(self.h, _ptr(x), _ptr(v), _ptr(xm), _ptr(dx)))
         return dx
+
+    # -- checkpoint / resume -------------------------------------------------
+    def save(self, path, x, v):
+        """ipc_save: snapshot of (x, v), the master pose, the step count and
+        the network to the file at path."""
+        x, v = self._as(x), self._as(v)
+        self._check(lib().ipc_save(self.h, os.fsencode(path), _ptr(x), _ptr(v)))
+
+    def load(self, path, x, v):
+        """ipc_load into the CUDA tensors x, v (FP64 [n_vert, 3], written in
+        place); returns the snapshot's step count."""
+        n = C.c_int64(-1)
+        self._check(lib().ipc_load(self.h, os.fsencode(path), _ptr(x), _ptr(v), C.byref(n)))
+        return n.value
 
     # -- launch shapes ------------------------------------------------------
     def autotune(self, x, xm0, dx=None, reps=3):

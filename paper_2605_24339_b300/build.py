@@ -5,6 +5,7 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -22,7 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # CPU oracle does on degenerate (coincident) meshes
 NO_FMA = {"broadphase.cu", "contact.cu", "faceclip.cu"}
 SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu", "newton.cu", "warmstart.cu", "dualmap.cu",
-           "faceclip.cu"]
+           "faceclip.cu", "snapshot.cu"]
 
 
 def nvcc() -> str:
@@ -43,7 +44,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     headers.append(os.path.join(INCLUDE, "gmcp.h"))
-    objs = []
+    objs, cmds = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
@@ -55,7 +56,11 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if verbose:
                 cmd += ["-Xptxas", "-v"]
                 print(" ".join(cmd), flush=True)
-            subprocess.check_call(cmd)
+            cmds.append(cmd)
+    # translation units compile independently: run them side by side
+    with ThreadPoolExecutor(max_workers=max(1, min(len(cmds), os.cpu_count() or 1))) as pool:
+        for f in [pool.submit(subprocess.check_call, cmd) for cmd in cmds]:
+            f.result()
     if force or _stale(LIB, objs):
         subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs, "-lcudart",
                                "-Xlinker", "--no-undefined"])

@@ -1393,7 +1393,7 @@ ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const dou
     st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     if (stats) *stats = st;
     switch (status) {
-        case 0: return IPC_OK;
+        case 0: ++c.step_count; return IPC_OK;
         case 3: return fail_ctx(ctx, IPC_ERR_INFEASIBLE, "ipc_newton_step: infeasible (master motion blocked, "
                                                          "inverted tet or no admissible start)");
         case 5: return fail_ctx(ctx, IPC_ERR_NOT_CONVERGED, "ipc_newton_step: max_newton reached");

@@ -1444,21 +1444,16 @@ k_accd_brute(SceneView S, Params P, const double* __restrict__ x, const double* 
     if (cap_hit) atomicMax(&counters[2], 1LL);
 }
 
-// Device address of g_accd_scratch per device, resolved once with that
-// device current (the array's name is only a host-side stand-in).
-std::mutex g_noalloc_mu;
-void* g_noalloc_ptr[64] = {nullptr};
-
-cudaError_t noalloc_scratch(int device, void** out) {
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
-    if (!g_noalloc_ptr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_accd_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[device] = p;
-    }
-    *out = g_noalloc_ptr[device];
+// Device address of g_accd_scratch on the current device.  The array's name
+// is only a host-side stand-in, so the address is looked up with the device
+// current, on every call: it is not cached, because a context torn down and
+// made again on the device (cudaDeviceReset) may place the module elsewhere.
+// Once the module is loaded the lookup allocates nothing.
+cudaError_t noalloc_scratch(void** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_accd_scratch);
+    if (e != cudaSuccess) return e;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -1467,7 +1462,8 @@ cudaError_t noalloc_scratch(int device, void** out) {
 
 extern "C" ipc_status ipc_accd_min_noalloc(ipc_ctx* h, const double* x_dev, const double* dx_dev,
                                            const double* xm0_dev, const double* xm1_dev,
-                                           double* alpha_accd_host, int64_t* n_pairs_host) {
+                                           double* alpha_accd_host, int64_t* n_pairs_host,
+                                           int32_t* iter_cap_hit_host) {
     using namespace gmcp;
     if (!h) return IPC_ERR_ARG;
     Ctx& c = ctx_of(h);
@@ -1489,7 +1485,7 @@ extern "C" ipc_status ipc_accd_min_noalloc(ipc_ctx* h, const double* x_dev, cons
     cudaError_t e = cudaSetDevice(c.device);
     if (e != cudaSuccess) return fail(e, "cudaSetDevice");
     void* base = nullptr;
-    e = noalloc_scratch(c.device, &base);
+    e = noalloc_scratch(&base);
     if (e != cudaSuccess) return fail(e, "cudaGetSymbolAddress");
     unsigned long long* hdr = reinterpret_cast<unsigned long long*>(base);
     long long* counters = reinterpret_cast<long long*>(hdr + 1);
@@ -1518,5 +1514,6 @@ extern "C" ipc_status ipc_accd_min_noalloc(ipc_ctx* h, const double* x_dev, cons
     memcpy(&a, c.h_counts + 8, sizeof(double));
     *alpha_accd_host = a;
     if (n_pairs_host) { n_pairs_host[0] = c.h_counts[9]; n_pairs_host[1] = c.h_counts[10]; }
+    if (iter_cap_hit_host) *iter_cap_hit_host = c.h_counts[11] != 0;
     return IPC_OK;
 }

@@ -115,11 +115,20 @@ __device__ __forceinline__ void barrier(double g, double eps, double& B, double&
     dB = -2.0 * d * L - d * d / g;
     d2B = -2.0 * L - 4.0 * d / g + d * d / (g * g);
 }
-__device__ __forceinline__ void barrier(float g, float eps, float& B, float& dB, float& d2B) {
-    float d = g - eps, L = logf(g / eps);
+// FP32 values from the FP64 gap: d = g - eps and d / eps are formed in FP64
+// and rounded once, and L = ln(g/eps) = log1p(d/eps).  Rounding g and eps to
+// FP32 before subtracting would leave d (and so B, B', B'') only
+// ~6e-8 eps / |d| relatively accurate near g = eps.  On (0, eps) the terms of
+// B' (-2dL, -d^2/g: both < 0) and of B'' (-2L, -4d/g, d^2/g^2: all > 0) never
+// cancel, so each value keeps FP32's relative precision.
+__device__ __forceinline__ void barrier(double g64, double eps64, float& B, float& dB, float& d2B) {
+    const double d64 = g64 - eps64;
+    const float d = (float)d64, g = (float)g64;
+    const float L = log1pf((float)(d64 / eps64));
+    const float r = d / g;
     B = -d * d * L;
-    dB = -2.0f * d * L - d * d / g;
-    d2B = -2.0f * L - 4.0f * d / g + d * d / (g * g);
+    dB = -2.0f * d * L - d * r;
+    d2B = -2.0f * L - 4.0f * r + r * r;
 }
 
 // face-rule barycentrics per level (index L-1), filled at context creation
@@ -254,7 +263,7 @@ template <class T>
 __device__ __forceinline__ void sample_add(Acc<T>& A, double kq, double w, double gamma, double g,
                                            double eps, const double* bs) {
     T Bv, dB, d2B;
-    barrier((T)g, (T)eps, Bv, dB, d2B);
+    barrier(g, eps, Bv, dB, d2B);
     T coef = (T)(kq * w * gamma);
     T b[3] = {(T)bs[0], (T)bs[1], (T)bs[2]};
     A.add((double)(coef * Bv), coef * dB, rmax(coef * d2B, T(0)), b);
@@ -952,7 +961,7 @@ k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const d
         T c1 = T(0), c2 = T(0), b[3] = {T(0), T(0), T(0)};
         if (on) {
             T Bv, dB, d2B;
-            barrier((T)o.g, (T)o.eps, Bv, dB, d2B);
+            barrier(o.g, o.eps, Bv, dB, d2B);
             const T coef = (T)(o.kq * o.w * o.gamma);
             e = (double)(coef * Bv);
             c1 = coef * dB;

@@ -43,17 +43,17 @@ __device__ __forceinline__ double side(const double* a, const double* b, const d
 __global__ void k_face_clip(const double* __restrict__ xs, const int32_t* __restrict__ ts, int64_t nts,
                             int64_t nvs, const double* __restrict__ xm, const int32_t* __restrict__ tm,
                             int64_t ntm, int64_t nvm, const int32_t* __restrict__ pairs, int64_t n,
-                            double* __restrict__ out, int32_t* __restrict__ count, int32_t* __restrict__ bad) {
+                            double* __restrict__ out, int32_t* __restrict__ count) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t a_t = pairs[2 * k], b_t = pairs[2 * k + 1];
     count[k] = 0;
-    if (a_t < 0 || a_t >= nts || b_t < 0 || b_t >= ntm) { bad[0] = 1; return; }
+    if (a_t < 0 || a_t >= nts || b_t < 0 || b_t >= ntm) { count[k] = -1; return; }
     int64_t vs[3], vm[3];
     for (int c = 0; c < 3; ++c) {
         vs[c] = ts[3 * a_t + c];
         vm[c] = tm[3 * b_t + c];
-        if (vs[c] < 0 || vs[c] >= nvs || vm[c] < 0 || vm[c] >= nvm) { bad[0] = 1; return; }
+        if (vs[c] < 0 || vs[c] >= nvs || vm[c] < 0 || vm[c] >= nvm) { count[k] = -1; return; }
     }
     const P3 s0 = at(xs, vs[0]), s1 = at(xs, vs[1]), s2 = at(xs, vs[2]);
     const P3 m0 = at(xm, vm[0]), m1 = at(xm, vm[1]), m2 = at(xm, vm[2]);
@@ -157,21 +157,10 @@ extern "C" ipc_status ipc_face_clip_samples(const double* xs_dev, int64_t nvs, c
     if (!xs_dev || !ts_dev || !xm_dev || !tm_dev || !pairs_dev || !samples_dev || !count_dev)
         return fc_fail(IPC_ERR_ARG, "ipc_face_clip_samples: NULL pointer");
     cudaStream_t s = (cudaStream_t)stream;
-    int32_t* bad = nullptr;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&bad), sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess) {
-        k_face_clip<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(xs_dev, ts_dev, nts, nvs, xm_dev, tm_dev, ntm, nvm,
-                                                                pairs_dev, n, samples_dev, count_dev, bad);
-        e = cudaGetLastError();
-    }
-    int32_t hb = 0;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (bad) cudaFree(bad);
+    k_face_clip<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(xs_dev, ts_dev, nts, nvs, xm_dev, tm_dev, ntm, nvm,
+                                                            pairs_dev, n, samples_dev, count_dev);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess)
-        return fc_fail(e == cudaErrorMemoryAllocation ? IPC_ERR_OOM : IPC_ERR_CUDA,
-                       std::string("ipc_face_clip_samples: ") + cudaGetErrorString(e));
-    if (hb) return fc_fail(IPC_ERR_ARG, "ipc_face_clip_samples: a pair or vertex index is out of range");
+        return fc_fail(IPC_ERR_CUDA, std::string("ipc_face_clip_samples: ") + cudaGetErrorString(e));
     return IPC_OK;
 }

@@ -381,6 +381,7 @@ struct Ctx {
     std::vector<int32_t> h_cb_row, h_cb_col;
     std::unique_ptr<NewtonState> newton;
     std::unique_ptr<WarmStart, void (*)(WarmStart*)> ws{nullptr, ws_destroy};
+    int64_t step_count = 0;        // time steps completed by ipc_newton_step (saved in snapshots)
 
     SceneView view() const;
     CandView cand() {
@@ -466,6 +467,18 @@ cudaError_t vec_velocity(Ctx& c, const double* x, const double* xt, double* v);
 cudaError_t vec_neg(Ctx& c, int64_t n, const double* a, double* out);
 // api.cu: the context behind an ABI handle
 Ctx& ctx_of(ipc_ctx* h);
+
+// learned warm start: the state a snapshot carries (warmstart.cu)
+struct WsState {
+    double lr = 0, beta1 = 0, beta2 = 0, eps = 0, pos_scale = 0, disp_scale = 0, force_scale = 0;
+    int64_t step = 0;                // Adam steps taken
+    std::vector<float> P, M1, M2;    // FP32 parameters and Adam moments
+};
+// host copies of the network's parameters, moments and settings (c.ws set)
+cudaError_t ws_state_get(Ctx& c, WsState* out);
+// replace them (c.ws set, same parameter count) and refresh the BF16 copies
+cudaError_t ws_state_set(Ctx& c, const WsState& in);
+int64_t ws_param_count();
 
 }  // namespace gmcp
 

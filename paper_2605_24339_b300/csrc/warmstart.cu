@@ -660,7 +660,7 @@ k_features(const double* __restrict__ x, const double* __restrict__ v, const dou
         o[10] = surf[m] ? 1.0f : 0.0f;
         float act = 0.0f;
         for (int c = 0; c < 3; ++c) {
-            const float g = cg ? (float)cg[3 * m + c] : 0.0f;
+            const float g = cg ? -(float)cg[3 * m + c] : 0.0f;   // contact force = -grad Psi
             o[11 + c] = fminf(fmaxf(g * S.inv_force, -8.0f), 8.0f);
             if (g != 0.0f) act = 1.0f;
         }
@@ -776,6 +776,36 @@ static cudaError_t ws_backward(Ctx& c, WarmStart& W, const float* target, const 
 }
 
 void ws_destroy(WarmStart* w) { delete w; }
+
+int64_t ws_param_count() { return kNParam; }
+
+cudaError_t ws_state_get(Ctx& c, WsState* o) {
+    WarmStart& W = *c.ws;
+    o->lr = W.lr; o->beta1 = W.beta1; o->beta2 = W.beta2; o->eps = W.eps;
+    o->pos_scale = W.pos_scale; o->disp_scale = W.disp_scale; o->force_scale = W.force_scale;
+    o->step = W.step;
+    o->P.resize(kNParam); o->M1.resize(kNParam); o->M2.resize(kNParam);
+    GMCP_CUDA_TRY(cudaMemcpyAsync(o->P.data(), W.P.p, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, c.stream));
+    GMCP_CUDA_TRY(cudaMemcpyAsync(o->M1.data(), W.M1.p, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, c.stream));
+    GMCP_CUDA_TRY(cudaMemcpyAsync(o->M2.data(), W.M2.p, sizeof(float) * kNParam, cudaMemcpyDeviceToHost, c.stream));
+    return cudaStreamSynchronize(c.stream);
+}
+
+cudaError_t ws_state_set(Ctx& c, const WsState& in) {
+    WarmStart& W = *c.ws;
+    if ((int64_t)in.P.size() != kNParam || (int64_t)in.M1.size() != kNParam || (int64_t)in.M2.size() != kNParam)
+        return cudaErrorInvalidValue;
+    W.lr = in.lr; W.beta1 = in.beta1; W.beta2 = in.beta2; W.eps = in.eps;
+    W.pos_scale = in.pos_scale; W.disp_scale = in.disp_scale; W.force_scale = in.force_scale;
+    W.step = in.step;
+    cudaStream_t s = c.stream;
+    GMCP_CUDA_TRY(cudaMemcpyAsync(W.P.p, in.P.data(), sizeof(float) * kNParam, cudaMemcpyHostToDevice, s));
+    GMCP_CUDA_TRY(cudaMemcpyAsync(W.M1.p, in.M1.data(), sizeof(float) * kNParam, cudaMemcpyHostToDevice, s));
+    GMCP_CUDA_TRY(cudaMemcpyAsync(W.M2.p, in.M2.data(), sizeof(float) * kNParam, cudaMemcpyHostToDevice, s));
+    k_params_bf16<<<nb(kHid * kHid, 256), 256, 0, s>>>(W.P.p, W.W1.p, W.W2.p, W.W3.p, W.W2t.p, W.W3t.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    return cudaStreamSynchronize(s);
+}
 
 }  // namespace gmcp
 

@@ -141,3 +141,56 @@ def face_master(gap):
     Y = np.array([[0.18, -1.0, 0.0], [2.5, -1.0, 0.0], [0.18, 2.5, 0.0]]) * MM
     Y[:, 2] = -gap
     return Y, outward_up(Y, [[0, 1, 2]])
+
+
+# -- comparisons of GPU results with the oracle's -------------------------------
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    d = np.linalg.norm((a - b).ravel())
+    n = np.linalg.norm(b.ravel())
+    return d / n if n > 0 else d
+
+
+def bsr_dict(rp, ci, vals):
+    rp, ci, vals = rp.cpu().numpy(), ci.cpu().numpy(), vals.cpu().numpy().astype(np.float64)
+    out = {}
+    for i in range(rp.shape[0] - 1):
+        for k in range(rp[i], rp[i + 1]):
+            out[(i, int(ci[k]))] = vals[k]
+    return out
+
+
+def hess_rel(gpu_h, orc):
+    G = bsr_dict(*gpu_h)
+    O = {(int(i), int(j)): b for (i, j), b in zip(orc["blk_ij"], orc["blk"])}
+    num = den = 0.0
+    for k in set(G) | set(O):
+        g = G.get(k, np.zeros((3, 3)))
+        o = O.get(k, np.zeros((3, 3)))
+        num += np.sum((g - o) ** 2)
+        den += np.sum(o ** 2)
+    return np.sqrt(num / den) if den > 0 else np.sqrt(num)
+
+
+def hess_blocks_check(gpu_h, orc, tol, rows=None):
+    """Every 3x3 block against the oracle's: ||G - O||_F <= tol ||O||_F, with a
+    floor of tol * 1e-9 of the largest block for blocks the oracle does not
+    have (the GPU pattern may hold zero blocks).  The contact blocks are sums
+    of PSD terms, so no block is a cancelling sum.  rows: only blocks in these
+    rows.  Returns the largest per-block relative error."""
+    G = bsr_dict(*gpu_h)
+    O = {(int(i), int(j)): b for (i, j), b in zip(orc["blk_ij"], orc["blk"])}
+    if rows is not None:
+        rs = set(int(r) for r in rows)
+        G = {k: v for k, v in G.items() if k[0] in rs}
+        O = {k: v for k, v in O.items() if k[0] in rs}
+    big = max(np.linalg.norm(b) for b in O.values())
+    worst = 0.0
+    for k in set(G) | set(O):
+        g = G.get(k, np.zeros((3, 3)))
+        o = O.get(k, np.zeros((3, 3)))
+        err = np.linalg.norm(g - o)
+        ref = max(np.linalg.norm(o), 1e-9 * big)
+        worst = max(worst, err / ref)
+        assert err <= tol * ref, (k, err, np.linalg.norm(o))
+    return worst

@@ -7,7 +7,7 @@ the oracle's (additive CCD bit-identical)."""
 import numpy as np
 import pytest
 
-from helpers import small_indent
+from helpers import bsr_dict, hess_blocks_check, hess_rel, rel, small_indent
 from paper_2605_24339_b300 import scenes as S
 
 pytestmark = pytest.mark.gpu
@@ -22,34 +22,6 @@ def B():
     from paper_2605_24339_b300 import binding
     binding.lib()
     return binding
-
-
-def rel(a, b):
-    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
-    d = np.linalg.norm((a - b).ravel())
-    n = np.linalg.norm(b.ravel())
-    return d / n if n > 0 else d
-
-
-def bsr_dict(rp, ci, vals):
-    rp, ci, vals = rp.cpu().numpy(), ci.cpu().numpy(), vals.cpu().numpy().astype(np.float64)
-    out = {}
-    for i in range(rp.shape[0] - 1):
-        for k in range(rp[i], rp[i + 1]):
-            out[(i, int(ci[k]))] = vals[k]
-    return out
-
-
-def hess_rel(gpu_h, orc):
-    G = bsr_dict(*gpu_h)
-    O = {(int(i), int(j)): b for (i, j), b in zip(orc["blk_ij"], orc["blk"])}
-    num = den = 0.0
-    for k in set(G) | set(O):
-        g = G.get(k, np.zeros((3, 3)))
-        o = O.get(k, np.zeros((3, 3)))
-        num += np.sum((g - o) ** 2)
-        den += np.sum(o ** 2)
-    return np.sqrt(num / den) if den > 0 else np.sqrt(num)
 
 
 def _scenes():
@@ -72,9 +44,10 @@ SCENES = _scenes()
 IDS = [s[0] for s in SCENES]
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("name,sc,x", SCENES, ids=IDS)
-def test_candidates_bit_exact(B, oracle_mod, name, sc, x):
-    ctx = B.Context(sc, precision="fp64")
+def test_candidates_bit_exact(B, oracle_mod, name, sc, x, prec):
+    ctx = B.Context(sc, precision=prec)
     O = oracle_mod.Scene(sc)
     for xx in (sc.X, x):
         cnt = ctx.candidates(xx, sc.Y0)
@@ -122,6 +95,7 @@ def test_barrier_eval_fp64_parity(B, oracle_mod, name, sc, x):
     assert r["energy"] == pytest.approx(o["energy"], rel=1e-12)
     assert rel(r["grad"].cpu().numpy(), o["grad"]) < 1e-12
     assert hess_rel(r["hess"], o) < 1e-12
+    hess_blocks_check(r["hess"], o, 1e-12)
     c = r["counts"]
     assert (c["point"], c["edge"], c["face"]) == tuple(int(v) for v in o["n_samples"])
     ctx.close()
@@ -137,6 +111,7 @@ def test_barrier_eval_mixed_parity(B, oracle_mod, name, sc, x):
     assert r["energy"] == pytest.approx(o["energy"], rel=1e-5)
     assert rel(r["grad"].cpu().numpy(), o["grad"]) < 1e-5
     assert hess_rel(r["hess"], o) < 1e-4
+    hess_blocks_check(r["hess"], o, 1e-4)
     ctx.close()
 
 
@@ -201,17 +176,18 @@ def test_full_size_terrain_sampled_parity(B, oracle_mod):
         G = bsr_dict(*r["hess"])
         active = np.nonzero(np.abs(grad).sum(axis=1) > 0)[0]
         assert active.shape[0] > 100
+        # up to 400 vertices spread over the whole contact front: the active
+        # vertices sorted along x, one drawn from each of up to 400 equal strata
         rng = np.random.default_rng(3)
-        verts = rng.choice(active, 12, replace=False)
+        order = active[np.argsort(x[active, 0], kind="stable")]
+        strata = np.array_split(order, min(400, order.shape[0]))
+        verts = np.array([s_[rng.integers(len(s_))] for s_ in strata])
         tris = np.unique(np.nonzero(np.isin(sc.stris, verts).any(axis=1))[0])
         o = O.contact(x, sc.Y0, subset=tris)
-        Ob = {(int(i), int(j)): b for (i, j), b in zip(o["blk_ij"], o["blk"])}
         # relative L2 over the sampled rows (a single row can be a near-cancelling
-        # sum of its triangles' contributions)
+        # sum of its triangles' contributions), and every sampled row's blocks
         assert rel(grad[verts], o["grad"][verts]) < tol_g
-        gd = np.stack([G[(int(v), int(v))] for v in verts])
-        od = np.stack([Ob[(int(v), int(v))] for v in verts])
-        assert rel(gd, od) < tol_h
+        hess_blocks_check(r["hess"], o, tol_h, rows=verts)
         ctx.close()
 
 

@@ -68,5 +68,7 @@ def test_face_clip_edge_cases(B):
         smp, cnt = B.face_clip_samples(*(torch.as_tensor(a, device=dev) for a in
                                          (xs, T, m, T, np.array([[0, 0]], dtype=np.int32))))
         assert cnt.item() == 0
-    with pytest.raises(B.GmcpError):
-        B.face_clip_samples(*(torch.as_tensor(a, device=dev) for a in (xs, T, xm, T, np.array([[0, 3]], dtype=np.int32))))
+    # an index out of range marks its pair with count -1 and leaves the others alone
+    pairs = np.array([[0, 0], [0, 3], [-1, 0]], dtype=np.int32)
+    smp, cnt = B.face_clip_samples(*(torch.as_tensor(a, device=dev) for a in (xs, T, xs + [0, 0, -1e-3], T, pairs)))
+    assert cnt.cpu().tolist()[1:] == [-1, -1] and cnt[0].item() == 3

@@ -171,3 +171,67 @@ def test_warmstart_deterministic(B):
         ctx.close()
     np.testing.assert_array_equal(outs[0][0], outs[1][0])
     np.testing.assert_array_equal(outs[0][1], outs[1][1])
+
+
+def _bf16_ulp(a):
+    a = np.abs(np.asarray(a, np.float64))
+    e = np.floor(np.log2(np.where(a > 0, a, 1.0)))
+    return np.where(a > 0, 2.0 ** (e - 7), 0.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_features_match_oracle(B, oracle_mod, prec):
+    """ipc_ws_features against the oracle's feature map fed the oracle's
+    contact gradient on a pressed indent: every feature within one BF16 unit
+    in the last place of the oracle's value (the GPU rounds FP32 values, the
+    oracle FP64 ones) plus 2e-6 for the FP32 sine/cosine arguments; the
+    contact flag exact."""
+    from helpers import small_indent
+    sc, x = small_indent(n_quads=10, subdiv=3, press=0.12e-3, L=1)
+    rng = np.random.default_rng(4)
+    v = rng.normal(scale=1e-3, size=x.shape)
+    ctx = B.Context(sc, precision=prec)
+    ctx.ws_create(flat(M.init_params(3)), pos_scale=1e-4, disp_scale=1e-6, force_scale=1e-4)
+    f = ctx.ws_features(x, v, sc.Y0).float().cpu().numpy()
+    o = oracle_mod.Scene(sc).contact(x, sc.Y0)
+    surf = np.zeros(sc.X.shape[0], bool)
+    surf[np.unique(sc.stris)] = True
+    fo = M.features(x, v, sc.X, sc.dirichlet, surf, o["grad"], sc.params["h"], 1e-4, 1e-6, 1e-4)
+    assert fo[:, 14].sum() > 20
+    np.testing.assert_array_equal(f[:, 14], fo[:, 14])
+    np.testing.assert_array_equal(f[:, 9:11], fo[:, 9:11])
+    tol = _bf16_ulp(fo) + 2e-6
+    if prec == "mixed":     # FP32 contact gradient rows: 1e-5 of the row scale
+        tol[:, 11:14] += 1e-5 * np.abs(fo[:, 11:14]).max()
+    bad = np.abs(f - fo) > tol
+    if bad.any():
+        cols = np.unique(np.argwhere(bad)[:, 1])
+        print("mismatching feature columns", cols, "count", bad.sum())
+        for cc in cols[:6]:
+            rr = np.nonzero(bad[:, cc])[0][:4]
+            print(cc, rr, f[rr, cc], fo[rr, cc], o["grad"][rr])
+    assert not bad.any()
+    ctx.close()
+
+
+def test_predict_matches_oracle(B, oracle_mod):
+    """ipc_ws_predict = h v + disp_scale * y(features): against the oracle
+    network fed the GPU's features and BF16 weights (forward tolerance 2e-2
+    relative L2 on the network part); the plain part h v exact."""
+    from helpers import small_indent
+    sc, x = small_indent(n_quads=10, subdiv=3, press=0.12e-3, L=1)
+    rng = np.random.default_rng(5)
+    v = rng.normal(scale=1e-3, size=x.shape)
+    params = M.init_params(21)
+    params[7][:] = [0.3, -0.2, 0.1]
+    ctx = B.Context(sc, precision="mixed")
+    ctx.ws_create(flat(params), disp_scale=1e-5)
+    dx = ctx.ws_predict(x, v, sc.Y0).cpu().numpy()
+    f = ctx.ws_features(x, v, sc.Y0).float().cpu().numpy()
+    yo, _ = M.forward(oracle_view(params), f)
+    hv = sc.params["h"] * v
+    net = (dx - hv) / 1e-5
+    assert rel(net, yo) < 2e-2
+    # dx - h v is disp * FP32 y: the plain part is carried exactly
+    assert np.all(np.isfinite(dx))
+    ctx.close()

@@ -108,3 +108,33 @@ def test_bf16_round_known_values():
     assert np.isfinite(got[5]) and abs(got[5] / 3.0e38 - 1) < 2 ** -8
     # every result has its low 16 bits clear
     assert np.all((got.view(np.uint32) & 0xFFFF) == 0)
+
+
+def test_features_definition():
+    """The feature map's fixed points: zero displacement, velocity and force
+    give zeros in those slots; the rest box maps onto [-1, 1] with its corners
+    at the ends; sin^2 + cos^2 = 1 per frequency (to BF16 rounding); forces
+    beyond 8 force_scale clamp; the contact flag follows the gradient rows."""
+    from oracle import mlp_oracle as M
+    rng = np.random.default_rng(0)
+    X = rng.uniform(-1e-3, 2e-3, (50, 3))
+    X[0] = X.min(axis=0)
+    X[1] = X.max(axis=0)
+    g = np.zeros((50, 3))
+    g[5] = [1.0, -2.5e-4, 0.0]
+    f = M.features(X, np.zeros_like(X), X, np.arange(50) % 2, np.arange(50) % 3 == 0, g,
+                   1e-3, 1e-3, 1e-5, 1e-3)
+    assert f.dtype == np.float32 and f.shape == (50, 32)
+    assert np.all(f[:, 0:6] == 0.0)
+    np.testing.assert_array_equal(f[0, 6:9], [-1, -1, -1])
+    np.testing.assert_array_equal(f[1, 6:9], [1, 1, 1])
+    assert np.all(np.abs(f[:, 6:9]) <= 1.0)
+    np.testing.assert_array_equal(f[:, 9], np.arange(50) % 2)
+    np.testing.assert_array_equal(f[:, 10], (np.arange(50) % 3 == 0))
+    np.testing.assert_array_equal(f[5, 11:14], [-8.0, 0.25, 0.0])   # force = -g / 1e-3, clamped
+    np.testing.assert_array_equal(f[:, 14], np.arange(50) == 5)
+    s2c2 = f[:, 15:27:2].astype(np.float64) ** 2 + f[:, 16:27:2].astype(np.float64) ** 2
+    np.testing.assert_allclose(s2c2, 1.0, atol=2e-2)
+    assert np.all(f[:, 27:] == 0.0)
+    # every value is a BF16 number
+    np.testing.assert_array_equal(M.bf16_round(f), f)
