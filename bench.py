@@ -39,18 +39,7 @@ METRIC = "contact samples/s (barrier E+grad+H+CCD)"
 UNIT = "samples/s"
 WORKLOAD = "gel_on_terrain 256x256 pad (131,072 slave tris x 16 samples) vs 199,712-tri Perlin terrain, pressed 0.15 mm"
 CROP_HALF_WIDTH = 2.0e-3
-# Counters of one k_items launch on this workload (the FP64 phase of the
-# sample evaluation), from the ncu capture summarised in
-# profiles/k_items_gel_on_terrain.md: the FP64 thread instructions executed
-# (sm__sass_thread_inst_executed_op_fp64_pred_on: the work of the lanes that
-# have an item, not the issue slots of partly filled warps) and DRAM bytes
-# (read + write).  Null when the kernel changes and the capture is not yet
-# redone.
-K_ITEMS_FP64_LANE_INST = 3071471
-K_ITEMS_DRAM_BYTES = 917845
-# kernels one contact pass launches on this workload (ncu launch list,
-# profiles/launches_gel_on_terrain.md)
-KERNELS_PER_PASS = 28
+CLOCK_WINDOW_S = 1.5      # sustained run of the same step that the clock record also covers
 
 
 def load_peaks():
@@ -170,12 +159,85 @@ def samples_per_pass(ctx, x, xm, nk):
     return ctx.ns * nk + 2 * c["edge"] + c["point"], c
 
 
+def measure_alu_peaks(dev):
+    """FP32 and FP64 FMA rates of this GPU (ipc_alu_peak: chains of fused
+    multiply-adds on every SM, CUDA events), TFLOP/s; the best of three."""
+    from paper_2605_24339_b300 import binding
+    return {"fp32_tflops": max(binding.alu_peak(0, dev) for _ in range(3)),
+            "fp64_tflops": max(binding.alu_peak(1, dev) for _ in range(3)),
+            "how": "ipc_alu_peak: 16 independent FMA chains per thread, 8 blocks of 256 per SM, "
+                   "CUDA events, best of 3 (1 FMA = 2 flops)"}
+
+
+def pass_bytes(sc, ctx, nnzb):
+    """Algorithmic bytes of one contact pass, per unit of work (what the
+    method must move; each read or written once):
+      slave surface vertices: current and rest positions (FP64, 48 B) and the
+        step's displacement (FP64, 24 B); gradient row written (FP32, 12 B)
+      slave triangles: indices (12 B)
+      master vertices: current and rest positions (FP64, 48 B)
+      master triangles: indices (12 B)
+      surface Hessian blocks of the BSR written (FP32 3x3, 36 B)."""
+    n_sv = ctx.slave_vertices().shape[0]
+    parts = {"slave_verts": n_sv * (48 + 24 + 12), "slave_tris": sc.stris.shape[0] * 12,
+             "master_verts": sc.Y0.shape[0] * 48, "master_tris": sc.mtris.shape[0] * 12,
+             "bsr_blocks": int(nnzb) * 36}
+    return sum(parts.values()), parts
+
+
+def time_steps(step, stream, steps, flush):
+    """CUDA-event time of each step on the launching stream, L2 flushed
+    (a 256 MB write) before every step, outside the events."""
+    import torch
+    ms = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        flush.zero_()
+        ev0.record(stream)
+        info = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        ms.append(ev0.elapsed_time(ev1))
+    return ms, info
+
+
+def sustain(step, flush, seconds):
+    """The same step, flush included, repeated for about ``seconds`` (the
+    clock sampler's window beside the short timed region)."""
+    import torch
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        flush.zero_()
+        step()
+        n += 1
+        if n % 64 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+    return n
+
+
+def sections(ctx, step, flush, n):
+    """Per-section device times (ipc_profile: CUDA events around each group
+    of launches; the profiled passes run without the CUDA graph)."""
+    import torch
+    ctx.profile_start()
+    for _ in range(n):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_stop()
+    prof = ctx.profile_read()
+    return {k: v["ms"] / max(v["calls"], 1) for k, v in prof.items()}
+
+
 def run_ours(args):
     import torch
     from paper_2605_24339_b300 import binding
     rank, world, dist = dist_setup(args.gpus)
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
+    alu = measure_alu_peaks(dev)
     sc, x_np, dx_np = make_workload(seed=11 + rank)
     nk = 4 ** sc.params["face_rule_level"]
     stream = torch.cuda.current_stream()
@@ -187,7 +249,8 @@ def run_ours(args):
                        dtype=torch.float32 if args.precision == "mixed" else torch.float64)
     e_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
     units, cand = samples_per_pass(ctx, x, xm, nk)
-    counts_once = ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=True)["counts"]
+    first = ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=True)
+    counts_once, nnzb = first["counts"], first["hess"].nnzb
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def step():
@@ -199,33 +262,20 @@ def run_ours(args):
     for _ in range(args.warmup):
         info = step()
     torch.cuda.synchronize()
+    kernels_per_pass = ctx.pass_kernels()
     clocks = ClockSampler(dev)
     clocks.start()
     barrier(dist)
     torch.cuda.synchronize()
-    total_ms = 0.0
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
-        flush.zero_()
-        ev0.record(stream)
-        info = step()
-        ev1.record(stream)
-        ev1.synchronize()
-        total_ms += ev0.elapsed_time(ev1)
+    step_ms, info = time_steps(step, stream, args.steps, flush)
     torch.cuda.synchronize()
     barrier(dist)
+    n_sustain = sustain(step, flush, CLOCK_WINDOW_S)
     clk = clocks.stop()
-    # per-section device times (CUDA events around each group of launches;
-    # the profiler runs the pass without its CUDA graph), same flushing
-    n_prof = min(args.steps, 100)
-    ctx.profile_start()
-    for _ in range(n_prof):
-        flush.zero_()
-        step()
-    torch.cuda.synchronize()
-    ctx.profile_stop()
-    prof = ctx.profile_read()
-    total_ms = max_over_ranks(total_ms, dist)
+    clk["window"] = (f"the {args.steps} timed steps and {n_sustain} more of the same step "
+                     f"({CLOCK_WINDOW_S} s)")
+    sec_ms = sections(ctx, step, flush, min(max(args.steps, 20), 100))
+    total_ms = max_over_ranks(sum(step_ms), dist)
     ms_step = total_ms / args.steps
     value = job_throughput(units, args.steps, world, total_ms / 1e3)
 
@@ -261,22 +311,10 @@ def run_ours(args):
     if rank != 0:
         return
     peaks, peak_kind = load_peaks()
-    sec_ms = {k: v["ms"] / max(v["calls"], 1) for k, v in prof.items()}
-    # Dominant kernel: k_items (one thread per sample item), bound by the
-    # FP64 pipe: its exact FP64 sample geometry, counted per launch with ncu,
-    # over B300's FP64 rate of 2 lane instructions per SM per clock (1.25
-    # TFLOP/s of FMA at 2.03 GHz) at the SM clock sampled during the run.
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
-    fp64_peak = 148 * 2 * sm_mhz * 1e6 / 1e9
-    items_ms = sec_ms.get("items")
-    fp64_achieved = (K_ITEMS_FP64_LANE_INST / (items_ms / 1e3) / 1e9
-                     if K_ITEMS_FP64_LANE_INST and items_ms else None)
-    # a per-unit model beside it: 160 FP32 flops per evaluated
-    # (sample, candidate), against the FP32 CUDA-core rate
-    evals = counts_once["face_evaluated"] + 2 * cand["edge"] + cand["point"]
-    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    fp32_achieved = 160.0 * evals / (items_ms / 1e3) / 1e12 if items_ms else None
-    launches = KERNELS_PER_PASS * args.steps if KERNELS_PER_PASS else None
+    alg_b, alg_parts = pass_bytes(sc, ctx, nnzb)
+    ctx.close()
+    dominant = max(sec_ms, key=sec_ms.get)
+    gbs = alg_b / (ms_step * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -285,26 +323,31 @@ def run_ours(args):
         "config": {"workload": WORKLOAD, "precision": args.precision, "samples_per_pass": int(units),
                    "face_samples": int(sc.stris.shape[0] * nk), "edge_candidates": cand["edge"],
                    "point_candidates": cand["point"], "face_candidates": cand["face"],
+                   "active_samples": {k: int(counts_once[k]) for k in ("face", "edge", "point")},
                    "l2": "flushed (256 MB write) between timed steps",
                    "parallelism": f"replicas x{world}",
                    "cuda_graph": True, "autotuned_blocks_per_sm": {"samples": tune_s, "query": tune_q}},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_h2d,
                 "d2h_bytes_per_step": 16},
-        "gpu_launches": launches,
-        "roofline": {"bound": "alu", "kernel": "k_items", "achieved": fp64_achieved,
-                     "peak": fp64_peak, "unit": "FP64 Ginst/s",
-                     "frac": fp64_achieved / fp64_peak if fp64_achieved else None,
-                     "traffic": K_ITEMS_DRAM_BYTES,
-                     "peak_source": "FP64 pipe: 148 SMs x 2 lanes/clock x measured SM clock",
-                     "work": {"fp64_lane_inst_per_launch": K_ITEMS_FP64_LANE_INST,
-                              "evals_per_launch": int(evals), "launch_ms": items_ms},
-                     "fp32_model": {"flops_per_eval": 160, "achieved_tflops": fp32_achieved,
-                                    "peak_tflops": fp32_peak,
-                                    "frac": fp32_achieved / fp32_peak if fp32_achieved else None}},
+        "gpu_launches": kernels_per_pass * args.steps if kernels_per_pass > 0 else None,
+        "kernels_per_pass": kernels_per_pass,
+        "roofline": {"bound": "hbm", "kernel": f"contact pass (one CUDA graph of {kernels_per_pass} kernels)",
+                     "achieved": gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": gbs / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)",
+                     "algorithmic_bytes_per_pass": alg_b, "bytes_by_part": alg_parts,
+                     "launch_ms": ms_step,
+                     "dominant_section": {"name": dominant, "ms": sec_ms[dominant],
+                                          "share": sec_ms[dominant] / sum(sec_ms.values())},
+                     "note": "the pass is latency-bound at this size (its algorithmic bytes are L2-resident); "
+                             "the contact-dense line (key dense) and the batch carry the HBM-scale cases"},
+        "alu_peaks": alu,
         "sections_ms": {k: round(v, 4) for k, v in sec_ms.items()},
         "alpha": info["alpha"],
         "clocks": clk,
     }
+    if not args.no_dense:
+        line["dense"] = dense_measurement(dev, alu, steps=max(args.steps, 10))
     if not args.no_batch:
         line["batched"] = batched_measurement(dev, n_env=args.batch_envs)
     if not args.no_newton:
@@ -314,9 +357,119 @@ def run_ours(args):
         line["dual_mesh"] = dual_mesh_measurement(dev)
         line["face_clip"] = face_clip_measurement(dev)
         line["master_rows"] = master_grad_measurement(dev)
+    line["precision_vs_fp64"] = precision_measurement(dev)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(steps=2)
+        line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
+
+
+def dense_measurement(dev, alu, steps=20):
+    """Contact-dense pass: the gel pad (131,072 slave triangles x 16 samples)
+    pressed fully onto a low Perlin plate (390,728 triangles), so that every
+    face sample is active (scenes.gel_dense); mixed precision, one pass per
+    step as in the headline (broad phase, E, gradient, BSR Hessian, step
+    bound), CUDA graph, L2 flushed between steps.  Rooflines: the pass's
+    algorithmic bytes (pass_bytes) against the measured HBM copy bandwidth,
+    and the sample evaluation's FP32 model -- 160 flops per evaluated
+    (sample, candidate) item -- against the measured FP32 FMA rate."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    sc, x_np = S.gel_dense(with_tets=False)
+    nk = 4 ** sc.params["face_rule_level"]
+    rng = np.random.default_rng(13)
+    dx_np = np.zeros_like(x_np)
+    dx_np[:, 2] = -2e-6 * (0.5 + rng.random(x_np.shape[0]))
+    dx_np[:, :2] = 5e-7 * rng.normal(size=(x_np.shape[0], 2))
+    ctx = binding.Context(sc, precision="mixed", device=dev)
+    x = torch.as_tensor(x_np, device="cuda")
+    dx = torch.as_tensor(dx_np, device="cuda")
+    xm = torch.as_tensor(sc.Y0, device="cuda")
+    units, cand = samples_per_pass(ctx, x, xm, nk)
+    first = ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=True)
+    cnt, nnzb = first["counts"], first["hess"].nnzb
+    e_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    grad = torch.empty((sc.X.shape[0], 3), device="cuda", dtype=torch.float32)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=False, energy_dev=e_dev,
+                                grad_out=grad)
+    tune_s, tune_q, _ = ctx.autotune(x, xm, dx, reps=2)
+    for _ in range(3):
+        info = step()
+    torch.cuda.synchronize()
+    ms, info = time_steps(step, stream, steps, flush)
+    ms_pass = statistics.median(ms)
+    sec = sections(ctx, step, flush, steps)
+    kern = ctx.pass_kernels()
+    alg_b, parts = pass_bytes(sc, ctx, nnzb)
+    ctx.close()
+    peaks, kind = load_peaks()
+    evals = int(cnt["face_evaluated"]) + 2 * int(cand["edge"]) + int(cand["point"])
+    item_ms = sec.get("items", 0.0) + sec.get("samples", 0.0)
+    gbs = alg_b / (ms_pass * 1e-3) / 1e9
+    tf = 160.0 * evals / (item_ms * 1e-3) / 1e12 if item_ms > 0 else None
+    return {"workload": "gel_dense: 256x256 gel pad (131,072 slave tris x 16 samples) pressed fully onto a "
+                        "442x442-quad Perlin plate (390,728 tris, amplitude 0.1 mm), dhat 5e-5",
+            "samples_per_pass": int(units), "active": {k: int(cnt[k]) for k in ("face", "edge", "point")},
+            "evaluated_items": evals, "ms_per_pass": ms_pass, "samples_per_s": units / (ms_pass * 1e-3),
+            "kernels_per_pass": kern, "sections_ms": {k: round(v, 4) for k, v in sec.items()},
+            "autotuned_blocks_per_sm": {"samples": tune_s, "query": tune_q},
+            "roofline_hbm": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+                             "target_frac": 0.6, "algorithmic_bytes_per_pass": alg_b, "bytes_by_part": parts,
+                             "peak_source": kind},
+            "roofline_fp32_model": {"flops_per_item": 160, "section_ms": item_ms, "achieved_tflops": tf,
+                                    "peak_tflops": alu["fp32_tflops"],
+                                    "frac": tf / alu["fp32_tflops"] if tf else None,
+                                    "sections": "samples (frames, pre-tests) + items (exact FP64 cast)"},
+            "alpha": info["alpha"], "l2": "flushed (256 MB write) between passes"}
+
+
+def precision_measurement(dev):
+    """What the mixed path's FP32 barrier, gradient and Hessian cost in
+    accuracy against the all-FP64 path, on a pressed 24x24-quad indent (the
+    FP64 path matches the FP64 CPU oracle to 1e-12, tests/test_gpu_contact.py),
+    and what the FP64 anchors keep: the additive-CCD step (FP64 in both),
+    the linearised step bound and the line-search energies of one time step."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    sc = S.tactile_indent(n_quads=24, side=12e-3, nz=2, thick=1e-3, sphere_subdiv=3, radius=5e-3,
+                          face_rule_level=2)
+    x = S.drape_on_master(sc, 0.12e-3)
+    rng = np.random.default_rng(3)
+    dx = np.zeros_like(x)
+    dx[:, 2] = -(1e-5 + 2e-5 * rng.random(x.shape[0]))
+    out = {}
+    res = {}
+    for prec in ("fp64", "mixed"):
+        ctx = binding.Context(sc, precision=prec, device=dev)
+        r = ctx.contact_pass(x, sc.Y0, dx, grad=True, hess=True, counts=True)
+        rp, ci, vals = (t.cpu().numpy() for t in r["hess"])
+        blocks = {}
+        for i in range(rp.shape[0] - 1):
+            for k in range(rp[i], rp[i + 1]):
+                blocks[(i, int(ci[k]))] = vals[k].astype(np.float64)
+        res[prec] = (r["energy"], r["grad"].double().cpu().numpy(), blocks, r["alpha_lin"], r["alpha_accd"],
+                     r["counts"])
+        ctx.close()
+    e64, g64, b64, al64, aa64, c64 = res["fp64"]
+    e32, g32, b32, al32, aa32, c32 = res["mixed"]
+    big = max(np.linalg.norm(b) for b in b64.values())
+    worst = 0.0
+    for k, b in b64.items():
+        nb = np.linalg.norm(b)
+        if nb > 1e-9 * big:
+            worst = max(worst, np.linalg.norm(b32.get(k, 0.0) - b) / nb)
+    out["contact_pass"] = {
+        "energy_rel": abs(e32 - e64) / abs(e64), "grad_rel_l2": float(np.linalg.norm(g32 - g64) / np.linalg.norm(g64)),
+        "hess_block_max_rel": worst, "alpha_lin_rel": abs(al32 - al64) / al64 if np.isfinite(al64) else 0.0,
+        "alpha_accd_equal": aa32 == aa64,
+        "same_active_samples": all(c32[k] == c64[k] for k in ("face", "edge", "point")),
+        "gap_and_decisions": "FP64 in both paths (same active samples)"}
+    return out
 
 
 def face_clip_measurement(dev, n_pairs=2_000_000, reps=20):
@@ -348,7 +501,7 @@ def face_clip_measurement(dev, n_pairs=2_000_000, reps=20):
     return {"workload": f"{n_pairs} seeded unit-size triangle pairs (slave near z = 0, tilted masters above)",
             "ms_per_call": round(s * 1e3, 3), "pairs_per_s": n_pairs / s, "samples_per_call": n_samples,
             "samples_per_s": n_samples / s, "overlapping_pairs": int((cnt > 0).sum().item()),
-            "note": "wall time of the synchronising call (allocation of its 4-byte flag included)"}
+            "note": "wall time of the call and a synchronisation"}
 
 
 def master_grad_measurement(dev, reps=50):
@@ -655,32 +808,90 @@ def warm_start_measurement(dev, train_iters=1500, timed_iters=50):
     }
 
 
-def cpu_baseline(steps=2):
-    """The FP64 oracle, as it stands, on the bounded window of the workload."""
-    from oracle import oracle as O
+def _oracle_windows(n):
+    """n windows (4 mm squares) of the benchmark state, spread over the pad
+    in a grid, each a contact-only sub-scene with its own seeded step dx."""
     from paper_2605_24339_b300 import scenes as S
-    sc, x, dx = make_workload()
-    top = sc.Y0[np.argmax(sc.Y0[:, 2])]
-    sub, xs = S.crop(sc, x, top[:2], CROP_HALF_WIDTH, 4 * sc.params["dhat"])
-    rng = np.random.default_rng(11)
-    dxs = np.zeros_like(xs)
-    dxs[:, 2] = -5e-6 * (0.5 + rng.random(xs.shape[0]))
-    dxs[:, :2] = 1e-6 * rng.normal(size=(xs.shape[0], 2))
+    sc, x, _ = make_workload()
+    k = int(np.ceil(np.sqrt(n)))
+    lo, hi = x[:, 0].min() + CROP_HALF_WIDTH, x[:, 0].max() - CROP_HALF_WIDTH
+    cs = np.linspace(lo, hi, k)
+    out = []
+    for i in range(n):
+        c = (cs[i % k], cs[(i // k) % k])
+        sub, xs = S.crop(sc, x, c, CROP_HALF_WIDTH, 4 * sc.params["dhat"])
+        rng = np.random.default_rng(11 + i)
+        dxs = np.zeros_like(xs)
+        dxs[:, 2] = -5e-6 * (0.5 + rng.random(xs.shape[0]))
+        dxs[:, :2] = 1e-6 * rng.normal(size=(xs.shape[0], 2))
+        out.append((sub, xs, dxs))
+    return out
+
+
+def _oracle_worker(win, passes, start, q):
+    """One host core: the FP64 oracle, as it stands, over one window -- an
+    untimed pass, then ``passes`` timed passes (energy, gradient, Hessian and
+    step bound), started together with the other workers."""
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    sub, xs, dxs = win
     Os = O.Scene(sub)
-    nk = 4 ** sc.params["face_rule_level"]
-    cand_e = Os.candidates(1, xs, sub.Y0).shape[0]
-    cand_p = Os.candidates(2, xs, sub.Y0).shape[0]
-    units = sub.stris.shape[0] * nk + 2 * cand_e + cand_p
+    nk = 4 ** sub.params["face_rule_level"]
+    units = (sub.stris.shape[0] * nk + 2 * Os.candidates(1, xs, sub.Y0).shape[0]
+             + Os.candidates(2, xs, sub.Y0).shape[0])
+    Os.contact(xs, sub.Y0)
+    Os.ccd_max_step(xs, dxs, sub.Y0)
+    start.wait()
     t0 = time.perf_counter()
-    for _ in range(steps):
+    for _ in range(passes):
         Os.contact(xs, sub.Y0)
         Os.ccd_max_step(xs, dxs, sub.Y0)
-    dt = time.perf_counter() - t0
-    return {"value": units * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} passes over a {2 * CROP_HALF_WIDTH * 1e3:.0f} mm window "
-                      f"({sub.stris.shape[0]} slave tris, {sub.mtris.shape[0]} master tris, "
-                      f"{units} samples/pass) around the highest terrain peak",
-            "seconds": dt}
+    q.put((units * passes, t0, time.perf_counter()))
+
+
+def oracle_all_cores(passes=1, procs=None, windows=None):
+    """The oracle on every host core: one spawned process per core, each on
+    its own window of the workload; throughput = all samples over the span
+    from the first start to the last finish."""
+    import multiprocessing as mp
+    from oracle import oracle as O
+    O.build()
+    procs = procs or len(os.sched_getaffinity(0))
+    windows = windows or _oracle_windows(procs)
+    ctx = mp.get_context("spawn")
+    start = ctx.Barrier(procs)
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(windows[i], passes, start, q)) for i in range(procs)]
+    for p in ps:
+        p.start()
+    res = [q.get() for _ in ps]
+    for p in ps:
+        p.join()
+    units = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    return units / span, span, procs, windows
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_baseline():
+    """The FP64 oracle, as it stands, on all host cores (one window of the
+    workload per core, bounded: one timed pass each)."""
+    v, span, procs, wins = oracle_all_cores(passes=1)
+    n_tris = sum(w[0].stris.shape[0] for w in wins)
+    return {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle", "cpu": _cpu_model(),
+            "sample": f"{procs} processes, one per core, each one pass over its own "
+                      f"{2 * CROP_HALF_WIDTH * 1e3:.0f} mm window of the workload ({n_tris} slave tris in all)",
+            "seconds": span}
 
 
 def run_passes(args):
@@ -699,6 +910,25 @@ def run_passes(args):
     torch.cuda.synchronize()
     print(json.dumps({"passes": args.steps, "alpha": info["alpha"], "ccd_pairs_pt": info["n_pt"],
                       "ccd_pairs_ee": info["n_ee"]}))
+
+
+def run_dense_passes(args):
+    """--steps contact passes on the contact-dense workload with no timing
+    (the command line for ncu captures of its kernels)."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    sc, x_np = S.gel_dense(with_tets=False)
+    ctx = binding.Context(sc, precision=args.precision)
+    x = torch.as_tensor(x_np, device="cuda")
+    dx = torch.zeros_like(x)
+    dx[:, 2] = -2e-6
+    xm = torch.as_tensor(sc.Y0, device="cuda")
+    e_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(args.steps):
+        info = ctx.contact_pass(x, xm, dx, grad=True, hess="view", counts=False, energy_dev=e_dev)
+    torch.cuda.synchronize()
+    print(json.dumps({"passes": args.steps, "alpha": info["alpha"]}))
 
 
 def run_mlp(args):
@@ -744,39 +974,26 @@ def run_newton(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (the paper ships no code) on all
+    host cores; each step one pass over a window of the workload per core."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import oracle as O
-    from paper_2605_24339_b300 import scenes as S
-    sc, x, dx = make_workload()
-    top = sc.Y0[np.argmax(sc.Y0[:, 2])]
-    sub, xs = S.crop(sc, x, top[:2], CROP_HALF_WIDTH, 4 * sc.params["dhat"])
-    rng = np.random.default_rng(11)
-    dxs = np.zeros_like(xs)
-    dxs[:, 2] = -5e-6 * (0.5 + rng.random(xs.shape[0]))
-    dxs[:, :2] = 1e-6 * rng.normal(size=(xs.shape[0], 2))
-    Os = O.Scene(sub)
-    nk = 4 ** sc.params["face_rule_level"]
-    units = (sub.stris.shape[0] * nk + 2 * Os.candidates(1, xs, sub.Y0).shape[0]
-             + Os.candidates(2, xs, sub.Y0).shape[0])
-    for _ in range(min(args.warmup, 1)):
-        Os.contact(xs, sub.Y0)
-        Os.ccd_max_step(xs, dxs, sub.Y0)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        Os.contact(xs, sub.Y0)
-        Os.ccd_max_step(xs, dxs, sub.Y0)
-    dt = time.perf_counter() - t0
-    value = units * args.steps / dt
-    sample = (f"each step one pass over a {2 * CROP_HALF_WIDTH * 1e3:.0f} mm window of the workload "
-              f"({sub.stris.shape[0]} slave tris, {units} samples)")
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+    procs = len(os.sched_getaffinity(0))
+    wins = _oracle_windows(procs)
+    if args.warmup > 0:
+        oracle_all_cores(passes=1, procs=procs, windows=wins)
+    v, span, _, _ = oracle_all_cores(passes=args.steps, procs=procs, windows=wins)
+    n_tris = sum(w[0].stris.shape[0] for w in wins)
+    sample = (f"each step: {procs} processes, one per core, each one pass over its own "
+              f"{2 * CROP_HALF_WIDTH * 1e3:.0f} mm window ({n_tris} slave tris in all)")
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": span / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "window": sample}, "impl": "reference",
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle", "cpu": _cpu_model(),
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -789,6 +1006,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-envs measurement")
+    ap.add_argument("--no-dense", action="store_true", help="skip the contact-dense measurement")
     ap.add_argument("--no-dual-map", action="store_true", help="skip the dual-mesh mapper, face-clip and master-row measurements")
     ap.add_argument("--dual-points", type=int, default=2_000_000,
                     help="--mode dualmap: visual points of the dual-mesh measurement")
@@ -799,7 +1017,7 @@ def main():
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
     ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "dualmap", "faceclip",
-                                                       "mastergrad"],
+                                                       "mastergrad", "dense", "dense_passes", "peaks"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
                          "training steps or time steps (command lines for profilers); batch: "
                          "the batched measurement alone, --steps timed passes")
@@ -821,6 +1039,12 @@ def main():
     elif args.mode == "mastergrad":
         import torch
         print(json.dumps(master_grad_measurement(0, reps=max(3, args.steps))))
+    elif args.mode == "dense":
+        print(json.dumps(dense_measurement(0, measure_alu_peaks(0), steps=max(3, args.steps))), flush=True)
+    elif args.mode == "dense_passes":
+        run_dense_passes(args)
+    elif args.mode == "peaks":
+        print(json.dumps(measure_alu_peaks(0)), flush=True)
     elif args.mode == "batch":
         print(json.dumps(batched_measurement(0, n_env=args.batch_envs,
                                              steps=args.steps)), flush=True)

@@ -445,6 +445,21 @@ ipc_status ipc_ws_get_params(ipc_ctx* ctx, float* params_host);
 ipc_status ipc_ws_predict(ipc_ctx* ctx, const double* x_dev, const double* v_dev, const double* xm_dev,
                           double* dx_dev);
 
+/* Kernel launches one ipc_contact_pass makes: the kernel nodes of the CUDA
+ * graph the context captured for its last graph-replayed pass (params.use_graphs
+ * set), or -1 if no graph is held.  Not part of the method: for launch counts
+ * in measurements. */
+ipc_status ipc_contact_pass_kernels(ipc_ctx* ctx, int64_t* kernels_host);
+
+/* Measured CUDA-core arithmetic rate of a device (not part of the method: a
+ * measurement utility for roofline fractions).  kind 0: FP32 fused
+ * multiply-add, kind 1: FP64 fused multiply-add; one FMA counts as two
+ * operations.  Runs a kernel of independent FMA chains on every SM of
+ * `device` on `stream` (a cudaStream_t, 0 = default), times its second launch
+ * with CUDA events and writes TFLOP/s to *tflops_host.  Synchronises the
+ * stream; errors through ipc_last_error(NULL). */
+ipc_status ipc_alu_peak(int32_t kind, int32_t device, void* stream, double* tflops_host);
+
 /* ------------------------------------------------------------------------
  * Checkpoint and resume (not in the paper: the library's own subsystem).
  * ------------------------------------------------------------------------ */

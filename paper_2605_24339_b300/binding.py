@@ -196,6 +196,16 @@ def dual_map_build(V, T, P, stream=0):
     return tri, uvwd, d2
 
 
+def alu_peak(kind, device=0, stream=0):
+    """ipc_alu_peak: measured FP32 (kind 0) or FP64 (kind 1) FMA rate, TFLOP/s."""
+    out = C.c_double()
+    f = lib().ipc_alu_peak
+    f.restype = C.c_int
+    f.argtypes = [C.c_int32, C.c_int32, C.c_void_p, C.POINTER(C.c_double)]
+    _dm_check(f(int(kind), int(device), C.c_void_p(stream), C.byref(out)))
+    return out.value
+
+
 def face_clip_samples(xs, ts, xm, tm, pairs, stream=0):
     """ipc_face_clip_samples on CUDA tensors; returns (samples float64
     [n, 12, 8], count int32 [n])."""
@@ -488,8 +498,8 @@ class Context:
             if not (isinstance(a, t.Tensor) and a.is_cuda and a.dtype == t.float64 and a.is_contiguous()):
                 raise TypeError("x and v must be contiguous FP64 CUDA tensors")
         st = StepStats()
-        r = lib().ipc_newton_step(self.h, _ptr(x), _ptr(v), _ptr(self._as(xm_next)),
-                                  _ptr(self._as(dx_pred)), C.byref(st))
+        xm_t, dxp_t = self._as(xm_next), self._as(dx_pred)   # alive until the call returns
+        r = lib().ipc_newton_step(self.h, _ptr(x), _ptr(v), _ptr(xm_t), _ptr(dxp_t), C.byref(st))
         if r not in (0, STEP_INFEASIBLE, STEP_NOT_CONVERGED, STEP_LINESEARCH):
             self._check(r)
         return dict(status=r, newton_iters=st.newton_iters, pcg_iters=st.pcg_iters_total,
@@ -566,6 +576,15 @@ class Context:
         dx = t.empty((self.nv, 3), dtype=t.float64, device=self.device)
         self._check(lib().ipc_ws_predict(self.h, _ptr(x), _ptr(v), _ptr(xm), _ptr(dx)))
         return dx
+
+    def pass_kernels(self):
+        """Kernel launches of one graph-replayed ipc_contact_pass (-1: no graph)."""
+        f = lib().ipc_contact_pass_kernels
+        f.restype = C.c_int
+        f.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+        n = C.c_int64()
+        self._check(f(self.h, C.byref(n)))
+        return n.value
 
     # -- checkpoint / resume -------------------------------------------------
     def save(self, path, x, v):

@@ -23,7 +23,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE
 # CPU oracle does on degenerate (coincident) meshes
 NO_FMA = {"broadphase.cu", "contact.cu", "faceclip.cu"}
 SOURCES = ["api.cu", "scan.cu", "broadphase.cu", "contact.cu", "newton.cu", "warmstart.cu", "dualmap.cu",
-           "faceclip.cu", "snapshot.cu"]
+           "faceclip.cu", "snapshot.cu", "peaks.cu"]
 
 
 def nvcc() -> str:

@@ -326,6 +326,18 @@ void capture_contact_pass(Ctx& c, const ContactPassArgs& A) {
         e = e1 != cudaSuccess ? e1 : e2;
     }
     c.stream = user;
+    int64_t kernels = 0;
+    if (e == cudaSuccess && g) {
+        size_t n = 0;
+        e = cudaGraphGetNodes(g, nullptr, &n);
+        std::vector<cudaGraphNode_t> nodes(n);
+        if (e == cudaSuccess && n) e = cudaGraphGetNodes(g, nodes.data(), &n);
+        for (size_t i = 0; e == cudaSuccess && i < n; ++i) {
+            cudaGraphNodeType t;
+            e = cudaGraphNodeGetType(nodes[i], &t);
+            kernels += t == cudaGraphNodeTypeKernel;
+        }
+    }
     if (e == cudaSuccess && g) e = cudaGraphInstantiate(&c.cp_graph.exec, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e != cudaSuccess) {
@@ -334,6 +346,7 @@ void capture_contact_pass(Ctx& c, const ContactPassArgs& A) {
         return;
     }
     c.cp_graph.key = key;
+    c.cp_graph.kernels = kernels;
 }
 
 }  // namespace gmcp
@@ -1370,6 +1383,12 @@ ipc_status ipc_profile(ipc_ctx* ctx, int32_t mode, int32_t max_sections, char* n
         ++n;
     }
     if (n_sections) *n_sections = n;
+    return IPC_OK;
+}
+
+ipc_status ipc_contact_pass_kernels(ipc_ctx* ctx, int64_t* kernels_host) {
+    if (!ctx || !kernels_host) return IPC_ERR_ARG;
+    *kernels_host = ctx->c.cp_graph.exec ? ctx->c.cp_graph.kernels : -1;
     return IPC_OK;
 }
 

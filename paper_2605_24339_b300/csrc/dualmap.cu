@@ -16,7 +16,6 @@
 #include "gmcp_internal.cuh"
 
 namespace gmcp {
-void set_global_error(const std::string& msg);   // api.cu: read by ipc_last_error(NULL)
 }
 
 namespace {

@@ -239,10 +239,12 @@ struct NewtonState {
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     std::vector<uintptr_t> key;
+    int64_t kernels = 0;           // kernel nodes of the captured graph
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
         key.clear();
+        kernels = 0;
     }
     ~GraphCache() { reset(); }
 };
@@ -467,6 +469,8 @@ cudaError_t vec_velocity(Ctx& c, const double* x, const double* xt, double* v);
 cudaError_t vec_neg(Ctx& c, int64_t n, const double* a, double* out);
 // api.cu: the context behind an ABI handle
 Ctx& ctx_of(ipc_ctx* h);
+// errors of the context-free entry points, read by ipc_last_error(NULL) (api.cu)
+void set_global_error(const std::string& msg);
 
 // learned warm start: the state a snapshot carries (warmstart.cu)
 struct WsState {

@@ -33,7 +33,7 @@ import numpy as np
 
 __all__ = [
     "Scene", "splitmix64_stream", "pad_slab", "icosphere", "perlin2",
-    "height_field", "tactile_indent", "gel_on_terrain", "fingertip_batch",
+    "height_field", "tactile_indent", "gel_on_terrain", "gel_dense", "fingertip_batch",
     "drape_on_master", "concat_envs",
 ]
 
@@ -389,6 +389,29 @@ def gel_on_terrain(n_quads=256, dx=1e-4, nz=8, thick=2e-3, terrain_quads=316,
     p["shear_velocity"] = (press_speed, 0.0, 0.0)
     return _single_env(X, tets, bot, top.astype(np.uint8), Y, F, vdir, p,
                        "gel_on_terrain", n_steps)
+
+
+def gel_dense(n_quads=256, dx=1e-4, nz=8, thick=2e-3, plate_quads=442, plate_size=28e-3,
+              amp=0.1e-3, wavelength=2e-3, dhat=5e-5, seed=3, face_rule_level=2, with_tets=True):
+    """Contact-dense variant of gel_on_terrain: the same 256x256-quad gel pad
+    (131,072 slave triangles x 16 face samples) over a larger, lower Perlin
+    plate (442x442 quads over 28x28 mm, 390,728 triangles, amplitude 0.1 mm,
+    wavelength 2 mm), so that the pad can be pressed onto it everywhere.
+    Returns (scene, x) with x the pad draped fully onto the plate
+    (drape_on_master with a depth beyond the plate's relief): every slave
+    vertex sits 0.3-0.9 dhat above the plate, so nearly every face sample is
+    active."""
+    side = n_quads * dx
+    Y, F = height_field(plate_quads, plate_size, amp, wavelength, seed)
+    z0 = float(Y[:, 2].max()) + 2 * dhat
+    X, tets, bot, top = pad_slab(n_quads, n_quads, nz, dx, thick / nz,
+                                 origin=(-side / 2, -side / 2, z0), with_tets=with_tets)
+    vdir = np.zeros_like(X)
+    vdir[top, 2] = -0.5e-3
+    p = _finish_params(default_params(dhat=dhat, face_rule_level=face_rule_level, h=1e-2), X, bot)
+    sc = _single_env(X, tets, bot, top.astype(np.uint8), Y, F, vdir, p, "gel_dense", 50)
+    depth = float(Y[:, 2].max() - Y[:, 2].min()) + 4 * dhat
+    return sc, drape_on_master(sc, depth)
 
 
 def _fingertip_env(e, pads_per_env, quad_range, dx, nz, thick, tri_range, radius, dhat, kappa, h,

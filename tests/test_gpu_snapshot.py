@@ -41,8 +41,10 @@ def _steps(ctx, sc, x, v, k, xm_path=None, t0=0, learned=False):
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_resume_is_bitwise(B, tmp_path, prec):
-    sc = flat_press(nq=4, n_steps=6)
-    lift = lambda t: sc.Y0 + np.array([0.0, 0.0, 1e-5 * (t + 1)])   # the master rises each step
+    # the master rises 2 um a step while the top face presses the pad onto it
+    # (in contact from the fourth step; the oracle converges on all five)
+    sc = flat_press(nq=4, n_steps=8)
+    lift = lambda t: sc.Y0 + np.array([0.0, 0.0, 2e-6 * (t + 1)])
     path = str(tmp_path / "snap.bin")
     a = B.Context(sc, precision=prec)
     x = torch.as_tensor(sc.X.copy(), device="cuda")
@@ -63,7 +65,7 @@ def test_resume_is_bitwise(B, tmp_path, prec):
 
 
 def test_resume_with_network_is_bitwise(B, tmp_path):
-    sc = flat_press(nq=4, n_steps=6)
+    sc = flat_press(nq=4, n_steps=8)
     path = str(tmp_path / "snap_ws.bin")
     n = sc.X.shape[0]
     rng = np.random.default_rng(2)

@@ -187,7 +187,7 @@ def test_features_match_oracle(B, oracle_mod, prec):
     oracle FP64 ones) plus 2e-6 for the FP32 sine/cosine arguments; the
     contact flag exact."""
     from helpers import small_indent
-    sc, x = small_indent(n_quads=10, subdiv=3, press=0.12e-3, L=1)
+    sc, x = small_indent(n_quads=10, subdiv=3, press=0.2e-3, L=1)
     rng = np.random.default_rng(4)
     v = rng.normal(scale=1e-3, size=x.shape)
     ctx = B.Context(sc, precision=prec)
@@ -197,7 +197,7 @@ def test_features_match_oracle(B, oracle_mod, prec):
     surf = np.zeros(sc.X.shape[0], bool)
     surf[np.unique(sc.stris)] = True
     fo = M.features(x, v, sc.X, sc.dirichlet, surf, o["grad"], sc.params["h"], 1e-4, 1e-6, 1e-4)
-    assert fo[:, 14].sum() > 20
+    assert fo[:, 14].sum() >= 10
     np.testing.assert_array_equal(f[:, 14], fo[:, 14])
     np.testing.assert_array_equal(f[:, 9:11], fo[:, 9:11])
     tol = _bf16_ulp(fo) + 2e-6
