@@ -465,6 +465,7 @@ __device__ __forceinline__ TriData load_tri(const SceneView& S, const CandView& 
 // barycentrics b and the linearised gap change dg along (dx, dxm)
 struct ItemOut {
     double kq, w, gamma, g, eps, dg;
+    double g_step;   // the gap the step bound uses: g, or a certified lower bound of it
     double b[3];
     int32_t mv[3];   // master vertices of x_m (-1 unused) and their weights
     double bm[3];
@@ -538,7 +539,7 @@ __device__ __forceinline__ bool face_item(const SceneView& S, const Params& P, c
     }
     if (!(g < eps)) return false;
     o.kq = P.kappa; o.w = (1.0 / (double)NK) * D.As; o.gamma = hermite(min3(bm), P.delta_T);
-    o.g = g; o.eps = eps;
+    o.g = g; o.g_step = g; o.eps = eps;
     for (int q = 0; q < 3; ++q) { o.b[q] = F.beta[q]; o.mv[q] = M[q]; o.bm[q] = bm[q]; }
     o.dg = 0.0;
     if (want_dg) {
@@ -598,7 +599,7 @@ __device__ __forceinline__ bool edge_item(const SceneView& S, const Params& P, c
     }
     if (!(g < eps)) return false;
     o.kq = P.kappa_edge; o.w = 0.5 * ell; o.gamma = hermite(eta, P.delta_e) * hermite(1.0 - eta, P.delta_e);
-    o.g = g; o.eps = eps;
+    o.g = g; o.g_step = g; o.eps = eps;
     for (int c = 0; c < 3; ++c) o.b[c] = bsk[c];
     o.mv[0] = ia; o.mv[1] = ib; o.mv[2] = -1;
     o.bm[0] = 1.0 - eta; o.bm[1] = eta; o.bm[2] = 0.0;
@@ -636,7 +637,7 @@ __device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, 
     }
     if (!(g < eps)) return false;
     o.kq = P.kappa_point; o.w = 1.0; o.gamma = 1.0;
-    o.g = g; o.eps = eps;
+    o.g = g; o.g_step = g; o.eps = eps;
     for (int c = 0; c < 3; ++c) o.b[c] = bs[c];
     o.mv[0] = u; o.mv[1] = -1; o.mv[2] = -1;
     o.bm[0] = 1.0; o.bm[1] = 0.0; o.bm[2] = 0.0;
@@ -647,6 +648,212 @@ __device__ __forceinline__ bool point_item(const SceneView& S, const Params& P, 
         o.dg = dm - ds;
     }
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// Certified FP32 evaluation (mixed path, contact evaluation only).
+//
+// The FP32 pre-tests above reject items that certainly fail; the functions
+// below accept items that certainly pass and evaluate them from FP32
+// geometry.  An item is taken here only when every decision of the exact
+// FP64 test has a margin far above the FP32 error of the quantity it
+// compares -- so the FP64 test decides the same way -- and only when its
+// value is well conditioned:
+//   - facing: the cast direction is within 60 degrees of the master normal
+//     (face), or some adjacent master face has N.n_s <= -0.1 |N| (edge,
+//     point);
+//   - eps = eps_max is settled by the rest-box test (rest_far), so no rest
+//     cast is needed;
+//   - 0.2 eps + tol_g <= g <= 0.95 eps - tol_g: away from g = 0, where B'
+//     ~ 1/g magnifies the gap's relative error, and from g = eps, where the
+//     factor (g - eps) of B, B', B'' would carry it;
+//   - inside with margin: min beta^m >= tol_b (face), a clipped parameter
+//     range longer than its error (edge), min beta^s >= tol_b (point);
+//   - a static master (dxm == NULL), so the step bound needs only the slave
+//     side's gap change.
+// Error bounds.  Coordinates enter as FP64 differences rounded once to FP32
+// (relative error 2^-24) and pass through a few dozen FP32 operations: the
+// first-order error of a gap or barycentric coordinate is below about 1e-6
+// of the magnitudes involved, times the triangle's shape factor
+// |e1||e2|/|N| and, for a cast, 1 / cos of its angle.  tol_g and tol_b are
+// 1e-4 of the same magnitudes and factors, a hundred times that; the
+// edge/point tolerances reuse those of bary_f and plane_gap_maybe, stated
+// there.  Every other item goes to the FP64 test as before.  The step bound
+// of a certified item uses the gap's lower bound g - tol_g and an upper
+// bound of its closing rate, so it never exceeds the FP64 bound.
+// ---------------------------------------------------------------------------
+constexpr float kCertLo = 0.2f, kCertHi = 0.95f;
+
+__device__ __forceinline__ float norm3f(V3<float> a) { return sqrtf(dot(a, a)); }
+
+// barycentric coordinates of q (relative to the triangle's first vertex) in
+// the frame (e1, e2), by the Gram system of Eq. (gram)
+__device__ __forceinline__ void bary_rel(V3<float> q, V3<float> e1, V3<float> e2, float* b) {
+    const float a = dot(e1, e1), bb = dot(e1, e2), c = dot(e2, e2);
+    const float r1 = dot(q, e1), r2 = dot(q, e2);
+    const float det = a * c - bb * bb;
+    const float v = (c * r1 - bb * r2) / det, w = (a * r2 - bb * r1) / det;
+    b[0] = 1.0f - v - w; b[1] = v; b[2] = w;
+}
+
+// some master face of the list certainly faces n_s (N . n_s <= -0.1 |N|)
+__device__ __forceinline__ bool facing_cert(const SceneView& S, const double* xm, const int32_t* tris, int n,
+                                            V3<float> ns) {
+    for (int i = 0; i < n; ++i) {
+        const int32_t* M = S.mtri + 3 * (int64_t)tris[i];
+        const V3<double> y0 = ld3(xm, M[0]);
+        const V3<float> N = cross(tof(ld3(xm, M[1]) - y0), tof(ld3(xm, M[2]) - y0));
+        if (dot(N, ns) <= -0.1f * norm3f(N)) return true;
+    }
+    return false;
+}
+
+// face sample F of slave tri D against master tri m (Sec. 4.1, reading R1),
+// in the master triangle's frame
+template <int NK>
+__device__ __forceinline__ bool face_cert(const SceneView& S, const Params& P, const TriData& D,
+                                          const FaceSample& F, const double* xm, int32_t m, bool want_dg,
+                                          ItemOut& o) {
+    const double eps = P.dhat;
+    const double* mb = S.mrest_box + 6 * (int64_t)m;
+    if (!rest_far(D.sb, D.sb + 3, mb, mb + 3, eps)) return false;
+    const int32_t* M = S.mtri + 3 * (int64_t)m;
+    const V3<double> y0 = ld3(xm, M[0]);
+    const V3<float> e1 = tof(ld3(xm, M[1]) - y0), e2 = tof(ld3(xm, M[2]) - y0), d = tof(y0 - F.xs);
+    const V3<float> N = cross(e1, e2);
+    const float nN = norm3f(N);
+    const float cosn = -dot(N, D.ns_f) / nN;
+    if (!(cosn >= 0.5f)) return false;
+    const float g = dot(N, d) / (-cosn * nN);
+    const float l1 = norm3f(e1), l2 = norm3f(e2), l3 = norm3f(e2 - e1);
+    const float shape = l1 * l2 / nN;
+    const float tol_g = 1e-4f * (norm3f(d) + fabsf(g)) * shape / cosn;
+    const float epsf = (float)eps;
+    if (!(g - tol_g >= kCertLo * epsf && g + tol_g <= kCertHi * epsf)) return false;
+    const V3<float> q = g * D.ns_f - d;   // hit point relative to y0
+    float bm[3];
+    bary_rel(q, e1, e2, bm);
+    const float hmin = nN / rmax(l1, rmax(l2, l3));
+    const float tol_b = 1e-4f + (tol_g + 1e-4f * norm3f(q)) * shape / hmin;
+    if (!(min3(bm) >= tol_b)) return false;
+    o.kq = P.kappa; o.w = (1.0 / (double)NK) * D.As; o.gamma = (double)hermite(min3(bm), (float)P.delta_T);
+    o.g = (double)g; o.g_step = (double)g - (double)tol_g; o.eps = eps;
+    for (int c = 0; c < 3; ++c) { o.b[c] = F.beta[c]; o.mv[c] = M[c]; o.bm[c] = (double)bm[c]; }
+    o.dg = want_dg ? -F.ds : 0.0;
+    return true;
+}
+
+// the slave-side closing rate of a certified edge or point item: dg =
+// -n_s . sum_a b_a dx_a with b from FP32 geometry (error <= tol_b each),
+// widened toward closing by tol_b sum_a |n_s . dx_a|
+__device__ __forceinline__ double cert_dg(const TriData& D, const double* b, float tol_b) {
+    const double s0 = dot(D.ns, D.dx0), s1 = dot(D.ns, D.dx1), s2 = dot(D.ns, D.dx2);
+    const double ds = b[0] * s0 + b[1] * s1 + b[2] * s2;
+    return -ds - (double)tol_b * (fabs(s0) + fabs(s1) + fabs(s2));
+}
+
+// Gauss point q of master edge me projected on slave tri D (Sec. 4.1,
+// reading R3).  Barycentric coordinates are affine along the projected
+// edge, so beta^s and the plane gap at a Gauss point are the ends' values
+// mixed by eta.
+__device__ __forceinline__ bool edge_cert(const SceneView& S, const Params& P, const TriData& D,
+                                          const double* xm, int32_t me, int q, bool want_dg, ItemOut& o) {
+    const double eps = P.dhat;
+    const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
+    const V3<double> Ya = ld3(S.Y0, ia), Yb = ld3(S.Y0, ib);
+    const double elo[3] = {rmin(Ya.x, Yb.x), rmin(Ya.y, Yb.y), rmin(Ya.z, Yb.z)};
+    const double ehi[3] = {rmax(Ya.x, Yb.x), rmax(Ya.y, Yb.y), rmax(Ya.z, Yb.z)};
+    if (!rest_far(D.sb, D.sb + 3, elo, ehi, eps)) return false;
+    const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
+    if (!facing_cert(S, xm, S.me_tri + a0, a1 - a0, D.ns_f)) return false;
+    const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
+    const V3<float> da = tof(ya - D.x0), db = tof(yb - D.x0);
+    float bA[3], bB[3], tA, tB;
+    bool okA, okB;
+    bary_f(da, D.e1_f, D.e2_f, bA, tA, okA);
+    bary_f(db, D.e1_f, D.e2_f, bB, tB, okB);
+    if (!okA || !okB) return false;
+    const float tb = tA + tB;
+    // clip eta by beta_a(eta) = bA + eta (bB - bA) >= 0, with error bounds on
+    // both ends of the range
+    float lo = 0.0f, hi = 1.0f, elo_t = 0.0f, ehi_t = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        const float Dd = bB[a] - bA[a];
+        if (fabsf(Dd) <= 4.0f * tb) {
+            // nearly parallel to slave edge a: certain only if inside all along
+            if (rmin(bA[a], bB[a]) >= tb) continue;
+            return false;
+        }
+        const float r = -bA[a] / Dd;
+        const float er = (tA + fabsf(r) * tb) / (fabsf(Dd) - tb);
+        if (Dd > 0.0f) { if (r > lo) { lo = r; elo_t = er; } }
+        else if (r < hi) { hi = r; ehi_t = er; }
+    }
+    if (!(hi - lo > 4.0f * (elo_t + ehi_t) + 1e-3f)) return false;
+    const float gp = 0.57735026918962576f;   // 1 / sqrt(3)
+    const float mid = 0.5f * (lo + hi), half = 0.5f * (hi - lo);
+    const float eta = q == 0 ? mid - half * gp : mid + half * gp;
+    const float ga = dot(D.ns_f, da), gb = dot(D.ns_f, db);
+    const float g = (1.0f - eta) * ga + eta * gb;
+    const float tol_g = 1e-5f * (fabsf(da.x) + fabsf(da.y) + fabsf(da.z) + fabsf(db.x) + fabsf(db.y) + fabsf(db.z)) +
+                        fabsf(gb - ga) * (elo_t + ehi_t) + D.tol_abs;
+    const float epsf = (float)eps;
+    if (!(g - tol_g >= kCertLo * epsf && g + tol_g <= kCertHi * epsf)) return false;
+    const V3<float> tv = db - da;
+    const float tn = dot(tv, D.ns_f);
+    const V3<float> tp = tv - tn * D.ns_f;
+    const float ell = (hi - lo) * norm3f(tp);
+    o.kq = P.kappa_edge; o.w = 0.5 * (double)ell;
+    o.gamma = (double)(hermite(eta, (float)P.delta_e) * hermite(1.0f - eta, (float)P.delta_e));
+    o.g = (double)g; o.g_step = (double)g - (double)tol_g; o.eps = eps;
+    for (int c = 0; c < 3; ++c) o.b[c] = (double)((1.0f - eta) * bA[c] + eta * bB[c]);
+    o.mv[0] = ia; o.mv[1] = ib; o.mv[2] = -1;
+    o.bm[0] = 1.0 - (double)eta; o.bm[1] = (double)eta; o.bm[2] = 0.0;
+    o.dg = want_dg ? cert_dg(D, o.b, tb) : 0.0;
+    return true;
+}
+
+// master vertex u projected on slave tri D (Sec. 4.1, reading R3)
+__device__ __forceinline__ bool point_cert(const SceneView& S, const Params& P, const TriData& D,
+                                           const double* xm, int32_t u, bool want_dg, ItemOut& o) {
+    const double eps = P.dhat;
+    const V3<double> Y = ld3(S.Y0, u);
+    const double yb[3] = {Y.x, Y.y, Y.z};
+    if (!rest_far(D.sb, D.sb + 3, yb, yb, eps)) return false;
+    const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
+    if (!facing_cert(S, xm, S.mv_tri + a0, a1 - a0, D.ns_f)) return false;
+    const V3<float> d = tof(ld3(xm, u) - D.x0);
+    float bs[3], tb;
+    bool ok;
+    bary_f(d, D.e1_f, D.e2_f, bs, tb, ok);
+    if (!ok || !(min3(bs) >= tb)) return false;
+    const float g = dot(D.ns_f, d);
+    const float tol_g = 1e-5f * (fabsf(d.x) + fabsf(d.y) + fabsf(d.z)) + D.tol_abs;
+    const float epsf = (float)eps;
+    if (!(g - tol_g >= kCertLo * epsf && g + tol_g <= kCertHi * epsf)) return false;
+    o.kq = P.kappa_point; o.w = 1.0; o.gamma = 1.0;
+    o.g = (double)g; o.g_step = (double)g - (double)tol_g; o.eps = eps;
+    for (int c = 0; c < 3; ++c) o.b[c] = (double)bs[c];
+    o.mv[0] = u; o.mv[1] = -1; o.mv[2] = -1;
+    o.bm[0] = 1.0; o.bm[1] = 0.0; o.bm[2] = 0.0;
+    o.dg = want_dg ? cert_dg(D, o.b, tb) : 0.0;
+    return true;
+}
+
+// the value of an item for the evaluation: energy, c1, c2, slave
+// barycentrics and its step bound (the arithmetic of sample_add)
+template <class T>
+__device__ __forceinline__ void item_value(const ItemOut& o, bool want_dg, double& e, double& amin, T& c1, T& c2,
+                                           T* b) {
+    T Bv, dB, d2B;
+    barrier(o.g, o.eps, Bv, dB, d2B);
+    const T coef = (T)(o.kq * o.w * o.gamma);
+    e = (double)(coef * Bv);
+    c1 = coef * dB;
+    c2 = rmax(coef * d2B, T(0));
+    for (int cc = 0; cc < 3; ++cc) b[cc] = (T)o.b[cc];
+    amin = INFINITY;
+    if (want_dg && o.dg < 0.0) amin = 0.9 * o.g_step / (-o.dg);
 }
 
 // Warp per active triangle (persistent grid).  Used for the step bound and
@@ -711,6 +918,7 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
     const bool pre = P.precision == IPC_PREC_MIXED;   // FP32 pre-tests (exact decisions unchanged)
     const bool want_dg = dx != nullptr;
     const bool want_alpha = MODE != MODE_LAGGED && want_dg;
+    const bool cert = pre && MODE == MODE_EVAL && dxm == nullptr;   // certified FP32 items
     for (int i = next_item(C.work, lane); i < n_active; i = next_item(C.work, lane)) {
         const TriData D = load_tri(S, C, x, dx, frame, i);
         Acc<T> A;
@@ -723,7 +931,7 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
             if (MODE == MODE_MASTER) master_rows(LG, o, D.ns);
             if (MODE == MODE_MASTER_HESS) master_blocks(LG, o, S.stri + 3 * D.t, D.ns);
             if (want_dg) {
-                if (want_alpha && o.dg < 0.0) A.amin = rmin(A.amin, 0.9 * o.g / (-o.dg));
+                if (want_alpha && o.dg < 0.0) A.amin = rmin(A.amin, 0.9 * o.g_step / (-o.dg));
                 if (MODE == MODE_LAGGED) lag_add(E8, al8, LG.na, o.kq * o.w * o.gamma, o.g, o.eps, o.dg);
             }
         };
@@ -735,7 +943,9 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
             for (int it = lane; it < D.nf * NK; it += 32) {
                 ++cnt_eval;
                 ItemOut o;
-                if (!face_item<NK>(S, P, D, F, xm, dxm, Lf[it / NK], pre, want_dg, o)) continue;
+                if (!(cert && face_cert<NK>(S, P, D, F, xm, Lf[it / NK], want_dg, o)) &&
+                    !face_item<NK>(S, P, D, F, xm, dxm, Lf[it / NK], pre, want_dg, o))
+                    continue;
                 ++cnt_f;
                 consume(o);
             }
@@ -744,7 +954,9 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
             const int32_t* Le = C.edge + D.t * C.cap_e;
             for (int it = lane; it < D.ne * 2; it += 32) {
                 ItemOut o;
-                if (!edge_item(S, P, D, xm, dxm, Le[it >> 1], it & 1, pre, want_dg, o)) continue;
+                if (!(cert && edge_cert(S, P, D, xm, Le[it >> 1], it & 1, want_dg, o)) &&
+                    !edge_item(S, P, D, xm, dxm, Le[it >> 1], it & 1, pre, want_dg, o))
+                    continue;
                 ++cnt_e;
                 consume(o);
             }
@@ -753,7 +965,9 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
             const int32_t* Lp = C.point + D.t * C.cap_p;
             for (int it = lane; it < D.np; it += 32) {
                 ItemOut o;
-                if (!point_item(S, P, D, xm, dxm, Lp[it], pre, want_dg, o)) continue;
+                if (!(cert && point_cert(S, P, D, xm, Lp[it], want_dg, o)) &&
+                    !point_item(S, P, D, xm, dxm, Lp[it], pre, want_dg, o))
+                    continue;
                 ++cnt_p;
                 consume(o);
             }
@@ -865,13 +1079,14 @@ __device__ __forceinline__ void item_store(const ItemBufs& B, int64_t s, double 
 template <int NK, class T>
 __global__ void __launch_bounds__(256)
 k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
-            const double* __restrict__ frame, const int32_t* __restrict__ items, ItemBufs B,
-            int32_t* __restrict__ list, int32_t* __restrict__ n_list, int32_t* __restrict__ n_list2,
-            long long* counters) {
+            const double* __restrict__ dx, const double* __restrict__ frame, const int32_t* __restrict__ items,
+            ItemBufs B, int32_t* __restrict__ list, int32_t* __restrict__ n_list, int32_t* __restrict__ n_list2,
+            long long* counters, bool cert) {
     const int64_t n = *B.n;
     if (n > B.cap) return;
     const bool pre = P.precision == IPC_PREC_MIXED;
-    long long cnt_eval = 0;
+    const bool want_dg = dx != nullptr;
+    long long cnt_eval = 0, cnt_f = 0, cnt_e = 0, cnt_p = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     // whole warps iterate together (the list append is per warp)
     for (int64_t sb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); sb < n; sb += stride) {
@@ -880,26 +1095,43 @@ k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, con
         if (s < n) {
             const int i = B.owner[s];
             const int q = (int)(s - items[2 * i]);
-            const TriData D = load_tri(S, C, x, nullptr, frame, i);
+            const TriData D = load_tri(S, C, x, cert ? dx : nullptr, frame, i);
             const ItemRef R = item_ref<NK>(D, q);
             keep = true;
             face = R.kind == 0;
+            bool certified = false;
+            ItemOut o;
             if (R.kind == 0) {
                 ++cnt_eval;
                 if (pre) {
-                    const FaceSample F = face_sample(P, D, R.k, false);
-                    const int32_t* M = S.mtri + 3 * (int64_t)C.face[D.t * C.cap_f + R.j];
+                    const FaceSample F = face_sample(P, D, R.k, cert && want_dg);
+                    const int32_t m = C.face[D.t * C.cap_f + R.j];
+                    const int32_t* M = S.mtri + 3 * (int64_t)m;
                     keep = face_pre(P, D, F, ld3(xm, M[0]), ld3(xm, M[1]), ld3(xm, M[2]));
+                    certified = keep && cert && face_cert<NK>(S, P, D, F, xm, m, want_dg, o);
+                    cnt_f += certified;
                 }
             } else if (R.kind == 1) {
                 if (pre) {
                     const int32_t me = C.edge[D.t * C.cap_e + R.j];
                     keep = edge_pre(P, D, ld3(xm, S.medge[2 * (int64_t)me]), ld3(xm, S.medge[2 * (int64_t)me + 1]));
+                    certified = keep && cert && edge_cert(S, P, D, xm, me, R.k, want_dg, o);
+                    cnt_e += certified;
                 }
             } else if (pre) {
-                keep = point_pre(P, D, ld3(xm, C.point[D.t * C.cap_p + R.j]));
+                const int32_t u = C.point[D.t * C.cap_p + R.j];
+                keep = point_pre(P, D, ld3(xm, u));
+                certified = keep && cert && point_cert(S, P, D, xm, u, want_dg, o);
+                cnt_p += certified;
             }
-            if (!keep) {
+            if (certified) {
+                // an active item evaluated from certified FP32 geometry
+                double e, amin;
+                T c1, c2, b[3];
+                item_value<T>(o, want_dg, e, amin, c1, c2, b);
+                item_store<T>(B, s, e, amin, c1, c2, b);
+                keep = false;
+            } else if (!keep) {
                 const T z[3] = {T(0), T(0), T(0)};
                 item_store<T>(B, s, 0.0, INFINITY, T(0), T(0), z);
             }
@@ -911,8 +1143,15 @@ k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, con
         if (keep) list[face ? (int64_t)at_f : B.cap - 1 - at_o] = (int32_t)s;
     }
     if (counters) {
-        for (int o = 16; o > 0; o >>= 1) cnt_eval += shfl_x(cnt_eval, o);
-        if ((threadIdx.x & 31) == 0 && cnt_eval) atomic_add_ll(&counters[3], cnt_eval);
+        for (int o = 16; o > 0; o >>= 1) {
+            cnt_eval += shfl_x(cnt_eval, o);
+            cnt_f += shfl_x(cnt_f, o); cnt_e += shfl_x(cnt_e, o); cnt_p += shfl_x(cnt_p, o);
+        }
+        if ((threadIdx.x & 31) == 0 && (cnt_eval | cnt_f | cnt_e | cnt_p)) {
+            atomic_add_ll(&counters[3], cnt_eval);
+            atomic_add_ll(&counters[0], cnt_f); atomic_add_ll(&counters[1], cnt_e);
+            atomic_add_ll(&counters[2], cnt_p);
+        }
     }
 }
 
@@ -959,16 +1198,7 @@ k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const d
         }
         double e = 0.0, amin = INFINITY;
         T c1 = T(0), c2 = T(0), b[3] = {T(0), T(0), T(0)};
-        if (on) {
-            T Bv, dB, d2B;
-            barrier(o.g, o.eps, Bv, dB, d2B);
-            const T coef = (T)(o.kq * o.w * o.gamma);
-            e = (double)(coef * Bv);
-            c1 = coef * dB;
-            c2 = rmax(coef * d2B, T(0));
-            for (int cc = 0; cc < 3; ++cc) b[cc] = (T)o.b[cc];
-            if (want_dg && o.dg < 0.0) amin = 0.9 * o.g / (-o.dg);
-        }
+        if (on) item_value<T>(o, want_dg, e, amin, c1, c2, b);
         item_store<T>(B, s, e, amin, c1, c2, b);
     }
     if (counters) {
@@ -1179,8 +1409,11 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     GMCP_CUDA_TRY(cudaGetLastError());
     int32_t* n_list = c.misc_i32.p + kSlotItemList;
     int32_t* n_list2 = c.misc_i32.p + kSlotItemList2;
-    k_items_pre<NK, T><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, c.tri_frame.p,
-                                                       c.tri_items.p, B, c.item_list.p, n_list, n_list2, counters);
+    // certified FP32 items: mixed path, evaluation, static master
+    const bool cert = !kMaster && c.P.precision == IPC_PREC_MIXED && dxm == nullptr;
+    k_items_pre<NK, T><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
+                                                       c.tri_items.p, B, c.item_list.p, n_list, n_list2, counters,
+                                                       cert);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (kMaster) {
         k_items<NK, T, MODE><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,

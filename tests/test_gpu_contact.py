@@ -209,17 +209,27 @@ def test_contact_pass_fused_matches_separate_and_oracle(B, oracle_mod, prec, mov
     assert r["energy"] == e["energy"]
     assert torch.equal(r["grad"], e["grad"])
     assert torch.equal(r["hess"][2], e["hess"][2])
-    assert (r["alpha"], r["alpha_lin"], r["alpha_accd"]) == (c["alpha"], c["alpha_lin"], c["alpha_accd"])
+    assert r["alpha_accd"] == c["alpha_accd"]
+    if prec == "fp64" or moving:
+        assert (r["alpha"], r["alpha_lin"]) == (c["alpha"], c["alpha_lin"])
+    else:
+        # mixed, static master: samples evaluated from certified FP32 geometry
+        # bound the step with a lower bound of their gap, so the fused pass's
+        # alpha_lin never exceeds the FP64 bound of ccd_max_step and stays
+        # within 2e-3 of it
+        assert r["alpha_lin"] <= c["alpha_lin"] and r["alpha_lin"] >= (1 - 2e-3) * c["alpha_lin"]
+        assert r["alpha"] <= c["alpha"] and r["alpha"] >= (1 - 2e-3) * c["alpha"]
     # and against the oracle
     o = O.contact(x, sc.Y0)
     tol = 1e-12 if prec == "fp64" else 1e-5
     assert r["energy"] == pytest.approx(o["energy"], rel=tol)
     assert rel(r["grad"].cpu().numpy(), o["grad"]) < tol
     a, al, aa = O.ccd_max_step(x, dx, sc.Y0, xm1)
+    arel = 1e-9 if prec == "fp64" or moving else 2e-3
     assert r["alpha_accd"] == aa
-    assert r["alpha"] <= a and r["alpha"] == pytest.approx(a, rel=1e-9)
+    assert r["alpha"] <= a and r["alpha"] == pytest.approx(a, rel=arel)
     if np.isfinite(al):
-        assert r["alpha_lin"] <= al and r["alpha_lin"] == pytest.approx(al, rel=1e-9)
+        assert r["alpha_lin"] <= al and r["alpha_lin"] == pytest.approx(al, rel=arel)
     ctx.close()
 
 
