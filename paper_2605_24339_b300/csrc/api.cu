@@ -23,7 +23,7 @@ SceneView Ctx::view() const {
     S.me_tri_off = me_tri_off.p; S.me_tri = me_tri.p; S.mv_tri_off = mv_tri_off.p; S.mv_tri = mv_tri.p;
     S.mtri_own_edge = mtri_own_edge.p; S.mtri_own_vert = mtri_own_vert.p;
     S.stri_own_vert = stri_own_vert.p; S.stri_own_edge = stri_own_edge.p; S.sedge = sedge.p;
-    S.stri_env = stri_env.p; S.mtri_env = mtri_env.p;
+    S.stri_env = stri_env.p; S.mtri_env = mtri_env.p; S.mvert_env = mvert_env.p;
     S.X = X.p; S.Y0 = Y0.p; S.srest_box = srest_box.p; S.mrest_box = mrest_box.p;
     S.grid_org = grid_org.p; S.grid_inv = grid_inv.p; S.grid_dim = grid_dim.p; S.grid_off = grid_off.p;
     S.grid_org_f = grid_org_f.p; S.grid_inv_f = grid_inv_f.p;
@@ -258,6 +258,8 @@ cudaError_t grow_items(Ctx& c) {
     GMCP_CUDA_TRY(c.item_rd.ensure(2 * (size_t)c.cap_items));
     GMCP_CUDA_TRY(c.item_rt.ensure(5 * sizeof(double) * (size_t)c.cap_items));
     GMCP_CUDA_TRY(c.item_list.ensure((size_t)c.cap_items));
+    GMCP_CUDA_TRY(c.item_mask.ensure((size_t)c.cap_items / 32 + 2));
+    GMCP_CUDA_TRY(c.item_mid.ensure((size_t)c.cap_items));
     c.cp_graph.reset();
     return cudaSuccess;
 }
@@ -303,7 +305,8 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.item_rd.p, (uintptr_t)c.item_rt.p, (uintptr_t)c.cap_items, (uintptr_t)c.item_list.p, (uintptr_t)c.tri_G32.p, (uintptr_t)c.tri_S32.p, (uintptr_t)c.tri_n32.p,
             (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,
             (uintptr_t)c.cb_val64.p, (uintptr_t)c.u64_tmp.p, (uintptr_t)c.i64_tmp.p, (uintptr_t)c.misc_i32.p,
-            (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p};
+            (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p, (uintptr_t)c.mboxf_in.p, (uintptr_t)c.tri_f32.p,
+            (uintptr_t)c.ym32.p, (uintptr_t)c.item_mask.p, (uintptr_t)c.item_mid.p};
 }
 
 // Capture one pass on the context's private capture stream (nothing runs);
@@ -785,6 +788,12 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
     CK(c.sedge.upload(sedge.data(), sedge.size(), s));
     CK(c.stri_env.upload(s_env.data(), s_env.size(), s));
     CK(c.mtri_env.upload(m_env.data(), m_env.size(), s));
+    {
+        std::vector<int32_t> mv_env((size_t)nmv + 1, 0);
+        for (int e = 0; e < c.n_env; ++e)
+            for (int64_t u = c.env_mvert_off[e]; u < c.env_mvert_off[e + 1]; ++u) mv_env[u] = e;
+        CK(c.mvert_env.upload(mv_env.data(), mv_env.size(), s));
+    }
     CK(c.X.upload(sc->pad_rest, 3 * nv, s));
     CK(c.Y0.upload(sc->m_rest, 3 * nmv, s));
     CK(c.srest_box.upload(sbox.data(), sbox.size(), s));

@@ -182,7 +182,8 @@ __constant__ float c_rule_f[2][16][6];
 // ---------------------------------------------------------------------------
 __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
                                  const double* __restrict__ dxm, float* __restrict__ mboxf,
-                                 int4* __restrict__ mcell, int32_t* __restrict__ cnt) {
+                                 int4* __restrict__ mcell, int32_t* __restrict__ cnt,
+                                 float* __restrict__ mboxf_in) {
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int32_t* T = S.mtri + 3 * m;
@@ -212,6 +213,10 @@ __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
         flo[c] = lo_f32(lo[c]); fhi[c] = hi_f32(hi[c]);
         mag[c] = fabsf(flo[c]) + fabsf(fhi[c]);
         mboxf[6 * m + c] = flo[c]; mboxf[6 * m + 3 + c] = fhi[c];
+        // FP32 bounds inside the exact static box (empty for a swept box,
+        // which is not the box the exact face test uses)
+        mboxf_in[6 * m + c] = dxm ? INFINITY : __double2float_ru(lo[c]);
+        mboxf_in[6 * m + 3 + c] = dxm ? -INFINITY : __double2float_rd(hi[c]);
     }
     const int e = S.mtri_env[m];
     I3 a, b;
@@ -668,12 +673,17 @@ template <int NK>
 __global__ void __launch_bounds__(256)
 k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
                 const double* __restrict__ x, const double* __restrict__ xm,
-                const float* __restrict__ mboxf) {
+                const float* __restrict__ mboxf, const float* __restrict__ mboxf_in) {
     const int n = min(*W.n, W.cap);
     const double eps = P.dhat;
     // eps rounded up, with a relative slack that covers the FP64 rounding of
     // the grown master box
     const float eps_up = __double2float_ru(eps * (1.0 + 0x1p-20));
+    // and rounded down with the same slack: a sample bound inside the inner
+    // FP32 box grown by eps_dn is inside the FP64 grown box, whose bounds
+    // (lo - eps, hi + eps, one rounding each) are closer to the exact box
+    // than eps 2^-20
+    const float eps_dn = __double2float_rd(eps * (1.0 - 0x1p-20));
     const double (*rule)[3] = c_rule[P.L - 1];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int2 pr = W.p[i];
@@ -690,14 +700,20 @@ k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
             own_v[j] = S.mtri_own_vert[3 * (int64_t)m + j];
         }
         const int32_t* T = S.stri + 3 * t;
-        // face: FP32 pre-test on conservative sample bounds, then the exact test
-        bool maybe = false;
+        // face: FP32 tests on conservative sample bounds -- certainly outside
+        // every grown box (no pair), certainly inside one (a pair) -- then
+        // the exact test for the rest
+        bool maybe = false, sure = false;
         {
-            float L[3], H[3];
-            for (int c = 0; c < 3; ++c) { L[c] = __fsub_rd(Bf[c], eps_up); H[c] = __fadd_ru(Bf[3 + c], eps_up); }
+            const float* Bi = mboxf_in + 6 * (int64_t)m;
+            float L[3], H[3], Li[3], Hi[3];
+            for (int c = 0; c < 3; ++c) {
+                L[c] = __fsub_rd(Bf[c], eps_up); H[c] = __fadd_ru(Bf[3 + c], eps_up);
+                Li[c] = __fsub_ru(Bi[c], eps_dn); Hi[c] = __fadd_rd(Bi[3 + c], eps_dn);
+            }
             const float (*rf)[6] = c_rule_f[P.L - 1];
-            for (int q = 0; q < NK && !maybe; ++q) {
-                bool in = true;
+            for (int q = 0; q < NK && !sure; ++q) {
+                bool in = true, inside = true;
                 for (int c = 0; c < 3 && in; ++c) {
                     // bounds of ((b0 x0 + b1 x1) + b2 x2) with b >= 0
                     float lo = 0.0f, hi = 0.0f;
@@ -707,11 +723,15 @@ k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
                         hi = __fadd_ru(hi, __fmul_ru(xh >= 0.0f ? rf[q][3 + a] : rf[q][a], xh));
                     }
                     in = !(hi < L[c] || lo > H[c]);
+                    inside = inside && lo >= Li[c] && hi <= Hi[c];
                 }
-                maybe = in;
+                maybe = maybe || in;
+                sure = in && inside;
             }
         }
-        if (maybe) {
+        if (sure) {
+            cand_append(C, t, 0, m);
+        } else if (maybe) {
             double x0[3], x1[3], x2[3];
             load3(x, T[0], x0); load3(x, T[1], x1); load3(x, T[2], x2);
             double B[6];
@@ -1135,6 +1155,7 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     cudaStream_t s = c.stream;
     GMCP_CUDA_TRY(c.mcell.ensure((size_t)c.nmt + 1));
     GMCP_CUDA_TRY(c.mboxf.ensure(6 * (size_t)c.nmt + 6));
+    GMCP_CUDA_TRY(c.mboxf_in.ensure(6 * (size_t)c.nmt + 6));
     GMCP_CUDA_TRY(c.cell_cnt.ensure((size_t)c.n_cells + 1));
     GMCP_CUDA_TRY(c.cell_start.ensure((size_t)c.n_cells + 2));
     GMCP_CUDA_TRY(c.scan_tmp.ensure(2 * scan_tmp_size(c.n_cells)));
@@ -1142,7 +1163,8 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     const int B = 256;
     const unsigned g = (unsigned)((c.nmt + B - 1) / B);
     if (c.nmt > 0) {
-        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mboxf.p, c.mcell.p, c.cell_cnt.p);
+        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mboxf.p, c.mcell.p, c.cell_cnt.p,
+                                         c.mboxf_in.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     // scan into start + 1 (start[0] = 0), which the fill advances in place
@@ -1228,9 +1250,9 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
                                                           c.cell_ent.p, W);
         GMCP_CUDA_TRY(cudaGetLastError());
         if (P.nk == 4)
-            k_contact_exact<4><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mboxf.p);
+            k_contact_exact<4><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mboxf.p, c.mboxf_in.p);
         else
-            k_contact_exact<16><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mboxf.p);
+            k_contact_exact<16><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mboxf.p, c.mboxf_in.p);
         GMCP_CUDA_TRY(cudaGetLastError());
         if (lazy) break;   // the caller reads the overflow slot after it synchronises
         int32_t need = 0;

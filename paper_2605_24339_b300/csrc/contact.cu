@@ -326,6 +326,8 @@ __global__ void k_pass_begin(int32_t* misc, int hess) {
     misc[kSlotVCount] = 0;
     misc[kSlotItemList] = 0;
     misc[kSlotItemList2] = 0;
+    misc[kSlotItemMid] = 0;
+    misc[kSlotItemMid2] = 0;
     if (hess) {
         const int32_t h = ++misc[kSlotHPass];
         misc[kSlotBCount + (h & 1)] = 0;
@@ -375,10 +377,16 @@ __global__ void k_touch(SceneView S, CandView C, TouchArgs A) {
 // reserves a contiguous range of slots for them (items[2 i] = first slot,
 // items[2 i + 1] = count; the ranges' order depends on scheduling, the
 // per-triangle results do not) and adds them to *n_items.
+// With tf32 != NULL (mixed path) it also writes tf32[64 i ...]: the nk face
+// samples ((b0 x0 + b1 x1) + b2 x2, FP64) minus the environment's grid
+// origin, rounded to FP32 (3 nk floats), the unit normal in FP32 at
+// [48, 51) and the three vertices minus the origin in FP32 at [51, 60): the
+// inputs of the FP32 pre-filter of the sample items.
 __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ x,
                             double* __restrict__ frame, int nk, int32_t* __restrict__ items,
                             int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp,
-                            const int32_t* __restrict__ misc) {
+                            const int32_t* __restrict__ misc, float* __restrict__ tf32 = nullptr,
+                            int L = 1) {
     const int n_active = *C.n_active;
     const int32_t ps = tri_stamp ? misc[kSlotPass] : 0;
     const int lane = threadIdx.x & 31;
@@ -403,6 +411,21 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
             f[3] = 0.5 * clen;
             f[4] = cr0.x / clen0; f[5] = cr0.y / clen0; f[6] = cr0.z / clen0;
             f[7] = 1e-12 * (fabs(x0.x) + fabs(x0.y) + fabs(x0.z)) + 1e-30;
+            if (tf32) {
+                const int e = S.stri_env[t];
+                const V3<double> org = {S.grid_org[3 * e], S.grid_org[3 * e + 1], S.grid_org[3 * e + 2]};
+                float* o = tf32 + 64 * (int64_t)i;
+                for (int k = 0; k < nk; ++k) {
+                    double b[3] = {c_rule[L - 1][k][0], c_rule[L - 1][k][1], c_rule[L - 1][k][2]};
+                    const V3<float> xs = tof(interp(b, x0, x1, x2) - org);
+                    o[3 * k] = xs.x; o[3 * k + 1] = xs.y; o[3 * k + 2] = xs.z;
+                }
+                o[48] = (float)f[0]; o[49] = (float)f[1]; o[50] = (float)f[2];
+                const V3<float> v0 = tof(x0 - org), v1 = tof(x1 - org), v2 = tof(x2 - org);
+                o[51] = v0.x; o[52] = v0.y; o[53] = v0.z;
+                o[54] = v1.x; o[55] = v1.y; o[56] = v1.z;
+                o[57] = v2.x; o[58] = v2.y; o[59] = v2.z;
+            }
             if (items) {
                 const int32_t* cnt = C.count + 4 * t;
                 n = min(cnt[0], C.cap_f) * nk + 2 * min(cnt[1], C.cap_e) + min(cnt[2], C.cap_p);
@@ -1036,7 +1059,64 @@ struct ItemBufs {
     void* rt;            // [cap][5] c1, c2, b0, b1, b2 (T)
     const int32_t* n;    // items requested
     int64_t cap;
+    uint32_t* mask;      // [cap / 32 + 1] bit set: the slot holds a record (else it contributes nothing)
 };
+
+// master vertices minus their environment's grid origin, rounded to FP32
+// (w = 0): the master side of the face items' FP32 pre-filter
+__global__ void k_master_f32(SceneView S, const double* __restrict__ xm, float4* __restrict__ ym32) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= S.nmv) return;
+    const int e = S.mvert_env[u];
+    ym32[u] = make_float4((float)(xm[3 * u] - S.grid_org[3 * e]), (float)(xm[3 * u + 1] - S.grid_org[3 * e + 1]),
+                          (float)(xm[3 * u + 2] - S.grid_org[3 * e + 2]), 0.0f);
+}
+
+// FP32 pre-filter of a face item in its environment's frame (coordinates
+// relative to the grid origin, rounded once from FP64 values): true only
+// when the exact FP64 test (face_geom<double> with g < eps <= eps_max)
+// certainly fails.  Each coordinate carries an absolute error of at most
+// 2^-24 of its magnitude, so differences of two carry at most
+// del = 2^-23 max|v|.  From there (first order, then widened):
+//   N = e1 x e2 is within rel_N |N| of the exact normal, rel_N = 8 del
+//   (l1 + l2) / |N| + 1e-5;
+//   a cast with N.n_s >= (rel_N + 1e-3) |N| certainly faces away; one with
+//   N.n_s > -(rel_N + 0.05) |N| is left to the later tests;
+//   the gap g = N.d / N.n_s is within tol_g = (2 rel_N (|d| + |g|) + 8 del)
+//   / cos + 1e-4 (|d| + |g|), cos = -N.n_s / |N|;
+//   the hit point's barycentric coordinates are within tol_b = 0.02 +
+//   4 (tol_g + 4 del) / h_min, h_min the triangle's smallest height.
+__device__ __forceinline__ bool face_reject_f32(V3<float> xs, V3<float> ns, V3<float> y0, V3<float> y1, V3<float> y2,
+                                                float eps_max) {
+    const float R = rmax(rmax(fabsf(xs.x), rmax(fabsf(xs.y), fabsf(xs.z))),
+                         rmax(rmax(fabsf(y0.x), rmax(fabsf(y0.y), fabsf(y0.z))),
+                              rmax(rmax(fabsf(y1.x), rmax(fabsf(y1.y), fabsf(y1.z))),
+                                   rmax(fabsf(y2.x), rmax(fabsf(y2.y), fabsf(y2.z))))));
+    const float del = 1.1920929e-7f * R;   // 2^-23 R
+    const V3<float> e1 = y1 - y0, e2 = y2 - y0, N = cross(e1, e2);
+    const float nN = sqrtf(dot(N, N));
+    const float l1 = sqrtf(dot(e1, e1)), l2 = sqrtf(dot(e2, e2));
+    const float rel_N = 8.0f * del * (l1 + l2) / nN + 1e-5f;
+    const float den = dot(N, ns);
+    if (!(nN > 0.0f)) return false;
+    if (den >= (rel_N + 1e-3f) * nN) return true;           // faces away
+    if (den > -(rel_N + 0.05f) * nN) return false;           // near grazing: later tests decide
+    const float cosn = -den / nN;
+    const V3<float> d = y0 - xs;
+    const float g = dot(N, d) / den;
+    const float dn = sqrtf(dot(d, d));
+    const float tol_g = (2.0f * rel_N * (dn + fabsf(g)) + 8.0f * del) / cosn + 1e-4f * (dn + fabsf(g));
+    if (g > eps_max * (1.0f + 1e-6f) + tol_g || g < -tol_g) return true;
+    const V3<float> q = g * ns - d;    // hit point relative to y0
+    const float a = dot(e1, e1), bb = dot(e1, e2), c = dot(e2, e2);
+    const float r1 = dot(q, e1), r2 = dot(q, e2);
+    const float det = a * c - bb * bb;
+    const float v = (c * r1 - bb * r2) / det, w = (a * r2 - bb * r1) / det;
+    const float l3 = sqrtf(dot(e2 - e1, e2 - e1));
+    const float hmin = nN / rmax(l1, rmax(l2, l3));
+    const float tol_b = 0.02f + 4.0f * (tol_g + 4.0f * del) / hmin;
+    return rmin(1.0f - v - w, rmin(v, w)) < -tol_b;
+}
 
 __global__ void k_fill_owner(CandView C, const int32_t* __restrict__ items, ItemBufs B) {
     if ((int64_t)*B.n > B.cap) return;
@@ -1071,57 +1151,160 @@ __device__ __forceinline__ void item_store(const ItemBufs& B, int64_t s, double 
     rt[5 * s + 2] = b[0]; rt[5 * s + 3] = b[1]; rt[5 * s + 4] = b[2];
 }
 
-// Phase 1, one thread per item slot: the FP32 pre-test only.  Items that
-// fail it get their (empty) contribution here; the others are listed for
-// phase 2, which then runs the FP64 geometry on full warps (most of the
-// slots fail the pre-test, and a warp instruction on the FP64 pipe costs
-// the same however few of its lanes are active).
-template <int NK, class T>
+// FP32 pre-filter of an edge or point item in the environment's frame: true
+// only when the exact FP64 test certainly fails.  An edge (a != b) or a
+// master vertex (a == b) has no active sample when the plane distances
+// n_s . (y - x0) of both ends are certainly above eps_max or below 0
+// (plane_gap_maybe's bound plus 8 del for the frame's rounding, del =
+// 2^-23 max|v|), or when both ends are certainly outside one edge of the
+// slave triangle (bary_f's bound plus 16 del / h for the frame's rounding,
+// h the slave triangle's smallest height); for a vertex, when it is
+// certainly outside any slave edge.
+__device__ __forceinline__ bool edge_reject_f32(V3<float> x0, V3<float> x1, V3<float> x2, V3<float> ns,
+                                                V3<float> ya, V3<float> yb, float eps_max) {
+    float R = 0.0f;
+    for (const V3<float>& v : {x0, x1, x2, ya, yb}) R = rmax(R, rmax(fabsf(v.x), rmax(fabsf(v.y), fabsf(v.z))));
+    const float del = 1.1920929e-7f * R;
+    const V3<float> da = ya - x0, db = yb - x0;
+    if (!plane_gap_maybe(ns, da, db, eps_max, 8.0f * del)) return true;
+    const V3<float> e1 = x1 - x0, e2 = x2 - x0;
+    float fa[3], fb[3], ta, tb;
+    bool oka, okb;
+    bary_f(da, e1, e2, fa, ta, oka);
+    bary_f(db, e1, e2, fb, tb, okb);
+    if (!(oka && okb)) return false;
+    const V3<float> N = cross(e1, e2);
+    const float l1 = sqrtf(dot(e1, e1)), l2 = sqrtf(dot(e2, e2)), l3 = sqrtf(dot(e2 - e1, e2 - e1));
+    const float hmin = sqrtf(dot(N, N)) / rmax(l1, rmax(l2, l3));
+    const float slack = 16.0f * del / hmin;
+    for (int a = 0; a < 3; ++a)
+        if (fa[a] < -(ta + slack) && fb[a] < -(tb + slack)) return true;
+    return false;
+}
+
+// Phase 1, one thread per item slot: the FP32 pre-filter of the face items
+// in the environment's frame (face_reject_f32; no FP64 arithmetic), which
+// most face candidates of dense contact fail.  Items that fail it hold no
+// record (their mask bit stays clear and they contribute nothing); every
+// other item gets its mask bit and is listed for phase 1b.
+template <int NK>
 __global__ void __launch_bounds__(256)
-k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
-            const double* __restrict__ dx, const double* __restrict__ frame, const int32_t* __restrict__ items,
-            ItemBufs B, int32_t* __restrict__ list, int32_t* __restrict__ n_list, int32_t* __restrict__ n_list2,
-            long long* counters, bool cert) {
+k_items_pre(SceneView S, Params P, CandView C, const int32_t* __restrict__ items, ItemBufs B,
+            int32_t* __restrict__ mid, int32_t* __restrict__ n_mid, int32_t* __restrict__ n_mid2,
+            long long* counters, const float* __restrict__ tf32, const float4* __restrict__ ym32) {
     const int64_t n = *B.n;
     if (n > B.cap) return;
-    const bool pre = P.precision == IPC_PREC_MIXED;
-    const bool want_dg = dx != nullptr;
-    long long cnt_eval = 0, cnt_f = 0, cnt_e = 0, cnt_p = 0;
+    long long cnt_eval = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // whole warps iterate together (the list append is per warp)
+    // whole warps iterate together (mask words and list appends are per warp)
     for (int64_t sb = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); sb < n; sb += stride) {
         const int64_t s = sb + (threadIdx.x & 31);
-        bool keep = false, face = false;
+        bool pass = false, face = false;
         if (s < n) {
+            const int i = B.owner[s];
+            const int q = (int)(s - items[2 * i]);
+            const int64_t t = C.active[i];
+            const int nf = min(C.count[4 * t], C.cap_f), ne = min(C.count[4 * t + 1], C.cap_e);
+            pass = true;
+            const float* tf = tf32 ? tf32 + 64 * (int64_t)i : nullptr;
+            if (q < nf * NK) {
+                ++cnt_eval;
+                face = true;
+                if (tf) {
+                    const int k = q % NK;
+                    const int32_t* M = S.mtri + 3 * (int64_t)C.face[t * C.cap_f + q / NK];
+                    const float4 a = ym32[M[0]], b = ym32[M[1]], c = ym32[M[2]];
+                    pass = !face_reject_f32({tf[3 * k], tf[3 * k + 1], tf[3 * k + 2]}, {tf[48], tf[49], tf[50]},
+                                            {a.x, a.y, a.z}, {b.x, b.y, b.z}, {c.x, c.y, c.z}, (float)P.dhat);
+                }
+            } else if (tf) {
+                // an edge (either Gauss point) or a master vertex
+                const int r = q - nf * NK;
+                int32_t ia, ib;
+                if (r < 2 * ne) {
+                    const int32_t me = C.edge[t * C.cap_e + (r >> 1)];
+                    ia = S.medge[2 * (int64_t)me]; ib = S.medge[2 * (int64_t)me + 1];
+                } else {
+                    ia = ib = C.point[t * C.cap_p + (r - 2 * ne)];
+                }
+                const float4 a = ym32[ia], b = ym32[ib];
+                pass = !edge_reject_f32({tf[51], tf[52], tf[53]}, {tf[54], tf[55], tf[56]}, {tf[57], tf[58], tf[59]},
+                                        {tf[48], tf[49], tf[50]}, {a.x, a.y, a.z}, {b.x, b.y, b.z}, (float)P.dhat);
+            }
+        }
+        // one mask word per 32 slots (the warp's slots start at a multiple of 32)
+        const unsigned word = __ballot_sync(0xffffffffu, pass);
+        if ((threadIdx.x & 31) == 0 && sb < n) B.mask[sb >> 5] = word;
+        // faces from the front of the list, edges and points from the back
+        const int at_f = warp_reserve_c(pass && face, n_mid);
+        const int at_o = warp_reserve_c(pass && !face, n_mid2);
+        if (pass) mid[face ? (int64_t)at_f : B.cap - 1 - at_o] = (int32_t)s;
+    }
+    if (counters) {
+        for (int o = 16; o > 0; o >>= 1) cnt_eval += shfl_x(cnt_eval, o);
+        if ((threadIdx.x & 31) == 0 && cnt_eval) atomic_add_ll(&counters[3], cnt_eval);
+    }
+}
+
+// Phase 1b, one thread per item past the pre-filter (full warps): the
+// local-frame FP32 pre-tests of the mixed path (face_pre, edge_pre,
+// point_pre), which reject; then, for the evaluation with a static master,
+// the certified FP32 evaluation (face_cert, edge_cert, point_cert), which
+// stores the item's record.  Rejected items get an empty record; the others
+// are listed for phase 2 (faces from the front of the list, edges and points
+// from the back, so that phase 2 runs warps of one kind).  The FP64 path
+// lists every item.
+template <int NK, class T, bool FACES>
+__global__ void __launch_bounds__(256)
+k_items_mid(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
+            const double* __restrict__ dx, const double* __restrict__ frame, const int32_t* __restrict__ items,
+            ItemBufs B, const int32_t* __restrict__ mid, const int32_t* __restrict__ n_mid,
+            int32_t* __restrict__ list, int32_t* __restrict__ n_list, int32_t* __restrict__ n_list2,
+            long long* counters, bool cert) {
+    if ((int64_t)*B.n > B.cap) return;
+    const int nm = *n_mid;
+    const bool pre = P.precision == IPC_PREC_MIXED;
+    const bool want_dg = dx != nullptr;
+    long long cnt_f = 0, cnt_e = 0, cnt_p = 0;
+    const int stride = gridDim.x * blockDim.x;
+    for (int cb = blockIdx.x * blockDim.x + (threadIdx.x & ~31); cb < nm; cb += stride) {
+        const int c = cb + (threadIdx.x & 31);
+        bool keep = false, face = FACES;
+        int64_t s = 0;
+        if (c < nm) {
+            s = FACES ? mid[c] : mid[B.cap - 1 - c];
             const int i = B.owner[s];
             const int q = (int)(s - items[2 * i]);
             const TriData D = load_tri(S, C, x, cert ? dx : nullptr, frame, i);
             const ItemRef R = item_ref<NK>(D, q);
             keep = true;
-            face = R.kind == 0;
             bool certified = false;
             ItemOut o;
-            if (R.kind == 0) {
-                ++cnt_eval;
+            // the certified evaluation first (most items past the pre-filter
+            // are active), then the local reject tests for the rest
+            if (FACES) {
                 if (pre) {
                     const FaceSample F = face_sample(P, D, R.k, cert && want_dg);
                     const int32_t m = C.face[D.t * C.cap_f + R.j];
-                    const int32_t* M = S.mtri + 3 * (int64_t)m;
-                    keep = face_pre(P, D, F, ld3(xm, M[0]), ld3(xm, M[1]), ld3(xm, M[2]));
-                    certified = keep && cert && face_cert<NK>(S, P, D, F, xm, m, want_dg, o);
+                    certified = cert && face_cert<NK>(S, P, D, F, xm, m, want_dg, o);
+                    if (!certified) {
+                        const int32_t* M = S.mtri + 3 * (int64_t)m;
+                        keep = face_pre(P, D, F, ld3(xm, M[0]), ld3(xm, M[1]), ld3(xm, M[2]));
+                    }
                     cnt_f += certified;
                 }
             } else if (R.kind == 1) {
                 if (pre) {
                     const int32_t me = C.edge[D.t * C.cap_e + R.j];
-                    keep = edge_pre(P, D, ld3(xm, S.medge[2 * (int64_t)me]), ld3(xm, S.medge[2 * (int64_t)me + 1]));
-                    certified = keep && cert && edge_cert(S, P, D, xm, me, R.k, want_dg, o);
+                    certified = cert && edge_cert(S, P, D, xm, me, R.k, want_dg, o);
+                    if (!certified)
+                        keep = edge_pre(P, D, ld3(xm, S.medge[2 * (int64_t)me]), ld3(xm, S.medge[2 * (int64_t)me + 1]));
                     cnt_e += certified;
                 }
             } else if (pre) {
                 const int32_t u = C.point[D.t * C.cap_p + R.j];
-                keep = point_pre(P, D, ld3(xm, u));
-                certified = keep && cert && point_cert(S, P, D, xm, u, want_dg, o);
+                certified = cert && point_cert(S, P, D, xm, u, want_dg, o);
+                if (!certified) keep = point_pre(P, D, ld3(xm, u));
                 cnt_p += certified;
             }
             if (certified) {
@@ -1136,19 +1319,15 @@ k_items_pre(SceneView S, Params P, CandView C, const double* __restrict__ x, con
                 item_store<T>(B, s, 0.0, INFINITY, T(0), T(0), z);
             }
         }
-        // face survivors from the front of the list, edge and point survivors
-        // from the back, so that the FP64 phase runs warps of one kind
         const int at_f = warp_reserve_c(keep && face, n_list);
         const int at_o = warp_reserve_c(keep && !face, n_list2);
         if (keep) list[face ? (int64_t)at_f : B.cap - 1 - at_o] = (int32_t)s;
     }
     if (counters) {
         for (int o = 16; o > 0; o >>= 1) {
-            cnt_eval += shfl_x(cnt_eval, o);
             cnt_f += shfl_x(cnt_f, o); cnt_e += shfl_x(cnt_e, o); cnt_p += shfl_x(cnt_p, o);
         }
-        if ((threadIdx.x & 31) == 0 && (cnt_eval | cnt_f | cnt_e | cnt_p)) {
-            atomic_add_ll(&counters[3], cnt_eval);
+        if ((threadIdx.x & 31) == 0 && (cnt_f | cnt_e | cnt_p)) {
             atomic_add_ll(&counters[0], cnt_f); atomic_add_ll(&counters[1], cnt_e);
             atomic_add_ll(&counters[2], cnt_p);
         }
@@ -1231,6 +1410,7 @@ k_tri_reduce(CandView C, const double* __restrict__ frame, const int32_t* __rest
         Acc<T> A;
         A.zero();
         auto take = [&](int64_t s) {
+            if (!((B.mask[s >> 5] >> (s & 31)) & 1u)) return;   // contributes nothing
             const T b[3] = {rt[5 * s + 2], rt[5 * s + 3], rt[5 * s + 4]};
             A.add(B.rd[2 * s], rt[5 * s], rt[5 * s + 1], b);
             A.amin = rmin(A.amin, B.rd[2 * s + 1]);
@@ -1394,26 +1574,49 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     GMCP_CUDA_TRY(c.item_rd.ensure(2 * (size_t)c.cap_items));
     GMCP_CUDA_TRY(c.item_rt.ensure(5 * sizeof(T) * (size_t)c.cap_items));
     GMCP_CUDA_TRY(c.item_list.ensure((size_t)c.cap_items));
+    GMCP_CUDA_TRY(c.item_mask.ensure((size_t)c.cap_items / 32 + 2));
+    GMCP_CUDA_TRY(c.item_mid.ensure((size_t)c.cap_items));
     int32_t* n_items = c.misc_i32.p + 16;
     GMCP_CUDA_TRY(cudaMemsetAsync(n_items, 0, sizeof(int32_t), c.stream));
     if (kMaster) {
         // outside a contact pass: fresh item lists, and no pass stamps
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + kSlotItemList, 0, sizeof(int32_t), c.stream));
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + kSlotItemList2, 0, sizeof(int32_t), c.stream));
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + kSlotItemMid, 0, 2 * sizeof(int32_t), c.stream));
+    }
+    // the FP32 face pre-filter's inputs (mixed path): samples per active
+    // triangle and master vertices, both in the environment's frame
+    const bool f32pre = c.P.precision == IPC_PREC_MIXED && c.nmv > 0;
+    if (f32pre) {
+        GMCP_CUDA_TRY(c.tri_f32.ensure(64 * (size_t)c.ns + 64));
+        GMCP_CUDA_TRY(c.ym32.ensure(4 * (size_t)c.nmv + 4));
+        k_master_f32<<<(unsigned)((c.nmv + 255) / 256), 256, 0, c.stream>>>(c.view(), xm, (float4*)c.ym32.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
     }
     k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, c.tri_items.p, n_items,
-                                               kMaster ? nullptr : c.tri_stamp.p, c.misc_i32.p);
+                                               kMaster ? nullptr : c.tri_stamp.p, c.misc_i32.p,
+                                               f32pre ? c.tri_f32.p : nullptr, c.P.L);
     GMCP_CUDA_TRY(cudaGetLastError());
-    ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items};
+    ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items, c.item_mask.p};
     k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
     GMCP_CUDA_TRY(cudaGetLastError());
     int32_t* n_list = c.misc_i32.p + kSlotItemList;
     int32_t* n_list2 = c.misc_i32.p + kSlotItemList2;
     // certified FP32 items: mixed path, evaluation, static master
     const bool cert = !kMaster && c.P.precision == IPC_PREC_MIXED && dxm == nullptr;
-    k_items_pre<NK, T><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
-                                                       c.tri_items.p, B, c.item_list.p, n_list, n_list2, counters,
-                                                       cert);
+    int32_t* n_mid = c.misc_i32.p + kSlotItemMid;
+    int32_t* n_mid2 = c.misc_i32.p + kSlotItemMid2;
+    k_items_pre<NK><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), c.tri_items.p, B, c.item_mid.p, n_mid,
+                                                    n_mid2, counters, f32pre ? c.tri_f32.p : nullptr,
+                                                    f32pre ? (const float4*)c.ym32.p : nullptr);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    k_items_mid<NK, T, true><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
+                                                             c.tri_items.p, B, c.item_mid.p, n_mid, c.item_list.p,
+                                                             n_list, n_list2, counters, cert);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    k_items_mid<NK, T, false><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
+                                                              c.tri_items.p, B, c.item_mid.p, n_mid2, c.item_list.p,
+                                                              n_list, n_list2, counters, cert);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (kMaster) {
         k_items<NK, T, MODE><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,

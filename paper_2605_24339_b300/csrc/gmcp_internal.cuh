@@ -74,6 +74,7 @@ struct SceneView {
     const int32_t* sedge;         // [nse][2]
     const int32_t* stri_env;      // [ns]
     const int32_t* mtri_env;      // [nmt]
+    const int32_t* mvert_env;     // [nmv]
     const double* X;              // pad rest [nv][3]
     const double* Y0;             // master at t = 0 [nmv][3]
     const double* srest_box;      // [ns][6] rest box of slave tris (lo xyz, hi xyz)
@@ -278,6 +279,8 @@ constexpr int kSlotVCount = 20;  // vertices listed in this evaluation
 constexpr int kSlotBCount = 21;  // [2] blocks listed, by Hessian-pass parity
 constexpr int kSlotItemList = 23; // face items that passed the FP32 pre-tests (listed from the front)
 constexpr int kSlotItemList2 = 24; // edge and point items that passed (listed from the back)
+constexpr int kSlotItemMid = 25;   // face items past the FP32 pre-filter (listed from the front)
+constexpr int kSlotItemMid2 = 26;  // edge and point items past it (listed from the back)
 
 // ------------------------------------------------------------------------
 // the context
@@ -300,7 +303,7 @@ struct Ctx {
     // static device topology
     DBuf<int32_t> stri, mtri, medge, me_tri_off, me_tri, mv_tri_off, mv_tri;
     DBuf<int32_t> mtri_own_edge, mtri_own_vert, stri_own_vert, stri_own_edge, sedge;
-    DBuf<int32_t> stri_env, mtri_env;
+    DBuf<int32_t> stri_env, mtri_env, mvert_env;
     DBuf<double> X, Y0, srest_box, mrest_box;
     DBuf<double> grid_org, grid_inv;
     DBuf<float> grid_org_f, grid_inv_f;
@@ -318,6 +321,7 @@ struct Ctx {
     // per-call broad-phase buffers
     DBuf<int4> mcell;                           // [nmt] lowest cell (x, y, z) and env
     DBuf<float> mboxf;                          // conservative FP32 master boxes
+    DBuf<float> mboxf_in;                       // FP32 boxes inside the exact static master boxes
     DBuf<int2> ccd_pairs;                       // primitive pairs for ACCD
     DBuf<int2> coarse_pairs, coarse_swept;      // (query entry, master) pairs: contact, swept
     int32_t cap_ccd = 0, cap_coarse = 0, cap_coarse_swept = 0;
@@ -343,6 +347,10 @@ struct Ctx {
     DBuf<double> item_rd;                       // [cap_items][2] energy, step bound
     DBuf<unsigned char> item_rt;                // [cap_items][5] c1, c2, b (FP32 or FP64)
     DBuf<int32_t> item_list;                    // [cap_items] slots that passed the pre-tests
+    DBuf<uint32_t> item_mask;                   // [cap_items / 32 + 1] slots that hold a record
+    DBuf<int32_t> item_mid;                     // [cap_items] slots past the FP32 pre-filter
+    DBuf<float> tri_f32;                        // [n_active][64] FP32 samples, normal, vertices (env frame)
+    DBuf<float> ym32;                           // [nmv][4] master vertices in FP32 (env frame)
     int64_t cap_items = 0;
     // outputs touched by the active triangles (pass stamps and lists)
     DBuf<int32_t> tri_stamp, v_stamp, b_stamp;  // [ns], [nv], [cb_nnzb]
