@@ -69,6 +69,14 @@ typedef struct {
     void* stream;               /* cudaStream_t */
     int32_t use_graphs;         /* 1: replay repeated contact passes and PCG iteration
                                    chunks as captured CUDA graphs (same results) */
+    int32_t face_sampler;       /* face samples: 0 = the fixed slave-side rule of
+                                   face_rule_level (4^L centroids per slave triangle);
+                                   1 = the paper's clipped-overlap rule (Sec. 4.1: the
+                                   master triangle projected on the slave plane, clipped
+                                   by the slave triangle, fan-triangulated, 3-point Gauss
+                                   per sub-triangle; see ipc_face_clip_samples), with face
+                                   candidates the (slave tri, master tri) pairs whose boxes
+                                   meet within dhat */
 } ipc_params;
 
 /* Scene: a batch of independent environments concatenated; indices are

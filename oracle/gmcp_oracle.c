@@ -173,6 +173,7 @@ typedef struct {
     int nk; double* rule;  /* face rule barycentrics [nk][3] */
     int all_pairs;         /* 1: skip the broad phase and test every pair */
     double dhat_guard, kappa_guard;  /* primitive guard barrier (0: off) */
+    int face_clip;         /* 1: the paper's clipped-overlap face samples (reading R20) */
     int nsv, nse;
     int32_t* svert;        /* unique slave surface vertices */
     int32_t* sedge;        /* unique slave edges [nse][2] */
@@ -288,6 +289,7 @@ ORC_API void orc_scene_free(orc_scene* s) {
 }
 ORC_API int orc_scene_n_medges(const orc_scene* s) { return s->nme; }
 ORC_API void orc_scene_set_all_pairs(orc_scene* s, int flag) { s->all_pairs = flag; }
+ORC_API void orc_scene_set_face_clip(orc_scene* s, int flag) { s->face_clip = flag; }
 static int g_verbose = 0;
 ORC_API void orc_set_verbose(int v) { g_verbose = v; }
 ORC_API void orc_scene_medges(const orc_scene* s, int32_t* out) {
@@ -333,7 +335,17 @@ static int64_t candidates_sub(const orc_scene* s, int kind, const double* x, con
         int e = s->stri_env[t];
         double slo[3], shi[3];
         tri_box(x, T, slo, shi);
-        if (kind == 0) {
+        if (kind == 0 && s->face_clip) {
+            /* clipped-overlap face samples (reading R20): the slave tri's box
+             * meets the master tri's box grown by dhat */
+            for (int64_t m = s->env_mtri_off[e]; m < s->env_mtri_off[e + 1]; ++m) {
+                double lo[3], hi[3];
+                tri_box(xm, s->mtri + 3 * m, lo, hi);
+                int ok = 1;
+                for (int c = 0; c < 3 && ok && !s->all_pairs; ++c) ok = slo[c] <= hi[c] + eps && lo[c] - eps <= shi[c];
+                if (ok) ivec_push2(&v, t, (int32_t)m);
+            }
+        } else if (kind == 0) {
             for (int k = 0; k < s->nk; ++k) interp3(s->rule + 3 * k, x0, x1, x2, samp + 3 * k);
             for (int64_t m = s->env_mtri_off[e]; m < s->env_mtri_off[e + 1]; ++m) {
                 double lo[3], hi[3];
@@ -443,7 +455,8 @@ static int any_facing(const orc_scene* s, const double* xm, const int32_t* tris,
     return 0;
 }
 
-/* forward declarations (definitions with the CCD code below) */
+/* forward declarations (definitions with the CCD code and the clipper below) */
+ORC_API int orc_face_clip_samples(const double* xs, const double* xm, double* out);
 static double ps_dist2(const double* p, const double* a, const double* b);
 ORC_API double orc_pt_dist2(const double* p, const double* t0, const double* t1, const double* t2);
 ORC_API double orc_ee_dist2(const double* a0, const double* a1, const double* b0, const double* b1);
@@ -638,7 +651,41 @@ static void collect_samples(const orc_scene* s, const double* x, const double* x
             memset(&smp, 0, sizeof(smp));
             smp.stri = t; smp.feat = f;
             for (int c = 0; c < 3; ++c) smp.ns[c] = ns[c];
-            if (kind == 0) {
+            if (kind == 0 && s->face_clip) {
+                /* clipped-overlap face samples (Sec. 4.1 "Face samples", reading
+                 * R20): the pair counts when the master tri faces the slave;
+                 * each sample of the clipped overlap (orc_face_clip_samples) is
+                 * active when 0 < g < eps, eps from the same slave point at
+                 * rest (reading R5); weight = its Gauss weight, gamma =
+                 * H(min beta^m, delta_T) */
+                const int32_t* M = s->mtri + 3 * f;
+                const double *y0 = xm + 3 * M[0], *y1 = xm + 3 * M[1], *y2 = xm + 3 * M[2];
+                double e1[3], e2[3], N[3];
+                sub3(y1, y0, e1); sub3(y2, y0, e2); cross3(e1, e2, N);
+                if (!(dot3(N, ns) < 0.0)) continue;
+                double xs9[9], xm9[9], cs[96];
+                for (int c = 0; c < 3; ++c) {
+                    xs9[c] = x0[c]; xs9[3 + c] = x1[c]; xs9[6 + c] = x2[c];
+                    xm9[c] = y0[c]; xm9[3 + c] = y1[c]; xm9[6 + c] = y2[c];
+                }
+                int nsmp = orc_face_clip_samples(xs9, xm9, cs);
+                for (int k = 0; k < nsmp; ++k) {
+                    const double* o = cs + 8 * k;
+                    double g = o[6];
+                    if (!(g > 0.0)) continue;
+                    double xs0[3], g0, bm0[3]; int facing0;
+                    interp3(o, X0, X1, X2, xs0);
+                    int ok0 = face_geom(xs0, ns0, Y0 + 3 * M[0], Y0 + 3 * M[1], Y0 + 3 * M[2], &g0, bm0, &facing0);
+                    double eps = eps_from_ref(ok0, g0, eps_max);
+                    if (!(g < eps)) continue;
+                    smp.type = 2; smp.g = g; smp.eps = eps;
+                    smp.sv[0] = T[0]; smp.sv[1] = T[1]; smp.sv[2] = T[2];
+                    smp.w = o[7]; smp.gamma = orc_hermite(min3(o + 3), s->delta_T);
+                    smp.kq = s->kappa;
+                    for (int c = 0; c < 3; ++c) { smp.bs[c] = o[c]; smp.bm[c] = o[3 + c]; smp.mv[c] = M[c]; }
+                    svec_push(out, &smp);
+                }
+            } else if (kind == 0) {
                 /* face samples */
                 const int32_t* M = s->mtri + 3 * f;
                 const double *y0 = xm + 3 * M[0], *y1 = xm + 3 * M[1], *y2 = xm + 3 * M[2];

@@ -72,6 +72,7 @@ def _declare(L):
     L.orc_candidates.restype = I64; L.orc_candidates.argtypes = [P, I, P, P, C.POINTER(ip)]
     L.orc_free.argtypes = [P]
     L.orc_scene_set_all_pairs.argtypes = [P, I]
+    L.orc_scene_set_face_clip.argtypes = [P, I]
     L.orc_set_verbose.argtypes = [I]
     L.orc_scene_set_guard.argtypes = [P, D, D]
     L.orc_contact_lagged.argtypes = [P, P, P, P, I, P, P]
@@ -253,6 +254,7 @@ class Scene:
             p["dhat"], p["kappa"], p["kappa_edge"], p["kappa_point"], p["delta_T"],
             p["delta_e"], int(p["face_rule_level"]))
         lib().orc_scene_set_guard(self.h, p.get("dhat_guard", 0.0), p.get("kappa_guard", 0.0))
+        lib().orc_scene_set_face_clip(self.h, int(p.get("face_sampler", 0)))
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

@@ -39,7 +39,7 @@ class Params(C.Structure):
                 ("max_newton", C.c_int32), ("max_pcg", C.c_int32), ("max_halvings", C.c_int32),
                 ("ccd_slack", C.c_double), ("ccd_max_iter", C.c_int32), ("dhat_guard", C.c_double),
                 ("kappa_guard", C.c_double), ("device", C.c_int32), ("stream", C.c_void_p),
-                ("use_graphs", C.c_int32)]
+                ("use_graphs", C.c_int32), ("face_sampler", C.c_int32)]
 
 
 class SceneC(C.Structure):
@@ -248,6 +248,7 @@ def make_params(p: dict, precision="fp64", device=0, stream=0) -> Params:
     q.device = int(device)
     q.stream = C.c_void_p(int(stream)) if stream else None
     q.use_graphs = int(p.get("use_graphs", 1))
+    q.face_sampler = int(p.get("face_sampler", 0))
     return q
 
 

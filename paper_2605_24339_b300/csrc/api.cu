@@ -926,9 +926,9 @@ ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx*
         return IPC_ERR_ARG;
     }
     if (!(params->dhat > 0.0) || !(params->ccd_slack > 0.0 && params->ccd_slack < 1.0) ||
-        params->ccd_max_iter < 1 ||
+        params->ccd_max_iter < 1 || (params->face_sampler != 0 && params->face_sampler != 1) ||
         (params->precision != IPC_PREC_FP64 && params->precision != IPC_PREC_MIXED)) {
-        g_create_error = "ipc_create: invalid dhat, ccd_slack, ccd_max_iter or precision";
+        g_create_error = "ipc_create: invalid dhat, ccd_slack, ccd_max_iter, face_sampler or precision";
         return IPC_ERR_ARG;
     }
     int ndev = 0;
@@ -951,6 +951,7 @@ ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx*
         c.P.L = params->face_rule_level; c.P.nk = 1 << (2 * c.P.L);
         c.P.dhat_guard = params->dhat_guard; c.P.kappa_guard = params->kappa_guard;
         c.P.ccd_slack = params->ccd_slack; c.P.ccd_max_iter = params->ccd_max_iter;
+        c.P.face_clip = params->face_sampler;
         c.graphs = params->use_graphs != 0;
         c.n_env = scene->n_env;
         auto cp = [&](const int64_t* p) { return std::vector<int64_t>(p, p + scene->n_env + 1); };

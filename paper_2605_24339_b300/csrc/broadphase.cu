@@ -704,7 +704,19 @@ k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
         // every grown box (no pair), certainly inside one (a pair) -- then
         // the exact test for the rest
         bool maybe = false, sure = false;
-        {
+        if (P.face_clip) {
+            // clipped-overlap samples: the slave tri's box meets the master
+            // tri's box grown by eps (exact FP64 boxes, as for edges)
+            const double* qb = Q.box + 6 * (int64_t)li;
+            double B[6];
+            exact_mbox(S, xm, nullptr, m, B, B + 3);
+            bool ok = true;
+            for (int c = 0; c < 3 && ok; ++c) {
+                const double lo = B[c] - eps, hi = B[3 + c] + eps;
+                ok = qb[c] <= hi && lo <= qb[3 + c];
+            }
+            sure = ok;
+        } else {
             const float* Bi = mboxf_in + 6 * (int64_t)m;
             float L[3], H[3], Li[3], Hi[3];
             for (int c = 0; c < 3; ++c) {

@@ -31,6 +31,7 @@
 // are FP32; the energy sum stays FP64.
 #include <cfloat>
 
+#include "faceclip.cuh"
 #include "gmcp_internal.cuh"
 
 namespace gmcp {
@@ -378,10 +379,11 @@ __global__ void k_touch(SceneView S, CandView C, TouchArgs A) {
 // items[2 i + 1] = count; the ranges' order depends on scheduling, the
 // per-triangle results do not) and adds them to *n_items.
 // With tf32 != NULL (mixed path) it also writes tf32[64 i ...]: the nk face
-// samples ((b0 x0 + b1 x1) + b2 x2, FP64) minus the environment's grid
-// origin, rounded to FP32 (3 nk floats), the unit normal in FP32 at
-// [48, 51) and the three vertices minus the origin in FP32 at [51, 60): the
-// inputs of the FP32 pre-filter of the sample items.
+// samples relative to the environment's grid origin in FP32 (3 nk floats,
+// interpolated in FP32 from the vertices below, so within 2^-22 max|v| of
+// the exact samples), the unit normal in FP32 at [48, 51) and the three
+// vertices minus the origin, rounded to FP32, at [51, 60): the inputs of the
+// FP32 pre-filter of the sample items.
 __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ x,
                             double* __restrict__ frame, int nk, int32_t* __restrict__ items,
                             int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp,
@@ -415,13 +417,16 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
                 const int e = S.stri_env[t];
                 const V3<double> org = {S.grid_org[3 * e], S.grid_org[3 * e + 1], S.grid_org[3 * e + 2]};
                 float* o = tf32 + 64 * (int64_t)i;
+                const V3<float> v0 = tof(x0 - org), v1 = tof(x1 - org), v2 = tof(x2 - org);
                 for (int k = 0; k < nk; ++k) {
-                    double b[3] = {c_rule[L - 1][k][0], c_rule[L - 1][k][1], c_rule[L - 1][k][2]};
-                    const V3<float> xs = tof(interp(b, x0, x1, x2) - org);
-                    o[3 * k] = xs.x; o[3 * k + 1] = xs.y; o[3 * k + 2] = xs.z;
+                    // FP32 from the rounded vertices (within 2^-22 max|v| of the exact sample)
+                    const float b0 = (float)c_rule[L - 1][k][0], b1 = (float)c_rule[L - 1][k][1],
+                                b2 = (float)c_rule[L - 1][k][2];
+                    o[3 * k] = b0 * v0.x + b1 * v1.x + b2 * v2.x;
+                    o[3 * k + 1] = b0 * v0.y + b1 * v1.y + b2 * v2.y;
+                    o[3 * k + 2] = b0 * v0.z + b1 * v1.z + b2 * v2.z;
                 }
                 o[48] = (float)f[0]; o[49] = (float)f[1]; o[50] = (float)f[2];
-                const V3<float> v0 = tof(x0 - org), v1 = tof(x1 - org), v2 = tof(x2 - org);
                 o[51] = v0.x; o[52] = v0.y; o[53] = v0.z;
                 o[54] = v1.x; o[55] = v1.y; o[56] = v1.z;
                 o[57] = v2.x; o[58] = v2.y; o[59] = v2.z;
@@ -879,6 +884,48 @@ __device__ __forceinline__ void item_value(const ItemOut& o, bool want_dg, doubl
     if (want_dg && o.dg < 0.0) amin = 0.9 * o.g_step / (-o.dg);
 }
 
+// The paper's clipped-overlap face samples of slave tri D against master
+// tri m (Sec. 4.1 "Face samples", ipc_params.face_sampler = 1): the pair
+// counts when the master triangle faces the slave (N . n_s < 0); each clip
+// sample (fclip::clip_samples) is active when 0 < g < eps, eps from the same
+// slave point at rest cast onto the rest master (Eq. adaptive_eps, reading
+// R5), with weight w = its Gauss weight (area / 3) and gamma =
+// H(min beta^m, delta_T) (Eq. gamma).  emit(o) is called for each.
+template <class Emit>
+__device__ __forceinline__ int face_clip_items(const SceneView& S, const Params& P, const TriData& D,
+                                               const double* xm, const double* dxm, int32_t m, bool want_dg,
+                                               Emit&& emit) {
+    const int32_t* M = S.mtri + 3 * (int64_t)m;
+    const V3<double> y0 = ld3(xm, M[0]), y1 = ld3(xm, M[1]), y2 = ld3(xm, M[2]);
+    if (!(dot(cross(y1 - y0, y2 - y0), D.ns) < 0.0)) return 0;
+    const double* mb = S.mrest_box + 6 * (int64_t)m;
+    const bool far0 = rest_far(D.sb, D.sb + 3, mb, mb + 3, P.dhat);
+    auto p3 = [](V3<double> v) { return fclip::P3{v.x, v.y, v.z}; };
+    return fclip::clip_samples(p3(D.x0), p3(D.x1), p3(D.x2), p3(y0), p3(y1), p3(y2),
+                               [&](const double* bs, const double* bm, double g, double w) {
+        if (!(g > 0.0)) return;
+        double eps = P.dhat;
+        if (!far0) {
+            const V3<double> xs0 = interp(bs, D.X0, D.X1, D.X2);
+            double g0, bm0[3];
+            if (face_geom<double>(xs0, D.ns0, ld3(S.Y0, M[0]), ld3(S.Y0, M[1]), ld3(S.Y0, M[2]), g0, bm0))
+                eps = rmin(0.9 * g0, P.dhat);
+        }
+        if (!(g < eps)) return;
+        ItemOut o;
+        o.kq = P.kappa; o.w = w; o.gamma = hermite(min3(bm), P.delta_T);
+        o.g = g; o.g_step = g; o.eps = eps;
+        for (int c = 0; c < 3; ++c) { o.b[c] = bs[c]; o.mv[c] = M[c]; o.bm[c] = bm[c]; }
+        o.dg = 0.0;
+        if (want_dg) {
+            const double ds = dot(D.ns, interp(bs, D.dx0, D.dx1, D.dx2));
+            const double dm = dxm ? dot(D.ns, interp(bm, ld3(dxm, M[0]), ld3(dxm, M[1]), ld3(dxm, M[2]))) : 0.0;
+            o.dg = dm - ds;
+        }
+        emit(o);
+    });
+}
+
 // Warp per active triangle (persistent grid).  Used for the step bound and
 // the lagged energies of the line search, and for the contact evaluation
 // when the item buffer is too small (then run_if_over selects it).
@@ -923,7 +970,7 @@ __device__ void master_blocks(const ModeArgs& LG, const ItemOut& o, const int32_
     }
 }
 
-template <int NK, class T, int MODE>
+template <int NK, class T, int MODE, bool CLIP = false>
 __global__ void __launch_bounds__(256)
 k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
           const double* __restrict__ xm, double* __restrict__ triE, T* __restrict__ triG,
@@ -960,7 +1007,15 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
         };
         // face items (lane, lane + 32, ...): 32 is a multiple of NK, so each
         // lane keeps one sample
-        {
+        if (CLIP) {
+            // clipped-overlap samples: one lane per candidate pair
+            const int32_t* Lf = C.face + D.t * C.cap_f;
+            for (int j = lane; j < D.nf; j += 32)
+                cnt_eval += face_clip_items(S, P, D, xm, dxm, Lf[j], want_dg, [&](const ItemOut& o) {
+                    ++cnt_f;
+                    consume(o);
+                });
+        } else {
             const FaceSample F = face_sample(P, D, lane % NK, want_dg);
             const int32_t* Lf = C.face + D.t * C.cap_f;
             for (int it = lane; it < D.nf * NK; it += 32) {
@@ -1073,11 +1128,13 @@ __global__ void k_master_f32(SceneView S, const double* __restrict__ xm, float4*
 }
 
 // FP32 pre-filter of a face item in its environment's frame (coordinates
-// relative to the grid origin, rounded once from FP64 values): true only
-// when the exact FP64 test (face_geom<double> with g < eps <= eps_max)
-// certainly fails.  Each coordinate carries an absolute error of at most
-// 2^-24 of its magnitude, so differences of two carry at most
-// del = 2^-23 max|v|.  From there (first order, then widened):
+// relative to the grid origin: master vertices rounded once from FP64, the
+// sample interpolated in FP32 from rounded slave vertices): true only when
+// the exact FP64 test (face_geom<double> with g < eps <= eps_max) certainly
+// fails.  A master coordinate is within 2^-24 of its magnitude of the exact
+// value and a sample coordinate within 2^-22 max|v|, so the differences
+// below carry at most del = 2^-21 max|v|.  From there (first order, then
+// widened):
 //   N = e1 x e2 is within rel_N |N| of the exact normal, rel_N = 8 del
 //   (l1 + l2) / |N| + 1e-5;
 //   a cast with N.n_s >= (rel_N + 1e-3) |N| certainly faces away; one with
@@ -1092,7 +1149,7 @@ __device__ __forceinline__ bool face_reject_f32(V3<float> xs, V3<float> ns, V3<f
                          rmax(rmax(fabsf(y0.x), rmax(fabsf(y0.y), fabsf(y0.z))),
                               rmax(rmax(fabsf(y1.x), rmax(fabsf(y1.y), fabsf(y1.z))),
                                    rmax(fabsf(y2.x), rmax(fabsf(y2.y), fabsf(y2.z))))));
-    const float del = 1.1920929e-7f * R;   // 2^-23 R
+    const float del = 4.7683716e-7f * R;   // 2^-21 R
     const V3<float> e1 = y1 - y0, e2 = y2 - y0, N = cross(e1, e2);
     const float nN = sqrtf(dot(N, N));
     const float l1 = sqrtf(dot(e1, e1)), l2 = sqrtf(dot(e2, e2));
@@ -1254,25 +1311,29 @@ k_items_pre(SceneView S, Params P, CandView C, const int32_t* __restrict__ items
 // are listed for phase 2 (faces from the front of the list, edges and points
 // from the back, so that phase 2 runs warps of one kind).  The FP64 path
 // lists every item.
-template <int NK, class T, bool FACES>
+template <int NK, class T>
 __global__ void __launch_bounds__(256)
 k_items_mid(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
             const double* __restrict__ dx, const double* __restrict__ frame, const int32_t* __restrict__ items,
             ItemBufs B, const int32_t* __restrict__ mid, const int32_t* __restrict__ n_mid,
-            int32_t* __restrict__ list, int32_t* __restrict__ n_list, int32_t* __restrict__ n_list2,
-            long long* counters, bool cert) {
+            const int32_t* __restrict__ n_mid2, int32_t* __restrict__ list, int32_t* __restrict__ n_list,
+            int32_t* __restrict__ n_list2, long long* counters, bool cert) {
     if ((int64_t)*B.n > B.cap) return;
-    const int nm = *n_mid;
+    // faces (the front of the list) first, then edges and points (the back):
+    // only the warp at the boundary holds both kinds
+    const int nmf = *n_mid;
+    const int nm = nmf + *n_mid2;
     const bool pre = P.precision == IPC_PREC_MIXED;
     const bool want_dg = dx != nullptr;
     long long cnt_f = 0, cnt_e = 0, cnt_p = 0;
     const int stride = gridDim.x * blockDim.x;
     for (int cb = blockIdx.x * blockDim.x + (threadIdx.x & ~31); cb < nm; cb += stride) {
         const int c = cb + (threadIdx.x & 31);
-        bool keep = false, face = FACES;
+        const bool faces = c < nmf;
+        bool keep = false, face = faces;
         int64_t s = 0;
         if (c < nm) {
-            s = FACES ? mid[c] : mid[B.cap - 1 - c];
+            s = faces ? mid[c] : mid[B.cap - 1 - (c - nmf)];
             const int i = B.owner[s];
             const int q = (int)(s - items[2 * i]);
             const TriData D = load_tri(S, C, x, cert ? dx : nullptr, frame, i);
@@ -1282,7 +1343,7 @@ k_items_mid(SceneView S, Params P, CandView C, const double* __restrict__ x, con
             ItemOut o;
             // the certified evaluation first (most items past the pre-filter
             // are active), then the local reject tests for the rest
-            if (FACES) {
+            if (faces) {
                 if (pre) {
                     const FaceSample F = face_sample(P, D, R.k, cert && want_dg);
                     const int32_t m = C.face[D.t * C.cap_f + R.j];
@@ -1553,6 +1614,11 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     const int threads = 256;
     const int sms = sm_count(c.device);
     const int blocks = sms * c.tune_samples_bpsm;
+    // the warp-per-triangle kernel, instantiated for the face rule in use
+    auto launch_k_samples = [&](auto... a) {
+        if (c.P.face_clip) k_samples<NK, T, MODE, true><<<blocks, threads, 0, c.stream>>>(a...);
+        else k_samples<NK, T, MODE, false><<<blocks, threads, 0, c.stream>>>(a...);
+    };
     GMCP_CUDA_TRY(c.tri_frame.ensure(8 * (size_t)c.ns + 8));
     constexpr bool kMaster = MODE == MODE_MASTER || MODE == MODE_MASTER_HESS;
     if (MODE != MODE_EVAL && !kMaster) {
@@ -1560,7 +1626,19 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
                                                    nullptr, nullptr);
         GMCP_CUDA_TRY(cudaGetLastError());
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
-        k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
+        launch_k_samples(
+            c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG,
+            c.tri_frame.p, nullptr, 0);
+        return cudaGetLastError();
+    }
+    if (MODE == MODE_EVAL && c.P.face_clip) {
+        // clipped-overlap face samples: a variable number per pair, evaluated
+        // by the warp-per-triangle kernel (the items' fixed slots do not apply)
+        k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
+                                                   c.tri_stamp.p, c.misc_i32.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
+        launch_k_samples(
             c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG,
             c.tri_frame.p, nullptr, 0);
         return cudaGetLastError();
@@ -1610,13 +1688,9 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
                                                     n_mid2, counters, f32pre ? c.tri_f32.p : nullptr,
                                                     f32pre ? (const float4*)c.ym32.p : nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
-    k_items_mid<NK, T, true><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
-                                                             c.tri_items.p, B, c.item_mid.p, n_mid, c.item_list.p,
-                                                             n_list, n_list2, counters, cert);
-    GMCP_CUDA_TRY(cudaGetLastError());
-    k_items_mid<NK, T, false><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
-                                                              c.tri_items.p, B, c.item_mid.p, n_mid2, c.item_list.p,
-                                                              n_list, n_list2, counters, cert);
+    k_items_mid<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
+                                                      c.tri_items.p, B, c.item_mid.p, n_mid, n_mid2, c.item_list.p,
+                                                      n_list, n_list2, counters, cert);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (kMaster) {
         k_items<NK, T, MODE><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
@@ -1625,7 +1699,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
         GMCP_CUDA_TRY(cudaGetLastError());
         // oversized item sets: the warp-per-triangle kernel instead
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
-        k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
+        launch_k_samples(
             c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG,
             c.tri_frame.p, n_items, c.cap_items);
         return cudaGetLastError();
@@ -1642,7 +1716,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
                                                         G, Sm, N, alpha_bits);
     GMCP_CUDA_TRY(cudaGetLastError());
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
-    k_samples<NK, T, MODE><<<blocks, threads, 0, c.stream>>>(
+    launch_k_samples(
         c.view(), c.P, c.cand(), x, xm, c.tri_E.p, G, Sm, N, counters, dx, dxm, alpha_bits, LG,
         c.tri_frame.p, n_items, c.cap_items);
     return cudaGetLastError();

@@ -96,6 +96,7 @@ struct Params {
     double dhat_guard, kappa_guard;
     double ccd_slack;
     int ccd_max_iter;
+    int face_clip;         // 1: the paper's clipped-overlap face samples (ipc_params.face_sampler)
 };
 
 // Candidate list storage: fixed capacity per slave triangle.
