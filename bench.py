@@ -432,7 +432,8 @@ def precision_measurement(dev):
     accuracy against the all-FP64 path, on a pressed 24x24-quad indent (the
     FP64 path matches the FP64 CPU oracle to 1e-12, tests/test_gpu_contact.py),
     and what the FP64 anchors keep: the additive-CCD step (FP64 in both),
-    the linearised step bound and the line-search energies of one time step."""
+    the linearised step bound, and one implicit-Euler step (its line-search
+    energy sum and PCG dot products are FP64 in both precisions)."""
     import torch
     from paper_2605_24339_b300 import binding
     from paper_2605_24339_b300 import scenes as S
@@ -468,7 +469,28 @@ def precision_measurement(dev):
         "hess_block_max_rel": worst, "alpha_lin_rel": abs(al32 - al64) / al64 if np.isfinite(al64) else 0.0,
         "alpha_accd_equal": aa32 == aa64,
         "same_active_samples": all(c32[k] == c64[k] for k in ("face", "edge", "point")),
-        "gap_and_decisions": "FP64 in both paths (same active samples)"}
+        "gap_and_decisions": "FP64 in both paths, or FP32 certified to decide as FP64 (same active samples)"}
+    # one implicit-Euler step of the same pad pressed onto the sphere from the
+    # draped state: the FP64 anchors (line-search energy sum, PCG dot products,
+    # step bounds) are FP64 in both precisions
+    top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
+    steps = {}
+    for prec in ("fp64", "mixed"):
+        ctx = binding.Context(sc, precision=prec, device=dev, params={"pcg_rel_tol": 1e-6})
+        xs = torch.as_tensor(x.copy(), device="cuda")
+        vs = torch.as_tensor(sc.v_dirichlet.copy(), device="cuda")
+        r = ctx.newton_step(xs, vs)
+        steps[prec] = (xs.cpu().numpy(), r)
+        ctx.close()
+    (x64, r64), (x32, r32) = steps["fp64"], steps["mixed"]
+    disp = np.linalg.norm(x64 - x)
+    out["time_step"] = {
+        "status": [r64["status"], r32["status"]], "newton_iters": [r64["newton_iters"], r32["newton_iters"]],
+        "pcg_iters": [r64["pcg_iters"], r32["pcg_iters"]],
+        "position_rel_to_displacement": float(np.linalg.norm(x32 - x64) / disp) if disp > 0 else 0.0,
+        "incremental_potential_rel": abs(r32["energy"] - r64["energy"]) / abs(r64["energy"]),
+        "residual": [r64["residual"], r32["residual"]],
+        "note": "mixed (FP32 barrier, gradient, Hessian, PCG vectors and matrix) against FP64, same start state"}
     return out
 
 
@@ -914,11 +936,15 @@ def run_passes(args):
 
 def run_dense_passes(args):
     """--steps contact passes on the contact-dense workload with no timing
-    (the command line for ncu captures of its kernels)."""
+    (the command line for ncu captures of its kernels); --dense-quads sets the
+    pad's quads per side (256 in the measured workload; the plate scales with
+    it, keeping its 0.063 mm triangles)."""
     import torch
     from paper_2605_24339_b300 import binding
     from paper_2605_24339_b300 import scenes as S
-    sc, x_np = S.gel_dense(with_tets=False)
+    q = args.dense_quads
+    sc, x_np = S.gel_dense(n_quads=q, plate_quads=max(8, (442 * q) // 256), plate_size=28e-3 * q / 256,
+                           with_tets=False)
     ctx = binding.Context(sc, precision=args.precision)
     x = torch.as_tensor(x_np, device="cuda")
     dx = torch.zeros_like(x)
@@ -1014,6 +1040,8 @@ def main():
                     help="skip the time-step measurement (newton_step key)")
     ap.add_argument("--batch-envs", type=int, default=512,
                     help="environments in the batched measurement")
+    ap.add_argument("--dense-quads", type=int, default=256,
+                    help="--mode dense_passes: gel pad quads per side (256 = the measured workload)")
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
     ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "dualmap", "faceclip",
