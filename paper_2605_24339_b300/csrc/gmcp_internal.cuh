@@ -235,6 +235,19 @@ struct NewtonState {
     DBuf<double> alphas;                 // [8]
     DBuf<double> scal;                   // solver scalars
     DBuf<int32_t> bad;                   // inverted-tet flag
+    // environments: the PCG works per environment (own scalars, stopping,
+    // reductions), on rows padded per environment to a multiple of four
+    int n_env = 1;
+    DBuf<int32_t> vprow;                 // [nv] padded PCG row of each vertex
+    DBuf<int32_t> prow_v;                // [nvp] vertex of each padded row, -1 for padding
+    int64_t nblk_v = 0, nblk_p = 0;      // blocks of the vertex-row and padded-row kernels
+    DBuf<int4> blk_v, blk_p;             // per block: env, first row, end row, first block of the env
+    std::vector<int32_t> h_env_nblk_v, h_env_nblk_p;   // blocks per env
+    DBuf<int32_t> env_nblk_v, env_nblk_p;
+    DBuf<double> escal;                  // [n_env][kEnvScal] per-environment PCG scalars
+    DBuf<unsigned> ecount;               // [3][n_env] last-block counters (init/spmv, update, spare)
+    double* h_pcg = nullptr;             // pinned [n_env][4]: break, done, iterations (host reads)
+    ~NewtonState() { if (h_pcg) cudaFreeHost(h_pcg); }
 };
 
 // A captured CUDA graph and the arguments it was captured with.
@@ -466,7 +479,8 @@ cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double*
 cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess, double* Ec_dev, double* Ee_dev,
                             double* E_dev, double* gnorm2_dev);
 cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double* out);
-cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters);
+cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters,
+                      int* env_iters = nullptr);   // env_iters: [n_env] iterations per environment
 // elementwise helpers
 cudaError_t vec_axpy(Ctx& c, int64_t n, double a, const double* x, const double* p, double* out);
 cudaError_t vec_xhat(Ctx& c, const double* x, const double* v, double* xhat);

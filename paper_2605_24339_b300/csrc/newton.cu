@@ -479,6 +479,7 @@ enum : int {
 // beta in int32 / FP32, so that the per-iteration kernels test and read them
 // without FP64 instructions (each costs a full warp issue on the B300's
 // narrow FP64 pipe).
+constexpr int kEnvScal = 16;   // doubles of per-environment scalars
 __device__ __forceinline__ int* pcg_ictl(double* scal) { return reinterpret_cast<int*>(scal + kCtlI); }
 __device__ __forceinline__ float* pcg_fctl(double* scal) { return reinterpret_cast<float*>(scal + kCtlF); }
 template <class V>
@@ -532,10 +533,13 @@ __device__ __forceinline__ void block_sums256(R v0, R v1, double (*sh)[kPcgThrea
     }
 }
 
-// Each block contributes NV values (v0, v1); returns true in the last block
-// to arrive, where thread 0 then holds the fixed-order totals in *t0, *t1.
+// Each block contributes NV values (v0, v1) to its environment's sums;
+// returns true in the environment's last block to arrive, where thread 0
+// then holds the environment's fixed-order totals in *t0, *t1.  The blocks
+// of one environment are consecutive (first block b_first, nb of them) and
+// count at *counter; part is [2][gridDim].
 template <int NV, class R>
-__device__ bool last_block_sums(R v0, R v1, double* part /* [2][gridDim] */, unsigned* counter, double* t0,
+__device__ bool last_block_sums(R v0, R v1, double* part, unsigned* counter, int b_first, int nb, double* t0,
                                 double* t1) {
     __shared__ double sh[2][kPcgThreads / 32];
     __shared__ bool am_last;
@@ -545,16 +549,16 @@ __device__ bool last_block_sums(R v0, R v1, double* part /* [2][gridDim] */, uns
         part[blockIdx.x] = b0;
         if (NV > 1) part[gridDim.x + blockIdx.x] = b1;
         __threadfence();
-        am_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        am_last = atomicAdd(counter, 1u) == (unsigned)nb - 1u;
     }
     __syncthreads();
     if (!am_last) return false;
     __threadfence();
     const volatile double* vp = part;
     double s0 = 0.0, s1 = 0.0;
-    for (unsigned k = threadIdx.x; k < gridDim.x; k += kPcgThreads) {
-        s0 += vp[k];
-        if (NV > 1) s1 += vp[gridDim.x + k];
+    for (int k = threadIdx.x; k < nb; k += kPcgThreads) {
+        s0 += vp[b_first + k];
+        if (NV > 1) s1 += vp[gridDim.x + b_first + k];
     }
     __syncthreads();   // the first pass's readers of sh are done
     block_sums256<NV, double>(s0, s1, sh, t0, t1);
@@ -600,34 +604,44 @@ __device__ __forceinline__ void load_blk(const double* A, int64_t g, int lane, d
 // diagonal is the first stored block of its row
 template <class TA, class V>
 __global__ void k_diag_inv(int64_t nv, const int32_t* __restrict__ goff, const TA* __restrict__ A,
-                           V* __restrict__ Pinv) {
+                           const int32_t* __restrict__ vprow, V* __restrict__ Pinv) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     double D[9], I[9];
     const int64_t g = goff[v >> 5];
     for (int q = 0; q < 9; ++q) D[q] = (double)A[sell_idx<TA>(g, (int)(v & 31), q)];
     inv3(D, I);
-    for (int q = 0; q < 9; ++q) Pinv[9 * v + q] = (V)I[q];
+    const int64_t r = vprow[v];
+    for (int q = 0; q < 9; ++q) Pinv[9 * r + q] = (V)I[q];
 }
 
 // x = 0, r = b, z = P^-1 b; p = z (FP64), or, where the SpMV forms the
 // direction, p (first of the pair) = 0 and beta = 0 so that it forms p = z;
 // b.b and r.z
+// Launch geometry of the per-row kernels: block b covers rows [B.y, B.z) of
+// environment B.x (B = blk[b]; B.w its environment's first block), so every
+// dot product is a per-environment sum whose blocks start at the
+// environment's first row.  Vertex-row kernels (init, SpMV): 256 vertex
+// rows a block; padded-row kernels (update, direction): 512 padded rows.
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bvec, double* __restrict__ x,
+k_pcg_init(const int4* __restrict__ blk, const int32_t* __restrict__ env_nblk, const int32_t* __restrict__ vprow,
+           const V* __restrict__ Pinv, const double* __restrict__ bvec, double* __restrict__ x,
            V* __restrict__ xh, V* __restrict__ xl, V* __restrict__ r, V* __restrict__ z, V* __restrict__ p, double* part,
-           unsigned* counter, double* scal, double rel_tol) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+           unsigned* counters, double* escal, double rel_tol) {
+    const int4 B = blk[blockIdx.x];
+    double* scal = escal + kEnvScal * B.x;
+    const int64_t iv = (int64_t)B.y + threadIdx.x;   // vertex row
     V bb = V(0), rz = V(0);
-    if (i < nv) {
-        const V b0 = (V)bvec[3 * i], b1 = (V)bvec[3 * i + 1], b2 = (V)bvec[3 * i + 2];
+    if (iv < B.z) {
+        const int64_t i = vprow[iv];                  // padded row
+        const V b0 = (V)bvec[3 * iv], b1 = (V)bvec[3 * iv + 1], b2 = (V)bvec[3 * iv + 2];
         V zz[3];
         mul33(Pinv + 9 * i, b0, b1, b2, zz);
         const V bv[3] = {b0, b1, b2};
         for (int q = 0; q < 3; ++q) {
             if (sizeof(V) == 8) {
-                x[3 * i + q] = 0.0;
+                x[3 * iv + q] = 0.0;
             } else {
                 xh[3 * i + q] = V(0);
                 xl[3 * i + q] = V(0);
@@ -642,7 +656,7 @@ k_pcg_init(int64_t nv, const V* __restrict__ Pinv, const double* __restrict__ bv
         p[4 * i + 3] = V(0);
     }
     double tb, tr;
-    if (last_block_sums<2, V>(bb, rz, part, counter, &tb, &tr) && threadIdx.x == 0) {
+    if (last_block_sums<2, V>(bb, rz, part, counters + B.x, B.w, env_nblk[B.x], &tb, &tr) && threadIdx.x == 0) {
         scal[kBb] = tb;
         scal[kRz] = tr;
         scal[kThr] = rel_tol * sqrt(tb);
@@ -684,22 +698,26 @@ __device__ __forceinline__ void dir_row(const V* p_old, const V* z, int64_t j, V
 // the breakdown flag).
 template <class TA, class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_spmv(int64_t nv, int64_t nvp, const int32_t* __restrict__ rp, const int32_t* __restrict__ goff,
+k_pcg_spmv(const int4* __restrict__ blk, const int32_t* __restrict__ env_nblk, const int32_t* __restrict__ vprow,
+           int64_t nvp, const int32_t* __restrict__ rp, const int32_t* __restrict__ goff,
            const int32_t* __restrict__ sci, const int32_t* __restrict__ llen, const int32_t* __restrict__ lgoff,
            const int32_t* __restrict__ lcol, const int32_t* __restrict__ lmir, const TA* __restrict__ A,
-           V* __restrict__ ppair, const V* __restrict__ z, V* __restrict__ Ap, double* part, unsigned* counter,
-           double* scal) {
+           V* __restrict__ ppair, const V* __restrict__ z, V* __restrict__ Ap, double* part, unsigned* counters,
+           double* escal) {
     pdl_wait();
     pdl_trigger();
+    const int4 B = blk[blockIdx.x];
+    double* scal = escal + kEnvScal * B.x;
     if (pcg_ictl(scal)[0] != 0) return;
     const int it = pcg_ictl(scal)[1];
     constexpr bool kFused = PcgDir<V>::kFused;
     const V be = pcg_scalar<V>(scal, kBe);
     const V* p_old = kFused ? ppair + 4 * nvp * (it & 1) : ppair;
     V* p_new = ppair + 4 * nvp * ((it + 1) & 1);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = (int64_t)B.y + threadIdx.x;   // vertex row (the matrix storage's row)
     V pap = V(0);
-    if (i < nv) {
+    if (i < B.z) {
+        const int64_t ir = vprow[i];                  // its padded row (the vectors' row)
         const int64_t g0 = goff[i >> 5];
         const int lane = (int)(i & 31);
         const int ll = llen[i];
@@ -764,16 +782,17 @@ k_pcg_spmv(int64_t nv, int64_t nvp, const int32_t* __restrict__ rp, const int32_
             a2 += b[6] * p0 + b[7] * p1 + b[8] * p2;
         }
         const V y0 = (V)a0, y1 = (V)a1, y2 = (V)a2;
-        Ap[3 * i] = y0;
-        Ap[3 * i + 1] = y1;
-        Ap[3 * i + 2] = y2;
+        Ap[3 * ir] = y0;
+        Ap[3 * ir + 1] = y1;
+        Ap[3 * ir + 2] = y2;
         V q0, q1, q2;
-        dir_row(p_old, z, i, be, q0, q1, q2);
-        if constexpr (kFused) reinterpret_cast<float4*>(p_new)[i] = make_float4(q0, q1, q2, 0.f);
+        dir_row(p_old, z, ir, be, q0, q1, q2);
+        if constexpr (kFused) reinterpret_cast<float4*>(p_new)[ir] = make_float4(q0, q1, q2, 0.f);
         pap = q0 * y0 + q1 * y1 + q2 * y2;
     }
     double t, unused;
-    if (last_block_sums<1, V>(pap, V(0), part, counter, &t, &unused) && threadIdx.x == 0) {
+    if (last_block_sums<1, V>(pap, V(0), part, counters + B.x, B.w, env_nblk[B.x], &t, &unused) &&
+        threadIdx.x == 0) {
         scal[kPAp] = t;
         if (t > 0.0) {
             scal[kAl] = scal[kRz] / t;
@@ -873,20 +892,22 @@ __device__ __forceinline__ void add_pair(float& hi, float& lo, float v) {
 // below nv) when V is FP64, else the float pair (xh, xl).
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __restrict__ x, V* __restrict__ xh,
+k_pcg_update(const int4* __restrict__ blk, const int32_t* __restrict__ env_nblk, const int32_t* __restrict__ prow_v,
+             int64_t nvp, const V* __restrict__ Pinv, double* __restrict__ x, V* __restrict__ xh,
              V* __restrict__ xl, V* __restrict__ r, V* __restrict__ z, const V* __restrict__ ppair,
-             const V* __restrict__ Ap, double* part, unsigned* counter, double* scal) {
+             const V* __restrict__ Ap, double* part, unsigned* counters, double* escal) {
     constexpr int R = PcgRows<V>::R;
     pdl_wait();
     pdl_trigger();
+    const int4 B = blk[blockIdx.x];
+    double* scal = escal + kEnvScal * B.x;
     if (pcg_ictl(scal)[0] != 0) return;
     const int it = pcg_ictl(scal)[1];
     const V* p = PcgDir<V>::kFused ? ppair + 4 * nvp * ((it + 1) & 1) : ppair;   // this iteration's direction
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i0 = R * t;
+    const int64_t i0 = (int64_t)B.y + R * threadIdx.x;   // padded rows (an environment's range is a multiple of 4)
     const V alv = pcg_scalar<V>(scal, kAl);
     V rr = V(0), rz = V(0);
-    if (i0 < nvp) {
+    if (i0 < B.z) {
         V pv[4 * R], av[3 * R], rv[3 * R];
         ldv<V, 4 * R>(p + 4 * i0, pv);
         ldv<V, 3 * R>(Ap + 3 * i0, av);
@@ -903,9 +924,11 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
             stv<V, 3 * R>(xl + 3 * i0, lv);
         } else {
 #pragma unroll
-            for (int a = 0; a < R; ++a)
-                if (i0 + a < nv)
-                    for (int q = 0; q < 3; ++q) x[3 * (i0 + a) + q] += (double)alv * (double)pv[4 * a + q];
+            for (int a = 0; a < R; ++a) {
+                const int64_t v = prow_v[i0 + a];
+                if (v >= 0)
+                    for (int q = 0; q < 3; ++q) x[3 * v + q] += (double)alv * (double)pv[4 * a + q];
+            }
         }
 #pragma unroll
         for (int e = 0; e < 3 * R; ++e) rv[e] -= alv * av[e];
@@ -928,7 +951,7 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
             }
     }
     double trr, trz;
-    if (last_block_sums<2, V>(rr, rz, part, counter, &trr, &trz) && threadIdx.x == 0) {
+    if (last_block_sums<2, V>(rr, rz, part, counters + B.x, B.w, env_nblk[B.x], &trr, &trz) && threadIdx.x == 0) {
         scal[kRr] = trr;
         if (sqrt(trr) <= scal[kThr]) {
             scal[kDone] = 1.0;
@@ -949,12 +972,14 @@ k_pcg_update(int64_t nv, int64_t nvp, const V* __restrict__ Pinv, double* __rest
 // p = z + beta p (FP64 path; z [nvp][3], p [nvp][4]), two rows per thread
 template <class V>
 __global__ void __launch_bounds__(kPcgThreads)
-k_pcg_dir(int64_t nvp, const V* __restrict__ z, V* __restrict__ p, double* scal) {
+k_pcg_dir(const int4* __restrict__ blk, const V* __restrict__ z, V* __restrict__ p, double* escal) {
     pdl_wait();
     pdl_trigger();
+    const int4 B = blk[blockIdx.x];
+    double* scal = escal + kEnvScal * B.x;
     if (pcg_ictl(scal)[0] != 0) return;
-    const int64_t i0 = 2 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-    if (i0 >= nvp) return;
+    const int64_t i0 = (int64_t)B.y + 2 * threadIdx.x;
+    if (i0 >= B.z) return;
     const V be = (V)scal[kBe];
     V zv[6], pv[8];
     ldv<V, 6>(z + 3 * i0, zv);
@@ -966,11 +991,13 @@ k_pcg_dir(int64_t nvp, const V* __restrict__ z, V* __restrict__ p, double* scal)
     stv<V, 8>(p + 4 * i0, pv);
 }
 
-// x = hi + lo in FP64 (mixed path, after the solve)
-__global__ void k_pair_to_f64(int64_t n, const float* __restrict__ hi, const float* __restrict__ lo,
-                              double* __restrict__ x) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] = (double)hi[i] + (double)lo[i];
+// x = hi + lo in FP64 (mixed path, after the solve), per vertex from its padded row
+__global__ void k_pair_to_f64(int64_t nv, const int32_t* __restrict__ vprow, const float* __restrict__ hi,
+                              const float* __restrict__ lo, double* __restrict__ x) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int64_t r = vprow[v];
+    for (int q = 0; q < 3; ++q) x[3 * v + q] = (double)hi[3 * r + q] + (double)lo[3 * r + q];
 }
 
 // elementwise products into w (for a fixed-order dot product)
@@ -1144,20 +1171,21 @@ template <class TA, class V>
 static void pcg_queue(Ctx& c, const TA* A, const V* Pinv, V* r, V* z, V* p, V* Ap, double* xout, V* xh, V* xl,
                       int count) {
     NewtonState& N = *c.newton;
-    const int64_t nv = c.nv;
     cudaStream_t s = c.stream;
-    const unsigned g_row = nblk(nv, kPcgThreads);
     const int64_t nvp = N.nvp;
-    const unsigned g_multi = nblk(nvp / PcgRows<V>::R, kPcgThreads);
+    const unsigned g_row = (unsigned)N.nblk_v, g_multi = (unsigned)N.nblk_p;
+    unsigned* cnt_spmv = N.ecount.p + N.n_env;
+    unsigned* cnt_upd = N.ecount.p + 2 * N.n_env;
     for (int j = 0; j < count; ++j) {
-        launch_pdl(k_pcg_spmv<TA, V>, g_row, s, nv, nvp, (const int32_t*)N.rp.p, (const int32_t*)N.goff.p,
+        launch_pdl(k_pcg_spmv<TA, V>, g_row, s, (const int4*)N.blk_v.p, (const int32_t*)N.env_nblk_v.p,
+                   (const int32_t*)N.vprow.p, nvp, (const int32_t*)N.rp.p, (const int32_t*)N.goff.p,
                    (const int32_t*)N.sci.p, (const int32_t*)N.llen.p, (const int32_t*)N.lgoff.p,
-                   (const int32_t*)N.lcol.p, (const int32_t*)N.lmir.p, A, p, (const V*)z, Ap, N.part.p,
-                   N.counters.p + 1, N.scal.p);
-        launch_pdl(k_pcg_update<V>, g_multi, s, nv, nvp, Pinv, xout, xh, xl, r, z, (const V*)p, (const V*)Ap,
-                   N.part.p, N.counters.p + 2, N.scal.p);
-        if (!PcgDir<V>::kFused)
-            launch_pdl(k_pcg_dir<V>, nblk(nvp / 2, kPcgThreads), s, nvp, (const V*)z, p, N.scal.p);
+                   (const int32_t*)N.lcol.p, (const int32_t*)N.lmir.p, A, p, (const V*)z, Ap, N.part.p, cnt_spmv,
+                   N.escal.p);
+        launch_pdl(k_pcg_update<V>, g_multi, s, (const int4*)N.blk_p.p, (const int32_t*)N.env_nblk_p.p,
+                   (const int32_t*)N.prow_v.p, nvp, Pinv, xout, xh, xl, r, z, (const V*)p, (const V*)Ap, N.part.p,
+                   cnt_upd, N.escal.p);
+        if (!PcgDir<V>::kFused) launch_pdl(k_pcg_dir<V>, g_multi, s, (const int4*)N.blk_p.p, (const V*)z, p, N.escal.p);
     }
 }
 
@@ -1170,8 +1198,9 @@ static cudaError_t pcg_enqueue_iters(Ctx& c, double* xout, int count) {
         pcg_queue<double, double>(c, N.A64.p, N.Pinv.p, N.r.p, N.z.p, N.p.p, N.Ap.p, xout, nullptr, nullptr,
                                   count);
     GMCP_CUDA_TRY(cudaGetLastError());
-    // stop flags and iteration count for the host
-    return cudaMemcpyAsync(c.pin->pcg, N.scal.p + kBreak, 3 * sizeof(double), cudaMemcpyDeviceToHost, c.stream);
+    // every environment's stop flags and iteration count for the host
+    return cudaMemcpy2DAsync(N.h_pcg, 4 * sizeof(double), N.escal.p + kBreak, kEnvScal * sizeof(double),
+                             3 * sizeof(double), N.n_env, cudaMemcpyDeviceToHost, c.stream);
 }
 
 constexpr int kPcgChunk = 16;
@@ -1187,7 +1216,9 @@ static bool pcg_chunk_graph(Ctx& c, double* xout) {
                                         (uintptr_t)N.scal.p, (uintptr_t)N.counters.p, (uintptr_t)c.pin,
                                         (uintptr_t)N.xh32.p, (uintptr_t)N.xl32.p, (uintptr_t)N.sci.p,
                                         (uintptr_t)N.goff.p, (uintptr_t)N.llen.p, (uintptr_t)N.lgoff.p,
-                                        (uintptr_t)N.lcol.p, (uintptr_t)N.lmir.p};
+                                        (uintptr_t)N.lcol.p, (uintptr_t)N.lmir.p, (uintptr_t)N.escal.p,
+                                        (uintptr_t)N.ecount.p, (uintptr_t)N.h_pcg, (uintptr_t)N.blk_v.p,
+                                        (uintptr_t)N.blk_p.p};
     if (c.pcg_graph.exec && c.pcg_graph.key == key) return true;
     c.pcg_graph.reset();
     if (!c.cap_stream && cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -1222,22 +1253,27 @@ static bool pcg_chunk_graph(Ctx& c, double* xout) {
 // iteration's update is skipped) or after max_it iterations.  The host reads
 // the flags once per 16 iterations (a captured graph per chunk when graphs
 // are on); kernels after the stop return at once.  Returns the iterations.
-cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters) {
+cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters,
+                      int* env_iters) {
     NewtonState& N = *c.newton;
     const int64_t nv = c.nv;
     cudaStream_t s = c.stream;
-    const unsigned gr = nblk(nv, kPcgThreads);
+    const unsigned gr = (unsigned)N.nblk_v;
     if (c.P.precision == IPC_PREC_MIXED) {
-        k_diag_inv<float, float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.goff.p, N.A32.p, N.Pinv32.p);
-        k_pcg_init<float><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv32.p, b, xout, N.xh32.p, N.xl32.p, N.r32.p,
-                                                     N.z32.p, N.p32.p, N.part.p, N.counters.p, N.scal.p, rel_tol);
+        k_diag_inv<float, float><<<nblk(nv, 256), 256, 0, s>>>(nv, N.goff.p, N.A32.p, N.vprow.p, N.Pinv32.p);
+        k_pcg_init<float><<<gr, kPcgThreads, 0, s>>>(N.blk_v.p, N.env_nblk_v.p, N.vprow.p, N.Pinv32.p, b, xout,
+                                                     N.xh32.p, N.xl32.p, N.r32.p, N.z32.p, N.p32.p, N.part.p,
+                                                     N.ecount.p, N.escal.p, rel_tol);
     } else {
-        k_diag_inv<double, double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.goff.p, N.A64.p, N.Pinv.p);
-        k_pcg_init<double><<<gr, kPcgThreads, 0, s>>>(nv, N.Pinv.p, b, xout, nullptr, nullptr, N.r.p, N.z.p,
-                                                      N.p.p, N.part.p, N.counters.p, N.scal.p, rel_tol);
+        k_diag_inv<double, double><<<nblk(nv, 256), 256, 0, s>>>(nv, N.goff.p, N.A64.p, N.vprow.p, N.Pinv.p);
+        k_pcg_init<double><<<gr, kPcgThreads, 0, s>>>(N.blk_v.p, N.env_nblk_v.p, N.vprow.p, N.Pinv.p, b, xout,
+                                                      nullptr, nullptr, N.r.p, N.z.p, N.p.p, N.part.p,
+                                                      N.ecount.p, N.escal.p, rel_tol);
     }
     GMCP_CUDA_TRY(cudaGetLastError());
     const bool graph = c.graphs && !c.prof.on && pcg_chunk_graph(c, xout);
+    const int ne = N.n_env;
+    for (int e = 0; e < ne; ++e) if (env_iters) env_iters[e] = max_it;
     *iters = max_it;
     for (int it = 0; it < max_it;) {
         const int chunk = std::min(kPcgChunk, max_it - it);
@@ -1245,14 +1281,21 @@ cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int
         else GMCP_CUDA_TRY(pcg_enqueue_iters(c, xout, chunk));
         it += chunk;
         GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-        const double* hb = c.pin->pcg;
-        if (hb[0] != 0.0 || hb[1] != 0.0) {
-            *iters = (int)hb[2];
-            break;
-        }
+        bool all = true;
+        for (int e = 0; e < ne && all; ++e) all = N.h_pcg[4 * e] != 0.0 || N.h_pcg[4 * e + 1] != 0.0;
+        if (all) break;
     }
+    // iterations: per environment, and the largest (the solve's length)
+    int mx = 0;
+    for (int e = 0; e < ne; ++e) {
+        const bool stopped = N.h_pcg[4 * e] != 0.0 || N.h_pcg[4 * e + 1] != 0.0;
+        const int k = stopped ? (int)N.h_pcg[4 * e + 2] : max_it;
+        if (env_iters) env_iters[e] = k;
+        mx = std::max(mx, k);
+    }
+    *iters = mx;
     if (c.P.precision == IPC_PREC_MIXED) {
-        k_pair_to_f64<<<nblk(3 * nv, 256), 256, 0, s>>>(3 * nv, N.xh32.p, N.xl32.p, xout);
+        k_pair_to_f64<<<nblk(nv, 256), 256, 0, s>>>(nv, N.vprow.p, N.xh32.p, N.xl32.p, xout);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -1406,6 +1449,56 @@ cudaError_t newton_setup(Ctx& c) {
     N.ngroups = ngroups;
     N.nlgroups = nlgroups;
 
+    // Environments: PCG rows of environment e are padded to a multiple of
+    // four and laid out one environment after the other; the PCG kernels'
+    // blocks never span two environments (256 vertex rows or 512 padded rows
+    // a block, counted from the environment's first row).  With one
+    // environment the padded rows are the vertices, padded at the end.
+    const int ne = c.n_env;
+    N.n_env = ne;
+    std::vector<int64_t> poff(ne + 1, 0);
+    for (int e = 0; e < ne; ++e) {
+        const int64_t n_e = c.env_vert_off[e + 1] - c.env_vert_off[e];
+        if (n_e <= 0) return cudaErrorInvalidValue;   // an environment without pad vertices
+        poff[e + 1] = poff[e] + (n_e + 3) / 4 * 4;
+    }
+    const int64_t nvp_env = poff[ne];
+    std::vector<int32_t> vprow(nv), prow_v(nvp_env, -1);
+    std::vector<int4> blk_v, blk_p;
+    N.h_env_nblk_v.assign(ne, 0);
+    N.h_env_nblk_p.assign(ne, 0);
+    for (int e = 0; e < ne; ++e) {
+        const int64_t v0 = c.env_vert_off[e], v1 = c.env_vert_off[e + 1];
+        for (int64_t v = v0; v < v1; ++v) {
+            vprow[v] = (int32_t)(poff[e] + (v - v0));
+            prow_v[poff[e] + (v - v0)] = (int32_t)v;
+        }
+        const int first_v = (int)blk_v.size(), first_p = (int)blk_p.size();
+        for (int64_t r = v0; r < v1; r += kPcgThreads)
+            blk_v.push_back(make_int4(e, (int)r, (int)std::min<int64_t>(r + kPcgThreads, v1), first_v));
+        for (int64_t r = poff[e]; r < poff[e + 1]; r += 2 * kPcgThreads)
+            blk_p.push_back(make_int4(e, (int)r, (int)std::min<int64_t>(r + 2 * kPcgThreads, poff[e + 1]), first_p));
+        N.h_env_nblk_v[e] = (int32_t)blk_v.size() - first_v;
+        N.h_env_nblk_p[e] = (int32_t)blk_p.size() - first_p;
+    }
+    N.nblk_v = (int64_t)blk_v.size();
+    N.nblk_p = (int64_t)blk_p.size();
+    // the SpMV reads the direction at the padded rows of its columns
+    for (auto& col : sci) if (col >= 0) col = vprow[col];
+    for (auto& col : lcol) if (col >= 0) col = vprow[col];
+    GMCP_CUDA_TRY(N.vprow.upload(vprow.data(), vprow.size(), s));
+    GMCP_CUDA_TRY(N.prow_v.upload(prow_v.data(), prow_v.size(), s));
+    GMCP_CUDA_TRY(N.blk_v.upload(blk_v.data(), blk_v.size(), s));
+    GMCP_CUDA_TRY(N.blk_p.upload(blk_p.data(), blk_p.size(), s));
+    GMCP_CUDA_TRY(N.env_nblk_v.upload(N.h_env_nblk_v.data(), ne, s));
+    GMCP_CUDA_TRY(N.env_nblk_p.upload(N.h_env_nblk_p.data(), ne, s));
+    GMCP_CUDA_TRY(N.escal.ensure((size_t)kEnvScal * ne));
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.escal.p, 0, sizeof(double) * kEnvScal * ne, s));
+    GMCP_CUDA_TRY(N.ecount.ensure(3 * (size_t)ne));
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.ecount.p, 0, sizeof(unsigned) * 3 * ne, s));
+    if (cudaMallocHost(reinterpret_cast<void**>(&N.h_pcg), sizeof(double) * 4 * ne) != cudaSuccess)
+        return cudaErrorMemoryAllocation;
+
     const size_t n3 = 3 * (size_t)nv;
     GMCP_CUDA_TRY(N.goff.upload(goff.data(), goff.size(), s));
     GMCP_CUDA_TRY(N.gslice.upload(gslice.data(), gslice.size(), s));
@@ -1432,8 +1525,8 @@ cudaError_t newton_setup(Ctx& c) {
     if (f32) GMCP_CUDA_TRY(N.tH32.ensure(HBlk<float>::kPerTet * ((size_t)nt + 1)));
     else GMCP_CUDA_TRY(N.tH64.ensure(HBlk<double>::kPerTet * ((size_t)nt + 1)));
     GMCP_CUDA_TRY(N.tE8.ensure(8 * (size_t)nt + 8));
-    // PCG vectors: rows padded to a multiple of four, the padding zero
-    const int64_t nvp = (nv + 3) / 4 * 4;
+    // PCG vectors: rows padded per environment (above), the padding zero
+    const int64_t nvp = nvp_env;
     N.nvp = nvp;
     if (f32) {
         GMCP_CUDA_TRY(N.A32.ensure(288 * (size_t)ngroups + 288));
@@ -1460,7 +1553,7 @@ cudaError_t newton_setup(Ctx& c) {
         GMCP_CUDA_TRY(N.Pinv.ensure(9 * (size_t)nvp));
         GMCP_CUDA_TRY(cudaMemsetAsync(N.Pinv.p, 0, sizeof(double) * 9 * nvp, s));
     }
-    GMCP_CUDA_TRY(N.part.ensure(2 * (size_t)nblk(nv, kPcgThreads) + 2));
+    GMCP_CUDA_TRY(N.part.ensure(2 * (size_t)std::max(N.nblk_v, N.nblk_p) + 2));
     GMCP_CUDA_TRY(N.counters.ensure(4));
     GMCP_CUDA_TRY(cudaMemsetAsync(N.counters.p, 0, 4 * sizeof(unsigned), s));
     for (DBuf<double>* b : {&N.w, &N.xhat, &N.xt, &N.G, &N.dirn, &N.tmp, &N.P, &N.dP, &N.xi, &N.xl})
