@@ -352,6 +352,7 @@ def run_ours(args):
         line["batched"] = batched_measurement(dev, n_env=args.batch_envs)
     if not args.no_newton:
         line["newton_step"] = newton_measurement(dev)
+        line["batched_step"] = batched_step_measurement(dev, n_env=args.step_envs)
         line["warm_start"] = warm_start_measurement(dev)
     if not args.no_dual_map:
         line["dual_mesh"] = dual_mesh_measurement(dev)
@@ -772,6 +773,81 @@ def newton_measurement(dev, start_step=20, n_states=4):
     return out
 
 
+def batched_step_measurement(dev, n_env=16, steps=3):
+    """Batched time steps (ipc_newton_step_envs): n_env fingertip environments
+    of the batched workload's recipe with their tetrahedra (5 pads of 16-128
+    quads of 0.25 mm, 2 tet layers, around a perturbed convex object of
+    2k-80k triangles), every pad starting 1.5 dhat pressed toward its object
+    (in contact from the first step) with its top face driven at 0.5 mm/s.
+    Each environment has its own Newton iteration, solve, step bound and
+    stopping; one call steps them all.  Timed: ``steps`` batched steps after
+    one untimed step (which builds the time-stepper state), and the same
+    steps taken one environment at a time with a context per environment
+    (the batch's results are bit for bit those)."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    dhat = 1e-4
+    parts = [S._fingertip_env(e, 5, (16, 128), 0.25e-3, 2, 0.5e-3, (2000, 80000), 15e-3, dhat, 1e5, 1e-3,
+                              0.5e-3, 100, 3, 1, 1.5 * dhat, True) for e in range(n_env)]
+    sc = S.concat_envs([p[0] for p in parts], name="fingertip_batch")
+    x0 = np.concatenate([p[1] for p in parts])
+    top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
+    vd = torch.as_tensor(sc.v_dirichlet, device="cuda")
+    out = {"workload": f"fingertip_batch {n_env} envs x 5 pads (16-128 quads, 2 tet layers, 4 samples/tri) vs "
+                       f"2k-80k-tri objects, pads 1.5 dhat pressed, top faces at 0.5 mm/s, h = 1 ms",
+           "n_env": n_env, "n_vert": int(sc.X.shape[0]), "n_tet": int(sc.tets.shape[0]),
+           "slave_tris": int(sc.stris.shape[0]), "master_tris": int(sc.mtris.shape[0]),
+           "newton_tol": sc.params["newton_tol"]}
+    ctx = binding.Context(sc, precision="mixed", device=dev)
+    x = torch.as_tensor(x0, device="cuda")
+    v = vd.clone()
+    ctx.newton_step_envs(x, v)
+    v[top] = vd[top]
+    times, iters, statuses = [], [], []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r, per = ctx.newton_step_envs(x, v)
+        torch.cuda.synchronize()
+        times.append((time.perf_counter() - t0) * 1e3)
+        v[top] = vd[top]
+        iters.append([q["newton_iters"] for q in per])
+        statuses.append(sorted(set(q["status"] for q in per)))
+    ctx.close()
+    ms = statistics.median(times)
+    out["batched"] = {"ms_per_step_median": ms, "ms_per_step": [round(t, 1) for t in times],
+                      "env_steps_per_s": n_env / (ms / 1e3),
+                      "newton_iters_max": [max(i) for i in iters], "newton_iters_mean": [float(np.mean(i)) for i in iters],
+                      "statuses": statuses}
+    # the same states stepped one environment at a time
+    seq = []
+    vo = 0
+    for e, (pe, xe) in enumerate(parts):
+        c = binding.Context(pe, precision="mixed", device=dev, params=sc.params)
+        xg = torch.as_tensor(xe, device="cuda")
+        tp = torch.as_tensor(pe.dirichlet.astype(bool), device="cuda")
+        vde = torch.as_tensor(pe.v_dirichlet, device="cuda")
+        vg = vde.clone()
+        c.newton_step(xg, vg)
+        vg[tp] = vde[tp]
+        tt = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c.newton_step(xg, vg)
+            torch.cuda.synchronize()
+            tt.append((time.perf_counter() - t0) * 1e3)
+            vg[tp] = vde[tp]
+        c.close()
+        seq.append(tt)
+    seq_ms = [sum(t[k] for t in seq) for k in range(steps)]
+    out["one_env_at_a_time"] = {"ms_per_step_median": statistics.median(seq_ms),
+                                "env_steps_per_s": n_env / (statistics.median(seq_ms) / 1e3)}
+    out["speedup_batched_vs_one_at_a_time"] = statistics.median(seq_ms) / ms
+    return out
+
+
 def warm_start_measurement(dev, train_iters=1500, timed_iters=50):
     """Learned warm start on the terrain press: tensor-core training
     throughput (one Adam step = forward + backward over all 594,441
@@ -1040,11 +1116,14 @@ def main():
                     help="skip the time-step measurement (newton_step key)")
     ap.add_argument("--batch-envs", type=int, default=512,
                     help="environments in the batched measurement")
+    ap.add_argument("--step-envs", type=int, default=16,
+                    help="environments in the batched time-step measurement")
     ap.add_argument("--dense-quads", type=int, default=256,
                     help="--mode dense_passes: gel pad quads per side (256 = the measured workload)")
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
-    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "dualmap", "faceclip",
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "batchstep",
+                                                       "dualmap", "faceclip",
                                                        "mastergrad", "dense", "dense_passes", "peaks"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
                          "training steps or time steps (command lines for profilers); batch: "
@@ -1073,6 +1152,8 @@ def main():
         run_dense_passes(args)
     elif args.mode == "peaks":
         print(json.dumps(measure_alu_peaks(0)), flush=True)
+    elif args.mode == "batchstep":
+        print(json.dumps(batched_step_measurement(0, n_env=args.step_envs, steps=max(1, args.steps))), flush=True)
     elif args.mode == "batch":
         print(json.dumps(batched_measurement(0, n_env=args.batch_envs,
                                              steps=args.steps)), flush=True)

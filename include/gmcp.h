@@ -305,9 +305,35 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
  * block pattern).  The call synchronises params.stream several times per
  * iteration.  Returns IPC_ERR_NOT_CONVERGED after max_newton iterations
  * (x and v then hold the last iterate); on IPC_ERR_INFEASIBLE and
- * IPC_ERR_LINESEARCH x and v are left at x^t, v^t. */
+ * IPC_ERR_LINESEARCH x and v are left at x^t, v^t.
+ * Environments: each is a time step of its own, as ipc_newton_step_envs
+ * describes; the status is IPC_OK when every environment converged, else
+ * that of the first environment that did not, and stats (n_env > 1) sums
+ * pcg_iters_total, line_search_halvings and energy, takes the largest
+ * newton_iters, residual and res0 and the smallest alpha0 and last_alpha,
+ * and counts in pred_used the environments that took the prediction. */
 ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
                            const double* dx_pred_dev, ipc_step_stats* stats);
+
+/* The time step of ipc_newton_step for every environment of the scene at
+ * once (the paper's batched environments, Sec. 5): each environment has its
+ * own incremental potential, residual scale, Newton iterate, PCG solve
+ * (stopping per environment), step bound (Sec. 4.5, minimum over its own
+ * samples and pairs), line search and stopping.  Every sum and minimum of
+ * environment e is the one a context holding that environment alone
+ * computes, in the same order, so its result is bit for bit that of
+ * stepping it alone with the same parameters.  Environments run side by
+ * side: one that has stopped keeps its state while the others iterate.
+ * An environment whose master cannot move to xm_next keeps its master pose.
+ *  x_dev, v_dev, xm_next_dev, dx_pred_dev: as for ipc_newton_step, for the
+ *  whole scene;
+ *  stats_host (host [n_env], may be NULL): each environment's statistics;
+ *  status_host (host [n_env], may be NULL): each environment's ipc_status
+ *  (IPC_OK, IPC_ERR_INFEASIBLE, IPC_ERR_NOT_CONVERGED, IPC_ERR_LINESEARCH);
+ *  x and v of an environment follow its own status as for ipc_newton_step.
+ * Returns what ipc_newton_step returns. */
+ipc_status ipc_newton_step_envs(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
+                                const double* dx_pred_dev, ipc_step_stats* stats_host, int32_t* status_host);
 
 /* Autotuner (not part of the method): times full contact passes at (x_dev,
  * xm0_dev) with step dx_dev (may be NULL) for candidate launch shapes -- the

@@ -165,6 +165,8 @@ def lib():
     L.ipc_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
     L.ipc_newton_step.restype = C.c_int
     L.ipc_newton_step.argtypes = [P, P, P, P, P, C.POINTER(StepStats)]
+    L.ipc_newton_step_envs.restype = C.c_int
+    L.ipc_newton_step_envs.argtypes = [P, P, P, P, P, C.POINTER(StepStats), P]
     L.ipc_dual_map_build.restype = C.c_int
     L.ipc_dual_map_build.argtypes = [P, C.c_int64, P, C.c_int64, P, C.c_int64, P, P, P, P]
     L.ipc_face_clip_samples.restype = C.c_int
@@ -321,6 +323,7 @@ class Context:
             raise GmcpError(st, L.ipc_last_error(None).decode())
         self.h = h
         self.nv, self.ns, self.nmv = sc.n_vert, sc.n_stri, sc.n_mvert
+        self.n_env = int(sc.n_env)
 
     def close(self):
         if getattr(self, "h", None):
@@ -503,10 +506,32 @@ class Context:
         r = lib().ipc_newton_step(self.h, _ptr(x), _ptr(v), _ptr(xm_t), _ptr(dxp_t), C.byref(st))
         if r not in (0, STEP_INFEASIBLE, STEP_NOT_CONVERGED, STEP_LINESEARCH):
             self._check(r)
-        return dict(status=r, newton_iters=st.newton_iters, pcg_iters=st.pcg_iters_total,
+        return self._stats_dict(st, r)
+
+    @staticmethod
+    def _stats_dict(st, status):
+        return dict(status=status, newton_iters=st.newton_iters, pcg_iters=st.pcg_iters_total,
                     halvings=st.line_search_halvings, residual=st.residual, res0=st.res0,
                     alpha0=st.alpha0, last_alpha=st.last_alpha, energy=st.energy, ms=st.ms_total,
                     pred_used=st.pred_used)
+
+    def newton_step_envs(self, x, v, xm_next=None, dx_pred=None):
+        """The step of every environment (ipc_newton_step_envs): in place on
+        x, v; returns (overall status, [per-environment statistics dicts
+        with their own ``status``])."""
+        t = self.torch
+        for a in (x, v):
+            if not (isinstance(a, t.Tensor) and a.is_cuda and a.dtype == t.float64 and a.is_contiguous()):
+                raise TypeError("x and v must be contiguous FP64 CUDA tensors")
+        ne = self.n_env
+        st = (StepStats * ne)()
+        status = np.zeros(ne, dtype=np.int32)
+        xm_t, dxp_t = self._as(xm_next), self._as(dx_pred)   # alive until the call returns
+        r = lib().ipc_newton_step_envs(self.h, _ptr(x), _ptr(v), _ptr(xm_t), _ptr(dxp_t), st,
+                                       status.ctypes.data)
+        if r not in (0, STEP_INFEASIBLE, STEP_NOT_CONVERGED, STEP_LINESEARCH):
+            self._check(r)
+        return r, [self._stats_dict(st[e], int(status[e])) for e in range(ne)]
 
     # -- learned warm start -------------------------------------------------
     def ws_create(self, params, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, pos_scale=1e-3,

@@ -362,209 +362,308 @@ void capture_contact_pass(Ctx& c, const ContactPassArgs& A) {
 namespace gmcp {
 namespace {
 
-// alpha = min(1, alpha_lin, alpha_accd) for x -> x + alpha dx with the master
-// moving by dxm (NULL = static).  candidates_current: the broad phase of
-// (x, xm0) is the last one run on the context (then it is not repeated and,
-// for a static master, the additive CCD reuses its grid).
+// Every environment is a problem of its own: the iteration below runs them
+// side by side, each with its own energies, residual, step bounds, line
+// search and stopping, and every quantity of environment e is computed
+// exactly as for a scene holding that environment alone (per-environment
+// fixed-order sums, per-environment minima).
+
+// per environment: alpha_e = min(1, alpha_lin, alpha_accd) for x -> x +
+// alpha dx with the master moving by dxm (NULL = static), into
+// N.h_ealpha.  candidates_current: the broad phase of (x, xm0) is the last
+// one run on the context (then it is not repeated and, for a static master,
+// the additive CCD reuses its grid).
 cudaError_t ccd_bound(Ctx& c, const double* x, const double* dx, const double* xm0, const double* dxm,
-                      bool candidates_current, double* alpha) {
-    const unsigned long long init[2] = {0x7FF0000000000000ULL, 0x3FF0000000000000ULL};
-    GMCP_CUDA_TRY(cudaMemcpyAsync(c.u64_tmp.p, init, sizeof(init), cudaMemcpyHostToDevice, c.stream));
+                      bool candidates_current) {
+    NewtonState& N = *c.newton;
+    const int ne = N.n_env;
+    unsigned long long* hb = N.h_ebits;
+    for (int e = 0; e < ne; ++e) {
+        hb[2 * e] = 0x7FF0000000000000ULL;       // +inf
+        hb[2 * e + 1] = 0x3FF0000000000000ULL;   // 1.0
+    }
+    GMCP_CUDA_TRY(cudaMemcpyAsync(N.ebits.p, hb, sizeof(unsigned long long) * 2 * ne, cudaMemcpyHostToDevice,
+                                  c.stream));
     GMCP_CUDA_TRY(cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
     if (!candidates_current) GMCP_CUDA_TRY(run_candidates(c, x, xm0));
-    GMCP_CUDA_TRY(contact_alpha_lin(c, x, xm0, dx, dxm, c.u64_tmp.p));
-    GMCP_CUDA_TRY(bp_ccd_accd(c, x, dx, xm0, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8, dxm == nullptr));
-    unsigned long long bits[2];
-    GMCP_CUDA_TRY(cudaMemcpyAsync(bits, c.u64_tmp.p, sizeof(bits), cudaMemcpyDeviceToHost, c.stream));
+    GMCP_CUDA_TRY(contact_alpha_lin(c, x, xm0, dx, dxm, N.ebits.p, 2));
+    GMCP_CUDA_TRY(bp_ccd_accd(c, x, dx, xm0, dxm, N.ebits.p + 1, c.i64_tmp.p + 8, dxm == nullptr, false, 2));
+    GMCP_CUDA_TRY(cudaMemcpyAsync(hb, N.ebits.p, sizeof(unsigned long long) * 2 * ne, cudaMemcpyDeviceToHost,
+                                  c.stream));
     GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
-    double al, aa;
-    memcpy(&al, &bits[0], 8);
-    memcpy(&aa, &bits[1], 8);
-    if (al < INFINITY) al *= (1.0 - 1e-10);
-    *alpha = std::min(1.0, std::min(al, aa));
-    return cudaSuccess;
-}
-
-// largest k in [0, max_halv] batch: first j with finite elastic energy at
-// xi + (a 2^-j) dP; returns -1 if none up to max_halv
-cudaError_t first_feasible(Ctx& c, const double* xi, const double* dP, double a, int max_halv, int* j_out,
-                           double* a_out) {
-    NewtonState& N = *c.newton;
-    double* hb = c.h_scalars;
-    for (int base = 0; base <= max_halv; base += 8) {
-        const int na = std::min(8, max_halv - base + 1);
-        double al[8];
-        for (int j = 0; j < na; ++j) al[j] = std::ldexp(a, -(base + j));
-        GMCP_CUDA_TRY(cudaMemcpyAsync(N.alphas.p, al, sizeof(double) * na, cudaMemcpyHostToDevice, c.stream));
-        GMCP_CUDA_TRY(nh_energy_multi(c, xi, dP, N.alphas.p, na, N.scal.p + 48));
-        GMCP_CUDA_TRY(cudaMemcpyAsync(hb, N.scal.p + 48, sizeof(double) * na, cudaMemcpyDeviceToHost, c.stream));
-        GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
-        for (int j = 0; j < na; ++j)
-            if (std::isfinite(hb[j])) { *j_out = base + j; *a_out = al[j]; return cudaSuccess; }
+    for (int e = 0; e < ne; ++e) {
+        double al, aa;
+        memcpy(&al, &hb[2 * e], 8);
+        memcpy(&aa, &hb[2 * e + 1], 8);
+        if (al < INFINITY) al *= (1.0 - 1e-10);
+        N.h_ealpha[e] = std::min(1.0, std::min(al, aa));
     }
-    *j_out = -1;
     return cudaSuccess;
 }
 
-// start point: Dirichlet vertices at xhat (their motion must be admissible),
-// free vertices moved toward P by the CCD-limited fraction, halved until
-// every tet keeps J > 0.  x0 may alias neither x nor P.  ok = false: none.
-cudaError_t start_point(Ctx& c, const double* x, const double* P, double* x0, double* alpha0, bool* ok) {
+// copy es[slot .. slot + k) of every environment to the host (N.h_es, same
+// layout) and wait
+cudaError_t read_es(Ctx& c, int slot, int k) {
     NewtonState& N = *c.newton;
+    GMCP_CUDA_TRY(cudaMemcpy2DAsync(N.h_es + slot, kES * sizeof(double), N.es.p + slot, kES * sizeof(double),
+                                    sizeof(double) * k, N.n_env, cudaMemcpyDeviceToHost, c.stream));
+    return cudaStreamSynchronize(c.stream);
+}
+
+// upload a host mask [n_env] (nonzero = selected) to N.emask + k n_env; the
+// stream is drained first, so no earlier copy still reads the pinned slot
+const int32_t* put_mask(Ctx& c, int k, const std::vector<uint8_t>& m, bool invert = false) {
+    NewtonState& N = *c.newton;
+    cudaStreamSynchronize(c.stream);
+    int32_t* h = N.h_emask + (size_t)k * N.n_env;
+    for (int e = 0; e < N.n_env; ++e) h[e] = (m[e] != 0) != invert ? 1 : 0;
+    cudaMemcpyAsync(N.emask.p + (size_t)k * N.n_env, h, sizeof(int32_t) * N.n_env, cudaMemcpyHostToDevice,
+                    c.stream);
+    return N.emask.p + (size_t)k * N.n_env;
+}
+
+// per environment with need[e]: the first j in [0, max_halv] with a finite
+// elastic energy at xi + (a_e 2^-j) dP (batches of 8); j_out[e] = -1 if none
+cudaError_t first_feasible(Ctx& c, const double* xi, const double* dP, const std::vector<double>& a,
+                           int max_halv, const std::vector<uint8_t>& need, std::vector<int>& j_out,
+                           std::vector<double>& a_out) {
+    NewtonState& N = *c.newton;
+    const int ne = N.n_env;
+    std::vector<uint8_t> pending(need);
+    j_out.assign(ne, -1);
+    a_out.assign(ne, 0.0);
+    for (int base = 0; base <= max_halv; base += 8) {
+        bool any = false;
+        for (int e = 0; e < ne; ++e) any = any || pending[e];
+        if (!any) break;
+        const int na = std::min(8, max_halv - base + 1);
+        for (int e = 0; e < ne; ++e)
+            for (int j = 0; j < na; ++j) N.h_eal[8 * e + j] = std::ldexp(a[e], -(base + j));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(N.eal.p, N.h_eal, sizeof(double) * 8 * ne, cudaMemcpyHostToDevice, c.stream));
+        GMCP_CUDA_TRY(nh_energy_multi(c, xi, dP, N.eal.p, na, kEsFe));
+        GMCP_CUDA_TRY(read_es(c, kEsFe, na));
+        for (int e = 0; e < ne; ++e) {
+            if (!pending[e]) continue;
+            for (int j = 0; j < na; ++j)
+                if (std::isfinite(N.h_es[kES * e + kEsFe + j])) {
+                    j_out[e] = base + j;
+                    a_out[e] = N.h_eal[8 * e + j];
+                    pending[e] = 0;
+                    break;
+                }
+        }
+    }
+    return cudaSuccess;
+}
+
+// start point of each environment with need[e]: Dirichlet vertices at xhat
+// (their motion must be admissible), free vertices moved toward P by the
+// CCD-limited fraction, halved until every tet keeps J > 0.  ok[e] = 0: none
+// (x0 = x there, as for environments not asked).  x0 may alias neither x nor P.
+cudaError_t start_point(Ctx& c, const double* x, const double* P, double* x0, const std::vector<uint8_t>& need,
+                        std::vector<double>& alpha0, std::vector<uint8_t>& ok) {
+    NewtonState& N = *c.newton;
+    const int ne = N.n_env;
     const int64_t n = 3 * c.nv;
-    *ok = false;
-    bool has_dir = false;
-    for (uint8_t d : c.h_dir) if (d) { has_dir = true; break; }
+    std::vector<uint8_t> alive(need);
+    std::vector<int> j;
+    std::vector<double> aj;
     GMCP_CUDA_TRY(cudaMemcpyAsync(N.xi.p, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, c.stream));
-    if (has_dir) {
+    bool any_dir = false;
+    for (int e = 0; e < ne; ++e) any_dir = any_dir || (alive[e] && N.h_has_dir[e]);
+    if (any_dir) {
         GMCP_CUDA_TRY(vec_dir_delta(c, x, N.xhat.p, N.dP.p));
-        double a;
-        GMCP_CUDA_TRY(ccd_bound(c, x, N.dP.p, N.xm.p, nullptr, false, &a));
-        if (a < 1.0) return cudaSuccess;
+        GMCP_CUDA_TRY(ccd_bound(c, x, N.dP.p, N.xm.p, nullptr, false));
+        std::vector<uint8_t> chk(ne, 0);
+        for (int e = 0; e < ne; ++e) {
+            if (!alive[e] || !N.h_has_dir[e]) continue;
+            if (N.h_ealpha[e] < 1.0) alive[e] = 0;
+            else chk[e] = 1;
+        }
         GMCP_CUDA_TRY(vec_set_dir(c, N.xhat.p, N.xi.p));
-        int j;
-        double aj;
         GMCP_CUDA_TRY(cudaMemsetAsync(N.dP.p, 0, sizeof(double) * n, c.stream));
-        GMCP_CUDA_TRY(first_feasible(c, N.xi.p, N.dP.p, 0.0, 0, &j, &aj));
-        if (j < 0) return cudaSuccess;
+        GMCP_CUDA_TRY(first_feasible(c, N.xi.p, N.dP.p, std::vector<double>(ne, 0.0), 0, chk, j, aj));
+        for (int e = 0; e < ne; ++e)
+            if (chk[e] && j[e] < 0) alive[e] = 0;
     }
     GMCP_CUDA_TRY(vec_free_delta(c, P, N.xi.p, N.dP.p));
-    double a;
-    GMCP_CUDA_TRY(ccd_bound(c, N.xi.p, N.dP.p, N.xm.p, nullptr, false, &a));
-    int j;
-    double aj;
-    GMCP_CUDA_TRY(first_feasible(c, N.xi.p, N.dP.p, a, c.prm.max_halvings, &j, &aj));
-    if (j < 0) return cudaSuccess;
-    GMCP_CUDA_TRY(vec_axpy(c, n, aj, N.xi.p, N.dP.p, x0));
-    *alpha0 = aj;
-    *ok = true;
+    GMCP_CUDA_TRY(ccd_bound(c, N.xi.p, N.dP.p, N.xm.p, nullptr, false));
+    const std::vector<double> a(N.h_ealpha, N.h_ealpha + ne);
+    GMCP_CUDA_TRY(first_feasible(c, N.xi.p, N.dP.p, a, c.prm.max_halvings, alive, j, aj));
+    alpha0.assign(ne, 0.0);
+    for (int e = 0; e < ne; ++e) {
+        if (alive[e] && j[e] < 0) alive[e] = 0;
+        N.h_ealpha[e] = alive[e] ? aj[e] : 0.0;
+        if (alive[e]) alpha0[e] = aj[e];
+    }
+    GMCP_CUDA_TRY(cudaMemcpyAsync(N.ealpha.p, N.h_ealpha, sizeof(double) * ne, cudaMemcpyHostToDevice, c.stream));
+    const int32_t* m_ok = put_mask(c, 3, alive);
+    GMCP_CUDA_TRY(vec_axpy_env(c, N.xi.p, N.dP.p, N.ealpha.p, m_ok, x0));
+    const int32_t* m_bad = put_mask(c, 2, alive, true);
+    GMCP_CUDA_TRY(vec_copy_env(c, x, m_bad, x0));
+    ok = alive;
     return cudaSuccess;
 }
 
 }  // namespace
 
-// status: 0 converged, 3 infeasible, 5 not converged, 6 line search
+// One implicit-Euler step of every environment.  status_out[e]: 0
+// converged, 3 infeasible, 5 not converged, 6 line search.
 cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, const double* dx_pred,
                        ipc_step_stats* st, int* status_out) {
     NewtonState& N = *c.newton;
+    const int ne = N.n_env;
     const int64_t n = 3 * c.nv;
     cudaStream_t s = c.stream;
     const double h = c.prm.h, h2 = h * h;
-    double* hb = c.h_scalars;
-    double* sc = N.scal.p;   // [56] Ec [57] Ee [58] E [59] |G|^2 [60] G.p
-    int status = 0;
+    std::vector<int> status(ne, 0);
+    std::vector<uint8_t> run(ne, 1);
+    for (int e = 0; e < ne; ++e) st[e] = ipc_step_stats{};
+    auto any = [&](const std::vector<uint8_t>& m) {
+        for (uint8_t b : m) if (b) return true;
+        return false;
+    };
     GMCP_CUDA_TRY(cudaMemcpyAsync(N.xt.p, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     GMCP_CUDA_TRY(vec_xhat(c, x, v, N.xhat.p));
-    // master motion with the pad held at x^t
+    // master motion with the pad held at x^t; an environment whose master
+    // cannot move there keeps its master and stops
     if (xm_next && c.nmv > 0) {
         const int64_t m = 3 * c.nmv;
         GMCP_CUDA_TRY(cudaMemsetAsync(N.tmp.p, 0, sizeof(double) * n, s));
         GMCP_CUDA_TRY(cudaMemcpyAsync(N.dxm.p, xm_next, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
         GMCP_CUDA_TRY(vec_axpy(c, m, -1.0, N.dxm.p, N.xm.p, N.dxm.p));
-        double a;
-        GMCP_CUDA_TRY(ccd_bound(c, x, N.tmp.p, N.xm.p, N.dxm.p, false, &a));
-        if (a < 1.0) { *status_out = 3; return cudaSuccess; }
-        GMCP_CUDA_TRY(cudaMemcpyAsync(N.xm.p, xm_next, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
+        GMCP_CUDA_TRY(ccd_bound(c, x, N.tmp.p, N.xm.p, N.dxm.p, false));
+        for (int e = 0; e < ne; ++e)
+            if (N.h_ealpha[e] < 1.0) { status[e] = 3; run[e] = 0; }
+        GMCP_CUDA_TRY(vec_copy_master_env(c, xm_next, put_mask(c, 0, run), N.xm.p));
     }
     // residual scale from the CCD-filtered plain predictor (reading R8)
-    double a0 = 0.0, gscale;
-    bool ok;
-    GMCP_CUDA_TRY(start_point(c, x, N.xhat.p, N.tmp.p, &a0, &ok));
-    if (!ok) { *status_out = 3; return cudaSuccess; }
-    GMCP_CUDA_TRY(assemble_system(c, N.tmp.p, false, sc + 56, sc + 57, sc + 58, sc + 59));
-    GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 59, sizeof(double), cudaMemcpyDeviceToHost, s));
-    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-    gscale = std::sqrt(hb[0]);
+    std::vector<double> a0, gscale(ne, 0.0);
+    std::vector<uint8_t> ok;
+    GMCP_CUDA_TRY(start_point(c, x, N.xhat.p, N.tmp.p, run, a0, ok));
+    for (int e = 0; e < ne; ++e)
+        if (run[e] && !ok[e]) { status[e] = 3; run[e] = 0; }
+    GMCP_CUDA_TRY(assemble_system(c, N.tmp.p, false));
+    GMCP_CUDA_TRY(read_es(c, kEsG2, 1));
+    for (int e = 0; e < ne; ++e) gscale[e] = std::sqrt(N.h_es[kES * e + kEsG2]);
     // a predicted start goes through the same CCD-filtered start point and is
     // kept only if its residual is not worse than the plain predictor's
-    bool use_pred = false;
-    if (dx_pred) {
-        double al = 0.0;
+    std::vector<uint8_t> use_pred(ne, 0);
+    if (dx_pred && any(run)) {
+        std::vector<double> al;
+        std::vector<uint8_t> okp;
         GMCP_CUDA_TRY(vec_axpy(c, n, 1.0, x, dx_pred, N.P.p));
-        GMCP_CUDA_TRY(start_point(c, x, N.P.p, N.xl.p, &al, &ok));
-        if (ok) {
-            GMCP_CUDA_TRY(assemble_system(c, N.xl.p, false, sc + 56, sc + 57, sc + 58, sc + 59));
-            int32_t bad = 0;
-            GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 59, sizeof(double), cudaMemcpyDeviceToHost, s));
-            GMCP_CUDA_TRY(cudaMemcpyAsync(&bad, N.bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-            if (!bad && std::sqrt(hb[0]) <= gscale) {
-                use_pred = true;
-                a0 = al;
-            }
-        }
-    }
-    st->pred_used = use_pred ? 1 : 0;
-    GMCP_CUDA_TRY(cudaMemcpyAsync(x, use_pred ? N.xl.p : N.tmp.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    st->alpha0 = a0;
-    st->res0 = gscale;
-    // floor: force of a 1e-3 strain on one element, h^2 E lbar^2 1e-3
-    gscale = std::max(gscale, 1e-3 * h2 * c.prm.youngs * N.lbar * N.lbar);
-    for (int it = 0; status == 0; ++it) {
-        GMCP_CUDA_TRY(assemble_system(c, x, true, sc + 56, sc + 57, sc + 58, sc + 59));
-        int32_t bad = 0;
-        GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 56, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        GMCP_CUDA_TRY(cudaMemcpyAsync(&bad, N.bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-        if (bad || !std::isfinite(hb[2])) { status = 3; break; }
-        st->energy = hb[2];
-        st->residual = std::sqrt(hb[3]) / gscale;
-        if (st->residual <= c.prm.newton_tol) break;
-        if (it >= c.prm.max_newton) { status = 5; break; }
-        st->newton_iters = it + 1;
-        int pit = 0;
-        GMCP_CUDA_TRY(vec_neg(c, n, N.G.p, N.tmp.p));
-        {
-            ProfScope ps(c.prof, s, "pcg");
-            GMCP_CUDA_TRY(pcg_solve(c, N.tmp.p, N.dirn.p, c.prm.pcg_rel_tol, c.prm.max_pcg, &pit));
-        }
-        st->pcg_iters_total += pit;
-        GMCP_CUDA_TRY(vec_zero_dir(c, N.dirn.p));
-        GMCP_CUDA_TRY(dot_dev(c, N.G.p, N.dirn.p, n, sc + 60));
-        double al;
-        {
-            ProfScope ps(c.prof, s, "step_bound");
-            GMCP_CUDA_TRY(ccd_bound(c, x, N.dirn.p, N.xm.p, nullptr, true, &al));
-        }
-        GMCP_CUDA_TRY(cudaMemcpyAsync(hb + 8, sc + 60, sizeof(double), cudaMemcpyDeviceToHost, s));
-        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-        const double gp = hb[8];
-        const double c0 = 1e-4;
-        // backtracking on the frozen-linear energy: slot 0 is alpha = 0 (the
-        // reference), slots 1..7 the next halvings
-        // the first batch tries the full step only (it is usually taken);
-        // later batches try seven halvings at once
-        bool accepted = false;
-        for (int hv0 = 0, nk = 1; hv0 <= c.prm.max_halvings && !accepted; hv0 += nk) {
-            nk = hv0 == 0 ? 1 : std::min(7, c.prm.max_halvings - hv0 + 1);
-            double als[8];
-            als[0] = 0.0;
-            for (int j = 0; j < nk; ++j) als[1 + j] = std::ldexp(al, -(hv0 + j));
-            GMCP_CUDA_TRY(cudaMemcpyAsync(N.alphas.p, als, sizeof(double) * (nk + 1), cudaMemcpyHostToDevice, s));
-            {
-                ProfScope ps(c.prof, s, "line_search");
-                GMCP_CUDA_TRY(energy_batch(c, x, N.dirn.p, N.alphas.p, nk + 1, true, sc + 48, sc + 57));
-            }
-            GMCP_CUDA_TRY(cudaMemcpyAsync(hb, sc + 48, sizeof(double) * (nk + 1), cudaMemcpyDeviceToHost, s));
-            GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-            const double E0 = hb[0];
-            for (int j = 0; j < nk; ++j)
-                if (hb[1 + j] <= E0 + c0 * als[1 + j] * gp) {
-                    accepted = true;
-                    al = als[1 + j];
-                    st->last_alpha = al;
-                    st->line_search_halvings += hv0 + j;
-                    break;
+        GMCP_CUDA_TRY(start_point(c, x, N.P.p, N.xl.p, run, al, okp));
+        if (any(okp)) {
+            GMCP_CUDA_TRY(assemble_system(c, N.xl.p, false));
+            GMCP_CUDA_TRY(cudaMemcpyAsync(N.h_ebad, N.ebad.p, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, s));
+            GMCP_CUDA_TRY(read_es(c, kEsG2, 1));
+            for (int e = 0; e < ne; ++e)
+                if (okp[e] && !N.h_ebad[e] && std::sqrt(N.h_es[kES * e + kEsG2]) <= gscale[e]) {
+                    use_pred[e] = 1;
+                    a0[e] = al[e];
                 }
         }
-        if (!accepted) { status = 6; break; }
-        GMCP_CUDA_TRY(vec_axpy(c, n, al, x, N.dirn.p, x));
     }
-    if (status == 0 || status == 5) GMCP_CUDA_TRY(vec_velocity(c, x, N.xt.p, v));
-    if (status != 0 && status != 5)
-        GMCP_CUDA_TRY(cudaMemcpyAsync(x, N.xt.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    GMCP_CUDA_TRY(cudaMemcpyAsync(x, N.tmp.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    if (any(use_pred)) GMCP_CUDA_TRY(vec_copy_env(c, N.xl.p, put_mask(c, 0, use_pred), x));
+    for (int e = 0; e < ne; ++e) {
+        st[e].pred_used = use_pred[e];
+        st[e].alpha0 = a0[e];
+        st[e].res0 = gscale[e];
+        // floor: force of a 1e-3 strain on one element, h^2 E lbar^2 1e-3
+        gscale[e] = std::max(gscale[e], 1e-3 * h2 * c.prm.youngs * N.h_lbar[e] * N.h_lbar[e]);
+    }
+    std::vector<int> env_pit(ne, 0);
+    std::vector<double> al_acc(ne, 0.0);
+    const double c0 = 1e-4;
+    for (int it = 0; any(run); ++it) {
+        GMCP_CUDA_TRY(assemble_system(c, x, true));
+        GMCP_CUDA_TRY(cudaMemcpyAsync(N.h_ebad, N.ebad.p, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, s));
+        GMCP_CUDA_TRY(read_es(c, kEsEc, 4));
+        for (int e = 0; e < ne; ++e) {
+            if (!run[e]) continue;
+            const double* he = N.h_es + kES * e;
+            if (N.h_ebad[e] || !std::isfinite(he[kEsE])) { status[e] = 3; run[e] = 0; continue; }
+            st[e].energy = he[kEsE];
+            st[e].residual = std::sqrt(he[kEsG2]) / gscale[e];
+            if (st[e].residual <= c.prm.newton_tol) { run[e] = 0; continue; }
+            if (it >= c.prm.max_newton) { status[e] = 5; run[e] = 0; continue; }
+            st[e].newton_iters = it + 1;
+        }
+        if (!any(run)) break;
+        // the environments still iterating solve; the others get b = 0 (their
+        // solve stops at once) and a zero direction
+        const int32_t* m_run = put_mask(c, 0, run);
+        GMCP_CUDA_TRY(vec_neg(c, n, N.G.p, N.tmp.p));
+        GMCP_CUDA_TRY(vec_zero_env(c, m_run, N.tmp.p));
+        {
+            ProfScope ps(c.prof, s, "pcg");
+            int pit = 0;
+            GMCP_CUDA_TRY(pcg_solve(c, N.tmp.p, N.dirn.p, c.prm.pcg_rel_tol, c.prm.max_pcg, &pit, env_pit.data()));
+        }
+        for (int e = 0; e < ne; ++e)
+            if (run[e]) st[e].pcg_iters_total += env_pit[e];
+        GMCP_CUDA_TRY(vec_zero_dir(c, N.dirn.p));
+        GMCP_CUDA_TRY(vec_zero_env(c, m_run, N.dirn.p));
+        GMCP_CUDA_TRY(dot_env(c, N.G.p, N.dirn.p, kEsGp));
+        {
+            ProfScope ps(c.prof, s, "step_bound");
+            GMCP_CUDA_TRY(ccd_bound(c, x, N.dirn.p, N.xm.p, nullptr, true));
+        }
+        const std::vector<double> al(N.h_ealpha, N.h_ealpha + ne);
+        GMCP_CUDA_TRY(read_es(c, kEsGp, 1));
+        std::vector<double> gp(ne);
+        for (int e = 0; e < ne; ++e) gp[e] = N.h_es[kES * e + kEsGp];
+        // backtracking on the frozen-linear energy: slot 0 is alpha = 0 (the
+        // reference), the next slots the next halvings; the first batch
+        // tries the full step only (it is usually taken), later batches
+        // seven halvings at once
+        std::vector<uint8_t> searching(run), accepted(ne, 0);
+        for (int hv0 = 0, nk = 1; hv0 <= c.prm.max_halvings && any(searching); hv0 += nk) {
+            nk = hv0 == 0 ? 1 : std::min(7, c.prm.max_halvings - hv0 + 1);
+            for (int e = 0; e < ne; ++e) {
+                N.h_eal[8 * e] = 0.0;
+                for (int j = 0; j < nk; ++j) N.h_eal[8 * e + 1 + j] = std::ldexp(al[e], -(hv0 + j));
+            }
+            GMCP_CUDA_TRY(cudaMemcpyAsync(N.eal.p, N.h_eal, sizeof(double) * 8 * ne, cudaMemcpyHostToDevice, s));
+            {
+                ProfScope ps(c.prof, s, "line_search");
+                GMCP_CUDA_TRY(energy_batch(c, x, N.dirn.p, N.eal.p, nk + 1, true, true));
+            }
+            GMCP_CUDA_TRY(read_es(c, kEsE8, nk + 1));
+            for (int e = 0; e < ne; ++e) {
+                if (!searching[e]) continue;
+                const double* E = N.h_es + kES * e + kEsE8;
+                for (int j = 0; j < nk; ++j) {
+                    const double a = N.h_eal[8 * e + 1 + j];
+                    if (E[1 + j] <= E[0] + c0 * a * gp[e]) {
+                        searching[e] = 0;
+                        accepted[e] = 1;
+                        al_acc[e] = a;
+                        st[e].last_alpha = a;
+                        st[e].line_search_halvings += hv0 + j;
+                        break;
+                    }
+                }
+            }
+        }
+        for (int e = 0; e < ne; ++e) {
+            if (run[e] && !accepted[e]) { status[e] = 6; run[e] = 0; }
+            N.h_ealpha[e] = accepted[e] ? al_acc[e] : 0.0;
+        }
+        if (any(accepted)) {
+            GMCP_CUDA_TRY(cudaMemcpyAsync(N.ealpha.p, N.h_ealpha, sizeof(double) * ne, cudaMemcpyHostToDevice, s));
+            GMCP_CUDA_TRY(vec_axpy_env(c, x, N.dirn.p, N.ealpha.p, put_mask(c, 1, accepted), x));
+        }
+    }
+    // converged or out of iterations: the velocity; otherwise x back to x^t
+    std::vector<uint8_t> keep(ne);
+    for (int e = 0; e < ne; ++e) keep[e] = status[e] == 0 || status[e] == 5;
+    GMCP_CUDA_TRY(vec_velocity_env(c, x, N.xt.p, put_mask(c, 0, keep), v));
+    GMCP_CUDA_TRY(vec_copy_env(c, N.xt.p, put_mask(c, 1, keep, true), x));
     GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-    *status_out = status;
+    for (int e = 0; e < ne; ++e) status_out[e] = status[e];
     return cudaSuccess;
 }
 
@@ -1402,8 +1501,18 @@ ipc_status ipc_contact_pass_kernels(ipc_ctx* ctx, int64_t* kernels_host) {
     return IPC_OK;
 }
 
-ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
-                           const double* dx_pred_dev, ipc_step_stats* stats) {
+static ipc_status newton_status(ipc_ctx* ctx, int status) {
+    switch (status) {
+        case 0: return IPC_OK;
+        case 3: return fail_ctx(ctx, IPC_ERR_INFEASIBLE, "ipc_newton_step: infeasible (master motion blocked, "
+                                                         "inverted tet or no admissible start)");
+        case 5: return fail_ctx(ctx, IPC_ERR_NOT_CONVERGED, "ipc_newton_step: max_newton reached");
+        default: return fail_ctx(ctx, IPC_ERR_LINESEARCH, "ipc_newton_step: line search exhausted max_halvings");
+    }
+}
+
+ipc_status ipc_newton_step_envs(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
+                                const double* dx_pred_dev, ipc_step_stats* stats_host, int32_t* status_host) {
     if (!ctx) return IPC_ERR_ARG;
     Ctx& c = ctx->c;
     if (!x_dev || !v_dev) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: NULL x or v");
@@ -1415,19 +1524,52 @@ ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const dou
     API_CK(ctx, cudaSetDevice(c.device));
     const auto t_start = std::chrono::steady_clock::now();
     API_CK(ctx, newton_setup(c));
-    int status = 0;
-    ipc_step_stats st{};
-    const cudaError_t e = newton_run(c, x_dev, v_dev, xm_next_dev, dx_pred_dev, &st, &status);
+    const int ne = c.n_env;
+    std::vector<int> status(ne, 0);
+    std::vector<ipc_step_stats> st(ne);
+    const cudaError_t e = newton_run(c, x_dev, v_dev, xm_next_dev, dx_pred_dev, st.data(), status.data());
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ipc_newton_step");
-    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
-    if (stats) *stats = st;
-    switch (status) {
-        case 0: ++c.step_count; return IPC_OK;
-        case 3: return fail_ctx(ctx, IPC_ERR_INFEASIBLE, "ipc_newton_step: infeasible (master motion blocked, "
-                                                         "inverted tet or no admissible start)");
-        case 5: return fail_ctx(ctx, IPC_ERR_NOT_CONVERGED, "ipc_newton_step: max_newton reached");
-        default: return fail_ctx(ctx, IPC_ERR_LINESEARCH, "ipc_newton_step: line search exhausted max_halvings");
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    int first_bad = 0;
+    for (int k = 0; k < ne; ++k) {
+        st[k].ms_total = ms;
+        if (stats_host) stats_host[k] = st[k];
+        if (status_host) status_host[k] = status[k] == 0 ? IPC_OK : status[k] == 3 ? IPC_ERR_INFEASIBLE
+                                                         : status[k] == 5 ? IPC_ERR_NOT_CONVERGED
+                                                                          : IPC_ERR_LINESEARCH;
+        if (!first_bad && status[k]) first_bad = status[k];
     }
+    if (!first_bad) ++c.step_count;
+    return newton_status(ctx, first_bad);
+}
+
+ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
+                           const double* dx_pred_dev, ipc_step_stats* stats) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    const int ne = std::max(c.n_env, 1);
+    std::vector<ipc_step_stats> st(ne);
+    const ipc_status r = ipc_newton_step_envs(ctx, x_dev, v_dev, xm_next_dev, dx_pred_dev, st.data(), nullptr);
+    if (stats && (r == IPC_OK || r == IPC_ERR_INFEASIBLE || r == IPC_ERR_NOT_CONVERGED || r == IPC_ERR_LINESEARCH)) {
+        // several environments: counts summed, newton_iters and residual the
+        // largest, alpha0 / last_alpha the smallest, energy summed,
+        // pred_used the number of environments that used the prediction
+        ipc_step_stats a = st[0];
+        for (int k = 1; k < ne; ++k) {
+            const ipc_step_stats& b = st[k];
+            a.newton_iters = std::max(a.newton_iters, b.newton_iters);
+            a.pcg_iters_total += b.pcg_iters_total;
+            a.line_search_halvings += b.line_search_halvings;
+            a.residual = std::max(a.residual, b.residual);
+            a.res0 = std::max(a.res0, b.res0);
+            a.alpha0 = std::min(a.alpha0, b.alpha0);
+            a.last_alpha = std::min(a.last_alpha, b.last_alpha);
+            a.energy += b.energy;
+            a.pred_used += b.pred_used;
+        }
+        *stats = a;
+    }
+    return r;
 }
 
 }  // extern "C"

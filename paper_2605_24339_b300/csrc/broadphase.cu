@@ -1086,15 +1086,28 @@ k_ccd_exact(SceneView S, QueryList Q, PairList C, const double* __restrict__ x,
 __global__ void __launch_bounds__(256)
 k_accd_pairs(SceneView S, Params P, PairList L, const double* __restrict__ x,
              const double* __restrict__ dx, const double* __restrict__ xm0,
-             const double* __restrict__ dxm, unsigned long long* alpha_bits, long long* counters) {
+             const double* __restrict__ dxm, unsigned long long* alpha_bits, long long* counters,
+             int alpha_stride) {
     const int n = min(*L.n, L.cap);
     double best = 1.0;
     long long n_pt = 0, n_ee = 0;
     int cap_hit = 0;
+    // alpha_stride > 0: one bound per environment at alpha_bits[alpha_stride
+    // * env]; a thread keeps the minimum of its current environment and
+    // publishes it when the environment changes (the minimum is exact)
+    int env = -1;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int2 pr = L.p[i];
         const int kind = (int)((unsigned)pr.x >> 30);
         const int32_t a = pr.x & 0x3FFFFFFF, b = pr.y;
+        if (alpha_stride > 0) {
+            const int e = kind == 0 ? S.mtri_env[b] : kind == 1 ? S.stri_env[b] : S.mvert_env[S.medge[2 * (int64_t)b]];
+            if (e != env) {
+                if (env >= 0 && best < 1.0) atomic_min_pos(alpha_bits + (int64_t)alpha_stride * env, best);
+                env = e;
+                best = 1.0;
+            }
+        }
         double X12[12], P12[12];
         int32_t va[4];          // the four vertices: first primitive's, then the second's
         bool first_slave;
@@ -1127,6 +1140,8 @@ k_accd_pairs(SceneView S, Params P, PairList L, const double* __restrict__ x,
         cap_hit |= it >= P.ccd_max_iter;
         best = dmin_(best, r);
     }
+    if (alpha_stride > 0 && env >= 0 && best < 1.0) atomic_min_pos(alpha_bits + (int64_t)alpha_stride * env, best);
+    if (alpha_stride > 0) best = 1.0;
     // warp reductions (min is exact; counters are integers)
     for (int o = 16; o > 0; o >>= 1) {
         best = dmin_(best, __shfl_xor_sync(0xffffffffu, best, o));
@@ -1282,7 +1297,7 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
 
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
                         const double* dxm, unsigned long long* alpha_bits, long long* counters,
-                        bool reuse_grid, bool lazy) {
+                        bool reuse_grid, bool lazy, int alpha_stride) {
     if (!(reuse_grid && dxm == nullptr)) GMCP_CUDA_TRY(bp_build_grid(c, xm0, dxm, true, lazy));
     ProfScope ps(c.prof, c.stream, "accd");
     if (c.ns == 0) return cudaSuccess;
@@ -1314,7 +1329,7 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
         GMCP_CUDA_TRY(cudaGetLastError());
         k_ccd_exact<<<flat, 256, 0, c.stream>>>(S, Q, C, x, dx, xm0, dxm, c.mboxf.p, L);
         GMCP_CUDA_TRY(cudaGetLastError());
-        k_accd_pairs<<<flat, 256, 0, c.stream>>>(S, c.P, L, x, dx, xm0, dxm, alpha_bits, counters);
+        k_accd_pairs<<<flat, 256, 0, c.stream>>>(S, c.P, L, x, dx, xm0, dxm, alpha_bits, counters, alpha_stride);
         GMCP_CUDA_TRY(cudaGetLastError());
         // a lazy caller reads the overflow slots after it synchronises and redoes the pass
         if (lazy) return cudaSuccess;

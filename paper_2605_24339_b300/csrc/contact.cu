@@ -60,6 +60,12 @@ struct ModeArgs {
     unsigned long long* h_count = nullptr;
     int64_t h_cap = 0;
     int32_t m_off = 0;         // index of master vertex 0 in the joint numbering
+    // MODE_ALPHA: the bound of a sample on slave triangle t goes to
+    // alpha_bits[alpha_stride * env(t)] (0: one bound for the whole scene)
+    int alpha_stride = 0;
+    // MODE_LAGGED: the step sizes of slave triangle t are at
+    // alphas[alphas_stride * env(t)] (0: the same for the whole scene)
+    int alphas_stride = 0;
 };
 
 
@@ -991,6 +997,11 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
     const bool cert = pre && MODE == MODE_EVAL && dxm == nullptr;   // certified FP32 items
     for (int i = next_item(C.work, lane); i < n_active; i = next_item(C.work, lane)) {
         const TriData D = load_tri(S, C, x, dx, frame, i);
+        if (MODE == MODE_LAGGED && LG.alphas_stride > 0) {
+            const double* ae = LG.alphas + (int64_t)LG.alphas_stride * S.stri_env[D.t];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) al8[j] = j < LG.na ? ae[j] : 0.0;
+        }
         Acc<T> A;
         A.zero();
         double E8[8];
@@ -1080,7 +1091,8 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) A.amin = rmin(A.amin, shfl_x(A.amin, o));
             if (lane == 0 && A.amin < INFINITY)
-                atomicMin(alpha_bits, (unsigned long long)__double_as_longlong(A.amin));
+                atomicMin(alpha_bits + (int64_t)LG.alpha_stride * S.stri_env[D.t],
+                          (unsigned long long)__double_as_longlong(A.amin));
         }
     }
     // counters (integers: order does not matter)
@@ -1846,12 +1858,16 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
 }
 
 cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const double* dx,
-                              const double* dxm, unsigned long long* alpha_bits) {
+                              const double* dxm, unsigned long long* alpha_bits, int alpha_stride) {
     ProfScope ps(c.prof, c.stream, "alpha_lin");
+    ModeArgs LG;
+    LG.alpha_stride = alpha_stride;
     // the step bound always uses FP64 geometry
     if (c.P.nk == 4)
-        return launch_samples<4, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm, alpha_bits);
-    return launch_samples<16, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm, alpha_bits);
+        return launch_samples<4, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm,
+                                                     alpha_bits, LG);
+    return launch_samples<16, double, MODE_ALPHA>(c, x, xm, nullptr, nullptr, nullptr, nullptr, dx, dxm,
+                                                  alpha_bits, LG);
 }
 
 cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m) {
@@ -1880,17 +1896,19 @@ cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32
 }
 
 cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,
-                           const double* alphas_dev, int na, double* triE8, double* energies_dev) {
+                           const double* alphas_dev, int na, double* triE8, double* energies_dev,
+                           int alphas_stride) {
     ProfScope ps(c.prof, c.stream, "lagged");
     if (na < 1 || na > 8) return cudaErrorInvalidValue;
     GMCP_CUDA_TRY(cudaMemsetAsync(triE8, 0, sizeof(double) * (size_t)na * (size_t)c.ns, c.stream));
     ModeArgs LG;
-    LG.alphas = alphas_dev; LG.na = na; LG.triE8 = triE8; LG.ns = c.ns;
+    LG.alphas = alphas_dev; LG.na = na; LG.triE8 = triE8; LG.ns = c.ns; LG.alphas_stride = alphas_stride;
     if (c.P.nk == 4)
         GMCP_CUDA_TRY((launch_samples<4, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, LG)));
     else
         GMCP_CUDA_TRY((launch_samples<16, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, LG)));
-    for (int j = 0; j < na; ++j) GMCP_CUDA_TRY(reduce_sum(c, triE8 + (int64_t)j * c.ns, c.ns, energies_dev + j));
+    if (energies_dev)
+        for (int j = 0; j < na; ++j) GMCP_CUDA_TRY(reduce_sum(c, triE8 + (int64_t)j * c.ns, c.ns, energies_dev + j));
     return cudaSuccess;
 }
 

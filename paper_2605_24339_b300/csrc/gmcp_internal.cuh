@@ -198,8 +198,31 @@ struct ProfScope {
 // the contact pattern) with per-block contribution lists, and the solver's
 // vectors
 // ------------------------------------------------------------------------
+// A segmented sum: blocks of 2048 elements counted from each segment's
+// (environment's) first element; per block: segment, first element, end,
+// first block of the segment.  With one segment the blocks and the order of
+// the sums are those of reduce_sum.
+struct SegRed {
+    int64_t nblk = 0;
+    DBuf<int4> blk;
+    DBuf<int32_t> nblk_env;    // [n_env] blocks of each segment
+    DBuf<int32_t> first_blk;   // [n_env] first block of each segment
+};
+
+// per-environment Newton scalars ([n_env][kES] doubles)
+constexpr int kES = 64;
+enum : int {
+    kEsEc = 0, kEsEe = 1, kEsE = 2, kEsG2 = 3, kEsEin = 4, kEsGp = 5,
+    kEsE8 = 8,      // [8] line-search totals
+    kEsEin8 = 16,   // [8] inertia terms
+    kEsEe8 = 24,    // [8] elastic energies
+    kEsEc8 = 32,    // [8] lagged contact energies
+    kEsAl = 40,     // [8] the step sizes being tried
+    kEsFe = 48      // [8] elastic energies of the start-point halvings
+};
+
 struct NewtonState {
-    double mu = 0, lam = 0, lbar = 0;
+    double mu = 0, lam = 0;
     int64_t nnzb = 0;
     DBuf<int32_t> tets;                  // [nt][4]
     DBuf<double> Dminv, vol, mass;       // [nt][9], [nt], [nv]
@@ -232,9 +255,7 @@ struct NewtonState {
     DBuf<double> xm, dxm;                // current master [nmv][3] and its motion
     DBuf<double> ein8;                   // [8][nv] inertia energy terms
     DBuf<double> triE8;                  // [8][ns] lagged contact energies
-    DBuf<double> alphas;                 // [8]
     DBuf<double> scal;                   // solver scalars
-    DBuf<int32_t> bad;                   // inverted-tet flag
     // environments: the PCG works per environment (own scalars, stopping,
     // reductions), on rows padded per environment to a multiple of four
     int n_env = 1;
@@ -245,9 +266,32 @@ struct NewtonState {
     std::vector<int32_t> h_env_nblk_v, h_env_nblk_p;   // blocks per env
     DBuf<int32_t> env_nblk_v, env_nblk_p;
     DBuf<double> escal;                  // [n_env][kEnvScal] per-environment PCG scalars
+    DBuf<int32_t> vert_env, tet_env;     // [nv], [nt] environment of each vertex / tet
+    SegRed seg_v3, seg_v, seg_t, seg_s;  // segmented sums over 3 nv, nv, nt, ns elements
+    DBuf<double> seg_part;               // block partials of the segmented sums
+    DBuf<double> es;                     // [n_env][kES] per-environment Newton scalars
+    DBuf<int32_t> ebad;                  // [n_env] inverted-tet flag per environment
+    DBuf<double> ealpha;                 // [n_env] step size per environment
+    DBuf<double> eal;                    // [n_env][8] step sizes tried per environment
+    DBuf<int32_t> emask;                 // [4][n_env] environment masks
+    DBuf<unsigned long long> ebits;      // [n_env][2] step bounds (linearised, additive CCD) as bits
+    DBuf<double> ezero;                  // one 0.0
+    std::vector<double> h_lbar;          // cube root of each environment's mean tet volume
+    std::vector<uint8_t> h_has_dir;      // environment has Dirichlet vertices
+    // pinned host copies (one allocation, h_pin)
+    void* h_pin = nullptr;
+    double* h_es = nullptr;              // [n_env][kES]
+    double* h_eal = nullptr;             // [n_env][8]
+    double* h_ealpha = nullptr;          // [n_env]
+    unsigned long long* h_ebits = nullptr;   // [n_env][2]
+    int32_t* h_emask = nullptr;          // [4][n_env]
+    int32_t* h_ebad = nullptr;           // [n_env]
     DBuf<unsigned> ecount;               // [3][n_env] last-block counters (init/spmv, update, spare)
     double* h_pcg = nullptr;             // pinned [n_env][4]: break, done, iterations (host reads)
-    ~NewtonState() { if (h_pcg) cudaFreeHost(h_pcg); }
+    ~NewtonState() {
+        if (h_pcg) cudaFreeHost(h_pcg);
+        if (h_pin) cudaFreeHost(h_pin);
+    }
 };
 
 // A captured CUDA graph and the arguments it was captured with.
@@ -431,7 +475,7 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
 // triangles at xm0 (static master, same call), so the swept grid equals them
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
                         const double* dxm, unsigned long long* alpha_bits, long long* counters,
-                        bool reuse_grid = false, bool lazy = false);
+                        bool reuse_grid = false, bool lazy = false, int alpha_stride = 0);
 // scan.cu
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
                                size_t tmp_n, cudaStream_t s);
@@ -448,15 +492,19 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
                          const double* dx = nullptr, const double* dxm = nullptr,
                          unsigned long long* alpha_bits = nullptr);
 cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const double* dx,
-                              const double* dxm, unsigned long long* alpha_bits);
+                              const double* dxm, unsigned long long* alpha_bits, int alpha_stride = 0);
 cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out, const int32_t* stamp = nullptr,
                        const int32_t* pass = nullptr);
 int sm_count(int device);
 // frozen-linear ("lagged") contact energy of the samples active at (x, xm),
 // evaluated at x + alphas[j] p for j < na (na <= 8) into energies_dev[j]
-// (FP64 in both precisions); needs the candidate lists of (x, xm)
+// (FP64 in both precisions; energies_dev NULL: the per-triangle terms
+// triE8 [na][ns] only); needs the candidate lists of (x, xm).
+// alphas_stride > 0: a slave triangle of environment e uses
+// alphas_dev[alphas_stride * e + j]
 cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,
-                           const double* alphas_dev, int na, double* triE8, double* energies_dev);
+                           const double* alphas_dev, int na, double* triE8, double* energies_dev,
+                           int alphas_stride = 0);
 // gradient of the contact potential with respect to the master vertices,
 // [nmv][3] FP64 (zeroed first; FP64 atomics, so the summation order varies)
 cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m);
@@ -466,19 +514,23 @@ cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32
                                 int64_t cap, unsigned long long* count);
 // newton.cu
 cudaError_t newton_setup(Ctx& c);
-cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev, int32_t* bad);
-// elastic energies at x + alphas[j] p (j < na <= 8) into energies_dev[j];
-// +inf where some tet has J <= 0
-cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_dev,
-                            int na, double* energies_dev);
-// total energies at x + alphas[j] p into out_dev[j]; with ee0_dev (alphas[0]
-// = 0 and the elastic energy at x already summed there) the elastic energy
-// of slot 0 is taken from it instead of being evaluated again
-cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_dev, int na,
-                         bool with_contact, double* out_dev, const double* ee0_dev = nullptr);
-cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess, double* Ec_dev, double* Ee_dev,
-                            double* E_dev, double* gnorm2_dev);
-cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double* out);
+// The Newton iteration runs per environment: each sum below is one
+// fixed-order sum per environment, the same as over a scene holding that
+// environment alone; the results go to N.es [n_env][kES].
+// elastic energy per environment into es[kEsEe]; inverted-tet flags in N.ebad
+cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess);
+// elastic energies at x + alphas_env[8 e + j] p (j < na <= 8) into es[slot +
+// j]; +inf where a tet of the environment has J <= 0
+cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na, int slot);
+// total energies at x + alphas_env[8 e + j] p into es[kEsE8 + j]; ee0:
+// alphas_env[8 e] = 0 and es[kEsEe] already holds the elastic energy at x
+cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_env, int na,
+                         bool with_contact, bool ee0);
+// es[kEsEc], es[kEsEe], es[kEsE], es[kEsG2] at x, the gradient N.G and
+// optionally the matrix
+cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess);
+// a . b per environment (3 nv entries) into es[slot]
+cudaError_t dot_env(Ctx& c, const double* a, const double* b, int slot);
 cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters,
                       int* env_iters = nullptr);   // env_iters: [n_env] iterations per environment
 // elementwise helpers
@@ -490,6 +542,13 @@ cudaError_t vec_free_delta(Ctx& c, const double* P, const double* xi, double* dP
 cudaError_t vec_zero_dir(Ctx& c, double* p);
 cudaError_t vec_velocity(Ctx& c, const double* x, const double* xt, double* v);
 cudaError_t vec_neg(Ctx& c, int64_t n, const double* a, double* out);
+// per environment (mask [n_env], nonzero = selected)
+cudaError_t vec_axpy_env(Ctx& c, const double* x, const double* p, const double* alpha_env, const int32_t* mask,
+                         double* out);   // out = x + alpha_env[e] p (selected), x (others)
+cudaError_t vec_copy_env(Ctx& c, const double* src, const int32_t* mask, double* dst);   // selected only
+cudaError_t vec_zero_env(Ctx& c, const int32_t* mask, double* a);                        // unselected only
+cudaError_t vec_copy_master_env(Ctx& c, const double* src, const int32_t* mask, double* dst);   // master vertices
+cudaError_t vec_velocity_env(Ctx& c, const double* x, const double* xt, const int32_t* mask, double* v);
 // api.cu: the context behind an ABI handle
 Ctx& ctx_of(ipc_ctx* h);
 // errors of the context-free entry points, read by ipc_last_error(NULL) (api.cu)

@@ -288,7 +288,8 @@ __device__ void nh_hessian_blocks(const double* Fd, double lnJd, double mud, dou
 template <bool WANT_HESS, class TH>
 __global__ void __launch_bounds__(128)
 k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
-          double* __restrict__ tG, TH* __restrict__ tH, int32_t* __restrict__ bad) {
+          double* __restrict__ tG, TH* __restrict__ tH, int32_t* __restrict__ bad,
+          const int32_t* __restrict__ tet_env) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= E.nt) return;
     double x4[12], X4[12], F[9], lnJ, psi;
@@ -297,7 +298,7 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
     const double* Dmi = E.Dminv + 9 * t;
     const double vol = E.vol[t];
     if (!nh_energy(Dmi, vol, E.mu, E.lam, x4, X4, &psi, F, &lnJ)) {
-        atomicMax(bad, 1);
+        atomicMax(bad + (tet_env ? tet_env[t] : 0), 1);
         tE[t] = INFINITY;
         for (int q = 0; q < 12; ++q) tG[12 * t + q] = 0.0;
         if (WANT_HESS)
@@ -326,11 +327,13 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
 }
 
 // elastic energies at x + alpha_j p for j < na (<= 8), layout [na][nt]
+// (alphas of tet t's environment: alphas[astride * env + j])
 __global__ void k_nh_energy_multi(ElasticView E, const double* __restrict__ x,
-                                  const double* __restrict__ p, const double* __restrict__ alphas, int na,
-                                  double* __restrict__ tE8) {
+                                  const double* __restrict__ p, const double* __restrict__ alphas_env, int astride,
+                                  const int32_t* __restrict__ tet_env, int na, double* __restrict__ tE8) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= E.nt) return;
+    const double* alphas = alphas_env + (int64_t)astride * tet_env[t];
     double x4[12], p4[12], X4[12], y4[12], F[9], lnJ, psi;
     load_tet(E, x, t, x4);
     load_tet(E, p, t, p4);
@@ -1009,9 +1012,11 @@ __global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __r
 // inertia terms 1/2 m |x + a_j p - xhat|^2 per vertex, layout [na][nv]
 __global__ void k_inertia_multi(int64_t nv, const double* __restrict__ x, const double* __restrict__ p,
                                 const double* __restrict__ xhat, const double* __restrict__ mass,
-                                const double* __restrict__ alphas, int na, double* __restrict__ out) {
+                                const double* __restrict__ alphas_env, int astride,
+                                const int32_t* __restrict__ vert_env, int na, double* __restrict__ out) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
+    const double* alphas = alphas_env + (int64_t)astride * vert_env[v];
     const double m = mass[v];
     for (int j = 0; j < na; ++j) {
         const double a = alphas[j];
@@ -1024,13 +1029,103 @@ __global__ void k_inertia_multi(int64_t nv, const double* __restrict__ x, const 
     }
 }
 
-// E_j = Ein_j + h^2 (Ee_j + Ec_j)
+// E_j = Ein_j + h^2 (Ee_j + Ec_j), per environment (block e, thread j; the
+// arrays at stride kES)
 __global__ void k_combine(int na, const double* __restrict__ ein, const double* __restrict__ ee,
                           const double* __restrict__ ec, double h2, double* __restrict__ out) {
     const int j = threadIdx.x;
     if (j >= na) return;
-    const double c = ec ? ec[j] : 0.0;
-    out[j] = (isfinite(ee[j]) && isfinite(c)) ? ein[j] + h2 * (ee[j] + c) : INFINITY;
+    const int64_t o = (int64_t)kES * blockIdx.x;
+    const double c = ec ? ec[o + j] : 0.0;
+    out[o + j] = (isfinite(ee[o + j]) && isfinite(c)) ? ein[o + j] + h2 * (ee[o + j] + c) : INFINITY;
+}
+
+// segmented sums: block b adds its 2048 elements of segment B.x as
+// k_reduce_partial does (8 strided passes of 256 threads, a shuffle tree,
+// the eight warp sums); stamp: only entries whose stamp equals *pass.
+// blockIdx.y = j sums in[j * in_stride ...] into part[j * gridDim.x ...].
+__global__ void k_seg_partial(const double* __restrict__ in, int64_t in_stride, const int4* __restrict__ blk,
+                              double* __restrict__ part, const int32_t* __restrict__ stamp,
+                              const int32_t* __restrict__ pass) {
+    __shared__ double sh[8];
+    const int4 B = blk[blockIdx.x];
+    in += in_stride * blockIdx.y;
+    part += (int64_t)gridDim.x * blockIdx.y;
+    const int32_t ps = pass ? *pass : 0;
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) {
+        const int64_t k = (int64_t)B.y + (int64_t)i * 256 + threadIdx.x;
+        if (k < B.z && (!stamp || stamp[k] == ps)) s += in[k];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < 8 ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = v;
+    }
+}
+// one block of 1024 threads per segment (blockIdx.x) and sum j
+// (blockIdx.y): the segment's block partials as k_reduce_final sums them,
+// into out[out_stride * e + j]
+__global__ void k_seg_final(const double* __restrict__ part, int64_t nblk_all,
+                            const int32_t* __restrict__ nblk_env, const int32_t* __restrict__ first_blk,
+                            double* __restrict__ out, int out_stride) {
+    __shared__ double sh[32];
+    const int e = blockIdx.x;
+    part += nblk_all * blockIdx.y;
+    out += blockIdx.y;
+    const int nb = nblk_env[e], b0 = first_blk[e];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < nb; k += 1024) s += part[b0 + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = sh[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) out[(int64_t)out_stride * e] = v;
+    }
+}
+
+// out = x + alpha_env[env] p per vertex of the environments with mask[env]
+// != 0 (mask NULL: all); the others get out = x
+__global__ void k_axpy_env(int64_t nv, const double* __restrict__ x, const double* __restrict__ p,
+                           const double* __restrict__ alpha_env, const int32_t* __restrict__ mask,
+                           const int32_t* __restrict__ vert_env, double* __restrict__ out) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const int e = vert_env[v];
+    if (mask && !mask[e]) {
+        if (out != x)
+            for (int c = 0; c < 3; ++c) out[3 * v + c] = x[3 * v + c];
+        return;
+    }
+    const double a = alpha_env[e];
+    for (int c = 0; c < 3; ++c) out[3 * v + c] = x[3 * v + c] + a * p[3 * v + c];
+}
+// v = (x - xt) / h for the vertices of the environments with mask[env] != 0
+__global__ void k_velocity_env(int64_t nv, const double* __restrict__ x, const double* __restrict__ xt, double h,
+                               const int32_t* __restrict__ mask, const int32_t* __restrict__ vert_env,
+                               double* __restrict__ v) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= nv || !mask[vert_env[u]]) return;
+    for (int c = 0; c < 3; ++c) v[3 * u + c] = (x[3 * u + c] - xt[3 * u + c]) / h;
+}
+// dst[v] = src[v] for the vertices of the environments with mask[env] != 0
+__global__ void k_copy_env(int64_t nv, const double* __restrict__ src, const int32_t* __restrict__ mask,
+                           const int32_t* __restrict__ vert_env, double* __restrict__ dst) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv || !mask[vert_env[v]]) return;
+    for (int c = 0; c < 3; ++c) dst[3 * v + c] = src[3 * v + c];
+}
+// a[v] = 0 for the vertices of the environments with mask[env] == 0
+__global__ void k_zero_env(int64_t nv, const int32_t* __restrict__ mask, const int32_t* __restrict__ vert_env,
+                           double* __restrict__ a) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv || mask[vert_env[v]]) return;
+    a[3 * v] = 0.0; a[3 * v + 1] = 0.0; a[3 * v + 2] = 0.0;
 }
 
 // ---------------------------------------------------------------- vectors ---
@@ -1085,31 +1180,47 @@ __global__ void k_neg(int64_t n, const double* __restrict__ a, double* __restric
 // ---------------------------------------------------------------------------
 static unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess, double* energy_dev, int32_t* bad) {
+// segmented fixed-order sums (see SegRed): na sums of R's segments, the
+// j-th over in + j in_stride, into out[out_stride e + j]
+static cudaError_t seg_sum(Ctx& c, const SegRed& R, const double* in, int64_t in_stride, int na, double* out,
+                           int out_stride, const int32_t* stamp = nullptr, const int32_t* pass = nullptr) {
     NewtonState& N = *c.newton;
-    ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, c.X.p, N.mu, N.lam};
-    if (c.nt == 0) return cudaSuccess;
-    const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    const unsigned g = nblk(c.nt, 128);
-    if (!want_hess)
-        k_nh_eval<false, double><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, nullptr, bad);
-    else if (f32)
-        k_nh_eval<true, float><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH32.p, bad);
-    else
-        k_nh_eval<true, double><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH64.p, bad);
-    GMCP_CUDA_TRY(cudaGetLastError());
-    return reduce_sum(c, N.tE.p, c.nt, energy_dev);
+    if (na < 1) return cudaSuccess;
+    if (R.nblk > 0) {
+        k_seg_partial<<<dim3((unsigned)R.nblk, (unsigned)na), 256, 0, c.stream>>>(in, in_stride, R.blk.p,
+                                                                                 N.seg_part.p, stamp, pass);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    k_seg_final<<<dim3((unsigned)N.n_env, (unsigned)na), 1024, 0, c.stream>>>(N.seg_part.p, R.nblk, R.nblk_env.p,
+                                                                             R.first_blk.p, out, out_stride);
+    return cudaGetLastError();
 }
 
-cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_dev,
-                            int na, double* energies_dev) {
+cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess) {
     NewtonState& N = *c.newton;
     ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, c.X.p, N.mu, N.lam};
-    if (c.nt == 0) return cudaMemsetAsync(energies_dev, 0, sizeof(double) * na, c.stream);
-    k_nh_energy_multi<<<nblk(c.nt, 128), 128, 0, c.stream>>>(E, x, p, alphas_dev, na, N.tE8.p);
-    GMCP_CUDA_TRY(cudaGetLastError());
-    for (int j = 0; j < na; ++j) GMCP_CUDA_TRY(reduce_sum(c, N.tE8.p + (int64_t)j * c.nt, c.nt, energies_dev + j));
-    return cudaSuccess;
+    if (c.nt > 0) {
+        const bool f32 = c.P.precision == IPC_PREC_MIXED;
+        const unsigned g = nblk(c.nt, 128);
+        if (!want_hess)
+            k_nh_eval<false, double><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, nullptr, N.ebad.p, N.tet_env.p);
+        else if (f32)
+            k_nh_eval<true, float><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH32.p, N.ebad.p, N.tet_env.p);
+        else
+            k_nh_eval<true, double><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, N.tH64.p, N.ebad.p, N.tet_env.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    return seg_sum(c, N.seg_t, N.tE.p, 0, 1, N.es.p + kEsEe, kES);
+}
+
+cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na, int slot) {
+    NewtonState& N = *c.newton;
+    ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, c.X.p, N.mu, N.lam};
+    if (c.nt > 0) {
+        k_nh_energy_multi<<<nblk(c.nt, 128), 128, 0, c.stream>>>(E, x, p, alphas_env, 8, N.tet_env.p, na, N.tE8.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    return seg_sum(c, N.seg_t, N.tE8.p, c.nt, na, N.es.p + slot, kES);
 }
 
 cudaError_t assemble_grad(Ctx& c, const double* x, const double* xhat, const void* cgrad, bool cgrad_f32,
@@ -1137,12 +1248,13 @@ cudaError_t assemble_bsr(Ctx& c) {
     return cudaGetLastError();
 }
 
-// dot(a, b) -> out (device), fixed order
-cudaError_t dot_dev(Ctx& c, const double* a, const double* b, int64_t n, double* out) {
+// dot(a, b) per environment (3 nv entries) into es[slot], fixed order
+cudaError_t dot_env(Ctx& c, const double* a, const double* b, int slot) {
     NewtonState& N = *c.newton;
+    const int64_t n = 3 * c.nv;
     k_mul<<<nblk(n, 256), 256, 0, c.stream>>>(n, a, b, N.w.p);
     GMCP_CUDA_TRY(cudaGetLastError());
-    return reduce_sum(c, N.w.p, n, out);
+    return seg_sum(c, N.seg_v3, N.w.p, 0, 1, N.es.p + slot, kES);
 }
 
 // Block-Jacobi PCG for A p = b (A on the pattern N.rp / N.ci; FP32 in the
@@ -1314,6 +1426,27 @@ static void h_inv3(const double* A, double* I) {
     I[8] = (A[0] * A[4] - A[1] * A[3]) / d;
 }
 
+// blocks of 2048 elements counted from each segment's first element
+// (elements scale * off[e] .. scale * off[e + 1])
+static cudaError_t build_seg(SegRed& R, const std::vector<int64_t>& off, int64_t scale, cudaStream_t s) {
+    const int ne = (int)off.size() - 1;
+    std::vector<int4> blk;
+    std::vector<int32_t> nb(ne), fb(ne);
+    for (int e = 0; e < ne; ++e) {
+        const int64_t a = scale * off[e], b = scale * off[e + 1];
+        fb[e] = (int32_t)blk.size();
+        for (int64_t k = a; k < b; k += 2048)
+            blk.push_back(make_int4(e, (int)k, (int)std::min<int64_t>(k + 2048, b), fb[e]));
+        nb[e] = (int32_t)blk.size() - fb[e];
+    }
+    R.nblk = (int64_t)blk.size();
+    if (!blk.empty()) GMCP_CUDA_TRY(R.blk.upload(blk.data(), blk.size(), s));
+    GMCP_CUDA_TRY(R.nblk_env.upload(nb.data(), nb.size(), s));
+    GMCP_CUDA_TRY(R.first_blk.upload(fb.data(), fb.size(), s));
+    // host vectors must outlive the copies
+    return cudaStreamSynchronize(s);
+}
+
 cudaError_t newton_setup(Ctx& c) {
     if (c.newton) return cudaSuccess;
     auto Np = std::make_unique<NewtonState>();
@@ -1326,7 +1459,6 @@ cudaError_t newton_setup(Ctx& c) {
     std::vector<double> Dminv(9 * (size_t)nt), vol(nt), mass(nv, 0.0);
     const int32_t* T = c.h_tets.data();
     const double* X = c.h_X.data();
-    double vsum = 0.0;
     for (int64_t t = 0; t < nt; ++t) {
         const int32_t* Tt = T + 4 * t;
         double Dm[9];
@@ -1335,11 +1467,9 @@ cudaError_t newton_setup(Ctx& c) {
         const double det = Dm[0] * (Dm[4] * Dm[8] - Dm[5] * Dm[7]) - Dm[1] * (Dm[3] * Dm[8] - Dm[5] * Dm[6]) +
                            Dm[2] * (Dm[3] * Dm[7] - Dm[4] * Dm[6]);
         vol[t] = fabs(det) / 6.0;
-        vsum += vol[t];
         h_inv3(Dm, &Dminv[9 * t]);
         for (int a = 0; a < 4; ++a) mass[Tt[a]] += q.density * vol[t] / 4.0;
     }
-    N.lbar = nt > 0 ? cbrt(vsum / (double)nt) : 0.0;
     // vertex -> tet corner (t*4+a), increasing tet
     std::vector<int32_t> vte_off(nv + 1, 0), vte(4 * (size_t)nt);
     for (int64_t e = 0; e < 4 * nt; ++e) vte_off[T[e] + 1]++;
@@ -1499,6 +1629,60 @@ cudaError_t newton_setup(Ctx& c) {
     if (cudaMallocHost(reinterpret_cast<void**>(&N.h_pcg), sizeof(double) * 4 * ne) != cudaSuccess)
         return cudaErrorMemoryAllocation;
 
+    // The Newton iteration per environment: the environment of each vertex
+    // and tet, segmented sums over vertices (1 and 3 entries each), tets and
+    // slave triangles, the per-environment scalars, flags and step sizes, and
+    // pinned host copies of them.
+    if (c.env_tet_off[ne] != nt || c.env_stri_off[ne] != c.ns || 3 * nv > INT32_MAX) return cudaErrorInvalidValue;
+    {
+        std::vector<int32_t> venv(nv), tenv(nt);
+        N.h_lbar.assign(ne, 0.0);
+        N.h_has_dir.assign(ne, 0);
+        for (int e = 0; e < ne; ++e) {
+            for (int64_t v = c.env_vert_off[e]; v < c.env_vert_off[e + 1]; ++v) {
+                venv[v] = e;
+                if (c.h_dir[v]) N.h_has_dir[e] = 1;
+            }
+            double ve = 0.0;   // the order of the whole-scene sum, over this environment's tets
+            for (int64_t t = c.env_tet_off[e]; t < c.env_tet_off[e + 1]; ++t) {
+                tenv[t] = e;
+                ve += vol[t];
+            }
+            const int64_t nte = c.env_tet_off[e + 1] - c.env_tet_off[e];
+            N.h_lbar[e] = nte > 0 ? cbrt(ve / (double)nte) : 0.0;
+        }
+        GMCP_CUDA_TRY(N.vert_env.upload(venv.data(), venv.size(), s));
+        GMCP_CUDA_TRY(N.tet_env.upload(tenv.data(), tenv.size(), s));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    GMCP_CUDA_TRY(build_seg(N.seg_v, c.env_vert_off, 1, s));
+    GMCP_CUDA_TRY(build_seg(N.seg_v3, c.env_vert_off, 3, s));
+    GMCP_CUDA_TRY(build_seg(N.seg_t, c.env_tet_off, 1, s));
+    GMCP_CUDA_TRY(build_seg(N.seg_s, c.env_stri_off, 1, s));
+    const int64_t seg_max = std::max(std::max(N.seg_v.nblk, N.seg_v3.nblk), std::max(N.seg_t.nblk, N.seg_s.nblk));
+    GMCP_CUDA_TRY(N.seg_part.ensure(8 * (size_t)seg_max + 8));
+    GMCP_CUDA_TRY(N.es.ensure((size_t)kES * ne));
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.es.p, 0, sizeof(double) * kES * ne, s));
+    GMCP_CUDA_TRY(N.ebad.ensure((size_t)ne));
+    GMCP_CUDA_TRY(N.ealpha.ensure((size_t)ne));
+    GMCP_CUDA_TRY(N.eal.ensure(8 * (size_t)ne));
+    GMCP_CUDA_TRY(N.emask.ensure(4 * (size_t)ne));
+    GMCP_CUDA_TRY(N.ebits.ensure(2 * (size_t)ne));
+    GMCP_CUDA_TRY(N.ezero.ensure(1));
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.ezero.p, 0, sizeof(double), s));
+    {
+        const size_t bytes = sizeof(double) * ((size_t)kES + 8 + 1) * ne + sizeof(unsigned long long) * 2 * ne +
+                             sizeof(int32_t) * 5 * ne;
+        if (cudaMallocHost(&N.h_pin, bytes) != cudaSuccess) return cudaErrorMemoryAllocation;
+        char* q = (char*)N.h_pin;
+        N.h_es = (double*)q;                 q += sizeof(double) * kES * ne;
+        N.h_eal = (double*)q;                q += sizeof(double) * 8 * ne;
+        N.h_ealpha = (double*)q;             q += sizeof(double) * ne;
+        N.h_ebits = (unsigned long long*)q;  q += sizeof(unsigned long long) * 2 * ne;
+        N.h_emask = (int32_t*)q;             q += sizeof(int32_t) * 4 * ne;
+        N.h_ebad = (int32_t*)q;
+    }
+
     const size_t n3 = 3 * (size_t)nv;
     GMCP_CUDA_TRY(N.goff.upload(goff.data(), goff.size(), s));
     GMCP_CUDA_TRY(N.gslice.upload(gslice.data(), gslice.size(), s));
@@ -1566,9 +1750,7 @@ cudaError_t newton_setup(Ctx& c) {
         GMCP_CUDA_TRY(cudaMemcpyAsync(N.xm.p, c.Y0.p, sizeof(double) * 3 * c.nmv, cudaMemcpyDeviceToDevice, s));
     GMCP_CUDA_TRY(N.ein8.ensure(8 * (size_t)nv));
     GMCP_CUDA_TRY(N.triE8.ensure(8 * (size_t)c.ns + 8));
-    GMCP_CUDA_TRY(N.alphas.ensure(8));
     GMCP_CUDA_TRY(N.scal.ensure(64));
-    GMCP_CUDA_TRY(N.bad.ensure(4));
     // host vectors must outlive the asynchronous copies
     GMCP_CUDA_TRY(cudaStreamSynchronize(s));
     c.newton = std::move(Np);
@@ -1578,62 +1760,99 @@ cudaError_t newton_setup(Ctx& c) {
 // ---------------------------------------------------------------------------
 // energies and the assembled system
 // ---------------------------------------------------------------------------
-// total incremental potential at x + alphas[j] p, j < na (<= 8), into
-// out_dev[j]; the contact term is the frozen-linear potential of the samples
-// active at x (requires the candidate lists of x)
-cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_dev, int na,
-                         bool with_contact, double* out_dev, const double* ee0_dev) {
+// total incremental potential of each environment at x + alphas_env[8 e +
+// j] p, j < na (<= 8), into es[kEsE8 + j]; the contact term is the
+// frozen-linear potential of the samples active at x (requires the candidate
+// lists of x).  ee0: alphas_env[8 e] = 0 and es[kEsEe] holds the elastic
+// energy at x (the same per-tet values and the same fixed-order sum), so
+// slot 0's elastic energy is not evaluated again.
+cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_env, int na,
+                         bool with_contact, bool ee0) {
     NewtonState& N = *c.newton;
-    double* sc = N.scal.p;   // [16..23] Ein  [24..31] Ee  [32..39] Ec
-    if (ee0_dev && na > 1) {
-        // alphas[0] = 0: the elastic energy at x is known (same per-tet
-        // values and the same fixed-order sum)
-        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_dev + 1, na - 1, sc + 25));
-        GMCP_CUDA_TRY(cudaMemcpyAsync(sc + 24, ee0_dev, sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    double* es = N.es.p;
+    const int ne = N.n_env;
+    if (ee0 && na > 1) {
+        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_env + 1, na - 1, kEsEe8 + 1));
+        GMCP_CUDA_TRY(cudaMemcpy2DAsync(es + kEsEe8, kES * sizeof(double), es + kEsEe, kES * sizeof(double),
+                                        sizeof(double), ne, cudaMemcpyDeviceToDevice, c.stream));
     } else {
-        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_dev, na, sc + 24));
+        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_env, na, kEsEe8));
     }
-    k_inertia_multi<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, p, N.xhat.p, N.mass.p, alphas_dev, na, N.ein8.p);
+    k_inertia_multi<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, p, N.xhat.p, N.mass.p, alphas_env, 8,
+                                                           N.vert_env.p, na, N.ein8.p);
     GMCP_CUDA_TRY(cudaGetLastError());
-    for (int j = 0; j < na; ++j) GMCP_CUDA_TRY(reduce_sum(c, N.ein8.p + (int64_t)j * c.nv, c.nv, sc + 16 + j));
-    if (with_contact) GMCP_CUDA_TRY(contact_lagged(c, x, N.xm.p, p, alphas_dev, na, N.triE8.p, sc + 32));
+    GMCP_CUDA_TRY(seg_sum(c, N.seg_v, N.ein8.p, c.nv, na, es + kEsEin8, kES));
+    if (with_contact) {
+        GMCP_CUDA_TRY(contact_lagged(c, x, N.xm.p, p, alphas_env, na, N.triE8.p, nullptr, 8));
+        GMCP_CUDA_TRY(seg_sum(c, N.seg_s, N.triE8.p, c.ns, na, es + kEsEc8, kES));
+    }
     const double h2 = c.prm.h * c.prm.h;
-    k_combine<<<1, 32, 0, c.stream>>>(na, sc + 16, sc + 24, with_contact ? sc + 32 : nullptr, h2, out_dev);
+    k_combine<<<ne, 32, 0, c.stream>>>(na, es + kEsEin8, es + kEsEe8, with_contact ? es + kEsEc8 : nullptr, h2,
+                                       es + kEsE8);
     return cudaGetLastError();
 }
 
-// E, gradient G (Dirichlet rows zero), optionally the matrix A, and |G|^2 at
-// x; the broad phase runs at (x, current master).  Outputs: Ec_dev, Ee_dev
-// (contact and elastic potentials), E_dev (total), gnorm2_dev, and the
-// inverted-tet flag in N.bad.
-cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess, double* Ec_dev, double* Ee_dev,
-                            double* E_dev, double* gnorm2_dev) {
+// per environment: contact and elastic potentials es[kEsEc], es[kEsEe], the
+// total es[kEsE] and |G|^2 es[kEsG2] at x, the gradient G (Dirichlet rows
+// zero), optionally the matrix A; inverted-tet flags in N.ebad.  The broad
+// phase runs at (x, current master).
+cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess) {
     NewtonState& N = *c.newton;
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    GMCP_CUDA_TRY(cudaMemsetAsync(N.bad.p, 0, sizeof(int32_t), c.stream));
+    double* es = N.es.p;
+    const int ne = N.n_env;
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.ebad.p, 0, sizeof(int32_t) * ne, c.stream));
     {
         ProfScope ps(c.prof, c.stream, "elastic");
-        GMCP_CUDA_TRY(nh_eval(c, x, want_hess, Ee_dev, N.bad.p));
+        GMCP_CUDA_TRY(nh_eval(c, x, want_hess));
     }
     GMCP_CUDA_TRY(run_candidates(c, x, N.xm.p));
     void* cg = f32 ? (void*)N.cgrad32.p : (void*)N.cgrad64.p;
-    GMCP_CUDA_TRY(contact_eval(c, x, N.xm.p, Ec_dev, cg, want_hess, nullptr));
+    GMCP_CUDA_TRY(contact_eval(c, x, N.xm.p, nullptr, cg, want_hess, nullptr));
+    // the contact energy of the samples of this pass (stamped triangles)
+    GMCP_CUDA_TRY(seg_sum(c, N.seg_s, c.tri_E.p, 0, 1, es + kEsEc, kES, c.tri_stamp.p, c.misc_i32.p + kSlotPass));
     {
         ProfScope ps(c.prof, c.stream, "assemble");
         GMCP_CUDA_TRY(assemble_grad(c, x, N.xhat.p, cg, f32, N.G.p));
         if (want_hess) GMCP_CUDA_TRY(assemble_bsr(c));
     }
-    // total energy: inertia at x (slot 0 with alpha 0, p unused)
-    double* sc = N.scal.p;
-    const double zero = 0.0;
-    GMCP_CUDA_TRY(cudaMemcpyAsync(N.alphas.p, &zero, sizeof(double), cudaMemcpyHostToDevice, c.stream));
-    k_inertia_multi<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, nullptr, N.xhat.p, N.mass.p, N.alphas.p, 1, N.ein8.p);
+    // total energy: inertia at x (one term, alpha 0, p unused)
+    k_inertia_multi<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, nullptr, N.xhat.p, N.mass.p, N.ezero.p, 0,
+                                                           N.vert_env.p, 1, N.ein8.p);
     GMCP_CUDA_TRY(cudaGetLastError());
-    GMCP_CUDA_TRY(reduce_sum(c, N.ein8.p, c.nv, sc + 40));
+    GMCP_CUDA_TRY(seg_sum(c, N.seg_v, N.ein8.p, 0, 1, es + kEsEin, kES));
     const double h2 = c.prm.h * c.prm.h;
-    k_combine<<<1, 32, 0, c.stream>>>(1, sc + 40, Ee_dev, Ec_dev, h2, E_dev);
+    k_combine<<<ne, 32, 0, c.stream>>>(1, es + kEsEin, es + kEsEe, es + kEsEc, h2, es + kEsE);
     GMCP_CUDA_TRY(cudaGetLastError());
-    return dot_dev(c, N.G.p, N.G.p, 3 * c.nv, gnorm2_dev);
+    return dot_env(c, N.G.p, N.G.p, kEsG2);
+}
+
+// ------------------------------------------------- per-environment vectors ---
+cudaError_t vec_axpy_env(Ctx& c, const double* x, const double* p, const double* alpha_env, const int32_t* mask,
+                         double* out) {
+    NewtonState& N = *c.newton;
+    k_axpy_env<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, p, alpha_env, mask, N.vert_env.p, out);
+    return cudaGetLastError();
+}
+cudaError_t vec_copy_env(Ctx& c, const double* src, const int32_t* mask, double* dst) {
+    NewtonState& N = *c.newton;
+    k_copy_env<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, src, mask, N.vert_env.p, dst);
+    return cudaGetLastError();
+}
+cudaError_t vec_zero_env(Ctx& c, const int32_t* mask, double* a) {
+    NewtonState& N = *c.newton;
+    k_zero_env<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, mask, N.vert_env.p, a);
+    return cudaGetLastError();
+}
+cudaError_t vec_copy_master_env(Ctx& c, const double* src, const int32_t* mask, double* dst) {
+    if (c.nmv == 0) return cudaSuccess;
+    k_copy_env<<<nblk(c.nmv, 256), 256, 0, c.stream>>>(c.nmv, src, mask, c.mvert_env.p, dst);
+    return cudaGetLastError();
+}
+cudaError_t vec_velocity_env(Ctx& c, const double* x, const double* xt, const int32_t* mask, double* v) {
+    NewtonState& N = *c.newton;
+    k_velocity_env<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, xt, c.prm.h, mask, N.vert_env.p, v);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- vectors ---
