@@ -352,7 +352,7 @@ def run_ours(args):
         line["batched"] = batched_measurement(dev, n_env=args.batch_envs)
     if not args.no_newton:
         line["newton_step"] = newton_measurement(dev)
-        line["batched_step"] = batched_step_measurement(dev, n_env=args.step_envs)
+        line["batched_step"] = batched_step_measurement(dev, n_env=args.step_envs, steps=10)
         line["warm_start"] = warm_start_measurement(dev)
     if not args.no_dual_map:
         line["dual_mesh"] = dual_mesh_measurement(dev)
@@ -773,7 +773,7 @@ def newton_measurement(dev, start_step=20, n_states=4):
     return out
 
 
-def batched_step_measurement(dev, n_env=16, steps=3):
+def batched_step_measurement(dev, n_env=16, steps=3, alone_envs=16):
     """Batched time steps (ipc_newton_step_envs): n_env fingertip environments
     of the batched workload's recipe with their tetrahedra (5 pads of 16-128
     quads of 0.25 mm, 2 tet layers, around a perturbed convex object of
@@ -783,13 +783,26 @@ def batched_step_measurement(dev, n_env=16, steps=3):
     stopping; one call steps them all.  Timed: ``steps`` batched steps after
     one untimed step (which builds the time-stepper state), and the same
     steps taken one environment at a time with a context per environment
-    (the batch's results are bit for bit those)."""
+    (the batch's results are bit for bit those), for the first
+    ``alone_envs`` environments; the comparison is in environment-steps
+    per second."""
     import torch
     from paper_2605_24339_b300 import binding
     from paper_2605_24339_b300 import scenes as S
     dhat = 1e-4
-    parts = [S._fingertip_env(e, 5, (16, 128), 0.25e-3, 2, 0.5e-3, (2000, 80000), 15e-3, dhat, 1e5, 1e-3,
-                              0.5e-3, 100, 3, 1, 1.5 * dhat, True) for e in range(n_env)]
+    args = (5, (16, 128), 0.25e-3, 2, 0.5e-3, (2000, 80000), 15e-3, dhat, 1e5, 1e-3, 0.5e-3, 100, 3, 1,
+            1.5 * dhat, True)
+    t0 = time.perf_counter()
+    workers = max(1, min(32, os.cpu_count() or 1))
+    if n_env > 16 and workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(S._fingertip_env, range(n_env), *[[a] * n_env for a in args],
+                                chunksize=max(1, n_env // (4 * workers))))
+    else:
+        parts = [S._fingertip_env(e, *args) for e in range(n_env)]
+    gen_s = time.perf_counter() - t0
     sc = S.concat_envs([p[0] for p in parts], name="fingertip_batch")
     x0 = np.concatenate([p[1] for p in parts])
     top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
@@ -798,11 +811,17 @@ def batched_step_measurement(dev, n_env=16, steps=3):
                        f"2k-80k-tri objects, pads 1.5 dhat pressed, top faces at 0.5 mm/s, h = 1 ms",
            "n_env": n_env, "n_vert": int(sc.X.shape[0]), "n_tet": int(sc.tets.shape[0]),
            "slave_tris": int(sc.stris.shape[0]), "master_tris": int(sc.mtris.shape[0]),
-           "newton_tol": sc.params["newton_tol"]}
+           "newton_tol": sc.params["newton_tol"], "scene_build_s": round(gen_s, 1)}
+    t0 = time.perf_counter()
     ctx = binding.Context(sc, precision="mixed", device=dev)
     x = torch.as_tensor(x0, device="cuda")
     v = vd.clone()
+    torch.cuda.synchronize()
+    out["context_create_s"] = round(time.perf_counter() - t0, 2)
+    t0 = time.perf_counter()
     ctx.newton_step_envs(x, v)
+    torch.cuda.synchronize()
+    out["first_step_s_with_setup"] = round(time.perf_counter() - t0, 2)
     v[top] = vd[top]
     times, iters, statuses = [], [], []
     for _ in range(steps):
@@ -814,6 +833,8 @@ def batched_step_measurement(dev, n_env=16, steps=3):
         v[top] = vd[top]
         iters.append([q["newton_iters"] for q in per])
         statuses.append(sorted(set(q["status"] for q in per)))
+    free_b, total_b = torch.cuda.mem_get_info()
+    out["gpu_mem_used_gb"] = round((total_b - free_b) / 1e9, 1)
     ctx.close()
     ms = statistics.median(times)
     out["batched"] = {"ms_per_step_median": ms, "ms_per_step": [round(t, 1) for t in times],
@@ -822,8 +843,7 @@ def batched_step_measurement(dev, n_env=16, steps=3):
                       "statuses": statuses}
     # the same states stepped one environment at a time
     seq = []
-    vo = 0
-    for e, (pe, xe) in enumerate(parts):
+    for e, (pe, xe) in enumerate(parts[:alone_envs]):
         c = binding.Context(pe, precision="mixed", device=dev, params=sc.params)
         xg = torch.as_tensor(xe, device="cuda")
         tp = torch.as_tensor(pe.dirichlet.astype(bool), device="cuda")
@@ -841,10 +861,12 @@ def batched_step_measurement(dev, n_env=16, steps=3):
             vg[tp] = vde[tp]
         c.close()
         seq.append(tt)
+    na = len(seq)
     seq_ms = [sum(t[k] for t in seq) for k in range(steps)]
-    out["one_env_at_a_time"] = {"ms_per_step_median": statistics.median(seq_ms),
-                                "env_steps_per_s": n_env / (statistics.median(seq_ms) / 1e3)}
-    out["speedup_batched_vs_one_at_a_time"] = statistics.median(seq_ms) / ms
+    rate = na / (statistics.median(seq_ms) / 1e3)
+    out["one_env_at_a_time"] = {"envs": na, "ms_for_these_envs_median": statistics.median(seq_ms),
+                                "env_steps_per_s": rate}
+    out["env_steps_per_s_batched_over_one_at_a_time"] = out["batched"]["env_steps_per_s"] / rate
     return out
 
 
@@ -1116,7 +1138,7 @@ def main():
                     help="skip the time-step measurement (newton_step key)")
     ap.add_argument("--batch-envs", type=int, default=512,
                     help="environments in the batched measurement")
-    ap.add_argument("--step-envs", type=int, default=16,
+    ap.add_argument("--step-envs", type=int, default=64,
                     help="environments in the batched time-step measurement")
     ap.add_argument("--dense-quads", type=int, default=256,
                     help="--mode dense_passes: gel pad quads per side (256 = the measured workload)")
