@@ -1489,7 +1489,13 @@ typedef struct {
     double h, rho, E, nu, mu, lam, grav[3];
     double tol, pcg_tol; int max_newton, max_pcg, max_halv; double slack; int ccd_max_iter;
     int32_t* rp; int32_t* ci; int64_t nnzb;
-    double* xm;     /* current master positions */
+    double* xm;     /* current master positions (kinematic master) */
+    /* deformable master (joint step): the system's vertices are the pad's
+     * npad vertices followed by the master's; own copies of the system's
+     * rest positions, tets and Dirichlet flags; external nodal forces */
+    int joint, npad;
+    double* Xsys; int32_t* Tsys; uint8_t* Dsys;
+    double* fext;
 } orc_sim;
 
 typedef struct {
@@ -1500,11 +1506,81 @@ typedef struct {
     int pred_used;           /* 1 if the predicted start was taken */
 } orc_stats;
 
+/* extra (row, col) pairs of the block pattern, both orders (joint step) */
+typedef struct { int32_t* a; int64_t n, cap; } pvec;
+static void pvec_push(pvec* v, int32_t i, int32_t j) {
+    if (v->n + 2 > v->cap) { v->cap = v->cap ? 2 * v->cap : 4096; v->a = (int32_t*)realloc(v->a, sizeof(int32_t) * 2 * v->cap); }
+    v->a[2 * v->n] = i; v->a[2 * v->n + 1] = j; ++v->n;
+    v->a[2 * v->n] = j; v->a[2 * v->n + 1] = i; ++v->n;
+}
+
+static orc_sim* sim_init(orc_sim* s, orc_scene* sc, int nv, const double* X, int nt, const int32_t* tets,
+                         const uint8_t* dir, double h, double rho, double E, double nu,
+                         const double* grav, double tol, double pcg_tol, int max_newton,
+                         int max_pcg, int max_halv, double slack, int ccd_max_iter, const pvec* extra);
+
 ORC_API orc_sim* orc_sim_create(orc_scene* sc, int nv, const double* X, int nt, const int32_t* tets,
                                 const uint8_t* dir, double h, double rho, double E, double nu,
                                 const double* grav, double tol, double pcg_tol, int max_newton,
                                 int max_pcg, int max_halv, double slack, int ccd_max_iter) {
     orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+    return sim_init(s, sc, nv, X, nt, tets, dir, h, rho, E, nu, grav, tol, pcg_tol, max_newton, max_pcg,
+                    max_halv, slack, ccd_max_iter, NULL);
+}
+
+/* Joint step with a deformable master (Sec. 4.2-4.3 with Eq. gap: the
+ * contact potential depends on the master vertices through x_m): the system
+ * is the pad (npad vertices, ntp tets, Dirichlet flags dir) followed by the
+ * master body (the scene's nmv master vertices at rest sc->Y0, nmt4 tets
+ * mtets over master vertex indices, Dirichlet flags mdir), one material.
+ * The block pattern also holds every (slave-triangle vertex, master-triangle
+ * vertex) pair of the same environment, so every contact block has a place.
+ * Single environment. */
+ORC_API orc_sim* orc_sim_create_joint(orc_scene* sc, int npad, const double* X, int ntp, const int32_t* tets,
+                                      const uint8_t* dir, int nmt4, const int32_t* mtets, const uint8_t* mdir,
+                                      double h, double rho, double E, double nu, const double* grav, double tol,
+                                      double pcg_tol, int max_newton, int max_pcg, int max_halv, double slack,
+                                      int ccd_max_iter) {
+    orc_sim* s = (orc_sim*)calloc(1, sizeof(orc_sim));
+    const int nm = (int)sc->nmv, nsys = npad + nm, nts = ntp + nmt4;
+    s->joint = 1;
+    s->npad = npad;
+    s->Xsys = (double*)malloc(sizeof(double) * 3 * (size_t)nsys);
+    s->Tsys = (int32_t*)malloc(sizeof(int32_t) * 4 * (size_t)(nts > 0 ? nts : 1));
+    s->Dsys = (uint8_t*)calloc((size_t)nsys, 1);
+    memcpy(s->Xsys, X, sizeof(double) * 3 * (size_t)npad);
+    memcpy(s->Xsys + 3 * (size_t)npad, sc->Y0, sizeof(double) * 3 * (size_t)nm);
+    memcpy(s->Tsys, tets, sizeof(int32_t) * 4 * (size_t)ntp);
+    for (int64_t e = 0; e < 4 * (int64_t)nmt4; ++e) s->Tsys[4 * (int64_t)ntp + e] = npad + mtets[e];
+    memcpy(s->Dsys, dir, (size_t)npad);
+    if (mdir) memcpy(s->Dsys + npad, mdir, (size_t)nm);
+    pvec extra = {0, 0, 0};
+    for (int64_t t = 0; t < sc->ns; ++t)
+        for (int64_t m = 0; m < sc->nmt; ++m) {
+            if (sc->stri_env[t] != sc->mtri_env[m]) continue;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) pvec_push(&extra, sc->stri[3 * t + a], npad + sc->mtri[3 * m + b]);
+        }
+    for (int64_t m = 0; m < sc->nmt; ++m)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (a != b) pvec_push(&extra, npad + sc->mtri[3 * m + a], npad + sc->mtri[3 * m + b]);
+    sim_init(s, sc, nsys, s->Xsys, nts, s->Tsys, s->Dsys, h, rho, E, nu, grav, tol, pcg_tol, max_newton, max_pcg,
+             max_halv, slack, ccd_max_iter, &extra);
+    free(extra.a);
+    return s;
+}
+
+/* external nodal forces f [nsys][3] (joint step): the energy gains -h^2 f.x */
+ORC_API void orc_sim_set_fext(orc_sim* s, const double* f) {
+    if (!s->fext) s->fext = (double*)malloc(sizeof(double) * 3 * (size_t)s->nv);
+    memcpy(s->fext, f, sizeof(double) * 3 * (size_t)s->nv);
+}
+
+static orc_sim* sim_init(orc_sim* s, orc_scene* sc, int nv, const double* X, int nt, const int32_t* tets,
+                         const uint8_t* dir, double h, double rho, double E, double nu,
+                         const double* grav, double tol, double pcg_tol, int max_newton,
+                         int max_pcg, int max_halv, double slack, int ccd_max_iter, const pvec* extra) {
     s->sc = sc; s->nv = nv; s->nt = nt; s->X = X; s->tets = tets; s->dir = dir;
     s->h = h; s->rho = rho; s->E = E; s->nu = nu;
     s->mu = E / (2.0 * (1.0 + nu)); s->lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
@@ -1524,9 +1600,11 @@ ORC_API orc_sim* orc_sim_create(orc_scene* sc, int nv, const double* X, int nt, 
         for (int a = 0; a < 4; ++a) s->mass[T[a]] += rho * s->vol[t] / 4.0;
     }
     /* block pattern: vertex adjacency through tets, plus the diagonal */
-    int32_t* pr = (int32_t*)malloc(sizeof(int32_t) * 2 * (16 * (size_t)nt + nv));
+    const int64_t nx = extra ? extra->n : 0;
+    int32_t* pr = (int32_t*)malloc(sizeof(int32_t) * 2 * (16 * (size_t)nt + nv + (size_t)nx));
     int64_t np = 0;
     for (int v = 0; v < nv; ++v) { pr[2 * np] = v; pr[2 * np + 1] = v; ++np; }
+    for (int64_t e = 0; e < nx; ++e) { pr[2 * np] = extra->a[2 * e]; pr[2 * np + 1] = extra->a[2 * e + 1]; ++np; }
     for (int t = 0; t < nt; ++t)
         for (int a = 0; a < 4; ++a)
             for (int b = 0; b < 4; ++b)
@@ -1549,7 +1627,8 @@ ORC_API orc_sim* orc_sim_create(orc_scene* sc, int nv, const double* X, int nt, 
 
 ORC_API void orc_sim_free(orc_sim* s) {
     if (!s) return;
-    free(s->Dminv); free(s->vol); free(s->mass); free(s->rp); free(s->ci); free(s->xm); free(s);
+    free(s->Dminv); free(s->vol); free(s->mass); free(s->rp); free(s->ci); free(s->xm);
+    free(s->Xsys); free(s->Tsys); free(s->Dsys); free(s->fext); free(s);
 }
 ORC_API int64_t orc_sim_nnzb(const orc_sim* s) { return s->nnzb; }
 ORC_API void orc_sim_mass(const orc_sim* s, double* out) { memcpy(out, s->mass, sizeof(double) * s->nv); }
@@ -1666,8 +1745,13 @@ static int newton_eval(const orc_sim* s, const double* x, const double* xhat, do
             G[3 * i + c] += s->mass[i] * d;
         }
     if (A) for (int i = 0; i < nv; ++i) { int64_t k = blk_index(s, i, i); for (int c = 0; c < 3; ++c) A[9 * k + 4 * c] += s->mass[i]; }
+    /* external forces (joint step): -h^2 f.x */
+    double Ef = 0.0;
+    if (s->fext)
+        for (int i = 0; i < 3 * nv; ++i) { Ef -= s->fext[i] * x[i]; G[i] -= h2 * s->fext[i]; }
     samples->n = 0;
-    collect_samples(s->sc, x, s->xm, 0, NULL, samples);
+    const double* xm = s->joint ? x + 3 * (size_t)s->npad : s->xm;
+    collect_samples(s->sc, x, xm, 0, NULL, samples);
     double Ec = 0.0;
     for (int64_t q = 0; q < samples->n; ++q) {
         const orc_sample* k = samples->a + q;
@@ -1688,8 +1772,31 @@ static int newton_eval(const orc_sim* s, const double* x, const double* xhat, do
                         for (int qq = 0; qq < 3; ++qq) A[9 * bi + 3 * p + qq] += h2 * c2 * k->bs[a] * k->bs[b] * k->ns[p] * k->ns[qq];
                 }
         }
+        if (!s->joint) continue;
+        /* deformable master: the gap gradient is bm_j n_s on master vertex
+         * j; its rows and its blocks with the slave and master vertices */
+        for (int j = 0; j < 3; ++j) {
+            if (k->mv[j] < 0) continue;
+            const int mj = s->npad + k->mv[j];
+            for (int c = 0; c < 3; ++c) G[3 * mj + c] += h2 * c1 * k->bm[j] * k->ns[c];
+            if (!A) continue;
+            for (int r = 0; r < 6; ++r) {
+                int row;
+                double wr;
+                if (r < 3) { if (T[r] < 0) continue; row = T[r]; wr = -k->bs[r]; }
+                else { if (k->mv[r - 3] < 0) continue; row = s->npad + k->mv[r - 3]; wr = k->bm[r - 3]; }
+                const int64_t b1 = blk_index(s, row, mj), b2 = blk_index(s, mj, row);
+                if (b1 < 0 || b2 < 0) { fprintf(stderr, "orc: contact block outside the pattern\n"); abort(); }
+                for (int p = 0; p < 3; ++p)
+                    for (int qq = 0; qq < 3; ++qq) {
+                        const double v = h2 * c2 * wr * k->bm[j] * k->ns[p] * k->ns[qq];
+                        A[9 * b1 + 3 * p + qq] += v;
+                        if (r < 3) A[9 * b2 + 3 * p + qq] += v;   /* its transpose (n n^T is symmetric) */
+                    }
+            }
+        }
     }
-    *E = Ein + h2 * (Ee + Ec);
+    *E = Ein + h2 * (Ee + Ec + Ef);
     for (int i = 0; i < nv; ++i)
         if (s->dir[i]) {
             for (int c = 0; c < 3; ++c) G[3 * i + c] = 0.0;
@@ -1715,19 +1822,30 @@ static double lagged_energy(const orc_sim* s, const double* x, const double* xha
     for (int i = 0; i < nv; ++i)
         for (int c = 0; c < 3; ++c) { double d = tmp[3 * i + c] - xhat[3 * i + c]; Ein += 0.5 * s->mass[i] * d * d; }
     double Ec = 0.0;
+    const double* pm = s->joint ? p + 3 * (size_t)s->npad : NULL;
     for (int64_t q = 0; q < smp->n; ++q) {
         const orc_sample* k = smp->a + q;
-        double gt = k->g + a * sample_dgdx(s->sc, k, p, NULL);
+        double gt = k->g + a * sample_dgdx(s->sc, k, p, pm);
         if (!(gt > 0.0)) return INFINITY;
         double B, dB, d2B;
         orc_barrier(gt, k->eps, &B, &dB, &d2B);
         Ec += k->kq * k->w * k->gamma * B;
     }
-    return Ein + s->h * s->h * (Ee + Ec);
+    double Ef = 0.0;
+    if (s->fext)
+        for (int i = 0; i < 3 * nv; ++i) Ef -= s->fext[i] * tmp[i];
+    return Ein + s->h * s->h * (Ee + Ec + Ef);
 }
 
 static double max_step_to(const orc_sim* s, const double* x, const double* dP) {
-    return orc_ccd_max_step(s->sc, x, dP, s->xm, NULL, s->slack, s->ccd_max_iter, NULL, NULL);
+    if (!s->joint) return orc_ccd_max_step(s->sc, x, dP, s->xm, NULL, s->slack, s->ccd_max_iter, NULL, NULL);
+    /* both bodies move: the master part of x and dP is its motion */
+    const double* xm = x + 3 * (size_t)s->npad;
+    const double* dm = dP + 3 * (size_t)s->npad;
+    orc_accd_info info;
+    const double al = orc_alpha_lin(s->sc, x, xm, dP, dm);
+    const double aa = orc_accd_min(s->sc, x, dP, xm, dm, s->slack, s->ccd_max_iter, &info);
+    return dmin(1.0, dmin(al, aa));
 }
 
 /* start point: Dirichlet vertices at xhat, free vertices moved toward P by
@@ -1783,8 +1901,8 @@ ORC_API int orc_newton_step(orc_sim* s, double* x, double* v, const double* xm_n
     memcpy(xt, x, sizeof(double) * n);
     for (int i = 0; i < nv; ++i) for (int c = 0; c < 3; ++c) xhat[3 * i + c] = x[3 * i + c] + h * v[3 * i + c] + h * h * s->grav[c];
     int status = 0;
-    /* master motion with the pad held at x^t */
-    if (xm_next) {
+    /* master motion with the pad held at x^t (kinematic master only) */
+    if (xm_next && !s->joint) {
         double* z = (double*)calloc((size_t)n, sizeof(double));
         double a = orc_ccd_max_step(s->sc, x, z, s->xm, xm_next, s->slack, s->ccd_max_iter, NULL, NULL);
         free(z);

@@ -101,6 +101,9 @@ def _declare(L):
     L.orc_nh_tet.restype = I; L.orc_nh_tet.argtypes = [P, D, D, D, P, P, dp, P, P]
     L.orc_sim_create.restype = P
     L.orc_sim_create.argtypes = [P, I, P, I, P, P, D, D, D, D, P, D, D, I, I, I, D, I]
+    L.orc_sim_create_joint.restype = P
+    L.orc_sim_create_joint.argtypes = [P, I, P, I, P, P, I, P, P, D, D, D, D, P, D, D, I, I, I, D, I]
+    L.orc_sim_set_fext.argtypes = [P, P]
     L.orc_sim_free.argtypes = [P]
     L.orc_sim_nnzb.restype = I64; L.orc_sim_nnzb.argtypes = [P]
     L.orc_sim_mass.argtypes = [P, P]
@@ -374,11 +377,25 @@ class Sim:
                           Dr=np.ascontiguousarray(sc.dirichlet, dtype=np.uint8),
                           g=_f64(p["gravity"]))
         k = self._keep
-        self.h = lib().orc_sim_create(
-            scene.h, sc.X.shape[0], _p(scene._keep["X"]), sc.tets.shape[0], _p(k["T"]),
-            _p(k["Dr"]), p["h"], p["density"], p["youngs"], p["poisson"], _p(k["g"]),
-            p["newton_tol"], p["pcg_rel_tol"], int(p["max_newton"]), int(p["max_pcg"]),
-            int(p["max_halvings"]), p["ccd_slack"], int(p["ccd_max_iter"]))
+        self.joint = getattr(sc, "mtets", None) is not None
+        if self.joint:
+            # deformable master: the system is the pad, then the master body
+            k["MT"] = np.ascontiguousarray(sc.mtets, dtype=np.int32)
+            md = getattr(sc, "mdirichlet", None)
+            k["MD"] = np.ascontiguousarray(md if md is not None else np.zeros(sc.Y0.shape[0]), dtype=np.uint8)
+            self.h = lib().orc_sim_create_joint(
+                scene.h, sc.X.shape[0], _p(scene._keep["X"]), sc.tets.shape[0], _p(k["T"]), _p(k["Dr"]),
+                k["MT"].shape[0], _p(k["MT"]), _p(k["MD"]), p["h"], p["density"], p["youngs"], p["poisson"],
+                _p(k["g"]), p["newton_tol"], p["pcg_rel_tol"], int(p["max_newton"]), int(p["max_pcg"]),
+                int(p["max_halvings"]), p["ccd_slack"], int(p["ccd_max_iter"]))
+            self.nsys = sc.X.shape[0] + sc.Y0.shape[0]
+        else:
+            self.h = lib().orc_sim_create(
+                scene.h, sc.X.shape[0], _p(scene._keep["X"]), sc.tets.shape[0], _p(k["T"]),
+                _p(k["Dr"]), p["h"], p["density"], p["youngs"], p["poisson"], _p(k["g"]),
+                p["newton_tol"], p["pcg_rel_tol"], int(p["max_newton"]), int(p["max_pcg"]),
+                int(p["max_halvings"]), p["ccd_slack"], int(p["ccd_max_iter"]))
+            self.nsys = sc.X.shape[0]
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -390,9 +407,14 @@ class Sim:
         return lib().orc_sim_nnzb(self.h)
 
     def mass(self):
-        out = np.zeros(self.scene.sc.X.shape[0])
+        out = np.zeros(self.nsys)
         lib().orc_sim_mass(self.h, _p(out))
         return out
+
+    def set_fext(self, f):
+        """External nodal forces [nsys, 3] of the joint step."""
+        self._keep["F"] = _f64(f).copy()
+        lib().orc_sim_set_fext(self.h, _p(self._keep["F"]))
 
     def set_master(self, xm):
         xm = _f64(xm)
@@ -406,7 +428,7 @@ class Sim:
         return x, v, st
 
     def pattern(self):
-        nv = self.scene.sc.X.shape[0]
+        nv = self.nsys
         rp = np.zeros(nv + 1, dtype=np.int32)
         ci = np.zeros(self.nnzb, dtype=np.int32)
         lib().orc_sim_pattern(self.h, _p(rp), _p(ci))

@@ -34,7 +34,7 @@ import numpy as np
 __all__ = [
     "Scene", "splitmix64_stream", "pad_slab", "icosphere", "perlin2",
     "height_field", "tactile_indent", "gel_on_terrain", "gel_dense", "fingertip_batch",
-    "drape_on_master", "concat_envs",
+    "drape_on_master", "concat_envs", "patch_test", "top_face_tris",
 ]
 
 _MASK64 = (1 << 64) - 1
@@ -256,6 +256,10 @@ class Scene:
     params: dict
     name: str = ""
     n_steps: int = 10
+    # deformable master (joint step): tets over the master vertices and
+    # their Dirichlet flags; None = a kinematic master
+    mtets: Optional[np.ndarray] = None
+    mdirichlet: Optional[np.ndarray] = None
 
     @property
     def n_env(self) -> int:
@@ -348,6 +352,55 @@ def _finish_params(p, X, S):
     if p.get("kappa_guard") is None:
         p["kappa_guard"] = 0.0          # primitive guard barrier off by default
     return p
+
+
+def top_face_tris(nx: int, ny: int, nz: int):
+    """Top-face triangles of ``pad_slab(nx, ny, nz, ...)``, oriented so that
+    (x1-x0)x(x2-x0) points to +z (out of the slab)."""
+    def vid(ii, jj):
+        return ii + (nx + 1) * (jj + (ny + 1) * nz)
+    F = []
+    for i in range(nx):
+        for j in range(ny):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            F.append((a, b, c))
+            F.append((a, c, d))
+    return np.asarray(F, dtype=np.int32)
+
+
+def patch_test(slave_n=(5, 5, 2), master_n=(4, 4, 2), gap=0.002, dhat=1e-3, kappa=1e4, youngs=1000.0,
+               poisson=0.0, pressure=10.0, h=1.0, density=1.0, face_rule_level=1, shift=(0.0, 0.0)):
+    """Contact patch test (Sec. 5.1, "Contact patch test"): two elastic blocks
+    of 1 x 1 x 0.5, the upper one ``gap`` above the lower one, with
+    non-matching structured tet meshes (``slave_n`` and ``master_n`` cells
+    along x, y, z).  The upper block is the pad: its bottom face is the slave
+    (tactile) surface.  The lower block is a deformable master: its top face
+    gives the master triangles, its bottom face is held (Dirichlet).  A
+    uniform pressure on the upper block's top face is applied as nodal forces
+    (each top triangle's force split evenly over its vertices).  With Poisson
+    ratio 0 the exact static state is a uniform stress sigma_zz = -pressure in
+    both blocks.  Returns (scene, f_ext) with f_ext [n_pad + n_master, 3];
+    ``scene.mtets`` / ``scene.mdirichlet`` describe the master body."""
+    sx, sy, sz = slave_n
+    mx, my, mz = master_n
+    Xm, Tm, _, _ = pad_slab(mx, my, mz, 1.0 / mx, 0.5 / mz, origin=(shift[0], shift[1], 0.0))
+    Fm = top_face_tris(mx, my, mz)
+    Xs, Ts, Bs, top_s = pad_slab(sx, sy, sz, 1.0 / sx, 0.5 / sz, origin=(0.0, 0.0, 0.5 + gap))
+    mdir = (np.abs(Xm[:, 2]) < 1e-12).astype(np.uint8)
+    p = default_params(dhat=dhat, kappa=kappa, h=h, density=density, youngs=youngs, poisson=poisson,
+                       face_rule_level=face_rule_level, gravity=(0.0, 0.0, 0.0))
+    p = _finish_params(p, Xs, Bs)
+    sc = _single_env(Xs, Ts, Bs, np.zeros(Xs.shape[0], dtype=np.uint8), Xm, Fm, np.zeros_like(Xs), p,
+                     "patch_test", 3)
+    sc.mtets = np.ascontiguousarray(Tm, dtype=np.int32)
+    sc.mdirichlet = mdir
+    f = np.zeros((Xs.shape[0] + Xm.shape[0], 3))
+    Ft = top_face_tris(sx, sy, sz)
+    for tri in Ft:
+        P = Xs[tri]
+        area = 0.5 * np.linalg.norm(np.cross(P[1] - P[0], P[2] - P[0]))
+        f[tri, 2] -= pressure * area / 3.0
+    return sc, f
 
 
 def tactile_indent(n_quads=32, side=16e-3, nz=4, thick=2e-3, sphere_subdiv=3,

@@ -194,3 +194,33 @@ def hess_blocks_check(gpu_h, orc, tol, rows=None):
         worst = max(worst, err / ref)
         assert err <= tol * ref, (k, err, np.linalg.norm(o))
     return worst
+
+
+def cauchy_stress(X, T, x, youngs, poisson):
+    """Cauchy stress of every tet [nt, 3, 3] for compressible Neo-Hookean
+    (the material of the time step): P = mu (F - F^-T) + lam ln J F^-T,
+    sigma = P F^T / J."""
+    mu = youngs / (2 * (1 + poisson))
+    lam = youngs * poisson / ((1 + poisson) * (1 - 2 * poisson))
+    Dm = np.stack([X[T[:, k]] - X[T[:, 0]] for k in (1, 2, 3)], axis=2)
+    Ds = np.stack([x[T[:, k]] - x[T[:, 0]] for k in (1, 2, 3)], axis=2)
+    F = Ds @ np.linalg.inv(Dm)
+    J = np.linalg.det(F)
+    Fit = np.transpose(np.linalg.inv(F), (0, 2, 1))
+    P = mu * (F - Fit) + lam * np.log(J)[:, None, None] * Fit
+    return P @ np.transpose(F, (0, 2, 1)) / J[:, None, None]
+
+
+def patch_report(sc, x):
+    """sigma_zz mean, its largest relative error against -pressure and the
+    largest other stress component, per block, for a patch-test state x
+    (pad vertices, then master vertices)."""
+    n = sc.X.shape[0]
+    out = {}
+    for name, X, T, xs in (("upper", sc.X, sc.tets, x[:n]), ("lower", sc.Y0, sc.mtets, x[n:])):
+        sig = cauchy_stress(X, T, xs, sc.params["youngs"], sc.params["poisson"])
+        szz = sig[:, 2, 2]
+        other = np.abs(sig[:, [0, 1, 0, 0, 1], [0, 1, 1, 2, 2]]).max()
+        out[name] = dict(mean=float(szz.mean()), max_rel_err=float(np.abs(szz / -10.0 - 1.0).max()),
+                         spurious=float(other))
+    return out
