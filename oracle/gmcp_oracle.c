@@ -1571,7 +1571,8 @@ ORC_API orc_sim* orc_sim_create_joint(orc_scene* sc, int npad, const double* X, 
     return s;
 }
 
-/* external nodal forces f [nsys][3] (joint step): the energy gains -h^2 f.x */
+/* external nodal forces f [nsys][3] (joint step): the energy gains
+ * -h^2 f.(x - xhat), i.e. -h^2 f.x up to a constant of the step */
 ORC_API void orc_sim_set_fext(orc_sim* s, const double* f) {
     if (!s->fext) s->fext = (double*)malloc(sizeof(double) * 3 * (size_t)s->nv);
     memcpy(s->fext, f, sizeof(double) * 3 * (size_t)s->nv);
@@ -1745,10 +1746,12 @@ static int newton_eval(const orc_sim* s, const double* x, const double* xhat, do
             G[3 * i + c] += s->mass[i] * d;
         }
     if (A) for (int i = 0; i < nv; ++i) { int64_t k = blk_index(s, i, i); for (int c = 0; c < 3; ++c) A[9 * k + 4 * c] += s->mass[i]; }
-    /* external forces (joint step): -h^2 f.x */
+    /* external forces (joint step): -h^2 f.(x - xhat), the work -h^2 f.x
+     * up to a constant of the step (same gradient and minimiser; relative to
+     * xhat it stays small, so its rounding does not swamp the line search) */
     double Ef = 0.0;
     if (s->fext)
-        for (int i = 0; i < 3 * nv; ++i) { Ef -= s->fext[i] * x[i]; G[i] -= h2 * s->fext[i]; }
+        for (int i = 0; i < 3 * nv; ++i) { Ef -= s->fext[i] * (x[i] - xhat[i]); G[i] -= h2 * s->fext[i]; }
     samples->n = 0;
     const double* xm = s->joint ? x + 3 * (size_t)s->npad : s->xm;
     collect_samples(s->sc, x, xm, 0, NULL, samples);
@@ -1811,30 +1814,51 @@ static int newton_eval(const orc_sim* s, const double* x, const double* xhat, do
     return 1;
 }
 
-/* lagged energy E_i(x_i + a p): inertia + h^2 (elastic + sum coef B(g + a dg)) */
-static double lagged_energy(const orc_sim* s, const double* x, const double* xhat, const svec* smp,
-                            const double* p, double a, double* tmp) {
-    int nv = s->nv;
-    for (int i = 0; i < 3 * nv; ++i) tmp[i] = x[i] + a * p[i];
-    double Ee;
-    if (!elastic_eval(s, tmp, &Ee, NULL, NULL)) return INFINITY;
-    double Ein = 0.0;
+/* change of the lagged energy from x_i to x_i + a p (reading R22):
+ *   dE = sum_v m_v (a p_v.(x_v - xhat_v) + a^2/2 |p_v|^2)
+ *      + h^2 ( sum_tets [psi(x + a p) - psi(x)]
+ *            + sum_k kappa w gamma [B(g + a dg) - B(g)]  -  a f.p ),
+ * each term's change formed on its own before the sums, so that the test
+ * against the predicted decrease is not lost in the rounding of the total
+ * energy; +inf if a tet inverts or a sample's gap reaches 0 */
+static double lagged_delta(const orc_sim* s, const double* x, const double* xhat, const svec* smp,
+                           const double* p, double a) {
+    const int nv = s->nv;
+    double dEe = 0.0;
+    for (int t = 0; t < s->nt; ++t) {
+        const int32_t* T = s->tets + 4 * t;
+        double x4[12], y4[12], X4[12], psi0, psi1;
+        for (int q = 0; q < 4; ++q)
+            for (int c = 0; c < 3; ++c) {
+                x4[3 * q + c] = x[3 * T[q] + c];
+                y4[3 * q + c] = x[3 * T[q] + c] + a * p[3 * T[q] + c];
+                X4[3 * q + c] = s->X[3 * T[q] + c];
+            }
+        if (!orc_nh_tet(s->Dminv + 9 * t, s->vol[t], s->mu, s->lam, X4, y4, &psi1, NULL, NULL)) return INFINITY;
+        orc_nh_tet(s->Dminv + 9 * t, s->vol[t], s->mu, s->lam, X4, x4, &psi0, NULL, NULL);
+        dEe += psi1 - psi0;
+    }
+    double dEin = 0.0;
     for (int i = 0; i < nv; ++i)
-        for (int c = 0; c < 3; ++c) { double d = tmp[3 * i + c] - xhat[3 * i + c]; Ein += 0.5 * s->mass[i] * d * d; }
-    double Ec = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double pc = p[3 * i + c];
+            dEin += s->mass[i] * (a * pc * (x[3 * i + c] - xhat[3 * i + c]) + 0.5 * a * a * pc * pc);
+        }
+    double dEc = 0.0;
     const double* pm = s->joint ? p + 3 * (size_t)s->npad : NULL;
     for (int64_t q = 0; q < smp->n; ++q) {
         const orc_sample* k = smp->a + q;
         double gt = k->g + a * sample_dgdx(s->sc, k, p, pm);
         if (!(gt > 0.0)) return INFINITY;
-        double B, dB, d2B;
-        orc_barrier(gt, k->eps, &B, &dB, &d2B);
-        Ec += k->kq * k->w * k->gamma * B;
+        double B1, B0, dB, d2B;
+        orc_barrier(gt, k->eps, &B1, &dB, &d2B);
+        orc_barrier(k->g, k->eps, &B0, &dB, &d2B);
+        dEc += k->kq * k->w * k->gamma * (B1 - B0);
     }
-    double Ef = 0.0;
+    double dEf = 0.0;
     if (s->fext)
-        for (int i = 0; i < 3 * nv; ++i) Ef -= s->fext[i] * tmp[i];
-    return Ein + s->h * s->h * (Ee + Ec + Ef);
+        for (int i = 0; i < 3 * nv; ++i) dEf -= a * s->fext[i] * p[i];
+    return dEin + s->h * s->h * (dEe + dEc + dEf);
 }
 
 static double max_step_to(const orc_sim* s, const double* x, const double* dP) {
@@ -1968,8 +1992,8 @@ ORC_API int orc_newton_step(orc_sim* s, double* x, double* v, const double* xm_n
         double c0 = 1e-4;
         int ok = 0;
         for (int hv = 0; hv <= s->max_halv; ++hv) {
-            double Ea = lagged_energy(s, x, xhat, &smp, p, al, tmp);
-            if (Ea <= E + c0 * al * gp) { ok = 1; break; }
+            double dE = lagged_delta(s, x, xhat, &smp, p, al);
+            if (dE <= c0 * al * gp) { ok = 1; break; }
             al *= 0.5;
         }
         if (!ok) { status = 6; break; }
