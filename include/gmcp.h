@@ -315,6 +315,49 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
 ipc_status ipc_newton_step(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
                            const double* dx_pred_dev, ipc_step_stats* stats);
 
+/* Deformable master (Sec. 4.2-4.3 with Eq. gap: the contact potential
+ * depends on the master vertices through x_m, so a master body that
+ * deforms takes its share of every sample's force and stiffness).  The
+ * master vertices of the scene become simulated vertices of a second
+ * elastic body (the context's material, density and gravity); its tets
+ * index master vertices.  Call before the first time step of the context;
+ * ipc_newton_step_joint then steps both bodies in one system. */
+typedef struct {
+    int64_t n_mtet;
+    const int32_t* m_tets;        /* [n_mtet][4] master vertex indices, positive volume at m_rest (host) */
+    const uint8_t* m_dirichlet;   /* [n_mvert] 1 = prescribed master vertex; NULL = none (host) */
+    double pattern_radius;        /* slave-master block pattern: every (slave triangle vertex,
+                                     master triangle vertex) pair whose triangles' rest boxes are
+                                     within this distance; 0 = 2 x the larger mean edge length of
+                                     the two surfaces + 2 dhat.  Contact between triangles farther
+                                     apart at rest fails the step with IPC_ERR_CAPACITY. */
+} ipc_master_body;
+
+/* Attach the master body (host arrays, copied).  Single environment.
+ * Errors: IPC_ERR_ARG (indices out of range, n_env > 1, or the time-stepper
+ * state already built by an earlier step). */
+ipc_status ipc_set_master_body(ipc_ctx* ctx, const ipc_master_body* body);
+
+/* One implicit-Euler step of the pad and the deformable master together:
+ * the step of ipc_newton_step over the joint system (pad vertices, then
+ * master vertices), with the contact rows and blocks of the master vertices
+ * (each sample's gap gradient is bm_j n_s on master vertex j, Eq. gap with
+ * the frozen linearisation) and, on both bodies, the step bound of Sec. 4.5
+ * and the additive CCD with both sides moving.
+ *  x_dev, v_dev: device FP64 [n_vert + n_mvert][3], the pad's vertices then
+ *  the master's, in and out as for ipc_newton_step (Dirichlet vertices of
+ *  either body move to x + h v);
+ *  f_ext_dev: external nodal forces, device FP64 [n_vert + n_mvert][3]
+ *  (NULL = none); the incremental potential gains -h^2 f.x (written as
+ *  -h^2 f.(x - xhat), which differs by a constant of the step);
+ *  stats (host) may be NULL.
+ * The master rows and blocks are summed in a fixed order (entries sorted by
+ * destination, then by value), so the step is deterministic.  Errors as
+ * ipc_newton_step, plus IPC_ERR_ARG without ipc_set_master_body and
+ * IPC_ERR_CAPACITY when a contact block falls outside the block pattern. */
+ipc_status ipc_newton_step_joint(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* f_ext_dev,
+                                 ipc_step_stats* stats);
+
 /* The time step of ipc_newton_step for every environment of the scene at
  * once (the paper's batched environments, Sec. 5): each environment has its
  * own incremental potential, residual scale, Newton iterate, PCG solve
@@ -509,8 +552,9 @@ ipc_status ipc_alu_peak(int32_t kind, int32_t device, void* stream, double* tflo
  * given the snapshot by ipc_load continues bit for bit.  The file has a
  * versioned header, the sizes of the scene and an FNV-1a checksum; it is
  * written beside path and renamed, so a failed write leaves no torn file.
- * Synchronises params.stream.  IPC_ERR_ARG for NULL arguments or a file
- * that cannot be written. */
+ * Synchronises params.stream.  IPC_ERR_ARG for NULL arguments, a file
+ * that cannot be written, or a context with a master body (ipc_set_master_body;
+ * not supported). */
 ipc_status ipc_save(ipc_ctx* ctx, const char* path, const double* x_dev, const double* v_dev);
 
 /* Read a snapshot written by ipc_save into a context created from the same

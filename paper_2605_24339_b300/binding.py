@@ -79,6 +79,11 @@ class StepStats(C.Structure):
                 ("energy", C.c_double), ("ms_total", C.c_double), ("pred_used", C.c_int32)]
 
 
+class MasterBody(C.Structure):
+    _fields_ = [("n_mtet", C.c_int64), ("m_tets", C.c_void_p), ("m_dirichlet", C.c_void_p),
+                ("pattern_radius", C.c_double)]
+
+
 class WsParams(C.Structure):
     _fields_ = [("params_host", C.c_void_p), ("lr", C.c_double), ("beta1", C.c_double),
                 ("beta2", C.c_double), ("eps", C.c_double), ("pos_scale", C.c_double),
@@ -165,6 +170,10 @@ def lib():
     L.ipc_set_launch_shape.argtypes = [P, C.c_int32, C.c_int32]
     L.ipc_newton_step.restype = C.c_int
     L.ipc_newton_step.argtypes = [P, P, P, P, P, C.POINTER(StepStats)]
+    L.ipc_set_master_body.restype = C.c_int
+    L.ipc_set_master_body.argtypes = [P, C.POINTER(MasterBody)]
+    L.ipc_newton_step_joint.restype = C.c_int
+    L.ipc_newton_step_joint.argtypes = [P, P, P, P, C.POINTER(StepStats)]
     L.ipc_newton_step_envs.restype = C.c_int
     L.ipc_newton_step_envs.argtypes = [P, P, P, P, P, C.POINTER(StepStats), P]
     L.ipc_dual_map_build.restype = C.c_int
@@ -324,6 +333,15 @@ class Context:
         self.h = h
         self.nv, self.ns, self.nmv = sc.n_vert, sc.n_stri, sc.n_mvert
         self.n_env = int(sc.n_env)
+        self.joint = getattr(scene, "mtets", None) is not None
+        if self.joint:
+            # deformable master: the scene's master body joins the time step
+            mt = np.ascontiguousarray(scene.mtets, dtype=np.int32)
+            md = getattr(scene, "mdirichlet", None)
+            md = np.ascontiguousarray(md if md is not None else np.zeros(self.nmv), dtype=np.uint8)
+            self._mbody = (mt, md)
+            body = MasterBody(mt.shape[0], mt.ctypes.data, md.ctypes.data, float(p.get("joint_radius", 0.0)))
+            self._check(L.ipc_set_master_body(self.h, C.byref(body)))
 
     def close(self):
         if getattr(self, "h", None):
@@ -481,7 +499,7 @@ class Context:
 
     def profile_read(self):
         n = C.c_int32()
-        K = 16
+        K = 64
         names = C.create_string_buffer(32 * K)
         ms = (C.c_double * K)()
         calls = (C.c_int64 * K)()
@@ -514,6 +532,21 @@ class Context:
                     halvings=st.line_search_halvings, residual=st.residual, res0=st.res0,
                     alpha0=st.alpha0, last_alpha=st.last_alpha, energy=st.energy, ms=st.ms_total,
                     pred_used=st.pred_used)
+
+    def newton_step_joint(self, x, v, f_ext=None):
+        """In-place step of the pad and the deformable master together
+        (ipc_newton_step_joint): x, v are [n_pad + n_master, 3] FP64 CUDA
+        tensors; f_ext the external nodal forces (same shape) or None."""
+        t = self.torch
+        for a in (x, v):
+            if not (isinstance(a, t.Tensor) and a.is_cuda and a.dtype == t.float64 and a.is_contiguous()):
+                raise TypeError("x and v must be contiguous FP64 CUDA tensors")
+        st = StepStats()
+        f_t = self._as(f_ext)   # alive until the call returns
+        r = lib().ipc_newton_step_joint(self.h, _ptr(x), _ptr(v), _ptr(f_t), C.byref(st))
+        if r not in (0, STEP_INFEASIBLE, STEP_NOT_CONVERGED, STEP_LINESEARCH):
+            self._check(r)
+        return self._stats_dict(st, r)
 
     def newton_step_envs(self, x, v, xm_next=None, dx_pred=None):
         """The step of every environment (ipc_newton_step_envs): in place on

@@ -464,7 +464,7 @@ cudaError_t start_point(Ctx& c, const double* x, const double* P, double* x0, co
                         std::vector<double>& alpha0, std::vector<uint8_t>& ok) {
     NewtonState& N = *c.newton;
     const int ne = N.n_env;
-    const int64_t n = 3 * c.nv;
+    const int64_t n = 3 * N.nsys;
     std::vector<uint8_t> alive(need);
     std::vector<int> j;
     std::vector<double> aj;
@@ -473,7 +473,7 @@ cudaError_t start_point(Ctx& c, const double* x, const double* P, double* x0, co
     for (int e = 0; e < ne; ++e) any_dir = any_dir || (alive[e] && N.h_has_dir[e]);
     if (any_dir) {
         GMCP_CUDA_TRY(vec_dir_delta(c, x, N.xhat.p, N.dP.p));
-        GMCP_CUDA_TRY(ccd_bound(c, x, N.dP.p, N.xm.p, nullptr, false));
+        GMCP_CUDA_TRY(ccd_bound(c, x, N.dP.p, master_of(c, x), master_dir_of(c, N.dP.p), false));
         std::vector<uint8_t> chk(ne, 0);
         for (int e = 0; e < ne; ++e) {
             if (!alive[e] || !N.h_has_dir[e]) continue;
@@ -487,7 +487,7 @@ cudaError_t start_point(Ctx& c, const double* x, const double* P, double* x0, co
             if (chk[e] && j[e] < 0) alive[e] = 0;
     }
     GMCP_CUDA_TRY(vec_free_delta(c, P, N.xi.p, N.dP.p));
-    GMCP_CUDA_TRY(ccd_bound(c, N.xi.p, N.dP.p, N.xm.p, nullptr, false));
+    GMCP_CUDA_TRY(ccd_bound(c, N.xi.p, N.dP.p, master_of(c, N.xi.p), master_dir_of(c, N.dP.p), false));
     const std::vector<double> a(N.h_ealpha, N.h_ealpha + ne);
     GMCP_CUDA_TRY(first_feasible(c, N.xi.p, N.dP.p, a, c.prm.max_halvings, alive, j, aj));
     alpha0.assign(ne, 0.0);
@@ -508,12 +508,17 @@ cudaError_t start_point(Ctx& c, const double* x, const double* P, double* x0, co
 }  // namespace
 
 // One implicit-Euler step of every environment.  status_out[e]: 0
-// converged, 3 infeasible, 5 not converged, 6 line search.
+// converged, 3 infeasible, 5 not converged, 6 line search.  Joint step
+// (deformable master): x, v hold the pad and then the master vertices, and
+// f_ext the external nodal forces (or NULL).
 cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, const double* dx_pred,
-                       ipc_step_stats* st, int* status_out) {
+                       ipc_step_stats* st, int* status_out, const double* f_ext) {
     NewtonState& N = *c.newton;
     const int ne = N.n_env;
-    const int64_t n = 3 * c.nv;
+    const int64_t n = 3 * N.nsys;
+    N.fext = f_ext;
+    N.joint_miss = false;
+    struct ResetF { NewtonState& N; ~ResetF() { N.fext = nullptr; } } reset_f{N};
     cudaStream_t s = c.stream;
     const double h = c.prm.h, h2 = h * h;
     std::vector<int> status(ne, 0);
@@ -527,7 +532,7 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
     GMCP_CUDA_TRY(vec_xhat(c, x, v, N.xhat.p));
     // master motion with the pad held at x^t; an environment whose master
     // cannot move there keeps its master and stops
-    if (xm_next && c.nmv > 0) {
+    if (xm_next && c.nmv > 0 && !N.joint) {
         const int64_t m = 3 * c.nmv;
         GMCP_CUDA_TRY(cudaMemsetAsync(N.tmp.p, 0, sizeof(double) * n, s));
         GMCP_CUDA_TRY(cudaMemcpyAsync(N.dxm.p, xm_next, sizeof(double) * m, cudaMemcpyDeviceToDevice, s));
@@ -609,16 +614,17 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
         GMCP_CUDA_TRY(dot_env(c, N.G.p, N.dirn.p, kEsGp));
         {
             ProfScope ps(c.prof, s, "step_bound");
-            GMCP_CUDA_TRY(ccd_bound(c, x, N.dirn.p, N.xm.p, nullptr, true));
+            GMCP_CUDA_TRY(ccd_bound(c, x, N.dirn.p, master_of(c, x), master_dir_of(c, N.dirn.p), true));
         }
         const std::vector<double> al(N.h_ealpha, N.h_ealpha + ne);
         GMCP_CUDA_TRY(read_es(c, kEsGp, 1));
         std::vector<double> gp(ne);
         for (int e = 0; e < ne; ++e) gp[e] = N.h_es[kES * e + kEsGp];
-        // backtracking on the frozen-linear energy: slot 0 is alpha = 0 (the
-        // reference), the next slots the next halvings; the first batch
-        // tries the full step only (it is usually taken), later batches
-        // seven halvings at once
+        // backtracking on the frozen-linear energy: the batch gives each
+        // step size's energy change from x (reading R22; slot 0 is alpha = 0,
+        // change 0), tested against 1e-4 alpha G.p; the first batch tries the
+        // full step only (it is usually taken), later batches seven halvings
+        // at once
         std::vector<uint8_t> searching(run), accepted(ne, 0);
         for (int hv0 = 0, nk = 1; hv0 <= c.prm.max_halvings && any(searching); hv0 += nk) {
             nk = hv0 == 0 ? 1 : std::min(7, c.prm.max_halvings - hv0 + 1);
@@ -637,7 +643,7 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
                 const double* E = N.h_es + kES * e + kEsE8;
                 for (int j = 0; j < nk; ++j) {
                     const double a = N.h_eal[8 * e + 1 + j];
-                    if (E[1 + j] <= E[0] + c0 * a * gp[e]) {
+                    if (E[1 + j] <= c0 * a * gp[e]) {
                         searching[e] = 0;
                         accepted[e] = 1;
                         al_acc[e] = a;
@@ -1075,6 +1081,9 @@ ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx*
         if (c.nt >= ((int64_t)1 << 27)) throw Fail{IPC_ERR_ARG, "n_tet must be below 2^27"};
         // kept for the time stepper, whose state is built on its first call
         c.h_X.assign(scene->pad_rest, scene->pad_rest + 3 * c.nv);
+        c.h_Y0.assign(scene->m_rest, scene->m_rest + 3 * c.nmv);
+        c.h_stri.assign(scene->s_tris, scene->s_tris + 3 * c.ns);
+        c.h_mtri.assign(scene->m_tris, scene->m_tris + 3 * c.nmt);
         if (c.nt > 0) c.h_tets.assign(scene->tets, scene->tets + 4 * c.nt);
         if (scene->dirichlet) c.h_dir.assign(scene->dirichlet, scene->dirichlet + c.nv);
         else c.h_dir.assign(c.nv, 0);
@@ -1511,10 +1520,68 @@ static ipc_status newton_status(ipc_ctx* ctx, int status) {
     }
 }
 
+static ipc_status step_checks(ipc_ctx* ctx) {
+    Ctx& c = ctx->c;
+    if (c.nt == 0 && c.h_mtets.empty()) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: the scene has no tets");
+    if (!(c.prm.h > 0.0) || !(c.prm.density > 0.0) || !(c.prm.youngs > 0.0) ||
+        !(c.prm.poisson > -1.0 && c.prm.poisson < 0.5) || c.prm.max_newton < 0 || c.prm.max_pcg < 1 ||
+        c.prm.max_halvings < 0)
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: invalid h, material or iteration limits");
+    return IPC_OK;
+}
+
+ipc_status ipc_set_master_body(ipc_ctx* ctx, const ipc_master_body* body) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!body || (body->n_mtet > 0 && !body->m_tets) || body->n_mtet < 0)
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_set_master_body: NULL body or tets");
+    if (c.n_env != 1) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_set_master_body: one environment only");
+    if (c.newton) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_set_master_body: the time stepper already exists");
+    for (int64_t i = 0; i < 4 * body->n_mtet; ++i)
+        if (body->m_tets[i] < 0 || body->m_tets[i] >= c.nmv)
+            return fail_ctx(ctx, IPC_ERR_ARG, "ipc_set_master_body: m_tets index out of range");
+    if (c.nv + c.nmv >= ((int64_t)1 << 30) || c.nt + body->n_mtet >= ((int64_t)1 << 27))
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_set_master_body: system too large");
+    c.h_mtets.assign(body->m_tets, body->m_tets + 4 * body->n_mtet);
+    if (body->m_dirichlet) c.h_mdir.assign(body->m_dirichlet, body->m_dirichlet + c.nmv);
+    else c.h_mdir.assign(c.nmv, 0);
+    c.joint_radius = body->pattern_radius;
+    c.joint = true;
+    return IPC_OK;
+}
+
+ipc_status ipc_newton_step_joint(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* f_ext_dev,
+                                 ipc_step_stats* stats) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!c.joint) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step_joint: no master body (ipc_set_master_body)");
+    if (!x_dev || !v_dev) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step_joint: NULL x or v");
+    const ipc_status chk = step_checks(ctx);
+    if (chk != IPC_OK) return chk;
+    API_CK(ctx, cudaSetDevice(c.device));
+    const auto t_start = std::chrono::steady_clock::now();
+    API_CK(ctx, newton_setup(c));
+    int status = 0;
+    ipc_step_stats st{};
+    const cudaError_t e = newton_run(c, x_dev, v_dev, nullptr, nullptr, &st, &status, f_ext_dev);
+    if (e != cudaSuccess && c.newton && c.newton->joint_miss) {
+        cudaGetLastError();
+        return fail_ctx(ctx, IPC_ERR_CAPACITY, "ipc_newton_step_joint: a contact block fell outside the "
+                                               "slave-master block pattern (raise pattern_radius)");
+    }
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "ipc_newton_step_joint");
+    st.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+    if (stats) *stats = st;
+    if (status == 0) ++c.step_count;
+    return newton_status(ctx, status);
+}
+
 ipc_status ipc_newton_step_envs(ipc_ctx* ctx, double* x_dev, double* v_dev, const double* xm_next_dev,
                                 const double* dx_pred_dev, ipc_step_stats* stats_host, int32_t* status_host) {
     if (!ctx) return IPC_ERR_ARG;
     Ctx& c = ctx->c;
+    if (c.joint) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: the context has a master body "
+                                                   "(ipc_newton_step_joint)");
     if (!x_dev || !v_dev) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: NULL x or v");
     if (c.nt == 0) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_newton_step: the scene has no tets");
     if (!(c.prm.h > 0.0) || !(c.prm.density > 0.0) || !(c.prm.youngs > 0.0) ||
@@ -1527,7 +1594,7 @@ ipc_status ipc_newton_step_envs(ipc_ctx* ctx, double* x_dev, double* v_dev, cons
     const int ne = c.n_env;
     std::vector<int> status(ne, 0);
     std::vector<ipc_step_stats> st(ne);
-    const cudaError_t e = newton_run(c, x_dev, v_dev, xm_next_dev, dx_pred_dev, st.data(), status.data());
+    const cudaError_t e = newton_run(c, x_dev, v_dev, xm_next_dev, dx_pred_dev, st.data(), status.data(), nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "ipc_newton_step");
     const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     int first_bad = 0;

@@ -60,6 +60,9 @@ struct ModeArgs {
     unsigned long long* h_count = nullptr;
     int64_t h_cap = 0;
     int32_t m_off = 0;         // index of master vertex 0 in the joint numbering
+    // with h_rows: the gradient rows of the master vertices are appended to
+    // the same list as entries (row, -1) whose first three values are the row
+    bool h_rows = false;
     // MODE_ALPHA: the bound of a sample on slave triangle t goes to
     // alpha_bits[alpha_stride * env(t)] (0: one bound for the whole scene)
     int alpha_stride = 0;
@@ -294,8 +297,15 @@ __device__ __forceinline__ int warp_reserve_c(bool pred, int32_t* counter) {
 
 // one sample of the frozen-linear potential (lagged energy of the line
 // search, reading R6): g~ = g + a dg; +inf once g~ <= 0, 0 from eps on
+// the change coef [B(g + a_j dg) - B(g)] of a frozen sample's barrier
+// (the line search compares changes, not totals)
 __device__ __forceinline__ void lag_add(double* E8, const double* al, int na, double coef, double g,
                                         double eps, double dg) {
+    double e0 = 0.0;
+    if (g < eps) {
+        const double d = g - eps, L = log(g / eps);
+        e0 = coef * (-d * d * L);
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         if (j >= na) break;
@@ -307,7 +317,7 @@ __device__ __forceinline__ void lag_add(double* E8, const double* al, int na, do
             const double d = gt - eps, L = log(gt / eps);
             e = coef * (-d * d * L);
         }
-        E8[j] += e;
+        E8[j] += e - e0;
     }
 }
 
@@ -967,9 +977,20 @@ __device__ void master_blocks(const ModeArgs& LG, const ItemOut& o, const int32_
     double Bv, dB, d2B;
     barrier(o.g, o.eps, Bv, dB, d2B);
     const double c2 = rmax(o.kq * o.w * o.gamma * d2B, 0.0);
+    const double c1 = o.kq * o.w * o.gamma * dB;
     for (int j = 0; j < 3; ++j) {
         if (o.mv[j] < 0) continue;
         const int32_t cj = LG.m_off + o.mv[j];
+        if (LG.h_rows) {
+            const unsigned long long at = atomicAdd(LG.h_count, 1ull);
+            if ((int64_t)at < LG.h_cap) {
+                LG.h_ij[2 * at] = cj; LG.h_ij[2 * at + 1] = -1;
+                double* b = LG.h_blk + 9 * at;
+                const double f = c1 * o.bm[j];
+                b[0] = f * ns.x; b[1] = f * ns.y; b[2] = f * ns.z;
+                for (int q = 3; q < 9; ++q) b[q] = 0.0;
+            }
+        }
         for (int a = 0; a < 3; ++a) put_block(LG, Ts[a], cj, -c2 * o.b[a] * o.bm[j], ns);
         for (int i = 0; i < 3; ++i)
             if (o.mv[i] >= 0) put_block(LG, LG.m_off + o.mv[i], cj, c2 * o.bm[i] * o.bm[j], ns);
@@ -1883,11 +1904,12 @@ cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, doubl
 }
 
 cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32_t* ij, double* blk,
-                                int64_t cap, unsigned long long* count) {
+                                int64_t cap, unsigned long long* count, bool rows) {
     ProfScope ps(c.prof, c.stream, "master_hess");
     GMCP_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), c.stream));
     ModeArgs LG;
     LG.h_ij = ij; LG.h_blk = blk; LG.h_count = count; LG.h_cap = cap; LG.m_off = (int32_t)c.nv;
+    LG.h_rows = rows;
     if (c.P.nk == 4)
         return launch_samples<4, double, MODE_MASTER_HESS>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                             nullptr, nullptr, LG);
@@ -1897,16 +1919,16 @@ cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32
 
 cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,
                            const double* alphas_dev, int na, double* triE8, double* energies_dev,
-                           int alphas_stride) {
+                           int alphas_stride, const double* pm) {
     ProfScope ps(c.prof, c.stream, "lagged");
     if (na < 1 || na > 8) return cudaErrorInvalidValue;
     GMCP_CUDA_TRY(cudaMemsetAsync(triE8, 0, sizeof(double) * (size_t)na * (size_t)c.ns, c.stream));
     ModeArgs LG;
     LG.alphas = alphas_dev; LG.na = na; LG.triE8 = triE8; LG.ns = c.ns; LG.alphas_stride = alphas_stride;
     if (c.P.nk == 4)
-        GMCP_CUDA_TRY((launch_samples<4, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, LG)));
+        GMCP_CUDA_TRY((launch_samples<4, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, pm, nullptr, LG)));
     else
-        GMCP_CUDA_TRY((launch_samples<16, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, nullptr, nullptr, LG)));
+        GMCP_CUDA_TRY((launch_samples<16, double, MODE_LAGGED>(c, x, xm, nullptr, nullptr, nullptr, nullptr, p, pm, nullptr, LG)));
     if (energies_dev)
         for (int j = 0; j < na; ++j) GMCP_CUDA_TRY(reduce_sum(c, triE8 + (int64_t)j * c.ns, c.ns, energies_dev + j));
     return cudaSuccess;

@@ -224,6 +224,21 @@ enum : int {
 struct NewtonState {
     double mu = 0, lam = 0;
     int64_t nnzb = 0;
+    // the system's vertices and tets: the pad's, or (joint step with a
+    // deformable master) the pad's followed by the master body's
+    bool joint = false;
+    int64_t nsys = 0, ntsys = 0;
+    DBuf<double> Xsys;                   // [nsys][3] rest positions
+    const double* fext = nullptr;        // external nodal forces of the current step (joint), or NULL
+    // joint step: the master entries (rows and blocks), their counting sort
+    // by destination row, and the summed blocks at their pattern positions
+    int64_t ml_cap = 0;
+    DBuf<int32_t> ml_ij;                 // [cap][2] (row, col), col -1 = a gradient row
+    DBuf<double> ml_blk;                 // [cap][9]
+    DBuf<unsigned long long> ml_count;   // entries needed
+    DBuf<int32_t> ml_cnt, ml_off, ml_cur, ml_perm, ml_tmp, ml_err;
+    DBuf<double> xvals;                  // [nnzb][9] master blocks (FP64, unscaled), zero elsewhere
+    bool joint_miss = false;             // a contact block fell outside the pattern
     DBuf<int32_t> tets;                  // [nt][4]
     DBuf<double> Dminv, vol, mass;       // [nt][9], [nt], [nv]
     DBuf<uint8_t> dir;                   // [nv]
@@ -446,6 +461,14 @@ struct Ctx {
     std::vector<int32_t> h_tets;
     std::vector<uint8_t> h_dir;
     std::vector<double> h_X;
+    std::vector<double> h_Y0;                  // master rest positions
+    std::vector<int32_t> h_stri, h_mtri;       // slave and master triangles
+    // deformable master (joint step): the master body's tets and Dirichlet
+    // flags, and the radius of the slave-master block pattern
+    bool joint = false;
+    std::vector<int32_t> h_mtets;
+    std::vector<uint8_t> h_mdir;
+    double joint_radius = 0.0;
     std::vector<int32_t> h_cb_row, h_cb_col;
     std::unique_ptr<NewtonState> newton;
     std::unique_ptr<WarmStart, void (*)(WarmStart*)> ws{nullptr, ws_destroy};
@@ -501,17 +524,19 @@ int sm_count(int device);
 // (FP64 in both precisions; energies_dev NULL: the per-triangle terms
 // triE8 [na][ns] only); needs the candidate lists of (x, xm).
 // alphas_stride > 0: a slave triangle of environment e uses
-// alphas_dev[alphas_stride * e + j]
+// alphas_dev[alphas_stride * e + j]; pm: the master's direction (a
+// deformable master, NULL = static)
 cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,
                            const double* alphas_dev, int na, double* triE8, double* energies_dev,
-                           int alphas_stride = 0);
+                           int alphas_stride = 0, const double* pm = nullptr);
 // gradient of the contact potential with respect to the master vertices,
 // [nmv][3] FP64 (zeroed first; FP64 atomics, so the summation order varies)
 cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m);
 // slave-master (slave row) and master-master Hessian blocks of the active
-// samples, appended in arbitrary order; *count receives the number needed
+// samples, appended in arbitrary order; *count receives the number needed;
+// rows: also the master vertices' gradient rows, as entries (row, -1)
 cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32_t* ij, double* blk,
-                                int64_t cap, unsigned long long* count);
+                                int64_t cap, unsigned long long* count, bool rows = false);
 // newton.cu
 cudaError_t newton_setup(Ctx& c);
 // The Newton iteration runs per environment: each sum below is one
@@ -520,10 +545,12 @@ cudaError_t newton_setup(Ctx& c);
 // elastic energy per environment into es[kEsEe]; inverted-tet flags in N.ebad
 cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess);
 // elastic energies at x + alphas_env[8 e + j] p (j < na <= 8) into es[slot +
-// j]; +inf where a tet of the environment has J <= 0
-cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na, int slot);
-// total energies at x + alphas_env[8 e + j] p into es[kEsE8 + j]; ee0:
-// alphas_env[8 e] = 0 and es[kEsEe] already holds the elastic energy at x
+// j]; +inf where a tet of the environment has J <= 0; delta: their change
+// from x (per tet, against the energies of the last nh_eval at x)
+cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na, int slot,
+                            bool delta = false);
+// changes of the total energy from x to x + alphas_env[8 e + j] p into
+// es[kEsE8 + j]; ee0: alphas_env[8 e] = 0
 cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_env, int na,
                          bool with_contact, bool ee0);
 // es[kEsEc], es[kEsEe], es[kEsE], es[kEsG2] at x, the gradient N.G and
@@ -531,6 +558,12 @@ cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double*
 cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess);
 // a . b per environment (3 nv entries) into es[slot]
 cudaError_t dot_env(Ctx& c, const double* a, const double* b, int slot);
+// the master positions / direction that go with system positions x /
+// direction p (the joint step's master rows, else the kinematic master /
+// NULL); the joint step's master rows and blocks
+const double* master_of(Ctx& c, const double* x);
+const double* master_dir_of(Ctx& c, const double* p);
+cudaError_t joint_master_terms(Ctx& c, const double* x, bool want_hess);
 cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters,
                       int* env_iters = nullptr);   // env_iters: [n_env] iterations per environment
 // elementwise helpers

@@ -328,9 +328,11 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
 
 // elastic energies at x + alpha_j p for j < na (<= 8), layout [na][nt]
 // (alphas of tet t's environment: alphas[astride * env + j])
+// (base: subtract each tet's energy at x, base[t], to give the change)
 __global__ void k_nh_energy_multi(ElasticView E, const double* __restrict__ x,
                                   const double* __restrict__ p, const double* __restrict__ alphas_env, int astride,
-                                  const int32_t* __restrict__ tet_env, int na, double* __restrict__ tE8) {
+                                  const int32_t* __restrict__ tet_env, int na, double* __restrict__ tE8,
+                                  const double* __restrict__ base) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= E.nt) return;
     const double* alphas = alphas_env + (int64_t)astride * tet_env[t];
@@ -342,7 +344,8 @@ __global__ void k_nh_energy_multi(ElasticView E, const double* __restrict__ x,
     for (int j = 0; j < na; ++j) {
         const double a = alphas[j];
         for (int q = 0; q < 12; ++q) y4[q] = x4[q] + a * p4[q];
-        tE8[(int64_t)j * E.nt + t] = nh_energy(Dmi, E.vol[t], E.mu, E.lam, y4, X4, &psi, F, &lnJ) ? psi : INFINITY;
+        const bool ok = nh_energy(Dmi, E.vol[t], E.mu, E.lam, y4, X4, &psi, F, &lnJ);
+        tE8[(int64_t)j * E.nt + t] = ok ? (base ? psi - base[t] : psi) : INFINITY;
     }
 }
 
@@ -351,7 +354,7 @@ __global__ void k_assemble_grad(int64_t nv, const double* __restrict__ x, const 
                                 const double* __restrict__ mass, const uint8_t* __restrict__ dir,
                                 const int32_t* __restrict__ vt_off, const int32_t* __restrict__ vt_ent,
                                 const double* __restrict__ tG, const void* __restrict__ cgrad, int cgrad_f32,
-                                double h2, double* __restrict__ G) {
+                                const double* __restrict__ fext, double h2, double* __restrict__ G) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     if (dir[v]) { G[3 * v] = 0.0; G[3 * v + 1] = 0.0; G[3 * v + 2] = 0.0; return; }
@@ -369,6 +372,9 @@ __global__ void k_assemble_grad(int64_t nv, const double* __restrict__ x, const 
     } else {
         const double* g = (const double*)cgrad;
         c0 = g[3 * v]; c1 = g[3 * v + 1]; c2 = g[3 * v + 2];
+    }
+    if (fext) {   // external forces: -h^2 f
+        c0 -= fext[3 * v]; c1 -= fext[3 * v + 1]; c2 -= fext[3 * v + 2];
     }
     const double m = mass[v];
     G[3 * v] = m * (x[3 * v] - xhat[3 * v]) + h2 * (e0 + c0);
@@ -401,6 +407,7 @@ __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __re
                                 const int32_t* __restrict__ bt_off,
                                 const int32_t* __restrict__ bt_ent, const TH* __restrict__ tH,
                                 const int32_t* __restrict__ cmap, const TC* __restrict__ cvals,
+                                const double* __restrict__ xvals,
                                 const double* __restrict__ mass, const uint8_t* __restrict__ dir, double h2,
                                 TA* __restrict__ A) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -445,6 +452,10 @@ __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __re
         const TC* C = cvals + 9 * (int64_t)cb;
         for (int q = 0; q < 9; ++q) s[q] += (TA)C[q];
     }
+    if (xvals) {   // joint step: the blocks with master vertices
+        const double* X9 = xvals + 9 * b;
+        for (int q = 0; q < 9; ++q) s[q] += (TA)X9[q];
+    }
     const TA h2a = (TA)h2;
     for (int q = 0; q < 9; ++q) s[q] *= h2a;
     if (i == j) {
@@ -452,6 +463,83 @@ __global__ void k_assemble_sell(int64_t nv, int64_t ngroups, const int32_t* __re
         s[0] += m; s[4] += m; s[8] += m;
     }
     for (int q = 0; q < 9; ++q) A[sell_idx<TA>(g, lane, q)] = s[q];
+}
+
+// ------------------------------------------------- joint step: master entries ---
+// The master rows and blocks come as an unordered list (row, col, 9 values;
+// col -1 = a gradient row) from the sample kernels.  They are counted and
+// placed by destination row (integer atomics), each row's entries sorted by
+// (col, value bits) and every run of equal col summed in that order, so the
+// sums do not depend on the order the list was written in.
+__global__ void k_ml_count(const int32_t* __restrict__ ij, const unsigned long long* __restrict__ count,
+                           int64_t cap, int64_t nsys, int32_t* __restrict__ cnt, int32_t* __restrict__ err) {
+    const int64_t n = min((int64_t)*count, cap);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = ij[2 * e];
+        if (r < 0 || r >= nsys) { atomicExch(err, 2); continue; }
+        atomicAdd(&cnt[r], 1);
+    }
+}
+__global__ void k_ml_fill(const int32_t* __restrict__ ij, const unsigned long long* __restrict__ count, int64_t cap,
+                          int64_t nsys, const int32_t* __restrict__ off, int32_t* __restrict__ cur,
+                          int32_t* __restrict__ perm) {
+    const int64_t n = min((int64_t)*count, cap);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = ij[2 * e];
+        if (r < 0 || r >= nsys) continue;
+        perm[off[r] + atomicAdd(&cur[r], 1)] = (int32_t)e;
+    }
+}
+__device__ __forceinline__ bool ml_less(const int32_t* ij, const double* blk, int32_t a, int32_t b) {
+    const int32_t ca = ij[2 * (int64_t)a + 1], cb = ij[2 * (int64_t)b + 1];
+    if (ca != cb) return ca < cb;
+    for (int q = 0; q < 9; ++q) {
+        const unsigned long long ua = (unsigned long long)__double_as_longlong(blk[9 * (int64_t)a + q]);
+        const unsigned long long ub = (unsigned long long)__double_as_longlong(blk[9 * (int64_t)b + q]);
+        if (ua != ub) return ua < ub;
+    }
+    return false;
+}
+// one thread per system row: sort, then sum the runs; rows (col -1) go to
+// cgrad, blocks (col >= row) to xvals at their pattern position (the stored
+// half; the entries (j, i) of a master-master pair are the transposes)
+template <class TG>
+__global__ void k_ml_reduce(int64_t nsys, const int32_t* __restrict__ off, int32_t* __restrict__ perm,
+                            const int32_t* __restrict__ ij, const double* __restrict__ blk,
+                            const int32_t* __restrict__ rp, const int32_t* __restrict__ llen,
+                            const int32_t* __restrict__ ci, double* __restrict__ xvals, TG* __restrict__ cgrad,
+                            int32_t* __restrict__ err) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nsys) return;
+    const int32_t b0 = off[r], b1 = off[r + 1];
+    for (int32_t k = b0 + 1; k < b1; ++k) {   // insertion sort (short rows)
+        const int32_t v = perm[k];
+        int32_t m = k - 1;
+        while (m >= b0 && ml_less(ij, blk, v, perm[m])) { perm[m + 1] = perm[m]; --m; }
+        perm[m + 1] = v;
+    }
+    for (int32_t k = b0; k < b1;) {
+        const int32_t col = ij[2 * (int64_t)perm[k] + 1];
+        double sum[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        int32_t k2 = k;
+        for (; k2 < b1 && ij[2 * (int64_t)perm[k2] + 1] == col; ++k2) {
+            const double* B = blk + 9 * (int64_t)perm[k2];
+            for (int q = 0; q < 9; ++q) sum[q] += B[q];
+        }
+        k = k2;
+        if (col < 0) {
+            for (int q = 0; q < 3; ++q) cgrad[3 * r + q] = (TG)sum[q];
+        } else if (xvals && col >= r) {
+            int32_t lo = rp[r] + llen[r], hi = rp[r + 1] - 1, at = -1;
+            while (lo <= hi) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (ci[mid] == col) { at = mid; break; }
+                if (ci[mid] < col) lo = mid + 1; else hi = mid - 1;
+            }
+            if (at < 0) { atomicExch(err, 1); continue; }
+            for (int q = 0; q < 9; ++q) xvals[9 * (int64_t)at + q] = sum[q];
+        }
+    }
 }
 
 // ------------------------------------------------------------------ PCG ---
@@ -1013,19 +1101,39 @@ __global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __r
 __global__ void k_inertia_multi(int64_t nv, const double* __restrict__ x, const double* __restrict__ p,
                                 const double* __restrict__ xhat, const double* __restrict__ mass,
                                 const double* __restrict__ alphas_env, int astride,
-                                const int32_t* __restrict__ vert_env, int na, double* __restrict__ out) {
+                                const int32_t* __restrict__ vert_env, int na, double* __restrict__ out,
+                                const double* __restrict__ fext, double h2, int delta) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     const double* alphas = alphas_env + (int64_t)astride * vert_env[v];
     const double m = mass[v];
+    if (delta) {
+        // the change from x: m (a p.(x - xhat) + a^2/2 |p|^2) - h^2 a f.p
+        for (int j = 0; j < na; ++j) {
+            const double a = alphas[j];
+            double e = 0.0, w = 0.0;
+            for (int c = 0; c < 3; ++c) {
+                const double pc = p[3 * v + c];
+                e += m * (a * pc * (x[3 * v + c] - xhat[3 * v + c]) + 0.5 * a * a * pc * pc);
+                if (fext) w += a * fext[3 * v + c] * pc;
+            }
+            out[(int64_t)j * nv + v] = fext ? e - h2 * w : e;
+        }
+        return;
+    }
     for (int j = 0; j < na; ++j) {
         const double a = alphas[j];
-        double e = 0.0;
+        double e = 0.0, w = 0.0;
         for (int c = 0; c < 3; ++c) {
-            const double d = (p ? x[3 * v + c] + a * p[3 * v + c] : x[3 * v + c]) - xhat[3 * v + c];
+            const double xa = p ? x[3 * v + c] + a * p[3 * v + c] : x[3 * v + c];
+            const double d = xa - xhat[3 * v + c];
             e += 0.5 * m * d * d;
+            if (fext) w += fext[3 * v + c] * d;
         }
-        out[(int64_t)j * nv + v] = e;
+        // external forces (joint step): -h^2 f.(x - xhat) per vertex, the
+        // work -h^2 f.x up to a constant of the step (small, so its
+        // rounding does not swamp the line search's sufficient-decrease test)
+        out[(int64_t)j * nv + v] = fext ? e - h2 * w : e;
     }
 }
 
@@ -1198,10 +1306,10 @@ static cudaError_t seg_sum(Ctx& c, const SegRed& R, const double* in, int64_t in
 
 cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess) {
     NewtonState& N = *c.newton;
-    ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, c.X.p, N.mu, N.lam};
-    if (c.nt > 0) {
+    ElasticView E{N.ntsys, N.tets.p, N.Dminv.p, N.vol.p, N.Xsys.p, N.mu, N.lam};
+    if (N.ntsys > 0) {
         const bool f32 = c.P.precision == IPC_PREC_MIXED;
-        const unsigned g = nblk(c.nt, 128);
+        const unsigned g = nblk(N.ntsys, 128);
         if (!want_hess)
             k_nh_eval<false, double><<<g, 128, 0, c.stream>>>(E, x, N.tE.p, N.tG.p, nullptr, N.ebad.p, N.tet_env.p);
         else if (f32)
@@ -1213,22 +1321,25 @@ cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess) {
     return seg_sum(c, N.seg_t, N.tE.p, 0, 1, N.es.p + kEsEe, kES);
 }
 
-cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na, int slot) {
+cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na, int slot,
+                            bool delta) {
     NewtonState& N = *c.newton;
-    ElasticView E{c.nt, N.tets.p, N.Dminv.p, N.vol.p, c.X.p, N.mu, N.lam};
-    if (c.nt > 0) {
-        k_nh_energy_multi<<<nblk(c.nt, 128), 128, 0, c.stream>>>(E, x, p, alphas_env, 8, N.tet_env.p, na, N.tE8.p);
+    ElasticView E{N.ntsys, N.tets.p, N.Dminv.p, N.vol.p, N.Xsys.p, N.mu, N.lam};
+    if (N.ntsys > 0) {
+        k_nh_energy_multi<<<nblk(N.ntsys, 128), 128, 0, c.stream>>>(E, x, p, alphas_env, 8, N.tet_env.p, na,
+                                                                   N.tE8.p, delta ? N.tE.p : nullptr);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
-    return seg_sum(c, N.seg_t, N.tE8.p, c.nt, na, N.es.p + slot, kES);
+    return seg_sum(c, N.seg_t, N.tE8.p, N.ntsys, na, N.es.p + slot, kES);
 }
 
 cudaError_t assemble_grad(Ctx& c, const double* x, const double* xhat, const void* cgrad, bool cgrad_f32,
                           double* G) {
     NewtonState& N = *c.newton;
     const double h2 = c.prm.h * c.prm.h;
-    k_assemble_grad<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, xhat, N.mass.p, N.dir.p, N.vte_off.p,
-                                                          N.vte.p, N.tG.p, cgrad, cgrad_f32 ? 1 : 0, h2, G);
+    k_assemble_grad<<<nblk(N.nsys, 256), 256, 0, c.stream>>>(N.nsys, x, xhat, N.mass.p, N.dir.p, N.vte_off.p,
+                                                            N.vte.p, N.tG.p, cgrad, cgrad_f32 ? 1 : 0, N.fext, h2,
+                                                            G);
     return cudaGetLastError();
 }
 
@@ -1239,19 +1350,19 @@ cudaError_t assemble_bsr(Ctx& c) {
     if (g == 0) return cudaSuccess;
     if (c.P.precision == IPC_PREC_MIXED)
         k_assemble_sell<float, float, float><<<g, 256, 0, c.stream>>>(
-            c.nv, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.llen.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH32.p, N.cmap.p,
-            c.cb_val32.p, N.mass.p, N.dir.p, h2, N.A32.p);
+            N.nsys, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.llen.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH32.p, N.cmap.p,
+            c.cb_val32.p, N.joint ? N.xvals.p : nullptr, N.mass.p, N.dir.p, h2, N.A32.p);
     else
         k_assemble_sell<double, double, double><<<g, 256, 0, c.stream>>>(
-            c.nv, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.llen.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH64.p, N.cmap.p,
-            c.cb_val64.p, N.mass.p, N.dir.p, h2, N.A64.p);
+            N.nsys, N.ngroups, N.goff.p, N.gslice.p, N.rp.p, N.llen.p, N.ci.p, N.bt_off.p, N.bt.p, N.tH64.p, N.cmap.p,
+            c.cb_val64.p, N.joint ? N.xvals.p : nullptr, N.mass.p, N.dir.p, h2, N.A64.p);
     return cudaGetLastError();
 }
 
 // dot(a, b) per environment (3 nv entries) into es[slot], fixed order
 cudaError_t dot_env(Ctx& c, const double* a, const double* b, int slot) {
     NewtonState& N = *c.newton;
-    const int64_t n = 3 * c.nv;
+    const int64_t n = 3 * N.nsys;
     k_mul<<<nblk(n, 256), 256, 0, c.stream>>>(n, a, b, N.w.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     return seg_sum(c, N.seg_v3, N.w.p, 0, 1, N.es.p + slot, kES);
@@ -1368,7 +1479,7 @@ static bool pcg_chunk_graph(Ctx& c, double* xout) {
 cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int max_it, int* iters,
                       int* env_iters) {
     NewtonState& N = *c.newton;
-    const int64_t nv = c.nv;
+    const int64_t nv = N.nsys;
     cudaStream_t s = c.stream;
     const unsigned gr = (unsigned)N.nblk_v;
     if (c.P.precision == IPC_PREC_MIXED) {
@@ -1451,14 +1562,36 @@ cudaError_t newton_setup(Ctx& c) {
     if (c.newton) return cudaSuccess;
     auto Np = std::make_unique<NewtonState>();
     NewtonState& N = *Np;
-    const int64_t nv = c.nv, nt = c.nt;
     cudaStream_t s = c.stream;
     const ipc_params& q = c.prm;
+    // The system: the pad's vertices and tets, followed (joint step with a
+    // deformable master) by the master body's.
+    const bool joint = c.joint;
+    std::vector<double> Xj;
+    std::vector<int32_t> Tj;
+    std::vector<uint8_t> Dj;
+    if (joint) {
+        if (c.n_env != 1) return cudaErrorInvalidValue;
+        Xj = c.h_X;
+        Xj.insert(Xj.end(), c.h_Y0.begin(), c.h_Y0.end());
+        Tj = c.h_tets;
+        for (int32_t m : c.h_mtets) Tj.push_back(m + (int32_t)c.nv);
+        Dj = c.h_dir;
+        Dj.insert(Dj.end(), c.h_mdir.begin(), c.h_mdir.end());
+    }
+    const int64_t nv = joint ? c.nv + c.nmv : c.nv;
+    const int64_t nt = joint ? (int64_t)Tj.size() / 4 : c.nt;
+    const std::vector<uint8_t>& Dir = joint ? Dj : c.h_dir;
+    const std::vector<int64_t> ev = joint ? std::vector<int64_t>{0, nv} : c.env_vert_off;
+    const std::vector<int64_t> et = joint ? std::vector<int64_t>{0, nt} : c.env_tet_off;
+    N.joint = joint;
+    N.nsys = nv;
+    N.ntsys = nt;
     N.mu = q.youngs / (2.0 * (1.0 + q.poisson));
     N.lam = q.youngs * q.poisson / ((1.0 + q.poisson) * (1.0 - 2.0 * q.poisson));
     std::vector<double> Dminv(9 * (size_t)nt), vol(nt), mass(nv, 0.0);
-    const int32_t* T = c.h_tets.data();
-    const double* X = c.h_X.data();
+    const int32_t* T = joint ? Tj.data() : c.h_tets.data();
+    const double* X = joint ? Xj.data() : c.h_X.data();
     for (int64_t t = 0; t < nt; ++t) {
         const int32_t* Tt = T + 4 * t;
         double Dm[9];
@@ -1478,6 +1611,56 @@ cudaError_t newton_setup(Ctx& c) {
         std::vector<int32_t> cur(vte_off.begin(), vte_off.end() - 1);
         for (int64_t e = 0; e < 4 * nt; ++e) vte[cur[T[e]]++] = (int32_t)e;
     }
+    // joint step: every (slave triangle vertex, master triangle vertex) pair
+    // whose triangles' rest boxes come within the pattern radius, and the
+    // vertex pairs of each master triangle
+    std::vector<std::vector<int32_t>> jx(joint ? nv : 0);
+    if (joint) {
+        const int64_t np = c.nv;
+        auto mean_edge = [](const std::vector<int32_t>& F, const double* P) {
+            double sum = 0.0;
+            int64_t n = 0;
+            for (size_t t = 0; t + 2 < F.size(); t += 3)
+                for (int a = 0; a < 3; ++a) {
+                    const double* u = P + 3 * (int64_t)F[t + a];
+                    const double* w = P + 3 * (int64_t)F[t + (a + 1) % 3];
+                    sum += sqrt((u[0] - w[0]) * (u[0] - w[0]) + (u[1] - w[1]) * (u[1] - w[1]) + (u[2] - w[2]) * (u[2] - w[2]));
+                    ++n;
+                }
+            return n ? sum / (double)n : 0.0;
+        };
+        double R = c.joint_radius;
+        if (!(R > 0.0))
+            R = 2.0 * std::max(mean_edge(c.h_stri, c.h_X.data()), mean_edge(c.h_mtri, c.h_Y0.data())) + 2.0 * c.P.dhat;
+        auto box = [](const int32_t* F, const double* P, double* lo, double* hi) {
+            for (int q = 0; q < 3; ++q) { lo[q] = INFINITY; hi[q] = -INFINITY; }
+            for (int a = 0; a < 3; ++a)
+                for (int q = 0; q < 3; ++q) {
+                    lo[q] = std::min(lo[q], P[3 * (int64_t)F[a] + q]);
+                    hi[q] = std::max(hi[q], P[3 * (int64_t)F[a] + q]);
+                }
+        };
+        std::vector<double> mb(6 * (size_t)c.nmt);
+        for (int64_t m = 0; m < c.nmt; ++m) box(&c.h_mtri[3 * m], c.h_Y0.data(), &mb[6 * m], &mb[6 * m + 3]);
+        for (int64_t t = 0; t < c.ns; ++t) {
+            double lo[3], hi[3];
+            box(&c.h_stri[3 * t], c.h_X.data(), lo, hi);
+            for (int64_t m = 0; m < c.nmt; ++m) {
+                bool near = true;
+                for (int q = 0; q < 3; ++q) near = near && lo[q] - R <= mb[6 * m + 3 + q] && mb[6 * m + q] <= hi[q] + R;
+                if (!near) continue;
+                for (int a = 0; a < 3; ++a)
+                    for (int b = 0; b < 3; ++b) {
+                        const int32_t u = c.h_stri[3 * t + a], w = (int32_t)np + c.h_mtri[3 * m + b];
+                        jx[u].push_back(w);
+                        jx[w].push_back(u);
+                    }
+            }
+        }
+        for (int64_t m = 0; m < c.nmt; ++m)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) jx[np + c.h_mtri[3 * m + a]].push_back((int32_t)np + c.h_mtri[3 * m + b]);
+    }
     // block pattern, row by row: the diagonal, every vertex sharing a tet, and
     // the contact pattern; tb[16 t + 4 a + b] = index of block (T[a], T[b])
     std::vector<int32_t> rp(nv + 1, 0), ci;
@@ -1491,7 +1674,9 @@ cudaError_t newton_setup(Ctx& c) {
             const int64_t t = vte[k] >> 2;
             for (int q = 0; q < 4; ++q) row.push_back(T[4 * t + q]);
         }
-        for (int k = c.h_cb_row[i]; k < c.h_cb_row[i + 1]; ++k) row.push_back(c.h_cb_col[k]);
+        if (i < c.nv)
+            for (int k = c.h_cb_row[i]; k < c.h_cb_row[i + 1]; ++k) row.push_back(c.h_cb_col[k]);
+        if (joint) row.insert(row.end(), jx[i].begin(), jx[i].end());
         std::sort(row.begin(), row.end());
         row.erase(std::unique(row.begin(), row.end()), row.end());
         const int64_t base = (int64_t)ci.size();
@@ -1519,7 +1704,7 @@ cudaError_t newton_setup(Ctx& c) {
     }
     // global block -> contact block
     std::vector<int32_t> cmap(nnzb, -1);
-    for (int64_t i = 0; i < nv; ++i)
+    for (int64_t i = 0; i < c.nv; ++i)
         for (int k = c.h_cb_row[i]; k < c.h_cb_row[i + 1]; ++k) {
             const int64_t pos = std::lower_bound(ci.begin() + rp[i], ci.begin() + rp[i + 1], c.h_cb_col[k]) - ci.begin();
             cmap[pos] = k;
@@ -1588,7 +1773,7 @@ cudaError_t newton_setup(Ctx& c) {
     N.n_env = ne;
     std::vector<int64_t> poff(ne + 1, 0);
     for (int e = 0; e < ne; ++e) {
-        const int64_t n_e = c.env_vert_off[e + 1] - c.env_vert_off[e];
+        const int64_t n_e = ev[e + 1] - ev[e];
         if (n_e <= 0) return cudaErrorInvalidValue;   // an environment without pad vertices
         poff[e + 1] = poff[e] + (n_e + 3) / 4 * 4;
     }
@@ -1598,7 +1783,7 @@ cudaError_t newton_setup(Ctx& c) {
     N.h_env_nblk_v.assign(ne, 0);
     N.h_env_nblk_p.assign(ne, 0);
     for (int e = 0; e < ne; ++e) {
-        const int64_t v0 = c.env_vert_off[e], v1 = c.env_vert_off[e + 1];
+        const int64_t v0 = ev[e], v1 = ev[e + 1];
         for (int64_t v = v0; v < v1; ++v) {
             vprow[v] = (int32_t)(poff[e] + (v - v0));
             prow_v[poff[e] + (v - v0)] = (int32_t)v;
@@ -1633,31 +1818,31 @@ cudaError_t newton_setup(Ctx& c) {
     // and tet, segmented sums over vertices (1 and 3 entries each), tets and
     // slave triangles, the per-environment scalars, flags and step sizes, and
     // pinned host copies of them.
-    if (c.env_tet_off[ne] != nt || c.env_stri_off[ne] != c.ns || 3 * nv > INT32_MAX) return cudaErrorInvalidValue;
+    if (et[ne] != nt || c.env_stri_off[ne] != c.ns || 3 * nv > INT32_MAX) return cudaErrorInvalidValue;
     {
         std::vector<int32_t> venv(nv), tenv(nt);
         N.h_lbar.assign(ne, 0.0);
         N.h_has_dir.assign(ne, 0);
         for (int e = 0; e < ne; ++e) {
-            for (int64_t v = c.env_vert_off[e]; v < c.env_vert_off[e + 1]; ++v) {
+            for (int64_t v = ev[e]; v < ev[e + 1]; ++v) {
                 venv[v] = e;
-                if (c.h_dir[v]) N.h_has_dir[e] = 1;
+                if (Dir[v]) N.h_has_dir[e] = 1;
             }
             double ve = 0.0;   // the order of the whole-scene sum, over this environment's tets
-            for (int64_t t = c.env_tet_off[e]; t < c.env_tet_off[e + 1]; ++t) {
+            for (int64_t t = et[e]; t < et[e + 1]; ++t) {
                 tenv[t] = e;
                 ve += vol[t];
             }
-            const int64_t nte = c.env_tet_off[e + 1] - c.env_tet_off[e];
+            const int64_t nte = et[e + 1] - et[e];
             N.h_lbar[e] = nte > 0 ? cbrt(ve / (double)nte) : 0.0;
         }
         GMCP_CUDA_TRY(N.vert_env.upload(venv.data(), venv.size(), s));
         GMCP_CUDA_TRY(N.tet_env.upload(tenv.data(), tenv.size(), s));
         GMCP_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    GMCP_CUDA_TRY(build_seg(N.seg_v, c.env_vert_off, 1, s));
-    GMCP_CUDA_TRY(build_seg(N.seg_v3, c.env_vert_off, 3, s));
-    GMCP_CUDA_TRY(build_seg(N.seg_t, c.env_tet_off, 1, s));
+    GMCP_CUDA_TRY(build_seg(N.seg_v, ev, 1, s));
+    GMCP_CUDA_TRY(build_seg(N.seg_v3, ev, 3, s));
+    GMCP_CUDA_TRY(build_seg(N.seg_t, et, 1, s));
     GMCP_CUDA_TRY(build_seg(N.seg_s, c.env_stri_off, 1, s));
     const int64_t seg_max = std::max(std::max(N.seg_v.nblk, N.seg_v3.nblk), std::max(N.seg_t.nblk, N.seg_s.nblk));
     GMCP_CUDA_TRY(N.seg_part.ensure(8 * (size_t)seg_max + 8));
@@ -1695,7 +1880,22 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.Dminv.upload(Dminv.data(), Dminv.size(), s));
     GMCP_CUDA_TRY(N.vol.upload(vol.data(), vol.size(), s));
     GMCP_CUDA_TRY(N.mass.upload(mass.data(), mass.size(), s));
-    GMCP_CUDA_TRY(N.dir.upload(c.h_dir.data(), c.h_dir.size(), s));
+    GMCP_CUDA_TRY(N.dir.upload(Dir.data(), Dir.size(), s));
+    GMCP_CUDA_TRY(N.Xsys.upload(X, 3 * (size_t)nv, s));
+    if (joint) {
+        N.ml_cap = std::max<int64_t>((int64_t)1 << 16, 64 * c.ns);
+        GMCP_CUDA_TRY(N.ml_ij.ensure(2 * (size_t)N.ml_cap));
+        GMCP_CUDA_TRY(N.ml_blk.ensure(9 * (size_t)N.ml_cap));
+        GMCP_CUDA_TRY(N.ml_perm.ensure((size_t)N.ml_cap));
+        GMCP_CUDA_TRY(N.ml_count.ensure(1));
+        GMCP_CUDA_TRY(N.ml_cnt.ensure((size_t)nv + 1));
+        GMCP_CUDA_TRY(N.ml_off.ensure((size_t)nv + 2));
+        GMCP_CUDA_TRY(N.ml_cur.ensure((size_t)nv + 1));
+        GMCP_CUDA_TRY(N.ml_tmp.ensure(2 * scan_tmp_size(nv + 1)));
+        GMCP_CUDA_TRY(N.ml_err.ensure(1));
+        GMCP_CUDA_TRY(N.xvals.ensure(9 * (size_t)nnzb + 9));
+        GMCP_CUDA_TRY(cudaMemsetAsync(N.xvals.p, 0, sizeof(double) * (9 * (size_t)nnzb + 9), s));
+    }
     GMCP_CUDA_TRY(N.vte_off.upload(vte_off.data(), vte_off.size(), s));
     GMCP_CUDA_TRY(N.vte.upload(vte.data(), vte.size(), s));
     GMCP_CUDA_TRY(N.rp.upload(rp.data(), rp.size(), s));
@@ -1760,33 +1960,98 @@ cudaError_t newton_setup(Ctx& c) {
 // ---------------------------------------------------------------------------
 // energies and the assembled system
 // ---------------------------------------------------------------------------
-// total incremental potential of each environment at x + alphas_env[8 e +
-// j] p, j < na (<= 8), into es[kEsE8 + j]; the contact term is the
-// frozen-linear potential of the samples active at x (requires the candidate
-// lists of x).  ee0: alphas_env[8 e] = 0 and es[kEsEe] holds the elastic
-// energy at x (the same per-tet values and the same fixed-order sum), so
-// slot 0's elastic energy is not evaluated again.
+// the master positions that belong to system positions x: the master rows
+// of x in the joint step, else the context's kinematic master
+const double* master_of(Ctx& c, const double* x) {
+    return c.newton->joint ? x + 3 * c.nv : c.newton->xm.p;
+}
+const double* master_dir_of(Ctx& c, const double* p) {
+    return c.newton->joint ? p + 3 * c.nv : nullptr;
+}
+
+// Joint step: the gradient rows of the master vertices (into the contact
+// gradient's rows nv .. nsys) and, with want_hess, the blocks with master
+// vertices (into xvals), from the samples of the last pass at x, summed in a
+// fixed order (see k_ml_reduce).  A block outside the pattern sets
+// N.joint_miss and fails the call.
+cudaError_t joint_master_terms(Ctx& c, const double* x, bool want_hess) {
+    NewtonState& N = *c.newton;
+    const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    const double* xm = x + 3 * c.nv;
+    const int64_t nsys = N.nsys;
+    for (int attempt = 0;; ++attempt) {
+        GMCP_CUDA_TRY(contact_master_hess(c, x, xm, N.ml_ij.p, N.ml_blk.p, N.ml_cap, N.ml_count.p, true));
+        unsigned long long need = 0;
+        GMCP_CUDA_TRY(cudaMemcpyAsync(&need, N.ml_count.p, sizeof(need), cudaMemcpyDeviceToHost, c.stream));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        if ((int64_t)need <= N.ml_cap) break;
+        if (attempt >= 2) return cudaErrorInvalidValue;
+        N.ml_cap = (int64_t)need + (int64_t)need / 2 + 1024;
+        GMCP_CUDA_TRY(N.ml_ij.ensure(2 * (size_t)N.ml_cap));
+        GMCP_CUDA_TRY(N.ml_blk.ensure(9 * (size_t)N.ml_cap));
+        GMCP_CUDA_TRY(N.ml_perm.ensure((size_t)N.ml_cap));
+    }
+    cudaStream_t s = c.stream;
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.ml_cnt.p, 0, sizeof(int32_t) * (nsys + 1), s));
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.ml_cur.p, 0, sizeof(int32_t) * (nsys + 1), s));
+    GMCP_CUDA_TRY(cudaMemsetAsync(N.ml_err.p, 0, sizeof(int32_t), s));
+    const size_t gb = f32 ? sizeof(float) : sizeof(double);
+    char* cg = f32 ? (char*)N.cgrad32.p : (char*)N.cgrad64.p;
+    GMCP_CUDA_TRY(cudaMemsetAsync(cg + gb * 3 * c.nv, 0, gb * 3 * (nsys - c.nv), s));
+    if (want_hess) GMCP_CUDA_TRY(cudaMemsetAsync(N.xvals.p, 0, sizeof(double) * 9 * N.nnzb, s));
+    const unsigned g = (unsigned)std::min<int64_t>(4096, (N.ml_cap + 255) / 256);
+    k_ml_count<<<g, 256, 0, s>>>(N.ml_ij.p, N.ml_count.p, N.ml_cap, nsys, N.ml_cnt.p, N.ml_err.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    GMCP_CUDA_TRY(exclusive_scan_i32(N.ml_cnt.p, N.ml_off.p, nsys + 1, N.ml_tmp.p, N.ml_tmp.n, s));
+    k_ml_fill<<<g, 256, 0, s>>>(N.ml_ij.p, N.ml_count.p, N.ml_cap, nsys, N.ml_off.p, N.ml_cur.p, N.ml_perm.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    double* xv = want_hess ? N.xvals.p : nullptr;
+    if (f32)
+        k_ml_reduce<float><<<nblk(nsys, 128), 128, 0, s>>>(nsys, N.ml_off.p, N.ml_perm.p, N.ml_ij.p, N.ml_blk.p,
+                                                          N.rp.p, N.llen.p, N.ci.p, xv, N.cgrad32.p, N.ml_err.p);
+    else
+        k_ml_reduce<double><<<nblk(nsys, 128), 128, 0, s>>>(nsys, N.ml_off.p, N.ml_perm.p, N.ml_ij.p, N.ml_blk.p,
+                                                           N.rp.p, N.llen.p, N.ci.p, xv, N.cgrad64.p, N.ml_err.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    int32_t err = 0;
+    GMCP_CUDA_TRY(cudaMemcpyAsync(&err, N.ml_err.p, sizeof(err), cudaMemcpyDeviceToHost, s));
+    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) {
+        N.joint_miss = true;
+        return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
+}
+
+// change of each environment's incremental potential from x to x +
+// alphas_env[8 e + j] p, j < na (<= 8), into es[kEsE8 + j] (reading R22:
+// every term's change is formed before the sums -- per tet, per vertex, per
+// sample -- so the sufficient-decrease test is not lost in the rounding of
+// the total); the contact term is the frozen-linear potential of the samples
+// active at x (requires the candidate lists and per-tet energies of x, i.e.
+// the system assembled at x).  ee0: alphas_env[8 e] = 0, whose change is 0.
 cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_env, int na,
                          bool with_contact, bool ee0) {
     NewtonState& N = *c.newton;
     double* es = N.es.p;
     const int ne = N.n_env;
     if (ee0 && na > 1) {
-        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_env + 1, na - 1, kEsEe8 + 1));
-        GMCP_CUDA_TRY(cudaMemcpy2DAsync(es + kEsEe8, kES * sizeof(double), es + kEsEe, kES * sizeof(double),
-                                        sizeof(double), ne, cudaMemcpyDeviceToDevice, c.stream));
+        // slot 0 is alpha = 0: no change
+        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_env + 1, na - 1, kEsEe8 + 1, true));
+        GMCP_CUDA_TRY(cudaMemset2DAsync(es + kEsEe8, kES * sizeof(double), 0, sizeof(double), ne, c.stream));
     } else {
-        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_env, na, kEsEe8));
-    }
-    k_inertia_multi<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, p, N.xhat.p, N.mass.p, alphas_env, 8,
-                                                           N.vert_env.p, na, N.ein8.p);
-    GMCP_CUDA_TRY(cudaGetLastError());
-    GMCP_CUDA_TRY(seg_sum(c, N.seg_v, N.ein8.p, c.nv, na, es + kEsEin8, kES));
-    if (with_contact) {
-        GMCP_CUDA_TRY(contact_lagged(c, x, N.xm.p, p, alphas_env, na, N.triE8.p, nullptr, 8));
-        GMCP_CUDA_TRY(seg_sum(c, N.seg_s, N.triE8.p, c.ns, na, es + kEsEc8, kES));
+        GMCP_CUDA_TRY(nh_energy_multi(c, x, p, alphas_env, na, kEsEe8, true));
     }
     const double h2 = c.prm.h * c.prm.h;
+    k_inertia_multi<<<nblk(N.nsys, 256), 256, 0, c.stream>>>(N.nsys, x, p, N.xhat.p, N.mass.p, alphas_env, 8,
+                                                             N.vert_env.p, na, N.ein8.p, N.fext, h2, 1);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    GMCP_CUDA_TRY(seg_sum(c, N.seg_v, N.ein8.p, N.nsys, na, es + kEsEin8, kES));
+    if (with_contact) {
+        GMCP_CUDA_TRY(contact_lagged(c, x, master_of(c, x), p, alphas_env, na, N.triE8.p, nullptr, 8,
+                                     N.joint ? p + 3 * c.nv : nullptr));
+        GMCP_CUDA_TRY(seg_sum(c, N.seg_s, N.triE8.p, c.ns, na, es + kEsEc8, kES));
+    }
     k_combine<<<ne, 32, 0, c.stream>>>(na, es + kEsEin8, es + kEsEe8, with_contact ? es + kEsEc8 : nullptr, h2,
                                        es + kEsE8);
     return cudaGetLastError();
@@ -1806,22 +2071,24 @@ cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess) {
         ProfScope ps(c.prof, c.stream, "elastic");
         GMCP_CUDA_TRY(nh_eval(c, x, want_hess));
     }
-    GMCP_CUDA_TRY(run_candidates(c, x, N.xm.p));
+    const double* xm = master_of(c, x);
+    GMCP_CUDA_TRY(run_candidates(c, x, xm));
     void* cg = f32 ? (void*)N.cgrad32.p : (void*)N.cgrad64.p;
-    GMCP_CUDA_TRY(contact_eval(c, x, N.xm.p, nullptr, cg, want_hess, nullptr));
+    GMCP_CUDA_TRY(contact_eval(c, x, xm, nullptr, cg, want_hess, nullptr));
     // the contact energy of the samples of this pass (stamped triangles)
     GMCP_CUDA_TRY(seg_sum(c, N.seg_s, c.tri_E.p, 0, 1, es + kEsEc, kES, c.tri_stamp.p, c.misc_i32.p + kSlotPass));
+    if (N.joint) GMCP_CUDA_TRY(joint_master_terms(c, x, want_hess));
     {
         ProfScope ps(c.prof, c.stream, "assemble");
         GMCP_CUDA_TRY(assemble_grad(c, x, N.xhat.p, cg, f32, N.G.p));
         if (want_hess) GMCP_CUDA_TRY(assemble_bsr(c));
     }
     // total energy: inertia at x (one term, alpha 0, p unused)
-    k_inertia_multi<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, nullptr, N.xhat.p, N.mass.p, N.ezero.p, 0,
-                                                           N.vert_env.p, 1, N.ein8.p);
+    const double h2 = c.prm.h * c.prm.h;
+    k_inertia_multi<<<nblk(N.nsys, 256), 256, 0, c.stream>>>(N.nsys, x, nullptr, N.xhat.p, N.mass.p, N.ezero.p, 0,
+                                                             N.vert_env.p, 1, N.ein8.p, N.fext, h2, 0);
     GMCP_CUDA_TRY(cudaGetLastError());
     GMCP_CUDA_TRY(seg_sum(c, N.seg_v, N.ein8.p, 0, 1, es + kEsEin, kES));
-    const double h2 = c.prm.h * c.prm.h;
     k_combine<<<ne, 32, 0, c.stream>>>(1, es + kEsEin, es + kEsEe, es + kEsEc, h2, es + kEsE);
     GMCP_CUDA_TRY(cudaGetLastError());
     return dot_env(c, N.G.p, N.G.p, kEsG2);
@@ -1831,17 +2098,17 @@ cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess) {
 cudaError_t vec_axpy_env(Ctx& c, const double* x, const double* p, const double* alpha_env, const int32_t* mask,
                          double* out) {
     NewtonState& N = *c.newton;
-    k_axpy_env<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, p, alpha_env, mask, N.vert_env.p, out);
+    k_axpy_env<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, x, p, alpha_env, mask, N.vert_env.p, out);
     return cudaGetLastError();
 }
 cudaError_t vec_copy_env(Ctx& c, const double* src, const int32_t* mask, double* dst) {
     NewtonState& N = *c.newton;
-    k_copy_env<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, src, mask, N.vert_env.p, dst);
+    k_copy_env<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, src, mask, N.vert_env.p, dst);
     return cudaGetLastError();
 }
 cudaError_t vec_zero_env(Ctx& c, const int32_t* mask, double* a) {
     NewtonState& N = *c.newton;
-    k_zero_env<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, mask, N.vert_env.p, a);
+    k_zero_env<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, mask, N.vert_env.p, a);
     return cudaGetLastError();
 }
 cudaError_t vec_copy_master_env(Ctx& c, const double* src, const int32_t* mask, double* dst) {
@@ -1851,7 +2118,7 @@ cudaError_t vec_copy_master_env(Ctx& c, const double* src, const int32_t* mask, 
 }
 cudaError_t vec_velocity_env(Ctx& c, const double* x, const double* xt, const int32_t* mask, double* v) {
     NewtonState& N = *c.newton;
-    k_velocity_env<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, xt, c.prm.h, mask, N.vert_env.p, v);
+    k_velocity_env<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, x, xt, c.prm.h, mask, N.vert_env.p, v);
     return cudaGetLastError();
 }
 
@@ -1862,27 +2129,27 @@ cudaError_t vec_axpy(Ctx& c, int64_t n, double a, const double* x, const double*
 }
 cudaError_t vec_xhat(Ctx& c, const double* x, const double* v, double* xhat) {
     const double* g = c.prm.gravity;
-    k_xhat<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, x, v, c.prm.h, g[0], g[1], g[2], xhat);
+    k_xhat<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, x, v, c.prm.h, g[0], g[1], g[2], xhat);
     return cudaGetLastError();
 }
 cudaError_t vec_dir_delta(Ctx& c, const double* x, const double* xhat, double* dP) {
-    k_dir_delta<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, c.newton->dir.p, x, xhat, dP);
+    k_dir_delta<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, c.newton->dir.p, x, xhat, dP);
     return cudaGetLastError();
 }
 cudaError_t vec_set_dir(Ctx& c, const double* src, double* dst) {
-    k_set_dir<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, c.newton->dir.p, src, dst);
+    k_set_dir<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, c.newton->dir.p, src, dst);
     return cudaGetLastError();
 }
 cudaError_t vec_free_delta(Ctx& c, const double* P, const double* xi, double* dP) {
-    k_free_delta<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, c.newton->dir.p, P, xi, dP);
+    k_free_delta<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, c.newton->dir.p, P, xi, dP);
     return cudaGetLastError();
 }
 cudaError_t vec_zero_dir(Ctx& c, double* p) {
-    k_zero_dir<<<nblk(c.nv, 256), 256, 0, c.stream>>>(c.nv, c.newton->dir.p, p);
+    k_zero_dir<<<nblk(c.newton->nsys, 256), 256, 0, c.stream>>>(c.newton->nsys, c.newton->dir.p, p);
     return cudaGetLastError();
 }
 cudaError_t vec_velocity(Ctx& c, const double* x, const double* xt, double* v) {
-    const int64_t n = 3 * c.nv;
+    const int64_t n = 3 * c.newton->nsys;
     k_velocity<<<nblk(n, 256), 256, 0, c.stream>>>(n, x, xt, c.prm.h, v);
     return cudaGetLastError();
 }

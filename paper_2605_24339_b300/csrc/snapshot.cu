@@ -94,6 +94,7 @@ ipc_status ipc_save(ipc_ctx* ctx, const char* path, const double* x_dev, const d
     if (!ctx) return IPC_ERR_ARG;
     Ctx& c = ctx_of(ctx);
     if (!path || !x_dev || !v_dev) return snap_fail(c, IPC_ERR_ARG, "ipc_save: NULL path, x or v");
+    if (c.joint) return snap_fail(c, IPC_ERR_ARG, "ipc_save: contexts with a master body are not supported");
     cudaError_t e = cudaSetDevice(c.device);
     const int64_t n3 = 3 * c.nv, m3 = 3 * c.nmv;
     std::vector<double> x(n3), v(n3), xm(m3);
@@ -151,6 +152,7 @@ ipc_status ipc_load(ipc_ctx* ctx, const char* path, double* x_dev, double* v_dev
     if (!ctx) return IPC_ERR_ARG;
     Ctx& c = ctx_of(ctx);
     if (!path || !x_dev || !v_dev) return snap_fail(c, IPC_ERR_ARG, "ipc_load: NULL path, x or v");
+    if (c.joint) return snap_fail(c, IPC_ERR_ARG, "ipc_load: contexts with a master body are not supported");
     std::vector<unsigned char> buf;
     {
         FILE* fp = fopen(path, "rb");
