@@ -354,6 +354,8 @@ def run_ours(args):
         line["newton_step"] = newton_measurement(dev)
         line["batched_step"] = batched_step_measurement(dev, n_env=args.step_envs, steps=10)
         line["warm_start"] = warm_start_measurement(dev)
+    if not args.no_newton:
+        line["patch_test"] = patch_measurement(dev)
     if not args.no_dual_map:
         line["dual_mesh"] = dual_mesh_measurement(dev)
         line["face_clip"] = face_clip_measurement(dev)
@@ -870,6 +872,46 @@ def batched_step_measurement(dev, n_env=16, steps=3, alone_envs=16):
     return out
 
 
+def patch_measurement(dev, steps=12):
+    """Contact patch test with a deformable master (Sec. 5.1, Table
+    patch_test): two 1 x 1 x 0.5 blocks on non-matching structured tet
+    meshes (5x5x2 and 4x4x2 cells), E = 1000, nu = 0, a pressure of 10 on the
+    upper block's top, the lower block's bottom held, h = 0.05 s, FP64 (the
+    free lateral mode of the upper block makes the system too ill-conditioned
+    for the FP32 matrix to reach the 1e-6 residual at rest); ``steps`` joint
+    time steps (ipc_newton_step_joint) per kappa.
+    Reported per kappa: sigma_zz mean and largest relative error per block,
+    the largest other stress component, statuses, Newton iterations and the
+    median wall time of a step.  The exact state is sigma_zz = -10."""
+    import torch
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests"))
+    from helpers import patch_report
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    out = {"workload": "patch_test 5x5x2 over 4x4x2 cells, E 1000, nu 0, pressure 10, h 0.05 s, "
+                       f"{steps} steps", "paper_table": {"1e4": [8.00e-4, 6.00e-3], "1e6": [4.66e-5, 2.48e-4],
+                                                          "1e8": [4.66e-5, 2.48e-4]}}
+    for kappa in (1e4, 1e6, 1e8):
+        sc, f = S.patch_test(kappa=kappa, h=0.05, density=1.0)
+        ctx = binding.Context(sc, precision="fp64", device=dev)
+        x = torch.as_tensor(np.concatenate([sc.X, sc.Y0]), device="cuda")
+        v = torch.zeros_like(x)
+        ft = torch.as_tensor(f, device="cuda")
+        times, st = [], []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = ctx.newton_step_joint(x, v, f_ext=ft)
+            torch.cuda.synchronize()
+            times.append((time.perf_counter() - t0) * 1e3)
+            st.append((r["status"], r["newton_iters"]))
+        ctx.close()
+        rep = patch_report(sc, x.cpu().numpy())
+        out[f"kappa_{kappa:.0e}"] = {"report": rep, "status_iters": st,
+                                     "ms_per_step_median": statistics.median(times)}
+    return out
+
+
 def warm_start_measurement(dev, train_iters=1500, timed_iters=50):
     """Learned warm start on the terrain press: tensor-core training
     throughput (one Adam step = forward + backward over all 594,441
@@ -1144,7 +1186,7 @@ def main():
                     help="--mode dense_passes: gel pad quads per side (256 = the measured workload)")
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
-    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "batchstep",
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "batchstep", "patch",
                                                        "dualmap", "faceclip",
                                                        "mastergrad", "dense", "dense_passes", "peaks"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
@@ -1174,6 +1216,8 @@ def main():
         run_dense_passes(args)
     elif args.mode == "peaks":
         print(json.dumps(measure_alu_peaks(0)), flush=True)
+    elif args.mode == "patch":
+        print(json.dumps(patch_measurement(0)), flush=True)
     elif args.mode == "batchstep":
         print(json.dumps(batched_step_measurement(0, n_env=args.step_envs, steps=max(1, args.steps))), flush=True)
     elif args.mode == "batch":
