@@ -281,6 +281,11 @@ struct NewtonState {
     std::vector<int32_t> h_env_nblk_v, h_env_nblk_p;   // blocks per env
     DBuf<int32_t> env_nblk_v, env_nblk_p;
     DBuf<double> escal;                  // [n_env][kEnvScal] per-environment PCG scalars
+    // environments of at most kSmallRows rows: solved by one block each
+    int64_t n_small = 0;
+    DBuf<int4> small_envs;               // [n_small] env, first row, end row
+    DBuf<int32_t> env_small;             // [n_env] 1 = small
+    DBuf<double> sm64;                   // their PCG vectors r, z, p, Ap (FP64 in both paths)
     DBuf<int32_t> vert_env, tet_env;     // [nv], [nt] environment of each vertex / tet
     SegRed seg_v3, seg_v, seg_t, seg_s;  // segmented sums over 3 nv, nv, nt, ns elements
     DBuf<double> seg_part;               // block partials of the segmented sums

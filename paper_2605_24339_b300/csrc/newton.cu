@@ -1082,11 +1082,178 @@ k_pcg_dir(const int4* __restrict__ blk, const V* __restrict__ z, V* __restrict__
     stv<V, 8>(p + 4 * i0, pv);
 }
 
+// ------------------------------------------ PCG of a small environment ---
+// One block of kSmallThreads runs the whole solve of one environment of at
+// most kSmallRows rows (the multi-block kernels pay two launches and a grid
+// of last-block handshakes per iteration, which dominate a system of a few
+// hundred rows; with more rows a thread, one SM's latency hiding falls short
+// and the multi-block path is faster): the same block-Jacobi PCG with p = 0
+// start, stop at
+// ||r|| <= rel_tol ||b||, at p^T A p <= 0 (update skipped) or after max_it
+// iterations; vectors on the padded rows, the matrix as the multi-block
+// SpMV reads it (stored blocks j >= i, transposed blocks j < i), x in FP64.
+// Dots per thread and warp in V, across warps in FP64 in a fixed order.
+// The environment's scalars are written as the multi-block solve writes
+// them, with its stop word set, so the multi-block kernels skip it.
+constexpr int kSmallThreads = 512;
+constexpr int kSmallRows = kSmallThreads;   // one row a thread: each row's loads are a short chain
+
+template <int NV, class R>
+__device__ __forceinline__ void small_sums(R v0, R v1, double* sh, double& t0, double& t1) {
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        if (NV > 1) v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();   // earlier readers of sh are done
+    if (lane == 0) { sh[w] = (double)v0; sh[32 + w] = (double)v1; }
+    __syncthreads();
+    if (w == 0) {
+        double a = lane < kSmallThreads / 32 ? sh[lane] : 0.0;
+        double b = lane < kSmallThreads / 32 ? sh[32 + lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (NV > 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) { sh[64] = a; sh[65] = b; }
+    }
+    __syncthreads();
+    t0 = sh[64];
+    t1 = sh[65];
+}
+
+// (TA, TP: the matrix and block-inverse storage; V: the vectors; used in
+// the FP64 path)
+template <class TA, class TP, class V>
+__global__ void __launch_bounds__(kSmallThreads)
+k_pcg_small(const int4* __restrict__ envs, const int32_t* __restrict__ vprow, const int32_t* __restrict__ rp,
+            const int32_t* __restrict__ goff, const int32_t* __restrict__ sci, const int32_t* __restrict__ llen,
+            const int32_t* __restrict__ lgoff, const int32_t* __restrict__ lcol, const int32_t* __restrict__ lmir,
+            const TA* __restrict__ A, const TP* __restrict__ Pinv, const double* __restrict__ bvec,
+            double* __restrict__ xout, V* __restrict__ r, V* __restrict__ z, V* __restrict__ p, V* __restrict__ Ap,
+            double* __restrict__ escal, double rel_tol, int max_it) {
+    __shared__ double sh[66];
+    const int4 E = envs[blockIdx.x];
+    double* scal = escal + kEnvScal * E.x;
+    // start: x = 0, r = b, z = P^-1 r, p = z
+    V lb = V(0), lrz = V(0);
+    for (int64_t i = E.y + threadIdx.x; i < E.z; i += kSmallThreads) {
+        const int64_t ir = vprow[i];
+        const V b0 = (V)bvec[3 * i], b1 = (V)bvec[3 * i + 1], b2 = (V)bvec[3 * i + 2];
+        V zz[3];
+        const TP* P9 = Pinv + 9 * ir;
+        for (int q = 0; q < 3; ++q) zz[q] = (V)P9[3 * q] * b0 + (V)P9[3 * q + 1] * b1 + (V)P9[3 * q + 2] * b2;
+        const V bv[3] = {b0, b1, b2};
+        for (int q = 0; q < 3; ++q) {
+            xout[3 * i + q] = 0.0;
+            r[3 * ir + q] = bv[q];
+            z[3 * ir + q] = zz[q];
+            p[4 * ir + q] = zz[q];
+            lb += bv[q] * bv[q];
+            lrz += bv[q] * zz[q];
+        }
+        p[4 * ir + 3] = V(0);
+    }
+    double bb, rz;
+    small_sums<2, V>(lb, lrz, sh, bb, rz);
+    const double thr = rel_tol * sqrt(bb);
+    int it = 0, done = bb > 0.0 ? 0 : 1, brk = 0;
+    while (!done && it < max_it) {
+        // Ap and p.Ap (p of the neighbours was written before the last sum's barrier)
+        V lpap = V(0);
+        for (int64_t i = E.y + threadIdx.x; i < E.z; i += kSmallThreads) {
+            const int64_t ir = vprow[i];
+            const int64_t g0 = goff[i >> 5];
+            const int lane = (int)(i & 31);
+            const int ll = llen[i];
+            const int len = rp[i + 1] - rp[i] - ll;
+            V a0 = V(0), a1 = V(0), a2 = V(0);
+            if (ll > 0) {
+                const int64_t lg0 = lgoff[i >> 5];
+                for (int k = 0; k < ll; ++k) {
+                    const int32_t m = lmir[32 * (lg0 + k) + lane];
+                    const int64_t j = lcol[32 * (lg0 + k) + lane];
+                    TA bt[9];
+                    load_blk(A, m >> 5, m & 31, bt);
+                    V b[9];
+                    for (int q = 0; q < 9; ++q) b[q] = (V)bt[q];
+                    const V p0 = p[4 * j], p1 = p[4 * j + 1], p2 = p[4 * j + 2];
+                    a0 += b[0] * p0 + b[3] * p1 + b[6] * p2;
+                    a1 += b[1] * p0 + b[4] * p1 + b[7] * p2;
+                    a2 += b[2] * p0 + b[5] * p1 + b[8] * p2;
+                }
+            }
+            for (int k = 0; k < len; ++k) {
+                const int64_t j = sci[32 * (g0 + k) + lane];
+                TA bt[9];
+                load_blk(A, g0 + k, lane, bt);
+                V b[9];
+                for (int q = 0; q < 9; ++q) b[q] = (V)bt[q];
+                const V p0 = p[4 * j], p1 = p[4 * j + 1], p2 = p[4 * j + 2];
+                a0 += b[0] * p0 + b[1] * p1 + b[2] * p2;
+                a1 += b[3] * p0 + b[4] * p1 + b[5] * p2;
+                a2 += b[6] * p0 + b[7] * p1 + b[8] * p2;
+            }
+            const V y0 = a0, y1 = a1, y2 = a2;
+            Ap[3 * ir] = y0; Ap[3 * ir + 1] = y1; Ap[3 * ir + 2] = y2;
+            lpap += p[4 * ir] * y0 + p[4 * ir + 1] * y1 + p[4 * ir + 2] * y2;
+        }
+        double pap, unused;
+        small_sums<1, V>(lpap, V(0), sh, pap, unused);
+        if (!(pap > 0.0)) { brk = 1; break; }
+        const V alv = (V)(rz / pap);
+        const double al = (double)alv;
+        V lrr = V(0), lrz2 = V(0);
+        for (int64_t i = E.y + threadIdx.x; i < E.z; i += kSmallThreads) {
+            const int64_t ir = vprow[i];
+            V rv[3], zz[3];
+            for (int q = 0; q < 3; ++q) {
+                xout[3 * i + q] += al * (double)p[4 * ir + q];
+                rv[q] = r[3 * ir + q] - alv * Ap[3 * ir + q];
+                r[3 * ir + q] = rv[q];
+            }
+            const TP* P9 = Pinv + 9 * ir;
+            for (int q = 0; q < 3; ++q)
+                zz[q] = (V)P9[3 * q] * rv[0] + (V)P9[3 * q + 1] * rv[1] + (V)P9[3 * q + 2] * rv[2];
+            for (int q = 0; q < 3; ++q) {
+                z[3 * ir + q] = zz[q];
+                lrr += rv[q] * rv[q];
+                lrz2 += rv[q] * zz[q];
+            }
+        }
+        double rr, rz2;
+        small_sums<2, V>(lrr, lrz2, sh, rr, rz2);
+        ++it;
+        if (sqrt(rr) <= thr) { done = 1; break; }
+        const V be = (V)(rz2 / rz);
+        rz = rz2;
+        for (int64_t i = E.y + threadIdx.x; i < E.z; i += kSmallThreads) {
+            const int64_t ir = vprow[i];
+            for (int q = 0; q < 3; ++q) p[4 * ir + q] = z[3 * ir + q] + be * p[4 * ir + q];
+        }
+        __syncthreads();   // p complete before the next product
+    }
+    if (threadIdx.x == 0) {
+        scal[kRz] = rz;
+        scal[kBb] = bb;
+        scal[kThr] = thr;
+        scal[kBreak] = brk ? 1.0 : 0.0;
+        scal[kDone] = done ? 1.0 : 0.0;
+        scal[kIters] = (double)it;
+        scal[kIt] = (double)it;
+        pcg_ictl(scal)[0] = 1;   // the multi-block kernels skip this environment
+        pcg_ictl(scal)[1] = it;
+    }
+}
+
 // x = hi + lo in FP64 (mixed path, after the solve), per vertex from its padded row
+// (skip: environments solved by k_pcg_small, whose x is already FP64)
 __global__ void k_pair_to_f64(int64_t nv, const int32_t* __restrict__ vprow, const float* __restrict__ hi,
-                              const float* __restrict__ lo, double* __restrict__ x) {
+                              const float* __restrict__ lo, double* __restrict__ x,
+                              const int32_t* __restrict__ vert_env, const int32_t* __restrict__ skip) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
+    if (skip && skip[vert_env[v]]) return;
     const int64_t r = vprow[v];
     for (int q = 0; q < 3; ++q) x[3 * v + q] = (double)hi[3 * r + q] + (double)lo[3 * r + q];
 }
@@ -1470,6 +1637,8 @@ static bool pcg_chunk_graph(Ctx& c, double* xout) {
     return true;
 }
 
+static int64_t nvp_of(const NewtonState& N) { return N.nvp; }
+
 // Block-Jacobi PCG for A p = b (A on the pattern N.rp / N.ci; FP32 matrix
 // and vectors in the mixed path, FP64 otherwise; FP64 solution and dots),
 // p = 0 start; stops at ||r|| <= rel_tol ||b||, at p^T A p <= 0 (that
@@ -1494,11 +1663,27 @@ cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int
                                                       N.ecount.p, N.escal.p, rel_tol);
     }
     GMCP_CUDA_TRY(cudaGetLastError());
-    const bool graph = c.graphs && !c.prof.on && pcg_chunk_graph(c, xout);
     const int ne = N.n_env;
+    // small environments: one block each solves the whole system
+    if (N.n_small > 0) {
+        if (c.P.precision == IPC_PREC_MIXED)
+            return cudaErrorInvalidValue;   // not reached: small environments are FP64 only
+        else
+            k_pcg_small<double, double, double><<<(unsigned)N.n_small, kSmallThreads, 0, s>>>(
+                N.small_envs.p, N.vprow.p, N.rp.p, N.goff.p, N.sci.p, N.llen.p, N.lgoff.p, N.lcol.p, N.lmir.p,
+                N.A64.p, N.Pinv.p, b, xout, N.sm64.p, N.sm64.p + 3 * nvp_of(N), N.sm64.p + 6 * nvp_of(N),
+                N.sm64.p + 10 * nvp_of(N), N.escal.p, rel_tol, max_it);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    const bool large = N.n_small < ne;
+    const bool graph = large && c.graphs && !c.prof.on && pcg_chunk_graph(c, xout);
     for (int e = 0; e < ne; ++e) if (env_iters) env_iters[e] = max_it;
     *iters = max_it;
-    for (int it = 0; it < max_it;) {
+    if (!large) {   // every environment was small: read their scalars once
+        GMCP_CUDA_TRY(pcg_enqueue_iters(c, xout, 0));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    for (int it = 0; large && it < max_it;) {
         const int chunk = std::min(kPcgChunk, max_it - it);
         if (graph && chunk == kPcgChunk) GMCP_CUDA_TRY(cudaGraphLaunch(c.pcg_graph.exec, s));
         else GMCP_CUDA_TRY(pcg_enqueue_iters(c, xout, chunk));
@@ -1518,7 +1703,8 @@ cudaError_t pcg_solve(Ctx& c, const double* b, double* xout, double rel_tol, int
     }
     *iters = mx;
     if (c.P.precision == IPC_PREC_MIXED) {
-        k_pair_to_f64<<<nblk(nv, 256), 256, 0, s>>>(nv, N.vprow.p, N.xh32.p, N.xl32.p, xout);
+        k_pair_to_f64<<<nblk(nv, 256), 256, 0, s>>>(nv, N.vprow.p, N.xh32.p, N.xl32.p, xout, N.vert_env.p,
+                                                    N.n_small > 0 ? N.env_small.p : nullptr);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -1798,6 +1984,25 @@ cudaError_t newton_setup(Ctx& c) {
     }
     N.nblk_v = (int64_t)blk_v.size();
     N.nblk_p = (int64_t)blk_p.size();
+    {
+        // small environments (by their own size only, so a batch solves each
+        // environment as a context holding it alone would); FP64 path only:
+        // with the FP32 matrix the one-block solve stalled on the joint patch
+        // test where the multi-block FP32 solve converges, so the mixed path
+        // keeps the multi-block kernels
+        std::vector<int4> small;
+        std::vector<int32_t> flag(ne, 0);
+        const bool f64 = c.P.precision != IPC_PREC_MIXED;
+        for (int e = 0; e < ne; ++e)
+            if (f64 && ev[e + 1] - ev[e] <= kSmallRows) {
+                small.push_back(make_int4(e, (int)ev[e], (int)ev[e + 1], 0));
+                flag[e] = 1;
+            }
+        N.n_small = (int64_t)small.size();
+        GMCP_CUDA_TRY(N.env_small.upload(flag.data(), flag.size(), s));
+        if (!small.empty()) GMCP_CUDA_TRY(N.small_envs.upload(small.data(), small.size(), s));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+    }
     // the SpMV reads the direction at the padded rows of its columns
     for (auto& col : sci) if (col >= 0) col = vprow[col];
     for (auto& col : lcol) if (col >= 0) col = vprow[col];
@@ -1911,6 +2116,7 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.tE8.ensure(8 * (size_t)nt + 8));
     // PCG vectors: rows padded per environment (above), the padding zero
     const int64_t nvp = nvp_env;
+    if (N.n_small > 0) GMCP_CUDA_TRY(N.sm64.ensure(13 * (size_t)nvp + 16));
     N.nvp = nvp;
     if (f32) {
         GMCP_CUDA_TRY(N.A32.ensure(288 * (size_t)ngroups + 288));
