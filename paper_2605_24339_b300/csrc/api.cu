@@ -25,6 +25,7 @@ SceneView Ctx::view() const {
     S.stri_own_vert = stri_own_vert.p; S.stri_own_edge = stri_own_edge.p; S.sedge = sedge.p;
     S.stri_env = stri_env.p; S.mtri_env = mtri_env.p; S.mvert_env = mvert_env.p;
     S.X = X.p; S.Y0 = Y0.p; S.srest_box = srest_box.p; S.mrest_box = mrest_box.p;
+    S.srest_box_f = srest_box_f.p; S.mrest_box_f = mrest_box_f.p; S.mvrest_box_f = mvrest_box_f.p;
     S.grid_org = grid_org.p; S.grid_inv = grid_inv.p; S.grid_dim = grid_dim.p; S.grid_off = grid_off.p;
     S.grid_org_f = grid_org_f.p; S.grid_inv_f = grid_inv_f.p;
     S.margin = margin;
@@ -306,7 +307,8 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.tri_G64.p, (uintptr_t)c.tri_S64.p, (uintptr_t)c.tri_n64.p, (uintptr_t)c.cb_val32.p,
             (uintptr_t)c.cb_val64.p, (uintptr_t)c.u64_tmp.p, (uintptr_t)c.i64_tmp.p, (uintptr_t)c.misc_i32.p,
             (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p, (uintptr_t)c.mboxf_in.p, (uintptr_t)c.tri_f32.p,
-            (uintptr_t)c.ym32.p, (uintptr_t)c.item_mask.p, (uintptr_t)c.item_mid.p};
+            (uintptr_t)c.ym32.p, (uintptr_t)c.item_mask.p, (uintptr_t)c.item_mid.p, (uintptr_t)c.tri_mid64.p,
+            (uintptr_t)c.tri_mid32.p, (uintptr_t)c.mtri_e32.p};
 }
 
 // Capture one pass on the context's private capture stream (nothing runs);
@@ -903,6 +905,28 @@ static void build_topology(Ctx& c, const ipc_scene* sc) {
     CK(c.Y0.upload(sc->m_rest, 3 * nmv, s));
     CK(c.srest_box.upload(sbox.data(), sbox.size(), s));
     CK(c.mrest_box.upload(mbox.data(), mbox.size(), s));
+    {
+        // FP32 copies rounded outward (lo down, hi up)
+        auto down = [](double v) { float f = (float)v; return (double)f > v ? std::nextafter(f, -INFINITY) : f; };
+        auto up = [](double v) { float f = (float)v; return (double)f < v ? std::nextafter(f, INFINITY) : f; };
+        auto outward = [&](const std::vector<double>& b) {
+            std::vector<float> o(b.size());
+            for (size_t k = 0; k < b.size(); k += 6)
+                for (int q = 0; q < 3; ++q) { o[k + q] = down(b[k + q]); o[k + 3 + q] = up(b[k + 3 + q]); }
+            return o;
+        };
+        const std::vector<float> sf = outward(sbox), mf = outward(mbox);
+        std::vector<float> vf(6 * (size_t)nmv + 6);
+        for (int64_t u = 0; u < nmv; ++u)
+            for (int q = 0; q < 3; ++q) {
+                vf[6 * u + q] = down(sc->m_rest[3 * u + q]);
+                vf[6 * u + 3 + q] = up(sc->m_rest[3 * u + q]);
+            }
+        CK(c.srest_box_f.upload(sf.data(), sf.size(), s));
+        CK(c.mrest_box_f.upload(mf.data(), mf.size(), s));
+        CK(c.mvrest_box_f.upload(vf.data(), vf.size(), s));
+        CK(cudaStreamSynchronize(s));   // the host vectors end here
+    }
     CK(c.grid_org.upload(org.data(), org.size(), s));
     CK(c.grid_inv.upload(inv.data(), inv.size(), s));
     std::vector<float> org_f(org.begin(), org.end()), inv_f(inv.begin(), inv.end());
@@ -1057,6 +1081,13 @@ ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx*
         c.P.dhat_guard = params->dhat_guard; c.P.kappa_guard = params->kappa_guard;
         c.P.ccd_slack = params->ccd_slack; c.P.ccd_max_iter = params->ccd_max_iter;
         c.P.face_clip = params->face_sampler;
+        c.P.inv_dhat = 1.0 / params->dhat;
+        {
+            const double r = params->dhat * (1.2 / 0.9);
+            float f = (float)(r * r);
+            if ((double)f < r * r) f = std::nextafter(f, INFINITY);
+            c.P.far_r2_f = f * (1.0f + 1e-6f);
+        }
         c.graphs = params->use_graphs != 0;
         c.n_env = scene->n_env;
         auto cp = [&](const int64_t* p) { return std::vector<int64_t>(p, p + scene->n_env + 1); };
@@ -1118,6 +1149,7 @@ void ipc_destroy(ipc_ctx* ctx) {
     if (c.aux_stream) cudaStreamDestroy(c.aux_stream);
     if (c.ev_touch0) cudaEventDestroy(c.ev_touch0);
     if (c.ev_touch1) cudaEventDestroy(c.ev_touch1);
+    if (c.ev_master) cudaEventDestroy(c.ev_master);
     if (c.ev_samples) cudaEventDestroy(c.ev_samples);
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_join) cudaEventDestroy(c.ev_join);

@@ -141,6 +141,19 @@ __device__ __forceinline__ void barrier(double g64, double eps64, float& B, floa
     d2B = -2.0f * L - 4.0f * r + r * r;
 }
 
+// the same with 1 / eps given (certified items, eps = dhat): d / eps as a
+// product; after the rounding to FP32 it matches the quotient but for ties
+__device__ __forceinline__ void barrier_inv(double g64, double eps64, double inv_eps, float& B, float& dB,
+                                            float& d2B) {
+    const double d64 = g64 - eps64;
+    const float d = (float)d64, g = (float)g64;
+    const float L = log1pf((float)(d64 * inv_eps));
+    const float r = d / g;
+    B = -d * d * L;
+    dB = -2.0f * d * L - d * r;
+    d2B = -2.0f * L - 4.0f * r + r * r;
+}
+
 // face-rule barycentrics per level (index L-1), filled at context creation
 __constant__ double c_rule[2][16][3];
 
@@ -236,6 +249,19 @@ __device__ __forceinline__ bool rest_far(const double* slo, const double* shi, c
                                          const double* mhi, double eps_max) {
     const double r = eps_max * (1.2 / 0.9);
     return box_dist2(slo, shi, mlo, mhi) >= r * r;
+}
+// certain FP32 version: boxes rounded outward and every operation rounded
+// down give a lower bound of the squared distance; r2f is the threshold
+// rounded up with a 1e-6 margin (Params::far_r2_f), so true implies that
+// rest_far holds in FP64 (false decides nothing)
+__device__ __forceinline__ bool rest_far_f(const float* slo, const float* shi, const float* mlo, const float* mhi,
+                                           float r2f) {
+    float s = 0.0f;
+    for (int q = 0; q < 3; ++q) {
+        const float d = fmaxf(0.0f, fmaxf(__fsub_rd(mlo[q], shi[q]), __fsub_rd(slo[q], mhi[q])));
+        s = __fadd_rd(s, __fmul_rd(d, d));
+    }
+    return s >= r2f;
 }
 
 __device__ __forceinline__ bool any_facing(const SceneView& S, const double* xm, const int32_t* tris,
@@ -400,11 +426,17 @@ __global__ void k_touch(SceneView S, CandView C, TouchArgs A) {
 // the exact samples), the unit normal in FP32 at [48, 51) and the three
 // vertices minus the origin, rounded to FP32, at [51, 60): the inputs of the
 // FP32 pre-filter of the sample items.
+// With tmid64 != NULL (mixed path) it also writes the middle stage's
+// per-triangle inputs: tmid32[12 i ...] the unit normal, x1 - x0 and x2 - x0
+// rounded to FP32 (the values the item kernels would form), tmid64[4 i ...]
+// n_s . dx_a for the three vertices (dx NULL: 0) and the sum of their
+// magnitudes: once per triangle instead of once per item.
 __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ x,
                             double* __restrict__ frame, int nk, int32_t* __restrict__ items,
                             int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp,
                             const int32_t* __restrict__ misc, float* __restrict__ tf32 = nullptr,
-                            int L = 1) {
+                            int L = 1, const double* __restrict__ dx = nullptr,
+                            double* __restrict__ tmid64 = nullptr, float* __restrict__ tmid32 = nullptr) {
     const int n_active = *C.n_active;
     const int32_t ps = tri_stamp ? misc[kSlotPass] : 0;
     const int lane = threadIdx.x & 31;
@@ -447,6 +479,20 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
                 o[54] = v1.x; o[55] = v1.y; o[56] = v1.z;
                 o[57] = v2.x; o[58] = v2.y; o[59] = v2.z;
             }
+            if (tmid64) {
+                const V3<double> ns = {f[0], f[1], f[2]};
+                float* m32 = tmid32 + 12 * (int64_t)i;
+                const V3<float> nf = tof(ns), e1 = tof(x1 - x0), e2 = tof(x2 - x0);
+                m32[0] = nf.x; m32[1] = nf.y; m32[2] = nf.z;
+                m32[3] = e1.x; m32[4] = e1.y; m32[5] = e1.z;
+                m32[6] = e2.x; m32[7] = e2.y; m32[8] = e2.z;
+                V3<double> d0 = {0, 0, 0}, d1 = {0, 0, 0}, d2 = {0, 0, 0};
+                if (dx) { d0 = ld3(dx, Tt[0]); d1 = ld3(dx, Tt[1]); d2 = ld3(dx, Tt[2]); }
+                double* m64 = tmid64 + 4 * (int64_t)i;
+                const double s0 = dot(ns, d0), s1 = dot(ns, d1), s2 = dot(ns, d2);
+                m64[0] = s0; m64[1] = s1; m64[2] = s2;
+                m64[3] = fabs(s0) + fabs(s1) + fabs(s2);
+            }
             if (items) {
                 const int32_t* cnt = C.count + 4 * t;
                 n = min(cnt[0], C.cap_f) * nk + 2 * min(cnt[1], C.cap_e) + min(cnt[2], C.cap_p);
@@ -479,6 +525,8 @@ struct TriData {
     double As;
     float tol_abs;
     const double* sb;      // rest box of the slave tri
+    const float* sbf;      // the same in FP32, rounded outward
+    double sdx[4];         // n_s . dx_a of the three vertices and the sum of their magnitudes (middle stage)
     int nf, ne, np;        // candidates (capped)
 };
 
@@ -498,10 +546,37 @@ __device__ __forceinline__ TriData load_tri(const SceneView& S, const CandView& 
     D.e1_f = tof(D.x1 - D.x0);
     D.e2_f = tof(D.x2 - D.x0);
     D.sb = S.srest_box + 6 * D.t;
+    D.sbf = S.srest_box_f + 6 * D.t;
     const int32_t* cnt = C.count + 4 * D.t;
     D.nf = min(cnt[0], C.cap_f); D.ne = min(cnt[1], C.cap_e); D.np = min(cnt[2], C.cap_p);
     D.dx0 = {0, 0, 0}; D.dx1 = {0, 0, 0}; D.dx2 = {0, 0, 0};
     if (dx) { D.dx0 = ld3(dx, Tt[0]); D.dx1 = ld3(dx, Tt[1]); D.dx2 = ld3(dx, Tt[2]); }
+    return D;
+}
+// the middle stage's view of a triangle: what it needs per item, read from
+// the per-triangle values k_tri_frame stored (tri_mid32: FP32 normal and
+// edges; tri_mid64: the normal's products with the vertex displacements)
+// instead of being formed again from FP64 coordinates for every item
+__device__ __forceinline__ TriData load_tri_mid(const SceneView& S, const CandView& C, const double* x,
+                                                const double* frame, const double* tmid64,
+                                                const float* tmid32, int i) {
+    TriData D;
+    D.t = C.active[i];
+    const int32_t* Tt = S.stri + 3 * D.t;
+    D.x0 = ld3(x, Tt[0]); D.x1 = ld3(x, Tt[1]); D.x2 = ld3(x, Tt[2]);
+    const double* fr = frame + 8 * (int64_t)i;
+    D.As = fr[3];
+    D.tol_abs = (float)fr[7];
+    const float* m = tmid32 + 12 * (int64_t)i;
+    D.ns_f = {m[0], m[1], m[2]};
+    D.e1_f = {m[3], m[4], m[5]};
+    D.e2_f = {m[6], m[7], m[8]};
+    const double* m64 = tmid64 + 4 * (int64_t)i;
+    for (int q = 0; q < 4; ++q) D.sdx[q] = m64[q];
+    D.sb = S.srest_box + 6 * D.t;
+    D.sbf = S.srest_box_f + 6 * D.t;
+    const int32_t* cnt = C.count + 4 * D.t;
+    D.nf = min(cnt[0], C.cap_f); D.ne = min(cnt[1], C.cap_e); D.np = min(cnt[2], C.cap_p);
     return D;
 }
 
@@ -741,12 +816,29 @@ __device__ __forceinline__ void bary_rel(V3<float> q, V3<float> e1, V3<float> e2
 }
 
 // some master face of the list certainly faces n_s (N . n_s <= -0.1 |N|)
-__device__ __forceinline__ bool facing_cert(const SceneView& S, const double* xm, const int32_t* tris, int n,
-                                            V3<float> ns) {
-    for (int i = 0; i < n; ++i) {
-        const int32_t* M = S.mtri + 3 * (int64_t)tris[i];
+// master triangle m's edges y1 - y0, y2 - y0 rounded to FP32: read from
+// the per-pass table (PRE, see k_mtri_e32) or formed from xm -- the same values
+template <bool PRE>
+__device__ __forceinline__ void mtri_edges(const SceneView& S, const double* xm, const float* mtri_e, int64_t m,
+                                           V3<float>& e1, V3<float>& e2) {
+    if (PRE) {
+        const float* E = mtri_e + 8 * m;
+        e1 = {E[0], E[1], E[2]};
+        e2 = {E[3], E[4], E[5]};
+    } else {
+        const int32_t* M = S.mtri + 3 * m;
         const V3<double> y0 = ld3(xm, M[0]);
-        const V3<float> N = cross(tof(ld3(xm, M[1]) - y0), tof(ld3(xm, M[2]) - y0));
+        e1 = tof(ld3(xm, M[1]) - y0);
+        e2 = tof(ld3(xm, M[2]) - y0);
+    }
+}
+template <bool PRE = false>
+__device__ __forceinline__ bool facing_cert(const SceneView& S, const double* xm, const int32_t* tris, int n,
+                                            V3<float> ns, const float* mtri_e = nullptr) {
+    for (int i = 0; i < n; ++i) {
+        V3<float> e1, e2;
+        mtri_edges<PRE>(S, xm, mtri_e, tris[i], e1, e2);
+        const V3<float> N = cross(e1, e2);
         if (dot(N, ns) <= -0.1f * norm3f(N)) return true;
     }
     return false;
@@ -754,16 +846,24 @@ __device__ __forceinline__ bool facing_cert(const SceneView& S, const double* xm
 
 // face sample F of slave tri D against master tri m (Sec. 4.1, reading R1),
 // in the master triangle's frame
-template <int NK>
+template <int NK, bool PRE = false>
 __device__ __forceinline__ bool face_cert(const SceneView& S, const Params& P, const TriData& D,
                                           const FaceSample& F, const double* xm, int32_t m, bool want_dg,
-                                          ItemOut& o) {
+                                          ItemOut& o, const float* mtri_e = nullptr) {
     const double eps = P.dhat;
     const double* mb = S.mrest_box + 6 * (int64_t)m;
-    if (!rest_far(D.sb, D.sb + 3, mb, mb + 3, eps)) return false;
+    if (PRE) {
+        const float* mf = S.mrest_box_f + 6 * (int64_t)m;
+        if (!rest_far_f(D.sbf, D.sbf + 3, mf, mf + 3, P.far_r2_f) && !rest_far(D.sb, D.sb + 3, mb, mb + 3, eps))
+            return false;
+    } else if (!rest_far(D.sb, D.sb + 3, mb, mb + 3, eps)) {
+        return false;
+    }
     const int32_t* M = S.mtri + 3 * (int64_t)m;
     const V3<double> y0 = ld3(xm, M[0]);
-    const V3<float> e1 = tof(ld3(xm, M[1]) - y0), e2 = tof(ld3(xm, M[2]) - y0), d = tof(y0 - F.xs);
+    V3<float> e1, e2;
+    mtri_edges<PRE>(S, xm, mtri_e, m, e1, e2);
+    const V3<float> d = tof(y0 - F.xs);
     const V3<float> N = cross(e1, e2);
     const float nN = norm3f(N);
     const float cosn = -dot(N, D.ns_f) / nN;
@@ -790,7 +890,12 @@ __device__ __forceinline__ bool face_cert(const SceneView& S, const Params& P, c
 // the slave-side closing rate of a certified edge or point item: dg =
 // -n_s . sum_a b_a dx_a with b from FP32 geometry (error <= tol_b each),
 // widened toward closing by tol_b sum_a |n_s . dx_a|
+template <bool PRE = false>
 __device__ __forceinline__ double cert_dg(const TriData& D, const double* b, float tol_b) {
+    if (PRE) {   // n_s . dx_a and their magnitudes' sum from the frame kernel
+        const double ds = b[0] * D.sdx[0] + b[1] * D.sdx[1] + b[2] * D.sdx[2];
+        return -ds - (double)tol_b * D.sdx[3];
+    }
     const double s0 = dot(D.ns, D.dx0), s1 = dot(D.ns, D.dx1), s2 = dot(D.ns, D.dx2);
     const double ds = b[0] * s0 + b[1] * s1 + b[2] * s2;
     return -ds - (double)tol_b * (fabs(s0) + fabs(s1) + fabs(s2));
@@ -800,16 +905,28 @@ __device__ __forceinline__ double cert_dg(const TriData& D, const double* b, flo
 // reading R3).  Barycentric coordinates are affine along the projected
 // edge, so beta^s and the plane gap at a Gauss point are the ends' values
 // mixed by eta.
+template <bool PRE = false>
 __device__ __forceinline__ bool edge_cert(const SceneView& S, const Params& P, const TriData& D,
-                                          const double* xm, int32_t me, int q, bool want_dg, ItemOut& o) {
+                                          const double* xm, int32_t me, int q, bool want_dg, ItemOut& o,
+                                          const float* mtri_e = nullptr) {
     const double eps = P.dhat;
     const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
-    const V3<double> Ya = ld3(S.Y0, ia), Yb = ld3(S.Y0, ib);
-    const double elo[3] = {rmin(Ya.x, Yb.x), rmin(Ya.y, Yb.y), rmin(Ya.z, Yb.z)};
-    const double ehi[3] = {rmax(Ya.x, Yb.x), rmax(Ya.y, Yb.y), rmax(Ya.z, Yb.z)};
-    if (!rest_far(D.sb, D.sb + 3, elo, ehi, eps)) return false;
+    bool far = false;
+    if (PRE) {
+        const float* va = S.mvrest_box_f + 6 * (int64_t)ia;
+        const float* vb = S.mvrest_box_f + 6 * (int64_t)ib;
+        const float flo[3] = {fminf(va[0], vb[0]), fminf(va[1], vb[1]), fminf(va[2], vb[2])};
+        const float fhi[3] = {fmaxf(va[3], vb[3]), fmaxf(va[4], vb[4]), fmaxf(va[5], vb[5])};
+        far = rest_far_f(D.sbf, D.sbf + 3, flo, fhi, P.far_r2_f);
+    }
+    if (!far) {
+        const V3<double> Ya = ld3(S.Y0, ia), Yb = ld3(S.Y0, ib);
+        const double elo[3] = {rmin(Ya.x, Yb.x), rmin(Ya.y, Yb.y), rmin(Ya.z, Yb.z)};
+        const double ehi[3] = {rmax(Ya.x, Yb.x), rmax(Ya.y, Yb.y), rmax(Ya.z, Yb.z)};
+        if (!rest_far(D.sb, D.sb + 3, elo, ehi, eps)) return false;
+    }
     const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
-    if (!facing_cert(S, xm, S.me_tri + a0, a1 - a0, D.ns_f)) return false;
+    if (!facing_cert<PRE>(S, xm, S.me_tri + a0, a1 - a0, D.ns_f, mtri_e)) return false;
     const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
     const V3<float> da = tof(ya - D.x0), db = tof(yb - D.x0);
     float bA[3], bB[3], tA, tB;
@@ -853,19 +970,28 @@ __device__ __forceinline__ bool edge_cert(const SceneView& S, const Params& P, c
     for (int c = 0; c < 3; ++c) o.b[c] = (double)((1.0f - eta) * bA[c] + eta * bB[c]);
     o.mv[0] = ia; o.mv[1] = ib; o.mv[2] = -1;
     o.bm[0] = 1.0 - (double)eta; o.bm[1] = (double)eta; o.bm[2] = 0.0;
-    o.dg = want_dg ? cert_dg(D, o.b, tb) : 0.0;
+    o.dg = want_dg ? cert_dg<PRE>(D, o.b, tb) : 0.0;
     return true;
 }
 
 // master vertex u projected on slave tri D (Sec. 4.1, reading R3)
+template <bool PRE = false>
 __device__ __forceinline__ bool point_cert(const SceneView& S, const Params& P, const TriData& D,
-                                           const double* xm, int32_t u, bool want_dg, ItemOut& o) {
+                                           const double* xm, int32_t u, bool want_dg, ItemOut& o,
+                                           const float* mtri_e = nullptr) {
     const double eps = P.dhat;
-    const V3<double> Y = ld3(S.Y0, u);
-    const double yb[3] = {Y.x, Y.y, Y.z};
-    if (!rest_far(D.sb, D.sb + 3, yb, yb, eps)) return false;
+    bool far = false;
+    if (PRE) {
+        const float* vu = S.mvrest_box_f + 6 * (int64_t)u;
+        far = rest_far_f(D.sbf, D.sbf + 3, vu, vu + 3, P.far_r2_f);
+    }
+    if (!far) {
+        const V3<double> Y = ld3(S.Y0, u);
+        const double yb[3] = {Y.x, Y.y, Y.z};
+        if (!rest_far(D.sb, D.sb + 3, yb, yb, eps)) return false;
+    }
     const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
-    if (!facing_cert(S, xm, S.mv_tri + a0, a1 - a0, D.ns_f)) return false;
+    if (!facing_cert<PRE>(S, xm, S.mv_tri + a0, a1 - a0, D.ns_f, mtri_e)) return false;
     const V3<float> d = tof(ld3(xm, u) - D.x0);
     float bs[3], tb;
     bool ok;
@@ -880,7 +1006,7 @@ __device__ __forceinline__ bool point_cert(const SceneView& S, const Params& P, 
     for (int c = 0; c < 3; ++c) o.b[c] = (double)bs[c];
     o.mv[0] = u; o.mv[1] = -1; o.mv[2] = -1;
     o.bm[0] = 1.0; o.bm[1] = 0.0; o.bm[2] = 0.0;
-    o.dg = want_dg ? cert_dg(D, o.b, tb) : 0.0;
+    o.dg = want_dg ? cert_dg<PRE>(D, o.b, tb) : 0.0;
     return true;
 }
 
@@ -898,6 +1024,27 @@ __device__ __forceinline__ void item_value(const ItemOut& o, bool want_dg, doubl
     for (int cc = 0; cc < 3; ++cc) b[cc] = (T)o.b[cc];
     amin = INFINITY;
     if (want_dg && o.dg < 0.0) amin = 0.9 * o.g_step / (-o.dg);
+}
+// a certified item of the mixed path (eps = dhat, T = FP32): the barrier
+// from 1/dhat, and the step bound 0.9 g_step / (-dg) in FP32, lowered by
+// 1e-6 to stay below the FP64 quotient (three FP32 roundings are < 2e-7)
+template <class T>
+__device__ __forceinline__ void item_value_cert(const ItemOut& o, bool want_dg, double inv_dhat, double& e,
+                                                double& amin, T& c1, T& c2, T* b) {
+    if constexpr (sizeof(T) == 4) {
+        float Bv, dB, d2B;
+        barrier_inv(o.g, o.eps, inv_dhat, Bv, dB, d2B);
+        const float coef = (float)(o.kq * o.w * o.gamma);
+        e = (double)(coef * Bv);
+        c1 = coef * dB;
+        c2 = rmax(coef * d2B, 0.0f);
+        for (int cc = 0; cc < 3; ++cc) b[cc] = (float)o.b[cc];
+        amin = INFINITY;
+        if (want_dg && o.dg < 0.0)
+            amin = (double)(0.9f * (float)o.g_step / (float)(-o.dg)) * (1.0 - 1e-6);
+    } else {
+        item_value<T>(o, want_dg, e, amin, c1, c2, b);
+    }
 }
 
 // The paper's clipped-overlap face samples of slave tri D against master
@@ -1344,19 +1491,34 @@ k_items_pre(SceneView S, Params P, CandView C, const int32_t* __restrict__ items
 // are listed for phase 2 (faces from the front of the list, edges and points
 // from the back, so that phase 2 runs warps of one kind).  The FP64 path
 // lists every item.
+// master triangles' edges y1 - y0, y2 - y0 rounded to FP32, once per pass
+// (the certified tests read them per item)
+__global__ void k_mtri_e32(SceneView S, const double* __restrict__ xm, float* __restrict__ out) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= S.nmt) return;
+    const int32_t* M = S.mtri + 3 * m;
+    const V3<double> y0 = ld3(xm, M[0]);
+    const V3<float> e1 = tof(ld3(xm, M[1]) - y0), e2 = tof(ld3(xm, M[2]) - y0);
+    float* o = out + 8 * m;
+    o[0] = e1.x; o[1] = e1.y; o[2] = e1.z;
+    o[3] = e2.x; o[4] = e2.y; o[5] = e2.z;
+    o[6] = 0.0f; o[7] = 0.0f;
+}
+
 template <int NK, class T>
 __global__ void __launch_bounds__(256)
 k_items_mid(SceneView S, Params P, CandView C, const double* __restrict__ x, const double* __restrict__ xm,
             const double* __restrict__ dx, const double* __restrict__ frame, const int32_t* __restrict__ items,
             ItemBufs B, const int32_t* __restrict__ mid, const int32_t* __restrict__ n_mid,
             const int32_t* __restrict__ n_mid2, int32_t* __restrict__ list, int32_t* __restrict__ n_list,
-            int32_t* __restrict__ n_list2, long long* counters, bool cert) {
+            int32_t* __restrict__ n_list2, long long* counters, bool cert, const double* __restrict__ tmid64,
+            const float* __restrict__ tmid32, const float* __restrict__ mtri_e) {
     if ((int64_t)*B.n > B.cap) return;
     // faces (the front of the list) first, then edges and points (the back):
     // only the warp at the boundary holds both kinds
     const int nmf = *n_mid;
     const int nm = nmf + *n_mid2;
-    const bool pre = P.precision == IPC_PREC_MIXED;
+    const bool pre = P.precision == IPC_PREC_MIXED && tmid64 != nullptr;
     const bool want_dg = dx != nullptr;
     long long cnt_f = 0, cnt_e = 0, cnt_p = 0;
     const int stride = gridDim.x * blockDim.x;
@@ -1367,50 +1529,54 @@ k_items_mid(SceneView S, Params P, CandView C, const double* __restrict__ x, con
         int64_t s = 0;
         if (c < nm) {
             s = faces ? mid[c] : mid[B.cap - 1 - (c - nmf)];
-            const int i = B.owner[s];
-            const int q = (int)(s - items[2 * i]);
-            const TriData D = load_tri(S, C, x, cert ? dx : nullptr, frame, i);
-            const ItemRef R = item_ref<NK>(D, q);
             keep = true;
-            bool certified = false;
-            ItemOut o;
-            // the certified evaluation first (most items past the pre-filter
-            // are active), then the local reject tests for the rest
-            if (faces) {
-                if (pre) {
-                    const FaceSample F = face_sample(P, D, R.k, cert && want_dg);
+            if (pre) {
+                const int i = B.owner[s];
+                const int q = (int)(s - items[2 * i]);
+                const TriData D = load_tri_mid(S, C, x, frame, tmid64, tmid32, i);
+                const ItemRef R = item_ref<NK>(D, q);
+                bool certified = false;
+                ItemOut o;
+                // the certified evaluation first (most items past the pre-filter
+                // are active), then the local reject tests for the rest
+                if (faces) {
+                    FaceSample F;
+                    for (int a = 0; a < 3; ++a) F.beta[a] = c_rule[P.L - 1][R.k][a];
+                    F.xs = interp(F.beta, D.x0, D.x1, D.x2);
+                    // n_s . (the sample's displacement) from the vertices' products
+                    F.ds = cert && want_dg ? F.beta[0] * D.sdx[0] + F.beta[1] * D.sdx[1] + F.beta[2] * D.sdx[2]
+                                           : 0.0;
                     const int32_t m = C.face[D.t * C.cap_f + R.j];
-                    certified = cert && face_cert<NK>(S, P, D, F, xm, m, want_dg, o);
+                    certified = cert && face_cert<NK, true>(S, P, D, F, xm, m, want_dg, o, mtri_e);
                     if (!certified) {
+                        F.xs_rel = tof(F.xs - D.x0);
                         const int32_t* M = S.mtri + 3 * (int64_t)m;
                         keep = face_pre(P, D, F, ld3(xm, M[0]), ld3(xm, M[1]), ld3(xm, M[2]));
                     }
                     cnt_f += certified;
-                }
-            } else if (R.kind == 1) {
-                if (pre) {
+                } else if (R.kind == 1) {
                     const int32_t me = C.edge[D.t * C.cap_e + R.j];
-                    certified = cert && edge_cert(S, P, D, xm, me, R.k, want_dg, o);
+                    certified = cert && edge_cert<true>(S, P, D, xm, me, R.k, want_dg, o, mtri_e);
                     if (!certified)
                         keep = edge_pre(P, D, ld3(xm, S.medge[2 * (int64_t)me]), ld3(xm, S.medge[2 * (int64_t)me + 1]));
                     cnt_e += certified;
+                } else {
+                    const int32_t u = C.point[D.t * C.cap_p + R.j];
+                    certified = cert && point_cert<true>(S, P, D, xm, u, want_dg, o, mtri_e);
+                    if (!certified) keep = point_pre(P, D, ld3(xm, u));
+                    cnt_p += certified;
                 }
-            } else if (pre) {
-                const int32_t u = C.point[D.t * C.cap_p + R.j];
-                certified = cert && point_cert(S, P, D, xm, u, want_dg, o);
-                if (!certified) keep = point_pre(P, D, ld3(xm, u));
-                cnt_p += certified;
-            }
-            if (certified) {
-                // an active item evaluated from certified FP32 geometry
-                double e, amin;
-                T c1, c2, b[3];
-                item_value<T>(o, want_dg, e, amin, c1, c2, b);
-                item_store<T>(B, s, e, amin, c1, c2, b);
-                keep = false;
-            } else if (!keep) {
-                const T z[3] = {T(0), T(0), T(0)};
-                item_store<T>(B, s, 0.0, INFINITY, T(0), T(0), z);
+                if (certified) {
+                    // an active item evaluated from certified FP32 geometry
+                    double e, amin;
+                    T c1, c2, b[3];
+                    item_value_cert<T>(o, want_dg, P.inv_dhat, e, amin, c1, c2, b);
+                    item_store<T>(B, s, e, amin, c1, c2, b);
+                    keep = false;
+                } else if (!keep) {
+                    const T z[3] = {T(0), T(0), T(0)};
+                    item_store<T>(B, s, 0.0, INFINITY, T(0), T(0), z);
+                }
             }
         }
         const int at_f = warp_reserve_c(keep && face, n_list);
@@ -1701,20 +1867,33 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     if (f32pre) {
         GMCP_CUDA_TRY(c.tri_f32.ensure(64 * (size_t)c.ns + 64));
         GMCP_CUDA_TRY(c.ym32.ensure(4 * (size_t)c.nmv + 4));
-        k_master_f32<<<(unsigned)((c.nmv + 255) / 256), 256, 0, c.stream>>>(c.view(), xm, (float4*)c.ym32.p);
+        GMCP_CUDA_TRY(c.tri_mid64.ensure(4 * (size_t)c.ns + 8));
+        GMCP_CUDA_TRY(c.tri_mid32.ensure(12 * (size_t)c.ns + 12));
+        GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
+        // the master's FP32 tables depend on xm alone: beside the frame kernel
+        // on the side stream when the pass has forked one
+        cudaStream_t ms = c.side_master ? c.aux_stream : c.stream;
+        k_master_f32<<<(unsigned)((c.nmv + 255) / 256), 256, 0, ms>>>(c.view(), xm, (float4*)c.ym32.p);
         GMCP_CUDA_TRY(cudaGetLastError());
+        k_mtri_e32<<<(unsigned)((c.nmt + 255) / 256), 256, 0, ms>>>(c.view(), xm, c.mtri_e32.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+        if (c.side_master) GMCP_CUDA_TRY(cudaEventRecord(c.ev_master, c.aux_stream));
     }
+    // certified FP32 items: mixed path, evaluation, static master (the
+    // middle stage then reads dx's products with the normals from the frame
+    // kernel's table)
+    const bool cert = !kMaster && c.P.precision == IPC_PREC_MIXED && dxm == nullptr;
     k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, c.tri_items.p, n_items,
                                                kMaster ? nullptr : c.tri_stamp.p, c.misc_i32.p,
-                                               f32pre ? c.tri_f32.p : nullptr, c.P.L);
+                                               f32pre ? c.tri_f32.p : nullptr, c.P.L, cert ? dx : nullptr,
+                                               f32pre ? c.tri_mid64.p : nullptr, f32pre ? c.tri_mid32.p : nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items, c.item_mask.p};
     k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
     GMCP_CUDA_TRY(cudaGetLastError());
+    if (f32pre && c.side_master) GMCP_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.ev_master, 0));
     int32_t* n_list = c.misc_i32.p + kSlotItemList;
     int32_t* n_list2 = c.misc_i32.p + kSlotItemList2;
-    // certified FP32 items: mixed path, evaluation, static master
-    const bool cert = !kMaster && c.P.precision == IPC_PREC_MIXED && dxm == nullptr;
     int32_t* n_mid = c.misc_i32.p + kSlotItemMid;
     int32_t* n_mid2 = c.misc_i32.p + kSlotItemMid2;
     k_items_pre<NK><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), c.tri_items.p, B, c.item_mid.p, n_mid,
@@ -1723,7 +1902,10 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     GMCP_CUDA_TRY(cudaGetLastError());
     k_items_mid<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
                                                       c.tri_items.p, B, c.item_mid.p, n_mid, n_mid2, c.item_list.p,
-                                                      n_list, n_list2, counters, cert);
+                                                      n_list, n_list2, counters, cert,
+                                                      f32pre ? c.tri_mid64.p : nullptr,
+                                                      f32pre ? c.tri_mid32.p : nullptr,
+                                                      f32pre ? c.mtri_e32.p : nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (kMaster) {
         k_items<NK, T, MODE><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
@@ -1815,6 +1997,10 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
         GMCP_CUDA_TRY(cudaGetLastError());
         if (fork) GMCP_CUDA_TRY(cudaEventRecord(c.ev_touch1, c.aux_stream));
     }
+    // the sample stage may put the master's FP32 tables on the side stream
+    if (fork && !c.ev_master) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_master, cudaEventDisableTiming));
+    struct SideFlag { bool& f; SideFlag(bool& r, bool v) : f(r) { f = v; } ~SideFlag() { f = false; } };
+    SideFlag side_flag(c.side_master, fork);
     {
         ProfScope ps(c.prof, c.stream, "samples");
         if (f32) {

@@ -79,6 +79,12 @@ struct SceneView {
     const double* Y0;             // master at t = 0 [nmv][3]
     const double* srest_box;      // [ns][6] rest box of slave tris (lo xyz, hi xyz)
     const double* mrest_box;      // [nmt][6] rest box of master tris
+    // the same boxes in FP32 rounded outward (lo down, hi up), and each
+    // master vertex's rest position as such a box: certain lower bounds of
+    // rest distances
+    const float* srest_box_f;     // [ns][6]
+    const float* mrest_box_f;     // [nmt][6]
+    const float* mvrest_box_f;    // [nmv][6]
     // broad-phase grid, one dense box of cells per environment
     const double* grid_org;       // [n_env][3]
     const double* grid_inv;       // [n_env] 1 / cell size
@@ -97,6 +103,9 @@ struct Params {
     double ccd_slack;
     int ccd_max_iter;
     int face_clip;         // 1: the paper's clipped-overlap face samples (ipc_params.face_sampler)
+    double inv_dhat;       // 1 / dhat
+    float far_r2_f;        // (dhat 1.2/0.9)^2 rounded up to FP32 and raised by 1e-6: rest boxes whose
+                           // certain FP32 distance bound reaches it are rest-far in FP64 too
 };
 
 // Candidate list storage: fixed capacity per slave triangle.
@@ -383,6 +392,12 @@ struct Ctx {
     DBuf<int32_t> mtri_own_edge, mtri_own_vert, stri_own_vert, stri_own_edge, sedge;
     DBuf<int32_t> stri_env, mtri_env, mvert_env;
     DBuf<double> X, Y0, srest_box, mrest_box;
+    DBuf<float> srest_box_f, mrest_box_f, mvrest_box_f;
+    // mixed path, per pass: the middle sample stage's inputs computed once per
+    // triangle or sample instead of once per item (see k_tri_frame, k_mtri_e32)
+    DBuf<double> tri_mid64;                     // [n_active][4]: ns . dx_a (3) and the sum of their magnitudes
+    DBuf<float> tri_mid32;                      // [n_active][12]: unit normal, x1 - x0, x2 - x0 in FP32
+    DBuf<float> mtri_e32;                       // [nmt][8]: y1 - y0, y2 - y0 of each master tri in FP32
     DBuf<double> grid_org, grid_inv;
     DBuf<float> grid_org_f, grid_inv_f;
     DBuf<int32_t> grid_dim;
@@ -412,6 +427,8 @@ struct Ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t aux_stream = nullptr;          // touched-output lists beside the sample evaluation
     cudaEvent_t ev_touch0 = nullptr, ev_touch1 = nullptr, ev_samples = nullptr;
+    cudaEvent_t ev_master = nullptr;   // the master's FP32 tables done on the side stream
+    bool side_master = false;          // set while a contact pass has forked the side stream
     DBuf<int32_t> cell_cnt, cell_start, cell_ent;
     DBuf<int32_t> scan_tmp;
     DBuf<int32_t> cand_face, cand_edge, cand_point, cand_count, active, misc_i32;
