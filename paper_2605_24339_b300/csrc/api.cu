@@ -198,6 +198,19 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
                                       cudaMemcpyHostToDevice, c.stream));
         GMCP_CUDA_TRY(cudaMemsetAsync(c.i64_tmp.p + 8, 0, 4 * sizeof(long long), c.stream));
     }
+    // mixed path: the master's FP32 tables depend on xm0 alone, so they are
+    // built on the side stream beside the broad phase
+    struct PreFlag { bool& f; ~PreFlag() { f = false; } } pre_flag{c.master_pre};
+    if (c.P.precision == IPC_PREC_MIXED && c.nmv > 0 && !c.prof.on && !c.P.face_clip) {
+        if (!c.aux_stream) GMCP_CUDA_TRY(cudaStreamCreateWithFlags(&c.aux_stream, cudaStreamNonBlocking));
+        if (!c.ev_mfork) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_mfork, cudaEventDisableTiming));
+        if (!c.ev_master) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_master, cudaEventDisableTiming));
+        GMCP_CUDA_TRY(cudaEventRecord(c.ev_mfork, c.stream));
+        GMCP_CUDA_TRY(cudaStreamWaitEvent(c.aux_stream, c.ev_mfork, 0));
+        GMCP_CUDA_TRY(master_tables(c, A.xm0, c.aux_stream));
+        GMCP_CUDA_TRY(cudaEventRecord(c.ev_master, c.aux_stream));
+        c.master_pre = true;
+    }
     GMCP_CUDA_TRY(run_candidates(c, A.x, A.xm0, A.lazy));
     // With a static master the swept query reads the same grid and nothing
     // else of the contact evaluation: it runs on a second stream, forked
@@ -308,7 +321,8 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.cb_val64.p, (uintptr_t)c.u64_tmp.p, (uintptr_t)c.i64_tmp.p, (uintptr_t)c.misc_i32.p,
             (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p, (uintptr_t)c.mboxf_in.p, (uintptr_t)c.tri_f32.p,
             (uintptr_t)c.ym32.p, (uintptr_t)c.item_mask.p, (uintptr_t)c.item_mid.p, (uintptr_t)c.tri_mid64.p,
-            (uintptr_t)c.tri_mid32.p, (uintptr_t)c.mtri_e32.p};
+            (uintptr_t)c.tri_mid32.p, (uintptr_t)c.mtri_e32.p, (uintptr_t)c.mtri_pre.p,
+            (uintptr_t)c.use_mtri_pre};
 }
 
 // Capture one pass on the context's private capture stream (nothing runs);
@@ -1150,6 +1164,7 @@ void ipc_destroy(ipc_ctx* ctx) {
     if (c.ev_touch0) cudaEventDestroy(c.ev_touch0);
     if (c.ev_touch1) cudaEventDestroy(c.ev_touch1);
     if (c.ev_master) cudaEventDestroy(c.ev_master);
+    if (c.ev_mfork) cudaEventDestroy(c.ev_mfork);
     if (c.ev_samples) cudaEventDestroy(c.ev_samples);
     if (c.ev_fork) cudaEventDestroy(c.ev_fork);
     if (c.ev_join) cudaEventDestroy(c.ev_join);
@@ -1373,6 +1388,8 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
         } else if (c.pin->flags[16] > c.cap_items) {
             API_CK(ctx, grow_items(c));
         }
+        // the next passes' choice of the face pre-filter's master table
+        c.use_mtri_pre = c.P.precision == IPC_PREC_MIXED && (int64_t)c.pin->flags[16] >= 8 * c.nmt;
     }
     if (energy_host) *energy_host = c.pin->energy;
     if (counts) {

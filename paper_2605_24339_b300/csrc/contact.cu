@@ -1307,6 +1307,36 @@ __global__ void k_master_f32(SceneView S, const double* __restrict__ xm, float4*
                           (float)(xm[3 * u + 2] - S.grid_org[3 * e + 2]), 0.0f);
 }
 
+// What the FP32 face pre-filter needs of a master triangle, once per pass
+// from the FP32 master vertices (the same operations face_reject_f32 would
+// run per item): [24 m ...] = y0 (3), e1 = y1 - y0 (3), e2 = y2 - y0 (3),
+// N = e1 x e2 (3), |N|, |e1|, |e2|, |e2 - e1|, max |coordinate| of the
+// three vertices, e1.e1, e1.e2, e2.e2, their Gram determinant, 3 unused.
+constexpr int kMtriPre = 24;
+__global__ void k_mtri_pre(SceneView S, const float4* __restrict__ ym32, float* __restrict__ out) {
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= S.nmt) return;
+    const int32_t* M = S.mtri + 3 * m;
+    const float4 A = ym32[M[0]], B4 = ym32[M[1]], C4 = ym32[M[2]];
+    const V3<float> y0 = {A.x, A.y, A.z}, y1 = {B4.x, B4.y, B4.z}, y2 = {C4.x, C4.y, C4.z};
+    const V3<float> e1 = y1 - y0, e2 = y2 - y0, N = cross(e1, e2);
+    float* o = out + kMtriPre * m;
+    o[0] = y0.x; o[1] = y0.y; o[2] = y0.z;
+    o[3] = e1.x; o[4] = e1.y; o[5] = e1.z;
+    o[6] = e2.x; o[7] = e2.y; o[8] = e2.z;
+    o[9] = N.x; o[10] = N.y; o[11] = N.z;
+    o[12] = sqrtf(dot(N, N));
+    o[13] = sqrtf(dot(e1, e1));
+    o[14] = sqrtf(dot(e2, e2));
+    o[15] = sqrtf(dot(e2 - e1, e2 - e1));
+    o[16] = rmax(rmax(fabsf(y0.x), rmax(fabsf(y0.y), fabsf(y0.z))),
+                 rmax(rmax(fabsf(y1.x), rmax(fabsf(y1.y), fabsf(y1.z))), rmax(fabsf(y2.x), rmax(fabsf(y2.y), fabsf(y2.z)))));
+    const float a = dot(e1, e1), bb = dot(e1, e2), c = dot(e2, e2);
+    o[17] = a; o[18] = bb; o[19] = c;
+    o[20] = a * c - bb * bb;
+    o[21] = 0.0f; o[22] = 0.0f; o[23] = 0.0f;
+}
+
 // FP32 pre-filter of a face item in its environment's frame (coordinates
 // relative to the grid origin: master vertices rounded once from FP64, the
 // sample interpolated in FP32 from rounded slave vertices): true only when
@@ -1350,6 +1380,36 @@ __device__ __forceinline__ bool face_reject_f32(V3<float> xs, V3<float> ns, V3<f
     const float det = a * c - bb * bb;
     const float v = (c * r1 - bb * r2) / det, w = (a * r2 - bb * r1) / det;
     const float l3 = sqrtf(dot(e2 - e1, e2 - e1));
+    const float hmin = nN / rmax(l1, rmax(l2, l3));
+    const float tol_b = 0.02f + 4.0f * (tol_g + 4.0f * del) / hmin;
+    return rmin(1.0f - v - w, rmin(v, w)) < -tol_b;
+}
+
+// the same test with the master triangle's part read from its k_mtri_pre
+// record: the same operations on the same values, so the same decisions
+__device__ __forceinline__ bool face_reject_f32_rec(V3<float> xs, V3<float> ns, const float* rec, float eps_max) {
+    const float4* r4 = reinterpret_cast<const float4*>(rec);
+    const float4 q0 = r4[0], q1 = r4[1], q2 = r4[2], q3 = r4[3], q4 = r4[4], q5 = r4[5];
+    const V3<float> y0 = {q0.x, q0.y, q0.z}, e1 = {q0.w, q1.x, q1.y}, e2 = {q1.z, q1.w, q2.x};
+    const V3<float> N = {q2.y, q2.z, q2.w};
+    const float nN = q3.x, l1 = q3.y, l2 = q3.z, l3 = q3.w, Rm = q4.x;
+    const float a = q4.y, bb = q4.z, c = q4.w, det = q5.x;
+    const float R = rmax(rmax(fabsf(xs.x), rmax(fabsf(xs.y), fabsf(xs.z))), Rm);
+    const float del = 4.7683716e-7f * R;   // 2^-21 R
+    const float rel_N = 8.0f * del * (l1 + l2) / nN + 1e-5f;
+    const float den = dot(N, ns);
+    if (!(nN > 0.0f)) return false;
+    if (den >= (rel_N + 1e-3f) * nN) return true;           // faces away
+    if (den > -(rel_N + 0.05f) * nN) return false;           // near grazing: later tests decide
+    const float cosn = -den / nN;
+    const V3<float> d = y0 - xs;
+    const float g = dot(N, d) / den;
+    const float dn = sqrtf(dot(d, d));
+    const float tol_g = (2.0f * rel_N * (dn + fabsf(g)) + 8.0f * del) / cosn + 1e-4f * (dn + fabsf(g));
+    if (g > eps_max * (1.0f + 1e-6f) + tol_g || g < -tol_g) return true;
+    const V3<float> q = g * ns - d;    // hit point relative to y0
+    const float r1 = dot(q, e1), r2 = dot(q, e2);
+    const float v = (c * r1 - bb * r2) / det, w = (a * r2 - bb * r1) / det;
     const float hmin = nN / rmax(l1, rmax(l2, l3));
     const float tol_b = 0.02f + 4.0f * (tol_g + 4.0f * del) / hmin;
     return rmin(1.0f - v - w, rmin(v, w)) < -tol_b;
@@ -1428,7 +1488,8 @@ template <int NK>
 __global__ void __launch_bounds__(256)
 k_items_pre(SceneView S, Params P, CandView C, const int32_t* __restrict__ items, ItemBufs B,
             int32_t* __restrict__ mid, int32_t* __restrict__ n_mid, int32_t* __restrict__ n_mid2,
-            long long* counters, const float* __restrict__ tf32, const float4* __restrict__ ym32) {
+            long long* counters, const float* __restrict__ tf32, const float4* __restrict__ ym32,
+            const float* __restrict__ mtri_pre) {
     const int64_t n = *B.n;
     if (n > B.cap) return;
     long long cnt_eval = 0;
@@ -1449,10 +1510,16 @@ k_items_pre(SceneView S, Params P, CandView C, const int32_t* __restrict__ items
                 face = true;
                 if (tf) {
                     const int k = q % NK;
-                    const int32_t* M = S.mtri + 3 * (int64_t)C.face[t * C.cap_f + q / NK];
-                    const float4 a = ym32[M[0]], b = ym32[M[1]], c = ym32[M[2]];
-                    pass = !face_reject_f32({tf[3 * k], tf[3 * k + 1], tf[3 * k + 2]}, {tf[48], tf[49], tf[50]},
-                                            {a.x, a.y, a.z}, {b.x, b.y, b.z}, {c.x, c.y, c.z}, (float)P.dhat);
+                    const int64_t m = C.face[t * C.cap_f + q / NK];
+                    if (mtri_pre) {
+                        pass = !face_reject_f32_rec({tf[3 * k], tf[3 * k + 1], tf[3 * k + 2]},
+                                                    {tf[48], tf[49], tf[50]}, mtri_pre + kMtriPre * m, (float)P.dhat);
+                    } else {
+                        const int32_t* M = S.mtri + 3 * m;
+                        const float4 a = ym32[M[0]], b = ym32[M[1]], c = ym32[M[2]];
+                        pass = !face_reject_f32({tf[3 * k], tf[3 * k + 1], tf[3 * k + 2]}, {tf[48], tf[49], tf[50]},
+                                                {a.x, a.y, a.z}, {b.x, b.y, b.z}, {c.x, c.y, c.z}, (float)P.dhat);
+                    }
                 }
             } else if (tf) {
                 // an edge (either Gauss point) or a master vertex
@@ -1806,6 +1873,30 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t n, doubl
     }
 }
 
+}  // namespace
+
+// the master's FP32 tables of the mixed path (vertices in the environment's
+// frame, triangle edges, the face pre-filter's per-triangle part), from xm,
+// on stream s
+cudaError_t master_tables(Ctx& c, const double* xm, cudaStream_t s) {
+    GMCP_CUDA_TRY(c.ym32.ensure(4 * (size_t)c.nmv + 4));
+    GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
+    GMCP_CUDA_TRY(c.mtri_pre.ensure((size_t)kMtriPre * c.nmt + kMtriPre));
+    if (c.nmv == 0) return cudaSuccess;
+    k_master_f32<<<(unsigned)((c.nmv + 255) / 256), 256, 0, s>>>(c.view(), xm, (float4*)c.ym32.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    if (c.nmt == 0) return cudaSuccess;
+    k_mtri_e32<<<(unsigned)((c.nmt + 255) / 256), 256, 0, s>>>(c.view(), xm, c.mtri_e32.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    // the face pre-filter's per-triangle table pays only when most master
+    // triangles take many face items (see Ctx::use_mtri_pre)
+    if (!c.use_mtri_pre) return cudaSuccess;
+    k_mtri_pre<<<(unsigned)((c.nmt + 255) / 256), 256, 0, s>>>(c.view(), (const float4*)c.ym32.p, c.mtri_pre.p);
+    return cudaGetLastError();
+}
+
+namespace {
+
 template <int NK, class T, int MODE>
 cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* Sm, T* N,
                            long long* counters, const double* dx, const double* dxm,
@@ -1870,14 +1961,15 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
         GMCP_CUDA_TRY(c.tri_mid64.ensure(4 * (size_t)c.ns + 8));
         GMCP_CUDA_TRY(c.tri_mid32.ensure(12 * (size_t)c.ns + 12));
         GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
-        // the master's FP32 tables depend on xm alone: beside the frame kernel
-        // on the side stream when the pass has forked one
-        cudaStream_t ms = c.side_master ? c.aux_stream : c.stream;
-        k_master_f32<<<(unsigned)((c.nmv + 255) / 256), 256, 0, ms>>>(c.view(), xm, (float4*)c.ym32.p);
-        GMCP_CUDA_TRY(cudaGetLastError());
-        k_mtri_e32<<<(unsigned)((c.nmt + 255) / 256), 256, 0, ms>>>(c.view(), xm, c.mtri_e32.p);
-        GMCP_CUDA_TRY(cudaGetLastError());
-        if (c.side_master) GMCP_CUDA_TRY(cudaEventRecord(c.ev_master, c.aux_stream));
+        GMCP_CUDA_TRY(c.mtri_pre.ensure((size_t)kMtriPre * c.nmt + kMtriPre));
+        // the master's FP32 tables depend on xm alone: already enqueued at
+        // the start of a contact pass (c.master_pre), else beside the frame
+        // kernel on the side stream when the pass has forked one
+        if (!c.master_pre) {
+            cudaStream_t ms = c.side_master ? c.aux_stream : c.stream;
+            GMCP_CUDA_TRY(master_tables(c, xm, ms));
+            if (c.side_master) GMCP_CUDA_TRY(cudaEventRecord(c.ev_master, c.aux_stream));
+        }
     }
     // certified FP32 items: mixed path, evaluation, static master (the
     // middle stage then reads dx's products with the normals from the frame
@@ -1891,14 +1983,15 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items, c.item_mask.p};
     k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
     GMCP_CUDA_TRY(cudaGetLastError());
-    if (f32pre && c.side_master) GMCP_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.ev_master, 0));
+    if (f32pre && (c.side_master || c.master_pre)) GMCP_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.ev_master, 0));
     int32_t* n_list = c.misc_i32.p + kSlotItemList;
     int32_t* n_list2 = c.misc_i32.p + kSlotItemList2;
     int32_t* n_mid = c.misc_i32.p + kSlotItemMid;
     int32_t* n_mid2 = c.misc_i32.p + kSlotItemMid2;
     k_items_pre<NK><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), c.tri_items.p, B, c.item_mid.p, n_mid,
                                                     n_mid2, counters, f32pre ? c.tri_f32.p : nullptr,
-                                                    f32pre ? (const float4*)c.ym32.p : nullptr);
+                                                    f32pre ? (const float4*)c.ym32.p : nullptr,
+                                                    f32pre && c.use_mtri_pre ? c.mtri_pre.p : nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     k_items_mid<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
                                                       c.tri_items.p, B, c.item_mid.p, n_mid, n_mid2, c.item_list.p,

@@ -398,6 +398,7 @@ struct Ctx {
     DBuf<double> tri_mid64;                     // [n_active][4]: ns . dx_a (3) and the sum of their magnitudes
     DBuf<float> tri_mid32;                      // [n_active][12]: unit normal, x1 - x0, x2 - x0 in FP32
     DBuf<float> mtri_e32;                       // [nmt][8]: y1 - y0, y2 - y0 of each master tri in FP32
+    DBuf<float> mtri_pre;                       // [nmt][24]: each master tri's part of the FP32 face pre-filter
     DBuf<double> grid_org, grid_inv;
     DBuf<float> grid_org_f, grid_inv_f;
     DBuf<int32_t> grid_dim;
@@ -428,7 +429,14 @@ struct Ctx {
     cudaStream_t aux_stream = nullptr;          // touched-output lists beside the sample evaluation
     cudaEvent_t ev_touch0 = nullptr, ev_touch1 = nullptr, ev_samples = nullptr;
     cudaEvent_t ev_master = nullptr;   // the master's FP32 tables done on the side stream
+    cudaEvent_t ev_mfork = nullptr;    // a contact pass's start, for that side stream
     bool side_master = false;          // set while a contact pass has forked the side stream
+    bool master_pre = false;           // the tables of this pass are already enqueued (ev_master)
+    // the face pre-filter reads a per-master-triangle table (built each pass
+    // over every master triangle) instead of forming each triangle's part
+    // per item; set after a contact pass whose sample items outnumbered the
+    // master triangles eightfold (results are the same either way)
+    bool use_mtri_pre = false;
     DBuf<int32_t> cell_cnt, cell_start, cell_ent;
     DBuf<int32_t> scan_tmp;
     DBuf<int32_t> cand_face, cand_edge, cand_point, cand_count, active, misc_i32;
@@ -521,6 +529,8 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
 cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double* xm0,
                         const double* dxm, unsigned long long* alpha_bits, long long* counters,
                         bool reuse_grid = false, bool lazy = false, int alpha_stride = 0);
+// the master's FP32 tables of the mixed path from xm on stream s (contact.cu)
+cudaError_t master_tables(Ctx& c, const double* xm, cudaStream_t s);
 // scan.cu
 cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp,
                                size_t tmp_n, cudaStream_t s);
