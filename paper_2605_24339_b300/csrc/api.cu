@@ -564,7 +564,10 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
     GMCP_CUDA_TRY(start_point(c, x, N.xhat.p, N.tmp.p, run, a0, ok));
     for (int e = 0; e < ne; ++e)
         if (run[e] && !ok[e]) { status[e] = 3; run[e] = 0; }
-    GMCP_CUDA_TRY(assemble_system(c, N.tmp.p, false));
+    // without a prediction the iteration starts at this point: its system,
+    // with the matrix, serves the first iteration too
+    const bool reuse = dx_pred == nullptr;
+    GMCP_CUDA_TRY(assemble_system(c, N.tmp.p, reuse));
     GMCP_CUDA_TRY(read_es(c, kEsG2, 1));
     for (int e = 0; e < ne; ++e) gscale[e] = std::sqrt(N.h_es[kES * e + kEsG2]);
     // a predicted start goes through the same CCD-filtered start point and is
@@ -599,7 +602,7 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
     std::vector<double> al_acc(ne, 0.0);
     const double c0 = 1e-4;
     for (int it = 0; any(run); ++it) {
-        GMCP_CUDA_TRY(assemble_system(c, x, true));
+        if (!(it == 0 && reuse)) GMCP_CUDA_TRY(assemble_system(c, x, true));
         GMCP_CUDA_TRY(cudaMemcpyAsync(N.h_ebad, N.ebad.p, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, s));
         GMCP_CUDA_TRY(read_es(c, kEsEc, 4));
         for (int e = 0; e < ne; ++e) {
