@@ -439,7 +439,8 @@ const int32_t* put_mask(Ctx& c, int k, const std::vector<uint8_t>& m, bool inver
 }
 
 // per environment with need[e]: the first j in [0, max_halv] with a finite
-// elastic energy at xi + (a_e 2^-j) dP (batches of 8); j_out[e] = -1 if none
+// elastic energy at xi + (a_e 2^-j) dP (j = 0 first, then batches of 8);
+// j_out[e] = -1 if none
 cudaError_t first_feasible(Ctx& c, const double* xi, const double* dP, const std::vector<double>& a,
                            int max_halv, const std::vector<uint8_t>& need, std::vector<int>& j_out,
                            std::vector<double>& a_out) {
@@ -448,11 +449,13 @@ cudaError_t first_feasible(Ctx& c, const double* xi, const double* dP, const std
     std::vector<uint8_t> pending(need);
     j_out.assign(ne, -1);
     a_out.assign(ne, 0.0);
-    for (int base = 0; base <= max_halv; base += 8) {
+    // the first batch tries the step size itself (it is usually feasible),
+    // later batches eight halvings at once
+    for (int base = 0, na = 1; base <= max_halv; base += na) {
         bool any = false;
         for (int e = 0; e < ne; ++e) any = any || pending[e];
         if (!any) break;
-        const int na = std::min(8, max_halv - base + 1);
+        na = base == 0 ? 1 : std::min(8, max_halv - base + 1);
         for (int e = 0; e < ne; ++e)
             for (int j = 0; j < na; ++j) N.h_eal[8 * e + j] = std::ldexp(a[e], -(base + j));
         GMCP_CUDA_TRY(cudaMemcpyAsync(N.eal.p, N.h_eal, sizeof(double) * 8 * ne, cudaMemcpyHostToDevice, c.stream));
@@ -561,7 +564,10 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
     // residual scale from the CCD-filtered plain predictor (reading R8)
     std::vector<double> a0, gscale(ne, 0.0);
     std::vector<uint8_t> ok;
-    GMCP_CUDA_TRY(start_point(c, x, N.xhat.p, N.tmp.p, run, a0, ok));
+    {
+        ProfScope ps(c.prof, s, "start_point");
+        GMCP_CUDA_TRY(start_point(c, x, N.xhat.p, N.tmp.p, run, a0, ok));
+    }
     for (int e = 0; e < ne; ++e)
         if (run[e] && !ok[e]) { status[e] = 3; run[e] = 0; }
     // without a prediction the iteration starts at this point: its system,
