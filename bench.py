@@ -581,7 +581,7 @@ def master_grad_measurement(dev, reps=50):
             "ms_per_call": round(ms, 4), "master_rows": rows, "balance_rel": bal,
             "hess_ms_per_call": round(statistics.median(hts) * 1e3, 4), "hess_blocks": int(n.value),
             "l2": "flushed (256 MB write) between calls",
-            "note": "broad phase + item-parallel FP64 sample kernels (k_items_pre, k_items) with FP64 atomics"}
+            "note": "broad phase + item-parallel FP64 sample kernels (k_items_pre, k_items); the rows' entries sorted by master vertex and summed in a fixed order (two host synchronisations)"}
 
 
 def dual_mesh_measurement(dev, n_points=2_000_000, reps=50):

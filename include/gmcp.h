@@ -217,9 +217,9 @@ ipc_status ipc_barrier_eval(ipc_ctx* ctx, const double* x_dev, const double* xm_
  * of its slave rows (equal and opposite forces, zero net torque).
  *  x_dev [n_vert][3], xm_dev [n_mvert][3] (device, FP64): the state;
  *  grad_m_dev [n_mvert][3] (device, FP64, caller-owned): overwritten.
- * Samples are evaluated in FP64 in both precision modes; the rows are summed
- * with FP64 atomics, so repeated calls agree to rounding, not bitwise.
- * Asynchronous on params.stream. */
+ * Samples are evaluated in FP64 in both precision modes; each row is summed
+ * in a fixed order (the sample entries sorted by master vertex, then by
+ * value), so repeated calls agree bitwise.  Synchronises params.stream. */
 ipc_status ipc_master_grad(ipc_ctx* ctx, const double* x_dev, const double* xm_dev, double* grad_m_dev);
 
 /* Hessian blocks of the contact potential that involve master vertices

@@ -1286,7 +1286,11 @@ ipc_status ipc_master_grad(ipc_ctx* ctx, const double* x_dev, const double* xm_d
     if (c.nmv == 0) return IPC_OK;
     API_CK(ctx, cudaSetDevice(c.device));
     API_CK(ctx, run_candidates(c, x_dev, xm_dev));
-    API_CK(ctx, contact_master_grad(c, x_dev, xm_dev, grad_m_dev));
+    // the rows summed in a fixed order (entries sorted by master vertex, then
+    // by value), so repeated calls agree bitwise
+    API_CK(ctx, cudaMemsetAsync(grad_m_dev, 0, sizeof(double) * 3 * (size_t)c.nmv, c.stream));
+    API_CK(ctx, sorted_master_terms(c, x_dev, xm_dev, c.nv + c.nmv, c.nv, grad_m_dev, false, nullptr, nullptr,
+                                    nullptr, nullptr, nullptr));
     return IPC_OK;
 }
 

@@ -40,19 +40,18 @@ namespace {
 constexpr int MODE_EVAL = 0;
 constexpr int MODE_ALPHA = 1;
 constexpr int MODE_LAGGED = 2;
-constexpr int MODE_MASTER = 3;   // gradient rows of the master vertices
-constexpr int MODE_MASTER_HESS = 4;   // slave-master and master-master Hessian blocks
+constexpr int MODE_MASTER_HESS = 4;   // the master vertices' entries: gradient rows and Hessian blocks
 
 // outputs of the modes beyond the evaluation.  MODE_LAGGED: the frozen-
-// linear energies, per active sample kappa w gamma B(g + a_j dg) for up to 8
-// step sizes a_j along the direction dx.  MODE_MASTER / MODE_MASTER_HESS:
-// the master rows and blocks.
+// linear energy changes, per active sample kappa w gamma [B(g + a_j dg) -
+// B(g)] for up to 8 step sizes a_j along the direction dx.  MODE_MASTER_HESS:
+// the master vertices' entries (gradient rows and Hessian blocks), appended
+// to a list that the caller sorts and sums in a fixed order.
 struct ModeArgs {
     const double* alphas = nullptr;
     int na = 0;
     double* triE8 = nullptr;   // [8][ns]
     int64_t ns = 0;
-    double* grad_m = nullptr;  // MODE_MASTER: [nmv][3], accumulated
     // MODE_MASTER_HESS: blocks (row, col) with value coef n n^T, appended at
     // *h_count (entries past h_cap are counted, not written)
     int32_t* h_ij = nullptr;   // [h_cap][2]
@@ -63,6 +62,7 @@ struct ModeArgs {
     // with h_rows: the gradient rows of the master vertices are appended to
     // the same list as entries (row, -1) whose first three values are the row
     bool h_rows = false;
+    bool h_blocks = true;      // with false: the rows alone
     // MODE_ALPHA: the bound of a sample on slave triangle t goes to
     // alpha_bits[alpha_stride * env(t)] (0: one bound for the whole scene)
     int alpha_stride = 0;
@@ -1102,21 +1102,6 @@ __device__ void put_block(const ModeArgs& LG, int32_t r, int32_t c, double coef,
         for (int q = 0; q < 3; ++q) b[3 * p + q] = coef * nn[p] * nn[q];
 }
 
-// g = n_s . (x_m - x_s) with x_m = sum_j bm_j y_j: the row of master vertex
-// y_j is kappa w gamma B'(g) bm_j n_s, the counterpart of the slave rows
-// -kappa w gamma B'(g) beta_i n_s
-__device__ void master_rows(const ModeArgs& LG, const ItemOut& o, const V3<double>& ns) {
-    double Bv, dB, d2B;
-    barrier(o.g, o.eps, Bv, dB, d2B);
-    const double c1 = o.kq * o.w * o.gamma * dB;
-    for (int j = 0; j < 3; ++j) {
-        if (o.mv[j] < 0) continue;
-        double* gm = LG.grad_m + 3 * (int64_t)o.mv[j];
-        const double f = c1 * o.bm[j];
-        atomicAdd(gm, f * ns.x); atomicAdd(gm + 1, f * ns.y); atomicAdd(gm + 2, f * ns.z);
-    }
-}
-
 // the sample's gap gradient is (-beta_a n_s) on its slave vertices Ts[a] and
 // (bm_j n_s) on its master vertices; its Gauss-Newton block between two of
 // them is max(kappa w gamma B''(g), 0) w_u w_v n_s n_s^T
@@ -1138,6 +1123,7 @@ __device__ void master_blocks(const ModeArgs& LG, const ItemOut& o, const int32_
                 for (int q = 3; q < 9; ++q) b[q] = 0.0;
             }
         }
+        if (!LG.h_blocks) continue;
         for (int a = 0; a < 3; ++a) put_block(LG, Ts[a], cj, -c2 * o.b[a] * o.bm[j], ns);
         for (int i = 0; i < 3; ++i)
             if (o.mv[i] >= 0) put_block(LG, LG.m_off + o.mv[i], cj, c2 * o.bm[i] * o.bm[j], ns);
@@ -1177,7 +1163,6 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
         for (int j = 0; j < 8; ++j) E8[j] = 0.0;
         auto consume = [&](const ItemOut& o) {
             if (MODE == MODE_EVAL) sample_add<T>(A, o.kq, o.w, o.gamma, o.g, o.eps, o.b);
-            if (MODE == MODE_MASTER) master_rows(LG, o, D.ns);
             if (MODE == MODE_MASTER_HESS) master_blocks(LG, o, S.stri + 3 * D.t, D.ns);
             if (want_dg) {
                 if (want_alpha && o.dg < 0.0) A.amin = rmin(A.amin, 0.9 * o.g_step / (-o.dg));
@@ -1694,10 +1679,6 @@ k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const d
             on = point_item(S, P, D, xm, dxm, C.point[D.t * C.cap_p + R.j], false, want_dg, o);
             cnt_p += on;
         }
-        if (MODE == MODE_MASTER) {
-            if (on) master_rows(LG, o, D.ns);
-            continue;
-        }
         if (MODE == MODE_MASTER_HESS) {
             if (on) master_blocks(LG, o, S.stri + 3 * D.t, D.ns);
             continue;
@@ -1910,7 +1891,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
         else k_samples<NK, T, MODE, false><<<blocks, threads, 0, c.stream>>>(a...);
     };
     GMCP_CUDA_TRY(c.tri_frame.ensure(8 * (size_t)c.ns + 8));
-    constexpr bool kMaster = MODE == MODE_MASTER || MODE == MODE_MASTER_HESS;
+    constexpr bool kMaster = MODE == MODE_MASTER_HESS;
     if (MODE != MODE_EVAL && !kMaster) {
         k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
                                                    nullptr, nullptr);
@@ -2170,25 +2151,13 @@ cudaError_t contact_alpha_lin(Ctx& c, const double* x, const double* xm, const d
                                                   alpha_bits, LG);
 }
 
-cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m) {
-    ProfScope ps(c.prof, c.stream, "master_grad");
-    GMCP_CUDA_TRY(cudaMemsetAsync(grad_m, 0, sizeof(double) * 3 * (size_t)c.nmv, c.stream));
-    ModeArgs LG;
-    LG.grad_m = grad_m;
-    if (c.P.nk == 4)
-        return launch_samples<4, double, MODE_MASTER>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                       nullptr, nullptr, LG);
-    return launch_samples<16, double, MODE_MASTER>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                    nullptr, nullptr, LG);
-}
-
 cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32_t* ij, double* blk,
-                                int64_t cap, unsigned long long* count, bool rows) {
+                                int64_t cap, unsigned long long* count, bool rows, bool blocks) {
     ProfScope ps(c.prof, c.stream, "master_hess");
     GMCP_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(unsigned long long), c.stream));
     ModeArgs LG;
     LG.h_ij = ij; LG.h_blk = blk; LG.h_count = count; LG.h_cap = cap; LG.m_off = (int32_t)c.nv;
-    LG.h_rows = rows;
+    LG.h_rows = rows; LG.h_blocks = blocks;
     if (c.P.nk == 4)
         return launch_samples<4, double, MODE_MASTER_HESS>(c, x, xm, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                             nullptr, nullptr, LG);

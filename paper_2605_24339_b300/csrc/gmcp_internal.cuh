@@ -239,13 +239,7 @@ struct NewtonState {
     int64_t nsys = 0, ntsys = 0;
     DBuf<double> Xsys;                   // [nsys][3] rest positions
     const double* fext = nullptr;        // external nodal forces of the current step (joint), or NULL
-    // joint step: the master entries (rows and blocks), their counting sort
-    // by destination row, and the summed blocks at their pattern positions
-    int64_t ml_cap = 0;
-    DBuf<int32_t> ml_ij;                 // [cap][2] (row, col), col -1 = a gradient row
-    DBuf<double> ml_blk;                 // [cap][9]
-    DBuf<unsigned long long> ml_count;   // entries needed
-    DBuf<int32_t> ml_cnt, ml_off, ml_cur, ml_perm, ml_tmp, ml_err;
+    // joint step: the summed master blocks at their pattern positions
     DBuf<double> xvals;                  // [nnzb][9] master blocks (FP64, unscaled), zero elsewhere
     bool joint_miss = false;             // a contact block fell outside the pattern
     DBuf<int32_t> tets;                  // [nt][4]
@@ -437,6 +431,13 @@ struct Ctx {
     // per item; set after a contact pass whose sample items outnumbered the
     // master triangles eightfold (results are the same either way)
     bool use_mtri_pre = false;
+    // master entries of the samples (gradient rows and Hessian blocks of the
+    // master vertices) and their counting sort by destination row
+    int64_t ml_cap = 0;
+    DBuf<int32_t> ml_ij;                 // [cap][2] (row, col), col -1 = a gradient row
+    DBuf<double> ml_blk;                 // [cap][9]
+    DBuf<unsigned long long> ml_count;   // entries needed
+    DBuf<int32_t> ml_cnt, ml_off, ml_cur, ml_perm, ml_tmp, ml_err;
     DBuf<int32_t> cell_cnt, cell_start, cell_ent;
     DBuf<int32_t> scan_tmp;
     DBuf<int32_t> cand_face, cand_edge, cand_point, cand_count, active, misc_i32;
@@ -561,14 +562,19 @@ int sm_count(int device);
 cudaError_t contact_lagged(Ctx& c, const double* x, const double* xm, const double* p,
                            const double* alphas_dev, int na, double* triE8, double* energies_dev,
                            int alphas_stride = 0, const double* pm = nullptr);
-// gradient of the contact potential with respect to the master vertices,
-// [nmv][3] FP64 (zeroed first; FP64 atomics, so the summation order varies)
-cudaError_t contact_master_grad(Ctx& c, const double* x, const double* xm, double* grad_m);
 // slave-master (slave row) and master-master Hessian blocks of the active
 // samples, appended in arbitrary order; *count receives the number needed;
 // rows: also the master vertices' gradient rows, as entries (row, -1)
 cudaError_t contact_master_hess(Ctx& c, const double* x, const double* xm, int32_t* ij, double* blk,
-                                int64_t cap, unsigned long long* count, bool rows = false);
+                                int64_t cap, unsigned long long* count, bool rows = false, bool blocks = true);
+// the master entries of the samples at (x, xm) -- gradient rows, and with
+// xvals the blocks too -- sorted by destination row (then by value) and
+// summed in that order: row r (joint numbering) into rows_out[3 (r -
+// row_base)] (FP32 or FP64), blocks (col >= row) into xvals at their place in
+// the pattern (rp, llen, ci); *miss set when a block has no place
+cudaError_t sorted_master_terms(Ctx& c, const double* x, const double* xm, int64_t nrows, int64_t row_base,
+                                void* rows_out, bool rows_f32, const int32_t* rp, const int32_t* llen,
+                                const int32_t* ci, double* xvals, bool* miss);
 // newton.cu
 cudaError_t newton_setup(Ctx& c);
 // The Newton iteration runs per environment: each sum below is one

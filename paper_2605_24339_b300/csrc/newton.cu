@@ -508,7 +508,7 @@ __global__ void k_ml_reduce(int64_t nsys, const int32_t* __restrict__ off, int32
                             const int32_t* __restrict__ ij, const double* __restrict__ blk,
                             const int32_t* __restrict__ rp, const int32_t* __restrict__ llen,
                             const int32_t* __restrict__ ci, double* __restrict__ xvals, TG* __restrict__ cgrad,
-                            int32_t* __restrict__ err) {
+                            int64_t row_base, int32_t* __restrict__ err) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nsys) return;
     const int32_t b0 = off[r], b1 = off[r + 1];
@@ -528,7 +528,8 @@ __global__ void k_ml_reduce(int64_t nsys, const int32_t* __restrict__ off, int32
         }
         k = k2;
         if (col < 0) {
-            for (int q = 0; q < 3; ++q) cgrad[3 * r + q] = (TG)sum[q];
+            if (r >= row_base)
+                for (int q = 0; q < 3; ++q) cgrad[3 * (r - row_base) + q] = (TG)sum[q];
         } else if (xvals && col >= r) {
             int32_t lo = rp[r] + llen[r], hi = rp[r + 1] - 1, at = -1;
             while (lo <= hi) {
@@ -2088,16 +2089,6 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.dir.upload(Dir.data(), Dir.size(), s));
     GMCP_CUDA_TRY(N.Xsys.upload(X, 3 * (size_t)nv, s));
     if (joint) {
-        N.ml_cap = std::max<int64_t>((int64_t)1 << 16, 64 * c.ns);
-        GMCP_CUDA_TRY(N.ml_ij.ensure(2 * (size_t)N.ml_cap));
-        GMCP_CUDA_TRY(N.ml_blk.ensure(9 * (size_t)N.ml_cap));
-        GMCP_CUDA_TRY(N.ml_perm.ensure((size_t)N.ml_cap));
-        GMCP_CUDA_TRY(N.ml_count.ensure(1));
-        GMCP_CUDA_TRY(N.ml_cnt.ensure((size_t)nv + 1));
-        GMCP_CUDA_TRY(N.ml_off.ensure((size_t)nv + 2));
-        GMCP_CUDA_TRY(N.ml_cur.ensure((size_t)nv + 1));
-        GMCP_CUDA_TRY(N.ml_tmp.ensure(2 * scan_tmp_size(nv + 1)));
-        GMCP_CUDA_TRY(N.ml_err.ensure(1));
         GMCP_CUDA_TRY(N.xvals.ensure(9 * (size_t)nnzb + 9));
         GMCP_CUDA_TRY(cudaMemsetAsync(N.xvals.p, 0, sizeof(double) * (9 * (size_t)nnzb + 9), s));
     }
@@ -2175,58 +2166,74 @@ const double* master_dir_of(Ctx& c, const double* p) {
     return c.newton->joint ? p + 3 * c.nv : nullptr;
 }
 
+// The master entries of the samples at (x, xm), sorted by destination and
+// summed in a fixed order (see k_ml_reduce): the rows, and with xvals the
+// blocks.  Uses the context's entry buffers (grown and retried when the
+// entries outnumber them).
+cudaError_t sorted_master_terms(Ctx& c, const double* x, const double* xm, int64_t nrows, int64_t row_base,
+                                void* rows_out, bool rows_f32, const int32_t* rp, const int32_t* llen,
+                                const int32_t* ci, double* xvals, bool* miss) {
+    cudaStream_t s = c.stream;
+    if (c.ml_cap == 0) c.ml_cap = std::max<int64_t>((int64_t)1 << 16, 64 * c.ns);
+    for (int attempt = 0;; ++attempt) {
+        GMCP_CUDA_TRY(c.ml_ij.ensure(2 * (size_t)c.ml_cap));
+        GMCP_CUDA_TRY(c.ml_blk.ensure(9 * (size_t)c.ml_cap));
+        GMCP_CUDA_TRY(c.ml_perm.ensure((size_t)c.ml_cap));
+        GMCP_CUDA_TRY(c.ml_count.ensure(1));
+        GMCP_CUDA_TRY(contact_master_hess(c, x, xm, c.ml_ij.p, c.ml_blk.p, c.ml_cap, c.ml_count.p, true,
+                                          xvals != nullptr));
+        unsigned long long need = 0;
+        GMCP_CUDA_TRY(cudaMemcpyAsync(&need, c.ml_count.p, sizeof(need), cudaMemcpyDeviceToHost, s));
+        GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+        if ((int64_t)need <= c.ml_cap) break;
+        if (attempt >= 2) return cudaErrorInvalidValue;
+        c.ml_cap = (int64_t)need + (int64_t)need / 2 + 1024;
+    }
+    GMCP_CUDA_TRY(c.ml_cnt.ensure((size_t)nrows + 1));
+    GMCP_CUDA_TRY(c.ml_off.ensure((size_t)nrows + 2));
+    GMCP_CUDA_TRY(c.ml_cur.ensure((size_t)nrows + 1));
+    GMCP_CUDA_TRY(c.ml_tmp.ensure(2 * scan_tmp_size(nrows + 1)));
+    GMCP_CUDA_TRY(c.ml_err.ensure(1));
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.ml_cnt.p, 0, sizeof(int32_t) * (nrows + 1), s));
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.ml_cur.p, 0, sizeof(int32_t) * (nrows + 1), s));
+    GMCP_CUDA_TRY(cudaMemsetAsync(c.ml_err.p, 0, sizeof(int32_t), s));
+    const unsigned g = (unsigned)std::min<int64_t>(4096, (c.ml_cap + 255) / 256);
+    k_ml_count<<<g, 256, 0, s>>>(c.ml_ij.p, c.ml_count.p, c.ml_cap, nrows, c.ml_cnt.p, c.ml_err.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    GMCP_CUDA_TRY(exclusive_scan_i32(c.ml_cnt.p, c.ml_off.p, nrows + 1, c.ml_tmp.p, c.ml_tmp.n, s));
+    k_ml_fill<<<g, 256, 0, s>>>(c.ml_ij.p, c.ml_count.p, c.ml_cap, nrows, c.ml_off.p, c.ml_cur.p, c.ml_perm.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    if (rows_f32)
+        k_ml_reduce<float><<<nblk(nrows, 128), 128, 0, s>>>(nrows, c.ml_off.p, c.ml_perm.p, c.ml_ij.p, c.ml_blk.p, rp,
+                                                           llen, ci, xvals, (float*)rows_out, row_base, c.ml_err.p);
+    else
+        k_ml_reduce<double><<<nblk(nrows, 128), 128, 0, s>>>(nrows, c.ml_off.p, c.ml_perm.p, c.ml_ij.p, c.ml_blk.p,
+                                                            rp, llen, ci, xvals, (double*)rows_out, row_base,
+                                                            c.ml_err.p);
+    GMCP_CUDA_TRY(cudaGetLastError());
+    int32_t err = 0;
+    GMCP_CUDA_TRY(cudaMemcpyAsync(&err, c.ml_err.p, sizeof(err), cudaMemcpyDeviceToHost, s));
+    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (miss) *miss = err != 0;
+    return err ? cudaErrorInvalidValue : cudaSuccess;
+}
+
 // Joint step: the gradient rows of the master vertices (into the contact
 // gradient's rows nv .. nsys) and, with want_hess, the blocks with master
-// vertices (into xvals), from the samples of the last pass at x, summed in a
-// fixed order (see k_ml_reduce).  A block outside the pattern sets
-// N.joint_miss and fails the call.
+// vertices (into xvals), from the samples of the last pass at x.  A block
+// outside the pattern sets N.joint_miss and fails the call.
 cudaError_t joint_master_terms(Ctx& c, const double* x, bool want_hess) {
     NewtonState& N = *c.newton;
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
-    const double* xm = x + 3 * c.nv;
-    const int64_t nsys = N.nsys;
-    for (int attempt = 0;; ++attempt) {
-        GMCP_CUDA_TRY(contact_master_hess(c, x, xm, N.ml_ij.p, N.ml_blk.p, N.ml_cap, N.ml_count.p, true));
-        unsigned long long need = 0;
-        GMCP_CUDA_TRY(cudaMemcpyAsync(&need, N.ml_count.p, sizeof(need), cudaMemcpyDeviceToHost, c.stream));
-        GMCP_CUDA_TRY(cudaStreamSynchronize(c.stream));
-        if ((int64_t)need <= N.ml_cap) break;
-        if (attempt >= 2) return cudaErrorInvalidValue;
-        N.ml_cap = (int64_t)need + (int64_t)need / 2 + 1024;
-        GMCP_CUDA_TRY(N.ml_ij.ensure(2 * (size_t)N.ml_cap));
-        GMCP_CUDA_TRY(N.ml_blk.ensure(9 * (size_t)N.ml_cap));
-        GMCP_CUDA_TRY(N.ml_perm.ensure((size_t)N.ml_cap));
-    }
-    cudaStream_t s = c.stream;
-    GMCP_CUDA_TRY(cudaMemsetAsync(N.ml_cnt.p, 0, sizeof(int32_t) * (nsys + 1), s));
-    GMCP_CUDA_TRY(cudaMemsetAsync(N.ml_cur.p, 0, sizeof(int32_t) * (nsys + 1), s));
-    GMCP_CUDA_TRY(cudaMemsetAsync(N.ml_err.p, 0, sizeof(int32_t), s));
     const size_t gb = f32 ? sizeof(float) : sizeof(double);
     char* cg = f32 ? (char*)N.cgrad32.p : (char*)N.cgrad64.p;
-    GMCP_CUDA_TRY(cudaMemsetAsync(cg + gb * 3 * c.nv, 0, gb * 3 * (nsys - c.nv), s));
-    if (want_hess) GMCP_CUDA_TRY(cudaMemsetAsync(N.xvals.p, 0, sizeof(double) * 9 * N.nnzb, s));
-    const unsigned g = (unsigned)std::min<int64_t>(4096, (N.ml_cap + 255) / 256);
-    k_ml_count<<<g, 256, 0, s>>>(N.ml_ij.p, N.ml_count.p, N.ml_cap, nsys, N.ml_cnt.p, N.ml_err.p);
-    GMCP_CUDA_TRY(cudaGetLastError());
-    GMCP_CUDA_TRY(exclusive_scan_i32(N.ml_cnt.p, N.ml_off.p, nsys + 1, N.ml_tmp.p, N.ml_tmp.n, s));
-    k_ml_fill<<<g, 256, 0, s>>>(N.ml_ij.p, N.ml_count.p, N.ml_cap, nsys, N.ml_off.p, N.ml_cur.p, N.ml_perm.p);
-    GMCP_CUDA_TRY(cudaGetLastError());
-    double* xv = want_hess ? N.xvals.p : nullptr;
-    if (f32)
-        k_ml_reduce<float><<<nblk(nsys, 128), 128, 0, s>>>(nsys, N.ml_off.p, N.ml_perm.p, N.ml_ij.p, N.ml_blk.p,
-                                                          N.rp.p, N.llen.p, N.ci.p, xv, N.cgrad32.p, N.ml_err.p);
-    else
-        k_ml_reduce<double><<<nblk(nsys, 128), 128, 0, s>>>(nsys, N.ml_off.p, N.ml_perm.p, N.ml_ij.p, N.ml_blk.p,
-                                                           N.rp.p, N.llen.p, N.ci.p, xv, N.cgrad64.p, N.ml_err.p);
-    GMCP_CUDA_TRY(cudaGetLastError());
-    int32_t err = 0;
-    GMCP_CUDA_TRY(cudaMemcpyAsync(&err, N.ml_err.p, sizeof(err), cudaMemcpyDeviceToHost, s));
-    GMCP_CUDA_TRY(cudaStreamSynchronize(s));
-    if (err) {
-        N.joint_miss = true;
-        return cudaErrorInvalidValue;
-    }
-    return cudaSuccess;
+    GMCP_CUDA_TRY(cudaMemsetAsync(cg + gb * 3 * c.nv, 0, gb * 3 * (N.nsys - c.nv), c.stream));
+    if (want_hess) GMCP_CUDA_TRY(cudaMemsetAsync(N.xvals.p, 0, sizeof(double) * 9 * N.nnzb, c.stream));
+    bool miss = false;
+    const cudaError_t e = sorted_master_terms(c, x, x + 3 * c.nv, N.nsys, 0, cg, f32, N.rp.p, N.llen.p, N.ci.p,
+                                              want_hess ? N.xvals.p : nullptr, &miss);
+    if (miss) N.joint_miss = true;
+    return e;
 }
 
 // change of each environment's incremental potential from x to x +
