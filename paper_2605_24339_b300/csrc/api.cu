@@ -492,7 +492,14 @@ cudaError_t start_point(Ctx& c, const double* x, const double* P, double* x0, co
     for (int e = 0; e < ne; ++e) any_dir = any_dir || (alive[e] && N.h_has_dir[e]);
     if (any_dir) {
         GMCP_CUDA_TRY(vec_dir_delta(c, x, N.xhat.p, N.dP.p));
-        GMCP_CUDA_TRY(ccd_bound(c, x, N.dP.p, master_of(c, x), master_dir_of(c, N.dP.p), false));
+        // the Dirichlet motion moves contact primitives only where Dirichlet
+        // vertices lie on a contact surface; elsewhere its bound is exactly 1
+        // (no sample's gap and no primitive pair moves)
+        bool any_surf = false;
+        for (int e = 0; e < ne; ++e) any_surf = any_surf || (alive[e] && N.h_has_dir[e] && N.h_dir_surf[e]);
+        if (any_surf) GMCP_CUDA_TRY(ccd_bound(c, x, N.dP.p, master_of(c, x), master_dir_of(c, N.dP.p), false));
+        else
+            for (int e = 0; e < ne; ++e) N.h_ealpha[e] = 1.0;
         std::vector<uint8_t> chk(ne, 0);
         for (int e = 0; e < ne; ++e) {
             if (!alive[e] || !N.h_has_dir[e]) continue;

@@ -301,6 +301,7 @@ struct NewtonState {
     DBuf<double> ezero;                  // one 0.0
     std::vector<double> h_lbar;          // cube root of each environment's mean tet volume
     std::vector<uint8_t> h_has_dir;      // environment has Dirichlet vertices
+    std::vector<uint8_t> h_dir_surf;     // ... among the vertices of its contact surfaces
     // pinned host copies (one allocation, h_pin)
     void* h_pin = nullptr;
     double* h_es = nullptr;              // [n_env][kES]

@@ -2029,6 +2029,7 @@ cudaError_t newton_setup(Ctx& c) {
         std::vector<int32_t> venv(nv), tenv(nt);
         N.h_lbar.assign(ne, 0.0);
         N.h_has_dir.assign(ne, 0);
+        N.h_dir_surf.assign(ne, 0);
         for (int e = 0; e < ne; ++e) {
             for (int64_t v = ev[e]; v < ev[e + 1]; ++v) {
                 venv[v] = e;
@@ -2042,6 +2043,19 @@ cudaError_t newton_setup(Ctx& c) {
             const int64_t nte = et[e + 1] - et[e];
             N.h_lbar[e] = nte > 0 ? cbrt(ve / (double)nte) : 0.0;
         }
+        // Dirichlet vertices on a contact surface (else their motion alone
+        // moves no contact primitive, and its step bound is 1)
+        for (int64_t t = 0; t < c.ns; ++t)
+            for (int a = 0; a < 3; ++a) {
+                const int32_t v = c.h_stri[3 * t + a];
+                if (Dir[v]) N.h_dir_surf[venv[v]] = 1;
+            }
+        if (joint)
+            for (int64_t m = 0; m < c.nmt; ++m)
+                for (int a = 0; a < 3; ++a) {
+                    const int64_t v = c.nv + c.h_mtri[3 * m + a];
+                    if (Dir[v]) N.h_dir_surf[venv[v]] = 1;
+                }
         GMCP_CUDA_TRY(N.vert_env.upload(venv.data(), venv.size(), s));
         GMCP_CUDA_TRY(N.tet_env.upload(tenv.data(), tenv.size(), s));
         GMCP_CUDA_TRY(cudaStreamSynchronize(s));
