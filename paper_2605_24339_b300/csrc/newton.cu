@@ -27,21 +27,24 @@ __device__ __forceinline__ double det3(const double* A) {
     return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
            A[2] * (A[3] * A[7] - A[4] * A[6]);
 }
+// (one FP64 division: the cofactors times 1/det; B300's FP64 divide is a
+// long sequence on the slow pipe)
 __device__ __forceinline__ void inv3(const double* A, double* I) {
-    const double d = det3(A);
-    I[0] = (A[4] * A[8] - A[5] * A[7]) / d; I[1] = (A[2] * A[7] - A[1] * A[8]) / d;
-    I[2] = (A[1] * A[5] - A[2] * A[4]) / d; I[3] = (A[5] * A[6] - A[3] * A[8]) / d;
-    I[4] = (A[0] * A[8] - A[2] * A[6]) / d; I[5] = (A[2] * A[3] - A[0] * A[5]) / d;
-    I[6] = (A[3] * A[7] - A[4] * A[6]) / d; I[7] = (A[1] * A[6] - A[0] * A[7]) / d;
-    I[8] = (A[0] * A[4] - A[1] * A[3]) / d;
+    const double r = 1.0 / det3(A);
+    I[0] = (A[4] * A[8] - A[5] * A[7]) * r; I[1] = (A[2] * A[7] - A[1] * A[8]) * r;
+    I[2] = (A[1] * A[5] - A[2] * A[4]) * r; I[3] = (A[5] * A[6] - A[3] * A[8]) * r;
+    I[4] = (A[0] * A[8] - A[2] * A[6]) * r; I[5] = (A[2] * A[3] - A[0] * A[5]) * r;
+    I[6] = (A[3] * A[7] - A[4] * A[6]) * r; I[7] = (A[1] * A[6] - A[0] * A[7]) * r;
+    I[8] = (A[0] * A[4] - A[1] * A[3]) * r;
 }
 
-// (J - 1) - ln J without cancellation: Taylor series for |d| < 1e-2
-// (truncation below 1e-17 relative), else the plain difference
-__device__ __forceinline__ double d_minus_log1p(double d) {
+// (J - 1) - ln J without cancellation, d = J - 1 and l = ln J = log1p(d):
+// Taylor series for |d| < 1e-2 (truncation below 1e-17 relative), else the
+// plain difference
+__device__ __forceinline__ double d_minus_log1p(double d, double l) {
     if (fabs(d) < 1e-2)
-        return d * d * (1.0 / 2 - d * (1.0 / 3 - d * (1.0 / 4 - d * (1.0 / 5 - d * (1.0 / 6 - d * (1.0 / 7 - d * (1.0 / 8 - d / 9.0)))))));
-    return d - log1p(d);
+        return d * d * (1.0 / 2 - d * (1.0 / 3 - d * (1.0 / 4 - d * (1.0 / 5 - d * (1.0 / 6 - d * (1.0 / 7 - d * (1.0 / 8 - d * (1.0 / 9))))))));
+    return d - l;
 }
 
 struct ElasticView {
@@ -59,17 +62,17 @@ struct ElasticView {
 //   J - 1 = tr H + q, q = sum of principal 2x2 minors of H + det H,
 // (algebraically mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2, with the
 // first-order terms cancelled exactly so the energy keeps its relative
-// precision at small strain).  Returns false if J <= 0.
+// precision at small strain).  Returns false if J <= 0; else also J itself,
+// formed as 1 + (J - 1).
 __device__ __forceinline__ bool nh_energy(const double* Dmi, double vol, double mu, double lam,
                                           const double* x4, const double* X4, double* psi, double* F,
-                                          double* lnJ) {
-    double Du[9], H[9];
-    for (int r = 0; r < 3; ++r)
-        for (int c = 0; c < 3; ++c)
-            Du[3 * r + c] = (x4[3 * (c + 1) + r] - X4[3 * (c + 1) + r]) - (x4[r] - X4[r]);
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            H[3 * i + j] = Du[3 * i] * Dmi[j] + Du[3 * i + 1] * Dmi[3 + j] + Du[3 * i + 2] * Dmi[6 + j];
+                                          double* lnJ, double* J) {
+    double u[12], H[9];
+    for (int q = 0; q < 12; ++q) u[q] = x4[q] - X4[q];
+    for (int i = 0; i < 3; ++i) {
+        const double d1 = u[3 + i] - u[i], d2 = u[6 + i] - u[i], d3 = u[9 + i] - u[i];
+        for (int j = 0; j < 3; ++j) H[3 * i + j] = d1 * Dmi[j] + d2 * Dmi[3 + j] + d3 * Dmi[6 + j];
+    }
     for (int i = 0; i < 9; ++i) F[i] = H[i];
     F[0] += 1.0; F[4] += 1.0; F[8] += 1.0;
     const double trH = H[0] + H[4] + H[8];
@@ -80,7 +83,8 @@ __device__ __forceinline__ bool nh_energy(const double* Dmi, double vol, double 
     double nH = 0.0;
     for (int i = 0; i < 9; ++i) nH += H[i] * H[i];
     *lnJ = log1p(jm1);
-    *psi = vol * (mu * (d_minus_log1p(jm1) - q) + 0.5 * mu * nH + 0.5 * lam * (*lnJ) * (*lnJ));
+    *psi = vol * (mu * (d_minus_log1p(jm1, *lnJ) - q) + 0.5 * mu * nH + 0.5 * lam * (*lnJ) * (*lnJ));
+    *J = 1.0 + jm1;
     return true;
 }
 
@@ -183,11 +187,14 @@ __device__ __forceinline__ void load_hblk(const double* H, double* h) {
 // 9x9 eigen-decomposition.  With D[m] the rows of dF/dx and d_m = V^T D[m],
 // block (m, n) = V_tet U M_mn U^T, M_mn = sum_k max(l_k, 0) (E_k d_m)(E_k d_n)^T.
 template <class R>
-__device__ void nh_hessian_blocks(const double* Fd, double lnJd, double mud, double lamd, const double* Dd,
+__device__ void nh_hessian_blocks(const double* Fd, double lnJd, double mud, double lamd, const double* Dmi,
                                   double vold, R* out /* [10][HBlk<R>::kStride] */) {
-    R F[9], D[12];
+    R F[9], D[12];   // D[m][j] = dF_ij / dx_{m,i}: rows 1..3 of D are Dm^-1, row 0 minus their sum
     for (int i = 0; i < 9; ++i) F[i] = (R)Fd[i];
-    for (int i = 0; i < 12; ++i) D[i] = (R)Dd[i];
+    for (int j = 0; j < 3; ++j) {
+        D[3 + j] = (R)Dmi[j]; D[6 + j] = (R)Dmi[3 + j]; D[9 + j] = (R)Dmi[6 + j];
+        D[j] = -(D[3 + j] + D[6 + j] + D[9 + j]);
+    }
     const R mu = (R)mud, lam = (R)lamd, vol = (R)vold;
     // SVD from the eigen-decomposition of F^T F
     R S[9], V[9];
@@ -292,12 +299,12 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
           const int32_t* __restrict__ tet_env) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= E.nt) return;
-    double x4[12], X4[12], F[9], lnJ, psi;
+    double x4[12], X4[12], F[9], lnJ, J, psi;
     load_tet(E, x, t, x4);
     load_tet(E, E.X, t, X4);
     const double* Dmi = E.Dminv + 9 * t;
     const double vol = E.vol[t];
-    if (!nh_energy(Dmi, vol, E.mu, E.lam, x4, X4, &psi, F, &lnJ)) {
+    if (!nh_energy(Dmi, vol, E.mu, E.lam, x4, X4, &psi, F, &lnJ, &J)) {
         atomicMax(bad + (tet_env ? tet_env[t] : 0), 1);
         tE[t] = INFINITY;
         for (int q = 0; q < 12; ++q) tG[12 * t + q] = 0.0;
@@ -306,24 +313,28 @@ k_nh_eval(ElasticView E, const double* __restrict__ x, double* __restrict__ tE,
         return;
     }
     tE[t] = psi;
-    double Fi[9], G[9];
-    inv3(F, Fi);
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) G[3 * i + j] = Fi[3 * j + i];
-    double D[12];   // D[m][j] = dF_ij / dx_{m,i}
-    for (int j = 0; j < 3; ++j) {
-        D[3 + j] = Dmi[j]; D[6 + j] = Dmi[3 + j]; D[9 + j] = Dmi[6 + j];
-        D[j] = -(D[3 + j] + D[6 + j] + D[9 + j]);
-    }
+    // first Piola stress times the volume, V (mu (F - F^-T) + lambda ln J F^-T),
+    // with F^-T = C / J (C the cofactor matrix of F):
+    //   V P = (mu V) F + ((lambda ln J - mu) V / J) C
+    double C[9];
+    C[0] = F[4] * F[8] - F[5] * F[7]; C[1] = F[5] * F[6] - F[3] * F[8]; C[2] = F[3] * F[7] - F[4] * F[6];
+    C[3] = F[2] * F[7] - F[1] * F[8]; C[4] = F[0] * F[8] - F[2] * F[6]; C[5] = F[1] * F[6] - F[0] * F[7];
+    C[6] = F[1] * F[5] - F[2] * F[4]; C[7] = F[2] * F[3] - F[0] * F[5]; C[8] = F[0] * F[4] - F[1] * F[3];
+    const double mv = E.mu * vol, cv = (E.lam * lnJ - E.mu) * vol / J;
     double P[9];
-    for (int i = 0; i < 9; ++i) P[i] = E.mu * (F[i] - G[i]) + E.lam * lnJ * G[i];
-    for (int m = 0; m < 4; ++m)
-        for (int i = 0; i < 3; ++i) {
-            double s = 0.0;
-            for (int j = 0; j < 3; ++j) s += P[3 * i + j] * D[3 * m + j];
-            tG[12 * t + 3 * m + i] = vol * s;
+    for (int i = 0; i < 9; ++i) P[i] = mv * F[i] + cv * C[i];
+    // gradient rows: vertex m >= 1 gets P (Dm^-1 row m-1), vertex 0 minus their sum
+    for (int i = 0; i < 3; ++i) {
+        double s0 = 0.0;
+        for (int m = 1; m < 4; ++m) {
+            const double* d = Dmi + 3 * (m - 1);
+            const double sm = P[3 * i] * d[0] + P[3 * i + 1] * d[1] + P[3 * i + 2] * d[2];
+            tG[12 * t + 3 * m + i] = sm;
+            s0 += sm;
         }
-    if (WANT_HESS) nh_hessian_blocks<TH>(F, lnJ, E.mu, E.lam, D, vol, tH + HBlk<TH>::kPerTet * t);
+        tG[12 * t + i] = -s0;
+    }
+    if (WANT_HESS) nh_hessian_blocks<TH>(F, lnJ, E.mu, E.lam, Dmi, vol, tH + HBlk<TH>::kPerTet * t);
 }
 
 // elastic energies at x + alpha_j p for j < na (<= 8), layout [na][nt]
@@ -336,7 +347,7 @@ __global__ void k_nh_energy_multi(ElasticView E, const double* __restrict__ x,
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= E.nt) return;
     const double* alphas = alphas_env + (int64_t)astride * tet_env[t];
-    double x4[12], p4[12], X4[12], y4[12], F[9], lnJ, psi;
+    double x4[12], p4[12], X4[12], y4[12], F[9], lnJ, J, psi;
     load_tet(E, x, t, x4);
     load_tet(E, p, t, p4);
     load_tet(E, E.X, t, X4);
@@ -344,7 +355,7 @@ __global__ void k_nh_energy_multi(ElasticView E, const double* __restrict__ x,
     for (int j = 0; j < na; ++j) {
         const double a = alphas[j];
         for (int q = 0; q < 12; ++q) y4[q] = x4[q] + a * p4[q];
-        const bool ok = nh_energy(Dmi, E.vol[t], E.mu, E.lam, y4, X4, &psi, F, &lnJ);
+        const bool ok = nh_energy(Dmi, E.vol[t], E.mu, E.lam, y4, X4, &psi, F, &lnJ, &J);
         tE8[(int64_t)j * E.nt + t] = ok ? (base ? psi - base[t] : psi) : INFINITY;
     }
 }
