@@ -438,8 +438,9 @@ const int32_t* put_mask(Ctx& c, int k, const std::vector<uint8_t>& m, bool inver
     return N.emask.p + (size_t)k * N.n_env;
 }
 
-// per environment with need[e]: the first j in [0, max_halv] with a finite
-// elastic energy at xi + (a_e 2^-j) dP (j = 0 first, then batches of 8);
+// per environment with need[e]: the first j in [0, max_halv] where every
+// tet keeps J > 0 (a finite elastic energy) at xi + (a_e 2^-j) dP (j = 0
+// first, then batches of 8);
 // j_out[e] = -1 if none
 cudaError_t first_feasible(Ctx& c, const double* xi, const double* dP, const std::vector<double>& a,
                            int max_halv, const std::vector<uint8_t>& need, std::vector<int>& j_out,
@@ -459,7 +460,7 @@ cudaError_t first_feasible(Ctx& c, const double* xi, const double* dP, const std
         for (int e = 0; e < ne; ++e)
             for (int j = 0; j < na; ++j) N.h_eal[8 * e + j] = std::ldexp(a[e], -(base + j));
         GMCP_CUDA_TRY(cudaMemcpyAsync(N.eal.p, N.h_eal, sizeof(double) * 8 * ne, cudaMemcpyHostToDevice, c.stream));
-        GMCP_CUDA_TRY(nh_energy_multi(c, xi, dP, N.eal.p, na, kEsFe));
+        GMCP_CUDA_TRY(nh_feasible_multi(c, xi, dP, N.eal.p, na, kEsFe));
         GMCP_CUDA_TRY(read_es(c, kEsFe, na));
         for (int e = 0; e < ne; ++e) {
             if (!pending[e]) continue;

@@ -588,6 +588,11 @@ cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess);
 // from x (per tet, against the energies of the last nh_eval at x)
 cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na, int slot,
                             bool delta = false);
+// inversion test alone: es[slot + j] = 0 where every tet of the environment
+// keeps J > 0 at x + alphas_env[8 e + j] p (j < na <= 8), +inf where not (the
+// same decision as nh_energy_multi's)
+cudaError_t nh_feasible_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na,
+                              int slot);
 // changes of the total energy from x to x + alphas_env[8 e + j] p into
 // es[kEsE8 + j]; ee0: alphas_env[8 e] = 0
 cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double* alphas_env, int na,

@@ -57,7 +57,24 @@ struct ElasticView {
 };
 
 // Displacement gradient H = (Ds - Dm) Dm^-1 from the vertex displacements
-// u = x - X, F = I + H, and the Neo-Hookean energy of the tet in the form
+// u = x - X, q = sum of principal 2x2 minors of H + det H and J - 1 = tr H + q
+// (the energy and the inversion test below share it, so they decide J > 0
+// alike)
+__device__ __forceinline__ void nh_strain(const double* Dmi, const double* x4, const double* X4, double* H,
+                                          double* q, double* jm1) {
+    double u[12];
+    for (int k = 0; k < 12; ++k) u[k] = x4[k] - X4[k];
+    for (int i = 0; i < 3; ++i) {
+        const double d1 = u[3 + i] - u[i], d2 = u[6 + i] - u[i], d3 = u[9 + i] - u[i];
+        for (int j = 0; j < 3; ++j) H[3 * i + j] = d1 * Dmi[j] + d2 * Dmi[3 + j] + d3 * Dmi[6 + j];
+    }
+    const double trH = H[0] + H[4] + H[8];
+    const double minors = (H[0] * H[4] - H[1] * H[3]) + (H[0] * H[8] - H[2] * H[6]) + (H[4] * H[8] - H[5] * H[7]);
+    *q = minors + det3(H);
+    *jm1 = trH + *q;
+}
+
+// F = I + H and the Neo-Hookean energy of the tet in the form
 //   V [mu ((J-1) - ln J - q) + mu/2 |H|^2 + lambda/2 (ln J)^2],
 //   J - 1 = tr H + q, q = sum of principal 2x2 minors of H + det H,
 // (algebraically mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2, with the
@@ -67,18 +84,10 @@ struct ElasticView {
 __device__ __forceinline__ bool nh_energy(const double* Dmi, double vol, double mu, double lam,
                                           const double* x4, const double* X4, double* psi, double* F,
                                           double* lnJ, double* J) {
-    double u[12], H[9];
-    for (int q = 0; q < 12; ++q) u[q] = x4[q] - X4[q];
-    for (int i = 0; i < 3; ++i) {
-        const double d1 = u[3 + i] - u[i], d2 = u[6 + i] - u[i], d3 = u[9 + i] - u[i];
-        for (int j = 0; j < 3; ++j) H[3 * i + j] = d1 * Dmi[j] + d2 * Dmi[3 + j] + d3 * Dmi[6 + j];
-    }
+    double H[9], q, jm1;
+    nh_strain(Dmi, x4, X4, H, &q, &jm1);
     for (int i = 0; i < 9; ++i) F[i] = H[i];
     F[0] += 1.0; F[4] += 1.0; F[8] += 1.0;
-    const double trH = H[0] + H[4] + H[8];
-    const double minors = (H[0] * H[4] - H[1] * H[3]) + (H[0] * H[8] - H[2] * H[6]) + (H[4] * H[8] - H[5] * H[7]);
-    const double q = minors + det3(H);
-    const double jm1 = trH + q;
     if (!(jm1 > -1.0)) return false;
     double nH = 0.0;
     for (int i = 0; i < 9; ++i) nH += H[i] * H[i];
@@ -357,6 +366,28 @@ __global__ void k_nh_energy_multi(ElasticView E, const double* __restrict__ x,
         for (int q = 0; q < 12; ++q) y4[q] = x4[q] + a * p4[q];
         const bool ok = nh_energy(Dmi, E.vol[t], E.mu, E.lam, y4, X4, &psi, F, &lnJ, &J);
         tE8[(int64_t)j * E.nt + t] = ok ? (base ? psi - base[t] : psi) : INFINITY;
+    }
+}
+
+// inversion test at x + alpha_j p for j < na (<= 8): 0 where the tet keeps
+// J > 0, +inf where not (the energy's own test, without the energy), layout
+// [na][nt]
+__global__ void k_nh_feasible(ElasticView E, const double* __restrict__ x, const double* __restrict__ p,
+                              const double* __restrict__ alphas_env, int astride,
+                              const int32_t* __restrict__ tet_env, int na, double* __restrict__ tE8) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E.nt) return;
+    const double* alphas = alphas_env + (int64_t)astride * tet_env[t];
+    double x4[12], p4[12], X4[12], y4[12], H[9], q, jm1;
+    load_tet(E, x, t, x4);
+    load_tet(E, p, t, p4);
+    load_tet(E, E.X, t, X4);
+    const double* Dmi = E.Dminv + 9 * t;
+    for (int j = 0; j < na; ++j) {
+        const double a = alphas[j];
+        for (int k = 0; k < 12; ++k) y4[k] = x4[k] + a * p4[k];
+        nh_strain(Dmi, y4, X4, H, &q, &jm1);
+        tE8[(int64_t)j * E.nt + t] = jm1 > -1.0 ? 0.0 : INFINITY;
     }
 }
 
@@ -1507,6 +1538,17 @@ cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const doub
     if (N.ntsys > 0) {
         k_nh_energy_multi<<<nblk(N.ntsys, 128), 128, 0, c.stream>>>(E, x, p, alphas_env, 8, N.tet_env.p, na,
                                                                    N.tE8.p, delta ? N.tE.p : nullptr);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    return seg_sum(c, N.seg_t, N.tE8.p, N.ntsys, na, N.es.p + slot, kES);
+}
+
+cudaError_t nh_feasible_multi(Ctx& c, const double* x, const double* p, const double* alphas_env, int na,
+                              int slot) {
+    NewtonState& N = *c.newton;
+    ElasticView E{N.ntsys, N.tets.p, N.Dminv.p, N.vol.p, N.Xsys.p, N.mu, N.lam};
+    if (N.ntsys > 0) {
+        k_nh_feasible<<<nblk(N.ntsys, 128), 128, 0, c.stream>>>(E, x, p, alphas_env, 8, N.tet_env.p, na, N.tE8.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     return seg_sum(c, N.seg_t, N.tE8.p, N.ntsys, na, N.es.p + slot, kES);
