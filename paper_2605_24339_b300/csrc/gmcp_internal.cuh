@@ -259,6 +259,9 @@ struct NewtonState {
     DBuf<int32_t> bt_off, bt;            // block -> (t*16 + a*4 + b)
     DBuf<int32_t> cmap;                  // block -> contact block or -1
     DBuf<double> tE, tG, tE8;            // per-tet energy [nt], gradient [nt][12], energies [8][nt]
+                                         // (mixed path: tG holds the gradient as FP32 pairs hi, lo)
+    DBuf<float> Dm2, vol2;               // mixed path: Dm^-1 [nt][9] and volumes [nt] as FP32 pairs
+    DBuf<float> uh4, ul4, ph4, pl4;      // mixed path: x - X and a direction p split into pairs [nv][4] each
     DBuf<double> tH64;                   // per-tet Hessian, 10 blocks [nt][10][10] (FP64 path)
     DBuf<float> tH32;                    // the same in FP32, [nt][10][12] (mixed path)
     DBuf<double> A64, Pinv;              // global matrix [ngroups][288] (FP64 path), P^-1 [nvp][9]

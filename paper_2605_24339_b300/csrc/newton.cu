@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "gmcp_internal.cuh"
+#include "dfloat.cuh"
 
 namespace gmcp {
 namespace {
@@ -195,9 +196,9 @@ __device__ __forceinline__ void load_hblk(const double* H, double* h) {
 // Clamping the eigenvalues at zero gives the same (unique) projection as a
 // 9x9 eigen-decomposition.  With D[m] the rows of dF/dx and d_m = V^T D[m],
 // block (m, n) = V_tet U M_mn U^T, M_mn = sum_k max(l_k, 0) (E_k d_m)(E_k d_n)^T.
-template <class R>
-__device__ void nh_hessian_blocks(const double* Fd, double lnJd, double mud, double lamd, const double* Dmi,
-                                  double vold, R* out /* [10][HBlk<R>::kStride] */) {
+template <class R, class In = double>
+__device__ void nh_hessian_blocks(const In* Fd, In lnJd, In mud, In lamd, const In* Dmi, In vold,
+                                  R* out /* [10][HBlk<R>::kStride] */) {
     R F[9], D[12];   // D[m][j] = dF_ij / dx_{m,i}: rows 1..3 of D are Dm^-1, row 0 minus their sum
     for (int i = 0; i < 9; ++i) F[i] = (R)Fd[i];
     for (int j = 0; j < 3; ++j) {
@@ -391,21 +392,230 @@ __global__ void k_nh_feasible(ElasticView E, const double* __restrict__ x, const
     }
 }
 
+// ---------------------------------------------- mixed path: double-float ---
+// The same elastic terms (the same formulas and branch points as the FP64
+// kernels above) in double-float arithmetic (about 48 bits, on the FP32
+// pipe): the displacement u = x - X and a direction p enter split into
+// pairs once per vertex (k_split_pairs), Dm^-1 and the volumes once at setup.
+struct ElasticViewDF {
+    int64_t nt;
+    const int32_t* tets;
+    const float2* Dmi;   // [nt][9]
+    const float2* vol;   // [nt]
+    dfl mu, lam;
+    dfl c13, c15, c23;   // 1/3, 1/5, 2/3 as pairs (series coefficients)
+};
+
+// u = x - X (or p alone when X is null) split into pairs, [nv][4] hi and lo
+__global__ void k_split_pairs(int64_t nv, const double* __restrict__ x, const double* __restrict__ X,
+                              float4* __restrict__ hi, float4* __restrict__ lo) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    dfl d[3];
+    for (int c = 0; c < 3; ++c) d[c] = df_from_double(X ? x[3 * v + c] - X[3 * v + c] : x[3 * v + c]);
+    hi[v] = make_float4(d[0].hi, d[1].hi, d[2].hi, 0.f);
+    lo[v] = make_float4(d[0].lo, d[1].lo, d[2].lo, 0.f);
+}
+
+__device__ __forceinline__ dfl ld_pair(const float2* p) {
+    const float2 v = __ldg(p);
+    return {v.x, v.y};
+}
+__device__ __forceinline__ void load_tet_pairs(const ElasticViewDF& E, const float4* hi, const float4* lo, int64_t t,
+                                               dfl* u4) {
+    for (int a = 0; a < 4; ++a) {
+        const int64_t v = E.tets[4 * t + a];
+        const float4 h = __ldg(hi + v), l = __ldg(lo + v);
+        u4[3 * a] = {h.x, l.x}; u4[3 * a + 1] = {h.y, l.y}; u4[3 * a + 2] = {h.z, l.z};
+    }
+}
+
+// nh_strain in pairs
+__device__ __forceinline__ void nh_strain_df(const dfl* Dmi, const dfl* u, dfl* H, dfl* q, dfl* jm1) {
+    for (int i = 0; i < 3; ++i) {
+        const dfl d1 = df_sub(u[3 + i], u[i]), d2 = df_sub(u[6 + i], u[i]), d3 = df_sub(u[9 + i], u[i]);
+        for (int j = 0; j < 3; ++j) H[3 * i + j] = df_fma(d3, Dmi[6 + j], df_fma(d2, Dmi[3 + j], df_mul(d1, Dmi[j])));
+    }
+    const dfl trH = df_add(df_add(H[0], H[4]), H[8]);
+    const dfl c00 = df_mms(H[4], H[8], H[5], H[7]);
+    const dfl minors = df_add(df_add(df_mms(H[0], H[4], H[1], H[3]), df_mms(H[0], H[8], H[2], H[6])), c00);
+    const dfl det = df_add(df_sub(df_mul(H[0], c00), df_mul(H[1], df_mms(H[3], H[8], H[5], H[6]))),
+                           df_mul(H[2], df_mms(H[3], H[7], H[4], H[6])));
+    *q = df_add(minors, det);
+    *jm1 = df_add(trH, *q);
+}
+
+// ln J = log1p(d) and (J - 1) - ln J for d = J - 1: for |d| < 1e-2 by
+// series, ln(1 + d) = 2 atanh(s) = 2 (s + s^3/3 + ... + s^9/9) with
+// s = d / (2 + d) (|s| < 5e-3, truncation below 4e-19 relative), and
+// d - ln(1 + d) = d^2 (1/2 - d/3 + d^2/4 - ... + d^7/9) (as in the FP64
+// kernels); otherwise in FP64 from the pair's value (no cancellation there)
+__device__ __forceinline__ void nh_log_df(const ElasticViewDF& E, dfl d, dfl* lnJ, dfl* dml) {
+    if (fabsf(d.hi) < 1e-2f) {
+        const dfl s = df_div(d, df_add(df_make(2.f), d));
+        const dfl t = df_mul(s, s);
+        const float in = 0.4f + t.hi * (2.f / 7.f + t.hi * (2.f / 9.f));
+        const dfl c1 = df_add(E.c23, df_mulf(t, in));
+        *lnJ = df_mul(s, df_add(df_make(2.f), df_mul(t, c1)));
+        const float tail = 1.f / 6.f - d.hi * (1.f / 7.f - d.hi * (1.f / 8.f - d.hi * (1.f / 9.f)));
+        const dfl s5 = df_sub(E.c15, df_mulf(d, tail));
+        const dfl s4 = df_sub(df_make(0.25f), df_mul(d, s5));
+        const dfl s3 = df_sub(E.c13, df_mul(d, s4));
+        const dfl s2 = df_sub(df_make(0.5f), df_mul(d, s3));
+        *dml = df_mul(df_mul(d, d), s2);
+    } else {
+        const double jd = df_to_double(d);
+        const double l = log1p(jd);
+        *lnJ = df_from_double(l);
+        *dml = df_from_double(jd - l);
+    }
+}
+
+// nh_energy in pairs: false if J <= 0
+__device__ __forceinline__ bool nh_energy_df(const ElasticViewDF& E, const dfl* Dmi, dfl vol, const dfl* u,
+                                             dfl* psi, dfl* H, dfl* lnJ, dfl* jm1) {
+    dfl q;
+    nh_strain_df(Dmi, u, H, &q, jm1);
+    if (!df_gt(*jm1, -1.f)) return false;
+    dfl nH = df_mul(H[0], H[0]);
+    for (int i = 1; i < 9; ++i) nH = df_fma(H[i], H[i], nH);
+    dfl dml;
+    nh_log_df(E, *jm1, lnJ, &dml);
+    const dfl a = df_mul(E.mu, df_sub(dml, q));
+    const dfl b = df_mul(E.mu, nH);
+    const dfl l2 = df_mul(E.lam, df_mul(*lnJ, *lnJ));
+    const dfl half = df_add(b, l2);
+    *psi = df_mul(vol, df_add(a, {0.5f * half.hi, 0.5f * half.lo}));
+    return true;
+}
+
+// k_nh_eval of the mixed path: energy (FP64 from the pair), gradient as
+// pairs [nt][12], FP32 Hessian blocks from the pairs' high parts
+template <bool WANT_HESS>
+__global__ void __launch_bounds__(128)
+k_nh_eval_df(ElasticViewDF E, const float4* __restrict__ uh, const float4* __restrict__ ul,
+             double* __restrict__ tE, float2* __restrict__ tG, float* __restrict__ tH, int32_t* __restrict__ bad,
+             const int32_t* __restrict__ tet_env) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E.nt) return;
+    dfl u[12], Dmi[9], H[9], psi, lnJ, jm1;
+    load_tet_pairs(E, uh, ul, t, u);
+    for (int k = 0; k < 9; ++k) Dmi[k] = ld_pair(E.Dmi + 9 * t + k);
+    const dfl vol = ld_pair(E.vol + t);
+    if (!nh_energy_df(E, Dmi, vol, u, &psi, H, &lnJ, &jm1)) {
+        atomicMax(bad + (tet_env ? tet_env[t] : 0), 1);
+        tE[t] = INFINITY;
+        for (int k = 0; k < 12; ++k) tG[12 * t + k] = make_float2(0.f, 0.f);
+        if (WANT_HESS)
+            for (int k = 0; k < HBlk<float>::kPerTet; ++k) tH[HBlk<float>::kPerTet * t + k] = 0.f;
+        return;
+    }
+    tE[t] = df_to_double(psi);
+    dfl F[9];
+    for (int k = 0; k < 9; ++k) F[k] = H[k];
+    F[0] = df_add(F[0], df_make(1.f)); F[4] = df_add(F[4], df_make(1.f)); F[8] = df_add(F[8], df_make(1.f));
+    // V P = (mu V) F + ((lambda ln J - mu) V / J) C, C the cofactors of F
+    dfl C[9];
+    C[0] = df_mms(F[4], F[8], F[5], F[7]); C[1] = df_mms(F[5], F[6], F[3], F[8]); C[2] = df_mms(F[3], F[7], F[4], F[6]);
+    C[3] = df_mms(F[2], F[7], F[1], F[8]); C[4] = df_mms(F[0], F[8], F[2], F[6]); C[5] = df_mms(F[1], F[6], F[0], F[7]);
+    C[6] = df_mms(F[1], F[5], F[2], F[4]); C[7] = df_mms(F[2], F[3], F[0], F[5]); C[8] = df_mms(F[0], F[4], F[1], F[3]);
+    const dfl J = df_add(df_make(1.f), jm1);
+    const dfl mv = df_mul(E.mu, vol);
+    const dfl cv = df_div(df_mul(df_sub(df_mul(E.lam, lnJ), E.mu), vol), J);
+    dfl P[9];
+    for (int k = 0; k < 9; ++k) P[k] = df_add(df_mul(mv, F[k]), df_mul(cv, C[k]));
+    for (int i = 0; i < 3; ++i) {
+        dfl s0 = df_make(0.f);
+        for (int m = 1; m < 4; ++m) {
+            const dfl* d = Dmi + 3 * (m - 1);
+            const dfl sm = df_fma(P[3 * i + 2], d[2], df_fma(P[3 * i + 1], d[1], df_mul(P[3 * i], d[0])));
+            tG[12 * t + 3 * m + i] = make_float2(sm.hi, sm.lo);
+            s0 = df_add(s0, sm);
+        }
+        tG[12 * t + i] = make_float2(-s0.hi, -s0.lo);
+    }
+    if (WANT_HESS) {
+        float Ff[9], Df[9];
+        for (int k = 0; k < 9; ++k) { Ff[k] = F[k].hi; Df[k] = Dmi[k].hi; }
+        nh_hessian_blocks<float, float>(Ff, lnJ.hi, E.mu.hi, E.lam.hi, Df, vol.hi, tH + HBlk<float>::kPerTet * t);
+    }
+}
+
+// k_nh_energy_multi of the mixed path (changes from base: FP64 energies of
+// the last evaluation at x)
+__global__ void __launch_bounds__(128)
+k_nh_energy_multi_df(ElasticViewDF E, const float4* __restrict__ uh, const float4* __restrict__ ul,
+                     const float4* __restrict__ ph, const float4* __restrict__ pl,
+                     const double* __restrict__ alphas_env, int astride, const int32_t* __restrict__ tet_env,
+                     int na, double* __restrict__ tE8, const double* __restrict__ base) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E.nt) return;
+    const double* alphas = alphas_env + (int64_t)astride * tet_env[t];
+    dfl u[12], p[12], Dmi[9], y[12], H[9], psi, lnJ, jm1;
+    load_tet_pairs(E, uh, ul, t, u);
+    load_tet_pairs(E, ph, pl, t, p);
+    for (int k = 0; k < 9; ++k) Dmi[k] = ld_pair(E.Dmi + 9 * t + k);
+    const dfl vol = ld_pair(E.vol + t);
+    for (int j = 0; j < na; ++j) {
+        const dfl a = df_from_double(alphas[j]);
+        for (int k = 0; k < 12; ++k) y[k] = df_fma(a, p[k], u[k]);
+        double out = INFINITY;
+        if (nh_energy_df(E, Dmi, vol, y, &psi, H, &lnJ, &jm1))
+            out = base ? ((double)psi.hi - base[t]) + (double)psi.lo : df_to_double(psi);
+        tE8[(int64_t)j * E.nt + t] = out;
+    }
+}
+
+// k_nh_feasible of the mixed path
+__global__ void __launch_bounds__(128)
+k_nh_feasible_df(ElasticViewDF E, const float4* __restrict__ uh, const float4* __restrict__ ul,
+                 const float4* __restrict__ ph, const float4* __restrict__ pl,
+                 const double* __restrict__ alphas_env, int astride, const int32_t* __restrict__ tet_env, int na,
+                 double* __restrict__ tE8) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E.nt) return;
+    const double* alphas = alphas_env + (int64_t)astride * tet_env[t];
+    dfl u[12], p[12], Dmi[9], y[12], H[9], q, jm1;
+    load_tet_pairs(E, uh, ul, t, u);
+    load_tet_pairs(E, ph, pl, t, p);
+    for (int k = 0; k < 9; ++k) Dmi[k] = ld_pair(E.Dmi + 9 * t + k);
+    for (int j = 0; j < na; ++j) {
+        const dfl a = df_from_double(alphas[j]);
+        for (int k = 0; k < 12; ++k) y[k] = df_fma(a, p[k], u[k]);
+        nh_strain_df(Dmi, y, H, &q, &jm1);
+        tE8[(int64_t)j * E.nt + t] = df_gt(jm1, -1.f) ? 0.0 : INFINITY;
+    }
+}
+
 // G = M (x - xhat) + h^2 (sum_tets g + contact g); Dirichlet rows zero
 __global__ void k_assemble_grad(int64_t nv, const double* __restrict__ x, const double* __restrict__ xhat,
                                 const double* __restrict__ mass, const uint8_t* __restrict__ dir,
                                 const int32_t* __restrict__ vt_off, const int32_t* __restrict__ vt_ent,
-                                const double* __restrict__ tG, const void* __restrict__ cgrad, int cgrad_f32,
-                                const double* __restrict__ fext, double h2, double* __restrict__ G) {
+                                const double* __restrict__ tG, int tg_pairs, const void* __restrict__ cgrad,
+                                int cgrad_f32, const double* __restrict__ fext, double h2, double* __restrict__ G) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= nv) return;
     if (dir[v]) { G[3 * v] = 0.0; G[3 * v + 1] = 0.0; G[3 * v + 2] = 0.0; return; }
     double e0 = 0.0, e1 = 0.0, e2 = 0.0;
-    for (int k = vt_off[v]; k < vt_off[v + 1]; ++k) {
-        const int ent = vt_ent[k];
-        const int64_t t = ent >> 2;
-        const int a = ent & 3;
-        e0 += tG[12 * t + 3 * a]; e1 += tG[12 * t + 3 * a + 1]; e2 += tG[12 * t + 3 * a + 2];
+    if (tg_pairs) {   // per-tet gradients as FP32 pairs (mixed path): summed as pairs
+        const float2* g = reinterpret_cast<const float2*>(tG);
+        dfl s0 = df_make(0.f), s1 = df_make(0.f), s2 = df_make(0.f);
+        for (int k = vt_off[v]; k < vt_off[v + 1]; ++k) {
+            const int ent = vt_ent[k];
+            const int64_t t = ent >> 2;
+            const int a = ent & 3;
+            s0 = df_add(s0, ld_pair(g + 12 * t + 3 * a));
+            s1 = df_add(s1, ld_pair(g + 12 * t + 3 * a + 1));
+            s2 = df_add(s2, ld_pair(g + 12 * t + 3 * a + 2));
+        }
+        e0 = df_to_double(s0); e1 = df_to_double(s1); e2 = df_to_double(s2);
+    } else {
+        for (int k = vt_off[v]; k < vt_off[v + 1]; ++k) {
+            const int ent = vt_ent[k];
+            const int64_t t = ent >> 2;
+            const int a = ent & 3;
+            e0 += tG[12 * t + 3 * a]; e1 += tG[12 * t + 3 * a + 1]; e2 += tG[12 * t + 3 * a + 2];
+        }
     }
     double c0, c1, c2;
     if (cgrad_f32) {
@@ -1514,10 +1724,38 @@ static cudaError_t seg_sum(Ctx& c, const SegRed& R, const double* in, int64_t in
     return cudaGetLastError();
 }
 
+// the mixed path's view of the elastic tables (pairs) and its input split
+static ElasticViewDF df_view(Ctx& c) {
+    NewtonState& N = *c.newton;
+    auto pair = [](double v) {
+        const float h = (float)v;
+        return dfl{h, (float)(v - (double)h)};
+    };
+    return ElasticViewDF{N.ntsys, N.tets.p, reinterpret_cast<const float2*>(N.Dm2.p),
+                         reinterpret_cast<const float2*>(N.vol2.p), pair(N.mu), pair(N.lam), pair(1.0 / 3.0),
+                         pair(1.0 / 5.0), pair(2.0 / 3.0)};
+}
+static cudaError_t split_pairs(Ctx& c, const double* v, const double* X, DBuf<float>& hi, DBuf<float>& lo) {
+    NewtonState& N = *c.newton;
+    k_split_pairs<<<nblk(N.nsys, 256), 256, 0, c.stream>>>(N.nsys, v, X, reinterpret_cast<float4*>(hi.p),
+                                                          reinterpret_cast<float4*>(lo.p));
+    return cudaGetLastError();
+}
+
 cudaError_t nh_eval(Ctx& c, const double* x, bool want_hess) {
     NewtonState& N = *c.newton;
     ElasticView E{N.ntsys, N.tets.p, N.Dminv.p, N.vol.p, N.Xsys.p, N.mu, N.lam};
-    if (N.ntsys > 0) {
+    if (N.ntsys > 0 && c.P.precision == IPC_PREC_MIXED) {
+        GMCP_CUDA_TRY(split_pairs(c, x, N.Xsys.p, N.uh4, N.ul4));
+        const unsigned g = nblk(N.ntsys, 128);
+        const ElasticViewDF D = df_view(c);
+        const float4* uh = reinterpret_cast<const float4*>(N.uh4.p);
+        const float4* ul = reinterpret_cast<const float4*>(N.ul4.p);
+        float2* tg = reinterpret_cast<float2*>(N.tG.p);
+        if (want_hess) k_nh_eval_df<true><<<g, 128, 0, c.stream>>>(D, uh, ul, N.tE.p, tg, N.tH32.p, N.ebad.p, N.tet_env.p);
+        else k_nh_eval_df<false><<<g, 128, 0, c.stream>>>(D, uh, ul, N.tE.p, tg, nullptr, N.ebad.p, N.tet_env.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    } else if (N.ntsys > 0) {
         const bool f32 = c.P.precision == IPC_PREC_MIXED;
         const unsigned g = nblk(N.ntsys, 128);
         if (!want_hess)
@@ -1535,7 +1773,15 @@ cudaError_t nh_energy_multi(Ctx& c, const double* x, const double* p, const doub
                             bool delta) {
     NewtonState& N = *c.newton;
     ElasticView E{N.ntsys, N.tets.p, N.Dminv.p, N.vol.p, N.Xsys.p, N.mu, N.lam};
-    if (N.ntsys > 0) {
+    if (N.ntsys > 0 && c.P.precision == IPC_PREC_MIXED) {
+        GMCP_CUDA_TRY(split_pairs(c, x, N.Xsys.p, N.uh4, N.ul4));
+        GMCP_CUDA_TRY(split_pairs(c, p, nullptr, N.ph4, N.pl4));
+        k_nh_energy_multi_df<<<nblk(N.ntsys, 128), 128, 0, c.stream>>>(
+            df_view(c), reinterpret_cast<const float4*>(N.uh4.p), reinterpret_cast<const float4*>(N.ul4.p),
+            reinterpret_cast<const float4*>(N.ph4.p), reinterpret_cast<const float4*>(N.pl4.p), alphas_env, 8,
+            N.tet_env.p, na, N.tE8.p, delta ? N.tE.p : nullptr);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    } else if (N.ntsys > 0) {
         k_nh_energy_multi<<<nblk(N.ntsys, 128), 128, 0, c.stream>>>(E, x, p, alphas_env, 8, N.tet_env.p, na,
                                                                    N.tE8.p, delta ? N.tE.p : nullptr);
         GMCP_CUDA_TRY(cudaGetLastError());
@@ -1547,7 +1793,15 @@ cudaError_t nh_feasible_multi(Ctx& c, const double* x, const double* p, const do
                               int slot) {
     NewtonState& N = *c.newton;
     ElasticView E{N.ntsys, N.tets.p, N.Dminv.p, N.vol.p, N.Xsys.p, N.mu, N.lam};
-    if (N.ntsys > 0) {
+    if (N.ntsys > 0 && c.P.precision == IPC_PREC_MIXED) {
+        GMCP_CUDA_TRY(split_pairs(c, x, N.Xsys.p, N.uh4, N.ul4));
+        GMCP_CUDA_TRY(split_pairs(c, p, nullptr, N.ph4, N.pl4));
+        k_nh_feasible_df<<<nblk(N.ntsys, 128), 128, 0, c.stream>>>(
+            df_view(c), reinterpret_cast<const float4*>(N.uh4.p), reinterpret_cast<const float4*>(N.ul4.p),
+            reinterpret_cast<const float4*>(N.ph4.p), reinterpret_cast<const float4*>(N.pl4.p), alphas_env, 8,
+            N.tet_env.p, na, N.tE8.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    } else if (N.ntsys > 0) {
         k_nh_feasible<<<nblk(N.ntsys, 128), 128, 0, c.stream>>>(E, x, p, alphas_env, 8, N.tet_env.p, na, N.tE8.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
@@ -1559,7 +1813,8 @@ cudaError_t assemble_grad(Ctx& c, const double* x, const double* xhat, const voi
     NewtonState& N = *c.newton;
     const double h2 = c.prm.h * c.prm.h;
     k_assemble_grad<<<nblk(N.nsys, 256), 256, 0, c.stream>>>(N.nsys, x, xhat, N.mass.p, N.dir.p, N.vte_off.p,
-                                                            N.vte.p, N.tG.p, cgrad, cgrad_f32 ? 1 : 0, N.fext, h2,
+                                                            N.vte.p, N.tG.p, c.P.precision == IPC_PREC_MIXED ? 1 : 0,
+                                                            cgrad, cgrad_f32 ? 1 : 0, N.fext, h2,
                                                             G);
     return cudaGetLastError();
 }
@@ -2169,6 +2424,20 @@ cudaError_t newton_setup(Ctx& c) {
     GMCP_CUDA_TRY(N.tE.ensure((size_t)nt + 1));
     GMCP_CUDA_TRY(N.tG.ensure(12 * (size_t)nt + 12));
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
+    if (f32) {
+        // Dm^-1 and the volumes as pairs, the input splits' buffers
+        std::vector<float> dm2(18 * (size_t)nt + 18), vol2(2 * (size_t)nt + 2);
+        auto put = [](float* d, double v) {
+            const float h = (float)v;
+            d[0] = h;
+            d[1] = (float)(v - (double)h);
+        };
+        for (size_t k = 0; k < 9 * (size_t)nt; ++k) put(&dm2[2 * k], Dminv[k]);
+        for (size_t k = 0; k < (size_t)nt; ++k) put(&vol2[2 * k], vol[k]);
+        GMCP_CUDA_TRY(N.Dm2.upload(dm2.data(), dm2.size(), s));
+        GMCP_CUDA_TRY(N.vol2.upload(vol2.data(), vol2.size(), s));
+        for (DBuf<float>* b : {&N.uh4, &N.ul4, &N.ph4, &N.pl4}) GMCP_CUDA_TRY(b->ensure(4 * (size_t)nv + 4));
+    }
     if (f32) GMCP_CUDA_TRY(N.tH32.ensure(HBlk<float>::kPerTet * ((size_t)nt + 1)));
     else GMCP_CUDA_TRY(N.tH64.ensure(HBlk<double>::kPerTet * ((size_t)nt + 1)));
     GMCP_CUDA_TRY(N.tE8.ensure(8 * (size_t)nt + 8));

