@@ -322,7 +322,7 @@ std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) 
             (uintptr_t)c.dxm.p, (uintptr_t)c.scal.p, (uintptr_t)c.mboxf_in.p, (uintptr_t)c.tri_f32.p,
             (uintptr_t)c.ym32.p, (uintptr_t)c.item_mask.p, (uintptr_t)c.item_mid.p, (uintptr_t)c.tri_mid64.p,
             (uintptr_t)c.tri_mid32.p, (uintptr_t)c.mtri_e32.p, (uintptr_t)c.mtri_pre.p,
-            (uintptr_t)c.use_mtri_pre};
+            (uintptr_t)c.use_mtri_pre, (uintptr_t)c.use_mtri_e32};
 }
 
 // Capture one pass on the context's private capture stream (nothing runs);
@@ -1411,6 +1411,7 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
         }
         // the next passes' choice of the face pre-filter's master table
         c.use_mtri_pre = c.P.precision == IPC_PREC_MIXED && (int64_t)c.pin->flags[16] >= 8 * c.nmt;
+        c.use_mtri_e32 = c.P.precision == IPC_PREC_MIXED && (int64_t)c.pin->flags[16] >= c.nmt;
     }
     if (energy_host) *energy_host = c.pin->energy;
     if (counts) {

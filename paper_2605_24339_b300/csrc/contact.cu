@@ -821,7 +821,7 @@ __device__ __forceinline__ void bary_rel(V3<float> q, V3<float> e1, V3<float> e2
 template <bool PRE>
 __device__ __forceinline__ void mtri_edges(const SceneView& S, const double* xm, const float* mtri_e, int64_t m,
                                            V3<float>& e1, V3<float>& e2) {
-    if (PRE) {
+    if (PRE && mtri_e) {
         const float* E = mtri_e + 8 * m;
         e1 = {E[0], E[1], E[2]};
         e2 = {E[3], E[4], E[5]};
@@ -1861,14 +1861,16 @@ __global__ void k_reduce_final(const double* __restrict__ part, int64_t n, doubl
 // on stream s
 cudaError_t master_tables(Ctx& c, const double* xm, cudaStream_t s) {
     GMCP_CUDA_TRY(c.ym32.ensure(4 * (size_t)c.nmv + 4));
-    GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
-    GMCP_CUDA_TRY(c.mtri_pre.ensure((size_t)kMtriPre * c.nmt + kMtriPre));
+    if (c.use_mtri_e32) GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
+    if (c.use_mtri_pre) GMCP_CUDA_TRY(c.mtri_pre.ensure((size_t)kMtriPre * c.nmt + kMtriPre));
     if (c.nmv == 0) return cudaSuccess;
     k_master_f32<<<(unsigned)((c.nmv + 255) / 256), 256, 0, s>>>(c.view(), xm, (float4*)c.ym32.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.nmt == 0) return cudaSuccess;
-    k_mtri_e32<<<(unsigned)((c.nmt + 255) / 256), 256, 0, s>>>(c.view(), xm, c.mtri_e32.p);
-    GMCP_CUDA_TRY(cudaGetLastError());
+    if (c.use_mtri_e32) {
+        k_mtri_e32<<<(unsigned)((c.nmt + 255) / 256), 256, 0, s>>>(c.view(), xm, c.mtri_e32.p);
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
     // the face pre-filter's per-triangle table pays only when most master
     // triangles take many face items (see Ctx::use_mtri_pre)
     if (!c.use_mtri_pre) return cudaSuccess;
@@ -1941,8 +1943,8 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
         GMCP_CUDA_TRY(c.ym32.ensure(4 * (size_t)c.nmv + 4));
         GMCP_CUDA_TRY(c.tri_mid64.ensure(4 * (size_t)c.ns + 8));
         GMCP_CUDA_TRY(c.tri_mid32.ensure(12 * (size_t)c.ns + 12));
-        GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
-        GMCP_CUDA_TRY(c.mtri_pre.ensure((size_t)kMtriPre * c.nmt + kMtriPre));
+        if (c.use_mtri_e32) GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
+        if (c.use_mtri_pre) GMCP_CUDA_TRY(c.mtri_pre.ensure((size_t)kMtriPre * c.nmt + kMtriPre));
         // the master's FP32 tables depend on xm alone: already enqueued at
         // the start of a contact pass (c.master_pre), else beside the frame
         // kernel on the side stream when the pass has forked one
@@ -1979,7 +1981,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
                                                       n_list, n_list2, counters, cert,
                                                       f32pre ? c.tri_mid64.p : nullptr,
                                                       f32pre ? c.tri_mid32.p : nullptr,
-                                                      f32pre ? c.mtri_e32.p : nullptr);
+                                                      f32pre && c.use_mtri_e32 ? c.mtri_e32.p : nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (kMaster) {
         k_items<NK, T, MODE><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,

@@ -435,6 +435,10 @@ struct Ctx {
     // per item; set after a contact pass whose sample items outnumbered the
     // master triangles eightfold (results are the same either way)
     bool use_mtri_pre = false;
+    // the master triangles' FP32 edges are tabled per pass only when the
+    // last pass had at least one face item per master triangle (else the
+    // middle stage forms them from xm: the same values)
+    bool use_mtri_e32 = false;
     // master entries of the samples (gradient rows and Hessian blocks of the
     // master vertices) and their counting sort by destination row
     int64_t ml_cap = 0;
