@@ -248,17 +248,31 @@ __device__ void nh_hessian_blocks(const In* Fd, In lnJd, In mud, In lamd, const 
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j)
             A[3 * i + j] = (i == j) ? mu + (c + lam) / (sg[i] * sg[i]) : lam / (sg[i] * sg[j]);
-    jacobi3(A, W);
+    // its projection is A itself where A is certainly positive definite
+    // (Sylvester's criterion, the determinant above 1e-6 (FP32) / 1e-12
+    // (FP64) of the cube of its largest entry, far above rounding);
+    // otherwise from its eigen-decomposition
     R Ah[9];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) {
-            R sum = R(0);
-            for (int k = 0; k < 3; ++k) {
-                const R l = A[4 * k];
-                if (l > R(0)) sum += W[3 * i + k] * l * W[3 * j + k];
+    const R m2 = A[0] * A[4] - A[1] * A[3];
+    const R d3 = A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) +
+                 A[2] * (A[3] * A[7] - A[4] * A[6]);
+    R amax = R(0);
+    for (int q = 0; q < 9; ++q) amax = fmax(amax, fabs(A[q]));
+    const R tol_pd = sizeof(R) == 4 ? R(1e-6) : R(1e-12);
+    if (A[0] > R(0) && m2 > R(0) && d3 > tol_pd * amax * amax * amax) {
+        for (int q = 0; q < 9; ++q) Ah[q] = A[q];
+    } else {
+        jacobi3(A, W);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                R sum = R(0);
+                for (int k = 0; k < 3; ++k) {
+                    const R l = A[4 * k];
+                    if (l > R(0)) sum += W[3 * i + k] * l * W[3 * j + k];
+                }
+                Ah[3 * i + j] = sum;
             }
-            Ah[3 * i + j] = sum;
-        }
+    }
     // twist / flip eigenvalues per pair (0,1), (0,2), (1,2), clamped
     R lp[3], lm[3];   // (lf + lt)/2 and (lf - lt)/2
     for (int k = 0; k < 3; ++k) {
