@@ -493,7 +493,7 @@ def precision_measurement(dev):
         "position_rel_to_displacement": float(np.linalg.norm(x32 - x64) / disp) if disp > 0 else 0.0,
         "incremental_potential_rel": abs(r32["energy"] - r64["energy"]) / abs(r64["energy"]),
         "residual": [r64["residual"], r32["residual"]],
-        "note": "mixed (FP32 barrier, gradient, Hessian, PCG vectors and matrix) against FP64, same start state"}
+        "note": "mixed (FP32 barrier, gradient, Hessian, PCG vectors and matrix; double-float elastic energy and gradient) against FP64, same start state"}
     return out
 
 
@@ -775,6 +775,30 @@ def newton_measurement(dev, start_step=20, n_states=4):
     return out
 
 
+def fingertip_step_scene(n_env):
+    """The batched time-step workload: n_env fingertip environments with
+    tets (5 pads of 16-128 quads of 0.25 mm, 2 tet layers, around a perturbed
+    convex object of 2k-80k triangles, each pad 1.5 dhat pressed toward it,
+    top faces driven at 0.5 mm/s), generated in spawn worker processes past
+    16 environments.  Returns (parts [(scene, x0) per env], the concatenated
+    scene, its x0)."""
+    from paper_2605_24339_b300 import scenes as S
+    dhat = 1e-4
+    args = (5, (16, 128), 0.25e-3, 2, 0.5e-3, (2000, 80000), 15e-3, dhat, 1e5, 1e-3, 0.5e-3, 100, 3, 1,
+            1.5 * dhat, True)
+    workers = max(1, min(32, os.cpu_count() or 1))
+    if n_env > 16 and workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(S._fingertip_env, range(n_env), *[[a] * n_env for a in args],
+                                chunksize=max(1, n_env // (4 * workers))))
+    else:
+        parts = [S._fingertip_env(e, *args) for e in range(n_env)]
+    sc = S.concat_envs([p[0] for p in parts], name="fingertip_batch")
+    return parts, sc, np.concatenate([p[1] for p in parts])
+
+
 def batched_step_measurement(dev, n_env=16, steps=3, alone_envs=16):
     """Batched time steps (ipc_newton_step_envs): n_env fingertip environments
     of the batched workload's recipe with their tetrahedra (5 pads of 16-128
@@ -790,23 +814,9 @@ def batched_step_measurement(dev, n_env=16, steps=3, alone_envs=16):
     per second."""
     import torch
     from paper_2605_24339_b300 import binding
-    from paper_2605_24339_b300 import scenes as S
-    dhat = 1e-4
-    args = (5, (16, 128), 0.25e-3, 2, 0.5e-3, (2000, 80000), 15e-3, dhat, 1e5, 1e-3, 0.5e-3, 100, 3, 1,
-            1.5 * dhat, True)
     t0 = time.perf_counter()
-    workers = max(1, min(32, os.cpu_count() or 1))
-    if n_env > 16 and workers > 1:
-        import concurrent.futures as cf
-        import multiprocessing as mp
-        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
-            parts = list(ex.map(S._fingertip_env, range(n_env), *[[a] * n_env for a in args],
-                                chunksize=max(1, n_env // (4 * workers))))
-    else:
-        parts = [S._fingertip_env(e, *args) for e in range(n_env)]
+    parts, sc, x0 = fingertip_step_scene(n_env)
     gen_s = time.perf_counter() - t0
-    sc = S.concat_envs([p[0] for p in parts], name="fingertip_batch")
-    x0 = np.concatenate([p[1] for p in parts])
     top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
     vd = torch.as_tensor(sc.v_dirichlet, device="cuda")
     out = {"workload": f"fingertip_batch {n_env} envs x 5 pads (16-128 quads, 2 tet layers, 4 samples/tri) vs "
@@ -1139,6 +1149,42 @@ def run_newton(args):
     print(json.dumps({"newton_steps": args.steps, "last": {k: st[k] for k in ("status", "newton_iters", "pcg_iters")}}))
 
 
+def run_profile_step(args):
+    """One time step between cudaProfilerStart and cudaProfilerStop, for a
+    launch list of that step alone (ncu --profile-from-start off): with
+    --prof-workload batch the batched time-step workload (--step-envs
+    environments, three steps first), with gel the gel_on_terrain press in
+    mixed precision (21 steps first, in contact from step 10)."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    if args.prof_workload == "batch":
+        _, sc, x0 = fingertip_step_scene(args.step_envs)
+        warm = 3
+    else:
+        sc = S.gel_on_terrain(n_quads=args.newton_quads)
+        x0 = sc.X.copy()
+        warm = 21
+    ctx = binding.Context(sc, precision=args.precision)
+    x = torch.as_tensor(x0, device="cuda")
+    vd = torch.as_tensor(sc.v_dirichlet, device="cuda")
+    top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
+    v = vd.clone()
+    step = (lambda: ctx.newton_step_envs(x, v)[1]) if args.prof_workload == "batch" else \
+        (lambda: [ctx.newton_step(x, v)])
+    for _ in range(warm):
+        step()
+        v[top] = vd[top]
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    per = step()
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    print(json.dumps({"workload": args.prof_workload, "newton_iters_max": max(q["newton_iters"] for q in per),
+                      "pcg_iters_max": max(q["pcg_iters"] for q in per),
+                      "statuses": sorted(set(q["status"] for q in per))}))
+
+
 def run_reference(args):
     """The reference arm: the FP64 CPU oracle (the paper ships no code) on all
     host cores; each step one pass over a window of the workload per core."""
@@ -1184,11 +1230,13 @@ def main():
                     help="environments in the batched time-step measurement")
     ap.add_argument("--dense-quads", type=int, default=256,
                     help="--mode dense_passes: gel pad quads per side (256 = the measured workload)")
+    ap.add_argument("--prof-workload", default="gel", choices=["gel", "batch"],
+                    help="--mode profstep: the time step captured (gel_on_terrain press, or the batched step)")
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
     ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "batchstep", "patch",
                                                        "dualmap", "faceclip",
-                                                       "mastergrad", "dense", "dense_passes", "peaks"],
+                                                       "mastergrad", "dense", "dense_passes", "peaks", "profstep"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
                          "training steps or time steps (command lines for profilers); batch: "
                          "the batched measurement alone, --steps timed passes")
@@ -1218,6 +1266,8 @@ def main():
         print(json.dumps(measure_alu_peaks(0)), flush=True)
     elif args.mode == "patch":
         print(json.dumps(patch_measurement(0)), flush=True)
+    elif args.mode == "profstep":
+        run_profile_step(args)
     elif args.mode == "batchstep":
         print(json.dumps(batched_step_measurement(0, n_env=args.step_envs, steps=max(1, args.steps))), flush=True)
     elif args.mode == "batch":

@@ -290,6 +290,11 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
  * ipc_step_stats).  Elasticity: compressible Neo-Hookean,
  * mu/2 (tr F^T F - 3) - mu ln J + lambda/2 (ln J)^2 per tet with its 9x9
  * dP/dF projected onto the PSD cone.
+ * Precision: IPC_PREC_FP64 evaluates every term in FP64; IPC_PREC_MIXED
+ * takes the contact terms of the mixed contact pass, FP32 Hessian blocks,
+ * matrix and PCG vectors, and the elastic energy, gradient and inversion
+ * test in double-float (FP32 pairs, ~48 bits), with energies, residuals
+ * and the line-search test summed in FP64.
  *  x_dev [n_vert][3] (device, FP64) holds x^t on entry and x^{t+1} on exit;
  *  v_dev the velocity, updated to (x^{t+1} - x^t) / h; Dirichlet vertices
  *  are moved to x + h v (their motion must be admissible);
