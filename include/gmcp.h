@@ -275,6 +275,24 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
                             double* energy_host, void* grad_dev, ipc_bsr_view* hess,
                             double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts);
 
+/* ipc_contact_pass with the pass's per-step inputs in host memory: the
+ * positions xs_host and displacements dxs_host ([n_svert][3] FP64, the
+ * slave-surface vertices in the order ipc_slave_vertices returns, the only
+ * pad vertices the pass reads) are copied to the device and scattered into
+ * x_dev and dx_dev (written: x_dev[ids[k]] = xs_host[k]), then the pass runs
+ * as ipc_contact_pass(ctx, x_dev, xm0_dev, xm1_dev, dx_dev, ...) with the
+ * same outputs.  The displacements' copy runs on a copy stream behind the
+ * positions' while the broad phase runs (only the swept query and the
+ * sample evaluation read them), and the copies are part of the pass's CUDA
+ * graph.  Both host buffers must be page-locked (cudaHostAlloc /
+ * cudaHostRegister; else IPC_ERR_ARG) and must not change until the call
+ * returns; dxs_host and dx_dev are both given or both NULL (no step bound).
+ * The results are bitwise those of the scatter followed by ipc_contact_pass. */
+ipc_status ipc_contact_pass_host(ipc_ctx* ctx, const double* xs_host, const double* dxs_host, double* x_dev,
+                                 double* dx_dev, const double* xm0_dev, const double* xm1_dev,
+                                 double* energy_dev, double* energy_host, void* grad_dev, ipc_bsr_view* hess,
+                                 double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts);
+
 /* One implicit-Euler time step (paper Sec. 2.1 problem statement): minimises
  *   E(x) = 1/2 (x - xhat)^T M (x - xhat) + h^2 (Psi_NH(x) + Psi_GMCP(x)),
  *   xhat = x^t + h v^t + h^2 gravity,

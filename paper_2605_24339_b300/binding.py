@@ -139,6 +139,9 @@ def lib():
     L.ipc_contact_pass.restype = C.c_int
     L.ipc_contact_pass.argtypes = [P, P, P, P, P, P, C.POINTER(C.c_double), P, C.POINTER(BsrView),
                                    C.POINTER(C.c_double), C.POINTER(CcdInfo), C.POINTER(SampleCounts)]
+    L.ipc_contact_pass_host.restype = C.c_int
+    L.ipc_contact_pass_host.argtypes = [P, P, P, P, P, P, P, P, C.POINTER(C.c_double), P, C.POINTER(BsrView),
+                                        C.POINTER(C.c_double), C.POINTER(CcdInfo), C.POINTER(SampleCounts)]
     L.ipc_profile.restype = C.c_int
     L.ipc_profile.argtypes = [P, C.c_int32, C.c_int32, P, P, P, C.POINTER(C.c_int32)]
     L.ipc_ws_create.restype = C.c_int
@@ -460,6 +463,24 @@ class Context:
                      energy_dev=None, grad_out=None, host_alpha=True):
         """ipc_contact_pass: barrier evaluation and step bound sharing one broad
         phase.  hess="view" returns the raw BsrView (no copy)."""
+        return self._contact_pass(None, None, x, xm0, dx, xm1, grad, hess, counts, energy_dev, grad_out,
+                                  host_alpha)
+
+    def contact_pass_host(self, xs_host, dxs_host, x, dx, xm0, xm1=None, grad=True, hess=True, counts=True,
+                          energy_dev=None, grad_out=None, host_alpha=True):
+        """ipc_contact_pass_host: the slave vertices' positions xs_host and
+        displacements dxs_host (page-locked CPU tensors [n_svert, 3], FP64, in
+        slave_vertices() order; dxs_host may be None with dx None) copied in
+        and scattered into x and dx inside the pass; outputs as contact_pass."""
+        t = self.torch
+        for h in (xs_host, dxs_host):
+            if h is not None and (h.device.type != "cpu" or h.dtype != t.float64 or not h.is_contiguous()):
+                raise ValueError("host inputs must be contiguous FP64 CPU tensors")
+        return self._contact_pass(xs_host, dxs_host, x, xm0, dx, xm1, grad, hess, counts, energy_dev, grad_out,
+                                  host_alpha)
+
+    def _contact_pass(self, xs_host, dxs_host, x, xm0, dx, xm1, grad, hess, counts, energy_dev, grad_out,
+                      host_alpha):
         t = self.torch
         x, xm0, dx, xm1 = self._as(x), self._as(xm0), self._as(dx), self._as(xm1)
         gdt = t.float32 if self.precision == "mixed" else t.float64
@@ -472,11 +493,16 @@ class Context:
         a = C.c_double()
         info = CcdInfo()
         want_a = dx is not None and host_alpha
-        self._check(lib().ipc_contact_pass(
-            self.h, _ptr(x), _ptr(xm0), _ptr(xm1), _ptr(dx), _ptr(energy_dev),
-            None if energy_dev is not None else C.byref(e), _ptr(g),
-            C.byref(bv) if hess else None, C.byref(a) if want_a else None,
-            C.byref(info) if want_a else None, C.byref(sc) if counts else None))
+        outs = (_ptr(energy_dev), None if energy_dev is not None else C.byref(e), _ptr(g),
+                C.byref(bv) if hess else None, C.byref(a) if want_a else None,
+                C.byref(info) if want_a else None, C.byref(sc) if counts else None)
+        if xs_host is None:
+            self._check(lib().ipc_contact_pass(self.h, _ptr(x), _ptr(xm0), _ptr(xm1), _ptr(dx), *outs))
+        else:
+            self._check(lib().ipc_contact_pass_host(
+                self.h, C.c_void_p(xs_host.data_ptr()),
+                None if dxs_host is None else C.c_void_p(dxs_host.data_ptr()), _ptr(x), _ptr(dx), _ptr(xm0),
+                _ptr(xm1), *outs))
         out = dict(energy=e.value if energy_dev is None else None, grad=g)
         if counts:
             out["counts"] = dict(face=sc.face, edge=sc.edge, point=sc.point, guard=sc.guard,

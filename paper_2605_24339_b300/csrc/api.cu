@@ -176,6 +176,10 @@ struct ContactPassArgs {
     double* edev;
     void* grad;
     bool hess, counts, host_energy, want_alpha, lazy;
+    // host inputs (ipc_contact_pass_host): the slave vertices' positions and
+    // displacements in page-locked host memory, scattered into x and dx
+    const double* xs_host = nullptr;
+    const double* dxs_host = nullptr;
 };
 
 // Everything one pass queues (no synchronisation): the master displacement,
@@ -183,6 +187,28 @@ struct ContactPassArgs {
 // step bounds, and (lazy) the copies of host-visible results and capacity
 // flags into the pinned area.
 cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
+    // host inputs: the slave vertices' positions are copied and scattered
+    // first; their displacements follow on the copy stream (after the
+    // positions on the bus) while the broad phase runs, and the two readers
+    // of dx (the swept query and the sample evaluation) wait for them
+    bool dx_wait = false;
+    if (A.xs_host && c.n_svert > 0) {
+        const size_t nb = sizeof(double) * 3 * (size_t)c.n_svert;
+        const unsigned g = (unsigned)((c.n_svert + 255) / 256);
+        GMCP_CUDA_TRY(cudaMemcpyAsync(c.xs_stage.p, A.xs_host, nb, cudaMemcpyHostToDevice, c.stream));
+        if (A.dxs_host && A.dx) {
+            GMCP_CUDA_TRY(cudaEventRecord(c.ev_xin, c.stream));
+            GMCP_CUDA_TRY(cudaStreamWaitEvent(c.h2d_stream, c.ev_xin, 0));
+            GMCP_CUDA_TRY(cudaMemcpyAsync(c.dxs_stage.p, A.dxs_host, nb, cudaMemcpyHostToDevice, c.h2d_stream));
+            k_scatter_slave<<<g, 256, 0, c.h2d_stream>>>(c.svert.p, c.n_svert, c.dxs_stage.p,
+                                                         const_cast<double*>(A.dx));
+            GMCP_CUDA_TRY(cudaGetLastError());
+            GMCP_CUDA_TRY(cudaEventRecord(c.ev_dxin, c.h2d_stream));
+            dx_wait = true;
+        }
+        k_scatter_slave<<<g, 256, 0, c.stream>>>(c.svert.p, c.n_svert, c.xs_stage.p, const_cast<double*>(A.x));
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
     const double* dxm = nullptr;
     if (A.dx && A.xm1) {
         GMCP_CUDA_TRY(c.dxm.ensure(3 * (size_t)c.nmv + 3));
@@ -223,6 +249,7 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
         if (!c.ev_join) GMCP_CUDA_TRY(cudaEventCreateWithFlags(&c.ev_join, cudaEventDisableTiming));
         GMCP_CUDA_TRY(cudaEventRecord(c.ev_fork, c.stream));
         GMCP_CUDA_TRY(cudaStreamWaitEvent(c.ccd_stream, c.ev_fork, 0));
+        if (dx_wait) GMCP_CUDA_TRY(cudaStreamWaitEvent(c.ccd_stream, c.ev_dxin, 0));
         cudaStream_t main = c.stream;
         c.stream = c.ccd_stream;
         const cudaError_t e = bp_ccd_accd(c, A.x, A.dx, A.xm0, dxm, c.u64_tmp.p + 1, c.i64_tmp.p + 8, true, true);
@@ -235,6 +262,7 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
         GMCP_CUDA_TRY(cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
         ctr = c.i64_tmp.p;
     }
+    if (dx_wait) GMCP_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.ev_dxin, 0));
     GMCP_CUDA_TRY(contact_eval(c, A.x, A.xm0, A.edev, A.grad, A.hess, ctr, A.dx, dxm,
                                A.dx ? c.u64_tmp.p : nullptr));
     if (fork)
@@ -299,7 +327,8 @@ cudaError_t grow_after_overflow(Ctx& c) {
 
 // the arguments and capacities a captured pass depends on
 std::vector<uintptr_t> contact_pass_key(const Ctx& c, const ContactPassArgs& A) {
-    return {(uintptr_t)A.x, (uintptr_t)A.xm0, (uintptr_t)A.xm1, (uintptr_t)A.dx, (uintptr_t)A.edev,
+    return {(uintptr_t)A.x, (uintptr_t)A.xm0, (uintptr_t)A.xm1, (uintptr_t)A.dx, (uintptr_t)A.xs_host,
+            (uintptr_t)A.dxs_host, (uintptr_t)c.xs_stage.p, (uintptr_t)c.dxs_stage.p, (uintptr_t)A.edev,
             (uintptr_t)A.grad, (uintptr_t)A.hess, (uintptr_t)A.counts, (uintptr_t)A.host_energy,
             (uintptr_t)A.want_alpha, (uintptr_t)c.cap_f, (uintptr_t)c.cap_e, (uintptr_t)c.cap_p,
             (uintptr_t)c.cell_ent.n, (uintptr_t)c.stream, (uintptr_t)c.tune_samples_bpsm,
@@ -1177,6 +1206,9 @@ void ipc_destroy(ipc_ctx* ctx) {
     c.pcg_graph.reset();
     if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
     if (c.ccd_stream) cudaStreamDestroy(c.ccd_stream);
+    if (c.h2d_stream) cudaStreamDestroy(c.h2d_stream);
+    if (c.ev_xin) cudaEventDestroy(c.ev_xin);
+    if (c.ev_dxin) cudaEventDestroy(c.ev_dxin);
     if (c.aux_stream) cudaStreamDestroy(c.aux_stream);
     if (c.ev_touch0) cudaEventDestroy(c.ev_touch0);
     if (c.ev_touch1) cudaEventDestroy(c.ev_touch1);
@@ -1369,10 +1401,11 @@ ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_
     return IPC_OK;
 }
 
-ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev,
-                            const double* xm1_dev, const double* dx_dev, double* energy_dev,
-                            double* energy_host, void* grad_dev, ipc_bsr_view* hess,
-                            double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts) {
+static ipc_status contact_pass_impl(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev,
+                                    const double* xm1_dev, const double* dx_dev, double* energy_dev,
+                                    double* energy_host, void* grad_dev, ipc_bsr_view* hess,
+                                    double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts,
+                                    const double* xs_host, const double* dxs_host) {
     if (!ctx) return IPC_ERR_ARG;
     Ctx& c = ctx->c;
     if (!x_dev || (!xm0_dev && c.nmv > 0)) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_contact_pass: NULL positions");
@@ -1384,7 +1417,7 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
     double* edev = energy_dev;
     if (energy_host && !energy_dev) edev = c.scal.p;
     ContactPassArgs A{x_dev, xm0_dev, xm1_dev, dx_dev, edev, grad_dev, hess != nullptr, counts != nullptr,
-                      energy_host != nullptr, want_alpha, lazy};
+                      energy_host != nullptr, want_alpha, lazy, xs_host, dxs_host};
     if (!lazy) {
         API_CK(ctx, enqueue_contact_pass(c, A));
     } else {
@@ -1441,6 +1474,45 @@ ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0
         }
     }
     return IPC_OK;
+}
+
+ipc_status ipc_contact_pass(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev,
+                            const double* xm1_dev, const double* dx_dev, double* energy_dev,
+                            double* energy_host, void* grad_dev, ipc_bsr_view* hess,
+                            double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts) {
+    return contact_pass_impl(ctx, x_dev, xm0_dev, xm1_dev, dx_dev, energy_dev, energy_host, grad_dev, hess,
+                             alpha_host, info, counts, nullptr, nullptr);
+}
+
+// a pointer into page-locked host memory (the copies are captured into
+// the pass's graph, which pageable memory cannot be)
+static bool page_locked(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+ipc_status ipc_contact_pass_host(ipc_ctx* ctx, const double* xs_host, const double* dxs_host, double* x_dev,
+                                 double* dx_dev, const double* xm0_dev, const double* xm1_dev,
+                                 double* energy_dev, double* energy_host, void* grad_dev, ipc_bsr_view* hess,
+                                 double* alpha_host, ipc_ccd_info* info, ipc_sample_counts* counts) {
+    if (!ctx) return IPC_ERR_ARG;
+    Ctx& c = ctx->c;
+    if (!xs_host || !x_dev || (dxs_host && !dx_dev) || (dx_dev && !dxs_host))
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_contact_pass_host: NULL pointer (dxs_host and dx_dev go together)");
+    if (c.n_svert > 0 && (!page_locked(xs_host) || (dxs_host && !page_locked(dxs_host))))
+        return fail_ctx(ctx, IPC_ERR_ARG, "ipc_contact_pass_host: host inputs must be page-locked");
+    API_CK(ctx, cudaSetDevice(c.device));
+    if (!c.h2d_stream) API_CK(ctx, cudaStreamCreateWithFlags(&c.h2d_stream, cudaStreamNonBlocking));
+    if (!c.ev_xin) API_CK(ctx, cudaEventCreateWithFlags(&c.ev_xin, cudaEventDisableTiming));
+    if (!c.ev_dxin) API_CK(ctx, cudaEventCreateWithFlags(&c.ev_dxin, cudaEventDisableTiming));
+    API_CK(ctx, c.xs_stage.ensure(3 * (size_t)c.n_svert + 3));
+    if (dxs_host) API_CK(ctx, c.dxs_stage.ensure(3 * (size_t)c.n_svert + 3));
+    return contact_pass_impl(ctx, x_dev, xm0_dev, xm1_dev, dx_dev, energy_dev, energy_host, grad_dev, hess,
+                             alpha_host, info, counts, xs_host, dxs_host);
 }
 
 ipc_status ipc_autotune(ipc_ctx* ctx, const double* x_dev, const double* xm0_dev, const double* dx_dev,

@@ -423,6 +423,9 @@ struct Ctx {
     DBuf<float> vbound_c;                       // [nv][8] per-vertex FP32 bounds for the contact query
     DBuf<float> vbound_s;                       // [nv][12] per-vertex FP32 swept bounds for the swept query
     cudaStream_t ccd_stream = nullptr;          // the swept query's branch of a contact pass
+    cudaStream_t h2d_stream = nullptr;          // host-input passes: the displacements' copy
+    cudaEvent_t ev_xin = nullptr, ev_dxin = nullptr;   // positions copied / displacements scattered
+    DBuf<double> xs_stage, dxs_stage;           // [n_svert][3] host inputs on the device
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaStream_t aux_stream = nullptr;          // touched-output lists beside the sample evaluation
     cudaEvent_t ev_touch0 = nullptr, ev_touch1 = nullptr, ev_samples = nullptr;

@@ -271,3 +271,45 @@ def test_scattered_surface_inputs_give_the_same_pass(B):
         assert torch.equal(a["grad"], b["grad"])
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_host_input_pass_equals_scatter_then_pass(B, prec):
+    """ipc_contact_pass_host: the slave vertices' positions and displacements
+    copied from page-locked host memory inside the pass (the displacements
+    behind the broad phase) give bitwise the pass on the scattered device
+    arrays -- energy, gradient, every Hessian block, alpha -- over several
+    calls whose host contents change (graph replays read the new values);
+    pageable host memory is refused."""
+    from paper_2605_24339_b300 import scenes as S
+    sc = S.gel_on_terrain(n_quads=16, nz=2, terrain_quads=24)
+    rng = np.random.default_rng(5)
+    ctx = B.Context(sc, precision=prec)
+    try:
+        ids = ctx.slave_vertices()
+        xm = torch.as_tensor(sc.Y0, device="cuda")
+        xs_h = torch.zeros((len(ids), 3), dtype=torch.float64).pin_memory()
+        dxs_h = torch.zeros((len(ids), 3), dtype=torch.float64).pin_memory()
+        x_a = torch.zeros((sc.X.shape[0], 3), dtype=torch.float64, device="cuda")
+        dx_a = torch.zeros_like(x_a)
+        x_b, dx_b = torch.zeros_like(x_a), torch.zeros_like(x_a)
+        for it in range(4):
+            x = sc.X.copy()
+            x[:, 2] -= (1.2 + 0.2 * it) * sc.params["dhat"]
+            dx = rng.normal(scale=1e-5 * (it + 1), size=x.shape)
+            xs_h.copy_(torch.as_tensor(x[ids]))
+            dxs_h.copy_(torch.as_tensor(dx[ids]))
+            ctx.scatter_slave(torch.as_tensor(x[ids], device="cuda"), x_a)
+            ctx.scatter_slave(torch.as_tensor(dx[ids], device="cuda"), dx_a)
+            a = ctx.contact_pass(x_a, xm, dx_a, grad=True, hess=True)
+            b = ctx.contact_pass_host(xs_h, dxs_h, x_b, dx_b, xm, grad=True, hess=True)
+            assert torch.equal(x_a, x_b) and torch.equal(dx_a, dx_b)
+            assert a["energy"] == b["energy"] and a["alpha"] == b["alpha"], it
+            assert a["alpha_lin"] == b["alpha_lin"] and a["alpha_accd"] == b["alpha_accd"]
+            assert torch.equal(a["grad"], b["grad"])
+            for pa, pb in zip(a["hess"], b["hess"]):   # row_ptr, col_idx, blocks
+                assert torch.equal(pa, pb)
+        with pytest.raises(B.GmcpError):
+            ctx.contact_pass_host(torch.zeros((len(ids), 3), dtype=torch.float64), None, x_b, None, xm)
+    finally:
+        ctx.close()
