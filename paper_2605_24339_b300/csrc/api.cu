@@ -1142,6 +1142,12 @@ ipc_status ipc_create(const ipc_params* params, const ipc_scene* scene, ipc_ctx*
         c.P.ccd_slack = params->ccd_slack; c.P.ccd_max_iter = params->ccd_max_iter;
         c.P.face_clip = params->face_sampler;
         c.P.inv_dhat = 1.0 / params->dhat;
+        c.P.kappa_f = (float)c.P.kappa; c.P.kappa_edge_f = (float)c.P.kappa_edge;
+        c.P.kappa_point_f = (float)c.P.kappa_point;
+        c.P.delta_T_f = (float)c.P.delta_T; c.P.delta_e_f = (float)c.P.delta_e;
+        c.P.dhat_hi = (float)params->dhat;
+        c.P.dhat_lo = (float)(params->dhat - (double)c.P.dhat_hi);
+        c.P.inv_dhat_f = (float)c.P.inv_dhat;
         {
             const double r = params->dhat * (1.2 / 0.9);
             float f = (float)(r * r);

@@ -141,21 +141,11 @@ __device__ __forceinline__ void barrier(double g64, double eps64, float& B, floa
     d2B = -2.0f * L - 4.0f * r + r * r;
 }
 
-// the same with 1 / eps given (certified items, eps = dhat): d / eps as a
-// product; after the rounding to FP32 it matches the quotient but for ties
-__device__ __forceinline__ void barrier_inv(double g64, double eps64, double inv_eps, float& B, float& dB,
-                                            float& d2B) {
-    const double d64 = g64 - eps64;
-    const float d = (float)d64, g = (float)g64;
-    const float L = log1pf((float)(d64 * inv_eps));
-    const float r = d / g;
-    B = -d * d * L;
-    dB = -2.0f * d * L - d * r;
-    d2B = -2.0f * L - 4.0f * r + r * r;
-}
 
-// face-rule barycentrics per level (index L-1), filled at context creation
+// face-rule barycentrics per level (index L-1), filled at context creation;
+// c_rule_f the same rounded to FP32 (the certified FP32 items)
 __constant__ double c_rule[2][16][3];
+__constant__ float c_rule_f[2][16][3];
 
 // Face ray cast of Sec. 4.1 (fixed slave-side rule): from xs along ns onto
 // the plane of (y0,y1,y2).  Returns true when the master tri faces the slave,
@@ -427,10 +417,11 @@ __global__ void k_touch(SceneView S, CandView C, TouchArgs A) {
 // vertices minus the origin, rounded to FP32, at [51, 60): the inputs of the
 // FP32 pre-filter of the sample items.
 // With tmid64 != NULL (mixed path) it also writes the middle stage's
-// per-triangle inputs: tmid32[12 i ...] the unit normal, x1 - x0 and x2 - x0
-// rounded to FP32 (the values the item kernels would form), tmid64[4 i ...]
-// n_s . dx_a for the three vertices (dx NULL: 0) and the sum of their
-// magnitudes: once per triangle instead of once per item.
+// per-triangle inputs: tmid32[16 i ...] the unit normal, x1 - x0 and x2 - x0
+// rounded to FP32 (the values the item kernels would form), a face
+// sample's weight A / nk, n_s . dx_a for the three vertices (dx NULL: 0)
+// and the sum of their magnitudes rounded up; tmid64[4 i ...] the same
+// products and sum in FP64: once per triangle instead of once per item.
 __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ x,
                             double* __restrict__ frame, int nk, int32_t* __restrict__ items,
                             int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp,
@@ -481,7 +472,7 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
             }
             if (tmid64) {
                 const V3<double> ns = {f[0], f[1], f[2]};
-                float* m32 = tmid32 + 12 * (int64_t)i;
+                float* m32 = tmid32 + 16 * (int64_t)i;
                 const V3<float> nf = tof(ns), e1 = tof(x1 - x0), e2 = tof(x2 - x0);
                 m32[0] = nf.x; m32[1] = nf.y; m32[2] = nf.z;
                 m32[3] = e1.x; m32[4] = e1.y; m32[5] = e1.z;
@@ -492,6 +483,10 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
                 const double s0 = dot(ns, d0), s1 = dot(ns, d1), s2 = dot(ns, d2);
                 m64[0] = s0; m64[1] = s1; m64[2] = s2;
                 m64[3] = fabs(s0) + fabs(s1) + fabs(s2);
+                m32[9] = (float)(f[3] / (double)nk);
+                m32[10] = (float)s0; m32[11] = (float)s1; m32[12] = (float)s2;
+                m32[13] = (float)m64[3] * 1.000001f;   // at least the sum
+                m32[14] = 0.0f; m32[15] = 0.0f;
             }
             if (items) {
                 const int32_t* cnt = C.count + 4 * t;
@@ -522,6 +517,8 @@ struct TriData {
     V3<double> x0, x1, x2, X0, X1, X2, dx0, dx1, dx2, ns, ns0;
     V3<float> ns_f;
     V3<float> e1_f, e2_f;  // x1 - x0, x2 - x0 (FP64 differences, rounded)
+    float w_f;             // a face sample's weight A / nk (middle stage)
+    float sdxf[4];         // sdx in FP32, the sum rounded up (middle stage)
     double As;
     float tol_abs;
     const double* sb;      // rest box of the slave tri
@@ -567,10 +564,12 @@ __device__ __forceinline__ TriData load_tri_mid(const SceneView& S, const CandVi
     const double* fr = frame + 8 * (int64_t)i;
     D.As = fr[3];
     D.tol_abs = (float)fr[7];
-    const float* m = tmid32 + 12 * (int64_t)i;
+    const float* m = tmid32 + 16 * (int64_t)i;
     D.ns_f = {m[0], m[1], m[2]};
     D.e1_f = {m[3], m[4], m[5]};
     D.e2_f = {m[6], m[7], m[8]};
+    D.w_f = m[9];
+    for (int q = 0; q < 4; ++q) D.sdxf[q] = m[10 + q];
     const double* m64 = tmid64 + 4 * (int64_t)i;
     for (int q = 0; q < 4; ++q) D.sdx[q] = m64[q];
     D.sb = S.srest_box + 6 * D.t;
@@ -1010,6 +1009,181 @@ __device__ __forceinline__ bool point_cert(const SceneView& S, const Params& P, 
     return true;
 }
 
+// ---- certified items of the middle stage, in FP32 throughout ----------
+// The same certificates as face_cert / edge_cert / point_cert (PRE), with
+// the item's weight, gap, barycentrics and closing rate kept in FP32: the
+// only FP64 operations left are the master positions relative to x0 (an
+// FP64 difference rounded once) and the two results stored.
+struct CertOut {
+    float coef;      // kappa_q w gamma
+    float g, gstep;  // the gap and a certified lower bound of it
+    float dg;        // the linearised gap change along dx, widened toward closing (0 without dx)
+    float b[3];      // slave barycentrics
+};
+
+__device__ __forceinline__ float l1f(V3<float> v) { return fabsf(v.x) + fabsf(v.y) + fabsf(v.z); }
+
+// dg = -n_s . sum_a b_a dx_a from the frame kernel's FP32 products, widened
+// toward closing by (tol_b + 2^-21) sum_a |n_s . dx_a| (tol_b the error of
+// each b_a, 2^-21 that of the FP32 products and sums, b_a <= 1 + tol_b)
+__device__ __forceinline__ float cert_dg_f(const TriData& D, const float* b, float tol_b) {
+    const float ds = b[0] * D.sdxf[0] + b[1] * D.sdxf[1] + b[2] * D.sdxf[2];
+    return -ds - (tol_b + 4.8e-7f) * D.sdxf[3];
+}
+
+// face sample k of slave tri D against master tri m.  The offset from the
+// sample to y0 is (y0 - x0) rounded to FP32 minus b1 e1 + b2 e2 in FP32, so
+// its error is below 2^-21 (|y0 - x0| + |e1| + |e2|) (1-norms); that bound
+// enters the gap and barycentric tolerances on top of face_cert's.
+template <int NK>
+__device__ __forceinline__ bool face_cert_f(const SceneView& S, const Params& P, const TriData& D, int k,
+                                            const double* xm, int32_t m, bool want_dg, CertOut& o,
+                                            const float* mtri_e) {
+    const double* mb = S.mrest_box + 6 * (int64_t)m;
+    const float* mf = S.mrest_box_f + 6 * (int64_t)m;
+    if (!rest_far_f(D.sbf, D.sbf + 3, mf, mf + 3, P.far_r2_f) && !rest_far(D.sb, D.sb + 3, mb, mb + 3, P.dhat))
+        return false;
+    const int32_t* M = S.mtri + 3 * (int64_t)m;
+    const V3<float> a = tof(ld3(xm, M[0]) - D.x0);
+    const float b0 = c_rule_f[P.L - 1][k][0], b1 = c_rule_f[P.L - 1][k][1], b2 = c_rule_f[P.L - 1][k][2];
+    const V3<float> d = a - (b1 * D.e1_f + b2 * D.e2_f);
+    const float dd = 4.8e-7f * (l1f(a) + l1f(D.e1_f) + l1f(D.e2_f));
+    V3<float> e1, e2;
+    mtri_edges<true>(S, xm, mtri_e, m, e1, e2);
+    const V3<float> N = cross(e1, e2);
+    const float nN = norm3f(N);
+    const float cosn = -dot(N, D.ns_f) / nN;
+    if (!(cosn >= 0.5f)) return false;
+    const float g = dot(N, d) / (-cosn * nN);
+    const float l1 = norm3f(e1), l2 = norm3f(e2), l3 = norm3f(e2 - e1);
+    const float shape = l1 * l2 / nN;
+    const float tol_g = (1e-4f * (norm3f(d) + fabsf(g)) + dd) * shape / cosn;
+    if (!(g - tol_g >= kCertLo * P.dhat_hi && g + tol_g <= kCertHi * P.dhat_hi)) return false;
+    const V3<float> q = g * D.ns_f - d;   // hit point relative to y0
+    float bm[3];
+    bary_rel(q, e1, e2, bm);
+    const float hmin = nN / rmax(l1, rmax(l2, l3));
+    const float tol_b = 1e-4f + (tol_g + 1e-4f * norm3f(q) + dd) * shape / hmin;
+    if (!(min3(bm) >= tol_b)) return false;
+    o.coef = P.kappa_f * D.w_f * hermite(min3(bm), P.delta_T_f);
+    o.g = g;
+    o.gstep = g - tol_g;
+    o.b[0] = b0; o.b[1] = b1; o.b[2] = b2;
+    o.dg = want_dg ? cert_dg_f(D, o.b, 0.0f) : 0.0f;
+    return true;
+}
+
+// Gauss point q of master edge me on slave tri D: edge_cert's certificate
+// (its FP32 geometry and tolerances unchanged), the item kept in FP32
+__device__ __forceinline__ bool edge_cert_f(const SceneView& S, const Params& P, const TriData& D,
+                                            const double* xm, int32_t me, int q, bool want_dg, CertOut& o,
+                                            const float* mtri_e) {
+    const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
+    {
+        const float* va = S.mvrest_box_f + 6 * (int64_t)ia;
+        const float* vb = S.mvrest_box_f + 6 * (int64_t)ib;
+        const float flo[3] = {fminf(va[0], vb[0]), fminf(va[1], vb[1]), fminf(va[2], vb[2])};
+        const float fhi[3] = {fmaxf(va[3], vb[3]), fmaxf(va[4], vb[4]), fmaxf(va[5], vb[5])};
+        if (!rest_far_f(D.sbf, D.sbf + 3, flo, fhi, P.far_r2_f)) {
+            const V3<double> Ya = ld3(S.Y0, ia), Yb = ld3(S.Y0, ib);
+            const double elo[3] = {rmin(Ya.x, Yb.x), rmin(Ya.y, Yb.y), rmin(Ya.z, Yb.z)};
+            const double ehi[3] = {rmax(Ya.x, Yb.x), rmax(Ya.y, Yb.y), rmax(Ya.z, Yb.z)};
+            if (!rest_far(D.sb, D.sb + 3, elo, ehi, P.dhat)) return false;
+        }
+    }
+    const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
+    if (!facing_cert<true>(S, xm, S.me_tri + a0, a1 - a0, D.ns_f, mtri_e)) return false;
+    const V3<float> da = tof(ld3(xm, ia) - D.x0), db = tof(ld3(xm, ib) - D.x0);
+    float bA[3], bB[3], tA, tB;
+    bool okA, okB;
+    bary_f(da, D.e1_f, D.e2_f, bA, tA, okA);
+    bary_f(db, D.e1_f, D.e2_f, bB, tB, okB);
+    if (!okA || !okB) return false;
+    const float tb = tA + tB;
+    float lo = 0.0f, hi = 1.0f, elo_t = 0.0f, ehi_t = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        const float Dd = bB[a] - bA[a];
+        if (fabsf(Dd) <= 4.0f * tb) {
+            if (rmin(bA[a], bB[a]) >= tb) continue;
+            return false;
+        }
+        const float r = -bA[a] / Dd;
+        const float er = (tA + fabsf(r) * tb) / (fabsf(Dd) - tb);
+        if (Dd > 0.0f) { if (r > lo) { lo = r; elo_t = er; } }
+        else if (r < hi) { hi = r; ehi_t = er; }
+    }
+    if (!(hi - lo > 4.0f * (elo_t + ehi_t) + 1e-3f)) return false;
+    const float gp = 0.57735026918962576f;   // 1 / sqrt(3)
+    const float mid = 0.5f * (lo + hi), half = 0.5f * (hi - lo);
+    const float eta = q == 0 ? mid - half * gp : mid + half * gp;
+    const float ga = dot(D.ns_f, da), gb = dot(D.ns_f, db);
+    const float g = (1.0f - eta) * ga + eta * gb;
+    const float tol_g = 1e-5f * (l1f(da) + l1f(db)) + fabsf(gb - ga) * (elo_t + ehi_t) + D.tol_abs;
+    if (!(g - tol_g >= kCertLo * P.dhat_hi && g + tol_g <= kCertHi * P.dhat_hi)) return false;
+    const V3<float> tv = db - da;
+    const float tn = dot(tv, D.ns_f);
+    const V3<float> tp = tv - tn * D.ns_f;
+    const float ell = (hi - lo) * norm3f(tp);
+    o.coef = P.kappa_edge_f * (0.5f * ell) * (hermite(eta, P.delta_e_f) * hermite(1.0f - eta, P.delta_e_f));
+    o.g = g;
+    o.gstep = g - tol_g;
+    for (int c = 0; c < 3; ++c) o.b[c] = (1.0f - eta) * bA[c] + eta * bB[c];
+    o.dg = want_dg ? cert_dg_f(D, o.b, tb) : 0.0f;
+    return true;
+}
+
+// master vertex u on slave tri D: point_cert's certificate, kept in FP32
+__device__ __forceinline__ bool point_cert_f(const SceneView& S, const Params& P, const TriData& D,
+                                             const double* xm, int32_t u, bool want_dg, CertOut& o,
+                                             const float* mtri_e) {
+    {
+        const float* vu = S.mvrest_box_f + 6 * (int64_t)u;
+        if (!rest_far_f(D.sbf, D.sbf + 3, vu, vu + 3, P.far_r2_f)) {
+            const V3<double> Y = ld3(S.Y0, u);
+            const double yb[3] = {Y.x, Y.y, Y.z};
+            if (!rest_far(D.sb, D.sb + 3, yb, yb, P.dhat)) return false;
+        }
+    }
+    const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
+    if (!facing_cert<true>(S, xm, S.mv_tri + a0, a1 - a0, D.ns_f, mtri_e)) return false;
+    const V3<float> d = tof(ld3(xm, u) - D.x0);
+    float bs[3], tb;
+    bool ok;
+    bary_f(d, D.e1_f, D.e2_f, bs, tb, ok);
+    if (!ok || !(min3(bs) >= tb)) return false;
+    const float g = dot(D.ns_f, d);
+    const float tol_g = 1e-5f * l1f(d) + D.tol_abs;
+    if (!(g - tol_g >= kCertLo * P.dhat_hi && g + tol_g <= kCertHi * P.dhat_hi)) return false;
+    o.coef = P.kappa_point_f;
+    o.g = g;
+    o.gstep = g - tol_g;
+    for (int c = 0; c < 3; ++c) o.b[c] = bs[c];
+    o.dg = want_dg ? cert_dg_f(D, o.b, tb) : 0.0f;
+    return true;
+}
+
+// value of a certified FP32 item (eps = dhat): the barrier's B, B' and B''
+// (as barrier() forms them) in FP32, with d = g - dhat formed against
+// dhat's FP32 pair (exact where g is within a factor two of dhat) and
+// d / dhat as a product with 1 / dhat, and the step bound 0.9 gstep / (-dg)
+// in FP32 lowered by 2e-6 (more than its rounding), so it stays at or
+// below the FP64 path's
+__device__ __forceinline__ void item_value_cert_f(const CertOut& o, bool want_dg, const Params& P, double& e,
+                                                  double& amin, float& c1, float& c2, float* b) {
+    const float d = (o.g - P.dhat_hi) - P.dhat_lo;
+    const float L = log1pf(d * P.inv_dhat_f);
+    const float r = d / o.g;
+    const float Bv = -d * d * L;
+    const float dB = -2.0f * d * L - d * r;
+    const float d2B = -2.0f * L - 4.0f * r + r * r;
+    e = (double)(o.coef * Bv);
+    c1 = o.coef * dB;
+    c2 = rmax(o.coef * d2B, 0.0f);
+    for (int cc = 0; cc < 3; ++cc) b[cc] = o.b[cc];
+    amin = INFINITY;
+    if (want_dg && o.dg < 0.0f) amin = (double)(0.9f * o.gstep / (-o.dg) * (1.0f - 2e-6f));
+}
+
 // the value of an item for the evaluation: energy, c1, c2, slave
 // barycentrics and its step bound (the arithmetic of sample_add)
 template <class T>
@@ -1025,28 +1199,6 @@ __device__ __forceinline__ void item_value(const ItemOut& o, bool want_dg, doubl
     amin = INFINITY;
     if (want_dg && o.dg < 0.0) amin = 0.9 * o.g_step / (-o.dg);
 }
-// a certified item of the mixed path (eps = dhat, T = FP32): the barrier
-// from 1/dhat, and the step bound 0.9 g_step / (-dg) in FP32, lowered by
-// 1e-6 to stay below the FP64 quotient (three FP32 roundings are < 2e-7)
-template <class T>
-__device__ __forceinline__ void item_value_cert(const ItemOut& o, bool want_dg, double inv_dhat, double& e,
-                                                double& amin, T& c1, T& c2, T* b) {
-    if constexpr (sizeof(T) == 4) {
-        float Bv, dB, d2B;
-        barrier_inv(o.g, o.eps, inv_dhat, Bv, dB, d2B);
-        const float coef = (float)(o.kq * o.w * o.gamma);
-        e = (double)(coef * Bv);
-        c1 = coef * dB;
-        c2 = rmax(coef * d2B, 0.0f);
-        for (int cc = 0; cc < 3; ++cc) b[cc] = (float)o.b[cc];
-        amin = INFINITY;
-        if (want_dg && o.dg < 0.0)
-            amin = (double)(0.9f * (float)o.g_step / (float)(-o.dg)) * (1.0 - 1e-6);
-    } else {
-        item_value<T>(o, want_dg, e, amin, c1, c2, b);
-    }
-}
-
 // The paper's clipped-overlap face samples of slave tri D against master
 // tri m (Sec. 4.1 "Face samples", ipc_params.face_sampler = 1): the pair
 // counts when the master triangle faces the slave (N . n_s < 0); each clip
@@ -1588,19 +1740,17 @@ k_items_mid(SceneView S, Params P, CandView C, const double* __restrict__ x, con
                 const TriData D = load_tri_mid(S, C, x, frame, tmid64, tmid32, i);
                 const ItemRef R = item_ref<NK>(D, q);
                 bool certified = false;
-                ItemOut o;
+                CertOut o;
                 // the certified evaluation first (most items past the pre-filter
-                // are active), then the local reject tests for the rest
+                // are active, and it runs in FP32), then the local reject
+                // tests for the rest
                 if (faces) {
-                    FaceSample F;
-                    for (int a = 0; a < 3; ++a) F.beta[a] = c_rule[P.L - 1][R.k][a];
-                    F.xs = interp(F.beta, D.x0, D.x1, D.x2);
-                    // n_s . (the sample's displacement) from the vertices' products
-                    F.ds = cert && want_dg ? F.beta[0] * D.sdx[0] + F.beta[1] * D.sdx[1] + F.beta[2] * D.sdx[2]
-                                           : 0.0;
                     const int32_t m = C.face[D.t * C.cap_f + R.j];
-                    certified = cert && face_cert<NK, true>(S, P, D, F, xm, m, want_dg, o, mtri_e);
+                    certified = cert && face_cert_f<NK>(S, P, D, R.k, xm, m, want_dg, o, mtri_e);
                     if (!certified) {
+                        FaceSample F;
+                        for (int a = 0; a < 3; ++a) F.beta[a] = c_rule[P.L - 1][R.k][a];
+                        F.xs = interp(F.beta, D.x0, D.x1, D.x2);
                         F.xs_rel = tof(F.xs - D.x0);
                         const int32_t* M = S.mtri + 3 * (int64_t)m;
                         keep = face_pre(P, D, F, ld3(xm, M[0]), ld3(xm, M[1]), ld3(xm, M[2]));
@@ -1608,22 +1758,23 @@ k_items_mid(SceneView S, Params P, CandView C, const double* __restrict__ x, con
                     cnt_f += certified;
                 } else if (R.kind == 1) {
                     const int32_t me = C.edge[D.t * C.cap_e + R.j];
-                    certified = cert && edge_cert<true>(S, P, D, xm, me, R.k, want_dg, o, mtri_e);
+                    certified = cert && edge_cert_f(S, P, D, xm, me, R.k, want_dg, o, mtri_e);
                     if (!certified)
                         keep = edge_pre(P, D, ld3(xm, S.medge[2 * (int64_t)me]), ld3(xm, S.medge[2 * (int64_t)me + 1]));
                     cnt_e += certified;
                 } else {
                     const int32_t u = C.point[D.t * C.cap_p + R.j];
-                    certified = cert && point_cert<true>(S, P, D, xm, u, want_dg, o, mtri_e);
+                    certified = cert && point_cert_f(S, P, D, xm, u, want_dg, o, mtri_e);
                     if (!certified) keep = point_pre(P, D, ld3(xm, u));
                     cnt_p += certified;
                 }
                 if (certified) {
                     // an active item evaluated from certified FP32 geometry
                     double e, amin;
-                    T c1, c2, b[3];
-                    item_value_cert<T>(o, want_dg, P.inv_dhat, e, amin, c1, c2, b);
-                    item_store<T>(B, s, e, amin, c1, c2, b);
+                    float c1, c2, bf[3];
+                    item_value_cert_f(o, want_dg, P, e, amin, c1, c2, bf);
+                    const T bt[3] = {(T)bf[0], (T)bf[1], (T)bf[2]};
+                    item_store<T>(B, s, e, amin, (T)c1, (T)c2, bt);
                     keep = false;
                 } else if (!keep) {
                     const T z[3] = {T(0), T(0), T(0)};
@@ -1942,7 +2093,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
         GMCP_CUDA_TRY(c.tri_f32.ensure(64 * (size_t)c.ns + 64));
         GMCP_CUDA_TRY(c.ym32.ensure(4 * (size_t)c.nmv + 4));
         GMCP_CUDA_TRY(c.tri_mid64.ensure(4 * (size_t)c.ns + 8));
-        GMCP_CUDA_TRY(c.tri_mid32.ensure(12 * (size_t)c.ns + 12));
+        GMCP_CUDA_TRY(c.tri_mid32.ensure(16 * (size_t)c.ns + 16));
         if (c.use_mtri_e32) GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
         if (c.use_mtri_pre) GMCP_CUDA_TRY(c.mtri_pre.ensure((size_t)kMtriPre * c.nmt + kMtriPre));
         // the master's FP32 tables depend on xm alone: already enqueued at
@@ -2016,6 +2167,9 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
 }  // namespace
 
 cudaError_t contact_init_constants(const double* rule_l1l2) {
+    float rf[2 * 16 * 3];
+    for (int q = 0; q < 2 * 16 * 3; ++q) rf[q] = (float)rule_l1l2[q];
+    GMCP_CUDA_TRY(cudaMemcpyToSymbol(c_rule_f, rf, sizeof(rf)));
     return cudaMemcpyToSymbol(c_rule, rule_l1l2, sizeof(double) * 2 * 16 * 3);
 }
 

@@ -106,6 +106,9 @@ struct Params {
     double inv_dhat;       // 1 / dhat
     float far_r2_f;        // (dhat 1.2/0.9)^2 rounded up to FP32 and raised by 1e-6: rest boxes whose
                            // certain FP32 distance bound reaches it are rest-far in FP64 too
+    // FP32 copies for the certified FP32 items of the mixed path: the
+    // stiffnesses, the gamma radii, dhat as a pair (hi + lo) and 1 / dhat
+    float kappa_f, kappa_edge_f, kappa_point_f, delta_T_f, delta_e_f, dhat_hi, dhat_lo, inv_dhat_f;
 };
 
 // Candidate list storage: fixed capacity per slave triangle.
