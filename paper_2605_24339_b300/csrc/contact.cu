@@ -1490,36 +1490,49 @@ __global__ void k_mtri_pre(SceneView S, const float4* __restrict__ ym32, float* 
 //   / cos + 1e-4 (|d| + |g|), cos = -N.n_s / |N|;
 //   the hit point's barycentric coordinates are within tol_b = 0.02 +
 //   4 (tol_g + 4 del) / h_min, h_min the triangle's smallest height.
-__device__ __forceinline__ bool face_reject_f32(V3<float> xs, V3<float> ns, V3<float> y0, V3<float> y1, V3<float> y2,
-                                                float eps_max) {
-    const float R = rmax(rmax(fabsf(xs.x), rmax(fabsf(xs.y), fabsf(xs.z))),
-                         rmax(rmax(fabsf(y0.x), rmax(fabsf(y0.y), fabsf(y0.z))),
-                              rmax(rmax(fabsf(y1.x), rmax(fabsf(y1.y), fabsf(y1.z))),
-                                   rmax(fabsf(y2.x), rmax(fabsf(y2.y), fabsf(y2.z))))));
+// the per-sample part of the face pre-filter, given the master triangle's
+// part: y0, its edges e1, e2, N = e1 x e2 and |N|, the edge lengths, the
+// largest coordinate magnitude Rm of its vertices and the Gram terms a =
+// e1.e1, bb = e1.e2, c = e2.e2, det = a c - bb^2.  Quotients by fast division
+// and |d| by the reciprocal square root: their few-ulp errors are far inside
+// the test's tolerances (1e-4 relative in g, 2^-21 R per coordinate, 0.02
+// in the barycentrics), so a rejection stays certain.
+__device__ __forceinline__ bool face_reject_core(V3<float> xs, V3<float> ns, V3<float> y0, V3<float> e1,
+                                                 V3<float> e2, V3<float> N, float nN, float l1, float l2, float l3,
+                                                 float Rm, float a, float bb, float c, float det, float eps_max) {
+    const float R = rmax(rmax(fabsf(xs.x), rmax(fabsf(xs.y), fabsf(xs.z))), Rm);
     const float del = 4.7683716e-7f * R;   // 2^-21 R
-    const V3<float> e1 = y1 - y0, e2 = y2 - y0, N = cross(e1, e2);
-    const float nN = sqrtf(dot(N, N));
-    const float l1 = sqrtf(dot(e1, e1)), l2 = sqrtf(dot(e2, e2));
-    const float rel_N = 8.0f * del * (l1 + l2) / nN + 1e-5f;
-    const float den = dot(N, ns);
     if (!(nN > 0.0f)) return false;
+    const float inv_nN = __fdividef(1.0f, nN);
+    const float rel_N = 8.0f * del * (l1 + l2) * inv_nN + 1e-5f;
+    const float den = dot(N, ns);
     if (den >= (rel_N + 1e-3f) * nN) return true;           // faces away
     if (den > -(rel_N + 0.05f) * nN) return false;           // near grazing: later tests decide
-    const float cosn = -den / nN;
+    const float cosn = -den * inv_nN;
     const V3<float> d = y0 - xs;
-    const float g = dot(N, d) / den;
-    const float dn = sqrtf(dot(d, d));
-    const float tol_g = (2.0f * rel_N * (dn + fabsf(g)) + 8.0f * del) / cosn + 1e-4f * (dn + fabsf(g));
+    const float g = __fdividef(dot(N, d), den);
+    const float dd = dot(d, d);
+    const float dn = dd > 0.0f ? dd * rsqrtf(dd) : 0.0f;
+    const float tol_g = __fdividef(2.0f * rel_N * (dn + fabsf(g)) + 8.0f * del, cosn) + 1e-4f * (dn + fabsf(g));
     if (g > eps_max * (1.0f + 1e-6f) + tol_g || g < -tol_g) return true;
     const V3<float> q = g * ns - d;    // hit point relative to y0
-    const float a = dot(e1, e1), bb = dot(e1, e2), c = dot(e2, e2);
     const float r1 = dot(q, e1), r2 = dot(q, e2);
-    const float det = a * c - bb * bb;
-    const float v = (c * r1 - bb * r2) / det, w = (a * r2 - bb * r1) / det;
-    const float l3 = sqrtf(dot(e2 - e1, e2 - e1));
-    const float hmin = nN / rmax(l1, rmax(l2, l3));
-    const float tol_b = 0.02f + 4.0f * (tol_g + 4.0f * del) / hmin;
+    const float inv_det = __fdividef(1.0f, det);
+    const float v = (c * r1 - bb * r2) * inv_det, w = (a * r2 - bb * r1) * inv_det;
+    const float hmin = nN * __fdividef(1.0f, rmax(l1, rmax(l2, l3)));
+    const float tol_b = 0.02f + 4.0f * (tol_g + 4.0f * del) * __fdividef(1.0f, hmin);
     return rmin(1.0f - v - w, rmin(v, w)) < -tol_b;
+}
+__device__ __forceinline__ bool face_reject_f32(V3<float> xs, V3<float> ns, V3<float> y0, V3<float> y1, V3<float> y2,
+                                                float eps_max) {
+    const float Rm = rmax(rmax(fabsf(y0.x), rmax(fabsf(y0.y), fabsf(y0.z))),
+                          rmax(rmax(fabsf(y1.x), rmax(fabsf(y1.y), fabsf(y1.z))),
+                               rmax(fabsf(y2.x), rmax(fabsf(y2.y), fabsf(y2.z)))));
+    const V3<float> e1 = y1 - y0, e2 = y2 - y0, N = cross(e1, e2);
+    const float nN = sqrtf(dot(N, N));
+    const float l1 = sqrtf(dot(e1, e1)), l2 = sqrtf(dot(e2, e2)), l3 = sqrtf(dot(e2 - e1, e2 - e1));
+    const float a = dot(e1, e1), bb = dot(e1, e2), c = dot(e2, e2);
+    return face_reject_core(xs, ns, y0, e1, e2, N, nN, l1, l2, l3, Rm, a, bb, c, a * c - bb * bb, eps_max);
 }
 
 // the same test with the master triangle's part read from its k_mtri_pre
@@ -1529,27 +1542,7 @@ __device__ __forceinline__ bool face_reject_f32_rec(V3<float> xs, V3<float> ns, 
     const float4 q0 = r4[0], q1 = r4[1], q2 = r4[2], q3 = r4[3], q4 = r4[4], q5 = r4[5];
     const V3<float> y0 = {q0.x, q0.y, q0.z}, e1 = {q0.w, q1.x, q1.y}, e2 = {q1.z, q1.w, q2.x};
     const V3<float> N = {q2.y, q2.z, q2.w};
-    const float nN = q3.x, l1 = q3.y, l2 = q3.z, l3 = q3.w, Rm = q4.x;
-    const float a = q4.y, bb = q4.z, c = q4.w, det = q5.x;
-    const float R = rmax(rmax(fabsf(xs.x), rmax(fabsf(xs.y), fabsf(xs.z))), Rm);
-    const float del = 4.7683716e-7f * R;   // 2^-21 R
-    const float rel_N = 8.0f * del * (l1 + l2) / nN + 1e-5f;
-    const float den = dot(N, ns);
-    if (!(nN > 0.0f)) return false;
-    if (den >= (rel_N + 1e-3f) * nN) return true;           // faces away
-    if (den > -(rel_N + 0.05f) * nN) return false;           // near grazing: later tests decide
-    const float cosn = -den / nN;
-    const V3<float> d = y0 - xs;
-    const float g = dot(N, d) / den;
-    const float dn = sqrtf(dot(d, d));
-    const float tol_g = (2.0f * rel_N * (dn + fabsf(g)) + 8.0f * del) / cosn + 1e-4f * (dn + fabsf(g));
-    if (g > eps_max * (1.0f + 1e-6f) + tol_g || g < -tol_g) return true;
-    const V3<float> q = g * ns - d;    // hit point relative to y0
-    const float r1 = dot(q, e1), r2 = dot(q, e2);
-    const float v = (c * r1 - bb * r2) / det, w = (a * r2 - bb * r1) / det;
-    const float hmin = nN / rmax(l1, rmax(l2, l3));
-    const float tol_b = 0.02f + 4.0f * (tol_g + 4.0f * del) / hmin;
-    return rmin(1.0f - v - w, rmin(v, w)) < -tol_b;
+    return face_reject_core(xs, ns, y0, e1, e2, N, q3.x, q3.y, q3.z, q3.w, q4.x, q4.y, q4.z, q4.w, q5.x, eps_max);
 }
 
 __global__ void k_fill_owner(CandView C, const int32_t* __restrict__ items, ItemBufs B) {
