@@ -610,7 +610,7 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
     // without a prediction the iteration starts at this point: its system,
     // with the matrix, serves the first iteration too
     const bool reuse = dx_pred == nullptr;
-    GMCP_CUDA_TRY(assemble_system(c, N.tmp.p, reuse));
+    GMCP_CUDA_TRY(assemble_system(c, N.tmp.p, reuse ? kHessAll : kHessNone));
     GMCP_CUDA_TRY(read_es(c, kEsG2, 1));
     for (int e = 0; e < ne; ++e) gscale[e] = std::sqrt(N.h_es[kES * e + kEsG2]);
     // a predicted start goes through the same CCD-filtered start point and is
@@ -622,7 +622,7 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
         GMCP_CUDA_TRY(vec_axpy(c, n, 1.0, x, dx_pred, N.P.p));
         GMCP_CUDA_TRY(start_point(c, x, N.P.p, N.xl.p, run, al, okp));
         if (any(okp)) {
-            GMCP_CUDA_TRY(assemble_system(c, N.xl.p, false));
+            GMCP_CUDA_TRY(assemble_system(c, N.xl.p, kHessNone));
             GMCP_CUDA_TRY(cudaMemcpyAsync(N.h_ebad, N.ebad.p, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, s));
             GMCP_CUDA_TRY(read_es(c, kEsG2, 1));
             for (int e = 0; e < ne; ++e)
@@ -645,7 +645,11 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
     std::vector<double> al_acc(ne, 0.0);
     const double c0 = 1e-4;
     for (int it = 0; any(run); ++it) {
-        if (!(it == 0 && reuse)) GMCP_CUDA_TRY(assemble_system(c, x, true));
+        // energies, gradient and the contact blocks; the elastic blocks and
+        // the matrix only once some environment goes on (the last
+        // evaluation of a step, at its converged point, needs neither)
+        const bool have_matrix = it == 0 && reuse;
+        if (!have_matrix) GMCP_CUDA_TRY(assemble_system(c, x, kHessContact));
         GMCP_CUDA_TRY(cudaMemcpyAsync(N.h_ebad, N.ebad.p, sizeof(int32_t) * ne, cudaMemcpyDeviceToHost, s));
         GMCP_CUDA_TRY(read_es(c, kEsEc, 4));
         for (int e = 0; e < ne; ++e) {
@@ -659,6 +663,7 @@ cudaError_t newton_run(Ctx& c, double* x, double* v, const double* xm_next, cons
             st[e].newton_iters = it + 1;
         }
         if (!any(run)) break;
+        if (!have_matrix) GMCP_CUDA_TRY(finish_hessian(c, x));
         // the environments still iterating solve; the others get b = 0 (their
         // solve stops at once) and a zero direction
         const int32_t* m_run = put_mask(c, 0, run);

@@ -612,7 +612,14 @@ cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double*
                          bool with_contact, bool ee0);
 // es[kEsEc], es[kEsEe], es[kEsE], es[kEsG2] at x, the gradient N.G and
 // optionally the matrix
-cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess);
+// what assemble_system evaluates besides the energies and the gradient:
+// nothing, the contact (and master) Hessian blocks, or every Hessian block
+// and the global matrix
+enum : int { kHessNone = 0, kHessContact = 1, kHessAll = 2 };
+cudaError_t assemble_system(Ctx& c, const double* x, int hess);
+// the elastic Hessian blocks and the global matrix at the x of the last
+// assemble_system(c, x, kHessContact)
+cudaError_t finish_hessian(Ctx& c, const double* x);
 // a . b per environment (3 nv entries) into es[slot]
 cudaError_t dot_env(Ctx& c, const double* a, const double* b, int slot);
 // the master positions / direction that go with system positions x /

@@ -601,6 +601,49 @@ k_nh_feasible_df(ElasticViewDF E, const float4* __restrict__ uh, const float4* _
     }
 }
 
+// The Hessian blocks alone, for a Newton iteration that goes on after the
+// convergence test (the energy and gradient at x were evaluated without
+// them): F and ln J from the same code as the evaluation, so the blocks are
+// bitwise those k_nh_eval(_df) would have written; inverted tets get zero
+// blocks (the evaluation flagged them).
+__global__ void __launch_bounds__(128)
+k_nh_hess_df(ElasticViewDF E, const float4* __restrict__ uh, const float4* __restrict__ ul,
+             float* __restrict__ tH) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E.nt) return;
+    dfl u[12], Dmi[9], H[9], q, jm1, lnJ, dml;
+    load_tet_pairs(E, uh, ul, t, u);
+    for (int k = 0; k < 9; ++k) Dmi[k] = ld_pair(E.Dmi + 9 * t + k);
+    nh_strain_df(Dmi, u, H, &q, &jm1);
+    if (!df_gt(jm1, -1.f)) {
+        for (int k = 0; k < HBlk<float>::kPerTet; ++k) tH[HBlk<float>::kPerTet * t + k] = 0.f;
+        return;
+    }
+    nh_log_df(E, jm1, &lnJ, &dml);
+    float Ff[9], Df[9];
+    for (int k = 0; k < 9; ++k) {
+        Ff[k] = k % 4 == 0 ? df_add(H[k], df_make(1.f)).hi : H[k].hi;   // as k_nh_eval_df forms F
+        Df[k] = Dmi[k].hi;
+    }
+    nh_hessian_blocks<float, float>(Ff, lnJ.hi, E.mu.hi, E.lam.hi, Df, ld_pair(E.vol + t).hi,
+                                    tH + HBlk<float>::kPerTet * t);
+}
+__global__ void __launch_bounds__(128)
+k_nh_hess64(ElasticView E, const double* __restrict__ x, double* __restrict__ tH) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= E.nt) return;
+    double x4[12], X4[12], F[9], lnJ, J, psi;
+    load_tet(E, x, t, x4);
+    load_tet(E, E.X, t, X4);
+    const double* Dmi = E.Dminv + 9 * t;
+    const double vol = E.vol[t];
+    if (!nh_energy(Dmi, vol, E.mu, E.lam, x4, X4, &psi, F, &lnJ, &J)) {
+        for (int k = 0; k < HBlk<double>::kPerTet; ++k) tH[HBlk<double>::kPerTet * t + k] = 0.0;
+        return;
+    }
+    nh_hessian_blocks<double>(F, lnJ, E.mu, E.lam, Dmi, vol, tH + HBlk<double>::kPerTet * t);
+}
+
 // G = M (x - xhat) + h^2 (sum_tets g + contact g); Dirichlet rows zero
 __global__ void k_assemble_grad(int64_t nv, const double* __restrict__ x, const double* __restrict__ xhat,
                                 const double* __restrict__ mass, const uint8_t* __restrict__ dir,
@@ -2624,7 +2667,7 @@ cudaError_t energy_batch(Ctx& c, const double* x, const double* p, const double*
 // total es[kEsE] and |G|^2 es[kEsG2] at x, the gradient G (Dirichlet rows
 // zero), optionally the matrix A; inverted-tet flags in N.ebad.  The broad
 // phase runs at (x, current master).
-cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess) {
+cudaError_t assemble_system(Ctx& c, const double* x, int hess) {
     NewtonState& N = *c.newton;
     const bool f32 = c.P.precision == IPC_PREC_MIXED;
     double* es = N.es.p;
@@ -2632,19 +2675,19 @@ cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess) {
     GMCP_CUDA_TRY(cudaMemsetAsync(N.ebad.p, 0, sizeof(int32_t) * ne, c.stream));
     {
         ProfScope ps(c.prof, c.stream, "elastic");
-        GMCP_CUDA_TRY(nh_eval(c, x, want_hess));
+        GMCP_CUDA_TRY(nh_eval(c, x, hess == kHessAll));
     }
     const double* xm = master_of(c, x);
     GMCP_CUDA_TRY(run_candidates(c, x, xm));
     void* cg = f32 ? (void*)N.cgrad32.p : (void*)N.cgrad64.p;
-    GMCP_CUDA_TRY(contact_eval(c, x, xm, nullptr, cg, want_hess, nullptr));
+    GMCP_CUDA_TRY(contact_eval(c, x, xm, nullptr, cg, hess != kHessNone, nullptr));
     // the contact energy of the samples of this pass (stamped triangles)
     GMCP_CUDA_TRY(seg_sum(c, N.seg_s, c.tri_E.p, 0, 1, es + kEsEc, kES, c.tri_stamp.p, c.misc_i32.p + kSlotPass));
-    if (N.joint) GMCP_CUDA_TRY(joint_master_terms(c, x, want_hess));
+    if (N.joint) GMCP_CUDA_TRY(joint_master_terms(c, x, hess != kHessNone));
     {
         ProfScope ps(c.prof, c.stream, "assemble");
         GMCP_CUDA_TRY(assemble_grad(c, x, N.xhat.p, cg, f32, N.G.p));
-        if (want_hess) GMCP_CUDA_TRY(assemble_bsr(c));
+        if (hess == kHessAll) GMCP_CUDA_TRY(assemble_bsr(c));
     }
     // total energy: inertia at x (one term, alpha 0, p unused)
     const double h2 = c.prm.h * c.prm.h;
@@ -2655,6 +2698,28 @@ cudaError_t assemble_system(Ctx& c, const double* x, bool want_hess) {
     k_combine<<<ne, 32, 0, c.stream>>>(1, es + kEsEin, es + kEsEe, es + kEsEc, h2, es + kEsE);
     GMCP_CUDA_TRY(cudaGetLastError());
     return dot_env(c, N.G.p, N.G.p, kEsG2);
+}
+
+// the elastic Hessian blocks at x and the global matrix, after an
+// assemble_system(c, x, kHessContact) (the contact and master blocks are
+// already in place)
+cudaError_t finish_hessian(Ctx& c, const double* x) {
+    NewtonState& N = *c.newton;
+    if (N.ntsys > 0) {
+        ProfScope ps(c.prof, c.stream, "elastic");
+        const unsigned g = nblk(N.ntsys, 128);
+        if (c.P.precision == IPC_PREC_MIXED) {
+            GMCP_CUDA_TRY(split_pairs(c, x, N.Xsys.p, N.uh4, N.ul4));
+            k_nh_hess_df<<<g, 128, 0, c.stream>>>(df_view(c), reinterpret_cast<const float4*>(N.uh4.p),
+                                                  reinterpret_cast<const float4*>(N.ul4.p), N.tH32.p);
+        } else {
+            ElasticView E{N.ntsys, N.tets.p, N.Dminv.p, N.vol.p, N.Xsys.p, N.mu, N.lam};
+            k_nh_hess64<<<g, 128, 0, c.stream>>>(E, x, N.tH64.p);
+        }
+        GMCP_CUDA_TRY(cudaGetLastError());
+    }
+    ProfScope ps(c.prof, c.stream, "assemble");
+    return assemble_bsr(c);
 }
 
 // ------------------------------------------------- per-environment vectors ---
