@@ -814,7 +814,6 @@ __device__ __forceinline__ void bary_rel(V3<float> q, V3<float> e1, V3<float> e2
     b[0] = 1.0f - v - w; b[1] = v; b[2] = w;
 }
 
-// some master face of the list certainly faces n_s (N . n_s <= -0.1 |N|)
 // master triangle m's edges y1 - y0, y2 - y0 rounded to FP32: read from
 // the per-pass table (PRE, see k_mtri_e32) or formed from xm -- the same values
 template <bool PRE>
@@ -831,6 +830,7 @@ __device__ __forceinline__ void mtri_edges(const SceneView& S, const double* xm,
         e2 = tof(ld3(xm, M[2]) - y0);
     }
 }
+// some master face of the list certainly faces n_s (N . n_s <= -0.1 |N|)
 template <bool PRE = false>
 __device__ __forceinline__ bool facing_cert(const SceneView& S, const double* xm, const int32_t* tris, int n,
                                             V3<float> ns, const float* mtri_e = nullptr) {
@@ -845,23 +845,17 @@ __device__ __forceinline__ bool facing_cert(const SceneView& S, const double* xm
 
 // face sample F of slave tri D against master tri m (Sec. 4.1, reading R1),
 // in the master triangle's frame
-template <int NK, bool PRE = false>
+template <int NK>
 __device__ __forceinline__ bool face_cert(const SceneView& S, const Params& P, const TriData& D,
                                           const FaceSample& F, const double* xm, int32_t m, bool want_dg,
-                                          ItemOut& o, const float* mtri_e = nullptr) {
+                                          ItemOut& o) {
     const double eps = P.dhat;
     const double* mb = S.mrest_box + 6 * (int64_t)m;
-    if (PRE) {
-        const float* mf = S.mrest_box_f + 6 * (int64_t)m;
-        if (!rest_far_f(D.sbf, D.sbf + 3, mf, mf + 3, P.far_r2_f) && !rest_far(D.sb, D.sb + 3, mb, mb + 3, eps))
-            return false;
-    } else if (!rest_far(D.sb, D.sb + 3, mb, mb + 3, eps)) {
-        return false;
-    }
+    if (!rest_far(D.sb, D.sb + 3, mb, mb + 3, eps)) return false;
     const int32_t* M = S.mtri + 3 * (int64_t)m;
     const V3<double> y0 = ld3(xm, M[0]);
     V3<float> e1, e2;
-    mtri_edges<PRE>(S, xm, mtri_e, m, e1, e2);
+    mtri_edges<false>(S, xm, nullptr, m, e1, e2);
     const V3<float> d = tof(y0 - F.xs);
     const V3<float> N = cross(e1, e2);
     const float nN = norm3f(N);
@@ -889,12 +883,7 @@ __device__ __forceinline__ bool face_cert(const SceneView& S, const Params& P, c
 // the slave-side closing rate of a certified edge or point item: dg =
 // -n_s . sum_a b_a dx_a with b from FP32 geometry (error <= tol_b each),
 // widened toward closing by tol_b sum_a |n_s . dx_a|
-template <bool PRE = false>
 __device__ __forceinline__ double cert_dg(const TriData& D, const double* b, float tol_b) {
-    if (PRE) {   // n_s . dx_a and their magnitudes' sum from the frame kernel
-        const double ds = b[0] * D.sdx[0] + b[1] * D.sdx[1] + b[2] * D.sdx[2];
-        return -ds - (double)tol_b * D.sdx[3];
-    }
     const double s0 = dot(D.ns, D.dx0), s1 = dot(D.ns, D.dx1), s2 = dot(D.ns, D.dx2);
     const double ds = b[0] * s0 + b[1] * s1 + b[2] * s2;
     return -ds - (double)tol_b * (fabs(s0) + fabs(s1) + fabs(s2));
@@ -904,28 +893,18 @@ __device__ __forceinline__ double cert_dg(const TriData& D, const double* b, flo
 // reading R3).  Barycentric coordinates are affine along the projected
 // edge, so beta^s and the plane gap at a Gauss point are the ends' values
 // mixed by eta.
-template <bool PRE = false>
 __device__ __forceinline__ bool edge_cert(const SceneView& S, const Params& P, const TriData& D,
-                                          const double* xm, int32_t me, int q, bool want_dg, ItemOut& o,
-                                          const float* mtri_e = nullptr) {
+                                          const double* xm, int32_t me, int q, bool want_dg, ItemOut& o) {
     const double eps = P.dhat;
     const int ia = S.medge[2 * (int64_t)me], ib = S.medge[2 * (int64_t)me + 1];
-    bool far = false;
-    if (PRE) {
-        const float* va = S.mvrest_box_f + 6 * (int64_t)ia;
-        const float* vb = S.mvrest_box_f + 6 * (int64_t)ib;
-        const float flo[3] = {fminf(va[0], vb[0]), fminf(va[1], vb[1]), fminf(va[2], vb[2])};
-        const float fhi[3] = {fmaxf(va[3], vb[3]), fmaxf(va[4], vb[4]), fmaxf(va[5], vb[5])};
-        far = rest_far_f(D.sbf, D.sbf + 3, flo, fhi, P.far_r2_f);
-    }
-    if (!far) {
+    {
         const V3<double> Ya = ld3(S.Y0, ia), Yb = ld3(S.Y0, ib);
         const double elo[3] = {rmin(Ya.x, Yb.x), rmin(Ya.y, Yb.y), rmin(Ya.z, Yb.z)};
         const double ehi[3] = {rmax(Ya.x, Yb.x), rmax(Ya.y, Yb.y), rmax(Ya.z, Yb.z)};
         if (!rest_far(D.sb, D.sb + 3, elo, ehi, eps)) return false;
     }
     const int a0 = S.me_tri_off[me], a1 = S.me_tri_off[me + 1];
-    if (!facing_cert<PRE>(S, xm, S.me_tri + a0, a1 - a0, D.ns_f, mtri_e)) return false;
+    if (!facing_cert<false>(S, xm, S.me_tri + a0, a1 - a0, D.ns_f)) return false;
     const V3<double> ya = ld3(xm, ia), yb = ld3(xm, ib);
     const V3<float> da = tof(ya - D.x0), db = tof(yb - D.x0);
     float bA[3], bB[3], tA, tB;
@@ -969,28 +948,21 @@ __device__ __forceinline__ bool edge_cert(const SceneView& S, const Params& P, c
     for (int c = 0; c < 3; ++c) o.b[c] = (double)((1.0f - eta) * bA[c] + eta * bB[c]);
     o.mv[0] = ia; o.mv[1] = ib; o.mv[2] = -1;
     o.bm[0] = 1.0 - (double)eta; o.bm[1] = (double)eta; o.bm[2] = 0.0;
-    o.dg = want_dg ? cert_dg<PRE>(D, o.b, tb) : 0.0;
+    o.dg = want_dg ? cert_dg(D, o.b, tb) : 0.0;
     return true;
 }
 
 // master vertex u projected on slave tri D (Sec. 4.1, reading R3)
-template <bool PRE = false>
 __device__ __forceinline__ bool point_cert(const SceneView& S, const Params& P, const TriData& D,
-                                           const double* xm, int32_t u, bool want_dg, ItemOut& o,
-                                           const float* mtri_e = nullptr) {
+                                           const double* xm, int32_t u, bool want_dg, ItemOut& o) {
     const double eps = P.dhat;
-    bool far = false;
-    if (PRE) {
-        const float* vu = S.mvrest_box_f + 6 * (int64_t)u;
-        far = rest_far_f(D.sbf, D.sbf + 3, vu, vu + 3, P.far_r2_f);
-    }
-    if (!far) {
+    {
         const V3<double> Y = ld3(S.Y0, u);
         const double yb[3] = {Y.x, Y.y, Y.z};
         if (!rest_far(D.sb, D.sb + 3, yb, yb, eps)) return false;
     }
     const int a0 = S.mv_tri_off[u], a1 = S.mv_tri_off[u + 1];
-    if (!facing_cert<PRE>(S, xm, S.mv_tri + a0, a1 - a0, D.ns_f, mtri_e)) return false;
+    if (!facing_cert<false>(S, xm, S.mv_tri + a0, a1 - a0, D.ns_f)) return false;
     const V3<float> d = tof(ld3(xm, u) - D.x0);
     float bs[3], tb;
     bool ok;
@@ -1005,7 +977,7 @@ __device__ __forceinline__ bool point_cert(const SceneView& S, const Params& P, 
     for (int c = 0; c < 3; ++c) o.b[c] = (double)bs[c];
     o.mv[0] = u; o.mv[1] = -1; o.mv[2] = -1;
     o.bm[0] = 1.0; o.bm[1] = 0.0; o.bm[2] = 0.0;
-    o.dg = want_dg ? cert_dg<PRE>(D, o.b, tb) : 0.0;
+    o.dg = want_dg ? cert_dg(D, o.b, tb) : 0.0;
     return true;
 }
 
