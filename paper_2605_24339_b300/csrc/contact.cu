@@ -431,9 +431,14 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
     const int n_active = *C.n_active;
     const int32_t ps = tri_stamp ? misc[kSlotPass] : 0;
     const int lane = threadIdx.x & 31;
-    // whole warps iterate together (the item slots are reserved per warp)
+    // whole warps iterate together (the item slots are reserved per warp),
+    // interleaved across blocks: the frame is FP64 work, and a warp-wide FP64
+    // instruction holds a sub-partition's narrow FP64 pipe for ~80 cycles, so
+    // a few thousand active tris must spread over the SMs rather than fill
+    // the first blocks
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t ib = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); ib < n_active; ib += stride) {
+    const int64_t wslot = blockIdx.x + (int64_t)gridDim.x * (threadIdx.x >> 5);
+    for (int64_t ib = 32 * wslot; ib < n_active; ib += stride) {
         const int i = (int)(ib + lane);
         const bool valid = i < n_active;
         int n = 0;
@@ -448,9 +453,10 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
             const V3<double> cr0 = cross(X1 - X0, X2 - X0);
             const double clen0 = sqrt(dot(cr0, cr0));
             double* f = frame + 8 * (int64_t)i;
-            f[0] = cr.x / clen; f[1] = cr.y / clen; f[2] = cr.z / clen;
+            const double ic = 1.0 / clen, ic0 = 1.0 / clen0;   // one FP64 division per normal
+            f[0] = cr.x * ic; f[1] = cr.y * ic; f[2] = cr.z * ic;
             f[3] = 0.5 * clen;
-            f[4] = cr0.x / clen0; f[5] = cr0.y / clen0; f[6] = cr0.z / clen0;
+            f[4] = cr0.x * ic0; f[5] = cr0.y * ic0; f[6] = cr0.z * ic0;
             f[7] = 1e-12 * (fabs(x0.x) + fabs(x0.y) + fabs(x0.z)) + 1e-30;
             if (tf32) {
                 const int e = S.stri_env[t];
@@ -483,7 +489,7 @@ __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ 
                 const double s0 = dot(ns, d0), s1 = dot(ns, d1), s2 = dot(ns, d2);
                 m64[0] = s0; m64[1] = s1; m64[2] = s2;
                 m64[3] = fabs(s0) + fabs(s1) + fabs(s2);
-                m32[9] = (float)(f[3] / (double)nk);
+                m32[9] = (float)(f[3] * (1.0 / (double)nk));   // nk a power of two: exact
                 m32[10] = (float)s0; m32[11] = (float)s1; m32[12] = (float)s2;
                 m32[13] = (float)m64[3] * 1.000001f;   // at least the sum
                 m32[14] = 0.0f; m32[15] = 0.0f;
