@@ -775,16 +775,16 @@ def newton_measurement(dev, start_step=20, n_states=4):
     return out
 
 
-def fingertip_step_scene(n_env):
+def fingertip_step_scene(n_env, layers=2):
     """The batched time-step workload: n_env fingertip environments with
-    tets (5 pads of 16-128 quads of 0.25 mm, 2 tet layers, around a perturbed
+    tets (5 pads of 16-128 quads of 0.25 mm, ``layers`` tet layers, around a perturbed
     convex object of 2k-80k triangles, each pad 1.5 dhat pressed toward it,
     top faces driven at 0.5 mm/s), generated in spawn worker processes past
     16 environments.  Returns (parts [(scene, x0) per env], the concatenated
     scene, its x0)."""
     from paper_2605_24339_b300 import scenes as S
     dhat = 1e-4
-    args = (5, (16, 128), 0.25e-3, 2, 0.5e-3, (2000, 80000), 15e-3, dhat, 1e5, 1e-3, 0.5e-3, 100, 3, 1,
+    args = (5, (16, 128), 0.25e-3, layers, 0.5e-3, (2000, 80000), 15e-3, dhat, 1e5, 1e-3, 0.5e-3, 100, 3, 1,
             1.5 * dhat, True)
     workers = max(1, min(32, os.cpu_count() or 1))
     if n_env > 16 and workers > 1:
@@ -799,10 +799,10 @@ def fingertip_step_scene(n_env):
     return parts, sc, np.concatenate([p[1] for p in parts])
 
 
-def batched_step_measurement(dev, n_env=16, steps=3, alone_envs=16):
+def batched_step_measurement(dev, n_env=16, steps=3, alone_envs=16, layers=2):
     """Batched time steps (ipc_newton_step_envs): n_env fingertip environments
     of the batched workload's recipe with their tetrahedra (5 pads of 16-128
-    quads of 0.25 mm, 2 tet layers, around a perturbed convex object of
+    quads of 0.25 mm, ``layers`` tet layers through their 0.5 mm, around a perturbed convex object of
     2k-80k triangles), every pad starting 1.5 dhat pressed toward its object
     (in contact from the first step) with its top face driven at 0.5 mm/s.
     Each environment has its own Newton iteration, solve, step bound and
@@ -815,11 +815,11 @@ def batched_step_measurement(dev, n_env=16, steps=3, alone_envs=16):
     import torch
     from paper_2605_24339_b300 import binding
     t0 = time.perf_counter()
-    parts, sc, x0 = fingertip_step_scene(n_env)
+    parts, sc, x0 = fingertip_step_scene(n_env, layers)
     gen_s = time.perf_counter() - t0
     top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
     vd = torch.as_tensor(sc.v_dirichlet, device="cuda")
-    out = {"workload": f"fingertip_batch {n_env} envs x 5 pads (16-128 quads, 2 tet layers, 4 samples/tri) vs "
+    out = {"workload": f"fingertip_batch {n_env} envs x 5 pads (16-128 quads, {layers} tet layers, 4 samples/tri) vs "
                        f"2k-80k-tri objects, pads 1.5 dhat pressed, top faces at 0.5 mm/s, h = 1 ms",
            "n_env": n_env, "n_vert": int(sc.X.shape[0]), "n_tet": int(sc.tets.shape[0]),
            "slave_tris": int(sc.stris.shape[0]), "master_tris": int(sc.mtris.shape[0]),
@@ -1226,6 +1226,8 @@ def main():
                     help="skip the time-step measurement (newton_step key)")
     ap.add_argument("--batch-envs", type=int, default=512,
                     help="environments in the batched measurement")
+    ap.add_argument("--step-layers", type=int, default=2,
+                    help="--mode batchstep: tet layers through each pad's 0.5 mm thickness")
     ap.add_argument("--step-envs", type=int, default=64,
                     help="environments in the batched time-step measurement")
     ap.add_argument("--dense-quads", type=int, default=256,
@@ -1269,7 +1271,8 @@ def main():
     elif args.mode == "profstep":
         run_profile_step(args)
     elif args.mode == "batchstep":
-        print(json.dumps(batched_step_measurement(0, n_env=args.step_envs, steps=max(1, args.steps))), flush=True)
+        print(json.dumps(batched_step_measurement(0, n_env=args.step_envs, steps=max(1, args.steps),
+                                                  layers=args.step_layers)), flush=True)
     elif args.mode == "batch":
         print(json.dumps(batched_measurement(0, n_env=args.batch_envs,
                                              steps=args.steps)), flush=True)
