@@ -353,6 +353,17 @@ def run_ours(args):
     if not args.no_newton:
         line["newton_step"] = newton_measurement(dev)
         line["batched_step"] = batched_step_measurement(dev, n_env=args.step_envs, steps=10)
+        if args.big_step_envs > 0:
+            # the batched workload's full environment count, stepped: one tet layer per pad, since
+            # two layers need ~320 GB at 512 environments (42.8 GB measured at 64)
+            import torch
+            torch.cuda.empty_cache()
+            free_gb = torch.cuda.mem_get_info()[0] / 1e9
+            if free_gb >= 230:
+                line["batched_step_full"] = batched_step_measurement(dev, n_env=args.big_step_envs, steps=10,
+                                                                     layers=1)
+            else:
+                line["batched_step_full"] = {"skipped": f"{free_gb:.0f} GB free, 230 GB wanted"}
         line["warm_start"] = warm_start_measurement(dev)
     if not args.no_newton:
         line["patch_test"] = patch_measurement(dev)
@@ -1228,6 +1239,8 @@ def main():
                     help="environments in the batched measurement")
     ap.add_argument("--step-layers", type=int, default=2,
                     help="--mode batchstep: tet layers through each pad's 0.5 mm thickness")
+    ap.add_argument("--big-step-envs", type=int, default=512,
+                    help="environments of the one-layer batched time-step measurement (0 skips it)")
     ap.add_argument("--step-envs", type=int, default=64,
                     help="environments in the batched time-step measurement")
     ap.add_argument("--dense-quads", type=int, default=256,
