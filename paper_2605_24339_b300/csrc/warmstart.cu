@@ -7,11 +7,15 @@
 //   weight grads dW[o, i] = sum_m dZ[m, o] H[m, i]  (M = 256, N = 256 | 32, K = vertices)
 // as tcgen05.mma kind::f16 (BF16 operands in shared memory, FP32 accumulators
 // in tensor memory), issued by one thread, completion signalled through an
-// mbarrier, accumulators read back with tcgen05.ld.  Operand tiles use the
-// no-swizzle K-major canonical layout: 8 x 16-byte core matrices, K-adjacent
-// core matrices 128 B apart (leading byte offset), 8-row groups (K/8) * 128 B
-// apart (stride byte offset).  The 256 -> 3 head, bias sums and Adam run on
-// the CUDA cores.  Every sum is in a fixed order, so training is deterministic.
+// mbarrier, accumulators read back with tcgen05.ld.  Operand tiles come in
+// by TMA (cp.async.bulk.tensor) in the swizzled K-major layout (rows of 64
+// or 32 BF16 values, 16-byte pieces permuted by the row index, 8-row groups
+// 1024 or 512 B apart), through rings of shared-memory stages, with loads,
+// MMAs and the epilogue in separate warps.  The 256 -> 3 head, bias sums and
+// Adam run on the CUDA cores.  Every sum is in a fixed order, so training is
+// deterministic.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -58,17 +62,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// shared-memory matrix descriptor: start address, leading / stride byte
-// offsets (all >> 4), descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
 // instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -96,7 +89,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;"); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count));
@@ -132,51 +124,52 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// byte offset of element (r, k) of a K-major no-swizzle tile with K columns
-__device__ __forceinline__ uint32_t tile_off(int r, int k, int K) {
-    return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
-}
-
-// 16-byte asynchronous global -> shared copy; src_bytes 0 fills zeros
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// queue the copy of rows [row0, row0 + R) x columns [k0, k0 + K) of a
-// row-major BF16 matrix (row stride ld elements; rows >= nrows read as zero)
-// into a K-major tile; eight consecutive threads fill one core matrix
-__device__ __forceinline__ void stage_tile_async(uint8_t* tile, const __nv_bfloat16* src, int64_t ld, int64_t row0,
-                                                 int64_t nrows, int R, int K, int64_t k0) {
-    const int per_row = K >> 3;
-    const int total = R * per_row;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-        const int rr = idx & 7;
-        const int j = (idx >> 3) % per_row;
-        const int rg = (idx >> 3) / per_row;
-        const int r = rg * 8 + rr;
-        const int64_t gr = row0 + r;
-        const bool ok = gr < nrows;
-        cp_async16(tile + tile_off(r, 8 * j, K), ok ? (const void*)(src + gr * ld + k0 + 8 * j) : (const void*)src,
-                   ok ? 16u : 0u);
-    }
-}
-
 // ----------------------------------------------------- activation GEMM ---
 // C = epilogue(A W^T), A [mp][K] BF16 row-major, W [256][K] BF16 row-major
 // (K-major), persistent over 128-row tiles with W resident in shared memory.
-// Two tensor-memory accumulators: the epilogue of tile i-1 runs while the
-// MMAs of tile i execute.  EPI 0: + bias, ReLU.  EPI 1: times (mask > 0),
-// mask [mp][256] BF16 (the previous layer's activation).  Writes C [mp][256]
-// (if non-null) and C^T [256][mp] (if non-null).
+// EPI 0: + bias, ReLU.  EPI 1: times (mask > 0), mask [mp][256] BF16 (the
+// previous layer's activation).  Writes C [mp][256] (if non-null) and
+// C^T [256][mp] (if non-null).  The operand tiles are brought in by the
+// tensor-memory accelerator (cp.async.bulk.tensor) in the swizzled K-major
+// layout: each tile row holds KC = min(K, 64) BF16 values (128 or 64 bytes)
+// with its 16-byte pieces permuted by the row index, the layout both TMA and
+// the tcgen05 shared-memory descriptors name SWIZZLE_128B / SWIZZLE_64B.
+// Roles: warp 0 loads (W once, then the A chunks of every tile into a ring
+// of NST stages), warp 1 issues the MMAs (one thread), warps 2..9 run the
+// epilogue out of two tensor-memory accumulators, so that loads, MMAs and
+// the epilogue of three consecutive tiles overlap.  The MMAs of a tile run
+// in increasing K, one K = 16 step at a time.
+__device__ __forceinline__ uint64_t umma_desc_sw(uint32_t saddr, int swz_bytes) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                                   // leading offset: unused when swizzled
+    d |= (uint64_t)(((8u * (uint32_t)swz_bytes) >> 4) & 0x3FFFu) << 32;  // 8-row groups apart
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)(swz_bytes == 128 ? 2 : 4) << 61;         // SWIZZLE_128B | SWIZZLE_64B
+    return d;
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+// 2D tiled TMA load of box (x, y) into shared memory, completing on mbar
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(mbar))
+        : "memory");
+}
+
 template <int K, int EPI>
-__device__ __forceinline__ void act_epilogue(uint32_t tacc, int64_t m0, int64_t mp, const float* __restrict__ bias,
-                                             const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ C,
-                                             __nv_bfloat16* __restrict__ CT) {
-    // warp w reads TMEM lanes 32 (w % 4) ..; the two warpgroups split the columns
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+__device__ __forceinline__ void act_epilogue_rows(uint32_t tacc, int quarter, int half, int64_t m0, int64_t mp,
+                                                  const float* __restrict__ bias,
+                                                  const __nv_bfloat16* __restrict__ mask,
+                                                  __nv_bfloat16* __restrict__ C, __nv_bfloat16* __restrict__ CT) {
+    const int lane = threadIdx.x & 31;
     const int r = quarter * 32 + lane;
     const int64_t gr = m0 + r;
     for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
@@ -211,179 +204,214 @@ __device__ __forceinline__ void act_epilogue(uint32_t tacc, int64_t m0, int64_t 
     }
 }
 
+template <int K>
+struct ActTma {
+    static constexpr int KC = K < 64 ? K : 64;          // BF16 values per tile row (one swizzle span)
+    static constexpr int SWZ = KC * 2;                  // bytes per tile row: 128 or 64
+    static constexpr int NCH = K / KC;                  // K chunks
+    static constexpr int NST = K >= 256 ? 5 : 8;        // A ring stages
+    static constexpr uint32_t A_BYTES = 128u * SWZ;     // one A chunk (128 rows)
+    static constexpr uint32_t W_BYTES = 256u * SWZ;     // one W chunk (256 rows)
+    static constexpr size_t SMEM = (size_t)NCH * W_BYTES + (size_t)NST * A_BYTES + 1024;  // + alignment
+    static constexpr int THREADS = 320;
+};
+
 template <int K, int EPI>
-__global__ void __launch_bounds__(256, 1)
-k_umma_act(const __nv_bfloat16* __restrict__ A, int64_t mp, const __nv_bfloat16* __restrict__ W,
-           const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ C,
-           __nv_bfloat16* __restrict__ CT, int* __restrict__ err) {
-    extern __shared__ __align__(1024) uint8_t smem[];
-    uint8_t* sW = smem;                                  // 256 x K
-    uint8_t* sA = smem + 256 * K * 2;                    // 128 x K
-    __shared__ __align__(8) uint64_t mbar;
+__global__ void __launch_bounds__(320, 1)
+k_umma_act_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmW, int64_t mp,
+               const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
+               __nv_bfloat16* __restrict__ C, __nv_bfloat16* __restrict__ CT, int* __restrict__ err) {
+    using T = ActTma<K>;
+    extern __shared__ uint8_t smem_raw[];
+    // the swizzled tiles want 1024-byte aligned bases
+    const uint32_t base_u = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + (((base_u + 1023u) & ~1023u) - base_u);
+    uint8_t* sW = smem;                                  // NCH chunks of 256 rows
+    uint8_t* sA = smem + T::NCH * T::W_BYTES;            // NST chunks of 128 rows
+    __shared__ __align__(8) uint64_t full[T::NST], empty[T::NST], wfull, accf[2], acce[2];
     __shared__ uint32_t tslot;
-    __shared__ int abort_flag;
-    const int warp = threadIdx.x >> 5;
-    if (warp == 0) tmem_alloc(&tslot, 512);
-    if (threadIdx.x == 0) { mbar_init(&mbar, 1); abort_flag = 0; }
-    stage_tile_async(sW, W, K, 0, 256, 256, K, 0);
-    cp_async_commit();
-    cp_async_wait_all();
-    fence_async_smem();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 1) tmem_alloc(&tslot, 512);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < T::NST; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        mbar_init(&wfull, 1);
+        for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 8); }
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
-    const uint32_t idesc = idesc_bf16(128, 256);
-    const uint32_t sbo = (K / 8) * 128;
-    uint32_t phase = 0;
     const int64_t ntiles = mp / 128;
-    int64_t prev = -1;                                   // tile whose epilogue is pending
-    int buf = 0;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t m0 = tile * 128;
-        stage_tile_async(sA, A, K, m0, mp, 128, K, 0);
-        cp_async_commit();
-        cp_async_wait_all();
-        fence_async_smem();
-        tc_fence_before();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc_fence_after();
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            mbar_expect_tx(&wfull, T::NCH * T::W_BYTES);
+            for (int c = 0; c < T::NCH; ++c) tma_load_2d(sW + c * T::W_BYTES, &tmW, c * T::KC, 0, &wfull);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int c = 0; c < T::NCH; ++c, ++it) {
+                    const uint32_t st = it % T::NST, ph = (it / T::NST) & 1u;
+                    if (!mbar_wait(&empty[st], ph ^ 1u)) { atomicExch(err, 1); ok = false; break; }
+                    mbar_expect_tx(&full[st], T::A_BYTES);
+                    tma_load_2d(sA + st * T::A_BYTES, &tmA, c * T::KC, (int)(tile * 128), &full[st]);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            const uint32_t idesc = idesc_bf16(128, 256);
+            bool ok = mbar_wait(&wfull, 0);
+            if (!ok) atomicExch(err, 1);
+            uint32_t it = 0, t = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++t) {
+                const uint32_t b = t & 1u, use = t >> 1;
+                if (!mbar_wait(&acce[b], (use & 1u) ^ 1u)) { atomicExch(err, 1); break; }
+                tc_fence_after();
+                for (int c = 0; c < T::NCH; ++c, ++it) {
+                    const uint32_t st = it % T::NST, ph = (it / T::NST) & 1u;
+                    if (!mbar_wait(&full[st], ph)) { atomicExch(err, 1); ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(sA + st * T::A_BYTES), w0 = smem_u32(sW + c * T::W_BYTES);
 #pragma unroll
-            for (int s = 0; s < K / 16; ++s)
-                umma_bf16(tmem + (uint32_t)(buf * 256), umma_desc(smem_u32(sA) + 256 * s, 128, sbo),
-                          umma_desc(smem_u32(sW) + 256 * s, 128, sbo), idesc, s > 0 ? 1u : 0u);
-            umma_commit(&mbar);
+                    for (int kk = 0; kk < T::KC / 16; ++kk)
+                        umma_bf16(tmem + b * 256u, umma_desc_sw(a0 + 32u * kk, T::SWZ),
+                                  umma_desc_sw(w0 + 32u * kk, T::SWZ), idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(&empty[st]);             // the stage is free once these MMAs finish
+                }
+                if (ok) umma_commit(&accf[b]);
+            }
         }
-        // the previous tile's epilogue overlaps these MMAs
-        if (prev >= 0) {
+    } else {
+        // epilogue: warps 2..9; warp w reads TMEM lanes 32 (w % 4) .. (its quarter of the tile's rows)
+        const int quarter = warp & 3, half = (warp - 2) >> 2;
+        uint32_t t = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+            const uint32_t b = t & 1u, use = t >> 1;
+            const bool got = mbar_wait(&accf[b], use & 1u);
+            if (!__all_sync(0xffffffffu, got)) { atomicExch(err, 1); break; }   // the whole warp leaves
             tc_fence_after();
-            act_epilogue<K, EPI>(tmem + (uint32_t)((buf ^ 1) * 256), prev * 128, mp, bias, mask, C, CT);
+            act_epilogue_rows<K, EPI>(tmem + b * 256u, quarter, half, tile * 128, mp, bias, mask, C, CT);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce[b]);
         }
-        if (!mbar_wait(&mbar, phase)) {
-            atomicExch(err, 1);
-            abort_flag = 1;
-        }
-        phase ^= 1u;
-        tc_fence_before();
-        __syncthreads();
-        if (abort_flag) { prev = -1; break; }
-        prev = tile;
-        buf ^= 1;
-    }
-    if (prev >= 0) {
-        tc_fence_after();
-        act_epilogue<K, EPI>(tmem + (uint32_t)((buf ^ 1) * 256), prev * 128, mp, bias, mask, C, CT);
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, 512);
+    if (warp == 1) tmem_dealloc(tmem, 512);
 }
 
-// ---------------------------------------------- weight-gradient GEMM ---
+// ------------------------------------------------ weight-gradient GEMM ---
 // partial[b][o][n] = sum over this CTA's vertex range of AT[o][m] BT[n][m]
 // (AT [256][mp], BT [NP][mp], BF16 row-major), split-K over vertices in
-// 64-wide chunks, two shared-memory stages (the next chunk loads while the
-// current one multiplies), two M = 128 accumulators (o < 128, o >= 128).
-// The row sums of AT over the same range (the bias gradient) are taken from
-// the staged tiles: bpart[b][o].
+// 64-wide chunks, two M = 128 accumulators (o < 128, o >= 128), and the row
+// sums of AT over the same range (the bias gradient): bpart[b][o].  The
+// chunks come in by TMA (128-byte swizzled K-major tiles: AT chunk 256 x 64,
+// BT chunk NP x 64) through a ring of NST stages.  Warp 0 loads, warp 1
+// issues the MMAs, warps 2..9 take the bias row sums from each staged AT
+// chunk (one row a thread, un-permuting the swizzle so that each row is
+// summed in increasing m) and, at the end, write the accumulators.
 template <int NP>
-__global__ void __launch_bounds__(256, 1)
-k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restrict__ BT, int64_t mp,
-             float* __restrict__ partial, float* __restrict__ bpart, int* __restrict__ err) {
-    constexpr int KC = 64;
-    constexpr uint32_t NCOL = (2 * NP) < 32 ? 32 : 2 * NP;
-    constexpr int SA = 256 * KC * 2, SB = NP * KC * 2;
-    extern __shared__ __align__(1024) uint8_t smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+struct WgradTma {
+    static constexpr int KC = 64;
+    static constexpr uint32_t SA = 256u * 128u, SB = (uint32_t)NP * 128u;
+    static constexpr int NST = NP >= 256 ? 3 : 5;
+    static constexpr uint32_t NCOL = (2 * NP) < 32 ? 32 : 2 * NP;
+    static constexpr size_t SMEM = (size_t)NST * (SA + SB) + 1024;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(320, 1)
+k_umma_wgrad_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t mp,
+                 float* __restrict__ partial, float* __restrict__ bpart, int* __restrict__ err) {
+    using T = WgradTma<NP>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t base_u = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + (((base_u + 1023u) & ~1023u) - base_u);
+    __shared__ __align__(8) uint64_t full[T::NST], empty[T::NST], accf;
     __shared__ uint32_t tslot;
-    __shared__ int abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0) tmem_alloc(&tslot, NCOL);
-    if (threadIdx.x == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); abort_flag = 0; }
+    if (warp == 1) tmem_alloc(&tslot, T::NCOL);
+    if (threadIdx.x == 0) {
+        // a stage is free when its MMAs finished (one commit) and the eight
+        // row-sum warps are done with it
+        for (int i = 0; i < T::NST; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 9); }
+        mbar_init(&accf, 1);
+    }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tslot;
-    const uint32_t idesc = idesc_bf16(128, NP);
-    const uint32_t sbo = (KC / 8) * 128;
-    const int64_t nch = mp / KC;
+    const int64_t nch = mp / T::KC;
     const int64_t c0 = nch * blockIdx.x / gridDim.x, c1 = nch * (blockIdx.x + 1) / gridDim.x;
-    uint32_t ph[2] = {0, 0};
-    bool used[2] = {false, false};
-    float rs = 0.0f;                                    // row sum of row tid
-    auto stage_of = [&](int st) { return smem + st * (SA + SB); };
-    if (c1 > c0) {
-        stage_tile_async(stage_of(0), AT, mp, 0, 256, 256, KC, c0 * KC);
-        stage_tile_async(stage_of(0) + SA, BT, mp, 0, NP, NP, KC, c0 * KC);
-        cp_async_commit();
-    }
-    for (int64_t ch = c0; ch < c1; ++ch) {
-        const int st = (int)((ch - c0) & 1);
-        uint8_t* sA = stage_of(st);
-        uint8_t* sB = sA + SA;
-        cp_async_wait_all();
-        fence_async_smem();
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int s = 0; s < KC / 16; ++s)
-                    umma_bf16(tmem + (uint32_t)(h * NP),
-                              umma_desc(smem_u32(sA) + (uint32_t)(h * 16) * sbo + 256 * s, 128, sbo),
-                              umma_desc(smem_u32(sB) + 256 * s, 128, sbo), idesc, (ch > c0 || s > 0) ? 1u : 0u);
-            umma_commit(&mbar[st]);
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            for (int64_t ch = c0; ch < c1; ++ch, ++it) {
+                const uint32_t st = it % T::NST, ph = (it / T::NST) & 1u;
+                if (!mbar_wait(&empty[st], ph ^ 1u)) { atomicExch(err, 1); break; }
+                uint8_t* sA = smem + st * (T::SA + T::SB);
+                mbar_expect_tx(&full[st], T::SA + T::SB);
+                tma_load_2d(sA, &tmA, (int)(ch * T::KC), 0, &full[st]);
+                tma_load_2d(sA + T::SA, &tmB, (int)(ch * T::KC), 0, &full[st]);
+            }
         }
-        used[st] = true;
-        // bias gradient: row sums of the staged AT rows (read-only use of the stage)
-        {
-            const int r = threadIdx.x;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(128, NP);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int64_t ch = c0; ch < c1; ++ch, ++it) {
+                const uint32_t st = it % T::NST, ph = (it / T::NST) & 1u;
+                if (!mbar_wait(&full[st], ph)) { atomicExch(err, 1); ok = false; break; }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(smem + st * (T::SA + T::SB)), b0 = a0 + T::SA;
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int s = 0; s < T::KC / 16; ++s)
+                        umma_bf16(tmem + (uint32_t)(h * NP), umma_desc_sw(a0 + (uint32_t)h * 16384u + 32u * s, 128),
+                                  umma_desc_sw(b0 + 32u * s, 128), idesc, (ch > c0 || s > 0) ? 1u : 0u);
+                umma_commit(&empty[st]);
+            }
+            if (ok && c1 > c0) umma_commit(&accf);
+        }
+    } else {
+        const int row = (warp - 2) * 32 + lane;          // AT row summed by this thread
+        float rs = 0.0f;
+        bool ok = true;
+        uint32_t it = 0;
+        for (int64_t ch = c0; ch < c1; ++ch, ++it) {
+            const uint32_t st = it % T::NST, ph = (it / T::NST) & 1u;
+            const bool got = mbar_wait(&full[st], ph);
+            if (!__all_sync(0xffffffffu, got)) { atomicExch(err, 1); ok = false; break; }
+            const uint8_t* rowp = smem + st * (T::SA + T::SB) + (row >> 3) * 1024 + (row & 7) * 128;
             float acc = 0.0f;
 #pragma unroll
-            for (int j = 0; j < KC / 8; ++j) {
-                const uint4 u = *reinterpret_cast<const uint4*>(sA + tile_off(r, 8 * j, KC));
+            for (int j = 0; j < T::KC / 8; ++j) {
+                const uint4 u = *reinterpret_cast<const uint4*>(rowp + ((j ^ (row & 7)) << 4));
                 const __nv_bfloat16* b = reinterpret_cast<const __nv_bfloat16*>(&u);
 #pragma unroll
                 for (int i = 0; i < 8; ++i) acc += __bfloat162float(b[i]);
             }
             rs += acc;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[st]);
         }
-        // prefetch the next chunk into the other stage once its MMAs finished
-        if (ch + 1 < c1) {
-            const int nst = st ^ 1;
-            if (used[nst]) {
-                if (!mbar_wait(&mbar[nst], ph[nst])) { atomicExch(err, 1); abort_flag = 1; }
-                ph[nst] ^= 1u;
-                used[nst] = false;
-            }
-            __syncthreads();
-            if (abort_flag) break;
-            stage_tile_async(stage_of(nst), AT, mp, 0, 256, 256, KC, (ch + 1) * KC);
-            stage_tile_async(stage_of(nst) + SA, BT, mp, 0, NP, NP, KC, (ch + 1) * KC);
-            cp_async_commit();
-        }
-    }
-    cp_async_wait_all();
-    // drain: wait for the MMAs still in flight
-    for (int st = 0; st < 2; ++st)
-        if (used[st] && !abort_flag) {
-            if (!mbar_wait(&mbar[st], ph[st])) { atomicExch(err, 1); abort_flag = 1; }
-            ph[st] ^= 1u;
-        }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    // warpgroup h reads accumulator h (rows o = 128 h + TMEM lane)
-    float* out = partial + (int64_t)blockIdx.x * 256 * NP;
-    {
-        const int h = warp >> 2, quarter = warp & 3;
+        // warps 2..9: accumulator h = (warp - 2) / 4, TMEM lanes 32 (warp % 4) ..
+        const int quarter = warp & 3, h = (warp - 2) >> 2;
         const int o = h * 128 + quarter * 32 + lane;
+        bool have = ok && c1 > c0 && mbar_wait(&accf, 0);
+        if (ok && c1 > c0 && !have) atomicExch(err, 1);
+        have = __all_sync(0xffffffffu, have);          // tcgen05.ld wants the whole warp
+        tc_fence_after();
+        float* out = partial + (int64_t)blockIdx.x * 256 * NP;
         for (int n0 = 0; n0 < NP; n0 += 16) {
             float v[16];
-            if (c1 > c0 && !abort_flag) {
+            if (have) {
                 tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(h * NP + n0), v);
             } else {
 #pragma unroll
@@ -392,12 +420,12 @@ k_umma_wgrad(const __nv_bfloat16* __restrict__ AT, const __nv_bfloat16* __restri
 #pragma unroll
             for (int i = 0; i < 16; ++i) out[(int64_t)o * NP + n0 + i] = v[i];
         }
+        bpart[(int64_t)blockIdx.x * 256 + row] = rs;
     }
-    bpart[(int64_t)blockIdx.x * 256 + threadIdx.x] = rs;
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(tmem, NCOL);
+    if (warp == 1) tmem_dealloc(tmem, T::NCOL);
 }
 
 // ------------------------------------------------------- CUDA-core part ---
@@ -486,21 +514,31 @@ __global__ void __launch_bounds__(1024) k_sum_parts(const double* __restrict__ p
 // visits; per block, the warps' sums are combined in warp order into
 // wpart[block][4][256] (rows 0-2 dW4, row 3 db4 in its first 3 entries).
 constexpr int kHeadRows = 32;
-__global__ void __launch_bounds__(256)
+constexpr int kHeadLd = kHid + 4;                 // row stride of the transposition tile (BF16 values)
+// Per-vertex head and loss: lane l of a warp holds columns 8 l .. 8 l + 7
+// of a row (one 16-byte load of h3, one 16-byte store of dz3) and the
+// matching 24 weights of W4 in registers; the three dot products are summed
+// over the warp by butterfly shuffles.  Each block walks tiles of 32 rows;
+// dz3^T leaves through a shared-memory transposition in 16-byte pieces.
+__global__ void __launch_bounds__(256, 2)
 k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, const float* __restrict__ target,
            const float* __restrict__ mask, int64_t n, int64_t mp, const double* __restrict__ msum,
            float* __restrict__ y, float* __restrict__ dy, __nv_bfloat16* __restrict__ dz3,
            __nv_bfloat16* __restrict__ dz3T, double* __restrict__ loss_part, float* __restrict__ wpart) {
-    __shared__ float w4[kOut * kHid];
-    __shared__ __nv_bfloat16 tileT[kHeadRows][kHid + 2];
+    __shared__ __align__(16) __nv_bfloat16 tileT[kHeadRows][kHeadLd];
     __shared__ double lsh[8];
     __shared__ float wsh[8][4][32];
     __shared__ double inv_den_s;
-    for (int i = threadIdx.x; i < kOut * kHid; i += blockDim.x) w4[i] = P[kOffW4 + i];
     // one FP64 reciprocal per block (FP64 runs at a small fraction of FP32 here)
     if (threadIdx.x == 0) inv_den_s = *msum > 0.0 ? 1.0 / (3.0 * (*msum)) : 0.0;
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j0 = 8 * lane;                       // this lane's first column
+    float w[3][8];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) w[c][i] = P[kOffW4 + c * kHid + j0 + i];
     const float inv_den = (float)inv_den_s;
     const float b0 = P[kOffB4], b1 = P[kOffB4 + 1], b2 = P[kOffB4 + 2];
     const int64_t ntile = mp / kHeadRows;
@@ -511,26 +549,41 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int i = 0; i < 8; ++i) gw[c][i] = 0.0f;
-    for (int64_t tile = t0; tile < t1; ++tile) {
-        const int64_t m0 = tile * kHeadRows;
-        // the warp's 4 rows together: all their loads are in flight at once
-        constexpr int RW = kHeadRows / 8;
-        float hv[RW][8], acc[RW][3];
+    // the warp's 4 rows of a tile travel together, and the next tile's rows
+    // (with their masks and targets) are loaded while this one is processed
+    constexpr int RW = kHeadRows / 8;
+    uint4 raw[RW];
+    float mkv[RW], tgv[RW];
+    auto load_rows = [&](int64_t tile, uint4* rw, float* mk, float* tg) {
 #pragma unroll
         for (int rr = 0; rr < RW; ++rr) {
-            const int64_t m = m0 + warp * RW + rr;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) hv[rr][i] = __bfloat162float(h3[m * kHid + lane + 32 * i]);
+            const int64_t m = tile * kHeadRows + warp * RW + rr;
+            rw[rr] = __ldg(reinterpret_cast<const uint4*>(h3 + m * kHid + j0));
+            mk[rr] = m < n ? __ldg(mask + m) : 0.0f;
+            tg[rr] = (m < n && lane < 3) ? __ldg(target + 3 * m + lane) : 0.0f;
         }
+    };
+    if (t0 < t1) load_rows(t0, raw, mkv, tgv);
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        const int64_t m0 = tile * kHeadRows;
+        float hv[RW][8], acc[RW][3], mkc[RW], tgc[RW];
+#pragma unroll
+        for (int rr = 0; rr < RW; ++rr) {
+            const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&raw[rr]);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) hv[rr][i] = __bfloat162float(hb[i]);
+            mkc[rr] = mkv[rr];
+            tgc[rr] = tgv[rr];
+        }
+        if (tile + 1 < t1) load_rows(tile + 1, raw, mkv, tgv);
 #pragma unroll
         for (int rr = 0; rr < RW; ++rr) {
             acc[rr][0] = acc[rr][1] = acc[rr][2] = 0.0f;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int j = lane + 32 * i;
-                acc[rr][0] += hv[rr][i] * w4[j];
-                acc[rr][1] += hv[rr][i] * w4[kHid + j];
-                acc[rr][2] += hv[rr][i] * w4[2 * kHid + j];
+                acc[rr][0] += hv[rr][i] * w[0][i];
+                acc[rr][1] += hv[rr][i] * w[1][i];
+                acc[rr][2] += hv[rr][i] * w[2][i];
             }
         }
 #pragma unroll
@@ -546,12 +599,12 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
             // every lane holds y; lane c < 3 forms component c of the loss
             // term and of dy in FP32, lane 0 accumulates the loss in FP64
             float dc = 0.0f;
-            const bool live = m < n && mask[m] != 0.0f && inv_den > 0.0f;
+            const bool live = m < n && mkc[rr] != 0.0f && inv_den > 0.0f;
             float lt = 0.0f;
             if (live && lane < 3) {
                 const float yy = acc[rr][lane] + (lane == 0 ? b0 : (lane == 1 ? b1 : b2));
-                const float e = yy - target[3 * m + lane];
-                const float mk = mask[m];
+                const float e = yy - tgc[rr];
+                const float mk = mkc[rr];
                 lt = mk * e * e * inv_den;
                 dc = 2.0f * mk * e * inv_den;
                 y[3 * m + lane] = yy;
@@ -562,20 +615,28 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
             if (lane == 0) lterm += (double)lt + (double)l1 + (double)l2;
             if (lane < 3) dy[3 * m + lane] = dc;
             gb[0] += d0; gb[1] += d1; gb[2] += d2;
+            __align__(16) __nv_bfloat16 o[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int j = lane + 32 * i;
                 gw[0][i] += d0 * hv[rr][i]; gw[1][i] += d1 * hv[rr][i]; gw[2][i] += d2 * hv[rr][i];
-                const float g = d0 * w4[j] + d1 * w4[kHid + j] + d2 * w4[2 * kHid + j];
-                const __nv_bfloat16 o = __float2bfloat16_rn(hv[rr][i] > 0.0f ? g : 0.0f);
-                dz3[m * kHid + j] = o;
-                tileT[r][j] = o;
+                const float g = d0 * w[0][i] + d1 * w[1][i] + d2 * w[2][i];
+                o[i] = __float2bfloat16_rn(hv[rr][i] > 0.0f ? g : 0.0f);
             }
+            const uint4 ov = *reinterpret_cast<const uint4*>(o);
+            *reinterpret_cast<uint4*>(dz3 + m * kHid + j0) = ov;
+            // kHeadLd * 2 bytes is a multiple of 8: two 8-byte pieces
+            uint2* tp = reinterpret_cast<uint2*>(&tileT[r][j0]);
+            tp[0] = make_uint2(ov.x, ov.y);
+            tp[1] = make_uint2(ov.z, ov.w);
         }
         __syncthreads();
-        for (int idx = threadIdx.x; idx < kHeadRows * kHid; idx += blockDim.x) {
-            const int r = idx & (kHeadRows - 1), j = idx / kHeadRows;
-            dz3T[(int64_t)j * mp + m0 + r] = tileT[r][j];
+        // dz3^T[j][m0 .. m0 + 31]: four threads a column, eight rows (16 bytes) each
+        for (int idx = threadIdx.x; idx < 4 * kHid; idx += blockDim.x) {
+            const int j = idx >> 2, seg = idx & 3;
+            __align__(16) __nv_bfloat16 col[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) col[q] = tileT[8 * seg + q][j];
+            *reinterpret_cast<uint4*>(dz3T + (int64_t)j * mp + m0 + 8 * seg) = *reinterpret_cast<const uint4*>(col);
         }
         __syncthreads();
     }
@@ -589,8 +650,10 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
         if (threadIdx.x < 128) {
             const int c = threadIdx.x >> 5, l = threadIdx.x & 31;
             float t = 0.0f;
-            for (int w = 0; w < 8; ++w) t += wsh[w][c][l];
-            out[c * kHid + l + 32 * i] = t;
+            for (int w8 = 0; w8 < 8; ++w8) t += wsh[w8][c][l];
+            // slot c < 3: column 8 l + i of dW4 row c; slot 3: db4 (lanes 0..2 of slice 0)
+            if (c < 3) out[c * kHid + 8 * l + i] = t;
+            else if (i == 0) out[3 * kHid + l] = t;
         }
         __syncthreads();
     }
@@ -598,7 +661,7 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < 8; ++w) t += lsh[w];
+        for (int w8 = 0; w8 < 8; ++w8) t += lsh[w8];
         loss_part[blockIdx.x] = t;
     }
 }
@@ -693,29 +756,71 @@ __global__ void k_predict(const float* __restrict__ y, const double* __restrict_
 
 unsigned nb(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
-constexpr size_t kActSmem(int K) { return (size_t)256 * K * 2 + (size_t)128 * K * 2; }
 // at least this much dynamic shared memory keeps one CTA per SM, so the
 // tensor-memory allocations of co-resident CTAs never exceed 512 columns
 constexpr size_t kOneCtaSmem = 120 * 1024;
 
+// cuTensorMapEncodeTiled from the driver (through the runtime, so the library
+// needs no link against libcuda)
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// tensor map of a row-major BF16 matrix [rows][cols] (cols contiguous),
+// read in boxes of box_rows x box_cols with the swizzle of a box_cols * 2
+// byte row (128 or 64 bytes)
+cudaError_t bf16_tmap(CUtensorMap* m, const __nv_bfloat16* base, int64_t rows, int cols, int box_rows,
+                      int box_cols) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tmap_encoder();
+    if (!enc) return cudaErrorNotSupported;
+    if (((uintptr_t)base & 15u) != 0 || (cols * 2) % 16 != 0 || (box_cols * 2 != 128 && box_cols * 2 != 64))
+        return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims, strides,
+                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           box_cols * 2 == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int K, int EPI>
 cudaError_t launch_act(Ctx& c, WarmStart& W, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const float* bias,
                        const __nv_bfloat16* mask, __nv_bfloat16* C, __nv_bfloat16* CT) {
-    const size_t sm = std::max(kActSmem(K), kOneCtaSmem);
-    GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_act<K, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    using T = ActTma<K>;
+    CUtensorMap ta, tw;
+    GMCP_CUDA_TRY(bf16_tmap(&ta, A, W.mp, K, 128, T::KC));
+    GMCP_CUDA_TRY(bf16_tmap(&tw, Wt, 256, K, 256, T::KC));
+    const size_t sm = std::max(T::SMEM, kOneCtaSmem);
+    GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_act_tma<K, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = (int)std::min<int64_t>(sm_count(c.device), W.mp / 128);
-    k_umma_act<K, EPI><<<grid, 256, sm, c.stream>>>(A, W.mp, Wt, bias, mask, C, CT, W.err.p);
+    k_umma_act_tma<K, EPI><<<grid, T::THREADS, sm, c.stream>>>(ta, tw, W.mp, bias, mask, C, CT, W.err.p);
     return cudaGetLastError();
 }
 
 template <int NP>
 cudaError_t launch_wgrad(Ctx& c, WarmStart& W, const __nv_bfloat16* AT, const __nv_bfloat16* BT, float* out,
                          float* bias_out) {
-    const size_t sm = std::max((size_t)2 * (256 + NP) * 64 * 2, kOneCtaSmem);
-    GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_wgrad<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    using T = WgradTma<NP>;
+    CUtensorMap ta, tb;
+    GMCP_CUDA_TRY(bf16_tmap(&ta, AT, 256, W.mp, 256, T::KC));
+    GMCP_CUDA_TRY(bf16_tmap(&tb, BT, NP, W.mp, NP, T::KC));
+    const size_t sm = std::max(T::SMEM, kOneCtaSmem);
+    GMCP_CUDA_TRY(cudaFuncSetAttribute(k_umma_wgrad_tma<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     const int grid = sm_count(c.device);
     float* bpart = W.part.p + (size_t)grid * 256 * NP;
-    k_umma_wgrad<NP><<<grid, 256, sm, c.stream>>>(AT, BT, W.mp, W.part.p, bpart, W.err.p);
+    k_umma_wgrad_tma<NP><<<grid, 320, sm, c.stream>>>(ta, tb, W.mp, W.part.p, bpart, W.err.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     k_reduce_part<<<nb(256 * NP, 256), 256, 0, c.stream>>>(W.part.p, grid, 256 * NP, 256 * NP, out);
     k_reduce_part<<<1, 256, 0, c.stream>>>(bpart, grid, 256, 256, bias_out);
