@@ -164,42 +164,70 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// 16 accumulator columns into r[] without waiting; tmem_ld_wait32 then
+// waits for the outstanding loads and ties the 32 registers to that point
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait32(uint32_t* r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; i += 8)
+        asm volatile("" : "+r"(r[i]), "+r"(r[i + 1]), "+r"(r[i + 2]), "+r"(r[i + 3]), "+r"(r[i + 4]),
+                     "+r"(r[i + 5]), "+r"(r[i + 6]), "+r"(r[i + 7]));
+}
+
+// epilogue of one 128-row tile: this warp's 32 rows (TMEM lane quarter),
+// columns [128 half, 128 half + 128), 32 columns per TMEM wait; the bias
+// comes from shared memory
 template <int K, int EPI>
 __device__ __forceinline__ void act_epilogue_rows(uint32_t tacc, int quarter, int half, int64_t m0, int64_t mp,
-                                                  const float* __restrict__ bias,
+                                                  const float* __restrict__ sbias,
                                                   const __nv_bfloat16* __restrict__ mask,
                                                   __nv_bfloat16* __restrict__ C, __nv_bfloat16* __restrict__ CT) {
     const int lane = threadIdx.x & 31;
     const int r = quarter * 32 + lane;
     const int64_t gr = m0 + r;
-    for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
-        float v[16];
-        tmem_ld16(tacc + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+    for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 32) {
+        uint4 mk[4];
+        if (EPI == 1) {
+            const uint4* mp4 = reinterpret_cast<const uint4*>(mask + gr * 256 + c0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) mk[q] = __ldg(mp4 + q);
+        }
+        uint32_t u[32];
+        const uint32_t ta = tacc + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+        tmem_ld16_nowait(ta, u);
+        tmem_ld16_nowait(ta + 16u, u + 16);
+        tmem_ld_wait32(u);
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(u[i]);
         if (EPI == 0) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i] + bias[c0 + i], 0.0f);
+            for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i] + sbias[c0 + i], 0.0f);
         } else {
-            const uint4* mk = reinterpret_cast<const uint4*>(mask + gr * 256 + c0);
-            uint4 m0v = __ldg(mk), m1v = __ldg(mk + 1);
-            const __nv_bfloat16* mb0 = reinterpret_cast<const __nv_bfloat16*>(&m0v);
-            const __nv_bfloat16* mb1 = reinterpret_cast<const __nv_bfloat16*>(&m1v);
+            const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(mk);
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (!(__bfloat162float(mb0[i]) > 0.0f)) v[i] = 0.0f;
-                if (!(__bfloat162float(mb1[i]) > 0.0f)) v[8 + i] = 0.0f;
-            }
+            for (int i = 0; i < 32; ++i)
+                if (!(__bfloat162float(mb[i]) > 0.0f)) v[i] = 0.0f;
         }
-        __align__(16) __nv_bfloat16 o[16];
+        __align__(16) __nv_bfloat16 o[32];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(v[i]);
+        for (int i = 0; i < 32; ++i) o[i] = __float2bfloat16_rn(v[i]);
         if (C) {
             uint4* dst = reinterpret_cast<uint4*>(C + gr * 256 + c0);
-            dst[0] = reinterpret_cast<const uint4*>(o)[0];
-            dst[1] = reinterpret_cast<const uint4*>(o)[1];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = reinterpret_cast<const uint4*>(o)[q];
         }
         if (CT) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) CT[(int64_t)(c0 + i) * mp + gr] = o[i];
+            for (int i = 0; i < 32; ++i) CT[(int64_t)(c0 + i) * mp + gr] = o[i];
         }
     }
 }
@@ -212,7 +240,7 @@ struct ActTma {
     static constexpr int NST = K >= 256 ? 5 : 8;        // A ring stages
     static constexpr uint32_t A_BYTES = 128u * SWZ;     // one A chunk (128 rows)
     static constexpr uint32_t W_BYTES = 256u * SWZ;     // one W chunk (256 rows)
-    static constexpr size_t SMEM = (size_t)NCH * W_BYTES + (size_t)NST * A_BYTES + 1024;  // + alignment
+    static constexpr size_t SMEM = (size_t)NCH * W_BYTES + (size_t)NST * A_BYTES + 1024 + 1024;  // + alignment, bias
     static constexpr int THREADS = 320;
 };
 
@@ -228,10 +256,13 @@ k_umma_act_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
     uint8_t* smem = smem_raw + (((base_u + 1023u) & ~1023u) - base_u);
     uint8_t* sW = smem;                                  // NCH chunks of 256 rows
     uint8_t* sA = smem + T::NCH * T::W_BYTES;            // NST chunks of 128 rows
+    float* sbias = reinterpret_cast<float*>(sA + T::NST * T::A_BYTES);   // [256] (EPI 0)
     __shared__ __align__(8) uint64_t full[T::NST], empty[T::NST], wfull, accf[2], acce[2];
     __shared__ uint32_t tslot;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 1) tmem_alloc(&tslot, 512);
+    if (EPI == 0)
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) sbias[i] = bias[i];
     if (threadIdx.x == 0) {
         for (int i = 0; i < T::NST; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         mbar_init(&wfull, 1);
@@ -292,7 +323,7 @@ k_umma_act_tma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ 
             const bool got = mbar_wait(&accf[b], use & 1u);
             if (!__all_sync(0xffffffffu, got)) { atomicExch(err, 1); break; }   // the whole warp leaves
             tc_fence_after();
-            act_epilogue_rows<K, EPI>(tmem + b * 256u, quarter, half, tile * 128, mp, bias, mask, C, CT);
+            act_epilogue_rows<K, EPI>(tmem + b * 256u, quarter, half, tile * 128, mp, sbias, mask, C, CT);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce[b]);
