@@ -93,6 +93,7 @@ void tri_edges(const int32_t* tris, int64_t n, std::vector<int32_t>& edges,
 }
 
 __global__ void k_count_sum(const int32_t* __restrict__ cnt, int64_t ns, long long* out) {
+    pass_dep_wait();
     // out[0..2] = totals per kind, out[3..5] = maxima
     long long s0 = 0, s1 = 0, s2 = 0;
     int m0 = 0, m1 = 0, m2 = 0;
@@ -116,6 +117,7 @@ __global__ void k_count_sum(const int32_t* __restrict__ cnt, int64_t ns, long lo
 // x[svert[k]] = xs[k] for the slave vertices (ipc_scatter_slave)
 __global__ void k_scatter_slave(const int32_t* __restrict__ svert, int64_t n, const double* __restrict__ xs,
                                 double* __restrict__ x) {
+    pass_dep_wait();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t v = svert[k];
@@ -125,6 +127,7 @@ __global__ void k_scatter_slave(const int32_t* __restrict__ svert, int64_t n, co
 }
 
 __global__ void k_sub(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o, int64_t n) {
+    pass_dep_wait();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) o[i] = a[i] - b[i];
 }
@@ -200,13 +203,13 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
             GMCP_CUDA_TRY(cudaEventRecord(c.ev_xin, c.stream));
             GMCP_CUDA_TRY(cudaStreamWaitEvent(c.h2d_stream, c.ev_xin, 0));
             GMCP_CUDA_TRY(cudaMemcpyAsync(c.dxs_stage.p, A.dxs_host, nb, cudaMemcpyHostToDevice, c.h2d_stream));
-            k_scatter_slave<<<g, 256, 0, c.h2d_stream>>>(c.svert.p, c.n_svert, c.dxs_stage.p,
+            launch_dep(k_scatter_slave, g, 256, 0, c.h2d_stream, c.svert.p, c.n_svert, c.dxs_stage.p,
                                                          const_cast<double*>(A.dx));
             GMCP_CUDA_TRY(cudaGetLastError());
             GMCP_CUDA_TRY(cudaEventRecord(c.ev_dxin, c.h2d_stream));
             dx_wait = true;
         }
-        k_scatter_slave<<<g, 256, 0, c.stream>>>(c.svert.p, c.n_svert, c.xs_stage.p, const_cast<double*>(A.x));
+        launch_dep(k_scatter_slave, g, 256, 0, c.stream, c.svert.p, c.n_svert, c.xs_stage.p, const_cast<double*>(A.x));
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     const double* dxm = nullptr;
@@ -214,7 +217,7 @@ cudaError_t enqueue_contact_pass(Ctx& c, const ContactPassArgs& A) {
         GMCP_CUDA_TRY(c.dxm.ensure(3 * (size_t)c.nmv + 3));
         const int64_t n = 3 * c.nmv;
         if (n > 0) {
-            k_sub<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(A.xm1, A.xm0, c.dxm.p, n);
+            launch_dep(k_sub, (unsigned)((n + 255) / 256), 256, 0, c.stream, A.xm1, A.xm0, c.dxm.p, n);
             GMCP_CUDA_TRY(cudaGetLastError());
         }
         dxm = c.dxm.p;
@@ -1247,7 +1250,7 @@ ipc_status ipc_candidates(ipc_ctx* ctx, const double* x_dev, const double* xm_de
     if (counts) {
         API_CK(ctx, cudaMemsetAsync(c.i64_tmp.p, 0, 8 * sizeof(long long), c.stream));
         const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(1024, (c.ns + 255) / 256));
-        k_count_sum<<<(unsigned)blocks, 256, 0, c.stream>>>(c.cand_count.p, c.ns, c.i64_tmp.p);
+        launch_dep(k_count_sum, (unsigned)blocks, 256, 0, c.stream, c.cand_count.p, c.ns, c.i64_tmp.p);
         API_CK(ctx, cudaGetLastError());
         API_CK(ctx, cudaMemcpyAsync(c.h_counts, c.i64_tmp.p, 6 * sizeof(long long), cudaMemcpyDeviceToHost, c.stream));
         API_CK(ctx, cudaStreamSynchronize(c.stream));
@@ -1378,7 +1381,7 @@ ipc_status ipc_ccd_max_step(ipc_ctx* ctx, const double* x_dev, const double* dx_
         API_CK(ctx, c.dxm.ensure(3 * (size_t)c.nmv + 3));
         const int64_t n = 3 * c.nmv;
         if (n > 0) {
-            k_sub<<<(unsigned)((n + 255) / 256), 256, 0, c.stream>>>(xm1_dev, xm0_dev, c.dxm.p, n);
+            launch_dep(k_sub, (unsigned)((n + 255) / 256), 256, 0, c.stream, xm1_dev, xm0_dev, c.dxm.p, n);
             API_CK(ctx, cudaGetLastError());
         }
         dxm = c.dxm.p;
@@ -1607,7 +1610,7 @@ ipc_status ipc_scatter_slave(ipc_ctx* ctx, const double* xs_dev, double* x_dev) 
     Ctx& c = ctx->c;
     if (c.n_svert == 0) return IPC_OK;
     if (!xs_dev || !x_dev) return fail_ctx(ctx, IPC_ERR_ARG, "ipc_scatter_slave: NULL pointer");
-    k_scatter_slave<<<(unsigned)((c.n_svert + 255) / 256), 256, 0, c.stream>>>(c.svert.p, c.n_svert, xs_dev, x_dev);
+    launch_dep(k_scatter_slave, (unsigned)((c.n_svert + 255) / 256), 256, 0, c.stream, c.svert.p, c.n_svert, xs_dev, x_dev);
     API_CK(ctx, cudaGetLastError());
     return IPC_OK;
 }

@@ -184,6 +184,7 @@ __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
                                  const double* __restrict__ dxm, float* __restrict__ mboxf,
                                  int4* __restrict__ mcell, int32_t* __restrict__ cnt,
                                  float* __restrict__ mboxf_in) {
+    pass_dep_wait();
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int32_t* T = S.mtri + 3 * m;
@@ -235,6 +236,7 @@ __global__ void k_mtri_box_count(SceneView S, const double* __restrict__ xm,
 __global__ void k_mtri_fill(SceneView S, const float* __restrict__ mboxf, const int4* __restrict__ mcell,
                             int32_t* __restrict__ cur, int32_t* __restrict__ ent, int64_t cap,
                             int32_t* __restrict__ overflow) {
+    pass_dep_wait();
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int e = mcell[m].w;
@@ -394,6 +396,7 @@ struct QueryList {
 template <bool SWEPT>
 __global__ void k_vert_bounds(int64_t n, const int32_t* __restrict__ svert, const double* __restrict__ x,
                               const double* __restrict__ dx, float* __restrict__ out) {
+    pass_dep_wait();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int64_t v = svert[k];
@@ -428,6 +431,7 @@ template <bool SWEPT>
 __global__ void __launch_bounds__(256)
 k_query_filter(SceneView S, Params P, const double* __restrict__ x, const float* __restrict__ vb_in,
                const int32_t* __restrict__ start, QueryList Q, int32_t* __restrict__ count) {
+    pass_dep_wait();
     // every lane runs to the warp-wide append at the end (lanes past the last
     // triangle work on triangle 0 and append nothing)
     const int64_t t_raw = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -567,6 +571,7 @@ struct PairList {
 __global__ void __launch_bounds__(256)
 k_query_walk(SceneView S, QueryList Q, const float* __restrict__ mboxf, const int4* __restrict__ mcell,
              const int32_t* __restrict__ start, const int32_t* __restrict__ ent, PairList L) {
+    pass_dep_wait();
     // pairs are staged per warp in shared memory and written out kWalkStage
     // at a time, one atomic per batch (a counter bumped per chunk serialises)
     constexpr int kWalkStage = 128;
@@ -674,6 +679,7 @@ __global__ void __launch_bounds__(256)
 k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
                 const double* __restrict__ x, const double* __restrict__ xm,
                 const float* __restrict__ mboxf, const float* __restrict__ mboxf_in) {
+    pass_dep_wait();
     const int n = min(*W.n, W.cap);
     const double eps = P.dhat;
     // eps rounded up, with a relative slack that covers the FP64 rounding of
@@ -804,6 +810,7 @@ k_contact_exact(SceneView S, Params P, CandView C, QueryList Q, PairList W,
 // outputs.
 __global__ void __launch_bounds__(256)
 k_contact_finish(CandView C, QueryList Q) {
+    pass_dep_wait();
     const int lane = threadIdx.x & 31;
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int nwarps = (int)(((int64_t)gridDim.x * blockDim.x) >> 5);
@@ -1006,6 +1013,7 @@ __global__ void __launch_bounds__(256)
 k_ccd_exact(SceneView S, QueryList Q, PairList C, const double* __restrict__ x,
             const double* __restrict__ dx, const double* __restrict__ xm0,
             const double* __restrict__ dxm, const float* __restrict__ mboxf, PairList L) {
+    pass_dep_wait();
     const int n = min(*C.n, C.cap);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int2 pr = C.p[i];
@@ -1088,6 +1096,7 @@ k_accd_pairs(SceneView S, Params P, PairList L, const double* __restrict__ x,
              const double* __restrict__ dx, const double* __restrict__ xm0,
              const double* __restrict__ dxm, unsigned long long* alpha_bits, long long* counters,
              int alpha_stride) {
+    pass_dep_wait();
     const int n = min(*L.n, L.cap);
     double best = 1.0;
     long long n_pt = 0, n_ee = 0;
@@ -1190,7 +1199,7 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
     const int B = 256;
     const unsigned g = (unsigned)((c.nmt + B - 1) / B);
     if (c.nmt > 0) {
-        k_mtri_box_count<<<g, B, 0, s>>>(S, xm, swept ? dxm : nullptr, c.mboxf.p, c.mcell.p, c.cell_cnt.p,
+        launch_dep(k_mtri_box_count, g, B, 0, s, S, xm, swept ? dxm : nullptr, c.mboxf.p, c.mcell.p, c.cell_cnt.p,
                                          c.mboxf_in.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
@@ -1212,7 +1221,7 @@ cudaError_t bp_build_grid(Ctx& c, const double* xm, const double* dxm, bool swep
         GMCP_CUDA_TRY(c.cell_ent.ensure((size_t)total + 1));
     }
     if (c.nmt > 0) {
-        k_mtri_fill<<<g, B, 0, s>>>(S, c.mboxf.p, c.mcell.p, c.cell_start.p + 1, c.cell_ent.p,
+        launch_dep(k_mtri_fill, g, B, 0, s, S, c.mboxf.p, c.mcell.p, c.cell_start.p + 1, c.cell_ent.p,
                                     (int64_t)c.cell_ent.n, c.misc_i32.p + 12);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
@@ -1258,10 +1267,10 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
     QueryList Q = query_list(c, false);
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p, 0, sizeof(int32_t) * 12, s));
     if (c.ns == 0) return cudaSuccess;
-    k_vert_bounds<false><<<(unsigned)((c.n_svert + 255) / 256), 256, 0, s>>>(c.n_svert, c.svert.p, x, nullptr,
+    launch_dep(k_vert_bounds<false>, (unsigned)((c.n_svert + 255) / 256), 256, 0, s, c.n_svert, c.svert.p, x, nullptr,
                                                                            c.vbound_c.p);
     GMCP_CUDA_TRY(cudaGetLastError());
-    k_query_filter<false><<<(unsigned)((c.ns + 255) / 256), 256, 0, s>>>(
+    launch_dep(k_query_filter<false>, (unsigned)((c.ns + 255) / 256), 256, 0, s, 
         S, P, x, c.vbound_c.p, c.cell_start.p, Q, c.cand_count.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.cap_coarse == 0) c.cap_coarse = (int32_t)std::min<int64_t>((1 << 16) + 2 * c.ns, 1 << 30);
@@ -1273,13 +1282,13 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
         GMCP_CUDA_TRY(cudaMemsetAsync(W.n, 0, sizeof(int32_t), s));
         GMCP_CUDA_TRY(cudaMemsetAsync(W.overflow, 0, sizeof(int32_t), s));
         GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), s));
-        k_query_walk<<<persistent_blocks(c), 256, 0, s>>>(S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
+        launch_dep(k_query_walk, persistent_blocks(c), 256, 0, s, S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
                                                           c.cell_ent.p, W);
         GMCP_CUDA_TRY(cudaGetLastError());
         if (P.nk == 4)
-            k_contact_exact<4><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mboxf.p, c.mboxf_in.p);
+            launch_dep(k_contact_exact<4>, flat, 256, 0, s, S, P, C, Q, W, x, xm, c.mboxf.p, c.mboxf_in.p);
         else
-            k_contact_exact<16><<<flat, 256, 0, s>>>(S, P, C, Q, W, x, xm, c.mboxf.p, c.mboxf_in.p);
+            launch_dep(k_contact_exact<16>, flat, 256, 0, s, S, P, C, Q, W, x, xm, c.mboxf.p, c.mboxf_in.p);
         GMCP_CUDA_TRY(cudaGetLastError());
         if (lazy) break;   // the caller reads the overflow slot after it synchronises
         int32_t need = 0;
@@ -1291,7 +1300,7 @@ cudaError_t bp_query_contact(Ctx& c, const double* x, const double* xm, bool laz
         // the lists restart empty
         GMCP_CUDA_TRY(cudaMemsetAsync(c.cand_count.p, 0, sizeof(int32_t) * 4 * c.ns, s));
     }
-    k_contact_finish<<<persistent_blocks(c), 256, 0, s>>>(C, Q);
+    launch_dep(k_contact_finish, persistent_blocks(c), 256, 0, s, C, Q);
     return cudaGetLastError();
 }
 
@@ -1305,10 +1314,10 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
     GMCP_CUDA_TRY(ensure_query_list(c, true));
     QueryList Q = query_list(c, true);
     GMCP_CUDA_TRY(cudaMemsetAsync(Q.n, 0, sizeof(int32_t), c.stream));
-    k_vert_bounds<true><<<(unsigned)((c.n_svert + 255) / 256), 256, 0, c.stream>>>(c.n_svert, c.svert.p, x, dx,
+    launch_dep(k_vert_bounds<true>, (unsigned)((c.n_svert + 255) / 256), 256, 0, c.stream, c.n_svert, c.svert.p, x, dx,
                                                                                  c.vbound_s.p);
     GMCP_CUDA_TRY(cudaGetLastError());
-    k_query_filter<true><<<(unsigned)((c.ns + 255) / 256), 256, 0, c.stream>>>(
+    launch_dep(k_query_filter<true>, (unsigned)((c.ns + 255) / 256), 256, 0, c.stream, 
         S, c.P, x, c.vbound_s.p, c.cell_start.p, Q, nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.cap_ccd == 0) c.cap_ccd = (int32_t)std::min<int64_t>((1 << 16) + c.ns / 4, 1 << 30);
@@ -1324,12 +1333,12 @@ cudaError_t bp_ccd_accd(Ctx& c, const double* x, const double* dx, const double*
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 10, 0, 2 * sizeof(int32_t), c.stream));
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 13, 0, 2 * sizeof(int32_t), c.stream));
         GMCP_CUDA_TRY(cudaMemsetAsync(Q.work, 0, sizeof(int32_t), c.stream));
-        k_query_walk<<<persistent_blocks(c), 256, 0, c.stream>>>(S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
+        launch_dep(k_query_walk, persistent_blocks(c), 256, 0, c.stream, S, Q, c.mboxf.p, c.mcell.p, c.cell_start.p,
                                                                c.cell_ent.p, C);
         GMCP_CUDA_TRY(cudaGetLastError());
-        k_ccd_exact<<<flat, 256, 0, c.stream>>>(S, Q, C, x, dx, xm0, dxm, c.mboxf.p, L);
+        launch_dep(k_ccd_exact, flat, 256, 0, c.stream, S, Q, C, x, dx, xm0, dxm, c.mboxf.p, L);
         GMCP_CUDA_TRY(cudaGetLastError());
-        k_accd_pairs<<<flat, 256, 0, c.stream>>>(S, c.P, L, x, dx, xm0, dxm, alpha_bits, counters, alpha_stride);
+        launch_dep(k_accd_pairs, flat, 256, 0, c.stream, S, c.P, L, x, dx, xm0, dxm, alpha_bits, counters, alpha_stride);
         GMCP_CUDA_TRY(cudaGetLastError());
         // a lazy caller reads the overflow slots after it synchronises and redoes the pass
         if (lazy) return cudaSuccess;
@@ -1379,12 +1388,14 @@ namespace gmcp {
 namespace {
 
 __global__ void k_noalloc_reset(unsigned long long* hdr) {
+    pass_dep_wait();
     hdr[0] = 0x3FF0000000000000ULL;   // alpha = 1.0
     hdr[1] = 0; hdr[2] = 0; hdr[3] = 0;
 }
 
 __global__ void k_noalloc_sub(const double* __restrict__ a, const double* __restrict__ b,
                               double* __restrict__ o, int64_t n) {
+    pass_dep_wait();
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) o[i] = a[i] - b[i];
 }
@@ -1394,6 +1405,7 @@ __global__ void __launch_bounds__(128)
 k_accd_brute(SceneView S, Params P, const double* __restrict__ x, const double* __restrict__ dx,
              const double* __restrict__ xm0, const double* __restrict__ dxm, int m_chunk,
              unsigned long long* alpha_bits, long long* counters) {
+    pass_dep_wait();
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= S.ns) return;
     const int64_t m_begin = (int64_t)blockIdx.y * m_chunk;

@@ -354,6 +354,7 @@ __device__ __forceinline__ void lag_add(double* E8, const double* al, int na, do
 // passes alternate by the parity of the Hessian-pass number (kSlotHPass).
 // ---------------------------------------------------------------------------
 __global__ void k_pass_begin(int32_t* misc, int hess) {
+    pass_dep_wait();
     const int32_t p = ++misc[kSlotPass];
     (void)p;
     misc[kSlotVCount] = 0;
@@ -384,6 +385,7 @@ struct TouchArgs {
 // each (stamps), one thread per (triangle, corner a): vertex T[a] and the
 // blocks (T[a], T[b]) of its row.  Runs beside the sample evaluation.
 __global__ void k_touch(SceneView S, CandView C, TouchArgs A) {
+    pass_dep_wait();
     const int n = 3 * *C.n_active;
     const int32_t ps = A.misc[kSlotPass], hs = A.misc[kSlotHPass];
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += gridDim.x * blockDim.x) {
@@ -425,9 +427,10 @@ __global__ void k_touch(SceneView S, CandView C, TouchArgs A) {
 __global__ void k_tri_frame(SceneView S, CandView C, const double* __restrict__ x,
                             double* __restrict__ frame, int nk, int32_t* __restrict__ items,
                             int32_t* __restrict__ n_items, int32_t* __restrict__ tri_stamp,
-                            const int32_t* __restrict__ misc, float* __restrict__ tf32 = nullptr,
-                            int L = 1, const double* __restrict__ dx = nullptr,
-                            double* __restrict__ tmid64 = nullptr, float* __restrict__ tmid32 = nullptr) {
+                            const int32_t* __restrict__ misc, float* __restrict__ tf32, int L,
+                            const double* __restrict__ dx, double* __restrict__ tmid64,
+                            float* __restrict__ tmid32) {
+    pass_dep_wait();
     const int n_active = *C.n_active;
     const int32_t ps = tri_stamp ? misc[kSlotPass] : 0;
     const int lane = threadIdx.x & 31;
@@ -1268,6 +1271,7 @@ k_samples(SceneView S, Params P, CandView C, const double* __restrict__ x,
           const double* __restrict__ dx, const double* __restrict__ dxm,
           unsigned long long* alpha_bits, ModeArgs LG, const double* __restrict__ frame,
           const int32_t* __restrict__ run_if_over, int64_t item_cap) {
+    pass_dep_wait();
     if (run_if_over && (int64_t)*run_if_over <= item_cap) return;
     const int lane = threadIdx.x & 31;
     const int n_active = *C.n_active;
@@ -1415,6 +1419,7 @@ struct ItemBufs {
 // master vertices minus their environment's grid origin, rounded to FP32
 // (w = 0): the master side of the face items' FP32 pre-filter
 __global__ void k_master_f32(SceneView S, const double* __restrict__ xm, float4* __restrict__ ym32) {
+    pass_dep_wait();
     const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (u >= S.nmv) return;
     const int e = S.mvert_env[u];
@@ -1429,6 +1434,7 @@ __global__ void k_master_f32(SceneView S, const double* __restrict__ xm, float4*
 // three vertices, e1.e1, e1.e2, e2.e2, their Gram determinant, 3 unused.
 constexpr int kMtriPre = 24;
 __global__ void k_mtri_pre(SceneView S, const float4* __restrict__ ym32, float* __restrict__ out) {
+    pass_dep_wait();
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int32_t* M = S.mtri + 3 * m;
@@ -1524,6 +1530,7 @@ __device__ __forceinline__ bool face_reject_f32_rec(V3<float> xs, V3<float> ns, 
 }
 
 __global__ void k_fill_owner(CandView C, const int32_t* __restrict__ items, ItemBufs B) {
+    pass_dep_wait();
     if ((int64_t)*B.n > B.cap) return;
     const int lane = threadIdx.x & 31;
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -1598,6 +1605,7 @@ k_items_pre(SceneView S, Params P, CandView C, const int32_t* __restrict__ items
             int32_t* __restrict__ mid, int32_t* __restrict__ n_mid, int32_t* __restrict__ n_mid2,
             long long* counters, const float* __restrict__ tf32, const float4* __restrict__ ym32,
             const float* __restrict__ mtri_pre) {
+    pass_dep_wait();
     const int64_t n = *B.n;
     if (n > B.cap) return;
     long long cnt_eval = 0;
@@ -1669,6 +1677,7 @@ k_items_pre(SceneView S, Params P, CandView C, const int32_t* __restrict__ items
 // master triangles' edges y1 - y0, y2 - y0 rounded to FP32, once per pass
 // (the certified tests read them per item)
 __global__ void k_mtri_e32(SceneView S, const double* __restrict__ xm, float* __restrict__ out) {
+    pass_dep_wait();
     const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (m >= S.nmt) return;
     const int32_t* M = S.mtri + 3 * m;
@@ -1688,6 +1697,7 @@ k_items_mid(SceneView S, Params P, CandView C, const double* __restrict__ x, con
             const int32_t* __restrict__ n_mid2, int32_t* __restrict__ list, int32_t* __restrict__ n_list,
             int32_t* __restrict__ n_list2, long long* counters, bool cert, const double* __restrict__ tmid64,
             const float* __restrict__ tmid32, const float* __restrict__ mtri_e) {
+    pass_dep_wait();
     if ((int64_t)*B.n > B.cap) return;
     // faces (the front of the list) first, then edges and points (the back):
     // only the warp at the boundary holds both kinds
@@ -1777,6 +1787,7 @@ k_items(SceneView S, Params P, CandView C, const double* __restrict__ x, const d
         const int32_t* __restrict__ items, ItemBufs B, const int32_t* __restrict__ list,
         const int32_t* __restrict__ n_list, const int32_t* __restrict__ n_list2, long long* counters,
         ModeArgs LG = ModeArgs()) {
+    pass_dep_wait();
     if ((int64_t)*B.n > B.cap) return;
     const int nf = *n_list;
     const int n = nf + *n_list2;
@@ -1826,6 +1837,7 @@ __global__ void __launch_bounds__(256)
 k_tri_reduce(CandView C, const double* __restrict__ frame, const int32_t* __restrict__ items, ItemBufs B,
              double* __restrict__ triE, T* __restrict__ triG, T* __restrict__ triS, T* __restrict__ triN,
              unsigned long long* alpha_bits) {
+    pass_dep_wait();
     if ((int64_t)*B.n > B.cap) return;
     const int lane = threadIdx.x & 31;
     const int warp = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -1877,6 +1889,7 @@ __global__ void k_gather_grad(const int32_t* __restrict__ off, const int32_t* __
                               const T* __restrict__ triG, const T* __restrict__ triN,
                               const int32_t* __restrict__ tri_stamp, const int32_t* __restrict__ misc,
                               const int32_t* __restrict__ v_list, TO* __restrict__ out) {
+    pass_dep_wait();
     const int n = misc[kSlotVCount];
     const int32_t ps = misc[kSlotPass];
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1906,6 +1919,7 @@ __global__ void k_gather_hess(const int32_t* __restrict__ off, const int32_t* __
                               const int32_t* __restrict__ tri_stamp, const int32_t* __restrict__ misc,
                               int32_t* const* __restrict__ b_list, const int32_t* __restrict__ b_stamp,
                               T* __restrict__ out) {
+    pass_dep_wait();
     const int32_t ps = misc[kSlotPass], hs = misc[kSlotHPass];
     const int n_cur = misc[kSlotBCount + (hs & 1)], n_prev = misc[kSlotBCount + ((hs + 1) & 1)];
     const int32_t* cur = b_list[hs & 1];
@@ -1945,6 +1959,7 @@ constexpr int kRedPer = 8;
 // (with stamp: only the entries whose stamp equals *pass count)
 __global__ void k_reduce_partial(const double* __restrict__ in, int64_t n, double* __restrict__ part,
                                  const int32_t* __restrict__ stamp, const int32_t* __restrict__ pass) {
+    pass_dep_wait();
     __shared__ double sh[kRedThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kRedThreads * kRedPer;
     const int32_t ps = pass ? *pass : 0;
@@ -1963,6 +1978,7 @@ __global__ void k_reduce_partial(const double* __restrict__ in, int64_t n, doubl
     }
 }
 __global__ void k_reduce_final(const double* __restrict__ part, int64_t n, double* __restrict__ out) {
+    pass_dep_wait();
     __shared__ double sh[32];
     double s = 0.0;
     for (int64_t k = threadIdx.x; k < n; k += 1024) s += part[k];
@@ -1986,17 +2002,17 @@ cudaError_t master_tables(Ctx& c, const double* xm, cudaStream_t s) {
     if (c.use_mtri_e32) GMCP_CUDA_TRY(c.mtri_e32.ensure(8 * (size_t)c.nmt + 8));
     if (c.use_mtri_pre) GMCP_CUDA_TRY(c.mtri_pre.ensure((size_t)kMtriPre * c.nmt + kMtriPre));
     if (c.nmv == 0) return cudaSuccess;
-    k_master_f32<<<(unsigned)((c.nmv + 255) / 256), 256, 0, s>>>(c.view(), xm, (float4*)c.ym32.p);
+    launch_dep(k_master_f32, (unsigned)((c.nmv + 255) / 256), 256, 0, s, c.view(), xm, (float4*)c.ym32.p);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (c.nmt == 0) return cudaSuccess;
     if (c.use_mtri_e32) {
-        k_mtri_e32<<<(unsigned)((c.nmt + 255) / 256), 256, 0, s>>>(c.view(), xm, c.mtri_e32.p);
+        launch_dep(k_mtri_e32, (unsigned)((c.nmt + 255) / 256), 256, 0, s, c.view(), xm, c.mtri_e32.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     // the face pre-filter's per-triangle table pays only when most master
     // triangles take many face items (see Ctx::use_mtri_pre)
     if (!c.use_mtri_pre) return cudaSuccess;
-    k_mtri_pre<<<(unsigned)((c.nmt + 255) / 256), 256, 0, s>>>(c.view(), (const float4*)c.ym32.p, c.mtri_pre.p);
+    launch_dep(k_mtri_pre, (unsigned)((c.nmt + 255) / 256), 256, 0, s, c.view(), (const float4*)c.ym32.p, c.mtri_pre.p);
     return cudaGetLastError();
 }
 
@@ -2011,14 +2027,14 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     const int blocks = sms * c.tune_samples_bpsm;
     // the warp-per-triangle kernel, instantiated for the face rule in use
     auto launch_k_samples = [&](auto... a) {
-        if (c.P.face_clip) k_samples<NK, T, MODE, true><<<blocks, threads, 0, c.stream>>>(a...);
-        else k_samples<NK, T, MODE, false><<<blocks, threads, 0, c.stream>>>(a...);
+        if (c.P.face_clip) launch_dep(k_samples<NK, T, MODE, true>, blocks, threads, 0, c.stream, a...);
+        else launch_dep(k_samples<NK, T, MODE, false>, blocks, threads, 0, c.stream, a...);
     };
     GMCP_CUDA_TRY(c.tri_frame.ensure(8 * (size_t)c.ns + 8));
     constexpr bool kMaster = MODE == MODE_MASTER_HESS;
     if (MODE != MODE_EVAL && !kMaster) {
-        k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
-                                                   nullptr, nullptr);
+        launch_dep(k_tri_frame, sms * 4, 256, 0, c.stream, c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
+                   nullptr, nullptr, nullptr, 1, nullptr, nullptr, nullptr);
         GMCP_CUDA_TRY(cudaGetLastError());
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
         launch_k_samples(
@@ -2029,8 +2045,8 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     if (MODE == MODE_EVAL && c.P.face_clip) {
         // clipped-overlap face samples: a variable number per pair, evaluated
         // by the warp-per-triangle kernel (the items' fixed slots do not apply)
-        k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
-                                                   c.tri_stamp.p, c.misc_i32.p);
+        launch_dep(k_tri_frame, sms * 4, 256, 0, c.stream, c.view(), c.cand(), x, c.tri_frame.p, NK, nullptr, nullptr,
+                   c.tri_stamp.p, c.misc_i32.p, nullptr, 1, nullptr, nullptr, nullptr);
         GMCP_CUDA_TRY(cudaGetLastError());
         GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
         launch_k_samples(
@@ -2080,25 +2096,25 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
     // middle stage then reads dx's products with the normals from the frame
     // kernel's table)
     const bool cert = !kMaster && c.P.precision == IPC_PREC_MIXED && dxm == nullptr;
-    k_tri_frame<<<sms * 4, 256, 0, c.stream>>>(c.view(), c.cand(), x, c.tri_frame.p, NK, c.tri_items.p, n_items,
+    launch_dep(k_tri_frame, sms * 4, 256, 0, c.stream, c.view(), c.cand(), x, c.tri_frame.p, NK, c.tri_items.p, n_items,
                                                kMaster ? nullptr : c.tri_stamp.p, c.misc_i32.p,
                                                f32pre ? c.tri_f32.p : nullptr, c.P.L, cert ? dx : nullptr,
                                                f32pre ? c.tri_mid64.p : nullptr, f32pre ? c.tri_mid32.p : nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     ItemBufs B{c.item_owner.p, c.item_rd.p, (void*)c.item_rt.p, n_items, c.cap_items, c.item_mask.p};
-    k_fill_owner<<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_items.p, B);
+    launch_dep(k_fill_owner, sms * 8, 256, 0, c.stream, c.cand(), c.tri_items.p, B);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (f32pre && (c.side_master || c.master_pre)) GMCP_CUDA_TRY(cudaStreamWaitEvent(c.stream, c.ev_master, 0));
     int32_t* n_list = c.misc_i32.p + kSlotItemList;
     int32_t* n_list2 = c.misc_i32.p + kSlotItemList2;
     int32_t* n_mid = c.misc_i32.p + kSlotItemMid;
     int32_t* n_mid2 = c.misc_i32.p + kSlotItemMid2;
-    k_items_pre<NK><<<sms * 16, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), c.tri_items.p, B, c.item_mid.p, n_mid,
+    launch_dep(k_items_pre<NK>, sms * 16, 256, 0, c.stream, c.view(), c.P, c.cand(), c.tri_items.p, B, c.item_mid.p, n_mid,
                                                     n_mid2, counters, f32pre ? c.tri_f32.p : nullptr,
                                                     f32pre ? (const float4*)c.ym32.p : nullptr,
                                                     f32pre && c.use_mtri_pre ? c.mtri_pre.p : nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
-    k_items_mid<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
+    launch_dep(k_items_mid<NK, T>, sms * 8, 256, 0, c.stream, c.view(), c.P, c.cand(), x, xm, dx, c.tri_frame.p,
                                                       c.tri_items.p, B, c.item_mid.p, n_mid, n_mid2, c.item_list.p,
                                                       n_list, n_list2, counters, cert,
                                                       f32pre ? c.tri_mid64.p : nullptr,
@@ -2106,7 +2122,7 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
                                                       f32pre && c.use_mtri_e32 ? c.mtri_e32.p : nullptr);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (kMaster) {
-        k_items<NK, T, MODE><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
+        launch_dep(k_items<NK, T, MODE>, sms * 64, 64, 0, c.stream, c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
                                                              c.tri_items.p, B, c.item_list.p, n_list, n_list2,
                                                              counters, LG);
         GMCP_CUDA_TRY(cudaGetLastError());
@@ -2121,11 +2137,11 @@ cudaError_t launch_samples(Ctx& c, const double* x, const double* xm, T* G, T* S
         ProfScope pi(c.prof, c.stream, "items");
         // 64-thread blocks, at most 168 registers a thread: 12 warps fit an
         // SM (8 with 256-thread blocks)
-        k_items<NK, T><<<sms * 64, 64, 0, c.stream>>>(c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
-                                                       c.tri_items.p, B, c.item_list.p, n_list, n_list2, counters);
+        launch_dep(k_items<NK, T>, sms * 64, 64, 0, c.stream, c.view(), c.P, c.cand(), x, xm, dx, dxm, c.tri_frame.p,
+                   c.tri_items.p, B, c.item_list.p, n_list, n_list2, counters, ModeArgs());
         GMCP_CUDA_TRY(cudaGetLastError());
     }
-    k_tri_reduce<NK, T><<<sms * 8, 256, 0, c.stream>>>(c.cand(), c.tri_frame.p, c.tri_items.p, B, c.tri_E.p,
+    launch_dep(k_tri_reduce<NK, T>, sms * 8, 256, 0, c.stream, c.cand(), c.tri_frame.p, c.tri_items.p, B, c.tri_E.p,
                                                         G, Sm, N, alpha_bits);
     GMCP_CUDA_TRY(cudaGetLastError());
     GMCP_CUDA_TRY(cudaMemsetAsync(c.misc_i32.p + 4, 0, sizeof(int32_t), c.stream));
@@ -2159,10 +2175,10 @@ cudaError_t reduce_sum(Ctx& c, const double* in, int64_t n, double* out, const i
     const int64_t nb = (n + per - 1) / per;
     GMCP_CUDA_TRY(c.red_tmp.ensure((size_t)nb + 2));
     if (nb > 0) {
-        k_reduce_partial<<<(unsigned)nb, kRedThreads, 0, c.stream>>>(in, n, c.red_tmp.p, stamp, pass);
+        launch_dep(k_reduce_partial, (unsigned)nb, kRedThreads, 0, c.stream, in, n, c.red_tmp.p, stamp, pass);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
-    k_reduce_final<<<1, 1024, 0, c.stream>>>(c.red_tmp.p, nb, out);
+    launch_dep(k_reduce_final, 1, 1024, 0, c.stream, c.red_tmp.p, nb, out);
     return cudaGetLastError();
 }
 
@@ -2174,7 +2190,7 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
     const int sms = sm_count(c.device);
     const unsigned flat = (unsigned)(sms * 8);
     int32_t* misc = c.misc_i32.p;
-    k_pass_begin<<<1, 1, 0, c.stream>>>(misc, hess ? 1 : 0);
+    launch_dep(k_pass_begin, 1, 1, 0, c.stream, misc, hess ? 1 : 0);
     GMCP_CUDA_TRY(cudaGetLastError());
     // The touched vertices and blocks depend on the active list alone: they
     // are listed on a third stream beside the sample evaluation (the
@@ -2194,7 +2210,7 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
             GMCP_CUDA_TRY(cudaStreamWaitEvent(c.aux_stream, c.ev_touch0, 0));
             ts = c.aux_stream;
         }
-        k_touch<<<flat, 256, 0, ts>>>(c.view(), c.cand(), TA);
+        launch_dep(k_touch, flat, 256, 0, ts, c.view(), c.cand(), TA);
         GMCP_CUDA_TRY(cudaGetLastError());
         if (fork) GMCP_CUDA_TRY(cudaEventRecord(c.ev_touch1, c.aux_stream));
     }
@@ -2231,10 +2247,10 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
         GMCP_CUDA_TRY(cudaMemsetAsync(grad_dev, 0, (f32 ? sizeof(float) : sizeof(double)) * 3 * (size_t)c.nv,
                                       c.stream));
         if (f32)
-            k_gather_grad<float, float><<<flat, 256, 0, c.stream>>>(c.vt_off.p, c.vt_ent.p, c.tri_G32.p, c.tri_n32.p,
+            launch_dep(k_gather_grad<float, float>, flat, 256, 0, c.stream, c.vt_off.p, c.vt_ent.p, c.tri_G32.p, c.tri_n32.p,
                                                                  c.tri_stamp.p, misc, c.v_list.p, (float*)grad_dev);
         else
-            k_gather_grad<double, double><<<flat, 256, 0, c.stream>>>(c.vt_off.p, c.vt_ent.p, c.tri_G64.p,
+            launch_dep(k_gather_grad<double, double>, flat, 256, 0, c.stream, c.vt_off.p, c.vt_ent.p, c.tri_G64.p,
                                                                    c.tri_n64.p, c.tri_stamp.p, misc, c.v_list.p,
                                                                    (double*)grad_dev);
         GMCP_CUDA_TRY(cudaGetLastError());
@@ -2243,10 +2259,10 @@ cudaError_t contact_eval(Ctx& c, const double* x, const double* xm, double* ener
         ProfScope ps(c.prof, hs_stream, "gather_hess");
         int32_t* const* lists = c.b_lists.p;
         if (f32)
-            k_gather_hess<float><<<flat, 256, 0, hs_stream>>>(c.cb_src_off.p, c.cb_src.p, c.tri_S32.p, c.tri_n32.p,
+            launch_dep(k_gather_hess<float>, flat, 256, 0, hs_stream, c.cb_src_off.p, c.cb_src.p, c.tri_S32.p, c.tri_n32.p,
                                                               c.tri_stamp.p, misc, lists, c.b_stamp.p, c.cb_val32.p);
         else
-            k_gather_hess<double><<<flat, 256, 0, hs_stream>>>(c.cb_src_off.p, c.cb_src.p, c.tri_S64.p, c.tri_n64.p,
+            launch_dep(k_gather_hess<double>, flat, 256, 0, hs_stream, c.cb_src_off.p, c.cb_src.p, c.tri_S64.p, c.tri_n64.p,
                                                                c.tri_stamp.p, misc, lists, c.b_stamp.p, c.cb_val64.p);
         GMCP_CUDA_TRY(cudaGetLastError());
     }

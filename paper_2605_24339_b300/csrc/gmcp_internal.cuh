@@ -663,6 +663,31 @@ cudaError_t ws_state_get(Ctx& c, WsState* out);
 cudaError_t ws_state_set(Ctx& c, const WsState& in);
 int64_t ws_param_count();
 
+// Programmatic dependent launch for the kernels of the contact pass: each is
+// launched with programmatic stream serialisation, so that its blocks are
+// scheduled while its predecessor in the stream drains, and each begins with
+// griddepcontrol.wait, which holds it until the predecessor has finished and
+// its memory is visible.  Every such kernel waits before anything else, so a
+// kernel's completion still implies that of every kernel before it in the
+// stream.  Launched without the attribute, the wait is a no-op.
+__device__ __forceinline__ void pass_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dep(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 }  // namespace gmcp
 
 // integer atomic add on a signed 64-bit counter (two's complement wraps the same)

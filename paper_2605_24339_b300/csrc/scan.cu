@@ -25,6 +25,7 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
 
 __global__ void k_scan_blocks(const int32_t* __restrict__ in, int32_t* __restrict__ out,
                               int32_t* __restrict__ block_sums, int64_t n) {
+    pass_dep_wait();
     __shared__ int warp_tot[kThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kPerBlock + (int64_t)threadIdx.x * kPerThread;
     int v[kPerThread];
@@ -54,6 +55,7 @@ __global__ void k_scan_blocks(const int32_t* __restrict__ in, int32_t* __restric
 }
 
 __global__ void k_add_offsets(int32_t* __restrict__ out, const int32_t* __restrict__ offs, int64_t n) {
+    pass_dep_wait();
     const int64_t base = (int64_t)blockIdx.x * kPerBlock + (int64_t)threadIdx.x * kPerThread;
     const int add = offs[blockIdx.x];
 #pragma unroll
@@ -62,6 +64,7 @@ __global__ void k_add_offsets(int32_t* __restrict__ out, const int32_t* __restri
 }
 
 __global__ void k_write_total(const int32_t* in, int32_t* out, int64_t n) {
+    pass_dep_wait();
     out[n] = n > 0 ? out[n - 1] + in[n - 1] : 0;
 }
 
@@ -71,11 +74,11 @@ cudaError_t scan_rec(const int32_t* in, int32_t* out, int64_t n, int32_t* tmp, c
     const int64_t nb = (n + kPerBlock - 1) / kPerBlock;
     int32_t* sums = tmp;                  // [nb]
     int32_t* sums_scan = tmp + nb + 1;    // [nb]
-    k_scan_blocks<<<(unsigned)nb, kThreads, 0, s>>>(in, out, sums, n);
+    launch_dep(k_scan_blocks, (unsigned)nb, kThreads, 0, s, in, out, sums, n);
     GMCP_CUDA_TRY(cudaGetLastError());
     if (nb > 1) {
         GMCP_CUDA_TRY(scan_rec(sums, sums_scan, nb, sums_scan + nb + 1, s));
-        k_add_offsets<<<(unsigned)nb, kThreads, 0, s>>>(out, sums_scan, n);
+        launch_dep(k_add_offsets, (unsigned)nb, kThreads, 0, s, out, sums_scan, n);
         GMCP_CUDA_TRY(cudaGetLastError());
     }
     return cudaSuccess;
@@ -99,7 +102,7 @@ cudaError_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32
                                size_t tmp_n, cudaStream_t s) {
     if (tmp_n < 2 * scan_tmp_size(n)) return cudaErrorInvalidValue;
     GMCP_CUDA_TRY(scan_rec(in, out, n, tmp, s));
-    k_write_total<<<1, 1, 0, s>>>(in, out, n);
+    launch_dep(k_write_total, 1, 1, 0, s, in, out, n);
     return cudaGetLastError();
 }
 
