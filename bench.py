@@ -781,7 +781,8 @@ def newton_measurement(dev, start_step=20, n_states=4):
             pcg.append(st["pcg_iters"])
             ok = ok and st["status"] == 0 and st["residual"] <= sc.params["newton_tol"]
         out[prec] = {"ms_per_step_median": statistics.median(times), "ms_per_step": [round(t, 1) for t in times],
-                     "newton_iters": iters, "pcg_iters": pcg, "all_converged": ok}
+                     "newton_iters": iters, "pcg_iters": pcg, "all_converged": ok,
+                     "newton_iters_per_s": sum(iters) / (sum(times) / 1e3)}
         ctx.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step_median"] / out["mixed"]["ms_per_step_median"]
     return out
@@ -863,6 +864,7 @@ def batched_step_measurement(dev, n_env=16, steps=3, alone_envs=16, layers=2):
     ms = statistics.median(times)
     out["batched"] = {"ms_per_step_median": ms, "ms_per_step": [round(t, 1) for t in times],
                       "env_steps_per_s": n_env / (ms / 1e3),
+                      "env_newton_iters_per_s": float(sum(sum(i) for i in iters)) / (sum(times) / 1e3),
                       "newton_iters_max": [max(i) for i in iters], "newton_iters_mean": [float(np.mean(i)) for i in iters],
                       "statuses": statuses}
     # the same states stepped one environment at a time
