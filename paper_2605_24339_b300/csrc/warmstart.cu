@@ -598,6 +598,9 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
     for (int64_t tile = t0; tile < t1; ++tile) {
         const int64_t m0 = tile * kHeadRows;
         float hv[RW][8], acc[RW][3], mkc[RW], tgc[RW];
+        // the tile's loss terms in FP32 (12 at most), added to the FP64 sum once a
+        // tile: FP64 instructions run at a small fraction of the FP32 rate here
+        float tile_loss = 0.0f;
 #pragma unroll
         for (int rr = 0; rr < RW; ++rr) {
             const __nv_bfloat16* hb = reinterpret_cast<const __nv_bfloat16*>(&raw[rr]);
@@ -628,7 +631,7 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
             const int r = warp * RW + rr;
             const int64_t m = m0 + r;
             // every lane holds y; lane c < 3 forms component c of the loss
-            // term and of dy in FP32, lane 0 accumulates the loss in FP64
+            // term and of dy in FP32, lane 0 sums the loss terms
             float dc = 0.0f;
             const bool live = m < n && mkc[rr] != 0.0f && inv_den > 0.0f;
             float lt = 0.0f;
@@ -643,7 +646,7 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
             const float d0 = __shfl_sync(0xffffffffu, dc, 0), d1 = __shfl_sync(0xffffffffu, dc, 1),
                         d2 = __shfl_sync(0xffffffffu, dc, 2);
             const float l1 = __shfl_sync(0xffffffffu, lt, 1), l2 = __shfl_sync(0xffffffffu, lt, 2);
-            if (lane == 0) lterm += (double)lt + (double)l1 + (double)l2;
+            tile_loss += (lt + l1) + l2;               // lane 0's copy is the one kept
             if (lane < 3) dy[3 * m + lane] = dc;
             gb[0] += d0; gb[1] += d1; gb[2] += d2;
             __align__(16) __nv_bfloat16 o[8];
@@ -660,6 +663,7 @@ k_head_bwd(const __nv_bfloat16* __restrict__ h3, const float* __restrict__ P, co
             tp[0] = make_uint2(ov.x, ov.y);
             tp[1] = make_uint2(ov.z, ov.w);
         }
+        if (lane == 0) lterm += (double)tile_loss;
         __syncthreads();
         // dz3^T[j][m0 .. m0 + 31]: four threads a column, eight rows (16 bytes) each
         for (int idx = threadIdx.x; idx < 4 * kHid; idx += blockDim.x) {
