@@ -352,6 +352,7 @@ def run_ours(args):
         line["batched"] = batched_measurement(dev, n_env=args.batch_envs)
     if not args.no_newton:
         line["newton_step"] = newton_measurement(dev)
+        line["config1_indent"] = config1_measurement(dev)
         line["batched_step"] = batched_step_measurement(dev, n_env=args.step_envs, steps=10)
         if args.big_step_envs > 0:
             # the batched workload's full environment count, stepped: one tet layer per pad, since
@@ -785,6 +786,47 @@ def newton_measurement(dev, start_step=20, n_states=4):
                      "newton_iters_per_s": sum(iters) / (sum(times) / 1e3)}
         ctx.close()
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_step_median"] / out["mixed"]["ms_per_step_median"]
+    return out
+
+
+def config1_measurement(dev):
+    """The single-environment indent as specified (32x32-quad pad, 2 mm Neo-Hookean slab pressed
+    0.3 mm in 10 steps onto the rigid subdivision-3 icosphere, dhat 1e-4, kappa 1e5, h 1 ms,
+    vertex jitter 1e-5 m, seed 1), stepped on the GPU in plain FP64 and in mixed precision up
+    to the first step that fails.  Reported per step: status (0 converged to the 1e-6 residual;
+    4 infeasible, the state kept; 6 not converged within max_newton iterations), Newton and PCG
+    iterations, the final residual and the wall time.  The fifth step fails in both: a slave
+    edge closes on a master edge near the indenter's tip where no sample measures the gap, and
+    the additive CCD stops each iterate short of it (with such pairs ~1e-13 m apart, later
+    steps take tens of seconds in FP64, so the run stops at the first failure)."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    sc = S.tactile_indent()
+    top = torch.as_tensor(sc.dirichlet.astype(bool), device="cuda")
+    vd = torch.as_tensor(sc.v_dirichlet, device="cuda")
+    out = {"workload": "tactile_indent: 32x32-quad pad (1,089 surface verts, 2,048 slave tris x 4 samples), "
+                       "2 mm slab (4 tet layers) pressed 0.3 mm in 10 steps onto a subdivision-3 icosphere "
+                       "(1,280 tris, radius 5 mm); dhat 1e-4, kappa 1e5, h 1 ms, jitter 1e-5 m",
+           "n_vert": int(sc.X.shape[0]), "n_tet": int(sc.tets.shape[0]), "max_newton": sc.params["max_newton"]}
+    for prec in ("fp64", "mixed"):
+        ctx = binding.Context(sc, precision=prec, device=dev)
+        x = torch.as_tensor(sc.X.copy(), device="cuda")
+        v = vd.clone()
+        rows = []
+        for _ in range(sc.n_steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = ctx.newton_step(x, v)
+            torch.cuda.synchronize()
+            rows.append({"status": r["status"], "newton_iters": r["newton_iters"], "pcg_iters": r["pcg_iters"],
+                         "residual": r["residual"], "ms": round((time.perf_counter() - t0) * 1e3, 2)})
+            v[top] = vd[top]
+            if r["status"] != 0:
+                break
+        ctx.close()
+        out[prec] = {"steps": rows, "converged_steps": sum(q["status"] == 0 for q in rows),
+                     "first_failed_step": next((k for k, q in enumerate(rows) if q["status"] != 0), None)}
     return out
 
 
@@ -1256,7 +1298,7 @@ def main():
                     help="--mode profstep: the time step captured (gel_on_terrain press, or the batched step)")
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
-    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "batch", "batchstep", "patch",
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "config1", "batch", "batchstep", "patch",
                                                        "dualmap", "faceclip",
                                                        "mastergrad", "dense", "dense_passes", "peaks", "profstep"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
@@ -1290,6 +1332,8 @@ def main():
         print(json.dumps(patch_measurement(0)), flush=True)
     elif args.mode == "profstep":
         run_profile_step(args)
+    elif args.mode == "config1":
+        print(json.dumps(config1_measurement(0)), flush=True)
     elif args.mode == "batchstep":
         print(json.dumps(batched_step_measurement(0, n_env=args.step_envs, steps=max(1, args.steps),
                                                   layers=args.step_layers)), flush=True)
