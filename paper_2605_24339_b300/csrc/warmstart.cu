@@ -706,8 +706,17 @@ __global__ void k_reduce_part(const float* __restrict__ partial, int64_t np, int
                               float* __restrict__ out) {
     const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= L) return;
+    // sixteen loads in flight at a time, added in the same order p = 0, 1, ...
     float s = 0.0f;
-    for (int64_t p = 0; p < np; ++p) s += partial[p * stride + l];
+    int64_t p = 0;
+    for (; p + 16 <= np; p += 16) {
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) v[q] = partial[(p + q) * stride + l];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) s += v[q];
+    }
+    for (; p < np; ++p) s += partial[p * stride + l];
     out[l] = s;
 }
 
