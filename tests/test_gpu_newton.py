@@ -146,3 +146,39 @@ def test_newton_step_deterministic(B):
         outs.append(x.cpu().numpy())
         ctx.close()
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_config1_indent_converging_steps_match_oracle(B, oracle_mod):
+    """The single-environment indent at its specified size (32x32-quad pad,
+    4 tet layers, subdivision-3 icosphere, dhat 1e-4, kappa 1e5, h 1 ms,
+    jitter 1e-5 m): its first four steps, which the oracle converges, on the
+    GPU from the oracle's previous state each time.  FP64: same status and
+    Newton iteration count, positions within 1e-10 of the step's
+    displacement; mixed: converged, within 1e-7.  (The fifth step locks in
+    both, on a primitive pair no sample covers near the indenter's tip.)"""
+    sc = S.tactile_indent()
+    O = oracle_mod.Scene(sc)
+    sim = oracle_mod.Sim(O)
+    ctx = {p: B.Context(sc, precision=p) for p in ("fp64", "mixed")}
+    top = sc.dirichlet.astype(bool)
+    x = sc.X.copy()
+    v = sc.v_dirichlet.copy()
+    iters = []
+    for step in range(4):
+        xo, vo, st = sim.step(x, v)
+        assert st.status == 0, (step, st.status)
+        iters.append(st.newton_iters)
+        for prec, tol in (("fp64", 1e-10), ("mixed", 1e-7)):
+            xg, vg = dev(x), dev(v)
+            r = ctx[prec].newton_step(xg, vg)
+            assert r["status"] == 0 and r["residual"] <= sc.params["newton_tol"], (prec, step, r)
+            if prec == "fp64":
+                assert r["newton_iters"] == st.newton_iters, (step, r["newton_iters"], st.newton_iters)
+            e = rel_disp(xg.cpu().numpy(), xo, x)
+            assert e < tol, (prec, step, e)
+            np.testing.assert_array_equal(xg.cpu().numpy()[top], xo[top])
+        x, v = xo, vo.copy()
+        v[top] = sc.v_dirichlet[top]
+    print("config 1 oracle Newton iterations, steps 0-3:", iters)
+    for c in ctx.values():
+        c.close()
