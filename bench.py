@@ -353,6 +353,7 @@ def run_ours(args):
     if not args.no_newton:
         line["newton_step"] = newton_measurement(dev)
         line["config1_indent"] = config1_measurement(dev)
+        line["ccd_stress"] = ccd_stress_measurement(dev)
         line["batched_step"] = batched_step_measurement(dev, n_env=args.step_envs, steps=10)
         if args.big_step_envs > 0:
             # the batched workload's full environment count, stepped: one tet layer per pad, since
@@ -830,6 +831,46 @@ def config1_measurement(dev):
     return out
 
 
+def ccd_stress_measurement(dev, calls=10):
+    """The step bound on the CCD / line-search stress workload at its specified size: 64
+    environments, each a free 128x128-quad pad (0.25 mm, 4 tet layers) moving at U[0.5, 2] m/s
+    toward a closed 30x30x1 mm thin shell (100x100 quads a face) from 1 mm away, at a seeded
+    random rotation; h = 1 ms, so a step moves a pad 0.5-2 mm, up to twice the shell's thickness.
+    Times ipc_ccd_max_step for the whole batch on the first step's displacement h v (broad phase
+    of the swept boxes, Eq. (ccd)/(global_ccd) over the samples, additive CCD over the swept
+    primitive pairs), inputs resident, after one untimed call."""
+    import torch
+    from paper_2605_24339_b300 import binding
+    from paper_2605_24339_b300 import scenes as S
+    t0 = time.perf_counter()
+    sc, v0 = S.ccd_stress()
+    gen_s = time.perf_counter() - t0
+    ctx = binding.Context(sc, precision="mixed", device=dev)
+    x = torch.as_tensor(sc.X, device="cuda")
+    dx = torch.as_tensor(sc.params["h"] * v0, device="cuda")
+    y0 = torch.as_tensor(sc.Y0, device="cuda")
+    r = ctx.ccd_max_step(x, dx, y0)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(calls):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = ctx.ccd_max_step(x, dx, y0)
+        torch.cuda.synchronize()
+        times.append((time.perf_counter() - t1) * 1e3)
+    ctx.close()
+    ms = statistics.median(times)
+    pairs = int(r["n_pt"]) + int(r["n_ee"])
+    return {"workload": "ccd_stress: 64 envs, 128x128-quad free pads at 0.5-2 m/s toward closed 1 mm shells "
+                        "(100x100 quads a face), random rotations, h = 1 ms",
+            "n_env": 64, "slave_tris": int(sc.stris.shape[0]), "master_tris": int(sc.mtris.shape[0]),
+            "scene_build_s": round(gen_s, 1), "ms_per_call": ms, "ms_per_call_all": [round(t, 2) for t in times],
+            "alpha": r["alpha"], "alpha_lin": r["alpha_lin"], "alpha_accd": r["alpha_accd"],
+            "accd_pairs": {"point_triangle": int(r["n_pt"]), "edge_edge": int(r["n_ee"])},
+            "accd_pairs_per_s": pairs / (ms / 1e3), "swept_tris": int(r["swept_tris"]),
+            "iter_cap_hit": r["iter_cap_hit"]}
+
+
 def fingertip_step_scene(n_env, layers=2):
     """The batched time-step workload: n_env fingertip environments with
     tets (5 pads of 16-128 quads of 0.25 mm, ``layers`` tet layers, around a perturbed
@@ -1298,7 +1339,7 @@ def main():
                     help="--mode profstep: the time step captured (gel_on_terrain press, or the batched step)")
     ap.add_argument("--newton-quads", type=int, default=256,
                     help="--mode newton: gel pad quads per side (256 = the measured workload)")
-    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "config1", "batch", "batchstep", "patch",
+    ap.add_argument("--mode", default="bench", choices=["bench", "passes", "mlp", "newton", "config1", "ccd", "batch", "batchstep", "patch",
                                                        "dualmap", "faceclip",
                                                        "mastergrad", "dense", "dense_passes", "peaks", "profstep"],
                     help="passes / mlp / newton: run --steps untimed contact passes, network "
@@ -1334,6 +1375,8 @@ def main():
         run_profile_step(args)
     elif args.mode == "config1":
         print(json.dumps(config1_measurement(0)), flush=True)
+    elif args.mode == "ccd":
+        print(json.dumps(ccd_stress_measurement(0)), flush=True)
     elif args.mode == "batchstep":
         print(json.dumps(batched_step_measurement(0, n_env=args.step_envs, steps=max(1, args.steps),
                                                   layers=args.step_layers)), flush=True)
