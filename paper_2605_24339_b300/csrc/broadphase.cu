@@ -1143,11 +1143,24 @@ k_accd_pairs(SceneView S, Params P, PairList L, const double* __restrict__ x,
                 P12[3 * q + c] = Pd ? Pd[3 * (int64_t)va[q] + c] : 0.0;
             }
         }
+        // ACCD's tc: the smallest bound known so far, this thread's or one
+        // published by any thread (alpha_bits only ever holds pair results or
+        // its initial 1).  A pair whose time of impact lies above tc stops as
+        // soon as its advance passes tc and returns tc, which cannot lower the
+        // minimum; a pair whose result lies below tc runs exactly as with
+        // tc = 1 (its advances never pass tc), so the minimum is bitwise that
+        // of running every pair to tc = 1.
+        unsigned long long* pub = alpha_stride > 0 ? alpha_bits + (int64_t)alpha_stride * env : alpha_bits;
+        const double known = __longlong_as_double((long long)*reinterpret_cast<volatile unsigned long long*>(pub));
+        const double tc = dmin_(best, dmin_(known, 1.0));
         int it;
-        const double r = accd(kind == 2 ? 1 : 0, X12, P12, P.ccd_slack, 1.0, P.ccd_max_iter, &it);
+        const double r = accd(kind == 2 ? 1 : 0, X12, P12, P.ccd_slack, tc, P.ccd_max_iter, &it);
         if (kind == 2) ++n_ee; else ++n_pt;
         cap_hit |= it >= P.ccd_max_iter;
-        best = dmin_(best, r);
+        if (r < best) {
+            best = r;
+            if (r < known) atomic_min_pos(pub, r);   // let the other threads stop early too
+        }
     }
     if (alpha_stride > 0 && env >= 0 && best < 1.0) atomic_min_pos(alpha_bits + (int64_t)alpha_stride * env, best);
     if (alpha_stride > 0) best = 1.0;
