@@ -132,7 +132,10 @@ typedef struct {
     double alpha_lin;      /* Eq. (global_ccd); +inf when no sample closes */
     double alpha_accd;     /* additive CCD minimum over primitive pairs */
     int64_t n_pairs_pt, n_pairs_ee;
-    int32_t iter_cap_hit;  /* 1 if some pair stopped at ccd_max_iter */
+    int32_t iter_cap_hit;  /* 1 if some pair stopped at ccd_max_iter.  Pairs run with the
+                              smallest bound found so far as their upper time, so a pair whose
+                              time of impact lies above the minimum may stop before the cap;
+                              the flag then reports the pairs that could set alpha_accd */
     int64_t swept_tris;    /* slave tris whose swept box reached a non-empty grid cell */
 } ipc_ccd_info;
 
